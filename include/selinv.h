@@ -1,0 +1,227 @@
+/*
+ * selinv.h -- C ABI of a GB300 (sm_103a) supernodal selected-inversion library.
+ *
+ * Problem (Alg. 1 and Alg. 2 of Jacquelin, Lin, Jia, Zhao, Yang,
+ * "A left-looking selected inversion algorithm and task parallelism on shared
+ * memory systems"): given a sparse symmetric or complex symmetric matrix A
+ * (already symmetrically permuted) with supernodal factorization
+ * A = L D L^T, compute the entries of A^{-1} on the pattern of L + L^T
+ * ("selected elements of A^{-1} such that L_{I,J} is not an empty block",
+ * output of Alg. 1), by the root-to-leaf elimination-tree recursion
+ *     A^{-1}_{C,K} = -A^{-1}_{C,C} Lhat_{C,K},   Lhat_{C,K} = L_{C,K} L_{K,K}^{-1}
+ *     A^{-1}_{K,K} = L_KK^{-T} D_K^{-1} L_KK^{-1} - Lhat_{C,K}^T A^{-1}_{C,K}
+ * with the diagonal block symmetrized (Sec. II-C).
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ *  - Integers: column/row indices int32, offsets int64.
+ *  - Supernode K has s_K columns super_ptr[K] .. super_ptr[K+1]-1 and a row
+ *    list rows(K) = its own s_K columns followed by its c_K rows C below them,
+ *    ascending (C = {I > K : L_{I,K} != 0} of Alg. 1 at the element level).
+ *  - Panel layout ("panels"): supernode K owns a column-major (s+c) x s block
+ *    with leading dimension s+c whose rows are rows(K); panels follow each
+ *    other in supernode order; selinv_plan_panel_offset(K) gives the first
+ *    element.  L, the cotangents and A^{-1} all use this layout.
+ *      L: the diagonal block is unit lower triangular; its diagonal and
+ *         strictly upper part are never read.
+ *      A^{-1}: the diagonal block is written in full (symmetric), rows s..
+ *         hold A^{-1}_{C,K}; together this is the lower part of A^{-1} on the
+ *         pattern of L, the upper part being its transpose.
+ *  - Transposes are plain for complex symmetric matrices (A = A^T), as the
+ *    configured workloads are complex symmetric, not Hermitian.
+ *  - Element types: SELINV_F64 = double, SELINV_C128 = two doubles (re, im).
+ *  - Device pointers are caller-owned (the library never frees them) and must
+ *    be 16-byte aligned.  Host arrays passed in are copied; the caller keeps
+ *    ownership.
+ *  - Numeric calls are asynchronous on the given cudaStream_t (passed as
+ *    void*; NULL = legacy default stream).  Errors found on the device
+ *    (timeouts of bounded waits, zero pivots, non-finite values) are latched
+ *    in a per-plan status word read by selinv_status() after synchronizing.
+ *  - Every call returns SELINV_OK (0) or a negative error code.
+ */
+#ifndef SELINV_H
+#define SELINV_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SELINV_OK 0
+#define SELINV_ERR_INVALID_ARG (-1)
+#define SELINV_ERR_BAD_ETREE (-2)    /* parent index not > child, or out of range   */
+#define SELINV_ERR_BAD_PATTERN (-3)  /* rows not sorted / not closed under the tree */
+#define SELINV_ERR_ZERO_PIVOT (-4)
+#define SELINV_ERR_NONFINITE (-5)
+#define SELINV_ERR_OOM (-6)
+#define SELINV_ERR_CUDA (-7)
+#define SELINV_ERR_TIMEOUT (-8)      /* a bounded device wait ran out              */
+#define SELINV_ERR_UNSUPPORTED (-9)
+
+typedef struct selinv_plan_s *selinv_plan;          /* opaque, owned by the library */
+typedef struct selinv_analysis_s *selinv_analysis;  /* opaque, owned by the library */
+
+typedef enum { SELINV_F64 = 0, SELINV_C128 = 1 } selinv_dtype;
+
+typedef enum {
+    SELINV_SCHED_PLAIN = 0,      /* one launch chain per supernode, K = N..1            */
+    SELINV_SCHED_LEVEL = 1,      /* one grouped launch per elimination-tree level        */
+    SELINV_SCHED_PERSISTENT = 2  /* one persistent launch, per-supernode completion flags */
+} selinv_schedule;
+
+typedef struct {
+    int symmetrize;        /* 1: A^{-1}_KK <- (X + X^T)/2 (Sec. II-C); default 1        */
+    int schedule;          /* selinv_schedule; default SELINV_SCHED_LEVEL               */
+    int autotune;          /* 1: pick kernel variants per size class by timing; default 0 */
+    int debug_checks;      /* 1: scan inputs for non-finite values; default 0           */
+    long long spin_limit;  /* iteration cap of every device spin-wait; default 1<<26     */
+    int use_graph;         /* 1: capture the level schedule in a CUDA graph; default 1  */
+    int fast_contraction;  /* 1: large contractions run FP64-exact on bf16 tensor cores
+                              (error-free slicing, FP64 accumulation); 0: DFMA only.
+                              default 1                                                 */
+} selinv_opts;
+
+/* Fills *opts with the defaults listed above. */
+void selinv_default_opts(selinv_opts *opts);
+
+/* ---------------------------------------------------------------------------
+ * Symbolic analysis (prerequisite; Sec. II-A supernodes, Sec. I/II-B tree).
+ * From the lower triangle of the (already permuted) matrix, CSC with rows
+ * ascending and row >= column: elimination tree, the column structure of L,
+ * and the supernode partition.
+ *   kind 0: fundamental supernodes of at most `cap` columns.
+ *   kind 1: fundamental, then relaxed: the group ending at supernode K merges
+ *           into K+1 when K+1 is its parent, the merged group has <= cap
+ *           columns and explicit zeros <= fill x its stored lower entries.
+ * Results are read with selinv_analysis_get:
+ *   field 0 parent[n] (int32, column etree), 3 super_ptr[nsuper+1] (int32),
+ *   4 sparent[nsuper] (int32), 5 rowptr[nsuper+1] (int64), 6 rows (int32),
+ *   7 -> returns nsuper, 8 -> returns nnz of L without relaxation.
+ * selinv_analysis_get returns the element count of the field (or the value
+ * for 7/8) and copies it to dst when dst != NULL; <0 on a bad field.
+ * Errors: INVALID_ARG (n < 0, cap < 1, null pointers), BAD_PATTERN (a row
+ * index < its column or >= n, or unsorted), OOM.
+ * ------------------------------------------------------------------------- */
+int selinv_analyse(int32_t n, const int64_t *colptr, const int32_t *rowind, int kind,
+                   int32_t cap, double fill, selinv_analysis *out);
+int64_t selinv_analysis_get(selinv_analysis a, int field, void *dst);
+void selinv_analysis_destroy(selinv_analysis a);
+
+/* ---------------------------------------------------------------------------
+ * selinv_symbolic: build the device-resident plan (Alg. 1 "find the
+ * collection of indices C", made explicit once): elimination-tree level sets,
+ * the split of every C into runs owned by one ancestor supernode, relative
+ * row indices of C inside each owner's row list (the gather lists of
+ * A^{-1}_{C,C}), work-item tables, and the scratch buffers of the numeric
+ * phase.  Host arrays (copied):
+ *   n, nsuper; super_ptr[nsuper+1] (super_ptr[0] = 0, increasing,
+ *   super_ptr[nsuper] = n); sparent[nsuper] (supernodal etree parent, -1 =
+ *   root, sparent[K] > K); rowptr[nsuper+1] (int64 offsets into rowind);
+ *   rowind: rows(K) as described above.
+ * opts may be NULL (defaults).  The plan lives on the current CUDA device.
+ * Errors: INVALID_ARG, BAD_ETREE (sparent[K] <= K or >= nsuper, or the first
+ * row below K not owned by sparent[K]), BAD_PATTERN (rows(K) not starting
+ * with K's columns, not ascending, or some C entry of K missing from the row
+ * list of its owner: the closure property the recursion relies on), OOM, CUDA.
+ * ------------------------------------------------------------------------- */
+int selinv_symbolic(int32_t n, int32_t nsuper, const int32_t *super_ptr, const int32_t *sparent,
+                    const int64_t *rowptr, const int32_t *rowind, const selinv_opts *opts,
+                    selinv_plan *out_plan);
+
+/* Releases the plan and all device memory it owns.  NULL is ignored. */
+void selinv_plan_destroy(selinv_plan plan);
+
+/* Number of panel elements (= elements of L, of A^{-1}, of every cotangent). */
+int64_t selinv_plan_nnz(selinv_plan plan);
+/* First element of supernode K's panel; -1 if K is out of range. */
+int64_t selinv_plan_panel_offset(selinv_plan plan, int32_t K);
+/* Algorithmic work of one selected inversion: flops F = sum_K 2c^2s + 2cs^2 +
+ * cs^2 + s^3 (real; complex work is 4x), bytes B = sum_K w (c(c+1)/2 +
+ * 2(c+s)s + s) with w = 8 (f64) or 16 (c128).  Either pointer may be NULL. */
+int selinv_plan_stats(selinv_plan plan, selinv_dtype dtype, double *flops, double *bytes);
+/* Copies one host-side plan array (for inspection and tests):
+ *   0 level[nsuper] int32 (root 0)   1 seg_ptr[nsuper+1] int64
+ *   2 seg_owner int32   3 seg_start int32   4 seg_coloff int32
+ *   5 rel_ptr[nseg+1] int64          6 relidx int32
+ *   7 level_ptr[nlevels+1] int64     8 level_list[nsuper] int32
+ *   9 panel_off[nsuper+1] int64
+ * Returns the element count, or <0 on a bad field.  dst may be NULL. */
+int64_t selinv_plan_get(selinv_plan plan, int field, void *dst);
+/* Changes the schedule / options of an existing plan. */
+int selinv_plan_set_opts(selinv_plan plan, const selinv_opts *opts);
+
+/* ---------------------------------------------------------------------------
+ * selinv_numeric: the selected inversion itself (Alg. 1 with the
+ * normalization of its first loop, symmetrization of Sec. II-C).
+ *   L_dev   panels of L (unit-lower diagonal blocks), device
+ *   D_dev   [n] diagonal of D, device
+ *   Ainv_dev panels, device, caller-allocated (selinv_plan_nnz elements);
+ *            every element is written.
+ * Not reentrant per plan: calls on one plan must not overlap on the GPU
+ * (they share the plan's scratch); use one plan per concurrent stream.
+ * Errors: INVALID_ARG, CUDA; device-side errors via selinv_status.
+ * ------------------------------------------------------------------------- */
+int selinv_numeric(selinv_plan plan, selinv_dtype dtype, const void *L_dev, const void *D_dev,
+                   void *Ainv_dev, void *cuda_stream);
+
+/* Batched selected inversion: nitems independent problems (e.g. pole shifts
+ * A - z_l S sharing one pattern, or different matrices), all tree levels of
+ * all items merged into one level-scheduled (or persistent) launch sequence.
+ * plans[i] may repeat.  Arrays are host arrays of device pointers.  The
+ * batch's schedule comes from plans[0]'s options. */
+int selinv_numeric_batched(int nitems, const selinv_plan *plans, const selinv_dtype *dtypes,
+                           const void *const *L, const void *const *D, void *const *Ainv,
+                           void *cuda_stream);
+
+/* ---------------------------------------------------------------------------
+ * Prerequisite factorization A = L D L^T without pivoting (Sec. IV uses a
+ * supernodal factorization with a symmetric permutation and no dynamic
+ * pivoting).  The matrix pattern must first be attached to the plan:
+ * selinv_plan_set_matrix(plan, n, colptr, rowind) with the same lower CSC
+ * given to selinv_analyse (host arrays, copied).  A_vals_dev holds the values
+ * of that CSC on the device.  Writes L (panels) and D.  A zero pivot latches
+ * SELINV_ERR_ZERO_PIVOT in the status word (the factors are then invalid).
+ * ------------------------------------------------------------------------- */
+int selinv_plan_set_matrix(selinv_plan plan, int32_t n, const int64_t *colptr,
+                           const int32_t *rowind);
+int selinv_factor(selinv_plan plan, selinv_dtype dtype, const void *A_vals_dev, void *L_dev,
+                  void *D_dev, void *cuda_stream);
+
+/* ---------------------------------------------------------------------------
+ * Reverse mode (no counterpart in the paper; the chain rule through the
+ * steps of Alg. 1 taken leaves-to-root, recomputing the gathers of
+ * A^{-1}_{C,C}).  F64 only.
+ *   selinv_adjoint: given the cotangent Ainv_bar of every stored lower entry of
+ *     A^{-1} (panels; the strictly upper part of diagonal blocks is ignored),
+ *     returns L_bar (panels, strictly lower entries) and D_bar [n].  Uses the
+ *     forward outputs L, D, Ainv.  Ainv_bar is not modified (the plan keeps a
+ *     working copy).
+ *   selinv_factor_adjoint: given L_bar, D_bar, returns A_bar on the stored
+ *     lower entries of A's CSC pattern (attached by selinv_plan_set_matrix):
+ *     the derivative with respect to each stored lower entry a_ij (i >= j) of
+ *     the symmetric matrix.
+ * ------------------------------------------------------------------------- */
+int selinv_adjoint(selinv_plan plan, selinv_dtype dtype, const void *L_dev, const void *D_dev,
+                   const void *Ainv_dev, const void *Ainv_bar_dev, void *L_bar_dev,
+                   void *D_bar_dev, void *cuda_stream);
+int selinv_factor_adjoint(selinv_plan plan, selinv_dtype dtype, const void *L_dev,
+                          const void *D_dev, const void *L_bar_dev, const void *D_bar_dev,
+                          void *A_bar_vals_dev, void *cuda_stream);
+
+/* Device status word of the plan after asynchronous work (synchronizes the
+ * plan's last stream, then returns and clears the latched code: SELINV_OK,
+ * SELINV_ERR_TIMEOUT, SELINV_ERR_ZERO_PIVOT or SELINV_ERR_NONFINITE). */
+int selinv_status(selinv_plan plan);
+
+/* Static text for an error code. */
+const char *selinv_error_string(int code);
+
+/* Number of kernel launches the library issued since load (for accounting). */
+int64_t selinv_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SELINV_H */

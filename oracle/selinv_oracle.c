@@ -1,0 +1,39 @@
+/*
+ * CPU oracle for supernodal selected inversion (Jacquelin, Lin, Jia, Zhao,
+ * Yang, "A left-looking selected inversion algorithm and task parallelism on
+ * shared memory systems").
+ *
+ * TEST INFRASTRUCTURE ONLY: only the tests, the smoke check and the
+ * CPU-baseline leg of the benchmark load this library.  It is plain C with
+ * no BLAS, written from the paper's definitions and algorithms, and shares
+ * no code with the GPU library.  Real values are double, complex values are
+ * double _Complex (complex symmetric: plain transposes).
+ *
+ * Entry points (suffix _d: real, _z: complex):
+ *   orc_symbolic / orc_sym_get / orc_sym_free / orc_plan  (oracle_symbolic.c)
+ *   orc_ldlt_*          supernodal-pattern LDL^T, no pivoting (Sec. IV prerequisite)
+ *   orc_selinv_*        Alg. 1 (pull), symmetrized diagonal blocks (Sec. II-C)
+ *   orc_selinv_push_*   Alg. 2 (left-looking push: outer/inner products)
+ *   orc_selinv_adjoint_*, orc_ldlt_adjoint_*   reverse mode of the two above
+ */
+#include <complex.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define CAT_(a, b) a##b
+#define CAT(a, b) CAT_(a, b)
+
+#define T double
+#define SFX _d
+#include "oracle_numeric.inc"
+#undef T
+#undef SFX
+
+#define T double _Complex
+#define SFX _z
+#include "oracle_numeric.inc"
+#undef T
+#undef SFX
+
+int orc_version(void) { return 1; }
