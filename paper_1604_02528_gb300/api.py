@@ -1,0 +1,98 @@
+"""Convenience layer over the C ABI: one object per sparsity pattern.
+
+    ctx = SelInvContext(n, colptr, rowind, kind="relaxed", cap=128, fill=0.1)
+    L, D = ctx.factor(A_vals)          # GPU LDL^T (prerequisite)
+    Z = ctx.selinv(L, D)               # selected inverse, panel layout
+
+All arithmetic runs in the native library; this module only allocates torch
+buffers and forwards pointers.
+"""
+from __future__ import annotations
+
+from typing import Optional, Tuple
+
+import numpy as np
+
+from . import _native as N
+
+KIND = {"fundamental": 0, "relaxed": 1}
+
+
+def torch_dtype(dtype: int):
+    import torch
+    return torch.complex128 if dtype == N.SELINV_C128 else torch.float64
+
+
+def selinv_dtype_of(t) -> int:
+    import torch
+    if t.dtype == torch.complex128:
+        return N.SELINV_C128
+    if t.dtype == torch.float64:
+        return N.SELINV_F64
+    raise TypeError(f"unsupported dtype {t.dtype}: float64 or complex128")
+
+
+class SelInvContext:
+    """Symbolic analysis + device plan of one lower-CSC pattern."""
+
+    def __init__(self, n: int, colptr, rowind, kind: str = "fundamental", cap: int = 64,
+                 fill: float = 0.0, opts: Optional[N.selinv_opts] = None):
+        self.n = int(n)
+        self.colptr = np.ascontiguousarray(colptr, dtype=np.int64)
+        self.rowind = np.ascontiguousarray(rowind, dtype=np.int32)
+        self.analysis = N.selinv_analyse(self.n, self.colptr, self.rowind, KIND[kind], cap, fill)
+        a = self.analysis
+        self.nsuper = a["nsuper"]
+        self.plan = N.selinv_symbolic(self.n, self.nsuper, a["super_ptr"], a["sparent"],
+                                      a["rowptr"], a["rows"], opts)
+        self._matrix_attached = False
+
+    @classmethod
+    def from_problem(cls, p, opts: Optional[N.selinv_opts] = None) -> "SelInvContext":
+        sn = p.supernodes
+        return cls(p.n, p.colptr, p.rowind, str(sn["kind"]), int(sn["cap"]), float(sn["fill"]), opts)
+
+    @property
+    def nnz(self) -> int:
+        return self.plan.nnz
+
+    def stats(self, dtype: int) -> Tuple[float, float]:
+        return N.selinv_plan_stats(self.plan, dtype)
+
+    def empty_panels(self, dtype: int, device="cuda"):
+        import torch
+        return torch.empty(self.nnz, dtype=torch_dtype(dtype), device=device)
+
+    def set_options(self, **kw):
+        o = N.selinv_default_opts()
+        for k, v in kw.items():
+            setattr(o, k, v)
+        N.selinv_plan_set_opts(self.plan, o)
+
+    def attach_matrix(self):
+        if not self._matrix_attached:
+            N.selinv_plan_set_matrix(self.plan, self.n, self.colptr, self.rowind)
+            self._matrix_attached = True
+
+    def factor(self, A_vals, L=None, D=None, stream=None):
+        """L (panels) and D of A = L D L^T from A's CSC values on the device."""
+        import torch
+        dt = selinv_dtype_of(A_vals)
+        self.attach_matrix()
+        if L is None:
+            L = self.empty_panels(dt, A_vals.device)
+        if D is None:
+            D = torch.empty(self.n, dtype=A_vals.dtype, device=A_vals.device)
+        N.selinv_factor(self.plan, dt, A_vals, L, D, stream)
+        return L, D
+
+    def selinv(self, L, D, out=None, stream=None):
+        """Selected inverse on the pattern of L (panel layout)."""
+        dt = selinv_dtype_of(L)
+        if out is None:
+            out = self.empty_panels(dt, L.device)
+        N.selinv_numeric(self.plan, dt, L, D, out, stream)
+        return out
+
+    def status(self) -> int:
+        return N.selinv_status(self.plan)

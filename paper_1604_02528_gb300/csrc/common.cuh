@@ -1,0 +1,120 @@
+// Internal types shared by the host plan code and the sm_103a kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "selinv.h"
+
+namespace selinv {
+
+// complex128 as two doubles; plain (non-conjugating) transposes throughout,
+// since the configured complex matrices are complex symmetric (A = A^T).
+struct __align__(16) zd {
+    double x, y;
+};
+
+__host__ __device__ inline zd make_zd(double a, double b) { zd r; r.x = a; r.y = b; return r; }
+
+template <typename T> struct Sc;
+template <> struct Sc<double> {
+    static __host__ __device__ inline double zero() { return 0.0; }
+    static __host__ __device__ inline double one() { return 1.0; }
+    static constexpr int kWords = 1;  // doubles per element
+};
+template <> struct Sc<zd> {
+    static __host__ __device__ inline zd zero() { return make_zd(0.0, 0.0); }
+    static __host__ __device__ inline zd one() { return make_zd(1.0, 0.0); }
+    static constexpr int kWords = 2;
+};
+
+// acc += a * b
+__host__ __device__ inline void madd(double &acc, double a, double b) { acc = fma(a, b, acc); }
+__host__ __device__ inline void madd(zd &acc, zd a, zd b) {
+    acc.x = fma(a.x, b.x, fma(-a.y, b.y, acc.x));
+    acc.y = fma(a.x, b.y, fma(a.y, b.x, acc.y));
+}
+// acc -= a * b
+__host__ __device__ inline void msub(double &acc, double a, double b) { acc = fma(-a, b, acc); }
+__host__ __device__ inline void msub(zd &acc, zd a, zd b) {
+    acc.x = fma(-a.x, b.x, fma(a.y, b.y, acc.x));
+    acc.y = fma(-a.x, b.y, fma(-a.y, b.x, acc.y));
+}
+__host__ __device__ inline double add(double a, double b) { return a + b; }
+__host__ __device__ inline zd add(zd a, zd b) { return make_zd(a.x + b.x, a.y + b.y); }
+__host__ __device__ inline double sub(double a, double b) { return a - b; }
+__host__ __device__ inline zd sub(zd a, zd b) { return make_zd(a.x - b.x, a.y - b.y); }
+__host__ __device__ inline double mul(double a, double b) { return a * b; }
+__host__ __device__ inline zd mul(zd a, zd b) {
+    return make_zd(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__host__ __device__ inline double neg(double a) { return -a; }
+__host__ __device__ inline zd neg(zd a) { return make_zd(-a.x, -a.y); }
+__host__ __device__ inline double half(double a) { return 0.5 * a; }
+__host__ __device__ inline zd half(zd a) { return make_zd(0.5 * a.x, 0.5 * a.y); }
+__host__ __device__ inline double scal(double a, double s) { return a * s; }
+__host__ __device__ inline zd scal(zd a, double s) { return make_zd(a.x * s, a.y * s); }
+// 1 / a (complex: by the textbook formula conj(a) / |a|^2 with scaling)
+__host__ __device__ inline double recip(double a) { return 1.0 / a; }
+__host__ __device__ inline zd recip(zd a) {
+    double m = fabs(a.x) > fabs(a.y) ? fabs(a.x) : fabs(a.y);
+    double s = m > 0 ? 1.0 / m : 0.0;
+    double ax = a.x * s, ay = a.y * s;
+    double d = ax * ax + ay * ay;
+    return make_zd(ax * s / d, -ay * s / d);
+}
+__host__ __device__ inline bool is_zero(double a) { return a == 0.0; }
+__host__ __device__ inline bool is_zero(zd a) { return a.x == 0.0 && a.y == 0.0; }
+__host__ __device__ inline bool finite_val(double a) { return isfinite(a); }
+__host__ __device__ inline bool finite_val(zd a) { return isfinite(a.x) && isfinite(a.y); }
+
+// Device view of one problem (one plan + one set of numeric buffers).
+struct ProbDesc {
+    // plan (device arrays)
+    const int32_t *super_ptr;   // [ns+1]
+    const int64_t *rowptr;      // [ns+1]
+    const int32_t *rows;        // row lists
+    const int64_t *panel_off;   // [ns+1]
+    const int64_t *colbase;     // [n] panel address of column j in its owner's panel
+    const int64_t *relbase;     // [rowptr[ns]] per C position: rel_ptr(segment) - seg_start
+    const int32_t *relidx;      // relative row indices
+    const int64_t *linv_off;    // [ns+1] offsets of L_KK^{-1} blocks (s*s each)
+    const int64_t *part_off;    // [ns] offset of K's split partials inside its level
+    const int32_t *sparent;     // [ns]
+    // numeric buffers
+    const void *L;              // panels
+    const void *D;              // [n]
+    void *Z;                    // panels (output A^{-1})
+    void *LD;                   // panels: Dinv_K in the diagonal block, Lhat below
+    void *Linv;                 // sum s^2
+    void *partial;              // split-k partials of A^{-1}_KK
+    int *counter;               // [ns] tiles done per supernode
+    int *done;                  // [ns] completion flags (persistent schedule)
+    int *status;                // latched error code
+    int32_t ns, n;
+    int32_t dtype;              // selinv_dtype
+    int32_t symmetrize;
+};
+
+// One unit of work of a tiled kernel: rows [tile*TM, tile*TM+TM) of C(K).
+struct Item {
+    int32_t prob;
+    int32_t K;
+    int32_t tile;
+    int32_t ntiles;
+};
+
+constexpr int kTM = 64;   // rows of C per work item
+
+// Size class of a supernode's width s: the column tile TN of its kernels.
+inline int bucket_of(int s) {
+    if (s <= 8) return 0;
+    if (s <= 16) return 1;
+    if (s <= 32) return 2;
+    if (s <= 64) return 3;
+    return 4;
+}
+constexpr int kNumBuckets = 5;
+constexpr int kBucketTN[kNumBuckets] = {8, 16, 32, 64, 128};
+
+}  // namespace selinv

@@ -1,0 +1,405 @@
+// sm_103a kernels of the selected-inversion traversal (Alg. 1 of the paper):
+//   k_linv    L_KK^{-1} and Dinv_K = L_KK^{-T} D_K^{-1} L_KK^{-1}       (Alg. 1 loop 1)
+//   k_lhat    Lhat_{C,K} = L_{C,K} L_KK^{-1}, tiled over rows of C       (Alg. 1 loop 1)
+//   k_selinv  A^{-1}_{C,K} = -A^{-1}_{C,C} Lhat_{C,K} with the gather of
+//             A^{-1}_{C,C} from the ancestors' panels fused into the GEMM,
+//             then the split contribution Lhat^T A^{-1}_{C,K} of every row
+//             tile, reduced in a fixed order by the last tile of K into
+//             A^{-1}_KK = Dinv_K - Lhat^T A^{-1}_{C,K}, symmetrized (Sec. II-C).
+// Every kernel works on a list of work items that may mix supernodes of
+// several problems (batched pole shifts / matrices) at one tree level.
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+#include "launch.h"
+
+namespace selinv {
+
+constexpr int kThreads = 256;
+constexpr int kTK = 16;
+
+__device__ inline void latch_status(int *status, int code) {
+    if (status) atomicCAS(status, 0, code);
+}
+
+// loads that bypass L1 (data written by other CTAs of the same launch)
+__device__ inline double ldcg(const double *p) { return __ldcg(p); }
+__device__ inline zd ldcg(const zd *p) {
+    const double2 v = __ldcg(reinterpret_cast<const double2 *>(p));
+    return make_zd(v.x, v.y);
+}
+
+// ---------------------------------------------------------------------------
+// k_linv: one CTA per supernode.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(128) k_linv(const ProbDesc *__restrict__ descs,
+                                              const int2 *__restrict__ work, int nwork) {
+    const int w = blockIdx.x;
+    if (w >= nwork) return;
+    const ProbDesc &P = descs[work[w].x];
+    const int K = work[w].y;
+    const int fc = P.super_ptr[K];
+    const int s = P.super_ptr[K + 1] - fc;
+    const int64_t ld = P.rowptr[K + 1] - P.rowptr[K];
+    const T *L = static_cast<const T *>(P.L) + P.panel_off[K];
+    const T *D = static_cast<const T *>(P.D) + fc;
+    T *Li = static_cast<T *>(P.Linv) + P.linv_off[K];
+    T *LD = static_cast<T *>(P.LD) + P.panel_off[K];
+    // column j of L_KK^{-1}: forward substitution with the unit lower L_KK
+    for (int j = threadIdx.x; j < s; j += blockDim.x) {
+        T *x = Li + (int64_t)j * s;
+        for (int i = 0; i < j; i++) x[i] = Sc<T>::zero();
+        x[j] = Sc<T>::one();
+        for (int i = j + 1; i < s; i++) {
+            T acc = Sc<T>::zero();
+            for (int k = j; k < i; k++) madd(acc, L[(int64_t)k * ld + i], x[k]);
+            x[i] = neg(acc);
+        }
+        if (is_zero(D[j]) || !finite_val(D[j])) latch_status(P.status, SELINV_ERR_ZERO_PIVOT);
+    }
+    __syncthreads();
+    // Dinv(i, j) = sum_{k >= max(i, j)} Linv(k, i) Linv(k, j) / D_k
+    for (int e = threadIdx.x; e < s * s; e += blockDim.x) {
+        const int i = e % s, j = e / s;
+        const int k0 = i > j ? i : j;
+        T acc = Sc<T>::zero();
+        for (int k = k0; k < s; k++)
+            madd(acc, mul(Li[(int64_t)i * s + k], recip(D[k])), Li[(int64_t)j * s + k]);
+        LD[(int64_t)j * ld + i] = acc;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// register-tiled GEMM core: acc[MI][NJ] += A(TM x kdim) * B(kdim x TN),
+// A and B staged tile by tile (TK) in shared memory by loader functors.
+// Thread (tx, ty) owns rows ty + TY*i and columns tx + TX*j.
+// ---------------------------------------------------------------------------
+template <int TN> struct Shape {
+    static constexpr int TX = TN < 16 ? TN : 16;
+    static constexpr int TY = kThreads / TX;
+    static constexpr int MI = kTM / TY;
+    static constexpr int NJ = TN / TX;
+};
+
+template <typename T, int TN, class LA, class LB>
+__device__ inline void tile_gemm(int kdim, const LA &la, const LB &lb,
+                                 T (&acc)[Shape<TN>::MI][Shape<TN>::NJ], T *As, T *Bs) {
+    using S = Shape<TN>;
+    const int tx = threadIdx.x % S::TX, ty = threadIdx.x / S::TX;
+    for (int k0 = 0; k0 < kdim; k0 += kTK) {
+        __syncthreads();
+        la(k0, As);
+        lb(k0, Bs);
+        __syncthreads();
+#pragma unroll 4
+        for (int kk = 0; kk < kTK; kk++) {
+            T a[S::MI], b[S::NJ];
+#pragma unroll
+            for (int i = 0; i < S::MI; i++) a[i] = As[kk * kTM + ty + S::TY * i];
+#pragma unroll
+            for (int j = 0; j < S::NJ; j++) b[j] = Bs[kk * TN + tx + S::TX * j];
+#pragma unroll
+            for (int i = 0; i < S::MI; i++)
+#pragma unroll
+                for (int j = 0; j < S::NJ; j++) madd(acc[i][j], a[i], b[j]);
+        }
+    }
+}
+
+// B loader: a column-major block X (ld ldx) restricted to kdim rows, s columns
+template <typename T, int TN> struct LoadColMajor {
+    const T *X;
+    int64_t ldx;
+    int kdim, s;
+    __device__ void operator()(int k0, T *Bs) const {
+        for (int e = threadIdx.x; e < kTK * TN; e += kThreads) {
+            const int kk = e % kTK, j = e / kTK;
+            const int k = k0 + kk;
+            Bs[kk * TN + j] = (k < kdim && j < s) ? X[(int64_t)j * ldx + k] : Sc<T>::zero();
+        }
+    }
+};
+
+// ---------------------------------------------------------------------------
+// k_lhat: Lhat(p, :) = L(s + p, :) L_KK^{-1} for the TM rows of one item.
+// ---------------------------------------------------------------------------
+template <typename T, int TN> struct LoadPanelRows {  // A = L rows s+p0.., k = column of K
+    const T *L;
+    int64_t ld;
+    int s, p0, c;
+    __device__ void operator()(int k0, T *As) const {
+        for (int e = threadIdx.x; e < kTK * kTM; e += kThreads) {
+            const int p = e % kTM, kk = e / kTM;
+            const int k = k0 + kk, pr = p0 + p;
+            As[kk * kTM + p] = (k < s && pr < c) ? L[(int64_t)k * ld + s + pr] : Sc<T>::zero();
+        }
+    }
+};
+
+template <typename T, int TN> __host__ __device__ constexpr int smem_a_elems() { return kTK * (kTM > TN ? kTM : TN); }
+template <typename T, int TN> __host__ __device__ constexpr size_t smem_bytes() {
+    return sizeof(T) * (size_t)(smem_a_elems<T, TN>() + kTK * TN);
+}
+
+template <typename T, int TN>
+__global__ void __launch_bounds__(kThreads) k_lhat(const ProbDesc *__restrict__ descs,
+                                                   const Item *__restrict__ items, int nitems) {
+    using S = Shape<TN>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *As = reinterpret_cast<T *>(smem_raw);
+    T *Bs = As + smem_a_elems<T, TN>();
+    const int w = blockIdx.x;
+    if (w >= nitems) return;
+    const Item it = items[w];
+    const ProbDesc &P = descs[it.prob];
+    const int K = it.K;
+    const int s = P.super_ptr[K + 1] - P.super_ptr[K];
+    const int64_t ld = P.rowptr[K + 1] - P.rowptr[K];
+    const int c = (int)(ld - s);
+    const int p0 = it.tile * kTM;
+    const T *L = static_cast<const T *>(P.L) + P.panel_off[K];
+    const T *Li = static_cast<const T *>(P.Linv) + P.linv_off[K];
+    T *LD = static_cast<T *>(P.LD) + P.panel_off[K];
+    T acc[S::MI][S::NJ];
+#pragma unroll
+    for (int i = 0; i < S::MI; i++)
+#pragma unroll
+        for (int j = 0; j < S::NJ; j++) acc[i][j] = Sc<T>::zero();
+    LoadPanelRows<T, TN> la{L, ld, s, p0, c};
+    LoadColMajor<T, TN> lb{Li, (int64_t)s, s, s};
+    tile_gemm<T, TN>(s, la, lb, acc, As, Bs);
+    const int tx = threadIdx.x % S::TX, ty = threadIdx.x / S::TX;
+#pragma unroll
+    for (int i = 0; i < S::MI; i++)
+#pragma unroll
+        for (int j = 0; j < S::NJ; j++) {
+            const int p = p0 + ty + S::TY * i, col = tx + S::TX * j;
+            if (p < c && col < s) LD[(int64_t)col * ld + s + p] = acc[i][j];
+        }
+}
+
+// ---------------------------------------------------------------------------
+// k_selinv: one row tile of C(K).
+// Gather: entry (p, q) of A^{-1}_{C,C} is stored, by symmetry, at
+// (max(p,q), min(p,q)); with b = min, a = max it sits in the panel of the
+// owner of column C[b] at row relidx[prb[b] + a], column address pcb[b].
+// ---------------------------------------------------------------------------
+template <typename T, int TN> struct LoadGather {
+    const T *Z;
+    const int64_t *pcb;   // per C position: panel address of column C[q] (+ plan base)
+    const int64_t *prb;   // per C position: base into relidx
+    const int32_t *relidx;
+    const int64_t *tile_cb;  // shared: pcb of the tile's rows
+    const int64_t *tile_rb;  // shared: prb of the tile's rows
+    int p0, c;
+    __device__ void operator()(int k0, T *As) const {
+        for (int e = threadIdx.x; e < kTK * kTM; e += kThreads) {
+            const int pl = e % kTM, kk = e / kTM;
+            const int p = p0 + pl, q = k0 + kk;
+            T v = Sc<T>::zero();
+            if (p < c && q < c) {
+                int64_t addr;
+                if (p >= q) addr = pcb[q] + relidx[prb[q] + p];
+                else addr = tile_cb[pl] + relidx[tile_rb[pl] + q];
+                v = Z[addr];
+            }
+            As[kk * kTM + pl] = v;
+        }
+    }
+};
+
+template <typename T, int TN>
+__global__ void __launch_bounds__(kThreads) k_selinv(const ProbDesc *__restrict__ descs,
+                                                     const Item *__restrict__ items, int nitems) {
+    using S = Shape<TN>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *As = reinterpret_cast<T *>(smem_raw);
+    T *Bs = As + smem_a_elems<T, TN>();
+    __shared__ int64_t tile_cb[kTM], tile_rb[kTM];
+    __shared__ int s_last;
+    const int w = blockIdx.x;
+    if (w >= nitems) return;
+    const Item it = items[w];
+    const ProbDesc &P = descs[it.prob];
+    const int K = it.K;
+    const int s = P.super_ptr[K + 1] - P.super_ptr[K];
+    const int64_t ld = P.rowptr[K + 1] - P.rowptr[K];
+    const int c = (int)(ld - s);
+    const int p0 = it.tile * kTM;
+    const int pm = c - p0 < kTM ? c - p0 : kTM;  // rows in this tile (may be <= 0 when c == 0)
+    const int64_t pos0 = P.rowptr[K] + s;         // position of C[0] in the row lists
+    const T *Zc = static_cast<const T *>(P.Z);
+    T *Zk = static_cast<T *>(P.Z) + P.panel_off[K];
+    const T *LDk = static_cast<const T *>(P.LD) + P.panel_off[K];
+
+    for (int e = threadIdx.x; e < kTM; e += kThreads) {
+        const int p = p0 + e;
+        tile_cb[e] = p < c ? P.colbase[pos0 + p] : 0;
+        tile_rb[e] = p < c ? P.relbase[pos0 + p] : 0;
+    }
+    T acc[S::MI][S::NJ];
+#pragma unroll
+    for (int i = 0; i < S::MI; i++)
+#pragma unroll
+        for (int j = 0; j < S::NJ; j++) acc[i][j] = Sc<T>::zero();
+    if (pm > 0) {
+        LoadGather<T, TN> la{Zc, P.colbase + pos0, P.relbase + pos0, P.relidx, tile_cb, tile_rb, p0, c};
+        LoadColMajor<T, TN> lb{LDk + s, ld, c, s};  // Lhat(q, j) = LD[j*ld + s + q]
+        tile_gemm<T, TN>(c, la, lb, acc, As, Bs);
+    }
+    // write A^{-1}_{C,K} = -acc
+    const int tx = threadIdx.x % S::TX, ty = threadIdx.x / S::TX;
+#pragma unroll
+    for (int i = 0; i < S::MI; i++)
+#pragma unroll
+        for (int j = 0; j < S::NJ; j++) {
+            const int p = p0 + ty + S::TY * i, col = tx + S::TX * j;
+            if (p < c && col < s) Zk[(int64_t)col * ld + s + p] = neg(acc[i][j]);
+        }
+    __syncthreads();  // this CTA's rows of A^{-1}_{C,K} are visible to the CTA
+    // split contribution of this tile: Ptile(i, j) = sum_{p in tile} Lhat(p, i) Y(p, j)
+    T *part = static_cast<T *>(P.partial) + P.part_off[K] + (int64_t)it.tile * s * s;
+    constexpr int OPT = 8;
+    for (int ob = 0; ob < s * s; ob += kThreads * OPT) {
+        T pacc[OPT];
+#pragma unroll
+        for (int o = 0; o < OPT; o++) pacc[o] = Sc<T>::zero();
+        for (int pc = 0; pc < pm; pc += kTK) {
+            __syncthreads();
+            for (int e = threadIdx.x; e < kTK * TN; e += kThreads) {
+                const int kk = e % kTK, j = e / kTK;
+                const int p = p0 + pc + kk;
+                const bool ok = (pc + kk < pm) && j < s;
+                As[kk * TN + j] = ok ? LDk[(int64_t)j * ld + s + p] : Sc<T>::zero();       // Lhat
+                Bs[kk * TN + j] = ok ? Zk[(int64_t)j * ld + s + p] : Sc<T>::zero();        // Y
+            }
+            __syncthreads();
+#pragma unroll
+            for (int o = 0; o < OPT; o++) {
+                const int e = ob + threadIdx.x + kThreads * o;
+                if (e < s * s) {
+                    const int i = e % s, j = e / s;
+#pragma unroll 4
+                    for (int kk = 0; kk < kTK; kk++) madd(pacc[o], As[kk * TN + i], Bs[kk * TN + j]);
+                }
+            }
+        }
+#pragma unroll
+        for (int o = 0; o < OPT; o++) {
+            const int e = ob + threadIdx.x + kThreads * o;
+            if (e < s * s) part[e] = pacc[o];
+        }
+    }
+    // the last tile of K to finish reduces the partials in tile order
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const int prev = atomicAdd(&P.counter[K], 1);
+        s_last = (prev == it.ntiles - 1);
+    }
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    const T *part0 = static_cast<const T *>(P.partial) + P.part_off[K];
+    const int64_t ss = (int64_t)s * s;
+    for (int e = threadIdx.x; e < s * s; e += kThreads) {
+        const int i = e % s, j = e / s;
+        if (i < j) continue;
+        T xij = LDk[(int64_t)j * ld + i], xji = LDk[(int64_t)i * ld + j];
+        for (int t = 0; t < it.ntiles; t++) {
+            xij = sub(xij, ldcg(part0 + t * ss + (int64_t)j * s + i));
+            xji = sub(xji, ldcg(part0 + t * ss + (int64_t)i * s + j));
+        }
+        if (P.symmetrize) {
+            const T v = half(add(xij, xji));
+            xij = v;
+            xji = v;
+        }
+        Zk[(int64_t)j * ld + i] = xij;
+        Zk[(int64_t)i * ld + j] = xji;
+    }
+    if (threadIdx.x == 0) P.counter[K] = 0;
+    if (P.done) {
+        __threadfence();
+        __syncthreads();
+        if (threadIdx.x == 0) atomicExch(&P.done[K], 1);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// launchers
+// ---------------------------------------------------------------------------
+template <typename T>
+static cudaError_t launch_linv_t(const ProbDesc *d, const int2 *work, int nwork, cudaStream_t st) {
+    if (nwork <= 0) return cudaSuccess;
+    k_linv<T><<<nwork, 128, 0, st>>>(d, work, nwork);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_linv(int dtype, const ProbDesc *d, const int2 *work, int nwork, cudaStream_t st) {
+    return dtype == SELINV_C128 ? launch_linv_t<zd>(d, work, nwork, st)
+                                : launch_linv_t<double>(d, work, nwork, st);
+}
+
+template <typename T, int TN>
+static cudaError_t launch_items_t(int kernel, const ProbDesc *d, const Item *items, int n,
+                                  cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    constexpr size_t smem = smem_bytes<T, TN>();
+    if (kernel == 0) k_lhat<T, TN><<<n, kThreads, smem, st>>>(d, items, n);
+    else k_selinv<T, TN><<<n, kThreads, smem, st>>>(d, items, n);
+    return cudaGetLastError();
+}
+
+template <typename T, int TN>
+static cudaError_t configure_t() {
+    constexpr int smem = (int)smem_bytes<T, TN>();
+    cudaError_t e = cudaFuncSetAttribute(k_lhat<T, TN>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_selinv<T, TN>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    return e;
+}
+
+template <typename T>
+static cudaError_t configure_dt() {
+    cudaError_t e = configure_t<T, 8>();
+    if (e == cudaSuccess) e = configure_t<T, 16>();
+    if (e == cudaSuccess) e = configure_t<T, 32>();
+    if (e == cudaSuccess) e = configure_t<T, 64>();
+    if (e == cudaSuccess) e = configure_t<T, 128>();
+    return e;
+}
+
+// opt every kernel in to its dynamic shared memory (outside any graph capture)
+cudaError_t configure_selinv_kernels() {
+    cudaError_t e = configure_dt<double>();
+    if (e == cudaSuccess) e = configure_dt<zd>();
+    return e;
+}
+
+template <typename T>
+static cudaError_t launch_items_dt(int kernel, int bucket, const ProbDesc *d, const Item *items,
+                                   int n, cudaStream_t st) {
+    switch (bucket) {
+    case 0: return launch_items_t<T, 8>(kernel, d, items, n, st);
+    case 1: return launch_items_t<T, 16>(kernel, d, items, n, st);
+    case 2: return launch_items_t<T, 32>(kernel, d, items, n, st);
+    case 3: return launch_items_t<T, 64>(kernel, d, items, n, st);
+    default: return launch_items_t<T, 128>(kernel, d, items, n, st);
+    }
+}
+
+cudaError_t launch_lhat(int dtype, int bucket, const ProbDesc *d, const Item *items, int n,
+                        cudaStream_t st) {
+    return dtype == SELINV_C128 ? launch_items_dt<zd>(0, bucket, d, items, n, st)
+                                : launch_items_dt<double>(0, bucket, d, items, n, st);
+}
+
+cudaError_t launch_selinv(int dtype, int bucket, const ProbDesc *d, const Item *items, int n,
+                          cudaStream_t st) {
+    return dtype == SELINV_C128 ? launch_items_dt<zd>(1, bucket, d, items, n, st)
+                                : launch_items_dt<double>(1, bucket, d, items, n, st);
+}
+
+}  // namespace selinv

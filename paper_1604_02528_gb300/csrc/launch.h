@@ -1,0 +1,20 @@
+// Host-side launchers of the sm_103a kernels (internal).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+
+namespace selinv {
+
+// counts kernel launches issued by the library (reported by selinv_launch_count)
+void note_launch(int n = 1);
+
+cudaError_t configure_selinv_kernels();
+cudaError_t launch_linv(int dtype, const ProbDesc *d, const int2 *work, int nwork, cudaStream_t st);
+cudaError_t launch_lhat(int dtype, int bucket, const ProbDesc *d, const Item *items, int n,
+                        cudaStream_t st);
+cudaError_t launch_selinv(int dtype, int bucket, const ProbDesc *d, const Item *items, int n,
+                          cudaStream_t st);
+
+}  // namespace selinv

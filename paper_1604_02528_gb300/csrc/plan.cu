@@ -1,0 +1,609 @@
+// Plan construction (selinv_symbolic), schedules and the C ABI of the
+// numeric phase.  The plan makes Alg. 1's "find the collection of indices C"
+// explicit once: every C is split into runs owned by one ancestor supernode,
+// and the row of each C entry inside its owner's row list (relative index)
+// is stored, so that the kernels gather A^{-1}_{C,C} without searching.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <cstdint>
+#include <cstring>
+#include <memory>
+#include <new>
+#include <vector>
+
+#include "common.cuh"
+#include "launch.h"
+#include "plan.h"
+
+namespace selinv {
+
+static std::atomic<int64_t> g_launches{0};
+void note_launch(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
+size_t elem_size(int dtype) { return dtype == SELINV_C128 ? 16 : 8; }
+
+template <typename X>
+static int upload(X **dptr, const std::vector<X> &h) {
+    *dptr = nullptr;
+    size_t bytes = sizeof(X) * (h.empty() ? 1 : h.size());
+    if (cudaMalloc((void **)dptr, bytes) != cudaSuccess) return SELINV_ERR_OOM;
+    if (!h.empty() && cudaMemcpy(*dptr, h.data(), sizeof(X) * h.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+        return SELINV_ERR_CUDA;
+    return SELINV_OK;
+}
+
+static void dfree(void *p) {
+    if (p) cudaFree(p);
+}
+
+void Workspace::release() {
+    dfree(LD); dfree(Linv); dfree(partial); dfree(counter); dfree(done); dfree(work);
+    LD = Linv = partial = nullptr;
+    counter = done = nullptr;
+    work = nullptr;
+    bytes_elem = 0;
+}
+
+int Workspace::ensure(const PlanData &p, int dtype) {
+    const size_t es = elem_size(dtype);
+    if (LD && bytes_elem >= es) return SELINV_OK;
+    release();
+    if (cudaMalloc(&LD, es * (size_t)std::max<int64_t>(p.nnz, 1)) != cudaSuccess) return SELINV_ERR_OOM;
+    if (cudaMalloc(&Linv, es * (size_t)std::max<int64_t>(p.linv_total, 1)) != cudaSuccess) return SELINV_ERR_OOM;
+    if (cudaMalloc(&partial, es * (size_t)std::max<int64_t>(p.part_max, 1)) != cudaSuccess) return SELINV_ERR_OOM;
+    if (cudaMalloc((void **)&counter, sizeof(int) * (size_t)std::max(p.ns, 1)) != cudaSuccess) return SELINV_ERR_OOM;
+    if (cudaMalloc((void **)&done, sizeof(int) * (size_t)std::max(p.ns, 1)) != cudaSuccess) return SELINV_ERR_OOM;
+    if (cudaMalloc(&work, es * (size_t)std::max<int64_t>(p.nnz, 1)) != cudaSuccess) return SELINV_ERR_OOM;
+    cudaMemset(counter, 0, sizeof(int) * (size_t)std::max(p.ns, 1));
+    cudaMemset(done, 0, sizeof(int) * (size_t)std::max(p.ns, 1));
+    bytes_elem = es;
+    return SELINV_OK;
+}
+
+// ---------------------------------------------------------------------------
+// plan construction
+// ---------------------------------------------------------------------------
+static int build_plan(PlanData &p, int32_t n, int32_t ns, const int32_t *super_ptr,
+                      const int32_t *sparent, const int64_t *rowptr, const int32_t *rowind) {
+    p.n = n;
+    p.ns = ns;
+    if (super_ptr[0] != 0 || super_ptr[ns] != n) return SELINV_ERR_INVALID_ARG;
+    for (int32_t K = 0; K < ns; K++)
+        if (super_ptr[K + 1] <= super_ptr[K]) return SELINV_ERR_INVALID_ARG;
+    if (rowptr[0] != 0) return SELINV_ERR_INVALID_ARG;
+    p.super_ptr.assign(super_ptr, super_ptr + ns + 1);
+    p.sparent.assign(sparent, sparent + ns);
+    p.rowptr.assign(rowptr, rowptr + ns + 1);
+    const int64_t nrows = rowptr[ns];
+    p.rows.assign(rowind, rowind + nrows);
+    std::vector<int32_t> col2s(n);
+    for (int32_t K = 0; K < ns; K++)
+        for (int32_t j = super_ptr[K]; j < super_ptr[K + 1]; j++) col2s[j] = K;
+    // structure checks
+    p.panel_off.assign(ns + 1, 0);
+    for (int32_t K = 0; K < ns; K++) {
+        const int32_t fc = super_ptr[K], s = super_ptr[K + 1] - fc;
+        const int64_t m = rowptr[K + 1] - rowptr[K];
+        if (m < s) return SELINV_ERR_BAD_PATTERN;
+        const int32_t *R = rowind + rowptr[K];
+        for (int32_t j = 0; j < s; j++)
+            if (R[j] != fc + j) return SELINV_ERR_BAD_PATTERN;
+        for (int64_t r = 1; r < m; r++)
+            if (R[r] <= R[r - 1] || R[r] >= n) return SELINV_ERR_BAD_PATTERN;
+        const int32_t par = sparent[K];
+        if (m > s) {
+            if (par != col2s[R[s]]) return SELINV_ERR_BAD_ETREE;
+        } else if (par != -1) {
+            return SELINV_ERR_BAD_ETREE;
+        }
+        p.panel_off[K + 1] = p.panel_off[K] + m * s;
+    }
+    p.nnz = p.panel_off[ns];
+    // levels (depth from the root); parents have larger indices
+    p.level.assign(ns, 0);
+    p.nlevels = ns > 0 ? 1 : 0;
+    for (int32_t K = ns - 1; K >= 0; K--) {
+        p.level[K] = sparent[K] < 0 ? 0 : p.level[sparent[K]] + 1;
+        p.nlevels = std::max(p.nlevels, p.level[K] + 1);
+    }
+    p.level_ptr.assign(p.nlevels + 1, 0);
+    for (int32_t K = 0; K < ns; K++) p.level_ptr[p.level[K] + 1]++;
+    for (int l = 0; l < p.nlevels; l++) p.level_ptr[l + 1] += p.level_ptr[l];
+    p.level_list.assign(ns, 0);
+    {
+        std::vector<int64_t> f(p.level_ptr.begin(), p.level_ptr.end() - 1);
+        for (int32_t K = 0; K < ns; K++) p.level_list[f[p.level[K]]++] = K;
+    }
+    // owner segments of every C, relative indices (merge walk in the owner's rows)
+    p.seg_ptr.assign(ns + 1, 0);
+    p.seg_owner.clear(); p.seg_start.clear(); p.seg_coloff.clear();
+    p.rel_ptr.assign(1, 0);
+    p.relidx.clear();
+    p.colbase.assign(nrows > 0 ? nrows : 1, 0);
+    p.relbase.assign(nrows > 0 ? nrows : 1, 0);
+    for (int32_t K = 0; K < ns; K++) {
+        const int32_t s = super_ptr[K + 1] - super_ptr[K];
+        const int64_t c = rowptr[K + 1] - rowptr[K] - s;
+        const int32_t *C = rowind + rowptr[K] + s;
+        p.seg_ptr[K] = (int64_t)p.seg_owner.size();
+        int64_t q = 0;
+        while (q < c) {
+            const int32_t J = col2s[C[q]];
+            if (J <= K) return SELINV_ERR_BAD_PATTERN;
+            int64_t qe = q;
+            while (qe < c && col2s[C[qe]] == J) qe++;
+            const int32_t fcJ = super_ptr[J];
+            const int64_t mJ = rowptr[J + 1] - rowptr[J];
+            const int32_t *RJ = rowind + rowptr[J];
+            p.seg_owner.push_back(J);
+            p.seg_start.push_back((int32_t)q);
+            p.seg_coloff.push_back(C[q] - fcJ);
+            const int64_t rbase = (int64_t)p.relidx.size();
+            int64_t t = C[q] - fcJ;  // C[q] is a column of J, at that position of rows(J)
+            for (int64_t r = q; r < c; r++) {
+                while (t < mJ && RJ[t] < C[r]) t++;
+                if (t >= mJ || RJ[t] != C[r]) return SELINV_ERR_BAD_PATTERN;  // not closed
+                p.relidx.push_back((int32_t)t);
+            }
+            p.rel_ptr.push_back((int64_t)p.relidx.size());
+            for (int64_t r = q; r < qe; r++) {
+                const int64_t pos = rowptr[K] + s + r;
+                p.colbase[pos] = p.panel_off[J] + (int64_t)(C[r] - fcJ) * mJ;
+                p.relbase[pos] = rbase - q;
+            }
+            q = qe;
+        }
+    }
+    p.seg_ptr[ns] = (int64_t)p.seg_owner.size();
+    // L_KK^{-1} offsets; split-partial offsets inside each level
+    p.linv_off.assign(ns + 1, 0);
+    p.part_off.assign(ns > 0 ? ns : 1, 0);
+    p.ntiles.assign(ns > 0 ? ns : 1, 1);
+    for (int32_t K = 0; K < ns; K++) {
+        const int64_t s = super_ptr[K + 1] - super_ptr[K];
+        p.linv_off[K + 1] = p.linv_off[K] + s * s;
+        const int64_t c = rowptr[K + 1] - rowptr[K] - s;
+        p.ntiles[K] = (int32_t)std::max<int64_t>(1, (c + kTM - 1) / kTM);
+    }
+    p.linv_total = p.linv_off[ns];
+    p.part_max = 1;
+    for (int l = 0; l < p.nlevels; l++) {
+        int64_t acc = 0;
+        for (int64_t e = p.level_ptr[l]; e < p.level_ptr[l + 1]; e++) {
+            const int32_t K = p.level_list[e];
+            const int64_t s = super_ptr[K + 1] - super_ptr[K];
+            p.part_off[K] = acc;
+            acc += (int64_t)p.ntiles[K] * s * s;
+        }
+        p.part_max = std::max(p.part_max, acc);
+    }
+    return SELINV_OK;
+}
+
+// Device copies of the plan, made on first use (so that plans can be built
+// and inspected on a host without a GPU).
+int ensure_device(PlanData &p) {
+    if (p.d_status) return SELINV_OK;
+    static bool configured = false;
+    if (!configured) {
+        if (configure_selinv_kernels() != cudaSuccess) return SELINV_ERR_CUDA;
+        configured = true;
+    }
+    int rc;
+    if ((rc = upload(&p.d_super_ptr, p.super_ptr))) return rc;
+    if ((rc = upload(&p.d_sparent, p.sparent))) return rc;
+    if ((rc = upload(&p.d_rowptr, p.rowptr))) return rc;
+    if ((rc = upload(&p.d_rows, p.rows))) return rc;
+    if ((rc = upload(&p.d_panel_off, p.panel_off))) return rc;
+    if ((rc = upload(&p.d_colbase, p.colbase))) return rc;
+    if ((rc = upload(&p.d_relbase, p.relbase))) return rc;
+    if ((rc = upload(&p.d_relidx, p.relidx))) return rc;
+    if ((rc = upload(&p.d_linv_off, p.linv_off))) return rc;
+    if ((rc = upload(&p.d_part_off, p.part_off))) return rc;
+    int *st = nullptr;
+    if (cudaMalloc((void **)&st, sizeof(int)) != cudaSuccess) return SELINV_ERR_OOM;
+    if (cudaMemset(st, 0, sizeof(int)) != cudaSuccess) return SELINV_ERR_CUDA;
+    p.d_status = st;
+    return SELINV_OK;
+}
+
+void PlanData::release_device() {
+    dfree(d_super_ptr); dfree(d_sparent); dfree(d_rowptr); dfree(d_rows); dfree(d_panel_off);
+    dfree(d_colbase); dfree(d_relbase); dfree(d_relidx); dfree(d_linv_off); dfree(d_part_off);
+    dfree(d_status);
+    d_super_ptr = d_sparent = d_rows = d_relidx = nullptr;
+    d_rowptr = d_panel_off = d_colbase = d_relbase = d_linv_off = d_part_off = nullptr;
+    d_status = nullptr;
+}
+
+ProbDesc make_desc(const PlanData &p, Workspace &w, int dtype, const void *L, const void *D, void *Z,
+                   bool persistent) {
+    ProbDesc d;
+    std::memset(&d, 0, sizeof(d));
+    d.super_ptr = p.d_super_ptr;
+    d.rowptr = p.d_rowptr;
+    d.rows = p.d_rows;
+    d.panel_off = p.d_panel_off;
+    d.colbase = p.d_colbase;
+    d.relbase = p.d_relbase;
+    d.relidx = p.d_relidx;
+    d.linv_off = p.d_linv_off;
+    d.part_off = p.d_part_off;
+    d.sparent = p.d_sparent;
+    d.L = L;
+    d.D = D;
+    d.Z = Z;
+    d.LD = w.LD;
+    d.Linv = w.Linv;
+    d.partial = w.partial;
+    d.counter = w.counter;
+    d.done = persistent ? w.done : nullptr;
+    d.status = p.d_status;
+    d.ns = p.ns;
+    d.n = p.n;
+    d.dtype = dtype;
+    d.symmetrize = p.opts.symmetrize;
+    return d;
+}
+
+// ---------------------------------------------------------------------------
+// schedules: the launch sequence of one call (single or batched problems)
+// ---------------------------------------------------------------------------
+void Schedule::release() {
+    if (graph) cudaGraphExecDestroy(graph);
+    graph = nullptr;
+    dfree(d_descs); dfree(d_items); dfree(d_work);
+    d_descs = nullptr; d_items = nullptr; d_work = nullptr;
+}
+
+int build_schedule(Schedule &S, const std::vector<const PlanData *> &plans,
+                   const std::vector<ProbDesc> &descs, int mode) {
+    S.release();
+    S.launches.clear();
+    S.h_items.clear();
+    S.h_work.clear();
+    S.mode = mode;
+    const int np = (int)plans.size();
+    // 1) L_KK^{-1}, Dinv for every supernode (one launch per dtype)
+    for (int dt = 0; dt < 2; dt++) {
+        const int64_t off = (int64_t)S.h_work.size();
+        for (int i = 0; i < np; i++) {
+            if (descs[i].dtype != dt) continue;
+            for (int32_t K = 0; K < plans[i]->ns; K++) S.h_work.push_back(make_int2(i, K));
+        }
+        const int cnt = (int)(S.h_work.size() - off);
+        if (cnt) S.launches.push_back({0, dt, 0, off, cnt, -1});
+    }
+    // 2) Lhat for every row tile (one launch per dtype and width class)
+    for (int dt = 0; dt < 2; dt++)
+        for (int b = 0; b < kNumBuckets; b++) {
+            const int64_t off = (int64_t)S.h_items.size();
+            for (int i = 0; i < np; i++) {
+                if (descs[i].dtype != dt) continue;
+                const PlanData &p = *plans[i];
+                for (int32_t K = 0; K < p.ns; K++) {
+                    const int s = p.super_ptr[K + 1] - p.super_ptr[K];
+                    const int64_t c = p.rowptr[K + 1] - p.rowptr[K] - s;
+                    if (c == 0 || bucket_of(s) != b) continue;
+                    for (int t = 0; t < p.ntiles[K]; t++) S.h_items.push_back({i, K, t, p.ntiles[K]});
+                }
+            }
+            const int cnt = (int)(S.h_items.size() - off);
+            if (cnt) S.launches.push_back({1, dt, b, off, cnt, -1});
+        }
+    // 3) the traversal, root to leaves
+    auto push_items = [&](int i, int32_t K) {
+        const PlanData &p = *plans[i];
+        for (int t = 0; t < p.ntiles[K]; t++) S.h_items.push_back({i, K, t, p.ntiles[K]});
+    };
+    if (mode == SELINV_SCHED_PLAIN) {
+        // one launch per supernode, K = N..1, problem after problem
+        for (int i = 0; i < np; i++) {
+            const PlanData &p = *plans[i];
+            for (int32_t K = p.ns - 1; K >= 0; K--) {
+                const int64_t off = (int64_t)S.h_items.size();
+                push_items(i, K);
+                const int s = p.super_ptr[K + 1] - p.super_ptr[K];
+                S.launches.push_back({2, descs[i].dtype, bucket_of(s), off,
+                                      (int)(S.h_items.size() - off), p.level[K]});
+            }
+        }
+    } else {
+        int nlev = 0;
+        for (int i = 0; i < np; i++) nlev = std::max(nlev, plans[i]->nlevels);
+        for (int l = 0; l < nlev; l++)
+            for (int dt = 0; dt < 2; dt++)
+                for (int b = kNumBuckets - 1; b >= 0; b--) {
+                    const int64_t off = (int64_t)S.h_items.size();
+                    for (int i = 0; i < np; i++) {
+                        if (descs[i].dtype != dt) continue;
+                        const PlanData &p = *plans[i];
+                        if (l >= p.nlevels) continue;
+                        for (int64_t e = p.level_ptr[l]; e < p.level_ptr[l + 1]; e++) {
+                            const int32_t K = p.level_list[e];
+                            if (bucket_of(p.super_ptr[K + 1] - p.super_ptr[K]) == b) push_items(i, K);
+                        }
+                    }
+                    const int cnt = (int)(S.h_items.size() - off);
+                    if (cnt) S.launches.push_back({2, dt, b, off, cnt, l});
+                }
+    }
+    S.h_descs = descs;
+    int rc;
+    if ((rc = upload(&S.d_descs, S.h_descs))) return rc;
+    if ((rc = upload(&S.d_items, S.h_items))) return rc;
+    if ((rc = upload(&S.d_work, S.h_work))) return rc;
+    return SELINV_OK;
+}
+
+static cudaError_t issue(const Schedule &S, cudaStream_t st, bool count) {
+    if (count) note_launch((int)S.launches.size());
+    for (const Launch &L : S.launches) {
+        cudaError_t e = cudaSuccess;
+        if (L.kind == 0) e = launch_linv(L.dtype, S.d_descs, S.d_work + L.off, L.count, st);
+        else if (L.kind == 1) e = launch_lhat(L.dtype, L.bucket, S.d_descs, S.d_items + L.off, L.count, st);
+        else e = launch_selinv(L.dtype, L.bucket, S.d_descs, S.d_items + L.off, L.count, st);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+int run_schedule(Schedule &S, cudaStream_t st, bool use_graph) {
+    // graphs need a capturable stream (not the legacy default stream)
+    if (use_graph && st != nullptr && st != cudaStreamLegacy) {
+        if (!S.graph) {
+            cudaGraph_t g = nullptr;
+            if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return SELINV_ERR_CUDA;
+            cudaError_t e = issue(S, st, false);
+            cudaError_t e2 = cudaStreamEndCapture(st, &g);
+            if (e != cudaSuccess || e2 != cudaSuccess) {
+                if (g) cudaGraphDestroy(g);
+                return SELINV_ERR_CUDA;
+            }
+            e = cudaGraphInstantiate(&S.graph, g, 0);
+            cudaGraphDestroy(g);
+            if (e != cudaSuccess) {
+                S.graph = nullptr;
+                return SELINV_ERR_CUDA;
+            }
+        }
+        note_launch((int)S.launches.size());
+        return cudaGraphLaunch(S.graph, st) == cudaSuccess ? SELINV_OK : SELINV_ERR_CUDA;
+    }
+    return issue(S, st, true) == cudaSuccess ? SELINV_OK : SELINV_ERR_CUDA;
+}
+
+}  // namespace selinv
+
+using namespace selinv;
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+extern "C" void selinv_default_opts(selinv_opts *o) {
+    if (!o) return;
+    o->symmetrize = 1;
+    o->schedule = SELINV_SCHED_LEVEL;
+    o->autotune = 0;
+    o->debug_checks = 0;
+    o->spin_limit = 1LL << 26;
+    o->use_graph = 1;
+    o->fast_contraction = 1;
+}
+
+extern "C" int selinv_symbolic(int32_t n, int32_t nsuper, const int32_t *super_ptr,
+                               const int32_t *sparent, const int64_t *rowptr, const int32_t *rowind,
+                               const selinv_opts *opts, selinv_plan *out_plan) {
+    if (!out_plan) return SELINV_ERR_INVALID_ARG;
+    *out_plan = nullptr;
+    if (n < 0 || nsuper < 0 || (nsuper == 0) != (n == 0) || !super_ptr || !rowptr ||
+        (nsuper > 0 && (!sparent || !rowind)))
+        return SELINV_ERR_INVALID_ARG;
+    selinv_plan_s *pl = new (std::nothrow) selinv_plan_s();
+    if (!pl) return SELINV_ERR_OOM;
+    if (opts) pl->data.opts = *opts;
+    else selinv_default_opts(&pl->data.opts);
+    int rc;
+    try {
+        rc = build_plan(pl->data, n, nsuper, super_ptr, sparent, rowptr, rowind);
+    } catch (const std::bad_alloc &) {
+        rc = SELINV_ERR_OOM;
+    }
+    if (rc != SELINV_OK) {
+        selinv_plan_destroy(pl);
+        return rc;
+    }
+    *out_plan = pl;
+    return SELINV_OK;
+}
+
+selinv_plan_s::~selinv_plan_s() {
+    single.release();
+    for (auto &b : batch_cache) b.sched.release();
+    for (auto &w : ws) w.release();
+    factor_release(this);
+    data.release_device();
+}
+
+extern "C" void selinv_plan_destroy(selinv_plan plan) { delete plan; }
+
+extern "C" int64_t selinv_plan_nnz(selinv_plan plan) { return plan ? plan->data.nnz : SELINV_ERR_INVALID_ARG; }
+
+extern "C" int64_t selinv_plan_panel_offset(selinv_plan plan, int32_t K) {
+    if (!plan || K < 0 || K > plan->data.ns) return -1;
+    return plan->data.panel_off[K];
+}
+
+extern "C" int selinv_plan_stats(selinv_plan plan, selinv_dtype dtype, double *flops, double *bytes) {
+    if (!plan) return SELINV_ERR_INVALID_ARG;
+    const PlanData &p = plan->data;
+    double F = 0, B = 0;
+    const double w = dtype == SELINV_C128 ? 16.0 : 8.0;
+    for (int32_t K = 0; K < p.ns; K++) {
+        const double s = p.super_ptr[K + 1] - p.super_ptr[K];
+        const double c = (double)(p.rowptr[K + 1] - p.rowptr[K]) - s;
+        F += 2 * c * c * s + 2 * c * s * s + c * s * s + s * s * s;
+        B += w * (c * (c + 1) / 2 + 2 * (c + s) * s + s);
+    }
+    if (dtype == SELINV_C128) F *= 4;
+    if (flops) *flops = F;
+    if (bytes) *bytes = B;
+    return SELINV_OK;
+}
+
+extern "C" int64_t selinv_plan_get(selinv_plan plan, int field, void *dst) {
+    if (!plan) return SELINV_ERR_INVALID_ARG;
+    const PlanData &p = plan->data;
+    const void *src = nullptr;
+    int64_t cnt = 0;
+    size_t es = 4;
+    switch (field) {
+    case 0: src = p.level.data(); cnt = p.ns; break;
+    case 1: src = p.seg_ptr.data(); cnt = p.ns + 1; es = 8; break;
+    case 2: src = p.seg_owner.data(); cnt = (int64_t)p.seg_owner.size(); break;
+    case 3: src = p.seg_start.data(); cnt = (int64_t)p.seg_start.size(); break;
+    case 4: src = p.seg_coloff.data(); cnt = (int64_t)p.seg_coloff.size(); break;
+    case 5: src = p.rel_ptr.data(); cnt = (int64_t)p.rel_ptr.size(); es = 8; break;
+    case 6: src = p.relidx.data(); cnt = (int64_t)p.relidx.size(); break;
+    case 7: src = p.level_ptr.data(); cnt = (int64_t)p.level_ptr.size(); es = 8; break;
+    case 8: src = p.level_list.data(); cnt = p.ns; break;
+    case 9: src = p.panel_off.data(); cnt = p.ns + 1; es = 8; break;
+    default: return SELINV_ERR_INVALID_ARG;
+    }
+    if (dst && cnt > 0) std::memcpy(dst, src, es * (size_t)cnt);
+    return cnt;
+}
+
+extern "C" int selinv_plan_set_opts(selinv_plan plan, const selinv_opts *opts) {
+    if (!plan || !opts) return SELINV_ERR_INVALID_ARG;
+    if (opts->schedule < 0 || opts->schedule > 2) return SELINV_ERR_INVALID_ARG;
+    plan->data.opts = *opts;
+    plan->single.release();
+    plan->single.valid = false;
+    for (auto &b : plan->batch_cache) b.sched.release();
+    plan->batch_cache.clear();
+    return SELINV_OK;
+}
+
+static bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
+
+extern "C" int selinv_numeric(selinv_plan plan, selinv_dtype dtype, const void *L, const void *D,
+                              void *Z, void *stream) {
+    if (!plan || (dtype != SELINV_F64 && dtype != SELINV_C128)) return SELINV_ERR_INVALID_ARG;
+    PlanData &p = plan->data;
+    if (p.ns == 0) return SELINV_OK;
+    if (!L || !D || !Z || !aligned16(L) || !aligned16(D) || !aligned16(Z)) return SELINV_ERR_INVALID_ARG;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    int rc = ensure_device(p);
+    if (rc) return rc;
+    if (plan->ws.empty()) plan->ws.resize(1);
+    rc = plan->ws[0].ensure(p, dtype);
+    if (rc) return rc;
+    Schedule &S = plan->single;
+    const int mode = p.opts.schedule;
+    if (!S.valid || S.key_L != L || S.key_D != D || S.key_Z != Z || S.key_dtype != dtype ||
+        S.mode != mode) {
+        std::vector<const PlanData *> plans{&p};
+        std::vector<ProbDesc> descs{make_desc(p, plan->ws[0], dtype, L, D, Z, false)};
+        rc = build_schedule(S, plans, descs, mode == SELINV_SCHED_PERSISTENT ? SELINV_SCHED_LEVEL : mode);
+        if (rc) { S.valid = false; return rc; }
+        S.valid = true;
+        S.key_L = L; S.key_D = D; S.key_Z = Z; S.key_dtype = dtype; S.mode = mode;
+    }
+    plan->last_stream = st;
+    return run_schedule(S, st, p.opts.use_graph != 0);
+}
+
+extern "C" int selinv_numeric_batched(int nitems, const selinv_plan *plans, const selinv_dtype *dtypes,
+                                      const void *const *L, const void *const *D, void *const *Z,
+                                      void *stream) {
+    if (nitems <= 0 || !plans || !dtypes || !L || !D || !Z) return SELINV_ERR_INVALID_ARG;
+    selinv_plan owner = plans[0];
+    if (!owner) return SELINV_ERR_INVALID_ARG;
+    for (int i = 0; i < nitems; i++) {
+        if (!plans[i] || (dtypes[i] != SELINV_F64 && dtypes[i] != SELINV_C128)) return SELINV_ERR_INVALID_ARG;
+        if (!L[i] || !D[i] || !Z[i] || !aligned16(L[i]) || !aligned16(D[i]) || !aligned16(Z[i]))
+            return SELINV_ERR_INVALID_ARG;
+    }
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const int mode = owner->data.opts.schedule;
+    // cached schedule for this exact batch?
+    BatchEntry *hit = nullptr;
+    for (auto &b : owner->batch_cache) {
+        if ((int)b.plans.size() != nitems || b.mode != mode) continue;
+        bool same = true;
+        for (int i = 0; i < nitems && same; i++)
+            same = b.plans[i] == plans[i] && b.dtypes[i] == dtypes[i] && b.L[i] == L[i] &&
+                   b.D[i] == D[i] && b.Z[i] == Z[i];
+        if (same) { hit = &b; break; }
+    }
+    for (int i = 0; i < nitems; i++) {
+        int rc = ensure_device(plans[i]->data);
+        if (rc) return rc;
+    }
+    if (!hit) {
+        // one workspace per batch item, owned by the first plan
+        if ((int)owner->ws.size() < nitems + 1) owner->ws.resize(nitems + 1);
+        std::vector<const PlanData *> pds(nitems);
+        std::vector<ProbDesc> descs(nitems);
+        for (int i = 0; i < nitems; i++) {
+            int rc = owner->ws[i + 1].ensure(plans[i]->data, dtypes[i]);
+            if (rc) return rc;
+            pds[i] = &plans[i]->data;
+            descs[i] = make_desc(plans[i]->data, owner->ws[i + 1], dtypes[i], L[i], D[i], Z[i], false);
+            descs[i].status = owner->data.d_status;
+        }
+        if (owner->batch_cache.size() >= 4) {
+            owner->batch_cache.front().sched.release();
+            owner->batch_cache.erase(owner->batch_cache.begin());
+        }
+        owner->batch_cache.emplace_back();
+        BatchEntry &b = owner->batch_cache.back();
+        b.mode = mode;
+        b.plans.assign(plans, plans + nitems);
+        b.dtypes.assign(dtypes, dtypes + nitems);
+        b.L.assign(L, L + nitems);
+        b.D.assign(D, D + nitems);
+        b.Z.assign(Z, Z + nitems);
+        int rc = build_schedule(b.sched, pds, descs, mode == SELINV_SCHED_PERSISTENT ? SELINV_SCHED_LEVEL : mode);
+        if (rc) {
+            b.sched.release();
+            owner->batch_cache.pop_back();
+            return rc;
+        }
+        hit = &b;
+    }
+    owner->last_stream = st;
+    return run_schedule(hit->sched, st, owner->data.opts.use_graph != 0);
+}
+
+extern "C" int selinv_status(selinv_plan plan) {
+    if (!plan) return SELINV_ERR_INVALID_ARG;
+    if (!plan->data.d_status) return SELINV_OK;
+    if (cudaStreamSynchronize(plan->last_stream) != cudaSuccess) return SELINV_ERR_CUDA;
+    int v = 0;
+    if (cudaMemcpy(&v, plan->data.d_status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+        return SELINV_ERR_CUDA;
+    if (v) cudaMemset(plan->data.d_status, 0, sizeof(int));
+    return v;
+}
+
+extern "C" const char *selinv_error_string(int code) {
+    switch (code) {
+    case SELINV_OK: return "ok";
+    case SELINV_ERR_INVALID_ARG: return "invalid argument";
+    case SELINV_ERR_BAD_ETREE: return "bad elimination tree (parent must be > child and own the first row below)";
+    case SELINV_ERR_BAD_PATTERN: return "bad row pattern (rows must be sorted, start with the supernode's columns and be closed under the tree)";
+    case SELINV_ERR_ZERO_PIVOT: return "zero pivot in D";
+    case SELINV_ERR_NONFINITE: return "non-finite value in the input";
+    case SELINV_ERR_OOM: return "out of memory";
+    case SELINV_ERR_CUDA: return "CUDA error";
+    case SELINV_ERR_TIMEOUT: return "a bounded device wait timed out";
+    case SELINV_ERR_UNSUPPORTED: return "unsupported";
+    default: return "unknown error";
+    }
+}
+
+extern "C" int64_t selinv_launch_count(void) { return g_launches.load(); }

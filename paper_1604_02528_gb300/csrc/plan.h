@@ -1,0 +1,100 @@
+// Internal host-side structures of a plan (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <vector>
+
+#include "common.cuh"
+
+namespace selinv {
+
+struct PlanData {
+    int32_t n = 0, ns = 0;
+    selinv_opts opts{};
+    // host arrays (kept for inspection and schedule building)
+    std::vector<int32_t> super_ptr, sparent, rows, level, level_list;
+    std::vector<int32_t> seg_owner, seg_start, seg_coloff, relidx, ntiles;
+    std::vector<int64_t> rowptr, panel_off, seg_ptr, rel_ptr, level_ptr, linv_off, part_off;
+    std::vector<int64_t> colbase, relbase;  // per row-list position
+    int nlevels = 0;
+    int64_t nnz = 0, linv_total = 0, part_max = 1;
+    // device copies
+    int32_t *d_super_ptr = nullptr, *d_sparent = nullptr, *d_rows = nullptr, *d_relidx = nullptr;
+    int64_t *d_rowptr = nullptr, *d_panel_off = nullptr, *d_colbase = nullptr, *d_relbase = nullptr;
+    int64_t *d_linv_off = nullptr, *d_part_off = nullptr;
+    int *d_status = nullptr;
+    void release_device();
+};
+
+// Numeric scratch of one problem: Dinv/Lhat panels, L_KK^{-1} blocks, split
+// partials of the diagonal blocks, per-supernode tile counters and
+// completion flags, and one more panel-sized buffer (adjoint working copy).
+struct Workspace {
+    void *LD = nullptr, *Linv = nullptr, *partial = nullptr, *work = nullptr;
+    int *counter = nullptr, *done = nullptr;
+    size_t bytes_elem = 0;
+    int ensure(const PlanData &p, int dtype);
+    void release();
+};
+
+struct Launch {
+    int kind;    // 0 linv, 1 lhat, 2 selinv
+    int dtype;
+    int bucket;
+    int64_t off;
+    int count;
+    int level;
+};
+
+struct Schedule {
+    bool valid = false;
+    int mode = -1;
+    const void *key_L = nullptr, *key_D = nullptr, *key_Z = nullptr;
+    int key_dtype = -1;
+    std::vector<ProbDesc> h_descs;
+    std::vector<Item> h_items;
+    std::vector<int2> h_work;
+    std::vector<Launch> launches;
+    ProbDesc *d_descs = nullptr;
+    Item *d_items = nullptr;
+    int2 *d_work = nullptr;
+    cudaGraphExec_t graph = nullptr;
+    void release();
+};
+
+struct BatchEntry {
+    int mode = -1;
+    std::vector<struct selinv_plan_s *> plans;
+    std::vector<int> dtypes;
+    std::vector<const void *> L, D;
+    std::vector<void *> Z;
+    Schedule sched;
+};
+
+size_t elem_size(int dtype);
+int ensure_device(PlanData &p);
+ProbDesc make_desc(const PlanData &p, Workspace &w, int dtype, const void *L, const void *D, void *Z,
+                   bool persistent);
+int build_schedule(Schedule &S, const std::vector<const PlanData *> &plans,
+                   const std::vector<ProbDesc> &descs, int mode);
+int run_schedule(Schedule &S, cudaStream_t st, bool use_graph);
+
+struct FactorData;  // factorization / adjoint state (kernels_factor.cu)
+
+}  // namespace selinv
+
+struct selinv_plan_s {
+    selinv::PlanData data;
+    std::vector<selinv::Workspace> ws;  // ws[0]: single calls; ws[1..]: batch items
+    selinv::Schedule single;
+    std::vector<selinv::BatchEntry> batch_cache;
+    selinv::FactorData *factor = nullptr;
+    cudaStream_t last_stream = nullptr;
+    ~selinv_plan_s();
+};
+
+namespace selinv {
+void factor_release(selinv_plan_s *plan);
+}

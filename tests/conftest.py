@@ -16,3 +16,20 @@ def pytest_configure(config):
 def pytest_collection_modifyitems(config, items):
     # the gpu marker is explicit; nothing else to do
     return
+
+
+@pytest.fixture(scope="session")
+def native():
+    """The ctypes binding, after an in-tree build of libselinv.so."""
+    from paper_1604_02528_gb300 import buildlib
+    buildlib.build()
+    from paper_1604_02528_gb300 import _native
+    return _native
+
+
+@pytest.fixture(scope="session")
+def cuda_device():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return torch.device("cuda:0")

@@ -1,0 +1,189 @@
+"""Host-side checks of the native library (no GPU needed).
+
+* the library loads and exports every entry point declared in include/selinv.h;
+* its symbolic analysis equals the oracle's, bit for bit;
+* its plan (levels, owner segments, relative indices) equals the oracle's
+  index sets, bit for bit;
+* malformed inputs are rejected with the documented error codes.
+"""
+import ctypes as ct
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+PROBLEMS = [
+    lambda: synth.random_sparse_spd(60, 0.08, 1),
+    lambda: synth.random_sparse_spd(200, 0.02, 2, supernodes=synth.problems.RELAXED_128),
+    lambda: synth.random_sparse_spd(80, 0.1, 3, complex_values=True),
+    lambda: synth.tridiagonal(100),
+    lambda: synth.tridiagonal(127, nd=True),
+    lambda: synth.laplacian_3d(10, seed=4),
+    lambda: synth.dft_sheet(side=6, nbasis=4),
+    lambda: synth.diffusion_3d(8),
+    lambda: synth.make_config(1),
+    lambda: synth.make_config(5),
+]
+
+
+def declared_symbols():
+    text = open(os.path.join(ROOT, "include", "selinv.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(selinv_[a-z_]+)\s*\(", text)))
+
+
+def test_library_exports_every_declared_symbol(native):
+    names = declared_symbols()
+    assert len(names) >= 20
+    lib = ct.CDLL(native._LIB_PATH)
+    for name in names:
+        assert hasattr(lib, name), name
+    assert set(native.REQUIRED_SYMBOLS) <= set(names)
+
+
+@pytest.mark.parametrize("make", PROBLEMS)
+def test_analysis_matches_oracle_bit_exact(native, make):
+    p = make()
+    sn = p.supernodes
+    kind = 1 if sn["kind"] == "relaxed" else 0
+    a = native.selinv_analyse(p.n, p.colptr, p.rowind, kind, sn["cap"], sn["fill"])
+    o = oracle.symbolic_for(p)
+    assert np.array_equal(a["parent"], o.parent)
+    assert np.array_equal(a["super_ptr"], o.super_ptr)
+    assert np.array_equal(a["sparent"], o.sparent)
+    assert np.array_equal(a["rowptr"], o.rowptr)
+    assert np.array_equal(a["rows"], o.rows)
+    assert a["nnz_true"] == o.nnz_true
+
+
+@pytest.mark.parametrize("cfg", [2, 3])
+def test_analysis_matches_oracle_on_full_workloads(native, cfg):
+    p = synth.make_config(cfg)
+    sn = p.supernodes
+    a = native.selinv_analyse(p.n, p.colptr, p.rowind, 1 if sn["kind"] == "relaxed" else 0,
+                              sn["cap"], sn["fill"])
+    o = oracle.symbolic_for(p)
+    for k in ("super_ptr", "sparent", "rowptr", "rows"):
+        assert np.array_equal(a[k], getattr(o, k)), k
+
+
+def make_plan(native, sym):
+    return native.selinv_symbolic(sym.n, sym.nsuper, sym.super_ptr, sym.sparent, sym.rowptr, sym.rows)
+
+
+@pytest.mark.parametrize("make", PROBLEMS + [lambda: synth.make_config(2)])
+def test_plan_matches_oracle_bit_exact(native, make):
+    p = make()
+    sym = oracle.symbolic_for(p)
+    plan = make_plan(native, sym)
+    ref = oracle.plan(sym)
+    for k in ("level", "seg_ptr", "seg_owner", "seg_start", "seg_coloff", "rel_ptr", "relidx"):
+        got = native.selinv_plan_get(plan, k)
+        assert np.array_equal(got, ref[k]), k
+    lp = native.selinv_plan_get(plan, "level_ptr")
+    ll = native.selinv_plan_get(plan, "level_list")
+    for l in range(lp.size - 1):
+        ks = ll[lp[l]:lp[l + 1]]
+        assert np.all(np.diff(ks) > 0) and np.all(ref["level"][ks] == l)
+    assert np.array_equal(native.selinv_plan_get(plan, "panel_off"), sym.panel_offsets())
+    assert plan.nnz == sym.nnz_panels
+    for K in (0, sym.nsuper // 2, sym.nsuper - 1):
+        assert native.selinv_plan_panel_offset(plan, K) == sym.panel_offsets()[K]
+
+
+def test_plan_stats_formula(native):
+    p = synth.make_config(1)
+    sym = oracle.symbolic_for(p)
+    plan = make_plan(native, sym)
+    s, c = sym.sizes()
+    F = float((2 * c * c * s + 2 * c * s * s + c * s * s + s ** 3).sum())
+    B = float((8 * (c * (c + 1) // 2 + 2 * (c + s) * s + s)).sum())
+    f, b = native.selinv_plan_stats(plan, native.SELINV_F64)
+    assert f == F and b == B
+    f2, b2 = native.selinv_plan_stats(plan, native.SELINV_C128)
+    assert f2 == 4 * F and b2 == 2 * B
+
+
+def _sym_arrays(p):
+    sym = oracle.symbolic_for(p)
+    return sym, [sym.super_ptr.copy(), sym.sparent.copy(), sym.rowptr.copy(), sym.rows.copy()]
+
+
+def test_rejects_malformed_plans(native):
+    p = synth.laplacian_3d(5, seed=1)
+    sym, (sp, par, rp, rows) = _sym_arrays(p)
+    n, ns = sym.n, sym.nsuper
+
+    def code(sp_, par_, rp_, rows_, n_=n, ns_=ns):
+        try:
+            native.selinv_symbolic(n_, ns_, sp_, par_, rp_, rows_)
+            return 0
+        except native.SelinvError as e:
+            return e.code
+
+    assert code(sp, par, rp, rows) == 0
+    # parent not the owner of the first row below (breaks the tree)
+    K = int(np.nonzero(par >= 0)[0][0])
+    bad = par.copy(); bad[K] = K
+    assert code(sp, bad, rp, rows) == -2
+    bad = par.copy(); bad[ns - 1] = 0
+    assert code(sp, bad, rp, rows) == -2
+    # unsorted rows
+    K = int(np.argmax(np.diff(rp) - np.diff(sp) >= 2))
+    bad = rows.copy()
+    s = sp[K + 1] - sp[K]
+    a, b = rp[K] + s, rp[K] + s + 1
+    bad[a], bad[b] = bad[b], bad[a]
+    assert code(sp, par, rp, bad) == -3
+    # structure not closed under the tree: remove from the row list of the
+    # owner J of C_K[0] a row C_K[p] that lies below J's own columns
+    col2s = np.repeat(np.arange(ns), np.diff(sp))
+    found = False
+    for K in range(ns):
+        s = sp[K + 1] - sp[K]
+        C = rows[rp[K] + s:rp[K + 1]]
+        if C.size < 2:
+            continue
+        J = col2s[C[0]]
+        below = [x for x in C[1:] if x >= sp[J + 1]]
+        if not below:
+            continue
+        RJ = rows[rp[J]:rp[J + 1]]
+        drop = rp[J] + int(np.searchsorted(RJ, below[0]))
+        rows2 = np.delete(rows, drop)
+        rp2 = rp.copy(); rp2[J + 1:] -= 1
+        assert code(sp, par, rp2, rows2) in (-3, -2)
+        found = True
+        break
+    assert found
+    # super_ptr not increasing / not ending at n
+    bad = sp.copy(); bad[-1] = n + 1
+    assert code(bad, par, rp, rows) == -1
+    # bad sizes
+    assert code(sp, par, rp, rows, ns_=-1) == -1
+
+
+def test_analysis_rejects_bad_csc(native):
+    p = synth.random_sparse_spd(30, 0.2, 9)
+    ri = p.rowind.copy()
+    c0 = int(np.argmax(np.diff(p.colptr) >= 2))
+    ri[p.colptr[c0]] = -1 if c0 == 0 else c0 - 1         # row above the diagonal
+    with pytest.raises(native.SelinvError) as e:
+        native.selinv_analyse(p.n, p.colptr, ri, 0, 64, 0.0)
+    assert e.value.code == -3
+    with pytest.raises(native.SelinvError) as e:
+        native.selinv_analyse(p.n, p.colptr, p.rowind, 0, 0, 0.0)
+    assert e.value.code == -1
+
+
+def test_status_without_device_work_is_ok(native):
+    p = synth.tridiagonal(10)
+    sym = oracle.symbolic_for(p)
+    plan = make_plan(native, sym)
+    assert native.selinv_status(plan) == 0
