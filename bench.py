@@ -1,0 +1,337 @@
+#!/usr/bin/env python
+"""Benchmark: supernodal selected inversion on one GB300.
+
+Workload (default): 3D 7-point Laplacian on a 40^3 grid (N = 64000), diagonal
+6 + U(0,1), geometric nested dissection, relaxed supernodes (<= 128 columns,
+<= 10% explicit zeros), real FP64, synthetic and seeded.  One step = one
+selected inversion: normalization (L_KK^{-1}, Dinv, Lhat), the root-to-leaf
+traversal (gather of A^{-1}_{C,C}, A^{-1}_{C,K}, A^{-1}_{K,K}) and the
+write-back, on a plan built once for the pattern; the factors come from the
+library's GPU LDL^T, outside the timed region.
+
+Metric: GFLOP/s of the algorithmic count F = sum_K 2c^2 s + 2cs^2 + cs^2 + s^3
+(same F for every variant), time per step, fraction of the FP64 roof.
+Multi-GPU: replicas only (one independent selected inversion per rank).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.070   # SMs x FP64 FMA/clk/SM x flop/FMA x GHz = 1258.6
+METRIC = "selinv time and FP64 GFLOP/s (% of peak); batched & adjoint vs plain on one GB300"
+WORKLOAD = "3D 7-point Laplacian 40^3 (N=64000), diag 6+U(0,1), nested dissection, relaxed supernodes <=128 cols / <=10% zeros, FP64, plain selinv"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--config", type=int, default=2)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--schedule", type=int, default=1, help="0 plain, 1 level")
+    return ap.parse_args()
+
+
+def dist_info():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons while running."""
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+            time.sleep(0.3)
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            time.sleep(0.2)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = max(mx, float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx or None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for f in ("kernels_selinv.cu", "common.cuh"):
+        with open(os.path.join(ROOT, "paper_1604_02528_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel: str):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, if it
+    was taken on the current kernel sources (else None)."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.txt")
+    if not os.path.exists(path):
+        return None
+    want = kernel_source_hash()
+    for line in open(path):
+        parts = line.split()
+        if len(parts) >= 3 and parts[0] == kernel and parts[1] == want:
+            return float(parts[2])
+    return None
+
+
+def sample_kmin(sym, flops_target):
+    """Smallest K such that the root-side supernodes K..N carry ~flops_target."""
+    s, c = sym.sizes()
+    F = (2 * c * c * s + 2 * c * s * s + c * s * s + s ** 3).astype(np.float64)
+    acc = np.cumsum(F[::-1])
+    idx = int(np.searchsorted(acc, flops_target))
+    kmin = max(0, sym.nsuper - 1 - idx)
+    return kmin, float(F[kmin:].sum())
+
+
+def oracle_sample_setup(problem):
+    import oracle
+    sym = oracle.symbolic_for(problem)
+    L, D = oracle.ldlt(problem, sym)
+    return sym, L, D
+
+
+def oracle_sample_run(sym, L, D, kmin):
+    import oracle
+    t = time.perf_counter()
+    oracle.selinv_top(sym, L, D, kmin)
+    return time.perf_counter() - t
+
+
+def run_reference(args):
+    """The CPU oracle, as it stands, on bounded root-side samples of the workload."""
+    rank, world, _ = dist_info()
+    if rank != 0:
+        return
+    import synth
+    p = synth.make_config(args.config)
+    sym, L, D = oracle_sample_setup(p)
+    kmin, fs = sample_kmin(sym, 3.0e9)
+    for _ in range(args.warmup):
+        oracle_sample_run(sym, L, D, kmin)
+    times = [oracle_sample_run(sym, L, D, kmin) for _ in range(args.steps)]
+    tot = sum(times)
+    value = fs * len(times) / tot / 1e9
+    sample = (f"supernodes {kmin}..{sym.nsuper - 1} of {sym.nsuper} (root side of the tree), "
+              f"{fs:.3e} of {sample_kmin(sym, 1e30)[1]:.3e} flops per step")
+    line = {"impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": "GFLOP/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(1e3 * tot / len(times), 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "sample": sample},
+            "cpu_baseline": {"value": round(value, 4), "unit": "GFLOP/s", "cores": 1,
+                             "kind": "oracle", "sample": sample},
+            "e2e": {"value": round(value, 4), "unit": "GFLOP/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_info()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group(backend="gloo")
+    if args.impl == "reference":
+        run_reference(args)
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+        return
+
+    import torch
+    import synth
+    from paper_1604_02528_gb300 import _native as N
+    from paper_1604_02528_gb300.api import SelInvContext
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    p = synth.make_config(args.config)
+    ctx = SelInvContext.from_problem(p)
+    o = N.selinv_default_opts()
+    o.schedule = args.schedule
+    N.selinv_plan_set_opts(ctx.plan, o)
+    dt = N.SELINV_C128 if p.values.dtype.kind == "c" else N.SELINV_F64
+    A = torch.from_numpy(p.values).to(dev)
+    L, D = ctx.factor(A)
+    torch.cuda.synchronize()
+    if ctx.status() != 0:
+        raise RuntimeError("factorization reported a device error")
+    F, B = ctx.stats(dt)
+    Z = torch.empty_like(L)
+    stream = torch.cuda.Stream(device=dev)
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)  # > L2 (129 MB)
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            N.selinv_numeric(ctx.plan, dt, L, D, Z, stream)
+    stream.synchronize()
+    if ctx.status() != 0:
+        raise RuntimeError("selected inversion reported a device error")
+
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    torch.cuda.synchronize()
+    launches0 = N.selinv_launch_count()
+    with ClockSampler(local) as clk:
+        with torch.cuda.stream(stream):
+            for i in range(args.steps):
+                flush.fill_(i & 0xFF)          # evict L2 between timed steps (outside events)
+                ev[i][0].record(stream)
+                N.selinv_numeric(ctx.plan, dt, L, D, Z, stream)
+                ev[i][1].record(stream)
+        stream.synchronize()
+    torch.cuda.synchronize()
+    launches = N.selinv_launch_count() - launches0
+    times = [a.elapsed_time(b) for a, b in ev]
+    tot_ms = sum(times)
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([tot_ms], dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        tot_ms = float(t.item())
+    ms_step = tot_ms / args.steps
+    value = world * F / (ms_step * 1e-3) / 1e9
+
+    # roofline of the dominant kernel (the fused gather-GEMM + diagonal block)
+    kms, kcnt = N.selinv_numeric_profile(ctx.plan, dt, L, D, Z, stream)
+    s_, c_ = None, None
+    sp = np.asarray(ctx.analysis["super_ptr"], np.int64)
+    rp = np.asarray(ctx.analysis["rowptr"], np.int64)
+    s_ = np.diff(sp).astype(np.float64)
+    c_ = np.diff(rp).astype(np.float64) - s_
+    mult = 4.0 if dt == N.SELINV_C128 else 1.0
+    f_dom = mult * float((2 * c_ * c_ * s_ + 2 * c_ * s_ * s_).sum())   # A4 + A5 contractions
+    achieved = f_dom / (kms[2] * 1e-3) / 1e9 if kms[2] > 0 else None
+    traffic = ncu_traffic("k_selinv")
+    roof = {"bound": "alu", "achieved": round(achieved, 3) if achieved else None,
+            "peak": round(FP64_PEAK_GFLOPS, 1), "unit": "GFLOP/s",
+            "frac": round(achieved / FP64_PEAK_GFLOPS, 4) if achieved else None,
+            "traffic": traffic, "kernel": "k_selinv",
+            "kernel_ms_per_step": round(kms[2], 3), "launches_per_step": kcnt[2],
+            "peak_note": "FP64 FMA pipe: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (measured DFMA loop 1204)"}
+
+    # end to end through the C ABI from host buffers: plan from host arrays,
+    # H2D of L and D, selected inversion, D2H of A^{-1}
+    Lh = L.cpu().pin_memory()
+    Dh = D.cpu().pin_memory()
+    Zh = torch.empty(Z.shape, dtype=Z.dtype).pin_memory()
+    a = ctx.analysis
+    e2e_steps = max(3, min(args.steps, 10))
+    Ld = torch.empty_like(L)
+    Dd = torch.empty_like(D)
+    Zd = torch.empty_like(Z)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        plan = N.selinv_symbolic(p.n, a["nsuper"], a["super_ptr"], a["sparent"], a["rowptr"], a["rows"])
+        with torch.cuda.stream(stream):
+            Ld.copy_(Lh, non_blocking=True)
+            Dd.copy_(Dh, non_blocking=True)
+            N.selinv_numeric(plan, dt, Ld, Dd, Zd, stream)
+            Zh.copy_(Zd, non_blocking=True)
+        stream.synchronize()
+        del plan
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    esz = L.element_size()
+    e2e = {"value": round(world * F / e2e_s / 1e9, 4), "unit": "GFLOP/s",
+           "h2d_bytes_per_step": int((L.numel() + D.numel()) * esz),
+           "d2h_bytes_per_step": int(Z.numel() * esz),
+           "ms_per_step": round(1e3 * e2e_s, 3),
+           "includes": "selinv_symbolic from host arrays + H2D + selinv_numeric + D2H"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        sym, Lo, Do = oracle_sample_setup(p)
+        kmin, fs = sample_kmin(sym, 1.2e10)
+        secs = oracle_sample_run(sym, Lo, Do, kmin)
+        cpu = {"value": round(fs / secs / 1e9, 4), "unit": "GFLOP/s", "cores": 1, "kind": "oracle",
+               "sample": f"root-side supernodes {kmin}..{sym.nsuper - 1} of {sym.nsuper}, "
+                         f"{fs:.3e} of {F:.3e} flops, {secs:.1f} s"}
+
+    clocks = clk.summary()
+    if rank == 0:
+        line = {"metric": METRIC, "value": round(value, 3), "unit": "GFLOP/s", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_step, 3),
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                "data": "synthetic",
+                "config": {"workload": WORKLOAD, "n": p.n, "nsuper": ctx.nsuper, "nnz_L": ctx.nnz,
+                           "flops_per_step": F, "bytes_per_step": B,
+                           "schedule": ["plain", "level"][args.schedule],
+                           "l2": "flushed between timed steps (256 MB write)",
+                           "parallelism": "replicas" if world > 1 else "single GPU",
+                           "fp64_frac": round(value / world / FP64_PEAK_GFLOPS, 4)},
+                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": int(launches), "clocks": clocks}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

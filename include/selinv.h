@@ -209,6 +209,15 @@ int selinv_factor_adjoint(selinv_plan plan, selinv_dtype dtype, const void *L_de
                           const void *D_dev, const void *L_bar_dev, const void *D_bar_dev,
                           void *A_bar_vals_dev, void *cuda_stream);
 
+/* Runs selinv_numeric once without graph capture, timing every kernel
+ * launch with CUDA events on the stream, and synchronizes.  kernel_ms[k] and
+ * kernel_launches[k] (k = 0: L_KK^{-1} / Dinv, 1: Lhat, 2: the fused
+ * gather-GEMM + diagonal block) receive the summed device time in ms and the
+ * launch count of each kernel kind.  For measurement only. */
+int selinv_numeric_profile(selinv_plan plan, selinv_dtype dtype, const void *L_dev,
+                           const void *D_dev, void *Ainv_dev, void *cuda_stream, double *kernel_ms,
+                           int64_t *kernel_launches);
+
 /* Device status word of the plan after asynchronous work (synchronizes the
  * plan's last stream, then returns and clears the latched code: SELINV_OK,
  * SELINV_ERR_TIMEOUT, SELINV_ERR_ZERO_PIVOT or SELINV_ERR_NONFINITE). */

@@ -52,6 +52,9 @@ def _load():
                 f = getattr(lib, name + sfx)
                 f.restype = ct.c_int
                 f.argtypes = [ct.c_int32, P, P, P, P, P, P, P, ct.c_int]
+            f = getattr(lib, "orc_selinv_top" + sfx)
+            f.restype = ct.c_int
+            f.argtypes = [ct.c_int32, P, P, P, P, P, P, P, ct.c_int, ct.c_int32]
             f = getattr(lib, "orc_selinv_adjoint" + sfx)
             f.restype = ct.c_int
             f.argtypes = [ct.c_int32, P, P, P, P, P, P, P, P, P, P]
@@ -199,6 +202,19 @@ def selinv(sym: Sym, L: np.ndarray, D: np.ndarray, symmetrize: bool = True) -> n
     rc = getattr(lib, "orc_selinv" + _sfx(L.dtype))(*_sym_args(sym), _p(L), _p(D), _p(Z),
                                                    int(symmetrize))
     _check(rc, "selinv")
+    return Z
+
+
+def selinv_top(sym: Sym, L: np.ndarray, D: np.ndarray, kmin: int, Z: np.ndarray = None,
+               symmetrize: bool = True) -> np.ndarray:
+    """Alg. 1 for the supernodes K >= kmin only (root side of the tree)."""
+    lib = _load()
+    L = np.ascontiguousarray(L); D = np.ascontiguousarray(D, dtype=L.dtype)
+    if Z is None:
+        Z = np.zeros_like(L)
+    rc = getattr(lib, "orc_selinv_top" + _sfx(L.dtype))(*_sym_args(sym), _p(L), _p(D), _p(Z),
+                                                       int(symmetrize), int(kmin))
+    _check(rc, "selinv_top")
     return Z
 
 

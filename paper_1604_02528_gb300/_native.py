@@ -55,6 +55,7 @@ def _load() -> ct.CDLL:
         "selinv_plan_set_opts": (I, [P, P]),
         "selinv_numeric": (I, [P, I, P, P, P, P]),
         "selinv_numeric_batched": (I, [I, P, P, P, P, P, P]),
+        "selinv_numeric_profile": (I, [P, I, P, P, P, P, P, P]),
         "selinv_plan_set_matrix": (I, [P, I32, P, P]),
         "selinv_factor": (I, [P, I, P, P, P, P]),
         "selinv_adjoint": (I, [P, I, P, P, P, P, P, P, P]),
@@ -77,7 +78,7 @@ REQUIRED_SYMBOLS = ("selinv_default_opts", "selinv_analyse", "selinv_analysis_ge
                     "selinv_analysis_destroy", "selinv_symbolic", "selinv_plan_destroy",
                     "selinv_plan_nnz", "selinv_plan_panel_offset", "selinv_plan_stats",
                     "selinv_plan_get", "selinv_plan_set_opts", "selinv_numeric",
-                    "selinv_numeric_batched", "selinv_plan_set_matrix", "selinv_factor",
+                    "selinv_numeric_batched", "selinv_numeric_profile", "selinv_plan_set_matrix", "selinv_factor",
                     "selinv_adjoint", "selinv_factor_adjoint", "selinv_status",
                     "selinv_error_string", "selinv_launch_count")
 
@@ -227,6 +228,15 @@ def selinv_plan_set_opts(plan: Plan, opts: selinv_opts):
 def selinv_numeric(plan: Plan, dtype: int, L, D, Ainv, stream=None):
     _check(LIB.selinv_numeric(plan.handle, int(dtype), _dptr(L), _dptr(D), _dptr(Ainv),
                               _stream(stream)), "selinv_numeric")
+
+
+def selinv_numeric_profile(plan: Plan, dtype: int, L, D, Ainv, stream=None):
+    """Per-kernel-kind device time (ms) and launch counts of one call."""
+    ms = (ct.c_double * 3)()
+    cnt = (ct.c_int64 * 3)()
+    _check(LIB.selinv_numeric_profile(plan.handle, int(dtype), _dptr(L), _dptr(D), _dptr(Ainv),
+                                      _stream(stream), ms, cnt), "selinv_numeric_profile")
+    return list(ms), list(cnt)
 
 
 def selinv_numeric_batched(plans: Sequence[Plan], dtypes: Sequence[int], Ls, Ds, Zs, stream=None):

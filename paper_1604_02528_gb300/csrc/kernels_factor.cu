@@ -1,0 +1,352 @@
+// Prerequisite factorization A = L D L^T without pivoting, supernodal,
+// left-looking, level by level from the leaves (Sec. IV of the paper uses a
+// supernodal factorization with a symmetric permutation and no dynamic
+// pivoting; Sec. II-C: LDL^T for symmetric A).
+//
+//   k_assemble  scatter A's CSC values into the panels (after a memset)
+//   k_fupdate   one row tile of supernode J pulls the updates of every
+//               descendant K whose C meets J's columns:
+//                 panel_J(rel(p), col(q)) -= sum_k L_K(p,k) D_K(k) L_K(q,k)
+//               over the run of C_K owned by J (p >= q) -- the same owner
+//               segments and relative indices the selected inversion
+//               gathers with.  Each tile owns its rows: no atomics,
+//               a fixed descendant order: deterministic.
+//   k_fdiag     dense LDL^T of J's diagonal block in place (one CTA)
+//   k_ftrsm     L(C,J) = A(C,J) L_JJ^{-T} D_J^{-1}, one thread per row
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "common.cuh"
+#include "launch.h"
+#include "plan.h"
+
+namespace selinv {
+
+struct FactorDesc {
+    const int32_t *super_ptr;
+    const int64_t *rowptr;
+    const int64_t *panel_off;
+    const int32_t *relidx;
+    const int64_t *rel_ptr;
+    const int32_t *seg_K, *seg_start, *seg_end, *seg_coloff;
+    const int64_t *dseg_ptr;  // [ns+1] segments owned by J (descendant updates)
+    const int32_t *dseg;
+    void *L;
+    void *D;
+    int *status;
+};
+
+struct FactorData {
+    int32_t n = -1;
+    int64_t nnzA = 0;
+    std::vector<int64_t> a_pos;       // panel position of every stored entry of A
+    int64_t *d_a_pos = nullptr;
+    int32_t *d_seg_K = nullptr, *d_seg_start = nullptr, *d_seg_end = nullptr, *d_seg_coloff = nullptr;
+    int32_t *d_dseg = nullptr;
+    int64_t *d_dseg_ptr = nullptr, *d_rel_ptr = nullptr;
+    // launch lists
+    std::vector<int2> h_tiles;        // (J, row tile) per level, leaves first
+    std::vector<int> h_js;            // J per level
+    std::vector<int64_t> tile_lptr, j_lptr;
+    int2 *d_tiles = nullptr;
+    int *d_js = nullptr;
+    FactorDesc *d_desc = nullptr;
+    const void *key_L = nullptr, *key_D = nullptr;
+    int key_dtype = -1;
+    // adjoint state
+    void *adj = nullptr;
+};
+
+constexpr int kFT = 64;  // rows per factor tile
+
+template <typename T>
+__global__ void k_assemble(const int64_t *__restrict__ pos, const T *__restrict__ vals, int64_t nnz,
+                           T *__restrict__ L) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nnz;
+         e += (int64_t)gridDim.x * blockDim.x)
+        L[pos[e]] = vals[e];
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_fupdate(const FactorDesc *__restrict__ fd,
+                                                 const int2 *__restrict__ tiles, int ntiles) {
+    const int w = blockIdx.x;
+    if (w >= ntiles) return;
+    const FactorDesc &F = *fd;
+    const int J = tiles[w].x;
+    const int rt = tiles[w].y;
+    const int64_t ldJ = F.rowptr[J + 1] - F.rowptr[J];
+    const int64_t r0 = (int64_t)rt * kFT;
+    const int64_t r1 = r0 + kFT < ldJ ? r0 + kFT : ldJ;
+    T *PJ = static_cast<T *>(F.L) + F.panel_off[J];
+    const T *Lall = static_cast<const T *>(F.L);
+    const T *Dall = static_cast<const T *>(F.D);
+    __shared__ int s_pa, s_pb;
+    for (int64_t di = F.dseg_ptr[J]; di < F.dseg_ptr[J + 1]; di++) {
+        const int t = F.dseg[di];
+        const int K = F.seg_K[t];
+        const int st = F.seg_start[t], en = F.seg_end[t], coloff = F.seg_coloff[t];
+        const int sK = F.super_ptr[K + 1] - F.super_ptr[K];
+        const int64_t ldK = F.rowptr[K + 1] - F.rowptr[K];
+        const int cK = (int)(ldK - sK);
+        const int32_t *rel = F.relidx + F.rel_ptr[t];  // rel[p - st], p in [st, cK)
+        __syncthreads();  // previous descendant's updates are complete
+        if (threadIdx.x == 0) {
+            // p-range whose target rows fall in [r0, r1): rel is increasing
+            int a = st, b = cK;
+            while (a < b) { const int m = (a + b) / 2; if (rel[m - st] < r0) a = m + 1; else b = m; }
+            int c2 = a, d2 = cK;
+            while (c2 < d2) { const int m = (c2 + d2) / 2; if (rel[m - st] < r1) c2 = m + 1; else d2 = m; }
+            s_pa = a;
+            s_pb = c2;
+        }
+        __syncthreads();
+        const int pa = s_pa, pb = s_pb;
+        const int np = pb - pa, nq = en - st;
+        if (np <= 0) continue;
+        const T *LK = Lall + F.panel_off[K];
+        const T *DK = Dall + F.super_ptr[K];
+        for (int e = threadIdx.x; e < np * nq; e += blockDim.x) {
+            const int p = pa + e % np, q = st + e / np;
+            if (p < q) continue;  // strictly upper part of J's diagonal block: not stored
+            T u = Sc<T>::zero();
+            for (int k = 0; k < sK; k++)
+                madd(u, mul(LK[(int64_t)k * ldK + sK + p], DK[k]), LK[(int64_t)k * ldK + sK + q]);
+            T *dst = PJ + (int64_t)(coloff + q - st) * ldJ + rel[p - st];
+            *dst = sub(*dst, u);
+        }
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_fdiag(const FactorDesc *__restrict__ fd,
+                                               const int *__restrict__ js, int nj) {
+    const int w = blockIdx.x;
+    if (w >= nj) return;
+    const FactorDesc &F = *fd;
+    const int J = js[w];
+    const int fc = F.super_ptr[J];
+    const int s = F.super_ptr[J + 1] - fc;
+    const int64_t ld = F.rowptr[J + 1] - F.rowptr[J];
+    T *P = static_cast<T *>(F.L) + F.panel_off[J];
+    T *D = static_cast<T *>(F.D) + fc;
+    __shared__ T s_d;
+    for (int j = 0; j < s; j++) {
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            const T d = P[(int64_t)j * ld + j];
+            if (is_zero(d) || !finite_val(d)) atomicCAS(F.status, 0, SELINV_ERR_ZERO_PIVOT);
+            s_d = d;
+            D[j] = d;
+        }
+        __syncthreads();
+        const T rd = recip(s_d);
+        for (int i = j + 1 + threadIdx.x; i < s; i += blockDim.x) P[(int64_t)j * ld + i] = mul(P[(int64_t)j * ld + i], rd);
+        __syncthreads();
+        // a_ik -= L_ij d L_kj for j < k <= i < s
+        const int m = s - j - 1;
+        for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
+            const int i = j + 1 + e % m, k = j + 1 + e / m;
+            if (k > i) continue;
+            T *a = P + (int64_t)k * ld + i;
+            *a = sub(*a, mul(mul(P[(int64_t)j * ld + i], s_d), P[(int64_t)j * ld + k]));
+        }
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < s * s; e += blockDim.x) {
+        const int i = e % s, k = e / s;
+        if (i == k) P[(int64_t)k * ld + i] = Sc<T>::one();
+        else if (i < k) P[(int64_t)k * ld + i] = Sc<T>::zero();
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(64) k_ftrsm(const FactorDesc *__restrict__ fd,
+                                              const int2 *__restrict__ tiles, int ntiles) {
+    const int w = blockIdx.x;
+    if (w >= ntiles) return;
+    const FactorDesc &F = *fd;
+    const int J = tiles[w].x;
+    const int fc = F.super_ptr[J];
+    const int s = F.super_ptr[J + 1] - fc;
+    const int64_t ld = F.rowptr[J + 1] - F.rowptr[J];
+    const int64_t r = (int64_t)tiles[w].y * kFT + threadIdx.x;  // panel row
+    if (r < s || r >= ld) return;
+    T *P = static_cast<T *>(F.L) + F.panel_off[J];
+    const T *D = static_cast<const T *>(F.D) + fc;
+    // x (D L_JJ^T) = a : x_j = (a_j - sum_{k<j} x_k D_k L_jk) / D_j, in place
+    for (int j = 0; j < s; j++) {
+        T acc = P[(int64_t)j * ld + r];
+        for (int k = 0; k < j; k++) msub(acc, mul(P[(int64_t)k * ld + r], D[k]), P[(int64_t)k * ld + j]);
+        P[(int64_t)j * ld + r] = mul(acc, recip(D[j]));
+    }
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+void factor_release(selinv_plan_s *plan) {
+    FactorData *f = plan->factor;
+    if (!f) return;
+    auto fr = [](void *p) { if (p) cudaFree(p); };
+    fr(f->d_a_pos); fr(f->d_seg_K); fr(f->d_seg_start); fr(f->d_seg_end); fr(f->d_seg_coloff);
+    fr(f->d_dseg); fr(f->d_dseg_ptr); fr(f->d_rel_ptr); fr(f->d_tiles); fr(f->d_js); fr(f->d_desc);
+    adjoint_release(f->adj);
+    delete f;
+    plan->factor = nullptr;
+}
+
+template <typename X>
+static int up(X **d, const std::vector<X> &h) {
+    *d = nullptr;
+    if (cudaMalloc((void **)d, sizeof(X) * std::max<size_t>(1, h.size())) != cudaSuccess) return SELINV_ERR_OOM;
+    if (!h.empty() && cudaMemcpy(*d, h.data(), sizeof(X) * h.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+        return SELINV_ERR_CUDA;
+    return SELINV_OK;
+}
+
+// segment tables (descendant lists per owner) shared by factor and adjoint
+int factor_tables(selinv_plan_s *plan) {
+    FactorData *f = plan->factor;
+    if (f->d_dseg) return SELINV_OK;
+    const PlanData &p = plan->data;
+    int rc = ensure_device(plan->data);
+    if (rc) return rc;
+    const size_t nseg = p.seg_owner.size();
+    std::vector<int32_t> segK(nseg), segEnd(nseg);
+    for (int32_t K = 0; K < p.ns; K++) {
+        const int64_t c = p.rowptr[K + 1] - p.rowptr[K] - (p.super_ptr[K + 1] - p.super_ptr[K]);
+        for (int64_t t = p.seg_ptr[K]; t < p.seg_ptr[K + 1]; t++) {
+            segK[t] = K;
+            segEnd[t] = (t + 1 < p.seg_ptr[K + 1]) ? p.seg_start[t + 1] : (int32_t)c;
+        }
+    }
+    std::vector<int64_t> dptr(p.ns + 1, 0);
+    for (size_t t = 0; t < nseg; t++) dptr[p.seg_owner[t] + 1]++;
+    for (int32_t J = 0; J < p.ns; J++) dptr[J + 1] += dptr[J];
+    std::vector<int32_t> dseg(std::max<size_t>(1, nseg));
+    {
+        std::vector<int64_t> fl(dptr.begin(), dptr.end() - 1);
+        for (size_t t = 0; t < nseg; t++) dseg[fl[p.seg_owner[t]]++] = (int32_t)t;  // ascending K
+    }
+    // per-level launch lists, leaves first
+    f->h_tiles.clear(); f->h_js.clear();
+    f->tile_lptr.assign(1, 0); f->j_lptr.assign(1, 0);
+    for (int l = p.nlevels - 1; l >= 0; l--) {
+        for (int64_t e = p.level_ptr[l]; e < p.level_ptr[l + 1]; e++) {
+            const int32_t J = p.level_list[e];
+            const int64_t ld = p.rowptr[J + 1] - p.rowptr[J];
+            for (int64_t t = 0; t < (ld + kFT - 1) / kFT; t++) f->h_tiles.push_back(make_int2(J, (int)t));
+            f->h_js.push_back(J);
+        }
+        f->tile_lptr.push_back((int64_t)f->h_tiles.size());
+        f->j_lptr.push_back((int64_t)f->h_js.size());
+    }
+    if ((rc = up(&f->d_seg_K, segK))) return rc;
+    if ((rc = up(&f->d_seg_start, p.seg_start))) return rc;
+    if ((rc = up(&f->d_seg_end, segEnd))) return rc;
+    if ((rc = up(&f->d_seg_coloff, p.seg_coloff))) return rc;
+    if ((rc = up(&f->d_dseg_ptr, dptr))) return rc;
+    if ((rc = up(&f->d_dseg, dseg))) return rc;
+    if ((rc = up(&f->d_rel_ptr, p.rel_ptr))) return rc;
+    if ((rc = up(&f->d_tiles, f->h_tiles))) return rc;
+    if ((rc = up(&f->d_js, f->h_js))) return rc;
+    if (cudaMalloc((void **)&f->d_desc, sizeof(FactorDesc)) != cudaSuccess) return SELINV_ERR_OOM;
+    return SELINV_OK;
+}
+
+FactorDesc *factor_desc(selinv_plan_s *plan, void *L, void *D, cudaStream_t st) {
+    FactorData *f = plan->factor;
+    const PlanData &p = plan->data;
+    FactorDesc h;
+    h.super_ptr = p.d_super_ptr;
+    h.rowptr = p.d_rowptr;
+    h.panel_off = p.d_panel_off;
+    h.relidx = p.d_relidx;
+    h.rel_ptr = f->d_rel_ptr;
+    h.seg_K = f->d_seg_K;
+    h.seg_start = f->d_seg_start;
+    h.seg_end = f->d_seg_end;
+    h.seg_coloff = f->d_seg_coloff;
+    h.dseg_ptr = f->d_dseg_ptr;
+    h.dseg = f->d_dseg;
+    h.L = L;
+    h.D = D;
+    h.status = p.d_status;
+    cudaMemcpyAsync(f->d_desc, &h, sizeof(h), cudaMemcpyHostToDevice, st);
+    return f->d_desc;
+}
+
+template <typename T>
+static int factor_t(selinv_plan_s *plan, const void *A, void *L, void *D, cudaStream_t st) {
+    FactorData *f = plan->factor;
+    const PlanData &p = plan->data;
+    FactorDesc *fd = factor_desc(plan, L, D, st);
+    if (cudaMemsetAsync(L, 0, sizeof(T) * (size_t)p.nnz, st) != cudaSuccess) return SELINV_ERR_CUDA;
+    if (f->nnzA > 0) {
+        const int blocks = (int)std::min<int64_t>((f->nnzA + 255) / 256, 152 * 8);
+        k_assemble<T><<<blocks, 256, 0, st>>>(f->d_a_pos, static_cast<const T *>(A), f->nnzA, static_cast<T *>(L));
+        note_launch();
+    }
+    const int nl = (int)f->tile_lptr.size() - 1;
+    for (int l = 0; l < nl; l++) {
+        const int64_t t0 = f->tile_lptr[l], t1 = f->tile_lptr[l + 1];
+        const int64_t j0 = f->j_lptr[l], j1 = f->j_lptr[l + 1];
+        if (t1 > t0) k_fupdate<T><<<(int)(t1 - t0), 256, 0, st>>>(fd, f->d_tiles + t0, (int)(t1 - t0));
+        if (j1 > j0) k_fdiag<T><<<(int)(j1 - j0), 256, 0, st>>>(fd, f->d_js + j0, (int)(j1 - j0));
+        if (t1 > t0) k_ftrsm<T><<<(int)(t1 - t0), kFT, 0, st>>>(fd, f->d_tiles + t0, (int)(t1 - t0));
+        note_launch(3);
+    }
+    return cudaGetLastError() == cudaSuccess ? SELINV_OK : SELINV_ERR_CUDA;
+}
+
+}  // namespace selinv
+
+using namespace selinv;
+
+extern "C" int selinv_plan_set_matrix(selinv_plan plan, int32_t n, const int64_t *colptr,
+                                      const int32_t *rowind) {
+    if (!plan || !colptr || (n > 0 && !rowind) || n != plan->data.n) return SELINV_ERR_INVALID_ARG;
+    const PlanData &p = plan->data;
+    std::vector<int32_t> col2s(n);
+    for (int32_t K = 0; K < p.ns; K++)
+        for (int32_t j = p.super_ptr[K]; j < p.super_ptr[K + 1]; j++) col2s[j] = K;
+    std::vector<int64_t> pos(colptr[n] > 0 ? colptr[n] : 0);
+    for (int32_t j = 0; j < n; j++) {
+        const int32_t K = col2s[j];
+        const int32_t *R = p.rows.data() + p.rowptr[K];
+        const int64_t m = p.rowptr[K + 1] - p.rowptr[K];
+        int64_t t = j - p.super_ptr[K];
+        for (int64_t e = colptr[j]; e < colptr[j + 1]; e++) {
+            const int32_t i = rowind[e];
+            if (i < j || i >= n) return SELINV_ERR_BAD_PATTERN;
+            while (t < m && R[t] < i) t++;
+            if (t >= m || R[t] != i) return SELINV_ERR_BAD_PATTERN;  // A not inside L's pattern
+            pos[e] = p.panel_off[K] + (int64_t)(j - p.super_ptr[K]) * m + t;
+        }
+    }
+    if (!plan->factor) plan->factor = new FactorData();
+    FactorData *f = plan->factor;
+    if (f->d_a_pos) cudaFree(f->d_a_pos);
+    f->d_a_pos = nullptr;
+    f->n = n;
+    f->nnzA = (int64_t)pos.size();
+    f->a_pos = pos;
+    int rc = ensure_device(plan->data);
+    if (rc) return rc;
+    return up(&f->d_a_pos, f->a_pos);
+}
+
+extern "C" int selinv_factor(selinv_plan plan, selinv_dtype dtype, const void *A, void *L, void *D,
+                             void *stream) {
+    if (!plan || !plan->factor || (dtype != SELINV_F64 && dtype != SELINV_C128)) return SELINV_ERR_INVALID_ARG;
+    if (plan->data.ns == 0) return SELINV_OK;
+    if (!L || !D || (plan->factor->nnzA > 0 && !A)) return SELINV_ERR_INVALID_ARG;
+    int rc = factor_tables(plan);
+    if (rc) return rc;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    plan->last_stream = st;
+    return dtype == SELINV_C128 ? factor_t<zd>(plan, A, L, D, st) : factor_t<double>(plan, A, L, D, st);
+}

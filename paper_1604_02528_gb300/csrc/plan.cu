@@ -516,6 +516,45 @@ extern "C" int selinv_numeric(selinv_plan plan, selinv_dtype dtype, const void *
     return run_schedule(S, st, p.opts.use_graph != 0);
 }
 
+extern "C" int selinv_numeric_profile(selinv_plan plan, selinv_dtype dtype, const void *L,
+                                      const void *D, void *Z, void *stream, double *kernel_ms,
+                                      int64_t *kernel_launches) {
+    if (!kernel_ms || !kernel_launches) return SELINV_ERR_INVALID_ARG;
+    // build (or reuse) the schedule through the normal path, without a graph
+    selinv_opts saved = plan ? plan->data.opts : selinv_opts{};
+    if (!plan) return SELINV_ERR_INVALID_ARG;
+    plan->data.opts.use_graph = 0;
+    int rc = selinv_numeric(plan, dtype, L, D, Z, stream);
+    plan->data.opts = saved;
+    if (rc) return rc;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (cudaStreamSynchronize(st) != cudaSuccess) return SELINV_ERR_CUDA;
+    Schedule &S = plan->single;
+    std::vector<cudaEvent_t> ev(2 * S.launches.size());
+    for (auto &e : ev) cudaEventCreate(&e);
+    for (int k = 0; k < 3; k++) { kernel_ms[k] = 0; kernel_launches[k] = 0; }
+    for (size_t i = 0; i < S.launches.size(); i++) {
+        const Launch &L = S.launches[i];
+        cudaEventRecord(ev[2 * i], st);
+        cudaError_t e;
+        if (L.kind == 0) e = launch_linv(L.dtype, S.d_descs, S.d_work + L.off, L.count, st);
+        else if (L.kind == 1) e = launch_lhat(L.dtype, L.bucket, S.d_descs, S.d_items + L.off, L.count, st);
+        else e = launch_selinv(L.dtype, L.bucket, S.d_descs, S.d_items + L.off, L.count, st);
+        cudaEventRecord(ev[2 * i + 1], st);
+        if (e != cudaSuccess) rc = SELINV_ERR_CUDA;
+    }
+    note_launch((int)S.launches.size());
+    if (cudaStreamSynchronize(st) != cudaSuccess) rc = SELINV_ERR_CUDA;
+    for (size_t i = 0; i < S.launches.size() && rc == SELINV_OK; i++) {
+        float ms = 0;
+        cudaEventElapsedTime(&ms, ev[2 * i], ev[2 * i + 1]);
+        kernel_ms[S.launches[i].kind] += ms;
+        kernel_launches[S.launches[i].kind] += 1;
+    }
+    for (auto &e : ev) cudaEventDestroy(e);
+    return rc;
+}
+
 extern "C" int selinv_numeric_batched(int nitems, const selinv_plan *plans, const selinv_dtype *dtypes,
                                       const void *const *L, const void *const *D, void *const *Z,
                                       void *stream) {

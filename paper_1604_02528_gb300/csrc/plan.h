@@ -97,4 +97,6 @@ struct selinv_plan_s {
 
 namespace selinv {
 void factor_release(selinv_plan_s *plan);
+void adjoint_release(void *adj);
+int factor_tables(selinv_plan_s *plan);
 }
