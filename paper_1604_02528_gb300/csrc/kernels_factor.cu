@@ -27,6 +27,7 @@ namespace selinv {
 struct FactorDesc {
     const int32_t *super_ptr;
     const int64_t *rowptr;
+    const int32_t *rows;
     const int64_t *panel_off;
     const int32_t *relidx;
     const int64_t *rel_ptr;
@@ -80,6 +81,7 @@ __global__ void __launch_bounds__(256) k_fupdate(const FactorDesc *__restrict__ 
     const int64_t ldJ = F.rowptr[J + 1] - F.rowptr[J];
     const int64_t r0 = (int64_t)rt * kFT;
     const int64_t r1 = r0 + kFT < ldJ ? r0 + kFT : ldJ;
+    const int fcJ = F.super_ptr[J];
     T *PJ = static_cast<T *>(F.L) + F.panel_off[J];
     const T *Lall = static_cast<const T *>(F.L);
     const T *Dall = static_cast<const T *>(F.D);
@@ -87,7 +89,7 @@ __global__ void __launch_bounds__(256) k_fupdate(const FactorDesc *__restrict__ 
     for (int64_t di = F.dseg_ptr[J]; di < F.dseg_ptr[J + 1]; di++) {
         const int t = F.dseg[di];
         const int K = F.seg_K[t];
-        const int st = F.seg_start[t], en = F.seg_end[t], coloff = F.seg_coloff[t];
+        const int st = F.seg_start[t], en = F.seg_end[t];
         const int sK = F.super_ptr[K + 1] - F.super_ptr[K];
         const int64_t ldK = F.rowptr[K + 1] - F.rowptr[K];
         const int cK = (int)(ldK - sK);
@@ -114,7 +116,9 @@ __global__ void __launch_bounds__(256) k_fupdate(const FactorDesc *__restrict__ 
             T u = Sc<T>::zero();
             for (int k = 0; k < sK; k++)
                 madd(u, mul(LK[(int64_t)k * ldK + sK + p], DK[k]), LK[(int64_t)k * ldK + sK + q]);
-            T *dst = PJ + (int64_t)(coloff + q - st) * ldJ + rel[p - st];
+            // the run's columns need not be consecutive columns of J: address by value
+            const int col = F.rows[F.rowptr[K] + sK + q] - fcJ;
+            T *dst = PJ + (int64_t)col * ldJ + rel[p - st];
             *dst = sub(*dst, u);
         }
     }
@@ -263,6 +267,7 @@ FactorDesc *factor_desc(selinv_plan_s *plan, void *L, void *D, cudaStream_t st) 
     FactorDesc h;
     h.super_ptr = p.d_super_ptr;
     h.rowptr = p.d_rowptr;
+    h.rows = p.d_rows;
     h.panel_off = p.d_panel_off;
     h.relidx = p.d_relidx;
     h.rel_ptr = f->d_rel_ptr;
