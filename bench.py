@@ -47,6 +47,8 @@ def parse():
     ap.add_argument("--config", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--schedule", type=int, default=1, help="0 plain, 1 level")
+    ap.add_argument("--fast", type=int, default=1,
+                    help="1: FP64-exact tensor-core contraction for s >= 16; 0: DFMA only")
     return ap.parse_args()
 
 
@@ -211,6 +213,7 @@ def main():
     ctx = SelInvContext.from_problem(p)
     o = N.selinv_default_opts()
     o.schedule = args.schedule
+    o.fast_contraction = args.fast
     N.selinv_plan_set_opts(ctx.plan, o)
     dt = N.SELINV_C128 if p.values.dtype.kind == "c" else N.SELINV_F64
     A = torch.from_numpy(p.values).to(dev)
@@ -257,23 +260,41 @@ def main():
     ms_step = tot_ms / args.steps
     value = world * F / (ms_step * 1e-3) / 1e9
 
-    # roofline of the dominant kernel (the fused gather-GEMM + diagonal block)
+    # roofline of the dominant kernel, timed live with CUDA events per launch
     kms, kcnt = N.selinv_numeric_profile(ctx.plan, dt, L, D, Z, stream)
-    s_, c_ = None, None
     sp = np.asarray(ctx.analysis["super_ptr"], np.int64)
     rp = np.asarray(ctx.analysis["rowptr"], np.int64)
     s_ = np.diff(sp).astype(np.float64)
     c_ = np.diff(rp).astype(np.float64) - s_
     mult = 4.0 if dt == N.SELINV_C128 else 1.0
-    f_dom = mult * float((2 * c_ * c_ * s_ + 2 * c_ * s_ * s_).sum())   # A4 + A5 contractions
-    achieved = f_dom / (kms[2] * 1e-3) / 1e9 if kms[2] > 0 else None
-    traffic = ncu_traffic("k_selinv")
-    roof = {"bound": "alu", "achieved": round(achieved, 3) if achieved else None,
-            "peak": round(FP64_PEAK_GFLOPS, 1), "unit": "GFLOP/s",
-            "frac": round(achieved / FP64_PEAK_GFLOPS, 4) if achieved else None,
-            "traffic": traffic, "kernel": "k_selinv",
-            "kernel_ms_per_step": round(kms[2], 3), "launches_per_step": kcnt[2],
-            "peak_note": "FP64 FMA pipe: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (measured DFMA loop 1204)"}
+    oz = (s_ >= 16) & (dt == N.SELINV_F64) & bool(args.fast)
+    dom = int(np.argmax(kms))
+    name = N.PROFILE_KINDS[dom]
+    # algorithmic flops of the supernodes each kernel kind processes
+    f_of = {"k_selinv": mult * float(((2 * c_ * c_ * s_ + 2 * c_ * s_ * s_) * ~oz).sum()),
+            "k_selinv_oz": mult * float((2 * c_ * c_ * s_ * oz).sum()),
+            "k_diag": mult * float((2 * c_ * s_ * s_ * oz).sum()),
+            "k_lhat": mult * float((c_ * s_ * s_).sum()),
+            "k_linv": mult * float((s_ ** 3).sum()),
+            "k_lhat_digits": 0.0}
+    f_dom = f_of[name]
+    achieved = f_dom / (kms[dom] * 1e-3) / 1e9 if kms[dom] > 0 else None
+    traffic = ncu_traffic(name)
+    if name == "k_selinv_oz":
+        # FP64-exact products on bf16 tensor cores: 28 digit-pair mma per FP64 product
+        peak, unit, bound = 604.0, "TFLOP/s", "tensor"
+        ach = 28.0 * f_dom / (kms[dom] * 1e-3) / 1e12 if kms[dom] > 0 else None
+        note = ("bf16 mma.sync m16n8k16 throughput measured on this GB300 (604 TFLOP/s); "
+                "achieved counts 28 bf16 digit-pair products per FP64 multiply-add")
+    else:
+        peak, unit, bound, ach = FP64_PEAK_GFLOPS, "GFLOP/s", "alu", achieved
+        note = "FP64 FMA pipe: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (measured DFMA loop 1204)"
+    roof = {"bound": bound, "achieved": round(ach, 3) if ach else None, "peak": peak, "unit": unit,
+            "frac": round(ach / peak, 4) if ach else None, "traffic": traffic, "kernel": name,
+            "kernel_ms_per_step": round(kms[dom], 3), "launches_per_step": int(kcnt[dom]),
+            "fp64_equiv_gflops": round(achieved, 2) if achieved else None,
+            "kernel_ms_all": {k: round(v, 3) for k, v in zip(N.PROFILE_KINDS, kms)},
+            "peak_note": note}
 
     # end to end through the C ABI from host buffers: plan from host arrays,
     # H2D of L and D, selected inversion, D2H of A^{-1}
@@ -322,6 +343,7 @@ def main():
                 "config": {"workload": WORKLOAD, "n": p.n, "nsuper": ctx.nsuper, "nnz_L": ctx.nnz,
                            "flops_per_step": F, "bytes_per_step": B,
                            "schedule": ["plain", "level"][args.schedule],
+                           "contraction": "bf16 tensor cores, FP64-exact slicing" if args.fast else "FP64 DFMA",
                            "l2": "flushed between timed steps (256 MB write)",
                            "parallelism": "replicas" if world > 1 else "single GPU",
                            "fp64_frac": round(value / world / FP64_PEAK_GFLOPS, 4)},

@@ -22,6 +22,9 @@ SELINV_SCHED_PLAIN = 0
 SELINV_SCHED_LEVEL = 1
 SELINV_SCHED_PERSISTENT = 2
 
+# kernel kinds reported by selinv_numeric_profile
+PROFILE_KINDS = ("k_linv", "k_lhat", "k_selinv", "k_lhat_digits", "k_selinv_oz", "k_diag")
+
 
 class SelinvError(RuntimeError):
     def __init__(self, code: int, what: str = ""):
@@ -231,9 +234,10 @@ def selinv_numeric(plan: Plan, dtype: int, L, D, Ainv, stream=None):
 
 
 def selinv_numeric_profile(plan: Plan, dtype: int, L, D, Ainv, stream=None):
-    """Per-kernel-kind device time (ms) and launch counts of one call."""
-    ms = (ct.c_double * 3)()
-    cnt = (ct.c_int64 * 3)()
+    """Per-kernel-kind device time (ms) and launch counts of one call, indexed
+    by PROFILE_KINDS."""
+    ms = (ct.c_double * len(PROFILE_KINDS))()
+    cnt = (ct.c_int64 * len(PROFILE_KINDS))()
     _check(LIB.selinv_numeric_profile(plan.handle, int(dtype), _dptr(L), _dptr(D), _dptr(Ainv),
                                       _stream(stream), ms, cnt), "selinv_numeric_profile")
     return list(ms), list(cnt)

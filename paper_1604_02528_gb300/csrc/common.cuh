@@ -91,6 +91,9 @@ struct ProbDesc {
     int *counter;               // [ns] tiles done per supernode
     int *done;                  // [ns] completion flags (persistent schedule)
     int *status;                // latched error code
+    uint16_t *lhs;              // bf16 digit planes of Lhat (tensor-core contraction)
+    const int64_t *lhs_off;     // [ns+1] offsets into lhs (elements)
+    int *colexp;                // [n] biased exponent of each column of Lhat
     int32_t ns, n;
     int32_t dtype;              // selinv_dtype
     int32_t symmetrize;

@@ -1,0 +1,772 @@
+// Reverse mode of the selected inversion and of the LDL^T factorization
+// (FP64).  The paper has no adjoint; this is the chain rule through the
+// steps of Alg. 1 taken in reverse order, with every accumulation written in
+// pull form so that each output has one owner (deterministic, no atomics).
+//
+// Selected-inversion adjoint, leaves -> root.  With Zbar the cotangent of
+// every stored lower entry of A^{-1}, for each K:
+//   S      = symmetric cotangent of the diagonal block (S_ii = Zbar_ii,
+//            S_ij = S_ji = Zbar_ij / 2)                       [k_adj_ybar]
+//   Ybar   = Zbar_{C,K} - Lhat S                              [k_adj_ybar]
+//   Lhatb  = -Y S - A^{-1}_{C,C} Ybar  (the gather recomputed) [k_adj_lhbar]
+//   Zbar(C,C) += sym(-Ybar Lhat^T): pulled by each ancestor J from its
+//            descendants' (Ybar, Lhat) over the owner runs of C [k_adj_pull]
+//   Lbar_CK = Lhatb M^T, M = L_KK^{-1}; Mbar = L_CK^T Lhatb + 2 D^{-1} M S;
+//   Lbar_KK = -(M^T Mbar M^T) strictly lower; Dbar_k = -(M S M^T)_kk / D_k^2
+//                                                             [k_adj_lhbar + finisher]
+// Factorization adjoint, root -> leaves (reverse of k_fupdate / k_fdiag / k_ftrsm):
+//   Lbar_CJ -= (Abar(C,C) L_CJ) o D, the gathered Abar with its diagonal
+//   doubled; Dbar_k -= 1/2 (L_CJ^T Abar(C,C) L_CJ)_kk          [k_fadj_pull]
+//   Abar_CJ = Lbar_CJ D^{-1} L_JJ^{-1}; Nbar = A_CJ^T Lbar_CJ;
+//   Ubar = -N^T Nbar N^T with N = L_JJ^{-T} D^{-1}; then the reverse of the
+//   dense LDL^T of the diagonal block                          [k_fadj_trsm + finisher]
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "common.cuh"
+#include "launch.h"
+#include "plan.h"
+#include "tile_gemm.cuh"
+
+namespace selinv {
+
+struct AdjDesc {
+    const int32_t *super_ptr;
+    const int64_t *rowptr;
+    const int32_t *rows;
+    const int64_t *panel_off;
+    const int64_t *colbase, *relbase;
+    const int32_t *relidx;
+    const int64_t *rel_ptr;
+    const int32_t *seg_K, *seg_start, *seg_end;
+    const int64_t *dseg_ptr;
+    const int32_t *dseg;
+    const int64_t *linv_off, *part_off;
+    const double *L, *D, *Z, *LD, *Linv;
+    double *Zb;       // working cotangent of A^{-1} (panels)
+    double *YB;       // S in the diagonal block, Ybar below (panels)
+    double *Lb;       // Lbar (panels)
+    double *Db;       // Dbar [n]
+    double *Ab;       // Abar (panels)
+    double *partial;  // split partials
+    int *counter;     // per-supernode tile counters
+    double *fin;      // finisher scratch: 2 s*s per supernode at 2*linv_off
+};
+
+struct AdjData {
+    bool built = false;
+    std::vector<Item> items;          // (J, tile, ntiles) per level, levels deepest first
+    std::vector<int64_t> lvl_ptr;     // per level: [start, end) of items, buckets sorted
+    std::vector<int> lvl_bucket_ptr;  // per level x bucket offsets (kNumBuckets+1 per level)
+    std::vector<int2> tiles;          // (J, 64-row panel tile) per level
+    std::vector<int64_t> tile_lptr;
+    std::vector<int2> linv_work;
+    std::vector<Item> lhat_items;
+    std::vector<int> lhat_bptr;
+    Item *d_items = nullptr, *d_lhat = nullptr;
+    int2 *d_tiles = nullptr, *d_linv = nullptr;
+    double *YB = nullptr, *Zb = nullptr, *Lbw = nullptr, *Ab = nullptr, *fin = nullptr;
+    AdjDesc *d_desc = nullptr;
+    ProbDesc *d_pdesc = nullptr;
+};
+
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_adj_pull(const AdjDesc *__restrict__ ad,
+                                                  const int2 *__restrict__ tiles, int ntiles) {
+    const int w = blockIdx.x;
+    if (w >= ntiles) return;
+    const AdjDesc &A = *ad;
+    const int J = tiles[w].x;
+    const int64_t ldJ = A.rowptr[J + 1] - A.rowptr[J];
+    const int64_t r0 = (int64_t)tiles[w].y * 64;
+    const int64_t r1 = r0 + 64 < ldJ ? r0 + 64 : ldJ;
+    const int fcJ = A.super_ptr[J];
+    double *ZbJ = A.Zb + A.panel_off[J];
+    __shared__ int s_pa, s_pb;
+    for (int64_t di = A.dseg_ptr[J]; di < A.dseg_ptr[J + 1]; di++) {
+        const int t = A.dseg[di];
+        const int K = A.seg_K[t];
+        const int st = A.seg_start[t], en = A.seg_end[t];
+        const int sK = A.super_ptr[K + 1] - A.super_ptr[K];
+        const int64_t ldK = A.rowptr[K + 1] - A.rowptr[K];
+        const int cK = (int)(ldK - sK);
+        const int32_t *rel = A.relidx + A.rel_ptr[t];
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int a = st, b = cK;
+            while (a < b) { const int m = (a + b) / 2; if (rel[m - st] < r0) a = m + 1; else b = m; }
+            int c2 = a, d2 = cK;
+            while (c2 < d2) { const int m = (c2 + d2) / 2; if (rel[m - st] < r1) c2 = m + 1; else d2 = m; }
+            s_pa = a;
+            s_pb = c2;
+        }
+        __syncthreads();
+        const int pa = s_pa, np = s_pb - s_pa, nq = en - st;
+        if (np <= 0) continue;
+        const double *Yb = A.YB + A.panel_off[K] + sK;   // Ybar(p, k) = Yb[k*ldK + p]
+        const double *Lh = A.LD + A.panel_off[K] + sK;   // Lhat(p, k)
+        for (int e = threadIdx.x; e < np * nq; e += blockDim.x) {
+            const int p = pa + e % np, q = st + e / np;
+            if (p < q) continue;
+            double v = 0.0;
+            for (int k = 0; k < sK; k++) {
+                v = fma(Yb[(int64_t)k * ldK + p], Lh[(int64_t)k * ldK + q], v);
+                if (p != q) v = fma(Yb[(int64_t)k * ldK + q], Lh[(int64_t)k * ldK + p], v);
+            }
+            const int col = A.rows[A.rowptr[K] + sK + q] - fcJ;
+            ZbJ[(int64_t)col * ldJ + rel[p - st]] -= v;
+        }
+    }
+}
+
+// S (tile 0) and Ybar rows of one tile
+__global__ void __launch_bounds__(256) k_adj_ybar(const AdjDesc *__restrict__ ad,
+                                                  const Item *__restrict__ items, int nitems) {
+    const int w = blockIdx.x;
+    if (w >= nitems) return;
+    const AdjDesc &A = *ad;
+    const Item it = items[w];
+    const int J = it.K;
+    const int s = A.super_ptr[J + 1] - A.super_ptr[J];
+    const int64_t ld = A.rowptr[J + 1] - A.rowptr[J];
+    const int c = (int)(ld - s);
+    const double *Zb = A.Zb + A.panel_off[J];
+    double *YB = A.YB + A.panel_off[J];
+    const double *Lh = A.LD + A.panel_off[J] + s;
+    auto S = [&](int a, int b) -> double {
+        if (a == b) return Zb[(int64_t)b * ld + a];
+        return 0.5 * (a > b ? Zb[(int64_t)b * ld + a] : Zb[(int64_t)a * ld + b]);
+    };
+    if (it.tile == 0)
+        for (int e = threadIdx.x; e < s * s; e += blockDim.x) YB[(int64_t)(e / s) * ld + e % s] = S(e % s, e / s);
+    const int p0 = it.tile * kTM;
+    const int pm = c - p0 < kTM ? c - p0 : kTM;
+    for (int e = threadIdx.x; e < pm * s; e += blockDim.x) {
+        const int p = p0 + e % pm, j = e / pm;
+        double v = Zb[(int64_t)j * ld + s + p];
+        for (int k = 0; k < s; k++) v = fma(-Lh[(int64_t)k * ld + p], S(k, j), v);
+        YB[(int64_t)j * ld + s + p] = v;
+    }
+}
+
+// the selected-inversion finisher of J (whole CTA): Mbar, Lbar_JJ, Dbar_J
+__device__ void adj_finish_selinv(const AdjDesc &A, int J, int ntiles) {
+    const int fc = A.super_ptr[J];
+    const int s = A.super_ptr[J + 1] - fc;
+    const int64_t ld = A.rowptr[J + 1] - A.rowptr[J];
+    const int64_t ss = (int64_t)s * s;
+    const double *Li = A.Linv + A.linv_off[J];       // M(i, k) = Li[k*s + i]
+    const double *S = A.YB + A.panel_off[J];          // S(a, b) = S[b*ld + a]
+    const double *D = A.D + fc;
+    const double *part = A.partial + A.part_off[J];
+    double *Mb = A.fin + 2 * A.linv_off[J];
+    double *W = Mb + ss;
+    for (int e = threadIdx.x; e < s * s; e += blockDim.x) {
+        const int i = e % s, j = e / s;
+        double v = 0.0;
+        for (int t = 0; t < ntiles; t++) v += ldcg(part + t * ss + (int64_t)j * s + i);
+        double m = 0.0;
+        for (int k = 0; k < s; k++) m = fma(Li[(int64_t)k * s + i], S[(int64_t)j * ld + k], m);
+        Mb[(int64_t)j * s + i] = v + 2.0 * m / D[i];
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < s * s; e += blockDim.x) {   // W = Mbar M^T
+        const int a = e % s, j = e / s;
+        double v = 0.0;
+        for (int b = 0; b < s; b++) v = fma(Mb[(int64_t)b * s + a], Li[(int64_t)b * s + j], v);
+        W[(int64_t)j * s + a] = v;
+    }
+    __syncthreads();
+    double *LbJ = A.Lb + A.panel_off[J];
+    for (int e = threadIdx.x; e < s * s; e += blockDim.x) {   // Lbar_JJ = -(M^T W), strictly lower
+        const int i = e % s, j = e / s;
+        double v = 0.0;
+        if (i > j)
+            for (int a = 0; a < s; a++) v = fma(-Li[(int64_t)i * s + a], W[(int64_t)j * s + a], v);
+        LbJ[(int64_t)j * ld + i] = v;
+    }
+    for (int k = threadIdx.x; k < s; k += blockDim.x) {       // Dbar_k = -(M S M^T)_kk / D_k^2
+        double v = 0.0;
+        for (int a = 0; a < s; a++) {
+            double r = 0.0;
+            for (int b = 0; b < s; b++) r = fma(S[(int64_t)b * ld + a], Li[(int64_t)b * s + k], r);
+            v = fma(Li[(int64_t)a * s + k], r, v);
+        }
+        A.Db[fc + k] = -v / (D[k] * D[k]);
+    }
+}
+
+// Lhat_bar rows of one tile (gather-GEMM with B = Ybar), the split Mbar term,
+// then Lbar_C rows; the last tile runs the finisher.
+template <int TN>
+__global__ void __launch_bounds__(kThreads) k_adj_lhbar(const AdjDesc *__restrict__ ad,
+                                                        const Item *__restrict__ items, int nitems) {
+    using Sh = Shape<TN>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    double *As = reinterpret_cast<double *>(smem_raw);
+    double *Bs = As + kTK * (kTM > TN ? kTM : TN);
+    double *Rows = Bs + kTK * TN;                         // [TM][TN] Lhat_bar rows of the tile
+    __shared__ int64_t tile_cb[kTM], tile_rb[kTM];
+    __shared__ int s_last;
+    const int w = blockIdx.x;
+    if (w >= nitems) return;
+    const AdjDesc &A = *ad;
+    const Item it = items[w];
+    const int J = it.K;
+    const int s = A.super_ptr[J + 1] - A.super_ptr[J];
+    const int64_t ld = A.rowptr[J + 1] - A.rowptr[J];
+    const int c = (int)(ld - s);
+    const int p0 = it.tile * kTM;
+    const int pm = c - p0 < kTM ? c - p0 : kTM;
+    const int64_t pos0 = A.rowptr[J] + s;
+    const int64_t off = A.panel_off[J];
+    for (int e = threadIdx.x; e < kTM; e += kThreads) {
+        const int p = p0 + e;
+        tile_cb[e] = p < c ? A.colbase[pos0 + p] : 0;
+        tile_rb[e] = p < c ? A.relbase[pos0 + p] : 0;
+    }
+    double acc[Sh::MI][Sh::NJ];
+#pragma unroll
+    for (int i = 0; i < Sh::MI; i++)
+#pragma unroll
+        for (int j = 0; j < Sh::NJ; j++) acc[i][j] = 0.0;
+    if (pm > 0) {
+        LoadGather<double, TN> la{A.Z, A.colbase + pos0, A.relbase + pos0, A.relidx, tile_cb, tile_rb, p0, c};
+        LoadColMajor<double, TN> lb{A.YB + off + s, ld, c, s};
+        tile_gemm<double, TN>(c, la, lb, acc, As, Bs);
+    }
+    const int tx = threadIdx.x % Sh::TX, ty = threadIdx.x / Sh::TX;
+#pragma unroll
+    for (int i = 0; i < Sh::MI; i++)
+#pragma unroll
+        for (int j = 0; j < Sh::NJ; j++)
+            Rows[(ty + Sh::TY * i) * TN + tx + Sh::TX * j] = -acc[i][j];
+    __syncthreads();
+    // Lhat_bar = -(G Ybar) - Y S
+    const double *Y = A.Z + off + s;
+    const double *S = A.YB + off;
+    for (int e = threadIdx.x; e < kTM * s; e += kThreads) {
+        const int pl = e % kTM, j = e / kTM;
+        if (pl >= pm) continue;
+        double v = Rows[pl * TN + j];
+        for (int k = 0; k < s; k++) v = fma(-Y[(int64_t)k * ld + p0 + pl], S[(int64_t)j * ld + k], v);
+        Rows[pl * TN + j] = v;
+    }
+    __syncthreads();
+    // split term of Mbar: P(i, j) = sum_p L_C(p, i) Lhat_bar(p, j)
+    const int64_t ss = (int64_t)s * s;
+    double *part = A.partial + A.part_off[J] + (int64_t)it.tile * ss;
+    const double *Lc = A.L + off + s;
+    for (int e = threadIdx.x; e < s * s; e += kThreads) {
+        const int i = e % s, j = e / s;
+        double v = 0.0;
+        for (int pl = 0; pl < pm; pl++) v = fma(Lc[(int64_t)i * ld + p0 + pl], Rows[pl * TN + j], v);
+        part[e] = v;
+    }
+    // Lbar_C rows = Lhat_bar M^T
+    const double *Li = A.Linv + A.linv_off[J];
+    double *Lb = A.Lb + off + s;
+    for (int e = threadIdx.x; e < kTM * s; e += kThreads) {
+        const int pl = e % kTM, j = e / kTM;
+        if (pl >= pm) continue;
+        double v = 0.0;
+        for (int k = 0; k < s; k++) v = fma(Rows[pl * TN + k], Li[(int64_t)k * s + j], v);
+        Lb[(int64_t)j * ld + p0 + pl] = v;
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = (atomicAdd(&A.counter[J], 1) == it.ntiles - 1);
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    adj_finish_selinv(A, J, it.ntiles);
+    if (threadIdx.x == 0) A.counter[J] = 0;
+}
+
+// ---------------------------------------------------------------------------
+// factorization adjoint
+// ---------------------------------------------------------------------------
+template <int TN>
+__global__ void __launch_bounds__(kThreads) k_fadj_pull(const AdjDesc *__restrict__ ad,
+                                                        const Item *__restrict__ items, int nitems) {
+    using Sh = Shape<TN>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    double *As = reinterpret_cast<double *>(smem_raw);
+    double *Bs = As + kTK * (kTM > TN ? kTM : TN);
+    double *Rows = Bs + kTK * TN;
+    __shared__ int64_t tile_cb[kTM], tile_rb[kTM];
+    __shared__ int s_last;
+    const int w = blockIdx.x;
+    if (w >= nitems) return;
+    const AdjDesc &A = *ad;
+    const Item it = items[w];
+    const int J = it.K;
+    const int fc = A.super_ptr[J];
+    const int s = A.super_ptr[J + 1] - fc;
+    const int64_t ld = A.rowptr[J + 1] - A.rowptr[J];
+    const int c = (int)(ld - s);
+    const int p0 = it.tile * kTM;
+    const int pm = c - p0 < kTM ? c - p0 : kTM;
+    const int64_t pos0 = A.rowptr[J] + s;
+    const int64_t off = A.panel_off[J];
+    for (int e = threadIdx.x; e < kTM; e += kThreads) {
+        const int p = p0 + e;
+        tile_cb[e] = p < c ? A.colbase[pos0 + p] : 0;
+        tile_rb[e] = p < c ? A.relbase[pos0 + p] : 0;
+    }
+    double acc[Sh::MI][Sh::NJ];
+#pragma unroll
+    for (int i = 0; i < Sh::MI; i++)
+#pragma unroll
+        for (int j = 0; j < Sh::NJ; j++) acc[i][j] = 0.0;
+    if (pm > 0) {
+        LoadGather<double, TN, true> la{A.Ab, A.colbase + pos0, A.relbase + pos0, A.relidx, tile_cb, tile_rb, p0, c};
+        LoadColMajor<double, TN> lb{A.L + off + s, ld, c, s};
+        tile_gemm<double, TN>(c, la, lb, acc, As, Bs);
+    }
+    const int tx = threadIdx.x % Sh::TX, ty = threadIdx.x / Sh::TX;
+#pragma unroll
+    for (int i = 0; i < Sh::MI; i++)
+#pragma unroll
+        for (int j = 0; j < Sh::NJ; j++) Rows[(ty + Sh::TY * i) * TN + tx + Sh::TX * j] = acc[i][j];
+    __syncthreads();
+    const double *D = A.D + fc;
+    const double *Lc = A.L + off + s;
+    double *Lb = A.Lb + off + s;
+    for (int e = threadIdx.x; e < kTM * s; e += kThreads) {
+        const int pl = e % kTM, k = e / kTM;
+        if (pl >= pm) continue;
+        Lb[(int64_t)k * ld + p0 + pl] -= Rows[pl * TN + k] * D[k];
+    }
+    double *part = A.partial + A.part_off[J] + (int64_t)it.tile * s * s;
+    for (int k = threadIdx.x; k < s; k += kThreads) {
+        double v = 0.0;
+        for (int pl = 0; pl < pm; pl++) v = fma(Lc[(int64_t)k * ld + p0 + pl], Rows[pl * TN + k], v);
+        part[k] = v;
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = (atomicAdd(&A.counter[J], 1) == it.ntiles - 1);
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    const double *part0 = A.partial + A.part_off[J];
+    for (int k = threadIdx.x; k < s; k += kThreads) {
+        double v = 0.0;
+        for (int t = 0; t < it.ntiles; t++) v += ldcg(part0 + (int64_t)t * s * s + k);
+        A.Db[fc + k] -= 0.5 * v;
+    }
+    if (threadIdx.x == 0) A.counter[J] = 0;
+}
+
+// the factorization finisher of J: Ubar -> (Lbar_JJ, Dbar_J), then the reverse
+// of the dense LDL^T of the diagonal block -> Abar_JJ
+__device__ void adj_finish_factor(const AdjDesc &A, int J, int ntiles) {
+    const int fc = A.super_ptr[J];
+    const int s = A.super_ptr[J + 1] - fc;
+    const int64_t ld = A.rowptr[J + 1] - A.rowptr[J];
+    const int64_t ss = (int64_t)s * s;
+    const double *Li = A.Linv + A.linv_off[J];     // M(i, k) = Li[k*s + i]
+    const double *D = A.D + fc;
+    const double *L = A.L + A.panel_off[J];         // L(i, k) = L[k*ld + i], unit diagonal
+    double *LbJ = A.Lb + A.panel_off[J];
+    double *Db = A.Db + fc;
+    double *F1 = A.fin + 2 * A.linv_off[J];
+    double *F2 = F1 + ss;
+    const double *part = A.partial + A.part_off[J];
+    auto N = [&](int i, int j) { return Li[(int64_t)i * s + j] / D[j]; };  // N = M^T D^{-1}
+    for (int e = threadIdx.x; e < s * s; e += blockDim.x) {  // F1 = Nbar
+        double v = 0.0;
+        for (int t = 0; t < ntiles; t++) v += ldcg(part + t * ss + e);
+        F1[e] = v;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < s * s; e += blockDim.x) {  // F2 = Nbar N^T
+        const int i = e % s, j = e / s;
+        double v = 0.0;
+        for (int k = 0; k < s; k++) v = fma(F1[(int64_t)k * s + i], N(j, k), v);
+        F2[e] = v;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < s * s; e += blockDim.x) {  // F1 = Ubar = -N^T F2
+        const int i = e % s, j = e / s;
+        double v = 0.0;
+        for (int k = 0; k < s; k++) v = fma(-N(k, i), F2[(int64_t)j * s + k], v);
+        F1[e] = v;
+    }
+    __syncthreads();
+    // U = D L^T: Dbar_i += sum_{j>=i} Ubar(i,j) L(j,i); Lbar(j,i) += Ubar(i,j) D_i (j > i)
+    for (int i = threadIdx.x; i < s; i += blockDim.x) {
+        double v = F1[(int64_t)i * s + i];
+        for (int j = i + 1; j < s; j++) v = fma(F1[(int64_t)j * s + i], L[(int64_t)i * ld + j], v);
+        Db[i] += v;
+    }
+    for (int e = threadIdx.x; e < s * s; e += blockDim.x) {
+        const int j = e % s, i = e / s;
+        if (j > i) LbJ[(int64_t)i * ld + j] += F1[(int64_t)j * s + i] * D[i];
+    }
+    __syncthreads();
+    // reverse of the dense LDL^T of the block: Pbar starts as (Lbar strictly lower, Dbar on the diagonal)
+    double *Pb = F2;
+    for (int e = threadIdx.x; e < s * s; e += blockDim.x) {
+        const int i = e % s, k = e / s;
+        Pb[e] = i > k ? LbJ[(int64_t)k * ld + i] : (i == k ? Db[i] : 0.0);
+    }
+    __shared__ double red[kThreads];
+    for (int j = s - 1; j >= 0; j--) {
+        __syncthreads();
+        const double d = D[j];
+        // column j of Pbar from the updates of step j (they read columns > j only)
+        double dpart = 0.0;
+        for (int r = j + 1 + threadIdx.x; r < s; r += blockDim.x) {
+            double v = 0.0;
+            for (int k = j + 1; k <= r; k++) v = fma(Pb[(int64_t)k * s + r], L[(int64_t)j * ld + k], v);
+            for (int i = r; i < s; i++) v = fma(Pb[(int64_t)r * s + i], L[(int64_t)j * ld + i], v);
+            Pb[(int64_t)j * s + r] -= d * v;
+            // dbar -= sum_{k <= i} Pbar(i,k) L(i,j) L(k,j), grouped by k = r
+            double u = 0.0;
+            for (int i = r; i < s; i++) u = fma(Pb[(int64_t)r * s + i], L[(int64_t)j * ld + i], u);
+            dpart = fma(-u, L[(int64_t)j * ld + r], dpart);
+        }
+        __syncthreads();
+        // reverse of L(r, j) = a(r, j) / d
+        for (int r = j + 1 + threadIdx.x; r < s; r += blockDim.x) {
+            const double lb = Pb[(int64_t)j * s + r];
+            Pb[(int64_t)j * s + r] = lb / d;
+            dpart -= lb * L[(int64_t)j * ld + r] / d;
+        }
+        red[threadIdx.x] = dpart;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double t = 0.0;
+            for (int q = 0; q < (int)blockDim.x; q++) t += red[q];
+            Pb[(int64_t)j * s + j] += t;
+        }
+    }
+    __syncthreads();
+    double *AbJ = A.Ab + A.panel_off[J];
+    for (int e = threadIdx.x; e < s * s; e += blockDim.x) {
+        const int i = e % s, k = e / s;
+        AbJ[(int64_t)k * ld + i] = i >= k ? Pb[e] : 0.0;
+    }
+}
+
+// Abar_C rows = Lbar_C D^{-1} L_JJ^{-1}; split Nbar = A_C^T Lbar_C; finisher
+template <int TN>
+__global__ void __launch_bounds__(kThreads) k_fadj_trsm(const AdjDesc *__restrict__ ad,
+                                                        const Item *__restrict__ items, int nitems) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    double *Ar = reinterpret_cast<double *>(smem_raw);    // [TM][TN] A_C rows
+    double *Br = Ar + kTM * TN;                            // [TM][TN] Lbar_C rows
+    __shared__ int s_last;
+    const int w = blockIdx.x;
+    if (w >= nitems) return;
+    const AdjDesc &A = *ad;
+    const Item it = items[w];
+    const int J = it.K;
+    const int fc = A.super_ptr[J];
+    const int s = A.super_ptr[J + 1] - fc;
+    const int64_t ld = A.rowptr[J + 1] - A.rowptr[J];
+    const int c = (int)(ld - s);
+    const int p0 = it.tile * kTM;
+    const int pm = c - p0 < kTM ? c - p0 : kTM;
+    const int64_t off = A.panel_off[J];
+    const double *L = A.L + off;
+    const double *D = A.D + fc;
+    const double *Li = A.Linv + A.linv_off[J];
+    const double *Lb = A.Lb + off + s;
+    double *Ab = A.Ab + off + s;
+    for (int e = threadIdx.x; e < kTM * s; e += kThreads) {
+        const int pl = e % kTM, j = e / kTM;
+        double a = 0.0;
+        if (pl < pm) {
+            // A_C(p, j) = sum_{k <= j} L_C(p, k) D_k L_JJ(j, k)
+            for (int k = 0; k <= j; k++) {
+                const double ljk = (k == j) ? 1.0 : L[(int64_t)k * ld + j];
+                a = fma(L[(int64_t)k * ld + s + p0 + pl] * D[k], ljk, a);
+            }
+            Br[pl * TN + j] = Lb[(int64_t)j * ld + p0 + pl];
+        } else {
+            Br[pl * TN + j] = 0.0;
+        }
+        Ar[pl * TN + j] = a;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < kTM * s; e += kThreads) {  // Abar_C = (Lbar_C D^{-1}) M
+        const int pl = e % kTM, j = e / kTM;
+        if (pl >= pm) continue;
+        double v = 0.0;
+        for (int k = j; k < s; k++) v = fma(Br[pl * TN + k] / D[k], Li[(int64_t)j * s + k], v);
+        Ab[(int64_t)j * ld + p0 + pl] = v;
+    }
+    const int64_t ss = (int64_t)s * s;
+    double *part = A.partial + A.part_off[J] + (int64_t)it.tile * ss;
+    for (int e = threadIdx.x; e < s * s; e += kThreads) {    // Nbar partial = A_C^T Lbar_C
+        const int i = e % s, j = e / s;
+        double v = 0.0;
+        for (int pl = 0; pl < pm; pl++) v = fma(Ar[pl * TN + i], Br[pl * TN + j], v);
+        part[e] = v;
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = (atomicAdd(&A.counter[J], 1) == it.ntiles - 1);
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    adj_finish_factor(A, J, it.ntiles);
+    if (threadIdx.x == 0) A.counter[J] = 0;
+}
+
+__global__ void k_gather_vals(const int64_t *__restrict__ pos, const double *__restrict__ src,
+                              int64_t n, double *__restrict__ dst) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+        dst[e] = src[pos[e]];
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+template <int TN> static size_t lhbar_smem() {
+    return sizeof(double) * ((size_t)kTK * (kTM > TN ? kTM : TN) + kTK * TN + (size_t)kTM * TN);
+}
+template <int TN> static size_t trsm_smem() { return sizeof(double) * 2 * (size_t)kTM * TN; }
+
+static cudaError_t configure_adjoint() {
+    static bool done = false;
+    if (done) return cudaSuccess;
+    cudaError_t e = cudaSuccess;
+#define CFG(K, TN, SZ) if (e == cudaSuccess) e = cudaFuncSetAttribute(K<TN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SZ<TN>())
+    CFG(k_adj_lhbar, 8, lhbar_smem); CFG(k_adj_lhbar, 16, lhbar_smem); CFG(k_adj_lhbar, 32, lhbar_smem);
+    CFG(k_adj_lhbar, 64, lhbar_smem); CFG(k_adj_lhbar, 128, lhbar_smem);
+    CFG(k_fadj_pull, 8, lhbar_smem); CFG(k_fadj_pull, 16, lhbar_smem); CFG(k_fadj_pull, 32, lhbar_smem);
+    CFG(k_fadj_pull, 64, lhbar_smem); CFG(k_fadj_pull, 128, lhbar_smem);
+    CFG(k_fadj_trsm, 8, trsm_smem); CFG(k_fadj_trsm, 16, trsm_smem); CFG(k_fadj_trsm, 32, trsm_smem);
+    CFG(k_fadj_trsm, 64, trsm_smem); CFG(k_fadj_trsm, 128, trsm_smem);
+#undef CFG
+    done = e == cudaSuccess;
+    return e;
+}
+
+template <template <int> class KF> struct Dummy {};
+
+static void launch_bucket(int kind, int b, const AdjDesc *d, const Item *items, int n, cudaStream_t st) {
+    if (n <= 0) return;
+#define L3(KERN, TN, SZ) KERN<TN><<<n, kThreads, SZ<TN>(), st>>>(d, items, n)
+    switch (kind * 8 + b) {
+    case 0: L3(k_adj_lhbar, 8, lhbar_smem); break;
+    case 1: L3(k_adj_lhbar, 16, lhbar_smem); break;
+    case 2: L3(k_adj_lhbar, 32, lhbar_smem); break;
+    case 3: L3(k_adj_lhbar, 64, lhbar_smem); break;
+    case 4: L3(k_adj_lhbar, 128, lhbar_smem); break;
+    case 8: L3(k_fadj_pull, 8, lhbar_smem); break;
+    case 9: L3(k_fadj_pull, 16, lhbar_smem); break;
+    case 10: L3(k_fadj_pull, 32, lhbar_smem); break;
+    case 11: L3(k_fadj_pull, 64, lhbar_smem); break;
+    case 12: L3(k_fadj_pull, 128, lhbar_smem); break;
+    case 16: L3(k_fadj_trsm, 8, trsm_smem); break;
+    case 17: L3(k_fadj_trsm, 16, trsm_smem); break;
+    case 18: L3(k_fadj_trsm, 32, trsm_smem); break;
+    case 19: L3(k_fadj_trsm, 64, trsm_smem); break;
+    default: L3(k_fadj_trsm, 128, trsm_smem); break;
+    }
+#undef L3
+    note_launch();
+}
+
+void adjoint_release(void *p) {
+    AdjData *a = static_cast<AdjData *>(p);
+    if (!a) return;
+    auto fr = [](void *q) { if (q) cudaFree(q); };
+    fr(a->d_items); fr(a->d_lhat); fr(a->d_tiles); fr(a->d_linv);
+    fr(a->YB); fr(a->Zb); fr(a->Lbw); fr(a->Ab); fr(a->fin); fr(a->d_desc); fr(a->d_pdesc);
+    delete a;
+}
+
+template <typename X>
+static int upl(X **d, const std::vector<X> &h) {
+    *d = nullptr;
+    if (cudaMalloc((void **)d, sizeof(X) * std::max<size_t>(1, h.size())) != cudaSuccess) return SELINV_ERR_OOM;
+    if (!h.empty() && cudaMemcpy(*d, h.data(), sizeof(X) * h.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+        return SELINV_ERR_CUDA;
+    return SELINV_OK;
+}
+
+static int adj_build(selinv_plan_s *plan) {
+    if (!plan->factor) plan->factor = new FactorData();
+    int rc = factor_tables(plan);
+    if (rc) return rc;
+    FactorData *f = plan->factor;
+    if (f->adj) return SELINV_OK;
+    const PlanData &p = plan->data;
+    AdjData *a = new AdjData();
+    // per level (deepest first) items sorted by bucket; 64-row panel tiles
+    a->lvl_bucket_ptr.push_back(0);
+    for (int l = p.nlevels - 1; l >= 0; l--) {
+        for (int b = 0; b < kNumBuckets; b++) {
+            for (int64_t e = p.level_ptr[l]; e < p.level_ptr[l + 1]; e++) {
+                const int32_t J = p.level_list[e];
+                if (bucket_of(p.super_ptr[J + 1] - p.super_ptr[J]) != b) continue;
+                for (int t = 0; t < p.ntiles[J]; t++) a->items.push_back({0, J, t, p.ntiles[J]});
+            }
+            a->lvl_bucket_ptr.push_back((int)a->items.size());
+        }
+    }
+    a->tiles = f->h_tiles;          // (J, 64-row tile), deepest level first
+    a->tile_lptr = f->tile_lptr;
+    for (int32_t K = 0; K < p.ns; K++) a->linv_work.push_back(make_int2(0, K));
+    a->lhat_bptr.push_back(0);
+    for (int b = 0; b < kNumBuckets; b++) {
+        for (int32_t K = 0; K < p.ns; K++) {
+            const int s = p.super_ptr[K + 1] - p.super_ptr[K];
+            const int64_t c = p.rowptr[K + 1] - p.rowptr[K] - s;
+            if (c == 0 || bucket_of(s) != b) continue;
+            for (int t = 0; t < p.ntiles[K]; t++) a->lhat_items.push_back({0, K, t, p.ntiles[K]});
+        }
+        a->lhat_bptr.push_back((int)a->lhat_items.size());
+    }
+    if ((rc = upl(&a->d_items, a->items)) || (rc = upl(&a->d_lhat, a->lhat_items)) ||
+        (rc = upl(&a->d_tiles, a->tiles)) || (rc = upl(&a->d_linv, a->linv_work))) {
+        adjoint_release(a);
+        return rc;
+    }
+    const size_t nz = (size_t)std::max<int64_t>(p.nnz, 1);
+    if (cudaMalloc((void **)&a->YB, 8 * nz) || cudaMalloc((void **)&a->Zb, 8 * nz) ||
+        cudaMalloc((void **)&a->Lbw, 8 * nz) || cudaMalloc((void **)&a->Ab, 8 * nz) ||
+        cudaMalloc((void **)&a->fin, 8 * (size_t)std::max<int64_t>(2 * p.linv_total, 1)) ||
+        cudaMalloc((void **)&a->d_desc, sizeof(AdjDesc)) || cudaMalloc((void **)&a->d_pdesc, sizeof(ProbDesc))) {
+        adjoint_release(a);
+        return SELINV_ERR_OOM;
+    }
+    f->adj = a;
+    return SELINV_OK;
+}
+
+static AdjDesc make_adesc(selinv_plan_s *plan, const double *L, const double *D, const double *Z,
+                          double *Lb, double *Db) {
+    const PlanData &p = plan->data;
+    FactorData *f = plan->factor;
+    AdjData *a = static_cast<AdjData *>(f->adj);
+    Workspace &w = plan->ws[0];
+    AdjDesc h;
+    h.super_ptr = p.d_super_ptr; h.rowptr = p.d_rowptr; h.rows = p.d_rows; h.panel_off = p.d_panel_off;
+    h.colbase = p.d_colbase; h.relbase = p.d_relbase; h.relidx = p.d_relidx; h.rel_ptr = f->d_rel_ptr;
+    h.seg_K = f->d_seg_K; h.seg_start = f->d_seg_start; h.seg_end = f->d_seg_end;
+    h.dseg_ptr = f->d_dseg_ptr; h.dseg = f->d_dseg;
+    h.linv_off = p.d_linv_off; h.part_off = p.d_part_off;
+    h.L = L; h.D = D; h.Z = Z;
+    h.LD = static_cast<const double *>(w.LD);
+    h.Linv = static_cast<const double *>(w.Linv);
+    h.Zb = a->Zb; h.YB = a->YB; h.Lb = Lb; h.Db = Db; h.Ab = a->Ab;
+    h.partial = static_cast<double *>(w.partial);
+    h.counter = w.counter;
+    h.fin = a->fin;
+    return h;
+}
+
+// L_KK^{-1}, Dinv and Lhat of every supernode (the forward normalization)
+static int adj_normalize(selinv_plan_s *plan, const void *L, const void *D, cudaStream_t st) {
+    AdjData *a = static_cast<AdjData *>(plan->factor->adj);
+    ProbDesc pd = make_desc(plan->data, plan->ws[0], SELINV_F64, L, D, nullptr, false);
+    cudaMemcpyAsync(a->d_pdesc, &pd, sizeof(pd), cudaMemcpyHostToDevice, st);
+    launch_linv(SELINV_F64, a->d_pdesc, a->d_linv, (int)a->linv_work.size(), st);
+    note_launch();
+    for (int b = 0; b < kNumBuckets; b++) {
+        const int n = a->lhat_bptr[b + 1] - a->lhat_bptr[b];
+        if (n > 0) {
+            launch_lhat(SELINV_F64, b, a->d_pdesc, a->d_lhat + a->lhat_bptr[b], n, st);
+            note_launch();
+        }
+    }
+    return cudaGetLastError() == cudaSuccess ? SELINV_OK : SELINV_ERR_CUDA;
+}
+
+static int adj_prepare(selinv_plan_s *plan) {
+    int rc = ensure_device(plan->data);
+    if (rc) return rc;
+    if ((rc = adj_build(plan))) return rc;
+    if (plan->ws.empty()) plan->ws.resize(1);
+    if ((rc = plan->ws[0].ensure(plan->data, SELINV_F64))) return rc;
+    return configure_adjoint() == cudaSuccess ? SELINV_OK : SELINV_ERR_CUDA;
+}
+
+}  // namespace selinv
+
+using namespace selinv;
+
+extern "C" int selinv_adjoint(selinv_plan plan, selinv_dtype dtype, const void *L, const void *D,
+                              const void *Z, const void *Zbar, void *Lbar, void *Dbar, void *stream) {
+    if (!plan) return SELINV_ERR_INVALID_ARG;
+    if (dtype != SELINV_F64) return SELINV_ERR_UNSUPPORTED;
+    if (plan->data.ns == 0) return SELINV_OK;
+    if (!L || !D || !Z || !Zbar || !Lbar || !Dbar) return SELINV_ERR_INVALID_ARG;
+    int rc = adj_prepare(plan);
+    if (rc) return rc;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    plan->last_stream = st;
+    const PlanData &p = plan->data;
+    AdjData *a = static_cast<AdjData *>(plan->factor->adj);
+    if ((rc = adj_normalize(plan, L, D, st))) return rc;
+    const size_t bytes = 8 * (size_t)p.nnz;
+    cudaMemcpyAsync(a->Zb, Zbar, bytes, cudaMemcpyDeviceToDevice, st);
+    cudaMemsetAsync(Lbar, 0, bytes, st);
+    cudaMemsetAsync(Dbar, 0, 8 * (size_t)p.n, st);
+    AdjDesc h = make_adesc(plan, static_cast<const double *>(L), static_cast<const double *>(D),
+                           static_cast<const double *>(Z), static_cast<double *>(Lbar),
+                           static_cast<double *>(Dbar));
+    cudaMemcpyAsync(a->d_desc, &h, sizeof(h), cudaMemcpyHostToDevice, st);
+    const int nl = p.nlevels;
+    for (int li = 0; li < nl; li++) {  // deepest level first
+        const int64_t t0 = a->tile_lptr[li], t1 = a->tile_lptr[li + 1];
+        if (t1 > t0) { k_adj_pull<<<(int)(t1 - t0), 256, 0, st>>>(a->d_desc, a->d_tiles + t0, (int)(t1 - t0)); note_launch(); }
+        const int i0 = a->lvl_bucket_ptr[li * kNumBuckets], i1 = a->lvl_bucket_ptr[(li + 1) * kNumBuckets];
+        if (i1 > i0) { k_adj_ybar<<<i1 - i0, 256, 0, st>>>(a->d_desc, a->d_items + i0, i1 - i0); note_launch(); }
+        for (int b = 0; b < kNumBuckets; b++) {
+            const int b0 = a->lvl_bucket_ptr[li * kNumBuckets + b], b1 = a->lvl_bucket_ptr[li * kNumBuckets + b + 1];
+            launch_bucket(0, b, a->d_desc, a->d_items + b0, b1 - b0, st);
+        }
+    }
+    return cudaGetLastError() == cudaSuccess ? SELINV_OK : SELINV_ERR_CUDA;
+}
+
+extern "C" int selinv_factor_adjoint(selinv_plan plan, selinv_dtype dtype, const void *L, const void *D,
+                                     const void *Lbar, const void *Dbar, void *Abar_vals, void *stream) {
+    if (!plan || !plan->factor) return SELINV_ERR_INVALID_ARG;
+    if (dtype != SELINV_F64) return SELINV_ERR_UNSUPPORTED;
+    if (plan->data.ns == 0) return SELINV_OK;
+    if (!L || !D || !Lbar || !Dbar || (plan->factor->nnzA > 0 && !Abar_vals)) return SELINV_ERR_INVALID_ARG;
+    int rc = adj_prepare(plan);
+    if (rc) return rc;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    plan->last_stream = st;
+    const PlanData &p = plan->data;
+    FactorData *f = plan->factor;
+    AdjData *a = static_cast<AdjData *>(f->adj);
+    if ((rc = adj_normalize(plan, L, D, st))) return rc;
+    const size_t bytes = 8 * (size_t)p.nnz;
+    // working copies: Lbar -> Lbw, Dbar -> YB's first n slots (YB is free here)
+    cudaMemcpyAsync(a->Lbw, Lbar, bytes, cudaMemcpyDeviceToDevice, st);
+    cudaMemcpyAsync(a->YB, Dbar, 8 * (size_t)p.n, cudaMemcpyDeviceToDevice, st);
+    cudaMemsetAsync(a->Ab, 0, bytes, st);
+    AdjDesc h = make_adesc(plan, static_cast<const double *>(L), static_cast<const double *>(D), nullptr,
+                           a->Lbw, a->YB);
+    cudaMemcpyAsync(a->d_desc, &h, sizeof(h), cudaMemcpyHostToDevice, st);
+    const int nl = p.nlevels;
+    for (int li = nl - 1; li >= 0; li--) {  // root level first
+        for (int b = 0; b < kNumBuckets; b++) {
+            const int b0 = a->lvl_bucket_ptr[li * kNumBuckets + b], b1 = a->lvl_bucket_ptr[li * kNumBuckets + b + 1];
+            launch_bucket(1, b, a->d_desc, a->d_items + b0, b1 - b0, st);
+        }
+        for (int b = 0; b < kNumBuckets; b++) {
+            const int b0 = a->lvl_bucket_ptr[li * kNumBuckets + b], b1 = a->lvl_bucket_ptr[li * kNumBuckets + b + 1];
+            launch_bucket(2, b, a->d_desc, a->d_items + b0, b1 - b0, st);
+        }
+    }
+    if (f->nnzA > 0) {
+        const int blocks = (int)std::min<int64_t>((f->nnzA + 255) / 256, 152 * 8);
+        k_gather_vals<<<blocks, 256, 0, st>>>(f->d_a_pos, a->Ab, f->nnzA, static_cast<double *>(Abar_vals));
+        note_launch();
+    }
+    return cudaGetLastError() == cudaSuccess ? SELINV_OK : SELINV_ERR_CUDA;
+}

@@ -24,42 +24,6 @@
 
 namespace selinv {
 
-struct FactorDesc {
-    const int32_t *super_ptr;
-    const int64_t *rowptr;
-    const int32_t *rows;
-    const int64_t *panel_off;
-    const int32_t *relidx;
-    const int64_t *rel_ptr;
-    const int32_t *seg_K, *seg_start, *seg_end, *seg_coloff;
-    const int64_t *dseg_ptr;  // [ns+1] segments owned by J (descendant updates)
-    const int32_t *dseg;
-    void *L;
-    void *D;
-    int *status;
-};
-
-struct FactorData {
-    int32_t n = -1;
-    int64_t nnzA = 0;
-    std::vector<int64_t> a_pos;       // panel position of every stored entry of A
-    int64_t *d_a_pos = nullptr;
-    int32_t *d_seg_K = nullptr, *d_seg_start = nullptr, *d_seg_end = nullptr, *d_seg_coloff = nullptr;
-    int32_t *d_dseg = nullptr;
-    int64_t *d_dseg_ptr = nullptr, *d_rel_ptr = nullptr;
-    // launch lists
-    std::vector<int2> h_tiles;        // (J, row tile) per level, leaves first
-    std::vector<int> h_js;            // J per level
-    std::vector<int64_t> tile_lptr, j_lptr;
-    int2 *d_tiles = nullptr;
-    int *d_js = nullptr;
-    FactorDesc *d_desc = nullptr;
-    const void *key_L = nullptr, *key_D = nullptr;
-    int key_dtype = -1;
-    // adjoint state
-    void *adj = nullptr;
-};
-
 constexpr int kFT = 64;  // rows per factor tile
 
 template <typename T>

@@ -1,0 +1,311 @@
+// FP64-exact contraction A^{-1}_{C,K} = -A^{-1}_{C,C} Lhat_{C,K} on the bf16
+// tensor cores (mma.sync m16n8k16, fp32 accumulate).
+//
+// GB300's FP64 pipe delivers ~1.26 TFLOP/s, while its bf16 tensor path is
+// hundreds of times faster.  Each FP64 operand is cut, without rounding
+// error, into 7 balanced base-256 digits in [-128, 128] on a fixed-point
+// grid shared by its row (A: the gathered A^{-1}_{C,C}, exponent = row
+// maximum) or its column (B: Lhat, exponent = column maximum).  Every digit
+// is exact in bf16 and every digit product (<= 2^14) is exact in fp32.
+// Products of digit pairs (i, j) with i + j = g share the scale 2^{-8g}, so
+// they are summed into one fp32 accumulator per g; with at most 7 pairs per
+// g and 128 k-values between flushes the sums stay below 2^24 and are
+// therefore exact.  Every 128 k-values the 7 accumulators are folded exactly
+// into two int64 words per output element; the FP64 result is formed once
+// at the end.  Pairs with i + j > 6 are dropped: the result carries
+// 2^-53-level error relative to (row max) x (column max), like a DGEMM with
+// a max-norm bound.  FP64 accumulation is kept throughout (the int64 sums
+// are exact), as the tree recursion propagates error.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "common.cuh"
+#include "launch.h"
+
+namespace selinv {
+
+constexpr int kDig = 7;          // digits per operand
+constexpr int kOzK = 16;         // k per mma step
+constexpr int kFlushSteps = 8;   // 128 k per exact fp32 chunk
+constexpr int kApad = 24;        // smem row stride (bf16) of a 16-wide k slab: conflict-free
+constexpr int kOzThreads = 256;
+
+// biased exponent of |x| (0 for zero / subnormal)
+__device__ __forceinline__ int bexp(double x) {
+    return (int)((__double_as_longlong(x) >> 52) & 0x7FF);
+}
+
+// bf16 bit pattern of a small integer v (|v| <= 128): exact via an fp32
+// round trip through the magic constant 1.5 * 2^23.
+__device__ __forceinline__ uint32_t bf16_of_int(int v) {
+    const float f = __int_as_float(0x4B400000 + v) - 12582912.0f;
+    return __float_as_uint(f) >> 16;
+}
+
+// 7 balanced base-256 digits (most significant first) of x on the grid of
+// biased exponent E (E >= exponent of x): x ~= sum_i d_i 2^(E-1022-7-8i).
+__device__ __forceinline__ void digits7(double x, int E, int d[kDig]) {
+    const long long b = __double_as_longlong(x);
+    const int ex = (int)((b >> 52) & 0x7FF);
+    unsigned long long mant = ex ? ((b & 0xFFFFFFFFFFFFFull) | (1ull << 52)) : 0ull;
+    const int sh = E - ex - 2;                       // M = mant * 2^(2 - (E - ex)) < 2^55
+    unsigned long long M = sh < 0 ? (mant << (-sh)) : (sh < 64 ? (mant >> sh) : 0ull);
+#pragma unroll
+    for (int i = kDig - 1; i >= 1; i--) {
+        int v = (int)(M & 0xFFull);
+        M >>= 8;
+        if (v >= 128) { v -= 256; M += 1; }
+        d[i] = v;
+    }
+    d[0] = (int)M;                                   // <= 128
+    if (b < 0) {
+#pragma unroll
+        for (int i = 0; i < kDig; i++) d[i] = -d[i];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// k_lhat_digits: digit planes of Lhat_{C,K} (per column j: exponent over all
+// q) in the layout plane[j][q] (q contiguous, padded to c16 with zeros).
+// One warp per column.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_lhat_digits(const ProbDesc *__restrict__ descs,
+                                                     const int2 *__restrict__ work, int nwork) {
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    const int w = blockIdx.x;
+    if (w >= nwork) return;
+    const ProbDesc &P = descs[work[w].x];
+    const int K = work[w].y >> 8;           // (K << 8) | column block of 8
+    const int jb = work[w].y & 0xFF;
+    const int fc = P.super_ptr[K];
+    const int s = P.super_ptr[K + 1] - fc;
+    const int64_t ld = P.rowptr[K + 1] - P.rowptr[K];
+    const int c = (int)(ld - s);
+    const int c16 = (c + 15) & ~15;
+    const int j = jb * 8 + warp;
+    if (j >= s) return;
+    const double *Lh = static_cast<const double *>(P.LD) + P.panel_off[K] + (int64_t)j * ld + s;
+    int E = 0;
+    for (int q = lane; q < c; q += 32) E = max(E, bexp(Lh[q]));
+#pragma unroll
+    for (int o = 16; o; o >>= 1) E = max(E, __shfl_xor_sync(0xffffffffu, E, o));
+    if (lane == 0) P.colexp[fc + j] = E;
+    uint16_t *pl = P.lhs + P.lhs_off[K];
+    const int64_t plane = (int64_t)s * c16;
+    for (int q = lane; q < c16; q += 32) {
+        int d[kDig];
+        if (q < c) digits7(Lh[q], E, d);
+        else {
+#pragma unroll
+            for (int i = 0; i < kDig; i++) d[i] = 0;
+        }
+#pragma unroll
+        for (int i = 0; i < kDig; i++)
+            pl[i * plane + (int64_t)j * c16 + q] = (uint16_t)bf16_of_int(d[i]);
+    }
+}
+
+__device__ __forceinline__ void mma_bf16(float (&c)[4], uint32_t a0, uint32_t a1, uint32_t a2,
+                                         uint32_t a3, uint32_t b0, uint32_t b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
+        "{%8,%9}, {%0,%1,%2,%3};\n"
+        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+        : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+    const uint32_t s = (uint32_t)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem));
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::); }
+
+// ---------------------------------------------------------------------------
+// k_selinv_oz<TN>: one (K, row tile of 64, column tile of TN) item.
+// 8 warps: warp w owns m-tile (w % 4) and n-tiles (w / 4) + 2 t, t < TN/16.
+// ---------------------------------------------------------------------------
+template <int TN> struct OzShape {
+    static constexpr int NT = TN / 16;   // n-tiles (of 8) per warp
+};
+
+template <int TN>
+__global__ void __launch_bounds__(kOzThreads, 1) k_selinv_oz(const ProbDesc *__restrict__ descs,
+                                                             const Item *__restrict__ items, int nitems) {
+    constexpr int NT = OzShape<TN>::NT;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    // layout: A digits [7][64][kApad] bf16 | B digits [7][TN][kApad] bf16 |
+    //         acc hi/lo [64][TN] int64 x 2 | row exponents [64] int
+    uint16_t *As = reinterpret_cast<uint16_t *>(smem_raw);
+    uint16_t *Bs = As + kDig * kTM * kApad;
+    long long *Hi = reinterpret_cast<long long *>(Bs + kDig * TN * kApad);
+    long long *Lo = Hi + kTM * TN;
+    int *rowE = reinterpret_cast<int *>(Lo + kTM * TN);
+    __shared__ int64_t tile_cb[kTM], tile_rb[kTM];
+
+    const int w = blockIdx.x;
+    if (w >= nitems) return;
+    const Item it = items[w];
+    const ProbDesc &P = descs[it.prob];
+    const int K = it.K;
+    const int fc = P.super_ptr[K];
+    const int s = P.super_ptr[K + 1] - fc;
+    const int64_t ld = P.rowptr[K + 1] - P.rowptr[K];
+    const int c = (int)(ld - s);
+    const int c16 = (c + 15) & ~15;
+    const int ncol = (s + TN - 1) / TN;
+    const int tile = it.tile / ncol;          // row tile
+    const int ct = it.tile % ncol;            // column tile
+    const int p0 = tile * kTM, n0 = ct * TN;
+    const int64_t pos0 = P.rowptr[K] + s;
+    const double *Z = static_cast<const double *>(P.Z);
+    const int64_t *pcb = P.colbase + pos0;
+    const int64_t *prb = P.relbase + pos0;
+    const int32_t *relidx = P.relidx;
+
+    for (int e = threadIdx.x; e < kTM; e += kOzThreads) {
+        const int p = p0 + e;
+        tile_cb[e] = p < c ? pcb[p] : 0;
+        tile_rb[e] = p < c ? prb[p] : 0;
+        rowE[e] = 0;
+    }
+    for (int e = threadIdx.x; e < kTM * TN; e += kOzThreads) { Hi[e] = 0; Lo[e] = 0; }
+    __syncthreads();
+
+    // gathered entry (p, q) of A^{-1}_{C,C}, stored at (max, min) by symmetry
+    auto gather = [&](int pl, int q) -> double {
+        const int p = p0 + pl;
+        if (p >= c || q >= c) return 0.0;
+        const int64_t addr = p >= q ? pcb[q] + relidx[prb[q] + p] : tile_cb[pl] + relidx[tile_rb[pl] + q];
+        return Z[addr];
+    };
+
+    // pass 1: row exponents (max over the whole row of the gathered block)
+    {
+        const int pl = threadIdx.x % kTM;       // 4 threads per row
+        const int part = threadIdx.x / kTM;
+        int E = 0;
+        if (p0 + pl < c)
+            for (int q = part; q < c; q += kOzThreads / kTM) E = max(E, bexp(gather(pl, q)));
+        atomicMax(&rowE[pl], E);
+    }
+    __syncthreads();
+
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    const int mt = warp % 4;                  // m-tile: rows mt*16 .. +15
+    const int grp = lane / 4, qd = lane % 4;
+    float acc[NT][kDig][4];
+#pragma unroll
+    for (int t = 0; t < NT; t++)
+#pragma unroll
+        for (int g = 0; g < kDig; g++)
+#pragma unroll
+            for (int r = 0; r < 4; r++) acc[t][g][r] = 0.f;
+
+    const uint16_t *Bg = P.lhs + P.lhs_off[K];
+    const int64_t bplane = (int64_t)s * c16;
+    const int nsteps = c16 / kOzK;
+    for (int step = 0; step < nsteps; step++) {
+        const int k0 = step * kOzK;
+        __syncthreads();  // previous step's fragments consumed
+        // B digits: plane i, column n0 + j, q = k0 .. k0 + 15 (two 16-byte halves)
+        for (int e = threadIdx.x; e < kDig * TN * 2; e += kOzThreads) {
+            const int half = e & 1, j = (e >> 1) % TN, i = (e >> 1) / TN;
+            uint16_t *dst = Bs + (i * TN + j) * kApad + half * 8;
+            if (n0 + j < s) cp_async16(dst, Bg + i * bplane + (int64_t)(n0 + j) * c16 + k0 + half * 8);
+            else *reinterpret_cast<uint4 *>(dst) = make_uint4(0, 0, 0, 0);
+        }
+        // A digits: gather, cut, store (two adjacent k per thread -> bf16x2 words)
+        for (int e = threadIdx.x; e < kTM * (kOzK / 2); e += kOzThreads) {
+            const int pl = e % kTM, kk = (e / kTM) * 2;
+            int d0[kDig], d1[kDig];
+            digits7(gather(pl, k0 + kk), rowE[pl], d0);
+            digits7(gather(pl, k0 + kk + 1), rowE[pl], d1);
+#pragma unroll
+            for (int i = 0; i < kDig; i++)
+                *reinterpret_cast<uint32_t *>(As + (i * kTM + pl) * kApad + kk) =
+                    bf16_of_int(d0[i]) | (bf16_of_int(d1[i]) << 16);
+        }
+        cp_async_wait_all();
+        __syncthreads();
+        // 28 digit pairs (i + j <= 6) per n-tile
+        uint32_t a[kDig][4];
+#pragma unroll
+        for (int i = 0; i < kDig; i++) {
+            const uint16_t *base = As + (i * kTM + mt * 16) * kApad;
+            a[i][0] = *reinterpret_cast<const uint32_t *>(base + grp * kApad + qd * 2);
+            a[i][1] = *reinterpret_cast<const uint32_t *>(base + (grp + 8) * kApad + qd * 2);
+            a[i][2] = *reinterpret_cast<const uint32_t *>(base + grp * kApad + qd * 2 + 8);
+            a[i][3] = *reinterpret_cast<const uint32_t *>(base + (grp + 8) * kApad + qd * 2 + 8);
+        }
+#pragma unroll
+        for (int t = 0; t < NT; t++) {
+            const int nt = (warp / 4) + 2 * t;  // n-tile index (8 columns)
+#pragma unroll
+            for (int j = 0; j < kDig; j++) {
+                const uint16_t *bb = Bs + (j * TN + nt * 8 + grp) * kApad;
+                const uint32_t b0 = *reinterpret_cast<const uint32_t *>(bb + qd * 2);
+                const uint32_t b1 = *reinterpret_cast<const uint32_t *>(bb + qd * 2 + 8);
+#pragma unroll
+                for (int i = 0; i + j < kDig; i++)
+                    mma_bf16(acc[t][i + j], a[i][0], a[i][1], a[i][2], a[i][3], b0, b1);
+            }
+        }
+        // fold the exact fp32 group sums into the int64 accumulators
+        if ((step + 1) % kFlushSteps == 0 || step + 1 == nsteps) {
+#pragma unroll
+            for (int t = 0; t < NT; t++) {
+                const int nt = (warp / 4) + 2 * t;
+#pragma unroll
+                for (int r = 0; r < 4; r++) {
+                    const int row = mt * 16 + grp + (r >= 2 ? 8 : 0);
+                    const int col = nt * 8 + qd * 2 + (r & 1);
+                    long long g[kDig];
+#pragma unroll
+                    for (int q = 0; q < kDig; q++) { g[q] = (long long)__float2int_rn(acc[t][q][r]); acc[t][q][r] = 0.f; }
+                    Hi[row * TN + col] += (g[0] << 16) + (g[1] << 8) + g[2];
+                    Lo[row * TN + col] += (g[3] << 24) + (g[4] << 16) + (g[5] << 8) + g[6];
+                }
+            }
+        }
+    }
+    __syncthreads();
+    // Y = -(A^{-1}_{C,C} Lhat) in FP64: scale 2^(e_p + f_j - 14) (e = E - 1022)
+    double *Zk = static_cast<double *>(P.Z) + P.panel_off[K];
+    for (int e = threadIdx.x; e < kTM * TN; e += kOzThreads) {
+        const int row = e % kTM, col = e / kTM;
+        const int p = p0 + row, j = n0 + col;
+        if (p >= c || j >= s) continue;
+        const int sc = (rowE[row] - 1022) + (P.colexp[fc + j] - 1022) - 14;
+        const double y = ldexp((double)Hi[row * TN + col], sc - 16) + ldexp((double)Lo[row * TN + col], sc - 48);
+        Zk[(int64_t)j * ld + s + p] = -y;
+    }
+}
+
+template <int TN> constexpr size_t oz_smem_bytes() {
+    return sizeof(uint16_t) * (size_t)kDig * (kTM + TN) * kApad + 2 * sizeof(long long) * kTM * TN +
+           sizeof(int) * kTM;
+}
+
+cudaError_t configure_ozaki_kernels() {
+    cudaError_t e = cudaFuncSetAttribute(k_selinv_oz<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)oz_smem_bytes<16>());
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_selinv_oz<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)oz_smem_bytes<32>());
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_selinv_oz<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)oz_smem_bytes<64>());
+    return e;
+}
+
+cudaError_t launch_lhat_digits(const ProbDesc *d, const int2 *work, int nwork, cudaStream_t st) {
+    if (nwork <= 0) return cudaSuccess;
+    k_lhat_digits<<<nwork, 256, 0, st>>>(d, work, nwork);
+    return cudaGetLastError();
+}
+
+// TN = 16, 32 or 64 (a column tile); items carry tile = row_tile * ncol + col_tile
+cudaError_t launch_selinv_oz(int tn, const ProbDesc *d, const Item *items, int n, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    if (tn == 16) k_selinv_oz<16><<<n, kOzThreads, oz_smem_bytes<16>(), st>>>(d, items, n);
+    else if (tn == 32) k_selinv_oz<32><<<n, kOzThreads, oz_smem_bytes<32>(), st>>>(d, items, n);
+    else k_selinv_oz<64><<<n, kOzThreads, oz_smem_bytes<64>(), st>>>(d, items, n);
+    return cudaGetLastError();
+}
+
+}  // namespace selinv

@@ -12,21 +12,13 @@
 
 #include "common.cuh"
 #include "launch.h"
+#include "tile_gemm.cuh"
 
 namespace selinv {
 
-constexpr int kThreads = 256;
-constexpr int kTK = 16;
 
 __device__ inline void latch_status(int *status, int code) {
     if (status) atomicCAS(status, 0, code);
-}
-
-// loads that bypass L1 (data written by other CTAs of the same launch)
-__device__ inline double ldcg(const double *p) { return __ldcg(p); }
-__device__ inline zd ldcg(const zd *p) {
-    const double2 v = __ldcg(reinterpret_cast<const double2 *>(p));
-    return make_zd(v.x, v.y);
 }
 
 // ---------------------------------------------------------------------------
@@ -69,57 +61,6 @@ __global__ void __launch_bounds__(128) k_linv(const ProbDesc *__restrict__ descs
         LD[(int64_t)j * ld + i] = acc;
     }
 }
-
-// ---------------------------------------------------------------------------
-// register-tiled GEMM core: acc[MI][NJ] += A(TM x kdim) * B(kdim x TN),
-// A and B staged tile by tile (TK) in shared memory by loader functors.
-// Thread (tx, ty) owns rows ty + TY*i and columns tx + TX*j.
-// ---------------------------------------------------------------------------
-template <int TN> struct Shape {
-    static constexpr int TX = TN < 16 ? TN : 16;
-    static constexpr int TY = kThreads / TX;
-    static constexpr int MI = kTM / TY;
-    static constexpr int NJ = TN / TX;
-};
-
-template <typename T, int TN, class LA, class LB>
-__device__ inline void tile_gemm(int kdim, const LA &la, const LB &lb,
-                                 T (&acc)[Shape<TN>::MI][Shape<TN>::NJ], T *As, T *Bs) {
-    using S = Shape<TN>;
-    const int tx = threadIdx.x % S::TX, ty = threadIdx.x / S::TX;
-    for (int k0 = 0; k0 < kdim; k0 += kTK) {
-        __syncthreads();
-        la(k0, As);
-        lb(k0, Bs);
-        __syncthreads();
-#pragma unroll 4
-        for (int kk = 0; kk < kTK; kk++) {
-            T a[S::MI], b[S::NJ];
-#pragma unroll
-            for (int i = 0; i < S::MI; i++) a[i] = As[kk * kTM + ty + S::TY * i];
-#pragma unroll
-            for (int j = 0; j < S::NJ; j++) b[j] = Bs[kk * TN + tx + S::TX * j];
-#pragma unroll
-            for (int i = 0; i < S::MI; i++)
-#pragma unroll
-                for (int j = 0; j < S::NJ; j++) madd(acc[i][j], a[i], b[j]);
-        }
-    }
-}
-
-// B loader: a column-major block X (ld ldx) restricted to kdim rows, s columns
-template <typename T, int TN> struct LoadColMajor {
-    const T *X;
-    int64_t ldx;
-    int kdim, s;
-    __device__ void operator()(int k0, T *Bs) const {
-        for (int e = threadIdx.x; e < kTK * TN; e += kThreads) {
-            const int kk = e % kTK, j = e / kTK;
-            const int k = k0 + kk;
-            Bs[kk * TN + j] = (k < kdim && j < s) ? X[(int64_t)j * ldx + k] : Sc<T>::zero();
-        }
-    }
-};
 
 // ---------------------------------------------------------------------------
 // k_lhat: Lhat(p, :) = L(s + p, :) L_KK^{-1} for the TM rows of one item.
@@ -179,84 +120,14 @@ __global__ void __launch_bounds__(kThreads) k_lhat(const ProbDesc *__restrict__ 
         }
 }
 
-// ---------------------------------------------------------------------------
-// k_selinv: one row tile of C(K).
-// Gather: entry (p, q) of A^{-1}_{C,C} is stored, by symmetry, at
-// (max(p,q), min(p,q)); with b = min, a = max it sits in the panel of the
-// owner of column C[b] at row relidx[prb[b] + a], column address pcb[b].
-// ---------------------------------------------------------------------------
-template <typename T, int TN> struct LoadGather {
-    const T *Z;
-    const int64_t *pcb;   // per C position: panel address of column C[q] (+ plan base)
-    const int64_t *prb;   // per C position: base into relidx
-    const int32_t *relidx;
-    const int64_t *tile_cb;  // shared: pcb of the tile's rows
-    const int64_t *tile_rb;  // shared: prb of the tile's rows
-    int p0, c;
-    __device__ void operator()(int k0, T *As) const {
-        for (int e = threadIdx.x; e < kTK * kTM; e += kThreads) {
-            const int pl = e % kTM, kk = e / kTM;
-            const int p = p0 + pl, q = k0 + kk;
-            T v = Sc<T>::zero();
-            if (p < c && q < c) {
-                int64_t addr;
-                if (p >= q) addr = pcb[q] + relidx[prb[q] + p];
-                else addr = tile_cb[pl] + relidx[tile_rb[pl] + q];
-                v = Z[addr];
-            }
-            As[kk * kTM + pl] = v;
-        }
-    }
-};
-
+// Split contribution of one row tile to the diagonal block,
+// Ptile(i, j) = sum_{p in tile} Lhat(p, i) Y(p, j), written to the partial
+// buffer; the last tile of K to arrive reduces the partials in tile order
+// (deterministic) into A^{-1}_KK = Dinv_K - sum_t Ptile, symmetrized.
 template <typename T, int TN>
-__global__ void __launch_bounds__(kThreads) k_selinv(const ProbDesc *__restrict__ descs,
-                                                     const Item *__restrict__ items, int nitems) {
-    using S = Shape<TN>;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    T *As = reinterpret_cast<T *>(smem_raw);
-    T *Bs = As + smem_a_elems<T, TN>();
-    __shared__ int64_t tile_cb[kTM], tile_rb[kTM];
+__device__ void diag_block(const ProbDesc &P, const Item &it, int K, int s, int64_t ld, int c, int p0,
+                           int pm, const T *LDk, T *Zk, T *As, T *Bs) {
     __shared__ int s_last;
-    const int w = blockIdx.x;
-    if (w >= nitems) return;
-    const Item it = items[w];
-    const ProbDesc &P = descs[it.prob];
-    const int K = it.K;
-    const int s = P.super_ptr[K + 1] - P.super_ptr[K];
-    const int64_t ld = P.rowptr[K + 1] - P.rowptr[K];
-    const int c = (int)(ld - s);
-    const int p0 = it.tile * kTM;
-    const int pm = c - p0 < kTM ? c - p0 : kTM;  // rows in this tile (may be <= 0 when c == 0)
-    const int64_t pos0 = P.rowptr[K] + s;         // position of C[0] in the row lists
-    const T *Zc = static_cast<const T *>(P.Z);
-    T *Zk = static_cast<T *>(P.Z) + P.panel_off[K];
-    const T *LDk = static_cast<const T *>(P.LD) + P.panel_off[K];
-
-    for (int e = threadIdx.x; e < kTM; e += kThreads) {
-        const int p = p0 + e;
-        tile_cb[e] = p < c ? P.colbase[pos0 + p] : 0;
-        tile_rb[e] = p < c ? P.relbase[pos0 + p] : 0;
-    }
-    T acc[S::MI][S::NJ];
-#pragma unroll
-    for (int i = 0; i < S::MI; i++)
-#pragma unroll
-        for (int j = 0; j < S::NJ; j++) acc[i][j] = Sc<T>::zero();
-    if (pm > 0) {
-        LoadGather<T, TN> la{Zc, P.colbase + pos0, P.relbase + pos0, P.relidx, tile_cb, tile_rb, p0, c};
-        LoadColMajor<T, TN> lb{LDk + s, ld, c, s};  // Lhat(q, j) = LD[j*ld + s + q]
-        tile_gemm<T, TN>(c, la, lb, acc, As, Bs);
-    }
-    // write A^{-1}_{C,K} = -acc
-    const int tx = threadIdx.x % S::TX, ty = threadIdx.x / S::TX;
-#pragma unroll
-    for (int i = 0; i < S::MI; i++)
-#pragma unroll
-        for (int j = 0; j < S::NJ; j++) {
-            const int p = p0 + ty + S::TY * i, col = tx + S::TX * j;
-            if (p < c && col < s) Zk[(int64_t)col * ld + s + p] = neg(acc[i][j]);
-        }
     __syncthreads();  // this CTA's rows of A^{-1}_{C,K} are visible to the CTA
     // split contribution of this tile: Ptile(i, j) = sum_{p in tile} Lhat(p, i) Y(p, j)
     T *part = static_cast<T *>(P.partial) + P.part_off[K] + (int64_t)it.tile * s * s;
@@ -328,6 +199,85 @@ __global__ void __launch_bounds__(kThreads) k_selinv(const ProbDesc *__restrict_
 }
 
 // ---------------------------------------------------------------------------
+// k_selinv: one row tile of C(K).
+// Gather: entry (p, q) of A^{-1}_{C,C} is stored, by symmetry, at
+// (max(p,q), min(p,q)); with b = min, a = max it sits in the panel of the
+// owner of column C[b] at row relidx[prb[b] + a], column address pcb[b].
+// ---------------------------------------------------------------------------
+template <typename T, int TN>
+__global__ void __launch_bounds__(kThreads) k_selinv(const ProbDesc *__restrict__ descs,
+                                                     const Item *__restrict__ items, int nitems) {
+    using S = Shape<TN>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *As = reinterpret_cast<T *>(smem_raw);
+    T *Bs = As + smem_a_elems<T, TN>();
+    __shared__ int64_t tile_cb[kTM], tile_rb[kTM];
+    const int w = blockIdx.x;
+    if (w >= nitems) return;
+    const Item it = items[w];
+    const ProbDesc &P = descs[it.prob];
+    const int K = it.K;
+    const int s = P.super_ptr[K + 1] - P.super_ptr[K];
+    const int64_t ld = P.rowptr[K + 1] - P.rowptr[K];
+    const int c = (int)(ld - s);
+    const int p0 = it.tile * kTM;
+    const int pm = c - p0 < kTM ? c - p0 : kTM;  // rows in this tile (may be <= 0 when c == 0)
+    const int64_t pos0 = P.rowptr[K] + s;         // position of C[0] in the row lists
+    const T *Zc = static_cast<const T *>(P.Z);
+    T *Zk = static_cast<T *>(P.Z) + P.panel_off[K];
+    const T *LDk = static_cast<const T *>(P.LD) + P.panel_off[K];
+
+    for (int e = threadIdx.x; e < kTM; e += kThreads) {
+        const int p = p0 + e;
+        tile_cb[e] = p < c ? P.colbase[pos0 + p] : 0;
+        tile_rb[e] = p < c ? P.relbase[pos0 + p] : 0;
+    }
+    T acc[S::MI][S::NJ];
+#pragma unroll
+    for (int i = 0; i < S::MI; i++)
+#pragma unroll
+        for (int j = 0; j < S::NJ; j++) acc[i][j] = Sc<T>::zero();
+    if (pm > 0) {
+        LoadGather<T, TN> la{Zc, P.colbase + pos0, P.relbase + pos0, P.relidx, tile_cb, tile_rb, p0, c};
+        LoadColMajor<T, TN> lb{LDk + s, ld, c, s};  // Lhat(q, j) = LD[j*ld + s + q]
+        tile_gemm<T, TN>(c, la, lb, acc, As, Bs);
+    }
+    // write A^{-1}_{C,K} = -acc
+    const int tx = threadIdx.x % S::TX, ty = threadIdx.x / S::TX;
+#pragma unroll
+    for (int i = 0; i < S::MI; i++)
+#pragma unroll
+        for (int j = 0; j < S::NJ; j++) {
+            const int p = p0 + ty + S::TY * i, col = tx + S::TX * j;
+            if (p < c && col < s) Zk[(int64_t)col * ld + s + p] = neg(acc[i][j]);
+        }
+    diag_block<T, TN>(P, it, K, s, ld, c, p0, pm, LDk, Zk, As, Bs);
+}
+
+// k_diag: the diagonal block of K from A^{-1}_{C,K} already in the output
+// (written by the tensor-core contraction), one row tile per item.
+template <typename T, int TN>
+__global__ void __launch_bounds__(kThreads) k_diag(const ProbDesc *__restrict__ descs,
+                                                   const Item *__restrict__ items, int nitems) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *As = reinterpret_cast<T *>(smem_raw);
+    T *Bs = As + smem_a_elems<T, TN>();
+    const int w = blockIdx.x;
+    if (w >= nitems) return;
+    const Item it = items[w];
+    const ProbDesc &P = descs[it.prob];
+    const int K = it.K;
+    const int s = P.super_ptr[K + 1] - P.super_ptr[K];
+    const int64_t ld = P.rowptr[K + 1] - P.rowptr[K];
+    const int c = (int)(ld - s);
+    const int p0 = it.tile * kTM;
+    const int pm = c - p0 < kTM ? c - p0 : kTM;
+    T *Zk = static_cast<T *>(P.Z) + P.panel_off[K];
+    const T *LDk = static_cast<const T *>(P.LD) + P.panel_off[K];
+    diag_block<T, TN>(P, it, K, s, ld, c, p0, pm, LDk, Zk, As, Bs);
+}
+
+// ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
 template <typename T>
@@ -348,7 +298,8 @@ static cudaError_t launch_items_t(int kernel, const ProbDesc *d, const Item *ite
     if (n <= 0) return cudaSuccess;
     constexpr size_t smem = smem_bytes<T, TN>();
     if (kernel == 0) k_lhat<T, TN><<<n, kThreads, smem, st>>>(d, items, n);
-    else k_selinv<T, TN><<<n, kThreads, smem, st>>>(d, items, n);
+    else if (kernel == 1) k_selinv<T, TN><<<n, kThreads, smem, st>>>(d, items, n);
+    else k_diag<T, TN><<<n, kThreads, smem, st>>>(d, items, n);
     return cudaGetLastError();
 }
 
@@ -358,6 +309,8 @@ static cudaError_t configure_t() {
     cudaError_t e = cudaFuncSetAttribute(k_lhat<T, TN>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_selinv<T, TN>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_diag<T, TN>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     return e;
 }
 
@@ -400,6 +353,12 @@ cudaError_t launch_selinv(int dtype, int bucket, const ProbDesc *d, const Item *
                           cudaStream_t st) {
     return dtype == SELINV_C128 ? launch_items_dt<zd>(1, bucket, d, items, n, st)
                                 : launch_items_dt<double>(1, bucket, d, items, n, st);
+}
+
+cudaError_t launch_diag(int dtype, int bucket, const ProbDesc *d, const Item *items, int n,
+                        cudaStream_t st) {
+    return dtype == SELINV_C128 ? launch_items_dt<zd>(2, bucket, d, items, n, st)
+                                : launch_items_dt<double>(2, bucket, d, items, n, st);
 }
 
 }  // namespace selinv

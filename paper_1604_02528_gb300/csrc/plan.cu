@@ -40,6 +40,9 @@ static void dfree(void *p) {
 
 void Workspace::release() {
     dfree(LD); dfree(Linv); dfree(partial); dfree(counter); dfree(done); dfree(work);
+    dfree(lhs); dfree(colexp);
+    lhs = nullptr;
+    colexp = nullptr;
     LD = Linv = partial = nullptr;
     counter = done = nullptr;
     work = nullptr;
@@ -56,6 +59,9 @@ int Workspace::ensure(const PlanData &p, int dtype) {
     if (cudaMalloc((void **)&counter, sizeof(int) * (size_t)std::max(p.ns, 1)) != cudaSuccess) return SELINV_ERR_OOM;
     if (cudaMalloc((void **)&done, sizeof(int) * (size_t)std::max(p.ns, 1)) != cudaSuccess) return SELINV_ERR_OOM;
     if (cudaMalloc(&work, es * (size_t)std::max<int64_t>(p.nnz, 1)) != cudaSuccess) return SELINV_ERR_OOM;
+    if (cudaMalloc((void **)&lhs, sizeof(uint16_t) * (size_t)std::max<int64_t>(p.lhs_total, 8)) != cudaSuccess)
+        return SELINV_ERR_OOM;
+    if (cudaMalloc((void **)&colexp, sizeof(int) * (size_t)std::max(p.n, 1)) != cudaSuccess) return SELINV_ERR_OOM;
     cudaMemset(counter, 0, sizeof(int) * (size_t)std::max(p.ns, 1));
     cudaMemset(done, 0, sizeof(int) * (size_t)std::max(p.ns, 1));
     bytes_elem = es;
@@ -168,6 +174,15 @@ static int build_plan(PlanData &p, int32_t n, int32_t ns, const int32_t *super_p
         p.ntiles[K] = (int32_t)std::max<int64_t>(1, (c + kTM - 1) / kTM);
     }
     p.linv_total = p.linv_off[ns];
+    // digit planes of Lhat for the tensor-core path: 7 planes of s x roundup(c, 16)
+    p.lhs_off.assign(ns + 1, 0);
+    for (int32_t K = 0; K < ns; K++) {
+        const int64_t s = super_ptr[K + 1] - super_ptr[K];
+        const int64_t c = rowptr[K + 1] - rowptr[K] - s;
+        const int64_t c16 = (c + 15) / 16 * 16;
+        p.lhs_off[K + 1] = p.lhs_off[K] + (s >= kOzMinS ? 7 * s * c16 : 0);
+    }
+    p.lhs_total = p.lhs_off[ns];
     p.part_max = 1;
     for (int l = 0; l < p.nlevels; l++) {
         int64_t acc = 0;
@@ -189,6 +204,7 @@ int ensure_device(PlanData &p) {
     static bool configured = false;
     if (!configured) {
         if (configure_selinv_kernels() != cudaSuccess) return SELINV_ERR_CUDA;
+        if (configure_ozaki_kernels() != cudaSuccess) return SELINV_ERR_CUDA;
         configured = true;
     }
     int rc;
@@ -202,6 +218,7 @@ int ensure_device(PlanData &p) {
     if ((rc = upload(&p.d_relidx, p.relidx))) return rc;
     if ((rc = upload(&p.d_linv_off, p.linv_off))) return rc;
     if ((rc = upload(&p.d_part_off, p.part_off))) return rc;
+    if ((rc = upload(&p.d_lhs_off, p.lhs_off))) return rc;
     int *st = nullptr;
     if (cudaMalloc((void **)&st, sizeof(int)) != cudaSuccess) return SELINV_ERR_OOM;
     if (cudaMemset(st, 0, sizeof(int)) != cudaSuccess) return SELINV_ERR_CUDA;
@@ -212,7 +229,8 @@ int ensure_device(PlanData &p) {
 void PlanData::release_device() {
     dfree(d_super_ptr); dfree(d_sparent); dfree(d_rowptr); dfree(d_rows); dfree(d_panel_off);
     dfree(d_colbase); dfree(d_relbase); dfree(d_relidx); dfree(d_linv_off); dfree(d_part_off);
-    dfree(d_status);
+    dfree(d_lhs_off); dfree(d_status);
+    d_lhs_off = nullptr;
     d_super_ptr = d_sparent = d_rows = d_relidx = nullptr;
     d_rowptr = d_panel_off = d_colbase = d_relbase = d_linv_off = d_part_off = nullptr;
     d_status = nullptr;
@@ -241,6 +259,9 @@ ProbDesc make_desc(const PlanData &p, Workspace &w, int dtype, const void *L, co
     d.counter = w.counter;
     d.done = persistent ? w.done : nullptr;
     d.status = p.d_status;
+    d.lhs = w.lhs;
+    d.lhs_off = p.d_lhs_off;
+    d.colexp = w.colexp;
     d.ns = p.ns;
     d.n = p.n;
     d.dtype = dtype;
@@ -293,27 +314,96 @@ int build_schedule(Schedule &S, const std::vector<const PlanData *> &plans,
             const int cnt = (int)(S.h_items.size() - off);
             if (cnt) S.launches.push_back({1, dt, b, off, cnt, -1});
         }
+    // 2b) bf16 digit planes of Lhat for the tensor-core contraction
+    {
+        const int64_t off = (int64_t)S.h_work.size();
+        for (int i = 0; i < np; i++) {
+            const PlanData &p = *plans[i];
+            for (int32_t K = 0; K < p.ns; K++) {
+                const int s = p.super_ptr[K + 1] - p.super_ptr[K];
+                const int64_t c = p.rowptr[K + 1] - p.rowptr[K] - s;
+                if (c == 0 || !oz_eligible(descs[i].dtype, s, p.opts.fast_contraction)) continue;
+                for (int jb = 0; jb < (s + 7) / 8; jb++) S.h_work.push_back(make_int2(i, (K << 8) | jb));
+            }
+        }
+        const int cnt = (int)(S.h_work.size() - off);
+        if (cnt) S.launches.push_back({KL_DIGITS, SELINV_F64, 0, off, cnt, -1});
+    }
     // 3) the traversal, root to leaves
     auto push_items = [&](int i, int32_t K) {
         const PlanData &p = *plans[i];
         for (int t = 0; t < p.ntiles[K]; t++) S.h_items.push_back({i, K, t, p.ntiles[K]});
+    };
+    // tensor-core items: (row tile, column tile of width tn) pairs; c == 0 has none
+    auto push_oz = [&](int i, int32_t K, int tn) {
+        const PlanData &p = *plans[i];
+        const int s = p.super_ptr[K + 1] - p.super_ptr[K];
+        const int64_t c = p.rowptr[K + 1] - p.rowptr[K] - s;
+        if (c == 0) return;
+        const int ncol = (s + tn - 1) / tn;
+        for (int t = 0; t < p.ntiles[K]; t++)
+            for (int ct = 0; ct < ncol; ct++) S.h_items.push_back({i, K, t * ncol + ct, p.ntiles[K]});
     };
     if (mode == SELINV_SCHED_PLAIN) {
         // one launch per supernode, K = N..1, problem after problem
         for (int i = 0; i < np; i++) {
             const PlanData &p = *plans[i];
             for (int32_t K = p.ns - 1; K >= 0; K--) {
+                const int s = p.super_ptr[K + 1] - p.super_ptr[K];
+                if (oz_eligible(descs[i].dtype, s, p.opts.fast_contraction)) {
+                    const int tn = s <= 16 ? 16 : (s <= 32 ? 32 : 64);
+                    const int64_t off = (int64_t)S.h_items.size();
+                    push_oz(i, K, tn);
+                    S.launches.push_back({KL_SELINV_OZ, descs[i].dtype, tn, off,
+                                          (int)(S.h_items.size() - off), p.level[K]});
+                    const int64_t off2 = (int64_t)S.h_items.size();
+                    push_items(i, K);
+                    S.launches.push_back({KL_DIAG, descs[i].dtype, bucket_of(s), off2,
+                                          (int)(S.h_items.size() - off2), p.level[K]});
+                    continue;
+                }
                 const int64_t off = (int64_t)S.h_items.size();
                 push_items(i, K);
-                const int s = p.super_ptr[K + 1] - p.super_ptr[K];
-                S.launches.push_back({2, descs[i].dtype, bucket_of(s), off,
+                S.launches.push_back({KL_SELINV, descs[i].dtype, bucket_of(s), off,
                                       (int)(S.h_items.size() - off), p.level[K]});
             }
         }
     } else {
         int nlev = 0;
         for (int i = 0; i < np; i++) nlev = std::max(nlev, plans[i]->nlevels);
-        for (int l = 0; l < nlev; l++)
+        for (int l = 0; l < nlev; l++) {
+            // tensor-core contraction of every eligible supernode of the level
+            // (one launch per column-tile width), then their diagonal blocks
+            std::vector<std::pair<int, int32_t>> oz;  // (problem, K)
+            for (int i = 0; i < np; i++) {
+                const PlanData &p = *plans[i];
+                if (l >= p.nlevels) continue;
+                for (int64_t e = p.level_ptr[l]; e < p.level_ptr[l + 1]; e++) {
+                    const int32_t K = p.level_list[e];
+                    if (oz_eligible(descs[i].dtype, p.super_ptr[K + 1] - p.super_ptr[K], p.opts.fast_contraction))
+                        oz.push_back({i, K});
+                }
+            }
+            for (int tn : {64, 32, 16}) {
+                const int64_t off = (int64_t)S.h_items.size();
+                for (auto &ik : oz) {
+                    const PlanData &p = *plans[ik.first];
+                    const int s = p.super_ptr[ik.second + 1] - p.super_ptr[ik.second];
+                    if ((s <= 16 ? 16 : (s <= 32 ? 32 : 64)) == tn) push_oz(ik.first, ik.second, tn);
+                }
+                const int cnt = (int)(S.h_items.size() - off);
+                if (cnt) S.launches.push_back({KL_SELINV_OZ, SELINV_F64, tn, off, cnt, l});
+            }
+            for (int b = kNumBuckets - 1; b >= 0; b--) {
+                const int64_t off = (int64_t)S.h_items.size();
+                for (auto &ik : oz) {
+                    const PlanData &p = *plans[ik.first];
+                    if (bucket_of(p.super_ptr[ik.second + 1] - p.super_ptr[ik.second]) == b) push_items(ik.first, ik.second);
+                }
+                const int cnt = (int)(S.h_items.size() - off);
+                if (cnt) S.launches.push_back({KL_DIAG, SELINV_F64, b, off, cnt, l});
+            }
+            // fused DFMA kernel for everything else
             for (int dt = 0; dt < 2; dt++)
                 for (int b = kNumBuckets - 1; b >= 0; b--) {
                     const int64_t off = (int64_t)S.h_items.size();
@@ -323,12 +413,14 @@ int build_schedule(Schedule &S, const std::vector<const PlanData *> &plans,
                         if (l >= p.nlevels) continue;
                         for (int64_t e = p.level_ptr[l]; e < p.level_ptr[l + 1]; e++) {
                             const int32_t K = p.level_list[e];
-                            if (bucket_of(p.super_ptr[K + 1] - p.super_ptr[K]) == b) push_items(i, K);
+                            const int s = p.super_ptr[K + 1] - p.super_ptr[K];
+                            if (bucket_of(s) == b && !oz_eligible(dt, s, p.opts.fast_contraction)) push_items(i, K);
                         }
                     }
                     const int cnt = (int)(S.h_items.size() - off);
-                    if (cnt) S.launches.push_back({2, dt, b, off, cnt, l});
+                    if (cnt) S.launches.push_back({KL_SELINV, dt, b, off, cnt, l});
                 }
+        }
     }
     S.h_descs = descs;
     int rc;
@@ -338,13 +430,22 @@ int build_schedule(Schedule &S, const std::vector<const PlanData *> &plans,
     return SELINV_OK;
 }
 
+cudaError_t launch_one(const Schedule &S, const Launch &L, cudaStream_t st) {
+    switch (L.kind) {
+    case KL_LINV: return launch_linv(L.dtype, S.d_descs, S.d_work + L.off, L.count, st);
+    case KL_LHAT: return launch_lhat(L.dtype, L.bucket, S.d_descs, S.d_items + L.off, L.count, st);
+    case KL_SELINV: return launch_selinv(L.dtype, L.bucket, S.d_descs, S.d_items + L.off, L.count, st);
+    case KL_DIGITS: return launch_lhat_digits(S.d_descs, S.d_work + L.off, L.count, st);
+    case KL_SELINV_OZ: return launch_selinv_oz(L.bucket, S.d_descs, S.d_items + L.off, L.count, st);
+    case KL_DIAG: return launch_diag(L.dtype, L.bucket, S.d_descs, S.d_items + L.off, L.count, st);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
 static cudaError_t issue(const Schedule &S, cudaStream_t st, bool count) {
     if (count) note_launch((int)S.launches.size());
     for (const Launch &L : S.launches) {
-        cudaError_t e = cudaSuccess;
-        if (L.kind == 0) e = launch_linv(L.dtype, S.d_descs, S.d_work + L.off, L.count, st);
-        else if (L.kind == 1) e = launch_lhat(L.dtype, L.bucket, S.d_descs, S.d_items + L.off, L.count, st);
-        else e = launch_selinv(L.dtype, L.bucket, S.d_descs, S.d_items + L.off, L.count, st);
+        cudaError_t e = launch_one(S, L, st);
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
@@ -532,14 +633,11 @@ extern "C" int selinv_numeric_profile(selinv_plan plan, selinv_dtype dtype, cons
     Schedule &S = plan->single;
     std::vector<cudaEvent_t> ev(2 * S.launches.size());
     for (auto &e : ev) cudaEventCreate(&e);
-    for (int k = 0; k < 3; k++) { kernel_ms[k] = 0; kernel_launches[k] = 0; }
+    for (int k = 0; k < KL_NKINDS; k++) { kernel_ms[k] = 0; kernel_launches[k] = 0; }
     for (size_t i = 0; i < S.launches.size(); i++) {
         const Launch &L = S.launches[i];
         cudaEventRecord(ev[2 * i], st);
-        cudaError_t e;
-        if (L.kind == 0) e = launch_linv(L.dtype, S.d_descs, S.d_work + L.off, L.count, st);
-        else if (L.kind == 1) e = launch_lhat(L.dtype, L.bucket, S.d_descs, S.d_items + L.off, L.count, st);
-        else e = launch_selinv(L.dtype, L.bucket, S.d_descs, S.d_items + L.off, L.count, st);
+        cudaError_t e = launch_one(S, L, st);
         cudaEventRecord(ev[2 * i + 1], st);
         if (e != cudaSuccess) rc = SELINV_ERR_CUDA;
     }

@@ -18,12 +18,13 @@ struct PlanData {
     std::vector<int32_t> seg_owner, seg_start, seg_coloff, relidx, ntiles;
     std::vector<int64_t> rowptr, panel_off, seg_ptr, rel_ptr, level_ptr, linv_off, part_off;
     std::vector<int64_t> colbase, relbase;  // per row-list position
+    std::vector<int64_t> lhs_off;           // digit-plane offsets (tensor-core path)
     int nlevels = 0;
-    int64_t nnz = 0, linv_total = 0, part_max = 1;
+    int64_t nnz = 0, linv_total = 0, part_max = 1, lhs_total = 0;
     // device copies
     int32_t *d_super_ptr = nullptr, *d_sparent = nullptr, *d_rows = nullptr, *d_relidx = nullptr;
     int64_t *d_rowptr = nullptr, *d_panel_off = nullptr, *d_colbase = nullptr, *d_relbase = nullptr;
-    int64_t *d_linv_off = nullptr, *d_part_off = nullptr;
+    int64_t *d_linv_off = nullptr, *d_part_off = nullptr, *d_lhs_off = nullptr;
     int *d_status = nullptr;
     void release_device();
 };
@@ -34,13 +35,22 @@ struct PlanData {
 struct Workspace {
     void *LD = nullptr, *Linv = nullptr, *partial = nullptr, *work = nullptr;
     int *counter = nullptr, *done = nullptr;
+    uint16_t *lhs = nullptr;   // bf16 digit planes of Lhat
+    int *colexp = nullptr;     // [n]
     size_t bytes_elem = 0;
     int ensure(const PlanData &p, int dtype);
     void release();
 };
 
+// launch kinds
+enum { KL_LINV = 0, KL_LHAT = 1, KL_SELINV = 2, KL_DIGITS = 3, KL_SELINV_OZ = 4, KL_DIAG = 5, KL_NKINDS = 6 };
+
+// tensor-core (FP64-exact) contraction applies to real problems with s >= kOzMinS
+constexpr int kOzMinS = 16;
+inline bool oz_eligible(int dtype, int s, int fast) { return fast && dtype == SELINV_F64 && s >= kOzMinS; }
+
 struct Launch {
-    int kind;    // 0 linv, 1 lhat, 2 selinv
+    int kind;    // KL_*
     int dtype;
     int bucket;
     int64_t off;
@@ -81,7 +91,43 @@ int build_schedule(Schedule &S, const std::vector<const PlanData *> &plans,
                    const std::vector<ProbDesc> &descs, int mode);
 int run_schedule(Schedule &S, cudaStream_t st, bool use_graph);
 
-struct FactorData;  // factorization / adjoint state (kernels_factor.cu)
+// factorization / adjoint state
+struct FactorDesc {
+    const int32_t *super_ptr;
+    const int64_t *rowptr;
+    const int32_t *rows;
+    const int64_t *panel_off;
+    const int32_t *relidx;
+    const int64_t *rel_ptr;
+    const int32_t *seg_K, *seg_start, *seg_end, *seg_coloff;
+    const int64_t *dseg_ptr;  // [ns+1] segments owned by J (descendant updates)
+    const int32_t *dseg;
+    void *L;
+    void *D;
+    int *status;
+};
+
+struct FactorData {
+    int32_t n = -1;
+    int64_t nnzA = 0;
+    std::vector<int64_t> a_pos;       // panel position of every stored entry of A
+    int64_t *d_a_pos = nullptr;
+    int32_t *d_seg_K = nullptr, *d_seg_start = nullptr, *d_seg_end = nullptr, *d_seg_coloff = nullptr;
+    int32_t *d_dseg = nullptr;
+    int64_t *d_dseg_ptr = nullptr, *d_rel_ptr = nullptr;
+    // launch lists
+    std::vector<int2> h_tiles;        // (J, row tile) per level, leaves first
+    std::vector<int> h_js;            // J per level
+    std::vector<int64_t> tile_lptr, j_lptr;
+    int2 *d_tiles = nullptr;
+    int *d_js = nullptr;
+    FactorDesc *d_desc = nullptr;
+    const void *key_L = nullptr, *key_D = nullptr;
+    int key_dtype = -1;
+    // adjoint state
+    void *adj = nullptr;
+};
+
 
 }  // namespace selinv
 

@@ -1,0 +1,104 @@
+// Shared tile machinery of the FP64 / complex128 kernels: a register-tiled
+// GEMM core over shared-memory stages filled by loader functors, and the
+// loaders (column-major blocks, panel rows, the indexed gather of a
+// symmetric block of A^{-1} -- or of any panel-layout array -- on C x C).
+#pragma once
+
+#include "common.cuh"
+
+namespace selinv {
+
+constexpr int kThreads = 256;
+constexpr int kTK = 16;
+
+// loads that bypass L1 (data written by other CTAs of the same launch)
+__device__ inline double ldcg(const double *p) { return __ldcg(p); }
+__device__ inline zd ldcg(const zd *p) {
+    const double2 v = __ldcg(reinterpret_cast<const double2 *>(p));
+    return make_zd(v.x, v.y);
+}
+
+// ---------------------------------------------------------------------------
+// register-tiled GEMM core: acc[MI][NJ] += A(TM x kdim) * B(kdim x TN),
+// A and B staged tile by tile (TK) in shared memory by loader functors.
+// Thread (tx, ty) owns rows ty + TY*i and columns tx + TX*j.
+// ---------------------------------------------------------------------------
+template <int TN> struct Shape {
+    static constexpr int TX = TN < 16 ? TN : 16;
+    static constexpr int TY = kThreads / TX;
+    static constexpr int MI = kTM / TY;
+    static constexpr int NJ = TN / TX;
+};
+
+template <typename T, int TN, class LA, class LB>
+__device__ inline void tile_gemm(int kdim, const LA &la, const LB &lb,
+                                 T (&acc)[Shape<TN>::MI][Shape<TN>::NJ], T *As, T *Bs) {
+    using S = Shape<TN>;
+    const int tx = threadIdx.x % S::TX, ty = threadIdx.x / S::TX;
+    for (int k0 = 0; k0 < kdim; k0 += kTK) {
+        __syncthreads();
+        la(k0, As);
+        lb(k0, Bs);
+        __syncthreads();
+#pragma unroll 4
+        for (int kk = 0; kk < kTK; kk++) {
+            T a[S::MI], b[S::NJ];
+#pragma unroll
+            for (int i = 0; i < S::MI; i++) a[i] = As[kk * kTM + ty + S::TY * i];
+#pragma unroll
+            for (int j = 0; j < S::NJ; j++) b[j] = Bs[kk * TN + tx + S::TX * j];
+#pragma unroll
+            for (int i = 0; i < S::MI; i++)
+#pragma unroll
+                for (int j = 0; j < S::NJ; j++) madd(acc[i][j], a[i], b[j]);
+        }
+    }
+}
+
+// B loader: a column-major block X (ld ldx) restricted to kdim rows, s columns
+template <typename T, int TN> struct LoadColMajor {
+    const T *X;
+    int64_t ldx;
+    int kdim, s;
+    __device__ void operator()(int k0, T *Bs) const {
+        for (int e = threadIdx.x; e < kTK * TN; e += kThreads) {
+            const int kk = e % kTK, j = e / kTK;
+            const int k = k0 + kk;
+            Bs[kk * TN + j] = (k < kdim && j < s) ? X[(int64_t)j * ldx + k] : Sc<T>::zero();
+        }
+    }
+};
+
+// ---------------------------------------------------------------------------
+// Gather of entry (p, q) of a symmetric C x C block stored lower in the
+// ancestors' panels: at (max(p,q), min(p,q)); with b = min, a = max it sits
+// in the panel of the owner of column C[b], column address colbase[b], row
+// relidx[relbase[b] + a].  kDoubleDiag doubles the diagonal (reverse-mode
+// use, where the symmetric cotangent counts the diagonal twice).
+// ---------------------------------------------------------------------------
+template <typename T, int TN, bool kDoubleDiag = false> struct LoadGather {
+    const T *Z;
+    const int64_t *pcb;   // per C position: panel address of column C[q] (+ plan base)
+    const int64_t *prb;   // per C position: base into relidx
+    const int32_t *relidx;
+    const int64_t *tile_cb;  // shared: pcb of the tile's rows
+    const int64_t *tile_rb;  // shared: prb of the tile's rows
+    int p0, c;
+    __device__ void operator()(int k0, T *As) const {
+        for (int e = threadIdx.x; e < kTK * kTM; e += kThreads) {
+            const int pl = e % kTM, kk = e / kTM;
+            const int p = p0 + pl, q = k0 + kk;
+            T v = Sc<T>::zero();
+            if (p < c && q < c) {
+                int64_t addr;
+                if (p >= q) addr = pcb[q] + relidx[prb[q] + p];
+                else addr = tile_cb[pl] + relidx[tile_rb[pl] + q];
+                v = Z[addr];
+                if (kDoubleDiag && p == q) v = add(v, v);
+            }
+            As[kk * kTM + pl] = v;
+        }
+    }
+};
+
+}  // namespace selinv

@@ -113,3 +113,27 @@ def test_batched_mixed_problems_match_oracle(native, cuda_device):
     for i, (sym, L, D, Z) in enumerate(runs + [runs[0]]):
         G = Zs[i].cpu().numpy()
         assert oracle.block_errors(sym, G, Z).max() <= TOL, i
+
+
+@pytest.mark.parametrize("name,make", [CASES[1], CASES[3], CASES[7], CASES[9]])
+def test_tensor_core_and_dfma_paths_match_oracle(native, cuda_device, name, make):
+    """The FP64-exact bf16 tensor-core contraction and the DFMA contraction
+    both meet the tolerance; they differ only by rounding order."""
+    import torch
+    p = make()
+    sym, L, D, Z = oracle_run(p)
+    plan = native.selinv_symbolic(sym.n, sym.nsuper, sym.super_ptr, sym.sparent, sym.rowptr, sym.rows)
+    outs = []
+    for fast in (1, 0):
+        o = native.selinv_default_opts()
+        o.fast_contraction = fast
+        native.selinv_plan_set_opts(plan, o)
+        Lt = torch.from_numpy(L).cuda(); Dt = torch.from_numpy(D).cuda()
+        Zt = torch.full_like(Lt, float("nan"))
+        native.selinv_numeric(plan, native.SELINV_F64, Lt, Dt, Zt, torch.cuda.current_stream())
+        torch.cuda.synchronize()
+        assert native.selinv_status(plan) == 0
+        outs.append(Zt.cpu().numpy())
+    for G in outs:
+        assert oracle.block_errors(sym, G, Z).max() <= TOL
+    assert oracle.block_errors(sym, outs[0], outs[1]).max() <= TOL
