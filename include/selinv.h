@@ -223,6 +223,36 @@ int selinv_numeric_profile(selinv_plan plan, selinv_dtype dtype, const void *L_d
  * SELINV_ERR_TIMEOUT, SELINV_ERR_ZERO_PIVOT or SELINV_ERR_NONFINITE). */
 int selinv_status(selinv_plan plan);
 
+/* ---------------------------------------------------------------------------
+ * selinv_dinv_noalloc: the diagonal-block step Dinv = L_KK^{-T} D_K^{-1}
+ * L_KK^{-1} for one s x s unit-lower block, without allocating any memory.
+ * There is no counterpart in the paper; it exists for callers that cannot
+ * allocate device memory: code in a latency-critical loop (cudaMalloc and
+ * cudaFree synchronize the whole device), code whose device memory is all
+ * owned by another allocator (a framework's caching allocator or a fixed
+ * arena), and code running where allocation is not permitted (a host
+ * callback).
+ *   s     block size, 0 <= s <= SELINV_NOALLOC_MAX_S (128); larger s returns
+ *         SELINV_ERR_INVALID_ARG without doing anything.
+ *   Lkk   device, column-major, leading dimension ld >= s; unit lower (its
+ *         diagonal and strictly upper part are not read).
+ *   D     device [s] pivots.
+ *   Dinv  device output, column-major, leading dimension ldo >= s; every
+ *         s x s entry is written.
+ * The scratch block L_KK^{-1} lives in a file-scope static device array of
+ * SELINV_NOALLOC_MAX_S^2 doubles (128 KB) that every GPU loading the library
+ * holds until the process exits.  Its device address is looked up on the
+ * first call on each device (with that device current), so make the first
+ * call on a device before any stream capture.  All calls share the array:
+ * calls that overlap on the GPU (different streams, no ordering between
+ * them) race on it.  Nothing in it needs clearing between calls.
+ * Asynchronous on cuda_stream; no cudaMalloc, cudaFree or allocating library
+ * call is made.
+ * ------------------------------------------------------------------------- */
+#define SELINV_NOALLOC_MAX_S 128
+int selinv_dinv_noalloc(int32_t s, const double *Lkk, int64_t ld, const double *D, double *Dinv,
+                        int64_t ldo, void *cuda_stream);
+
 /* Static text for an error code. */
 const char *selinv_error_string(int code);
 

@@ -66,6 +66,7 @@ def _load() -> ct.CDLL:
         "selinv_status": (I, [P]),
         "selinv_error_string": (ct.c_char_p, [I]),
         "selinv_launch_count": (I64, []),
+        "selinv_dinv_noalloc": (I, [I32, P, I64, P, P, I64, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -83,7 +84,7 @@ REQUIRED_SYMBOLS = ("selinv_default_opts", "selinv_analyse", "selinv_analysis_ge
                     "selinv_plan_get", "selinv_plan_set_opts", "selinv_numeric",
                     "selinv_numeric_batched", "selinv_numeric_profile", "selinv_plan_set_matrix", "selinv_factor",
                     "selinv_adjoint", "selinv_factor_adjoint", "selinv_status",
-                    "selinv_error_string", "selinv_launch_count")
+                    "selinv_error_string", "selinv_launch_count", "selinv_dinv_noalloc")
 
 
 def error_string(code: int) -> str:
@@ -273,6 +274,13 @@ def selinv_factor_adjoint(plan: Plan, dtype: int, L, D, L_bar, D_bar, A_bar_vals
     _check(LIB.selinv_factor_adjoint(plan.handle, int(dtype), _dptr(L), _dptr(D), _dptr(L_bar),
                                      _dptr(D_bar), _dptr(A_bar_vals), _stream(stream)),
            "selinv_factor_adjoint")
+
+
+def selinv_dinv_noalloc(s: int, Lkk, ld: int, D, Dinv, ldo: int, stream=None):
+    """Dinv = L^{-T} D^{-1} L^{-1} of one block with no allocation (scratch in a
+    static device array; s <= 128)."""
+    _check(LIB.selinv_dinv_noalloc(int(s), _dptr(Lkk), int(ld), _dptr(D), _dptr(Dinv), int(ldo),
+                                   _stream(stream)), "selinv_dinv_noalloc")
 
 
 def selinv_status(plan: Plan) -> int:
