@@ -58,6 +58,9 @@ def _load():
             f = getattr(lib, "orc_selinv_adjoint" + sfx)
             f.restype = ct.c_int
             f.argtypes = [ct.c_int32, P, P, P, P, P, P, P, P, P, P]
+            f = getattr(lib, "orc_solve" + sfx)
+            f.restype = ct.c_int
+            f.argtypes = [ct.c_int32, P, P, P, P, P, P, P]
             f = getattr(lib, "orc_ldlt_adjoint" + sfx)
             f.restype = ct.c_int
             f.argtypes = [ct.c_int32, P, P, P, P, P, P, P, P, P]
@@ -227,6 +230,23 @@ def selinv_push(sym: Sym, L: np.ndarray, D: np.ndarray, symmetrize: bool = True)
                                                         int(symmetrize))
     _check(rc, "selinv_push")
     return Z
+
+
+def solve(sym: Sym, L: np.ndarray, D: np.ndarray, b: np.ndarray) -> np.ndarray:
+    """x with L D L^T x = b (forward / back substitution with the panels)."""
+    lib = _load()
+    L = np.ascontiguousarray(L); D = np.ascontiguousarray(D, dtype=L.dtype)
+    x = np.array(b, dtype=L.dtype, copy=True)
+    rc = getattr(lib, "orc_solve" + _sfx(L.dtype))(*_sym_args(sym), _p(L), _p(D), _p(x))
+    _check(rc, "solve")
+    return x
+
+
+def selected_column(sym: Sym, L: np.ndarray, D: np.ndarray, j: int) -> np.ndarray:
+    """Column j of A^{-1} (all n entries) by one solve."""
+    e = np.zeros(sym.n, dtype=L.dtype)
+    e[j] = 1
+    return solve(sym, L, D, e)
 
 
 def selinv_adjoint(sym: Sym, L, D, Z, Zbar) -> Tuple[np.ndarray, np.ndarray]:

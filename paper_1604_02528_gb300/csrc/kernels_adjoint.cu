@@ -670,7 +670,7 @@ static int adj_normalize(selinv_plan_s *plan, const void *L, const void *D, cuda
     AdjData *a = static_cast<AdjData *>(plan->factor->adj);
     ProbDesc pd = make_desc(plan->data, plan->ws[0], SELINV_F64, L, D, nullptr, false);
     cudaMemcpyAsync(a->d_pdesc, &pd, sizeof(pd), cudaMemcpyHostToDevice, st);
-    launch_linv(SELINV_F64, a->d_pdesc, a->d_linv, (int)a->linv_work.size(), st);
+    launch_linv(SELINV_F64, a->d_pdesc, a->d_linv, (int)a->linv_work.size(), 1, st);
     note_launch();
     for (int b = 0; b < kNumBuckets; b++) {
         const int n = a->lhat_bptr[b + 1] - a->lhat_bptr[b];

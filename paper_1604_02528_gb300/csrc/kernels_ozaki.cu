@@ -21,6 +21,7 @@
 
 #include "common.cuh"
 #include "launch.h"
+#include "tile_gemm.cuh"
 
 namespace selinv {
 
@@ -281,6 +282,161 @@ __global__ void __launch_bounds__(kOzThreads, 1) k_selinv_oz(const ProbDesc *__r
     }
 }
 
+
+// ---------------------------------------------------------------------------
+// k_diag_oz: split contribution of one 64-row tile to the diagonal block,
+// Ptile(i, j) = sum_{p in tile} Lhat(p, i) Y(p, j), Y = A^{-1}_{C,K} (already
+// written), on the bf16 tensor cores with the same exact digit scheme:
+//   A = Lhat^T restricted to the tile (rows i, k = p): the Lhat digit planes,
+//       exponent = column exponent of Lhat (a valid bound over any subset);
+//   B = Y restricted to the tile: digits on a per-tile column exponent.
+// k = 64 needs no flush (7 * 64 * 2^14 < 2^24).  The partial is written in
+// FP64; the last tile of K reduces all partials in tile order (diag_finish).
+// 8 warps: warp w owns m-tile w (16 rows i) and the 4 n-tiles of a 32-column
+// pass over j.
+// ---------------------------------------------------------------------------
+constexpr int kDK = 64;          // k extent (rows of the tile)
+constexpr int kDpad = kDK + 8;   // smem row stride (bf16), conflict-free fragment loads
+constexpr int kDJ = 32;          // columns j per pass
+
+__global__ void __launch_bounds__(kOzThreads, 1) k_diag_oz(const ProbDesc *__restrict__ descs,
+                                                           const Item *__restrict__ items, int nitems) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    uint16_t *As = reinterpret_cast<uint16_t *>(smem_raw);          // [7][128][kDpad]
+    uint16_t *Bs = As + kDig * 128 * kDpad;                         // [7][kDJ][kDpad]
+    int *colE = reinterpret_cast<int *>(Bs + kDig * kDJ * kDpad);   // [128]
+    const int w = blockIdx.x;
+    if (w >= nitems) return;
+    const Item it = items[w];
+    const ProbDesc &P = descs[it.prob];
+    const int K = it.K;
+    const int fc = P.super_ptr[K];
+    const int s = P.super_ptr[K + 1] - fc;
+    const int64_t ld = P.rowptr[K + 1] - P.rowptr[K];
+    const int c = (int)(ld - s);
+    const int c16 = (c + 15) & ~15;
+    const int p0 = it.tile * kTM;
+    const int pm = c - p0 < kTM ? c - p0 : kTM;
+    const int s16 = (s + 15) & ~15;
+    double *Zk = static_cast<double *>(P.Z) + P.panel_off[K];
+    const double *LDk = static_cast<const double *>(P.LD) + P.panel_off[K];
+    const double *Y = Zk + s;                                       // Y(p, j) = Y[j*ld + p]
+    const uint16_t *Ag = P.lhs + P.lhs_off[K];
+    const int64_t aplane = (int64_t)s * c16;
+    const int64_t ss = (int64_t)s * s;
+    double *part = static_cast<double *>(P.partial) + P.part_off[K] + (int64_t)it.tile * ss;
+
+    if (pm > 0) {
+        // A digits: rows i < s16, k = p0 .. p0 + 63 (zero past c16 and for i >= s)
+        const int kvalid = c16 - p0 < kDK ? c16 - p0 : kDK;     // multiple of 16
+        for (int e = threadIdx.x; e < kDig * s16 * (kDK / 8); e += kOzThreads) {
+            const int ch = e % (kDK / 8), i = (e / (kDK / 8)) % s16, pl = e / (kDK / 8) / s16;
+            uint16_t *dst = As + (pl * 128 + i) * kDpad + ch * 8;
+            if (i < s && ch * 8 < kvalid) cp_async16(dst, Ag + pl * aplane + (int64_t)i * c16 + p0 + ch * 8);
+            else *reinterpret_cast<uint4 *>(dst) = make_uint4(0, 0, 0, 0);
+        }
+        // per-tile column exponents of Y
+        for (int j = threadIdx.x; j < 128; j += kOzThreads) colE[j] = 0;
+        __syncthreads();
+        for (int e = threadIdx.x; e < pm * s; e += kOzThreads) {
+            const int pl = e % pm, j = e / pm;
+            atomicMax(&colE[j], bexp(Y[(int64_t)j * ld + p0 + pl]));
+        }
+        cp_async_wait_all();
+        __syncthreads();
+    }
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    const int grp = lane / 4, qd = lane % 4;
+    const int mt = warp;                       // rows i = mt*16 .. mt*16+15
+    for (int jb = 0; jb < s; jb += kDJ) {
+        if (pm > 0) {
+            __syncthreads();                   // previous pass done with Bs
+            // B digits: columns jb .. jb+31, k = tile rows (two adjacent p per word)
+            for (int e = threadIdx.x; e < kDJ * (kDK / 2); e += kOzThreads) {
+                const int jl = e % kDJ, kk = (e / kDJ) * 2;
+                const int j = jb + jl;
+                int d0[kDig], d1[kDig];
+                const double y0 = (j < s && kk < pm) ? Y[(int64_t)j * ld + p0 + kk] : 0.0;
+                const double y1 = (j < s && kk + 1 < pm) ? Y[(int64_t)j * ld + p0 + kk + 1] : 0.0;
+                const int E = j < s ? colE[j] : 0;
+                digits7(y0, E, d0);
+                digits7(y1, E, d1);
+#pragma unroll
+                for (int i = 0; i < kDig; i++)
+                    *reinterpret_cast<uint32_t *>(Bs + (i * kDJ + jl) * kDpad + kk) =
+                        bf16_of_int(d0[i]) | (bf16_of_int(d1[i]) << 16);
+            }
+            __syncthreads();
+        }
+        float acc[4][kDig][4];
+#pragma unroll
+        for (int t = 0; t < 4; t++)
+#pragma unroll
+            for (int g = 0; g < kDig; g++)
+#pragma unroll
+                for (int r = 0; r < 4; r++) acc[t][g][r] = 0.f;
+        if (pm > 0 && mt * 16 < s) {
+#pragma unroll 1
+            for (int ks = 0; ks < kDK / kOzK; ks++) {
+                uint32_t a[kDig][4];
+#pragma unroll
+                for (int i = 0; i < kDig; i++) {
+                    const uint16_t *base = As + (i * 128 + mt * 16) * kDpad + ks * 16;
+                    a[i][0] = *reinterpret_cast<const uint32_t *>(base + grp * kDpad + qd * 2);
+                    a[i][1] = *reinterpret_cast<const uint32_t *>(base + (grp + 8) * kDpad + qd * 2);
+                    a[i][2] = *reinterpret_cast<const uint32_t *>(base + grp * kDpad + qd * 2 + 8);
+                    a[i][3] = *reinterpret_cast<const uint32_t *>(base + (grp + 8) * kDpad + qd * 2 + 8);
+                }
+#pragma unroll
+                for (int t = 0; t < 4; t++) {
+#pragma unroll
+                    for (int j = 0; j < kDig; j++) {
+                        const uint16_t *bb = Bs + (j * kDJ + t * 8 + grp) * kDpad + ks * 16;
+                        const uint32_t b0 = *reinterpret_cast<const uint32_t *>(bb + qd * 2);
+                        const uint32_t b1 = *reinterpret_cast<const uint32_t *>(bb + qd * 2 + 8);
+#pragma unroll
+                        for (int i = 0; i + j < kDig; i++)
+                            mma_bf16(acc[t][i + j], a[i][0], a[i][1], a[i][2], a[i][3], b0, b1);
+                    }
+                }
+            }
+        }
+        // exact group sums -> FP64 partial (zeros when the tile is empty)
+        if (mt * 16 < s) {
+#pragma unroll
+            for (int t = 0; t < 4; t++)
+#pragma unroll
+                for (int r = 0; r < 4; r++) {
+                    const int i = mt * 16 + grp + (r >= 2 ? 8 : 0);
+                    const int j = jb + t * 8 + qd * 2 + (r & 1);
+                    if (i >= s || j >= s) continue;
+                    long long g[kDig];
+#pragma unroll
+                    for (int q = 0; q < kDig; q++) g[q] = (long long)__float2int_rn(acc[t][q][r]);
+                    const long long hi = (g[0] << 16) + (g[1] << 8) + g[2];
+                    const long long lo = (g[3] << 24) + (g[4] << 16) + (g[5] << 8) + g[6];
+                    double v = 0.0;
+                    if (pm > 0) {
+                        const int sc = (P.colexp[fc + i] - 1022) + (colE[j] - 1022) - 14;
+                        v = ldexp((double)hi, sc - 16) + ldexp((double)lo, sc - 48);
+                    }
+                    part[(int64_t)j * s + i] = v;
+                }
+        }
+    }
+    diag_finish<double>(P, K, s, ld, it.ntiles, LDk, Zk);
+}
+
+constexpr size_t diag_oz_smem() {
+    return sizeof(uint16_t) * (size_t)kDig * (128 + kDJ) * kDpad + sizeof(int) * 128;
+}
+
+cudaError_t launch_diag_oz(const ProbDesc *d, const Item *items, int n, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    k_diag_oz<<<n, kOzThreads, diag_oz_smem(), st>>>(d, items, n);
+    return cudaGetLastError();
+}
+
 template <int TN> constexpr size_t oz_smem_bytes() {
     return sizeof(uint16_t) * (size_t)kDig * (kTM + TN) * kApad + 2 * sizeof(long long) * kTM * TN +
            sizeof(int) * kTM;
@@ -290,6 +446,7 @@ cudaError_t configure_ozaki_kernels() {
     cudaError_t e = cudaFuncSetAttribute(k_selinv_oz<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)oz_smem_bytes<16>());
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_selinv_oz<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)oz_smem_bytes<32>());
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_selinv_oz<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)oz_smem_bytes<64>());
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_diag_oz, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)diag_oz_smem());
     return e;
 }
 

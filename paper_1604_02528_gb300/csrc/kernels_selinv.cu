@@ -22,11 +22,20 @@ __device__ inline void latch_status(int *status, int code) {
 }
 
 // ---------------------------------------------------------------------------
-// k_linv: one CTA per supernode.
+// k_linv: one CTA per supernode.  X = L_KK^{-1} by row-oriented forward
+// substitution on all columns at once: row k of X is final after step k-1,
+// and step k updates every X(i, j), i > k, j <= k, in parallel.  X stays in
+// shared memory when it fits (real blocks), else in the global scratch.
+// Then Dinv(i, j) = sum_{k >= max(i, j)} X(k, i) X(k, j) / D_k.
 // ---------------------------------------------------------------------------
+constexpr int kLinvThreads = 256;
+constexpr size_t kLinvSmemMax = 128 * 128 * sizeof(double);
+
 template <typename T>
-__global__ void __launch_bounds__(128) k_linv(const ProbDesc *__restrict__ descs,
-                                              const int2 *__restrict__ work, int nwork) {
+__global__ void __launch_bounds__(kLinvThreads) k_linv(const ProbDesc *__restrict__ descs,
+                                                       const int2 *__restrict__ work, int nwork,
+                                                       size_t smem_cap) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
     const int w = blockIdx.x;
     if (w >= nwork) return;
     const ProbDesc &P = descs[work[w].x];
@@ -38,26 +47,29 @@ __global__ void __launch_bounds__(128) k_linv(const ProbDesc *__restrict__ descs
     const T *D = static_cast<const T *>(P.D) + fc;
     T *Li = static_cast<T *>(P.Linv) + P.linv_off[K];
     T *LD = static_cast<T *>(P.LD) + P.panel_off[K];
-    // column j of L_KK^{-1}: forward substitution with the unit lower L_KK
-    for (int j = threadIdx.x; j < s; j += blockDim.x) {
-        T *x = Li + (int64_t)j * s;
-        for (int i = 0; i < j; i++) x[i] = Sc<T>::zero();
-        x[j] = Sc<T>::one();
-        for (int i = j + 1; i < s; i++) {
-            T acc = Sc<T>::zero();
-            for (int k = j; k < i; k++) madd(acc, L[(int64_t)k * ld + i], x[k]);
-            x[i] = neg(acc);
-        }
+    const bool in_smem = sizeof(T) * (size_t)s * s <= smem_cap;
+    T *X = in_smem ? reinterpret_cast<T *>(smem_raw) : Li;      // X(i, j) = X[j*s + i]
+    for (int e = threadIdx.x; e < s * s; e += kLinvThreads)
+        X[e] = (e % s == e / s) ? Sc<T>::one() : Sc<T>::zero();
+    for (int j = threadIdx.x; j < s; j += kLinvThreads)
         if (is_zero(D[j]) || !finite_val(D[j])) latch_status(P.status, SELINV_ERR_ZERO_PIVOT);
-    }
     __syncthreads();
-    // Dinv(i, j) = sum_{k >= max(i, j)} Linv(k, i) Linv(k, j) / D_k
-    for (int e = threadIdx.x; e < s * s; e += blockDim.x) {
+    for (int k = 0; k + 1 < s; k++) {
+        const int m = s - 1 - k;                 // rows i = k+1 .. s-1
+        for (int e = threadIdx.x; e < m * (k + 1); e += kLinvThreads) {
+            const int i = k + 1 + e % m, j = e / m;
+            msub(X[(int64_t)j * s + i], L[(int64_t)k * ld + i], X[(int64_t)j * s + k]);
+        }
+        __syncthreads();
+    }
+    if (in_smem)
+        for (int e = threadIdx.x; e < s * s; e += kLinvThreads) Li[e] = X[e];
+    for (int e = threadIdx.x; e < s * s; e += kLinvThreads) {
         const int i = e % s, j = e / s;
         const int k0 = i > j ? i : j;
         T acc = Sc<T>::zero();
         for (int k = k0; k < s; k++)
-            madd(acc, mul(Li[(int64_t)i * s + k], recip(D[k])), Li[(int64_t)j * s + k]);
+            madd(acc, mul(X[(int64_t)i * s + k], recip(D[k])), X[(int64_t)j * s + k]);
         LD[(int64_t)j * ld + i] = acc;
     }
 }
@@ -127,7 +139,6 @@ __global__ void __launch_bounds__(kThreads) k_lhat(const ProbDesc *__restrict__ 
 template <typename T, int TN>
 __device__ void diag_block(const ProbDesc &P, const Item &it, int K, int s, int64_t ld, int c, int p0,
                            int pm, const T *LDk, T *Zk, T *As, T *Bs) {
-    __shared__ int s_last;
     __syncthreads();  // this CTA's rows of A^{-1}_{C,K} are visible to the CTA
     // split contribution of this tile: Ptile(i, j) = sum_{p in tile} Lhat(p, i) Y(p, j)
     T *part = static_cast<T *>(P.partial) + P.part_off[K] + (int64_t)it.tile * s * s;
@@ -162,40 +173,7 @@ __device__ void diag_block(const ProbDesc &P, const Item &it, int K, int s, int6
             if (e < s * s) part[e] = pacc[o];
         }
     }
-    // the last tile of K to finish reduces the partials in tile order
-    __threadfence();
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        const int prev = atomicAdd(&P.counter[K], 1);
-        s_last = (prev == it.ntiles - 1);
-    }
-    __syncthreads();
-    if (!s_last) return;
-    __threadfence();
-    const T *part0 = static_cast<const T *>(P.partial) + P.part_off[K];
-    const int64_t ss = (int64_t)s * s;
-    for (int e = threadIdx.x; e < s * s; e += kThreads) {
-        const int i = e % s, j = e / s;
-        if (i < j) continue;
-        T xij = LDk[(int64_t)j * ld + i], xji = LDk[(int64_t)i * ld + j];
-        for (int t = 0; t < it.ntiles; t++) {
-            xij = sub(xij, ldcg(part0 + t * ss + (int64_t)j * s + i));
-            xji = sub(xji, ldcg(part0 + t * ss + (int64_t)i * s + j));
-        }
-        if (P.symmetrize) {
-            const T v = half(add(xij, xji));
-            xij = v;
-            xji = v;
-        }
-        Zk[(int64_t)j * ld + i] = xij;
-        Zk[(int64_t)i * ld + j] = xji;
-    }
-    if (threadIdx.x == 0) P.counter[K] = 0;
-    if (P.done) {
-        __threadfence();
-        __syncthreads();
-        if (threadIdx.x == 0) atomicExch(&P.done[K], 1);
-    }
+    diag_finish<T>(P, K, s, ld, it.ntiles, LDk, Zk);
 }
 
 // ---------------------------------------------------------------------------
@@ -281,15 +259,17 @@ __global__ void __launch_bounds__(kThreads) k_diag(const ProbDesc *__restrict__ 
 // launchers
 // ---------------------------------------------------------------------------
 template <typename T>
-static cudaError_t launch_linv_t(const ProbDesc *d, const int2 *work, int nwork, cudaStream_t st) {
+static cudaError_t launch_linv_t(const ProbDesc *d, const int2 *work, int nwork, int large, cudaStream_t st) {
     if (nwork <= 0) return cudaSuccess;
-    k_linv<T><<<nwork, 128, 0, st>>>(d, work, nwork);
+    // small blocks (s <= 32) need at most 16 KB; large ones get the 128 KB maximum
+    const size_t cap = large ? kLinvSmemMax : 32 * 32 * sizeof(T);
+    k_linv<T><<<nwork, kLinvThreads, cap, st>>>(d, work, nwork, cap);
     return cudaGetLastError();
 }
 
-cudaError_t launch_linv(int dtype, const ProbDesc *d, const int2 *work, int nwork, cudaStream_t st) {
-    return dtype == SELINV_C128 ? launch_linv_t<zd>(d, work, nwork, st)
-                                : launch_linv_t<double>(d, work, nwork, st);
+cudaError_t launch_linv(int dtype, const ProbDesc *d, const int2 *work, int nwork, int large, cudaStream_t st) {
+    return dtype == SELINV_C128 ? launch_linv_t<zd>(d, work, nwork, large, st)
+                                : launch_linv_t<double>(d, work, nwork, large, st);
 }
 
 template <typename T, int TN>
@@ -326,7 +306,10 @@ static cudaError_t configure_dt() {
 
 // opt every kernel in to its dynamic shared memory (outside any graph capture)
 cudaError_t configure_selinv_kernels() {
-    cudaError_t e = configure_dt<double>();
+    cudaError_t e = cudaFuncSetAttribute(k_linv<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kLinvSmemMax);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_linv<zd>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kLinvSmemMax);
+    if (e == cudaSuccess) e = configure_dt<double>();
     if (e == cudaSuccess) e = configure_dt<zd>();
     return e;
 }

@@ -11,7 +11,8 @@ namespace selinv {
 void note_launch(int n = 1);
 
 cudaError_t configure_selinv_kernels();
-cudaError_t launch_linv(int dtype, const ProbDesc *d, const int2 *work, int nwork, cudaStream_t st);
+// large = 1 for supernodes with s > 32 (128 KB of shared memory), 0 otherwise
+cudaError_t launch_linv(int dtype, const ProbDesc *d, const int2 *work, int nwork, int large, cudaStream_t st);
 cudaError_t launch_lhat(int dtype, int bucket, const ProbDesc *d, const Item *items, int n,
                         cudaStream_t st);
 cudaError_t launch_selinv(int dtype, int bucket, const ProbDesc *d, const Item *items, int n,
@@ -20,6 +21,7 @@ cudaError_t launch_diag(int dtype, int bucket, const ProbDesc *d, const Item *it
                         cudaStream_t st);
 cudaError_t configure_ozaki_kernels();
 cudaError_t launch_lhat_digits(const ProbDesc *d, const int2 *work, int nwork, cudaStream_t st);
+cudaError_t launch_diag_oz(const ProbDesc *d, const Item *items, int n, cudaStream_t st);
 cudaError_t launch_selinv_oz(int tn, const ProbDesc *d, const Item *items, int n, cudaStream_t st);
 
 }  // namespace selinv

@@ -287,16 +287,19 @@ int build_schedule(Schedule &S, const std::vector<const PlanData *> &plans,
     S.h_work.clear();
     S.mode = mode;
     const int np = (int)plans.size();
-    // 1) L_KK^{-1}, Dinv for every supernode (one launch per dtype)
-    for (int dt = 0; dt < 2; dt++) {
-        const int64_t off = (int64_t)S.h_work.size();
-        for (int i = 0; i < np; i++) {
-            if (descs[i].dtype != dt) continue;
-            for (int32_t K = 0; K < plans[i]->ns; K++) S.h_work.push_back(make_int2(i, K));
+    // 1) L_KK^{-1}, Dinv for every supernode (one launch per dtype and size class)
+    for (int dt = 0; dt < 2; dt++)
+        for (int large = 1; large >= 0; large--) {
+            const int64_t off = (int64_t)S.h_work.size();
+            for (int i = 0; i < np; i++) {
+                if (descs[i].dtype != dt) continue;
+                const PlanData &p = *plans[i];
+                for (int32_t K = 0; K < p.ns; K++)
+                    if ((p.super_ptr[K + 1] - p.super_ptr[K] > 32) == (large == 1)) S.h_work.push_back(make_int2(i, K));
+            }
+            const int cnt = (int)(S.h_work.size() - off);
+            if (cnt) S.launches.push_back({0, dt, large, off, cnt, -1});
         }
-        const int cnt = (int)(S.h_work.size() - off);
-        if (cnt) S.launches.push_back({0, dt, 0, off, cnt, -1});
-    }
     // 2) Lhat for every row tile (one launch per dtype and width class)
     for (int dt = 0; dt < 2; dt++)
         for (int b = 0; b < kNumBuckets; b++) {
@@ -394,14 +397,11 @@ int build_schedule(Schedule &S, const std::vector<const PlanData *> &plans,
                 const int cnt = (int)(S.h_items.size() - off);
                 if (cnt) S.launches.push_back({KL_SELINV_OZ, SELINV_F64, tn, off, cnt, l});
             }
-            for (int b = kNumBuckets - 1; b >= 0; b--) {
+            {
                 const int64_t off = (int64_t)S.h_items.size();
-                for (auto &ik : oz) {
-                    const PlanData &p = *plans[ik.first];
-                    if (bucket_of(p.super_ptr[ik.second + 1] - p.super_ptr[ik.second]) == b) push_items(ik.first, ik.second);
-                }
+                for (auto &ik : oz) push_items(ik.first, ik.second);
                 const int cnt = (int)(S.h_items.size() - off);
-                if (cnt) S.launches.push_back({KL_DIAG, SELINV_F64, b, off, cnt, l});
+                if (cnt) S.launches.push_back({KL_DIAG, SELINV_F64, 0, off, cnt, l});
             }
             // fused DFMA kernel for everything else
             for (int dt = 0; dt < 2; dt++)
@@ -432,12 +432,12 @@ int build_schedule(Schedule &S, const std::vector<const PlanData *> &plans,
 
 cudaError_t launch_one(const Schedule &S, const Launch &L, cudaStream_t st) {
     switch (L.kind) {
-    case KL_LINV: return launch_linv(L.dtype, S.d_descs, S.d_work + L.off, L.count, st);
+    case KL_LINV: return launch_linv(L.dtype, S.d_descs, S.d_work + L.off, L.count, L.bucket, st);
     case KL_LHAT: return launch_lhat(L.dtype, L.bucket, S.d_descs, S.d_items + L.off, L.count, st);
     case KL_SELINV: return launch_selinv(L.dtype, L.bucket, S.d_descs, S.d_items + L.off, L.count, st);
     case KL_DIGITS: return launch_lhat_digits(S.d_descs, S.d_work + L.off, L.count, st);
     case KL_SELINV_OZ: return launch_selinv_oz(L.bucket, S.d_descs, S.d_items + L.off, L.count, st);
-    case KL_DIAG: return launch_diag(L.dtype, L.bucket, S.d_descs, S.d_items + L.off, L.count, st);
+    case KL_DIAG: return launch_diag_oz(S.d_descs, S.d_items + L.off, L.count, st);
     default: return cudaErrorInvalidValue;
     }
 }

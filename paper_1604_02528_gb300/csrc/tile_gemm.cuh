@@ -101,4 +101,49 @@ template <typename T, int TN, bool kDoubleDiag = false> struct LoadGather {
     }
 };
 
+// ---------------------------------------------------------------------------
+// After a tile has written its split partial of the diagonal block: the last
+// tile of K to arrive (counter) reduces all partials in tile order
+// (deterministic) into A^{-1}_KK = Dinv_K - sum_t Ptile, symmetrized, and
+// flags K done when a completion array is present.
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ void diag_finish(const ProbDesc &P, int K, int s, int64_t ld, int ntiles, const T *LDk, T *Zk) {
+    __shared__ int s_last;
+    // the last tile of K to finish reduces the partials in tile order
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const int prev = atomicAdd(&P.counter[K], 1);
+        s_last = (prev == ntiles - 1);
+    }
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    const T *part0 = static_cast<const T *>(P.partial) + P.part_off[K];
+    const int64_t ss = (int64_t)s * s;
+    for (int e = threadIdx.x; e < s * s; e += kThreads) {
+        const int i = e % s, j = e / s;
+        if (i < j) continue;
+        T xij = LDk[(int64_t)j * ld + i], xji = LDk[(int64_t)i * ld + j];
+        for (int t = 0; t < ntiles; t++) {
+            xij = sub(xij, ldcg(part0 + t * ss + (int64_t)j * s + i));
+            xji = sub(xji, ldcg(part0 + t * ss + (int64_t)i * s + j));
+        }
+        if (P.symmetrize) {
+            const T v = half(add(xij, xji));
+            xij = v;
+            xji = v;
+        }
+        Zk[(int64_t)j * ld + i] = xij;
+        Zk[(int64_t)i * ld + j] = xji;
+    }
+    if (threadIdx.x == 0) P.counter[K] = 0;
+    if (P.done) {
+        __threadfence();
+        __syncthreads();
+        if (threadIdx.x == 0) atomicExch(&P.done[K], 1);
+    }
+}
+
 }  // namespace selinv

@@ -290,3 +290,18 @@ def test_selinv_adjoint_central_differences_on_L():
         Dm = D.copy(); Dm[k] -= h
         fd = (f(L, Dp) - f(L, Dm)) / (2 * h)
         assert abs(fd - Db[k]) <= 1e-6 * max(1.0, abs(Db[k]))
+
+
+@pytest.mark.parametrize("make", [lambda: synth.random_sparse_spd(70, 0.1, 51),
+                                  lambda: synth.random_sparse_spd(60, 0.1, 52, complex_values=True),
+                                  lambda: synth.laplacian_3d(7, seed=53)])
+def test_solve_matches_dense_solve(make):
+    """The oracle's substitution solve (used for sampled columns at full size)."""
+    p = make()
+    sym = oracle.symbolic_for(p)
+    L, D = oracle.ldlt(p, sym)
+    rng = np.random.default_rng(54)
+    b = rng.standard_normal(p.n).astype(p.values.dtype)
+    x = oracle.solve(sym, L, D, b)
+    ref = np.linalg.solve(p.dense(), b)
+    assert np.abs(x - ref).max() <= 1e-12 * np.abs(ref).max()
