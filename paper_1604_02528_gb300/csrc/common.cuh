@@ -94,6 +94,8 @@ struct ProbDesc {
     uint16_t *lhs;              // bf16 digit planes of Lhat (tensor-core contraction)
     const int64_t *lhs_off;     // [ns+1] offsets into lhs (elements)
     int *colexp;                // [n] biased exponent of each column of Lhat
+    int *colexpY;               // [n] biased exponent of each column of A^{-1}_{C,K} (atomic max)
+    long long *dacc;            // [2 * sum s^2] exact int64 sums of the diagonal-block products
     int32_t ns, n;
     int32_t dtype;              // selinv_dtype
     int32_t symmetrize;

@@ -269,6 +269,8 @@ __global__ void __launch_bounds__(kOzThreads, 1) k_selinv_oz(const ProbDesc *__r
             }
         }
     }
+    __shared__ int ymax[TN];
+    for (int e = threadIdx.x; e < TN; e += kOzThreads) ymax[e] = 0;
     __syncthreads();
     // Y = -(A^{-1}_{C,C} Lhat) in FP64: scale 2^(e_p + f_j - 14) (e = E - 1022)
     double *Zk = static_cast<double *>(P.Z) + P.panel_off[K];
@@ -279,19 +281,26 @@ __global__ void __launch_bounds__(kOzThreads, 1) k_selinv_oz(const ProbDesc *__r
         const int sc = (rowE[row] - 1022) + (P.colexp[fc + j] - 1022) - 14;
         const double y = ldexp((double)Hi[row * TN + col], sc - 16) + ldexp((double)Lo[row * TN + col], sc - 48);
         Zk[(int64_t)j * ld + s + p] = -y;
+        atomicMax(&ymax[col], bexp(y));
     }
+    __syncthreads();
+    // column exponents of A^{-1}_{C,K} over all row tiles (used by the diagonal block)
+    for (int col = threadIdx.x; col < TN; col += kOzThreads)
+        if (n0 + col < s && ymax[col] > 0) atomicMax(&P.colexpY[fc + n0 + col], ymax[col]);
 }
 
 
 // ---------------------------------------------------------------------------
-// k_diag_oz: split contribution of one 64-row tile to the diagonal block,
-// Ptile(i, j) = sum_{p in tile} Lhat(p, i) Y(p, j), Y = A^{-1}_{C,K} (already
-// written), on the bf16 tensor cores with the same exact digit scheme:
+// k_diag_oz: contribution of one 64-row tile to the diagonal block,
+// sum_{p in tile} Lhat(p, i) Y(p, j), Y = A^{-1}_{C,K} (already written), on
+// the bf16 tensor cores with the same exact digit scheme:
 //   A = Lhat^T restricted to the tile (rows i, k = p): the Lhat digit planes,
-//       exponent = column exponent of Lhat (a valid bound over any subset);
-//   B = Y restricted to the tile: digits on a per-tile column exponent.
-// k = 64 needs no flush (7 * 64 * 2^14 < 2^24).  The partial is written in
-// FP64; the last tile of K reduces all partials in tile order (diag_finish).
+//       exponent = column exponent of Lhat over all of C;
+//   B = Y restricted to the tile: digits on Y's column exponent over all of C
+//       (atomic max taken when Y was written).
+// k = 64 needs no flush (7 * 64 * 2^14 < 2^24).  Since every tile works on the
+// same grid, the tiles' integer sums are added exactly (int64 atomics, order
+// independent); the last tile forms A^{-1}_KK = Dinv - Lhat^T Y in FP64.
 // 8 warps: warp w owns m-tile w (16 rows i) and the 4 n-tiles of a 32-column
 // pass over j.
 // ---------------------------------------------------------------------------
@@ -324,7 +333,7 @@ __global__ void __launch_bounds__(kOzThreads, 1) k_diag_oz(const ProbDesc *__res
     const uint16_t *Ag = P.lhs + P.lhs_off[K];
     const int64_t aplane = (int64_t)s * c16;
     const int64_t ss = (int64_t)s * s;
-    double *part = static_cast<double *>(P.partial) + P.part_off[K] + (int64_t)it.tile * ss;
+    long long *acc64 = P.dacc + 2 * P.linv_off[K];            // [s*s] x (hi, lo)
 
     if (pm > 0) {
         // A digits: rows i < s16, k = p0 .. p0 + 63 (zero past c16 and for i >= s)
@@ -335,13 +344,8 @@ __global__ void __launch_bounds__(kOzThreads, 1) k_diag_oz(const ProbDesc *__res
             if (i < s && ch * 8 < kvalid) cp_async16(dst, Ag + pl * aplane + (int64_t)i * c16 + p0 + ch * 8);
             else *reinterpret_cast<uint4 *>(dst) = make_uint4(0, 0, 0, 0);
         }
-        // per-tile column exponents of Y
-        for (int j = threadIdx.x; j < 128; j += kOzThreads) colE[j] = 0;
-        __syncthreads();
-        for (int e = threadIdx.x; e < pm * s; e += kOzThreads) {
-            const int pl = e % pm, j = e / pm;
-            atomicMax(&colE[j], bexp(Y[(int64_t)j * ld + p0 + pl]));
-        }
+        // column exponents of Y over all of C (shared by every tile: exact sums)
+        for (int j = threadIdx.x; j < 128; j += kOzThreads) colE[j] = j < s ? P.colexpY[fc + j] : 0;
         cp_async_wait_all();
         __syncthreads();
     }
@@ -401,8 +405,9 @@ __global__ void __launch_bounds__(kOzThreads, 1) k_diag_oz(const ProbDesc *__res
                 }
             }
         }
-        // exact group sums -> FP64 partial (zeros when the tile is empty)
-        if (mt * 16 < s) {
+        // exact group sums of this tile -> int64, added exactly to the sums of
+        // all tiles of K (integer addition: the order does not matter)
+        if (pm > 0 && mt * 16 < s) {
 #pragma unroll
             for (int t = 0; t < 4; t++)
 #pragma unroll
@@ -415,16 +420,47 @@ __global__ void __launch_bounds__(kOzThreads, 1) k_diag_oz(const ProbDesc *__res
                     for (int q = 0; q < kDig; q++) g[q] = (long long)__float2int_rn(acc[t][q][r]);
                     const long long hi = (g[0] << 16) + (g[1] << 8) + g[2];
                     const long long lo = (g[3] << 24) + (g[4] << 16) + (g[5] << 8) + g[6];
-                    double v = 0.0;
-                    if (pm > 0) {
-                        const int sc = (P.colexp[fc + i] - 1022) + (colE[j] - 1022) - 14;
-                        v = ldexp((double)hi, sc - 16) + ldexp((double)lo, sc - 48);
-                    }
-                    part[(int64_t)j * s + i] = v;
+                    unsigned long long *dst = reinterpret_cast<unsigned long long *>(acc64 + 2 * ((int64_t)j * s + i));
+                    if (hi) atomicAdd(dst, (unsigned long long)hi);
+                    if (lo) atomicAdd(dst + 1, (unsigned long long)lo);
                 }
         }
     }
-    diag_finish<double>(P, K, s, ld, it.ntiles, LDk, Zk);
+    // the last tile of K: A^{-1}_KK = Dinv - (sums in FP64), symmetrized; reset the sums
+    __shared__ int s_last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = (atomicAdd(&P.counter[K], 1) == it.ntiles - 1);
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    for (int e = threadIdx.x; e < s * s; e += kOzThreads) {
+        const int i = e % s, j = e / s;
+        if (i < j) continue;
+        auto prod = [&](int a, int b) -> double {   // (Lhat^T Y)(a, b)
+            const long long *q = acc64 + 2 * ((int64_t)b * s + a);
+            const long long hi = (long long)__ldcg(reinterpret_cast<const unsigned long long *>(q));
+            const long long lo = (long long)__ldcg(reinterpret_cast<const unsigned long long *>(q) + 1);
+            const int ey = P.colexpY[fc + b];
+            if (ey == 0 || (hi == 0 && lo == 0)) return 0.0;
+            const int sc = (P.colexp[fc + a] - 1022) + (ey - 1022) - 14;
+            return ldexp((double)hi, sc - 16) + ldexp((double)lo, sc - 48);
+        };
+        double xij = LDk[(int64_t)j * ld + i] - prod(i, j);
+        double xji = LDk[(int64_t)i * ld + j] - prod(j, i);
+        if (P.symmetrize) { const double v = 0.5 * (xij + xji); xij = v; xji = v; }
+        Zk[(int64_t)j * ld + i] = xij;
+        Zk[(int64_t)i * ld + j] = xji;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < 2 * s * s; e += kOzThreads) acc64[e] = 0;
+    for (int j = threadIdx.x; j < s; j += kOzThreads) P.colexpY[fc + j] = 0;
+    if (threadIdx.x == 0) P.counter[K] = 0;
+    if (P.done) {
+        __threadfence();
+        __syncthreads();
+        if (threadIdx.x == 0) atomicExch(&P.done[K], 1);
+    }
 }
 
 constexpr size_t diag_oz_smem() {

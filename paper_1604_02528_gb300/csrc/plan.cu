@@ -40,9 +40,10 @@ static void dfree(void *p) {
 
 void Workspace::release() {
     dfree(LD); dfree(Linv); dfree(partial); dfree(counter); dfree(done); dfree(work);
-    dfree(lhs); dfree(colexp);
+    dfree(lhs); dfree(colexp); dfree(colexpY); dfree(dacc);
     lhs = nullptr;
-    colexp = nullptr;
+    colexp = colexpY = nullptr;
+    dacc = nullptr;
     LD = Linv = partial = nullptr;
     counter = done = nullptr;
     work = nullptr;
@@ -62,6 +63,11 @@ int Workspace::ensure(const PlanData &p, int dtype) {
     if (cudaMalloc((void **)&lhs, sizeof(uint16_t) * (size_t)std::max<int64_t>(p.lhs_total, 8)) != cudaSuccess)
         return SELINV_ERR_OOM;
     if (cudaMalloc((void **)&colexp, sizeof(int) * (size_t)std::max(p.n, 1)) != cudaSuccess) return SELINV_ERR_OOM;
+    if (cudaMalloc((void **)&colexpY, sizeof(int) * (size_t)std::max(p.n, 1)) != cudaSuccess) return SELINV_ERR_OOM;
+    if (cudaMalloc((void **)&dacc, sizeof(long long) * 2 * (size_t)std::max<int64_t>(p.linv_total, 1)) != cudaSuccess)
+        return SELINV_ERR_OOM;
+    cudaMemset(colexpY, 0, sizeof(int) * (size_t)std::max(p.n, 1));
+    cudaMemset(dacc, 0, sizeof(long long) * 2 * (size_t)std::max<int64_t>(p.linv_total, 1));
     cudaMemset(counter, 0, sizeof(int) * (size_t)std::max(p.ns, 1));
     cudaMemset(done, 0, sizeof(int) * (size_t)std::max(p.ns, 1));
     bytes_elem = es;
@@ -262,6 +268,8 @@ ProbDesc make_desc(const PlanData &p, Workspace &w, int dtype, const void *L, co
     d.lhs = w.lhs;
     d.lhs_off = p.d_lhs_off;
     d.colexp = w.colexp;
+    d.colexpY = w.colexpY;
+    d.dacc = w.dacc;
     d.ns = p.ns;
     d.n = p.n;
     d.dtype = dtype;

@@ -37,6 +37,8 @@ struct Workspace {
     int *counter = nullptr, *done = nullptr;
     uint16_t *lhs = nullptr;   // bf16 digit planes of Lhat
     int *colexp = nullptr;     // [n]
+    int *colexpY = nullptr;    // [n], zero between calls
+    long long *dacc = nullptr; // [2 * linv_total], zero between calls
     size_t bytes_elem = 0;
     int ensure(const PlanData &p, int dtype);
     void release();
