@@ -96,6 +96,10 @@ struct ProbDesc {
     int *colexp;                // [n] biased exponent of each column of Lhat
     int *colexpY;               // [n] biased exponent of each column of A^{-1}_{C,K} (atomic max)
     long long *dacc;            // [2 * sum s^2] exact int64 sums of the diagonal-block products
+    int *rowexp;                // [rowptr[ns]] exponent of each row of A^{-1}_{C,C} per C position
+    long long *yacc;            // [2 * nnz] exact int64 sums of split contractions, zero between calls
+    int *tcount;                // [sum ntiles] arrivals per (K, row tile), zero between calls
+    const int64_t *tile_base;   // [ns+1] prefix sums of the row tiles of each supernode
     int32_t ns, n;
     int32_t dtype;              // selinv_dtype
     int32_t symmetrize;

@@ -122,8 +122,77 @@ __device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::); }
 
 // ---------------------------------------------------------------------------
-// k_selinv_oz<TN>: one (K, row tile of 64, column tile of TN) item.
-// 8 warps: warp w owns m-tile (w % 4) and n-tiles (w / 4) + 2 t, t < TN/16.
+// Entry (p, q) of A^{-1}_{C,C} gathered from the ancestors' panels: stored at
+// (max, min) by symmetry; (p, q) are positions in C(K), pl = p - p0.
+// ---------------------------------------------------------------------------
+struct Gather {
+    const double *Z;
+    const int64_t *pcb, *prb;        // per C position of K
+    const int32_t *relidx;
+    const int64_t *tile_cb, *tile_rb; // the tile's rows (shared memory)
+    int p0, c;
+    __device__ __forceinline__ double operator()(int pl, int q) const {
+        const int p = p0 + pl;
+        if (p >= c || q >= c) return 0.0;
+        const int64_t addr = p >= q ? pcb[q] + relidx[prb[q] + p] : tile_cb[pl] + relidx[tile_rb[pl] + q];
+        return Z[addr];
+    }
+};
+
+// ---------------------------------------------------------------------------
+// k_rowexp: exponent of every row of A^{-1}_{C,C} (max over the whole row),
+// one 64-row tile per item, written per row-list position.  Separate from the
+// contraction so that it runs at full occupancy and so that every k-range of
+// a split contraction uses the same grid.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_rowexp(const ProbDesc *__restrict__ descs,
+                                                const Item *__restrict__ items, int nitems) {
+    __shared__ int64_t tile_cb[kTM], tile_rb[kTM];
+    __shared__ int rowE[kTM];
+    const int w = blockIdx.x;
+    if (w >= nitems) return;
+    const Item it = items[w];
+    const ProbDesc &P = descs[it.prob];
+    const int K = it.K;
+    const int s = P.super_ptr[K + 1] - P.super_ptr[K];
+    const int64_t ld = P.rowptr[K + 1] - P.rowptr[K];
+    const int c = (int)(ld - s);
+    const int p0 = it.tile * kTM;
+    const int64_t pos0 = P.rowptr[K] + s;
+    for (int e = threadIdx.x; e < kTM; e += blockDim.x) {
+        const int p = p0 + e;
+        tile_cb[e] = p < c ? P.colbase[pos0 + p] : 0;
+        tile_rb[e] = p < c ? P.relbase[pos0 + p] : 0;
+        rowE[e] = 0;
+    }
+    __syncthreads();
+    const Gather g{static_cast<const double *>(P.Z), P.colbase + pos0, P.relbase + pos0, P.relidx,
+                   tile_cb, tile_rb, p0, c};
+    const int pl = threadIdx.x % kTM, part = threadIdx.x / kTM;   // 4 threads per row
+    int E = 0;
+    if (p0 + pl < c) {
+        int q = part;
+        for (; q + 12 < c; q += 16) {
+            const double x0 = g(pl, q), x1 = g(pl, q + 4), x2 = g(pl, q + 8), x3 = g(pl, q + 12);
+            E = max(E, max(max(bexp(x0), bexp(x1)), max(bexp(x2), bexp(x3))));
+        }
+        for (; q < c; q += 4) E = max(E, bexp(g(pl, q)));
+    }
+    atomicMax(&rowE[pl], E);
+    __syncthreads();
+    for (int e = threadIdx.x; e < kTM; e += blockDim.x)
+        if (p0 + e < c) P.rowexp[pos0 + p0 + e] = rowE[e];
+}
+
+// ---------------------------------------------------------------------------
+// k_selinv_oz<TN>: one (K, row tile of 64, column tile of TN, k-range) item.
+// Items carry tile = (row_tile * ncol + col_tile) * nsplit + k_split and
+// ntiles = nsplit.  8 warps: warp w owns m-tile (w % 4) and n-tiles
+// (w / 4) + 2 t, t < TN/16.  The k loop is double buffered: the gather for
+// step + 1 is issued before the tensor-core work of step.  With nsplit > 1
+// the k-ranges of one row tile add their exact int64 sums into a global
+// buffer (integer atomics: order independent) and the last one to arrive
+// writes A^{-1}_{C,K} for the whole row tile.
 // ---------------------------------------------------------------------------
 template <int TN> struct OzShape {
     static constexpr int NT = TN / 16;   // n-tiles (of 8) per warp
@@ -133,15 +202,17 @@ template <int TN>
 __global__ void __launch_bounds__(kOzThreads, 1) k_selinv_oz(const ProbDesc *__restrict__ descs,
                                                              const Item *__restrict__ items, int nitems) {
     constexpr int NT = OzShape<TN>::NT;
+    constexpr int ABUF = kDig * kTM * kApad, BBUF = kDig * TN * kApad;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    // layout: A digits [7][64][kApad] bf16 | B digits [7][TN][kApad] bf16 |
+    // layout: A digits [2][7][64][kApad] bf16 | B digits [2][7][TN][kApad] bf16 |
     //         acc hi/lo [64][TN] int64 x 2 | row exponents [64] int
     uint16_t *As = reinterpret_cast<uint16_t *>(smem_raw);
-    uint16_t *Bs = As + kDig * kTM * kApad;
-    long long *Hi = reinterpret_cast<long long *>(Bs + kDig * TN * kApad);
+    uint16_t *Bs = As + 2 * ABUF;
+    long long *Hi = reinterpret_cast<long long *>(Bs + 2 * BBUF);
     long long *Lo = Hi + kTM * TN;
     int *rowE = reinterpret_cast<int *>(Lo + kTM * TN);
     __shared__ int64_t tile_cb[kTM], tile_rb[kTM];
+    __shared__ int s_last;
 
     const int w = blockIdx.x;
     if (w >= nitems) return;
@@ -154,77 +225,81 @@ __global__ void __launch_bounds__(kOzThreads, 1) k_selinv_oz(const ProbDesc *__r
     const int c = (int)(ld - s);
     const int c16 = (c + 15) & ~15;
     const int ncol = (s + TN - 1) / TN;
-    const int tile = it.tile / ncol;          // row tile
-    const int ct = it.tile % ncol;            // column tile
+    const int nsplit = it.ntiles;
+    const int ksp = it.tile % nsplit;
+    const int ct = (it.tile / nsplit) % ncol;
+    const int tile = it.tile / nsplit / ncol;
     const int p0 = tile * kTM, n0 = ct * TN;
     const int64_t pos0 = P.rowptr[K] + s;
-    const double *Z = static_cast<const double *>(P.Z);
-    const int64_t *pcb = P.colbase + pos0;
-    const int64_t *prb = P.relbase + pos0;
-    const int32_t *relidx = P.relidx;
+    const int nsteps = c16 / kOzK;
+    const int chunk = ((nsteps + nsplit - 1) / nsplit + kFlushSteps - 1) / kFlushSteps * kFlushSteps;
+    const int st0 = ksp * chunk;
+    const int st1 = st0 + chunk < nsteps ? st0 + chunk : nsteps;
 
     for (int e = threadIdx.x; e < kTM; e += kOzThreads) {
         const int p = p0 + e;
-        tile_cb[e] = p < c ? pcb[p] : 0;
-        tile_rb[e] = p < c ? prb[p] : 0;
-        rowE[e] = 0;
+        tile_cb[e] = p < c ? P.colbase[pos0 + p] : 0;
+        tile_rb[e] = p < c ? P.relbase[pos0 + p] : 0;
+        rowE[e] = p < c ? P.rowexp[pos0 + p] : 0;
     }
     for (int e = threadIdx.x; e < kTM * TN; e += kOzThreads) { Hi[e] = 0; Lo[e] = 0; }
     __syncthreads();
-
-    // gathered entry (p, q) of A^{-1}_{C,C}, stored at (max, min) by symmetry
-    auto gather = [&](int pl, int q) -> double {
-        const int p = p0 + pl;
-        if (p >= c || q >= c) return 0.0;
-        const int64_t addr = p >= q ? pcb[q] + relidx[prb[q] + p] : tile_cb[pl] + relidx[tile_rb[pl] + q];
-        return Z[addr];
-    };
-
-    // pass 1: row exponents (max over the whole row of the gathered block)
-    {
-        const int pl = threadIdx.x % kTM;       // 4 threads per row
-        const int part = threadIdx.x / kTM;
-        int E = 0;
-        if (p0 + pl < c)
-            for (int q = part; q < c; q += kOzThreads / kTM) E = max(E, bexp(gather(pl, q)));
-        atomicMax(&rowE[pl], E);
-    }
-    __syncthreads();
+    const Gather g{static_cast<const double *>(P.Z), P.colbase + pos0, P.relbase + pos0, P.relidx,
+                   tile_cb, tile_rb, p0, c};
 
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
     const int mt = warp % 4;                  // m-tile: rows mt*16 .. +15
     const int grp = lane / 4, qd = lane % 4;
+    // this thread's gather slots: row gl, k offsets gk, gk+1, gk+8, gk+9
+    const int gl = threadIdx.x % kTM, gk = (threadIdx.x / kTM) * 2;
     float acc[NT][kDig][4];
 #pragma unroll
     for (int t = 0; t < NT; t++)
 #pragma unroll
-        for (int g = 0; g < kDig; g++)
+        for (int gg = 0; gg < kDig; gg++)
 #pragma unroll
-            for (int r = 0; r < 4; r++) acc[t][g][r] = 0.f;
+            for (int r = 0; r < 4; r++) acc[t][gg][r] = 0.f;
 
     const uint16_t *Bg = P.lhs + P.lhs_off[K];
     const int64_t bplane = (int64_t)s * c16;
-    const int nsteps = c16 / kOzK;
-    for (int step = 0; step < nsteps; step++) {
+    double v0 = 0, v1 = 0, v2 = 0, v3 = 0;
+    if (st0 < st1) {
+        const int k0 = st0 * kOzK;
+        v0 = g(gl, k0 + gk); v1 = g(gl, k0 + gk + 1); v2 = g(gl, k0 + gk + 8); v3 = g(gl, k0 + gk + 9);
+    }
+    for (int step = st0; step < st1; step++) {
         const int k0 = step * kOzK;
-        __syncthreads();  // previous step's fragments consumed
+        const int buf = (step - st0) & 1;
+        uint16_t *Ab = As + buf * ABUF;
+        uint16_t *Bb = Bs + buf * BBUF;
         // B digits: plane i, column n0 + j, q = k0 .. k0 + 15 (two 16-byte halves)
         for (int e = threadIdx.x; e < kDig * TN * 2; e += kOzThreads) {
             const int half = e & 1, j = (e >> 1) % TN, i = (e >> 1) / TN;
-            uint16_t *dst = Bs + (i * TN + j) * kApad + half * 8;
+            uint16_t *dst = Bb + (i * TN + j) * kApad + half * 8;
             if (n0 + j < s) cp_async16(dst, Bg + i * bplane + (int64_t)(n0 + j) * c16 + k0 + half * 8);
             else *reinterpret_cast<uint4 *>(dst) = make_uint4(0, 0, 0, 0);
         }
-        // A digits: gather, cut, store (two adjacent k per thread -> bf16x2 words)
-        for (int e = threadIdx.x; e < kTM * (kOzK / 2); e += kOzThreads) {
-            const int pl = e % kTM, kk = (e / kTM) * 2;
+        // A digits of this step from the values gathered during the previous step
+        {
             int d0[kDig], d1[kDig];
-            digits7(gather(pl, k0 + kk), rowE[pl], d0);
-            digits7(gather(pl, k0 + kk + 1), rowE[pl], d1);
+            const int E = rowE[gl];
+            digits7(v0, E, d0);
+            digits7(v1, E, d1);
 #pragma unroll
             for (int i = 0; i < kDig; i++)
-                *reinterpret_cast<uint32_t *>(As + (i * kTM + pl) * kApad + kk) =
+                *reinterpret_cast<uint32_t *>(Ab + (i * kTM + gl) * kApad + gk) =
                     bf16_of_int(d0[i]) | (bf16_of_int(d1[i]) << 16);
+            digits7(v2, E, d0);
+            digits7(v3, E, d1);
+#pragma unroll
+            for (int i = 0; i < kDig; i++)
+                *reinterpret_cast<uint32_t *>(Ab + (i * kTM + gl) * kApad + gk + 8) =
+                    bf16_of_int(d0[i]) | (bf16_of_int(d1[i]) << 16);
+        }
+        // gather of the next step, in flight during this step's tensor-core work
+        if (step + 1 < st1) {
+            const int k1 = k0 + kOzK;
+            v0 = g(gl, k1 + gk); v1 = g(gl, k1 + gk + 1); v2 = g(gl, k1 + gk + 8); v3 = g(gl, k1 + gk + 9);
         }
         cp_async_wait_all();
         __syncthreads();
@@ -232,7 +307,7 @@ __global__ void __launch_bounds__(kOzThreads, 1) k_selinv_oz(const ProbDesc *__r
         uint32_t a[kDig][4];
 #pragma unroll
         for (int i = 0; i < kDig; i++) {
-            const uint16_t *base = As + (i * kTM + mt * 16) * kApad;
+            const uint16_t *base = Ab + (i * kTM + mt * 16) * kApad;
             a[i][0] = *reinterpret_cast<const uint32_t *>(base + grp * kApad + qd * 2);
             a[i][1] = *reinterpret_cast<const uint32_t *>(base + (grp + 8) * kApad + qd * 2);
             a[i][2] = *reinterpret_cast<const uint32_t *>(base + grp * kApad + qd * 2 + 8);
@@ -243,7 +318,7 @@ __global__ void __launch_bounds__(kOzThreads, 1) k_selinv_oz(const ProbDesc *__r
             const int nt = (warp / 4) + 2 * t;  // n-tile index (8 columns)
 #pragma unroll
             for (int j = 0; j < kDig; j++) {
-                const uint16_t *bb = Bs + (j * TN + nt * 8 + grp) * kApad;
+                const uint16_t *bb = Bb + (j * TN + nt * 8 + grp) * kApad;
                 const uint32_t b0 = *reinterpret_cast<const uint32_t *>(bb + qd * 2);
                 const uint32_t b1 = *reinterpret_cast<const uint32_t *>(bb + qd * 2 + 8);
 #pragma unroll
@@ -251,8 +326,9 @@ __global__ void __launch_bounds__(kOzThreads, 1) k_selinv_oz(const ProbDesc *__r
                     mma_bf16(acc[t][i + j], a[i][0], a[i][1], a[i][2], a[i][3], b0, b1);
             }
         }
-        // fold the exact fp32 group sums into the int64 accumulators
-        if ((step + 1) % kFlushSteps == 0 || step + 1 == nsteps) {
+        // fold the exact fp32 group sums into the int64 accumulators (each
+        // element has one owning thread: no synchronization needed)
+        if ((step - st0 + 1) % kFlushSteps == 0 || step + 1 == st1) {
 #pragma unroll
             for (int t = 0; t < NT; t++) {
                 const int nt = (warp / 4) + 2 * t;
@@ -260,35 +336,63 @@ __global__ void __launch_bounds__(kOzThreads, 1) k_selinv_oz(const ProbDesc *__r
                 for (int r = 0; r < 4; r++) {
                     const int row = mt * 16 + grp + (r >= 2 ? 8 : 0);
                     const int col = nt * 8 + qd * 2 + (r & 1);
-                    long long g[kDig];
+                    long long gq[kDig];
 #pragma unroll
-                    for (int q = 0; q < kDig; q++) { g[q] = (long long)__float2int_rn(acc[t][q][r]); acc[t][q][r] = 0.f; }
-                    Hi[row * TN + col] += (g[0] << 16) + (g[1] << 8) + g[2];
-                    Lo[row * TN + col] += (g[3] << 24) + (g[4] << 16) + (g[5] << 8) + g[6];
+                    for (int q = 0; q < kDig; q++) { gq[q] = (long long)__float2int_rn(acc[t][q][r]); acc[t][q][r] = 0.f; }
+                    Hi[row * TN + col] += (gq[0] << 16) + (gq[1] << 8) + gq[2];
+                    Lo[row * TN + col] += (gq[3] << 24) + (gq[4] << 16) + (gq[5] << 8) + gq[6];
                 }
             }
         }
     }
-    __shared__ int ymax[TN];
-    for (int e = threadIdx.x; e < TN; e += kOzThreads) ymax[e] = 0;
+    __shared__ int ymax[128];
+    for (int e = threadIdx.x; e < 128; e += kOzThreads) ymax[e] = 0;
     __syncthreads();
-    // Y = -(A^{-1}_{C,C} Lhat) in FP64: scale 2^(e_p + f_j - 14) (e = E - 1022)
     double *Zk = static_cast<double *>(P.Z) + P.panel_off[K];
-    for (int e = threadIdx.x; e < kTM * TN; e += kOzThreads) {
-        const int row = e % kTM, col = e / kTM;
-        const int p = p0 + row, j = n0 + col;
-        if (p >= c || j >= s) continue;
+    // Y = -(A^{-1}_{C,C} Lhat) in FP64: scale 2^(e_p + f_j - 14) (e = E - 1022)
+    auto emit = [&](int row, int j, long long hi, long long lo) {
         const int sc = (rowE[row] - 1022) + (P.colexp[fc + j] - 1022) - 14;
-        const double y = ldexp((double)Hi[row * TN + col], sc - 16) + ldexp((double)Lo[row * TN + col], sc - 48);
-        Zk[(int64_t)j * ld + s + p] = -y;
-        atomicMax(&ymax[col], bexp(y));
+        const double y = ldexp((double)hi, sc - 16) + ldexp((double)lo, sc - 48);
+        Zk[(int64_t)j * ld + s + p0 + row] = -y;
+        atomicMax(&ymax[j], bexp(y));
+    };
+    if (nsplit == 1) {
+        for (int e = threadIdx.x; e < kTM * TN; e += kOzThreads) {
+            const int row = e % kTM, col = e / kTM;
+            if (p0 + row < c && n0 + col < s) emit(row, n0 + col, Hi[row * TN + col], Lo[row * TN + col]);
+        }
+    } else {
+        long long *Yacc = P.yacc + 2 * P.panel_off[K];    // (hi, lo) per element of K's panel
+        for (int e = threadIdx.x; e < kTM * TN; e += kOzThreads) {
+            const int row = e % kTM, col = e / kTM;
+            if (p0 + row >= c || n0 + col >= s) continue;
+            unsigned long long *dst = reinterpret_cast<unsigned long long *>(Yacc + 2 * ((int64_t)(n0 + col) * ld + s + p0 + row));
+            if (Hi[row * TN + col]) atomicAdd(dst, (unsigned long long)Hi[row * TN + col]);
+            if (Lo[row * TN + col]) atomicAdd(dst + 1, (unsigned long long)Lo[row * TN + col]);
+        }
+        __threadfence();
+        __syncthreads();
+        int *ctr = P.tcount + P.tile_base[K] + tile;
+        if (threadIdx.x == 0) s_last = (atomicAdd(ctr, 1) == ncol * nsplit - 1);
+        __syncthreads();
+        if (!s_last) return;
+        __threadfence();
+        for (int e = threadIdx.x; e < kTM * s; e += kOzThreads) {
+            const int row = e % kTM, j = e / kTM;
+            if (p0 + row >= c) continue;
+            unsigned long long *q = reinterpret_cast<unsigned long long *>(Yacc + 2 * ((int64_t)j * ld + s + p0 + row));
+            const long long hi = (long long)__ldcg(q), lo = (long long)__ldcg(q + 1);
+            q[0] = 0ull;
+            q[1] = 0ull;
+            emit(row, j, hi, lo);
+        }
+        if (threadIdx.x == 0) *ctr = 0;
     }
     __syncthreads();
     // column exponents of A^{-1}_{C,K} over all row tiles (used by the diagonal block)
-    for (int col = threadIdx.x; col < TN; col += kOzThreads)
-        if (n0 + col < s && ymax[col] > 0) atomicMax(&P.colexpY[fc + n0 + col], ymax[col]);
+    for (int j = threadIdx.x; j < s; j += kOzThreads)
+        if (ymax[j] > 0) atomicMax(&P.colexpY[fc + j], ymax[j]);
 }
-
 
 // ---------------------------------------------------------------------------
 // k_diag_oz: contribution of one 64-row tile to the diagonal block,
@@ -474,7 +578,7 @@ cudaError_t launch_diag_oz(const ProbDesc *d, const Item *items, int n, cudaStre
 }
 
 template <int TN> constexpr size_t oz_smem_bytes() {
-    return sizeof(uint16_t) * (size_t)kDig * (kTM + TN) * kApad + 2 * sizeof(long long) * kTM * TN +
+    return sizeof(uint16_t) * 2 * (size_t)kDig * (kTM + TN) * kApad + 2 * sizeof(long long) * kTM * TN +
            sizeof(int) * kTM;
 }
 
@@ -484,6 +588,12 @@ cudaError_t configure_ozaki_kernels() {
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_selinv_oz<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)oz_smem_bytes<64>());
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_diag_oz, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)diag_oz_smem());
     return e;
+}
+
+cudaError_t launch_rowexp(const ProbDesc *d, const Item *items, int n, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    k_rowexp<<<n, 256, 0, st>>>(d, items, n);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_lhat_digits(const ProbDesc *d, const int2 *work, int nwork, cudaStream_t st) {

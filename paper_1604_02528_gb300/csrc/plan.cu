@@ -40,7 +40,9 @@ static void dfree(void *p) {
 
 void Workspace::release() {
     dfree(LD); dfree(Linv); dfree(partial); dfree(counter); dfree(done); dfree(work);
-    dfree(lhs); dfree(colexp); dfree(colexpY); dfree(dacc);
+    dfree(lhs); dfree(colexp); dfree(colexpY); dfree(dacc); dfree(rowexp); dfree(yacc); dfree(tcount);
+    rowexp = tcount = nullptr;
+    yacc = nullptr;
     lhs = nullptr;
     colexp = colexpY = nullptr;
     dacc = nullptr;
@@ -66,6 +68,14 @@ int Workspace::ensure(const PlanData &p, int dtype) {
     if (cudaMalloc((void **)&colexpY, sizeof(int) * (size_t)std::max(p.n, 1)) != cudaSuccess) return SELINV_ERR_OOM;
     if (cudaMalloc((void **)&dacc, sizeof(long long) * 2 * (size_t)std::max<int64_t>(p.linv_total, 1)) != cudaSuccess)
         return SELINV_ERR_OOM;
+    if (cudaMalloc((void **)&rowexp, sizeof(int) * (size_t)std::max<int64_t>(p.rowptr[p.ns], 1)) != cudaSuccess)
+        return SELINV_ERR_OOM;
+    const size_t ny = (dtype == SELINV_F64 && p.lhs_total > 0) ? 2 * (size_t)p.nnz : 2;
+    if (cudaMalloc((void **)&yacc, sizeof(long long) * ny) != cudaSuccess) return SELINV_ERR_OOM;
+    if (cudaMalloc((void **)&tcount, sizeof(int) * (size_t)std::max<int64_t>(p.tile_total, 1)) != cudaSuccess)
+        return SELINV_ERR_OOM;
+    cudaMemset(yacc, 0, sizeof(long long) * ny);
+    cudaMemset(tcount, 0, sizeof(int) * (size_t)std::max<int64_t>(p.tile_total, 1));
     cudaMemset(colexpY, 0, sizeof(int) * (size_t)std::max(p.n, 1));
     cudaMemset(dacc, 0, sizeof(long long) * 2 * (size_t)std::max<int64_t>(p.linv_total, 1));
     cudaMemset(counter, 0, sizeof(int) * (size_t)std::max(p.ns, 1));
@@ -189,6 +199,9 @@ static int build_plan(PlanData &p, int32_t n, int32_t ns, const int32_t *super_p
         p.lhs_off[K + 1] = p.lhs_off[K] + (s >= kOzMinS ? 7 * s * c16 : 0);
     }
     p.lhs_total = p.lhs_off[ns];
+    p.tile_base.assign(ns + 1, 0);
+    for (int32_t K = 0; K < ns; K++) p.tile_base[K + 1] = p.tile_base[K] + p.ntiles[K];
+    p.tile_total = p.tile_base[ns];
     p.part_max = 1;
     for (int l = 0; l < p.nlevels; l++) {
         int64_t acc = 0;
@@ -225,6 +238,7 @@ int ensure_device(PlanData &p) {
     if ((rc = upload(&p.d_linv_off, p.linv_off))) return rc;
     if ((rc = upload(&p.d_part_off, p.part_off))) return rc;
     if ((rc = upload(&p.d_lhs_off, p.lhs_off))) return rc;
+    if ((rc = upload(&p.d_tile_base, p.tile_base))) return rc;
     int *st = nullptr;
     if (cudaMalloc((void **)&st, sizeof(int)) != cudaSuccess) return SELINV_ERR_OOM;
     if (cudaMemset(st, 0, sizeof(int)) != cudaSuccess) return SELINV_ERR_CUDA;
@@ -235,8 +249,8 @@ int ensure_device(PlanData &p) {
 void PlanData::release_device() {
     dfree(d_super_ptr); dfree(d_sparent); dfree(d_rowptr); dfree(d_rows); dfree(d_panel_off);
     dfree(d_colbase); dfree(d_relbase); dfree(d_relidx); dfree(d_linv_off); dfree(d_part_off);
-    dfree(d_lhs_off); dfree(d_status);
-    d_lhs_off = nullptr;
+    dfree(d_lhs_off); dfree(d_tile_base); dfree(d_status);
+    d_lhs_off = d_tile_base = nullptr;
     d_super_ptr = d_sparent = d_rows = d_relidx = nullptr;
     d_rowptr = d_panel_off = d_colbase = d_relbase = d_linv_off = d_part_off = nullptr;
     d_status = nullptr;
@@ -270,6 +284,10 @@ ProbDesc make_desc(const PlanData &p, Workspace &w, int dtype, const void *L, co
     d.colexp = w.colexp;
     d.colexpY = w.colexpY;
     d.dacc = w.dacc;
+    d.rowexp = w.rowexp;
+    d.yacc = w.yacc;
+    d.tcount = w.tcount;
+    d.tile_base = p.d_tile_base;
     d.ns = p.ns;
     d.n = p.n;
     d.dtype = dtype;
@@ -345,15 +363,41 @@ int build_schedule(Schedule &S, const std::vector<const PlanData *> &plans,
         const PlanData &p = *plans[i];
         for (int t = 0; t < p.ntiles[K]; t++) S.h_items.push_back({i, K, t, p.ntiles[K]});
     };
-    // tensor-core items: (row tile, column tile of width tn) pairs; c == 0 has none
-    auto push_oz = [&](int i, int32_t K, int tn) {
+    // tensor-core items: (row tile, column tile of width tn, k-range) triples,
+    // ntiles field = number of k-ranges; c == 0 has none
+    auto oz_tn = [](int s) { return s <= 16 ? 16 : (s <= 32 ? 32 : 64); };
+    auto push_oz = [&](int i, int32_t K, int tn, int nsplit) {
         const PlanData &p = *plans[i];
         const int s = p.super_ptr[K + 1] - p.super_ptr[K];
         const int64_t c = p.rowptr[K + 1] - p.rowptr[K] - s;
         if (c == 0) return;
         const int ncol = (s + tn - 1) / tn;
         for (int t = 0; t < p.ntiles[K]; t++)
-            for (int ct = 0; ct < ncol; ct++) S.h_items.push_back({i, K, t * ncol + ct, p.ntiles[K]});
+            for (int ct = 0; ct < ncol; ct++)
+                for (int ks = 0; ks < nsplit; ks++) S.h_items.push_back({i, K, (t * ncol + ct) * nsplit + ks, nsplit});
+    };
+    // k-split of the contraction: enough CTAs for two per SM on narrow levels,
+    // each k-range at least 256 long
+    auto oz_split = [&](int i, int32_t K, int64_t level_ctas) {
+        const PlanData &p = *plans[i];
+        const int s = p.super_ptr[K + 1] - p.super_ptr[K];
+        const int64_t c = p.rowptr[K + 1] - p.rowptr[K] - s;
+        const int64_t want = (2 * 152 + level_ctas - 1) / std::max<int64_t>(level_ctas, 1);
+        const int64_t maxsplit = std::max<int64_t>(1, ((c + 15) / 16) / 16);
+        return (int)std::max<int64_t>(1, std::min(want, maxsplit));
+    };
+    auto oz_ctas = [&](int i, int32_t K) -> int64_t {
+        const PlanData &p = *plans[i];
+        const int s = p.super_ptr[K + 1] - p.super_ptr[K];
+        const int64_t c = p.rowptr[K + 1] - p.rowptr[K] - s;
+        if (c == 0) return 0;
+        return (int64_t)p.ntiles[K] * ((s + oz_tn(s) - 1) / oz_tn(s));
+    };
+    auto push_rowexp = [&](int i, int32_t K) {
+        const PlanData &p = *plans[i];
+        const int s = p.super_ptr[K + 1] - p.super_ptr[K];
+        if (p.rowptr[K + 1] - p.rowptr[K] == s) return;
+        for (int t = 0; t < p.ntiles[K]; t++) S.h_items.push_back({i, K, t, p.ntiles[K]});
     };
     if (mode == SELINV_SCHED_PLAIN) {
         // one launch per supernode, K = N..1, problem after problem
@@ -362,11 +406,17 @@ int build_schedule(Schedule &S, const std::vector<const PlanData *> &plans,
             for (int32_t K = p.ns - 1; K >= 0; K--) {
                 const int s = p.super_ptr[K + 1] - p.super_ptr[K];
                 if (oz_eligible(descs[i].dtype, s, p.opts.fast_contraction)) {
-                    const int tn = s <= 16 ? 16 : (s <= 32 ? 32 : 64);
+                    const int tn = oz_tn(s);
+                    const int64_t off0 = (int64_t)S.h_items.size();
+                    push_rowexp(i, K);
+                    if (S.h_items.size() > (size_t)off0)
+                        S.launches.push_back({KL_ROWEXP, descs[i].dtype, 0, off0,
+                                              (int)(S.h_items.size() - off0), p.level[K]});
                     const int64_t off = (int64_t)S.h_items.size();
-                    push_oz(i, K, tn);
-                    S.launches.push_back({KL_SELINV_OZ, descs[i].dtype, tn, off,
-                                          (int)(S.h_items.size() - off), p.level[K]});
+                    push_oz(i, K, tn, oz_split(i, K, oz_ctas(i, K)));
+                    if (S.h_items.size() > (size_t)off)
+                        S.launches.push_back({KL_SELINV_OZ, descs[i].dtype, tn, off,
+                                              (int)(S.h_items.size() - off), p.level[K]});
                     const int64_t off2 = (int64_t)S.h_items.size();
                     push_items(i, K);
                     S.launches.push_back({KL_DIAG, descs[i].dtype, bucket_of(s), off2,
@@ -395,12 +445,20 @@ int build_schedule(Schedule &S, const std::vector<const PlanData *> &plans,
                         oz.push_back({i, K});
                 }
             }
+            {
+                const int64_t off = (int64_t)S.h_items.size();
+                for (auto &ik : oz) push_rowexp(ik.first, ik.second);
+                const int cnt = (int)(S.h_items.size() - off);
+                if (cnt) S.launches.push_back({KL_ROWEXP, SELINV_F64, 0, off, cnt, l});
+            }
+            int64_t level_ctas = 0;
+            for (auto &ik : oz) level_ctas += oz_ctas(ik.first, ik.second);
             for (int tn : {64, 32, 16}) {
                 const int64_t off = (int64_t)S.h_items.size();
                 for (auto &ik : oz) {
                     const PlanData &p = *plans[ik.first];
                     const int s = p.super_ptr[ik.second + 1] - p.super_ptr[ik.second];
-                    if ((s <= 16 ? 16 : (s <= 32 ? 32 : 64)) == tn) push_oz(ik.first, ik.second, tn);
+                    if (oz_tn(s) == tn) push_oz(ik.first, ik.second, tn, oz_split(ik.first, ik.second, level_ctas));
                 }
                 const int cnt = (int)(S.h_items.size() - off);
                 if (cnt) S.launches.push_back({KL_SELINV_OZ, SELINV_F64, tn, off, cnt, l});
@@ -446,6 +504,7 @@ cudaError_t launch_one(const Schedule &S, const Launch &L, cudaStream_t st) {
     case KL_DIGITS: return launch_lhat_digits(S.d_descs, S.d_work + L.off, L.count, st);
     case KL_SELINV_OZ: return launch_selinv_oz(L.bucket, S.d_descs, S.d_items + L.off, L.count, st);
     case KL_DIAG: return launch_diag_oz(S.d_descs, S.d_items + L.off, L.count, st);
+    case KL_ROWEXP: return launch_rowexp(S.d_descs, S.d_items + L.off, L.count, st);
     default: return cudaErrorInvalidValue;
     }
 }
