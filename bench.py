@@ -276,7 +276,7 @@ def main():
             "k_diag": mult * float((2 * c_ * s_ * s_ * oz).sum()),
             "k_lhat": mult * float((c_ * s_ * s_).sum()),
             "k_linv": mult * float((s_ ** 3).sum()),
-            "k_lhat_digits": 0.0, "k_rowexp": 0.0}
+            "k_lhat_digits": 0.0}
     f_dom = f_of[name]
     achieved = f_dom / (kms[dom] * 1e-3) / 1e9 if kms[dom] > 0 else None
     traffic = ncu_traffic(name)

@@ -23,7 +23,7 @@ SELINV_SCHED_LEVEL = 1
 SELINV_SCHED_PERSISTENT = 2
 
 # kernel kinds reported by selinv_numeric_profile
-PROFILE_KINDS = ("k_linv", "k_lhat", "k_selinv", "k_lhat_digits", "k_selinv_oz", "k_diag", "k_rowexp")
+PROFILE_KINDS = ("k_linv", "k_lhat", "k_selinv", "k_lhat_digits", "k_selinv_oz", "k_diag")
 
 
 class SelinvError(RuntimeError):

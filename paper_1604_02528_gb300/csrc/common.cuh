@@ -96,7 +96,7 @@ struct ProbDesc {
     int *colexp;                // [n] biased exponent of each column of Lhat
     int *colexpY;               // [n] biased exponent of each column of A^{-1}_{C,K} (atomic max)
     long long *dacc;            // [2 * sum s^2] exact int64 sums of the diagonal-block products
-    int *rowexp;                // [rowptr[ns]] exponent of each row of A^{-1}_{C,C} per C position
+    int *colexpZ;               // [n] biased exponent of each whole column of the A^{-1} panels
     long long *yacc;            // [2 * nnz] exact int64 sums of split contractions, zero between calls
     int *tcount;                // [sum ntiles] arrivals per (K, row tile), zero between calls
     const int64_t *tile_base;   // [ns+1] prefix sums of the row tiles of each supernode

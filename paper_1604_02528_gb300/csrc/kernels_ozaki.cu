@@ -31,11 +31,6 @@ constexpr int kFlushSteps = 8;   // 128 k per exact fp32 chunk
 constexpr int kApad = 24;        // smem row stride (bf16) of a 16-wide k slab: conflict-free
 constexpr int kOzThreads = 256;
 
-// biased exponent of |x| (0 for zero / subnormal)
-__device__ __forceinline__ int bexp(double x) {
-    return (int)((__double_as_longlong(x) >> 52) & 0x7FF);
-}
-
 // bf16 bit pattern of a small integer v (|v| <= 128): exact via an fp32
 // round trip through the magic constant 1.5 * 2^23.
 __device__ __forceinline__ uint32_t bf16_of_int(int v) {
@@ -140,51 +135,6 @@ struct Gather {
 };
 
 // ---------------------------------------------------------------------------
-// k_rowexp: exponent of every row of A^{-1}_{C,C} (max over the whole row),
-// one 64-row tile per item, written per row-list position.  Separate from the
-// contraction so that it runs at full occupancy and so that every k-range of
-// a split contraction uses the same grid.
-// ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_rowexp(const ProbDesc *__restrict__ descs,
-                                                const Item *__restrict__ items, int nitems) {
-    __shared__ int64_t tile_cb[kTM], tile_rb[kTM];
-    __shared__ int rowE[kTM];
-    const int w = blockIdx.x;
-    if (w >= nitems) return;
-    const Item it = items[w];
-    const ProbDesc &P = descs[it.prob];
-    const int K = it.K;
-    const int s = P.super_ptr[K + 1] - P.super_ptr[K];
-    const int64_t ld = P.rowptr[K + 1] - P.rowptr[K];
-    const int c = (int)(ld - s);
-    const int p0 = it.tile * kTM;
-    const int64_t pos0 = P.rowptr[K] + s;
-    for (int e = threadIdx.x; e < kTM; e += blockDim.x) {
-        const int p = p0 + e;
-        tile_cb[e] = p < c ? P.colbase[pos0 + p] : 0;
-        tile_rb[e] = p < c ? P.relbase[pos0 + p] : 0;
-        rowE[e] = 0;
-    }
-    __syncthreads();
-    const Gather g{static_cast<const double *>(P.Z), P.colbase + pos0, P.relbase + pos0, P.relidx,
-                   tile_cb, tile_rb, p0, c};
-    const int pl = threadIdx.x % kTM, part = threadIdx.x / kTM;   // 4 threads per row
-    int E = 0;
-    if (p0 + pl < c) {
-        int q = part;
-        for (; q + 12 < c; q += 16) {
-            const double x0 = g(pl, q), x1 = g(pl, q + 4), x2 = g(pl, q + 8), x3 = g(pl, q + 12);
-            E = max(E, max(max(bexp(x0), bexp(x1)), max(bexp(x2), bexp(x3))));
-        }
-        for (; q < c; q += 4) E = max(E, bexp(g(pl, q)));
-    }
-    atomicMax(&rowE[pl], E);
-    __syncthreads();
-    for (int e = threadIdx.x; e < kTM; e += blockDim.x)
-        if (p0 + e < c) P.rowexp[pos0 + p0 + e] = rowE[e];
-}
-
-// ---------------------------------------------------------------------------
 // k_selinv_oz<TN>: one (K, row tile of 64, column tile of TN, k-range) item.
 // Items carry tile = (row_tile * ncol + col_tile) * nsplit + k_split and
 // ntiles = nsplit.  8 warps: warp w owns m-tile (w % 4) and n-tiles
@@ -236,13 +186,42 @@ __global__ void __launch_bounds__(kOzThreads, 1) k_selinv_oz(const ProbDesc *__r
     const int st0 = ksp * chunk;
     const int st1 = st0 + chunk < nsteps ? st0 + chunk : nsteps;
 
+    // Row exponents of the gathered block, bounded without gathering: entry
+    // (p, q) sits in the ancestor panel column C[min(p, q)], so row p is bounded
+    // by the largest whole-column exponent over C[0..p].
+    __shared__ int s_pre;
+    if (threadIdx.x == 0) s_pre = 0;
+    __syncthreads();
+    {
+        int e = 0;
+        for (int q = threadIdx.x; q < p0 && q < c; q += kOzThreads) e = max(e, P.colexpZ[P.rows[pos0 + q]]);
+        if (e) atomicMax(&s_pre, e);
+    }
     for (int e = threadIdx.x; e < kTM; e += kOzThreads) {
         const int p = p0 + e;
         tile_cb[e] = p < c ? P.colbase[pos0 + p] : 0;
         tile_rb[e] = p < c ? P.relbase[pos0 + p] : 0;
-        rowE[e] = p < c ? P.rowexp[pos0 + p] : 0;
+        rowE[e] = p < c ? P.colexpZ[P.rows[pos0 + p]] : 0;
     }
     for (int e = threadIdx.x; e < kTM * TN; e += kOzThreads) { Hi[e] = 0; Lo[e] = 0; }
+    __syncthreads();
+    if (threadIdx.x < 32) {                   // prefix max over the tile's 64 rows
+        int lo = max(rowE[threadIdx.x], s_pre), hi = rowE[threadIdx.x + 32];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int v = __shfl_up_sync(0xffffffffu, lo, o);
+            if ((int)threadIdx.x >= o) lo = max(lo, v);
+        }
+        const int carry = __shfl_sync(0xffffffffu, lo, 31);
+        hi = max(hi, carry);
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int v = __shfl_up_sync(0xffffffffu, hi, o);
+            if ((int)threadIdx.x >= o) hi = max(hi, v);
+        }
+        rowE[threadIdx.x] = lo;
+        rowE[threadIdx.x + 32] = hi;
+    }
     __syncthreads();
     const Gather g{static_cast<const double *>(P.Z), P.colbase + pos0, P.relbase + pos0, P.relidx,
                    tile_cb, tile_rb, p0, c};
@@ -303,28 +282,31 @@ __global__ void __launch_bounds__(kOzThreads, 1) k_selinv_oz(const ProbDesc *__r
         }
         cp_async_wait_all();
         __syncthreads();
-        // 28 digit pairs (i + j <= 6) per n-tile
-        uint32_t a[kDig][4];
-#pragma unroll
-        for (int i = 0; i < kDig; i++) {
-            const uint16_t *base = Ab + (i * kTM + mt * 16) * kApad;
-            a[i][0] = *reinterpret_cast<const uint32_t *>(base + grp * kApad + qd * 2);
-            a[i][1] = *reinterpret_cast<const uint32_t *>(base + (grp + 8) * kApad + qd * 2);
-            a[i][2] = *reinterpret_cast<const uint32_t *>(base + grp * kApad + qd * 2 + 8);
-            a[i][3] = *reinterpret_cast<const uint32_t *>(base + (grp + 8) * kApad + qd * 2 + 8);
-        }
+        // 28 digit pairs (i + j <= 6) per n-tile; consecutive mma target
+        // different accumulators (group i + j varies fastest, then the n-tile)
+        uint32_t b[NT][kDig][2];
 #pragma unroll
         for (int t = 0; t < NT; t++) {
             const int nt = (warp / 4) + 2 * t;  // n-tile index (8 columns)
 #pragma unroll
             for (int j = 0; j < kDig; j++) {
                 const uint16_t *bb = Bb + (j * TN + nt * 8 + grp) * kApad;
-                const uint32_t b0 = *reinterpret_cast<const uint32_t *>(bb + qd * 2);
-                const uint32_t b1 = *reinterpret_cast<const uint32_t *>(bb + qd * 2 + 8);
-#pragma unroll
-                for (int i = 0; i + j < kDig; i++)
-                    mma_bf16(acc[t][i + j], a[i][0], a[i][1], a[i][2], a[i][3], b0, b1);
+                b[t][j][0] = *reinterpret_cast<const uint32_t *>(bb + qd * 2);
+                b[t][j][1] = *reinterpret_cast<const uint32_t *>(bb + qd * 2 + 8);
             }
+        }
+#pragma unroll
+        for (int i = 0; i < kDig; i++) {
+            const uint16_t *base = Ab + (i * kTM + mt * 16) * kApad;
+            const uint32_t a0 = *reinterpret_cast<const uint32_t *>(base + grp * kApad + qd * 2);
+            const uint32_t a1 = *reinterpret_cast<const uint32_t *>(base + (grp + 8) * kApad + qd * 2);
+            const uint32_t a2 = *reinterpret_cast<const uint32_t *>(base + grp * kApad + qd * 2 + 8);
+            const uint32_t a3 = *reinterpret_cast<const uint32_t *>(base + (grp + 8) * kApad + qd * 2 + 8);
+#pragma unroll
+            for (int t = 0; t < NT; t++)
+#pragma unroll
+                for (int j = 0; i + j < kDig; j++)
+                    mma_bf16(acc[t][i + j], a0, a1, a2, a3, b[t][j][0], b[t][j][1]);
         }
         // fold the exact fp32 group sums into the int64 accumulators (each
         // element has one owning thread: no synchronization needed)
@@ -558,7 +540,12 @@ __global__ void __launch_bounds__(kOzThreads, 1) k_diag_oz(const ProbDesc *__res
     }
     __syncthreads();
     for (int e = threadIdx.x; e < 2 * s * s; e += kOzThreads) acc64[e] = 0;
-    for (int j = threadIdx.x; j < s; j += kOzThreads) P.colexpY[fc + j] = 0;
+    for (int j = threadIdx.x; j < s; j += kOzThreads) {  // exponent of the whole column
+        int ez = P.colexpY[fc + j];
+        for (int i = 0; i < s; i++) ez = max(ez, bexp(Zk[(int64_t)j * ld + i]));
+        P.colexpZ[fc + j] = ez;
+        P.colexpY[fc + j] = 0;
+    }
     if (threadIdx.x == 0) P.counter[K] = 0;
     if (P.done) {
         __threadfence();
@@ -588,12 +575,6 @@ cudaError_t configure_ozaki_kernels() {
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_selinv_oz<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)oz_smem_bytes<64>());
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_diag_oz, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)diag_oz_smem());
     return e;
-}
-
-cudaError_t launch_rowexp(const ProbDesc *d, const Item *items, int n, cudaStream_t st) {
-    if (n <= 0) return cudaSuccess;
-    k_rowexp<<<n, 256, 0, st>>>(d, items, n);
-    return cudaGetLastError();
 }
 
 cudaError_t launch_lhat_digits(const ProbDesc *d, const int2 *work, int nwork, cudaStream_t st) {

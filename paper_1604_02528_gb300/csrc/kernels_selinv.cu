@@ -222,36 +222,22 @@ __global__ void __launch_bounds__(kThreads) k_selinv(const ProbDesc *__restrict_
     }
     // write A^{-1}_{C,K} = -acc
     const int tx = threadIdx.x % S::TX, ty = threadIdx.x / S::TX;
+    __shared__ int ymax[TN];
+    for (int e = threadIdx.x; e < TN; e += kThreads) ymax[e] = 0;
+    __syncthreads();
 #pragma unroll
     for (int i = 0; i < S::MI; i++)
 #pragma unroll
         for (int j = 0; j < S::NJ; j++) {
             const int p = p0 + ty + S::TY * i, col = tx + S::TX * j;
-            if (p < c && col < s) Zk[(int64_t)col * ld + s + p] = neg(acc[i][j]);
+            if (p < c && col < s) {
+                Zk[(int64_t)col * ld + s + p] = neg(acc[i][j]);
+                atomicMax(&ymax[col], bexp(acc[i][j]));
+            }
         }
-    diag_block<T, TN>(P, it, K, s, ld, c, p0, pm, LDk, Zk, As, Bs);
-}
-
-// k_diag: the diagonal block of K from A^{-1}_{C,K} already in the output
-// (written by the tensor-core contraction), one row tile per item.
-template <typename T, int TN>
-__global__ void __launch_bounds__(kThreads) k_diag(const ProbDesc *__restrict__ descs,
-                                                   const Item *__restrict__ items, int nitems) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    T *As = reinterpret_cast<T *>(smem_raw);
-    T *Bs = As + smem_a_elems<T, TN>();
-    const int w = blockIdx.x;
-    if (w >= nitems) return;
-    const Item it = items[w];
-    const ProbDesc &P = descs[it.prob];
-    const int K = it.K;
-    const int s = P.super_ptr[K + 1] - P.super_ptr[K];
-    const int64_t ld = P.rowptr[K + 1] - P.rowptr[K];
-    const int c = (int)(ld - s);
-    const int p0 = it.tile * kTM;
-    const int pm = c - p0 < kTM ? c - p0 : kTM;
-    T *Zk = static_cast<T *>(P.Z) + P.panel_off[K];
-    const T *LDk = static_cast<const T *>(P.LD) + P.panel_off[K];
+    __syncthreads();
+    for (int e = threadIdx.x; e < s; e += kThreads)
+        if (ymax[e] > 0) atomicMax(&P.colexpY[P.super_ptr[K] + e], ymax[e]);
     diag_block<T, TN>(P, it, K, s, ld, c, p0, pm, LDk, Zk, As, Bs);
 }
 
@@ -278,8 +264,7 @@ static cudaError_t launch_items_t(int kernel, const ProbDesc *d, const Item *ite
     if (n <= 0) return cudaSuccess;
     constexpr size_t smem = smem_bytes<T, TN>();
     if (kernel == 0) k_lhat<T, TN><<<n, kThreads, smem, st>>>(d, items, n);
-    else if (kernel == 1) k_selinv<T, TN><<<n, kThreads, smem, st>>>(d, items, n);
-    else k_diag<T, TN><<<n, kThreads, smem, st>>>(d, items, n);
+    else k_selinv<T, TN><<<n, kThreads, smem, st>>>(d, items, n);
     return cudaGetLastError();
 }
 
@@ -289,8 +274,6 @@ static cudaError_t configure_t() {
     cudaError_t e = cudaFuncSetAttribute(k_lhat<T, TN>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_selinv<T, TN>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_diag<T, TN>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     return e;
 }
 
@@ -338,10 +321,5 @@ cudaError_t launch_selinv(int dtype, int bucket, const ProbDesc *d, const Item *
                                 : launch_items_dt<double>(1, bucket, d, items, n, st);
 }
 
-cudaError_t launch_diag(int dtype, int bucket, const ProbDesc *d, const Item *items, int n,
-                        cudaStream_t st) {
-    return dtype == SELINV_C128 ? launch_items_dt<zd>(2, bucket, d, items, n, st)
-                                : launch_items_dt<double>(2, bucket, d, items, n, st);
-}
 
 }  // namespace selinv

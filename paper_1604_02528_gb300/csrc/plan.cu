@@ -40,8 +40,8 @@ static void dfree(void *p) {
 
 void Workspace::release() {
     dfree(LD); dfree(Linv); dfree(partial); dfree(counter); dfree(done); dfree(work);
-    dfree(lhs); dfree(colexp); dfree(colexpY); dfree(dacc); dfree(rowexp); dfree(yacc); dfree(tcount);
-    rowexp = tcount = nullptr;
+    dfree(lhs); dfree(colexp); dfree(colexpY); dfree(dacc); dfree(colexpZ); dfree(yacc); dfree(tcount);
+    colexpZ = tcount = nullptr;
     yacc = nullptr;
     lhs = nullptr;
     colexp = colexpY = nullptr;
@@ -68,8 +68,8 @@ int Workspace::ensure(const PlanData &p, int dtype) {
     if (cudaMalloc((void **)&colexpY, sizeof(int) * (size_t)std::max(p.n, 1)) != cudaSuccess) return SELINV_ERR_OOM;
     if (cudaMalloc((void **)&dacc, sizeof(long long) * 2 * (size_t)std::max<int64_t>(p.linv_total, 1)) != cudaSuccess)
         return SELINV_ERR_OOM;
-    if (cudaMalloc((void **)&rowexp, sizeof(int) * (size_t)std::max<int64_t>(p.rowptr[p.ns], 1)) != cudaSuccess)
-        return SELINV_ERR_OOM;
+    if (cudaMalloc((void **)&colexpZ, sizeof(int) * (size_t)std::max(p.n, 1)) != cudaSuccess) return SELINV_ERR_OOM;
+    cudaMemset(colexpZ, 0, sizeof(int) * (size_t)std::max(p.n, 1));
     const size_t ny = (dtype == SELINV_F64 && p.lhs_total > 0) ? 2 * (size_t)p.nnz : 2;
     if (cudaMalloc((void **)&yacc, sizeof(long long) * ny) != cudaSuccess) return SELINV_ERR_OOM;
     if (cudaMalloc((void **)&tcount, sizeof(int) * (size_t)std::max<int64_t>(p.tile_total, 1)) != cudaSuccess)
@@ -284,7 +284,7 @@ ProbDesc make_desc(const PlanData &p, Workspace &w, int dtype, const void *L, co
     d.colexp = w.colexp;
     d.colexpY = w.colexpY;
     d.dacc = w.dacc;
-    d.rowexp = w.rowexp;
+    d.colexpZ = w.colexpZ;
     d.yacc = w.yacc;
     d.tcount = w.tcount;
     d.tile_base = p.d_tile_base;
@@ -393,12 +393,7 @@ int build_schedule(Schedule &S, const std::vector<const PlanData *> &plans,
         if (c == 0) return 0;
         return (int64_t)p.ntiles[K] * ((s + oz_tn(s) - 1) / oz_tn(s));
     };
-    auto push_rowexp = [&](int i, int32_t K) {
-        const PlanData &p = *plans[i];
-        const int s = p.super_ptr[K + 1] - p.super_ptr[K];
-        if (p.rowptr[K + 1] - p.rowptr[K] == s) return;
-        for (int t = 0; t < p.ntiles[K]; t++) S.h_items.push_back({i, K, t, p.ntiles[K]});
-    };
+
     if (mode == SELINV_SCHED_PLAIN) {
         // one launch per supernode, K = N..1, problem after problem
         for (int i = 0; i < np; i++) {
@@ -407,11 +402,6 @@ int build_schedule(Schedule &S, const std::vector<const PlanData *> &plans,
                 const int s = p.super_ptr[K + 1] - p.super_ptr[K];
                 if (oz_eligible(descs[i].dtype, s, p.opts.fast_contraction)) {
                     const int tn = oz_tn(s);
-                    const int64_t off0 = (int64_t)S.h_items.size();
-                    push_rowexp(i, K);
-                    if (S.h_items.size() > (size_t)off0)
-                        S.launches.push_back({KL_ROWEXP, descs[i].dtype, 0, off0,
-                                              (int)(S.h_items.size() - off0), p.level[K]});
                     const int64_t off = (int64_t)S.h_items.size();
                     push_oz(i, K, tn, oz_split(i, K, oz_ctas(i, K)));
                     if (S.h_items.size() > (size_t)off)
@@ -444,12 +434,6 @@ int build_schedule(Schedule &S, const std::vector<const PlanData *> &plans,
                     if (oz_eligible(descs[i].dtype, p.super_ptr[K + 1] - p.super_ptr[K], p.opts.fast_contraction))
                         oz.push_back({i, K});
                 }
-            }
-            {
-                const int64_t off = (int64_t)S.h_items.size();
-                for (auto &ik : oz) push_rowexp(ik.first, ik.second);
-                const int cnt = (int)(S.h_items.size() - off);
-                if (cnt) S.launches.push_back({KL_ROWEXP, SELINV_F64, 0, off, cnt, l});
             }
             int64_t level_ctas = 0;
             for (auto &ik : oz) level_ctas += oz_ctas(ik.first, ik.second);
@@ -504,7 +488,6 @@ cudaError_t launch_one(const Schedule &S, const Launch &L, cudaStream_t st) {
     case KL_DIGITS: return launch_lhat_digits(S.d_descs, S.d_work + L.off, L.count, st);
     case KL_SELINV_OZ: return launch_selinv_oz(L.bucket, S.d_descs, S.d_items + L.off, L.count, st);
     case KL_DIAG: return launch_diag_oz(S.d_descs, S.d_items + L.off, L.count, st);
-    case KL_ROWEXP: return launch_rowexp(S.d_descs, S.d_items + L.off, L.count, st);
     default: return cudaErrorInvalidValue;
     }
 }

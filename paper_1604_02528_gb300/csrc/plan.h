@@ -40,7 +40,7 @@ struct Workspace {
     int *colexp = nullptr;     // [n]
     int *colexpY = nullptr;    // [n], zero between calls
     long long *dacc = nullptr; // [2 * linv_total], zero between calls
-    int *rowexp = nullptr;     // [rowptr[ns]]
+    int *colexpZ = nullptr;    // [n], rewritten for every column in every call
     long long *yacc = nullptr; // [2 * nnz] (real problems with tensor-core supernodes), zero between calls
     int *tcount = nullptr;     // [tile_total], zero between calls
     size_t bytes_elem = 0;
@@ -49,8 +49,7 @@ struct Workspace {
 };
 
 // launch kinds
-enum { KL_LINV = 0, KL_LHAT = 1, KL_SELINV = 2, KL_DIGITS = 3, KL_SELINV_OZ = 4, KL_DIAG = 5, KL_ROWEXP = 6,
-       KL_NKINDS = 7 };
+enum { KL_LINV = 0, KL_LHAT = 1, KL_SELINV = 2, KL_DIGITS = 3, KL_SELINV_OZ = 4, KL_DIAG = 5, KL_NKINDS = 6 };
 
 // tensor-core (FP64-exact) contraction applies to real problems with s >= kOzMinS
 constexpr int kOzMinS = 16;

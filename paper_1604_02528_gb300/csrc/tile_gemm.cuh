@@ -11,6 +11,12 @@ namespace selinv {
 constexpr int kThreads = 256;
 constexpr int kTK = 16;
 
+// biased exponent of |x| (0 for zero / subnormal); complex: of the larger part
+__device__ __forceinline__ int bexp(double x) {
+    return (int)((__double_as_longlong(x) >> 52) & 0x7FF);
+}
+__device__ __forceinline__ int bexp(zd x) { return max(bexp(x.x), bexp(x.y)); }
+
 // loads that bypass L1 (data written by other CTAs of the same launch)
 __device__ inline double ldcg(const double *p) { return __ldcg(p); }
 __device__ inline zd ldcg(const zd *p) {
@@ -137,6 +143,15 @@ __device__ void diag_finish(const ProbDesc &P, int K, int s, int64_t ld, int nti
         }
         Zk[(int64_t)j * ld + i] = xij;
         Zk[(int64_t)i * ld + j] = xji;
+    }
+    __syncthreads();
+    // exponent of every whole column of K's panel (rows below: atomic max taken
+    // when they were written), for the row bounds of the descendants' gathers
+    for (int j = threadIdx.x; j < s; j += kThreads) {
+        int e = P.colexpY[P.super_ptr[K] + j];
+        for (int i = 0; i < s; i++) e = max(e, bexp(Zk[(int64_t)j * ld + i]));
+        P.colexpZ[P.super_ptr[K] + j] = e;
+        P.colexpY[P.super_ptr[K] + j] = 0;
     }
     if (threadIdx.x == 0) P.counter[K] = 0;
     if (P.done) {
