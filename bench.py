@@ -274,7 +274,9 @@ def main():
     f_of = {"k_selinv": mult * float(((2 * c_ * c_ * s_ + 2 * c_ * s_ * s_) * ~oz).sum()),
             "k_selinv_oz": mult * float((2 * c_ * c_ * s_ * oz).sum()),
             "k_diag": mult * float((2 * c_ * s_ * s_ * oz).sum()),
-            "k_lhat": mult * float((c_ * s_ * s_).sum()),
+            "k_lhat": mult * float((c_ * s_ * s_ * ~oz).sum()),
+            "k_lhat_oz": mult * float((c_ * s_ * s_ * oz).sum()),
+            "k_linv_digits": 0.0,
             "k_linv": mult * float((s_ ** 3).sum()),
             "k_lhat_digits": 0.0}
     f_dom = f_of[name]

@@ -23,7 +23,8 @@ SELINV_SCHED_LEVEL = 1
 SELINV_SCHED_PERSISTENT = 2
 
 # kernel kinds reported by selinv_numeric_profile
-PROFILE_KINDS = ("k_linv", "k_lhat", "k_selinv", "k_lhat_digits", "k_selinv_oz", "k_diag")
+PROFILE_KINDS = ("k_linv", "k_lhat", "k_selinv", "k_lhat_digits", "k_selinv_oz", "k_diag",
+                 "k_linv_digits", "k_lhat_oz")
 
 
 class SelinvError(RuntimeError):

@@ -97,6 +97,9 @@ struct ProbDesc {
     int *colexpY;               // [n] biased exponent of each column of A^{-1}_{C,K} (atomic max)
     long long *dacc;            // [2 * sum s^2] exact int64 sums of the diagonal-block products
     int *colexpZ;               // [n] biased exponent of each whole column of the A^{-1} panels
+    uint16_t *linvd;            // bf16 digit planes of L_KK^{-1} (tensor-core Lhat)
+    const int64_t *linvd_off;   // [ns+1]
+    int *linvexp;               // [n] column exponents of L_KK^{-1}
     long long *yacc;            // [2 * nnz] exact int64 sums of split contractions, zero between calls
     int *tcount;                // [sum ntiles] arrivals per (K, row tile), zero between calls
     const int64_t *tile_base;   // [ns+1] prefix sums of the row tiles of each supernode

@@ -377,6 +377,161 @@ __global__ void __launch_bounds__(kOzThreads, 1) k_selinv_oz(const ProbDesc *__r
 }
 
 // ---------------------------------------------------------------------------
+// k_linv_digits: bf16 digit planes of L_KK^{-1} for the tensor-core Lhat
+// product: per column j, exponent over k; layout plane[j][k], k padded to s16.
+// One warp per column.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_linv_digits(const ProbDesc *__restrict__ descs,
+                                                     const int2 *__restrict__ work, int nwork) {
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    const int w = blockIdx.x;
+    if (w >= nwork) return;
+    const ProbDesc &P = descs[work[w].x];
+    const int K = work[w].y >> 8;
+    const int jb = work[w].y & 0xFF;
+    const int fc = P.super_ptr[K];
+    const int s = P.super_ptr[K + 1] - fc;
+    const int s16 = (s + 15) & ~15;
+    const int j = jb * 8 + warp;
+    if (j >= s) return;
+    const double *X = static_cast<const double *>(P.Linv) + P.linv_off[K] + (int64_t)j * s;  // X(k, j)
+    int E = 0;
+    for (int k = lane; k < s; k += 32) E = max(E, bexp(X[k]));
+#pragma unroll
+    for (int o = 16; o; o >>= 1) E = max(E, __shfl_xor_sync(0xffffffffu, E, o));
+    if (lane == 0) P.linvexp[fc + j] = E;
+    uint16_t *pl = P.linvd + P.linvd_off[K];
+    const int64_t plane = (int64_t)s * s16;
+    for (int k = lane; k < s16; k += 32) {
+        int d[kDig];
+        if (k < s) digits7(X[k], E, d);
+        else {
+#pragma unroll
+            for (int i = 0; i < kDig; i++) d[i] = 0;
+        }
+#pragma unroll
+        for (int i = 0; i < kDig; i++) pl[i * plane + (int64_t)j * s16 + k] = (uint16_t)bf16_of_int(d[i]);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// k_lhat_oz<TN>: Lhat(p, j) = sum_k L(s + p, k) L_KK^{-1}(k, j) for one 64-row
+// tile and one column tile, on the bf16 tensor cores.  A = rows of L_{C,K}
+// (row exponent over its s entries), B = the digit planes of L_KK^{-1}.
+// k = s <= 128: a single exact fp32 chunk.
+// ---------------------------------------------------------------------------
+template <int TN>
+__global__ void __launch_bounds__(kOzThreads, 1) k_lhat_oz(const ProbDesc *__restrict__ descs,
+                                                           const Item *__restrict__ items, int nitems) {
+    constexpr int NT = TN / 16;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    uint16_t *As = reinterpret_cast<uint16_t *>(smem_raw);     // [7][64][kApad]
+    uint16_t *Bs = As + kDig * kTM * kApad;                    // [7][TN][kApad]
+    __shared__ int rowE[kTM];
+    const int w = blockIdx.x;
+    if (w >= nitems) return;
+    const Item it = items[w];
+    const ProbDesc &P = descs[it.prob];
+    const int K = it.K;
+    const int fc = P.super_ptr[K];
+    const int s = P.super_ptr[K + 1] - fc;
+    const int s16 = (s + 15) & ~15;
+    const int64_t ld = P.rowptr[K + 1] - P.rowptr[K];
+    const int c = (int)(ld - s);
+    const int ncol = (s + TN - 1) / TN;
+    const int tile = it.tile / ncol, ct = it.tile % ncol;
+    const int p0 = tile * kTM, n0 = ct * TN;
+    const double *Lc = static_cast<const double *>(P.L) + P.panel_off[K] + s;   // L_C(p, k) = Lc[k*ld + p]
+    for (int e = threadIdx.x; e < kTM; e += kOzThreads) rowE[e] = 0;
+    __syncthreads();
+    {
+        const int pl = threadIdx.x % kTM, part = threadIdx.x / kTM;
+        int E = 0;
+        if (p0 + pl < c)
+            for (int k = part; k < s; k += kOzThreads / kTM) E = max(E, bexp(Lc[(int64_t)k * ld + p0 + pl]));
+        atomicMax(&rowE[pl], E);
+    }
+    __syncthreads();
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    const int mt = warp % 4, grp = lane / 4, qd = lane % 4;
+    float acc[NT][kDig][4];
+#pragma unroll
+    for (int t = 0; t < NT; t++)
+#pragma unroll
+        for (int g = 0; g < kDig; g++)
+#pragma unroll
+            for (int r = 0; r < 4; r++) acc[t][g][r] = 0.f;
+    const uint16_t *Bg = P.linvd + P.linvd_off[K];
+    const int64_t bplane = (int64_t)s * s16;
+    for (int k0 = 0; k0 < s16; k0 += kOzK) {
+        __syncthreads();
+        for (int e = threadIdx.x; e < kDig * TN * 2; e += kOzThreads) {
+            const int half = e & 1, j = (e >> 1) % TN, i = (e >> 1) / TN;
+            uint16_t *dst = Bs + (i * TN + j) * kApad + half * 8;
+            if (n0 + j < s) cp_async16(dst, Bg + i * bplane + (int64_t)(n0 + j) * s16 + k0 + half * 8);
+            else *reinterpret_cast<uint4 *>(dst) = make_uint4(0, 0, 0, 0);
+        }
+        for (int e = threadIdx.x; e < kTM * (kOzK / 2); e += kOzThreads) {
+            const int pl = e % kTM, kk = (e / kTM) * 2;
+            const int p = p0 + pl, k = k0 + kk;
+            const double x0 = (p < c && k < s) ? Lc[(int64_t)k * ld + p] : 0.0;
+            const double x1 = (p < c && k + 1 < s) ? Lc[(int64_t)(k + 1) * ld + p] : 0.0;
+            int d0[kDig], d1[kDig];
+            digits7(x0, rowE[pl], d0);
+            digits7(x1, rowE[pl], d1);
+#pragma unroll
+            for (int i = 0; i < kDig; i++)
+                *reinterpret_cast<uint32_t *>(As + (i * kTM + pl) * kApad + kk) =
+                    bf16_of_int(d0[i]) | (bf16_of_int(d1[i]) << 16);
+        }
+        cp_async_wait_all();
+        __syncthreads();
+        uint32_t b[NT][kDig][2];
+#pragma unroll
+        for (int t = 0; t < NT; t++) {
+            const int nt = (warp / 4) + 2 * t;
+#pragma unroll
+            for (int j = 0; j < kDig; j++) {
+                const uint16_t *bb = Bs + (j * TN + nt * 8 + grp) * kApad;
+                b[t][j][0] = *reinterpret_cast<const uint32_t *>(bb + qd * 2);
+                b[t][j][1] = *reinterpret_cast<const uint32_t *>(bb + qd * 2 + 8);
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < kDig; i++) {
+            const uint16_t *base = As + (i * kTM + mt * 16) * kApad;
+            const uint32_t a0 = *reinterpret_cast<const uint32_t *>(base + grp * kApad + qd * 2);
+            const uint32_t a1 = *reinterpret_cast<const uint32_t *>(base + (grp + 8) * kApad + qd * 2);
+            const uint32_t a2 = *reinterpret_cast<const uint32_t *>(base + grp * kApad + qd * 2 + 8);
+            const uint32_t a3 = *reinterpret_cast<const uint32_t *>(base + (grp + 8) * kApad + qd * 2 + 8);
+#pragma unroll
+            for (int t = 0; t < NT; t++)
+#pragma unroll
+                for (int j = 0; i + j < kDig; j++)
+                    mma_bf16(acc[t][i + j], a0, a1, a2, a3, b[t][j][0], b[t][j][1]);
+        }
+    }
+    double *LD = static_cast<double *>(P.LD) + P.panel_off[K] + s;
+#pragma unroll
+    for (int t = 0; t < NT; t++) {
+        const int nt = (warp / 4) + 2 * t;
+#pragma unroll
+        for (int r = 0; r < 4; r++) {
+            const int row = mt * 16 + grp + (r >= 2 ? 8 : 0);
+            const int j = n0 + nt * 8 + qd * 2 + (r & 1);
+            if (p0 + row >= c || j >= s) continue;
+            long long gq[kDig];
+#pragma unroll
+            for (int q = 0; q < kDig; q++) gq[q] = (long long)__float2int_rn(acc[t][q][r]);
+            const long long hi = (gq[0] << 16) + (gq[1] << 8) + gq[2];
+            const long long lo = (gq[3] << 24) + (gq[4] << 16) + (gq[5] << 8) + gq[6];
+            const int sc = (rowE[row] - 1022) + (P.linvexp[fc + j] - 1022) - 14;
+            LD[(int64_t)j * ld + p0 + row] = ldexp((double)hi, sc - 16) + ldexp((double)lo, sc - 48);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
 // k_diag_oz: contribution of one 64-row tile to the diagonal block,
 // sum_{p in tile} Lhat(p, i) Y(p, j), Y = A^{-1}_{C,K} (already written), on
 // the bf16 tensor cores with the same exact digit scheme:
@@ -569,12 +724,33 @@ template <int TN> constexpr size_t oz_smem_bytes() {
            sizeof(int) * kTM;
 }
 
+template <int TN> constexpr size_t lhat_oz_smem() {
+    return sizeof(uint16_t) * (size_t)kDig * (kTM + TN) * kApad;
+}
+
 cudaError_t configure_ozaki_kernels() {
     cudaError_t e = cudaFuncSetAttribute(k_selinv_oz<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)oz_smem_bytes<16>());
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_selinv_oz<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)oz_smem_bytes<32>());
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_selinv_oz<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)oz_smem_bytes<64>());
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_diag_oz, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)diag_oz_smem());
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_lhat_oz<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lhat_oz_smem<16>());
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_lhat_oz<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lhat_oz_smem<32>());
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_lhat_oz<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lhat_oz_smem<64>());
     return e;
+}
+
+cudaError_t launch_linv_digits(const ProbDesc *d, const int2 *work, int nwork, cudaStream_t st) {
+    if (nwork <= 0) return cudaSuccess;
+    k_linv_digits<<<nwork, 256, 0, st>>>(d, work, nwork);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_lhat_oz(int tn, const ProbDesc *d, const Item *items, int n, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    if (tn == 16) k_lhat_oz<16><<<n, kOzThreads, lhat_oz_smem<16>(), st>>>(d, items, n);
+    else if (tn == 32) k_lhat_oz<32><<<n, kOzThreads, lhat_oz_smem<32>(), st>>>(d, items, n);
+    else k_lhat_oz<64><<<n, kOzThreads, lhat_oz_smem<64>(), st>>>(d, items, n);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_lhat_digits(const ProbDesc *d, const int2 *work, int nwork, cudaStream_t st) {

@@ -69,6 +69,9 @@ int Workspace::ensure(const PlanData &p, int dtype) {
     if (cudaMalloc((void **)&dacc, sizeof(long long) * 2 * (size_t)std::max<int64_t>(p.linv_total, 1)) != cudaSuccess)
         return SELINV_ERR_OOM;
     if (cudaMalloc((void **)&colexpZ, sizeof(int) * (size_t)std::max(p.n, 1)) != cudaSuccess) return SELINV_ERR_OOM;
+    if (cudaMalloc((void **)&linvexp, sizeof(int) * (size_t)std::max(p.n, 1)) != cudaSuccess) return SELINV_ERR_OOM;
+    if (cudaMalloc((void **)&linvd, sizeof(uint16_t) * (size_t)std::max<int64_t>(p.linvd_total, 8)) != cudaSuccess)
+        return SELINV_ERR_OOM;
     cudaMemset(colexpZ, 0, sizeof(int) * (size_t)std::max(p.n, 1));
     const size_t ny = (dtype == SELINV_F64 && p.lhs_total > 0) ? 2 * (size_t)p.nnz : 2;
     if (cudaMalloc((void **)&yacc, sizeof(long long) * ny) != cudaSuccess) return SELINV_ERR_OOM;
@@ -199,6 +202,12 @@ static int build_plan(PlanData &p, int32_t n, int32_t ns, const int32_t *super_p
         p.lhs_off[K + 1] = p.lhs_off[K] + (s >= kOzMinS ? 7 * s * c16 : 0);
     }
     p.lhs_total = p.lhs_off[ns];
+    p.linvd_off.assign(ns + 1, 0);
+    for (int32_t K = 0; K < ns; K++) {
+        const int64_t s = super_ptr[K + 1] - super_ptr[K];
+        p.linvd_off[K + 1] = p.linvd_off[K] + (s >= kOzMinS ? 7 * s * ((s + 15) / 16 * 16) : 0);
+    }
+    p.linvd_total = p.linvd_off[ns];
     p.tile_base.assign(ns + 1, 0);
     for (int32_t K = 0; K < ns; K++) p.tile_base[K + 1] = p.tile_base[K] + p.ntiles[K];
     p.tile_total = p.tile_base[ns];
@@ -239,6 +248,7 @@ int ensure_device(PlanData &p) {
     if ((rc = upload(&p.d_part_off, p.part_off))) return rc;
     if ((rc = upload(&p.d_lhs_off, p.lhs_off))) return rc;
     if ((rc = upload(&p.d_tile_base, p.tile_base))) return rc;
+    if ((rc = upload(&p.d_linvd_off, p.linvd_off))) return rc;
     int *st = nullptr;
     if (cudaMalloc((void **)&st, sizeof(int)) != cudaSuccess) return SELINV_ERR_OOM;
     if (cudaMemset(st, 0, sizeof(int)) != cudaSuccess) return SELINV_ERR_CUDA;
@@ -249,8 +259,8 @@ int ensure_device(PlanData &p) {
 void PlanData::release_device() {
     dfree(d_super_ptr); dfree(d_sparent); dfree(d_rowptr); dfree(d_rows); dfree(d_panel_off);
     dfree(d_colbase); dfree(d_relbase); dfree(d_relidx); dfree(d_linv_off); dfree(d_part_off);
-    dfree(d_lhs_off); dfree(d_tile_base); dfree(d_status);
-    d_lhs_off = d_tile_base = nullptr;
+    dfree(d_lhs_off); dfree(d_tile_base); dfree(d_linvd_off); dfree(d_status);
+    d_lhs_off = d_tile_base = d_linvd_off = nullptr;
     d_super_ptr = d_sparent = d_rows = d_relidx = nullptr;
     d_rowptr = d_panel_off = d_colbase = d_relbase = d_linv_off = d_part_off = nullptr;
     d_status = nullptr;
@@ -285,6 +295,9 @@ ProbDesc make_desc(const PlanData &p, Workspace &w, int dtype, const void *L, co
     d.colexpY = w.colexpY;
     d.dacc = w.dacc;
     d.colexpZ = w.colexpZ;
+    d.linvd = w.linvd;
+    d.linvd_off = p.d_linvd_off;
+    d.linvexp = w.linvexp;
     d.yacc = w.yacc;
     d.tcount = w.tcount;
     d.tile_base = p.d_tile_base;
@@ -326,7 +339,40 @@ int build_schedule(Schedule &S, const std::vector<const PlanData *> &plans,
             const int cnt = (int)(S.h_work.size() - off);
             if (cnt) S.launches.push_back({0, dt, large, off, cnt, -1});
         }
-    // 2) Lhat for every row tile (one launch per dtype and width class)
+    // 2) Lhat for every row tile: the tensor-core product for eligible
+    //    supernodes (after the digit planes of L_KK^{-1}), FP64 for the rest
+    {
+        const int64_t off = (int64_t)S.h_work.size();
+        for (int i = 0; i < np; i++) {
+            const PlanData &p = *plans[i];
+            for (int32_t K = 0; K < p.ns; K++) {
+                const int s = p.super_ptr[K + 1] - p.super_ptr[K];
+                const int64_t c = p.rowptr[K + 1] - p.rowptr[K] - s;
+                if (c == 0 || !oz_eligible(descs[i].dtype, s, p.opts.fast_contraction)) continue;
+                for (int jb = 0; jb < (s + 7) / 8; jb++) S.h_work.push_back(make_int2(i, (K << 8) | jb));
+            }
+        }
+        const int cnt = (int)(S.h_work.size() - off);
+        if (cnt) S.launches.push_back({KL_LINV_DIGITS, SELINV_F64, 0, off, cnt, -1});
+    }
+    for (int tn : {64, 32, 16}) {
+        const int64_t off = (int64_t)S.h_items.size();
+        for (int i = 0; i < np; i++) {
+            const PlanData &p = *plans[i];
+            for (int32_t K = 0; K < p.ns; K++) {
+                const int s = p.super_ptr[K + 1] - p.super_ptr[K];
+                const int64_t c = p.rowptr[K + 1] - p.rowptr[K] - s;
+                if (c == 0 || !oz_eligible(descs[i].dtype, s, p.opts.fast_contraction)) continue;
+                const int ktn = s <= 16 ? 16 : (s <= 32 ? 32 : 64);
+                if (ktn != tn) continue;
+                const int ncol = (s + tn - 1) / tn;
+                for (int t = 0; t < p.ntiles[K]; t++)
+                    for (int ct = 0; ct < ncol; ct++) S.h_items.push_back({i, K, t * ncol + ct, p.ntiles[K]});
+            }
+        }
+        const int cnt = (int)(S.h_items.size() - off);
+        if (cnt) S.launches.push_back({KL_LHAT_OZ, SELINV_F64, tn, off, cnt, -1});
+    }
     for (int dt = 0; dt < 2; dt++)
         for (int b = 0; b < kNumBuckets; b++) {
             const int64_t off = (int64_t)S.h_items.size();
@@ -336,7 +382,7 @@ int build_schedule(Schedule &S, const std::vector<const PlanData *> &plans,
                 for (int32_t K = 0; K < p.ns; K++) {
                     const int s = p.super_ptr[K + 1] - p.super_ptr[K];
                     const int64_t c = p.rowptr[K + 1] - p.rowptr[K] - s;
-                    if (c == 0 || bucket_of(s) != b) continue;
+                    if (c == 0 || bucket_of(s) != b || oz_eligible(dt, s, p.opts.fast_contraction)) continue;
                     for (int t = 0; t < p.ntiles[K]; t++) S.h_items.push_back({i, K, t, p.ntiles[K]});
                 }
             }
@@ -488,6 +534,8 @@ cudaError_t launch_one(const Schedule &S, const Launch &L, cudaStream_t st) {
     case KL_DIGITS: return launch_lhat_digits(S.d_descs, S.d_work + L.off, L.count, st);
     case KL_SELINV_OZ: return launch_selinv_oz(L.bucket, S.d_descs, S.d_items + L.off, L.count, st);
     case KL_DIAG: return launch_diag_oz(S.d_descs, S.d_items + L.off, L.count, st);
+    case KL_LINV_DIGITS: return launch_linv_digits(S.d_descs, S.d_work + L.off, L.count, st);
+    case KL_LHAT_OZ: return launch_lhat_oz(L.bucket, S.d_descs, S.d_items + L.off, L.count, st);
     default: return cudaErrorInvalidValue;
     }
 }

@@ -20,12 +20,14 @@ struct PlanData {
     std::vector<int64_t> colbase, relbase;  // per row-list position
     std::vector<int64_t> lhs_off;           // digit-plane offsets (tensor-core path)
     std::vector<int64_t> tile_base;         // prefix sums of the 64-row tiles of each supernode
+    std::vector<int64_t> linvd_off;         // digit planes of L_KK^{-1} (tensor-core path)
     int nlevels = 0;
-    int64_t nnz = 0, linv_total = 0, part_max = 1, lhs_total = 0, tile_total = 0;
+    int64_t nnz = 0, linv_total = 0, part_max = 1, lhs_total = 0, tile_total = 0, linvd_total = 0;
     // device copies
     int32_t *d_super_ptr = nullptr, *d_sparent = nullptr, *d_rows = nullptr, *d_relidx = nullptr;
     int64_t *d_rowptr = nullptr, *d_panel_off = nullptr, *d_colbase = nullptr, *d_relbase = nullptr;
     int64_t *d_linv_off = nullptr, *d_part_off = nullptr, *d_lhs_off = nullptr, *d_tile_base = nullptr;
+    int64_t *d_linvd_off = nullptr;
     int *d_status = nullptr;
     void release_device();
 };
@@ -41,6 +43,8 @@ struct Workspace {
     int *colexpY = nullptr;    // [n], zero between calls
     long long *dacc = nullptr; // [2 * linv_total], zero between calls
     int *colexpZ = nullptr;    // [n], rewritten for every column in every call
+    uint16_t *linvd = nullptr; // digit planes of L_KK^{-1}
+    int *linvexp = nullptr;    // [n]
     long long *yacc = nullptr; // [2 * nnz] (real problems with tensor-core supernodes), zero between calls
     int *tcount = nullptr;     // [tile_total], zero between calls
     size_t bytes_elem = 0;
@@ -49,7 +53,8 @@ struct Workspace {
 };
 
 // launch kinds
-enum { KL_LINV = 0, KL_LHAT = 1, KL_SELINV = 2, KL_DIGITS = 3, KL_SELINV_OZ = 4, KL_DIAG = 5, KL_NKINDS = 6 };
+enum { KL_LINV = 0, KL_LHAT = 1, KL_SELINV = 2, KL_DIGITS = 3, KL_SELINV_OZ = 4, KL_DIAG = 5, KL_LINV_DIGITS = 6,
+       KL_LHAT_OZ = 7, KL_NKINDS = 8 };
 
 // tensor-core (FP64-exact) contraction applies to real problems with s >= kOzMinS
 constexpr int kOzMinS = 16;
