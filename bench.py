@@ -46,6 +46,9 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--config", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-variants", action="store_true",
+                    help="skip the plain / batched / adjoint comparison runs")
+    ap.add_argument("--batch-poles", type=int, default=8)
     ap.add_argument("--schedule", type=int, default=1, help="0 plain, 1 level")
     ap.add_argument("--fast", type=int, default=1,
                     help="1: FP64-exact tensor-core contraction for s >= 16; 0: DFMA only")
@@ -135,6 +138,97 @@ def ncu_traffic(kernel: str):
         if len(parts) >= 3 and parts[0] == kernel and parts[1] == want:
             return float(parts[2])
     return None
+
+
+def time_calls(fn, stream, warmup, steps, flush=None):
+    """Mean device time (ms) of fn() on `stream` over `steps` calls after
+    `warmup`, CUDA events around each call, L2 flushed between calls."""
+    import torch
+    with torch.cuda.stream(stream):
+        for _ in range(warmup):
+            fn()
+    stream.synchronize()
+    tot = 0.0
+    for _ in range(steps):
+        if flush is not None:
+            with torch.cuda.stream(stream):
+                flush.fill_(1)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            a.record(stream)
+            fn()
+            b.record(stream)
+        stream.synchronize()
+        tot += a.elapsed_time(b)
+    return tot / steps
+
+
+def variant_plain(ctx, dt, L, D, Z, stream, flush, N):
+    """The plain per-supernode traversal (one launch chain per supernode)."""
+    o = N.selinv_default_opts()
+    o.schedule = N.SELINV_SCHED_PLAIN
+    N.selinv_plan_set_opts(ctx.plan, o)
+    ms = time_calls(lambda: N.selinv_numeric(ctx.plan, dt, L, D, Z, stream), stream, 1, 2, flush)
+    N.selinv_plan_set_opts(ctx.plan, N.selinv_default_opts())
+    return ms
+
+
+def variant_batched(dev, stream, flush, N, npoles, lap_scale):
+    """Pole shifts A - z_l I of the 40^3 pattern (complex) plus uneven
+    Laplacians (real): one batched call vs one call per problem."""
+    import torch
+    import synth
+    from paper_1604_02528_gb300.api import SelInvContext
+    base = synth.make_config(4)
+    e, eta = synth.pole_shifts()
+    idx = np.linspace(0, len(e) - 1, npoles).round().astype(int)
+    probs = [base.with_values(synth.problems.shifted_values(base, complex(e[l], eta[l]))) for l in idx]
+    probs += synth.batch_laplacians(lap_scale)
+    base_ctx = SelInvContext.from_problem(base)
+    ctxs, Ls, Ds, Zs, dts, flops = [], [], [], [], [], 0.0
+    for q in probs:
+        c = base_ctx if q.n == base.n and q.values.dtype.kind == "c" else SelInvContext.from_problem(q)
+        L, D = c.factor(torch.from_numpy(q.values).to(dev))
+        ctxs.append(c); Ls.append(L); Ds.append(D); Zs.append(torch.empty_like(L))
+        dts.append(N.SELINV_C128 if q.values.dtype.kind == "c" else N.SELINV_F64)
+        flops += c.stats(dts[-1])[0]
+    torch.cuda.synchronize()
+    plans = [c.plan for c in ctxs]
+    t_batched = time_calls(lambda: N.selinv_numeric_batched(plans, dts, Ls, Ds, Zs, stream), stream, 1, 2, flush)
+    def each():
+        for c, d, L, D, Z in zip(ctxs, dts, Ls, Ds, Zs):
+            N.selinv_numeric(c.plan, d, L, D, Z, stream)
+    t_each = time_calls(each, stream, 1, 2, flush)
+    return {"problems": f"{npoles} complex pole shifts of the 40^3 pattern + 8 Laplacians (side x {lap_scale})",
+            "batched_ms": round(t_batched, 3), "one_call_per_problem_ms": round(t_each, 3),
+            "speedup": round(t_each / t_batched, 3), "gflops": round(flops / t_batched / 1e6, 2)}
+
+
+def variant_adjoint(dev, stream, flush, N):
+    """Forward (selected inversion) vs reverse mode (selinv_adjoint +
+    selinv_factor_adjoint) on the 24^3 diffusion workload."""
+    import torch
+    import synth
+    from paper_1604_02528_gb300.api import SelInvContext
+    p = synth.make_config(5)
+    ctx = SelInvContext.from_problem(p)
+    L, D = ctx.factor(torch.from_numpy(p.values).to(dev))
+    Z = torch.empty_like(L)
+    N.selinv_numeric(ctx.plan, N.SELINV_F64, L, D, Z, stream)
+    stream.synchronize()
+    W = torch.randn(Z.shape, dtype=torch.float64, device=dev)
+    Lb, Db = torch.empty_like(L), torch.empty_like(D)
+    Ab = torch.empty(p.nnz_lower, dtype=torch.float64, device=dev)
+    t_fwd = time_calls(lambda: N.selinv_numeric(ctx.plan, N.SELINV_F64, L, D, Z, stream), stream, 2, 5, flush)
+    t_adj = time_calls(lambda: N.selinv_adjoint(ctx.plan, N.SELINV_F64, L, D, Z, W, Lb, Db, stream),
+                       stream, 2, 5, flush)
+    t_fadj = time_calls(lambda: N.selinv_factor_adjoint(ctx.plan, N.SELINV_F64, L, D, Lb, Db, Ab, stream),
+                        stream, 2, 5, flush)
+    F = ctx.stats(N.SELINV_F64)[0]
+    return {"workload": "3D diffusion 24^3 (N=13824), relaxed supernodes", "forward_ms": round(t_fwd, 3),
+            "selinv_adjoint_ms": round(t_adj, 3), "factor_adjoint_ms": round(t_fadj, 3),
+            "adjoint_over_forward": round((t_adj + t_fadj) / t_fwd, 3),
+            "forward_gflops": round(F / t_fwd / 1e6, 2)}
 
 
 def sample_kmin(sym, flops_target):
@@ -327,6 +421,14 @@ def main():
            "ms_per_step": round(1e3 * e2e_s, 3),
            "includes": "selinv_symbolic from host arrays + H2D + selinv_numeric + D2H"}
 
+    variants = None
+    if not args.no_variants:
+        variants = {"level_ms": round(ms_step, 3)}
+        variants["plain_ms"] = round(variant_plain(ctx, dt, L, D, Z, stream, flush, N), 3)
+        variants["level_over_plain_speedup"] = round(variants["plain_ms"] / ms_step, 3)
+        variants["batched"] = variant_batched(dev, stream, flush, N, args.batch_poles, 1.0)
+        variants["adjoint"] = variant_adjoint(dev, stream, flush, N)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         sym, Lo, Do = oracle_sample_setup(p)
@@ -349,7 +451,7 @@ def main():
                            "l2": "flushed between timed steps (256 MB write)",
                            "parallelism": "replicas" if world > 1 else "single GPU",
                            "fp64_frac": round(value / world / FP64_PEAK_GFLOPS, 4)},
-                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "variants": variants,
                 "gpu_launches": int(launches), "clocks": clocks}
         print(json.dumps(line), flush=True)
     if world > 1:
