@@ -43,6 +43,8 @@ struct AdjDesc {
     const int32_t *seg_K, *seg_start, *seg_end;
     const int64_t *dseg_ptr;
     const int32_t *dseg;
+    const int64_t *tseg_ptr;
+    const int4 *tseg;
     const int64_t *linv_off, *part_off;
     const double *L, *D, *Z, *LD, *Linv;
     double *Zb;       // working cotangent of A^{-1} (panels)
@@ -74,39 +76,25 @@ struct AdjData {
 
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) k_adj_pull(const AdjDesc *__restrict__ ad,
-                                                  const int2 *__restrict__ tiles, int ntiles) {
+                                                  const int2 *__restrict__ tiles, int ntiles, int64_t tile0) {
     const int w = blockIdx.x;
     if (w >= ntiles) return;
     const AdjDesc &A = *ad;
     const int J = tiles[w].x;
     const int64_t ldJ = A.rowptr[J + 1] - A.rowptr[J];
-    const int64_t r0 = (int64_t)tiles[w].y * 64;
-    const int64_t r1 = r0 + 64 < ldJ ? r0 + 64 : ldJ;
     const int fcJ = A.super_ptr[J];
     double *ZbJ = A.Zb + A.panel_off[J];
-    __shared__ int s_pa, s_pb;
-    for (int64_t di = A.dseg_ptr[J]; di < A.dseg_ptr[J + 1]; di++) {
-        const int t = A.dseg[di];
+    for (int64_t li = A.tseg_ptr[tile0 + w]; li < A.tseg_ptr[tile0 + w + 1]; li++) {
+        const int4 ts = A.tseg[li];
+        const int t = ts.x, pa = ts.y, np = ts.z - ts.y;
         const int K = A.seg_K[t];
-        const int st = A.seg_start[t], en = A.seg_end[t];
+        const int st = A.seg_start[t], nq = A.seg_end[t] - st;
         const int sK = A.super_ptr[K + 1] - A.super_ptr[K];
         const int64_t ldK = A.rowptr[K + 1] - A.rowptr[K];
-        const int cK = (int)(ldK - sK);
         const int32_t *rel = A.relidx + A.rel_ptr[t];
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            int a = st, b = cK;
-            while (a < b) { const int m = (a + b) / 2; if (rel[m - st] < r0) a = m + 1; else b = m; }
-            int c2 = a, d2 = cK;
-            while (c2 < d2) { const int m = (c2 + d2) / 2; if (rel[m - st] < r1) c2 = m + 1; else d2 = m; }
-            s_pa = a;
-            s_pb = c2;
-        }
-        __syncthreads();
-        const int pa = s_pa, np = s_pb - s_pa, nq = en - st;
-        if (np <= 0) continue;
         const double *Yb = A.YB + A.panel_off[K] + sK;   // Ybar(p, k) = Yb[k*ldK + p]
         const double *Lh = A.LD + A.panel_off[K] + sK;   // Lhat(p, k)
+        __syncthreads();  // the previous segment's updates to this tile are complete
         for (int e = threadIdx.x; e < np * nq; e += blockDim.x) {
             const int p = pa + e % np, q = st + e / np;
             if (p < q) continue;
@@ -654,6 +642,7 @@ static AdjDesc make_adesc(selinv_plan_s *plan, const double *L, const double *D,
     h.colbase = p.d_colbase; h.relbase = p.d_relbase; h.relidx = p.d_relidx; h.rel_ptr = f->d_rel_ptr;
     h.seg_K = f->d_seg_K; h.seg_start = f->d_seg_start; h.seg_end = f->d_seg_end;
     h.dseg_ptr = f->d_dseg_ptr; h.dseg = f->d_dseg;
+    h.tseg_ptr = f->d_tseg_ptr; h.tseg = f->d_tseg;
     h.linv_off = p.d_linv_off; h.part_off = p.d_part_off;
     h.L = L; h.D = D; h.Z = Z;
     h.LD = static_cast<const double *>(w.LD);
@@ -719,7 +708,7 @@ extern "C" int selinv_adjoint(selinv_plan plan, selinv_dtype dtype, const void *
     const int nl = p.nlevels;
     for (int li = 0; li < nl; li++) {  // deepest level first
         const int64_t t0 = a->tile_lptr[li], t1 = a->tile_lptr[li + 1];
-        if (t1 > t0) { k_adj_pull<<<(int)(t1 - t0), 256, 0, st>>>(a->d_desc, a->d_tiles + t0, (int)(t1 - t0)); note_launch(); }
+        if (t1 > t0) { k_adj_pull<<<(int)(t1 - t0), 256, 0, st>>>(a->d_desc, a->d_tiles + t0, (int)(t1 - t0), t0); note_launch(); }
         const int i0 = a->lvl_bucket_ptr[li * kNumBuckets], i1 = a->lvl_bucket_ptr[(li + 1) * kNumBuckets];
         if (i1 > i0) { k_adj_ybar<<<i1 - i0, 256, 0, st>>>(a->d_desc, a->d_items + i0, i1 - i0); note_launch(); }
         for (int b = 0; b < kNumBuckets; b++) {

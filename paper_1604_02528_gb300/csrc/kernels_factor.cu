@@ -36,44 +36,28 @@ __global__ void k_assemble(const int64_t *__restrict__ pos, const T *__restrict_
 
 template <typename T>
 __global__ void __launch_bounds__(256) k_fupdate(const FactorDesc *__restrict__ fd,
-                                                 const int2 *__restrict__ tiles, int ntiles) {
+                                                 const int2 *__restrict__ tiles, int ntiles, int64_t tile0) {
     const int w = blockIdx.x;
     if (w >= ntiles) return;
     const FactorDesc &F = *fd;
     const int J = tiles[w].x;
-    const int rt = tiles[w].y;
     const int64_t ldJ = F.rowptr[J + 1] - F.rowptr[J];
-    const int64_t r0 = (int64_t)rt * kFT;
-    const int64_t r1 = r0 + kFT < ldJ ? r0 + kFT : ldJ;
     const int fcJ = F.super_ptr[J];
     T *PJ = static_cast<T *>(F.L) + F.panel_off[J];
     const T *Lall = static_cast<const T *>(F.L);
     const T *Dall = static_cast<const T *>(F.D);
-    __shared__ int s_pa, s_pb;
-    for (int64_t di = F.dseg_ptr[J]; di < F.dseg_ptr[J + 1]; di++) {
-        const int t = F.dseg[di];
+    // (segment, p-range) pairs whose target rows fall in this tile, precomputed
+    for (int64_t li = F.tseg_ptr[tile0 + w]; li < F.tseg_ptr[tile0 + w + 1]; li++) {
+        const int4 ts = F.tseg[li];
+        const int t = ts.x, pa = ts.y, np = ts.z - ts.y;
         const int K = F.seg_K[t];
-        const int st = F.seg_start[t], en = F.seg_end[t];
+        const int st = F.seg_start[t], nq = F.seg_end[t] - st;
         const int sK = F.super_ptr[K + 1] - F.super_ptr[K];
         const int64_t ldK = F.rowptr[K + 1] - F.rowptr[K];
-        const int cK = (int)(ldK - sK);
         const int32_t *rel = F.relidx + F.rel_ptr[t];  // rel[p - st], p in [st, cK)
-        __syncthreads();  // previous descendant's updates are complete
-        if (threadIdx.x == 0) {
-            // p-range whose target rows fall in [r0, r1): rel is increasing
-            int a = st, b = cK;
-            while (a < b) { const int m = (a + b) / 2; if (rel[m - st] < r0) a = m + 1; else b = m; }
-            int c2 = a, d2 = cK;
-            while (c2 < d2) { const int m = (c2 + d2) / 2; if (rel[m - st] < r1) c2 = m + 1; else d2 = m; }
-            s_pa = a;
-            s_pb = c2;
-        }
-        __syncthreads();
-        const int pa = s_pa, pb = s_pb;
-        const int np = pb - pa, nq = en - st;
-        if (np <= 0) continue;
         const T *LK = Lall + F.panel_off[K];
         const T *DK = Dall + F.super_ptr[K];
+        __syncthreads();  // the previous segment's updates to this tile are complete
         for (int e = threadIdx.x; e < np * nq; e += blockDim.x) {
             const int p = pa + e % np, q = st + e / np;
             if (p < q) continue;  // strictly upper part of J's diagonal block: not stored
@@ -161,6 +145,7 @@ void factor_release(selinv_plan_s *plan) {
     auto fr = [](void *p) { if (p) cudaFree(p); };
     fr(f->d_a_pos); fr(f->d_seg_K); fr(f->d_seg_start); fr(f->d_seg_end); fr(f->d_seg_coloff);
     fr(f->d_dseg); fr(f->d_dseg_ptr); fr(f->d_rel_ptr); fr(f->d_tiles); fr(f->d_js); fr(f->d_desc);
+    fr(f->d_tseg_ptr); fr(f->d_tseg);
     adjoint_release(f->adj);
     delete f;
     plan->factor = nullptr;
@@ -212,6 +197,37 @@ int factor_tables(selinv_plan_s *plan) {
         f->tile_lptr.push_back((int64_t)f->h_tiles.size());
         f->j_lptr.push_back((int64_t)f->h_js.size());
     }
+    // per panel tile (launch order): the (segment, p-range) pairs that land in
+    // it, in ascending segment order (the fixed summation order)
+    {
+        std::vector<int64_t> tile_of(p.ns + 1, 0);      // index of (J, tile 0) in h_tiles
+        for (size_t w = 0; w < f->h_tiles.size(); w++)
+            if (f->h_tiles[w].y == 0) tile_of[f->h_tiles[w].x] = (int64_t)w;
+        std::vector<std::vector<int4>> lists(f->h_tiles.size());
+        for (int32_t J = 0; J < p.ns; J++)
+            for (int64_t di = dptr[J]; di < dptr[J + 1]; di++) {
+                const int32_t t = dseg[di];
+                const int32_t K = segK[t];
+                const int64_t cK = p.rowptr[K + 1] - p.rowptr[K] - (p.super_ptr[K + 1] - p.super_ptr[K]);
+                const int32_t *rel = p.relidx.data() + p.rel_ptr[t];
+                int64_t q = p.seg_start[t];
+                while (q < cK) {
+                    const int32_t tl = rel[q - p.seg_start[t]] / kFT;
+                    int64_t qe = q;
+                    while (qe < cK && rel[qe - p.seg_start[t]] / kFT == tl) qe++;
+                    lists[tile_of[J] + tl].push_back(make_int4(t, (int)q, (int)qe, 0));
+                    q = qe;
+                }
+            }
+        std::vector<int64_t> tptr(f->h_tiles.size() + 1, 0);
+        std::vector<int4> tseg;
+        for (size_t w = 0; w < lists.size(); w++) {
+            tseg.insert(tseg.end(), lists[w].begin(), lists[w].end());
+            tptr[w + 1] = (int64_t)tseg.size();
+        }
+        if ((rc = up(&f->d_tseg_ptr, tptr))) return rc;
+        if ((rc = up(&f->d_tseg, tseg))) return rc;
+    }
     if ((rc = up(&f->d_seg_K, segK))) return rc;
     if ((rc = up(&f->d_seg_start, p.seg_start))) return rc;
     if ((rc = up(&f->d_seg_end, segEnd))) return rc;
@@ -241,6 +257,8 @@ FactorDesc *factor_desc(selinv_plan_s *plan, void *L, void *D, cudaStream_t st) 
     h.seg_coloff = f->d_seg_coloff;
     h.dseg_ptr = f->d_dseg_ptr;
     h.dseg = f->d_dseg;
+    h.tseg_ptr = f->d_tseg_ptr;
+    h.tseg = f->d_tseg;
     h.L = L;
     h.D = D;
     h.status = p.d_status;
@@ -263,7 +281,7 @@ static int factor_t(selinv_plan_s *plan, const void *A, void *L, void *D, cudaSt
     for (int l = 0; l < nl; l++) {
         const int64_t t0 = f->tile_lptr[l], t1 = f->tile_lptr[l + 1];
         const int64_t j0 = f->j_lptr[l], j1 = f->j_lptr[l + 1];
-        if (t1 > t0) k_fupdate<T><<<(int)(t1 - t0), 256, 0, st>>>(fd, f->d_tiles + t0, (int)(t1 - t0));
+        if (t1 > t0) k_fupdate<T><<<(int)(t1 - t0), 256, 0, st>>>(fd, f->d_tiles + t0, (int)(t1 - t0), t0);
         if (j1 > j0) k_fdiag<T><<<(int)(j1 - j0), 256, 0, st>>>(fd, f->d_js + j0, (int)(j1 - j0));
         if (t1 > t0) k_ftrsm<T><<<(int)(t1 - t0), kFT, 0, st>>>(fd, f->d_tiles + t0, (int)(t1 - t0));
         note_launch(3);

@@ -113,6 +113,8 @@ struct FactorDesc {
     const int32_t *seg_K, *seg_start, *seg_end, *seg_coloff;
     const int64_t *dseg_ptr;  // [ns+1] segments owned by J (descendant updates)
     const int32_t *dseg;
+    const int64_t *tseg_ptr;  // per 64-row panel tile (launch order): its (segment, pa, pb) list
+    const int4 *tseg;
     void *L;
     void *D;
     int *status;
@@ -126,6 +128,8 @@ struct FactorData {
     int32_t *d_seg_K = nullptr, *d_seg_start = nullptr, *d_seg_end = nullptr, *d_seg_coloff = nullptr;
     int32_t *d_dseg = nullptr;
     int64_t *d_dseg_ptr = nullptr, *d_rel_ptr = nullptr;
+    int64_t *d_tseg_ptr = nullptr;
+    int4 *d_tseg = nullptr;
     // launch lists
     std::vector<int2> h_tiles;        // (J, row tile) per level, leaves first
     std::vector<int> h_js;            // J per level
