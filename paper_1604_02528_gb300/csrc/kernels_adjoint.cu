@@ -54,7 +54,7 @@ struct AdjDesc {
     double *Ab;       // Abar (panels)
     double *partial;  // split partials
     int *counter;     // per-supernode tile counters
-    double *fin;      // finisher scratch: 2 s*s per supernode at 2*linv_off
+    double *fin;      // per-supernode s x s scratch: 4 slots at 4*linv_off
 };
 
 struct AdjData {
@@ -67,8 +67,12 @@ struct AdjData {
     std::vector<int2> linv_work;
     std::vector<Item> lhat_items;
     std::vector<int> lhat_bptr;
+    std::vector<int2> gitems, citems;  // per level: (J, 32x32 tile) and (J, chunk | ntiles << 16)
+    std::vector<int> js;               // per level: supernodes
+    std::vector<int64_t> g_lptr, c_lptr, j_lptr;
     Item *d_items = nullptr, *d_lhat = nullptr;
-    int2 *d_tiles = nullptr, *d_linv = nullptr;
+    int2 *d_tiles = nullptr, *d_linv = nullptr, *d_gitems = nullptr, *d_citems = nullptr;
+    int *d_js = nullptr;
     double *YB = nullptr, *Zb = nullptr, *Lbw = nullptr, *Ab = nullptr, *fin = nullptr;
     AdjDesc *d_desc = nullptr;
     ProbDesc *d_pdesc = nullptr;
@@ -139,55 +143,8 @@ __global__ void __launch_bounds__(256) k_adj_ybar(const AdjDesc *__restrict__ ad
     }
 }
 
-// the selected-inversion finisher of J (whole CTA): Mbar, Lbar_JJ, Dbar_J
-__device__ void adj_finish_selinv(const AdjDesc &A, int J, int ntiles) {
-    const int fc = A.super_ptr[J];
-    const int s = A.super_ptr[J + 1] - fc;
-    const int64_t ld = A.rowptr[J + 1] - A.rowptr[J];
-    const int64_t ss = (int64_t)s * s;
-    const double *Li = A.Linv + A.linv_off[J];       // M(i, k) = Li[k*s + i]
-    const double *S = A.YB + A.panel_off[J];          // S(a, b) = S[b*ld + a]
-    const double *D = A.D + fc;
-    const double *part = A.partial + A.part_off[J];
-    double *Mb = A.fin + 2 * A.linv_off[J];
-    double *W = Mb + ss;
-    for (int e = threadIdx.x; e < s * s; e += blockDim.x) {
-        const int i = e % s, j = e / s;
-        double v = 0.0;
-        for (int t = 0; t < ntiles; t++) v += ldcg(part + t * ss + (int64_t)j * s + i);
-        double m = 0.0;
-        for (int k = 0; k < s; k++) m = fma(Li[(int64_t)k * s + i], S[(int64_t)j * ld + k], m);
-        Mb[(int64_t)j * s + i] = v + 2.0 * m / D[i];
-    }
-    __syncthreads();
-    for (int e = threadIdx.x; e < s * s; e += blockDim.x) {   // W = Mbar M^T
-        const int a = e % s, j = e / s;
-        double v = 0.0;
-        for (int b = 0; b < s; b++) v = fma(Mb[(int64_t)b * s + a], Li[(int64_t)b * s + j], v);
-        W[(int64_t)j * s + a] = v;
-    }
-    __syncthreads();
-    double *LbJ = A.Lb + A.panel_off[J];
-    for (int e = threadIdx.x; e < s * s; e += blockDim.x) {   // Lbar_JJ = -(M^T W), strictly lower
-        const int i = e % s, j = e / s;
-        double v = 0.0;
-        if (i > j)
-            for (int a = 0; a < s; a++) v = fma(-Li[(int64_t)i * s + a], W[(int64_t)j * s + a], v);
-        LbJ[(int64_t)j * ld + i] = v;
-    }
-    for (int k = threadIdx.x; k < s; k += blockDim.x) {       // Dbar_k = -(M S M^T)_kk / D_k^2
-        double v = 0.0;
-        for (int a = 0; a < s; a++) {
-            double r = 0.0;
-            for (int b = 0; b < s; b++) r = fma(S[(int64_t)b * ld + a], Li[(int64_t)b * s + k], r);
-            v = fma(Li[(int64_t)a * s + k], r, v);
-        }
-        A.Db[fc + k] = -v / (D[k] * D[k]);
-    }
-}
-
 // Lhat_bar rows of one tile (gather-GEMM with B = Ybar), the split Mbar term,
-// then Lbar_C rows; the last tile runs the finisher.
+// then Lbar_C rows.
 template <int TN>
 __global__ void __launch_bounds__(kThreads) k_adj_lhbar(const AdjDesc *__restrict__ ad,
                                                         const Item *__restrict__ items, int nitems) {
@@ -197,7 +154,6 @@ __global__ void __launch_bounds__(kThreads) k_adj_lhbar(const AdjDesc *__restric
     double *Bs = As + kTK * (kTM > TN ? kTM : TN);
     double *Rows = Bs + kTK * TN;                         // [TM][TN] Lhat_bar rows of the tile
     __shared__ int64_t tile_cb[kTM], tile_rb[kTM];
-    __shared__ int s_last;
     const int w = blockIdx.x;
     if (w >= nitems) return;
     const AdjDesc &A = *ad;
@@ -263,14 +219,6 @@ __global__ void __launch_bounds__(kThreads) k_adj_lhbar(const AdjDesc *__restric
         for (int k = 0; k < s; k++) v = fma(Rows[pl * TN + k], Li[(int64_t)k * s + j], v);
         Lb[(int64_t)j * ld + p0 + pl] = v;
     }
-    __threadfence();
-    __syncthreads();
-    if (threadIdx.x == 0) s_last = (atomicAdd(&A.counter[J], 1) == it.ntiles - 1);
-    __syncthreads();
-    if (!s_last) return;
-    __threadfence();
-    adj_finish_selinv(A, J, it.ntiles);
-    if (threadIdx.x == 0) A.counter[J] = 0;
 }
 
 // ---------------------------------------------------------------------------
@@ -349,106 +297,13 @@ __global__ void __launch_bounds__(kThreads) k_fadj_pull(const AdjDesc *__restric
     if (threadIdx.x == 0) A.counter[J] = 0;
 }
 
-// the factorization finisher of J: Ubar -> (Lbar_JJ, Dbar_J), then the reverse
-// of the dense LDL^T of the diagonal block -> Abar_JJ
-__device__ void adj_finish_factor(const AdjDesc &A, int J, int ntiles) {
-    const int fc = A.super_ptr[J];
-    const int s = A.super_ptr[J + 1] - fc;
-    const int64_t ld = A.rowptr[J + 1] - A.rowptr[J];
-    const int64_t ss = (int64_t)s * s;
-    const double *Li = A.Linv + A.linv_off[J];     // M(i, k) = Li[k*s + i]
-    const double *D = A.D + fc;
-    const double *L = A.L + A.panel_off[J];         // L(i, k) = L[k*ld + i], unit diagonal
-    double *LbJ = A.Lb + A.panel_off[J];
-    double *Db = A.Db + fc;
-    double *F1 = A.fin + 2 * A.linv_off[J];
-    double *F2 = F1 + ss;
-    const double *part = A.partial + A.part_off[J];
-    auto N = [&](int i, int j) { return Li[(int64_t)i * s + j] / D[j]; };  // N = M^T D^{-1}
-    for (int e = threadIdx.x; e < s * s; e += blockDim.x) {  // F1 = Nbar
-        double v = 0.0;
-        for (int t = 0; t < ntiles; t++) v += ldcg(part + t * ss + e);
-        F1[e] = v;
-    }
-    __syncthreads();
-    for (int e = threadIdx.x; e < s * s; e += blockDim.x) {  // F2 = Nbar N^T
-        const int i = e % s, j = e / s;
-        double v = 0.0;
-        for (int k = 0; k < s; k++) v = fma(F1[(int64_t)k * s + i], N(j, k), v);
-        F2[e] = v;
-    }
-    __syncthreads();
-    for (int e = threadIdx.x; e < s * s; e += blockDim.x) {  // F1 = Ubar = -N^T F2
-        const int i = e % s, j = e / s;
-        double v = 0.0;
-        for (int k = 0; k < s; k++) v = fma(-N(k, i), F2[(int64_t)j * s + k], v);
-        F1[e] = v;
-    }
-    __syncthreads();
-    // U = D L^T: Dbar_i += sum_{j>=i} Ubar(i,j) L(j,i); Lbar(j,i) += Ubar(i,j) D_i (j > i)
-    for (int i = threadIdx.x; i < s; i += blockDim.x) {
-        double v = F1[(int64_t)i * s + i];
-        for (int j = i + 1; j < s; j++) v = fma(F1[(int64_t)j * s + i], L[(int64_t)i * ld + j], v);
-        Db[i] += v;
-    }
-    for (int e = threadIdx.x; e < s * s; e += blockDim.x) {
-        const int j = e % s, i = e / s;
-        if (j > i) LbJ[(int64_t)i * ld + j] += F1[(int64_t)j * s + i] * D[i];
-    }
-    __syncthreads();
-    // reverse of the dense LDL^T of the block: Pbar starts as (Lbar strictly lower, Dbar on the diagonal)
-    double *Pb = F2;
-    for (int e = threadIdx.x; e < s * s; e += blockDim.x) {
-        const int i = e % s, k = e / s;
-        Pb[e] = i > k ? LbJ[(int64_t)k * ld + i] : (i == k ? Db[i] : 0.0);
-    }
-    __shared__ double red[kThreads];
-    for (int j = s - 1; j >= 0; j--) {
-        __syncthreads();
-        const double d = D[j];
-        // column j of Pbar from the updates of step j (they read columns > j only)
-        double dpart = 0.0;
-        for (int r = j + 1 + threadIdx.x; r < s; r += blockDim.x) {
-            double v = 0.0;
-            for (int k = j + 1; k <= r; k++) v = fma(Pb[(int64_t)k * s + r], L[(int64_t)j * ld + k], v);
-            for (int i = r; i < s; i++) v = fma(Pb[(int64_t)r * s + i], L[(int64_t)j * ld + i], v);
-            Pb[(int64_t)j * s + r] -= d * v;
-            // dbar -= sum_{k <= i} Pbar(i,k) L(i,j) L(k,j), grouped by k = r
-            double u = 0.0;
-            for (int i = r; i < s; i++) u = fma(Pb[(int64_t)r * s + i], L[(int64_t)j * ld + i], u);
-            dpart = fma(-u, L[(int64_t)j * ld + r], dpart);
-        }
-        __syncthreads();
-        // reverse of L(r, j) = a(r, j) / d
-        for (int r = j + 1 + threadIdx.x; r < s; r += blockDim.x) {
-            const double lb = Pb[(int64_t)j * s + r];
-            Pb[(int64_t)j * s + r] = lb / d;
-            dpart -= lb * L[(int64_t)j * ld + r] / d;
-        }
-        red[threadIdx.x] = dpart;
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            double t = 0.0;
-            for (int q = 0; q < (int)blockDim.x; q++) t += red[q];
-            Pb[(int64_t)j * s + j] += t;
-        }
-    }
-    __syncthreads();
-    double *AbJ = A.Ab + A.panel_off[J];
-    for (int e = threadIdx.x; e < s * s; e += blockDim.x) {
-        const int i = e % s, k = e / s;
-        AbJ[(int64_t)k * ld + i] = i >= k ? Pb[e] : 0.0;
-    }
-}
-
-// Abar_C rows = Lbar_C D^{-1} L_JJ^{-1}; split Nbar = A_C^T Lbar_C; finisher
+// Abar_C rows = Lbar_C D^{-1} L_JJ^{-1}; split Nbar = A_C^T Lbar_C
 template <int TN>
 __global__ void __launch_bounds__(kThreads) k_fadj_trsm(const AdjDesc *__restrict__ ad,
                                                         const Item *__restrict__ items, int nitems) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     double *Ar = reinterpret_cast<double *>(smem_raw);    // [TM][TN] A_C rows
     double *Br = Ar + kTM * TN;                            // [TM][TN] Lbar_C rows
-    __shared__ int s_last;
     const int w = blockIdx.x;
     if (w >= nitems) return;
     const AdjDesc &A = *ad;
@@ -497,20 +352,248 @@ __global__ void __launch_bounds__(kThreads) k_fadj_trsm(const AdjDesc *__restric
         for (int pl = 0; pl < pm; pl++) v = fma(Ar[pl * TN + i], Br[pl * TN + j], v);
         part[e] = v;
     }
-    __threadfence();
-    __syncthreads();
-    if (threadIdx.x == 0) s_last = (atomicAdd(&A.counter[J], 1) == it.ntiles - 1);
-    __syncthreads();
-    if (!s_last) return;
-    __threadfence();
-    adj_finish_factor(A, J, it.ntiles);
-    if (threadIdx.x == 0) A.counter[J] = 0;
 }
 
 __global__ void k_gather_vals(const int64_t *__restrict__ pos, const double *__restrict__ src,
                               int64_t n, double *__restrict__ dst) {
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
         dst[e] = src[pos[e]];
+}
+
+
+// ---------------------------------------------------------------------------
+// Per-supernode s x s steps of both adjoints, batched over a tree level and
+// spread over many CTAs.  Scratch per supernode J: 4 s x s slots at
+// 4 * linv_off[J] (selinv: Mbar, W, T1; factorization: Nbar, T2, N, U).
+// ---------------------------------------------------------------------------
+enum { OP_SEL_T1 = 0, OP_SEL_W, OP_SEL_LB, OP_FAC_T2, OP_FAC_U };
+
+// C (32 x 32 tile) of an s x s product; items (J, tile), tiles row-major over
+// ceil(s/32)^2.  256 threads, 2 x 2 outputs each, k staged 32 at a time.
+__global__ void __launch_bounds__(256) k_adj_gemm(const AdjDesc *__restrict__ ad, int op,
+                                                  const int2 *__restrict__ items, int nitems) {
+    __shared__ double As[32][33], Bs[32][33];
+    const int w = blockIdx.x;
+    if (w >= nitems) return;
+    const AdjDesc &A = *ad;
+    const int J = items[w].x;
+    const int s = A.super_ptr[J + 1] - A.super_ptr[J];
+    const int nt = (s + 31) / 32;
+    const int i0 = (items[w].y / nt) * 32, j0 = (items[w].y % nt) * 32;
+    const int64_t ss = (int64_t)s * s;
+    const int64_t ld = A.rowptr[J + 1] - A.rowptr[J];
+    const double *M = A.Linv + A.linv_off[J];             // M(i, k) = M[k*s + i]
+    double *F = A.fin + 4 * A.linv_off[J];
+    const double *S = A.YB + A.panel_off[J];              // S(k, j) = S[j*ld + k]
+    auto a_at = [&](int i, int k) -> double {
+        switch (op) {
+        case OP_SEL_T1: return M[(int64_t)k * s + i];                 // M
+        case OP_SEL_W: return F[(int64_t)k * s + i];                  // Mbar
+        case OP_SEL_LB: return M[(int64_t)i * s + k];                 // M^T
+        case OP_FAC_T2: return F[(int64_t)k * s + i];                 // Nbar
+        default: return F[2 * ss + (int64_t)i * s + k];               // N^T
+        }
+    };
+    auto b_at = [&](int k, int j) -> double {
+        switch (op) {
+        case OP_SEL_T1: return S[(int64_t)j * ld + k];                // S
+        case OP_SEL_W: return M[(int64_t)k * s + j];                  // M^T
+        case OP_SEL_LB: return F[ss + (int64_t)j * s + k];            // W
+        case OP_FAC_T2: return F[2 * ss + (int64_t)k * s + j];        // N^T
+        default: return F[ss + (int64_t)j * s + k];                   // T2
+        }
+    };
+    const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+    double acc[2][2] = {{0.0, 0.0}, {0.0, 0.0}};
+    for (int k0 = 0; k0 < s; k0 += 32) {
+        __syncthreads();
+        for (int e = threadIdx.x; e < 32 * 32; e += 256) {
+            const int r = e % 32, q = e / 32;
+            As[r][q] = (i0 + r < s && k0 + q < s) ? a_at(i0 + r, k0 + q) : 0.0;
+            Bs[q][r] = (k0 + q < s && j0 + r < s) ? b_at(k0 + q, j0 + r) : 0.0;
+        }
+        __syncthreads();
+#pragma unroll 8
+        for (int q = 0; q < 32; q++) {
+            const double a0 = As[ty][q], a1 = As[ty + 16][q];
+            const double b0 = Bs[q][tx], b1 = Bs[q][tx + 16];
+            acc[0][0] = fma(a0, b0, acc[0][0]);
+            acc[0][1] = fma(a0, b1, acc[0][1]);
+            acc[1][0] = fma(a1, b0, acc[1][0]);
+            acc[1][1] = fma(a1, b1, acc[1][1]);
+        }
+    }
+    double *Lb = A.Lb + A.panel_off[J];
+#pragma unroll
+    for (int u = 0; u < 2; u++)
+#pragma unroll
+        for (int v = 0; v < 2; v++) {
+            const int i = i0 + ty + 16 * u, j = j0 + tx + 16 * v;
+            if (i >= s || j >= s) continue;
+            const double x = acc[u][v];
+            switch (op) {
+            case OP_SEL_T1: F[2 * ss + (int64_t)j * s + i] = x; break;               // T1
+            case OP_SEL_W: F[ss + (int64_t)j * s + i] = x; break;                    // W
+            case OP_SEL_LB: Lb[(int64_t)j * ld + i] = i > j ? -x : 0.0; break;      // Lbar_JJ
+            case OP_FAC_T2: F[ss + (int64_t)j * s + i] = x; break;                   // T2
+            default: F[3 * ss + (int64_t)j * s + i] = -x; break;                     // Ubar
+            }
+        }
+}
+
+// selinv adjoint: Mbar = sum of the tile partials + 2 D^{-1} T1 (T1 = M S)
+__global__ void __launch_bounds__(256) k_adj_sel_mbar(const AdjDesc *__restrict__ ad,
+                                                      const int2 *__restrict__ items, int nitems) {
+    const int w = blockIdx.x;
+    if (w >= nitems) return;
+    const AdjDesc &A = *ad;
+    const int J = items[w].x, chunk = items[w].y;
+    const int fc = A.super_ptr[J];
+    const int s = A.super_ptr[J + 1] - fc;
+    const int ntiles = items[w].y >> 16;
+    const int64_t ss = (int64_t)s * s;
+    double *F = A.fin + 4 * A.linv_off[J];
+    const double *part = A.partial + A.part_off[J];
+    for (int64_t e = (int64_t)(chunk & 0xFFFF) * 4096 + threadIdx.x; e < ss && e < (int64_t)((chunk & 0xFFFF) + 1) * 4096;
+         e += blockDim.x) {
+        const int i = (int)(e % s);
+        double v = 0.0;
+        for (int t = 0; t < ntiles; t++) v += part[t * ss + e];
+        F[e] = v + 2.0 * F[2 * ss + e] / A.D[fc + i];
+    }
+}
+
+// selinv adjoint: Dbar_k = -(M S M^T)_kk / D_k^2 = -sum_a T1(k, a) M(k, a) / D_k^2
+__global__ void __launch_bounds__(128) k_adj_sel_dbar(const AdjDesc *__restrict__ ad,
+                                                      const int *__restrict__ js, int nj) {
+    const int w = blockIdx.x;
+    if (w >= nj) return;
+    const AdjDesc &A = *ad;
+    const int J = js[w];
+    const int fc = A.super_ptr[J];
+    const int s = A.super_ptr[J + 1] - fc;
+    const int64_t ss = (int64_t)s * s;
+    const double *M = A.Linv + A.linv_off[J];
+    const double *T1 = A.fin + 4 * A.linv_off[J] + 2 * ss;
+    for (int k = threadIdx.x; k < s; k += blockDim.x) {
+        double v = 0.0;
+        for (int a = 0; a < s; a++) v = fma(T1[(int64_t)a * s + k], M[(int64_t)a * s + k], v);
+        A.Db[fc + k] = -v / (A.D[fc + k] * A.D[fc + k]);
+    }
+}
+
+// factorization adjoint: Nbar = sum of the tile partials; N = M^T D^{-1}
+__global__ void __launch_bounds__(256) k_fadj_nbar(const AdjDesc *__restrict__ ad,
+                                                   const int2 *__restrict__ items, int nitems) {
+    const int w = blockIdx.x;
+    if (w >= nitems) return;
+    const AdjDesc &A = *ad;
+    const int J = items[w].x, chunk = items[w].y & 0xFFFF, ntiles = items[w].y >> 16;
+    const int fc = A.super_ptr[J];
+    const int s = A.super_ptr[J + 1] - fc;
+    const int64_t ss = (int64_t)s * s;
+    double *F = A.fin + 4 * A.linv_off[J];
+    const double *M = A.Linv + A.linv_off[J];
+    const double *part = A.partial + A.part_off[J];
+    for (int64_t e = (int64_t)chunk * 4096 + threadIdx.x; e < ss && e < (int64_t)(chunk + 1) * 4096; e += blockDim.x) {
+        const int i = (int)(e % s), j = (int)(e / s);
+        double v = 0.0;
+        for (int t = 0; t < ntiles; t++) v += part[t * ss + e];
+        F[e] = v;
+        F[2 * ss + e] = M[(int64_t)i * s + j] / A.D[fc + j];   // N(i, j) = M(j, i) / D_j
+    }
+}
+
+// factorization adjoint: U = D L^T gives Dbar_i += sum_{j>=i} Ubar(i,j) L(j,i),
+// Lbar(j,i) += Ubar(i,j) D_i (j > i)
+__global__ void __launch_bounds__(256) k_fadj_ubar(const AdjDesc *__restrict__ ad,
+                                                   const int *__restrict__ js, int nj) {
+    const int w = blockIdx.x;
+    if (w >= nj) return;
+    const AdjDesc &A = *ad;
+    const int J = js[w];
+    const int fc = A.super_ptr[J];
+    const int s = A.super_ptr[J + 1] - fc;
+    const int64_t ss = (int64_t)s * s;
+    const int64_t ld = A.rowptr[J + 1] - A.rowptr[J];
+    const double *U = A.fin + 4 * A.linv_off[J] + 3 * ss;
+    const double *L = A.L + A.panel_off[J];
+    double *Lb = A.Lb + A.panel_off[J];
+    for (int i = threadIdx.x; i < s; i += blockDim.x) {
+        double v = U[(int64_t)i * s + i];
+        for (int j = i + 1; j < s; j++) v = fma(U[(int64_t)j * s + i], L[(int64_t)i * ld + j], v);
+        A.Db[fc + i] += v;
+    }
+    for (int e = threadIdx.x; e < s * s; e += blockDim.x) {
+        const int j = e % s, i = e / s;
+        if (j > i) Lb[(int64_t)i * ld + j] += U[(int64_t)j * s + i] * A.D[fc + i];
+    }
+}
+
+// factorization adjoint: reverse of the dense LDL^T of J's diagonal block.
+// Pbar (s x s, lower) in shared memory starts as (Lbar strictly lower, Dbar on
+// the diagonal).  Step j (s-1 .. 0): for r > j,
+//   Pbar(r,j) -= D_j sum_{k>j} Pbar(max(r,k), min(r,k)) L(k,j)   (symmetric matvec)
+//   Dbar_j    -= sum_{j<k<=i} Pbar(i,k) L(i,j) L(k,j)
+// then the reverse of L(r,j) = a(r,j) / D_j.  One warp per row r, lanes over k.
+__global__ void __launch_bounds__(256) k_fadj_dense(const AdjDesc *__restrict__ ad,
+                                                    const int *__restrict__ js, int nj) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    double *Pb = reinterpret_cast<double *>(smem_raw);   // Pb(i, k) = Pb[k*s + i]
+    __shared__ double lj[128];
+    __shared__ double red[8];
+    const int w = blockIdx.x;
+    if (w >= nj) return;
+    const AdjDesc &A = *ad;
+    const int J = js[w];
+    const int fc = A.super_ptr[J];
+    const int s = A.super_ptr[J + 1] - fc;
+    const int64_t ld = A.rowptr[J + 1] - A.rowptr[J];
+    const double *L = A.L + A.panel_off[J];          // L(i, k) = L[k*ld + i]
+    double *Lb = A.Lb + A.panel_off[J];
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    for (int e = threadIdx.x; e < s * s; e += blockDim.x) {
+        const int i = e % s, k = e / s;
+        Pb[e] = i > k ? Lb[(int64_t)k * ld + i] : (i == k ? A.Db[fc + i] : 0.0);
+    }
+    for (int j = s - 1; j >= 0; j--) {
+        __syncthreads();
+        for (int k = threadIdx.x; k < s; k += blockDim.x) lj[k] = k > j ? L[(int64_t)j * ld + k] : 0.0;
+        __syncthreads();
+        const double d = A.D[fc + j];
+        double dpart = 0.0;
+        for (int r = j + 1 + warp; r < s; r += 8) {
+            double v = 0.0, u = 0.0;
+            for (int k = j + 1 + lane; k < s; k += 32) {
+                const double t = k >= r ? Pb[(int64_t)r * s + k] : Pb[(int64_t)k * s + r];
+                v = fma(t, lj[k], v);
+                if (k >= r) u = fma(t, lj[k], u);
+            }
+#pragma unroll
+            for (int o = 16; o; o >>= 1) {
+                v += __shfl_xor_sync(0xffffffffu, v, o);
+                u += __shfl_xor_sync(0xffffffffu, u, o);
+            }
+            if (lane == 0) {
+                const double pb = Pb[(int64_t)j * s + r] - d * v;   // then reverse the division
+                Pb[(int64_t)j * s + r] = pb / d;
+                dpart -= u * lj[r] + pb * lj[r] / d;
+            }
+        }
+        if (lane == 0) red[warp] = dpart;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double t = 0.0;
+            for (int q = 0; q < 8; q++) t += red[q];
+            Pb[(int64_t)j * s + j] += t;
+        }
+    }
+    __syncthreads();
+    double *Ab = A.Ab + A.panel_off[J];
+    for (int e = threadIdx.x; e < s * s; e += blockDim.x) {
+        const int i = e % s, k = e / s;
+        Ab[(int64_t)k * ld + i] = i >= k ? Pb[e] : 0.0;
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -533,11 +616,21 @@ static cudaError_t configure_adjoint() {
     CFG(k_fadj_trsm, 8, trsm_smem); CFG(k_fadj_trsm, 16, trsm_smem); CFG(k_fadj_trsm, 32, trsm_smem);
     CFG(k_fadj_trsm, 64, trsm_smem); CFG(k_fadj_trsm, 128, trsm_smem);
 #undef CFG
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_fadj_dense, cudaFuncAttributeMaxDynamicSharedMemorySize, 128 * 128 * 8);
     done = e == cudaSuccess;
     return e;
 }
 
 template <template <int> class KF> struct Dummy {};
+
+static void launch_level_gemm(AdjData *a, int op, int li, cudaStream_t st) {
+    const int64_t g0 = a->g_lptr[li], g1 = a->g_lptr[li + 1];
+    if (g1 > g0) {
+        k_adj_gemm<<<(int)(g1 - g0), 256, 0, st>>>(a->d_desc, op, a->d_gitems + g0, (int)(g1 - g0));
+        note_launch();
+    }
+}
 
 static void launch_bucket(int kind, int b, const AdjDesc *d, const Item *items, int n, cudaStream_t st) {
     if (n <= 0) return;
@@ -568,6 +661,7 @@ void adjoint_release(void *p) {
     if (!a) return;
     auto fr = [](void *q) { if (q) cudaFree(q); };
     fr(a->d_items); fr(a->d_lhat); fr(a->d_tiles); fr(a->d_linv);
+    fr(a->d_gitems); fr(a->d_citems); fr(a->d_js);
     fr(a->YB); fr(a->Zb); fr(a->Lbw); fr(a->Ab); fr(a->fin); fr(a->d_desc); fr(a->d_pdesc);
     delete a;
 }
@@ -601,6 +695,21 @@ static int adj_build(selinv_plan_s *plan) {
             a->lvl_bucket_ptr.push_back((int)a->items.size());
         }
     }
+    a->g_lptr.assign(1, 0); a->c_lptr.assign(1, 0); a->j_lptr.assign(1, 0);
+    for (int l = p.nlevels - 1; l >= 0; l--) {      // deepest first, like every list here
+        for (int64_t e = p.level_ptr[l]; e < p.level_ptr[l + 1]; e++) {
+            const int32_t J = p.level_list[e];
+            const int s = p.super_ptr[J + 1] - p.super_ptr[J];
+            const int nt = (s + 31) / 32;
+            for (int t = 0; t < nt * nt; t++) a->gitems.push_back(make_int2(J, t));
+            const int nch = (int)(((int64_t)s * s + 4095) / 4096);
+            for (int ch = 0; ch < nch; ch++) a->citems.push_back(make_int2(J, ch | (p.ntiles[J] << 16)));
+            a->js.push_back(J);
+        }
+        a->g_lptr.push_back((int64_t)a->gitems.size());
+        a->c_lptr.push_back((int64_t)a->citems.size());
+        a->j_lptr.push_back((int64_t)a->js.size());
+    }
     a->tiles = f->h_tiles;          // (J, 64-row tile), deepest level first
     a->tile_lptr = f->tile_lptr;
     for (int32_t K = 0; K < p.ns; K++) a->linv_work.push_back(make_int2(0, K));
@@ -615,14 +724,15 @@ static int adj_build(selinv_plan_s *plan) {
         a->lhat_bptr.push_back((int)a->lhat_items.size());
     }
     if ((rc = upl(&a->d_items, a->items)) || (rc = upl(&a->d_lhat, a->lhat_items)) ||
-        (rc = upl(&a->d_tiles, a->tiles)) || (rc = upl(&a->d_linv, a->linv_work))) {
+        (rc = upl(&a->d_tiles, a->tiles)) || (rc = upl(&a->d_linv, a->linv_work)) ||
+        (rc = upl(&a->d_gitems, a->gitems)) || (rc = upl(&a->d_citems, a->citems)) || (rc = upl(&a->d_js, a->js))) {
         adjoint_release(a);
         return rc;
     }
     const size_t nz = (size_t)std::max<int64_t>(p.nnz, 1);
     if (cudaMalloc((void **)&a->YB, 8 * nz) || cudaMalloc((void **)&a->Zb, 8 * nz) ||
         cudaMalloc((void **)&a->Lbw, 8 * nz) || cudaMalloc((void **)&a->Ab, 8 * nz) ||
-        cudaMalloc((void **)&a->fin, 8 * (size_t)std::max<int64_t>(2 * p.linv_total, 1)) ||
+        cudaMalloc((void **)&a->fin, 8 * (size_t)std::max<int64_t>(4 * p.linv_total, 1)) ||
         cudaMalloc((void **)&a->d_desc, sizeof(AdjDesc)) || cudaMalloc((void **)&a->d_pdesc, sizeof(ProbDesc))) {
         adjoint_release(a);
         return SELINV_ERR_OOM;
@@ -715,6 +825,14 @@ extern "C" int selinv_adjoint(selinv_plan plan, selinv_dtype dtype, const void *
             const int b0 = a->lvl_bucket_ptr[li * kNumBuckets + b], b1 = a->lvl_bucket_ptr[li * kNumBuckets + b + 1];
             launch_bucket(0, b, a->d_desc, a->d_items + b0, b1 - b0, st);
         }
+        // per-supernode s x s steps, batched over the level
+        const int64_t c0 = a->c_lptr[li], c1 = a->c_lptr[li + 1];
+        const int64_t j0 = a->j_lptr[li], j1 = a->j_lptr[li + 1];
+        launch_level_gemm(a, OP_SEL_T1, li, st);
+        if (c1 > c0) { k_adj_sel_mbar<<<(int)(c1 - c0), 256, 0, st>>>(a->d_desc, a->d_citems + c0, (int)(c1 - c0)); note_launch(); }
+        launch_level_gemm(a, OP_SEL_W, li, st);
+        launch_level_gemm(a, OP_SEL_LB, li, st);
+        if (j1 > j0) { k_adj_sel_dbar<<<(int)(j1 - j0), 128, 0, st>>>(a->d_desc, a->d_js + j0, (int)(j1 - j0)); note_launch(); }
     }
     return cudaGetLastError() == cudaSuccess ? SELINV_OK : SELINV_ERR_CUDA;
 }
@@ -750,6 +868,16 @@ extern "C" int selinv_factor_adjoint(selinv_plan plan, selinv_dtype dtype, const
         for (int b = 0; b < kNumBuckets; b++) {
             const int b0 = a->lvl_bucket_ptr[li * kNumBuckets + b], b1 = a->lvl_bucket_ptr[li * kNumBuckets + b + 1];
             launch_bucket(2, b, a->d_desc, a->d_items + b0, b1 - b0, st);
+        }
+        const int64_t c0 = a->c_lptr[li], c1 = a->c_lptr[li + 1];
+        const int64_t j0 = a->j_lptr[li], j1 = a->j_lptr[li + 1];
+        if (c1 > c0) { k_fadj_nbar<<<(int)(c1 - c0), 256, 0, st>>>(a->d_desc, a->d_citems + c0, (int)(c1 - c0)); note_launch(); }
+        launch_level_gemm(a, OP_FAC_T2, li, st);
+        launch_level_gemm(a, OP_FAC_U, li, st);
+        if (j1 > j0) {
+            k_fadj_ubar<<<(int)(j1 - j0), 256, 0, st>>>(a->d_desc, a->d_js + j0, (int)(j1 - j0));
+            k_fadj_dense<<<(int)(j1 - j0), 256, 128 * 128 * 8, st>>>(a->d_desc, a->d_js + j0, (int)(j1 - j0));
+            note_launch(2);
         }
     }
     if (f->nnzA > 0) {
