@@ -55,6 +55,23 @@ def parse():
     return ap.parse_args()
 
 
+def reduce_max_over_ranks(value: float) -> float:
+    """Max of `value` over all ranks (one process per GPU; replicas only, so
+    this timing reduction is the only cross-rank communication)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(value)
+    t = torch.tensor([float(value)], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank: float, world: int, max_ms: float) -> float:
+    """Whole-job throughput: the units all ranks processed / the slowest rank's time."""
+    return world * units_per_rank / (max_ms * 1e-3)
+
+
 def dist_info():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -345,14 +362,9 @@ def main():
     torch.cuda.synchronize()
     launches = N.selinv_launch_count() - launches0
     times = [a.elapsed_time(b) for a, b in ev]
-    tot_ms = sum(times)
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([tot_ms], dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        tot_ms = float(t.item())
+    tot_ms = reduce_max_over_ranks(sum(times))
     ms_step = tot_ms / args.steps
-    value = world * F / (ms_step * 1e-3) / 1e9
+    value = whole_job_rate(F, world, ms_step) / 1e9
 
     # roofline of the dominant kernel, timed live with CUDA events per launch
     kms, kcnt = N.selinv_numeric_profile(ctx.plan, dt, L, D, Z, stream)

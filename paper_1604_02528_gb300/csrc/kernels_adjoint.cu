@@ -566,7 +566,7 @@ __global__ void __launch_bounds__(256) k_fadj_dense(const AdjDesc *__restrict__ 
             double v = 0.0, u = 0.0;
             for (int k = j + 1 + lane; k < s; k += 32) {
                 const double t = k >= r ? Pb[(int64_t)r * s + k] : Pb[(int64_t)k * s + r];
-                v = fma(t, lj[k], v);
+                v = fma(k == r ? 2.0 * t : t, lj[k], v);   // the diagonal pair enters twice
                 if (k >= r) u = fma(t, lj[k], u);
             }
 #pragma unroll
