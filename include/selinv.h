@@ -67,15 +67,20 @@ typedef enum { SELINV_F64 = 0, SELINV_C128 = 1 } selinv_dtype;
 typedef enum {
     SELINV_SCHED_PLAIN = 0,      /* one launch chain per supernode, K = N..1            */
     SELINV_SCHED_LEVEL = 1,      /* one grouped launch per elimination-tree level        */
-    SELINV_SCHED_PERSISTENT = 2  /* one persistent launch, per-supernode completion flags */
+    SELINV_SCHED_PERSISTENT = 2  /* one persistent launch, per-supernode completion flags;
+                                    its traversal runs the FP64 / complex DFMA kernel
+                                    whatever fast_contraction says                     */
 } selinv_schedule;
 
 typedef struct {
     int symmetrize;        /* 1: A^{-1}_KK <- (X + X^T)/2 (Sec. II-C); default 1        */
     int schedule;          /* selinv_schedule; default SELINV_SCHED_LEVEL               */
     int autotune;          /* 1: pick kernel variants per size class by timing; default 0 */
-    int debug_checks;      /* 1: scan inputs for non-finite values; default 0           */
-    long long spin_limit;  /* iteration cap of every device spin-wait; default 1<<26     */
+    int debug_checks;      /* bit 0: scan inputs for non-finite values; bit 1: the
+                              persistent schedule waits on a flag that is never set,
+                              so every wait runs out (tests the timeout path); default 0 */
+    long long spin_limit;  /* polls (about 256 ns each) of every device spin-wait before
+                              it gives up and latches SELINV_ERR_TIMEOUT; default 1<<22 */
     int use_graph;         /* 1: capture the level schedule in a CUDA graph; default 1  */
     int fast_contraction;  /* 1: large contractions run FP64-exact on bf16 tensor cores
                               (error-free slicing, FP64 accumulation); 0: DFMA only.
@@ -211,9 +216,15 @@ int selinv_factor_adjoint(selinv_plan plan, selinv_dtype dtype, const void *L_de
 
 /* Runs selinv_numeric once without graph capture, timing every kernel
  * launch with CUDA events on the stream, and synchronizes.  kernel_ms[k] and
- * kernel_launches[k] (k = 0: L_KK^{-1} / Dinv, 1: Lhat, 2: the fused
- * gather-GEMM + diagonal block) receive the summed device time in ms and the
- * launch count of each kernel kind.  For measurement only. */
+ * kernel_launches[k] (arrays of SELINV_PROFILE_KINDS entries) receive the
+ * summed device time in ms and the launch count of each kernel kind:
+ *   0 L_KK^{-1} and Dinv (DFMA)        1 Lhat (DFMA)
+ *   2 gather-GEMM + diagonal (DFMA)    3 digit planes of Lhat
+ *   4 gather-GEMM on tensor cores      5 diagonal block after it
+ *   6 digit planes of L_KK^{-1}        7 Lhat on tensor cores
+ *   8 the persistent traversal
+ * For measurement only. */
+#define SELINV_PROFILE_KINDS 9
 int selinv_numeric_profile(selinv_plan plan, selinv_dtype dtype, const void *L_dev,
                            const void *D_dev, void *Ainv_dev, void *cuda_stream, double *kernel_ms,
                            int64_t *kernel_launches);

@@ -22,9 +22,20 @@ SELINV_SCHED_PLAIN = 0
 SELINV_SCHED_LEVEL = 1
 SELINV_SCHED_PERSISTENT = 2
 
+SELINV_OK = 0
+SELINV_ERR_INVALID_ARG = -1
+SELINV_ERR_BAD_ETREE = -2
+SELINV_ERR_BAD_PATTERN = -3
+SELINV_ERR_ZERO_PIVOT = -4
+SELINV_ERR_NONFINITE = -5
+SELINV_ERR_OOM = -6
+SELINV_ERR_CUDA = -7
+SELINV_ERR_TIMEOUT = -8
+SELINV_ERR_UNSUPPORTED = -9
+
 # kernel kinds reported by selinv_numeric_profile
 PROFILE_KINDS = ("k_linv", "k_lhat", "k_selinv", "k_lhat_digits", "k_selinv_oz", "k_diag",
-                 "k_linv_digits", "k_lhat_oz")
+                 "k_linv_digits", "k_lhat_oz", "k_selinv_persist")
 
 
 class SelinvError(RuntimeError):

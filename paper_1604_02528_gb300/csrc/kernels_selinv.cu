@@ -10,6 +10,8 @@
 // several problems (batched pole shifts / matrices) at one tree level.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include "common.cuh"
 #include "launch.h"
 #include "tile_gemm.cuh"
@@ -183,17 +185,11 @@ __device__ void diag_block(const ProbDesc &P, const Item &it, int K, int s, int6
 // owner of column C[b] at row relidx[prb[b] + a], column address pcb[b].
 // ---------------------------------------------------------------------------
 template <typename T, int TN>
-__global__ void __launch_bounds__(kThreads) k_selinv(const ProbDesc *__restrict__ descs,
-                                                     const Item *__restrict__ items, int nitems) {
+__device__ void selinv_item(const ProbDesc &P, const Item &it, unsigned char *smem_raw) {
     using S = Shape<TN>;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
     T *As = reinterpret_cast<T *>(smem_raw);
     T *Bs = As + smem_a_elems<T, TN>();
     __shared__ int64_t tile_cb[kTM], tile_rb[kTM];
-    const int w = blockIdx.x;
-    if (w >= nitems) return;
-    const Item it = items[w];
-    const ProbDesc &P = descs[it.prob];
     const int K = it.K;
     const int s = P.super_ptr[K + 1] - P.super_ptr[K];
     const int64_t ld = P.rowptr[K + 1] - P.rowptr[K];
@@ -241,9 +237,88 @@ __global__ void __launch_bounds__(kThreads) k_selinv(const ProbDesc *__restrict_
     diag_block<T, TN>(P, it, K, s, ld, c, p0, pm, LDk, Zk, As, Bs);
 }
 
+template <typename T, int TN>
+__global__ void __launch_bounds__(kThreads) k_selinv(const ProbDesc *__restrict__ descs,
+                                                     const Item *__restrict__ items, int nitems) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int w = blockIdx.x;
+    if (w >= nitems) return;
+    const Item it = items[w];
+    selinv_item<T, TN>(descs[it.prob], it, smem_raw);
+}
+
+// ---------------------------------------------------------------------------
+// k_selinv_persist: the whole traversal in one launch.  Work items are listed
+// root level first; each CTA claims the next item from a global ticket and,
+// before working on supernode K, waits for the completion flag of K's parent
+// (set by the last tile of the parent after its diagonal block is written;
+// done-ness is transitive up the tree).  An item only waits on items with
+// smaller tickets, which running CTAs have already claimed, so the schedule
+// cannot deadlock.  Every wait is capped at spin_limit polls; a wait that runs
+// out latches SELINV_ERR_TIMEOUT in the status word and the item proceeds (its
+// output is then invalid), so the kernel always terminates.  With
+// wait_on_unset the waits target a flag that nothing sets (a test of the
+// timeout path).
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_selinv_persist(const ProbDesc *__restrict__ descs,
+                                                             const Item *__restrict__ items,
+                                                             const int8_t *__restrict__ buckets, int nitems,
+                                                             int *ticket, long long spin_limit,
+                                                             int wait_on_unset) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ int s_task;
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) s_task = atomicAdd(ticket, 1);
+        __syncthreads();
+        const int task = s_task;
+        if (task >= nitems) return;
+        const Item it = items[task];
+        const ProbDesc &P = descs[it.prob];
+        const int par = P.sparent[it.K];
+        if (par >= 0 && threadIdx.x == 0) {
+            const volatile int *flag = P.done + (wait_on_unset ? P.ns : par);
+            long long polls = 0;
+            while (*flag == 0) {
+                if (++polls > spin_limit) {
+                    latch_status(P.status, SELINV_ERR_TIMEOUT);
+                    break;
+                }
+                __nanosleep(256);
+            }
+            __threadfence();
+        }
+        __syncthreads();
+        switch (buckets[task]) {
+        case 0: selinv_item<T, 8>(P, it, smem_raw); break;
+        case 1: selinv_item<T, 16>(P, it, smem_raw); break;
+        case 2: selinv_item<T, 32>(P, it, smem_raw); break;
+        case 3: selinv_item<T, 64>(P, it, smem_raw); break;
+        default: selinv_item<T, 128>(P, it, smem_raw); break;
+        }
+    }
+}
+
+// debug check of the inputs: latches SELINV_ERR_NONFINITE when any of the n
+// doubles is a NaN or an infinity (complex data: both parts)
+__global__ void __launch_bounds__(256) k_check_finite(const double *__restrict__ x, int64_t n, int *status) {
+    int bad = 0;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+        bad |= !isfinite(x[e]);
+    if (__syncthreads_or(bad) && threadIdx.x == 0) latch_status(status, SELINV_ERR_NONFINITE);
+}
+
 // ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
+cudaError_t launch_check_finite(const void *x, int64_t n, int *status, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    const int grid = (int)std::min<int64_t>((n + 255) / 256, 152 * 8);
+    k_check_finite<<<grid, 256, 0, st>>>(static_cast<const double *>(x), n, status);
+    return cudaGetLastError();
+}
+
 template <typename T>
 static cudaError_t launch_linv_t(const ProbDesc *d, const int2 *work, int nwork, int large, cudaStream_t st) {
     if (nwork <= 0) return cudaSuccess;
@@ -287,11 +362,36 @@ static cudaError_t configure_dt() {
     return e;
 }
 
+template <typename T> constexpr size_t persist_smem() { return smem_bytes<T, 128>(); }
+
+cudaError_t launch_selinv_persist(int dtype, const ProbDesc *d, const Item *items, const int8_t *buckets,
+                                  int n, int *ticket, long long spin_limit, int wait_on_unset,
+                                  cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    int dev = 0, nsm = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (dtype == SELINV_C128) {
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_selinv_persist<zd>, kThreads, persist_smem<zd>());
+        const int grid = std::max(1, std::min(n, nsm * std::max(per_sm, 1)));
+        k_selinv_persist<zd><<<grid, kThreads, persist_smem<zd>(), st>>>(d, items, buckets, n, ticket, spin_limit, wait_on_unset);
+    } else {
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_selinv_persist<double>, kThreads, persist_smem<double>());
+        const int grid = std::max(1, std::min(n, nsm * std::max(per_sm, 1)));
+        k_selinv_persist<double><<<grid, kThreads, persist_smem<double>(), st>>>(d, items, buckets, n, ticket, spin_limit, wait_on_unset);
+    }
+    return cudaGetLastError();
+}
+
 // opt every kernel in to its dynamic shared memory (outside any graph capture)
 cudaError_t configure_selinv_kernels() {
     cudaError_t e = cudaFuncSetAttribute(k_linv<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kLinvSmemMax);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_linv<zd>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kLinvSmemMax);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_selinv_persist<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)persist_smem<double>());
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_selinv_persist<zd>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)persist_smem<zd>());
     if (e == cudaSuccess) e = configure_dt<double>();
     if (e == cudaSuccess) e = configure_dt<zd>();
     return e;

@@ -39,7 +39,8 @@ static void dfree(void *p) {
 }
 
 void Workspace::release() {
-    dfree(LD); dfree(Linv); dfree(partial); dfree(counter); dfree(done); dfree(work);
+    dfree(LD); dfree(Linv); dfree(partial); dfree(counter); dfree(done); dfree(work); dfree(ticket);
+    ticket = nullptr;
     dfree(lhs); dfree(colexp); dfree(colexpY); dfree(dacc); dfree(colexpZ); dfree(yacc); dfree(tcount);
     colexpZ = tcount = nullptr;
     yacc = nullptr;
@@ -60,7 +61,9 @@ int Workspace::ensure(const PlanData &p, int dtype) {
     if (cudaMalloc(&Linv, es * (size_t)std::max<int64_t>(p.linv_total, 1)) != cudaSuccess) return SELINV_ERR_OOM;
     if (cudaMalloc(&partial, es * (size_t)std::max<int64_t>(p.part_max, 1)) != cudaSuccess) return SELINV_ERR_OOM;
     if (cudaMalloc((void **)&counter, sizeof(int) * (size_t)std::max(p.ns, 1)) != cudaSuccess) return SELINV_ERR_OOM;
-    if (cudaMalloc((void **)&done, sizeof(int) * (size_t)std::max(p.ns, 1)) != cudaSuccess) return SELINV_ERR_OOM;
+    // one extra flag (index ns) that nothing ever sets: the target of the timeout test
+    if (cudaMalloc((void **)&done, sizeof(int) * (size_t)(p.ns + 1)) != cudaSuccess) return SELINV_ERR_OOM;
+    if (cudaMalloc((void **)&ticket, sizeof(int)) != cudaSuccess) return SELINV_ERR_OOM;
     if (cudaMalloc(&work, es * (size_t)std::max<int64_t>(p.nnz, 1)) != cudaSuccess) return SELINV_ERR_OOM;
     if (cudaMalloc((void **)&lhs, sizeof(uint16_t) * (size_t)std::max<int64_t>(p.lhs_total, 8)) != cudaSuccess)
         return SELINV_ERR_OOM;
@@ -82,7 +85,8 @@ int Workspace::ensure(const PlanData &p, int dtype) {
     cudaMemset(colexpY, 0, sizeof(int) * (size_t)std::max(p.n, 1));
     cudaMemset(dacc, 0, sizeof(long long) * 2 * (size_t)std::max<int64_t>(p.linv_total, 1));
     cudaMemset(counter, 0, sizeof(int) * (size_t)std::max(p.ns, 1));
-    cudaMemset(done, 0, sizeof(int) * (size_t)std::max(p.ns, 1));
+    cudaMemset(done, 0, sizeof(int) * (size_t)(p.ns + 1));
+    cudaMemset(ticket, 0, sizeof(int));
     bytes_elem = es;
     return SELINV_OK;
 }
@@ -314,8 +318,8 @@ ProbDesc make_desc(const PlanData &p, Workspace &w, int dtype, const void *L, co
 void Schedule::release() {
     if (graph) cudaGraphExecDestroy(graph);
     graph = nullptr;
-    dfree(d_descs); dfree(d_items); dfree(d_work);
-    d_descs = nullptr; d_items = nullptr; d_work = nullptr;
+    dfree(d_descs); dfree(d_items); dfree(d_work); dfree(d_buckets);
+    d_descs = nullptr; d_items = nullptr; d_work = nullptr; d_buckets = nullptr;
 }
 
 int build_schedule(Schedule &S, const std::vector<const PlanData *> &plans,
@@ -397,7 +401,9 @@ int build_schedule(Schedule &S, const std::vector<const PlanData *> &plans,
             for (int32_t K = 0; K < p.ns; K++) {
                 const int s = p.super_ptr[K + 1] - p.super_ptr[K];
                 const int64_t c = p.rowptr[K + 1] - p.rowptr[K] - s;
-                if (c == 0 || !oz_eligible(descs[i].dtype, s, p.opts.fast_contraction)) continue;
+                if (c == 0 || mode == SELINV_SCHED_PERSISTENT ||
+                    !oz_eligible(descs[i].dtype, s, p.opts.fast_contraction))
+                    continue;
                 for (int jb = 0; jb < (s + 7) / 8; jb++) S.h_work.push_back(make_int2(i, (K << 8) | jb));
             }
         }
@@ -440,7 +446,30 @@ int build_schedule(Schedule &S, const std::vector<const PlanData *> &plans,
         return (int64_t)p.ntiles[K] * ((s + oz_tn(s) - 1) / oz_tn(s));
     };
 
-    if (mode == SELINV_SCHED_PLAIN) {
+    if (mode == SELINV_SCHED_PERSISTENT) {
+        // one persistent launch per element type over every supernode of every
+        // problem, root level first (FP64 / complex contraction kernel)
+        int nlev = 0;
+        for (int i = 0; i < np; i++) nlev = std::max(nlev, plans[i]->nlevels);
+        for (int dt = 0; dt < 2; dt++) {
+            const int64_t off = (int64_t)S.h_items.size();
+            for (int l = 0; l < nlev; l++)
+                for (int i = 0; i < np; i++) {
+                    if (descs[i].dtype != dt) continue;
+                    const PlanData &p = *plans[i];
+                    if (l >= p.nlevels) continue;
+                    for (int64_t e = p.level_ptr[l]; e < p.level_ptr[l + 1]; e++) push_items(i, p.level_list[e]);
+                }
+            const int cnt = (int)(S.h_items.size() - off);
+            S.h_buckets.resize(S.h_items.size());
+            for (int64_t e = off; e < (int64_t)S.h_items.size(); e++) {
+                const Item &it = S.h_items[e];
+                const PlanData &p = *plans[it.prob];
+                S.h_buckets[e] = (int8_t)bucket_of(p.super_ptr[it.K + 1] - p.super_ptr[it.K]);
+            }
+            if (cnt) S.launches.push_back({KL_PERSIST, dt, 0, off, cnt, 0});
+        }
+    } else if (mode == SELINV_SCHED_PLAIN) {
         // one launch per supernode, K = N..1, problem after problem
         for (int i = 0; i < np; i++) {
             const PlanData &p = *plans[i];
@@ -523,6 +552,7 @@ int build_schedule(Schedule &S, const std::vector<const PlanData *> &plans,
     if ((rc = upload(&S.d_descs, S.h_descs))) return rc;
     if ((rc = upload(&S.d_items, S.h_items))) return rc;
     if ((rc = upload(&S.d_work, S.h_work))) return rc;
+    if (!S.h_buckets.empty() && (rc = upload(&S.d_buckets, S.h_buckets))) return rc;
     return SELINV_OK;
 }
 
@@ -536,6 +566,14 @@ cudaError_t launch_one(const Schedule &S, const Launch &L, cudaStream_t st) {
     case KL_DIAG: return launch_diag_oz(S.d_descs, S.d_items + L.off, L.count, st);
     case KL_LINV_DIGITS: return launch_linv_digits(S.d_descs, S.d_work + L.off, L.count, st);
     case KL_LHAT_OZ: return launch_lhat_oz(L.bucket, S.d_descs, S.d_items + L.off, L.count, st);
+    case KL_PERSIST: {
+        for (size_t r = 0; r < S.reset_ptr.size(); r++) {
+            cudaError_t e = cudaMemsetAsync(S.reset_ptr[r], 0, S.reset_bytes[r], st);
+            if (e != cudaSuccess) return e;
+        }
+        return launch_selinv_persist(L.dtype, S.d_descs, S.d_items + L.off, S.d_buckets + L.off, L.count,
+                                     S.ticket, S.spin_limit, S.wait_on_unset, st);
+    }
     default: return cudaErrorInvalidValue;
     }
 }
@@ -587,7 +625,7 @@ extern "C" void selinv_default_opts(selinv_opts *o) {
     o->schedule = SELINV_SCHED_LEVEL;
     o->autotune = 0;
     o->debug_checks = 0;
-    o->spin_limit = 1LL << 26;
+    o->spin_limit = 1LL << 22;   // about a second of 256 ns polls
     o->use_graph = 1;
     o->fast_contraction = 1;
 }
@@ -705,13 +743,29 @@ extern "C" int selinv_numeric(selinv_plan plan, selinv_dtype dtype, const void *
     if (!S.valid || S.key_L != L || S.key_D != D || S.key_Z != Z || S.key_dtype != dtype ||
         S.mode != mode) {
         std::vector<const PlanData *> plans{&p};
-        std::vector<ProbDesc> descs{make_desc(p, plan->ws[0], dtype, L, D, Z, false)};
-        rc = build_schedule(S, plans, descs, mode == SELINV_SCHED_PERSISTENT ? SELINV_SCHED_LEVEL : mode);
+        const bool persist = mode == SELINV_SCHED_PERSISTENT;
+        std::vector<ProbDesc> descs{make_desc(p, plan->ws[0], dtype, L, D, Z, persist)};
+        rc = build_schedule(S, plans, descs, mode);
         if (rc) { S.valid = false; return rc; }
+        S.reset_ptr.clear(); S.reset_bytes.clear();
+        if (persist) {
+            S.ticket = plan->ws[0].ticket;
+            S.spin_limit = p.opts.spin_limit;
+            S.wait_on_unset = (p.opts.debug_checks & 2) ? 1 : 0;
+            S.reset_ptr = {plan->ws[0].done, plan->ws[0].ticket};
+            S.reset_bytes = {sizeof(int) * (size_t)(p.ns + 1), sizeof(int)};
+        }
         S.valid = true;
         S.key_L = L; S.key_D = D; S.key_Z = Z; S.key_dtype = dtype; S.mode = mode;
     }
     plan->last_stream = st;
+    if (p.opts.debug_checks & 1) {
+        const int64_t w = dtype == SELINV_C128 ? 2 : 1;
+        if (launch_check_finite(L, w * p.nnz, p.d_status, st) != cudaSuccess ||
+            launch_check_finite(D, w * p.n, p.d_status, st) != cudaSuccess)
+            return SELINV_ERR_CUDA;
+        note_launch(2);
+    }
     return run_schedule(S, st, p.opts.use_graph != 0);
 }
 
@@ -731,6 +785,7 @@ extern "C" int selinv_numeric_profile(selinv_plan plan, selinv_dtype dtype, cons
     Schedule &S = plan->single;
     std::vector<cudaEvent_t> ev(2 * S.launches.size());
     for (auto &e : ev) cudaEventCreate(&e);
+    static_assert(KL_NKINDS == SELINV_PROFILE_KINDS, "profile kinds");
     for (int k = 0; k < KL_NKINDS; k++) { kernel_ms[k] = 0; kernel_launches[k] = 0; }
     for (size_t i = 0; i < S.launches.size(); i++) {
         const Launch &L = S.launches[i];
@@ -787,7 +842,8 @@ extern "C" int selinv_numeric_batched(int nitems, const selinv_plan *plans, cons
             int rc = owner->ws[i + 1].ensure(plans[i]->data, dtypes[i]);
             if (rc) return rc;
             pds[i] = &plans[i]->data;
-            descs[i] = make_desc(plans[i]->data, owner->ws[i + 1], dtypes[i], L[i], D[i], Z[i], false);
+            descs[i] = make_desc(plans[i]->data, owner->ws[i + 1], dtypes[i], L[i], D[i], Z[i],
+                                 mode == SELINV_SCHED_PERSISTENT);
             descs[i].status = owner->data.d_status;
         }
         if (owner->batch_cache.size() >= 4) {
@@ -802,15 +858,36 @@ extern "C" int selinv_numeric_batched(int nitems, const selinv_plan *plans, cons
         b.L.assign(L, L + nitems);
         b.D.assign(D, D + nitems);
         b.Z.assign(Z, Z + nitems);
-        int rc = build_schedule(b.sched, pds, descs, mode == SELINV_SCHED_PERSISTENT ? SELINV_SCHED_LEVEL : mode);
+        int rc = build_schedule(b.sched, pds, descs, mode);
         if (rc) {
             b.sched.release();
             owner->batch_cache.pop_back();
             return rc;
         }
+        if (mode == SELINV_SCHED_PERSISTENT) {
+            // both element types share one ticket: the launches run one after the other
+            b.sched.ticket = owner->ws[1].ticket;
+            b.sched.spin_limit = owner->data.opts.spin_limit;
+            b.sched.wait_on_unset = (owner->data.opts.debug_checks & 2) ? 1 : 0;
+            for (int i = 0; i < nitems; i++) {
+                b.sched.reset_ptr.push_back(owner->ws[i + 1].done);
+                b.sched.reset_bytes.push_back(sizeof(int) * (size_t)(plans[i]->data.ns + 1));
+            }
+            b.sched.reset_ptr.push_back(owner->ws[1].ticket);
+            b.sched.reset_bytes.push_back(sizeof(int));
+        }
         hit = &b;
     }
     owner->last_stream = st;
+    if (owner->data.opts.debug_checks & 1) {
+        for (int i = 0; i < nitems; i++) {
+            const int64_t w = dtypes[i] == SELINV_C128 ? 2 : 1;
+            if (launch_check_finite(L[i], w * plans[i]->data.nnz, owner->data.d_status, st) != cudaSuccess ||
+                launch_check_finite(D[i], w * plans[i]->data.n, owner->data.d_status, st) != cudaSuccess)
+                return SELINV_ERR_CUDA;
+            note_launch(2);
+        }
+    }
     return run_schedule(hit->sched, st, owner->data.opts.use_graph != 0);
 }
 

@@ -43,6 +43,7 @@ struct Workspace {
     int *colexpY = nullptr;    // [n], zero between calls
     long long *dacc = nullptr; // [2 * linv_total], zero between calls
     int *colexpZ = nullptr;    // [n], rewritten for every column in every call
+    int *ticket = nullptr;     // work-item ticket of the persistent schedule
     uint16_t *linvd = nullptr; // digit planes of L_KK^{-1}
     int *linvexp = nullptr;    // [n]
     long long *yacc = nullptr; // [2 * nnz] (real problems with tensor-core supernodes), zero between calls
@@ -54,7 +55,7 @@ struct Workspace {
 
 // launch kinds
 enum { KL_LINV = 0, KL_LHAT = 1, KL_SELINV = 2, KL_DIGITS = 3, KL_SELINV_OZ = 4, KL_DIAG = 5, KL_LINV_DIGITS = 6,
-       KL_LHAT_OZ = 7, KL_NKINDS = 8 };
+       KL_LHAT_OZ = 7, KL_PERSIST = 8, KL_NKINDS = 9, KL_RESET = 100 };
 
 // tensor-core (FP64-exact) contraction applies to real problems with s >= kOzMinS
 constexpr int kOzMinS = 16;
@@ -77,10 +78,17 @@ struct Schedule {
     std::vector<ProbDesc> h_descs;
     std::vector<Item> h_items;
     std::vector<int2> h_work;
+    std::vector<int8_t> h_buckets;  // per item of the persistent launches
     std::vector<Launch> launches;
+    std::vector<void *> reset_ptr;  // memsets issued before the persistent launches
+    std::vector<size_t> reset_bytes;
     ProbDesc *d_descs = nullptr;
     Item *d_items = nullptr;
     int2 *d_work = nullptr;
+    int8_t *d_buckets = nullptr;
+    int *ticket = nullptr;
+    long long spin_limit = 0;
+    int wait_on_unset = 0;
     cudaGraphExec_t graph = nullptr;
     void release();
 };

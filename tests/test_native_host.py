@@ -187,3 +187,15 @@ def test_status_without_device_work_is_ok(native):
     sym = oracle.symbolic_for(p)
     plan = make_plan(native, sym)
     assert native.selinv_status(plan) == 0
+
+
+def test_binding_constants_match_header(native):
+    import re
+    from pathlib import Path
+    hdr = (Path(__file__).resolve().parents[1] / "include" / "selinv.h").read_text()
+    codes = dict(re.findall(r"#define (SELINV_(?:OK|ERR_\w+))\s+\(?(-?\d+)\)?", hdr))
+    assert len(codes) == 10
+    for name, val in codes.items():
+        assert getattr(native, name) == int(val), name
+    kinds = int(re.search(r"#define SELINV_PROFILE_KINDS (\d+)", hdr).group(1))
+    assert len(native.PROFILE_KINDS) == kinds
