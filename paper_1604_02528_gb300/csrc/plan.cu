@@ -40,7 +40,9 @@ static void dfree(void *p) {
 
 void Workspace::release() {
     dfree(LD); dfree(Linv); dfree(partial); dfree(counter); dfree(done); dfree(work); dfree(ticket);
+    dfree(partial_all);
     ticket = nullptr;
+    partial_all = nullptr;
     dfree(lhs); dfree(colexp); dfree(colexpY); dfree(dacc); dfree(colexpZ); dfree(yacc); dfree(tcount);
     colexpZ = tcount = nullptr;
     yacc = nullptr;
@@ -88,6 +90,13 @@ int Workspace::ensure(const PlanData &p, int dtype) {
     cudaMemset(done, 0, sizeof(int) * (size_t)(p.ns + 1));
     cudaMemset(ticket, 0, sizeof(int));
     bytes_elem = es;
+    return SELINV_OK;
+}
+
+int Workspace::ensure_persistent(const PlanData &p) {
+    if (partial_all) return SELINV_OK;
+    if (cudaMalloc(&partial_all, bytes_elem * (size_t)std::max<int64_t>(p.part_all, 1)) != cudaSuccess)
+        return SELINV_ERR_OOM;
     return SELINV_OK;
 }
 
@@ -226,6 +235,14 @@ static int build_plan(PlanData &p, int32_t n, int32_t ns, const int32_t *super_p
         }
         p.part_max = std::max(p.part_max, acc);
     }
+    p.part_off_all.assign(ns > 0 ? ns : 1, 0);
+    p.part_all = 0;
+    for (int32_t K = 0; K < ns; K++) {
+        const int64_t s = super_ptr[K + 1] - super_ptr[K];
+        p.part_off_all[K] = p.part_all;
+        p.part_all += (int64_t)p.ntiles[K] * s * s;
+    }
+    p.part_all = std::max<int64_t>(p.part_all, 1);
     return SELINV_OK;
 }
 
@@ -250,6 +267,7 @@ int ensure_device(PlanData &p) {
     if ((rc = upload(&p.d_relidx, p.relidx))) return rc;
     if ((rc = upload(&p.d_linv_off, p.linv_off))) return rc;
     if ((rc = upload(&p.d_part_off, p.part_off))) return rc;
+    if ((rc = upload(&p.d_part_off_all, p.part_off_all))) return rc;
     if ((rc = upload(&p.d_lhs_off, p.lhs_off))) return rc;
     if ((rc = upload(&p.d_tile_base, p.tile_base))) return rc;
     if ((rc = upload(&p.d_linvd_off, p.linvd_off))) return rc;
@@ -262,11 +280,11 @@ int ensure_device(PlanData &p) {
 
 void PlanData::release_device() {
     dfree(d_super_ptr); dfree(d_sparent); dfree(d_rowptr); dfree(d_rows); dfree(d_panel_off);
-    dfree(d_colbase); dfree(d_relbase); dfree(d_relidx); dfree(d_linv_off); dfree(d_part_off);
+    dfree(d_colbase); dfree(d_relbase); dfree(d_relidx); dfree(d_linv_off); dfree(d_part_off); dfree(d_part_off_all);
     dfree(d_lhs_off); dfree(d_tile_base); dfree(d_linvd_off); dfree(d_status);
     d_lhs_off = d_tile_base = d_linvd_off = nullptr;
     d_super_ptr = d_sparent = d_rows = d_relidx = nullptr;
-    d_rowptr = d_panel_off = d_colbase = d_relbase = d_linv_off = d_part_off = nullptr;
+    d_rowptr = d_panel_off = d_colbase = d_relbase = d_linv_off = d_part_off = d_part_off_all = nullptr;
     d_status = nullptr;
 }
 
@@ -282,14 +300,14 @@ ProbDesc make_desc(const PlanData &p, Workspace &w, int dtype, const void *L, co
     d.relbase = p.d_relbase;
     d.relidx = p.d_relidx;
     d.linv_off = p.d_linv_off;
-    d.part_off = p.d_part_off;
+    d.part_off = persistent ? p.d_part_off_all : p.d_part_off;
     d.sparent = p.d_sparent;
     d.L = L;
     d.D = D;
     d.Z = Z;
     d.LD = w.LD;
     d.Linv = w.Linv;
-    d.partial = w.partial;
+    d.partial = persistent ? w.partial_all : w.partial;
     d.counter = w.counter;
     d.done = persistent ? w.done : nullptr;
     d.status = p.d_status;
@@ -744,6 +762,7 @@ extern "C" int selinv_numeric(selinv_plan plan, selinv_dtype dtype, const void *
         S.mode != mode) {
         std::vector<const PlanData *> plans{&p};
         const bool persist = mode == SELINV_SCHED_PERSISTENT;
+        if (persist && (rc = plan->ws[0].ensure_persistent(p))) return rc;
         std::vector<ProbDesc> descs{make_desc(p, plan->ws[0], dtype, L, D, Z, persist)};
         rc = build_schedule(S, plans, descs, mode);
         if (rc) { S.valid = false; return rc; }
@@ -840,6 +859,7 @@ extern "C" int selinv_numeric_batched(int nitems, const selinv_plan *plans, cons
         std::vector<ProbDesc> descs(nitems);
         for (int i = 0; i < nitems; i++) {
             int rc = owner->ws[i + 1].ensure(plans[i]->data, dtypes[i]);
+            if (!rc && mode == SELINV_SCHED_PERSISTENT) rc = owner->ws[i + 1].ensure_persistent(plans[i]->data);
             if (rc) return rc;
             pds[i] = &plans[i]->data;
             descs[i] = make_desc(plans[i]->data, owner->ws[i + 1], dtypes[i], L[i], D[i], Z[i],

@@ -17,16 +17,17 @@ struct PlanData {
     std::vector<int32_t> super_ptr, sparent, rows, level, level_list;
     std::vector<int32_t> seg_owner, seg_start, seg_coloff, relidx, ntiles;
     std::vector<int64_t> rowptr, panel_off, seg_ptr, rel_ptr, level_ptr, linv_off, part_off;
+    std::vector<int64_t> part_off_all;  // split-partial offsets disjoint over all levels (persistent schedule)
     std::vector<int64_t> colbase, relbase;  // per row-list position
     std::vector<int64_t> lhs_off;           // digit-plane offsets (tensor-core path)
     std::vector<int64_t> tile_base;         // prefix sums of the 64-row tiles of each supernode
     std::vector<int64_t> linvd_off;         // digit planes of L_KK^{-1} (tensor-core path)
     int nlevels = 0;
-    int64_t nnz = 0, linv_total = 0, part_max = 1, lhs_total = 0, tile_total = 0, linvd_total = 0;
+    int64_t nnz = 0, linv_total = 0, part_max = 1, part_all = 1, lhs_total = 0, tile_total = 0, linvd_total = 0;
     // device copies
     int32_t *d_super_ptr = nullptr, *d_sparent = nullptr, *d_rows = nullptr, *d_relidx = nullptr;
     int64_t *d_rowptr = nullptr, *d_panel_off = nullptr, *d_colbase = nullptr, *d_relbase = nullptr;
-    int64_t *d_linv_off = nullptr, *d_part_off = nullptr, *d_lhs_off = nullptr, *d_tile_base = nullptr;
+    int64_t *d_linv_off = nullptr, *d_part_off = nullptr, *d_part_off_all = nullptr, *d_lhs_off = nullptr, *d_tile_base = nullptr;
     int64_t *d_linvd_off = nullptr;
     int *d_status = nullptr;
     void release_device();
@@ -37,6 +38,7 @@ struct PlanData {
 // completion flags, and one more panel-sized buffer (adjoint working copy).
 struct Workspace {
     void *LD = nullptr, *Linv = nullptr, *partial = nullptr, *work = nullptr;
+    void *partial_all = nullptr;  // persistent schedule: supernodes of every level in flight at once
     int *counter = nullptr, *done = nullptr;
     uint16_t *lhs = nullptr;   // bf16 digit planes of Lhat
     int *colexp = nullptr;     // [n]
@@ -50,12 +52,13 @@ struct Workspace {
     int *tcount = nullptr;     // [tile_total], zero between calls
     size_t bytes_elem = 0;
     int ensure(const PlanData &p, int dtype);
+    int ensure_persistent(const PlanData &p);
     void release();
 };
 
 // launch kinds
 enum { KL_LINV = 0, KL_LHAT = 1, KL_SELINV = 2, KL_DIGITS = 3, KL_SELINV_OZ = 4, KL_DIAG = 5, KL_LINV_DIGITS = 6,
-       KL_LHAT_OZ = 7, KL_PERSIST = 8, KL_NKINDS = 9, KL_RESET = 100 };
+       KL_LHAT_OZ = 7, KL_PERSIST = 8, KL_NKINDS = 9 };
 
 // tensor-core (FP64-exact) contraction applies to real problems with s >= kOzMinS
 constexpr int kOzMinS = 16;

@@ -99,7 +99,7 @@ template <typename T, int TN, bool kDoubleDiag = false> struct LoadGather {
                 int64_t addr;
                 if (p >= q) addr = pcb[q] + relidx[prb[q] + p];
                 else addr = tile_cb[pl] + relidx[tile_rb[pl] + q];
-                v = Z[addr];
+                v = ldcg(Z + addr);  // L2: written by other CTAs of a persistent launch
                 if (kDoubleDiag && p == q) v = add(v, v);
             }
             As[kk * kTM + pl] = v;
@@ -148,7 +148,7 @@ __device__ void diag_finish(const ProbDesc &P, int K, int s, int64_t ld, int nti
     // exponent of every whole column of K's panel (rows below: atomic max taken
     // when they were written), for the row bounds of the descendants' gathers
     for (int j = threadIdx.x; j < s; j += kThreads) {
-        int e = P.colexpY[P.super_ptr[K] + j];
+        int e = __ldcg(P.colexpY + P.super_ptr[K] + j);  // atomics of this launch
         for (int i = 0; i < s; i++) e = max(e, bexp(Zk[(int64_t)j * ld + i]));
         P.colexpZ[P.super_ptr[K] + j] = e;
         P.colexpY[P.super_ptr[K] + j] = 0;
