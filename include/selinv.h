@@ -128,8 +128,10 @@ void selinv_analysis_destroy(selinv_analysis a);
  * Errors: INVALID_ARG, BAD_ETREE (sparent[K] <= K or >= nsuper, or the first
  * row below K not owned by sparent[K]), BAD_PATTERN (rows(K) not starting
  * with K's columns, not ascending, or some C entry of K missing from the row
- * list of its owner: the closure property the recursion relies on), OOM, CUDA.
+ * list of its owner: the closure property the recursion relies on),
+ * UNSUPPORTED (a supernode wider than SELINV_MAX_SUPERNODE columns), OOM, CUDA.
  * ------------------------------------------------------------------------- */
+#define SELINV_MAX_SUPERNODE 128
 int selinv_symbolic(int32_t n, int32_t nsuper, const int32_t *super_ptr, const int32_t *sparent,
                     const int64_t *rowptr, const int32_t *rowind, const selinv_opts *opts,
                     selinv_plan *out_plan);

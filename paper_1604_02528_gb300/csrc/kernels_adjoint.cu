@@ -1,25 +1,30 @@
 // Reverse mode of the selected inversion and of the LDL^T factorization
 // (FP64).  The paper has no adjoint; this is the chain rule through the
-// steps of Alg. 1 taken in reverse order, with every accumulation written in
-// pull form so that each output has one owner (deterministic, no atomics).
+// steps of Alg. 1 taken in reverse order.  Every accumulation has one owner
+// and a fixed order (deterministic, no floating-point atomics).
 //
 // Selected-inversion adjoint, leaves -> root.  With Zbar the cotangent of
 // every stored lower entry of A^{-1}, for each K:
+//   Zbar on K's panel is completed by the extend-add of its children's
+//   update matrices V (below), which also starts V_K            [k_adj_asm]
 //   S      = symmetric cotangent of the diagonal block (S_ii = Zbar_ii,
 //            S_ij = S_ji = Zbar_ij / 2)                       [k_adj_ybar]
 //   Ybar   = Zbar_{C,K} - Lhat S                              [k_adj_ybar]
+//   V_K   -= sym(Ybar Lhat^T): the cotangent that the gather of A^{-1}(C,C)
+//            sends to the ancestors, handed to the parent as a dense c x c
+//            update matrix (multifrontal style: entries whose column belongs
+//            to the parent go to its panel, the rest into its own V)  [k_adj_vupd]
 //   Lhatb  = -Y S - A^{-1}_{C,C} Ybar  (the gather recomputed) [k_adj_lhbar]
-//   Zbar(C,C) += sym(-Ybar Lhat^T): pulled by each ancestor J from its
-//            descendants' (Ybar, Lhat) over the owner runs of C [k_adj_pull]
 //   Lbar_CK = Lhatb M^T, M = L_KK^{-1}; Mbar = L_CK^T Lhatb + 2 D^{-1} M S;
 //   Lbar_KK = -(M^T Mbar M^T) strictly lower; Dbar_k = -(M S M^T)_kk / D_k^2
-//                                                             [k_adj_lhbar + finisher]
+//                                            [k_adj_lhbar, k_adj_gemm, k_adj_sel_*]
 // Factorization adjoint, root -> leaves (reverse of k_fupdate / k_fdiag / k_ftrsm):
 //   Lbar_CJ -= (Abar(C,C) L_CJ) o D, the gathered Abar with its diagonal
 //   doubled; Dbar_k -= 1/2 (L_CJ^T Abar(C,C) L_CJ)_kk          [k_fadj_pull]
-//   Abar_CJ = Lbar_CJ D^{-1} L_JJ^{-1}; Nbar = A_CJ^T Lbar_CJ;
-//   Ubar = -N^T Nbar N^T with N = L_JJ^{-T} D^{-1}; then the reverse of the
-//   dense LDL^T of the diagonal block                          [k_fadj_trsm + finisher]
+//   Abar_CJ = Lbar_CJ D^{-1} L_JJ^{-1}; Nbar = A_CJ^T Lbar_CJ   [k_fadj_trsm]
+//   Ubar = -N^T Nbar N^T with N = L_JJ^{-T} D^{-1}  [k_fadj_nbar, k_adj_gemm, k_fadj_ubar]
+//   then the reverse of the dense LDL^T of the diagonal block in closed form
+//                                                   [k_adj_gemm, k_fadj_fold]
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -29,6 +34,7 @@
 #include "launch.h"
 #include "plan.h"
 #include "tile_gemm.cuh"
+#include "seg_update.cuh"
 
 namespace selinv {
 
@@ -55,6 +61,10 @@ struct AdjDesc {
     double *partial;  // split partials
     int *counter;     // per-supernode tile counters
     double *fin;      // per-supernode s x s scratch: 4 slots at 4*linv_off
+    const int32_t *sparent;
+    const int64_t *v_off;   // update matrix of K: c x c column-major at V + v_off[K]
+    const int32_t *chpos;   // row-list position p of C_K[q]: its position in rows(parent(K))
+    double *V;              // update matrices: the part of Zbar(C,C) not yet handed to an owner
 };
 
 struct AdjData {
@@ -62,16 +72,27 @@ struct AdjData {
     std::vector<Item> items;          // (J, tile, ntiles) per level, levels deepest first
     std::vector<int64_t> lvl_ptr;     // per level: [start, end) of items, buckets sorted
     std::vector<int> lvl_bucket_ptr;  // per level x bucket offsets (kNumBuckets+1 per level)
-    std::vector<int2> tiles;          // (J, 64-row panel tile) per level
-    std::vector<int64_t> tile_lptr;
     std::vector<int2> linv_work;
     std::vector<Item> lhat_items;
     std::vector<int> lhat_bptr;
     std::vector<int2> gitems, citems;  // per level: (J, 32x32 tile) and (J, chunk | ntiles << 16)
     std::vector<int> js;               // per level: supernodes
     std::vector<int64_t> g_lptr, c_lptr, j_lptr;
+    // update matrices (multifrontal hand-off of Zbar(C,C) from child to parent)
+    std::vector<int64_t> v_off;
+    std::vector<int32_t> chpos;
+    std::vector<int2> asm_items;      // (child, 4096-entry chunk) per level and child pass
+    std::vector<int64_t> asm_lptr;    // [level * npass + pass]
+    int npass = 0;
+    std::vector<int4> vitems;         // (K, row tile, column tile) of the lower c x c per level
+    std::vector<int64_t> v_lptr;
+    int2 *d_asm = nullptr;
+    int4 *d_vitems = nullptr;
+    int64_t *d_voff = nullptr;
+    int32_t *d_chpos = nullptr;
+    double *V = nullptr;
     Item *d_items = nullptr, *d_lhat = nullptr;
-    int2 *d_tiles = nullptr, *d_linv = nullptr, *d_gitems = nullptr, *d_citems = nullptr;
+    int2 *d_linv = nullptr, *d_gitems = nullptr, *d_citems = nullptr;
     int *d_js = nullptr;
     double *YB = nullptr, *Zb = nullptr, *Lbw = nullptr, *Ab = nullptr, *fin = nullptr;
     AdjDesc *d_desc = nullptr;
@@ -79,38 +100,66 @@ struct AdjData {
 };
 
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_adj_pull(const AdjDesc *__restrict__ ad,
-                                                  const int2 *__restrict__ tiles, int ntiles, int64_t tile0) {
+// Extend-add of one child's update matrix into its parent K (multifrontal
+// hand-off): entry (a, b), a >= b, of V_child lands at rows(K) positions
+// (pa, pb); into K's panel cotangent when C_child[b] is one of K's columns,
+// else into V_K.  One launch per child rank, so two children of one parent
+// never run together: no conflicts, a fixed order.
+__global__ void __launch_bounds__(256) k_adj_asm(const AdjDesc *__restrict__ ad, const int2 *__restrict__ items,
+                                                 int nitems) {
     const int w = blockIdx.x;
-    if (w >= ntiles) return;
+    if (w >= nitems) return;
     const AdjDesc &A = *ad;
-    const int J = tiles[w].x;
-    const int64_t ldJ = A.rowptr[J + 1] - A.rowptr[J];
-    const int fcJ = A.super_ptr[J];
-    double *ZbJ = A.Zb + A.panel_off[J];
-    for (int64_t li = A.tseg_ptr[tile0 + w]; li < A.tseg_ptr[tile0 + w + 1]; li++) {
-        const int4 ts = A.tseg[li];
-        const int t = ts.x, pa = ts.y, np = ts.z - ts.y;
-        const int K = A.seg_K[t];
-        const int st = A.seg_start[t], nq = A.seg_end[t] - st;
-        const int sK = A.super_ptr[K + 1] - A.super_ptr[K];
-        const int64_t ldK = A.rowptr[K + 1] - A.rowptr[K];
-        const int32_t *rel = A.relidx + A.rel_ptr[t];
-        const double *Yb = A.YB + A.panel_off[K] + sK;   // Ybar(p, k) = Yb[k*ldK + p]
-        const double *Lh = A.LD + A.panel_off[K] + sK;   // Lhat(p, k)
-        __syncthreads();  // the previous segment's updates to this tile are complete
-        for (int e = threadIdx.x; e < np * nq; e += blockDim.x) {
-            const int p = pa + e % np, q = st + e / np;
-            if (p < q) continue;
-            double v = 0.0;
-            for (int k = 0; k < sK; k++) {
-                v = fma(Yb[(int64_t)k * ldK + p], Lh[(int64_t)k * ldK + q], v);
-                if (p != q) v = fma(Yb[(int64_t)k * ldK + q], Lh[(int64_t)k * ldK + p], v);
-            }
-            const int col = A.rows[A.rowptr[K] + sK + q] - fcJ;
-            ZbJ[(int64_t)col * ldJ + rel[p - st]] -= v;
-        }
+    const int ch = items[w].x, chunk = items[w].y;
+    const int K = A.sparent[ch];
+    const int sch = A.super_ptr[ch + 1] - A.super_ptr[ch];
+    const int cch = (int)(A.rowptr[ch + 1] - A.rowptr[ch] - sch);
+    const int sK = A.super_ptr[K + 1] - A.super_ptr[K];
+    const int64_t ldK = A.rowptr[K + 1] - A.rowptr[K];
+    const int cK = (int)(ldK - sK);
+    const int32_t *pos = A.chpos + A.rowptr[ch] + sch;
+    const double *Vc = A.V + A.v_off[ch];
+    double *VK = A.V + A.v_off[K];
+    double *ZbK = A.Zb + A.panel_off[K];
+    const int64_t cc = (int64_t)cch * cch;
+    for (int64_t e = (int64_t)chunk * 4096 + threadIdx.x; e < cc && e < (int64_t)(chunk + 1) * 4096; e += 256) {
+        const int a = (int)(e % cch), b = (int)(e / cch);
+        if (a < b) continue;
+        const double v = Vc[e];
+        const int pa = pos[a], pb = pos[b];
+        if (pb < sK) ZbK[(int64_t)pb * ldK + pa] += v;
+        else VK[(int64_t)(pb - sK) * cK + (pa - sK)] += v;
     }
+}
+
+// V_K -= sym(Ybar Lhat^T) on one 64 x 64 tile of the lower c x c triangle:
+// [Ybar, Lhat] [Lhat, Ybar]^T over k' < 2s, the diagonal counted once
+__global__ void __launch_bounds__(256) k_adj_vupd(const AdjDesc *__restrict__ ad, const int4 *__restrict__ items,
+                                                  int nitems) {
+    __shared__ SegSmem<double> sm;
+    const int w = blockIdx.x;
+    if (w >= nitems) return;
+    const AdjDesc &A = *ad;
+    const int K = items[w].x, ti = items[w].y, tj = items[w].z;
+    const int sK = A.super_ptr[K + 1] - A.super_ptr[K];
+    const int64_t ld = A.rowptr[K + 1] - A.rowptr[K];
+    const int c = (int)(ld - sK);
+    const double *Yb = A.YB + A.panel_off[K] + sK;   // Ybar(p, k) = Yb[k*ld + p]
+    const double *Lh = A.LD + A.panel_off[K] + sK;   // Lhat(p, k)
+    double *VK = A.V + A.v_off[K];
+    const int pa = ti * kSegB, st = tj * kSegB;
+    const int np = c - pa < kSegB ? c - pa : kSegB, nq = c - st < kSegB ? c - st : kSegB;
+    auto x = [&](int pl, int k) {
+        return k < sK ? Yb[(int64_t)k * ld + pa + pl] : Lh[(int64_t)(k - sK) * ld + pa + pl];
+    };
+    auto y = [&](int ql, int k) {
+        return k < sK ? Lh[(int64_t)k * ld + st + ql] : Yb[(int64_t)(k - sK) * ld + st + ql];
+    };
+    auto out = [&](int pl, int ql, double v) {
+        if (pa + pl == st + ql) v *= 0.5;
+        VK[(int64_t)(st + ql) * c + pa + pl] -= v;
+    };
+    seg_update<double>(pa, np, st, nq, 2 * sK, x, y, out, sm);
 }
 
 // S (tile 0) and Ybar rows of one tile
@@ -366,7 +415,7 @@ __global__ void k_gather_vals(const int64_t *__restrict__ pos, const double *__r
 // spread over many CTAs.  Scratch per supernode J: 4 s x s slots at
 // 4 * linv_off[J] (selinv: Mbar, W, T1; factorization: Nbar, T2, N, U).
 // ---------------------------------------------------------------------------
-enum { OP_SEL_T1 = 0, OP_SEL_W, OP_SEL_LB, OP_FAC_T2, OP_FAC_U };
+enum { OP_SEL_T1 = 0, OP_SEL_W, OP_SEL_LB, OP_FAC_T2, OP_FAC_U, OP_FAC_T3, OP_FAC_G1, OP_FAC_G2 };
 
 // C (32 x 32 tile) of an s x s product; items (J, tile), tiles row-major over
 // ceil(s/32)^2.  256 threads, 2 x 2 outputs each, k staged 32 at a time.
@@ -385,13 +434,18 @@ __global__ void __launch_bounds__(256) k_adj_gemm(const AdjDesc *__restrict__ ad
     const double *M = A.Linv + A.linv_off[J];             // M(i, k) = M[k*s + i]
     double *F = A.fin + 4 * A.linv_off[J];
     const double *S = A.YB + A.panel_off[J];              // S(k, j) = S[j*ld + k]
+    const double *LJ = A.L + A.panel_off[J];              // L_JJ(i, k) = LJ[k*ld + i], unit lower
+    const double *LbJ = A.Lb + A.panel_off[J];
     auto a_at = [&](int i, int k) -> double {
         switch (op) {
         case OP_SEL_T1: return M[(int64_t)k * s + i];                 // M
         case OP_SEL_W: return F[(int64_t)k * s + i];                  // Mbar
         case OP_SEL_LB: return M[(int64_t)i * s + k];                 // M^T
         case OP_FAC_T2: return F[(int64_t)k * s + i];                 // Nbar
-        default: return F[2 * ss + (int64_t)i * s + k];               // N^T
+        case OP_FAC_U: return F[2 * ss + (int64_t)i * s + k];         // N^T
+        case OP_FAC_T3: return k == i ? 1.0 : (k > i ? LJ[(int64_t)i * ld + k] : 0.0);  // L_JJ^T
+        case OP_FAC_G1: return F[(int64_t)k * s + i];                 // P
+        default: return M[(int64_t)i * s + k];                        // M^T
         }
     };
     auto b_at = [&](int k, int j) -> double {
@@ -400,7 +454,10 @@ __global__ void __launch_bounds__(256) k_adj_gemm(const AdjDesc *__restrict__ ad
         case OP_SEL_W: return M[(int64_t)k * s + j];                  // M^T
         case OP_SEL_LB: return F[ss + (int64_t)j * s + k];            // W
         case OP_FAC_T2: return F[2 * ss + (int64_t)k * s + j];        // N^T
-        default: return F[ss + (int64_t)j * s + k];                   // T2
+        case OP_FAC_U: return F[ss + (int64_t)j * s + k];             // T2
+        case OP_FAC_T3: return k > j ? LbJ[(int64_t)j * ld + k] : 0.0;  // Lbar_JJ, strictly lower
+        case OP_FAC_G1: return M[(int64_t)j * s + k];                 // M
+        default: return F[ss + (int64_t)j * s + k];                   // P M
         }
     };
     const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
@@ -436,7 +493,12 @@ __global__ void __launch_bounds__(256) k_adj_gemm(const AdjDesc *__restrict__ ad
             case OP_SEL_W: F[ss + (int64_t)j * s + i] = x; break;                    // W
             case OP_SEL_LB: Lb[(int64_t)j * ld + i] = i > j ? -x : 0.0; break;      // Lbar_JJ
             case OP_FAC_T2: F[ss + (int64_t)j * s + i] = x; break;                   // T2
-            default: F[3 * ss + (int64_t)j * s + i] = -x; break;                     // Ubar
+            case OP_FAC_U: F[3 * ss + (int64_t)j * s + i] = -x; break;               // Ubar
+            case OP_FAC_T3:                                                          // P
+                F[(int64_t)j * s + i] = i > j ? x / A.D[A.super_ptr[J] + j] : (i == j ? A.Db[A.super_ptr[J] + i] : 0.0);
+                break;
+            case OP_FAC_G1: F[ss + (int64_t)j * s + i] = x; break;                   // P M
+            default: F[2 * ss + (int64_t)j * s + i] = x; break;                      // G = M^T P M
             }
         }
 }
@@ -530,69 +592,28 @@ __global__ void __launch_bounds__(256) k_fadj_ubar(const AdjDesc *__restrict__ a
     }
 }
 
-// factorization adjoint: reverse of the dense LDL^T of J's diagonal block.
-// Pbar (s x s, lower) in shared memory starts as (Lbar strictly lower, Dbar on
-// the diagonal).  Step j (s-1 .. 0): for r > j,
-//   Pbar(r,j) -= D_j sum_{k>j} Pbar(max(r,k), min(r,k)) L(k,j)   (symmetric matvec)
-//   Dbar_j    -= sum_{j<k<=i} Pbar(i,k) L(i,j) L(k,j)
-// then the reverse of L(r,j) = a(r,j) / D_j.  One warp per row r, lanes over k.
-__global__ void __launch_bounds__(256) k_fadj_dense(const AdjDesc *__restrict__ ad,
-                                                    const int *__restrict__ js, int nj) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    double *Pb = reinterpret_cast<double *>(smem_raw);   // Pb(i, k) = Pb[k*s + i]
-    __shared__ double lj[128];
-    __shared__ double red[8];
+// factorization adjoint: reverse of the dense LDL^T of J's diagonal block in
+// closed form.  With X = L^{-1} dA L^{-T} one has dD = diag(X) and
+// dL = L stril(X) D^{-1}, so dloss = <P, X> with
+//   P = stril(L^T Lbar D^{-1}) + diag(Dbar),
+// and the full-matrix gradient is G = L^{-T} P L^{-1} = M^T P M (M = L_JJ^{-1};
+// three s x s products in k_adj_gemm).  The stored lower entries of the
+// symmetric block get G(i,j) + G(j,i) below the diagonal, G(i,i) on it.
+__global__ void __launch_bounds__(256) k_fadj_fold(const AdjDesc *__restrict__ ad,
+                                                   const int *__restrict__ js, int nj) {
     const int w = blockIdx.x;
     if (w >= nj) return;
     const AdjDesc &A = *ad;
     const int J = js[w];
-    const int fc = A.super_ptr[J];
-    const int s = A.super_ptr[J + 1] - fc;
+    const int s = A.super_ptr[J + 1] - A.super_ptr[J];
     const int64_t ld = A.rowptr[J + 1] - A.rowptr[J];
-    const double *L = A.L + A.panel_off[J];          // L(i, k) = L[k*ld + i]
-    double *Lb = A.Lb + A.panel_off[J];
-    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-    for (int e = threadIdx.x; e < s * s; e += blockDim.x) {
-        const int i = e % s, k = e / s;
-        Pb[e] = i > k ? Lb[(int64_t)k * ld + i] : (i == k ? A.Db[fc + i] : 0.0);
-    }
-    for (int j = s - 1; j >= 0; j--) {
-        __syncthreads();
-        for (int k = threadIdx.x; k < s; k += blockDim.x) lj[k] = k > j ? L[(int64_t)j * ld + k] : 0.0;
-        __syncthreads();
-        const double d = A.D[fc + j];
-        double dpart = 0.0;
-        for (int r = j + 1 + warp; r < s; r += 8) {
-            double v = 0.0, u = 0.0;
-            for (int k = j + 1 + lane; k < s; k += 32) {
-                const double t = k >= r ? Pb[(int64_t)r * s + k] : Pb[(int64_t)k * s + r];
-                v = fma(k == r ? 2.0 * t : t, lj[k], v);   // the diagonal pair enters twice
-                if (k >= r) u = fma(t, lj[k], u);
-            }
-#pragma unroll
-            for (int o = 16; o; o >>= 1) {
-                v += __shfl_xor_sync(0xffffffffu, v, o);
-                u += __shfl_xor_sync(0xffffffffu, u, o);
-            }
-            if (lane == 0) {
-                const double pb = Pb[(int64_t)j * s + r] - d * v;   // then reverse the division
-                Pb[(int64_t)j * s + r] = pb / d;
-                dpart -= u * lj[r] + pb * lj[r] / d;
-            }
-        }
-        if (lane == 0) red[warp] = dpart;
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            double t = 0.0;
-            for (int q = 0; q < 8; q++) t += red[q];
-            Pb[(int64_t)j * s + j] += t;
-        }
-    }
-    __syncthreads();
+    const int64_t ss = (int64_t)s * s;
+    const double *G = A.fin + 4 * A.linv_off[J] + 2 * ss;
     double *Ab = A.Ab + A.panel_off[J];
     for (int e = threadIdx.x; e < s * s; e += blockDim.x) {
         const int i = e % s, k = e / s;
-        Ab[(int64_t)k * ld + i] = i >= k ? Pb[e] : 0.0;
+        Ab[(int64_t)k * ld + i] = i > k ? G[(int64_t)k * s + i] + G[(int64_t)i * s + k]
+                                        : (i == k ? G[(int64_t)k * s + i] : 0.0);
     }
 }
 
@@ -616,8 +637,6 @@ static cudaError_t configure_adjoint() {
     CFG(k_fadj_trsm, 8, trsm_smem); CFG(k_fadj_trsm, 16, trsm_smem); CFG(k_fadj_trsm, 32, trsm_smem);
     CFG(k_fadj_trsm, 64, trsm_smem); CFG(k_fadj_trsm, 128, trsm_smem);
 #undef CFG
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_fadj_dense, cudaFuncAttributeMaxDynamicSharedMemorySize, 128 * 128 * 8);
     done = e == cudaSuccess;
     return e;
 }
@@ -660,9 +679,10 @@ void adjoint_release(void *p) {
     AdjData *a = static_cast<AdjData *>(p);
     if (!a) return;
     auto fr = [](void *q) { if (q) cudaFree(q); };
-    fr(a->d_items); fr(a->d_lhat); fr(a->d_tiles); fr(a->d_linv);
+    fr(a->d_items); fr(a->d_lhat); fr(a->d_linv);
     fr(a->d_gitems); fr(a->d_citems); fr(a->d_js);
     fr(a->YB); fr(a->Zb); fr(a->Lbw); fr(a->Ab); fr(a->fin); fr(a->d_desc); fr(a->d_pdesc);
+    fr(a->d_asm); fr(a->d_vitems); fr(a->d_voff); fr(a->d_chpos); fr(a->V);
     delete a;
 }
 
@@ -710,8 +730,6 @@ static int adj_build(selinv_plan_s *plan) {
         a->c_lptr.push_back((int64_t)a->citems.size());
         a->j_lptr.push_back((int64_t)a->js.size());
     }
-    a->tiles = f->h_tiles;          // (J, 64-row tile), deepest level first
-    a->tile_lptr = f->tile_lptr;
     for (int32_t K = 0; K < p.ns; K++) a->linv_work.push_back(make_int2(0, K));
     a->lhat_bptr.push_back(0);
     for (int b = 0; b < kNumBuckets; b++) {
@@ -723,8 +741,68 @@ static int adj_build(selinv_plan_s *plan) {
         }
         a->lhat_bptr.push_back((int)a->lhat_items.size());
     }
+    // update matrices: offsets, positions of every C_K entry in its parent's
+    // row list, extend-add items per level and child rank, lower tiles of V_K
+    a->v_off.assign(p.ns + 1, 0);
+    for (int32_t K = 0; K < p.ns; K++) {
+        const int64_t c = p.rowptr[K + 1] - p.rowptr[K] - (p.super_ptr[K + 1] - p.super_ptr[K]);
+        a->v_off[K + 1] = a->v_off[K] + c * c;
+    }
+    a->chpos.assign(std::max<int64_t>(p.rowptr[p.ns], 1), 0);
+    std::vector<int> rank(p.ns, 0), nchild(p.ns, 0);
+    for (int32_t K = 0; K < p.ns; K++) {
+        const int32_t P = p.sparent[K];
+        const int s = p.super_ptr[K + 1] - p.super_ptr[K];
+        if (P < 0) continue;
+        rank[K] = nchild[P]++;
+        const int32_t *RP = p.rows.data() + p.rowptr[P];
+        const int64_t mP = p.rowptr[P + 1] - p.rowptr[P];
+        int64_t t = 0;
+        for (int64_t r = p.rowptr[K] + s; r < p.rowptr[K + 1]; r++) {   // both lists ascending
+            while (t < mP && RP[t] < p.rows[r]) t++;
+            a->chpos[r] = (int32_t)t;
+        }
+    }
+    a->npass = 1;
+    for (int32_t K = 0; K < p.ns; K++) a->npass = std::max(a->npass, nchild[K]);
+    std::vector<int64_t> kid_ptr(p.ns + 1, 0);
+    for (int32_t K = 0; K < p.ns; K++) kid_ptr[K + 1] = kid_ptr[K] + nchild[K];
+    std::vector<int32_t> kids(std::max<int64_t>(kid_ptr[p.ns], 1));
+    for (int32_t K = 0; K < p.ns; K++)
+        if (p.sparent[K] >= 0) kids[kid_ptr[p.sparent[K]] + rank[K]] = K;
+    a->asm_lptr.assign(1, 0);
+    a->v_lptr.assign(1, 0);
+    for (int l = p.nlevels - 1; l >= 0; l--) {
+        for (int r = 0; r < a->npass; r++) {
+            for (int64_t e = p.level_ptr[l]; e < p.level_ptr[l + 1]; e++) {
+                const int32_t K = p.level_list[e];
+                if (r >= nchild[K]) continue;
+                const int32_t ch = kids[kid_ptr[K] + r];
+                const int64_t cc = a->v_off[ch + 1] - a->v_off[ch];
+                for (int64_t ck = 0; ck < (cc + 4095) / 4096; ck++) a->asm_items.push_back(make_int2(ch, (int)ck));
+            }
+            a->asm_lptr.push_back((int64_t)a->asm_items.size());
+        }
+        for (int64_t e = p.level_ptr[l]; e < p.level_ptr[l + 1]; e++) {
+            const int32_t K = p.level_list[e];
+            const int64_t c = p.rowptr[K + 1] - p.rowptr[K] - (p.super_ptr[K + 1] - p.super_ptr[K]);
+            const int nt = (int)((c + kSegB - 1) / kSegB);
+            for (int ti = 0; ti < nt; ti++)
+                for (int tj = 0; tj <= ti; tj++) a->vitems.push_back(make_int4(K, ti, tj, 0));
+        }
+        a->v_lptr.push_back((int64_t)a->vitems.size());
+    }
+    if ((rc = upl(&a->d_asm, a->asm_items)) || (rc = upl(&a->d_vitems, a->vitems)) ||
+        (rc = upl(&a->d_voff, a->v_off)) || (rc = upl(&a->d_chpos, a->chpos))) {
+        adjoint_release(a);
+        return rc;
+    }
+    if (cudaMalloc((void **)&a->V, 8 * (size_t)std::max<int64_t>(a->v_off[p.ns], 1)) != cudaSuccess) {
+        adjoint_release(a);
+        return SELINV_ERR_OOM;
+    }
     if ((rc = upl(&a->d_items, a->items)) || (rc = upl(&a->d_lhat, a->lhat_items)) ||
-        (rc = upl(&a->d_tiles, a->tiles)) || (rc = upl(&a->d_linv, a->linv_work)) ||
+        (rc = upl(&a->d_linv, a->linv_work)) ||
         (rc = upl(&a->d_gitems, a->gitems)) || (rc = upl(&a->d_citems, a->citems)) || (rc = upl(&a->d_js, a->js))) {
         adjoint_release(a);
         return rc;
@@ -761,6 +839,10 @@ static AdjDesc make_adesc(selinv_plan_s *plan, const double *L, const double *D,
     h.partial = static_cast<double *>(w.partial);
     h.counter = w.counter;
     h.fin = a->fin;
+    h.sparent = p.d_sparent;
+    h.v_off = a->d_voff;
+    h.chpos = a->d_chpos;
+    h.V = a->V;
     return h;
 }
 
@@ -815,12 +897,18 @@ extern "C" int selinv_adjoint(selinv_plan plan, selinv_dtype dtype, const void *
                            static_cast<const double *>(Z), static_cast<double *>(Lbar),
                            static_cast<double *>(Dbar));
     cudaMemcpyAsync(a->d_desc, &h, sizeof(h), cudaMemcpyHostToDevice, st);
+    cudaMemsetAsync(a->V, 0, 8 * (size_t)std::max<int64_t>(a->v_off[p.ns], 1), st);
     const int nl = p.nlevels;
     for (int li = 0; li < nl; li++) {  // deepest level first
-        const int64_t t0 = a->tile_lptr[li], t1 = a->tile_lptr[li + 1];
-        if (t1 > t0) { k_adj_pull<<<(int)(t1 - t0), 256, 0, st>>>(a->d_desc, a->d_tiles + t0, (int)(t1 - t0), t0); note_launch(); }
+        // the children's update matrices complete Zbar on K's panel and start V_K
+        for (int r = 0; r < a->npass; r++) {
+            const int64_t x0 = a->asm_lptr[li * a->npass + r], x1 = a->asm_lptr[li * a->npass + r + 1];
+            if (x1 > x0) { k_adj_asm<<<(int)(x1 - x0), 256, 0, st>>>(a->d_desc, a->d_asm + x0, (int)(x1 - x0)); note_launch(); }
+        }
         const int i0 = a->lvl_bucket_ptr[li * kNumBuckets], i1 = a->lvl_bucket_ptr[(li + 1) * kNumBuckets];
         if (i1 > i0) { k_adj_ybar<<<i1 - i0, 256, 0, st>>>(a->d_desc, a->d_items + i0, i1 - i0); note_launch(); }
+        const int64_t v0 = a->v_lptr[li], v1 = a->v_lptr[li + 1];
+        if (v1 > v0) { k_adj_vupd<<<(int)(v1 - v0), 256, 0, st>>>(a->d_desc, a->d_vitems + v0, (int)(v1 - v0)); note_launch(); }
         for (int b = 0; b < kNumBuckets; b++) {
             const int b0 = a->lvl_bucket_ptr[li * kNumBuckets + b], b1 = a->lvl_bucket_ptr[li * kNumBuckets + b + 1];
             launch_bucket(0, b, a->d_desc, a->d_items + b0, b1 - b0, st);
@@ -876,8 +964,14 @@ extern "C" int selinv_factor_adjoint(selinv_plan plan, selinv_dtype dtype, const
         launch_level_gemm(a, OP_FAC_U, li, st);
         if (j1 > j0) {
             k_fadj_ubar<<<(int)(j1 - j0), 256, 0, st>>>(a->d_desc, a->d_js + j0, (int)(j1 - j0));
-            k_fadj_dense<<<(int)(j1 - j0), 256, 128 * 128 * 8, st>>>(a->d_desc, a->d_js + j0, (int)(j1 - j0));
-            note_launch(2);
+            note_launch();
+        }
+        launch_level_gemm(a, OP_FAC_T3, li, st);
+        launch_level_gemm(a, OP_FAC_G1, li, st);
+        launch_level_gemm(a, OP_FAC_G2, li, st);
+        if (j1 > j0) {
+            k_fadj_fold<<<(int)(j1 - j0), 256, 0, st>>>(a->d_desc, a->d_js + j0, (int)(j1 - j0));
+            note_launch();
         }
     }
     if (f->nnzA > 0) {

@@ -21,6 +21,7 @@
 #include "common.cuh"
 #include "launch.h"
 #include "plan.h"
+#include "seg_update.cuh"
 
 namespace selinv {
 
@@ -37,6 +38,7 @@ __global__ void k_assemble(const int64_t *__restrict__ pos, const T *__restrict_
 template <typename T>
 __global__ void __launch_bounds__(256) k_fupdate(const FactorDesc *__restrict__ fd,
                                                  const int2 *__restrict__ tiles, int ntiles, int64_t tile0) {
+    __shared__ SegSmem<T> sm;
     const int w = blockIdx.x;
     if (w >= ntiles) return;
     const FactorDesc &F = *fd;
@@ -55,20 +57,18 @@ __global__ void __launch_bounds__(256) k_fupdate(const FactorDesc *__restrict__ 
         const int sK = F.super_ptr[K + 1] - F.super_ptr[K];
         const int64_t ldK = F.rowptr[K + 1] - F.rowptr[K];
         const int32_t *rel = F.relidx + F.rel_ptr[t];  // rel[p - st], p in [st, cK)
-        const T *LK = Lall + F.panel_off[K];
+        const T *LC = Lall + F.panel_off[K] + sK;      // L_K(p, k) = LC[k*ldK + p]
         const T *DK = Dall + F.super_ptr[K];
+        const int32_t *colq = F.rows + F.rowptr[K] + sK;
         __syncthreads();  // the previous segment's updates to this tile are complete
-        for (int e = threadIdx.x; e < np * nq; e += blockDim.x) {
-            const int p = pa + e % np, q = st + e / np;
-            if (p < q) continue;  // strictly upper part of J's diagonal block: not stored
-            T u = Sc<T>::zero();
-            for (int k = 0; k < sK; k++)
-                madd(u, mul(LK[(int64_t)k * ldK + sK + p], DK[k]), LK[(int64_t)k * ldK + sK + q]);
-            // the run's columns need not be consecutive columns of J: address by value
-            const int col = F.rows[F.rowptr[K] + sK + q] - fcJ;
-            T *dst = PJ + (int64_t)col * ldJ + rel[p - st];
+        auto x = [&](int pl, int k) { return mul(LC[(int64_t)k * ldK + pa + pl], DK[k]); };
+        auto y = [&](int ql, int k) { return LC[(int64_t)k * ldK + st + ql]; };
+        // the run's columns need not be consecutive columns of J: address by value
+        auto out = [&](int pl, int ql, T u) {
+            T *dst = PJ + (int64_t)(colq[st + ql] - fcJ) * ldJ + rel[pa + pl - st];
             *dst = sub(*dst, u);
-        }
+        };
+        seg_update<T>(pa, np, st, nq, sK, x, y, out, sm);
     }
 }
 

@@ -125,6 +125,7 @@ static int build_plan(PlanData &p, int32_t n, int32_t ns, const int32_t *super_p
         const int32_t fc = super_ptr[K], s = super_ptr[K + 1] - fc;
         const int64_t m = rowptr[K + 1] - rowptr[K];
         if (m < s) return SELINV_ERR_BAD_PATTERN;
+        if (s > SELINV_MAX_SUPERNODE) return SELINV_ERR_UNSUPPORTED;  // widest column tile of the kernels
         const int32_t *R = rowind + rowptr[K];
         for (int32_t j = 0; j < s; j++)
             if (R[j] != fc + j) return SELINV_ERR_BAD_PATTERN;

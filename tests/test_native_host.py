@@ -167,6 +167,13 @@ def test_rejects_malformed_plans(native):
     assert code(bad, par, rp, rows) == -1
     # bad sizes
     assert code(sp, par, rp, rows, ns_=-1) == -1
+    # one dense supernode of 129 columns: wider than the kernels' column tile
+    m = 129
+    rows_d = np.arange(m, dtype=np.int32)
+    assert code(np.array([0, m], np.int32), np.array([-1], np.int32), np.array([0, m], np.int64), rows_d,
+                n_=m, ns_=1) == native.SELINV_ERR_UNSUPPORTED
+    assert code(np.array([0, 128], np.int32), np.array([-1], np.int32), np.array([0, 128], np.int64),
+                rows_d[:128], n_=128, ns_=1) == 0
 
 
 def test_analysis_rejects_bad_csc(native):
