@@ -45,12 +45,6 @@ struct AdjDesc {
     const int64_t *panel_off;
     const int64_t *colbase, *relbase;
     const int32_t *relidx;
-    const int64_t *rel_ptr;
-    const int32_t *seg_K, *seg_start, *seg_end;
-    const int64_t *dseg_ptr;
-    const int32_t *dseg;
-    const int64_t *tseg_ptr;
-    const int4 *tseg;
     const int64_t *linv_off, *part_off;
     const double *L, *D, *Z, *LD, *Linv;
     double *Zb;       // working cotangent of A^{-1} (panels)
@@ -78,19 +72,7 @@ struct AdjData {
     std::vector<int2> gitems, citems;  // per level: (J, 32x32 tile) and (J, chunk | ntiles << 16)
     std::vector<int> js;               // per level: supernodes
     std::vector<int64_t> g_lptr, c_lptr, j_lptr;
-    // update matrices (multifrontal hand-off of Zbar(C,C) from child to parent)
-    std::vector<int64_t> v_off;
-    std::vector<int32_t> chpos;
-    std::vector<int2> asm_items;      // (child, 4096-entry chunk) per level and child pass
-    std::vector<int64_t> asm_lptr;    // [level * npass + pass]
-    int npass = 0;
-    std::vector<int4> vitems;         // (K, row tile, column tile) of the lower c x c per level
-    std::vector<int64_t> v_lptr;
-    int2 *d_asm = nullptr;
-    int4 *d_vitems = nullptr;
-    int64_t *d_voff = nullptr;
-    int32_t *d_chpos = nullptr;
-    double *V = nullptr;
+    double *V = nullptr;  // update matrices (tables shared with the factorization)
     Item *d_items = nullptr, *d_lhat = nullptr;
     int2 *d_linv = nullptr, *d_gitems = nullptr, *d_citems = nullptr;
     int *d_js = nullptr;
@@ -682,7 +664,7 @@ void adjoint_release(void *p) {
     fr(a->d_items); fr(a->d_lhat); fr(a->d_linv);
     fr(a->d_gitems); fr(a->d_citems); fr(a->d_js);
     fr(a->YB); fr(a->Zb); fr(a->Lbw); fr(a->Ab); fr(a->fin); fr(a->d_desc); fr(a->d_pdesc);
-    fr(a->d_asm); fr(a->d_vitems); fr(a->d_voff); fr(a->d_chpos); fr(a->V);
+    fr(a->V);
     delete a;
 }
 
@@ -741,63 +723,7 @@ static int adj_build(selinv_plan_s *plan) {
         }
         a->lhat_bptr.push_back((int)a->lhat_items.size());
     }
-    // update matrices: offsets, positions of every C_K entry in its parent's
-    // row list, extend-add items per level and child rank, lower tiles of V_K
-    a->v_off.assign(p.ns + 1, 0);
-    for (int32_t K = 0; K < p.ns; K++) {
-        const int64_t c = p.rowptr[K + 1] - p.rowptr[K] - (p.super_ptr[K + 1] - p.super_ptr[K]);
-        a->v_off[K + 1] = a->v_off[K] + c * c;
-    }
-    a->chpos.assign(std::max<int64_t>(p.rowptr[p.ns], 1), 0);
-    std::vector<int> rank(p.ns, 0), nchild(p.ns, 0);
-    for (int32_t K = 0; K < p.ns; K++) {
-        const int32_t P = p.sparent[K];
-        const int s = p.super_ptr[K + 1] - p.super_ptr[K];
-        if (P < 0) continue;
-        rank[K] = nchild[P]++;
-        const int32_t *RP = p.rows.data() + p.rowptr[P];
-        const int64_t mP = p.rowptr[P + 1] - p.rowptr[P];
-        int64_t t = 0;
-        for (int64_t r = p.rowptr[K] + s; r < p.rowptr[K + 1]; r++) {   // both lists ascending
-            while (t < mP && RP[t] < p.rows[r]) t++;
-            a->chpos[r] = (int32_t)t;
-        }
-    }
-    a->npass = 1;
-    for (int32_t K = 0; K < p.ns; K++) a->npass = std::max(a->npass, nchild[K]);
-    std::vector<int64_t> kid_ptr(p.ns + 1, 0);
-    for (int32_t K = 0; K < p.ns; K++) kid_ptr[K + 1] = kid_ptr[K] + nchild[K];
-    std::vector<int32_t> kids(std::max<int64_t>(kid_ptr[p.ns], 1));
-    for (int32_t K = 0; K < p.ns; K++)
-        if (p.sparent[K] >= 0) kids[kid_ptr[p.sparent[K]] + rank[K]] = K;
-    a->asm_lptr.assign(1, 0);
-    a->v_lptr.assign(1, 0);
-    for (int l = p.nlevels - 1; l >= 0; l--) {
-        for (int r = 0; r < a->npass; r++) {
-            for (int64_t e = p.level_ptr[l]; e < p.level_ptr[l + 1]; e++) {
-                const int32_t K = p.level_list[e];
-                if (r >= nchild[K]) continue;
-                const int32_t ch = kids[kid_ptr[K] + r];
-                const int64_t cc = a->v_off[ch + 1] - a->v_off[ch];
-                for (int64_t ck = 0; ck < (cc + 4095) / 4096; ck++) a->asm_items.push_back(make_int2(ch, (int)ck));
-            }
-            a->asm_lptr.push_back((int64_t)a->asm_items.size());
-        }
-        for (int64_t e = p.level_ptr[l]; e < p.level_ptr[l + 1]; e++) {
-            const int32_t K = p.level_list[e];
-            const int64_t c = p.rowptr[K + 1] - p.rowptr[K] - (p.super_ptr[K + 1] - p.super_ptr[K]);
-            const int nt = (int)((c + kSegB - 1) / kSegB);
-            for (int ti = 0; ti < nt; ti++)
-                for (int tj = 0; tj <= ti; tj++) a->vitems.push_back(make_int4(K, ti, tj, 0));
-        }
-        a->v_lptr.push_back((int64_t)a->vitems.size());
-    }
-    if ((rc = upl(&a->d_asm, a->asm_items)) || (rc = upl(&a->d_vitems, a->vitems)) ||
-        (rc = upl(&a->d_voff, a->v_off)) || (rc = upl(&a->d_chpos, a->chpos))) {
-        adjoint_release(a);
-        return rc;
-    }
-    if (cudaMalloc((void **)&a->V, 8 * (size_t)std::max<int64_t>(a->v_off[p.ns], 1)) != cudaSuccess) {
+    if (cudaMalloc((void **)&a->V, 8 * (size_t)std::max<int64_t>(f->u_off[p.ns], 1)) != cudaSuccess) {
         adjoint_release(a);
         return SELINV_ERR_OOM;
     }
@@ -827,10 +753,7 @@ static AdjDesc make_adesc(selinv_plan_s *plan, const double *L, const double *D,
     Workspace &w = plan->ws[0];
     AdjDesc h;
     h.super_ptr = p.d_super_ptr; h.rowptr = p.d_rowptr; h.rows = p.d_rows; h.panel_off = p.d_panel_off;
-    h.colbase = p.d_colbase; h.relbase = p.d_relbase; h.relidx = p.d_relidx; h.rel_ptr = f->d_rel_ptr;
-    h.seg_K = f->d_seg_K; h.seg_start = f->d_seg_start; h.seg_end = f->d_seg_end;
-    h.dseg_ptr = f->d_dseg_ptr; h.dseg = f->d_dseg;
-    h.tseg_ptr = f->d_tseg_ptr; h.tseg = f->d_tseg;
+    h.colbase = p.d_colbase; h.relbase = p.d_relbase; h.relidx = p.d_relidx;
     h.linv_off = p.d_linv_off; h.part_off = p.d_part_off;
     h.L = L; h.D = D; h.Z = Z;
     h.LD = static_cast<const double *>(w.LD);
@@ -840,8 +763,8 @@ static AdjDesc make_adesc(selinv_plan_s *plan, const double *L, const double *D,
     h.counter = w.counter;
     h.fin = a->fin;
     h.sparent = p.d_sparent;
-    h.v_off = a->d_voff;
-    h.chpos = a->d_chpos;
+    h.v_off = f->d_uoff;
+    h.chpos = f->d_chpos;
     h.V = a->V;
     return h;
 }
@@ -897,18 +820,19 @@ extern "C" int selinv_adjoint(selinv_plan plan, selinv_dtype dtype, const void *
                            static_cast<const double *>(Z), static_cast<double *>(Lbar),
                            static_cast<double *>(Dbar));
     cudaMemcpyAsync(a->d_desc, &h, sizeof(h), cudaMemcpyHostToDevice, st);
-    cudaMemsetAsync(a->V, 0, 8 * (size_t)std::max<int64_t>(a->v_off[p.ns], 1), st);
+    FactorData *f = plan->factor;
+    cudaMemsetAsync(a->V, 0, 8 * (size_t)std::max<int64_t>(f->u_off[p.ns], 1), st);
     const int nl = p.nlevels;
     for (int li = 0; li < nl; li++) {  // deepest level first
         // the children's update matrices complete Zbar on K's panel and start V_K
-        for (int r = 0; r < a->npass; r++) {
-            const int64_t x0 = a->asm_lptr[li * a->npass + r], x1 = a->asm_lptr[li * a->npass + r + 1];
-            if (x1 > x0) { k_adj_asm<<<(int)(x1 - x0), 256, 0, st>>>(a->d_desc, a->d_asm + x0, (int)(x1 - x0)); note_launch(); }
+        for (int r = 0; r < f->npass; r++) {
+            const int64_t x0 = f->asm_lptr[li * f->npass + r], x1 = f->asm_lptr[li * f->npass + r + 1];
+            if (x1 > x0) { k_adj_asm<<<(int)(x1 - x0), 256, 0, st>>>(a->d_desc, f->d_asm + x0, (int)(x1 - x0)); note_launch(); }
         }
         const int i0 = a->lvl_bucket_ptr[li * kNumBuckets], i1 = a->lvl_bucket_ptr[(li + 1) * kNumBuckets];
         if (i1 > i0) { k_adj_ybar<<<i1 - i0, 256, 0, st>>>(a->d_desc, a->d_items + i0, i1 - i0); note_launch(); }
-        const int64_t v0 = a->v_lptr[li], v1 = a->v_lptr[li + 1];
-        if (v1 > v0) { k_adj_vupd<<<(int)(v1 - v0), 256, 0, st>>>(a->d_desc, a->d_vitems + v0, (int)(v1 - v0)); note_launch(); }
+        const int64_t v0 = f->u_lptr[li], v1 = f->u_lptr[li + 1];
+        if (v1 > v0) { k_adj_vupd<<<(int)(v1 - v0), 256, 0, st>>>(a->d_desc, f->d_uitems + v0, (int)(v1 - v0)); note_launch(); }
         for (int b = 0; b < kNumBuckets; b++) {
             const int b0 = a->lvl_bucket_ptr[li * kNumBuckets + b], b1 = a->lvl_bucket_ptr[li * kNumBuckets + b + 1];
             launch_bucket(0, b, a->d_desc, a->d_items + b0, b1 - b0, st);

@@ -1,18 +1,16 @@
-// Prerequisite factorization A = L D L^T without pivoting, supernodal,
-// left-looking, level by level from the leaves (Sec. IV of the paper uses a
-// supernodal factorization with a symmetric permutation and no dynamic
-// pivoting; Sec. II-C: LDL^T for symmetric A).
+// Prerequisite factorization A = L D L^T without pivoting, supernodal, level
+// by level from the leaves (Sec. IV of the paper uses a supernodal
+// factorization with a symmetric permutation and no dynamic pivoting; Sec.
+// II-C: LDL^T for symmetric A), in multifrontal form:
 //
 //   k_assemble  scatter A's CSC values into the panels (after a memset)
-//   k_fupdate   one row tile of supernode J pulls the updates of every
-//               descendant K whose C meets J's columns:
-//                 panel_J(rel(p), col(q)) -= sum_k L_K(p,k) D_K(k) L_K(q,k)
-//               over the run of C_K owned by J (p >= q) -- the same owner
-//               segments and relative indices the selected inversion
-//               gathers with.  Each tile owns its rows: no atomics,
-//               a fixed descendant order: deterministic.
+//   k_fasm      extend-add of each child's update matrix U_child into its
+//               parent J: entries whose column is one of J's columns go to
+//               J's panel, the rest into U_J (one launch per child rank, so
+//               no two writers meet; fixed order: deterministic)
 //   k_fdiag     dense LDL^T of J's diagonal block in place (one CTA)
 //   k_ftrsm     L(C,J) = A(C,J) L_JJ^{-T} D_J^{-1}, one thread per row
+//   k_fupd      U_J -= L_CJ D_J L_CJ^T (lower c x c, 64 x 64 tiles)
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -35,41 +33,62 @@ __global__ void k_assemble(const int64_t *__restrict__ pos, const T *__restrict_
         L[pos[e]] = vals[e];
 }
 
+// Extend-add of one child's update matrix into its parent J: entry (a, b),
+// a >= b, of U_child lands at rows(J) positions (pa, pb) -- in J's panel when
+// the column C_child[b] is one of J's columns, else in U_J.  One launch per
+// child rank: two children of one parent never run together.
 template <typename T>
-__global__ void __launch_bounds__(256) k_fupdate(const FactorDesc *__restrict__ fd,
-                                                 const int2 *__restrict__ tiles, int ntiles, int64_t tile0) {
+__global__ void __launch_bounds__(256) k_fasm(const FactorDesc *__restrict__ fd, const int2 *__restrict__ items,
+                                              int nitems) {
+    const int w = blockIdx.x;
+    if (w >= nitems) return;
+    const FactorDesc &F = *fd;
+    const int ch = items[w].x, chunk = items[w].y;
+    const int J = F.sparent[ch];
+    const int sch = F.super_ptr[ch + 1] - F.super_ptr[ch];
+    const int cch = (int)(F.rowptr[ch + 1] - F.rowptr[ch] - sch);
+    const int sJ = F.super_ptr[J + 1] - F.super_ptr[J];
+    const int64_t ldJ = F.rowptr[J + 1] - F.rowptr[J];
+    const int cJ = (int)(ldJ - sJ);
+    const int32_t *pos = F.chpos + F.rowptr[ch] + sch;
+    const T *Uc = static_cast<const T *>(F.U) + F.u_off[ch];
+    T *UJ = static_cast<T *>(F.U) + F.u_off[J];
+    T *PJ = static_cast<T *>(F.L) + F.panel_off[J];
+    const int64_t cc = (int64_t)cch * cch;
+    for (int64_t e = (int64_t)chunk * 4096 + threadIdx.x; e < cc && e < (int64_t)(chunk + 1) * 4096; e += 256) {
+        const int a = (int)(e % cch), b = (int)(e / cch);
+        if (a < b) continue;
+        const T v = Uc[e];
+        const int pa = pos[a], pb = pos[b];
+        T *dst = pb < sJ ? PJ + (int64_t)pb * ldJ + pa : UJ + (int64_t)(pb - sJ) * cJ + (pa - sJ);
+        *dst = add(*dst, v);
+    }
+}
+
+// U_J -= L_CJ D_J L_CJ^T on one 64 x 64 tile of the lower c x c triangle
+template <typename T>
+__global__ void __launch_bounds__(256) k_fupd(const FactorDesc *__restrict__ fd, const int4 *__restrict__ items,
+                                              int nitems) {
     __shared__ SegSmem<T> sm;
     const int w = blockIdx.x;
-    if (w >= ntiles) return;
+    if (w >= nitems) return;
     const FactorDesc &F = *fd;
-    const int J = tiles[w].x;
-    const int64_t ldJ = F.rowptr[J + 1] - F.rowptr[J];
-    const int fcJ = F.super_ptr[J];
-    T *PJ = static_cast<T *>(F.L) + F.panel_off[J];
-    const T *Lall = static_cast<const T *>(F.L);
-    const T *Dall = static_cast<const T *>(F.D);
-    // (segment, p-range) pairs whose target rows fall in this tile, precomputed
-    for (int64_t li = F.tseg_ptr[tile0 + w]; li < F.tseg_ptr[tile0 + w + 1]; li++) {
-        const int4 ts = F.tseg[li];
-        const int t = ts.x, pa = ts.y, np = ts.z - ts.y;
-        const int K = F.seg_K[t];
-        const int st = F.seg_start[t], nq = F.seg_end[t] - st;
-        const int sK = F.super_ptr[K + 1] - F.super_ptr[K];
-        const int64_t ldK = F.rowptr[K + 1] - F.rowptr[K];
-        const int32_t *rel = F.relidx + F.rel_ptr[t];  // rel[p - st], p in [st, cK)
-        const T *LC = Lall + F.panel_off[K] + sK;      // L_K(p, k) = LC[k*ldK + p]
-        const T *DK = Dall + F.super_ptr[K];
-        const int32_t *colq = F.rows + F.rowptr[K] + sK;
-        __syncthreads();  // the previous segment's updates to this tile are complete
-        auto x = [&](int pl, int k) { return mul(LC[(int64_t)k * ldK + pa + pl], DK[k]); };
-        auto y = [&](int ql, int k) { return LC[(int64_t)k * ldK + st + ql]; };
-        // the run's columns need not be consecutive columns of J: address by value
-        auto out = [&](int pl, int ql, T u) {
-            T *dst = PJ + (int64_t)(colq[st + ql] - fcJ) * ldJ + rel[pa + pl - st];
-            *dst = sub(*dst, u);
-        };
-        seg_update<T>(pa, np, st, nq, sK, x, y, out, sm);
-    }
+    const int J = items[w].x, ti = items[w].y, tj = items[w].z;
+    const int sJ = F.super_ptr[J + 1] - F.super_ptr[J];
+    const int64_t ld = F.rowptr[J + 1] - F.rowptr[J];
+    const int c = (int)(ld - sJ);
+    const T *LC = static_cast<const T *>(F.L) + F.panel_off[J] + sJ;   // L(p, k) = LC[k*ld + p]
+    const T *DJ = static_cast<const T *>(F.D) + F.super_ptr[J];
+    T *UJ = static_cast<T *>(F.U) + F.u_off[J];
+    const int pa = ti * kSegB, st = tj * kSegB;
+    const int np = c - pa < kSegB ? c - pa : kSegB, nq = c - st < kSegB ? c - st : kSegB;
+    auto x = [&](int pl, int k) { return mul(LC[(int64_t)k * ld + pa + pl], DJ[k]); };
+    auto y = [&](int ql, int k) { return LC[(int64_t)k * ld + st + ql]; };
+    auto out = [&](int pl, int ql, T v) {
+        T *dst = UJ + (int64_t)(st + ql) * c + pa + pl;
+        *dst = sub(*dst, v);
+    };
+    seg_update<T>(pa, np, st, nq, sJ, x, y, out, sm);
 }
 
 template <typename T>
@@ -143,9 +162,8 @@ void factor_release(selinv_plan_s *plan) {
     FactorData *f = plan->factor;
     if (!f) return;
     auto fr = [](void *p) { if (p) cudaFree(p); };
-    fr(f->d_a_pos); fr(f->d_seg_K); fr(f->d_seg_start); fr(f->d_seg_end); fr(f->d_seg_coloff);
-    fr(f->d_dseg); fr(f->d_dseg_ptr); fr(f->d_rel_ptr); fr(f->d_tiles); fr(f->d_js); fr(f->d_desc);
-    fr(f->d_tseg_ptr); fr(f->d_tseg);
+    fr(f->d_a_pos); fr(f->d_tiles); fr(f->d_js); fr(f->d_desc);
+    fr(f->d_asm); fr(f->d_uitems); fr(f->d_uoff); fr(f->d_chpos); fr(f->U);
     adjoint_release(f->adj);
     delete f;
     plan->factor = nullptr;
@@ -160,30 +178,14 @@ static int up(X **d, const std::vector<X> &h) {
     return SELINV_OK;
 }
 
-// segment tables (descendant lists per owner) shared by factor and adjoint
+// launch lists and update-matrix tables, shared by the factorization and
+// the selected-inversion adjoint
 int factor_tables(selinv_plan_s *plan) {
     FactorData *f = plan->factor;
-    if (f->d_dseg) return SELINV_OK;
+    if (f->d_desc) return SELINV_OK;
     const PlanData &p = plan->data;
     int rc = ensure_device(plan->data);
     if (rc) return rc;
-    const size_t nseg = p.seg_owner.size();
-    std::vector<int32_t> segK(nseg), segEnd(nseg);
-    for (int32_t K = 0; K < p.ns; K++) {
-        const int64_t c = p.rowptr[K + 1] - p.rowptr[K] - (p.super_ptr[K + 1] - p.super_ptr[K]);
-        for (int64_t t = p.seg_ptr[K]; t < p.seg_ptr[K + 1]; t++) {
-            segK[t] = K;
-            segEnd[t] = (t + 1 < p.seg_ptr[K + 1]) ? p.seg_start[t + 1] : (int32_t)c;
-        }
-    }
-    std::vector<int64_t> dptr(p.ns + 1, 0);
-    for (size_t t = 0; t < nseg; t++) dptr[p.seg_owner[t] + 1]++;
-    for (int32_t J = 0; J < p.ns; J++) dptr[J + 1] += dptr[J];
-    std::vector<int32_t> dseg(std::max<size_t>(1, nseg));
-    {
-        std::vector<int64_t> fl(dptr.begin(), dptr.end() - 1);
-        for (size_t t = 0; t < nseg; t++) dseg[fl[p.seg_owner[t]]++] = (int32_t)t;  // ascending K
-    }
     // per-level launch lists, leaves first
     f->h_tiles.clear(); f->h_js.clear();
     f->tile_lptr.assign(1, 0); f->j_lptr.assign(1, 0);
@@ -197,46 +199,64 @@ int factor_tables(selinv_plan_s *plan) {
         f->tile_lptr.push_back((int64_t)f->h_tiles.size());
         f->j_lptr.push_back((int64_t)f->h_js.size());
     }
-    // per panel tile (launch order): the (segment, p-range) pairs that land in
-    // it, in ascending segment order (the fixed summation order)
-    {
-        std::vector<int64_t> tile_of(p.ns + 1, 0);      // index of (J, tile 0) in h_tiles
-        for (size_t w = 0; w < f->h_tiles.size(); w++)
-            if (f->h_tiles[w].y == 0) tile_of[f->h_tiles[w].x] = (int64_t)w;
-        std::vector<std::vector<int4>> lists(f->h_tiles.size());
-        for (int32_t J = 0; J < p.ns; J++)
-            for (int64_t di = dptr[J]; di < dptr[J + 1]; di++) {
-                const int32_t t = dseg[di];
-                const int32_t K = segK[t];
-                const int64_t cK = p.rowptr[K + 1] - p.rowptr[K] - (p.super_ptr[K + 1] - p.super_ptr[K]);
-                const int32_t *rel = p.relidx.data() + p.rel_ptr[t];
-                int64_t q = p.seg_start[t];
-                while (q < cK) {
-                    const int32_t tl = rel[q - p.seg_start[t]] / kFT;
-                    int64_t qe = q;
-                    while (qe < cK && rel[qe - p.seg_start[t]] / kFT == tl) qe++;
-                    lists[tile_of[J] + tl].push_back(make_int4(t, (int)q, (int)qe, 0));
-                    q = qe;
-                }
-            }
-        std::vector<int64_t> tptr(f->h_tiles.size() + 1, 0);
-        std::vector<int4> tseg;
-        for (size_t w = 0; w < lists.size(); w++) {
-            tseg.insert(tseg.end(), lists[w].begin(), lists[w].end());
-            tptr[w + 1] = (int64_t)tseg.size();
-        }
-        if ((rc = up(&f->d_tseg_ptr, tptr))) return rc;
-        if ((rc = up(&f->d_tseg, tseg))) return rc;
+    // update matrices: offsets; the position of every C_K entry in its
+    // parent's row list (closure: C_K lies inside rows(parent)); children by rank
+    f->u_off.assign(p.ns + 1, 0);
+    for (int32_t K = 0; K < p.ns; K++) {
+        const int64_t c = p.rowptr[K + 1] - p.rowptr[K] - (p.super_ptr[K + 1] - p.super_ptr[K]);
+        f->u_off[K + 1] = f->u_off[K] + c * c;
     }
-    if ((rc = up(&f->d_seg_K, segK))) return rc;
-    if ((rc = up(&f->d_seg_start, p.seg_start))) return rc;
-    if ((rc = up(&f->d_seg_end, segEnd))) return rc;
-    if ((rc = up(&f->d_seg_coloff, p.seg_coloff))) return rc;
-    if ((rc = up(&f->d_dseg_ptr, dptr))) return rc;
-    if ((rc = up(&f->d_dseg, dseg))) return rc;
-    if ((rc = up(&f->d_rel_ptr, p.rel_ptr))) return rc;
+    f->chpos.assign(std::max<int64_t>(p.rowptr[p.ns], 1), 0);
+    std::vector<int> rank(p.ns, 0), nchild(p.ns, 0);
+    for (int32_t K = 0; K < p.ns; K++) {
+        const int32_t P = p.sparent[K];
+        if (P < 0) continue;
+        rank[K] = nchild[P]++;
+        const int s = p.super_ptr[K + 1] - p.super_ptr[K];
+        const int32_t *RP = p.rows.data() + p.rowptr[P];
+        const int64_t mP = p.rowptr[P + 1] - p.rowptr[P];
+        int64_t t = 0;
+        for (int64_t r = p.rowptr[K] + s; r < p.rowptr[K + 1]; r++) {   // both lists ascending
+            while (t < mP && RP[t] < p.rows[r]) t++;
+            f->chpos[r] = (int32_t)t;
+        }
+    }
+    f->npass = 1;
+    for (int32_t K = 0; K < p.ns; K++) f->npass = std::max(f->npass, nchild[K]);
+    std::vector<int64_t> kid_ptr(p.ns + 1, 0);
+    for (int32_t K = 0; K < p.ns; K++) kid_ptr[K + 1] = kid_ptr[K] + nchild[K];
+    std::vector<int32_t> kids(std::max<int64_t>(kid_ptr[p.ns], 1));
+    for (int32_t K = 0; K < p.ns; K++)
+        if (p.sparent[K] >= 0) kids[kid_ptr[p.sparent[K]] + rank[K]] = K;
+    f->asm_items.clear(); f->uitems.clear();
+    f->asm_lptr.assign(1, 0);
+    f->u_lptr.assign(1, 0);
+    for (int l = p.nlevels - 1; l >= 0; l--) {
+        for (int r = 0; r < f->npass; r++) {
+            for (int64_t e = p.level_ptr[l]; e < p.level_ptr[l + 1]; e++) {
+                const int32_t K = p.level_list[e];
+                if (r >= nchild[K]) continue;
+                const int32_t ch = kids[kid_ptr[K] + r];
+                const int64_t cc = f->u_off[ch + 1] - f->u_off[ch];
+                for (int64_t ck = 0; ck < (cc + 4095) / 4096; ck++) f->asm_items.push_back(make_int2(ch, (int)ck));
+            }
+            f->asm_lptr.push_back((int64_t)f->asm_items.size());
+        }
+        for (int64_t e = p.level_ptr[l]; e < p.level_ptr[l + 1]; e++) {
+            const int32_t K = p.level_list[e];
+            const int64_t c = p.rowptr[K + 1] - p.rowptr[K] - (p.super_ptr[K + 1] - p.super_ptr[K]);
+            const int nt = (int)((c + kSegB - 1) / kSegB);
+            for (int ti = 0; ti < nt; ti++)
+                for (int tj = 0; tj <= ti; tj++) f->uitems.push_back(make_int4(K, ti, tj, 0));
+        }
+        f->u_lptr.push_back((int64_t)f->uitems.size());
+    }
     if ((rc = up(&f->d_tiles, f->h_tiles))) return rc;
     if ((rc = up(&f->d_js, f->h_js))) return rc;
+    if ((rc = up(&f->d_asm, f->asm_items))) return rc;
+    if ((rc = up(&f->d_uitems, f->uitems))) return rc;
+    if ((rc = up(&f->d_uoff, f->u_off))) return rc;
+    if ((rc = up(&f->d_chpos, f->chpos))) return rc;
     if (cudaMalloc((void **)&f->d_desc, sizeof(FactorDesc)) != cudaSuccess) return SELINV_ERR_OOM;
     return SELINV_OK;
 }
@@ -246,19 +266,13 @@ FactorDesc *factor_desc(selinv_plan_s *plan, void *L, void *D, cudaStream_t st) 
     const PlanData &p = plan->data;
     FactorDesc h;
     h.super_ptr = p.d_super_ptr;
+    h.sparent = p.d_sparent;
     h.rowptr = p.d_rowptr;
     h.rows = p.d_rows;
     h.panel_off = p.d_panel_off;
-    h.relidx = p.d_relidx;
-    h.rel_ptr = f->d_rel_ptr;
-    h.seg_K = f->d_seg_K;
-    h.seg_start = f->d_seg_start;
-    h.seg_end = f->d_seg_end;
-    h.seg_coloff = f->d_seg_coloff;
-    h.dseg_ptr = f->d_dseg_ptr;
-    h.dseg = f->d_dseg;
-    h.tseg_ptr = f->d_tseg_ptr;
-    h.tseg = f->d_tseg;
+    h.u_off = f->d_uoff;
+    h.chpos = f->d_chpos;
+    h.U = f->U;
     h.L = L;
     h.D = D;
     h.status = p.d_status;
@@ -270,8 +284,17 @@ template <typename T>
 static int factor_t(selinv_plan_s *plan, const void *A, void *L, void *D, cudaStream_t st) {
     FactorData *f = plan->factor;
     const PlanData &p = plan->data;
+    const size_t ubytes = sizeof(T) * (size_t)std::max<int64_t>(f->u_off[p.ns], 1);
+    if (f->U_bytes < ubytes) {
+        if (f->U) cudaFree(f->U);
+        f->U = nullptr;
+        f->U_bytes = 0;
+        if (cudaMalloc(&f->U, ubytes) != cudaSuccess) return SELINV_ERR_OOM;
+        f->U_bytes = ubytes;
+    }
     FactorDesc *fd = factor_desc(plan, L, D, st);
     if (cudaMemsetAsync(L, 0, sizeof(T) * (size_t)p.nnz, st) != cudaSuccess) return SELINV_ERR_CUDA;
+    if (cudaMemsetAsync(f->U, 0, ubytes, st) != cudaSuccess) return SELINV_ERR_CUDA;
     if (f->nnzA > 0) {
         const int blocks = (int)std::min<int64_t>((f->nnzA + 255) / 256, 152 * 8);
         k_assemble<T><<<blocks, 256, 0, st>>>(f->d_a_pos, static_cast<const T *>(A), f->nnzA, static_cast<T *>(L));
@@ -279,11 +302,17 @@ static int factor_t(selinv_plan_s *plan, const void *A, void *L, void *D, cudaSt
     }
     const int nl = (int)f->tile_lptr.size() - 1;
     for (int l = 0; l < nl; l++) {
+        // the children's update matrices complete J's panel and start U_J
+        for (int r = 0; r < f->npass; r++) {
+            const int64_t x0 = f->asm_lptr[l * f->npass + r], x1 = f->asm_lptr[l * f->npass + r + 1];
+            if (x1 > x0) { k_fasm<T><<<(int)(x1 - x0), 256, 0, st>>>(fd, f->d_asm + x0, (int)(x1 - x0)); note_launch(); }
+        }
         const int64_t t0 = f->tile_lptr[l], t1 = f->tile_lptr[l + 1];
         const int64_t j0 = f->j_lptr[l], j1 = f->j_lptr[l + 1];
-        if (t1 > t0) k_fupdate<T><<<(int)(t1 - t0), 256, 0, st>>>(fd, f->d_tiles + t0, (int)(t1 - t0), t0);
+        const int64_t u0 = f->u_lptr[l], u1 = f->u_lptr[l + 1];
         if (j1 > j0) k_fdiag<T><<<(int)(j1 - j0), 256, 0, st>>>(fd, f->d_js + j0, (int)(j1 - j0));
         if (t1 > t0) k_ftrsm<T><<<(int)(t1 - t0), kFT, 0, st>>>(fd, f->d_tiles + t0, (int)(t1 - t0));
+        if (u1 > u0) k_fupd<T><<<(int)(u1 - u0), 256, 0, st>>>(fd, f->d_uitems + u0, (int)(u1 - u0));
         note_launch(3);
     }
     return cudaGetLastError() == cudaSuccess ? SELINV_OK : SELINV_ERR_CUDA;

@@ -116,16 +116,13 @@ int run_schedule(Schedule &S, cudaStream_t st, bool use_graph);
 // factorization / adjoint state
 struct FactorDesc {
     const int32_t *super_ptr;
+    const int32_t *sparent;
     const int64_t *rowptr;
     const int32_t *rows;
     const int64_t *panel_off;
-    const int32_t *relidx;
-    const int64_t *rel_ptr;
-    const int32_t *seg_K, *seg_start, *seg_end, *seg_coloff;
-    const int64_t *dseg_ptr;  // [ns+1] segments owned by J (descendant updates)
-    const int32_t *dseg;
-    const int64_t *tseg_ptr;  // per 64-row panel tile (launch order): its (segment, pa, pb) list
-    const int4 *tseg;
+    const int64_t *u_off;     // [ns+1] update matrix of K: c x c column-major at U + u_off[K]
+    const int32_t *chpos;     // per row-list entry of C_K: its position in rows(parent(K))
+    void *U;                  // update matrices (element type of the factorization)
     void *L;
     void *D;
     int *status;
@@ -136,17 +133,27 @@ struct FactorData {
     int64_t nnzA = 0;
     std::vector<int64_t> a_pos;       // panel position of every stored entry of A
     int64_t *d_a_pos = nullptr;
-    int32_t *d_seg_K = nullptr, *d_seg_start = nullptr, *d_seg_end = nullptr, *d_seg_coloff = nullptr;
-    int32_t *d_dseg = nullptr;
-    int64_t *d_dseg_ptr = nullptr, *d_rel_ptr = nullptr;
-    int64_t *d_tseg_ptr = nullptr;
-    int4 *d_tseg = nullptr;
-    // launch lists
-    std::vector<int2> h_tiles;        // (J, row tile) per level, leaves first
+    // launch lists, leaves first
+    std::vector<int2> h_tiles;        // (J, row tile) per level
     std::vector<int> h_js;            // J per level
     std::vector<int64_t> tile_lptr, j_lptr;
     int2 *d_tiles = nullptr;
     int *d_js = nullptr;
+    // update matrices (multifrontal hand-off from child to parent; shared
+    // with the selected-inversion adjoint)
+    std::vector<int64_t> u_off;
+    std::vector<int32_t> chpos;
+    std::vector<int2> asm_items;      // (child, 4096-entry chunk) per level and child rank
+    std::vector<int64_t> asm_lptr;    // [level * npass + rank]
+    int npass = 1;
+    std::vector<int4> uitems;         // (K, row tile, column tile) of the lower c x c, per level
+    std::vector<int64_t> u_lptr;
+    int2 *d_asm = nullptr;
+    int4 *d_uitems = nullptr;
+    int64_t *d_uoff = nullptr;
+    int32_t *d_chpos = nullptr;
+    void *U = nullptr;
+    size_t U_bytes = 0;
     FactorDesc *d_desc = nullptr;
     const void *key_L = nullptr, *key_D = nullptr;
     int key_dtype = -1;
