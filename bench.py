@@ -135,9 +135,18 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def kernel_source_hash() -> str:
+KERNEL_SOURCES = {
+    "k_selinv_oz": ("kernels_ozaki.cu", "common.cuh"),
+    "k_diag": ("kernels_ozaki.cu", "common.cuh"),
+}
+DEFAULT_SOURCES = ("kernels_selinv.cu", "tile_gemm.cuh", "common.cuh")
+
+
+def kernel_source_hash(kernel: str) -> str:
+    """Hash of the sources that define `kernel` (a traffic figure taken on
+    other sources no longer applies)."""
     h = hashlib.sha256()
-    for f in ("kernels_selinv.cu", "common.cuh"):
+    for f in KERNEL_SOURCES.get(kernel, DEFAULT_SOURCES):
         with open(os.path.join(ROOT, "paper_1604_02528_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -149,7 +158,7 @@ def ncu_traffic(kernel: str):
     path = os.path.join(ROOT, "profiles", "ncu_traffic.txt")
     if not os.path.exists(path):
         return None
-    want = kernel_source_hash()
+    want = kernel_source_hash(kernel)
     for line in open(path):
         parts = line.split()
         if len(parts) >= 3 and parts[0] == kernel and parts[1] == want:
@@ -186,6 +195,17 @@ def variant_plain(ctx, dt, L, D, Z, stream, flush, N):
     o.schedule = N.SELINV_SCHED_PLAIN
     N.selinv_plan_set_opts(ctx.plan, o)
     ms = time_calls(lambda: N.selinv_numeric(ctx.plan, dt, L, D, Z, stream), stream, 1, 2, flush)
+    N.selinv_plan_set_opts(ctx.plan, N.selinv_default_opts())
+    return ms
+
+
+def variant_schedule(ctx, dt, L, D, Z, stream, flush, N, schedule, fast):
+    """Another schedule / contraction choice on the same inputs."""
+    o = N.selinv_default_opts()
+    o.schedule = schedule
+    o.fast_contraction = fast
+    N.selinv_plan_set_opts(ctx.plan, o)
+    ms = time_calls(lambda: N.selinv_numeric(ctx.plan, dt, L, D, Z, stream), stream, 2, 3, flush)
     N.selinv_plan_set_opts(ctx.plan, N.selinv_default_opts())
     return ms
 
@@ -438,6 +458,10 @@ def main():
         variants = {"level_ms": round(ms_step, 3)}
         variants["plain_ms"] = round(variant_plain(ctx, dt, L, D, Z, stream, flush, N), 3)
         variants["level_over_plain_speedup"] = round(variants["plain_ms"] / ms_step, 3)
+        variants["level_dfma_ms"] = round(variant_schedule(ctx, dt, L, D, Z, stream, flush, N,
+                                                           N.SELINV_SCHED_LEVEL, 0), 3)
+        variants["persistent_dfma_ms"] = round(variant_schedule(ctx, dt, L, D, Z, stream, flush, N,
+                                                                N.SELINV_SCHED_PERSISTENT, 0), 3)
         variants["batched"] = variant_batched(dev, stream, flush, N, args.batch_poles, 1.0)
         variants["adjoint"] = variant_adjoint(dev, stream, flush, N)
 

@@ -60,6 +60,37 @@ __device__ __forceinline__ void digits7(double x, int E, int d[kDig]) {
     }
 }
 
+// (hi * 2^32 + lo) * 2^(sc - 48) as a double, rounded once to nearest even,
+// with integer operations only (the FP64 pipe is GB300's scarcest unit).
+__device__ __forceinline__ double fixed_to_double(long long hi, long long lo, int sc) {
+    const __int128 n = ((__int128)hi << 32) + (__int128)lo;
+    if (n == 0) return 0.0;
+    const unsigned long long sgn = n < 0 ? 0x8000000000000000ull : 0ull;
+    const unsigned __int128 m = n < 0 ? (unsigned __int128)(-n) : (unsigned __int128)n;
+    const unsigned long long mh = (unsigned long long)(m >> 64), ml = (unsigned long long)m;
+    const int nb = mh ? 128 - __clzll((long long)mh) : 64 - __clzll((long long)ml);   // bit length
+    unsigned long long q;
+    int e2 = sc - 48;                                   // value = q * 2^e2 below
+    if (nb <= 53) {
+        q = ml << (53 - nb);
+        e2 -= 53 - nb;
+    } else {
+        const int r = nb - 53;
+        q = (unsigned long long)(m >> r);
+        const unsigned __int128 rem = m & ((((unsigned __int128)1) << r) - 1);
+        const unsigned __int128 half = ((unsigned __int128)1) << (r - 1);
+        if (rem > half || (rem == half && (q & 1ull))) q++;
+        e2 += r;
+        if (q >> 53) { q >>= 1; e2++; }
+    }
+    const int be = e2 + 52 + 1023;                      // q in [2^52, 2^53)
+    if (be <= 0 || be >= 2047) {                        // outside the normal range
+        const double v = ldexp((double)q, e2);
+        return sgn ? -v : v;
+    }
+    return __longlong_as_double((long long)(sgn | ((unsigned long long)be << 52) | (q & 0xFFFFFFFFFFFFFull)));
+}
+
 // ---------------------------------------------------------------------------
 // k_lhat_digits: digit planes of Lhat_{C,K} (per column j: exponent over all
 // q) in the layout plane[j][q] (q contiguous, padded to c16 with zeros).
@@ -334,7 +365,7 @@ __global__ void __launch_bounds__(kOzThreads, 1) k_selinv_oz(const ProbDesc *__r
     // Y = -(A^{-1}_{C,C} Lhat) in FP64: scale 2^(e_p + f_j - 14) (e = E - 1022)
     auto emit = [&](int row, int j, long long hi, long long lo) {
         const int sc = (rowE[row] - 1022) + (P.colexp[fc + j] - 1022) - 14;
-        const double y = ldexp((double)hi, sc - 16) + ldexp((double)lo, sc - 48);
+        const double y = fixed_to_double(hi, lo, sc);
         Zk[(int64_t)j * ld + s + p0 + row] = -y;
         atomicMax(&ymax[j], bexp(y));
     };
@@ -526,7 +557,7 @@ __global__ void __launch_bounds__(kOzThreads, 1) k_lhat_oz(const ProbDesc *__res
             const long long hi = (gq[0] << 16) + (gq[1] << 8) + gq[2];
             const long long lo = (gq[3] << 24) + (gq[4] << 16) + (gq[5] << 8) + gq[6];
             const int sc = (rowE[row] - 1022) + (P.linvexp[fc + j] - 1022) - 14;
-            LD[(int64_t)j * ld + p0 + row] = ldexp((double)hi, sc - 16) + ldexp((double)lo, sc - 48);
+            LD[(int64_t)j * ld + p0 + row] = fixed_to_double(hi, lo, sc);
         }
     }
 }
@@ -675,6 +706,9 @@ __global__ void __launch_bounds__(kOzThreads, 1) k_diag_oz(const ProbDesc *__res
     __syncthreads();
     if (!s_last) return;
     __threadfence();
+    __shared__ int cz[128];   // exponent of each whole column of K's panel
+    for (int j = threadIdx.x; j < s; j += kOzThreads) cz[j] = P.colexpY[fc + j];
+    __syncthreads();
     for (int e = threadIdx.x; e < s * s; e += kOzThreads) {
         const int i = e % s, j = e / s;
         if (i < j) continue;
@@ -685,20 +719,20 @@ __global__ void __launch_bounds__(kOzThreads, 1) k_diag_oz(const ProbDesc *__res
             const int ey = P.colexpY[fc + b];
             if (ey == 0 || (hi == 0 && lo == 0)) return 0.0;
             const int sc = (P.colexp[fc + a] - 1022) + (ey - 1022) - 14;
-            return ldexp((double)hi, sc - 16) + ldexp((double)lo, sc - 48);
+            return fixed_to_double(hi, lo, sc);
         };
         double xij = LDk[(int64_t)j * ld + i] - prod(i, j);
         double xji = LDk[(int64_t)i * ld + j] - prod(j, i);
         if (P.symmetrize) { const double v = 0.5 * (xij + xji); xij = v; xji = v; }
         Zk[(int64_t)j * ld + i] = xij;
         Zk[(int64_t)i * ld + j] = xji;
+        atomicMax(&cz[j], bexp(xij));
+        atomicMax(&cz[i], bexp(xji));
     }
     __syncthreads();
     for (int e = threadIdx.x; e < 2 * s * s; e += kOzThreads) acc64[e] = 0;
-    for (int j = threadIdx.x; j < s; j += kOzThreads) {  // exponent of the whole column
-        int ez = P.colexpY[fc + j];
-        for (int i = 0; i < s; i++) ez = max(ez, bexp(Zk[(int64_t)j * ld + i]));
-        P.colexpZ[fc + j] = ez;
+    for (int j = threadIdx.x; j < s; j += kOzThreads) {
+        P.colexpZ[fc + j] = cz[j];
         P.colexpY[fc + j] = 0;
     }
     if (threadIdx.x == 0) P.counter[K] = 0;

@@ -27,11 +27,13 @@ __device__ inline void latch_status(int *status, int code) {
 // k_linv: one CTA per supernode.  X = L_KK^{-1} by row-oriented forward
 // substitution on all columns at once: row k of X is final after step k-1,
 // and step k updates every X(i, j), i > k, j <= k, in parallel.  X stays in
-// shared memory when it fits (real blocks), else in the global scratch.
-// Then Dinv(i, j) = sum_{k >= max(i, j)} X(k, i) X(k, j) / D_k.
+// shared memory when it fits (odd stride: row and column walks hit distinct
+// banks), else in the global scratch.  Then the symmetric
+// Dinv(i, j) = sum_{k >= max(i, j)} X(k, i) X(k, j) / D_k, lower half
+// computed and mirrored.
 // ---------------------------------------------------------------------------
 constexpr int kLinvThreads = 256;
-constexpr size_t kLinvSmemMax = 128 * 128 * sizeof(double);
+constexpr size_t kLinvSmemMax = (128 * 129 + 128) * sizeof(double);
 
 template <typename T>
 __global__ void __launch_bounds__(kLinvThreads) k_linv(const ProbDesc *__restrict__ descs,
@@ -49,30 +51,38 @@ __global__ void __launch_bounds__(kLinvThreads) k_linv(const ProbDesc *__restric
     const T *D = static_cast<const T *>(P.D) + fc;
     T *Li = static_cast<T *>(P.Linv) + P.linv_off[K];
     T *LD = static_cast<T *>(P.LD) + P.panel_off[K];
-    const bool in_smem = sizeof(T) * (size_t)s * s <= smem_cap;
-    T *X = in_smem ? reinterpret_cast<T *>(smem_raw) : Li;      // X(i, j) = X[j*s + i]
-    for (int e = threadIdx.x; e < s * s; e += kLinvThreads)
-        X[e] = (e % s == e / s) ? Sc<T>::one() : Sc<T>::zero();
-    for (int j = threadIdx.x; j < s; j += kLinvThreads)
+    const int sp = s | 1;
+    const bool in_smem = sizeof(T) * ((size_t)s * sp + s) <= smem_cap;
+    const int lx = in_smem ? sp : s;                              // X(i, j) = X[j*lx + i]
+    T *X = in_smem ? reinterpret_cast<T *>(smem_raw) : Li;
+    T *rD = in_smem ? X + (size_t)s * sp : nullptr;
+    for (int e = threadIdx.x; e < s * s; e += kLinvThreads) {
+        const int i = e % s, j = e / s;
+        X[j * lx + i] = i == j ? Sc<T>::one() : Sc<T>::zero();
+    }
+    for (int j = threadIdx.x; j < s; j += kLinvThreads) {
         if (is_zero(D[j]) || !finite_val(D[j])) latch_status(P.status, SELINV_ERR_ZERO_PIVOT);
+        if (in_smem) rD[j] = recip(D[j]);
+    }
     __syncthreads();
     for (int k = 0; k + 1 < s; k++) {
         const int m = s - 1 - k;                 // rows i = k+1 .. s-1
         for (int e = threadIdx.x; e < m * (k + 1); e += kLinvThreads) {
             const int i = k + 1 + e % m, j = e / m;
-            msub(X[(int64_t)j * s + i], L[(int64_t)k * ld + i], X[(int64_t)j * s + k]);
+            msub(X[j * lx + i], L[(int64_t)k * ld + i], X[j * lx + k]);
         }
         __syncthreads();
     }
     if (in_smem)
-        for (int e = threadIdx.x; e < s * s; e += kLinvThreads) Li[e] = X[e];
+        for (int e = threadIdx.x; e < s * s; e += kLinvThreads) Li[e] = X[(e / s) * lx + e % s];
     for (int e = threadIdx.x; e < s * s; e += kLinvThreads) {
         const int i = e % s, j = e / s;
-        const int k0 = i > j ? i : j;
+        if (i < j) continue;
         T acc = Sc<T>::zero();
-        for (int k = k0; k < s; k++)
-            madd(acc, mul(X[(int64_t)i * s + k], recip(D[k])), X[(int64_t)j * s + k]);
+        for (int k = i; k < s; k++)
+            madd(acc, mul(X[i * lx + k], in_smem ? rD[k] : recip(D[k])), X[j * lx + k]);
         LD[(int64_t)j * ld + i] = acc;
+        LD[(int64_t)i * ld + j] = acc;
     }
 }
 
@@ -322,8 +332,8 @@ cudaError_t launch_check_finite(const void *x, int64_t n, int *status, cudaStrea
 template <typename T>
 static cudaError_t launch_linv_t(const ProbDesc *d, const int2 *work, int nwork, int large, cudaStream_t st) {
     if (nwork <= 0) return cudaSuccess;
-    // small blocks (s <= 32) need at most 16 KB; large ones get the 128 KB maximum
-    const size_t cap = large ? kLinvSmemMax : 32 * 32 * sizeof(T);
+    // small blocks (s <= 32) need at most 17 KB; large ones get room for s = 128 (real)
+    const size_t cap = large ? kLinvSmemMax : (32 * 33 + 32) * sizeof(T);
     k_linv<T><<<nwork, kLinvThreads, cap, st>>>(d, work, nwork, cap);
     return cudaGetLastError();
 }

@@ -128,6 +128,10 @@ __device__ void diag_finish(const ProbDesc &P, int K, int s, int64_t ld, int nti
     __threadfence();
     const T *part0 = static_cast<const T *>(P.partial) + P.part_off[K];
     const int64_t ss = (int64_t)s * s;
+    __shared__ int cz[128];   // exponent of each whole column of K's panel
+    for (int j = threadIdx.x; j < s; j += kThreads)
+        cz[j] = __ldcg(P.colexpY + P.super_ptr[K] + j);   // atomics of this launch
+    __syncthreads();
     for (int e = threadIdx.x; e < s * s; e += kThreads) {
         const int i = e % s, j = e / s;
         if (i < j) continue;
@@ -143,14 +147,14 @@ __device__ void diag_finish(const ProbDesc &P, int K, int s, int64_t ld, int nti
         }
         Zk[(int64_t)j * ld + i] = xij;
         Zk[(int64_t)i * ld + j] = xji;
+        atomicMax(&cz[j], bexp(xij));
+        atomicMax(&cz[i], bexp(xji));
     }
     __syncthreads();
     // exponent of every whole column of K's panel (rows below: atomic max taken
     // when they were written), for the row bounds of the descendants' gathers
     for (int j = threadIdx.x; j < s; j += kThreads) {
-        int e = __ldcg(P.colexpY + P.super_ptr[K] + j);  // atomics of this launch
-        for (int i = 0; i < s; i++) e = max(e, bexp(Zk[(int64_t)j * ld + i]));
-        P.colexpZ[P.super_ptr[K] + j] = e;
+        P.colexpZ[P.super_ptr[K] + j] = cz[j];
         P.colexpY[P.super_ptr[K] + j] = 0;
     }
     if (threadIdx.x == 0) P.counter[K] = 0;
