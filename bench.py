@@ -35,7 +35,17 @@ import numpy as np  # noqa: E402
 
 FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.070   # SMs x FP64 FMA/clk/SM x flop/FMA x GHz = 1258.6
 METRIC = "selinv time and FP64 GFLOP/s (% of peak); batched & adjoint vs plain on one GB300"
-WORKLOAD = "3D 7-point Laplacian 40^3 (N=64000), diag 6+U(0,1), nested dissection, relaxed supernodes <=128 cols / <=10% zeros, FP64, plain selinv"
+WORKLOADS = {
+    1: "2D 5-point Laplacian 63x63 (N=3969) + 0.1 I, nested dissection, fundamental supernodes <=64 cols, FP64, plain selinv",
+    2: "3D 7-point Laplacian 40^3 (N=64000), diag 6+U(0,1), nested dissection, relaxed supernodes <=128 cols / <=10% zeros, FP64, plain selinv",
+    3: "DFT-like complex symmetric H - zS, 1024 atoms x 16 basis functions (N=16384), z=-0.2+0.05i, complex128, plain selinv",
+    5: "3D variable-coefficient diffusion 24^3 (N=13824), theta=exp(0.5 N(0,1)), relaxed supernodes, FP64, plain selinv",
+}
+WORKLOAD = WORKLOADS[2]
+
+
+def workload_name(cfg: int) -> str:
+    return WORKLOADS.get(cfg, f"synthetic configuration {cfg}")
 
 
 def parse():
@@ -49,7 +59,7 @@ def parse():
     ap.add_argument("--no-variants", action="store_true",
                     help="skip the plain / batched / adjoint comparison runs")
     ap.add_argument("--batch-poles", type=int, default=8)
-    ap.add_argument("--schedule", type=int, default=1, help="0 plain, 1 level")
+    ap.add_argument("--schedule", type=int, default=1, help="0 plain, 1 level, 2 persistent")
     ap.add_argument("--fast", type=int, default=1,
                     help="1: FP64-exact tensor-core contraction for s >= 16; 0: DFMA only")
     return ap.parse_args()
@@ -312,7 +322,7 @@ def run_reference(args):
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": round(1e3 * tot / len(times), 3), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "sample": sample},
+            "config": {"workload": workload_name(args.config), "sample": sample},
             "cpu_baseline": {"value": round(value, 4), "unit": "GFLOP/s", "cores": 1,
                              "kind": "oracle", "sample": sample},
             "e2e": {"value": round(value, 4), "unit": "GFLOP/s", "h2d_bytes_per_step": 0,
@@ -478,11 +488,11 @@ def main():
     if rank == 0:
         line = {"metric": METRIC, "value": round(value, 3), "unit": "GFLOP/s", "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_step, 3),
-                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-                "data": "synthetic",
-                "config": {"workload": WORKLOAD, "n": p.n, "nsuper": ctx.nsuper, "nnz_L": ctx.nnz,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "c128" if dt == N.SELINV_C128 else "f64", "data": "synthetic",
+                "config": {"workload": workload_name(args.config), "n": p.n, "nsuper": ctx.nsuper, "nnz_L": ctx.nnz,
                            "flops_per_step": F, "bytes_per_step": B,
-                           "schedule": ["plain", "level"][args.schedule],
+                           "schedule": ["plain", "level", "persistent"][args.schedule],
                            "contraction": "bf16 tensor cores, FP64-exact slicing" if args.fast else "FP64 DFMA",
                            "l2": "flushed between timed steps (256 MB write)",
                            "parallelism": "replicas" if world > 1 else "single GPU",
