@@ -61,7 +61,7 @@ def parse():
     ap.add_argument("--batch-poles", type=int, default=8)
     ap.add_argument("--schedule", type=int, default=1, help="0 plain, 1 level, 2 persistent")
     ap.add_argument("--fast", type=int, default=1,
-                    help="1: FP64-exact tensor-core contraction for s >= 16; 0: DFMA only")
+                    help="FP64-exact tensor-core contraction for s >= 16 -- 1: tcgen05, 2: mma.sync; 0: DFMA only")
     return ap.parse_args()
 
 
@@ -147,9 +147,23 @@ class ClockSampler:
 
 KERNEL_SOURCES = {
     "k_selinv_oz": ("kernels_ozaki.cu", "common.cuh"),
+    "k_selinv_tc": ("kernels_tc.cu", "umma.cuh", "fixedpoint.cuh", "common.cuh"),
     "k_diag": ("kernels_ozaki.cu", "common.cuh"),
 }
 DEFAULT_SOURCES = ("kernels_selinv.cu", "tile_gemm.cuh", "common.cuh")
+
+
+def measured_peaks():
+    """Roofline denominators: the machine's measured copy bandwidth and dense bf16
+    rate, else the recipe's fallback figures."""
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+        return {"hbm_gbs": float(d["hbm_gbs"]), "bf16_tflops": float(d["bf16_tflops"]),
+                "source": "of measured (MEASURED_PEAKS.json bf16_tflops)"}
+    except (OSError, KeyError, ValueError):
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "source": "of fallback (1.9 PFLOP/s)"}
 
 
 def kernel_source_hash(kernel: str) -> str:
@@ -404,11 +418,14 @@ def main():
     c_ = np.diff(rp).astype(np.float64) - s_
     mult = 4.0 if dt == N.SELINV_C128 else 1.0
     oz = (s_ >= 16) & (dt == N.SELINV_F64) & bool(args.fast)
+    peaks = measured_peaks()
     dom = int(np.argmax(kms))
     name = N.PROFILE_KINDS[dom]
     # algorithmic flops of the supernodes each kernel kind processes
     f_of = {"k_selinv": mult * float(((2 * c_ * c_ * s_ + 2 * c_ * s_ * s_) * ~oz).sum()),
             "k_selinv_oz": mult * float((2 * c_ * c_ * s_ * oz).sum()),
+            "k_selinv_tc": mult * float((2 * c_ * c_ * s_ * oz).sum()),
+            "k_selinv_persist": mult * float((2 * c_ * c_ * s_ + 2 * c_ * s_ * s_).sum()),
             "k_diag": mult * float((2 * c_ * s_ * s_ * oz).sum()),
             "k_lhat": mult * float((c_ * s_ * s_ * ~oz).sum()),
             "k_lhat_oz": mult * float((c_ * s_ * s_ * oz).sum()),
@@ -418,12 +435,12 @@ def main():
     f_dom = f_of[name]
     achieved = f_dom / (kms[dom] * 1e-3) / 1e9 if kms[dom] > 0 else None
     traffic = ncu_traffic(name)
-    if name == "k_selinv_oz":
-        # FP64-exact products on bf16 tensor cores: 28 digit-pair mma per FP64 product
-        peak, unit, bound = 604.0, "TFLOP/s", "tensor"
+    if name in ("k_selinv_oz", "k_selinv_tc", "k_diag", "k_lhat_oz"):
+        # FP64-exact products on bf16 tensor cores: 28 digit-pair products per FP64 product
+        peak, unit, bound = peaks["bf16_tflops"], "TFLOP/s", "tensor"
         ach = 28.0 * f_dom / (kms[dom] * 1e-3) / 1e12 if kms[dom] > 0 else None
-        note = ("bf16 mma.sync m16n8k16 throughput measured on this GB300 (604 TFLOP/s); "
-                "achieved counts 28 bf16 digit-pair products per FP64 multiply-add")
+        note = (f"dense bf16 peak {peaks['source']} (burst: the kernel is timed inside one "
+                f"selected inversion); achieved counts the 28 bf16 digit-pair products per FP64 multiply-add")
     else:
         peak, unit, bound, ach = FP64_PEAK_GFLOPS, "GFLOP/s", "alu", achieved
         note = "FP64 FMA pipe: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (measured DFMA loop 1204)"
@@ -493,7 +510,8 @@ def main():
                 "config": {"workload": workload_name(args.config), "n": p.n, "nsuper": ctx.nsuper, "nnz_L": ctx.nnz,
                            "flops_per_step": F, "bytes_per_step": B,
                            "schedule": ["plain", "level", "persistent"][args.schedule],
-                           "contraction": "bf16 tensor cores, FP64-exact slicing" if args.fast else "FP64 DFMA",
+                           "contraction": {0: "FP64 DFMA", 1: "tcgen05 bf16, FP64-exact slicing",
+                                           2: "mma.sync bf16, FP64-exact slicing"}[args.fast],
                            "l2": "flushed between timed steps (256 MB write)",
                            "parallelism": "replicas" if world > 1 else "single GPU",
                            "fp64_frac": round(value / world / FP64_PEAK_GFLOPS, 4)},

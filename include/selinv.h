@@ -82,9 +82,10 @@ typedef struct {
     long long spin_limit;  /* polls (about 256 ns each) of every device spin-wait before
                               it gives up and latches SELINV_ERR_TIMEOUT; default 1<<22 */
     int use_graph;         /* 1: capture the level schedule in a CUDA graph; default 1  */
-    int fast_contraction;  /* 1: large contractions run FP64-exact on bf16 tensor cores
-                              (error-free slicing, FP64 accumulation); 0: DFMA only.
-                              default 1                                                 */
+    int fast_contraction;  /* contraction of the large real supernodes (s >= 16): FP64-exact
+                              on bf16 tensor cores (error-free slicing, exact integer
+                              accumulation) -- 1: tcgen05 with tensor-memory accumulators
+                              (default), 2: mma.sync; 0: FP64 DFMA only                 */
 } selinv_opts;
 
 /* Fills *opts with the defaults listed above. */
@@ -224,9 +225,9 @@ int selinv_factor_adjoint(selinv_plan plan, selinv_dtype dtype, const void *L_de
  *   2 gather-GEMM + diagonal (DFMA)    3 digit planes of Lhat
  *   4 gather-GEMM on tensor cores      5 diagonal block after it
  *   6 digit planes of L_KK^{-1}        7 Lhat on tensor cores
- *   8 the persistent traversal
+ *   8 the persistent traversal          9 gather-GEMM on tcgen05
  * For measurement only. */
-#define SELINV_PROFILE_KINDS 9
+#define SELINV_PROFILE_KINDS 10
 int selinv_numeric_profile(selinv_plan plan, selinv_dtype dtype, const void *L_dev,
                            const void *D_dev, void *Ainv_dev, void *cuda_stream, double *kernel_ms,
                            int64_t *kernel_launches);

@@ -1,0 +1,352 @@
+// A^{-1}_{C,K} = -A^{-1}_{C,C} Lhat_{C,K} (Alg. 1, the product after the
+// gather) on the 5th-generation tensor cores: the FP64-exact digit scheme of
+// the mma.sync kernel (7 balanced base-256 digits per operand on a row /
+// column exponent grid, digit products grouped by i + j into exact fp32
+// sums, folded into int64 every 128 k), with
+//   * a 128-row x TN-column output tile per CTA whose 7 group accumulators
+//     live in tensor memory (7 TN columns), written by tcgen05.mma issued from
+//     one thread, completion signalled through mbarriers;
+//   * operands in shared memory in the K-major layout without swizzle, two
+//     stages: while the tensor cores work on step k, all 8 warps gather the
+//     A^{-1}(C,C) entries of step k + 1, cut them into digits (integer
+//     operations only) and copy the Lhat digit planes of step k + 1;
+//   * every 128 k the group sums are read from tensor memory and added as
+//     int64 into per-element (hi, lo) words in shared memory.
+// Split-k items add their int64 words into a global buffer (exact, order
+// independent); the last item of a row tile writes A^{-1}_{C,K} for it.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "common.cuh"
+#include "fixedpoint.cuh"
+#include "launch.h"
+#include "tile_gemm.cuh"
+#include "umma.cuh"
+
+namespace selinv {
+
+constexpr int kTcM = 128;          // rows of C per item (tensor-memory lanes)
+constexpr int kTcThreads = 256;
+constexpr int kTcDig = 7;
+constexpr int kTcFlush = 8;        // k16 steps per exact fp32 chunk (128 k)
+
+template <int TN> struct TcCfg {
+    static constexpr int A_PLANE = kTcM * 16;    // bf16 elements of one digit plane per k16 step
+    static constexpr int B_PLANE = TN * 16;
+    static constexpr int A_STAGE = kTcDig * A_PLANE;
+    static constexpr int B_STAGE = kTcDig * B_PLANE;
+    static constexpr uint32_t TCOLS = kTcDig * TN <= 128 ? 128u : (kTcDig * TN <= 256 ? 256u : 512u);
+    static constexpr size_t SMEM =
+        sizeof(uint16_t) * 2 * (size_t)(A_STAGE + B_STAGE) + sizeof(long long) * 2 * (size_t)kTcM * TN +
+        sizeof(int) * kTcM;
+};
+
+// x = M * 2^(E - 1076) with |M| < 2^54 (E >= the biased exponent of x),
+// truncated toward zero; integer operations only.
+__device__ __forceinline__ long long fixed54(double x, int E) {
+    const long long b = __double_as_longlong(x);
+    const int ex = (int)((b >> 52) & 0x7FF);
+    const long long mant = ex ? ((b & 0xFFFFFFFFFFFFFll) | (1ll << 52)) : 0ll;
+    const int sh = E - ex - 1;
+    const long long M = sh < 0 ? (mant << 1) : (sh < 63 ? (mant >> sh) : 0ll);
+    return b < 0 ? -M : M;
+}
+
+// With u = M + 0x80808080808080 (M as above), byte t of u minus 128 is the
+// balanced base-256 digit of weight 256^t, in [-128, 127].  Two digits (u0's
+// in the low half, u1's in the high half) as a bf16 pair; exact: the digit
+// is formed in fp32 as (1.5 * 2^23 + byte) - (1.5 * 2^23 + 128).
+__device__ __forceinline__ uint32_t digit_pair(unsigned long long u0, unsigned long long u1, int shift) {
+    const float f0 = __int_as_float(0x4B400000 | (int)((u0 >> shift) & 0xFFull)) - 12583040.0f;
+    const float f1 = __int_as_float(0x4B400000 | (int)((u1 >> shift) & 0xFFull)) - 12583040.0f;
+    uint32_t r;
+    asm("cvt.rn.bf16x2.f32 %0, %1, %2;\n" : "=r"(r) : "f"(f1), "f"(f0));
+    return r;
+}
+
+// Entry (p, q) of A^{-1}_{C,C}: stored at (max, min) by symmetry; pl = p - p0.
+struct TcGather {
+    const double *Z;
+    const int64_t *pcb, *prb;
+    const int32_t *relidx;
+    const int64_t *tile_cb, *tile_rb;
+    int p0, c;
+    __device__ __forceinline__ double operator()(int pl, int q) const {
+        const int p = p0 + pl;
+        if (p >= c || q >= c) return 0.0;
+        const int64_t addr = p >= q ? pcb[q] + relidx[prb[q] + p] : tile_cb[pl] + relidx[tile_rb[pl] + q];
+        return Z[addr];
+    }
+};
+
+template <int TN>
+__global__ void __launch_bounds__(kTcThreads, 1) k_selinv_tc(const ProbDesc *__restrict__ descs,
+                                                             const Item *__restrict__ items, int nitems,
+                                                             long long wait_limit) {
+    using Cfg = TcCfg<TN>;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    uint16_t *As = reinterpret_cast<uint16_t *>(smem_raw);                // [2][7][A_PLANE]
+    uint16_t *Bs = As + 2 * Cfg::A_STAGE;                                  // [2][7][B_PLANE]
+    long long *Hi = reinterpret_cast<long long *>(Bs + 2 * Cfg::B_STAGE);  // [TN][128]
+    long long *Lo = Hi + kTcM * TN;                                        // [TN][128]
+    int *rowE = reinterpret_cast<int *>(Lo + kTcM * TN);                   // [128]
+    __shared__ int64_t tile_cb[kTcM], tile_rb[kTcM];
+    __shared__ __align__(8) uint64_t mbar[2];
+    __shared__ uint32_t s_tmem;
+    __shared__ int s_pre, s_last, s_abort;
+    __shared__ int ymax[128];
+
+    const int w = blockIdx.x;
+    if (w >= nitems) return;
+    const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
+    const Item it = items[w];
+    const ProbDesc &P = descs[it.prob];
+    const int K = it.K;
+    const int fc = P.super_ptr[K];
+    const int s = P.super_ptr[K + 1] - fc;
+    const int64_t ld = P.rowptr[K + 1] - P.rowptr[K];
+    const int c = (int)(ld - s);
+    const int c16 = (c + 15) & ~15;
+    const int ncol = (s + TN - 1) / TN;
+    const int nsplit = it.ntiles;
+    const int ksp = it.tile % nsplit;
+    const int ct = (it.tile / nsplit) % ncol;
+    const int tile = it.tile / nsplit / ncol;
+    const int p0 = tile * kTcM, n0 = ct * TN;
+    const int64_t pos0 = P.rowptr[K] + s;
+    const int nsteps = c16 / 16;
+    const int chunk = ((nsteps + nsplit - 1) / nsplit + kTcFlush - 1) / kTcFlush * kTcFlush;
+    const int st0 = ksp * chunk;
+    const int st1 = st0 + chunk < nsteps ? st0 + chunk : nsteps;
+
+    // row exponents of the gathered block: row p is bounded by the largest
+    // whole-column exponent of A^{-1} over C[0..p] (entry (p, q) sits in
+    // the ancestor column C[min(p, q)])
+    if (tid == 0) { s_pre = 0; s_abort = 0; }
+    __syncthreads();
+    {
+        int e = 0;
+        for (int q = tid; q < p0 && q < c; q += kTcThreads) e = max(e, P.colexpZ[P.rows[pos0 + q]]);
+        if (e) atomicMax(&s_pre, e);
+    }
+    for (int e = tid; e < kTcM; e += kTcThreads) {
+        const int p = p0 + e;
+        tile_cb[e] = p < c ? P.colbase[pos0 + p] : 0;
+        tile_rb[e] = p < c ? P.relbase[pos0 + p] : 0;
+        rowE[e] = p < c ? P.colexpZ[P.rows[pos0 + p]] : 0;
+    }
+    for (int e = tid; e < 2 * kTcM * TN; e += kTcThreads) Hi[e] = 0;   // Hi and Lo
+    for (int e = tid; e < 128; e += kTcThreads) ymax[e] = 0;
+    if (tid == 0) {
+        umma::mbar_init(&mbar[0], 1);
+        umma::mbar_init(&mbar[1], 1);
+        umma::mbar_init_fence();
+    }
+    if (warp == 0) {
+        umma::tmem_alloc(&s_tmem, Cfg::TCOLS);
+        umma::tmem_relinquish();
+    }
+    umma::fence_before_sync();
+    __syncthreads();
+    umma::fence_after_sync();
+    if (warp == 0) {                          // prefix max over the 128 rows
+        int carry = s_pre;
+        for (int b = 0; b < kTcM; b += 32) {
+            int v = max(rowE[b + lane], carry);
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int u = __shfl_up_sync(0xffffffffu, v, o);
+                if (lane >= o) v = max(v, u);
+            }
+            rowE[b + lane] = v;
+            carry = __shfl_sync(0xffffffffu, v, 31);
+        }
+    }
+    __syncthreads();
+    const uint32_t tmem = s_tmem;
+    const TcGather g{static_cast<const double *>(P.Z), P.colbase + pos0, P.relbase + pos0, P.relidx,
+                     tile_cb, tile_rb, p0, c};
+    const uint16_t *Bg = P.lhs + P.lhs_off[K];
+    const int64_t bplane = (int64_t)s * c16;
+    const uint32_t idesc = umma::idesc_bf16_f32(kTcM, TN);
+
+    // this thread's A slot: row r, the 8 k-values kh*8 .. kh*8+7 of each step
+    const int r = tid % kTcM, kh = tid / kTcM;
+    const int E = rowE[r];
+    double v[8];
+    if (st0 < st1) {
+#pragma unroll
+        for (int u = 0; u < 8; u++) v[u] = g(r, st0 * 16 + kh * 8 + u);
+    }
+    int chunk0 = st0;
+    bool aborted = false;
+    int last_stage = -1, last_use = 0;        // the most recent commit (uniform over the CTA)
+    for (int step = st0; step < st1; step++) {
+        const int i_ = step - st0;
+        const int stage = i_ & 1, use = i_ >> 1;
+        const int k0 = step * 16;
+        uint16_t *Ab = As + stage * Cfg::A_STAGE;
+        uint16_t *Bb = Bs + stage * Cfg::B_STAGE;
+        if (i_ >= 2 && !umma::mbar_wait(&mbar[stage], (uint32_t)((use - 1) & 1), wait_limit)) s_abort = 1;
+        // Lhat digit planes of this step: core-matrix rows of 8 q (16 bytes)
+        for (int e = tid; e < kTcDig * TN * 2; e += kTcThreads) {
+            const int kg = e & 1, n = (e >> 1) % TN, pl = (e >> 1) / TN;
+            uint16_t *dst = Bb + pl * Cfg::B_PLANE + (n / 8) * 128 + kg * 64 + (n % 8) * 8;
+            if (n0 + n < s) umma::cp_async16(dst, Bg + pl * bplane + (int64_t)(n0 + n) * c16 + k0 + kg * 8);
+            else *reinterpret_cast<uint4 *>(dst) = make_uint4(0, 0, 0, 0);
+        }
+        // A digit planes of this step from the values gathered one step ahead
+        {
+            unsigned long long u8[8];
+#pragma unroll
+            for (int u = 0; u < 8; u++) u8[u] = (unsigned long long)(fixed54(v[u], E) + 0x80808080808080ll);
+            uint16_t *dst = Ab + (r / 8) * 128 + kh * 64 + (r % 8) * 8;
+#pragma unroll
+            for (int pl = 0; pl < kTcDig; pl++) {
+                const int sh = 8 * (kTcDig - 1 - pl);
+                uint4 q;
+                q.x = digit_pair(u8[0], u8[1], sh);
+                q.y = digit_pair(u8[2], u8[3], sh);
+                q.z = digit_pair(u8[4], u8[5], sh);
+                q.w = digit_pair(u8[6], u8[7], sh);
+                *reinterpret_cast<uint4 *>(dst + pl * Cfg::A_PLANE) = q;
+            }
+        }
+        // gather of the next step, in flight during this step's tensor-core work
+        if (step + 1 < st1) {
+#pragma unroll
+            for (int u = 0; u < 8; u++) v[u] = g(r, k0 + 16 + kh * 8 + u);
+        }
+        umma::cp_async_wait_all();
+        umma::fence_proxy_async();
+        __syncthreads();
+        if (s_abort) { aborted = true; break; }
+        const bool first = step == chunk0;
+        if (tid == 0) {
+            umma::fence_after_sync();
+            const uint32_t a0 = umma::smem_u32(Ab), b0 = umma::smem_u32(Bb);
+#pragma unroll
+            for (int i = 0; i < kTcDig; i++) {
+                const uint64_t ad = umma::smem_desc(a0 + i * Cfg::A_PLANE * 2, 128, 256);
+#pragma unroll
+                for (int j = 0; i + j < kTcDig; j++) {
+                    const uint64_t bd = umma::smem_desc(b0 + j * Cfg::B_PLANE * 2, 128, 256);
+                    // group i + j starts from zero at its first product of a chunk (i == 0)
+                    umma::mma_bf16(tmem + (uint32_t)((i + j) * TN), ad, bd, idesc, (first && i == 0) ? 0u : 1u);
+                }
+            }
+            umma::commit(&mbar[stage]);
+        }
+        last_stage = stage;
+        last_use = use;
+        if (step + 1 - chunk0 == kTcFlush || step + 1 == st1) {
+            // fold the chunk's exact fp32 group sums into the int64 words
+            const bool ok = umma::mbar_wait(&mbar[stage], (uint32_t)(use & 1), wait_limit);
+            umma::fence_after_sync();
+            if (ok) {
+                const int lb = 32 * (warp % 4), row = lb + lane, half = warp / 4;
+#pragma unroll 1
+                for (int cb = 0; cb < TN / 16; cb++) {
+                    const int col0 = half * (TN / 2) + cb * 8;
+                    uint32_t acc[kTcDig][8];
+#pragma unroll
+                    for (int gq = 0; gq < kTcDig; gq++)
+                        umma::tmem_ld8(tmem + ((uint32_t)lb << 16) + (uint32_t)(gq * TN + col0), acc[gq]);
+                    umma::tmem_wait_ld();
+#pragma unroll
+                    for (int jj = 0; jj < 8; jj++) {
+                        long long gv[kTcDig];
+#pragma unroll
+                        for (int gq = 0; gq < kTcDig; gq++) gv[gq] = (long long)__float2int_rn(__uint_as_float(acc[gq][jj]));
+                        Hi[(col0 + jj) * kTcM + row] += (gv[0] << 16) + (gv[1] << 8) + gv[2];
+                        Lo[(col0 + jj) * kTcM + row] += (gv[3] << 24) + (gv[4] << 16) + (gv[5] << 8) + gv[6];
+                    }
+                }
+            } else {
+                s_abort = 1;
+            }
+            umma::fence_before_sync();
+            __syncthreads();
+            if (s_abort) { aborted = true; break; }
+            chunk0 = step + 1;
+        }
+    }
+    if (aborted) {
+        // a wait ran out: report, give in-flight products a bounded chance to
+        // drain, release the tensor memory and leave
+        if (tid == 0) atomicCAS(P.status, 0, SELINV_ERR_TIMEOUT);
+        if (last_stage >= 0) umma::mbar_wait(&mbar[last_stage], (uint32_t)(last_use & 1), wait_limit);
+        umma::fence_before_sync();
+        __syncthreads();
+        if (warp == 0) umma::tmem_dealloc(tmem, Cfg::TCOLS);
+        return;
+    }
+    umma::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) umma::tmem_dealloc(tmem, Cfg::TCOLS);
+
+    double *Zk = static_cast<double *>(P.Z) + P.panel_off[K];
+    // Y = -(A^{-1}_{C,C} Lhat): A digits on 2^(E - 1028 - 8i), Lhat digits on
+    // 2^(F - 1029 - 8j), so the value is (hi 2^-16 + lo 2^-48) 2^(E + F - 2057)
+    auto emit = [&](int row, int j, long long hi, long long lo) {
+        const int sc = (rowE[row] - 1022) + (P.colexp[fc + j] - 1022) - 13;
+        const double y = fixed_to_double(hi, lo, sc);
+        Zk[(int64_t)j * ld + s + p0 + row] = -y;
+        atomicMax(&ymax[j], bexp(y));
+    };
+    if (nsplit == 1) {
+        for (int e = tid; e < kTcM * TN; e += kTcThreads) {
+            const int row = e % kTcM, col = e / kTcM;
+            if (p0 + row < c && n0 + col < s) emit(row, n0 + col, Hi[col * kTcM + row], Lo[col * kTcM + row]);
+        }
+    } else {
+        long long *Yacc = P.yacc + 2 * P.panel_off[K];    // (hi, lo) per element of K's panel
+        for (int e = tid; e < kTcM * TN; e += kTcThreads) {
+            const int row = e % kTcM, col = e / kTcM;
+            if (p0 + row >= c || n0 + col >= s) continue;
+            unsigned long long *dst = reinterpret_cast<unsigned long long *>(Yacc + 2 * ((int64_t)(n0 + col) * ld + s + p0 + row));
+            const long long h = Hi[col * kTcM + row], l = Lo[col * kTcM + row];
+            if (h) atomicAdd(dst, (unsigned long long)h);
+            if (l) atomicAdd(dst + 1, (unsigned long long)l);
+        }
+        __threadfence();
+        __syncthreads();
+        int *ctr = P.tcount + P.tile_base[K] + tile;
+        if (tid == 0) s_last = (atomicAdd(ctr, 1) == ncol * nsplit - 1);
+        __syncthreads();
+        if (!s_last) return;
+        __threadfence();
+        for (int e = tid; e < kTcM * s; e += kTcThreads) {
+            const int row = e % kTcM, j = e / kTcM;
+            if (p0 + row >= c) continue;
+            unsigned long long *q = reinterpret_cast<unsigned long long *>(Yacc + 2 * ((int64_t)j * ld + s + p0 + row));
+            const long long hi = (long long)__ldcg(q), lo = (long long)__ldcg(q + 1);
+            q[0] = 0ull;
+            q[1] = 0ull;
+            emit(row, j, hi, lo);
+        }
+        if (tid == 0) *ctr = 0;
+    }
+    __syncthreads();
+    // column exponents of A^{-1}_{C,K} over all row tiles (used by the diagonal block)
+    for (int j = tid; j < s; j += kTcThreads)
+        if (ymax[j] > 0) atomicMax(&P.colexpY[fc + j], ymax[j]);
+}
+
+cudaError_t configure_tc_kernels() {
+    cudaError_t e = cudaFuncSetAttribute(k_selinv_tc<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TcCfg<16>::SMEM);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_selinv_tc<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TcCfg<32>::SMEM);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_selinv_tc<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TcCfg<64>::SMEM);
+    return e;
+}
+
+cudaError_t launch_selinv_tc(int tn, const ProbDesc *d, const Item *items, int n, long long wait_limit,
+                             cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    if (tn == 16) k_selinv_tc<16><<<n, kTcThreads, TcCfg<16>::SMEM, st>>>(d, items, n, wait_limit);
+    else if (tn == 32) k_selinv_tc<32><<<n, kTcThreads, TcCfg<32>::SMEM, st>>>(d, items, n, wait_limit);
+    else k_selinv_tc<64><<<n, kTcThreads, TcCfg<64>::SMEM, st>>>(d, items, n, wait_limit);
+    return cudaGetLastError();
+}
+
+}  // namespace selinv

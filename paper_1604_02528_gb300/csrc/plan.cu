@@ -255,6 +255,7 @@ int ensure_device(PlanData &p) {
     if (!configured) {
         if (configure_selinv_kernels() != cudaSuccess) return SELINV_ERR_CUDA;
         if (configure_ozaki_kernels() != cudaSuccess) return SELINV_ERR_CUDA;
+        if (configure_tc_kernels() != cudaSuccess) return SELINV_ERR_CUDA;
         configured = true;
     }
     int rc;
@@ -437,13 +438,22 @@ int build_schedule(Schedule &S, const std::vector<const PlanData *> &plans,
     // tensor-core items: (row tile, column tile of width tn, k-range) triples,
     // ntiles field = number of k-ranges; c == 0 has none
     auto oz_tn = [](int s) { return s <= 16 ? 16 : (s <= 32 ? 32 : 64); };
+    // row tiles of the contraction: 64 rows on mma.sync, 128 on tcgen05
+    auto use_tc = [&](int i) { return plans[i]->opts.fast_contraction == 1; };
+    auto row_tiles = [&](int i, int32_t K) -> int64_t {
+        const PlanData &p = *plans[i];
+        if (!use_tc(i)) return p.ntiles[K];
+        const int64_t c = p.rowptr[K + 1] - p.rowptr[K] - (p.super_ptr[K + 1] - p.super_ptr[K]);
+        return (c + kTcRows - 1) / kTcRows;
+    };
     auto push_oz = [&](int i, int32_t K, int tn, int nsplit) {
         const PlanData &p = *plans[i];
         const int s = p.super_ptr[K + 1] - p.super_ptr[K];
         const int64_t c = p.rowptr[K + 1] - p.rowptr[K] - s;
         if (c == 0) return;
         const int ncol = (s + tn - 1) / tn;
-        for (int t = 0; t < p.ntiles[K]; t++)
+        const int64_t nt = row_tiles(i, K);
+        for (int t = 0; t < nt; t++)
             for (int ct = 0; ct < ncol; ct++)
                 for (int ks = 0; ks < nsplit; ks++) S.h_items.push_back({i, K, (t * ncol + ct) * nsplit + ks, nsplit});
     };
@@ -462,7 +472,7 @@ int build_schedule(Schedule &S, const std::vector<const PlanData *> &plans,
         const int s = p.super_ptr[K + 1] - p.super_ptr[K];
         const int64_t c = p.rowptr[K + 1] - p.rowptr[K] - s;
         if (c == 0) return 0;
-        return (int64_t)p.ntiles[K] * ((s + oz_tn(s) - 1) / oz_tn(s));
+        return row_tiles(i, K) * ((s + oz_tn(s) - 1) / oz_tn(s));
     };
 
     if (mode == SELINV_SCHED_PERSISTENT) {
@@ -499,7 +509,7 @@ int build_schedule(Schedule &S, const std::vector<const PlanData *> &plans,
                     const int64_t off = (int64_t)S.h_items.size();
                     push_oz(i, K, tn, oz_split(i, K, oz_ctas(i, K)));
                     if (S.h_items.size() > (size_t)off)
-                        S.launches.push_back({KL_SELINV_OZ, descs[i].dtype, tn, off,
+                        S.launches.push_back({use_tc(i) ? KL_SELINV_TC : KL_SELINV_OZ, descs[i].dtype, tn, off,
                                               (int)(S.h_items.size() - off), p.level[K]});
                     const int64_t off2 = (int64_t)S.h_items.size();
                     push_items(i, K);
@@ -531,16 +541,18 @@ int build_schedule(Schedule &S, const std::vector<const PlanData *> &plans,
             }
             int64_t level_ctas = 0;
             for (auto &ik : oz) level_ctas += oz_ctas(ik.first, ik.second);
-            for (int tn : {64, 32, 16}) {
-                const int64_t off = (int64_t)S.h_items.size();
-                for (auto &ik : oz) {
-                    const PlanData &p = *plans[ik.first];
-                    const int s = p.super_ptr[ik.second + 1] - p.super_ptr[ik.second];
-                    if (oz_tn(s) == tn) push_oz(ik.first, ik.second, tn, oz_split(ik.first, ik.second, level_ctas));
+            for (int tc = 1; tc >= 0; tc--)
+                for (int tn : {64, 32, 16}) {
+                    const int64_t off = (int64_t)S.h_items.size();
+                    for (auto &ik : oz) {
+                        const PlanData &p = *plans[ik.first];
+                        const int s = p.super_ptr[ik.second + 1] - p.super_ptr[ik.second];
+                        if (oz_tn(s) == tn && use_tc(ik.first) == (tc == 1))
+                            push_oz(ik.first, ik.second, tn, oz_split(ik.first, ik.second, level_ctas));
+                    }
+                    const int cnt = (int)(S.h_items.size() - off);
+                    if (cnt) S.launches.push_back({tc ? KL_SELINV_TC : KL_SELINV_OZ, SELINV_F64, tn, off, cnt, l});
                 }
-                const int cnt = (int)(S.h_items.size() - off);
-                if (cnt) S.launches.push_back({KL_SELINV_OZ, SELINV_F64, tn, off, cnt, l});
-            }
             {
                 const int64_t off = (int64_t)S.h_items.size();
                 for (auto &ik : oz) push_items(ik.first, ik.second);
@@ -585,6 +597,8 @@ cudaError_t launch_one(const Schedule &S, const Launch &L, cudaStream_t st) {
     case KL_DIAG: return launch_diag_oz(S.d_descs, S.d_items + L.off, L.count, st);
     case KL_LINV_DIGITS: return launch_linv_digits(S.d_descs, S.d_work + L.off, L.count, st);
     case KL_LHAT_OZ: return launch_lhat_oz(L.bucket, S.d_descs, S.d_items + L.off, L.count, st);
+    case KL_SELINV_TC:
+        return launch_selinv_tc(L.bucket, S.d_descs, S.d_items + L.off, L.count, S.spin_limit, st);
     case KL_PERSIST: {
         for (size_t r = 0; r < S.reset_ptr.size(); r++) {
             cudaError_t e = cudaMemsetAsync(S.reset_ptr[r], 0, S.reset_bytes[r], st);
@@ -735,6 +749,7 @@ extern "C" int64_t selinv_plan_get(selinv_plan plan, int field, void *dst) {
 extern "C" int selinv_plan_set_opts(selinv_plan plan, const selinv_opts *opts) {
     if (!plan || !opts) return SELINV_ERR_INVALID_ARG;
     if (opts->schedule < 0 || opts->schedule > 2) return SELINV_ERR_INVALID_ARG;
+    if (opts->fast_contraction < 0 || opts->fast_contraction > 2) return SELINV_ERR_INVALID_ARG;
     plan->data.opts = *opts;
     plan->single.release();
     plan->single.valid = false;
@@ -768,9 +783,9 @@ extern "C" int selinv_numeric(selinv_plan plan, selinv_dtype dtype, const void *
         rc = build_schedule(S, plans, descs, mode);
         if (rc) { S.valid = false; return rc; }
         S.reset_ptr.clear(); S.reset_bytes.clear();
+        S.spin_limit = p.opts.spin_limit;
         if (persist) {
             S.ticket = plan->ws[0].ticket;
-            S.spin_limit = p.opts.spin_limit;
             S.wait_on_unset = (p.opts.debug_checks & 2) ? 1 : 0;
             S.reset_ptr = {plan->ws[0].done, plan->ws[0].ticket};
             S.reset_bytes = {sizeof(int) * (size_t)(p.ns + 1), sizeof(int)};
@@ -885,10 +900,10 @@ extern "C" int selinv_numeric_batched(int nitems, const selinv_plan *plans, cons
             owner->batch_cache.pop_back();
             return rc;
         }
+        b.sched.spin_limit = owner->data.opts.spin_limit;
         if (mode == SELINV_SCHED_PERSISTENT) {
             // both element types share one ticket: the launches run one after the other
             b.sched.ticket = owner->ws[1].ticket;
-            b.sched.spin_limit = owner->data.opts.spin_limit;
             b.sched.wait_on_unset = (owner->data.opts.debug_checks & 2) ? 1 : 0;
             for (int i = 0; i < nitems; i++) {
                 b.sched.reset_ptr.push_back(owner->ws[i + 1].done);

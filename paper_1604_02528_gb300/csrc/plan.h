@@ -58,11 +58,13 @@ struct Workspace {
 
 // launch kinds
 enum { KL_LINV = 0, KL_LHAT = 1, KL_SELINV = 2, KL_DIGITS = 3, KL_SELINV_OZ = 4, KL_DIAG = 5, KL_LINV_DIGITS = 6,
-       KL_LHAT_OZ = 7, KL_PERSIST = 8, KL_NKINDS = 9 };
+       KL_LHAT_OZ = 7, KL_PERSIST = 8, KL_SELINV_TC = 9, KL_NKINDS = 10 };
 
-// tensor-core (FP64-exact) contraction applies to real problems with s >= kOzMinS
+// tensor-core (FP64-exact) contraction applies to real problems with s >= kOzMinS;
+// fast_contraction 1 runs the gather-GEMM on tcgen05, 2 on mma.sync
 constexpr int kOzMinS = 16;
 inline bool oz_eligible(int dtype, int s, int fast) { return fast && dtype == SELINV_F64 && s >= kOzMinS; }
+constexpr int kTcRows = 128;   // rows of C per tcgen05 item
 
 struct Launch {
     int kind;    // KL_*
@@ -90,7 +92,7 @@ struct Schedule {
     int2 *d_work = nullptr;
     int8_t *d_buckets = nullptr;
     int *ticket = nullptr;
-    long long spin_limit = 0;
+    long long spin_limit = 0;   // bound of every device wait of the schedule's kernels
     int wait_on_unset = 0;
     cudaGraphExec_t graph = nullptr;
     void release();

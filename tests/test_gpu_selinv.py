@@ -117,14 +117,14 @@ def test_batched_mixed_problems_match_oracle(native, cuda_device):
 
 @pytest.mark.parametrize("name,make", [CASES[1], CASES[3], CASES[7], CASES[9]])
 def test_tensor_core_and_dfma_paths_match_oracle(native, cuda_device, name, make):
-    """The FP64-exact bf16 tensor-core contraction and the DFMA contraction
-    both meet the tolerance; they differ only by rounding order."""
+    """The FP64-exact bf16 tensor-core contraction (tcgen05 and mma.sync) and
+    the DFMA contraction all meet the tolerance; they differ only by rounding."""
     import torch
     p = make()
     sym, L, D, Z = oracle_run(p)
     plan = native.selinv_symbolic(sym.n, sym.nsuper, sym.super_ptr, sym.sparent, sym.rowptr, sym.rows)
     outs = []
-    for fast in (1, 0):
+    for fast in (1, 2, 0):
         o = native.selinv_default_opts()
         o.fast_contraction = fast
         native.selinv_plan_set_opts(plan, o)
@@ -136,4 +136,5 @@ def test_tensor_core_and_dfma_paths_match_oracle(native, cuda_device, name, make
         outs.append(Zt.cpu().numpy())
     for G in outs:
         assert oracle.block_errors(sym, G, Z).max() <= TOL
-    assert oracle.block_errors(sym, outs[0], outs[1]).max() <= TOL
+    assert oracle.block_errors(sym, outs[0], outs[2]).max() <= TOL
+    assert oracle.block_errors(sym, outs[1], outs[2]).max() <= TOL
