@@ -118,6 +118,16 @@ struct Item {
 
 constexpr int kTM = 64;   // rows of C per work item
 
+#ifdef __CUDACC__
+// atomicMax on a shared slot that every active lane of the warp targets: one
+// atomic per warp instead of one per lane (the lanes would serialize on it)
+__device__ __forceinline__ void warp_uniform_atomic_max(int *slot, int v) {
+    const unsigned mask = __activemask();
+    const int m = __reduce_max_sync(mask, v);
+    if ((int)(threadIdx.x & 31) == __ffs(mask) - 1) atomicMax(slot, m);
+}
+#endif
+
 // Size class of a supernode's width s: the column tile TN of its kernels.
 inline int bucket_of(int s) {
     if (s <= 8) return 0;

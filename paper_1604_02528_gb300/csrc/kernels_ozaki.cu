@@ -1,12 +1,12 @@
-// FP64-exact contraction A^{-1}_{C,K} = -A^{-1}_{C,C} Lhat_{C,K} on the bf16
+// FP64-exact contraction A^{-1}_{C,K} = -A^{-1}_{C,C} Lhat_{C,K} on the fp16
 // tensor cores (mma.sync m16n8k16, fp32 accumulate).
 //
-// GB300's FP64 pipe delivers ~1.26 TFLOP/s, while its bf16 tensor path is
+// GB300's FP64 pipe delivers ~1.26 TFLOP/s, while its 16-bit tensor path is
 // hundreds of times faster.  Each FP64 operand is cut, without rounding
 // error, into 7 balanced base-256 digits in [-128, 128] on a fixed-point
 // grid shared by its row (A: the gathered A^{-1}_{C,C}, exponent = row
 // maximum) or its column (B: Lhat, exponent = column maximum).  Every digit
-// is exact in bf16 and every digit product (<= 2^14) is exact in fp32.
+// is exact in fp16 and every digit product (<= 2^14) is exact in fp32.
 // Products of digit pairs (i, j) with i + j = g share the scale 2^{-8g}, so
 // they are summed into one fp32 accumulator per g; with at most 7 pairs per
 // g and 128 k-values between flushes the sums stay below 2^24 and are
@@ -17,6 +17,7 @@
 // a max-norm bound.  FP64 accumulation is kept throughout (the int64 sums
 // are exact), as the tree recursion propagates error.
 #include <cuda_runtime.h>
+#include <cuda_fp16.h>
 #include <stdint.h>
 
 #include "common.cuh"
@@ -29,14 +30,14 @@ namespace selinv {
 constexpr int kDig = 7;          // digits per operand
 constexpr int kOzK = 16;         // k per mma step
 constexpr int kFlushSteps = 8;   // 128 k per exact fp32 chunk
-constexpr int kApad = 24;        // smem row stride (bf16) of a 16-wide k slab: conflict-free
+constexpr int kApad = 24;        // smem row stride (fp16) of a 16-wide k slab: conflict-free
 constexpr int kOzThreads = 256;
 
-// bf16 bit pattern of a small integer v (|v| <= 128): exact via an fp32
-// round trip through the magic constant 1.5 * 2^23.
-__device__ __forceinline__ uint32_t bf16_of_int(int v) {
+// fp16 bit pattern of a small integer v (|v| <= 128): exact via an fp32
+// round trip through the magic constant 1.5 * 2^23, then an exact narrowing.
+__device__ __forceinline__ uint32_t f16_of_int(int v) {
     const float f = __int_as_float(0x4B400000 + v) - 12582912.0f;
-    return __float_as_uint(f) >> 16;
+    return (uint32_t)__half_as_ushort(__float2half_rn(f));
 }
 
 // 7 balanced base-256 digits (most significant first) of x on the grid of
@@ -98,14 +99,14 @@ __global__ void __launch_bounds__(256) k_lhat_digits(const ProbDesc *__restrict_
         }
 #pragma unroll
         for (int i = 0; i < kDig; i++)
-            pl[i * plane + (int64_t)j * c16 + q] = (uint16_t)bf16_of_int(d[i]);
+            pl[i * plane + (int64_t)j * c16 + q] = (uint16_t)f16_of_int(d[i]);
     }
 }
 
-__device__ __forceinline__ void mma_bf16(float (&c)[4], uint32_t a0, uint32_t a1, uint32_t a2,
-                                         uint32_t a3, uint32_t b0, uint32_t b1) {
+__device__ __forceinline__ void mma_f16(float (&c)[4], uint32_t a0, uint32_t a1, uint32_t a2,
+                                        uint32_t a3, uint32_t b0, uint32_t b1) {
     asm volatile(
-        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
+        "mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
         "{%8,%9}, {%0,%1,%2,%3};\n"
         : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
         : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
@@ -155,7 +156,7 @@ __global__ void __launch_bounds__(kOzThreads, 1) k_selinv_oz(const ProbDesc *__r
     constexpr int NT = OzShape<TN>::NT;
     constexpr int ABUF = kDig * kTM * kApad, BBUF = kDig * TN * kApad;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    // layout: A digits [2][7][64][kApad] bf16 | B digits [2][7][TN][kApad] bf16 |
+    // layout: A digits [2][7][64][kApad] fp16 | B digits [2][7][TN][kApad] fp16 |
     //         acc hi/lo [64][TN] int64 x 2 | row exponents [64] int
     uint16_t *As = reinterpret_cast<uint16_t *>(smem_raw);
     uint16_t *Bs = As + 2 * ABUF;
@@ -268,13 +269,13 @@ __global__ void __launch_bounds__(kOzThreads, 1) k_selinv_oz(const ProbDesc *__r
 #pragma unroll
             for (int i = 0; i < kDig; i++)
                 *reinterpret_cast<uint32_t *>(Ab + (i * kTM + gl) * kApad + gk) =
-                    bf16_of_int(d0[i]) | (bf16_of_int(d1[i]) << 16);
+                    f16_of_int(d0[i]) | (f16_of_int(d1[i]) << 16);
             digits7(v2, E, d0);
             digits7(v3, E, d1);
 #pragma unroll
             for (int i = 0; i < kDig; i++)
                 *reinterpret_cast<uint32_t *>(Ab + (i * kTM + gl) * kApad + gk + 8) =
-                    bf16_of_int(d0[i]) | (bf16_of_int(d1[i]) << 16);
+                    f16_of_int(d0[i]) | (f16_of_int(d1[i]) << 16);
         }
         // gather of the next step, in flight during this step's tensor-core work
         if (step + 1 < st1) {
@@ -307,7 +308,7 @@ __global__ void __launch_bounds__(kOzThreads, 1) k_selinv_oz(const ProbDesc *__r
             for (int t = 0; t < NT; t++)
 #pragma unroll
                 for (int j = 0; i + j < kDig; j++)
-                    mma_bf16(acc[t][i + j], a0, a1, a2, a3, b[t][j][0], b[t][j][1]);
+                    mma_f16(acc[t][i + j], a0, a1, a2, a3, b[t][j][0], b[t][j][1]);
         }
         // fold the exact fp32 group sums into the int64 accumulators (each
         // element has one owning thread: no synchronization needed)
@@ -337,7 +338,7 @@ __global__ void __launch_bounds__(kOzThreads, 1) k_selinv_oz(const ProbDesc *__r
         const int sc = (rowE[row] - 1022) + (P.colexp[fc + j] - 1022) - 14;
         const double y = fixed_to_double(hi, lo, sc);
         Zk[(int64_t)j * ld + s + p0 + row] = -y;
-        atomicMax(&ymax[j], bexp(y));
+        warp_uniform_atomic_max(&ymax[j], bexp(y));   // the lanes of a warp share column j
     };
     if (nsplit == 1) {
         for (int e = threadIdx.x; e < kTM * TN; e += kOzThreads) {
@@ -378,7 +379,7 @@ __global__ void __launch_bounds__(kOzThreads, 1) k_selinv_oz(const ProbDesc *__r
 }
 
 // ---------------------------------------------------------------------------
-// k_linv_digits: bf16 digit planes of L_KK^{-1} for the tensor-core Lhat
+// k_linv_digits: fp16 digit planes of L_KK^{-1} for the tensor-core Lhat
 // product: per column j, exponent over k; layout plane[j][k], k padded to s16.
 // One warp per column.
 // ---------------------------------------------------------------------------
@@ -411,13 +412,13 @@ __global__ void __launch_bounds__(256) k_linv_digits(const ProbDesc *__restrict_
             for (int i = 0; i < kDig; i++) d[i] = 0;
         }
 #pragma unroll
-        for (int i = 0; i < kDig; i++) pl[i * plane + (int64_t)j * s16 + k] = (uint16_t)bf16_of_int(d[i]);
+        for (int i = 0; i < kDig; i++) pl[i * plane + (int64_t)j * s16 + k] = (uint16_t)f16_of_int(d[i]);
     }
 }
 
 // ---------------------------------------------------------------------------
 // k_lhat_oz<TN>: Lhat(p, j) = sum_k L(s + p, k) L_KK^{-1}(k, j) for one 64-row
-// tile and one column tile, on the bf16 tensor cores.  A = rows of L_{C,K}
+// tile and one column tile, on the fp16 tensor cores.  A = rows of L_{C,K}
 // (row exponent over its s entries), B = the digit planes of L_KK^{-1}.
 // k = s <= 128: a single exact fp32 chunk.
 // ---------------------------------------------------------------------------
@@ -483,7 +484,7 @@ __global__ void __launch_bounds__(kOzThreads, 1) k_lhat_oz(const ProbDesc *__res
 #pragma unroll
             for (int i = 0; i < kDig; i++)
                 *reinterpret_cast<uint32_t *>(As + (i * kTM + pl) * kApad + kk) =
-                    bf16_of_int(d0[i]) | (bf16_of_int(d1[i]) << 16);
+                    f16_of_int(d0[i]) | (f16_of_int(d1[i]) << 16);
         }
         cp_async_wait_all();
         __syncthreads();
@@ -509,7 +510,7 @@ __global__ void __launch_bounds__(kOzThreads, 1) k_lhat_oz(const ProbDesc *__res
             for (int t = 0; t < NT; t++)
 #pragma unroll
                 for (int j = 0; i + j < kDig; j++)
-                    mma_bf16(acc[t][i + j], a0, a1, a2, a3, b[t][j][0], b[t][j][1]);
+                    mma_f16(acc[t][i + j], a0, a1, a2, a3, b[t][j][0], b[t][j][1]);
         }
     }
     double *LD = static_cast<double *>(P.LD) + P.panel_off[K] + s;
@@ -535,7 +536,7 @@ __global__ void __launch_bounds__(kOzThreads, 1) k_lhat_oz(const ProbDesc *__res
 // ---------------------------------------------------------------------------
 // k_diag_oz: contribution of one 64-row tile to the diagonal block,
 // sum_{p in tile} Lhat(p, i) Y(p, j), Y = A^{-1}_{C,K} (already written), on
-// the bf16 tensor cores with the same exact digit scheme:
+// the fp16 tensor cores with the same exact digit scheme:
 //   A = Lhat^T restricted to the tile (rows i, k = p): the Lhat digit planes,
 //       exponent = column exponent of Lhat over all of C;
 //   B = Y restricted to the tile: digits on Y's column exponent over all of C
@@ -547,7 +548,7 @@ __global__ void __launch_bounds__(kOzThreads, 1) k_lhat_oz(const ProbDesc *__res
 // pass over j.
 // ---------------------------------------------------------------------------
 constexpr int kDK = 64;          // k extent (rows of the tile)
-constexpr int kDpad = kDK + 8;   // smem row stride (bf16), conflict-free fragment loads
+constexpr int kDpad = kDK + 8;   // smem row stride (fp16), conflict-free fragment loads
 constexpr int kDJ = 32;          // columns j per pass
 
 __global__ void __launch_bounds__(kOzThreads, 1) k_diag_oz(const ProbDesc *__restrict__ descs,
@@ -610,7 +611,7 @@ __global__ void __launch_bounds__(kOzThreads, 1) k_diag_oz(const ProbDesc *__res
 #pragma unroll
                 for (int i = 0; i < kDig; i++)
                     *reinterpret_cast<uint32_t *>(Bs + (i * kDJ + jl) * kDpad + kk) =
-                        bf16_of_int(d0[i]) | (bf16_of_int(d1[i]) << 16);
+                        f16_of_int(d0[i]) | (f16_of_int(d1[i]) << 16);
             }
             __syncthreads();
         }
@@ -642,7 +643,7 @@ __global__ void __launch_bounds__(kOzThreads, 1) k_diag_oz(const ProbDesc *__res
                         const uint32_t b1 = *reinterpret_cast<const uint32_t *>(bb + qd * 2 + 8);
 #pragma unroll
                         for (int i = 0; i + j < kDig; i++)
-                            mma_bf16(acc[t][i + j], a[i][0], a[i][1], a[i][2], a[i][3], b0, b1);
+                            mma_f16(acc[t][i + j], a[i][0], a[i][1], a[i][2], a[i][3], b0, b1);
                     }
                 }
             }

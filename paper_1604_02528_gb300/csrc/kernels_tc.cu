@@ -1,8 +1,8 @@
 // A^{-1}_{C,K} = -A^{-1}_{C,C} Lhat_{C,K} (Alg. 1, the product after the
 // gather) on the 5th-generation tensor cores: the FP64-exact digit scheme of
-// the mma.sync kernel (7 balanced base-256 digits per operand on a row /
-// column exponent grid, digit products grouped by i + j into exact fp32
-// sums, folded into int64 every 128 k), with
+// the mma.sync kernel (7 balanced base-256 digits per operand, held in fp16,
+// on a row / column exponent grid; digit products grouped by i + j into
+// exact fp32 sums, folded into int64 every 128 k), with
 //   * a 128-row x TN-column output tile per CTA whose 7 group accumulators
 //     live in tensor memory (7 TN columns), written by tcgen05.mma issued from
 //     one thread, completion signalled through mbarriers;
@@ -12,8 +12,8 @@
 //     operations only) and copy the Lhat digit planes of step k + 1;
 //   * every 128 k the group sums are read from tensor memory and added as
 //     int64 into per-element (hi, lo) words in shared memory.
-// Split-k items add their int64 words into a global buffer (exact, order
-// independent); the last item of a row tile writes A^{-1}_{C,K} for it.
+// Split-k items store their int64 words in a per-CTA slab slot; the last item
+// of a row tile sums the slots (exact) and writes A^{-1}_{C,K} for it.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -53,36 +53,51 @@ __device__ __forceinline__ long long fixed54(double x, int E) {
 }
 
 // With u = M + 0x80808080808080 (M as above), byte t of u minus 128 is the
-// balanced base-256 digit of weight 256^t, in [-128, 127].  Two digits (u0's
-// in the low half, u1's in the high half) as a bf16 pair; exact: the digit
-// is formed in fp32 as (1.5 * 2^23 + byte) - (1.5 * 2^23 + 128).
-__device__ __forceinline__ uint32_t digit_pair(unsigned long long u0, unsigned long long u1, int shift) {
-    const float f0 = __int_as_float(0x4B400000 | (int)((u0 >> shift) & 0xFFull)) - 12583040.0f;
-    const float f1 = __int_as_float(0x4B400000 | (int)((u1 >> shift) & 0xFFull)) - 12583040.0f;
+// balanced base-256 digit of weight 256^t, in [-128, 127].  The digits of
+// byte t of two values as an fp16 pair (w0's in the low half): the bytes are
+// placed in the mantissas of 1024 + byte (fp16 bits 0x6400 | byte) and 1152
+// is subtracted -- exact, three instructions per pair.
+template <int T>
+__device__ __forceinline__ uint32_t digit_pair(uint32_t w0, uint32_t w1) {
+    const uint32_t b = __byte_perm(w0, w1, (T & 3) | (((T & 3) + 4) << 8) | (((T & 3) + 4) << 16)) & 0x00FF00FFu;
+    const uint32_t h = b | 0x64006400u;
     uint32_t r;
-    asm("cvt.rn.bf16x2.f32 %0, %1, %2;\n" : "=r"(r) : "f"(f1), "f"(f0));
+    asm("add.rn.f16x2 %0, %1, %2;\n" : "=r"(r) : "r"(h), "r"(0xE480E480u));   // + (-1152, -1152)
     return r;
 }
 
-// Entry (p, q) of A^{-1}_{C,C}: stored at (max, min) by symmetry; pl = p - p0.
+// Digit plane PL (weight 256^(6 - PL)) of the 8 values whose biased fixed-
+// point words are (lo[u], hi[u]): one 16-byte core-matrix row of fp16.
+template <int PL>
+__device__ __forceinline__ void store_plane(uint16_t *dst, const uint32_t (&lo)[8], const uint32_t (&hi)[8]) {
+    constexpr int T = 6 - PL;
+    const uint32_t(&w)[8] = T >= 4 ? hi : lo;
+    uint4 q;
+    q.x = digit_pair<T>(w[0], w[1]);
+    q.y = digit_pair<T>(w[2], w[3]);
+    q.z = digit_pair<T>(w[4], w[5]);
+    q.w = digit_pair<T>(w[6], w[7]);
+    *reinterpret_cast<uint4 *>(dst) = q;
+}
+
+// Address of entry (p, q) of A^{-1}_{C,C} in the ancestors' panels (stored at
+// (max, min) by symmetry), or -1 outside C x C; pl = p - p0.
 struct TcGather {
-    const double *Z;
     const int64_t *pcb, *prb;
     const int32_t *relidx;
     const int64_t *tile_cb, *tile_rb;
     int p0, c;
-    __device__ __forceinline__ double operator()(int pl, int q) const {
+    __device__ __forceinline__ int64_t addr(int pl, int q) const {
         const int p = p0 + pl;
-        if (p >= c || q >= c) return 0.0;
-        const int64_t addr = p >= q ? pcb[q] + relidx[prb[q] + p] : tile_cb[pl] + relidx[tile_rb[pl] + q];
-        return Z[addr];
+        if (p >= c || q >= c) return -1;
+        return p >= q ? pcb[q] + relidx[prb[q] + p] : tile_cb[pl] + relidx[tile_rb[pl] + q];
     }
 };
 
 template <int TN>
 __global__ void __launch_bounds__(kTcThreads, 1) k_selinv_tc(const ProbDesc *__restrict__ descs,
                                                              const Item *__restrict__ items, int nitems,
-                                                             long long wait_limit) {
+                                                             long long *__restrict__ slab, long long wait_limit) {
     using Cfg = TcCfg<TN>;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     uint16_t *As = reinterpret_cast<uint16_t *>(smem_raw);                // [2][7][A_PLANE]
@@ -164,24 +179,35 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_selinv_tc(const ProbDesc *__r
     }
     __syncthreads();
     const uint32_t tmem = s_tmem;
-    const TcGather g{static_cast<const double *>(P.Z), P.colbase + pos0, P.relbase + pos0, P.relidx,
-                     tile_cb, tile_rb, p0, c};
+    const TcGather g{P.colbase + pos0, P.relbase + pos0, P.relidx, tile_cb, tile_rb, p0, c};
+    const double *Zg = static_cast<const double *>(P.Z);
     const uint16_t *Bg = P.lhs + P.lhs_off[K];
     const int64_t bplane = (int64_t)s * c16;
-    const uint32_t idesc = umma::idesc_bf16_f32(kTcM, TN);
+    const uint32_t idesc = umma::idesc_f16_f32(kTcM, TN);
 
-    // this thread's A slot: row r, the 8 k-values kh*8 .. kh*8+7 of each step
+    // this thread's A slot: row r, the 8 k-values kh*8 .. kh*8+7 of each step.
+    // Two-deep software pipeline over the dependent loads of the gather: the
+    // values of step t are loaded during step t-1, their addresses looked up
+    // during step t-2.
     const int r = tid % kTcM, kh = tid / kTcM;
     const int E = rowE[r];
     double v[8];
+    int64_t an[8];
     if (st0 < st1) {
 #pragma unroll
-        for (int u = 0; u < 8; u++) v[u] = g(r, st0 * 16 + kh * 8 + u);
+        for (int u = 0; u < 8; u++) {
+            const int64_t a = g.addr(r, st0 * 16 + kh * 8 + u);
+            v[u] = a >= 0 ? Zg[a] : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < 8; u++) an[u] = st0 + 1 < st1 ? g.addr(r, (st0 + 1) * 16 + kh * 8 + u) : -1;
     }
     int chunk0 = st0;
     bool aborted = false;
     int last_stage = -1, last_use = 0;        // the most recent commit (uniform over the CTA)
-    for (int step = st0; step < st1; step++) {
+    // one k16 step: digits of v (loaded during the previous step), then the
+    // loads of the next step into v; false when a wait ran out
+    auto body = [&](int step) -> bool {
         const int i_ = step - st0;
         const int stage = i_ & 1, use = i_ >> 1;
         const int k0 = step * 16;
@@ -195,42 +221,46 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_selinv_tc(const ProbDesc *__r
             if (n0 + n < s) umma::cp_async16(dst, Bg + pl * bplane + (int64_t)(n0 + n) * c16 + k0 + kg * 8);
             else *reinterpret_cast<uint4 *>(dst) = make_uint4(0, 0, 0, 0);
         }
-        // A digit planes of this step from the values gathered one step ahead
+        // A digit planes of this step
         {
-            unsigned long long u8[8];
+            uint32_t lo[8], hi[8];
 #pragma unroll
-            for (int u = 0; u < 8; u++) u8[u] = (unsigned long long)(fixed54(v[u], E) + 0x80808080808080ll);
-            uint16_t *dst = Ab + (r / 8) * 128 + kh * 64 + (r % 8) * 8;
-#pragma unroll
-            for (int pl = 0; pl < kTcDig; pl++) {
-                const int sh = 8 * (kTcDig - 1 - pl);
-                uint4 q;
-                q.x = digit_pair(u8[0], u8[1], sh);
-                q.y = digit_pair(u8[2], u8[3], sh);
-                q.z = digit_pair(u8[4], u8[5], sh);
-                q.w = digit_pair(u8[6], u8[7], sh);
-                *reinterpret_cast<uint4 *>(dst + pl * Cfg::A_PLANE) = q;
+            for (int u = 0; u < 8; u++) {
+                const unsigned long long w = (unsigned long long)(fixed54(v[u], E) + 0x80808080808080ll);
+                lo[u] = (uint32_t)w;
+                hi[u] = (uint32_t)(w >> 32);
             }
+            uint16_t *dst = Ab + (r / 8) * 128 + kh * 64 + (r % 8) * 8;
+            store_plane<0>(dst + 0 * Cfg::A_PLANE, lo, hi);
+            store_plane<1>(dst + 1 * Cfg::A_PLANE, lo, hi);
+            store_plane<2>(dst + 2 * Cfg::A_PLANE, lo, hi);
+            store_plane<3>(dst + 3 * Cfg::A_PLANE, lo, hi);
+            store_plane<4>(dst + 4 * Cfg::A_PLANE, lo, hi);
+            store_plane<5>(dst + 5 * Cfg::A_PLANE, lo, hi);
+            store_plane<6>(dst + 6 * Cfg::A_PLANE, lo, hi);
         }
-        // gather of the next step, in flight during this step's tensor-core work
-        if (step + 1 < st1) {
+        // loads of the next step's values (in flight until its digits are
+        // formed), address lookups of the one after
 #pragma unroll
-            for (int u = 0; u < 8; u++) v[u] = g(r, k0 + 16 + kh * 8 + u);
-        }
+        for (int u = 0; u < 8; u++) v[u] = an[u] >= 0 ? Zg[an[u]] : 0.0;
+#pragma unroll
+        for (int u = 0; u < 8; u++) an[u] = step + 2 < st1 ? g.addr(r, k0 + 32 + kh * 8 + u) : -1;
         umma::cp_async_wait_all();
         umma::fence_proxy_async();
         __syncthreads();
-        if (s_abort) { aborted = true; break; }
+        if (s_abort) return false;
         const bool first = step == chunk0;
         if (tid == 0) {
             umma::fence_after_sync();
-            const uint32_t a0 = umma::smem_u32(Ab), b0 = umma::smem_u32(Bb);
+            // plane i's descriptor = plane 0's + the plane offset in the start-address field
+            const uint64_t ad0 = umma::smem_desc(umma::smem_u32(Ab), 128, 256);
+            const uint64_t bd0 = umma::smem_desc(umma::smem_u32(Bb), 128, 256);
 #pragma unroll
             for (int i = 0; i < kTcDig; i++) {
-                const uint64_t ad = umma::smem_desc(a0 + i * Cfg::A_PLANE * 2, 128, 256);
+                const uint64_t ad = ad0 + (uint64_t)(i * Cfg::A_PLANE * 2 / 16);
 #pragma unroll
                 for (int j = 0; i + j < kTcDig; j++) {
-                    const uint64_t bd = umma::smem_desc(b0 + j * Cfg::B_PLANE * 2, 128, 256);
+                    const uint64_t bd = bd0 + (uint64_t)(j * Cfg::B_PLANE * 2 / 16);
                     // group i + j starts from zero at its first product of a chunk (i == 0)
                     umma::mma_bf16(tmem + (uint32_t)((i + j) * TN), ad, bd, idesc, (first && i == 0) ? 0u : 1u);
                 }
@@ -267,10 +297,13 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_selinv_tc(const ProbDesc *__r
             }
             umma::fence_before_sync();
             __syncthreads();
-            if (s_abort) { aborted = true; break; }
+            if (s_abort) return false;
             chunk0 = step + 1;
         }
-    }
+        return true;
+    };
+    for (int step = st0; step < st1; step++)
+        if (!body(step)) { aborted = true; break; }
     if (aborted) {
         // a wait ran out: report, give in-flight products a bounded chance to
         // drain, release the tensor memory and leave
@@ -292,7 +325,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_selinv_tc(const ProbDesc *__r
         const int sc = (rowE[row] - 1022) + (P.colexp[fc + j] - 1022) - 13;
         const double y = fixed_to_double(hi, lo, sc);
         Zk[(int64_t)j * ld + s + p0 + row] = -y;
-        atomicMax(&ymax[j], bexp(y));
+        warp_uniform_atomic_max(&ymax[j], bexp(y));   // the lanes of a warp share column j
     };
     if (nsplit == 1) {
         for (int e = tid; e < kTcM * TN; e += kTcThreads) {
@@ -300,14 +333,13 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_selinv_tc(const ProbDesc *__r
             if (p0 + row < c && n0 + col < s) emit(row, n0 + col, Hi[col * kTcM + row], Lo[col * kTcM + row]);
         }
     } else {
-        long long *Yacc = P.yacc + 2 * P.panel_off[K];    // (hi, lo) per element of K's panel
+        // split k: this CTA's partial tile goes to its slab slot (plain
+        // stores); the last CTA of the row tile sums the slots of all column
+        // tiles and k-ranges in k order (integer sums: exact) and writes Y
+        long long *mine = slab + (int64_t)blockIdx.x * 2 * kTcM * 64;
         for (int e = tid; e < kTcM * TN; e += kTcThreads) {
-            const int row = e % kTcM, col = e / kTcM;
-            if (p0 + row >= c || n0 + col >= s) continue;
-            unsigned long long *dst = reinterpret_cast<unsigned long long *>(Yacc + 2 * ((int64_t)(n0 + col) * ld + s + p0 + row));
-            const long long h = Hi[col * kTcM + row], l = Lo[col * kTcM + row];
-            if (h) atomicAdd(dst, (unsigned long long)h);
-            if (l) atomicAdd(dst + 1, (unsigned long long)l);
+            mine[e] = Hi[e];
+            mine[kTcM * 64 + e] = Lo[e];
         }
         __threadfence();
         __syncthreads();
@@ -316,13 +348,18 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_selinv_tc(const ProbDesc *__r
         __syncthreads();
         if (!s_last) return;
         __threadfence();
+        // the row tile's items are consecutive: (column tile, k-range) ordered
+        const int64_t group0 = (int64_t)blockIdx.x - (it.tile - tile * ncol * nsplit);
         for (int e = tid; e < kTcM * s; e += kTcThreads) {
             const int row = e % kTcM, j = e / kTcM;
             if (p0 + row >= c) continue;
-            unsigned long long *q = reinterpret_cast<unsigned long long *>(Yacc + 2 * ((int64_t)j * ld + s + p0 + row));
-            const long long hi = (long long)__ldcg(q), lo = (long long)__ldcg(q + 1);
-            q[0] = 0ull;
-            q[1] = 0ull;
+            const int ctj = j / TN, col = j % TN;
+            long long hi = 0, lo = 0;
+            for (int k2 = 0; k2 < nsplit; k2++) {
+                const long long *sl = slab + (group0 + ctj * nsplit + k2) * 2 * kTcM * 64;
+                hi += __ldcg(sl + col * kTcM + row);
+                lo += __ldcg(sl + kTcM * 64 + col * kTcM + row);
+            }
             emit(row, j, hi, lo);
         }
         if (tid == 0) *ctr = 0;
@@ -340,12 +377,12 @@ cudaError_t configure_tc_kernels() {
     return e;
 }
 
-cudaError_t launch_selinv_tc(int tn, const ProbDesc *d, const Item *items, int n, long long wait_limit,
-                             cudaStream_t st) {
+cudaError_t launch_selinv_tc(int tn, const ProbDesc *d, const Item *items, int n, long long *slab,
+                             long long wait_limit, cudaStream_t st) {
     if (n <= 0) return cudaSuccess;
-    if (tn == 16) k_selinv_tc<16><<<n, kTcThreads, TcCfg<16>::SMEM, st>>>(d, items, n, wait_limit);
-    else if (tn == 32) k_selinv_tc<32><<<n, kTcThreads, TcCfg<32>::SMEM, st>>>(d, items, n, wait_limit);
-    else k_selinv_tc<64><<<n, kTcThreads, TcCfg<64>::SMEM, st>>>(d, items, n, wait_limit);
+    if (tn == 16) k_selinv_tc<16><<<n, kTcThreads, TcCfg<16>::SMEM, st>>>(d, items, n, slab, wait_limit);
+    else if (tn == 32) k_selinv_tc<32><<<n, kTcThreads, TcCfg<32>::SMEM, st>>>(d, items, n, slab, wait_limit);
+    else k_selinv_tc<64><<<n, kTcThreads, TcCfg<64>::SMEM, st>>>(d, items, n, slab, wait_limit);
     return cudaGetLastError();
 }
 

@@ -338,8 +338,8 @@ ProbDesc make_desc(const PlanData &p, Workspace &w, int dtype, const void *L, co
 void Schedule::release() {
     if (graph) cudaGraphExecDestroy(graph);
     graph = nullptr;
-    dfree(d_descs); dfree(d_items); dfree(d_work); dfree(d_buckets);
-    d_descs = nullptr; d_items = nullptr; d_work = nullptr; d_buckets = nullptr;
+    dfree(d_descs); dfree(d_items); dfree(d_work); dfree(d_buckets); dfree(tcslab);
+    d_descs = nullptr; d_items = nullptr; d_work = nullptr; d_buckets = nullptr; tcslab = nullptr;
 }
 
 int build_schedule(Schedule &S, const std::vector<const PlanData *> &plans,
@@ -584,6 +584,13 @@ int build_schedule(Schedule &S, const std::vector<const PlanData *> &plans,
     if ((rc = upload(&S.d_items, S.h_items))) return rc;
     if ((rc = upload(&S.d_work, S.h_work))) return rc;
     if (!S.h_buckets.empty() && (rc = upload(&S.d_buckets, S.h_buckets))) return rc;
+    // one partial (hi, lo) tile of 128 x 64 per CTA of the widest tcgen05 launch
+    int64_t tc_ctas = 0;
+    for (const Launch &L : S.launches)
+        if (L.kind == KL_SELINV_TC) tc_ctas = std::max<int64_t>(tc_ctas, L.count);
+    if (tc_ctas > 0 &&
+        cudaMalloc((void **)&S.tcslab, sizeof(long long) * 2 * kTcRows * 64 * (size_t)tc_ctas) != cudaSuccess)
+        return SELINV_ERR_OOM;
     return SELINV_OK;
 }
 
@@ -598,7 +605,7 @@ cudaError_t launch_one(const Schedule &S, const Launch &L, cudaStream_t st) {
     case KL_LINV_DIGITS: return launch_linv_digits(S.d_descs, S.d_work + L.off, L.count, st);
     case KL_LHAT_OZ: return launch_lhat_oz(L.bucket, S.d_descs, S.d_items + L.off, L.count, st);
     case KL_SELINV_TC:
-        return launch_selinv_tc(L.bucket, S.d_descs, S.d_items + L.off, L.count, S.spin_limit, st);
+        return launch_selinv_tc(L.bucket, S.d_descs, S.d_items + L.off, L.count, S.tcslab, S.spin_limit, st);
     case KL_PERSIST: {
         for (size_t r = 0; r < S.reset_ptr.size(); r++) {
             cudaError_t e = cudaMemsetAsync(S.reset_ptr[r], 0, S.reset_bytes[r], st);

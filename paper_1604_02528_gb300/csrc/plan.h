@@ -92,6 +92,7 @@ struct Schedule {
     int2 *d_work = nullptr;
     int8_t *d_buckets = nullptr;
     int *ticket = nullptr;
+    long long *tcslab = nullptr;  // split-k partial tiles of the tcgen05 launches, one per CTA
     long long spin_limit = 0;   // bound of every device wait of the schedule's kernels
     int wait_on_unset = 0;
     cudaGraphExec_t graph = nullptr;

@@ -24,12 +24,15 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint
            ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
 }
 
-// Instruction descriptor of kind::f16 with bf16 A and B (both K-major), f32
+// Instruction descriptor of kind::f16 with 16-bit A and B (both K-major), f32
 // accumulator, M x N: D format in bits 4-5 (1 = f32), A format in bits 7-9
-// and B format in bits 10-12 (1 = bf16), N >> 3 in bits 17-22, M >> 4 in
-// bits 24-28.
+// and B format in bits 10-12 (0 = f16, 1 = bf16), N >> 3 in bits 17-22,
+// M >> 4 in bits 24-28.
 __host__ __device__ constexpr uint32_t idesc_bf16_f32(int M, int N) {
     return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+__host__ __device__ constexpr uint32_t idesc_f16_f32(int M, int N) {
+    return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
 // Tensor memory: allocation by one whole warp; the base address is written
@@ -45,7 +48,7 @@ __device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(taddr), "r"(ncols));
 }
 
-// D[tmem] (+)= A[smem] x B[smem]; issued by one thread.
+// D[tmem] (+)= A[smem] x B[smem] (kind::f16: fp16 or bf16 operands); issued by one thread.
 __device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
                                          uint32_t accumulate) {
     asm volatile(
