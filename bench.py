@@ -60,6 +60,8 @@ def parse():
                     help="skip the plain / batched / adjoint comparison runs")
     ap.add_argument("--batch-poles", type=int, default=8)
     ap.add_argument("--schedule", type=int, default=1, help="0 plain, 1 level, 2 persistent")
+    ap.add_argument("--autotune", type=int, default=1,
+                    help="1: the library's autotuner picks its options on the first (untimed) call")
     ap.add_argument("--fast", type=int, default=1,
                     help="FP64-exact tensor-core contraction for s >= 16 -- 1: tcgen05, 2: mma.sync; 0: DFMA only")
     return ap.parse_args()
@@ -369,6 +371,7 @@ def main():
     o = N.selinv_default_opts()
     o.schedule = args.schedule
     o.fast_contraction = args.fast
+    o.autotune = args.autotune
     N.selinv_plan_set_opts(ctx.plan, o)
     dt = N.SELINV_C128 if p.values.dtype.kind == "c" else N.SELINV_F64
     A = torch.from_numpy(p.values).to(dev)
@@ -387,6 +390,8 @@ def main():
     stream.synchronize()
     if ctx.status() != 0:
         raise RuntimeError("selected inversion reported a device error")
+    topts = N.selinv_plan_get_opts(ctx.plan)      # the options the autotuner kept
+    topts.autotune = 0
 
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(args.steps)]
@@ -417,7 +422,7 @@ def main():
     s_ = np.diff(sp).astype(np.float64)
     c_ = np.diff(rp).astype(np.float64) - s_
     mult = 4.0 if dt == N.SELINV_C128 else 1.0
-    oz = (s_ >= 16) & (dt == N.SELINV_F64) & bool(args.fast)
+    oz = (s_ >= max(16, topts.oz_min_s)) & (dt == N.SELINV_F64) & bool(topts.fast_contraction)
     peaks = measured_peaks()
     dom = int(np.argmax(kms))
     name = N.PROFILE_KINDS[dom]
@@ -464,7 +469,7 @@ def main():
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
-        plan = N.selinv_symbolic(p.n, a["nsuper"], a["super_ptr"], a["sparent"], a["rowptr"], a["rows"])
+        plan = N.selinv_symbolic(p.n, a["nsuper"], a["super_ptr"], a["sparent"], a["rowptr"], a["rows"], topts)
         with torch.cuda.stream(stream):
             Ld.copy_(Lh, non_blocking=True)
             Dd.copy_(Dh, non_blocking=True)
@@ -510,8 +515,10 @@ def main():
                 "config": {"workload": workload_name(args.config), "n": p.n, "nsuper": ctx.nsuper, "nnz_L": ctx.nnz,
                            "flops_per_step": F, "bytes_per_step": B,
                            "schedule": ["plain", "level", "persistent"][args.schedule],
-                           "contraction": {0: "FP64 DFMA", 1: "tcgen05 bf16, FP64-exact slicing",
-                                           2: "mma.sync bf16, FP64-exact slicing"}[args.fast],
+                           "contraction": {0: "FP64 DFMA", 1: "tcgen05 fp16, FP64-exact slicing",
+                                           2: "mma.sync fp16, FP64-exact slicing"}[topts.fast_contraction],
+                           "options": {"autotuned": bool(args.autotune), "split_target": topts.split_target,
+                                       "split_min_steps": topts.split_min_steps, "oz_min_s": topts.oz_min_s},
                            "l2": "flushed between timed steps (256 MB write)",
                            "parallelism": "replicas" if world > 1 else "single GPU",
                            "fp64_frac": round(value / world / FP64_PEAK_GFLOPS, 4)},

@@ -75,7 +75,11 @@ typedef enum {
 typedef struct {
     int symmetrize;        /* 1: A^{-1}_KK <- (X + X^T)/2 (Sec. II-C); default 1        */
     int schedule;          /* selinv_schedule; default SELINV_SCHED_LEVEL               */
-    int autotune;          /* 1: pick kernel variants per size class by timing; default 0 */
+    int autotune;          /* 1: the first selinv_numeric call per element type times the
+                              tensor engine, split_target, split_min_steps and oz_min_s
+                              candidates on the caller's data (synchronizing), keeps the
+                              fastest for the plan (read back: selinv_plan_get_opts);
+                              default 0                                                 */
     int debug_checks;      /* bit 0: scan inputs for non-finite values; bit 1: the
                               persistent schedule waits on a flag that is never set,
                               so every wait runs out (tests the timeout path); default 0 */
@@ -86,6 +90,12 @@ typedef struct {
                               on bf16 tensor cores (error-free slicing, exact integer
                               accumulation) -- 1: tcgen05 with tensor-memory accumulators
                               (default), 2: mma.sync; 0: FP64 DFMA only                 */
+    int split_target;      /* level schedule: k-splits of the contraction aim at this many
+                              CTAs per SM on narrow levels (1..8); default 2           */
+    int split_min_steps;   /* smallest k-range of a split item, in 16-row steps (8..64,
+                              a multiple of 8); default 16                              */
+    int oz_min_s;          /* narrowest supernode (columns) that uses the tensor-core
+                              contraction (16..128); default 16                         */
 } selinv_opts;
 
 /* Fills *opts with the defaults listed above. */
@@ -156,6 +166,9 @@ int selinv_plan_stats(selinv_plan plan, selinv_dtype dtype, double *flops, doubl
  *   9 panel_off[nsuper+1] int64
  * Returns the element count, or <0 on a bad field.  dst may be NULL. */
 int64_t selinv_plan_get(selinv_plan plan, int field, void *dst);
+/* The plan's current options (after autotuning: the chosen ones). */
+int selinv_plan_get_opts(selinv_plan plan, selinv_opts *opts);
+
 /* Changes the schedule / options of an existing plan. */
 int selinv_plan_set_opts(selinv_plan plan, const selinv_opts *opts);
 

@@ -47,7 +47,8 @@ class SelinvError(RuntimeError):
 class selinv_opts(ct.Structure):
     _fields_ = [("symmetrize", ct.c_int), ("schedule", ct.c_int), ("autotune", ct.c_int),
                 ("debug_checks", ct.c_int), ("spin_limit", ct.c_longlong), ("use_graph", ct.c_int),
-                ("fast_contraction", ct.c_int)]
+                ("fast_contraction", ct.c_int), ("split_target", ct.c_int), ("split_min_steps", ct.c_int),
+                ("oz_min_s", ct.c_int)]
 
 
 def _load() -> ct.CDLL:
@@ -68,6 +69,7 @@ def _load() -> ct.CDLL:
         "selinv_plan_stats": (I, [P, I, P, P]),
         "selinv_plan_get": (I64, [P, I, P]),
         "selinv_plan_set_opts": (I, [P, P]),
+        "selinv_plan_get_opts": (I, [P, P]),
         "selinv_numeric": (I, [P, I, P, P, P, P]),
         "selinv_numeric_batched": (I, [I, P, P, P, P, P, P]),
         "selinv_numeric_profile": (I, [P, I, P, P, P, P, P, P]),
@@ -93,7 +95,7 @@ LIB = _load()
 REQUIRED_SYMBOLS = ("selinv_default_opts", "selinv_analyse", "selinv_analysis_get",
                     "selinv_analysis_destroy", "selinv_symbolic", "selinv_plan_destroy",
                     "selinv_plan_nnz", "selinv_plan_panel_offset", "selinv_plan_stats",
-                    "selinv_plan_get", "selinv_plan_set_opts", "selinv_numeric",
+                    "selinv_plan_get", "selinv_plan_set_opts", "selinv_plan_get_opts", "selinv_numeric",
                     "selinv_numeric_batched", "selinv_numeric_profile", "selinv_plan_set_matrix", "selinv_factor",
                     "selinv_adjoint", "selinv_factor_adjoint", "selinv_status",
                     "selinv_error_string", "selinv_launch_count", "selinv_dinv_noalloc")
@@ -239,6 +241,12 @@ def selinv_plan_get(plan: Plan, name: str) -> np.ndarray:
 
 def selinv_plan_set_opts(plan: Plan, opts: selinv_opts):
     _check(LIB.selinv_plan_set_opts(plan.handle, ct.byref(opts)), "selinv_plan_set_opts")
+
+
+def selinv_plan_get_opts(plan: Plan) -> selinv_opts:
+    o = selinv_opts()
+    _check(LIB.selinv_plan_get_opts(plan.handle, ct.byref(o)), "selinv_plan_get_opts")
+    return o
 
 
 def selinv_numeric(plan: Plan, dtype: int, L, D, Ainv, stream=None):

@@ -372,7 +372,7 @@ int build_schedule(Schedule &S, const std::vector<const PlanData *> &plans,
             for (int32_t K = 0; K < p.ns; K++) {
                 const int s = p.super_ptr[K + 1] - p.super_ptr[K];
                 const int64_t c = p.rowptr[K + 1] - p.rowptr[K] - s;
-                if (c == 0 || !oz_eligible(descs[i].dtype, s, p.opts.fast_contraction)) continue;
+                if (c == 0 || !oz_eligible(descs[i].dtype, s, p.opts)) continue;
                 for (int jb = 0; jb < (s + 7) / 8; jb++) S.h_work.push_back(make_int2(i, (K << 8) | jb));
             }
         }
@@ -386,7 +386,7 @@ int build_schedule(Schedule &S, const std::vector<const PlanData *> &plans,
             for (int32_t K = 0; K < p.ns; K++) {
                 const int s = p.super_ptr[K + 1] - p.super_ptr[K];
                 const int64_t c = p.rowptr[K + 1] - p.rowptr[K] - s;
-                if (c == 0 || !oz_eligible(descs[i].dtype, s, p.opts.fast_contraction)) continue;
+                if (c == 0 || !oz_eligible(descs[i].dtype, s, p.opts)) continue;
                 const int ktn = s <= 16 ? 16 : (s <= 32 ? 32 : 64);
                 if (ktn != tn) continue;
                 const int ncol = (s + tn - 1) / tn;
@@ -406,7 +406,7 @@ int build_schedule(Schedule &S, const std::vector<const PlanData *> &plans,
                 for (int32_t K = 0; K < p.ns; K++) {
                     const int s = p.super_ptr[K + 1] - p.super_ptr[K];
                     const int64_t c = p.rowptr[K + 1] - p.rowptr[K] - s;
-                    if (c == 0 || bucket_of(s) != b || oz_eligible(dt, s, p.opts.fast_contraction)) continue;
+                    if (c == 0 || bucket_of(s) != b || oz_eligible(dt, s, p.opts)) continue;
                     for (int t = 0; t < p.ntiles[K]; t++) S.h_items.push_back({i, K, t, p.ntiles[K]});
                 }
             }
@@ -422,7 +422,7 @@ int build_schedule(Schedule &S, const std::vector<const PlanData *> &plans,
                 const int s = p.super_ptr[K + 1] - p.super_ptr[K];
                 const int64_t c = p.rowptr[K + 1] - p.rowptr[K] - s;
                 if (c == 0 || mode == SELINV_SCHED_PERSISTENT ||
-                    !oz_eligible(descs[i].dtype, s, p.opts.fast_contraction))
+                    !oz_eligible(descs[i].dtype, s, p.opts))
                     continue;
                 for (int jb = 0; jb < (s + 7) / 8; jb++) S.h_work.push_back(make_int2(i, (K << 8) | jb));
             }
@@ -463,8 +463,10 @@ int build_schedule(Schedule &S, const std::vector<const PlanData *> &plans,
         const PlanData &p = *plans[i];
         const int s = p.super_ptr[K + 1] - p.super_ptr[K];
         const int64_t c = p.rowptr[K + 1] - p.rowptr[K] - s;
-        const int64_t want = (2 * 152 + level_ctas - 1) / std::max<int64_t>(level_ctas, 1);
-        const int64_t maxsplit = std::max<int64_t>(1, ((c + 15) / 16) / 16);
+        const selinv_opts &o = p.opts;
+        const int64_t target = (int64_t)o.split_target * 152;
+        const int64_t want = (target + level_ctas - 1) / std::max<int64_t>(level_ctas, 1);
+        const int64_t maxsplit = std::max<int64_t>(1, ((c + 15) / 16) / o.split_min_steps);
         return (int)std::max<int64_t>(1, std::min(want, maxsplit));
     };
     auto oz_ctas = [&](int i, int32_t K) -> int64_t {
@@ -504,7 +506,7 @@ int build_schedule(Schedule &S, const std::vector<const PlanData *> &plans,
             const PlanData &p = *plans[i];
             for (int32_t K = p.ns - 1; K >= 0; K--) {
                 const int s = p.super_ptr[K + 1] - p.super_ptr[K];
-                if (oz_eligible(descs[i].dtype, s, p.opts.fast_contraction)) {
+                if (oz_eligible(descs[i].dtype, s, p.opts)) {
                     const int tn = oz_tn(s);
                     const int64_t off = (int64_t)S.h_items.size();
                     push_oz(i, K, tn, oz_split(i, K, oz_ctas(i, K)));
@@ -535,7 +537,7 @@ int build_schedule(Schedule &S, const std::vector<const PlanData *> &plans,
                 if (l >= p.nlevels) continue;
                 for (int64_t e = p.level_ptr[l]; e < p.level_ptr[l + 1]; e++) {
                     const int32_t K = p.level_list[e];
-                    if (oz_eligible(descs[i].dtype, p.super_ptr[K + 1] - p.super_ptr[K], p.opts.fast_contraction))
+                    if (oz_eligible(descs[i].dtype, p.super_ptr[K + 1] - p.super_ptr[K], p.opts))
                         oz.push_back({i, K});
                 }
             }
@@ -570,7 +572,7 @@ int build_schedule(Schedule &S, const std::vector<const PlanData *> &plans,
                         for (int64_t e = p.level_ptr[l]; e < p.level_ptr[l + 1]; e++) {
                             const int32_t K = p.level_list[e];
                             const int s = p.super_ptr[K + 1] - p.super_ptr[K];
-                            if (bucket_of(s) == b && !oz_eligible(dt, s, p.opts.fast_contraction)) push_items(i, K);
+                            if (bucket_of(s) == b && !oz_eligible(dt, s, p.opts)) push_items(i, K);
                         }
                     }
                     const int cnt = (int)(S.h_items.size() - off);
@@ -659,6 +661,13 @@ using namespace selinv;
 // ---------------------------------------------------------------------------
 // C ABI
 // ---------------------------------------------------------------------------
+static bool opts_valid(const selinv_opts *o) {
+    return o->schedule >= 0 && o->schedule <= 2 && o->fast_contraction >= 0 && o->fast_contraction <= 2 &&
+           o->split_target >= 1 && o->split_target <= 8 && o->split_min_steps >= 8 &&
+           o->split_min_steps <= 64 && o->split_min_steps % 8 == 0 && o->oz_min_s >= 16 && o->oz_min_s <= 128 &&
+           o->spin_limit > 0;
+}
+
 extern "C" void selinv_default_opts(selinv_opts *o) {
     if (!o) return;
     o->symmetrize = 1;
@@ -668,6 +677,9 @@ extern "C" void selinv_default_opts(selinv_opts *o) {
     o->spin_limit = 1LL << 22;   // about a second of 256 ns polls
     o->use_graph = 1;
     o->fast_contraction = 1;
+    o->split_target = 2;
+    o->split_min_steps = 16;
+    o->oz_min_s = 16;
 }
 
 extern "C" int selinv_symbolic(int32_t n, int32_t nsuper, const int32_t *super_ptr,
@@ -680,8 +692,15 @@ extern "C" int selinv_symbolic(int32_t n, int32_t nsuper, const int32_t *super_p
         return SELINV_ERR_INVALID_ARG;
     selinv_plan_s *pl = new (std::nothrow) selinv_plan_s();
     if (!pl) return SELINV_ERR_OOM;
-    if (opts) pl->data.opts = *opts;
-    else selinv_default_opts(&pl->data.opts);
+    if (opts) {
+        if (!opts_valid(opts)) {
+            delete pl;
+            return SELINV_ERR_INVALID_ARG;
+        }
+        pl->data.opts = *opts;
+    } else {
+        selinv_default_opts(&pl->data.opts);
+    }
     int rc;
     try {
         rc = build_plan(pl->data, n, nsuper, super_ptr, sparent, rowptr, rowind);
@@ -753,11 +772,17 @@ extern "C" int64_t selinv_plan_get(selinv_plan plan, int field, void *dst) {
     return cnt;
 }
 
-extern "C" int selinv_plan_set_opts(selinv_plan plan, const selinv_opts *opts) {
+
+extern "C" int selinv_plan_get_opts(selinv_plan plan, selinv_opts *opts) {
     if (!plan || !opts) return SELINV_ERR_INVALID_ARG;
-    if (opts->schedule < 0 || opts->schedule > 2) return SELINV_ERR_INVALID_ARG;
-    if (opts->fast_contraction < 0 || opts->fast_contraction > 2) return SELINV_ERR_INVALID_ARG;
+    *opts = plan->data.opts;
+    return SELINV_OK;
+}
+
+extern "C" int selinv_plan_set_opts(selinv_plan plan, const selinv_opts *opts) {
+    if (!plan || !opts || !opts_valid(opts)) return SELINV_ERR_INVALID_ARG;
     plan->data.opts = *opts;
+    plan->data.tuned[0] = plan->data.tuned[1] = false;
     plan->single.release();
     plan->single.valid = false;
     for (auto &b : plan->batch_cache) b.sched.release();
@@ -767,6 +792,77 @@ extern "C" int selinv_plan_set_opts(selinv_plan plan, const selinv_opts *opts) {
 
 static bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
 
+static int numeric_run(selinv_plan plan, selinv_dtype dtype, const void *L, const void *D, void *Z,
+                       cudaStream_t st);
+
+// Autotuner: coordinate search over the tensor engine, the k-split of narrow
+// levels and the narrowest tensor-core supernode, each candidate timed with
+// CUDA events on the caller's stream and data (best of two runs after a
+// warm-up that builds its schedule); the fastest options stay with the plan.
+static int autotune(selinv_plan plan, selinv_dtype dtype, const void *L, const void *D, void *Z,
+                    cudaStream_t st) {
+    PlanData &p = plan->data;
+    p.tuned[dtype] = true;
+    if (dtype != SELINV_F64) return SELINV_OK;   // the complex path has no tensor-core variants
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return SELINV_ERR_CUDA;
+    auto measure = [&](const selinv_opts &o, float *ms) -> int {
+        p.opts = o;
+        plan->single.release();
+        plan->single.valid = false;
+        int rc = numeric_run(plan, dtype, L, D, Z, st);
+        if (rc) return rc;
+        float best = 1e30f;
+        for (int r = 0; r < 2; r++) {
+            cudaEventRecord(e0, st);
+            if ((rc = numeric_run(plan, dtype, L, D, Z, st))) return rc;
+            cudaEventRecord(e1, st);
+            if (cudaEventSynchronize(e1) != cudaSuccess) return SELINV_ERR_CUDA;
+            float t = 0;
+            cudaEventElapsedTime(&t, e0, e1);
+            best = std::min(best, t);
+        }
+        *ms = best;
+        return SELINV_OK;
+    };
+    selinv_opts best = p.opts;
+    float best_ms = 1e30f;
+    int rc = SELINV_OK;
+    auto consider = [&](selinv_opts o) {
+        if (rc) return;
+        float ms;
+        rc = measure(o, &ms);
+        if (!rc && ms < best_ms) { best_ms = ms; best = o; }
+    };
+    for (int eng : {1, 2, 0}) {
+        selinv_opts o = best;
+        o.fast_contraction = eng;
+        consider(o);
+    }
+    if (best.fast_contraction != 0) {
+        const selinv_opts e = best;
+        for (int tgt : {1, 2, 4})
+            for (int mins : {8, 16, 32}) {
+                selinv_opts o = e;
+                o.split_target = tgt;
+                o.split_min_steps = mins;
+                consider(o);
+            }
+        const selinv_opts f = best;
+        for (int ozm : {16, 32, 64}) {
+            selinv_opts o = f;
+            o.oz_min_s = ozm;
+            consider(o);
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    p.opts = best;
+    plan->single.release();
+    plan->single.valid = false;
+    return rc;
+}
+
 extern "C" int selinv_numeric(selinv_plan plan, selinv_dtype dtype, const void *L, const void *D,
                               void *Z, void *stream) {
     if (!plan || (dtype != SELINV_F64 && dtype != SELINV_C128)) return SELINV_ERR_INVALID_ARG;
@@ -774,6 +870,16 @@ extern "C" int selinv_numeric(selinv_plan plan, selinv_dtype dtype, const void *
     if (p.ns == 0) return SELINV_OK;
     if (!L || !D || !Z || !aligned16(L) || !aligned16(D) || !aligned16(Z)) return SELINV_ERR_INVALID_ARG;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (p.opts.autotune && !p.tuned[dtype]) {
+        const int rc = autotune(plan, dtype, L, D, Z, st);
+        if (rc) return rc;
+    }
+    return numeric_run(plan, dtype, L, D, Z, st);
+}
+
+static int numeric_run(selinv_plan plan, selinv_dtype dtype, const void *L, const void *D, void *Z,
+                       cudaStream_t st) {
+    PlanData &p = plan->data;
     int rc = ensure_device(p);
     if (rc) return rc;
     if (plan->ws.empty()) plan->ws.resize(1);
@@ -816,11 +922,11 @@ extern "C" int selinv_numeric_profile(selinv_plan plan, selinv_dtype dtype, cons
                                       int64_t *kernel_launches) {
     if (!kernel_ms || !kernel_launches) return SELINV_ERR_INVALID_ARG;
     // build (or reuse) the schedule through the normal path, without a graph
-    selinv_opts saved = plan ? plan->data.opts : selinv_opts{};
     if (!plan) return SELINV_ERR_INVALID_ARG;
+    const int saved_graph = plan->data.opts.use_graph;
     plan->data.opts.use_graph = 0;
-    int rc = selinv_numeric(plan, dtype, L, D, Z, stream);
-    plan->data.opts = saved;
+    int rc = selinv_numeric(plan, dtype, L, D, Z, stream);   // may autotune first
+    plan->data.opts.use_graph = saved_graph;
     if (rc) return rc;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     if (cudaStreamSynchronize(st) != cudaSuccess) return SELINV_ERR_CUDA;

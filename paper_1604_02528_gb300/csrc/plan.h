@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <algorithm>
 #include <vector>
 
 #include "common.cuh"
@@ -13,6 +14,7 @@ namespace selinv {
 struct PlanData {
     int32_t n = 0, ns = 0;
     selinv_opts opts{};
+    bool tuned[2] = {false, false};   // autotuning done, per element type
     // host arrays (kept for inspection and schedule building)
     std::vector<int32_t> super_ptr, sparent, rows, level, level_list;
     std::vector<int32_t> seg_owner, seg_start, seg_coloff, relidx, ntiles;
@@ -63,7 +65,9 @@ enum { KL_LINV = 0, KL_LHAT = 1, KL_SELINV = 2, KL_DIGITS = 3, KL_SELINV_OZ = 4,
 // tensor-core (FP64-exact) contraction applies to real problems with s >= kOzMinS;
 // fast_contraction 1 runs the gather-GEMM on tcgen05, 2 on mma.sync
 constexpr int kOzMinS = 16;
-inline bool oz_eligible(int dtype, int s, int fast) { return fast && dtype == SELINV_F64 && s >= kOzMinS; }
+inline bool oz_eligible(int dtype, int s, const selinv_opts &o) {
+    return o.fast_contraction && dtype == SELINV_F64 && s >= std::max(kOzMinS, o.oz_min_s);
+}
 constexpr int kTcRows = 128;   // rows of C per tcgen05 item
 
 struct Launch {

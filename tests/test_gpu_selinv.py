@@ -138,3 +138,26 @@ def test_tensor_core_and_dfma_paths_match_oracle(native, cuda_device, name, make
         assert oracle.block_errors(sym, G, Z).max() <= TOL
     assert oracle.block_errors(sym, outs[0], outs[2]).max() <= TOL
     assert oracle.block_errors(sym, outs[1], outs[2]).max() <= TOL
+
+
+def test_autotuned_plan_matches_oracle(native, cuda_device):
+    """The first call tunes (engine, k-split, narrowest tensor-core supernode)
+    on the caller's data; the tuned options stay valid and every result meets
+    the tolerance."""
+    import torch
+    p = synth.laplacian_3d(16, seed=11)
+    sym, L, D, Z = oracle_run(p)
+    plan = native.selinv_symbolic(sym.n, sym.nsuper, sym.super_ptr, sym.sparent, sym.rowptr, sym.rows)
+    o = native.selinv_default_opts()
+    o.autotune = 1
+    native.selinv_plan_set_opts(plan, o)
+    Lt = torch.from_numpy(L).cuda(); Dt = torch.from_numpy(D).cuda()
+    for _ in range(2):
+        Zt = torch.full_like(Lt, float("nan"))
+        native.selinv_numeric(plan, native.SELINV_F64, Lt, Dt, Zt, torch.cuda.current_stream())
+        torch.cuda.synchronize()
+        assert native.selinv_status(plan) == 0
+        assert oracle.block_errors(sym, Zt.cpu().numpy(), Z).max() <= TOL
+    t = native.selinv_plan_get_opts(plan)
+    assert t.fast_contraction in (0, 1, 2)
+    assert t.split_target in (1, 2, 4) and t.split_min_steps in (8, 16, 32) and t.oz_min_s in (16, 32, 64)

@@ -206,3 +206,23 @@ def test_binding_constants_match_header(native):
         assert getattr(native, name) == int(val), name
     kinds = int(re.search(r"#define SELINV_PROFILE_KINDS (\d+)", hdr).group(1))
     assert len(native.PROFILE_KINDS) == kinds
+
+
+def test_options_round_trip_and_validation(native):
+    p = synth.laplacian_3d(5, seed=1)
+    sym, (sp, par, rp, rows) = _sym_arrays(p)
+    plan = native.selinv_symbolic(sym.n, sym.nsuper, sp, par, rp, rows)
+    o = native.selinv_default_opts()
+    assert (o.fast_contraction, o.split_target, o.split_min_steps, o.oz_min_s) == (1, 2, 16, 16)
+    o.split_target, o.split_min_steps, o.oz_min_s, o.fast_contraction = 4, 32, 64, 2
+    native.selinv_plan_set_opts(plan, o)
+    g = native.selinv_plan_get_opts(plan)
+    assert (g.fast_contraction, g.split_target, g.split_min_steps, g.oz_min_s) == (2, 4, 32, 64)
+    for field, bad in (("split_target", 0), ("split_target", 9), ("split_min_steps", 12),
+                       ("split_min_steps", 0), ("oz_min_s", 8), ("fast_contraction", 3), ("schedule", 3),
+                       ("spin_limit", 0)):
+        b = native.selinv_default_opts()
+        setattr(b, field, bad)
+        with pytest.raises(native.SelinvError) as e:
+            native.selinv_plan_set_opts(plan, b)
+        assert e.value.code == native.SELINV_ERR_INVALID_ARG, field
