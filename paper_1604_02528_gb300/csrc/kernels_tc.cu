@@ -26,9 +26,13 @@
 namespace selinv {
 
 constexpr int kTcM = 128;          // rows of C per item (tensor-memory lanes)
-constexpr int kTcThreads = 256;
+constexpr int kTcProd = 8;         // producer warps: gather + digits of A, copies of B
+constexpr int kTcEpi = 4;          // epilogue warps: one per tensor-memory lane quarter
+constexpr int kTcMmaWarp = kTcProd + kTcEpi;
+constexpr int kTcThreads = 32 * (kTcProd + kTcEpi + 1);
 constexpr int kTcDig = 7;
 constexpr int kTcFlush = 8;        // k16 steps per exact fp32 chunk (128 k)
+static_assert(kTcProd % 4 == 0, "epilogue warp w reads tensor-memory lanes 32 (w % 4) ..");
 
 template <int TN> struct TcCfg {
     static constexpr int A_PLANE = kTcM * 16;    // bf16 elements of one digit plane per k16 step
@@ -106,9 +110,13 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_selinv_tc(const ProbDesc *__r
     long long *Lo = Hi + kTcM * TN;                                        // [TN][128]
     int *rowE = reinterpret_cast<int *>(Lo + kTcM * TN);                   // [128]
     __shared__ int64_t tile_cb[kTcM], tile_rb[kTcM];
-    __shared__ __align__(8) uint64_t mbar[2];
+    // full[s]: the producer warps filled stage s; empty[s]: the products that
+    // read stage s are done; acc_full: a chunk's group sums are complete in
+    // tensor memory; tmem_free: the epilogue warps have read them
+    __shared__ __align__(8) uint64_t full[2], empty[2], acc_full, tmem_free;
     __shared__ uint32_t s_tmem;
-    __shared__ int s_pre, s_last, s_abort;
+    __shared__ int s_pre, s_last;
+    __shared__ volatile int s_abort;
     __shared__ int ymax[128];
 
     const int w = blockIdx.x;
@@ -133,6 +141,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_selinv_tc(const ProbDesc *__r
     const int chunk = ((nsteps + nsplit - 1) / nsplit + kTcFlush - 1) / kTcFlush * kTcFlush;
     const int st0 = ksp * chunk;
     const int st1 = st0 + chunk < nsteps ? st0 + chunk : nsteps;
+    const int n = st1 > st0 ? st1 - st0 : 0;                 // k16 steps of this item
+    const int nflush = (n + kTcFlush - 1) / kTcFlush;
 
     // row exponents of the gathered block: row p is bounded by the largest
     // whole-column exponent of A^{-1} over C[0..p] (entry (p, q) sits in
@@ -153,11 +163,15 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_selinv_tc(const ProbDesc *__r
     for (int e = tid; e < 2 * kTcM * TN; e += kTcThreads) Hi[e] = 0;   // Hi and Lo
     for (int e = tid; e < 128; e += kTcThreads) ymax[e] = 0;
     if (tid == 0) {
-        umma::mbar_init(&mbar[0], 1);
-        umma::mbar_init(&mbar[1], 1);
+        for (int st = 0; st < 2; st++) {
+            umma::mbar_init(&full[st], kTcProd);
+            umma::mbar_init(&empty[st], 1);
+        }
+        umma::mbar_init(&acc_full, 1);
+        umma::mbar_init(&tmem_free, kTcEpi);
         umma::mbar_init_fence();
     }
-    if (warp == 0) {
+    if (warp == kTcMmaWarp) {
         umma::tmem_alloc(&s_tmem, Cfg::TCOLS);
         umma::tmem_relinquish();
     }
@@ -179,144 +193,144 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_selinv_tc(const ProbDesc *__r
     }
     __syncthreads();
     const uint32_t tmem = s_tmem;
-    const TcGather g{P.colbase + pos0, P.relbase + pos0, P.relidx, tile_cb, tile_rb, p0, c};
-    const double *Zg = static_cast<const double *>(P.Z);
-    const uint16_t *Bg = P.lhs + P.lhs_off[K];
-    const int64_t bplane = (int64_t)s * c16;
-    const uint32_t idesc = umma::idesc_f16_f32(kTcM, TN);
 
-    // this thread's A slot: row r, the 8 k-values kh*8 .. kh*8+7 of each step.
-    // Two-deep software pipeline over the dependent loads of the gather: the
-    // values of step t are loaded during step t-1, their addresses looked up
-    // during step t-2.
-    const int r = tid % kTcM, kh = tid / kTcM;
-    const int E = rowE[r];
-    double v[8];
-    int64_t an[8];
-    if (st0 < st1) {
-#pragma unroll
-        for (int u = 0; u < 8; u++) {
-            const int64_t a = g.addr(r, st0 * 16 + kh * 8 + u);
-            v[u] = a >= 0 ? Zg[a] : 0.0;
-        }
-#pragma unroll
-        for (int u = 0; u < 8; u++) an[u] = st0 + 1 < st1 ? g.addr(r, (st0 + 1) * 16 + kh * 8 + u) : -1;
-    }
-    int chunk0 = st0;
-    bool aborted = false;
-    int last_stage = -1, last_use = 0;        // the most recent commit (uniform over the CTA)
-    // one k16 step: digits of v (loaded during the previous step), then the
-    // loads of the next step into v; false when a wait ran out
-    auto body = [&](int step) -> bool {
-        const int i_ = step - st0;
-        const int stage = i_ & 1, use = i_ >> 1;
-        const int k0 = step * 16;
-        uint16_t *Ab = As + stage * Cfg::A_STAGE;
-        uint16_t *Bb = Bs + stage * Cfg::B_STAGE;
-        if (i_ >= 2 && !umma::mbar_wait(&mbar[stage], (uint32_t)((use - 1) & 1), wait_limit)) s_abort = 1;
-        // Lhat digit planes of this step: core-matrix rows of 8 q (16 bytes)
-        for (int e = tid; e < kTcDig * TN * 2; e += kTcThreads) {
-            const int kg = e & 1, n = (e >> 1) % TN, pl = (e >> 1) / TN;
-            uint16_t *dst = Bb + pl * Cfg::B_PLANE + (n / 8) * 128 + kg * 64 + (n % 8) * 8;
-            if (n0 + n < s) umma::cp_async16(dst, Bg + pl * bplane + (int64_t)(n0 + n) * c16 + k0 + kg * 8);
-            else *reinterpret_cast<uint4 *>(dst) = make_uint4(0, 0, 0, 0);
-        }
-        // A digit planes of this step
-        {
-            uint32_t lo[8], hi[8];
+    if (warp < kTcProd) {
+        // ---- producers: A digits (gathered, two-deep load pipeline) and B planes
+        const TcGather g{P.colbase + pos0, P.relbase + pos0, P.relidx, tile_cb, tile_rb, p0, c};
+        const double *Zg = static_cast<const double *>(P.Z);
+        const uint16_t *Bg = P.lhs + P.lhs_off[K];
+        const int64_t bplane = (int64_t)s * c16;
+        const int r = tid % kTcM, kh = tid / kTcM;        // row r, k-values kh*8 .. kh*8+7
+        const int E = rowE[r];
+        double v[8];
+        int64_t an[8];
+        if (n > 0) {
 #pragma unroll
             for (int u = 0; u < 8; u++) {
-                const unsigned long long w = (unsigned long long)(fixed54(v[u], E) + 0x80808080808080ll);
-                lo[u] = (uint32_t)w;
-                hi[u] = (uint32_t)(w >> 32);
+                const int64_t a = g.addr(r, st0 * 16 + kh * 8 + u);
+                v[u] = a >= 0 ? Zg[a] : 0.0;
             }
-            uint16_t *dst = Ab + (r / 8) * 128 + kh * 64 + (r % 8) * 8;
-            store_plane<0>(dst + 0 * Cfg::A_PLANE, lo, hi);
-            store_plane<1>(dst + 1 * Cfg::A_PLANE, lo, hi);
-            store_plane<2>(dst + 2 * Cfg::A_PLANE, lo, hi);
-            store_plane<3>(dst + 3 * Cfg::A_PLANE, lo, hi);
-            store_plane<4>(dst + 4 * Cfg::A_PLANE, lo, hi);
-            store_plane<5>(dst + 5 * Cfg::A_PLANE, lo, hi);
-            store_plane<6>(dst + 6 * Cfg::A_PLANE, lo, hi);
+#pragma unroll
+            for (int u = 0; u < 8; u++) an[u] = n > 1 ? g.addr(r, (st0 + 1) * 16 + kh * 8 + u) : -1;
         }
-        // loads of the next step's values (in flight until its digits are
-        // formed), address lookups of the one after
+        for (int i_ = 0; i_ < n; i_++) {
+            const int step = st0 + i_, stage = i_ & 1, use = i_ >> 1, k0 = step * 16;
+            uint16_t *Ab = As + stage * Cfg::A_STAGE;
+            uint16_t *Bb = Bs + stage * Cfg::B_STAGE;
+            if (i_ >= 2 && !umma::mbar_wait(&empty[stage], (uint32_t)((use - 1) & 1), wait_limit)) {
+                s_abort = 1;
+                break;
+            }
+            // Lhat digit planes of this step: core-matrix rows of 8 q (16 bytes)
+            for (int e = tid; e < kTcDig * TN * 2; e += 32 * kTcProd) {
+                const int kg = e & 1, nn = (e >> 1) % TN, pl = (e >> 1) / TN;
+                uint16_t *dst = Bb + pl * Cfg::B_PLANE + (nn / 8) * 128 + kg * 64 + (nn % 8) * 8;
+                if (n0 + nn < s) umma::cp_async16(dst, Bg + pl * bplane + (int64_t)(n0 + nn) * c16 + k0 + kg * 8);
+                else *reinterpret_cast<uint4 *>(dst) = make_uint4(0, 0, 0, 0);
+            }
+            {
+                uint32_t lo[8], hi[8];
 #pragma unroll
-        for (int u = 0; u < 8; u++) v[u] = an[u] >= 0 ? Zg[an[u]] : 0.0;
-#pragma unroll
-        for (int u = 0; u < 8; u++) an[u] = step + 2 < st1 ? g.addr(r, k0 + 32 + kh * 8 + u) : -1;
-        umma::cp_async_wait_all();
-        umma::fence_proxy_async();
-        __syncthreads();
-        if (s_abort) return false;
-        const bool first = step == chunk0;
-        if (tid == 0) {
-            umma::fence_after_sync();
-            // plane i's descriptor = plane 0's + the plane offset in the start-address field
-            const uint64_t ad0 = umma::smem_desc(umma::smem_u32(Ab), 128, 256);
-            const uint64_t bd0 = umma::smem_desc(umma::smem_u32(Bb), 128, 256);
-#pragma unroll
-            for (int i = 0; i < kTcDig; i++) {
-                const uint64_t ad = ad0 + (uint64_t)(i * Cfg::A_PLANE * 2 / 16);
-#pragma unroll
-                for (int j = 0; i + j < kTcDig; j++) {
-                    const uint64_t bd = bd0 + (uint64_t)(j * Cfg::B_PLANE * 2 / 16);
-                    // group i + j starts from zero at its first product of a chunk (i == 0)
-                    umma::mma_bf16(tmem + (uint32_t)((i + j) * TN), ad, bd, idesc, (first && i == 0) ? 0u : 1u);
+                for (int u = 0; u < 8; u++) {
+                    const unsigned long long wv = (unsigned long long)(fixed54(v[u], E) + 0x80808080808080ll);
+                    lo[u] = (uint32_t)wv;
+                    hi[u] = (uint32_t)(wv >> 32);
                 }
+                uint16_t *dst = Ab + (r / 8) * 128 + kh * 64 + (r % 8) * 8;
+                store_plane<0>(dst + 0 * Cfg::A_PLANE, lo, hi);
+                store_plane<1>(dst + 1 * Cfg::A_PLANE, lo, hi);
+                store_plane<2>(dst + 2 * Cfg::A_PLANE, lo, hi);
+                store_plane<3>(dst + 3 * Cfg::A_PLANE, lo, hi);
+                store_plane<4>(dst + 4 * Cfg::A_PLANE, lo, hi);
+                store_plane<5>(dst + 5 * Cfg::A_PLANE, lo, hi);
+                store_plane<6>(dst + 6 * Cfg::A_PLANE, lo, hi);
             }
-            umma::commit(&mbar[stage]);
+            // loads of the next step's values, address lookups of the one after
+#pragma unroll
+            for (int u = 0; u < 8; u++) v[u] = an[u] >= 0 ? Zg[an[u]] : 0.0;
+#pragma unroll
+            for (int u = 0; u < 8; u++) an[u] = i_ + 2 < n ? g.addr(r, k0 + 32 + kh * 8 + u) : -1;
+            umma::cp_async_wait_all();
+            umma::fence_proxy_async();
+            __syncwarp();
+            if (lane == 0) umma::mbar_arrive(&full[stage]);
+            if (s_abort) break;
         }
-        last_stage = stage;
-        last_use = use;
-        if (step + 1 - chunk0 == kTcFlush || step + 1 == st1) {
-            // fold the chunk's exact fp32 group sums into the int64 words
-            const bool ok = umma::mbar_wait(&mbar[stage], (uint32_t)(use & 1), wait_limit);
-            umma::fence_after_sync();
-            if (ok) {
-                const int lb = 32 * (warp % 4), row = lb + lane, half = warp / 4;
-#pragma unroll 1
-                for (int cb = 0; cb < TN / 16; cb++) {
-                    const int col0 = half * (TN / 2) + cb * 8;
-                    uint32_t acc[kTcDig][8];
+    } else if (warp == kTcMmaWarp) {
+        // ---- one thread issues the products of every step
+        if (lane == 0) {
+            const uint32_t idesc = umma::idesc_f16_f32(kTcM, TN);
+            for (int i_ = 0; i_ < n; i_++) {
+                const int stage = i_ & 1, use = i_ >> 1, ch = i_ / kTcFlush;
+                const bool first = i_ % kTcFlush == 0;
+                if (!umma::mbar_wait(&full[stage], (uint32_t)(use & 1), wait_limit) ||
+                    (first && ch > 0 && !umma::mbar_wait(&tmem_free, (uint32_t)((ch - 1) & 1), wait_limit))) {
+                    s_abort = 1;
+                    break;
+                }
+                umma::fence_after_sync();
+                // plane i's descriptor = plane 0's + the plane offset in the start-address field
+                const uint64_t ad0 = umma::smem_desc(umma::smem_u32(As + stage * Cfg::A_STAGE), 128, 256);
+                const uint64_t bd0 = umma::smem_desc(umma::smem_u32(Bs + stage * Cfg::B_STAGE), 128, 256);
 #pragma unroll
-                    for (int gq = 0; gq < kTcDig; gq++)
-                        umma::tmem_ld8(tmem + ((uint32_t)lb << 16) + (uint32_t)(gq * TN + col0), acc[gq]);
-                    umma::tmem_wait_ld();
+                for (int i = 0; i < kTcDig; i++) {
+                    const uint64_t ad = ad0 + (uint64_t)(i * Cfg::A_PLANE * 2 / 16);
 #pragma unroll
-                    for (int jj = 0; jj < 8; jj++) {
-                        long long gv[kTcDig];
-#pragma unroll
-                        for (int gq = 0; gq < kTcDig; gq++) gv[gq] = (long long)__float2int_rn(__uint_as_float(acc[gq][jj]));
-                        Hi[(col0 + jj) * kTcM + row] += (gv[0] << 16) + (gv[1] << 8) + gv[2];
-                        Lo[(col0 + jj) * kTcM + row] += (gv[3] << 24) + (gv[4] << 16) + (gv[5] << 8) + gv[6];
+                    for (int j = 0; i + j < kTcDig; j++) {
+                        const uint64_t bd = bd0 + (uint64_t)(j * Cfg::B_PLANE * 2 / 16);
+                        // group i + j starts from zero at its first product of a chunk (i == 0)
+                        umma::mma_f16kind(tmem + (uint32_t)((i + j) * TN), ad, bd, idesc, (first && i == 0) ? 0u : 1u);
                     }
                 }
-            } else {
+                umma::commit(&empty[stage]);
+                if (i_ % kTcFlush == kTcFlush - 1 || i_ == n - 1) umma::commit(&acc_full);
+                if (s_abort) break;
+            }
+        }
+        __syncwarp();
+    } else {
+        // ---- epilogue: every chunk's exact fp32 group sums -> int64 (hi, lo)
+        const int lb = 32 * (warp % 4), row = lb + lane;
+        for (int f = 0; f < nflush; f++) {
+            if (!umma::mbar_wait(&acc_full, (uint32_t)(f & 1), wait_limit)) {
                 s_abort = 1;
+                break;
+            }
+            umma::fence_after_sync();
+#pragma unroll 1
+            for (int cb = 0; cb < TN / 8; cb++) {
+                uint32_t acc[kTcDig][8];
+#pragma unroll
+                for (int gq = 0; gq < kTcDig; gq++)
+                    umma::tmem_ld8(tmem + ((uint32_t)lb << 16) + (uint32_t)(gq * TN + cb * 8), acc[gq]);
+                umma::tmem_wait_ld();
+#pragma unroll
+                for (int jj = 0; jj < 8; jj++) {
+                    long long gv[kTcDig];
+#pragma unroll
+                    for (int gq = 0; gq < kTcDig; gq++) gv[gq] = (long long)__float2int_rn(__uint_as_float(acc[gq][jj]));
+                    Hi[(cb * 8 + jj) * kTcM + row] += (gv[0] << 16) + (gv[1] << 8) + gv[2];
+                    Lo[(cb * 8 + jj) * kTcM + row] += (gv[3] << 24) + (gv[4] << 16) + (gv[5] << 8) + gv[6];
+                }
             }
             umma::fence_before_sync();
-            __syncthreads();
-            if (s_abort) return false;
-            chunk0 = step + 1;
+            __syncwarp();
+            if (lane == 0) umma::mbar_arrive(&tmem_free);
+            if (s_abort) break;
         }
-        return true;
-    };
-    for (int step = st0; step < st1; step++)
-        if (!body(step)) { aborted = true; break; }
-    if (aborted) {
-        // a wait ran out: report, give in-flight products a bounded chance to
-        // drain, release the tensor memory and leave
-        if (tid == 0) atomicCAS(P.status, 0, SELINV_ERR_TIMEOUT);
-        if (last_stage >= 0) umma::mbar_wait(&mbar[last_stage], (uint32_t)(last_use & 1), wait_limit);
-        umma::fence_before_sync();
-        __syncthreads();
-        if (warp == 0) umma::tmem_dealloc(tmem, Cfg::TCOLS);
-        return;
     }
     umma::fence_before_sync();
     __syncthreads();
-    if (warp == 0) umma::tmem_dealloc(tmem, Cfg::TCOLS);
+    if (s_abort) {
+        // a wait ran out: report, let in-flight products drain (bounded),
+        // release the tensor memory and leave
+        if (tid == 0) atomicCAS(P.status, 0, SELINV_ERR_TIMEOUT);
+        if (warp == kTcMmaWarp && n > 0) umma::mbar_wait(&acc_full, (uint32_t)((nflush - 1) & 1), wait_limit);
+        __syncthreads();
+        if (warp == kTcMmaWarp) umma::tmem_dealloc(tmem, Cfg::TCOLS);
+        return;
+    }
+    if (warp == kTcMmaWarp) umma::tmem_dealloc(tmem, Cfg::TCOLS);
 
     double *Zk = static_cast<double *>(P.Z) + P.panel_off[K];
     // Y = -(A^{-1}_{C,C} Lhat): A digits on 2^(E - 1028 - 8i), Lhat digits on
