@@ -91,8 +91,12 @@ struct ProbDesc {
     int *counter;               // [ns] tiles done per supernode
     int *done;                  // [ns] completion flags (persistent schedule)
     int *status;                // latched error code
-    uint16_t *lhs;              // bf16 digit planes of Lhat (tensor-core contraction)
+    uint16_t *lhs;              // fp16 digit planes of Lhat, [plane][column][q] (mma.sync kernels)
     const int64_t *lhs_off;     // [ns+1] offsets into lhs (elements)
+    uint16_t *lhsu;             // the same digits in the tcgen05 operand layout: per plane and
+                                // 16-row step a block of roundup(s, 64) columns x 16 q, K-major
+                                // 8 x 8 core matrices (column groups 256 bytes apart); zero padding
+    const int64_t *lhsu_off;    // [ns+1] offsets into lhsu (elements)
     int *colexp;                // [n] biased exponent of each column of Lhat
     int *colexpY;               // [n] biased exponent of each column of A^{-1}_{C,K} (atomic max)
     long long *dacc;            // [2 * sum s^2] exact int64 sums of the diagonal-block products

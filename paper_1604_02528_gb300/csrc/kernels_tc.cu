@@ -85,16 +85,26 @@ __device__ __forceinline__ void store_plane(uint16_t *dst, const uint32_t (&lo)[
 }
 
 // Address of entry (p, q) of A^{-1}_{C,C} in the ancestors' panels (stored at
-// (max, min) by symmetry), or -1 outside C x C; pl = p - p0.
+// (max, min) by symmetry) in two parts: a base known at once and the relative
+// row, which comes from memory -- so that its load can stay in flight; base
+// -1 outside C x C.  pl = p - p0.
 struct TcGather {
     const int64_t *pcb, *prb;
     const int32_t *relidx;
     const int64_t *tile_cb, *tile_rb;
     int p0, c;
-    __device__ __forceinline__ int64_t addr(int pl, int q) const {
+    __device__ __forceinline__ void parts(int pl, int q, int64_t &base, int32_t &rel) const {
         const int p = p0 + pl;
-        if (p >= c || q >= c) return -1;
-        return p >= q ? pcb[q] + relidx[prb[q] + p] : tile_cb[pl] + relidx[tile_rb[pl] + q];
+        if (p >= c || q >= c) {
+            base = -1;
+            rel = 0;
+        } else if (p >= q) {
+            base = pcb[q];
+            rel = relidx[prb[q] + p];
+        } else {
+            base = tile_cb[pl];
+            rel = relidx[tile_rb[pl] + q];
+        }
     }
 };
 
@@ -110,9 +120,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_selinv_tc(const ProbDesc *__r
     long long *Lo = Hi + kTcM * TN;                                        // [TN][128]
     int *rowE = reinterpret_cast<int *>(Lo + kTcM * TN);                   // [128]
     __shared__ int64_t tile_cb[kTcM], tile_rb[kTcM];
-    // full[s]: the producer warps filled stage s; empty[s]: the products that
-    // read stage s are done; acc_full: a chunk's group sums are complete in
-    // tensor memory; tmem_free: the epilogue warps have read them
+    // full[s]: the producer warps wrote A and the bulk copies of B landed in
+    // stage s; empty[s]: the products that read stage s are done; acc_full: a
+    // chunk's group sums are complete in tensor memory; tmem_free: the
+    // epilogue warps have read them
     __shared__ __align__(8) uint64_t full[2], empty[2], acc_full, tmem_free;
     __shared__ uint32_t s_tmem;
     __shared__ int s_pre, s_last;
@@ -164,7 +175,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_selinv_tc(const ProbDesc *__r
     for (int e = tid; e < 128; e += kTcThreads) ymax[e] = 0;
     if (tid == 0) {
         for (int st = 0; st < 2; st++) {
-            umma::mbar_init(&full[st], kTcProd);
+            umma::mbar_init(&full[st], kTcProd + 1);   // + the arrival that expects B's bytes
             umma::mbar_init(&empty[st], 1);
         }
         umma::mbar_init(&acc_full, 1);
@@ -195,38 +206,32 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_selinv_tc(const ProbDesc *__r
     const uint32_t tmem = s_tmem;
 
     if (warp < kTcProd) {
-        // ---- producers: A digits (gathered, two-deep load pipeline) and B planes
+        // ---- producers: A digits, gathered with a two-deep load pipeline
         const TcGather g{P.colbase + pos0, P.relbase + pos0, P.relidx, tile_cb, tile_rb, p0, c};
         const double *Zg = static_cast<const double *>(P.Z);
-        const uint16_t *Bg = P.lhs + P.lhs_off[K];
-        const int64_t bplane = (int64_t)s * c16;
         const int r = tid % kTcM, kh = tid / kTcM;        // row r, k-values kh*8 .. kh*8+7
         const int E = rowE[r];
         double v[8];
-        int64_t an[8];
+        int64_t ab[8];
+        int32_t ar[8];
         if (n > 0) {
 #pragma unroll
             for (int u = 0; u < 8; u++) {
-                const int64_t a = g.addr(r, st0 * 16 + kh * 8 + u);
-                v[u] = a >= 0 ? Zg[a] : 0.0;
+                g.parts(r, st0 * 16 + kh * 8 + u, ab[u], ar[u]);
+                v[u] = ab[u] >= 0 ? Zg[ab[u] + ar[u]] : 0.0;
             }
 #pragma unroll
-            for (int u = 0; u < 8; u++) an[u] = n > 1 ? g.addr(r, (st0 + 1) * 16 + kh * 8 + u) : -1;
+            for (int u = 0; u < 8; u++) {
+                if (n > 1) g.parts(r, (st0 + 1) * 16 + kh * 8 + u, ab[u], ar[u]);
+                else ab[u] = -1;
+            }
         }
         for (int i_ = 0; i_ < n; i_++) {
             const int step = st0 + i_, stage = i_ & 1, use = i_ >> 1, k0 = step * 16;
             uint16_t *Ab = As + stage * Cfg::A_STAGE;
-            uint16_t *Bb = Bs + stage * Cfg::B_STAGE;
             if (i_ >= 2 && !umma::mbar_wait(&empty[stage], (uint32_t)((use - 1) & 1), wait_limit)) {
                 s_abort = 1;
                 break;
-            }
-            // Lhat digit planes of this step: core-matrix rows of 8 q (16 bytes)
-            for (int e = tid; e < kTcDig * TN * 2; e += 32 * kTcProd) {
-                const int kg = e & 1, nn = (e >> 1) % TN, pl = (e >> 1) / TN;
-                uint16_t *dst = Bb + pl * Cfg::B_PLANE + (nn / 8) * 128 + kg * 64 + (nn % 8) * 8;
-                if (n0 + nn < s) umma::cp_async16(dst, Bg + pl * bplane + (int64_t)(n0 + nn) * c16 + k0 + kg * 8);
-                else *reinterpret_cast<uint4 *>(dst) = make_uint4(0, 0, 0, 0);
             }
             {
                 uint32_t lo[8], hi[8];
@@ -247,19 +252,34 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_selinv_tc(const ProbDesc *__r
             }
             // loads of the next step's values, address lookups of the one after
 #pragma unroll
-            for (int u = 0; u < 8; u++) v[u] = an[u] >= 0 ? Zg[an[u]] : 0.0;
+            for (int u = 0; u < 8; u++) v[u] = ab[u] >= 0 ? Zg[ab[u] + ar[u]] : 0.0;
 #pragma unroll
-            for (int u = 0; u < 8; u++) an[u] = i_ + 2 < n ? g.addr(r, k0 + 32 + kh * 8 + u) : -1;
-            umma::cp_async_wait_all();
+            for (int u = 0; u < 8; u++) {
+                if (i_ + 2 < n) g.parts(r, k0 + 32 + kh * 8 + u, ab[u], ar[u]);
+                else ab[u] = -1;
+            }
             umma::fence_proxy_async();
             __syncwarp();
             if (lane == 0) umma::mbar_arrive(&full[stage]);
             if (s_abort) break;
         }
     } else if (warp == kTcMmaWarp) {
-        // ---- one thread issues the products of every step
+        // ---- one thread copies the Lhat digit planes (bulk, tcgen05 layout:
+        // one contiguous block per plane and step) and issues the products
         if (lane == 0) {
             const uint32_t idesc = umma::idesc_f16_f32(kTcM, TN);
+            const int64_t s64 = (s + 63) / 64 * 64;
+            const uint16_t *Bu = P.lhsu + P.lhsu_off[K] + (int64_t)(n0 / 8) * 128;
+            constexpr uint32_t kBBytes = TN * 16 * 2;
+            auto load_b = [&](int i_) {
+                const int st = i_ & 1;
+                umma::mbar_arrive_expect_tx(&full[st], kTcDig * kBBytes);
+#pragma unroll
+                for (int pl = 0; pl < kTcDig; pl++)
+                    umma::bulk_g2s(Bs + st * Cfg::B_STAGE + pl * Cfg::B_PLANE,
+                                   Bu + ((int64_t)pl * nsteps + st0 + i_) * s64 * 16, kBBytes, &full[st]);
+            };
+            if (n > 0) load_b(0);
             for (int i_ = 0; i_ < n; i_++) {
                 const int stage = i_ & 1, use = i_ >> 1, ch = i_ / kTcFlush;
                 const bool first = i_ % kTcFlush == 0;
@@ -284,6 +304,15 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_selinv_tc(const ProbDesc *__r
                 }
                 umma::commit(&empty[stage]);
                 if (i_ % kTcFlush == kTcFlush - 1 || i_ == n - 1) umma::commit(&acc_full);
+                // B of the next step into the other stage once the products of
+                // the step before this one have finished reading it
+                if (i_ + 1 < n) {
+                    if (i_ >= 1 && !umma::mbar_wait(&empty[(i_ + 1) & 1], (uint32_t)((((i_ + 1) >> 1) - 1) & 1), wait_limit)) {
+                        s_abort = 1;
+                        break;
+                    }
+                    load_b(i_ + 1);
+                }
                 if (s_abort) break;
             }
         }

@@ -43,10 +43,11 @@ void Workspace::release() {
     dfree(partial_all);
     ticket = nullptr;
     partial_all = nullptr;
-    dfree(lhs); dfree(colexp); dfree(colexpY); dfree(dacc); dfree(colexpZ); dfree(yacc); dfree(tcount);
+    dfree(lhs); dfree(lhsu); dfree(colexp); dfree(colexpY); dfree(dacc); dfree(colexpZ); dfree(yacc); dfree(tcount);
     colexpZ = tcount = nullptr;
     yacc = nullptr;
     lhs = nullptr;
+    lhsu = nullptr;
     colexp = colexpY = nullptr;
     dacc = nullptr;
     LD = Linv = partial = nullptr;
@@ -69,6 +70,9 @@ int Workspace::ensure(const PlanData &p, int dtype) {
     if (cudaMalloc(&work, es * (size_t)std::max<int64_t>(p.nnz, 1)) != cudaSuccess) return SELINV_ERR_OOM;
     if (cudaMalloc((void **)&lhs, sizeof(uint16_t) * (size_t)std::max<int64_t>(p.lhs_total, 8)) != cudaSuccess)
         return SELINV_ERR_OOM;
+    if (cudaMalloc((void **)&lhsu, sizeof(uint16_t) * (size_t)std::max<int64_t>(p.lhsu_total, 8)) != cudaSuccess)
+        return SELINV_ERR_OOM;
+    cudaMemset(lhsu, 0, sizeof(uint16_t) * (size_t)std::max<int64_t>(p.lhsu_total, 8));   // padding stays zero
     if (cudaMalloc((void **)&colexp, sizeof(int) * (size_t)std::max(p.n, 1)) != cudaSuccess) return SELINV_ERR_OOM;
     if (cudaMalloc((void **)&colexpY, sizeof(int) * (size_t)std::max(p.n, 1)) != cudaSuccess) return SELINV_ERR_OOM;
     if (cudaMalloc((void **)&dacc, sizeof(long long) * 2 * (size_t)std::max<int64_t>(p.linv_total, 1)) != cudaSuccess)
@@ -216,6 +220,14 @@ static int build_plan(PlanData &p, int32_t n, int32_t ns, const int32_t *super_p
         p.lhs_off[K + 1] = p.lhs_off[K] + (s >= kOzMinS ? 7 * s * c16 : 0);
     }
     p.lhs_total = p.lhs_off[ns];
+    p.lhsu_off.assign(ns + 1, 0);
+    for (int32_t K = 0; K < ns; K++) {
+        const int64_t s = super_ptr[K + 1] - super_ptr[K];
+        const int64_t c = rowptr[K + 1] - rowptr[K] - s;
+        const int64_t c16 = (c + 15) / 16 * 16, s64 = (s + 63) / 64 * 64;
+        p.lhsu_off[K + 1] = p.lhsu_off[K] + (s >= kOzMinS ? 7 * s64 * c16 : 0);
+    }
+    p.lhsu_total = p.lhsu_off[ns];
     p.linvd_off.assign(ns + 1, 0);
     for (int32_t K = 0; K < ns; K++) {
         const int64_t s = super_ptr[K + 1] - super_ptr[K];
@@ -271,6 +283,7 @@ int ensure_device(PlanData &p) {
     if ((rc = upload(&p.d_part_off, p.part_off))) return rc;
     if ((rc = upload(&p.d_part_off_all, p.part_off_all))) return rc;
     if ((rc = upload(&p.d_lhs_off, p.lhs_off))) return rc;
+    if ((rc = upload(&p.d_lhsu_off, p.lhsu_off))) return rc;
     if ((rc = upload(&p.d_tile_base, p.tile_base))) return rc;
     if ((rc = upload(&p.d_linvd_off, p.linvd_off))) return rc;
     int *st = nullptr;
@@ -283,8 +296,8 @@ int ensure_device(PlanData &p) {
 void PlanData::release_device() {
     dfree(d_super_ptr); dfree(d_sparent); dfree(d_rowptr); dfree(d_rows); dfree(d_panel_off);
     dfree(d_colbase); dfree(d_relbase); dfree(d_relidx); dfree(d_linv_off); dfree(d_part_off); dfree(d_part_off_all);
-    dfree(d_lhs_off); dfree(d_tile_base); dfree(d_linvd_off); dfree(d_status);
-    d_lhs_off = d_tile_base = d_linvd_off = nullptr;
+    dfree(d_lhs_off); dfree(d_lhsu_off); dfree(d_tile_base); dfree(d_linvd_off); dfree(d_status);
+    d_lhs_off = d_lhsu_off = d_tile_base = d_linvd_off = nullptr;
     d_super_ptr = d_sparent = d_rows = d_relidx = nullptr;
     d_rowptr = d_panel_off = d_colbase = d_relbase = d_linv_off = d_part_off = d_part_off_all = nullptr;
     d_status = nullptr;
@@ -315,6 +328,8 @@ ProbDesc make_desc(const PlanData &p, Workspace &w, int dtype, const void *L, co
     d.status = p.d_status;
     d.lhs = w.lhs;
     d.lhs_off = p.d_lhs_off;
+    d.lhsu = w.lhsu;
+    d.lhsu_off = p.d_lhsu_off;
     d.colexp = w.colexp;
     d.colexpY = w.colexpY;
     d.dacc = w.dacc;

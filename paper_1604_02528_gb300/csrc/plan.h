@@ -22,14 +22,15 @@ struct PlanData {
     std::vector<int64_t> part_off_all;  // split-partial offsets disjoint over all levels (persistent schedule)
     std::vector<int64_t> colbase, relbase;  // per row-list position
     std::vector<int64_t> lhs_off;           // digit-plane offsets (tensor-core path)
+    std::vector<int64_t> lhsu_off;          // the same in the tcgen05 operand layout
     std::vector<int64_t> tile_base;         // prefix sums of the 64-row tiles of each supernode
     std::vector<int64_t> linvd_off;         // digit planes of L_KK^{-1} (tensor-core path)
     int nlevels = 0;
-    int64_t nnz = 0, linv_total = 0, part_max = 1, part_all = 1, lhs_total = 0, tile_total = 0, linvd_total = 0;
+    int64_t nnz = 0, linv_total = 0, part_max = 1, part_all = 1, lhs_total = 0, lhsu_total = 0, tile_total = 0, linvd_total = 0;
     // device copies
     int32_t *d_super_ptr = nullptr, *d_sparent = nullptr, *d_rows = nullptr, *d_relidx = nullptr;
     int64_t *d_rowptr = nullptr, *d_panel_off = nullptr, *d_colbase = nullptr, *d_relbase = nullptr;
-    int64_t *d_linv_off = nullptr, *d_part_off = nullptr, *d_part_off_all = nullptr, *d_lhs_off = nullptr, *d_tile_base = nullptr;
+    int64_t *d_linv_off = nullptr, *d_part_off = nullptr, *d_part_off_all = nullptr, *d_lhs_off = nullptr, *d_lhsu_off = nullptr, *d_tile_base = nullptr;
     int64_t *d_linvd_off = nullptr;
     int *d_status = nullptr;
     void release_device();
@@ -42,7 +43,8 @@ struct Workspace {
     void *LD = nullptr, *Linv = nullptr, *partial = nullptr, *work = nullptr;
     void *partial_all = nullptr;  // persistent schedule: supernodes of every level in flight at once
     int *counter = nullptr, *done = nullptr;
-    uint16_t *lhs = nullptr;   // bf16 digit planes of Lhat
+    uint16_t *lhs = nullptr;   // fp16 digit planes of Lhat
+    uint16_t *lhsu = nullptr;  // the same in the tcgen05 operand layout (zero padding)
     int *colexp = nullptr;     // [n]
     int *colexpY = nullptr;    // [n], zero between calls
     long long *dacc = nullptr; // [2 * linv_total], zero between calls

@@ -78,6 +78,21 @@ __device__ __forceinline__ void mbar_arrive(uint64_t *mbar) {
     asm volatile("{\n.reg .b64 st;\nmbarrier.arrive.shared::cta.b64 st, [%0];\n}\n" ::"r"(smem_u32(mbar)) : "memory");
 }
 
+// One arrival that also raises the phase's expected transaction count.
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *mbar, uint32_t bytes) {
+    asm volatile("{\n.reg .b64 st;\nmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n}\n" ::"r"(
+                     smem_u32(mbar)), "r"(bytes)
+                 : "memory");
+}
+
+// Bulk copy global -> shared (async proxy), completion counted on the
+// mbarrier in bytes; both addresses 16-byte aligned, size a multiple of 16.
+__device__ __forceinline__ void bulk_g2s(void *smem, const void *gmem, uint32_t bytes, uint64_t *mbar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+                     smem_u32(smem)), "l"(gmem), "r"(bytes), "r"(smem_u32(mbar))
+                 : "memory");
+}
+
 // Waits for the completion of the phase with the given parity; gives up after
 // `limit` polls and returns false.
 __device__ __forceinline__ bool mbar_wait(uint64_t *mbar, uint32_t parity, long long limit) {
