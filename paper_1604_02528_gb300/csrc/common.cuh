@@ -121,6 +121,7 @@ struct Item {
 };
 
 constexpr int kTM = 64;   // rows of C per work item
+constexpr int kDiagCols = 32;   // columns j per work item of the tensor-core diagonal block
 
 #ifdef __CUDACC__
 // atomicMax on a shared slot that every active lane of the warp targets: one

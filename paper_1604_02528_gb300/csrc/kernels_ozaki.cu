@@ -557,7 +557,7 @@ __global__ void __launch_bounds__(kOzThreads, 1) k_lhat_oz(const ProbDesc *__res
 // ---------------------------------------------------------------------------
 constexpr int kDK = 64;          // k extent (rows of the tile)
 constexpr int kDpad = kDK + 8;   // smem row stride (fp16), conflict-free fragment loads
-constexpr int kDJ = 32;          // columns j per pass
+constexpr int kDJ = kDiagCols;   // columns j per item
 
 __global__ void __launch_bounds__(kOzThreads, 1) k_diag_oz(const ProbDesc *__restrict__ descs,
                                                            const Item *__restrict__ items, int nitems) {
@@ -575,7 +575,9 @@ __global__ void __launch_bounds__(kOzThreads, 1) k_diag_oz(const ProbDesc *__res
     const int64_t ld = P.rowptr[K + 1] - P.rowptr[K];
     const int c = (int)(ld - s);
     const int c16 = (c + 15) & ~15;
-    const int p0 = it.tile * kTM;
+    const int npass = (s + kDJ - 1) / kDJ;         // items (row tile, column pass)
+    const int pass = it.tile % npass;
+    const int p0 = (it.tile / npass) * kTM;
     const int pm = c - p0 < kTM ? c - p0 : kTM;
     const int s16 = (s + 15) & ~15;
     double *Zk = static_cast<double *>(P.Z) + P.panel_off[K];
@@ -603,7 +605,7 @@ __global__ void __launch_bounds__(kOzThreads, 1) k_diag_oz(const ProbDesc *__res
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
     const int grp = lane / 4, qd = lane % 4;
     const int mt = warp;                       // rows i = mt*16 .. mt*16+15
-    for (int jb = 0; jb < s; jb += kDJ) {
+    for (int jb = pass * kDJ; jb < s && jb < (pass + 1) * kDJ; jb += kDJ) {
         if (pm > 0) {
             __syncthreads();                   // previous pass done with Bs
             // B digits: columns jb .. jb+31, k = tile rows (two adjacent p per word)

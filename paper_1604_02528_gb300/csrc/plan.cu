@@ -450,6 +450,14 @@ int build_schedule(Schedule &S, const std::vector<const PlanData *> &plans,
         const PlanData &p = *plans[i];
         for (int t = 0; t < p.ntiles[K]; t++) S.h_items.push_back({i, K, t, p.ntiles[K]});
     };
+    // tensor-core diagonal block: (64-row tile, 32-column pass) items
+    auto push_diag = [&](int i, int32_t K) {
+        const PlanData &p = *plans[i];
+        const int s = p.super_ptr[K + 1] - p.super_ptr[K];
+        const int np = (s + kDiagCols - 1) / kDiagCols;
+        for (int t = 0; t < p.ntiles[K]; t++)
+            for (int jb = 0; jb < np; jb++) S.h_items.push_back({i, K, t * np + jb, p.ntiles[K] * np});
+    };
     // tensor-core items: (row tile, column tile of width tn, k-range) triples,
     // ntiles field = number of k-ranges; c == 0 has none
     auto oz_tn = [](int s) { return s <= 16 ? 16 : (s <= 32 ? 32 : 64); };
@@ -529,7 +537,7 @@ int build_schedule(Schedule &S, const std::vector<const PlanData *> &plans,
                         S.launches.push_back({use_tc(i) ? KL_SELINV_TC : KL_SELINV_OZ, descs[i].dtype, tn, off,
                                               (int)(S.h_items.size() - off), p.level[K]});
                     const int64_t off2 = (int64_t)S.h_items.size();
-                    push_items(i, K);
+                    push_diag(i, K);
                     S.launches.push_back({KL_DIAG, descs[i].dtype, bucket_of(s), off2,
                                           (int)(S.h_items.size() - off2), p.level[K]});
                     continue;
@@ -572,7 +580,7 @@ int build_schedule(Schedule &S, const std::vector<const PlanData *> &plans,
                 }
             {
                 const int64_t off = (int64_t)S.h_items.size();
-                for (auto &ik : oz) push_items(ik.first, ik.second);
+                for (auto &ik : oz) push_diag(ik.first, ik.second);
                 const int cnt = (int)(S.h_items.size() - off);
                 if (cnt) S.launches.push_back({KL_DIAG, SELINV_F64, 0, off, cnt, l});
             }
