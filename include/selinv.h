@@ -239,8 +239,9 @@ int selinv_factor_adjoint(selinv_plan plan, selinv_dtype dtype, const void *L_de
  *   4 gather-GEMM on tensor cores      5 diagonal block after it
  *   6 digit planes of L_KK^{-1}        7 Lhat on tensor cores
  *   8 the persistent traversal          9 gather-GEMM on tcgen05
+ *  10 split-k sums of the tcgen05 gather-GEMM
  * For measurement only. */
-#define SELINV_PROFILE_KINDS 10
+#define SELINV_PROFILE_KINDS 11
 int selinv_numeric_profile(selinv_plan plan, selinv_dtype dtype, const void *L_dev,
                            const void *D_dev, void *Ainv_dev, void *cuda_stream, double *kernel_ms,
                            int64_t *kernel_launches);

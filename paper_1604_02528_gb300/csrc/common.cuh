@@ -122,6 +122,8 @@ struct Item {
 
 constexpr int kTM = 64;   // rows of C per work item
 constexpr int kDiagCols = 32;   // columns j per work item of the tensor-core diagonal block
+// slab slot of a split-k tcgen05 item (int64 words): (hi, lo) of a 128 x 64 tile, then 128 row exponents
+constexpr long long kTcSlotWords = 2 * 128 * 64 + 64;
 
 #ifdef __CUDACC__
 // atomicMax on a shared slot that every active lane of the warp targets: one

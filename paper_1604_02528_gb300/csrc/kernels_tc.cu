@@ -12,8 +12,8 @@
 //     operations only) and copy the Lhat digit planes of step k + 1;
 //   * every 128 k the group sums are read from tensor memory and added as
 //     int64 into per-element (hi, lo) words in shared memory.
-// Split-k items store their int64 words in a per-CTA slab slot; the last item
-// of a row tile sums the slots (exact) and writes A^{-1}_{C,K} for it.
+// Split-k items store their int64 words in a per-CTA slab slot; k_tc_reduce,
+// launched next, sums the slots of each row tile (exact) and writes A^{-1}_{C,K}.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -32,6 +32,9 @@ constexpr int kTcMmaWarp = kTcProd + kTcEpi;
 constexpr int kTcThreads = 32 * (kTcProd + kTcEpi + 1);
 constexpr int kTcDig = 7;
 constexpr int kTcFlush = 8;        // k16 steps per exact fp32 chunk (128 k)
+// slab slot of a split-k item: (hi, lo) words [64 columns][128 rows] each, then the rows' exponents
+constexpr int64_t kTcSlot = kTcSlotWords;
+static_assert(kTcSlotWords == 2 * kTcM * 64 + kTcM / 2, "slot layout");
 static_assert(kTcProd % 4 == 0, "epilogue warp w reads tensor-memory lanes 32 (w % 4) ..");
 
 template <int TN> struct TcCfg {
@@ -126,7 +129,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_selinv_tc(const ProbDesc *__r
     // epilogue warps have read them
     __shared__ __align__(8) uint64_t full[2], empty[2], acc_full, tmem_free;
     __shared__ uint32_t s_tmem;
-    __shared__ int s_pre, s_last;
+    __shared__ int s_pre;
     __shared__ volatile int s_abort;
     __shared__ int ymax[128];
 
@@ -376,41 +379,78 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_selinv_tc(const ProbDesc *__r
             if (p0 + row < c && n0 + col < s) emit(row, n0 + col, Hi[col * kTcM + row], Lo[col * kTcM + row]);
         }
     } else {
-        // split k: this CTA's partial tile goes to its slab slot (plain
-        // stores); the last CTA of the row tile sums the slots of all column
-        // tiles and k-ranges in k order (integer sums: exact) and writes Y
-        long long *mine = slab + (int64_t)blockIdx.x * 2 * kTcM * 64;
+        // split k: the partial tile and the rows' exponents go to this CTA's
+        // slab slot; k_tc_reduce sums the slots of the row tile afterwards
+        long long *mine = slab + (int64_t)blockIdx.x * kTcSlot;
         for (int e = tid; e < kTcM * TN; e += kTcThreads) {
             mine[e] = Hi[e];
             mine[kTcM * 64 + e] = Lo[e];
         }
-        __threadfence();
-        __syncthreads();
-        int *ctr = P.tcount + P.tile_base[K] + tile;
-        if (tid == 0) s_last = (atomicAdd(ctr, 1) == ncol * nsplit - 1);
-        __syncthreads();
-        if (!s_last) return;
-        __threadfence();
-        // the row tile's items are consecutive: (column tile, k-range) ordered
-        const int64_t group0 = (int64_t)blockIdx.x - (it.tile - tile * ncol * nsplit);
-        for (int e = tid; e < kTcM * s; e += kTcThreads) {
-            const int row = e % kTcM, j = e / kTcM;
-            if (p0 + row >= c) continue;
-            const int ctj = j / TN, col = j % TN;
-            long long hi = 0, lo = 0;
-            for (int k2 = 0; k2 < nsplit; k2++) {
-                const long long *sl = slab + (group0 + ctj * nsplit + k2) * 2 * kTcM * 64;
-                hi += __ldcg(sl + col * kTcM + row);
-                lo += __ldcg(sl + kTcM * 64 + col * kTcM + row);
-            }
-            emit(row, j, hi, lo);
-        }
-        if (tid == 0) *ctr = 0;
+        int *re = reinterpret_cast<int *>(mine + 2 * kTcM * 64);
+        for (int e = tid; e < kTcM; e += kTcThreads) re[e] = rowE[e];
+        return;
     }
     __syncthreads();
     // column exponents of A^{-1}_{C,K} over all row tiles (used by the diagonal block)
     for (int j = tid; j < s; j += kTcThreads)
         if (ymax[j] > 0) atomicMax(&P.colexpY[fc + j], ymax[j]);
+}
+
+// Split-k reduction: one CTA per (row tile, 8 columns); each element sums
+// the int64 words of the row tile's k-range slots in k order (exact) and
+// forms A^{-1}_{C,K} = -(sum) on the row / column exponent grid.
+// red[w] = {index of the group's first item, its slab slot, column block}.
+template <int TN>
+__global__ void __launch_bounds__(256) k_tc_reduce(const ProbDesc *__restrict__ descs,
+                                                   const Item *__restrict__ items, const int4 *__restrict__ red,
+                                                   int nred, const long long *__restrict__ slab) {
+    __shared__ int ymax[8];
+    const int w = blockIdx.x;
+    if (w >= nred) return;
+    const int4 rr = red[w];
+    const Item it = items[rr.x];
+    const ProbDesc &P = descs[it.prob];
+    const int K = it.K;
+    const int fc = P.super_ptr[K];
+    const int s = P.super_ptr[K + 1] - fc;
+    const int64_t ld = P.rowptr[K + 1] - P.rowptr[K];
+    const int c = (int)(ld - s);
+    const int ncol = (s + TN - 1) / TN;
+    const int nsplit = it.ntiles;
+    const int p0 = (it.tile / nsplit / ncol) * kTcM;
+    const long long *first = slab + (int64_t)rr.y * kTcSlot;
+    const int *rowE = reinterpret_cast<const int *>(first + 2 * kTcM * 64);
+    if (threadIdx.x < 8) ymax[threadIdx.x] = 0;
+    __syncthreads();
+    double *Zk = static_cast<double *>(P.Z) + P.panel_off[K];
+    const int row = threadIdx.x % kTcM;
+    for (int jj = threadIdx.x / kTcM; jj < 8; jj += 256 / kTcM) {
+        const int j = rr.z * 8 + jj;
+        if (j >= s || p0 + row >= c) continue;
+        const int ctj = j / TN, col = j % TN;
+        long long hi = 0, lo = 0;
+        for (int k2 = 0; k2 < nsplit; k2++) {
+            const long long *sl = slab + ((int64_t)rr.y + ctj * nsplit + k2) * kTcSlot;
+            hi += sl[col * kTcM + row];
+            lo += sl[kTcM * 64 + col * kTcM + row];
+        }
+        const int sc = (rowE[row] - 1022) + (P.colexp[fc + j] - 1022) - 13;
+        const double y = fixed_to_double(hi, lo, sc);
+        Zk[(int64_t)j * ld + s + p0 + row] = -y;
+        warp_uniform_atomic_max(&ymax[jj], bexp(y));   // the lanes of a warp share column j
+    }
+    __syncthreads();
+    if (threadIdx.x < 8 && rr.z * 8 + (int)threadIdx.x < s && ymax[threadIdx.x] > 0)
+        atomicMax(&P.colexpY[fc + rr.z * 8 + threadIdx.x], ymax[threadIdx.x]);
+}
+
+cudaError_t launch_tc_reduce(int tn, const ProbDesc *d, const Item *items, const int4 *red, int n,
+                             const long long *slab, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    if (tn == 16) k_tc_reduce<16><<<n, 256, 0, st>>>(d, items, red, n, slab);
+    else if (tn == 32) k_tc_reduce<32><<<n, 256, 0, st>>>(d, items, red, n, slab);
+    else k_tc_reduce<64><<<n, 256, 0, st>>>(d, items, red, n, slab);
+    return cudaGetLastError();
 }
 
 cudaError_t configure_tc_kernels() {

@@ -353,8 +353,8 @@ ProbDesc make_desc(const PlanData &p, Workspace &w, int dtype, const void *L, co
 void Schedule::release() {
     if (graph) cudaGraphExecDestroy(graph);
     graph = nullptr;
-    dfree(d_descs); dfree(d_items); dfree(d_work); dfree(d_buckets); dfree(tcslab);
-    d_descs = nullptr; d_items = nullptr; d_work = nullptr; d_buckets = nullptr; tcslab = nullptr;
+    dfree(d_descs); dfree(d_items); dfree(d_work); dfree(d_buckets); dfree(tcslab); dfree(d_red);
+    d_descs = nullptr; d_items = nullptr; d_work = nullptr; d_buckets = nullptr; tcslab = nullptr; d_red = nullptr;
 }
 
 int build_schedule(Schedule &S, const std::vector<const PlanData *> &plans,
@@ -363,6 +363,7 @@ int build_schedule(Schedule &S, const std::vector<const PlanData *> &plans,
     S.launches.clear();
     S.h_items.clear();
     S.h_work.clear();
+    S.h_red.clear();
     S.mode = mode;
     const int np = (int)plans.size();
     // 1) L_KK^{-1}, Dinv for every supernode (one launch per dtype and size class)
@@ -450,6 +451,20 @@ int build_schedule(Schedule &S, const std::vector<const PlanData *> &plans,
         const PlanData &p = *plans[i];
         for (int t = 0; t < p.ntiles[K]; t++) S.h_items.push_back({i, K, t, p.ntiles[K]});
     };
+    // after a tcgen05 launch: the reduction of its split-k row tiles
+    auto add_tc_reduce = [&](const Launch tl) {
+        const int64_t off = (int64_t)S.h_red.size();
+        for (int64_t e = tl.off; e < tl.off + tl.count; e++) {
+            const Item &it = S.h_items[e];
+            const PlanData &p = *plans[it.prob];
+            const int s = p.super_ptr[it.K + 1] - p.super_ptr[it.K];
+            const int ncol = (s + tl.bucket - 1) / tl.bucket;
+            if (it.ntiles < 2 || it.tile % (it.ntiles * ncol) != 0) continue;   // not a group's first item
+            for (int cb = 0; cb < (s + 7) / 8; cb++) S.h_red.push_back(make_int4((int)e, (int)(e - tl.off), cb, 0));
+        }
+        const int cnt = (int)((int64_t)S.h_red.size() - off);
+        if (cnt) S.launches.push_back({KL_TC_REDUCE, SELINV_F64, tl.bucket, off, cnt, tl.level});
+    };
     // tensor-core diagonal block: (64-row tile, 32-column pass) items
     auto push_diag = [&](int i, int32_t K) {
         const PlanData &p = *plans[i];
@@ -533,9 +548,11 @@ int build_schedule(Schedule &S, const std::vector<const PlanData *> &plans,
                     const int tn = oz_tn(s);
                     const int64_t off = (int64_t)S.h_items.size();
                     push_oz(i, K, tn, oz_split(i, K, oz_ctas(i, K)));
-                    if (S.h_items.size() > (size_t)off)
+                    if (S.h_items.size() > (size_t)off) {
                         S.launches.push_back({use_tc(i) ? KL_SELINV_TC : KL_SELINV_OZ, descs[i].dtype, tn, off,
                                               (int)(S.h_items.size() - off), p.level[K]});
+                        if (use_tc(i)) add_tc_reduce(S.launches.back());
+                    }
                     const int64_t off2 = (int64_t)S.h_items.size();
                     push_diag(i, K);
                     S.launches.push_back({KL_DIAG, descs[i].dtype, bucket_of(s), off2,
@@ -576,7 +593,10 @@ int build_schedule(Schedule &S, const std::vector<const PlanData *> &plans,
                             push_oz(ik.first, ik.second, tn, oz_split(ik.first, ik.second, level_ctas));
                     }
                     const int cnt = (int)(S.h_items.size() - off);
-                    if (cnt) S.launches.push_back({tc ? KL_SELINV_TC : KL_SELINV_OZ, SELINV_F64, tn, off, cnt, l});
+                    if (cnt) {
+                        S.launches.push_back({tc ? KL_SELINV_TC : KL_SELINV_OZ, SELINV_F64, tn, off, cnt, l});
+                        if (tc) add_tc_reduce(S.launches.back());
+                    }
                 }
             {
                 const int64_t off = (int64_t)S.h_items.size();
@@ -614,8 +634,9 @@ int build_schedule(Schedule &S, const std::vector<const PlanData *> &plans,
     for (const Launch &L : S.launches)
         if (L.kind == KL_SELINV_TC) tc_ctas = std::max<int64_t>(tc_ctas, L.count);
     if (tc_ctas > 0 &&
-        cudaMalloc((void **)&S.tcslab, sizeof(long long) * 2 * kTcRows * 64 * (size_t)tc_ctas) != cudaSuccess)
+        cudaMalloc((void **)&S.tcslab, sizeof(long long) * (size_t)kTcSlotWords * (size_t)tc_ctas) != cudaSuccess)
         return SELINV_ERR_OOM;
+    if (!S.h_red.empty() && (rc = upload(&S.d_red, S.h_red))) return rc;
     return SELINV_OK;
 }
 
@@ -631,6 +652,8 @@ cudaError_t launch_one(const Schedule &S, const Launch &L, cudaStream_t st) {
     case KL_LHAT_OZ: return launch_lhat_oz(L.bucket, S.d_descs, S.d_items + L.off, L.count, st);
     case KL_SELINV_TC:
         return launch_selinv_tc(L.bucket, S.d_descs, S.d_items + L.off, L.count, S.tcslab, S.spin_limit, st);
+    case KL_TC_REDUCE:
+        return launch_tc_reduce(L.bucket, S.d_descs, S.d_items, S.d_red + L.off, L.count, S.tcslab, st);
     case KL_PERSIST: {
         for (size_t r = 0; r < S.reset_ptr.size(); r++) {
             cudaError_t e = cudaMemsetAsync(S.reset_ptr[r], 0, S.reset_bytes[r], st);

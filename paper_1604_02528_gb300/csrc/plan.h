@@ -62,7 +62,7 @@ struct Workspace {
 
 // launch kinds
 enum { KL_LINV = 0, KL_LHAT = 1, KL_SELINV = 2, KL_DIGITS = 3, KL_SELINV_OZ = 4, KL_DIAG = 5, KL_LINV_DIGITS = 6,
-       KL_LHAT_OZ = 7, KL_PERSIST = 8, KL_SELINV_TC = 9, KL_NKINDS = 10 };
+       KL_LHAT_OZ = 7, KL_PERSIST = 8, KL_SELINV_TC = 9, KL_TC_REDUCE = 10, KL_NKINDS = 11 };
 
 // tensor-core (FP64-exact) contraction applies to real problems with s >= kOzMinS;
 // fast_contraction 1 runs the gather-GEMM on tcgen05, 2 on mma.sync
@@ -90,6 +90,7 @@ struct Schedule {
     std::vector<Item> h_items;
     std::vector<int2> h_work;
     std::vector<int8_t> h_buckets;  // per item of the persistent launches
+    std::vector<int4> h_red;        // split-k reductions: (group's first item, its slab slot, 8-column block)
     std::vector<Launch> launches;
     std::vector<void *> reset_ptr;  // memsets issued before the persistent launches
     std::vector<size_t> reset_bytes;
@@ -97,6 +98,7 @@ struct Schedule {
     Item *d_items = nullptr;
     int2 *d_work = nullptr;
     int8_t *d_buckets = nullptr;
+    int4 *d_red = nullptr;
     int *ticket = nullptr;
     long long *tcslab = nullptr;  // split-k partial tiles of the tcgen05 launches, one per CTA
     long long spin_limit = 0;   // bound of every device wait of the schedule's kernels
