@@ -690,25 +690,30 @@ __global__ void __launch_bounds__(kOzThreads, 1) k_diag_oz(const ProbDesc *__res
     __shared__ int cz[128];   // exponent of each whole column of K's panel
     for (int j = threadIdx.x; j < s; j += kOzThreads) cz[j] = P.colexpY[fc + j];
     __syncthreads();
-    for (int e = threadIdx.x; e < s * s; e += kOzThreads) {
-        const int i = e % s, j = e / s;
-        if (i < j) continue;
-        auto prod = [&](int a, int b) -> double {   // (Lhat^T Y)(a, b)
-            const long long *q = acc64 + 2 * ((int64_t)b * s + a);
-            const long long hi = (long long)__ldcg(reinterpret_cast<const unsigned long long *>(q));
-            const long long lo = (long long)__ldcg(reinterpret_cast<const unsigned long long *>(q) + 1);
-            const int ey = P.colexpY[fc + b];
-            if (ey == 0 || (hi == 0 && lo == 0)) return 0.0;
-            const int sc = (P.colexp[fc + a] - 1022) + (ey - 1022) - 14;
-            return fixed_to_double(hi, lo, sc);
-        };
-        double xij = LDk[(int64_t)j * ld + i] - prod(i, j);
-        double xji = LDk[(int64_t)i * ld + j] - prod(j, i);
-        if (P.symmetrize) { const double v = 0.5 * (xij + xji); xij = v; xji = v; }
-        Zk[(int64_t)j * ld + i] = xij;
-        Zk[(int64_t)i * ld + j] = xji;
-        atomicMax(&cz[j], bexp(xij));
-        atomicMax(&cz[i], bexp(xji));
+    auto prod = [&](int a, int b) -> double {   // (Lhat^T Y)(a, b)
+        const long long *q = acc64 + 2 * ((int64_t)b * s + a);
+        const long long hi = (long long)__ldcg(reinterpret_cast<const unsigned long long *>(q));
+        const long long lo = (long long)__ldcg(reinterpret_cast<const unsigned long long *>(q) + 1);
+        const int ey = P.colexpY[fc + b];
+        if (ey == 0 || (hi == 0 && lo == 0)) return 0.0;
+        const int sc = (P.colexp[fc + a] - 1022) + (ey - 1022) - 14;
+        return fixed_to_double(hi, lo, sc);
+    };
+    // a warp per column j, lanes over the rows i >= j: column j's exponent is
+    // reduced in the warp, row i's (column i of the mirror) has one lane
+    for (int j = warp; j < s; j += kOzThreads / 32) {
+        int mj = 0;
+        for (int i = j + lane; i < s; i += 32) {
+            double xij = LDk[(int64_t)j * ld + i] - prod(i, j);
+            double xji = LDk[(int64_t)i * ld + j] - prod(j, i);
+            if (P.symmetrize) { const double v = 0.5 * (xij + xji); xij = v; xji = v; }
+            Zk[(int64_t)j * ld + i] = xij;
+            Zk[(int64_t)i * ld + j] = xji;
+            mj = max(mj, bexp(xij));
+            atomicMax(&cz[i], bexp(xji));
+        }
+        mj = __reduce_max_sync(0xffffffffu, mj);
+        if (lane == 0) atomicMax(&cz[j], mj);
     }
     __syncthreads();
     for (int e = threadIdx.x; e < 2 * s * s; e += kOzThreads) acc64[e] = 0;

@@ -132,23 +132,29 @@ __device__ void diag_finish(const ProbDesc &P, int K, int s, int64_t ld, int nti
     for (int j = threadIdx.x; j < s; j += kThreads)
         cz[j] = __ldcg(P.colexpY + P.super_ptr[K] + j);   // atomics of this launch
     __syncthreads();
-    for (int e = threadIdx.x; e < s * s; e += kThreads) {
-        const int i = e % s, j = e / s;
-        if (i < j) continue;
-        T xij = LDk[(int64_t)j * ld + i], xji = LDk[(int64_t)i * ld + j];
-        for (int t = 0; t < ntiles; t++) {
-            xij = sub(xij, ldcg(part0 + t * ss + (int64_t)j * s + i));
-            xji = sub(xji, ldcg(part0 + t * ss + (int64_t)i * s + j));
+    // a warp per column j, lanes over the rows i >= j: column j's exponent is
+    // reduced in the warp, row i's (column i of the mirror) has one lane
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    for (int j = warp; j < s; j += kThreads / 32) {
+        int mj = 0;
+        for (int i = j + lane; i < s; i += 32) {
+            T xij = LDk[(int64_t)j * ld + i], xji = LDk[(int64_t)i * ld + j];
+            for (int t = 0; t < ntiles; t++) {
+                xij = sub(xij, ldcg(part0 + t * ss + (int64_t)j * s + i));
+                xji = sub(xji, ldcg(part0 + t * ss + (int64_t)i * s + j));
+            }
+            if (P.symmetrize) {
+                const T v = half(add(xij, xji));
+                xij = v;
+                xji = v;
+            }
+            Zk[(int64_t)j * ld + i] = xij;
+            Zk[(int64_t)i * ld + j] = xji;
+            mj = max(mj, bexp(xij));
+            atomicMax(&cz[i], bexp(xji));
         }
-        if (P.symmetrize) {
-            const T v = half(add(xij, xji));
-            xij = v;
-            xji = v;
-        }
-        Zk[(int64_t)j * ld + i] = xij;
-        Zk[(int64_t)i * ld + j] = xji;
-        atomicMax(&cz[j], bexp(xij));
-        atomicMax(&cz[i], bexp(xji));
+        mj = __reduce_max_sync(0xffffffffu, mj);
+        if (lane == 0) atomicMax(&cz[j], mj);
     }
     __syncthreads();
     // exponent of every whole column of K's panel (rows below: atomic max taken
