@@ -437,7 +437,8 @@ def main():
             "k_linv_digits": 0.0,
             "k_linv": mult * float((s_ ** 3).sum()),
             "k_lhat_digits": 0.0,
-            "k_tc_reduce": 0.0}
+            "k_tc_reduce": 0.0,
+            "k_diag_fin": 0.0}
     f_dom = f_of[name]
     achieved = f_dom / (kms[dom] * 1e-3) / 1e9 if kms[dom] > 0 else None
     traffic = ncu_traffic(name)

@@ -240,8 +240,9 @@ int selinv_factor_adjoint(selinv_plan plan, selinv_dtype dtype, const void *L_de
  *   6 digit planes of L_KK^{-1}        7 Lhat on tensor cores
  *   8 the persistent traversal          9 gather-GEMM on tcgen05
  *  10 split-k sums of the tcgen05 gather-GEMM
+ *  11 diagonal block from the tensor-core sums (finisher)
  * For measurement only. */
-#define SELINV_PROFILE_KINDS 11
+#define SELINV_PROFILE_KINDS 12
 int selinv_numeric_profile(selinv_plan plan, selinv_dtype dtype, const void *L_dev,
                            const void *D_dev, void *Ainv_dev, void *cuda_stream, double *kernel_ms,
                            int64_t *kernel_launches);

@@ -551,7 +551,7 @@ __global__ void __launch_bounds__(kOzThreads, 1) k_lhat_oz(const ProbDesc *__res
 //       (atomic max taken when Y was written).
 // k = 64 needs no flush (7 * 64 * 2^14 < 2^24).  Since every tile works on the
 // same grid, the tiles' integer sums are added exactly (int64 atomics, order
-// independent); the last tile forms A^{-1}_KK = Dinv - Lhat^T Y in FP64.
+// independent); k_diag_fin then forms A^{-1}_KK = Dinv - Lhat^T Y in FP64.
 // 8 warps: warp w owns m-tile w (16 rows i) and the 4 n-tiles of a 32-column
 // pass over j.
 // ---------------------------------------------------------------------------
@@ -679,54 +679,50 @@ __global__ void __launch_bounds__(kOzThreads, 1) k_diag_oz(const ProbDesc *__res
                 }
         }
     }
-    // the last tile of K: A^{-1}_KK = Dinv - (sums in FP64), symmetrized; reset the sums
-    __shared__ int s_last;
-    __threadfence();
-    __syncthreads();
-    if (threadIdx.x == 0) s_last = (atomicAdd(&P.counter[K], 1) == it.ntiles - 1);
-    __syncthreads();
-    if (!s_last) return;
-    __threadfence();
-    __shared__ int cz[128];   // exponent of each whole column of K's panel
-    for (int j = threadIdx.x; j < s; j += kOzThreads) cz[j] = P.colexpY[fc + j];
-    __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
+// k_diag_fin: A^{-1}_KK = Dinv_K - Lhat^T Y from the exact tile sums of
+// k_diag_oz, symmetrized (Sec. II-C).  One CTA per 8 columns j of the block,
+// a warp per column, lanes over all rows i.  Entry (i, j) and its mirror are
+// formed from the same sums in the same order by the CTAs of columns j and i,
+// so the block is exactly symmetric; each CTA writes only its own columns and
+// their whole-column exponents (for the row bounds of later gathers).  The
+// sums are cleared before every call.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_diag_fin(const ProbDesc *__restrict__ descs,
+                                                  const Item *__restrict__ items, int nitems) {
+    const int w = blockIdx.x;
+    if (w >= nitems) return;
+    const Item it = items[w];
+    const ProbDesc &P = descs[it.prob];
+    const int K = it.K;
+    const int fc = P.super_ptr[K];
+    const int s = P.super_ptr[K + 1] - fc;
+    const int64_t ld = P.rowptr[K + 1] - P.rowptr[K];
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    const int j = it.tile * 8 + warp;
+    if (j >= s) return;                       // the whole warp
+    const double *LDk = static_cast<const double *>(P.LD) + P.panel_off[K];
+    double *Zk = static_cast<double *>(P.Z) + P.panel_off[K];
+    const long long *acc64 = P.dacc + 2 * P.linv_off[K];
     auto prod = [&](int a, int b) -> double {   // (Lhat^T Y)(a, b)
         const long long *q = acc64 + 2 * ((int64_t)b * s + a);
-        const long long hi = (long long)__ldcg(reinterpret_cast<const unsigned long long *>(q));
-        const long long lo = (long long)__ldcg(reinterpret_cast<const unsigned long long *>(q) + 1);
+        const long long hi = q[0], lo = q[1];
         const int ey = P.colexpY[fc + b];
         if (ey == 0 || (hi == 0 && lo == 0)) return 0.0;
         const int sc = (P.colexp[fc + a] - 1022) + (ey - 1022) - 14;
         return fixed_to_double(hi, lo, sc);
     };
-    // a warp per column j, lanes over the rows i >= j: column j's exponent is
-    // reduced in the warp, row i's (column i of the mirror) has one lane
-    for (int j = warp; j < s; j += kOzThreads / 32) {
-        int mj = 0;
-        for (int i = j + lane; i < s; i += 32) {
-            double xij = LDk[(int64_t)j * ld + i] - prod(i, j);
-            double xji = LDk[(int64_t)i * ld + j] - prod(j, i);
-            if (P.symmetrize) { const double v = 0.5 * (xij + xji); xij = v; xji = v; }
-            Zk[(int64_t)j * ld + i] = xij;
-            Zk[(int64_t)i * ld + j] = xji;
-            mj = max(mj, bexp(xij));
-            atomicMax(&cz[i], bexp(xji));
-        }
-        mj = __reduce_max_sync(0xffffffffu, mj);
-        if (lane == 0) atomicMax(&cz[j], mj);
+    int mj = 0;
+    for (int i = lane; i < s; i += 32) {
+        double x = LDk[(int64_t)j * ld + i] - prod(i, j);
+        if (P.symmetrize) x = 0.5 * (x + (LDk[(int64_t)i * ld + j] - prod(j, i)));
+        Zk[(int64_t)j * ld + i] = x;
+        mj = max(mj, bexp(x));
     }
-    __syncthreads();
-    for (int e = threadIdx.x; e < 2 * s * s; e += kOzThreads) acc64[e] = 0;
-    for (int j = threadIdx.x; j < s; j += kOzThreads) {
-        P.colexpZ[fc + j] = cz[j];
-        P.colexpY[fc + j] = 0;
-    }
-    if (threadIdx.x == 0) P.counter[K] = 0;
-    if (P.done) {
-        __threadfence();
-        __syncthreads();
-        if (threadIdx.x == 0) atomicExch(&P.done[K], 1);
-    }
+    mj = __reduce_max_sync(0xffffffffu, mj);
+    if (lane == 0) P.colexpZ[fc + j] = max(mj, P.colexpY[fc + j]);
 }
 
 constexpr size_t diag_oz_smem() {
@@ -736,6 +732,12 @@ constexpr size_t diag_oz_smem() {
 cudaError_t launch_diag_oz(const ProbDesc *d, const Item *items, int n, cudaStream_t st) {
     if (n <= 0) return cudaSuccess;
     k_diag_oz<<<n, kOzThreads, diag_oz_smem(), st>>>(d, items, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_diag_fin(const ProbDesc *d, const Item *items, int n, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    k_diag_fin<<<n, 256, 0, st>>>(d, items, n);
     return cudaGetLastError();
 }
 

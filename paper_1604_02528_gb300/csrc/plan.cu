@@ -364,6 +364,8 @@ int build_schedule(Schedule &S, const std::vector<const PlanData *> &plans,
     S.h_items.clear();
     S.h_work.clear();
     S.h_red.clear();
+    S.pre_ptr.clear();
+    S.pre_bytes.clear();
     S.mode = mode;
     const int np = (int)plans.size();
     // 1) L_KK^{-1}, Dinv for every supernode (one launch per dtype and size class)
@@ -465,6 +467,19 @@ int build_schedule(Schedule &S, const std::vector<const PlanData *> &plans,
         const int cnt = (int)((int64_t)S.h_red.size() - off);
         if (cnt) S.launches.push_back({KL_TC_REDUCE, SELINV_F64, tl.bucket, off, cnt, tl.level});
     };
+    // after a tensor-core diagonal-block launch: its finisher, (K, 8 columns) items
+    auto add_diag_fin = [&](const Launch dl) {
+        const int64_t off = (int64_t)S.h_items.size();
+        for (int64_t e = dl.off; e < dl.off + dl.count; e++) {
+            const Item it = S.h_items[e];
+            if (it.tile != 0) continue;                      // one entry per supernode
+            const PlanData &p = *plans[it.prob];
+            const int s = p.super_ptr[it.K + 1] - p.super_ptr[it.K];
+            for (int cb = 0; cb < (s + 7) / 8; cb++) S.h_items.push_back({it.prob, it.K, cb, 0});
+        }
+        const int cnt = (int)((int64_t)S.h_items.size() - off);
+        if (cnt) S.launches.push_back({KL_DIAG_FIN, SELINV_F64, 0, off, cnt, dl.level});
+    };
     // tensor-core diagonal block: (64-row tile, 32-column pass) items
     auto push_diag = [&](int i, int32_t K) {
         const PlanData &p = *plans[i];
@@ -557,6 +572,7 @@ int build_schedule(Schedule &S, const std::vector<const PlanData *> &plans,
                     push_diag(i, K);
                     S.launches.push_back({KL_DIAG, descs[i].dtype, bucket_of(s), off2,
                                           (int)(S.h_items.size() - off2), p.level[K]});
+                    add_diag_fin(S.launches.back());
                     continue;
                 }
                 const int64_t off = (int64_t)S.h_items.size();
@@ -602,7 +618,10 @@ int build_schedule(Schedule &S, const std::vector<const PlanData *> &plans,
                 const int64_t off = (int64_t)S.h_items.size();
                 for (auto &ik : oz) push_diag(ik.first, ik.second);
                 const int cnt = (int)(S.h_items.size() - off);
-                if (cnt) S.launches.push_back({KL_DIAG, SELINV_F64, 0, off, cnt, l});
+                if (cnt) {
+                    S.launches.push_back({KL_DIAG, SELINV_F64, 0, off, cnt, l});
+                    add_diag_fin(S.launches.back());
+                }
             }
             // fused DFMA kernel for everything else
             for (int dt = 0; dt < 2; dt++)
@@ -629,6 +648,21 @@ int build_schedule(Schedule &S, const std::vector<const PlanData *> &plans,
     if ((rc = upload(&S.d_items, S.h_items))) return rc;
     if ((rc = upload(&S.d_work, S.h_work))) return rc;
     if (!S.h_buckets.empty() && (rc = upload(&S.d_buckets, S.h_buckets))) return rc;
+    // the exact diagonal-block sums and the column maxima of A^{-1}_{C,K} start
+    // from zero in every call
+    {
+        std::vector<char> has(np, 0);
+        for (const Launch &L : S.launches)
+            if (L.kind == KL_DIAG)
+                for (int64_t e = L.off; e < L.off + L.count; e++) has[S.h_items[e].prob] = 1;
+        for (int i = 0; i < np; i++) {
+            if (!has[i]) continue;
+            S.pre_ptr.push_back(descs[i].dacc);
+            S.pre_bytes.push_back(sizeof(long long) * 2 * (size_t)std::max<int64_t>(plans[i]->linv_total, 1));
+            S.pre_ptr.push_back(descs[i].colexpY);
+            S.pre_bytes.push_back(sizeof(int) * (size_t)std::max(plans[i]->n, 1));
+        }
+    }
     // one partial (hi, lo) tile of 128 x 64 per CTA of the widest tcgen05 launch
     int64_t tc_ctas = 0;
     for (const Launch &L : S.launches)
@@ -654,6 +688,7 @@ cudaError_t launch_one(const Schedule &S, const Launch &L, cudaStream_t st) {
         return launch_selinv_tc(L.bucket, S.d_descs, S.d_items + L.off, L.count, S.tcslab, S.spin_limit, st);
     case KL_TC_REDUCE:
         return launch_tc_reduce(L.bucket, S.d_descs, S.d_items, S.d_red + L.off, L.count, S.tcslab, st);
+    case KL_DIAG_FIN: return launch_diag_fin(S.d_descs, S.d_items + L.off, L.count, st);
     case KL_PERSIST: {
         for (size_t r = 0; r < S.reset_ptr.size(); r++) {
             cudaError_t e = cudaMemsetAsync(S.reset_ptr[r], 0, S.reset_bytes[r], st);
@@ -666,8 +701,18 @@ cudaError_t launch_one(const Schedule &S, const Launch &L, cudaStream_t st) {
     }
 }
 
+static cudaError_t issue_pre(const Schedule &S, cudaStream_t st) {
+    for (size_t r = 0; r < S.pre_ptr.size(); r++) {
+        cudaError_t e = cudaMemsetAsync(S.pre_ptr[r], 0, S.pre_bytes[r], st);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
 static cudaError_t issue(const Schedule &S, cudaStream_t st, bool count) {
     if (count) note_launch((int)S.launches.size());
+    cudaError_t e0 = issue_pre(S, st);
+    if (e0 != cudaSuccess) return e0;
     for (const Launch &L : S.launches) {
         cudaError_t e = launch_one(S, L, st);
         if (e != cudaSuccess) return e;
@@ -981,6 +1026,7 @@ extern "C" int selinv_numeric_profile(selinv_plan plan, selinv_dtype dtype, cons
     for (auto &e : ev) cudaEventCreate(&e);
     static_assert(KL_NKINDS == SELINV_PROFILE_KINDS, "profile kinds");
     for (int k = 0; k < KL_NKINDS; k++) { kernel_ms[k] = 0; kernel_launches[k] = 0; }
+    if (issue_pre(S, st) != cudaSuccess) rc = SELINV_ERR_CUDA;
     for (size_t i = 0; i < S.launches.size(); i++) {
         const Launch &L = S.launches[i];
         cudaEventRecord(ev[2 * i], st);

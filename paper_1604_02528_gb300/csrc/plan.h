@@ -62,7 +62,7 @@ struct Workspace {
 
 // launch kinds
 enum { KL_LINV = 0, KL_LHAT = 1, KL_SELINV = 2, KL_DIGITS = 3, KL_SELINV_OZ = 4, KL_DIAG = 5, KL_LINV_DIGITS = 6,
-       KL_LHAT_OZ = 7, KL_PERSIST = 8, KL_SELINV_TC = 9, KL_TC_REDUCE = 10, KL_NKINDS = 11 };
+       KL_LHAT_OZ = 7, KL_PERSIST = 8, KL_SELINV_TC = 9, KL_TC_REDUCE = 10, KL_DIAG_FIN = 11, KL_NKINDS = 12 };
 
 // tensor-core (FP64-exact) contraction applies to real problems with s >= kOzMinS;
 // fast_contraction 1 runs the gather-GEMM on tcgen05, 2 on mma.sync
@@ -94,6 +94,8 @@ struct Schedule {
     std::vector<Launch> launches;
     std::vector<void *> reset_ptr;  // memsets issued before the persistent launches
     std::vector<size_t> reset_bytes;
+    std::vector<void *> pre_ptr;    // memsets issued at the start of every call
+    std::vector<size_t> pre_bytes;
     ProbDesc *d_descs = nullptr;
     Item *d_items = nullptr;
     int2 *d_work = nullptr;
