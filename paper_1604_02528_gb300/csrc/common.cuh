@@ -84,7 +84,8 @@ struct ProbDesc {
     // numeric buffers
     const void *L;              // panels
     const void *D;              // [n]
-    void *Z;                    // panels (output A^{-1})
+    void *Z;                    // panels (output A^{-1}; the gather source)
+    void *Yout;                 // panels: where the tcgen05 gather-GEMM writes -A^{-1}(C,C) B (= Z by default)
     void *LD;                   // panels: Dinv_K in the diagonal block, Lhat below
     void *Linv;                 // sum s^2
     void *partial;              // split-k partials of A^{-1}_KK

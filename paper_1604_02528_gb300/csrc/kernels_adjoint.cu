@@ -59,6 +59,7 @@ struct AdjDesc {
     const int64_t *v_off;   // update matrix of K: c x c column-major at V + v_off[K]
     const int32_t *chpos;   // row-list position p of C_K[q]: its position in rows(parent(K))
     double *V;              // update matrices: the part of Zbar(C,C) not yet handed to an owner
+    double *G;              // panels: -A^{-1}(C,C) Ybar, then Lhat_bar (supernodes on the split path)
 };
 
 struct AdjData {
@@ -79,6 +80,27 @@ struct AdjData {
     double *YB = nullptr, *Zb = nullptr, *Lbw = nullptr, *Ab = nullptr, *fin = nullptr;
     AdjDesc *d_desc = nullptr;
     ProbDesc *d_pdesc = nullptr;
+    // Selected-inversion adjoint, split by supernode width (rebuilt when the
+    // options change).  Wide supernodes (s >= the tensor-core threshold) run
+    // the gather-GEMM on the tcgen05 kernel and their c x s by s x s products
+    // as (K, 64-row tile, 32-column chunk[, 64-row half of s]) items; narrow
+    // ones keep the fused one-CTA-per-tile kernels.  Lists per level, deepest first.
+    int split_key = -1;
+    std::vector<Item> sm_items;               // narrow: (K, tile) per level x bucket
+    std::vector<int> sm_bptr;
+    std::vector<Item> wd_items;               // wide: (K, tile) per level
+    std::vector<int64_t> wd_lptr;
+    std::vector<int4> row_items, mbp_items;   // wide: (K, tile, chunk, 0) / (K, tile, chunk, half)
+    std::vector<int64_t> row_lptr, mbp_lptr;
+    std::vector<int2> dig_work;               // wide with c > 0: (0, K << 8 | 8-column block)
+    std::vector<int64_t> dig_lptr;
+    std::vector<std::vector<int>> tc_launch;  // per level: tcgen05 and reduction launches of `tcs`
+    Schedule tcs;                             // their items, split-k reductions and slab
+    Item *d_sm = nullptr, *d_wd = nullptr;
+    int4 *d_row = nullptr, *d_mbp = nullptr;
+    int2 *d_dig = nullptr;
+    ProbDesc *d_tcdesc = nullptr;
+    int *cy = nullptr;                        // column maxima the tcgen05 launches record (unused here)
 };
 
 // ---------------------------------------------------------------------------
@@ -253,6 +275,136 @@ __global__ void __launch_bounds__(kThreads) k_adj_lhbar(const AdjDesc *__restric
 }
 
 // ---------------------------------------------------------------------------
+// Split path of the wide supernodes.  The gather-GEMM G = -A^{-1}(C,C) Ybar
+// runs on the tcgen05 kernel (its row exponents: colexpZ, the largest biased
+// exponent of each column of A^{-1} on and below the diagonal, where every
+// gathered entry is stored); the s-inner products run as separate launches
+// of 64 x 32 output blocks so that a level's few tiles still fill the SMs.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_adj_colexpz(const AdjDesc *__restrict__ ad, const double *__restrict__ src,
+                                                     int *__restrict__ colexpZ, const int *__restrict__ js, int nj) {
+    const int w = blockIdx.x;
+    if (w >= nj) return;
+    const AdjDesc &A = *ad;
+    const int K = js[w];
+    const int fc = A.super_ptr[K];
+    const int s = A.super_ptr[K + 1] - fc;
+    const int64_t ld = A.rowptr[K + 1] - A.rowptr[K];
+    const double *Zk = src + A.panel_off[K];
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    for (int j = warp; j < s; j += 8) {
+        int e = 0;
+        for (int64_t r = j + lane; r < ld; r += 32) e = max(e, bexp(Zk[(int64_t)j * ld + r]));
+#pragma unroll
+        for (int o = 16; o; o >>= 1) e = max(e, __shfl_xor_sync(0xffffffffu, e, o));
+        if (lane == 0) colexpZ[fc + j] = e;
+    }
+}
+
+enum { RP_YBAR = 0, RP_LHB, RP_LBC, RP_MBP, RP_FAC, RP_FABAR, RP_FNBP };
+
+// One 64 x 32 block of
+//   RP_YBAR  Ybar = Zbar_{C,K} - Lhat S          (tile 0 also stores S)
+//   RP_LHB   G   -= Y S                          (G becomes Lhat_bar)
+//   RP_LBC   Lbar_{C,K} = Lhat_bar M^T
+//   RP_MBP   partial of tile t: P_t(i, j) = sum_{p in t} L_C(p, i) Lhat_bar(p, j),
+//            rows i of the item's 64-row half of s
+// and of the factorization adjoint (Lb = the working Lbar)
+//   RP_FAC   G = A_C = L_C D L_KK^T
+//   RP_FABAR Abar_C = Lbar_C D^{-1} M,  M = L_KK^{-1}
+//   RP_FNBP  partial of tile t: N_t(i, j) = sum_{p in t} A_C(p, i) Lbar_C(p, j)
+// items (K, 64-row tile of C, 32-column chunk of s, half).
+template <int OP>
+__global__ void __launch_bounds__(kThreads) k_adj_rowprod(const AdjDesc *__restrict__ ad,
+                                                          const int4 *__restrict__ items, int nitems) {
+    __shared__ double As[kTK * kTM], Bs[kTK * 32];
+    const int w = blockIdx.x;
+    if (w >= nitems) return;
+    const AdjDesc &A = *ad;
+    const int4 it = items[w];
+    const int K = it.x, t = it.y, j0 = it.z * 32, i0 = it.w * 64;
+    const int s = A.super_ptr[K + 1] - A.super_ptr[K];
+    const int64_t ld = A.rowptr[K + 1] - A.rowptr[K];
+    const int c = (int)(ld - s);
+    const int64_t off = A.panel_off[K];
+    const int p0 = t * kTM;
+    const int pm = c - p0 < kTM ? (c - p0 > 0 ? c - p0 : 0) : kTM;
+    const int nj = s - j0 < 32 ? s - j0 : 32;
+    constexpr bool kPart = OP == RP_MBP || OP == RP_FNBP;
+    const int mrows = kPart ? (s - i0 < 64 ? s - i0 : 64) : pm;
+    const int kdim = kPart ? pm : s;
+    const int fc = A.super_ptr[K];
+    const double *Zb = A.Zb + off;
+    const double *S = A.YB + off;      // S(k, j) = S[j * ld + k]
+    auto sym = [&](int k, int j) -> double {   // S from the cotangent's lower diagonal block
+        if (k == j) return Zb[(int64_t)j * ld + j];
+        return 0.5 * (k > j ? Zb[(int64_t)j * ld + k] : Zb[(int64_t)k * ld + j]);
+    };
+    auto a_at = [&](int r, int k) -> double {
+        if (OP == RP_YBAR) return A.LD[off + (int64_t)k * ld + s + p0 + r];
+        if (OP == RP_LHB) return A.Z[off + (int64_t)k * ld + s + p0 + r];
+        if (OP == RP_LBC) return A.G[off + (int64_t)k * ld + s + p0 + r];
+        if (OP == RP_MBP) return A.L[off + (int64_t)(i0 + r) * ld + s + p0 + k];
+        if (OP == RP_FAC) return A.L[off + (int64_t)k * ld + s + p0 + r] * A.D[fc + k];
+        if (OP == RP_FABAR) return A.Lb[off + (int64_t)k * ld + s + p0 + r];
+        return A.G[off + (int64_t)(i0 + r) * ld + s + p0 + k];
+    };
+    auto b_at = [&](int k, int jl) -> double {
+        const int j = j0 + jl;
+        if (OP == RP_YBAR) return sym(k, j);
+        if (OP == RP_LHB) return S[(int64_t)j * ld + k];
+        if (OP == RP_LBC) return A.Linv[A.linv_off[K] + (int64_t)k * s + j];
+        if (OP == RP_MBP) return A.G[off + (int64_t)j * ld + s + p0 + k];
+        if (OP == RP_FAC) return k == j ? 1.0 : (k < j ? A.L[off + (int64_t)k * ld + j] : 0.0);   // L_KK(j, k)
+        if (OP == RP_FABAR) return k >= j ? A.Linv[A.linv_off[K] + (int64_t)j * s + k] / A.D[fc + k] : 0.0;
+        return A.Lb[off + (int64_t)j * ld + s + p0 + k];
+    };
+    auto la = [&](int k0, double *Ash) {
+        for (int e = threadIdx.x; e < kTK * kTM; e += kThreads) {
+            const int r = e % kTM, k = k0 + e / kTM;
+            Ash[e] = (r < mrows && k < kdim) ? a_at(r, k) : 0.0;
+        }
+    };
+    auto lb = [&](int k0, double *Bsh) {
+        for (int e = threadIdx.x; e < kTK * 32; e += kThreads) {
+            const int kk = e % kTK, jl = e / kTK, k = k0 + kk;
+            Bsh[kk * 32 + jl] = (k < kdim && jl < nj) ? b_at(k, jl) : 0.0;
+        }
+    };
+    using Sh = Shape<32>;
+    double acc[Sh::MI][Sh::NJ];
+#pragma unroll
+    for (int i = 0; i < Sh::MI; i++)
+#pragma unroll
+        for (int j = 0; j < Sh::NJ; j++) acc[i][j] = 0.0;
+    tile_gemm<double, 32>(kdim, la, lb, acc, As, Bs);
+    const int tx = threadIdx.x % Sh::TX, ty = threadIdx.x / Sh::TX;
+#pragma unroll
+    for (int i = 0; i < Sh::MI; i++)
+#pragma unroll
+        for (int j = 0; j < Sh::NJ; j++) {
+            const int r = ty + Sh::TY * i, q = tx + Sh::TX * j;
+            if (r >= mrows || q >= nj) continue;
+            if (kPart) {
+                const int64_t ss = (int64_t)s * s;
+                A.partial[A.part_off[K] + (int64_t)t * ss + (int64_t)(j0 + q) * s + i0 + r] = acc[i][j];
+                continue;
+            }
+            const int64_t e = off + (int64_t)(j0 + q) * ld + s + p0 + r;
+            if (OP == RP_YBAR) A.YB[e] = A.Zb[e] - acc[i][j];
+            else if (OP == RP_LHB) A.G[e] -= acc[i][j];
+            else if (OP == RP_LBC) A.Lb[e] = acc[i][j];
+            else if (OP == RP_FAC) A.G[e] = acc[i][j];
+            else A.Ab[e] = acc[i][j];
+        }
+    if (OP == RP_YBAR && t == 0)
+        for (int e = threadIdx.x; e < s * nj; e += kThreads) {
+            const int k = e % s, j = j0 + e / s;
+            A.YB[off + (int64_t)j * ld + k] = sym(k, j);
+        }
+}
+
+// ---------------------------------------------------------------------------
 // factorization adjoint
 // ---------------------------------------------------------------------------
 template <int TN>
@@ -321,6 +473,64 @@ __global__ void __launch_bounds__(kThreads) k_fadj_pull(const AdjDesc *__restric
     __threadfence();
     const double *part0 = A.partial + A.part_off[J];
     for (int k = threadIdx.x; k < s; k += kThreads) {
+        double v = 0.0;
+        for (int t = 0; t < it.ntiles; t++) v += ldcg(part0 + (int64_t)t * s * s + k);
+        A.Db[fc + k] -= 0.5 * v;
+    }
+    if (threadIdx.x == 0) A.counter[J] = 0;
+}
+
+// k_fadj_pull for a wide supernode whose gather-GEMM ran on the tensor
+// cores: G = -Abar(C,C) L_C with every gathered entry counted once, so the
+// doubled diagonal adds Abar(C[p], C[p]) L_C(p, :) here.  A warp per column.
+__global__ void __launch_bounds__(256) k_fadj_pull_tc(const AdjDesc *__restrict__ ad,
+                                                      const Item *__restrict__ items, int nitems) {
+    __shared__ double dg[kTM];
+    __shared__ int s_last;
+    const int w = blockIdx.x;
+    if (w >= nitems) return;
+    const AdjDesc &A = *ad;
+    const Item it = items[w];
+    const int J = it.K;
+    const int fc = A.super_ptr[J];
+    const int s = A.super_ptr[J + 1] - fc;
+    const int64_t ld = A.rowptr[J + 1] - A.rowptr[J];
+    const int c = (int)(ld - s);
+    const int p0 = it.tile * kTM;
+    const int pm = c - p0 < kTM ? (c - p0 > 0 ? c - p0 : 0) : kTM;
+    const int64_t pos0 = A.rowptr[J] + s;
+    const int64_t off = A.panel_off[J];
+    for (int e = threadIdx.x; e < kTM; e += blockDim.x) {
+        const int p = p0 + e;
+        dg[e] = e < pm ? A.Ab[A.colbase[pos0 + p] + A.relidx[A.relbase[pos0 + p] + p]] : 0.0;
+    }
+    __syncthreads();
+    const double *D = A.D + fc;
+    const double *Lc = A.L + off + s;
+    const double *G = A.G + off + s;
+    double *Lb = A.Lb + off + s;
+    double *part = A.partial + A.part_off[J] + (int64_t)it.tile * s * s;
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    for (int k = warp; k < s; k += 8) {
+        double v = 0.0;
+        for (int pl = lane; pl < pm; pl += 32) {
+            const int64_t e = (int64_t)k * ld + p0 + pl;
+            const double r = fma(dg[pl], Lc[e], -G[e]);   // (Abar(C,C) L_C)(p, k), diagonal doubled
+            Lb[e] -= r * D[k];
+            v = fma(Lc[e], r, v);
+        }
+#pragma unroll
+        for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) part[k] = v;
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = (atomicAdd(&A.counter[J], 1) == it.ntiles - 1);
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    const double *part0 = A.partial + A.part_off[J];
+    for (int k = threadIdx.x; k < s; k += blockDim.x) {
         double v = 0.0;
         for (int t = 0; t < it.ntiles; t++) v += ldcg(part0 + (int64_t)t * s * s + k);
         A.Db[fc + k] -= 0.5 * v;
@@ -665,6 +875,8 @@ void adjoint_release(void *p) {
     fr(a->d_gitems); fr(a->d_citems); fr(a->d_js);
     fr(a->YB); fr(a->Zb); fr(a->Lbw); fr(a->Ab); fr(a->fin); fr(a->d_desc); fr(a->d_pdesc);
     fr(a->V);
+    fr(a->d_sm); fr(a->d_wd); fr(a->d_row); fr(a->d_mbp); fr(a->d_dig); fr(a->d_tcdesc); fr(a->cy);
+    a->tcs.release();
     delete a;
 }
 
@@ -766,6 +978,7 @@ static AdjDesc make_adesc(selinv_plan_s *plan, const double *L, const double *D,
     h.v_off = f->d_uoff;
     h.chpos = f->d_chpos;
     h.V = a->V;
+    h.G = static_cast<double *>(w.work);
     return h;
 }
 
@@ -784,6 +997,74 @@ static int adj_normalize(selinv_plan_s *plan, const void *L, const void *D, cuda
         }
     }
     return cudaGetLastError() == cudaSuccess ? SELINV_OK : SELINV_ERR_CUDA;
+}
+
+// The per-level lists of the selected-inversion adjoint for the current
+// options: wide supernodes are those the forward contracts on tcgen05.
+static int adj_split(selinv_plan_s *plan) {
+    AdjData *a = static_cast<AdjData *>(plan->factor->adj);
+    const PlanData &p = plan->data;
+    const selinv_opts &o = p.opts;
+    const int key = o.fast_contraction == 1 ? std::max(kOzMinS, o.oz_min_s) : 0;
+    if (key == a->split_key) return SELINV_OK;
+    auto fr = [](void *q) { if (q) cudaFree(q); };
+    fr(a->d_sm); fr(a->d_wd); fr(a->d_row); fr(a->d_mbp); fr(a->d_dig);
+    a->d_sm = a->d_wd = nullptr; a->d_row = a->d_mbp = nullptr; a->d_dig = nullptr;
+    a->tcs.release();
+    a->tcs.launches.clear();
+    a->sm_items.clear(); a->wd_items.clear(); a->row_items.clear(); a->mbp_items.clear(); a->dig_work.clear();
+    a->sm_bptr.assign(1, 0); a->wd_lptr.assign(1, 0); a->row_lptr.assign(1, 0); a->mbp_lptr.assign(1, 0); a->dig_lptr.assign(1, 0);
+    a->tc_launch.assign(p.nlevels, {});
+    auto wide = [&](int s) { return key > 0 && s >= key; };
+    for (int l = p.nlevels - 1; l >= 0; l--) {
+        for (int b = 0; b < kNumBuckets; b++) {
+            for (int64_t e = p.level_ptr[l]; e < p.level_ptr[l + 1]; e++) {
+                const int32_t J = p.level_list[e];
+                const int s = p.super_ptr[J + 1] - p.super_ptr[J];
+                if (wide(s) || bucket_of(s) != b) continue;
+                for (int t = 0; t < p.ntiles[J]; t++) a->sm_items.push_back({0, J, t, p.ntiles[J]});
+            }
+            a->sm_bptr.push_back((int)a->sm_items.size());
+        }
+        for (int64_t e = p.level_ptr[l]; e < p.level_ptr[l + 1]; e++) {
+            const int32_t J = p.level_list[e];
+            const int s = p.super_ptr[J + 1] - p.super_ptr[J];
+            if (!wide(s)) continue;
+            const int64_t c = p.rowptr[J + 1] - p.rowptr[J] - s;
+            for (int t = 0; t < p.ntiles[J]; t++) a->wd_items.push_back({0, J, t, p.ntiles[J]});
+            for (int t = 0; t < p.ntiles[J]; t++)
+                for (int ch = 0; ch < (s + 31) / 32; ch++) {
+                    a->row_items.push_back(make_int4(J, t, ch, 0));
+                    for (int h = 0; h < (s + 63) / 64; h++) a->mbp_items.push_back(make_int4(J, t, ch, h));
+                }
+            if (c > 0)
+                for (int jb = 0; jb < (s + 7) / 8; jb++) a->dig_work.push_back(make_int2(0, (J << 8) | jb));
+        }
+        a->wd_lptr.push_back((int64_t)a->wd_items.size());
+        a->row_lptr.push_back((int64_t)a->row_items.size());
+        a->mbp_lptr.push_back((int64_t)a->mbp_items.size());
+        a->dig_lptr.push_back((int64_t)a->dig_work.size());
+    }
+    int rc;
+    if ((rc = upl(&a->d_sm, a->sm_items)) || (rc = upl(&a->d_wd, a->wd_items)) || (rc = upl(&a->d_row, a->row_items)) ||
+        (rc = upl(&a->d_mbp, a->mbp_items)) || (rc = upl(&a->d_dig, a->dig_work)))
+        return rc;
+    if (!a->dig_work.empty()) {
+        // the forward's level schedule supplies the tcgen05 items of every
+        // level (row tiles, column tiles, k-splits) and their reductions
+        const ProbDesc pd = make_desc(p, plan->ws[0], SELINV_F64, nullptr, nullptr, nullptr, false);
+        if ((rc = build_schedule(a->tcs, {&p}, {pd}, SELINV_SCHED_LEVEL))) return rc;
+        for (int e = 0; e < (int)a->tcs.launches.size(); e++) {
+            const Launch &L = a->tcs.launches[e];
+            if ((L.kind == KL_SELINV_TC || L.kind == KL_TC_REDUCE) && L.level >= 0 && L.level < p.nlevels)
+                a->tc_launch[p.nlevels - 1 - L.level].push_back(e);
+        }
+    }
+    if (!a->d_tcdesc && cudaMalloc((void **)&a->d_tcdesc, sizeof(ProbDesc)) != cudaSuccess) return SELINV_ERR_OOM;
+    if (!a->cy && cudaMalloc((void **)&a->cy, sizeof(int) * (size_t)std::max(p.n, 1)) != cudaSuccess)
+        return SELINV_ERR_OOM;
+    a->split_key = key;
+    return SELINV_OK;
 }
 
 static int adj_prepare(selinv_plan_s *plan) {
@@ -807,6 +1088,7 @@ extern "C" int selinv_adjoint(selinv_plan plan, selinv_dtype dtype, const void *
     if (!L || !D || !Z || !Zbar || !Lbar || !Dbar) return SELINV_ERR_INVALID_ARG;
     int rc = adj_prepare(plan);
     if (rc) return rc;
+    if ((rc = adj_split(plan))) return rc;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     plan->last_stream = st;
     const PlanData &p = plan->data;
@@ -822,6 +1104,18 @@ extern "C" int selinv_adjoint(selinv_plan plan, selinv_dtype dtype, const void *
     cudaMemcpyAsync(a->d_desc, &h, sizeof(h), cudaMemcpyHostToDevice, st);
     FactorData *f = plan->factor;
     cudaMemsetAsync(a->V, 0, 8 * (size_t)std::max<int64_t>(f->u_off[p.ns], 1), st);
+    Workspace &w = plan->ws[0];
+    if (!a->dig_work.empty()) {
+        // tcgen05 gather-GEMM: A^{-1}(C,C) from Z, B = Ybar (digit planes of
+        // YB), output G; row exponents from Z's columns
+        ProbDesc pd = make_desc(p, w, SELINV_F64, L, D, const_cast<void *>(Z), false);
+        pd.LD = a->YB;
+        pd.Yout = w.work;
+        pd.colexpY = a->cy;
+        cudaMemcpyAsync(a->d_tcdesc, &pd, sizeof(pd), cudaMemcpyHostToDevice, st);
+        k_adj_colexpz<<<p.ns, 256, 0, st>>>(a->d_desc, static_cast<const double *>(Z), w.colexpZ, a->d_js, p.ns);
+        note_launch();
+    }
     const int nl = p.nlevels;
     for (int li = 0; li < nl; li++) {  // deepest level first
         // the children's update matrices complete Zbar on K's panel and start V_K
@@ -829,13 +1123,37 @@ extern "C" int selinv_adjoint(selinv_plan plan, selinv_dtype dtype, const void *
             const int64_t x0 = f->asm_lptr[li * f->npass + r], x1 = f->asm_lptr[li * f->npass + r + 1];
             if (x1 > x0) { k_adj_asm<<<(int)(x1 - x0), 256, 0, st>>>(a->d_desc, f->d_asm + x0, (int)(x1 - x0)); note_launch(); }
         }
-        const int i0 = a->lvl_bucket_ptr[li * kNumBuckets], i1 = a->lvl_bucket_ptr[(li + 1) * kNumBuckets];
-        if (i1 > i0) { k_adj_ybar<<<i1 - i0, 256, 0, st>>>(a->d_desc, a->d_items + i0, i1 - i0); note_launch(); }
+        const int i0 = a->sm_bptr[li * kNumBuckets], i1 = a->sm_bptr[(li + 1) * kNumBuckets];
+        if (i1 > i0) { k_adj_ybar<<<i1 - i0, 256, 0, st>>>(a->d_desc, a->d_sm + i0, i1 - i0); note_launch(); }
+        const int r0 = (int)a->row_lptr[li], r1 = (int)a->row_lptr[li + 1];
+        const int m0 = (int)a->mbp_lptr[li], m1 = (int)a->mbp_lptr[li + 1];
+        if (r1 > r0) { k_adj_rowprod<RP_YBAR><<<r1 - r0, kThreads, 0, st>>>(a->d_desc, a->d_row + r0, r1 - r0); note_launch(); }
         const int64_t v0 = f->u_lptr[li], v1 = f->u_lptr[li + 1];
         if (v1 > v0) { k_adj_vupd<<<(int)(v1 - v0), 256, 0, st>>>(a->d_desc, f->d_uitems + v0, (int)(v1 - v0)); note_launch(); }
+        const int d0 = (int)a->dig_lptr[li], d1 = (int)a->dig_lptr[li + 1];
+        if (d1 > d0) {
+            launch_lhat_digits(a->d_tcdesc, a->d_dig + d0, d1 - d0, st);
+            note_launch();
+            for (int e : a->tc_launch[li]) {
+                const Launch &Lt = a->tcs.launches[e];
+                if (Lt.kind == KL_SELINV_TC)
+                    launch_selinv_tc(Lt.bucket, a->d_tcdesc, a->tcs.d_items + Lt.off, Lt.count, a->tcs.tcslab,
+                                     p.opts.spin_limit, st);
+                else
+                    launch_tc_reduce(Lt.bucket, a->d_tcdesc, a->tcs.d_items, a->tcs.d_red + Lt.off, Lt.count,
+                                     a->tcs.tcslab, st);
+                note_launch();
+            }
+        }
         for (int b = 0; b < kNumBuckets; b++) {
-            const int b0 = a->lvl_bucket_ptr[li * kNumBuckets + b], b1 = a->lvl_bucket_ptr[li * kNumBuckets + b + 1];
-            launch_bucket(0, b, a->d_desc, a->d_items + b0, b1 - b0, st);
+            const int b0 = a->sm_bptr[li * kNumBuckets + b], b1 = a->sm_bptr[li * kNumBuckets + b + 1];
+            launch_bucket(0, b, a->d_desc, a->d_sm + b0, b1 - b0, st);
+        }
+        if (r1 > r0) {
+            k_adj_rowprod<RP_LHB><<<r1 - r0, kThreads, 0, st>>>(a->d_desc, a->d_row + r0, r1 - r0);
+            k_adj_rowprod<RP_MBP><<<m1 - m0, kThreads, 0, st>>>(a->d_desc, a->d_mbp + m0, m1 - m0);
+            k_adj_rowprod<RP_LBC><<<r1 - r0, kThreads, 0, st>>>(a->d_desc, a->d_row + r0, r1 - r0);
+            note_launch(3);
         }
         // per-supernode s x s steps, batched over the level
         const int64_t c0 = a->c_lptr[li], c1 = a->c_lptr[li + 1];
@@ -857,6 +1175,7 @@ extern "C" int selinv_factor_adjoint(selinv_plan plan, selinv_dtype dtype, const
     if (!L || !D || !Lbar || !Dbar || (plan->factor->nnzA > 0 && !Abar_vals)) return SELINV_ERR_INVALID_ARG;
     int rc = adj_prepare(plan);
     if (rc) return rc;
+    if ((rc = adj_split(plan))) return rc;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     plan->last_stream = st;
     const PlanData &p = plan->data;
@@ -871,15 +1190,51 @@ extern "C" int selinv_factor_adjoint(selinv_plan plan, selinv_dtype dtype, const
     AdjDesc h = make_adesc(plan, static_cast<const double *>(L), static_cast<const double *>(D), nullptr,
                            a->Lbw, a->YB);
     cudaMemcpyAsync(a->d_desc, &h, sizeof(h), cudaMemcpyHostToDevice, st);
+    Workspace &w = plan->ws[0];
+    const bool tc = !a->dig_work.empty();
+    if (tc) {
+        // tcgen05 gather-GEMM of the wide supernodes: A^{-1}(C,C) -> the
+        // finished Abar of the ancestors, B = L_C (digit planes of L, once),
+        // output G; Abar's column exponents follow level by level
+        ProbDesc pd = make_desc(p, w, SELINV_F64, L, D, a->Ab, false);
+        pd.LD = const_cast<void *>(L);   // read only: the digit kernel takes B from LD
+        pd.Yout = w.work;
+        pd.colexpY = a->cy;
+        cudaMemcpyAsync(a->d_tcdesc, &pd, sizeof(pd), cudaMemcpyHostToDevice, st);
+        launch_lhat_digits(a->d_tcdesc, a->d_dig, (int)a->dig_work.size(), st);
+        note_launch();
+    }
     const int nl = p.nlevels;
     for (int li = nl - 1; li >= 0; li--) {  // root level first
+        const int d0 = (int)a->dig_lptr[li], d1 = (int)a->dig_lptr[li + 1];
+        if (d1 > d0)
+            for (int e : a->tc_launch[li]) {
+                const Launch &Lt = a->tcs.launches[e];
+                if (Lt.kind == KL_SELINV_TC)
+                    launch_selinv_tc(Lt.bucket, a->d_tcdesc, a->tcs.d_items + Lt.off, Lt.count, a->tcs.tcslab,
+                                     p.opts.spin_limit, st);
+                else
+                    launch_tc_reduce(Lt.bucket, a->d_tcdesc, a->tcs.d_items, a->tcs.d_red + Lt.off, Lt.count,
+                                     a->tcs.tcslab, st);
+                note_launch();
+            }
         for (int b = 0; b < kNumBuckets; b++) {
-            const int b0 = a->lvl_bucket_ptr[li * kNumBuckets + b], b1 = a->lvl_bucket_ptr[li * kNumBuckets + b + 1];
-            launch_bucket(1, b, a->d_desc, a->d_items + b0, b1 - b0, st);
+            const int b0 = a->sm_bptr[li * kNumBuckets + b], b1 = a->sm_bptr[li * kNumBuckets + b + 1];
+            launch_bucket(1, b, a->d_desc, a->d_sm + b0, b1 - b0, st);
         }
+        const int w0 = (int)a->wd_lptr[li], w1 = (int)a->wd_lptr[li + 1];
+        if (w1 > w0) { k_fadj_pull_tc<<<w1 - w0, 256, 0, st>>>(a->d_desc, a->d_wd + w0, w1 - w0); note_launch(); }
         for (int b = 0; b < kNumBuckets; b++) {
-            const int b0 = a->lvl_bucket_ptr[li * kNumBuckets + b], b1 = a->lvl_bucket_ptr[li * kNumBuckets + b + 1];
-            launch_bucket(2, b, a->d_desc, a->d_items + b0, b1 - b0, st);
+            const int b0 = a->sm_bptr[li * kNumBuckets + b], b1 = a->sm_bptr[li * kNumBuckets + b + 1];
+            launch_bucket(2, b, a->d_desc, a->d_sm + b0, b1 - b0, st);
+        }
+        const int r0 = (int)a->row_lptr[li], r1 = (int)a->row_lptr[li + 1];
+        const int m0 = (int)a->mbp_lptr[li], m1 = (int)a->mbp_lptr[li + 1];
+        if (r1 > r0) {
+            k_adj_rowprod<RP_FAC><<<r1 - r0, kThreads, 0, st>>>(a->d_desc, a->d_row + r0, r1 - r0);
+            k_adj_rowprod<RP_FNBP><<<m1 - m0, kThreads, 0, st>>>(a->d_desc, a->d_mbp + m0, m1 - m0);
+            k_adj_rowprod<RP_FABAR><<<r1 - r0, kThreads, 0, st>>>(a->d_desc, a->d_row + r0, r1 - r0);
+            note_launch(3);
         }
         const int64_t c0 = a->c_lptr[li], c1 = a->c_lptr[li + 1];
         const int64_t j0 = a->j_lptr[li], j1 = a->j_lptr[li + 1];
@@ -896,6 +1251,10 @@ extern "C" int selinv_factor_adjoint(selinv_plan plan, selinv_dtype dtype, const
         if (j1 > j0) {
             k_fadj_fold<<<(int)(j1 - j0), 256, 0, st>>>(a->d_desc, a->d_js + j0, (int)(j1 - j0));
             note_launch();
+            if (tc && li > 0) {
+                k_adj_colexpz<<<(int)(j1 - j0), 256, 0, st>>>(a->d_desc, a->Ab, w.colexpZ, a->d_js + j0, (int)(j1 - j0));
+                note_launch();
+            }
         }
     }
     if (f->nnzA > 0) {

@@ -364,7 +364,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_selinv_tc(const ProbDesc *__r
     }
     if (warp == kTcMmaWarp) umma::tmem_dealloc(tmem, Cfg::TCOLS);
 
-    double *Zk = static_cast<double *>(P.Z) + P.panel_off[K];
+    double *Zk = static_cast<double *>(P.Yout) + P.panel_off[K];
     // Y = -(A^{-1}_{C,C} Lhat): A digits on 2^(E - 1028 - 8i), Lhat digits on
     // 2^(F - 1029 - 8j), so the value is (hi 2^-16 + lo 2^-48) 2^(E + F - 2057)
     auto emit = [&](int row, int j, long long hi, long long lo) {
@@ -422,7 +422,7 @@ __global__ void __launch_bounds__(256) k_tc_reduce(const ProbDesc *__restrict__ 
     const int *rowE = reinterpret_cast<const int *>(first + 2 * kTcM * 64);
     if (threadIdx.x < 8) ymax[threadIdx.x] = 0;
     __syncthreads();
-    double *Zk = static_cast<double *>(P.Z) + P.panel_off[K];
+    double *Zk = static_cast<double *>(P.Yout) + P.panel_off[K];
     const int row = threadIdx.x % kTcM;
     for (int jj = threadIdx.x / kTcM; jj < 8; jj += 256 / kTcM) {
         const int j = rr.z * 8 + jj;

@@ -320,6 +320,7 @@ ProbDesc make_desc(const PlanData &p, Workspace &w, int dtype, const void *L, co
     d.L = L;
     d.D = D;
     d.Z = Z;
+    d.Yout = Z;
     d.LD = w.LD;
     d.Linv = w.Linv;
     d.partial = persistent ? w.partial_all : w.partial;

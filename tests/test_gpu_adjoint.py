@@ -14,6 +14,7 @@ CASES = [
     ("dense150", lambda: synth.random_sparse_spd(150, 1.0, 43, supernodes=synth.problems.RELAXED_128)),
     ("diffusion-8", lambda: synth.diffusion_3d(8)),
     ("lap3d-12", lambda: synth.laplacian_3d(12, seed=44)),
+    ("diffusion-16", lambda: synth.diffusion_3d(16)),
 ]
 
 
@@ -34,8 +35,12 @@ def rel(a, b):
     return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
 
 
+@pytest.mark.parametrize("engine", [1, 0])
 @pytest.mark.parametrize("name,make", CASES)
-def test_adjoints_match_oracle(native, cuda_device, name, make):
+def test_adjoints_match_oracle(native, cuda_device, name, make, engine):
+    """engine 1: supernodes of 16 columns or more take the split path (tcgen05
+    gather-GEMM, 64 x 32 blocks for the s-inner products); 0: every supernode
+    on the fused FP64 kernels."""
     import torch
     from paper_1604_02528_gb300.api import SelInvContext
     p = make()
@@ -48,6 +53,10 @@ def test_adjoints_match_oracle(native, cuda_device, name, make):
     Ab0 = oracle.ldlt_adjoint(sym, L, D, Lb0, Db0)
     ctx = SelInvContext.from_problem(p)
     ctx.attach_matrix()
+    o = native.selinv_default_opts()
+    o.fast_contraction = engine
+    o.split_min_steps = 8       # k-split tcgen05 items from c >= 256 on
+    native.selinv_plan_set_opts(ctx.plan, o)
     t = lambda x: torch.from_numpy(np.ascontiguousarray(x)).cuda()
     Lt, Dt, Zt, Wt = t(L), t(D), t(Z), t(W)
     Lb = torch.full_like(Lt, float("nan")); Db = torch.full_like(Dt, float("nan"))
