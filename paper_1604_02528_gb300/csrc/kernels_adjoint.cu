@@ -70,8 +70,11 @@ struct AdjData {
     std::vector<int2> linv_work;
     std::vector<Item> lhat_items;
     std::vector<int> lhat_bptr;
-    std::vector<int2> gitems, citems;  // per level: (J, 32x32 tile) and (J, chunk | ntiles << 16)
+    std::vector<int2> gitems, citems;  // per level: (J, 16x16 tile) and (J, chunk | ntiles << 16)
     std::vector<int> js;               // per level: supernodes
+    std::vector<int2> cz_work;         // per level: (J, 8-column block)
+    std::vector<int64_t> cz_lptr;
+    int2 *d_cz = nullptr;
     std::vector<int64_t> g_lptr, c_lptr, j_lptr;
     double *V = nullptr;  // update matrices (tables shared with the factorization)
     Item *d_items = nullptr, *d_lhat = nullptr;
@@ -281,24 +284,25 @@ __global__ void __launch_bounds__(kThreads) k_adj_lhbar(const AdjDesc *__restric
 // gathered entry is stored); the s-inner products run as separate launches
 // of 64 x 32 output blocks so that a level's few tiles still fill the SMs.
 // ---------------------------------------------------------------------------
+// work (K, 8-column block): a warp per column
 __global__ void __launch_bounds__(256) k_adj_colexpz(const AdjDesc *__restrict__ ad, const double *__restrict__ src,
-                                                     int *__restrict__ colexpZ, const int *__restrict__ js, int nj) {
+                                                     int *__restrict__ colexpZ, const int2 *__restrict__ work,
+                                                     int nwork) {
     const int w = blockIdx.x;
-    if (w >= nj) return;
+    if (w >= nwork) return;
     const AdjDesc &A = *ad;
-    const int K = js[w];
+    const int K = work[w].x;
     const int fc = A.super_ptr[K];
     const int s = A.super_ptr[K + 1] - fc;
+    const int j = work[w].y * 8 + threadIdx.x / 32, lane = threadIdx.x % 32;
+    if (j >= s) return;
     const int64_t ld = A.rowptr[K + 1] - A.rowptr[K];
-    const double *Zk = src + A.panel_off[K];
-    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-    for (int j = warp; j < s; j += 8) {
-        int e = 0;
-        for (int64_t r = j + lane; r < ld; r += 32) e = max(e, bexp(Zk[(int64_t)j * ld + r]));
+    const double *Zj = src + A.panel_off[K] + (int64_t)j * ld;
+    int e = 0;
+    for (int64_t r = j + lane; r < ld; r += 32) e = max(e, bexp(Zj[r]));
 #pragma unroll
-        for (int o = 16; o; o >>= 1) e = max(e, __shfl_xor_sync(0xffffffffu, e, o));
-        if (lane == 0) colexpZ[fc + j] = e;
-    }
+    for (int o = 16; o; o >>= 1) e = max(e, __shfl_xor_sync(0xffffffffu, e, o));
+    if (lane == 0) colexpZ[fc + j] = e;
 }
 
 enum { RP_YBAR = 0, RP_LHB, RP_LBC, RP_MBP, RP_FAC, RP_FABAR, RP_FNBP };
@@ -609,18 +613,20 @@ __global__ void k_gather_vals(const int64_t *__restrict__ pos, const double *__r
 // ---------------------------------------------------------------------------
 enum { OP_SEL_T1 = 0, OP_SEL_W, OP_SEL_LB, OP_FAC_T2, OP_FAC_U, OP_FAC_T3, OP_FAC_G1, OP_FAC_G2 };
 
-// C (32 x 32 tile) of an s x s product; items (J, tile), tiles row-major over
-// ceil(s/32)^2.  256 threads, 2 x 2 outputs each, k staged 32 at a time.
+// C (16 x 16 tile) of an s x s product; items (J, tile), tiles row-major over
+// ceil(s/16)^2 (16 CTAs per 64 columns: the top levels hold one or two
+// supernodes).  256 threads, one output each, k staged 32 at a time.
+constexpr int kGT = 16;
 __global__ void __launch_bounds__(256) k_adj_gemm(const AdjDesc *__restrict__ ad, int op,
                                                   const int2 *__restrict__ items, int nitems) {
-    __shared__ double As[32][33], Bs[32][33];
+    __shared__ double As[kGT][33], Bs[32][kGT + 1];
     const int w = blockIdx.x;
     if (w >= nitems) return;
     const AdjDesc &A = *ad;
     const int J = items[w].x;
     const int s = A.super_ptr[J + 1] - A.super_ptr[J];
-    const int nt = (s + 31) / 32;
-    const int i0 = (items[w].y / nt) * 32, j0 = (items[w].y % nt) * 32;
+    const int nt = (s + kGT - 1) / kGT;
+    const int i0 = (items[w].y / nt) * kGT, j0 = (items[w].y % nt) * kGT;
     const int64_t ss = (int64_t)s * s;
     const int64_t ld = A.rowptr[J + 1] - A.rowptr[J];
     const double *M = A.Linv + A.linv_off[J];             // M(i, k) = M[k*s + i]
@@ -652,47 +658,35 @@ __global__ void __launch_bounds__(256) k_adj_gemm(const AdjDesc *__restrict__ ad
         default: return F[ss + (int64_t)j * s + k];                   // P M
         }
     };
-    const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
-    double acc[2][2] = {{0.0, 0.0}, {0.0, 0.0}};
+    const int tx = threadIdx.x % kGT, ty = threadIdx.x / kGT;
+    double acc = 0.0;
     for (int k0 = 0; k0 < s; k0 += 32) {
         __syncthreads();
-        for (int e = threadIdx.x; e < 32 * 32; e += 256) {
-            const int r = e % 32, q = e / 32;
+        for (int e = threadIdx.x; e < kGT * 32; e += 256) {
+            const int r = e % kGT, q = e / kGT;
             As[r][q] = (i0 + r < s && k0 + q < s) ? a_at(i0 + r, k0 + q) : 0.0;
             Bs[q][r] = (k0 + q < s && j0 + r < s) ? b_at(k0 + q, j0 + r) : 0.0;
         }
         __syncthreads();
 #pragma unroll 8
-        for (int q = 0; q < 32; q++) {
-            const double a0 = As[ty][q], a1 = As[ty + 16][q];
-            const double b0 = Bs[q][tx], b1 = Bs[q][tx + 16];
-            acc[0][0] = fma(a0, b0, acc[0][0]);
-            acc[0][1] = fma(a0, b1, acc[0][1]);
-            acc[1][0] = fma(a1, b0, acc[1][0]);
-            acc[1][1] = fma(a1, b1, acc[1][1]);
-        }
+        for (int q = 0; q < 32; q++) acc = fma(As[ty][q], Bs[q][tx], acc);
     }
     double *Lb = A.Lb + A.panel_off[J];
-#pragma unroll
-    for (int u = 0; u < 2; u++)
-#pragma unroll
-        for (int v = 0; v < 2; v++) {
-            const int i = i0 + ty + 16 * u, j = j0 + tx + 16 * v;
-            if (i >= s || j >= s) continue;
-            const double x = acc[u][v];
-            switch (op) {
-            case OP_SEL_T1: F[2 * ss + (int64_t)j * s + i] = x; break;               // T1
-            case OP_SEL_W: F[ss + (int64_t)j * s + i] = x; break;                    // W
-            case OP_SEL_LB: Lb[(int64_t)j * ld + i] = i > j ? -x : 0.0; break;      // Lbar_JJ
-            case OP_FAC_T2: F[ss + (int64_t)j * s + i] = x; break;                   // T2
-            case OP_FAC_U: F[3 * ss + (int64_t)j * s + i] = -x; break;               // Ubar
-            case OP_FAC_T3:                                                          // P
-                F[(int64_t)j * s + i] = i > j ? x / A.D[A.super_ptr[J] + j] : (i == j ? A.Db[A.super_ptr[J] + i] : 0.0);
-                break;
-            case OP_FAC_G1: F[ss + (int64_t)j * s + i] = x; break;                   // P M
-            default: F[2 * ss + (int64_t)j * s + i] = x; break;                      // G = M^T P M
-            }
-        }
+    const int i = i0 + ty, j = j0 + tx;
+    if (i >= s || j >= s) return;
+    const double x = acc;
+    switch (op) {
+    case OP_SEL_T1: F[2 * ss + (int64_t)j * s + i] = x; break;               // T1
+    case OP_SEL_W: F[ss + (int64_t)j * s + i] = x; break;                    // W
+    case OP_SEL_LB: Lb[(int64_t)j * ld + i] = i > j ? -x : 0.0; break;      // Lbar_JJ
+    case OP_FAC_T2: F[ss + (int64_t)j * s + i] = x; break;                   // T2
+    case OP_FAC_U: F[3 * ss + (int64_t)j * s + i] = -x; break;               // Ubar
+    case OP_FAC_T3:                                                          // P
+        F[(int64_t)j * s + i] = i > j ? x / A.D[A.super_ptr[J] + j] : (i == j ? A.Db[A.super_ptr[J] + i] : 0.0);
+        break;
+    case OP_FAC_G1: F[ss + (int64_t)j * s + i] = x; break;                   // P M
+    default: F[2 * ss + (int64_t)j * s + i] = x; break;                      // G = M^T P M
+    }
 }
 
 // selinv adjoint: Mbar = sum of the tile partials + 2 D^{-1} T1 (T1 = M S)
@@ -872,7 +866,7 @@ void adjoint_release(void *p) {
     if (!a) return;
     auto fr = [](void *q) { if (q) cudaFree(q); };
     fr(a->d_items); fr(a->d_lhat); fr(a->d_linv);
-    fr(a->d_gitems); fr(a->d_citems); fr(a->d_js);
+    fr(a->d_gitems); fr(a->d_citems); fr(a->d_js); fr(a->d_cz);
     fr(a->YB); fr(a->Zb); fr(a->Lbw); fr(a->Ab); fr(a->fin); fr(a->d_desc); fr(a->d_pdesc);
     fr(a->V);
     fr(a->d_sm); fr(a->d_wd); fr(a->d_row); fr(a->d_mbp); fr(a->d_dig); fr(a->d_tcdesc); fr(a->cy);
@@ -909,17 +903,19 @@ static int adj_build(selinv_plan_s *plan) {
             a->lvl_bucket_ptr.push_back((int)a->items.size());
         }
     }
-    a->g_lptr.assign(1, 0); a->c_lptr.assign(1, 0); a->j_lptr.assign(1, 0);
+    a->g_lptr.assign(1, 0); a->c_lptr.assign(1, 0); a->j_lptr.assign(1, 0); a->cz_lptr.assign(1, 0);
     for (int l = p.nlevels - 1; l >= 0; l--) {      // deepest first, like every list here
         for (int64_t e = p.level_ptr[l]; e < p.level_ptr[l + 1]; e++) {
             const int32_t J = p.level_list[e];
             const int s = p.super_ptr[J + 1] - p.super_ptr[J];
-            const int nt = (s + 31) / 32;
+            const int nt = (s + kGT - 1) / kGT;
             for (int t = 0; t < nt * nt; t++) a->gitems.push_back(make_int2(J, t));
             const int nch = (int)(((int64_t)s * s + 4095) / 4096);
             for (int ch = 0; ch < nch; ch++) a->citems.push_back(make_int2(J, ch | (p.ntiles[J] << 16)));
             a->js.push_back(J);
+            for (int jb = 0; jb < (s + 7) / 8; jb++) a->cz_work.push_back(make_int2(J, jb));
         }
+        a->cz_lptr.push_back((int64_t)a->cz_work.size());
         a->g_lptr.push_back((int64_t)a->gitems.size());
         a->c_lptr.push_back((int64_t)a->citems.size());
         a->j_lptr.push_back((int64_t)a->js.size());
@@ -941,7 +937,8 @@ static int adj_build(selinv_plan_s *plan) {
     }
     if ((rc = upl(&a->d_items, a->items)) || (rc = upl(&a->d_lhat, a->lhat_items)) ||
         (rc = upl(&a->d_linv, a->linv_work)) ||
-        (rc = upl(&a->d_gitems, a->gitems)) || (rc = upl(&a->d_citems, a->citems)) || (rc = upl(&a->d_js, a->js))) {
+        (rc = upl(&a->d_gitems, a->gitems)) || (rc = upl(&a->d_citems, a->citems)) || (rc = upl(&a->d_js, a->js)) ||
+        (rc = upl(&a->d_cz, a->cz_work))) {
         adjoint_release(a);
         return rc;
     }
@@ -987,6 +984,15 @@ static int adj_normalize(selinv_plan_s *plan, const void *L, const void *D, cuda
     AdjData *a = static_cast<AdjData *>(plan->factor->adj);
     ProbDesc pd = make_desc(plan->data, plan->ws[0], SELINV_F64, L, D, nullptr, false);
     cudaMemcpyAsync(a->d_pdesc, &pd, sizeof(pd), cudaMemcpyHostToDevice, st);
+    if (!a->tcs.launches.empty()) {
+        // the forward's own normalization launches (Lhat of the wide supernodes on the tensor cores)
+        for (const Launch &Ln : a->tcs.launches)
+            if (Ln.kind == KL_LINV || Ln.kind == KL_LINV_DIGITS || Ln.kind == KL_LHAT_OZ || Ln.kind == KL_LHAT) {
+                launch_with(a->tcs, Ln, a->d_pdesc, st);
+                note_launch();
+            }
+        return cudaGetLastError() == cudaSuccess ? SELINV_OK : SELINV_ERR_CUDA;
+    }
     launch_linv(SELINV_F64, a->d_pdesc, a->d_linv, (int)a->linv_work.size(), 1, st);
     note_launch();
     for (int b = 0; b < kNumBuckets; b++) {
@@ -1067,6 +1073,12 @@ static int adj_split(selinv_plan_s *plan) {
     return SELINV_OK;
 }
 
+// options that may change between calls without changing the lists
+static void adj_refresh(selinv_plan_s *plan) {
+    AdjData *a = static_cast<AdjData *>(plan->factor->adj);
+    a->tcs.spin_limit = plan->data.opts.spin_limit;
+}
+
 static int adj_prepare(selinv_plan_s *plan) {
     int rc = ensure_device(plan->data);
     if (rc) return rc;
@@ -1089,6 +1101,7 @@ extern "C" int selinv_adjoint(selinv_plan plan, selinv_dtype dtype, const void *
     int rc = adj_prepare(plan);
     if (rc) return rc;
     if ((rc = adj_split(plan))) return rc;
+    adj_refresh(plan);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     plan->last_stream = st;
     const PlanData &p = plan->data;
@@ -1113,7 +1126,8 @@ extern "C" int selinv_adjoint(selinv_plan plan, selinv_dtype dtype, const void *
         pd.Yout = w.work;
         pd.colexpY = a->cy;
         cudaMemcpyAsync(a->d_tcdesc, &pd, sizeof(pd), cudaMemcpyHostToDevice, st);
-        k_adj_colexpz<<<p.ns, 256, 0, st>>>(a->d_desc, static_cast<const double *>(Z), w.colexpZ, a->d_js, p.ns);
+        const int ncz = (int)a->cz_work.size();
+        k_adj_colexpz<<<ncz, 256, 0, st>>>(a->d_desc, static_cast<const double *>(Z), w.colexpZ, a->d_cz, ncz);
         note_launch();
     }
     const int nl = p.nlevels;
@@ -1135,13 +1149,7 @@ extern "C" int selinv_adjoint(selinv_plan plan, selinv_dtype dtype, const void *
             launch_lhat_digits(a->d_tcdesc, a->d_dig + d0, d1 - d0, st);
             note_launch();
             for (int e : a->tc_launch[li]) {
-                const Launch &Lt = a->tcs.launches[e];
-                if (Lt.kind == KL_SELINV_TC)
-                    launch_selinv_tc(Lt.bucket, a->d_tcdesc, a->tcs.d_items + Lt.off, Lt.count, a->tcs.tcslab,
-                                     p.opts.spin_limit, st);
-                else
-                    launch_tc_reduce(Lt.bucket, a->d_tcdesc, a->tcs.d_items, a->tcs.d_red + Lt.off, Lt.count,
-                                     a->tcs.tcslab, st);
+                launch_with(a->tcs, a->tcs.launches[e], a->d_tcdesc, st);
                 note_launch();
             }
         }
@@ -1176,6 +1184,7 @@ extern "C" int selinv_factor_adjoint(selinv_plan plan, selinv_dtype dtype, const
     int rc = adj_prepare(plan);
     if (rc) return rc;
     if ((rc = adj_split(plan))) return rc;
+    adj_refresh(plan);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     plan->last_stream = st;
     const PlanData &p = plan->data;
@@ -1209,13 +1218,7 @@ extern "C" int selinv_factor_adjoint(selinv_plan plan, selinv_dtype dtype, const
         const int d0 = (int)a->dig_lptr[li], d1 = (int)a->dig_lptr[li + 1];
         if (d1 > d0)
             for (int e : a->tc_launch[li]) {
-                const Launch &Lt = a->tcs.launches[e];
-                if (Lt.kind == KL_SELINV_TC)
-                    launch_selinv_tc(Lt.bucket, a->d_tcdesc, a->tcs.d_items + Lt.off, Lt.count, a->tcs.tcslab,
-                                     p.opts.spin_limit, st);
-                else
-                    launch_tc_reduce(Lt.bucket, a->d_tcdesc, a->tcs.d_items, a->tcs.d_red + Lt.off, Lt.count,
-                                     a->tcs.tcslab, st);
+                launch_with(a->tcs, a->tcs.launches[e], a->d_tcdesc, st);
                 note_launch();
             }
         for (int b = 0; b < kNumBuckets; b++) {
@@ -1251,8 +1254,9 @@ extern "C" int selinv_factor_adjoint(selinv_plan plan, selinv_dtype dtype, const
         if (j1 > j0) {
             k_fadj_fold<<<(int)(j1 - j0), 256, 0, st>>>(a->d_desc, a->d_js + j0, (int)(j1 - j0));
             note_launch();
-            if (tc && li > 0) {
-                k_adj_colexpz<<<(int)(j1 - j0), 256, 0, st>>>(a->d_desc, a->Ab, w.colexpZ, a->d_js + j0, (int)(j1 - j0));
+            const int z0 = (int)a->cz_lptr[li], z1 = (int)a->cz_lptr[li + 1];
+            if (tc && li > 0 && z1 > z0) {
+                k_adj_colexpz<<<z1 - z0, 256, 0, st>>>(a->d_desc, a->Ab, w.colexpZ, a->d_cz + z0, z1 - z0);
                 note_launch();
             }
         }

@@ -675,32 +675,35 @@ int build_schedule(Schedule &S, const std::vector<const PlanData *> &plans,
     return SELINV_OK;
 }
 
-cudaError_t launch_one(const Schedule &S, const Launch &L, cudaStream_t st) {
+// one launch of a schedule with the problem descriptors at `d`
+cudaError_t launch_with(const Schedule &S, const Launch &L, const ProbDesc *d, cudaStream_t st) {
     switch (L.kind) {
-    case KL_LINV: return launch_linv(L.dtype, S.d_descs, S.d_work + L.off, L.count, L.bucket, st);
-    case KL_LHAT: return launch_lhat(L.dtype, L.bucket, S.d_descs, S.d_items + L.off, L.count, st);
-    case KL_SELINV: return launch_selinv(L.dtype, L.bucket, S.d_descs, S.d_items + L.off, L.count, st);
-    case KL_DIGITS: return launch_lhat_digits(S.d_descs, S.d_work + L.off, L.count, st);
-    case KL_SELINV_OZ: return launch_selinv_oz(L.bucket, S.d_descs, S.d_items + L.off, L.count, st);
-    case KL_DIAG: return launch_diag_oz(S.d_descs, S.d_items + L.off, L.count, st);
-    case KL_LINV_DIGITS: return launch_linv_digits(S.d_descs, S.d_work + L.off, L.count, st);
-    case KL_LHAT_OZ: return launch_lhat_oz(L.bucket, S.d_descs, S.d_items + L.off, L.count, st);
+    case KL_LINV: return launch_linv(L.dtype, d, S.d_work + L.off, L.count, L.bucket, st);
+    case KL_LHAT: return launch_lhat(L.dtype, L.bucket, d, S.d_items + L.off, L.count, st);
+    case KL_SELINV: return launch_selinv(L.dtype, L.bucket, d, S.d_items + L.off, L.count, st);
+    case KL_DIGITS: return launch_lhat_digits(d, S.d_work + L.off, L.count, st);
+    case KL_SELINV_OZ: return launch_selinv_oz(L.bucket, d, S.d_items + L.off, L.count, st);
+    case KL_DIAG: return launch_diag_oz(d, S.d_items + L.off, L.count, st);
+    case KL_LINV_DIGITS: return launch_linv_digits(d, S.d_work + L.off, L.count, st);
+    case KL_LHAT_OZ: return launch_lhat_oz(L.bucket, d, S.d_items + L.off, L.count, st);
     case KL_SELINV_TC:
-        return launch_selinv_tc(L.bucket, S.d_descs, S.d_items + L.off, L.count, S.tcslab, S.spin_limit, st);
+        return launch_selinv_tc(L.bucket, d, S.d_items + L.off, L.count, S.tcslab, S.spin_limit, st);
     case KL_TC_REDUCE:
-        return launch_tc_reduce(L.bucket, S.d_descs, S.d_items, S.d_red + L.off, L.count, S.tcslab, st);
-    case KL_DIAG_FIN: return launch_diag_fin(S.d_descs, S.d_items + L.off, L.count, st);
+        return launch_tc_reduce(L.bucket, d, S.d_items, S.d_red + L.off, L.count, S.tcslab, st);
+    case KL_DIAG_FIN: return launch_diag_fin(d, S.d_items + L.off, L.count, st);
     case KL_PERSIST: {
         for (size_t r = 0; r < S.reset_ptr.size(); r++) {
             cudaError_t e = cudaMemsetAsync(S.reset_ptr[r], 0, S.reset_bytes[r], st);
             if (e != cudaSuccess) return e;
         }
-        return launch_selinv_persist(L.dtype, S.d_descs, S.d_items + L.off, S.d_buckets + L.off, L.count,
+        return launch_selinv_persist(L.dtype, d, S.d_items + L.off, S.d_buckets + L.off, L.count,
                                      S.ticket, S.spin_limit, S.wait_on_unset, st);
     }
     default: return cudaErrorInvalidValue;
     }
 }
+
+cudaError_t launch_one(const Schedule &S, const Launch &L, cudaStream_t st) { return launch_with(S, L, S.d_descs, st); }
 
 static cudaError_t issue_pre(const Schedule &S, cudaStream_t st) {
     for (size_t r = 0; r < S.pre_ptr.size(); r++) {
