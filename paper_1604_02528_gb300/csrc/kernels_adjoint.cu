@@ -83,10 +83,10 @@ struct AdjData {
     double *YB = nullptr, *Zb = nullptr, *Lbw = nullptr, *Ab = nullptr, *fin = nullptr;
     AdjDesc *d_desc = nullptr;
     ProbDesc *d_pdesc = nullptr;
-    // Selected-inversion adjoint, split by supernode width (rebuilt when the
+    // Both adjoints, split by supernode width (rebuilt when the
     // options change).  Wide supernodes (s >= the tensor-core threshold) run
     // the gather-GEMM on the tcgen05 kernel and their c x s by s x s products
-    // as (K, 64-row tile, 32-column chunk[, 64-row half of s]) items; narrow
+    // as (K, 32-row block, 32-column chunk) and (K, 64-row tile, chunk, 64-row half of s) items; narrow
     // ones keep the fused one-CTA-per-tile kernels.  Lists per level, deepest first.
     int split_key = -1;
     std::vector<Item> sm_items;               // narrow: (K, tile) per level x bucket
@@ -282,7 +282,7 @@ __global__ void __launch_bounds__(kThreads) k_adj_lhbar(const AdjDesc *__restric
 // runs on the tcgen05 kernel (its row exponents: colexpZ, the largest biased
 // exponent of each column of A^{-1} on and below the diagonal, where every
 // gathered entry is stored); the s-inner products run as separate launches
-// of 64 x 32 output blocks so that a level's few tiles still fill the SMs.
+// of 32 x 32 (and 64 x 32) output blocks so that a level's few tiles still fill the SMs.
 // ---------------------------------------------------------------------------
 // work (K, 8-column block): a warp per column
 __global__ void __launch_bounds__(256) k_adj_colexpz(const AdjDesc *__restrict__ ad, const double *__restrict__ src,
@@ -307,8 +307,8 @@ __global__ void __launch_bounds__(256) k_adj_colexpz(const AdjDesc *__restrict__
 
 enum { RP_YBAR = 0, RP_LHB, RP_LBC, RP_MBP, RP_FAC, RP_FABAR, RP_FNBP };
 
-// One 64 x 32 block of
-//   RP_YBAR  Ybar = Zbar_{C,K} - Lhat S          (tile 0 also stores S)
+// One 32 x 32 block (64 x 32 for the partials) of
+//   RP_YBAR  Ybar = Zbar_{C,K} - Lhat S          (block 0 also stores S)
 //   RP_LHB   G   -= Y S                          (G becomes Lhat_bar)
 //   RP_LBC   Lbar_{C,K} = Lhat_bar M^T
 //   RP_MBP   partial of tile t: P_t(i, j) = sum_{p in t} L_C(p, i) Lhat_bar(p, j),
@@ -317,11 +317,15 @@ enum { RP_YBAR = 0, RP_LHB, RP_LBC, RP_MBP, RP_FAC, RP_FABAR, RP_FNBP };
 //   RP_FAC   G = A_C = L_C D L_KK^T
 //   RP_FABAR Abar_C = Lbar_C D^{-1} M,  M = L_KK^{-1}
 //   RP_FNBP  partial of tile t: N_t(i, j) = sum_{p in t} A_C(p, i) Lbar_C(p, j)
-// items (K, 64-row tile of C, 32-column chunk of s, half).
+// items (K, t, 32-column chunk of s, half): t is the 32-row block of C, or
+// for the partials the 64-row tile of C whose slot they fill.
 template <int OP>
 __global__ void __launch_bounds__(kThreads) k_adj_rowprod(const AdjDesc *__restrict__ ad,
                                                           const int4 *__restrict__ items, int nitems) {
-    __shared__ double As[kTK * kTM], Bs[kTK * 32];
+    constexpr bool kPart = OP == RP_MBP || OP == RP_FNBP;
+    constexpr int BM = kPart ? 64 : 32;     // rows of the output block
+    constexpr int MI = BM / 16;
+    __shared__ double As[kTK * BM], Bs[kTK * 32];
     const int w = blockIdx.x;
     if (w >= nitems) return;
     const AdjDesc &A = *ad;
@@ -331,10 +335,10 @@ __global__ void __launch_bounds__(kThreads) k_adj_rowprod(const AdjDesc *__restr
     const int64_t ld = A.rowptr[K + 1] - A.rowptr[K];
     const int c = (int)(ld - s);
     const int64_t off = A.panel_off[K];
-    const int p0 = t * kTM;
-    const int pm = c - p0 < kTM ? (c - p0 > 0 ? c - p0 : 0) : kTM;
+    const int rb = kPart ? kTM : BM;          // rows of C per item index t
+    const int p0 = t * rb;
+    const int pm = c - p0 < rb ? (c - p0 > 0 ? c - p0 : 0) : rb;
     const int nj = s - j0 < 32 ? s - j0 : 32;
-    constexpr bool kPart = OP == RP_MBP || OP == RP_FNBP;
     const int mrows = kPart ? (s - i0 < 64 ? s - i0 : 64) : pm;
     const int kdim = kPart ? pm : s;
     const int fc = A.super_ptr[K];
@@ -363,31 +367,38 @@ __global__ void __launch_bounds__(kThreads) k_adj_rowprod(const AdjDesc *__restr
         if (OP == RP_FABAR) return k >= j ? A.Linv[A.linv_off[K] + (int64_t)j * s + k] / A.D[fc + k] : 0.0;
         return A.Lb[off + (int64_t)j * ld + s + p0 + k];
     };
-    auto la = [&](int k0, double *Ash) {
-        for (int e = threadIdx.x; e < kTK * kTM; e += kThreads) {
-            const int r = e % kTM, k = k0 + e / kTM;
-            Ash[e] = (r < mrows && k < kdim) ? a_at(r, k) : 0.0;
+    // thread (tx, ty) owns rows ty + 16 i and columns tx + 16 j of the block
+    const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+    double acc[MI][2];
+#pragma unroll
+    for (int i = 0; i < MI; i++) acc[i][0] = acc[i][1] = 0.0;
+    for (int k0 = 0; k0 < kdim; k0 += kTK) {
+        __syncthreads();
+        for (int e = threadIdx.x; e < kTK * BM; e += kThreads) {
+            const int r = e % BM, k = k0 + e / BM;
+            As[e] = (r < mrows && k < kdim) ? a_at(r, k) : 0.0;
         }
-    };
-    auto lb = [&](int k0, double *Bsh) {
         for (int e = threadIdx.x; e < kTK * 32; e += kThreads) {
             const int kk = e % kTK, jl = e / kTK, k = k0 + kk;
-            Bsh[kk * 32 + jl] = (k < kdim && jl < nj) ? b_at(k, jl) : 0.0;
+            Bs[kk * 32 + jl] = (k < kdim && jl < nj) ? b_at(k, jl) : 0.0;
         }
-    };
-    using Sh = Shape<32>;
-    double acc[Sh::MI][Sh::NJ];
+        __syncthreads();
+#pragma unroll 4
+        for (int kk = 0; kk < kTK; kk++) {
+            const double b0 = Bs[kk * 32 + tx], b1 = Bs[kk * 32 + tx + 16];
 #pragma unroll
-    for (int i = 0; i < Sh::MI; i++)
+            for (int i = 0; i < MI; i++) {
+                const double a = As[kk * BM + ty + 16 * i];
+                acc[i][0] = fma(a, b0, acc[i][0]);
+                acc[i][1] = fma(a, b1, acc[i][1]);
+            }
+        }
+    }
 #pragma unroll
-        for (int j = 0; j < Sh::NJ; j++) acc[i][j] = 0.0;
-    tile_gemm<double, 32>(kdim, la, lb, acc, As, Bs);
-    const int tx = threadIdx.x % Sh::TX, ty = threadIdx.x / Sh::TX;
+    for (int i = 0; i < MI; i++)
 #pragma unroll
-    for (int i = 0; i < Sh::MI; i++)
-#pragma unroll
-        for (int j = 0; j < Sh::NJ; j++) {
-            const int r = ty + Sh::TY * i, q = tx + Sh::TX * j;
+        for (int j = 0; j < 2; j++) {
+            const int r = ty + 16 * i, q = tx + 16 * j;
             if (r >= mrows || q >= nj) continue;
             if (kPart) {
                 const int64_t ss = (int64_t)s * s;
@@ -1037,12 +1048,13 @@ static int adj_split(selinv_plan_s *plan) {
             const int s = p.super_ptr[J + 1] - p.super_ptr[J];
             if (!wide(s)) continue;
             const int64_t c = p.rowptr[J + 1] - p.rowptr[J] - s;
+            const int nch = (s + 31) / 32;
             for (int t = 0; t < p.ntiles[J]; t++) a->wd_items.push_back({0, J, t, p.ntiles[J]});
+            for (int b = 0; b < std::max<int64_t>(1, (c + 31) / 32); b++)
+                for (int ch = 0; ch < nch; ch++) a->row_items.push_back(make_int4(J, b, ch, 0));
             for (int t = 0; t < p.ntiles[J]; t++)
-                for (int ch = 0; ch < (s + 31) / 32; ch++) {
-                    a->row_items.push_back(make_int4(J, t, ch, 0));
+                for (int ch = 0; ch < nch; ch++)
                     for (int h = 0; h < (s + 63) / 64; h++) a->mbp_items.push_back(make_int4(J, t, ch, h));
-                }
             if (c > 0)
                 for (int jb = 0; jb < (s + 7) / 8; jb++) a->dig_work.push_back(make_int2(0, (J << 8) | jb));
         }
