@@ -164,6 +164,8 @@ int selinv_plan_stats(selinv_plan plan, selinv_dtype dtype, double *flops, doubl
  *   5 rel_ptr[nseg+1] int64          6 relidx int32
  *   7 level_ptr[nlevels+1] int64     8 level_list[nsuper] int32
  *   9 panel_off[nsuper+1] int64
+ *  10 active[nsuper] int32: 1 if the supernode runs under the current
+ *     subset selection (selinv_plan_select), else 0
  * Returns the element count, or <0 on a bad field.  dst may be NULL. */
 int64_t selinv_plan_get(selinv_plan plan, int field, void *dst);
 /* The plan's current options (after autotuning: the chosen ones). */
@@ -229,6 +231,47 @@ int selinv_adjoint(selinv_plan plan, selinv_dtype dtype, const void *L_dev, cons
 int selinv_factor_adjoint(selinv_plan plan, selinv_dtype dtype, const void *L_dev,
                           const void *D_dev, const void *L_bar_dev, const void *D_bar_dev,
                           void *A_bar_vals_dev, void *cuda_stream);
+
+/* ---------------------------------------------------------------------------
+ * Subset selection (Sec. I: the selected elements may be all or only a
+ * subset of the nonzero entries of the factors -- e.g. the diagonal of
+ * A^{-1}, or the entries on A's own pattern).  Alg. 1 computes supernode K
+ * from its ancestors' blocks only, so the supernodes that must run are the
+ * owners of the selected columns and all their ancestors; the other
+ * subtrees are skipped.
+ *   selinv_plan_select: nsel entries (rows[e], cols[e]) of the permuted
+ *     matrix (host arrays, copied; an upper entry is taken as its symmetric
+ *     lower one).  Every entry must lie on the pattern of L + L^T, else
+ *     BAD_PATTERN and the plan is unchanged; indices out of range give
+ *     INVALID_ARG.  Later selinv_numeric / selinv_numeric_batched calls on
+ *     this plan run only the needed supernodes: the panels of the others are
+ *     not written.  nsel = 0 restores the full inversion.  pos_out (host,
+ *     nsel entries, may be NULL) receives each entry's panel position.
+ *     selinv_adjoint needs every block of A^{-1} and returns UNSUPPORTED
+ *     while a selection is set.
+ *   selinv_plan_selected: the number of selected entries; their panel
+ *     positions to pos_out (host) when it is not NULL.
+ *   selinv_gather: out_dev[e] = Ainv_dev[position of entry e] in the order
+ *     given to selinv_plan_select (device arrays, element type dtype).
+ * ------------------------------------------------------------------------- */
+int selinv_plan_select(selinv_plan plan, int64_t nsel, const int32_t *rows, const int32_t *cols,
+                       int64_t *pos_out);
+int64_t selinv_plan_selected(selinv_plan plan, int64_t *pos_out);
+int selinv_gather(selinv_plan plan, selinv_dtype dtype, const void *Ainv_dev, void *out_dev,
+                  void *cuda_stream);
+
+/* Pole-expansion sum (the use Sec. I names first, density functional
+ * theory: a function of A, e.g. the Fermi function, as a weighted sum of the
+ * selected inverses of shifted matrices A - z_l I on one pattern):
+ *   out_dev[e] = sum_{l=0}^{nitems-1} w_l Ainv[l][pos_dev[e]]
+ * in complex128 (w_l = weights[2l] + i weights[2l+1], host), terms added in
+ * the order l = 0, 1, ... (deterministic).  Ainv: host array of nitems
+ * device panel arrays of element type dtypes[l] (a real one counts as
+ * complex with zero imaginary part); pos_dev: device int64[npos] panel
+ * positions; out_dev: device complex128[npos]. */
+int selinv_pole_sum(int nitems, const selinv_dtype *dtypes, const void *const *Ainv,
+                    const double *weights, int64_t npos, const int64_t *pos_dev, void *out_dev,
+                    void *cuda_stream);
 
 /* Runs selinv_numeric once without graph capture, timing every kernel
  * launch with CUDA events on the stream, and synchronizes.  kernel_ms[k] and

@@ -12,6 +12,11 @@ the paper's definitions and algorithms with plain loops:
 * ``selinv``    -- Alg. 1 (pull), diagonal blocks symmetrized (Sec. II-C)
 * ``selinv_push`` -- Alg. 2 (left-looking push), a different summation order
 * ``selinv_adjoint``, ``ldlt_adjoint`` -- reverse mode of the two numeric steps
+* ``panel_position``, ``needed_supernodes`` -- subset selection (Sec. I: all
+  or a subset of the entries on the factors' pattern): where an entry of
+  A^{-1} is stored, and which supernodes Alg. 1 must run to produce it
+* ``pole_sum``  -- sum_l w_l A_l^{-1}[pos] over selected inverses of shifted
+  matrices (the density-functional-theory use Sec. I names)
 
 It shares no code with the GPU library.
 """
@@ -324,3 +329,42 @@ def block_errors(sym: Sym, G: np.ndarray, O: np.ndarray) -> np.ndarray:
     num = np.sqrt(np.add.reduceat(np.abs(d) ** 2, off[:-1])) if sym.nsuper else np.zeros(0)
     den = np.sqrt(np.add.reduceat(np.abs(o) ** 2, off[:-1])) if sym.nsuper else np.zeros(0)
     return num / np.where(den == 0, 1, den)
+
+
+# ---------------------------------------------------------------------------
+# subset selection and the pole-expansion sum
+# ---------------------------------------------------------------------------
+
+def panel_position(sym: Sym, i: int, j: int) -> int:
+    """Panel slot of entry (i, j) of A^{-1}: the stored lower entry
+    (max(i, j), min(i, j)) in the panel of the supernode owning the column,
+    at the row's place in that supernode's row list.  KeyError if the entry
+    is not on the pattern of L + L^T."""
+    i, j = max(int(i), int(j)), min(int(i), int(j))
+    K = int(np.searchsorted(sym.super_ptr, j, side="right")) - 1
+    R = sym.rows[sym.rowptr[K]:sym.rowptr[K + 1]]
+    k = int(np.searchsorted(R, i))
+    if k >= R.size or R[k] != i:
+        raise KeyError((i, j))
+    return int(sym.panel_offsets()[K] + (j - sym.super_ptr[K]) * R.size + k)
+
+
+def needed_supernodes(sym: Sym, cols) -> np.ndarray:
+    """Boolean mask of the supernodes Alg. 1 runs to produce entries in the
+    given columns: a supernode reads only blocks of its ancestors, so the
+    owners of the columns and every ancestor of an owner (walked up sparent)."""
+    need = np.zeros(sym.nsuper, dtype=bool)
+    for c in np.asarray(cols).ravel():
+        K = int(np.searchsorted(sym.super_ptr, int(c), side="right")) - 1
+        while K >= 0:
+            need[K] = True
+            K = int(sym.sparent[K])
+    return need
+
+
+def pole_sum(Zs, weights, pos) -> np.ndarray:
+    """sum_l w_l Z_l[pos] (complex), terms added in the order given."""
+    out = np.zeros(len(pos), dtype=np.complex128)
+    for Z, w in zip(Zs, weights):
+        out = out + complex(w) * np.asarray(Z)[np.asarray(pos)]
+    return out

@@ -82,6 +82,10 @@ def _load() -> ct.CDLL:
         "selinv_error_string": (ct.c_char_p, [I]),
         "selinv_launch_count": (I64, []),
         "selinv_dinv_noalloc": (I, [I32, P, I64, P, P, I64, P]),
+        "selinv_plan_select": (I, [P, I64, P, P, P]),
+        "selinv_plan_selected": (I64, [P, P]),
+        "selinv_gather": (I, [P, I, P, P, P]),
+        "selinv_pole_sum": (I, [I, P, P, P, I64, P, P, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -99,7 +103,8 @@ REQUIRED_SYMBOLS = ("selinv_default_opts", "selinv_analyse", "selinv_analysis_ge
                     "selinv_plan_get", "selinv_plan_set_opts", "selinv_plan_get_opts", "selinv_numeric",
                     "selinv_numeric_batched", "selinv_numeric_profile", "selinv_plan_set_matrix", "selinv_factor",
                     "selinv_adjoint", "selinv_factor_adjoint", "selinv_status",
-                    "selinv_error_string", "selinv_launch_count", "selinv_dinv_noalloc")
+                    "selinv_error_string", "selinv_launch_count", "selinv_dinv_noalloc",
+                    "selinv_plan_select", "selinv_plan_selected", "selinv_gather", "selinv_pole_sum")
 
 
 def error_string(code: int) -> str:
@@ -226,7 +231,7 @@ def selinv_plan_stats(plan: Plan, dtype: int) -> Tuple[float, float]:
 _PLAN_FIELDS = {"level": (0, np.int32), "seg_ptr": (1, np.int64), "seg_owner": (2, np.int32),
                 "seg_start": (3, np.int32), "seg_coloff": (4, np.int32), "rel_ptr": (5, np.int64),
                 "relidx": (6, np.int32), "level_ptr": (7, np.int64), "level_list": (8, np.int32),
-                "panel_off": (9, np.int64)}
+                "panel_off": (9, np.int64), "active": (10, np.int32)}
 
 
 def selinv_plan_get(plan: Plan, name: str) -> np.ndarray:
@@ -272,6 +277,38 @@ def selinv_numeric_batched(plans: Sequence[Plan], dtypes: Sequence[int], Ls, Ds,
         n, arr([p.handle for p in plans], ct.c_void_p), arr([int(d) for d in dtypes], ct.c_int),
         arr([_dptr(t) for t in Ls], ct.c_void_p), arr([_dptr(t) for t in Ds], ct.c_void_p),
         arr([_dptr(t) for t in Zs], ct.c_void_p), _stream(stream)), "selinv_numeric_batched")
+
+
+def selinv_plan_select(plan: Plan, rows, cols) -> np.ndarray:
+    """Restricts the plan to the entries (rows[e], cols[e]); returns their
+    panel positions.  Empty arrays restore the full inversion."""
+    r = _np(rows, np.int32)
+    c = _np(cols, np.int32)
+    if r.size != c.size:
+        raise ValueError("rows and cols differ in length")
+    pos = np.zeros(max(r.size, 1), dtype=np.int64)
+    _check(LIB.selinv_plan_select(plan.handle, int(r.size), _ptr(r), _ptr(c), _ptr(pos)), "selinv_plan_select")
+    return pos[:r.size]
+
+
+def selinv_plan_selected(plan: Plan) -> np.ndarray:
+    n = LIB.selinv_plan_selected(plan.handle, None)
+    pos = np.zeros(max(n, 1), dtype=np.int64)
+    LIB.selinv_plan_selected(plan.handle, _ptr(pos))
+    return pos[:n]
+
+
+def selinv_gather(plan: Plan, dtype: int, Ainv, out, stream=None):
+    _check(LIB.selinv_gather(plan.handle, int(dtype), _dptr(Ainv), _dptr(out), _stream(stream)), "selinv_gather")
+
+
+def selinv_pole_sum(dtypes: Sequence[int], Ainvs, weights, pos, out, stream=None):
+    """out[e] = sum_l weights[l] * Ainvs[l][pos[e]] (complex128 out, device pos)."""
+    n = len(Ainvs)
+    w = np.ascontiguousarray(np.asarray(weights, dtype=np.complex128)).view(np.float64)
+    arr = lambda xs, T: (T * n)(*xs)
+    _check(LIB.selinv_pole_sum(n, arr([int(d) for d in dtypes], ct.c_int), arr([_dptr(t) for t in Ainvs], ct.c_void_p),
+                               _ptr(w), int(pos.numel()), _dptr(pos), _dptr(out), _stream(stream)), "selinv_pole_sum")
 
 
 def selinv_plan_set_matrix(plan: Plan, n: int, colptr, rowind):

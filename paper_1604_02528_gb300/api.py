@@ -94,5 +94,30 @@ class SelInvContext:
         N.selinv_numeric(self.plan, dt, L, D, out, stream)
         return out
 
+    def select(self, rows, cols) -> np.ndarray:
+        """Restrict later selected inversions to the entries (rows[e], cols[e])
+        (and the supernodes they need); returns their panel positions.  Empty
+        arrays restore the full inversion."""
+        return N.selinv_plan_select(self.plan, rows, cols)
+
+    def gather(self, Ainv, out=None, stream=None):
+        """The selected entries of a panel array, in selection order."""
+        import torch
+        n = int(N.selinv_plan_selected(self.plan).size)
+        if out is None:
+            out = torch.empty(n, dtype=Ainv.dtype, device=Ainv.device)
+        N.selinv_gather(self.plan, selinv_dtype_of(Ainv), Ainv, out, stream)
+        return out
+
     def status(self) -> int:
         return N.selinv_status(self.plan)
+
+
+def pole_sum(Ainvs, weights, pos, stream=None):
+    """sum_l weights[l] * Ainvs[l][pos] on the device (complex128), e.g. a
+    pole expansion of a matrix function's diagonal; pos: device int64 panel
+    positions (from SelInvContext.select)."""
+    import torch
+    out = torch.empty(pos.numel(), dtype=torch.complex128, device=pos.device)
+    N.selinv_pole_sum([selinv_dtype_of(z) for z in Ainvs], list(Ainvs), weights, pos, out, stream)
+    return out

@@ -1070,8 +1070,13 @@ static int adj_split(selinv_plan_s *plan) {
     if (!a->dig_work.empty()) {
         // the forward's level schedule supplies the tcgen05 items of every
         // level (row tiles, column tiles, k-splits) and their reductions
+        // (every supernode: a subset selection of the forward does not apply here)
         const ProbDesc pd = make_desc(p, plan->ws[0], SELINV_F64, nullptr, nullptr, nullptr, false);
-        if ((rc = build_schedule(a->tcs, {&p}, {pd}, SELINV_SCHED_LEVEL))) return rc;
+        std::vector<uint8_t> sel;
+        sel.swap(plan->data.active);
+        rc = build_schedule(a->tcs, {&p}, {pd}, SELINV_SCHED_LEVEL);
+        sel.swap(plan->data.active);
+        if (rc) return rc;
         for (int e = 0; e < (int)a->tcs.launches.size(); e++) {
             const Launch &L = a->tcs.launches[e];
             if ((L.kind == KL_SELINV_TC || L.kind == KL_TC_REDUCE) && L.level >= 0 && L.level < p.nlevels)
@@ -1110,6 +1115,7 @@ extern "C" int selinv_adjoint(selinv_plan plan, selinv_dtype dtype, const void *
     if (dtype != SELINV_F64) return SELINV_ERR_UNSUPPORTED;
     if (plan->data.ns == 0) return SELINV_OK;
     if (!L || !D || !Z || !Zbar || !Lbar || !Dbar) return SELINV_ERR_INVALID_ARG;
+    if (!plan->data.active.empty()) return SELINV_ERR_UNSUPPORTED;   // needs every block of A^{-1}
     int rc = adj_prepare(plan);
     if (rc) return rc;
     if ((rc = adj_split(plan))) return rc;

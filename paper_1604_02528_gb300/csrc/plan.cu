@@ -296,8 +296,8 @@ int ensure_device(PlanData &p) {
 void PlanData::release_device() {
     dfree(d_super_ptr); dfree(d_sparent); dfree(d_rowptr); dfree(d_rows); dfree(d_panel_off);
     dfree(d_colbase); dfree(d_relbase); dfree(d_relidx); dfree(d_linv_off); dfree(d_part_off); dfree(d_part_off_all);
-    dfree(d_lhs_off); dfree(d_lhsu_off); dfree(d_tile_base); dfree(d_linvd_off); dfree(d_status);
-    d_lhs_off = d_lhsu_off = d_tile_base = d_linvd_off = nullptr;
+    dfree(d_lhs_off); dfree(d_lhsu_off); dfree(d_tile_base); dfree(d_linvd_off); dfree(d_status); dfree(d_sel_pos);
+    d_lhs_off = d_lhsu_off = d_tile_base = d_linvd_off = d_sel_pos = nullptr;
     d_super_ptr = d_sparent = d_rows = d_relidx = nullptr;
     d_rowptr = d_panel_off = d_colbase = d_relbase = d_linv_off = d_part_off = d_part_off_all = nullptr;
     d_status = nullptr;
@@ -369,6 +369,8 @@ int build_schedule(Schedule &S, const std::vector<const PlanData *> &plans,
     S.pre_bytes.clear();
     S.mode = mode;
     const int np = (int)plans.size();
+    // subset selection: supernodes outside every selected entry's ancestor chain do not run
+    auto act = [&](int i, int32_t K) { return plans[i]->active.empty() || plans[i]->active[K] != 0; };
     // 1) L_KK^{-1}, Dinv for every supernode (one launch per dtype and size class)
     for (int dt = 0; dt < 2; dt++)
         for (int large = 1; large >= 0; large--) {
@@ -377,7 +379,8 @@ int build_schedule(Schedule &S, const std::vector<const PlanData *> &plans,
                 if (descs[i].dtype != dt) continue;
                 const PlanData &p = *plans[i];
                 for (int32_t K = 0; K < p.ns; K++)
-                    if ((p.super_ptr[K + 1] - p.super_ptr[K] > 32) == (large == 1)) S.h_work.push_back(make_int2(i, K));
+                    if (act(i, K) && (p.super_ptr[K + 1] - p.super_ptr[K] > 32) == (large == 1))
+                        S.h_work.push_back(make_int2(i, K));
             }
             const int cnt = (int)(S.h_work.size() - off);
             if (cnt) S.launches.push_back({0, dt, large, off, cnt, -1});
@@ -391,7 +394,7 @@ int build_schedule(Schedule &S, const std::vector<const PlanData *> &plans,
             for (int32_t K = 0; K < p.ns; K++) {
                 const int s = p.super_ptr[K + 1] - p.super_ptr[K];
                 const int64_t c = p.rowptr[K + 1] - p.rowptr[K] - s;
-                if (c == 0 || !oz_eligible(descs[i].dtype, s, p.opts)) continue;
+                if (c == 0 || !act(i, K) || !oz_eligible(descs[i].dtype, s, p.opts)) continue;
                 for (int jb = 0; jb < (s + 7) / 8; jb++) S.h_work.push_back(make_int2(i, (K << 8) | jb));
             }
         }
@@ -405,7 +408,7 @@ int build_schedule(Schedule &S, const std::vector<const PlanData *> &plans,
             for (int32_t K = 0; K < p.ns; K++) {
                 const int s = p.super_ptr[K + 1] - p.super_ptr[K];
                 const int64_t c = p.rowptr[K + 1] - p.rowptr[K] - s;
-                if (c == 0 || !oz_eligible(descs[i].dtype, s, p.opts)) continue;
+                if (c == 0 || !act(i, K) || !oz_eligible(descs[i].dtype, s, p.opts)) continue;
                 const int ktn = s <= 16 ? 16 : (s <= 32 ? 32 : 64);
                 if (ktn != tn) continue;
                 const int ncol = (s + tn - 1) / tn;
@@ -425,7 +428,7 @@ int build_schedule(Schedule &S, const std::vector<const PlanData *> &plans,
                 for (int32_t K = 0; K < p.ns; K++) {
                     const int s = p.super_ptr[K + 1] - p.super_ptr[K];
                     const int64_t c = p.rowptr[K + 1] - p.rowptr[K] - s;
-                    if (c == 0 || bucket_of(s) != b || oz_eligible(dt, s, p.opts)) continue;
+                    if (c == 0 || !act(i, K) || bucket_of(s) != b || oz_eligible(dt, s, p.opts)) continue;
                     for (int t = 0; t < p.ntiles[K]; t++) S.h_items.push_back({i, K, t, p.ntiles[K]});
                 }
             }
@@ -440,7 +443,7 @@ int build_schedule(Schedule &S, const std::vector<const PlanData *> &plans,
             for (int32_t K = 0; K < p.ns; K++) {
                 const int s = p.super_ptr[K + 1] - p.super_ptr[K];
                 const int64_t c = p.rowptr[K + 1] - p.rowptr[K] - s;
-                if (c == 0 || mode == SELINV_SCHED_PERSISTENT ||
+                if (c == 0 || !act(i, K) || mode == SELINV_SCHED_PERSISTENT ||
                     !oz_eligible(descs[i].dtype, s, p.opts))
                     continue;
                 for (int jb = 0; jb < (s + 7) / 8; jb++) S.h_work.push_back(make_int2(i, (K << 8) | jb));
@@ -543,7 +546,8 @@ int build_schedule(Schedule &S, const std::vector<const PlanData *> &plans,
                     if (descs[i].dtype != dt) continue;
                     const PlanData &p = *plans[i];
                     if (l >= p.nlevels) continue;
-                    for (int64_t e = p.level_ptr[l]; e < p.level_ptr[l + 1]; e++) push_items(i, p.level_list[e]);
+                    for (int64_t e = p.level_ptr[l]; e < p.level_ptr[l + 1]; e++)
+                        if (act(i, p.level_list[e])) push_items(i, p.level_list[e]);
                 }
             const int cnt = (int)(S.h_items.size() - off);
             S.h_buckets.resize(S.h_items.size());
@@ -559,6 +563,7 @@ int build_schedule(Schedule &S, const std::vector<const PlanData *> &plans,
         for (int i = 0; i < np; i++) {
             const PlanData &p = *plans[i];
             for (int32_t K = p.ns - 1; K >= 0; K--) {
+                if (!act(i, K)) continue;
                 const int s = p.super_ptr[K + 1] - p.super_ptr[K];
                 if (oz_eligible(descs[i].dtype, s, p.opts)) {
                     const int tn = oz_tn(s);
@@ -594,7 +599,7 @@ int build_schedule(Schedule &S, const std::vector<const PlanData *> &plans,
                 if (l >= p.nlevels) continue;
                 for (int64_t e = p.level_ptr[l]; e < p.level_ptr[l + 1]; e++) {
                     const int32_t K = p.level_list[e];
-                    if (oz_eligible(descs[i].dtype, p.super_ptr[K + 1] - p.super_ptr[K], p.opts))
+                    if (act(i, K) && oz_eligible(descs[i].dtype, p.super_ptr[K + 1] - p.super_ptr[K], p.opts))
                         oz.push_back({i, K});
                 }
             }
@@ -635,7 +640,7 @@ int build_schedule(Schedule &S, const std::vector<const PlanData *> &plans,
                         for (int64_t e = p.level_ptr[l]; e < p.level_ptr[l + 1]; e++) {
                             const int32_t K = p.level_list[e];
                             const int s = p.super_ptr[K + 1] - p.super_ptr[K];
-                            if (bucket_of(s) == b && !oz_eligible(dt, s, p.opts)) push_items(i, K);
+                            if (act(i, K) && bucket_of(s) == b && !oz_eligible(dt, s, p.opts)) push_items(i, K);
                         }
                     }
                     const int cnt = (int)(S.h_items.size() - off);
@@ -861,6 +866,12 @@ extern "C" int64_t selinv_plan_get(selinv_plan plan, int field, void *dst) {
     case 7: src = p.level_ptr.data(); cnt = (int64_t)p.level_ptr.size(); es = 8; break;
     case 8: src = p.level_list.data(); cnt = p.ns; break;
     case 9: src = p.panel_off.data(); cnt = p.ns + 1; es = 8; break;
+    case 10: {   // supernodes that run under the current selection (1 = runs)
+        if (dst)
+            for (int32_t K = 0; K < p.ns; K++)
+                static_cast<int32_t *>(dst)[K] = p.active.empty() ? 1 : (int32_t)p.active[K];
+        return p.ns;
+    }
     default: return SELINV_ERR_INVALID_ARG;
     }
     if (dst && cnt > 0) std::memcpy(dst, src, es * (size_t)cnt);
@@ -1070,7 +1081,7 @@ extern "C" int selinv_numeric_batched(int nitems, const selinv_plan *plans, cons
         bool same = true;
         for (int i = 0; i < nitems && same; i++)
             same = b.plans[i] == plans[i] && b.dtypes[i] == dtypes[i] && b.L[i] == L[i] &&
-                   b.D[i] == D[i] && b.Z[i] == Z[i];
+                   b.D[i] == D[i] && b.Z[i] == Z[i] && b.sel_version[i] == plans[i]->data.sel_version;
         if (same) { hit = &b; break; }
     }
     for (int i = 0; i < nitems; i++) {
@@ -1103,6 +1114,7 @@ extern "C" int selinv_numeric_batched(int nitems, const selinv_plan *plans, cons
         b.L.assign(L, L + nitems);
         b.D.assign(D, D + nitems);
         b.Z.assign(Z, Z + nitems);
+        for (int i = 0; i < nitems; i++) b.sel_version.push_back(plans[i]->data.sel_version);
         int rc = build_schedule(b.sched, pds, descs, mode);
         if (rc) {
             b.sched.release();

@@ -25,6 +25,12 @@ struct PlanData {
     std::vector<int64_t> lhsu_off;          // the same in the tcgen05 operand layout
     std::vector<int64_t> tile_base;         // prefix sums of the 64-row tiles of each supernode
     std::vector<int64_t> linvd_off;         // digit planes of L_KK^{-1} (tensor-core path)
+    // subset selection: the supernodes that run (empty: all) and the panel
+    // positions of the selected entries
+    std::vector<uint8_t> active;
+    std::vector<int64_t> sel_pos;
+    int64_t sel_version = 0;
+    int64_t *d_sel_pos = nullptr;
     int nlevels = 0;
     int64_t nnz = 0, linv_total = 0, part_max = 1, part_all = 1, lhs_total = 0, lhsu_total = 0, tile_total = 0, linvd_total = 0;
     // device copies
@@ -115,6 +121,7 @@ struct BatchEntry {
     std::vector<int> dtypes;
     std::vector<const void *> L, D;
     std::vector<void *> Z;
+    std::vector<int64_t> sel_version;   // each plan's selection when the schedule was built
     Schedule sched;
 };
 
