@@ -262,9 +262,32 @@ def variant_batched(dev, stream, flush, N, npoles, lap_scale):
         for c, d, L, D, Z in zip(ctxs, dts, Ls, Ds, Zs):
             N.selinv_numeric(c.plan, d, L, D, Z, stream)
     t_each = time_calls(each, stream, 1, 2, flush)
+    # pole-expansion sum over the diagonal of the pole shifts (after the timings: the
+    # selection restricts the shared plan, which then needs every supernode anyway)
+    poles = [i for i, c in enumerate(ctxs) if c is base_ctx]
+    diag = np.arange(base.n)
+    pos = torch.from_numpy(N.selinv_plan_select(base_ctx.plan, diag, diag)).to(dev)
+    w = np.exp(1j * np.linspace(0.0, np.pi, len(poles)))
+    out = torch.empty(base.n, dtype=torch.complex128, device=dev)
+    t_pole = time_calls(lambda: N.selinv_pole_sum([dts[i] for i in poles], [Zs[i] for i in poles], w, pos, out,
+                                                  stream), stream, 3, 10, flush)
+    N.selinv_plan_select(base_ctx.plan, [], [])
     return {"problems": f"{npoles} complex pole shifts of the 40^3 pattern + 8 Laplacians (side x {lap_scale})",
             "batched_ms": round(t_batched, 3), "one_call_per_problem_ms": round(t_each, 3),
-            "speedup": round(t_each / t_batched, 3), "gflops": round(flops / t_batched / 1e6, 2)}
+            "speedup": round(t_each / t_batched, 3), "gflops": round(flops / t_batched / 1e6, 2),
+            "pole_sum_diag_ms": round(t_pole, 4)}
+
+
+def variant_selection(ctx, dt, L, D, Z, stream, flush, N):
+    """Subset selection: the diagonal of the first eighth of the columns (one
+    corner of the nested-dissection order) -- only their ancestor chains run."""
+    cols = np.arange(ctx.n // 8)
+    N.selinv_plan_select(ctx.plan, cols, cols)
+    active = N.selinv_plan_get(ctx.plan, "active")
+    ms = time_calls(lambda: N.selinv_numeric(ctx.plan, dt, L, D, Z, stream), stream, 2, 3, flush)
+    N.selinv_plan_select(ctx.plan, [], [])
+    return {"selected": f"diagonal of columns 0..{ctx.n // 8 - 1}", "supernodes_run": int(active.sum()),
+            "supernodes": int(active.size), "ms": round(ms, 3)}
 
 
 def variant_adjoint(dev, stream, flush, N):
@@ -496,6 +519,7 @@ def main():
                                                            N.SELINV_SCHED_LEVEL, 0), 3)
         variants["persistent_dfma_ms"] = round(variant_schedule(ctx, dt, L, D, Z, stream, flush, N,
                                                                 N.SELINV_SCHED_PERSISTENT, 0), 3)
+        variants["selection"] = variant_selection(ctx, dt, L, D, Z, stream, flush, N)
         variants["batched"] = variant_batched(dev, stream, flush, N, args.batch_poles, 1.0)
         variants["adjoint"] = variant_adjoint(dev, stream, flush, N)
 
