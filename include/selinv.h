@@ -29,7 +29,13 @@
  *         pattern of L, the upper part being its transpose.
  *  - Transposes are plain for complex symmetric matrices (A = A^T), as the
  *    configured workloads are complex symmetric, not Hermitian.
- *  - Element types: SELINV_F64 = double, SELINV_C128 = two doubles (re, im).
+ *  - Element types: SELINV_F64 = double, SELINV_C128 = two doubles (re, im)
+ *    of a complex symmetric matrix (A = A^T), SELINV_C128H = the same storage
+ *    for a complex Hermitian matrix (A = A^H, the variant of Sec. II-C with
+ *    conjugate transposes: A = L D L^H with real D, Dinv_K = L_KK^{-H}
+ *    D_K^{-1} L_KK^{-1}, A^{-1}_KK = Dinv_K - Lhat^H A^{-1}_{C,K}
+ *    symmetrized as (X + X^H)/2, and the upper part of A^{-1} is the
+ *    conjugate of the stored lower part).
  *  - Device pointers are caller-owned (the library never frees them) and must
  *    be 16-byte aligned.  Host arrays passed in are copied; the caller keeps
  *    ownership.
@@ -62,7 +68,7 @@ extern "C" {
 typedef struct selinv_plan_s *selinv_plan;          /* opaque, owned by the library */
 typedef struct selinv_analysis_s *selinv_analysis;  /* opaque, owned by the library */
 
-typedef enum { SELINV_F64 = 0, SELINV_C128 = 1 } selinv_dtype;
+typedef enum { SELINV_F64 = 0, SELINV_C128 = 1, SELINV_C128H = 2 } selinv_dtype;
 
 typedef enum {
     SELINV_SCHED_PLAIN = 0,      /* one launch chain per supernode, K = N..1            */

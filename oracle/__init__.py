@@ -9,7 +9,8 @@ the paper's definitions and algorithms with plain loops:
 * ``plan``      -- level of each supernode, the sets C of Alg. 1 split by
                    owning ancestor, and relative row indices
 * ``ldlt``      -- LDL^T without pivoting on the supernodal pattern (Sec. IV)
-* ``selinv``    -- Alg. 1 (pull), diagonal blocks symmetrized (Sec. II-C)
+* ``selinv``    -- Alg. 1 (pull), diagonal blocks symmetrized (Sec. II-C);
+                   ``hermitian=True``: conjugate transposes, A = A^H
 * ``selinv_push`` -- Alg. 2 (left-looking push), a different summation order
 * ``selinv_adjoint``, ``ldlt_adjoint`` -- reverse mode of the two numeric steps
 * ``panel_position``, ``needed_supernodes`` -- subset selection (Sec. I: all
@@ -69,6 +70,13 @@ def _load():
             f = getattr(lib, "orc_ldlt_adjoint" + sfx)
             f.restype = ct.c_int
             f.argtypes = [ct.c_int32, P, P, P, P, P, P, P, P, P]
+        # complex Hermitian: the factorization and Alg. 1 only
+        lib.orc_ldlt_h.restype = ct.c_int
+        lib.orc_ldlt_h.argtypes = [ct.c_int32, P, P, P, ct.c_int32, P, P, P, P, P, P]
+        lib.orc_selinv_h.restype = ct.c_int
+        lib.orc_selinv_h.argtypes = [ct.c_int32, P, P, P, P, P, P, P, ct.c_int]
+        lib.orc_selinv_top_h.restype = ct.c_int
+        lib.orc_selinv_top_h.argtypes = [ct.c_int32, P, P, P, P, P, P, P, ct.c_int, ct.c_int32]
         _lib = lib
     return _lib
 
@@ -188,27 +196,33 @@ def _check(rc: int, what: str):
 
 
 def ldlt(problem, sym: Sym) -> Tuple[np.ndarray, np.ndarray]:
-    """L (panel layout, unit diagonal block) and D of P A P^T = L D L^T."""
+    """L (panel layout, unit diagonal block) and D of P A P^T = L D L^T
+    (L D L^H for a Hermitian problem)."""
     lib = _load()
     dt = np.complex128 if problem.values.dtype.kind == "c" else np.float64
+    herm = bool(getattr(problem, "hermitian", False))
     vals = np.ascontiguousarray(problem.values, dtype=dt)
     colptr = np.ascontiguousarray(problem.colptr, dtype=np.int64)
     rowind = np.ascontiguousarray(problem.rowind, dtype=np.int32)
     L = np.zeros(sym.nnz_panels, dtype=dt)
     D = np.zeros(sym.n, dtype=dt)
-    rc = getattr(lib, "orc_ldlt" + _sfx(dt))(int(problem.n), _p(colptr), _p(rowind), _p(vals),
+    rc = getattr(lib, "orc_ldlt" + ("_h" if herm else _sfx(dt)))(int(problem.n), _p(colptr), _p(rowind), _p(vals),
                                             *_sym_args(sym), _p(L), _p(D))
     _check(rc, "ldlt")
     return L, D
 
 
-def selinv(sym: Sym, L: np.ndarray, D: np.ndarray, symmetrize: bool = True) -> np.ndarray:
-    """Selected inverse on the pattern of L (Alg. 1), panel layout."""
+def selinv(sym: Sym, L: np.ndarray, D: np.ndarray, symmetrize: bool = True,
+           hermitian: bool = False) -> np.ndarray:
+    """Selected inverse on the pattern of L (Alg. 1), panel layout; with
+    hermitian=True the conjugate-transpose form for A = A^H."""
     lib = _load()
     L = np.ascontiguousarray(L); D = np.ascontiguousarray(D, dtype=L.dtype)
     Z = np.zeros_like(L)
-    rc = getattr(lib, "orc_selinv" + _sfx(L.dtype))(*_sym_args(sym), _p(L), _p(D), _p(Z),
-                                                   int(symmetrize))
+    if hermitian and L.dtype.kind != "c":
+        raise ValueError("the Hermitian form takes complex values")
+    rc = getattr(lib, "orc_selinv" + ("_h" if hermitian else _sfx(L.dtype)))(*_sym_args(sym), _p(L), _p(D), _p(Z),
+                                                                            int(symmetrize))
     _check(rc, "selinv")
     return Z
 
@@ -300,12 +314,12 @@ def panel_entries(sym: Sym) -> Tuple[np.ndarray, np.ndarray, np.ndarray]:
     return r.astype(np.int64), cc.astype(np.int64), r >= cc
 
 
-def panels_to_dense(sym: Sym, Z: np.ndarray) -> np.ndarray:
-    """Symmetric dense matrix from the stored lower entries (small n)."""
+def panels_to_dense(sym: Sym, Z: np.ndarray, hermitian: bool = False) -> np.ndarray:
+    """Symmetric (Hermitian) dense matrix from the stored lower entries (small n)."""
     r, c, low = panel_entries(sym)
     out = np.zeros((sym.n, sym.n), dtype=Z.dtype)
+    out[c[low], r[low]] = np.conj(Z[low]) if hermitian else Z[low]
     out[r[low], c[low]] = Z[low]
-    out[c[low], r[low]] = Z[low]
     return out
 
 

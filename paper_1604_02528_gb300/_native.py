@@ -18,6 +18,7 @@ _LIB_PATH = os.path.join(_HERE, "libselinv.so")
 
 SELINV_F64 = 0
 SELINV_C128 = 1
+SELINV_C128H = 2   # complex Hermitian (conjugate transposes)
 SELINV_SCHED_PLAIN = 0
 SELINV_SCHED_LEVEL = 1
 SELINV_SCHED_PERSISTENT = 2
@@ -255,7 +256,27 @@ def selinv_plan_get_opts(plan: Plan) -> selinv_opts:
     return o
 
 
+def _need(t, elems: int, dtype: int, what: str):
+    """The library writes and reads whole panel / diagonal arrays: a smaller
+    buffer would be accessed out of bounds, so refuse it here."""
+    if t is None:
+        return
+    es = 8 if int(dtype) == SELINV_F64 else 16
+    if t.numel() * t.element_size() < elems * es:
+        raise ValueError(f"{what}: {t.numel() * t.element_size()} bytes, need {elems * es} "
+                         f"({elems} elements of {es} bytes)")
+
+
+def _need_panels(plan: Plan, dtype: int, panels=(), diags=()):
+    nnz = plan.nnz
+    for name, t in panels:
+        _need(t, nnz, dtype, name)
+    for name, t in diags:
+        _need(t, plan.n, dtype, name)
+
+
 def selinv_numeric(plan: Plan, dtype: int, L, D, Ainv, stream=None):
+    _need_panels(plan, dtype, [("L", L), ("Ainv", Ainv)], [("D", D)])
     _check(LIB.selinv_numeric(plan.handle, int(dtype), _dptr(L), _dptr(D), _dptr(Ainv),
                               _stream(stream)), "selinv_numeric")
 
@@ -263,6 +284,7 @@ def selinv_numeric(plan: Plan, dtype: int, L, D, Ainv, stream=None):
 def selinv_numeric_profile(plan: Plan, dtype: int, L, D, Ainv, stream=None):
     """Per-kernel-kind device time (ms) and launch counts of one call, indexed
     by PROFILE_KINDS."""
+    _need_panels(plan, dtype, [("L", L), ("Ainv", Ainv)], [("D", D)])
     ms = (ct.c_double * len(PROFILE_KINDS))()
     cnt = (ct.c_int64 * len(PROFILE_KINDS))()
     _check(LIB.selinv_numeric_profile(plan.handle, int(dtype), _dptr(L), _dptr(D), _dptr(Ainv),
@@ -272,6 +294,8 @@ def selinv_numeric_profile(plan: Plan, dtype: int, L, D, Ainv, stream=None):
 
 def selinv_numeric_batched(plans: Sequence[Plan], dtypes: Sequence[int], Ls, Ds, Zs, stream=None):
     n = len(plans)
+    for p, d, L, D, Z in zip(plans, dtypes, Ls, Ds, Zs):
+        _need_panels(p, d, [("L", L), ("Ainv", Z)], [("D", D)])
     arr = lambda xs, T: (T * n)(*xs)
     _check(LIB.selinv_numeric_batched(
         n, arr([p.handle for p in plans], ct.c_void_p), arr([int(d) for d in dtypes], ct.c_int),
@@ -299,12 +323,17 @@ def selinv_plan_selected(plan: Plan) -> np.ndarray:
 
 
 def selinv_gather(plan: Plan, dtype: int, Ainv, out, stream=None):
+    _need_panels(plan, dtype, [("Ainv", Ainv)])
+    _need(out, int(LIB.selinv_plan_selected(plan.handle, None)), dtype, "out")
     _check(LIB.selinv_gather(plan.handle, int(dtype), _dptr(Ainv), _dptr(out), _stream(stream)), "selinv_gather")
 
 
 def selinv_pole_sum(dtypes: Sequence[int], Ainvs, weights, pos, out, stream=None):
     """out[e] = sum_l weights[l] * Ainvs[l][pos[e]] (complex128 out, device pos)."""
     n = len(Ainvs)
+    if len(dtypes) != n or len(weights) != n:
+        raise ValueError("one dtype and one weight per term")
+    _need(out, int(pos.numel()), SELINV_C128, "out")
     w = np.ascontiguousarray(np.asarray(weights, dtype=np.complex128)).view(np.float64)
     arr = lambda xs, T: (T * n)(*xs)
     _check(LIB.selinv_pole_sum(n, arr([int(d) for d in dtypes], ct.c_int), arr([_dptr(t) for t in Ainvs], ct.c_void_p),
@@ -318,17 +347,21 @@ def selinv_plan_set_matrix(plan: Plan, n: int, colptr, rowind):
 
 
 def selinv_factor(plan: Plan, dtype: int, A_vals, L, D, stream=None):
+    _need_panels(plan, dtype, [("L", L)], [("D", D)])
     _check(LIB.selinv_factor(plan.handle, int(dtype), _dptr(A_vals), _dptr(L), _dptr(D),
                              _stream(stream)), "selinv_factor")
 
 
 def selinv_adjoint(plan: Plan, dtype: int, L, D, Ainv, Ainv_bar, L_bar, D_bar, stream=None):
+    _need_panels(plan, dtype, [("L", L), ("Ainv", Ainv), ("Ainv_bar", Ainv_bar), ("L_bar", L_bar)],
+                 [("D", D), ("D_bar", D_bar)])
     _check(LIB.selinv_adjoint(plan.handle, int(dtype), _dptr(L), _dptr(D), _dptr(Ainv),
                               _dptr(Ainv_bar), _dptr(L_bar), _dptr(D_bar), _stream(stream)),
            "selinv_adjoint")
 
 
 def selinv_factor_adjoint(plan: Plan, dtype: int, L, D, L_bar, D_bar, A_bar_vals, stream=None):
+    _need_panels(plan, dtype, [("L", L), ("L_bar", L_bar)], [("D", D), ("D_bar", D_bar)])
     _check(LIB.selinv_factor_adjoint(plan.handle, int(dtype), _dptr(L), _dptr(D), _dptr(L_bar),
                                      _dptr(D_bar), _dptr(A_bar_vals), _stream(stream)),
            "selinv_factor_adjoint")

@@ -20,13 +20,13 @@ KIND = {"fundamental": 0, "relaxed": 1}
 
 def torch_dtype(dtype: int):
     import torch
-    return torch.complex128 if dtype == N.SELINV_C128 else torch.float64
+    return torch.float64 if dtype == N.SELINV_F64 else torch.complex128
 
 
-def selinv_dtype_of(t) -> int:
+def selinv_dtype_of(t, hermitian: bool = False) -> int:
     import torch
     if t.dtype == torch.complex128:
-        return N.SELINV_C128
+        return N.SELINV_C128H if hermitian else N.SELINV_C128
     if t.dtype == torch.float64:
         return N.SELINV_F64
     raise TypeError(f"unsupported dtype {t.dtype}: float64 or complex128")
@@ -36,8 +36,9 @@ class SelInvContext:
     """Symbolic analysis + device plan of one lower-CSC pattern."""
 
     def __init__(self, n: int, colptr, rowind, kind: str = "fundamental", cap: int = 64,
-                 fill: float = 0.0, opts: Optional[N.selinv_opts] = None):
+                 fill: float = 0.0, opts: Optional[N.selinv_opts] = None, hermitian: bool = False):
         self.n = int(n)
+        self.hermitian = bool(hermitian)   # complex values are Hermitian (A = A^H), not symmetric
         self.colptr = np.ascontiguousarray(colptr, dtype=np.int64)
         self.rowind = np.ascontiguousarray(rowind, dtype=np.int32)
         self.analysis = N.selinv_analyse(self.n, self.colptr, self.rowind, KIND[kind], cap, fill)
@@ -50,7 +51,8 @@ class SelInvContext:
     @classmethod
     def from_problem(cls, p, opts: Optional[N.selinv_opts] = None) -> "SelInvContext":
         sn = p.supernodes
-        return cls(p.n, p.colptr, p.rowind, str(sn["kind"]), int(sn["cap"]), float(sn["fill"]), opts)
+        return cls(p.n, p.colptr, p.rowind, str(sn["kind"]), int(sn["cap"]), float(sn["fill"]), opts,
+                   hermitian=bool(getattr(p, "hermitian", False)))
 
     @property
     def nnz(self) -> int:
@@ -77,7 +79,7 @@ class SelInvContext:
     def factor(self, A_vals, L=None, D=None, stream=None):
         """L (panels) and D of A = L D L^T from A's CSC values on the device."""
         import torch
-        dt = selinv_dtype_of(A_vals)
+        dt = selinv_dtype_of(A_vals, self.hermitian)
         self.attach_matrix()
         if L is None:
             L = self.empty_panels(dt, A_vals.device)
@@ -88,7 +90,7 @@ class SelInvContext:
 
     def selinv(self, L, D, out=None, stream=None):
         """Selected inverse on the pattern of L (panel layout)."""
-        dt = selinv_dtype_of(L)
+        dt = selinv_dtype_of(L, self.hermitian)
         if out is None:
             out = self.empty_panels(dt, L.device)
         N.selinv_numeric(self.plan, dt, L, D, out, stream)

@@ -8,8 +8,9 @@
 
 namespace selinv {
 
-// complex128 as two doubles; plain (non-conjugating) transposes throughout,
-// since the configured complex matrices are complex symmetric (A = A^T).
+// complex128 as two doubles.  Transposes are plain for complex symmetric
+// problems (A = A^T); a Hermitian problem (ProbDesc::herm) conjugates every
+// transposed factor (cjif below).
 struct __align__(16) zd {
     double x, y;
 };
@@ -63,6 +64,10 @@ __host__ __device__ inline zd recip(zd a) {
     double d = ax * ax + ay * ay;
     return make_zd(ax * s / d, -ay * s / d);
 }
+// conjugate (identity for real values); cjif: only when h is set
+__host__ __device__ inline double cj(double a) { return a; }
+__host__ __device__ inline zd cj(zd a) { return make_zd(a.x, -a.y); }
+template <typename T> __host__ __device__ inline T cjif(T a, bool h) { return h ? cj(a) : a; }
 __host__ __device__ inline bool is_zero(double a) { return a == 0.0; }
 __host__ __device__ inline bool is_zero(zd a) { return a.x == 0.0 && a.y == 0.0; }
 __host__ __device__ inline bool finite_val(double a) { return isfinite(a); }
@@ -109,8 +114,9 @@ struct ProbDesc {
     int *tcount;                // [sum ntiles] arrivals per (K, row tile), zero between calls
     const int64_t *tile_base;   // [ns+1] prefix sums of the row tiles of each supernode
     int32_t ns, n;
-    int32_t dtype;              // selinv_dtype
+    int32_t dtype;              // element type: SELINV_F64 or SELINV_C128
     int32_t symmetrize;
+    int32_t herm;               // complex Hermitian (SELINV_C128H): conjugate transposes
 };
 
 // One unit of work of a tiled kernel: rows [tile*TM, tile*TM+TM) of C(K).

@@ -1,7 +1,8 @@
 // Prerequisite factorization A = L D L^T without pivoting, supernodal, level
 // by level from the leaves (Sec. IV of the paper uses a supernodal
 // factorization with a symmetric permutation and no dynamic pivoting; Sec.
-// II-C: LDL^T for symmetric A), in multifrontal form:
+// II-C: LDL^T for symmetric A, L D L^H for a Hermitian one, where every
+// transposed factor below is conjugated), in multifrontal form:
 //
 //   k_assemble  scatter A's CSC values into the panels (after a memset)
 //   k_fasm      extend-add of each child's update matrix U_child into its
@@ -83,7 +84,7 @@ __global__ void __launch_bounds__(256) k_fupd(const FactorDesc *__restrict__ fd,
     const int pa = ti * kSegB, st = tj * kSegB;
     const int np = c - pa < kSegB ? c - pa : kSegB, nq = c - st < kSegB ? c - st : kSegB;
     auto x = [&](int pl, int k) { return mul(LC[(int64_t)k * ld + pa + pl], DJ[k]); };
-    auto y = [&](int ql, int k) { return LC[(int64_t)k * ld + st + ql]; };
+    auto y = [&](int ql, int k) { return cjif(LC[(int64_t)k * ld + st + ql], F.herm != 0); };
     auto out = [&](int pl, int ql, T v) {
         T *dst = UJ + (int64_t)(st + ql) * c + pa + pl;
         *dst = sub(*dst, v);
@@ -122,7 +123,7 @@ __global__ void __launch_bounds__(256) k_fdiag(const FactorDesc *__restrict__ fd
             const int i = j + 1 + e % m, k = j + 1 + e / m;
             if (k > i) continue;
             T *a = P + (int64_t)k * ld + i;
-            *a = sub(*a, mul(mul(P[(int64_t)j * ld + i], s_d), P[(int64_t)j * ld + k]));
+            *a = sub(*a, mul(mul(P[(int64_t)j * ld + i], s_d), cjif(P[(int64_t)j * ld + k], F.herm != 0)));
         }
     }
     __syncthreads();
@@ -147,10 +148,11 @@ __global__ void __launch_bounds__(64) k_ftrsm(const FactorDesc *__restrict__ fd,
     if (r < s || r >= ld) return;
     T *P = static_cast<T *>(F.L) + F.panel_off[J];
     const T *D = static_cast<const T *>(F.D) + fc;
-    // x (D L_JJ^T) = a : x_j = (a_j - sum_{k<j} x_k D_k L_jk) / D_j, in place
+    // x (D L_JJ^T) = a : x_j = (a_j - sum_{k<j} x_k D_k L_jk) / D_j, in place (conj(L_jk): Hermitian)
+    const bool h = F.herm != 0;
     for (int j = 0; j < s; j++) {
         T acc = P[(int64_t)j * ld + r];
-        for (int k = 0; k < j; k++) msub(acc, mul(P[(int64_t)k * ld + r], D[k]), P[(int64_t)k * ld + j]);
+        for (int k = 0; k < j; k++) msub(acc, mul(P[(int64_t)k * ld + r], D[k]), cjif(P[(int64_t)k * ld + j], h));
         P[(int64_t)j * ld + r] = mul(acc, recip(D[j]));
     }
 }
@@ -261,7 +263,7 @@ int factor_tables(selinv_plan_s *plan) {
     return SELINV_OK;
 }
 
-FactorDesc *factor_desc(selinv_plan_s *plan, void *L, void *D, cudaStream_t st) {
+FactorDesc *factor_desc(selinv_plan_s *plan, void *L, void *D, cudaStream_t st, int herm) {
     FactorData *f = plan->factor;
     const PlanData &p = plan->data;
     FactorDesc h;
@@ -276,12 +278,13 @@ FactorDesc *factor_desc(selinv_plan_s *plan, void *L, void *D, cudaStream_t st) 
     h.L = L;
     h.D = D;
     h.status = p.d_status;
+    h.herm = herm;
     cudaMemcpyAsync(f->d_desc, &h, sizeof(h), cudaMemcpyHostToDevice, st);
     return f->d_desc;
 }
 
 template <typename T>
-static int factor_t(selinv_plan_s *plan, const void *A, void *L, void *D, cudaStream_t st) {
+static int factor_t(selinv_plan_s *plan, const void *A, void *L, void *D, cudaStream_t st, int herm) {
     FactorData *f = plan->factor;
     const PlanData &p = plan->data;
     const size_t ubytes = sizeof(T) * (size_t)std::max<int64_t>(f->u_off[p.ns], 1);
@@ -292,7 +295,7 @@ static int factor_t(selinv_plan_s *plan, const void *A, void *L, void *D, cudaSt
         if (cudaMalloc(&f->U, ubytes) != cudaSuccess) return SELINV_ERR_OOM;
         f->U_bytes = ubytes;
     }
-    FactorDesc *fd = factor_desc(plan, L, D, st);
+    FactorDesc *fd = factor_desc(plan, L, D, st, herm);
     if (cudaMemsetAsync(L, 0, sizeof(T) * (size_t)p.nnz, st) != cudaSuccess) return SELINV_ERR_CUDA;
     if (cudaMemsetAsync(f->U, 0, ubytes, st) != cudaSuccess) return SELINV_ERR_CUDA;
     if (f->nnzA > 0) {
@@ -357,12 +360,14 @@ extern "C" int selinv_plan_set_matrix(selinv_plan plan, int32_t n, const int64_t
 
 extern "C" int selinv_factor(selinv_plan plan, selinv_dtype dtype, const void *A, void *L, void *D,
                              void *stream) {
-    if (!plan || !plan->factor || (dtype != SELINV_F64 && dtype != SELINV_C128)) return SELINV_ERR_INVALID_ARG;
+    if (!plan || !plan->factor || (dtype != SELINV_F64 && dtype != SELINV_C128 && dtype != SELINV_C128H))
+        return SELINV_ERR_INVALID_ARG;
     if (plan->data.ns == 0) return SELINV_OK;
     if (!L || !D || (plan->factor->nnzA > 0 && !A)) return SELINV_ERR_INVALID_ARG;
     int rc = factor_tables(plan);
     if (rc) return rc;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     plan->last_stream = st;
-    return dtype == SELINV_C128 ? factor_t<zd>(plan, A, L, D, st) : factor_t<double>(plan, A, L, D, st);
+    return dtype == SELINV_F64 ? factor_t<double>(plan, A, L, D, st, 0)
+                               : factor_t<zd>(plan, A, L, D, st, dtype == SELINV_C128H);
 }

@@ -1,5 +1,6 @@
 // sm_103a kernels of the selected-inversion traversal (Alg. 1 of the paper):
 //   k_linv    L_KK^{-1} and Dinv_K = L_KK^{-T} D_K^{-1} L_KK^{-1}       (Alg. 1 loop 1)
+//             (L_KK^{-H} for a Hermitian problem, Sec. II-C; likewise Lhat^H below)
 //   k_lhat    Lhat_{C,K} = L_{C,K} L_KK^{-1}, tiled over rows of C       (Alg. 1 loop 1)
 //   k_selinv  A^{-1}_{C,K} = -A^{-1}_{C,C} Lhat_{C,K} with the gather of
 //             A^{-1}_{C,C} from the ancestors' panels fused into the GEMM,
@@ -75,14 +76,15 @@ __global__ void __launch_bounds__(kLinvThreads) k_linv(const ProbDesc *__restric
     }
     if (in_smem)
         for (int e = threadIdx.x; e < s * s; e += kLinvThreads) Li[e] = X[(e / s) * lx + e % s];
+    const bool h = P.herm != 0;
     for (int e = threadIdx.x; e < s * s; e += kLinvThreads) {
         const int i = e % s, j = e / s;
         if (i < j) continue;
         T acc = Sc<T>::zero();
         for (int k = i; k < s; k++)
-            madd(acc, mul(X[i * lx + k], in_smem ? rD[k] : recip(D[k])), X[j * lx + k]);
+            madd(acc, mul(cjif(X[i * lx + k], h), in_smem ? rD[k] : recip(D[k])), X[j * lx + k]);
         LD[(int64_t)j * ld + i] = acc;
-        LD[(int64_t)i * ld + j] = acc;
+        LD[(int64_t)i * ld + j] = cjif(acc, h);
     }
 }
 
@@ -165,7 +167,7 @@ __device__ void diag_block(const ProbDesc &P, const Item &it, int K, int s, int6
                 const int kk = e % kTK, j = e / kTK;
                 const int p = p0 + pc + kk;
                 const bool ok = (pc + kk < pm) && j < s;
-                As[kk * TN + j] = ok ? LDk[(int64_t)j * ld + s + p] : Sc<T>::zero();       // Lhat
+                As[kk * TN + j] = ok ? cjif(LDk[(int64_t)j * ld + s + p], P.herm != 0) : Sc<T>::zero();   // Lhat (conj.)
                 Bs[kk * TN + j] = ok ? Zk[(int64_t)j * ld + s + p] : Sc<T>::zero();        // Y
             }
             __syncthreads();
@@ -222,7 +224,8 @@ __device__ void selinv_item(const ProbDesc &P, const Item &it, unsigned char *sm
 #pragma unroll
         for (int j = 0; j < S::NJ; j++) acc[i][j] = Sc<T>::zero();
     if (pm > 0) {
-        LoadGather<T, TN> la{Zc, P.colbase + pos0, P.relbase + pos0, P.relidx, tile_cb, tile_rb, p0, c};
+        LoadGather<T, TN> la{Zc, P.colbase + pos0, P.relbase + pos0, P.relidx, tile_cb, tile_rb, p0, c,
+                             P.herm != 0};
         LoadColMajor<T, TN> lb{LDk + s, ld, c, s};  // Lhat(q, j) = LD[j*ld + s + q]
         tile_gemm<T, TN>(c, la, lb, acc, As, Bs);
     }

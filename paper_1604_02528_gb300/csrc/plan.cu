@@ -22,7 +22,7 @@ namespace selinv {
 static std::atomic<int64_t> g_launches{0};
 void note_launch(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
-size_t elem_size(int dtype) { return dtype == SELINV_C128 ? 16 : 8; }
+size_t elem_size(int dtype) { return dtype == SELINV_F64 ? 8 : 16; }
 
 template <typename X>
 static int upload(X **dptr, const std::vector<X> &h) {
@@ -343,7 +343,8 @@ ProbDesc make_desc(const PlanData &p, Workspace &w, int dtype, const void *L, co
     d.tile_base = p.d_tile_base;
     d.ns = p.ns;
     d.n = p.n;
-    d.dtype = dtype;
+    d.dtype = dtype == SELINV_C128H ? SELINV_C128 : dtype;   // element type of the kernels
+    d.herm = dtype == SELINV_C128H;
     d.symmetrize = p.opts.symmetrize;
     return d;
 }
@@ -836,14 +837,14 @@ extern "C" int selinv_plan_stats(selinv_plan plan, selinv_dtype dtype, double *f
     if (!plan) return SELINV_ERR_INVALID_ARG;
     const PlanData &p = plan->data;
     double F = 0, B = 0;
-    const double w = dtype == SELINV_C128 ? 16.0 : 8.0;
+    const double w = dtype == SELINV_F64 ? 8.0 : 16.0;
     for (int32_t K = 0; K < p.ns; K++) {
         const double s = p.super_ptr[K + 1] - p.super_ptr[K];
         const double c = (double)(p.rowptr[K + 1] - p.rowptr[K]) - s;
         F += 2 * c * c * s + 2 * c * s * s + c * s * s + s * s * s;
         B += w * (c * (c + 1) / 2 + 2 * (c + s) * s + s);
     }
-    if (dtype == SELINV_C128) F *= 4;
+    if (dtype != SELINV_F64) F *= 4;
     if (flops) *flops = F;
     if (bytes) *bytes = B;
     return SELINV_OK;
@@ -971,7 +972,7 @@ static int autotune(selinv_plan plan, selinv_dtype dtype, const void *L, const v
 
 extern "C" int selinv_numeric(selinv_plan plan, selinv_dtype dtype, const void *L, const void *D,
                               void *Z, void *stream) {
-    if (!plan || (dtype != SELINV_F64 && dtype != SELINV_C128)) return SELINV_ERR_INVALID_ARG;
+    if (!plan || (dtype != SELINV_F64 && dtype != SELINV_C128 && dtype != SELINV_C128H)) return SELINV_ERR_INVALID_ARG;
     PlanData &p = plan->data;
     if (p.ns == 0) return SELINV_OK;
     if (!L || !D || !Z || !aligned16(L) || !aligned16(D) || !aligned16(Z)) return SELINV_ERR_INVALID_ARG;
@@ -1014,7 +1015,7 @@ static int numeric_run(selinv_plan plan, selinv_dtype dtype, const void *L, cons
     }
     plan->last_stream = st;
     if (p.opts.debug_checks & 1) {
-        const int64_t w = dtype == SELINV_C128 ? 2 : 1;
+        const int64_t w = dtype == SELINV_F64 ? 1 : 2;
         if (launch_check_finite(L, w * p.nnz, p.d_status, st) != cudaSuccess ||
             launch_check_finite(D, w * p.n, p.d_status, st) != cudaSuccess)
             return SELINV_ERR_CUDA;
@@ -1068,7 +1069,8 @@ extern "C" int selinv_numeric_batched(int nitems, const selinv_plan *plans, cons
     selinv_plan owner = plans[0];
     if (!owner) return SELINV_ERR_INVALID_ARG;
     for (int i = 0; i < nitems; i++) {
-        if (!plans[i] || (dtypes[i] != SELINV_F64 && dtypes[i] != SELINV_C128)) return SELINV_ERR_INVALID_ARG;
+        if (!plans[i] || (dtypes[i] != SELINV_F64 && dtypes[i] != SELINV_C128 && dtypes[i] != SELINV_C128H))
+            return SELINV_ERR_INVALID_ARG;
         if (!L[i] || !D[i] || !Z[i] || !aligned16(L[i]) || !aligned16(D[i]) || !aligned16(Z[i]))
             return SELINV_ERR_INVALID_ARG;
     }
@@ -1138,7 +1140,7 @@ extern "C" int selinv_numeric_batched(int nitems, const selinv_plan *plans, cons
     owner->last_stream = st;
     if (owner->data.opts.debug_checks & 1) {
         for (int i = 0; i < nitems; i++) {
-            const int64_t w = dtypes[i] == SELINV_C128 ? 2 : 1;
+            const int64_t w = dtypes[i] == SELINV_F64 ? 1 : 2;
             if (launch_check_finite(L[i], w * plans[i]->data.nnz, owner->data.d_status, st) != cudaSuccess ||
                 launch_check_finite(D[i], w * plans[i]->data.n, owner->data.d_status, st) != cudaSuccess)
                 return SELINV_ERR_CUDA;

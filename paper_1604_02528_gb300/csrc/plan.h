@@ -14,7 +14,7 @@ namespace selinv {
 struct PlanData {
     int32_t n = 0, ns = 0;
     selinv_opts opts{};
-    bool tuned[2] = {false, false};   // autotuning done, per element type
+    bool tuned[3] = {false, false, false};   // autotuning done, per selinv_dtype
     // host arrays (kept for inspection and schedule building)
     std::vector<int32_t> super_ptr, sparent, rows, level, level_list;
     std::vector<int32_t> seg_owner, seg_start, seg_coloff, relidx, ntiles;
@@ -147,6 +147,7 @@ struct FactorDesc {
     void *L;
     void *D;
     int *status;
+    int herm;                 // complex Hermitian: A = L D L^H
 };
 
 struct FactorData {

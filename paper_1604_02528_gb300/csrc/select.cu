@@ -114,7 +114,7 @@ extern "C" int64_t selinv_plan_selected(selinv_plan plan, int64_t *pos_out) {
 }
 
 extern "C" int selinv_gather(selinv_plan plan, selinv_dtype dtype, const void *Ainv, void *out, void *stream) {
-    if (!plan || (dtype != SELINV_F64 && dtype != SELINV_C128)) return SELINV_ERR_INVALID_ARG;
+    if (!plan || (dtype != SELINV_F64 && dtype != SELINV_C128 && dtype != SELINV_C128H)) return SELINV_ERR_INVALID_ARG;
     PlanData &p = plan->data;
     const int64_t n = (int64_t)p.sel_pos.size();
     if (n == 0) return SELINV_OK;
@@ -144,7 +144,8 @@ extern "C" int selinv_pole_sum(int nitems, const selinv_dtype *dtypes, const voi
     if (npos == 0) return SELINV_OK;
     if (!pos || !out) return SELINV_ERR_INVALID_ARG;
     for (int l = 0; l < nitems; l++)
-        if (!Ainv[l] || (dtypes[l] != SELINV_F64 && dtypes[l] != SELINV_C128)) return SELINV_ERR_INVALID_ARG;
+        if (!Ainv[l] || (dtypes[l] != SELINV_F64 && dtypes[l] != SELINV_C128 && dtypes[l] != SELINV_C128H))
+            return SELINV_ERR_INVALID_ARG;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     for (int l0 = 0; l0 < nitems; l0 += kPoleChunk) {
         PoleTerms t;
@@ -155,7 +156,7 @@ extern "C" int selinv_pole_sum(int nitems, const selinv_dtype *dtypes, const voi
             t.Z[l] = Ainv[l0 + l];
             t.wr[l] = weights[2 * (l0 + l)];
             t.wi[l] = weights[2 * (l0 + l) + 1];
-            t.cplx[l] = dtypes[l0 + l] == SELINV_C128;
+            t.cplx[l] = dtypes[l0 + l] != SELINV_F64;
         }
         k_pole_sum<<<grid_for(npos), 256, 0, st>>>(t, pos, npos, static_cast<double2 *>(out));
         note_launch();

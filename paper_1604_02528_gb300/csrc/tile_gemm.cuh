@@ -90,6 +90,7 @@ template <typename T, int TN, bool kDoubleDiag = false> struct LoadGather {
     const int64_t *tile_cb;  // shared: pcb of the tile's rows
     const int64_t *tile_rb;  // shared: prb of the tile's rows
     int p0, c;
+    bool herm = false;    // Hermitian: an entry above the diagonal is the stored one's conjugate
     __device__ void operator()(int k0, T *As) const {
         for (int e = threadIdx.x; e < kTK * kTM; e += kThreads) {
             const int pl = e % kTM, kk = e / kTM;
@@ -100,6 +101,7 @@ template <typename T, int TN, bool kDoubleDiag = false> struct LoadGather {
                 if (p >= q) addr = pcb[q] + relidx[prb[q] + p];
                 else addr = tile_cb[pl] + relidx[tile_rb[pl] + q];
                 v = ldcg(Z + addr);  // L2: written by other CTAs of a persistent launch
+                if (p < q) v = cjif(v, herm);
                 if (kDoubleDiag && p == q) v = add(v, v);
             }
             As[kk * kTM + pl] = v;
@@ -143,10 +145,10 @@ __device__ void diag_finish(const ProbDesc &P, int K, int s, int64_t ld, int nti
                 xij = sub(xij, ldcg(part0 + t * ss + (int64_t)j * s + i));
                 xji = sub(xji, ldcg(part0 + t * ss + (int64_t)i * s + j));
             }
-            if (P.symmetrize) {
-                const T v = half(add(xij, xji));
+            if (P.symmetrize) {   // (X + X^T)/2, or (X + X^H)/2 (the diagonal becomes real)
+                const T v = half(add(xij, cjif(xji, P.herm != 0)));
                 xij = v;
-                xji = v;
+                xji = cjif(v, P.herm != 0);
             }
             Zk[(int64_t)j * ld + i] = xij;
             Zk[(int64_t)i * ld + j] = xji;

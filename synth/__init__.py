@@ -15,6 +15,8 @@ from .problems import (  # noqa: F401
     pole_shifts,
     batch_laplacians,
     random_sparse_spd,
+    random_sparse_hpd,
+    magnetic_laplacian_3d,
     tridiagonal,
     make_config,
     lower_pattern_weights,

@@ -21,7 +21,8 @@ import numpy as np
 __all__ = [
     "Problem", "grid_nd_order", "laplacian_2d", "laplacian_3d", "dft_sheet",
     "diffusion_3d", "pole_shifts", "batch_laplacians", "random_sparse_spd",
-    "tridiagonal", "make_config", "lower_pattern_weights",
+    "tridiagonal", "make_config", "lower_pattern_weights", "random_sparse_hpd",
+    "magnetic_laplacian_3d",
 ]
 
 FUNDAMENTAL_64 = {"kind": "fundamental", "cap": 64, "fill": 0.0}
@@ -52,6 +53,12 @@ class Problem:
         return self.values.dtype
 
     @property
+    def hermitian(self) -> bool:
+        """Complex Hermitian (A = A^H; stored lower values, the upper part is
+        their conjugate) rather than symmetric."""
+        return bool(self.meta.get("hermitian", False))
+
+    @property
     def nnz_lower(self) -> int:
         return int(self.colptr[-1])
 
@@ -63,8 +70,8 @@ class Problem:
         """Full symmetric dense matrix (small n only)."""
         a = np.zeros((self.n, self.n), dtype=self.values.dtype)
         cols = np.repeat(np.arange(self.n), np.diff(self.colptr))
+        a[cols, self.rowind] = np.conj(self.values) if self.hermitian else self.values
         a[self.rowind, cols] = self.values
-        a[cols, self.rowind] = self.values
         return a
 
     def diag_positions(self) -> np.ndarray:
@@ -448,6 +455,53 @@ def random_sparse_spd(n: int, density: float, seed: int, complex_values: bool = 
     dt = np.complex128 if complex_values else np.float64
     return Problem(f"rand_{n}_{seed}", n, colptr, rowind, vals.astype(dt), perm,
                    dict(supernodes or FUNDAMENTAL_64), {"seed": seed})
+
+
+def _hermitian_lower(n: int, perm: np.ndarray, diag: np.ndarray, ei: np.ndarray, ej: np.ndarray,
+                     ev: np.ndarray):
+    """Lower CSC of P A P^T for a Hermitian A given A[ei, ej] = ev (old
+    indices): the stored lower entry is ev where ei lands below ej after the
+    permutation, conj(ev) where it lands above."""
+    iperm = np.empty(n, dtype=np.int64)
+    iperm[perm] = np.arange(n, dtype=np.int64)
+    ev = np.where(iperm[ei] > iperm[ej], ev, np.conj(ev))
+    return _lower_csc(n, perm, diag, ei, ej, ev)
+
+
+def random_sparse_hpd(n: int, density: float, seed: int,
+                      supernodes: Optional[Dict[str, object]] = None) -> Problem:
+    """Random Hermitian positive definite matrix: off-diagonal entries with
+    real and imaginary parts N(0,1), real diagonal = row sum of |off-diagonal|
+    + 1, a random symmetric permutation."""
+    rng = np.random.default_rng(seed)
+    m = int(round(density * n * (n - 1) / 2))
+    iu = np.sort(rng.choice(n * (n - 1) // 2, size=min(m, n * (n - 1) // 2), replace=False))
+    r = np.floor((np.sqrt(8.0 * iu + 1) - 1) / 2).astype(np.int64) + 1
+    c = iu - r * (r - 1) // 2
+    ev = rng.standard_normal(r.size) + 1j * rng.standard_normal(r.size)
+    rs = np.zeros(n)
+    np.add.at(rs, r, np.abs(ev)); np.add.at(rs, c, np.abs(ev))
+    perm = rng.permutation(n)
+    colptr, rowind, vals, _ = _hermitian_lower(n, perm, rs + 1.0, r, c, ev)
+    return Problem(f"hpd_{n}_{seed}", n, colptr, rowind, vals.astype(np.complex128), perm,
+                   dict(supernodes or FUNDAMENTAL_64), {"seed": seed, "hermitian": True})
+
+
+def magnetic_laplacian_3d(nx: int, seed: int, flux: float = 0.25,
+                          supernodes: Optional[Dict[str, object]] = None) -> Problem:
+    """3D 7-point Laplacian with complex hopping -exp(i theta_e) on every edge
+    (theta_e = 2 pi flux U(-1, 1), a random magnetic-phase field), diagonal
+    6 + U(0,1): Hermitian positive definite, nested-dissection order."""
+    dims = (nx, nx, nx)
+    n = nx ** 3
+    rng = np.random.default_rng(seed)
+    diag = 6.0 + rng.uniform(0.0, 1.0, n)
+    perm = grid_nd_order(dims)
+    ei, ej = _grid_edges(dims)
+    theta = 2.0 * np.pi * flux * rng.uniform(-1.0, 1.0, ei.size)
+    colptr, rowind, vals, _ = _hermitian_lower(n, perm, diag, ei, ej, -np.exp(1j * theta))
+    return Problem(f"maglap3d_{nx}", n, colptr, rowind, vals.astype(np.complex128), perm,
+                   dict(supernodes or RELAXED_128), {"dims": dims, "seed": seed, "hermitian": True})
 
 
 # ---------------------------------------------------------------------------

@@ -226,3 +226,20 @@ def test_options_round_trip_and_validation(native):
         with pytest.raises(native.SelinvError) as e:
             native.selinv_plan_set_opts(plan, b)
         assert e.value.code == native.SELINV_ERR_INVALID_ARG, field
+
+
+def test_binding_refuses_undersized_buffers(native):
+    """A panel or diagonal buffer smaller than the plan needs is refused
+    before anything reaches the library (a complex type needs 16 bytes per
+    element: a float64 buffer of nnz elements is half the size)."""
+    import torch
+    p = synth.laplacian_3d(6, seed=1)
+    sym = oracle.symbolic_for(p)
+    plan = native.selinv_symbolic(sym.n, sym.nsuper, sym.super_ptr, sym.sparent, sym.rowptr, sym.rows)
+    real = torch.zeros(plan.nnz, dtype=torch.float64)
+    d = torch.zeros(sym.n, dtype=torch.complex128)
+    for dt in (native.SELINV_C128, native.SELINV_C128H):
+        with pytest.raises(ValueError, match="need"):
+            native.selinv_numeric(plan, dt, real, d, real)
+    with pytest.raises(ValueError, match="need"):
+        native.selinv_numeric(plan, native.SELINV_F64, real, real[:3], real)
