@@ -444,7 +444,7 @@ def main():
     rp = np.asarray(ctx.analysis["rowptr"], np.int64)
     s_ = np.diff(sp).astype(np.float64)
     c_ = np.diff(rp).astype(np.float64) - s_
-    mult = 4.0 if dt == N.SELINV_C128 else 1.0
+    mult = 1.0 if dt == N.SELINV_F64 else 4.0
     oz = (s_ >= max(16, topts.oz_min_s)) & (dt == N.SELINV_F64) & bool(topts.fast_contraction)
     peaks = measured_peaks()
     dom = int(np.argmax(kms))
@@ -461,7 +461,9 @@ def main():
             "k_linv": mult * float((s_ ** 3).sum()),
             "k_lhat_digits": 0.0,
             "k_tc_reduce": 0.0,
-            "k_diag_fin": 0.0}
+            "k_diag_fin": 0.0,
+            "k_push_diag": mult * float((2 * c_ * s_ * s_).sum()),
+            "k_push": mult * float((2 * c_ * c_ * s_).sum())}
     f_dom = f_of[name]
     achieved = f_dom / (kms[dom] * 1e-3) / 1e9 if kms[dom] > 0 else None
     traffic = ncu_traffic(name)
@@ -519,6 +521,8 @@ def main():
                                                            N.SELINV_SCHED_LEVEL, 0), 3)
         variants["persistent_dfma_ms"] = round(variant_schedule(ctx, dt, L, D, Z, stream, flush, N,
                                                                 N.SELINV_SCHED_PERSISTENT, 0), 3)
+        variants["push_dfma_ms"] = round(variant_schedule(ctx, dt, L, D, Z, stream, flush, N,
+                                                          N.SELINV_SCHED_PUSH, 0), 3)
         variants["selection"] = variant_selection(ctx, dt, L, D, Z, stream, flush, N)
         variants["batched"] = variant_batched(dev, stream, flush, N, args.batch_poles, 1.0)
         variants["adjoint"] = variant_adjoint(dev, stream, flush, N)

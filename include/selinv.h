@@ -73,9 +73,13 @@ typedef enum { SELINV_F64 = 0, SELINV_C128 = 1, SELINV_C128H = 2 } selinv_dtype;
 typedef enum {
     SELINV_SCHED_PLAIN = 0,      /* one launch chain per supernode, K = N..1            */
     SELINV_SCHED_LEVEL = 1,      /* one grouped launch per elimination-tree level        */
-    SELINV_SCHED_PERSISTENT = 2  /* one persistent launch, per-supernode completion flags;
+    SELINV_SCHED_PERSISTENT = 2, /* one persistent launch, per-supernode completion flags;
                                     its traversal runs the FP64 / complex DFMA kernel
                                     whatever fast_contraction says                     */
+    SELINV_SCHED_PUSH = 3        /* the left-looking form of Alg. 2, level by level from
+                                    the root: each finished supernode pushes its outer-
+                                    and inner-product updates into the descendants whose
+                                    C meets its columns (DFMA, every fast_contraction) */
 } selinv_schedule;
 
 typedef struct {
@@ -290,8 +294,10 @@ int selinv_pole_sum(int nitems, const selinv_dtype *dtypes, const void *const *A
  *   8 the persistent traversal          9 gather-GEMM on tcgen05
  *  10 split-k sums of the tcgen05 gather-GEMM
  *  11 diagonal block from the tensor-core sums (finisher)
+ *  12 push schedule: diagonal block from the pushed A^{-1}_{C,K}
+ *  13 push schedule: outer- and inner-product updates of the descendants
  * For measurement only. */
-#define SELINV_PROFILE_KINDS 12
+#define SELINV_PROFILE_KINDS 14
 int selinv_numeric_profile(selinv_plan plan, selinv_dtype dtype, const void *L_dev,
                            const void *D_dev, void *Ainv_dev, void *cuda_stream, double *kernel_ms,
                            int64_t *kernel_launches);

@@ -86,6 +86,8 @@ struct ProbDesc {
     const int64_t *linv_off;    // [ns+1] offsets of L_KK^{-1} blocks (s*s each)
     const int64_t *part_off;    // [ns] offset of K's split partials inside its level
     const int32_t *sparent;     // [ns]
+    const int64_t *seg_ptr;     // [ns+1] owner segments of each C (push schedule)
+    const int32_t *seg_start;   // first C position of each segment
     // numeric buffers
     const void *L;              // panels
     const void *D;              // [n]

@@ -261,6 +261,118 @@ __global__ void __launch_bounds__(kThreads) k_selinv(const ProbDesc *__restrict_
 }
 
 // ---------------------------------------------------------------------------
+// Push schedule: the left-looking form of Alg. 2.  A^{-1} starts at zero and
+// the levels run root first.  When K's level comes, every ancestor of K has
+// pushed its updates into K's rows C, so A^{-1}_{C,K} is complete, and
+// k_push_diag forms the diagonal block from it (the Ptile sums of k_selinv).
+// k_push then sends K's contributions to every descendant I' whose C' meets
+// K's columns, in one owner segment [q0, q1) of C': with the entries (p, q) of
+// A^{-1}_{C',C'} whose smaller index lies in the segment (all of them stored
+// in K's panel),
+//   inner product: rows p in [q0, q1), q in [q0, c')   (A^{-1}_{K,I'} of Alg. 2)
+//   outer product: rows p in [q1, c'), q in [q0, q1)   (A^{-1}_{I,I'}, I in C(K))
+//   A^{-1}(C'[p], I') -= sum_q A^{-1}(C'[p], C'[q]) Lhat(C'[q], I').
+// Over the owners of C' these regions cover every (p, q) once.  Two
+// supernodes of one level are never both ancestors of one I', so the writes
+// of one launch never meet, and their sources (panels of the level being
+// pushed) are not written by it.
+// ---------------------------------------------------------------------------
+template <typename T, int TN>
+__global__ void __launch_bounds__(kThreads) k_push_diag(const ProbDesc *__restrict__ descs,
+                                                        const Item *__restrict__ items, int nitems) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int w = blockIdx.x;
+    if (w >= nitems) return;
+    const Item it = items[w];
+    const ProbDesc &P = descs[it.prob];
+    const int K = it.K;
+    const int s = P.super_ptr[K + 1] - P.super_ptr[K];
+    const int64_t ld = P.rowptr[K + 1] - P.rowptr[K];
+    const int c = (int)(ld - s);
+    const int p0 = it.tile * kTM;
+    const int pm = c - p0 < kTM ? c - p0 : kTM;
+    T *As = reinterpret_cast<T *>(smem_raw);
+    T *Bs = As + smem_a_elems<T, TN>();
+    diag_block<T, TN>(P, it, K, s, ld, c, p0, pm, static_cast<const T *>(P.LD) + P.panel_off[K],
+                      static_cast<T *>(P.Z) + P.panel_off[K], As, Bs);
+}
+
+// A(pl, k) = A^{-1}(C[p0 + pl], C[q0 + k]); min of the two positions in the
+// segment, so the entry sits in the segment owner's panel (conjugated above
+// the diagonal for a Hermitian problem)
+template <typename T> struct LoadPush {
+    const T *Z;
+    const int64_t *pcb, *prb;   // per C position of I': column address / relidx base
+    const int32_t *relidx;
+    int p0, pm, q0, kd;
+    bool herm;
+    __device__ void operator()(int k0, T *As) const {
+        for (int e = threadIdx.x; e < kTK * kTM; e += kThreads) {
+            const int pl = e % kTM, kk = e / kTM;
+            T v = Sc<T>::zero();
+            if (pl < pm && k0 + kk < kd) {
+                const int p = p0 + pl, q = q0 + k0 + kk;
+                const int m = p < q ? p : q, M = p < q ? q : p;
+                v = Z[pcb[m] + relidx[prb[m] + M]];
+                if (p < q) v = cjif(v, herm);
+            }
+            As[kk * kTM + pl] = v;
+        }
+    }
+};
+
+// item: K = I', tile = row tile of the region, ntiles = (segment of I' << 1) | inner
+template <typename T, int TN>
+__global__ void __launch_bounds__(kThreads) k_push(const ProbDesc *__restrict__ descs,
+                                                   const Item *__restrict__ items, int nitems) {
+    using S = Shape<TN>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *As = reinterpret_cast<T *>(smem_raw);
+    T *Bs = As + smem_a_elems<T, TN>();
+    const int w = blockIdx.x;
+    if (w >= nitems) return;
+    const Item it = items[w];
+    const ProbDesc &P = descs[it.prob];
+    const int I = it.K;
+    const int s = P.super_ptr[I + 1] - P.super_ptr[I];
+    const int64_t ld = P.rowptr[I + 1] - P.rowptr[I];
+    const int c = (int)(ld - s);
+    const int64_t e = P.seg_ptr[I] + (it.ntiles >> 1);
+    const bool inner = (it.ntiles & 1) != 0;
+    const int q0 = P.seg_start[e];
+    const int q1 = e + 1 < P.seg_ptr[I + 1] ? P.seg_start[e + 1] : c;
+    const int rb = inner ? q0 : q1, re = inner ? q1 : c;
+    const int p0 = rb + it.tile * kTM;
+    const int pm = re - p0 < kTM ? re - p0 : kTM;
+    if (pm <= 0) return;
+    const int kd = (inner ? c : q1) - q0;
+    const int64_t pos0 = P.rowptr[I] + s;
+    const int64_t off = P.panel_off[I];
+    T *Z = static_cast<T *>(P.Z);
+    const T *LDi = static_cast<const T *>(P.LD) + off;
+    T acc[S::MI][S::NJ];
+#pragma unroll
+    for (int i = 0; i < S::MI; i++)
+#pragma unroll
+        for (int j = 0; j < S::NJ; j++) acc[i][j] = Sc<T>::zero();
+    LoadPush<T> la{Z, P.colbase + pos0, P.relbase + pos0, P.relidx, p0, pm, q0, kd, P.herm != 0};
+    LoadColMajor<T, TN> lb{LDi + s + q0, ld, kd, s};   // Lhat(q0 + k, j)
+    tile_gemm<T, TN>(kd, la, lb, acc, As, Bs);
+    const int tx = threadIdx.x % S::TX, ty = threadIdx.x / S::TX;
+    T *Zi = Z + off;
+#pragma unroll
+    for (int i = 0; i < S::MI; i++)
+#pragma unroll
+        for (int j = 0; j < S::NJ; j++) {
+            const int pl = ty + S::TY * i, col = tx + S::TX * j;
+            if (pl < pm && col < s) {
+                T *dst = Zi + (int64_t)col * ld + s + p0 + pl;
+                *dst = sub(*dst, acc[i][j]);
+            }
+        }
+}
+
+// ---------------------------------------------------------------------------
 // k_selinv_persist: the whole traversal in one launch.  Work items are listed
 // root level first; each CTA claims the next item from a global ticket and,
 // before working on supernode K, waits for the completion flag of K's parent
@@ -352,7 +464,9 @@ static cudaError_t launch_items_t(int kernel, const ProbDesc *d, const Item *ite
     if (n <= 0) return cudaSuccess;
     constexpr size_t smem = smem_bytes<T, TN>();
     if (kernel == 0) k_lhat<T, TN><<<n, kThreads, smem, st>>>(d, items, n);
-    else k_selinv<T, TN><<<n, kThreads, smem, st>>>(d, items, n);
+    else if (kernel == 1) k_selinv<T, TN><<<n, kThreads, smem, st>>>(d, items, n);
+    else if (kernel == 2) k_push_diag<T, TN><<<n, kThreads, smem, st>>>(d, items, n);
+    else k_push<T, TN><<<n, kThreads, smem, st>>>(d, items, n);
     return cudaGetLastError();
 }
 
@@ -362,6 +476,9 @@ static cudaError_t configure_t() {
     cudaError_t e = cudaFuncSetAttribute(k_lhat<T, TN>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_selinv<T, TN>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_push_diag<T, TN>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_push<T, TN>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     return e;
 }
 
@@ -432,6 +549,13 @@ cudaError_t launch_selinv(int dtype, int bucket, const ProbDesc *d, const Item *
                           cudaStream_t st) {
     return dtype == SELINV_C128 ? launch_items_dt<zd>(1, bucket, d, items, n, st)
                                 : launch_items_dt<double>(1, bucket, d, items, n, st);
+}
+
+// push schedule: kind 0 = diagonal blocks, 1 = the pushes (bucket of the target's width)
+cudaError_t launch_push(int dtype, int kind, int bucket, const ProbDesc *d, const Item *items, int n,
+                        cudaStream_t st) {
+    return dtype == SELINV_C128 ? launch_items_dt<zd>(2 + kind, bucket, d, items, n, st)
+                                : launch_items_dt<double>(2 + kind, bucket, d, items, n, st);
 }
 
 

@@ -286,6 +286,8 @@ int ensure_device(PlanData &p) {
     if ((rc = upload(&p.d_lhsu_off, p.lhsu_off))) return rc;
     if ((rc = upload(&p.d_tile_base, p.tile_base))) return rc;
     if ((rc = upload(&p.d_linvd_off, p.linvd_off))) return rc;
+    if ((rc = upload(&p.d_seg_ptr, p.seg_ptr))) return rc;
+    if ((rc = upload(&p.d_seg_start, p.seg_start))) return rc;
     int *st = nullptr;
     if (cudaMalloc((void **)&st, sizeof(int)) != cudaSuccess) return SELINV_ERR_OOM;
     if (cudaMemset(st, 0, sizeof(int)) != cudaSuccess) return SELINV_ERR_CUDA;
@@ -297,7 +299,9 @@ void PlanData::release_device() {
     dfree(d_super_ptr); dfree(d_sparent); dfree(d_rowptr); dfree(d_rows); dfree(d_panel_off);
     dfree(d_colbase); dfree(d_relbase); dfree(d_relidx); dfree(d_linv_off); dfree(d_part_off); dfree(d_part_off_all);
     dfree(d_lhs_off); dfree(d_lhsu_off); dfree(d_tile_base); dfree(d_linvd_off); dfree(d_status); dfree(d_sel_pos);
-    d_lhs_off = d_lhsu_off = d_tile_base = d_linvd_off = d_sel_pos = nullptr;
+    dfree(d_seg_ptr); dfree(d_seg_start);
+    d_lhs_off = d_lhsu_off = d_tile_base = d_linvd_off = d_sel_pos = d_seg_ptr = nullptr;
+    d_seg_start = nullptr;
     d_super_ptr = d_sparent = d_rows = d_relidx = nullptr;
     d_rowptr = d_panel_off = d_colbase = d_relbase = d_linv_off = d_part_off = d_part_off_all = nullptr;
     d_status = nullptr;
@@ -317,6 +321,8 @@ ProbDesc make_desc(const PlanData &p, Workspace &w, int dtype, const void *L, co
     d.linv_off = p.d_linv_off;
     d.part_off = persistent ? p.d_part_off_all : p.d_part_off;
     d.sparent = p.d_sparent;
+    d.seg_ptr = p.d_seg_ptr;
+    d.seg_start = p.d_seg_start;
     d.L = L;
     d.D = D;
     d.Z = Z;
@@ -444,7 +450,7 @@ int build_schedule(Schedule &S, const std::vector<const PlanData *> &plans,
             for (int32_t K = 0; K < p.ns; K++) {
                 const int s = p.super_ptr[K + 1] - p.super_ptr[K];
                 const int64_t c = p.rowptr[K + 1] - p.rowptr[K] - s;
-                if (c == 0 || !act(i, K) || mode == SELINV_SCHED_PERSISTENT ||
+                if (c == 0 || !act(i, K) || mode == SELINV_SCHED_PERSISTENT || mode == SELINV_SCHED_PUSH ||
                     !oz_eligible(descs[i].dtype, s, p.opts))
                     continue;
                 for (int jb = 0; jb < (s + 7) / 8; jb++) S.h_work.push_back(make_int2(i, (K << 8) | jb));
@@ -559,6 +565,64 @@ int build_schedule(Schedule &S, const std::vector<const PlanData *> &plans,
             }
             if (cnt) S.launches.push_back({KL_PERSIST, dt, 0, off, cnt, 0});
         }
+    } else if (mode == SELINV_SCHED_PUSH) {
+        // Alg. 2, left-looking: per level (root first) the diagonal blocks of its
+        // supernodes, then their pushes into the descendants, grouped by the
+        // width class of the target
+        int nlev = 0;
+        for (int i = 0; i < np; i++) nlev = std::max(nlev, plans[i]->nlevels);
+        // (I', segment) pairs by the level of the segment's owner
+        std::vector<std::vector<std::vector<int2>>> by_level(np);
+        for (int i = 0; i < np; i++) {
+            const PlanData &p = *plans[i];
+            by_level[i].assign(std::max(p.nlevels, 1), {});
+            for (int32_t I = 0; I < p.ns; I++) {
+                if (!act(i, I)) continue;
+                for (int64_t e = p.seg_ptr[I]; e < p.seg_ptr[I + 1]; e++)
+                    by_level[i][p.level[p.seg_owner[e]]].push_back(make_int2(I, (int)(e - p.seg_ptr[I])));
+            }
+        }
+        for (int l = 0; l < nlev; l++) {
+            for (int dt = 0; dt < 2; dt++)
+                for (int b = kNumBuckets - 1; b >= 0; b--) {
+                    const int64_t off = (int64_t)S.h_items.size();
+                    for (int i = 0; i < np; i++) {
+                        if (descs[i].dtype != dt) continue;
+                        const PlanData &p = *plans[i];
+                        if (l >= p.nlevels) continue;
+                        for (int64_t e = p.level_ptr[l]; e < p.level_ptr[l + 1]; e++) {
+                            const int32_t K = p.level_list[e];
+                            if (act(i, K) && bucket_of(p.super_ptr[K + 1] - p.super_ptr[K]) == b) push_items(i, K);
+                        }
+                    }
+                    const int cnt = (int)(S.h_items.size() - off);
+                    if (cnt) S.launches.push_back({KL_PUSH_DIAG, dt, b, off, cnt, l});
+                }
+            for (int dt = 0; dt < 2; dt++)
+                for (int b = kNumBuckets - 1; b >= 0; b--) {
+                    const int64_t off = (int64_t)S.h_items.size();
+                    for (int i = 0; i < np; i++) {
+                        if (descs[i].dtype != dt) continue;
+                        const PlanData &p = *plans[i];
+                        if (l >= p.nlevels) continue;
+                        for (const int2 &pr : by_level[i][l]) {
+                            const int32_t I = pr.x;
+                            const int s = p.super_ptr[I + 1] - p.super_ptr[I];
+                            if (bucket_of(s) != b) continue;
+                            const int64_t c = p.rowptr[I + 1] - p.rowptr[I] - s;
+                            const int64_t e = p.seg_ptr[I] + pr.y;
+                            const int64_t q0 = p.seg_start[e];
+                            const int64_t q1 = e + 1 < p.seg_ptr[I + 1] ? p.seg_start[e + 1] : c;
+                            for (int64_t t = 0; t < (q1 - q0 + kTM - 1) / kTM; t++)   // inner product rows
+                                S.h_items.push_back({i, I, (int)t, (pr.y << 1) | 1});
+                            for (int64_t t = 0; t < (c - q1 + kTM - 1) / kTM; t++)    // outer product rows
+                                S.h_items.push_back({i, I, (int)t, pr.y << 1});
+                        }
+                    }
+                    const int cnt = (int)(S.h_items.size() - off);
+                    if (cnt) S.launches.push_back({KL_PUSH, dt, b, off, cnt, l});
+                }
+        }
     } else if (mode == SELINV_SCHED_PLAIN) {
         // one launch per supernode, K = N..1, problem after problem
         for (int i = 0; i < np; i++) {
@@ -670,6 +734,12 @@ int build_schedule(Schedule &S, const std::vector<const PlanData *> &plans,
             S.pre_bytes.push_back(sizeof(int) * (size_t)std::max(plans[i]->n, 1));
         }
     }
+    // the push schedule accumulates into A^{-1}: zero at the start of every call
+    if (mode == SELINV_SCHED_PUSH)
+        for (int i = 0; i < np; i++) {
+            S.pre_ptr.push_back(descs[i].Z);
+            S.pre_bytes.push_back(elem_size(descs[i].dtype) * (size_t)std::max<int64_t>(plans[i]->nnz, 1));
+        }
     // one partial (hi, lo) tile of 128 x 64 per CTA of the widest tcgen05 launch
     int64_t tc_ctas = 0;
     for (const Launch &L : S.launches)
@@ -697,6 +767,8 @@ cudaError_t launch_with(const Schedule &S, const Launch &L, const ProbDesc *d, c
     case KL_TC_REDUCE:
         return launch_tc_reduce(L.bucket, d, S.d_items, S.d_red + L.off, L.count, S.tcslab, st);
     case KL_DIAG_FIN: return launch_diag_fin(d, S.d_items + L.off, L.count, st);
+    case KL_PUSH_DIAG: return launch_push(L.dtype, 0, L.bucket, d, S.d_items + L.off, L.count, st);
+    case KL_PUSH: return launch_push(L.dtype, 1, L.bucket, d, S.d_items + L.off, L.count, st);
     case KL_PERSIST: {
         for (size_t r = 0; r < S.reset_ptr.size(); r++) {
             cudaError_t e = cudaMemsetAsync(S.reset_ptr[r], 0, S.reset_bytes[r], st);
@@ -763,7 +835,7 @@ using namespace selinv;
 // C ABI
 // ---------------------------------------------------------------------------
 static bool opts_valid(const selinv_opts *o) {
-    return o->schedule >= 0 && o->schedule <= 2 && o->fast_contraction >= 0 && o->fast_contraction <= 2 &&
+    return o->schedule >= 0 && o->schedule <= 3 && o->fast_contraction >= 0 && o->fast_contraction <= 2 &&
            o->split_target >= 1 && o->split_target <= 8 && o->split_min_steps >= 8 &&
            o->split_min_steps <= 64 && o->split_min_steps % 8 == 0 && o->oz_min_s >= 16 && o->oz_min_s <= 128 &&
            o->spin_limit > 0;

@@ -38,6 +38,8 @@ struct PlanData {
     int64_t *d_rowptr = nullptr, *d_panel_off = nullptr, *d_colbase = nullptr, *d_relbase = nullptr;
     int64_t *d_linv_off = nullptr, *d_part_off = nullptr, *d_part_off_all = nullptr, *d_lhs_off = nullptr, *d_lhsu_off = nullptr, *d_tile_base = nullptr;
     int64_t *d_linvd_off = nullptr;
+    int64_t *d_seg_ptr = nullptr;      // owner segments (push schedule)
+    int32_t *d_seg_start = nullptr;
     int *d_status = nullptr;
     void release_device();
 };
@@ -68,7 +70,8 @@ struct Workspace {
 
 // launch kinds
 enum { KL_LINV = 0, KL_LHAT = 1, KL_SELINV = 2, KL_DIGITS = 3, KL_SELINV_OZ = 4, KL_DIAG = 5, KL_LINV_DIGITS = 6,
-       KL_LHAT_OZ = 7, KL_PERSIST = 8, KL_SELINV_TC = 9, KL_TC_REDUCE = 10, KL_DIAG_FIN = 11, KL_NKINDS = 12 };
+       KL_LHAT_OZ = 7, KL_PERSIST = 8, KL_SELINV_TC = 9, KL_TC_REDUCE = 10, KL_DIAG_FIN = 11,
+       KL_PUSH_DIAG = 12, KL_PUSH = 13, KL_NKINDS = 14 };
 
 // tensor-core (FP64-exact) contraction applies to real problems with s >= kOzMinS;
 // fast_contraction 1 runs the gather-GEMM on tcgen05, 2 on mma.sync
