@@ -243,6 +243,26 @@ int selinv_factor_adjoint(selinv_plan plan, selinv_dtype dtype, const void *L_de
                           void *A_bar_vals_dev, void *cuda_stream);
 
 /* ---------------------------------------------------------------------------
+ * selinv_numeric_lu: Alg. 1 for nonsymmetric values on the symmetric pattern
+ * (A = L U without pivoting, U kept separately, Sec. II-B; the factors come
+ * from the caller, as the paper's come from an external sparse LU):
+ *   Lhat_{C,K} = L_{C,K} L_KK^{-1},  Uhat_{K,C} = U_KK^{-1} U_{K,C},
+ *   A^{-1}_{C,K} = -A^{-1}_{C,C} Lhat_{C,K},  A^{-1}_{K,C} = -Uhat_{K,C} A^{-1}_{C,C},
+ *   A^{-1}_{K,K} = U_KK^{-1} L_KK^{-1} - Uhat_{K,C} A^{-1}_{C,K}  (no symmetrization).
+ *   L_dev   panels of L (unit lower diagonal blocks), as for selinv_numeric
+ *   Ut_dev  U transposed in the same panel layout: the diagonal block holds
+ *           U_KK^T (lower triangle with U's diagonal; the strict upper part is
+ *           never read), rows s.. hold U_{K,C}^T
+ *   Zl_dev  out: full diagonal blocks A^{-1}_KK and A^{-1}_{C,K} below them
+ *   Zu_dev  out: (A^{-1}_KK)^T and A^{-1}_{K,C}^T below them
+ * SELINV_F64 or SELINV_C128 (plain transposes), FP64 / complex FMA kernels,
+ * level schedule (the plain one when the plan's options ask for it).  A zero
+ * U_kk latches SELINV_ERR_ZERO_PIVOT.
+ * ------------------------------------------------------------------------- */
+int selinv_numeric_lu(selinv_plan plan, selinv_dtype dtype, const void *L_dev, const void *Ut_dev,
+                      void *Zl_dev, void *Zu_dev, void *cuda_stream);
+
+/* ---------------------------------------------------------------------------
  * Subset selection (Sec. I: the selected elements may be all or only a
  * subset of the nonzero entries of the factors -- e.g. the diagonal of
  * A^{-1}, or the entries on A's own pattern).  Alg. 1 computes supernode K

@@ -12,6 +12,8 @@ the paper's definitions and algorithms with plain loops:
 * ``selinv``    -- Alg. 1 (pull), diagonal blocks symmetrized (Sec. II-C);
                    ``hermitian=True``: conjugate transposes, A = A^H
 * ``selinv_push`` -- Alg. 2 (left-looking push), a different summation order
+* ``lu``, ``selinv_lu`` -- nonsymmetric values: LU without pivoting (U kept
+                   transposed in the panel layout) and Alg. 1 in its LU form
 * ``selinv_adjoint``, ``ldlt_adjoint`` -- reverse mode of the two numeric steps
 * ``panel_position``, ``needed_supernodes`` -- subset selection (Sec. I: all
   or a subset of the entries on the factors' pattern): where an entry of
@@ -77,6 +79,14 @@ def _load():
         lib.orc_selinv_h.argtypes = [ct.c_int32, P, P, P, P, P, P, P, ct.c_int]
         lib.orc_selinv_top_h.restype = ct.c_int
         lib.orc_selinv_top_h.argtypes = [ct.c_int32, P, P, P, P, P, P, P, ct.c_int, ct.c_int32]
+        # nonsymmetric values: LU and its Alg. 1
+        for sfx in ("_d", "_z"):
+            f = getattr(lib, "orc_lu" + sfx)
+            f.restype = ct.c_int
+            f.argtypes = [ct.c_int32, P, P, P, P, ct.c_int32, P, P, P, P, P, P]
+            f = getattr(lib, "orc_selinv_lu" + sfx)
+            f.restype = ct.c_int
+            f.argtypes = [ct.c_int32, P, P, P, P, P, P, P, P]
         _lib = lib
     return _lib
 
@@ -381,4 +391,48 @@ def pole_sum(Zs, weights, pos) -> np.ndarray:
     out = np.zeros(len(pos), dtype=np.complex128)
     for Z, w in zip(Zs, weights):
         out = out + complex(w) * np.asarray(Z)[np.asarray(pos)]
+    return out
+
+
+# ---------------------------------------------------------------------------
+# nonsymmetric values (LU form)
+# ---------------------------------------------------------------------------
+
+def lu(problem, sym: Sym) -> Tuple[np.ndarray, np.ndarray]:
+    """L (panels, unit diagonal block) and Ut (U transposed, same layout: the
+    diagonal block holds U_KK^T, rows s.. hold U(K,C)^T) of P A P^T = L U for a
+    problem with nonsymmetric values (``meta["upper"]``: the values a_ji on
+    the positions of the lower CSC)."""
+    lib = _load()
+    dt = np.complex128 if problem.values.dtype.kind == "c" else np.float64
+    lo = np.ascontiguousarray(problem.values, dtype=dt)
+    up = np.ascontiguousarray(problem.meta["upper"], dtype=dt)
+    colptr = np.ascontiguousarray(problem.colptr, dtype=np.int64)
+    rowind = np.ascontiguousarray(problem.rowind, dtype=np.int32)
+    L = np.zeros(sym.nnz_panels, dtype=dt)
+    Ut = np.zeros(sym.nnz_panels, dtype=dt)
+    rc = getattr(lib, "orc_lu" + _sfx(dt))(int(problem.n), _p(colptr), _p(rowind), _p(lo), _p(up),
+                                          *_sym_args(sym), _p(L), _p(Ut))
+    _check(rc, "lu")
+    return L, Ut
+
+
+def selinv_lu(sym: Sym, L: np.ndarray, Ut: np.ndarray) -> Tuple[np.ndarray, np.ndarray]:
+    """Alg. 1 in its LU form: (Zl, Zu) -- Zl holds the full diagonal blocks of
+    A^{-1} and A^{-1}_{C,K}, Zu their transposes and A^{-1}(K,C)^T."""
+    lib = _load()
+    L = np.ascontiguousarray(L)
+    Ut = np.ascontiguousarray(Ut, dtype=L.dtype)
+    Zl, Zu = np.zeros_like(L), np.zeros_like(L)
+    rc = getattr(lib, "orc_selinv_lu" + _sfx(L.dtype))(*_sym_args(sym), _p(L), _p(Ut), _p(Zl), _p(Zu))
+    _check(rc, "selinv_lu")
+    return Zl, Zu
+
+
+def panels_to_dense_lu(sym: Sym, Zl: np.ndarray, Zu: np.ndarray) -> np.ndarray:
+    """Dense matrix from the LU-form panels: (i, j), i >= j, from Zl; (j, i) from Zu."""
+    r, c, low = panel_entries(sym)
+    out = np.zeros((sym.n, sym.n), dtype=Zl.dtype)
+    out[c[low], r[low]] = Zu[low]
+    out[r[low], c[low]] = Zl[low]
     return out

@@ -85,6 +85,7 @@ def _load() -> ct.CDLL:
         "selinv_launch_count": (I64, []),
         "selinv_dinv_noalloc": (I, [I32, P, I64, P, P, I64, P]),
         "selinv_plan_select": (I, [P, I64, P, P, P]),
+        "selinv_numeric_lu": (I, [P, I, P, P, P, P, P]),
         "selinv_plan_selected": (I64, [P, P]),
         "selinv_gather": (I, [P, I, P, P, P]),
         "selinv_pole_sum": (I, [I, P, P, P, I64, P, P, P]),
@@ -106,7 +107,8 @@ REQUIRED_SYMBOLS = ("selinv_default_opts", "selinv_analyse", "selinv_analysis_ge
                     "selinv_numeric_batched", "selinv_numeric_profile", "selinv_plan_set_matrix", "selinv_factor",
                     "selinv_adjoint", "selinv_factor_adjoint", "selinv_status",
                     "selinv_error_string", "selinv_launch_count", "selinv_dinv_noalloc",
-                    "selinv_plan_select", "selinv_plan_selected", "selinv_gather", "selinv_pole_sum")
+                    "selinv_plan_select", "selinv_plan_selected", "selinv_gather", "selinv_pole_sum",
+                    "selinv_numeric_lu")
 
 
 def error_string(code: int) -> str:
@@ -280,6 +282,14 @@ def selinv_numeric(plan: Plan, dtype: int, L, D, Ainv, stream=None):
     _need_panels(plan, dtype, [("L", L), ("Ainv", Ainv)], [("D", D)])
     _check(LIB.selinv_numeric(plan.handle, int(dtype), _dptr(L), _dptr(D), _dptr(Ainv),
                               _stream(stream)), "selinv_numeric")
+
+
+def selinv_numeric_lu(plan: Plan, dtype: int, L, Ut, Zl, Zu, stream=None):
+    """The LU form: L and U^T panels in, the lower and the transposed upper
+    panels of A^{-1} out."""
+    _need_panels(plan, dtype, [("L", L), ("Ut", Ut), ("Zl", Zl), ("Zu", Zu)])
+    _check(LIB.selinv_numeric_lu(plan.handle, int(dtype), _dptr(L), _dptr(Ut), _dptr(Zl), _dptr(Zu),
+                                 _stream(stream)), "selinv_numeric_lu")
 
 
 def selinv_numeric_profile(plan: Plan, dtype: int, L, D, Ainv, stream=None):

@@ -119,6 +119,13 @@ struct ProbDesc {
     int32_t dtype;              // element type: SELINV_F64 or SELINV_C128
     int32_t symmetrize;
     int32_t herm;               // complex Hermitian (SELINV_C128H): conjugate transposes
+    // nonsymmetric values (LU form): U transposed in the panel layout, the
+    // upper part of A^{-1} transposed, Uhat^T, and (U_KK^T)^{-1} blocks
+    int32_t lu;
+    const void *Ut;
+    void *Zu;
+    void *LDu;
+    void *Vt;
 };
 
 // One unit of work of a tiled kernel: rows [tile*TM, tile*TM+TM) of C(K).

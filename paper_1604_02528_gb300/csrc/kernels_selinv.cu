@@ -36,6 +36,43 @@ __device__ inline void latch_status(int *status, int code) {
 constexpr int kLinvThreads = 256;
 constexpr size_t kLinvSmemMax = (128 * 129 + 128) * sizeof(double);
 
+// LU form of the normalisation (Alg. 1 first loop with U kept separately):
+// X = L_KK^{-1} and V = (U_KK^T)^{-1} (U_KK^T is the lower diagonal block of
+// Ut, non-unit diagonal) by row-oriented forward substitution, row k of V
+// scaled by 1 / U_kk when it is final; Dinv = U_KK^{-1} L_KK^{-1}, entry
+// (i, j) = sum_{k >= max(i, j)} V(k, i) X(k, j), the full (nonsymmetric) block.
+template <typename T>
+__device__ void linv_lu(const ProbDesc &P, int K, int s, int64_t ld, const T *L, T *X, T *LD) {
+    const T *U = static_cast<const T *>(P.Ut) + P.panel_off[K];   // U_KK^T(i, k) = U[k*ld + i]
+    T *V = static_cast<T *>(P.Vt) + P.linv_off[K];
+    for (int e = threadIdx.x; e < s * s; e += kLinvThreads) {
+        const int i = e % s, j = e / s;
+        X[e] = i == j ? Sc<T>::one() : Sc<T>::zero();
+        V[e] = i == j ? Sc<T>::one() : Sc<T>::zero();
+    }
+    for (int k = 0; k < s; k++) {
+        __syncthreads();
+        const T ukk = U[(int64_t)k * ld + k];
+        if (threadIdx.x == 0 && (is_zero(ukk) || !finite_val(ukk))) latch_status(P.status, SELINV_ERR_ZERO_PIVOT);
+        const T r = recip(ukk);
+        for (int j = threadIdx.x; j <= k; j += kLinvThreads) V[j * s + k] = mul(V[j * s + k], r);
+        __syncthreads();
+        const int m = s - 1 - k;
+        for (int e = threadIdx.x; e < m * (k + 1); e += kLinvThreads) {
+            const int i = k + 1 + e % m, j = e / m;
+            msub(X[j * s + i], L[(int64_t)k * ld + i], X[j * s + k]);
+            msub(V[j * s + i], U[(int64_t)k * ld + i], V[j * s + k]);
+        }
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < s * s; e += kLinvThreads) {
+        const int i = e % s, j = e / s;
+        T acc = Sc<T>::zero();
+        for (int k = i > j ? i : j; k < s; k++) madd(acc, V[i * s + k], X[j * s + k]);
+        LD[(int64_t)j * ld + i] = acc;
+    }
+}
+
 template <typename T>
 __global__ void __launch_bounds__(kLinvThreads) k_linv(const ProbDesc *__restrict__ descs,
                                                        const int2 *__restrict__ work, int nwork,
@@ -52,6 +89,10 @@ __global__ void __launch_bounds__(kLinvThreads) k_linv(const ProbDesc *__restric
     const T *D = static_cast<const T *>(P.D) + fc;
     T *Li = static_cast<T *>(P.Linv) + P.linv_off[K];
     T *LD = static_cast<T *>(P.LD) + P.panel_off[K];
+    if (P.lu) {   // nonsymmetric values: L_KK^{-1}, (U_KK^T)^{-1} and U_KK^{-1} L_KK^{-1} in global memory
+        linv_lu<T>(P, K, s, ld, L, Li, LD);
+        return;
+    }
     const int sp = s | 1;
     const bool in_smem = sizeof(T) * ((size_t)s * sp + s) <= smem_cap;
     const int lx = in_smem ? sp : s;                              // X(i, j) = X[j*lx + i]
@@ -125,25 +166,28 @@ __global__ void __launch_bounds__(kThreads) k_lhat(const ProbDesc *__restrict__ 
     const int64_t ld = P.rowptr[K + 1] - P.rowptr[K];
     const int c = (int)(ld - s);
     const int p0 = it.tile * kTM;
-    const T *L = static_cast<const T *>(P.L) + P.panel_off[K];
-    const T *Li = static_cast<const T *>(P.Linv) + P.linv_off[K];
-    T *LD = static_cast<T *>(P.LD) + P.panel_off[K];
-    T acc[S::MI][S::NJ];
+    // LU form: a second pass forms Uhat^T = U(K,C)^T (U_KK^T)^{-1}
+    for (int side = 0; side < (P.lu ? 2 : 1); side++) {
+        const T *L = static_cast<const T *>(side ? P.Ut : P.L) + P.panel_off[K];
+        const T *Li = static_cast<const T *>(side ? P.Vt : P.Linv) + P.linv_off[K];
+        T *LD = static_cast<T *>(side ? P.LDu : P.LD) + P.panel_off[K];
+        T acc[S::MI][S::NJ];
 #pragma unroll
-    for (int i = 0; i < S::MI; i++)
+        for (int i = 0; i < S::MI; i++)
 #pragma unroll
-        for (int j = 0; j < S::NJ; j++) acc[i][j] = Sc<T>::zero();
-    LoadPanelRows<T, TN> la{L, ld, s, p0, c};
-    LoadColMajor<T, TN> lb{Li, (int64_t)s, s, s};
-    tile_gemm<T, TN>(s, la, lb, acc, As, Bs);
-    const int tx = threadIdx.x % S::TX, ty = threadIdx.x / S::TX;
+            for (int j = 0; j < S::NJ; j++) acc[i][j] = Sc<T>::zero();
+        LoadPanelRows<T, TN> la{L, ld, s, p0, c};
+        LoadColMajor<T, TN> lb{Li, (int64_t)s, s, s};
+        tile_gemm<T, TN>(s, la, lb, acc, As, Bs);
+        const int tx = threadIdx.x % S::TX, ty = threadIdx.x / S::TX;
 #pragma unroll
-    for (int i = 0; i < S::MI; i++)
+        for (int i = 0; i < S::MI; i++)
 #pragma unroll
-        for (int j = 0; j < S::NJ; j++) {
-            const int p = p0 + ty + S::TY * i, col = tx + S::TX * j;
-            if (p < c && col < s) LD[(int64_t)col * ld + s + p] = acc[i][j];
-        }
+            for (int j = 0; j < S::NJ; j++) {
+                const int p = p0 + ty + S::TY * i, col = tx + S::TX * j;
+                if (p < c && col < s) LD[(int64_t)col * ld + s + p] = acc[i][j];
+            }
+    }
 }
 
 // Split contribution of one row tile to the diagonal block,
@@ -155,7 +199,9 @@ __device__ void diag_block(const ProbDesc &P, const Item &it, int K, int s, int6
                            int pm, const T *LDk, T *Zk, T *As, T *Bs) {
     __syncthreads();  // this CTA's rows of A^{-1}_{C,K} are visible to the CTA
     // split contribution of this tile: Ptile(i, j) = sum_{p in tile} Lhat(p, i) Y(p, j)
+    // (LU form: Uhat^T(p, i) in place of Lhat(p, i), A^{-1}_KK = U_KK^{-1} L_KK^{-1} - Uhat A^{-1}_{C,K})
     T *part = static_cast<T *>(P.partial) + P.part_off[K] + (int64_t)it.tile * s * s;
+    const T *Ak = P.lu ? static_cast<const T *>(P.LDu) + P.panel_off[K] : LDk;
     constexpr int OPT = 8;
     for (int ob = 0; ob < s * s; ob += kThreads * OPT) {
         T pacc[OPT];
@@ -167,7 +213,7 @@ __device__ void diag_block(const ProbDesc &P, const Item &it, int K, int s, int6
                 const int kk = e % kTK, j = e / kTK;
                 const int p = p0 + pc + kk;
                 const bool ok = (pc + kk < pm) && j < s;
-                As[kk * TN + j] = ok ? cjif(LDk[(int64_t)j * ld + s + p], P.herm != 0) : Sc<T>::zero();   // Lhat (conj.)
+                As[kk * TN + j] = ok ? cjif(Ak[(int64_t)j * ld + s + p], P.herm != 0) : Sc<T>::zero();   // Lhat (conj.)
                 Bs[kk * TN + j] = ok ? Zk[(int64_t)j * ld + s + p] : Sc<T>::zero();        // Y
             }
             __syncthreads();
@@ -187,7 +233,7 @@ __device__ void diag_block(const ProbDesc &P, const Item &it, int K, int s, int6
             if (e < s * s) part[e] = pacc[o];
         }
     }
-    diag_finish<T>(P, K, s, ld, it.ntiles, LDk, Zk);
+    diag_finish<T>(P, K, s, ld, it.ntiles, LDk, Zk, P.lu ? static_cast<T *>(P.Zu) + P.panel_off[K] : nullptr);
 }
 
 // ---------------------------------------------------------------------------
@@ -224,8 +270,9 @@ __device__ void selinv_item(const ProbDesc &P, const Item &it, unsigned char *sm
 #pragma unroll
         for (int j = 0; j < S::NJ; j++) acc[i][j] = Sc<T>::zero();
     if (pm > 0) {
+        // LU form: entries above the diagonal from the transposed upper panels
         LoadGather<T, TN> la{Zc, P.colbase + pos0, P.relbase + pos0, P.relidx, tile_cb, tile_rb, p0, c,
-                             P.herm != 0};
+                             P.herm != 0, P.lu ? static_cast<const T *>(P.Zu) : nullptr};
         LoadColMajor<T, TN> lb{LDk + s, ld, c, s};  // Lhat(q, j) = LD[j*ld + s + q]
         tile_gemm<T, TN>(c, la, lb, acc, As, Bs);
     }
@@ -247,6 +294,28 @@ __device__ void selinv_item(const ProbDesc &P, const Item &it, unsigned char *sm
     __syncthreads();
     for (int e = threadIdx.x; e < s; e += kThreads)
         if (ymax[e] > 0) atomicMax(&P.colexpY[P.super_ptr[K] + e], ymax[e]);
+    if (P.lu && pm > 0) {
+        // LU form: A^{-1}(K,C)^T = -A^{-1}(C,C)^T Uhat^T; entry (p, q) of the
+        // transposed gather is A^{-1}(C[q], C[p]): the same addresses with the
+        // two panel sets exchanged
+        T *Zu = static_cast<T *>(P.Zu);
+        const T *LDu = static_cast<const T *>(P.LDu) + P.panel_off[K];
+#pragma unroll
+        for (int i = 0; i < S::MI; i++)
+#pragma unroll
+            for (int j = 0; j < S::NJ; j++) acc[i][j] = Sc<T>::zero();
+        LoadGather<T, TN> lu{Zu, P.colbase + pos0, P.relbase + pos0, P.relidx, tile_cb, tile_rb, p0, c, false, Zc};
+        LoadColMajor<T, TN> lb{LDu + s, ld, c, s};
+        tile_gemm<T, TN>(c, lu, lb, acc, As, Bs);
+        T *Zuk = Zu + P.panel_off[K];
+#pragma unroll
+        for (int i = 0; i < S::MI; i++)
+#pragma unroll
+            for (int j = 0; j < S::NJ; j++) {
+                const int p = p0 + ty + S::TY * i, col = tx + S::TX * j;
+                if (p < c && col < s) Zuk[(int64_t)col * ld + s + p] = neg(acc[i][j]);
+            }
+    }
     diag_block<T, TN>(P, it, K, s, ld, c, p0, pm, LDk, Zk, As, Bs);
 }
 

@@ -39,6 +39,8 @@ static void dfree(void *p) {
 }
 
 void Workspace::release() {
+    dfree(LDu); dfree(Vt);
+    LDu = Vt = nullptr;
     dfree(LD); dfree(Linv); dfree(partial); dfree(counter); dfree(done); dfree(work); dfree(ticket);
     dfree(partial_all);
     ticket = nullptr;
@@ -94,6 +96,14 @@ int Workspace::ensure(const PlanData &p, int dtype) {
     cudaMemset(done, 0, sizeof(int) * (size_t)(p.ns + 1));
     cudaMemset(ticket, 0, sizeof(int));
     bytes_elem = es;
+    return SELINV_OK;
+}
+
+// the LU form's extra scratch (element size of the current workspace)
+int Workspace::ensure_lu(const PlanData &p) {
+    if (LDu) return SELINV_OK;
+    if (cudaMalloc(&LDu, bytes_elem * (size_t)std::max<int64_t>(p.nnz, 1)) != cudaSuccess) return SELINV_ERR_OOM;
+    if (cudaMalloc(&Vt, bytes_elem * (size_t)std::max<int64_t>(p.linv_total, 1)) != cudaSuccess) return SELINV_ERR_OOM;
     return SELINV_OK;
 }
 
@@ -378,6 +388,8 @@ int build_schedule(Schedule &S, const std::vector<const PlanData *> &plans,
     const int np = (int)plans.size();
     // subset selection: supernodes outside every selected entry's ancestor chain do not run
     auto act = [&](int i, int32_t K) { return plans[i]->active.empty() || plans[i]->active[K] != 0; };
+    // tensor-core contraction for this problem and width (never for the LU form)
+    auto ozok = [&](int i, int s) { return !descs[i].lu && oz_eligible(descs[i].dtype, s, plans[i]->opts); };
     // 1) L_KK^{-1}, Dinv for every supernode (one launch per dtype and size class)
     for (int dt = 0; dt < 2; dt++)
         for (int large = 1; large >= 0; large--) {
@@ -401,7 +413,7 @@ int build_schedule(Schedule &S, const std::vector<const PlanData *> &plans,
             for (int32_t K = 0; K < p.ns; K++) {
                 const int s = p.super_ptr[K + 1] - p.super_ptr[K];
                 const int64_t c = p.rowptr[K + 1] - p.rowptr[K] - s;
-                if (c == 0 || !act(i, K) || !oz_eligible(descs[i].dtype, s, p.opts)) continue;
+                if (c == 0 || !act(i, K) || !ozok(i, s)) continue;
                 for (int jb = 0; jb < (s + 7) / 8; jb++) S.h_work.push_back(make_int2(i, (K << 8) | jb));
             }
         }
@@ -415,7 +427,7 @@ int build_schedule(Schedule &S, const std::vector<const PlanData *> &plans,
             for (int32_t K = 0; K < p.ns; K++) {
                 const int s = p.super_ptr[K + 1] - p.super_ptr[K];
                 const int64_t c = p.rowptr[K + 1] - p.rowptr[K] - s;
-                if (c == 0 || !act(i, K) || !oz_eligible(descs[i].dtype, s, p.opts)) continue;
+                if (c == 0 || !act(i, K) || !ozok(i, s)) continue;
                 const int ktn = s <= 16 ? 16 : (s <= 32 ? 32 : 64);
                 if (ktn != tn) continue;
                 const int ncol = (s + tn - 1) / tn;
@@ -435,7 +447,7 @@ int build_schedule(Schedule &S, const std::vector<const PlanData *> &plans,
                 for (int32_t K = 0; K < p.ns; K++) {
                     const int s = p.super_ptr[K + 1] - p.super_ptr[K];
                     const int64_t c = p.rowptr[K + 1] - p.rowptr[K] - s;
-                    if (c == 0 || !act(i, K) || bucket_of(s) != b || oz_eligible(dt, s, p.opts)) continue;
+                    if (c == 0 || !act(i, K) || bucket_of(s) != b || ozok(i, s)) continue;
                     for (int t = 0; t < p.ntiles[K]; t++) S.h_items.push_back({i, K, t, p.ntiles[K]});
                 }
             }
@@ -451,7 +463,7 @@ int build_schedule(Schedule &S, const std::vector<const PlanData *> &plans,
                 const int s = p.super_ptr[K + 1] - p.super_ptr[K];
                 const int64_t c = p.rowptr[K + 1] - p.rowptr[K] - s;
                 if (c == 0 || !act(i, K) || mode == SELINV_SCHED_PERSISTENT || mode == SELINV_SCHED_PUSH ||
-                    !oz_eligible(descs[i].dtype, s, p.opts))
+                    !ozok(i, s))
                     continue;
                 for (int jb = 0; jb < (s + 7) / 8; jb++) S.h_work.push_back(make_int2(i, (K << 8) | jb));
             }
@@ -630,7 +642,7 @@ int build_schedule(Schedule &S, const std::vector<const PlanData *> &plans,
             for (int32_t K = p.ns - 1; K >= 0; K--) {
                 if (!act(i, K)) continue;
                 const int s = p.super_ptr[K + 1] - p.super_ptr[K];
-                if (oz_eligible(descs[i].dtype, s, p.opts)) {
+                if (ozok(i, s)) {
                     const int tn = oz_tn(s);
                     const int64_t off = (int64_t)S.h_items.size();
                     push_oz(i, K, tn, oz_split(i, K, oz_ctas(i, K)));
@@ -664,7 +676,7 @@ int build_schedule(Schedule &S, const std::vector<const PlanData *> &plans,
                 if (l >= p.nlevels) continue;
                 for (int64_t e = p.level_ptr[l]; e < p.level_ptr[l + 1]; e++) {
                     const int32_t K = p.level_list[e];
-                    if (act(i, K) && oz_eligible(descs[i].dtype, p.super_ptr[K + 1] - p.super_ptr[K], p.opts))
+                    if (act(i, K) && ozok(i, p.super_ptr[K + 1] - p.super_ptr[K]))
                         oz.push_back({i, K});
                 }
             }
@@ -705,7 +717,7 @@ int build_schedule(Schedule &S, const std::vector<const PlanData *> &plans,
                         for (int64_t e = p.level_ptr[l]; e < p.level_ptr[l + 1]; e++) {
                             const int32_t K = p.level_list[e];
                             const int s = p.super_ptr[K + 1] - p.super_ptr[K];
-                            if (act(i, K) && bucket_of(s) == b && !oz_eligible(dt, s, p.opts)) push_items(i, K);
+                            if (act(i, K) && bucket_of(s) == b && !ozok(i, s)) push_items(i, K);
                         }
                     }
                     const int cnt = (int)(S.h_items.size() - off);
@@ -890,6 +902,7 @@ extern "C" int selinv_symbolic(int32_t n, int32_t nsuper, const int32_t *super_p
 
 selinv_plan_s::~selinv_plan_s() {
     single.release();
+    lu.release();
     for (auto &b : batch_cache) b.sched.release();
     for (auto &w : ws) w.release();
     factor_release(this);
@@ -1093,6 +1106,44 @@ static int numeric_run(selinv_plan plan, selinv_dtype dtype, const void *L, cons
             return SELINV_ERR_CUDA;
         note_launch(2);
     }
+    return run_schedule(S, st, p.opts.use_graph != 0);
+}
+
+// The LU form (nonsymmetric values): the DFMA kernels with the descriptor's
+// LU fields set; level schedule unless the plan asks for the plain one.
+extern "C" int selinv_numeric_lu(selinv_plan plan, selinv_dtype dtype, const void *L, const void *Ut, void *Zl,
+                                 void *Zu, void *stream) {
+    if (!plan || (dtype != SELINV_F64 && dtype != SELINV_C128)) return SELINV_ERR_INVALID_ARG;
+    PlanData &p = plan->data;
+    if (p.ns == 0) return SELINV_OK;
+    if (!L || !Ut || !Zl || !Zu || !aligned16(L) || !aligned16(Ut) || !aligned16(Zl) || !aligned16(Zu))
+        return SELINV_ERR_INVALID_ARG;
+    int rc = ensure_device(p);
+    if (rc) return rc;
+    if (plan->ws.empty()) plan->ws.resize(1);
+    Workspace &w = plan->ws[0];
+    if ((rc = w.ensure(p, dtype)) || (rc = w.ensure_lu(p))) return rc;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    Schedule &S = plan->lu;
+    const int mode = p.opts.schedule == SELINV_SCHED_PLAIN ? SELINV_SCHED_PLAIN : SELINV_SCHED_LEVEL;
+    if (!S.valid || S.key_L != L || S.key_D != Ut || S.key_Z != Zl || S.key_Z2 != Zu || S.key_dtype != dtype ||
+        S.mode != mode) {
+        ProbDesc d = make_desc(p, w, dtype, L, nullptr, Zl, false);
+        d.lu = 1;
+        d.symmetrize = 0;
+        d.Ut = Ut;
+        d.Zu = Zu;
+        d.LDu = w.LDu;
+        d.Vt = w.Vt;
+        std::vector<const PlanData *> plans{&p};
+        std::vector<ProbDesc> descs{d};
+        rc = build_schedule(S, plans, descs, mode);
+        if (rc) { S.valid = false; return rc; }
+        S.spin_limit = p.opts.spin_limit;
+        S.valid = true;
+        S.key_L = L; S.key_D = Ut; S.key_Z = Zl; S.key_Z2 = Zu; S.key_dtype = dtype; S.mode = mode;
+    }
+    plan->last_stream = st;
     return run_schedule(S, st, p.opts.use_graph != 0);
 }
 

@@ -62,8 +62,11 @@ struct Workspace {
     int *linvexp = nullptr;    // [n]
     long long *yacc = nullptr; // [2 * nnz] (real problems with tensor-core supernodes), zero between calls
     int *tcount = nullptr;     // [tile_total], zero between calls
+    void *LDu = nullptr;       // LU form: Uhat^T panels
+    void *Vt = nullptr;        // LU form: (U_KK^T)^{-1} blocks
     size_t bytes_elem = 0;
     int ensure(const PlanData &p, int dtype);
+    int ensure_lu(const PlanData &p);
     int ensure_persistent(const PlanData &p);
     void release();
 };
@@ -93,7 +96,7 @@ struct Launch {
 struct Schedule {
     bool valid = false;
     int mode = -1;
-    const void *key_L = nullptr, *key_D = nullptr, *key_Z = nullptr;
+    const void *key_L = nullptr, *key_D = nullptr, *key_Z = nullptr, *key_Z2 = nullptr;
     int key_dtype = -1;
     std::vector<ProbDesc> h_descs;
     std::vector<Item> h_items;
@@ -193,6 +196,7 @@ struct selinv_plan_s {
     selinv::PlanData data;
     std::vector<selinv::Workspace> ws;  // ws[0]: single calls; ws[1..]: batch items
     selinv::Schedule single;
+    selinv::Schedule lu;                // the LU form (selinv_numeric_lu)
     std::vector<selinv::BatchEntry> batch_cache;
     selinv::FactorData *factor = nullptr;
     cudaStream_t last_stream = nullptr;

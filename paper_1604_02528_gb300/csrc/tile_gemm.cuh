@@ -91,6 +91,7 @@ template <typename T, int TN, bool kDoubleDiag = false> struct LoadGather {
     const int64_t *tile_rb;  // shared: prb of the tile's rows
     int p0, c;
     bool herm = false;    // Hermitian: an entry above the diagonal is the stored one's conjugate
+    const T *Zup = nullptr;   // LU form: the entries above the diagonal come from this panel set
     __device__ void operator()(int k0, T *As) const {
         for (int e = threadIdx.x; e < kTK * kTM; e += kThreads) {
             const int pl = e % kTM, kk = e / kTM;
@@ -100,7 +101,7 @@ template <typename T, int TN, bool kDoubleDiag = false> struct LoadGather {
                 int64_t addr;
                 if (p >= q) addr = pcb[q] + relidx[prb[q] + p];
                 else addr = tile_cb[pl] + relidx[tile_rb[pl] + q];
-                v = ldcg(Z + addr);  // L2: written by other CTAs of a persistent launch
+                v = ldcg((p < q && Zup ? Zup : Z) + addr);  // L2: written by other CTAs of a persistent launch
                 if (p < q) v = cjif(v, herm);
                 if (kDoubleDiag && p == q) v = add(v, v);
             }
@@ -115,8 +116,10 @@ template <typename T, int TN, bool kDoubleDiag = false> struct LoadGather {
 // (deterministic) into A^{-1}_KK = Dinv_K - sum_t Ptile, symmetrized, and
 // flags K done when a completion array is present.
 // ---------------------------------------------------------------------------
+// Zuk (LU form): receives the transpose of the block as well
 template <typename T>
-__device__ void diag_finish(const ProbDesc &P, int K, int s, int64_t ld, int ntiles, const T *LDk, T *Zk) {
+__device__ void diag_finish(const ProbDesc &P, int K, int s, int64_t ld, int ntiles, const T *LDk, T *Zk,
+                            T *Zuk = nullptr) {
     __shared__ int s_last;
     // the last tile of K to finish reduces the partials in tile order
     __threadfence();
@@ -145,13 +148,17 @@ __device__ void diag_finish(const ProbDesc &P, int K, int s, int64_t ld, int nti
                 xij = sub(xij, ldcg(part0 + t * ss + (int64_t)j * s + i));
                 xji = sub(xji, ldcg(part0 + t * ss + (int64_t)i * s + j));
             }
-            if (P.symmetrize) {   // (X + X^T)/2, or (X + X^H)/2 (the diagonal becomes real)
+            if (P.symmetrize && !Zuk) {   // (X + X^T)/2, or (X + X^H)/2 (the diagonal becomes real)
                 const T v = half(add(xij, cjif(xji, P.herm != 0)));
                 xij = v;
                 xji = cjif(v, P.herm != 0);
             }
             Zk[(int64_t)j * ld + i] = xij;
             Zk[(int64_t)i * ld + j] = xji;
+            if (Zuk) {
+                Zuk[(int64_t)j * ld + i] = xji;
+                Zuk[(int64_t)i * ld + j] = xij;
+            }
             mj = max(mj, bexp(xij));
             atomicMax(&cz[i], bexp(xji));
         }

@@ -22,7 +22,7 @@ __all__ = [
     "Problem", "grid_nd_order", "laplacian_2d", "laplacian_3d", "dft_sheet",
     "diffusion_3d", "pole_shifts", "batch_laplacians", "random_sparse_spd",
     "tridiagonal", "make_config", "lower_pattern_weights", "random_sparse_hpd",
-    "magnetic_laplacian_3d",
+    "magnetic_laplacian_3d", "random_sparse_nonsym",
 ]
 
 FUNDAMENTAL_64 = {"kind": "fundamental", "cap": 64, "fill": 0.0}
@@ -66,11 +66,20 @@ class Problem:
         return Problem(name or self.name, self.n, self.colptr, self.rowind, values,
                        self.perm, dict(self.supernodes), dict(self.meta))
 
+    @property
+    def nonsymmetric(self) -> bool:
+        """Nonsymmetric values on the symmetric pattern: ``meta["upper"]``
+        holds a_ji on the positions of the lower CSC."""
+        return "upper" in self.meta
+
     def dense(self) -> np.ndarray:
-        """Full symmetric dense matrix (small n only)."""
+        """Full dense matrix (small n only)."""
         a = np.zeros((self.n, self.n), dtype=self.values.dtype)
         cols = np.repeat(np.arange(self.n), np.diff(self.colptr))
-        a[cols, self.rowind] = np.conj(self.values) if self.hermitian else self.values
+        if self.nonsymmetric:
+            a[cols, self.rowind] = self.meta["upper"]
+        else:
+            a[cols, self.rowind] = np.conj(self.values) if self.hermitian else self.values
         a[self.rowind, cols] = self.values
         return a
 
@@ -485,6 +494,40 @@ def random_sparse_hpd(n: int, density: float, seed: int,
     colptr, rowind, vals, _ = _hermitian_lower(n, perm, rs + 1.0, r, c, ev)
     return Problem(f"hpd_{n}_{seed}", n, colptr, rowind, vals.astype(np.complex128), perm,
                    dict(supernodes or FUNDAMENTAL_64), {"seed": seed, "hermitian": True})
+
+
+def random_sparse_nonsym(n: int, density: float, seed: int, complex_values: bool = False,
+                         supernodes: Optional[Dict[str, object]] = None) -> Problem:
+    """Random symmetric pattern with independent values above and below the
+    diagonal (N(0,1); complex: both parts), diagonal = sum of |a_ij| + |a_ji|
+    over the row + 1 (diagonally dominant by rows and columns: LU without
+    pivoting exists), a random symmetric permutation."""
+    rng = np.random.default_rng(seed)
+    m = int(round(density * n * (n - 1) / 2))
+    iu = np.sort(rng.choice(n * (n - 1) // 2, size=min(m, n * (n - 1) // 2), replace=False))
+    r = np.floor((np.sqrt(8.0 * iu + 1) - 1) / 2).astype(np.int64) + 1
+    c = iu - r * (r - 1) // 2
+    if complex_values:
+        draw = lambda k: rng.standard_normal(k) + 1j * rng.standard_normal(k)
+    else:
+        draw = rng.standard_normal
+    below, above = draw(r.size), draw(r.size)       # A[r, c] and A[c, r]
+    rs = np.zeros(n)
+    for v in (below, above):
+        np.add.at(rs, r, np.abs(v))
+        np.add.at(rs, c, np.abs(v))
+    diag = rs + 1.0
+    perm = rng.permutation(n)
+    iperm = np.empty(n, dtype=np.int64)
+    iperm[perm] = np.arange(n)
+    low_first = iperm[r] > iperm[c]                  # A[r, c] lands below the diagonal
+    lo_in = np.where(low_first, below, above)
+    up_in = np.where(low_first, above, below)
+    colptr, rowind, vals, src = _lower_csc(n, perm, diag, r, c, lo_in)
+    up_all = np.concatenate([diag, up_in])
+    dt = np.complex128 if complex_values else np.float64
+    return Problem(f"nonsym_{n}_{seed}", n, colptr, rowind, vals.astype(dt), perm,
+                   dict(supernodes or FUNDAMENTAL_64), {"seed": seed, "upper": up_all[src].astype(dt)})
 
 
 def magnetic_laplacian_3d(nx: int, seed: int, flux: float = 0.25,
