@@ -105,7 +105,7 @@ typedef struct {
     int split_min_steps;   /* smallest k-range of a split item, in 16-row steps (8..64,
                               a multiple of 8); default 16                              */
     int oz_min_s;          /* narrowest supernode (columns) that uses the tensor-core
-                              contraction (16..128); default 16                         */
+                              contraction (1..128); default 16                          */
 } selinv_opts;
 
 /* Fills *opts with the defaults listed above. */

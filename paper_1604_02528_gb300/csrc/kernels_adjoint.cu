@@ -1022,7 +1022,9 @@ static int adj_split(selinv_plan_s *plan) {
     AdjData *a = static_cast<AdjData *>(plan->factor->adj);
     const PlanData &p = plan->data;
     const selinv_opts &o = p.opts;
-    const int key = o.fast_contraction == 1 ? std::max(kOzMinS, o.oz_min_s) : 0;
+    // (at least 8 columns: narrower supernodes keep the fused kernels, whose
+    // one CTA per tile wastes less than 32-column blocks would)
+    const int key = o.fast_contraction == 1 ? std::max(8, o.oz_min_s) : 0;
     if (key == a->split_key) return SELINV_OK;
     auto fr = [](void *q) { if (q) cudaFree(q); };
     fr(a->d_sm); fr(a->d_wd); fr(a->d_row); fr(a->d_mbp); fr(a->d_dig);

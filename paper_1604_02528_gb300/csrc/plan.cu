@@ -849,7 +849,7 @@ using namespace selinv;
 static bool opts_valid(const selinv_opts *o) {
     return o->schedule >= 0 && o->schedule <= 3 && o->fast_contraction >= 0 && o->fast_contraction <= 2 &&
            o->split_target >= 1 && o->split_target <= 8 && o->split_min_steps >= 8 &&
-           o->split_min_steps <= 64 && o->split_min_steps % 8 == 0 && o->oz_min_s >= 16 && o->oz_min_s <= 128 &&
+           o->split_min_steps <= 64 && o->split_min_steps % 8 == 0 && o->oz_min_s >= kOzMinS && o->oz_min_s <= 128 &&
            o->spin_limit > 0;
 }
 
@@ -1041,7 +1041,7 @@ static int autotune(selinv_plan plan, selinv_dtype dtype, const void *L, const v
                 consider(o);
             }
         const selinv_opts f = best;
-        for (int ozm : {16, 32, 64}) {
+        for (int ozm : {1, 8, 16, 32, 64}) {
             selinv_opts o = f;
             o.oz_min_s = ozm;
             consider(o);

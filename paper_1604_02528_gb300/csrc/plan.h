@@ -78,7 +78,7 @@ enum { KL_LINV = 0, KL_LHAT = 1, KL_SELINV = 2, KL_DIGITS = 3, KL_SELINV_OZ = 4,
 
 // tensor-core (FP64-exact) contraction applies to real problems with s >= kOzMinS;
 // fast_contraction 1 runs the gather-GEMM on tcgen05, 2 on mma.sync
-constexpr int kOzMinS = 16;
+constexpr int kOzMinS = 1;
 inline bool oz_eligible(int dtype, int s, const selinv_opts &o) {
     return o.fast_contraction && dtype == SELINV_F64 && s >= std::max(kOzMinS, o.oz_min_s);
 }

@@ -35,12 +35,12 @@ def rel(a, b):
     return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
 
 
-@pytest.mark.parametrize("engine", [1, 0])
+@pytest.mark.parametrize("engine,ozm", [(1, 16), (1, 8), (0, 16)])
 @pytest.mark.parametrize("name,make", CASES)
-def test_adjoints_match_oracle(native, cuda_device, name, make, engine):
-    """engine 1: supernodes of 16 columns or more take the split path (tcgen05
-    gather-GEMM, 64 x 32 blocks for the s-inner products); 0: every supernode
-    on the fused FP64 kernels."""
+def test_adjoints_match_oracle(native, cuda_device, name, make, engine, ozm):
+    """engine 1: supernodes of ozm columns or more take the split path
+    (tcgen05 gather-GEMM, 32 x 32 blocks for the s-inner products); 0: every
+    supernode on the fused FP64 kernels."""
     import torch
     from paper_1604_02528_gb300.api import SelInvContext
     p = make()
@@ -55,6 +55,7 @@ def test_adjoints_match_oracle(native, cuda_device, name, make, engine):
     ctx.attach_matrix()
     o = native.selinv_default_opts()
     o.fast_contraction = engine
+    o.oz_min_s = ozm
     o.split_min_steps = 8       # k-split tcgen05 items from c >= 256 on
     native.selinv_plan_set_opts(ctx.plan, o)
     t = lambda x: torch.from_numpy(np.ascontiguousarray(x)).cuda()

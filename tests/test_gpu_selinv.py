@@ -124,9 +124,10 @@ def test_tensor_core_and_dfma_paths_match_oracle(native, cuda_device, name, make
     sym, L, D, Z = oracle_run(p)
     plan = native.selinv_symbolic(sym.n, sym.nsuper, sym.super_ptr, sym.sparent, sym.rowptr, sym.rows)
     outs = []
-    for fast in (1, 2, 0):
+    for fast, ozm in ((1, 16), (2, 16), (0, 16), (1, 1), (2, 1)):   # oz_min_s 1: every supernode on the tensor cores
         o = native.selinv_default_opts()
         o.fast_contraction = fast
+        o.oz_min_s = ozm
         native.selinv_plan_set_opts(plan, o)
         Lt = torch.from_numpy(L).cuda(); Dt = torch.from_numpy(D).cuda()
         Zt = torch.full_like(Lt, float("nan"))
@@ -136,8 +137,8 @@ def test_tensor_core_and_dfma_paths_match_oracle(native, cuda_device, name, make
         outs.append(Zt.cpu().numpy())
     for G in outs:
         assert oracle.block_errors(sym, G, Z).max() <= TOL
-    assert oracle.block_errors(sym, outs[0], outs[2]).max() <= TOL
-    assert oracle.block_errors(sym, outs[1], outs[2]).max() <= TOL
+    for G in outs[:2] + outs[3:]:
+        assert oracle.block_errors(sym, G, outs[2]).max() <= TOL
 
 
 def test_autotuned_plan_matches_oracle(native, cuda_device):
@@ -160,4 +161,4 @@ def test_autotuned_plan_matches_oracle(native, cuda_device):
         assert oracle.block_errors(sym, Zt.cpu().numpy(), Z).max() <= TOL
     t = native.selinv_plan_get_opts(plan)
     assert t.fast_contraction in (0, 1, 2)
-    assert t.split_target in (1, 2, 4) and t.split_min_steps in (8, 16, 32) and t.oz_min_s in (16, 32, 64)
+    assert t.split_target in (1, 2, 4) and t.split_min_steps in (8, 16, 32) and t.oz_min_s in (1, 8, 16, 32, 64)

@@ -219,7 +219,7 @@ def test_options_round_trip_and_validation(native):
     g = native.selinv_plan_get_opts(plan)
     assert (g.fast_contraction, g.split_target, g.split_min_steps, g.oz_min_s) == (2, 4, 32, 64)
     for field, bad in (("split_target", 0), ("split_target", 9), ("split_min_steps", 12),
-                       ("split_min_steps", 0), ("oz_min_s", 8), ("fast_contraction", 3), ("schedule", 4),
+                       ("split_min_steps", 0), ("oz_min_s", 0), ("fast_contraction", 3), ("schedule", 4),
                        ("spin_limit", 0)):
         b = native.selinv_default_opts()
         setattr(b, field, bad)
