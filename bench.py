@@ -458,7 +458,8 @@ def main():
             "k_lhat": mult * float((c_ * s_ * s_ * ~oz).sum()),
             "k_lhat_oz": mult * float((c_ * s_ * s_ * oz).sum()),
             "k_linv_digits": 0.0,
-            "k_linv": mult * float((s_ ** 3).sum()),
+            "k_linv": mult * float((s_ ** 3 / 3 + (s_ ** 3 / 3) * (s_ <= 32)).sum()),
+            "k_dinv": mult * float(((s_ ** 3 / 3) * (s_ > 32)).sum()),
             "k_lhat_digits": 0.0,
             "k_tc_reduce": 0.0,
             "k_diag_fin": 0.0,

@@ -998,7 +998,8 @@ static int adj_normalize(selinv_plan_s *plan, const void *L, const void *D, cuda
     if (!a->tcs.launches.empty()) {
         // the forward's own normalization launches (Lhat of the wide supernodes on the tensor cores)
         for (const Launch &Ln : a->tcs.launches)
-            if (Ln.kind == KL_LINV || Ln.kind == KL_LINV_DIGITS || Ln.kind == KL_LHAT_OZ || Ln.kind == KL_LHAT) {
+            if (Ln.kind == KL_LINV || Ln.kind == KL_DINV || Ln.kind == KL_LINV_DIGITS || Ln.kind == KL_LHAT_OZ ||
+                Ln.kind == KL_LHAT) {
                 launch_with(a->tcs, Ln, a->d_pdesc, st);
                 note_launch();
             }

@@ -73,10 +73,11 @@ __device__ void linv_lu(const ProbDesc &P, int K, int s, int64_t ld, const T *L,
     }
 }
 
+// with_dinv = 0: only L_KK^{-1} (k_dinv forms Dinv_K afterwards, spread over tiles)
 template <typename T>
 __global__ void __launch_bounds__(kLinvThreads) k_linv(const ProbDesc *__restrict__ descs,
                                                        const int2 *__restrict__ work, int nwork,
-                                                       size_t smem_cap) {
+                                                       size_t smem_cap, int with_dinv) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int w = blockIdx.x;
     if (w >= nwork) return;
@@ -117,6 +118,7 @@ __global__ void __launch_bounds__(kLinvThreads) k_linv(const ProbDesc *__restric
     }
     if (in_smem)
         for (int e = threadIdx.x; e < s * s; e += kLinvThreads) Li[e] = X[(e / s) * lx + e % s];
+    if (!with_dinv) return;
     const bool h = P.herm != 0;
     for (int e = threadIdx.x; e < s * s; e += kLinvThreads) {
         const int i = e % s, j = e / s;
@@ -127,6 +129,62 @@ __global__ void __launch_bounds__(kLinvThreads) k_linv(const ProbDesc *__restric
         LD[(int64_t)j * ld + i] = acc;
         LD[(int64_t)i * ld + j] = cjif(acc, h);
     }
+}
+
+// ---------------------------------------------------------------------------
+// k_dinv: Dinv_K = X^T D_K^{-1} X (X^H for a Hermitian problem), X = L_KK^{-1}
+// from k_linv, for the wide supernodes: one 32 x 32 tile (i0 >= j0) of the
+// lower triangle per CTA, mirrored; k runs from i0 (X is lower triangular).
+// work (problem, K << 8 | tile), tiles row-major over the lower triangle.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(256) k_dinv(const ProbDesc *__restrict__ descs, const int2 *__restrict__ work,
+                                              int nwork) {
+    __shared__ T As[32][33], Bs[32][33];
+    __shared__ T rD[128];
+    const int w = blockIdx.x;
+    if (w >= nwork) return;
+    const ProbDesc &P = descs[work[w].x];
+    const int K = work[w].y >> 8, t = work[w].y & 0xFF;
+    const int fc = P.super_ptr[K];
+    const int s = P.super_ptr[K + 1] - fc;
+    const int64_t ld = P.rowptr[K + 1] - P.rowptr[K];
+    int ti = 0, r = t;
+    while (r > ti) { r -= ti + 1; ti++; }            // tile t -> (ti, tj), tj <= ti
+    const int i0 = ti * 32, j0 = r * 32;
+    const T *X = static_cast<const T *>(P.Linv) + P.linv_off[K];   // X(k, j) = X[j*s + k]
+    const T *D = static_cast<const T *>(P.D) + fc;
+    T *LD = static_cast<T *>(P.LD) + P.panel_off[K];
+    const bool h = P.herm != 0;
+    for (int k = threadIdx.x; k < s; k += 256) rD[k] = recip(D[k]);
+    const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+    T acc[2][2] = {{Sc<T>::zero(), Sc<T>::zero()}, {Sc<T>::zero(), Sc<T>::zero()}};
+    for (int k0 = i0; k0 < s; k0 += 32) {
+        __syncthreads();
+        for (int e = threadIdx.x; e < 32 * 32; e += 256) {
+            const int q = e % 32, rr = e / 32, k = k0 + q;   // k fastest: contiguous in X's columns
+            As[q][rr] = (k < s && i0 + rr < s) ? mul(cjif(X[(int64_t)(i0 + rr) * s + k], h), rD[k]) : Sc<T>::zero();
+            Bs[q][rr] = (k < s && j0 + rr < s) ? X[(int64_t)(j0 + rr) * s + k] : Sc<T>::zero();
+        }
+        __syncthreads();
+#pragma unroll 8
+        for (int q = 0; q < 32; q++) {
+            const T a0 = As[q][ty], a1 = As[q][ty + 16], b0 = Bs[q][tx], b1 = Bs[q][tx + 16];
+            madd(acc[0][0], a0, b0);
+            madd(acc[0][1], a0, b1);
+            madd(acc[1][0], a1, b0);
+            madd(acc[1][1], a1, b1);
+        }
+    }
+#pragma unroll
+    for (int u = 0; u < 2; u++)
+#pragma unroll
+        for (int v = 0; v < 2; v++) {
+            const int i = i0 + ty + 16 * u, j = j0 + tx + 16 * v;
+            if (i >= s || j >= s || i < j) continue;
+            LD[(int64_t)j * ld + i] = acc[u][v];
+            LD[(int64_t)i * ld + j] = cjif(acc[u][v], h);
+        }
 }
 
 // ---------------------------------------------------------------------------
@@ -514,17 +572,26 @@ cudaError_t launch_check_finite(const void *x, int64_t n, int *status, cudaStrea
 }
 
 template <typename T>
-static cudaError_t launch_linv_t(const ProbDesc *d, const int2 *work, int nwork, int large, cudaStream_t st) {
+static cudaError_t launch_linv_t(const ProbDesc *d, const int2 *work, int nwork, int large, int with_dinv,
+                                 cudaStream_t st) {
     if (nwork <= 0) return cudaSuccess;
     // small blocks (s <= 32) need at most 17 KB; large ones get room for s = 128 (real)
     const size_t cap = large ? kLinvSmemMax : (32 * 33 + 32) * sizeof(T);
-    k_linv<T><<<nwork, kLinvThreads, cap, st>>>(d, work, nwork, cap);
+    k_linv<T><<<nwork, kLinvThreads, cap, st>>>(d, work, nwork, cap, with_dinv);
     return cudaGetLastError();
 }
 
-cudaError_t launch_linv(int dtype, const ProbDesc *d, const int2 *work, int nwork, int large, cudaStream_t st) {
-    return dtype == SELINV_C128 ? launch_linv_t<zd>(d, work, nwork, large, st)
-                                : launch_linv_t<double>(d, work, nwork, large, st);
+cudaError_t launch_linv(int dtype, const ProbDesc *d, const int2 *work, int nwork, int large, cudaStream_t st,
+                        int with_dinv) {
+    return dtype == SELINV_C128 ? launch_linv_t<zd>(d, work, nwork, large, with_dinv, st)
+                                : launch_linv_t<double>(d, work, nwork, large, with_dinv, st);
+}
+
+cudaError_t launch_dinv(int dtype, const ProbDesc *d, const int2 *work, int nwork, cudaStream_t st) {
+    if (nwork <= 0) return cudaSuccess;
+    if (dtype == SELINV_C128) k_dinv<zd><<<nwork, 256, 0, st>>>(d, work, nwork);
+    else k_dinv<double><<<nwork, 256, 0, st>>>(d, work, nwork);
+    return cudaGetLastError();
 }
 
 template <typename T, int TN>

@@ -12,7 +12,9 @@ void note_launch(int n = 1);
 
 cudaError_t configure_selinv_kernels();
 // large = 1 for supernodes with s > 32 (128 KB of shared memory), 0 otherwise
-cudaError_t launch_linv(int dtype, const ProbDesc *d, const int2 *work, int nwork, int large, cudaStream_t st);
+cudaError_t launch_linv(int dtype, const ProbDesc *d, const int2 *work, int nwork, int large, cudaStream_t st,
+                        int with_dinv = 1);
+cudaError_t launch_dinv(int dtype, const ProbDesc *d, const int2 *work, int nwork, cudaStream_t st);
 cudaError_t launch_lhat(int dtype, int bucket, const ProbDesc *d, const Item *items, int n,
                         cudaStream_t st);
 cudaError_t launch_selinv(int dtype, int bucket, const ProbDesc *d, const Item *items, int n,

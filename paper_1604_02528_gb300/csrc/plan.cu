@@ -403,6 +403,19 @@ int build_schedule(Schedule &S, const std::vector<const PlanData *> &plans,
             }
             const int cnt = (int)(S.h_work.size() - off);
             if (cnt) S.launches.push_back({0, dt, large, off, cnt, -1});
+            if (!cnt || !large) continue;
+            // Dinv_K of the wide ones, a CTA per 32 x 32 tile of its lower triangle
+            // (the LU form's own Dinv comes from k_linv)
+            const int64_t off2 = (int64_t)S.h_work.size();
+            for (int64_t e = off; e < off + cnt; e++) {
+                const int2 wk = S.h_work[e];
+                if (descs[wk.x].lu) continue;
+                const int s = plans[wk.x]->super_ptr[wk.y + 1] - plans[wk.x]->super_ptr[wk.y];
+                const int nt = (s + 31) / 32;
+                for (int t = 0; t < nt * (nt + 1) / 2; t++) S.h_work.push_back(make_int2(wk.x, (wk.y << 8) | t));
+            }
+            const int cnt2 = (int)(S.h_work.size() - off2);
+            if (cnt2) S.launches.push_back({KL_DINV, dt, 0, off2, cnt2, -1});
         }
     // 2) Lhat for every row tile: the tensor-core product for eligible
     //    supernodes (after the digit planes of L_KK^{-1}), FP64 for the rest
@@ -766,7 +779,9 @@ int build_schedule(Schedule &S, const std::vector<const PlanData *> &plans,
 // one launch of a schedule with the problem descriptors at `d`
 cudaError_t launch_with(const Schedule &S, const Launch &L, const ProbDesc *d, cudaStream_t st) {
     switch (L.kind) {
-    case KL_LINV: return launch_linv(L.dtype, d, S.d_work + L.off, L.count, L.bucket, st);
+    // the wide supernodes' Dinv follows in KL_DINV launches (32 x 32 tiles)
+    case KL_LINV: return launch_linv(L.dtype, d, S.d_work + L.off, L.count, L.bucket, st, L.bucket == 0);
+    case KL_DINV: return launch_dinv(L.dtype, d, S.d_work + L.off, L.count, st);
     case KL_LHAT: return launch_lhat(L.dtype, L.bucket, d, S.d_items + L.off, L.count, st);
     case KL_SELINV: return launch_selinv(L.dtype, L.bucket, d, S.d_items + L.off, L.count, st);
     case KL_DIGITS: return launch_lhat_digits(d, S.d_work + L.off, L.count, st);
