@@ -151,6 +151,7 @@ KERNEL_SOURCES = {
     "k_selinv_oz": ("kernels_ozaki.cu", "common.cuh"),
     "k_selinv_tc": ("kernels_tc.cu", "umma.cuh", "fixedpoint.cuh", "common.cuh"),
     "k_diag": ("kernels_ozaki.cu", "common.cuh"),
+    "k_diag_tc": ("kernels_tc.cu", "umma.cuh", "fixedpoint.cuh", "common.cuh"),
 }
 DEFAULT_SOURCES = ("kernels_selinv.cu", "tile_gemm.cuh", "common.cuh")
 
@@ -464,11 +465,12 @@ def main():
             "k_tc_reduce": 0.0,
             "k_diag_fin": 0.0,
             "k_push_diag": mult * float((2 * c_ * s_ * s_).sum()),
-            "k_push": mult * float((2 * c_ * c_ * s_).sum())}
+            "k_push": mult * float((2 * c_ * c_ * s_).sum()),
+            "k_diag_tc": mult * float((2 * c_ * s_ * s_ * oz).sum())}
     f_dom = f_of[name]
     achieved = f_dom / (kms[dom] * 1e-3) / 1e9 if kms[dom] > 0 else None
     traffic = ncu_traffic(name)
-    if name in ("k_selinv_oz", "k_selinv_tc", "k_diag", "k_lhat_oz"):
+    if name in ("k_selinv_oz", "k_selinv_tc", "k_diag", "k_diag_tc", "k_lhat_oz"):
         # FP64-exact products on bf16 tensor cores: 28 digit-pair products per FP64 product
         peak, unit, bound = peaks["bf16_tflops"], "TFLOP/s", "tensor"
         ach = 28.0 * f_dom / (kms[dom] * 1e-3) / 1e12 if kms[dom] > 0 else None

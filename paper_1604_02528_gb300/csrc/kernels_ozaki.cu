@@ -690,8 +690,10 @@ __global__ void __launch_bounds__(kOzThreads, 1) k_diag_oz(const ProbDesc *__res
 // their whole-column exponents (for the row bounds of later gathers).  The
 // sums are cleared before every call.
 // ---------------------------------------------------------------------------
+// bshift: 1 when the sums come from k_diag_tc (its Y digits sit on a grid
+// twice as coarse as k_diag_oz's)
 __global__ void __launch_bounds__(256) k_diag_fin(const ProbDesc *__restrict__ descs,
-                                                  const Item *__restrict__ items, int nitems) {
+                                                  const Item *__restrict__ items, int nitems, int bshift) {
     const int w = blockIdx.x;
     if (w >= nitems) return;
     const Item it = items[w];
@@ -711,7 +713,7 @@ __global__ void __launch_bounds__(256) k_diag_fin(const ProbDesc *__restrict__ d
         const long long hi = q[0], lo = q[1];
         const int ey = P.colexpY[fc + b];
         if (ey == 0 || (hi == 0 && lo == 0)) return 0.0;
-        const int sc = (P.colexp[fc + a] - 1022) + (ey - 1022) - 14;
+        const int sc = (P.colexp[fc + a] - 1022) + (ey - 1022) - 14 + bshift;
         return fixed_to_double(hi, lo, sc);
     };
     int mj = 0;
@@ -735,9 +737,9 @@ cudaError_t launch_diag_oz(const ProbDesc *d, const Item *items, int n, cudaStre
     return cudaGetLastError();
 }
 
-cudaError_t launch_diag_fin(const ProbDesc *d, const Item *items, int n, cudaStream_t st) {
+cudaError_t launch_diag_fin(const ProbDesc *d, const Item *items, int n, int bshift, cudaStream_t st) {
     if (n <= 0) return cudaSuccess;
-    k_diag_fin<<<n, 256, 0, st>>>(d, items, n);
+    k_diag_fin<<<n, 256, 0, st>>>(d, items, n, bshift);
     return cudaGetLastError();
 }
 

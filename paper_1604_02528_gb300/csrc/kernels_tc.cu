@@ -174,7 +174,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_selinv_tc(const ProbDesc *__r
         tile_rb[e] = p < c ? P.relbase[pos0 + p] : 0;
         rowE[e] = p < c ? P.colexpZ[P.rows[pos0 + p]] : 0;
     }
-    for (int e = tid; e < 2 * kTcM * TN; e += kTcThreads) Hi[e] = 0;   // Hi and Lo
+    // Hi and Lo are written by the first flush; an item without steps leaves zeros
+    if (n == 0)
+        for (int e = tid; e < 2 * kTcM * TN; e += kTcThreads) Hi[e] = 0;
     for (int e = tid; e < 128; e += kTcThreads) ymax[e] = 0;
     if (tid == 0) {
         for (int st = 0; st < 2; st++) {
@@ -341,8 +343,16 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_selinv_tc(const ProbDesc *__r
                     long long gv[kTcDig];
 #pragma unroll
                     for (int gq = 0; gq < kTcDig; gq++) gv[gq] = (long long)__float2int_rn(__uint_as_float(acc[gq][jj]));
-                    Hi[(cb * 8 + jj) * kTcM + row] += (gv[0] << 16) + (gv[1] << 8) + gv[2];
-                    Lo[(cb * 8 + jj) * kTcM + row] += (gv[3] << 24) + (gv[4] << 16) + (gv[5] << 8) + gv[6];
+                    const long long h = (gv[0] << 16) + (gv[1] << 8) + gv[2];
+                    const long long l = (gv[3] << 24) + (gv[4] << 16) + (gv[5] << 8) + gv[6];
+                    long long *ph = Hi + (cb * 8 + jj) * kTcM + row, *pl = Lo + (cb * 8 + jj) * kTcM + row;
+                    if (f == 0) {   // the first chunk writes, the later ones add
+                        *ph = h;
+                        *pl = l;
+                    } else {
+                        *ph += h;
+                        *pl += l;
+                    }
                 }
             }
             umma::fence_before_sync();
@@ -453,10 +463,275 @@ cudaError_t launch_tc_reduce(int tn, const ProbDesc *d, const Item *items, const
     return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// Diagonal block on tcgen05: the exact sums of (Lhat^T Y)(i, j) over one chunk
+// of C rows for one column tile of K, added into K's per-entry int64 sums (the
+// sums k_diag_fin turns into A^{-1}_KK = Dinv_K - Lhat^T Y).
+//   A = Lhat^T: rows i of K (128 tensor-memory lanes, zero past s), k = rows q
+//       of C -- the digit planes of Lhat are already stored in this operand
+//       layout (they are the gather-GEMM's B), so one bulk copy per plane and
+//       16-row step brings them in;
+//   B = Y columns n0 .. n0 + TN - 1, k = q: 4 producer warps slice A^{-1}_{C,K}
+//       (written by the gather-GEMM of this level) into digit planes on the
+//       column exponents colexpY, integer operations only.
+// Digit products grouped by i + j into exact fp32 sums in tensor memory,
+// folded into int64 every 128 k, as in k_selinv_tc.  The A digits sit on the
+// grid 2^(F - 1029 - 8i) of Lhat's columns, the B digits on 2^(E - 1028 - 8j).
+// ---------------------------------------------------------------------------
+constexpr int kDtProd = 4;                       // producer warps (digit planes of Y)
+constexpr int kDtEpi = 4;                        // epilogue warps (tensor memory -> int64)
+constexpr int kDtMmaWarp = kDtProd + kDtEpi;
+constexpr int kDtThreads = 32 * (kDtProd + kDtEpi + 1);
+
+template <int TN> struct DtCfg {
+    static constexpr int A_PLANE = kTcM * 16;
+    static constexpr int B_PLANE = TN * 16;
+    static constexpr int A_STAGE = kTcDig * A_PLANE;
+    static constexpr int B_STAGE = kTcDig * B_PLANE;
+    static constexpr uint32_t TCOLS = kTcDig * TN <= 128 ? 128u : (kTcDig * TN <= 256 ? 256u : 512u);
+    static constexpr size_t SMEM =
+        sizeof(uint16_t) * 2 * (size_t)(A_STAGE + B_STAGE) + sizeof(long long) * 2 * (size_t)kTcM * TN;
+};
+static_assert(2 * 64 <= 32 * kDtProd, "a producer thread per (column, 8-row half) of a 64-column tile");
+
+// items: tile = chunk * ncol + column tile, ntiles = number of chunks
+template <int TN>
+__global__ void __launch_bounds__(kDtThreads, 1) k_diag_tc(const ProbDesc *__restrict__ descs,
+                                                           const Item *__restrict__ items, int nitems,
+                                                           long long wait_limit) {
+    using Cfg = DtCfg<TN>;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    uint16_t *As = reinterpret_cast<uint16_t *>(smem_raw);                // [2][7][A_PLANE]
+    uint16_t *Bs = As + 2 * Cfg::A_STAGE;                                  // [2][7][B_PLANE]
+    long long *Hi = reinterpret_cast<long long *>(Bs + 2 * Cfg::B_STAGE);  // [TN][128]
+    long long *Lo = Hi + kTcM * TN;
+    __shared__ __align__(8) uint64_t full[2], empty[2], acc_full, tmem_free;
+    __shared__ uint32_t s_tmem;
+    __shared__ volatile int s_abort;
+    __shared__ int colE[TN];
+
+    const int w = blockIdx.x;
+    if (w >= nitems) return;
+    const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
+    const Item it = items[w];
+    const ProbDesc &P = descs[it.prob];
+    const int K = it.K;
+    const int fc = P.super_ptr[K];
+    const int s = P.super_ptr[K + 1] - fc;
+    const int64_t ld = P.rowptr[K + 1] - P.rowptr[K];
+    const int c = (int)(ld - s);
+    const int nsteps = ((c + 15) & ~15) / 16;
+    const int ncol = (s + TN - 1) / TN;
+    const int nch = it.ntiles;
+    const int ct = it.tile % ncol, ch = it.tile / ncol;
+    const int n0 = ct * TN;
+    const int chunk = ((nsteps + nch - 1) / nch + kTcFlush - 1) / kTcFlush * kTcFlush;
+    const int st0 = ch * chunk;
+    const int st1 = st0 + chunk < nsteps ? st0 + chunk : nsteps;
+    const int n = st1 > st0 ? st1 - st0 : 0;
+    const int nflush = (n + kTcFlush - 1) / kTcFlush;
+    const int64_t s64 = (s + 63) / 64 * 64;
+
+    if (tid == 0) s_abort = 0;
+    // both A stages start at zero: the bulk copies fill rows < s64 only
+    for (int e = tid; e < 2 * Cfg::A_STAGE / 8; e += kDtThreads) reinterpret_cast<uint4 *>(As)[e] = make_uint4(0, 0, 0, 0);
+
+    for (int j = tid; j < TN; j += kDtThreads) colE[j] = n0 + j < s ? P.colexpY[fc + n0 + j] : 0;
+    if (tid == 0) {
+        for (int st = 0; st < 2; st++) {
+            umma::mbar_init(&full[st], kDtProd + 1);   // + the arrival that expects A's bytes
+            umma::mbar_init(&empty[st], 1);
+        }
+        umma::mbar_init(&acc_full, 1);
+        umma::mbar_init(&tmem_free, kDtEpi);
+        umma::mbar_init_fence();
+    }
+    if (warp == kDtMmaWarp) {
+        umma::tmem_alloc(&s_tmem, Cfg::TCOLS);
+        umma::tmem_relinquish();
+    }
+    umma::fence_proxy_async();   // the zeroed A stages are seen by the tensor cores
+    umma::fence_before_sync();
+    __syncthreads();
+    umma::fence_after_sync();
+    const uint32_t tmem = s_tmem;
+
+    if (warp < kDtProd) {
+        // ---- producers: column r of the tile, rows kh*8 .. kh*8+7 of each 16-row step
+        const int r = tid % TN, kh = tid / TN;
+        const bool act = kh < 2;
+        const double *Yc = static_cast<const double *>(P.Z) + P.panel_off[K] + (int64_t)(n0 + r) * ld + s;
+        const bool colok = act && n0 + r < s;
+        const int E = colok ? colE[r] : 0;
+        double v[8], v2[8];      // the values of this step and of the next one
+        auto fetch = [&](double (&x)[8], int step) {
+#pragma unroll
+            for (int u = 0; u < 8; u++) {
+                const int q = step * 16 + kh * 8 + u;
+                x[u] = (colok && step < st1 && q < c) ? Yc[q] : 0.0;
+            }
+        };
+        if (n > 0) {
+            fetch(v, st0);
+            fetch(v2, st0 + 1);
+        }
+        for (int i_ = 0; i_ < n; i_++) {
+            const int stage = i_ & 1, use = i_ >> 1;
+            uint16_t *Bb = Bs + stage * Cfg::B_STAGE;
+            if (i_ >= 2 && !umma::mbar_wait(&empty[stage], (uint32_t)((use - 1) & 1), wait_limit)) {
+                s_abort = 1;
+                break;
+            }
+            if (act) {
+                uint32_t lo[8], hi[8];
+#pragma unroll
+                for (int u = 0; u < 8; u++) {
+                    const unsigned long long wv = (unsigned long long)(fixed54(v[u], E) + 0x80808080808080ll);
+                    lo[u] = (uint32_t)wv;
+                    hi[u] = (uint32_t)(wv >> 32);
+                }
+                uint16_t *dst = Bb + (r / 8) * 128 + kh * 64 + (r % 8) * 8;
+                store_plane<0>(dst + 0 * Cfg::B_PLANE, lo, hi);
+                store_plane<1>(dst + 1 * Cfg::B_PLANE, lo, hi);
+                store_plane<2>(dst + 2 * Cfg::B_PLANE, lo, hi);
+                store_plane<3>(dst + 3 * Cfg::B_PLANE, lo, hi);
+                store_plane<4>(dst + 4 * Cfg::B_PLANE, lo, hi);
+                store_plane<5>(dst + 5 * Cfg::B_PLANE, lo, hi);
+                store_plane<6>(dst + 6 * Cfg::B_PLANE, lo, hi);
+            }
+#pragma unroll
+            for (int u = 0; u < 8; u++) v[u] = v2[u];
+            if (i_ + 2 < n) fetch(v2, st0 + i_ + 2);
+            umma::fence_proxy_async();
+            __syncwarp();
+            if (lane == 0) umma::mbar_arrive(&full[stage]);
+            if (s_abort) break;
+        }
+    } else if (warp == kDtMmaWarp) {
+        // ---- one thread copies the Lhat digit planes and issues the products
+        if (lane == 0) {
+            const uint32_t idesc = umma::idesc_f16_f32(kTcM, TN);
+            const uint16_t *Au = P.lhsu + P.lhsu_off[K];
+            const uint32_t aBytes = (uint32_t)(s64 * 16 * 2);
+            auto load_a = [&](int i_) {
+                const int st = i_ & 1;
+                umma::mbar_arrive_expect_tx(&full[st], kTcDig * aBytes);
+#pragma unroll
+                for (int pl = 0; pl < kTcDig; pl++)
+                    umma::bulk_g2s(As + st * Cfg::A_STAGE + pl * Cfg::A_PLANE,
+                                   Au + ((int64_t)pl * nsteps + st0 + i_) * s64 * 16, aBytes, &full[st]);
+            };
+            if (n > 0) load_a(0);
+            for (int i_ = 0; i_ < n; i_++) {
+                const int stage = i_ & 1, use = i_ >> 1, chk = i_ / kTcFlush;
+                const bool first = i_ % kTcFlush == 0;
+                if (!umma::mbar_wait(&full[stage], (uint32_t)(use & 1), wait_limit) ||
+                    (first && chk > 0 && !umma::mbar_wait(&tmem_free, (uint32_t)((chk - 1) & 1), wait_limit))) {
+                    s_abort = 1;
+                    break;
+                }
+                umma::fence_after_sync();
+                const uint64_t ad0 = umma::smem_desc(umma::smem_u32(As + stage * Cfg::A_STAGE), 128, 256);
+                const uint64_t bd0 = umma::smem_desc(umma::smem_u32(Bs + stage * Cfg::B_STAGE), 128, 256);
+#pragma unroll
+                for (int i = 0; i < kTcDig; i++) {
+                    const uint64_t ad = ad0 + (uint64_t)(i * Cfg::A_PLANE * 2 / 16);
+#pragma unroll
+                    for (int j = 0; i + j < kTcDig; j++) {
+                        const uint64_t bd = bd0 + (uint64_t)(j * Cfg::B_PLANE * 2 / 16);
+                        umma::mma_f16kind(tmem + (uint32_t)((i + j) * TN), ad, bd, idesc, (first && i == 0) ? 0u : 1u);
+                    }
+                }
+                umma::commit(&empty[stage]);
+                if (i_ % kTcFlush == kTcFlush - 1 || i_ == n - 1) umma::commit(&acc_full);
+                if (i_ + 1 < n) {
+                    if (i_ >= 1 && !umma::mbar_wait(&empty[(i_ + 1) & 1], (uint32_t)((((i_ + 1) >> 1) - 1) & 1), wait_limit)) {
+                        s_abort = 1;
+                        break;
+                    }
+                    load_a(i_ + 1);
+                }
+                if (s_abort) break;
+            }
+        }
+        __syncwarp();
+    } else {
+        // ---- epilogue: every chunk's exact fp32 group sums -> int64 (hi, lo)
+        const int lb = 32 * (warp % 4), row = lb + lane;
+        for (int f = 0; f < nflush; f++) {
+            if (!umma::mbar_wait(&acc_full, (uint32_t)(f & 1), wait_limit)) {
+                s_abort = 1;
+                break;
+            }
+            umma::fence_after_sync();
+#pragma unroll 1
+            for (int cb = 0; cb < TN / 8; cb++) {
+                uint32_t acc[kTcDig][8];
+#pragma unroll
+                for (int gq = 0; gq < kTcDig; gq++)
+                    umma::tmem_ld8(tmem + ((uint32_t)lb << 16) + (uint32_t)(gq * TN + cb * 8), acc[gq]);
+                umma::tmem_wait_ld();
+#pragma unroll
+                for (int jj = 0; jj < 8; jj++) {
+                    long long gv[kTcDig];
+#pragma unroll
+                    for (int gq = 0; gq < kTcDig; gq++) gv[gq] = (long long)__float2int_rn(__uint_as_float(acc[gq][jj]));
+                    const long long h = (gv[0] << 16) + (gv[1] << 8) + gv[2];
+                    const long long l = (gv[3] << 24) + (gv[4] << 16) + (gv[5] << 8) + gv[6];
+                    long long *ph = Hi + (cb * 8 + jj) * kTcM + row, *pl = Lo + (cb * 8 + jj) * kTcM + row;
+                    if (f == 0) {   // the first chunk writes, the later ones add
+                        *ph = h;
+                        *pl = l;
+                    } else {
+                        *ph += h;
+                        *pl += l;
+                    }
+                }
+            }
+            umma::fence_before_sync();
+            __syncwarp();
+            if (lane == 0) umma::mbar_arrive(&tmem_free);
+            if (s_abort) break;
+        }
+    }
+    umma::fence_before_sync();
+    __syncthreads();
+    if (s_abort) {
+        if (tid == 0) atomicCAS(P.status, 0, SELINV_ERR_TIMEOUT);
+        if (warp == kDtMmaWarp && n > 0) umma::mbar_wait(&acc_full, (uint32_t)((nflush - 1) & 1), wait_limit);
+        __syncthreads();
+        if (warp == kDtMmaWarp) umma::tmem_dealloc(tmem, Cfg::TCOLS);
+        return;
+    }
+    if (warp == kDtMmaWarp) umma::tmem_dealloc(tmem, Cfg::TCOLS);
+    if (n == 0) return;
+    // the chunk's exact sums into K's (cleared at the start of every call):
+    // integer additions, so the order of chunks and column tiles does not matter
+    long long *acc64 = P.dacc + 2 * P.linv_off[K];
+    for (int e = tid; e < kTcM * TN; e += kDtThreads) {
+        const int i = e % kTcM, col = e / kTcM, j = n0 + col;
+        if (i >= s || j >= s) continue;
+        const long long hi = Hi[col * kTcM + i], lo = Lo[col * kTcM + i];
+        unsigned long long *dst = reinterpret_cast<unsigned long long *>(acc64 + 2 * ((int64_t)j * s + i));
+        if (hi) atomicAdd(dst, (unsigned long long)hi);
+        if (lo) atomicAdd(dst + 1, (unsigned long long)lo);
+    }
+}
+
+cudaError_t launch_diag_tc(int tn, const ProbDesc *d, const Item *items, int n, long long wait_limit,
+                           cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    if (tn == 32) k_diag_tc<32><<<n, kDtThreads, DtCfg<32>::SMEM, st>>>(d, items, n, wait_limit);
+    else k_diag_tc<64><<<n, kDtThreads, DtCfg<64>::SMEM, st>>>(d, items, n, wait_limit);
+    return cudaGetLastError();
+}
+
 cudaError_t configure_tc_kernels() {
     cudaError_t e = cudaFuncSetAttribute(k_selinv_tc<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TcCfg<16>::SMEM);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_selinv_tc<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TcCfg<32>::SMEM);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_selinv_tc<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TcCfg<64>::SMEM);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_diag_tc<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)DtCfg<32>::SMEM);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_diag_tc<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)DtCfg<64>::SMEM);
     return e;
 }
 

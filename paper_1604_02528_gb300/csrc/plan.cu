@@ -504,7 +504,7 @@ int build_schedule(Schedule &S, const std::vector<const PlanData *> &plans,
         if (cnt) S.launches.push_back({KL_TC_REDUCE, SELINV_F64, tl.bucket, off, cnt, tl.level});
     };
     // after a tensor-core diagonal-block launch: its finisher, (K, 8 columns) items
-    auto add_diag_fin = [&](const Launch dl) {
+    auto add_diag_fin = [&](const Launch dl, int bshift) {
         const int64_t off = (int64_t)S.h_items.size();
         for (int64_t e = dl.off; e < dl.off + dl.count; e++) {
             const Item it = S.h_items[e];
@@ -514,7 +514,7 @@ int build_schedule(Schedule &S, const std::vector<const PlanData *> &plans,
             for (int cb = 0; cb < (s + 7) / 8; cb++) S.h_items.push_back({it.prob, it.K, cb, 0});
         }
         const int cnt = (int)((int64_t)S.h_items.size() - off);
-        if (cnt) S.launches.push_back({KL_DIAG_FIN, SELINV_F64, 0, off, cnt, dl.level});
+        if (cnt) S.launches.push_back({KL_DIAG_FIN, SELINV_F64, bshift, off, cnt, dl.level});
     };
     // tensor-core diagonal block: (64-row tile, 32-column pass) items
     auto push_diag = [&](int i, int32_t K) {
@@ -523,6 +523,22 @@ int build_schedule(Schedule &S, const std::vector<const PlanData *> &plans,
         const int np = (s + kDiagCols - 1) / kDiagCols;
         for (int t = 0; t < p.ntiles[K]; t++)
             for (int jb = 0; jb < np; jb++) S.h_items.push_back({i, K, t * np + jb, p.ntiles[K] * np});
+    };
+    // tcgen05 diagonal block: (chunk of C rows, column tile of width tn) items,
+    // ntiles field = number of chunks; enough chunks for about a CTA per SM over
+    // the level (diag_units: the level's column tiles), 8 steps at least
+    auto dtc_tn = [](int s) { return s <= 32 ? 32 : 64; };
+    auto push_diag_tc = [&](int i, int32_t K, int64_t diag_units) {
+        const PlanData &p = *plans[i];
+        const int s = p.super_ptr[K + 1] - p.super_ptr[K];
+        const int64_t c = p.rowptr[K + 1] - p.rowptr[K] - s;
+        const int tn = dtc_tn(s), ncol = (s + tn - 1) / tn;
+        const int64_t nsteps = (c + 15) / 16;
+        const int64_t target = 152;    // a CTA per SM over the level
+        const int64_t want = (target + diag_units - 1) / std::max<int64_t>(diag_units, 1);
+        const int nch = (int)std::max<int64_t>(1, std::min(want, (nsteps + 7) / 8));
+        for (int ch = 0; ch < nch; ch++)
+            for (int ct = 0; ct < ncol; ct++) S.h_items.push_back({i, K, ch * ncol + ct, nch});
     };
     // tensor-core items: (row tile, column tile of width tn, k-range) triples,
     // ntiles field = number of k-ranges; c == 0 has none
@@ -665,10 +681,17 @@ int build_schedule(Schedule &S, const std::vector<const PlanData *> &plans,
                         if (use_tc(i)) add_tc_reduce(S.launches.back());
                     }
                     const int64_t off2 = (int64_t)S.h_items.size();
-                    push_diag(i, K);
-                    S.launches.push_back({KL_DIAG, descs[i].dtype, bucket_of(s), off2,
-                                          (int)(S.h_items.size() - off2), p.level[K]});
-                    add_diag_fin(S.launches.back());
+                    if (use_tc(i)) {
+                        push_diag_tc(i, K, (s + dtc_tn(s) - 1) / dtc_tn(s));
+                        S.launches.push_back({KL_DIAG_TC, descs[i].dtype, dtc_tn(s), off2,
+                                              (int)(S.h_items.size() - off2), p.level[K]});
+                        add_diag_fin(S.launches.back(), 1);
+                    } else {
+                        push_diag(i, K);
+                        S.launches.push_back({KL_DIAG, descs[i].dtype, bucket_of(s), off2,
+                                              (int)(S.h_items.size() - off2), p.level[K]});
+                        add_diag_fin(S.launches.back(), 0);
+                    }
                     continue;
                 }
                 const int64_t off = (int64_t)S.h_items.size();
@@ -711,12 +734,31 @@ int build_schedule(Schedule &S, const std::vector<const PlanData *> &plans,
                     }
                 }
             {
+                // diagonal blocks: tcgen05 (per column-tile width) or mma.sync
+                int64_t diag_units = 0;
+                for (auto &ik : oz) {
+                    const int s = plans[ik.first]->super_ptr[ik.second + 1] - plans[ik.first]->super_ptr[ik.second];
+                    if (use_tc(ik.first)) diag_units += (s + dtc_tn(s) - 1) / dtc_tn(s);
+                }
+                for (int tn : {64, 32}) {
+                    const int64_t off = (int64_t)S.h_items.size();
+                    for (auto &ik : oz) {
+                        const int s = plans[ik.first]->super_ptr[ik.second + 1] - plans[ik.first]->super_ptr[ik.second];
+                        if (use_tc(ik.first) && dtc_tn(s) == tn) push_diag_tc(ik.first, ik.second, diag_units);
+                    }
+                    const int cnt = (int)(S.h_items.size() - off);
+                    if (cnt) {
+                        S.launches.push_back({KL_DIAG_TC, SELINV_F64, tn, off, cnt, l});
+                        add_diag_fin(S.launches.back(), 1);
+                    }
+                }
                 const int64_t off = (int64_t)S.h_items.size();
-                for (auto &ik : oz) push_diag(ik.first, ik.second);
+                for (auto &ik : oz)
+                    if (!use_tc(ik.first)) push_diag(ik.first, ik.second);
                 const int cnt = (int)(S.h_items.size() - off);
                 if (cnt) {
                     S.launches.push_back({KL_DIAG, SELINV_F64, 0, off, cnt, l});
-                    add_diag_fin(S.launches.back());
+                    add_diag_fin(S.launches.back(), 0);
                 }
             }
             // fused DFMA kernel for everything else
@@ -749,7 +791,7 @@ int build_schedule(Schedule &S, const std::vector<const PlanData *> &plans,
     {
         std::vector<char> has(np, 0);
         for (const Launch &L : S.launches)
-            if (L.kind == KL_DIAG)
+            if (L.kind == KL_DIAG || L.kind == KL_DIAG_TC)
                 for (int64_t e = L.off; e < L.off + L.count; e++) has[S.h_items[e].prob] = 1;
         for (int i = 0; i < np; i++) {
             if (!has[i]) continue;
@@ -772,6 +814,7 @@ int build_schedule(Schedule &S, const std::vector<const PlanData *> &plans,
     if (tc_ctas > 0 &&
         cudaMalloc((void **)&S.tcslab, sizeof(long long) * (size_t)kTcSlotWords * (size_t)tc_ctas) != cudaSuccess)
         return SELINV_ERR_OOM;
+
     if (!S.h_red.empty() && (rc = upload(&S.d_red, S.h_red))) return rc;
     return SELINV_OK;
 }
@@ -793,7 +836,8 @@ cudaError_t launch_with(const Schedule &S, const Launch &L, const ProbDesc *d, c
         return launch_selinv_tc(L.bucket, d, S.d_items + L.off, L.count, S.tcslab, S.spin_limit, st);
     case KL_TC_REDUCE:
         return launch_tc_reduce(L.bucket, d, S.d_items, S.d_red + L.off, L.count, S.tcslab, st);
-    case KL_DIAG_FIN: return launch_diag_fin(d, S.d_items + L.off, L.count, st);
+    case KL_DIAG_FIN: return launch_diag_fin(d, S.d_items + L.off, L.count, L.bucket, st);
+    case KL_DIAG_TC: return launch_diag_tc(L.bucket, d, S.d_items + L.off, L.count, S.spin_limit, st);
     case KL_PUSH_DIAG: return launch_push(L.dtype, 0, L.bucket, d, S.d_items + L.off, L.count, st);
     case KL_PUSH: return launch_push(L.dtype, 1, L.bucket, d, S.d_items + L.off, L.count, st);
     case KL_PERSIST: {
