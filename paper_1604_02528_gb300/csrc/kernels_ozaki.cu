@@ -431,7 +431,7 @@ __global__ void __launch_bounds__(256) k_linv_digits(const ProbDesc *__restrict_
 // k = s <= 128: a single exact fp32 chunk.
 // ---------------------------------------------------------------------------
 template <int TN>
-__global__ void __launch_bounds__(kOzThreads, 1) k_lhat_oz(const ProbDesc *__restrict__ descs,
+__global__ void __launch_bounds__(kOzThreads, TN <= 32 ? 2 : 1) k_lhat_oz(const ProbDesc *__restrict__ descs,
                                                            const Item *__restrict__ items, int nitems) {
     constexpr int NT = TN / 16;
     extern __shared__ __align__(16) unsigned char smem_raw[];

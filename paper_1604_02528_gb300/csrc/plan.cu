@@ -441,7 +441,7 @@ int build_schedule(Schedule &S, const std::vector<const PlanData *> &plans,
                 const int s = p.super_ptr[K + 1] - p.super_ptr[K];
                 const int64_t c = p.rowptr[K + 1] - p.rowptr[K] - s;
                 if (c == 0 || !act(i, K) || !ozok(i, s)) continue;
-                const int ktn = s <= 16 ? 16 : (s <= 32 ? 32 : 64);
+                const int ktn = s <= 16 ? 16 : 32;   // 32-column tiles: two CTAs per SM
                 if (ktn != tn) continue;
                 const int ncol = (s + tn - 1) / tn;
                 for (int t = 0; t < p.ntiles[K]; t++)
