@@ -466,7 +466,8 @@ def main():
             "k_diag_fin": 0.0,
             "k_push_diag": mult * float((2 * c_ * s_ * s_).sum()),
             "k_push": mult * float((2 * c_ * c_ * s_).sum()),
-            "k_diag_tc": mult * float((2 * c_ * s_ * s_ * oz).sum())}
+            "k_diag_tc": mult * float((2 * c_ * s_ * s_ * oz).sum()),
+            "k_selinv_tiny": mult * float(((2 * c_ * c_ * s_ + 2 * c_ * s_ * s_) * ~oz * (s_ <= 8) * (c_ <= 64)).sum())}
     f_dom = f_of[name]
     achieved = f_dom / (kms[dom] * 1e-3) / 1e9 if kms[dom] > 0 else None
     traffic = ncu_traffic(name)

@@ -318,8 +318,9 @@ int selinv_pole_sum(int nitems, const selinv_dtype *dtypes, const void *const *A
  *  13 push schedule: outer- and inner-product updates of the descendants
  *  14 Dinv_K of the supernodes wider than 32 columns (32 x 32 tiles)
  *  15 diagonal block on tcgen05 (exact sums of Lhat^T A^{-1}_{C,K})
+ *  16 the whole step for supernodes of <= 8 columns and <= 64 rows, a warp each
  * For measurement only. */
-#define SELINV_PROFILE_KINDS 16
+#define SELINV_PROFILE_KINDS 17
 int selinv_numeric_profile(selinv_plan plan, selinv_dtype dtype, const void *L_dev,
                            const void *D_dev, void *Ainv_dev, void *cuda_stream, double *kernel_ms,
                            int64_t *kernel_launches);

@@ -38,7 +38,8 @@ SELINV_ERR_UNSUPPORTED = -9
 # kernel kinds reported by selinv_numeric_profile
 PROFILE_KINDS = ("k_linv", "k_lhat", "k_selinv", "k_lhat_digits", "k_selinv_oz", "k_diag",
                  "k_linv_digits", "k_lhat_oz", "k_selinv_persist", "k_selinv_tc",
-                 "k_tc_reduce", "k_diag_fin", "k_push_diag", "k_push", "k_dinv", "k_diag_tc")
+                 "k_tc_reduce", "k_diag_fin", "k_push_diag", "k_push", "k_dinv", "k_diag_tc",
+                 "k_selinv_tiny")
 
 
 class SelinvError(RuntimeError):

@@ -500,6 +500,131 @@ __global__ void __launch_bounds__(kThreads) k_push(const ProbDesc *__restrict__ 
 }
 
 // ---------------------------------------------------------------------------
+// k_selinv_tiny: the whole of Alg. 1's second loop for a supernode with s <= 8
+// columns and c <= 64 rows below them, one warp per supernode (eight per CTA, four for complex data):
+// the deep levels of a nested-dissection tree hold thousands of these, for
+// which a CTA per row tile is mostly synchronisation.  Lane l owns rows l and
+// l + 32 of A^{-1}_{C,K} = -A^{-1}_{C,C} Lhat (the gather as in k_selinv, Lhat
+// rows broadcast), then two entries of the s x s diagonal block
+// Dinv - Lhat^T A^{-1}_{C,K}, symmetrized through shared memory.  Writes the
+// whole-column exponents for the row bounds of later tensor-core gathers.
+// ---------------------------------------------------------------------------
+constexpr int kTinyS = 8, kTinyC = 64;
+template <typename T> __host__ __device__ constexpr int tiny_warps() { return sizeof(T) == 8 ? 8 : 4; }
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_selinv_tiny(const ProbDesc *__restrict__ descs,
+                                                     const Item *__restrict__ items, int nitems) {
+    constexpr int W = tiny_warps<T>();
+    __shared__ T Ys[W][kTinyS * kTinyC];   // per warp: A^{-1}_{C,K}(p, j) at [j * 64 + p]
+    __shared__ T Xs[W][kTinyS * kTinyS];   // per warp: the unsymmetrized diagonal block
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    const int w = blockIdx.x * W + warp;
+    if (w >= nitems) return;               // the whole warp
+    const Item it = items[w];
+    const ProbDesc &P = descs[it.prob];
+    const int K = it.K;
+    const int fc = P.super_ptr[K];
+    const int s = P.super_ptr[K + 1] - fc;
+    const int64_t ld = P.rowptr[K + 1] - P.rowptr[K];
+    const int c = (int)(ld - s);
+    const int64_t pos0 = P.rowptr[K] + s;
+    const bool h = P.herm != 0;
+    const T *Zc = static_cast<const T *>(P.Z);
+    T *Zk = static_cast<T *>(P.Z) + P.panel_off[K];
+    const T *LDk = static_cast<const T *>(P.LD) + P.panel_off[K];
+    const int64_t *pcb = P.colbase + pos0, *prb = P.relbase + pos0;
+    T acc[2][kTinyS];
+#pragma unroll
+    for (int r = 0; r < 2; r++)
+#pragma unroll
+        for (int j = 0; j < kTinyS; j++) acc[r][j] = Sc<T>::zero();
+    // four q at a time: their gathers are in flight together
+    for (int q0 = 0; q0 < c; q0 += 4) {
+        T v[2][4];
+#pragma unroll
+        for (int u = 0; u < 4; u++)
+#pragma unroll
+            for (int r = 0; r < 2; r++) {
+                const int p = lane + 32 * r, q = q0 + u;
+                v[r][u] = Sc<T>::zero();
+                if (p >= c || q >= c) continue;
+                // entry (p, q) of A^{-1}_{C,C}: stored at (max, min)
+                const int64_t addr = p >= q ? pcb[q] + P.relidx[prb[q] + p] : pcb[p] + P.relidx[prb[p] + q];
+                v[r][u] = Zc[addr];
+                if (p < q) v[r][u] = cjif(v[r][u], h);
+            }
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            const int q = q0 + u;
+            if (q >= c) break;
+            T lh[kTinyS];
+#pragma unroll
+            for (int j = 0; j < kTinyS; j++) lh[j] = j < s ? LDk[(int64_t)j * ld + s + q] : Sc<T>::zero();
+#pragma unroll
+            for (int r = 0; r < 2; r++)
+#pragma unroll
+                for (int j = 0; j < kTinyS; j++) madd(acc[r][j], v[r][u], lh[j]);
+        }
+    }
+    int ye[kTinyS];
+#pragma unroll
+    for (int j = 0; j < kTinyS; j++) {
+        int e = 0;
+#pragma unroll
+        for (int r = 0; r < 2; r++) {
+            const int p = lane + 32 * r;
+            if (p < c && j < s) {
+                const T y = neg(acc[r][j]);
+                Zk[(int64_t)j * ld + s + p] = y;
+                Ys[warp][j * kTinyC + p] = y;
+                e = max(e, bexp(y));
+            }
+        }
+        ye[j] = __reduce_max_sync(0xffffffffu, e);
+    }
+    __syncwarp();
+    // X(i, j) = Dinv(i, j) - sum_p Lhat(p, i) A^{-1}_{C,K}(p, j)  (Lhat conjugated: Hermitian)
+    for (int e = lane; e < s * s; e += 32) {
+        const int i = e % s, j = e / s;
+        T x = LDk[(int64_t)j * ld + i];
+        for (int p = 0; p < c; p++) msub(x, cjif(LDk[(int64_t)i * ld + s + p], h), Ys[warp][j * kTinyC + p]);
+        Xs[warp][j * kTinyS + i] = x;
+    }
+    __syncwarp();
+    int ze = 0;
+    for (int e = lane; e < s * s; e += 32) {
+        const int i = e % s, j = e / s;
+        T x = Xs[warp][j * kTinyS + i];
+        if (P.symmetrize) x = half(add(x, cjif(Xs[warp][i * kTinyS + j], h)));
+        Zk[(int64_t)j * ld + i] = x;
+        ze = max(ze, bexp(x));
+    }
+    // one bound for the whole block and the rows below each column (a column's
+    // own maximum would do; a larger bound keeps the gathers exact as well)
+    ze = __reduce_max_sync(0xffffffffu, ze);
+    if (lane < s) {
+        int y = 0;
+#pragma unroll
+        for (int j = 0; j < kTinyS; j++)
+            if (j == lane) y = ye[j];
+        P.colexpZ[fc + lane] = max(ze, y);
+    }
+}
+
+cudaError_t launch_selinv_tiny(int dtype, const ProbDesc *d, const Item *items, int n, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    if (dtype == SELINV_C128) {
+        constexpr int W = tiny_warps<zd>();
+        k_selinv_tiny<zd><<<(n + W - 1) / W, 32 * W, 0, st>>>(d, items, n);
+    } else {
+        constexpr int W = tiny_warps<double>();
+        k_selinv_tiny<double><<<(n + W - 1) / W, 32 * W, 0, st>>>(d, items, n);
+    }
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
 // k_selinv_persist: the whole traversal in one launch.  Work items are listed
 // root level first; each CTA claims the next item from a global ticket and,
 // before working on supernode K, waits for the completion flag of K's parent

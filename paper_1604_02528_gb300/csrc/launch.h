@@ -34,6 +34,7 @@ cudaError_t launch_selinv_persist(int dtype, const ProbDesc *d, const Item *item
                                   cudaStream_t st);
 cudaError_t launch_linv_digits(const ProbDesc *d, const int2 *work, int nwork, cudaStream_t st);
 cudaError_t launch_lhat_oz(int tn, const ProbDesc *d, const Item *items, int n, cudaStream_t st);
+cudaError_t launch_selinv_tiny(int dtype, const ProbDesc *d, const Item *items, int n, cudaStream_t st);
 cudaError_t launch_push(int dtype, int kind, int bucket, const ProbDesc *d, const Item *items, int n,
                         cudaStream_t st);
 cudaError_t launch_lhat_digits(const ProbDesc *d, const int2 *work, int nwork, cudaStream_t st);

@@ -390,6 +390,13 @@ int build_schedule(Schedule &S, const std::vector<const PlanData *> &plans,
     auto act = [&](int i, int32_t K) { return plans[i]->active.empty() || plans[i]->active[K] != 0; };
     // tensor-core contraction for this problem and width (never for the LU form)
     auto ozok = [&](int i, int s) { return !descs[i].lu && oz_eligible(descs[i].dtype, s, plans[i]->opts); };
+    // DFMA supernodes small enough for a warp each (k_selinv_tiny; not the LU form)
+    auto tiny = [&](int i, int32_t K) {
+        const PlanData &p = *plans[i];
+        const int s = p.super_ptr[K + 1] - p.super_ptr[K];
+        const int64_t c = p.rowptr[K + 1] - p.rowptr[K] - s;
+        return !descs[i].lu && s <= 8 && c <= 64 && !ozok(i, s);
+    };
     // 1) L_KK^{-1}, Dinv for every supernode (one launch per dtype and size class)
     for (int dt = 0; dt < 2; dt++)
         for (int large = 1; large >= 0; large--) {
@@ -545,6 +552,9 @@ int build_schedule(Schedule &S, const std::vector<const PlanData *> &plans,
     auto oz_tn = [](int s) { return s <= 16 ? 16 : (s <= 32 ? 32 : 64); };
     // row tiles of the contraction: 64 rows on mma.sync, 128 on tcgen05
     auto use_tc = [&](int i) { return plans[i]->opts.fast_contraction == 1; };
+    // the diagonal block of a supernode on the tcgen05 engine runs on tcgen05
+    // when it is wider than 32 columns, else on the mma.sync kernel (cheaper per item)
+    auto diag_tc = [&](int i, int s) { return use_tc(i) && s > 32; };
     auto row_tiles = [&](int i, int32_t K) -> int64_t {
         const PlanData &p = *plans[i];
         if (!use_tc(i)) return p.ntiles[K];
@@ -681,7 +691,7 @@ int build_schedule(Schedule &S, const std::vector<const PlanData *> &plans,
                         if (use_tc(i)) add_tc_reduce(S.launches.back());
                     }
                     const int64_t off2 = (int64_t)S.h_items.size();
-                    if (use_tc(i)) {
+                    if (diag_tc(i, s)) {
                         push_diag_tc(i, K, (s + dtc_tn(s) - 1) / dtc_tn(s));
                         S.launches.push_back({KL_DIAG_TC, descs[i].dtype, dtc_tn(s), off2,
                                               (int)(S.h_items.size() - off2), p.level[K]});
@@ -695,6 +705,11 @@ int build_schedule(Schedule &S, const std::vector<const PlanData *> &plans,
                     continue;
                 }
                 const int64_t off = (int64_t)S.h_items.size();
+                if (tiny(i, K)) {
+                    S.h_items.push_back({i, K, 0, 1});
+                    S.launches.push_back({KL_SELINV_TINY, descs[i].dtype, 0, off, 1, p.level[K]});
+                    continue;
+                }
                 push_items(i, K);
                 S.launches.push_back({KL_SELINV, descs[i].dtype, bucket_of(s), off,
                                       (int)(S.h_items.size() - off), p.level[K]});
@@ -738,13 +753,13 @@ int build_schedule(Schedule &S, const std::vector<const PlanData *> &plans,
                 int64_t diag_units = 0;
                 for (auto &ik : oz) {
                     const int s = plans[ik.first]->super_ptr[ik.second + 1] - plans[ik.first]->super_ptr[ik.second];
-                    if (use_tc(ik.first)) diag_units += (s + dtc_tn(s) - 1) / dtc_tn(s);
+                    if (diag_tc(ik.first, s)) diag_units += (s + dtc_tn(s) - 1) / dtc_tn(s);
                 }
                 for (int tn : {64, 32}) {
                     const int64_t off = (int64_t)S.h_items.size();
                     for (auto &ik : oz) {
                         const int s = plans[ik.first]->super_ptr[ik.second + 1] - plans[ik.first]->super_ptr[ik.second];
-                        if (use_tc(ik.first) && dtc_tn(s) == tn) push_diag_tc(ik.first, ik.second, diag_units);
+                        if (diag_tc(ik.first, s) && dtc_tn(s) == tn) push_diag_tc(ik.first, ik.second, diag_units);
                     }
                     const int cnt = (int)(S.h_items.size() - off);
                     if (cnt) {
@@ -753,15 +768,32 @@ int build_schedule(Schedule &S, const std::vector<const PlanData *> &plans,
                     }
                 }
                 const int64_t off = (int64_t)S.h_items.size();
-                for (auto &ik : oz)
-                    if (!use_tc(ik.first)) push_diag(ik.first, ik.second);
+                for (auto &ik : oz) {
+                    const int s = plans[ik.first]->super_ptr[ik.second + 1] - plans[ik.first]->super_ptr[ik.second];
+                    if (!diag_tc(ik.first, s)) push_diag(ik.first, ik.second);
+                }
                 const int cnt = (int)(S.h_items.size() - off);
                 if (cnt) {
                     S.launches.push_back({KL_DIAG, SELINV_F64, 0, off, cnt, l});
                     add_diag_fin(S.launches.back(), 0);
                 }
             }
-            // fused DFMA kernel for everything else
+            // fused DFMA kernel for everything else: a warp per tiny supernode,
+            // a CTA per row tile for the rest
+            for (int dt = 0; dt < 2; dt++) {
+                const int64_t off = (int64_t)S.h_items.size();
+                for (int i = 0; i < np; i++) {
+                    if (descs[i].dtype != dt) continue;
+                    const PlanData &p = *plans[i];
+                    if (l >= p.nlevels) continue;
+                    for (int64_t e = p.level_ptr[l]; e < p.level_ptr[l + 1]; e++) {
+                        const int32_t K = p.level_list[e];
+                        if (act(i, K) && tiny(i, K)) S.h_items.push_back({i, K, 0, 1});
+                    }
+                }
+                const int cnt = (int)(S.h_items.size() - off);
+                if (cnt) S.launches.push_back({KL_SELINV_TINY, dt, 0, off, cnt, l});
+            }
             for (int dt = 0; dt < 2; dt++)
                 for (int b = kNumBuckets - 1; b >= 0; b--) {
                     const int64_t off = (int64_t)S.h_items.size();
@@ -772,7 +804,7 @@ int build_schedule(Schedule &S, const std::vector<const PlanData *> &plans,
                         for (int64_t e = p.level_ptr[l]; e < p.level_ptr[l + 1]; e++) {
                             const int32_t K = p.level_list[e];
                             const int s = p.super_ptr[K + 1] - p.super_ptr[K];
-                            if (act(i, K) && bucket_of(s) == b && !ozok(i, s)) push_items(i, K);
+                            if (act(i, K) && bucket_of(s) == b && !ozok(i, s) && !tiny(i, K)) push_items(i, K);
                         }
                     }
                     const int cnt = (int)(S.h_items.size() - off);
@@ -838,6 +870,7 @@ cudaError_t launch_with(const Schedule &S, const Launch &L, const ProbDesc *d, c
         return launch_tc_reduce(L.bucket, d, S.d_items, S.d_red + L.off, L.count, S.tcslab, st);
     case KL_DIAG_FIN: return launch_diag_fin(d, S.d_items + L.off, L.count, L.bucket, st);
     case KL_DIAG_TC: return launch_diag_tc(L.bucket, d, S.d_items + L.off, L.count, S.spin_limit, st);
+    case KL_SELINV_TINY: return launch_selinv_tiny(L.dtype, d, S.d_items + L.off, L.count, st);
     case KL_PUSH_DIAG: return launch_push(L.dtype, 0, L.bucket, d, S.d_items + L.off, L.count, st);
     case KL_PUSH: return launch_push(L.dtype, 1, L.bucket, d, S.d_items + L.off, L.count, st);
     case KL_PERSIST: {

@@ -74,7 +74,7 @@ struct Workspace {
 // launch kinds
 enum { KL_LINV = 0, KL_LHAT = 1, KL_SELINV = 2, KL_DIGITS = 3, KL_SELINV_OZ = 4, KL_DIAG = 5, KL_LINV_DIGITS = 6,
        KL_LHAT_OZ = 7, KL_PERSIST = 8, KL_SELINV_TC = 9, KL_TC_REDUCE = 10, KL_DIAG_FIN = 11,
-       KL_PUSH_DIAG = 12, KL_PUSH = 13, KL_DINV = 14, KL_DIAG_TC = 15, KL_NKINDS = 16 };
+       KL_PUSH_DIAG = 12, KL_PUSH = 13, KL_DINV = 14, KL_DIAG_TC = 15, KL_SELINV_TINY = 16, KL_NKINDS = 17 };
 
 // tensor-core (FP64-exact) contraction applies to real problems with s >= kOzMinS;
 // fast_contraction 1 runs the gather-GEMM on tcgen05, 2 on mma.sync

@@ -3,8 +3,11 @@ root-level-first order and wait on their parent's completion flag), its
 bounded waits, and the input checks.
 
 The persistent traversal runs the DFMA kernel of the level schedule item by
-item, so with the DFMA path forced on both sides the two schedules agree bit
-for bit; every output is also held to the oracle's tolerance.
+item (the level schedule gives supernodes of at most 8 columns and 64 rows a
+warp each instead, another summation order), so with the DFMA path forced on
+both sides the two schedules agree to rounding; every output is also held to
+the oracle's tolerance, and the persistent schedule with and without a CUDA
+graph agree bit for bit.
 """
 import numpy as np
 import pytest
@@ -57,8 +60,8 @@ def test_persistent_matches_level_and_oracle(native, cuda_device, name, make):
     G_per, st1 = run(native, plan, L, D, schedule=native.SELINV_SCHED_PERSISTENT, fast_contraction=0)
     G_gr, st2 = run(native, plan, L, D, schedule=native.SELINV_SCHED_PERSISTENT, fast_contraction=0, use_graph=0)
     assert st0 == st1 == st2 == 0
-    assert np.array_equal(G_per, G_lvl)
-    assert np.array_equal(G_gr, G_lvl)
+    assert oracle.block_errors(sym, G_per, G_lvl).max() <= 1e-13
+    assert np.array_equal(G_gr, G_per)
     assert oracle.block_errors(sym, G_per, Z).max() <= TOL
     # default options (tensor-core normalization where eligible), run twice on
     # the same buffers: flags and ticket are reset by every call
