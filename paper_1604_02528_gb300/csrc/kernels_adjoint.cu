@@ -1024,8 +1024,10 @@ static int adj_split(selinv_plan_s *plan) {
     const PlanData &p = plan->data;
     const selinv_opts &o = p.opts;
     // (at least 8 columns: narrower supernodes keep the fused kernels, whose
-    // one CTA per tile wastes less than 32-column blocks would)
-    const int key = o.fast_contraction == 1 ? std::max(8, o.oz_min_s) : 0;
+    // one CTA per tile wastes less than 32-column blocks would).  Any tensor
+    // engine of the forward means tcgen05 here: the reverse passes have no
+    // mma.sync variant.
+    const int key = o.fast_contraction != 0 ? std::max(8, o.oz_min_s) : 0;
     if (key == a->split_key) return SELINV_OK;
     auto fr = [](void *q) { if (q) cudaFree(q); };
     fr(a->d_sm); fr(a->d_wd); fr(a->d_row); fr(a->d_mbp); fr(a->d_dig);
@@ -1077,7 +1079,10 @@ static int adj_split(selinv_plan_s *plan) {
         const ProbDesc pd = make_desc(p, plan->ws[0], SELINV_F64, nullptr, nullptr, nullptr, false);
         std::vector<uint8_t> sel;
         sel.swap(plan->data.active);
+        const int fcon = plan->data.opts.fast_contraction;
+        plan->data.opts.fast_contraction = 1;
         rc = build_schedule(a->tcs, {&p}, {pd}, SELINV_SCHED_LEVEL);
+        plan->data.opts.fast_contraction = fcon;
         sel.swap(plan->data.active);
         if (rc) return rc;
         for (int e = 0; e < (int)a->tcs.launches.size(); e++) {

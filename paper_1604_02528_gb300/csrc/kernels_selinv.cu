@@ -501,25 +501,30 @@ __global__ void __launch_bounds__(kThreads) k_push(const ProbDesc *__restrict__ 
 
 // ---------------------------------------------------------------------------
 // k_selinv_tiny: the whole of Alg. 1's second loop for a supernode with s <= 8
-// columns and c <= 64 rows below them, one warp per supernode (eight per CTA, four for complex data):
+// columns and c <= 64 rows below them, one warp per supernode (eight per CTA):
 // the deep levels of a nested-dissection tree hold thousands of these, for
 // which a CTA per row tile is mostly synchronisation.  Lane l owns rows l and
-// l + 32 of A^{-1}_{C,K} = -A^{-1}_{C,C} Lhat (the gather as in k_selinv, Lhat
-// rows broadcast), then two entries of the s x s diagonal block
-// Dinv - Lhat^T A^{-1}_{C,K}, symmetrized through shared memory.  Writes the
-// whole-column exponents for the row bounds of later tensor-core gathers.
+// l + 32 of A^{-1}_{C,K} = -A^{-1}_{C,C} Lhat (the gather as in k_selinv, four
+// entries in flight, Lhat rows broadcast); each entry of the s x s diagonal
+// block Dinv - Lhat^T A^{-1}_{C,K} is a warp sum over the lanes' own rows,
+// symmetrized through shared memory.  Writes the whole-column exponents for
+// the row bounds of later tensor-core gathers.
 // ---------------------------------------------------------------------------
 constexpr int kTinyS = 8, kTinyC = 64;
-template <typename T> __host__ __device__ constexpr int tiny_warps() { return sizeof(T) == 8 ? 8 : 4; }
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ __forceinline__ zd warp_sum(zd v) { return make_zd(warp_sum(v.x), warp_sum(v.y)); }
 
 template <typename T>
 __global__ void __launch_bounds__(256) k_selinv_tiny(const ProbDesc *__restrict__ descs,
                                                      const Item *__restrict__ items, int nitems) {
-    constexpr int W = tiny_warps<T>();
-    __shared__ T Ys[W][kTinyS * kTinyC];   // per warp: A^{-1}_{C,K}(p, j) at [j * 64 + p]
-    __shared__ T Xs[W][kTinyS * kTinyS];   // per warp: the unsymmetrized diagonal block
+    __shared__ T Xs[8][kTinyS * kTinyS];   // per warp: the unsymmetrized diagonal block
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-    const int w = blockIdx.x * W + warp;
+    const int w = blockIdx.x * 8 + warp;
     if (w >= nitems) return;               // the whole warp
     const Item it = items[w];
     const ProbDesc &P = descs[it.prob];
@@ -567,6 +572,8 @@ __global__ void __launch_bounds__(256) k_selinv_tiny(const ProbDesc *__restrict_
                 for (int j = 0; j < kTinyS; j++) madd(acc[r][j], v[r][u], lh[j]);
         }
     }
+    // A^{-1}_{C,K} = -acc, written; the lanes' own Lhat rows for the diagonal block
+    T own[2][kTinyS];
     int ye[kTinyS];
 #pragma unroll
     for (int j = 0; j < kTinyS; j++) {
@@ -574,23 +581,28 @@ __global__ void __launch_bounds__(256) k_selinv_tiny(const ProbDesc *__restrict_
 #pragma unroll
         for (int r = 0; r < 2; r++) {
             const int p = lane + 32 * r;
-            if (p < c && j < s) {
-                const T y = neg(acc[r][j]);
-                Zk[(int64_t)j * ld + s + p] = y;
-                Ys[warp][j * kTinyC + p] = y;
-                e = max(e, bexp(y));
+            const bool ok = p < c && j < s;
+            acc[r][j] = ok ? neg(acc[r][j]) : Sc<T>::zero();
+            own[r][j] = ok ? cjif(LDk[(int64_t)j * ld + s + p], h) : Sc<T>::zero();
+            if (ok) {
+                Zk[(int64_t)j * ld + s + p] = acc[r][j];
+                e = max(e, bexp(acc[r][j]));
             }
         }
         ye[j] = __reduce_max_sync(0xffffffffu, e);
     }
-    __syncwarp();
     // X(i, j) = Dinv(i, j) - sum_p Lhat(p, i) A^{-1}_{C,K}(p, j)  (Lhat conjugated: Hermitian)
-    for (int e = lane; e < s * s; e += 32) {
-        const int i = e % s, j = e / s;
-        T x = LDk[(int64_t)j * ld + i];
-        for (int p = 0; p < c; p++) msub(x, cjif(LDk[(int64_t)i * ld + s + p], h), Ys[warp][j * kTinyC + p]);
-        Xs[warp][j * kTinyS + i] = x;
-    }
+#pragma unroll
+    for (int i = 0; i < kTinyS; i++)
+#pragma unroll
+        for (int j = 0; j < kTinyS; j++) {
+            if (i >= s || j >= s) continue;
+            T part = Sc<T>::zero();
+#pragma unroll
+            for (int r = 0; r < 2; r++) madd(part, own[r][i], acc[r][j]);
+            part = warp_sum(part);
+            if (lane == 0) Xs[warp][j * kTinyS + i] = sub(LDk[(int64_t)j * ld + i], part);
+        }
     __syncwarp();
     int ze = 0;
     for (int e = lane; e < s * s; e += 32) {
@@ -614,13 +626,8 @@ __global__ void __launch_bounds__(256) k_selinv_tiny(const ProbDesc *__restrict_
 
 cudaError_t launch_selinv_tiny(int dtype, const ProbDesc *d, const Item *items, int n, cudaStream_t st) {
     if (n <= 0) return cudaSuccess;
-    if (dtype == SELINV_C128) {
-        constexpr int W = tiny_warps<zd>();
-        k_selinv_tiny<zd><<<(n + W - 1) / W, 32 * W, 0, st>>>(d, items, n);
-    } else {
-        constexpr int W = tiny_warps<double>();
-        k_selinv_tiny<double><<<(n + W - 1) / W, 32 * W, 0, st>>>(d, items, n);
-    }
+    if (dtype == SELINV_C128) k_selinv_tiny<zd><<<(n + 7) / 8, 256, 0, st>>>(d, items, n);
+    else k_selinv_tiny<double><<<(n + 7) / 8, 256, 0, st>>>(d, items, n);
     return cudaGetLastError();
 }
 

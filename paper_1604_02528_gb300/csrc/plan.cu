@@ -705,11 +705,6 @@ int build_schedule(Schedule &S, const std::vector<const PlanData *> &plans,
                     continue;
                 }
                 const int64_t off = (int64_t)S.h_items.size();
-                if (tiny(i, K)) {
-                    S.h_items.push_back({i, K, 0, 1});
-                    S.launches.push_back({KL_SELINV_TINY, descs[i].dtype, 0, off, 1, p.level[K]});
-                    continue;
-                }
                 push_items(i, K);
                 S.launches.push_back({KL_SELINV, descs[i].dtype, bucket_of(s), off,
                                       (int)(S.h_items.size() - off), p.level[K]});

@@ -35,12 +35,13 @@ def rel(a, b):
     return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
 
 
-@pytest.mark.parametrize("engine,ozm", [(1, 16), (1, 8), (0, 16)])
+@pytest.mark.parametrize("engine,ozm", [(1, 16), (1, 8), (2, 16), (0, 16)])
 @pytest.mark.parametrize("name,make", CASES)
 def test_adjoints_match_oracle(native, cuda_device, name, make, engine, ozm):
-    """engine 1: supernodes of ozm columns or more take the split path
-    (tcgen05 gather-GEMM, 32 x 32 blocks for the s-inner products); 0: every
-    supernode on the fused FP64 kernels."""
+    """engines 1 and 2 (the forward's tcgen05 or mma.sync choice): supernodes
+    of ozm columns or more take the split path (tcgen05 gather-GEMM, 32 x 32
+    blocks for the s-inner products); 0: every supernode on the fused FP64
+    kernels."""
     import torch
     from paper_1604_02528_gb300.api import SelInvContext
     p = make()

@@ -84,7 +84,8 @@ def test_schedules_and_graphs_agree_bitwise(native, cuda_device, name, make):
     G_plain, _ = gpu_selinv(native, sym, L, D, schedule=0, use_graph=0, plan=plan)
     G_nograph, _ = gpu_selinv(native, sym, L, D, schedule=1, use_graph=0, plan=plan)
     G_rep, _ = gpu_selinv(native, sym, L, D, schedule=1, use_graph=1, plan=plan, repeat=3)
-    assert np.array_equal(G_level, G_plain)
+    # plain runs every DFMA supernode as CTA tiles, level the tiniest as a warp each
+    assert oracle.block_errors(sym, G_level, G_plain).max() <= 1e-13
     assert np.array_equal(G_level, G_nograph)
     assert np.array_equal(G_level, G_rep)
     assert oracle.block_errors(sym, G_level, Z).max() <= TOL
