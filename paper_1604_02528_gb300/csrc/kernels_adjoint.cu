@@ -75,6 +75,9 @@ struct AdjData {
     std::vector<int2> cz_work;         // per level: (J, 8-column block)
     std::vector<int64_t> cz_lptr;
     int2 *d_cz = nullptr;
+    std::vector<int4> vitems;          // per level: (J, 32-row tile, 32-column tile) of the lower c x c
+    std::vector<int64_t> v_lptr;
+    int4 *d_vitems = nullptr;
     std::vector<int64_t> g_lptr, c_lptr, j_lptr;
     double *V = nullptr;  // update matrices (tables shared with the factorization)
     Item *d_items = nullptr, *d_lhat = nullptr;
@@ -139,11 +142,13 @@ __global__ void __launch_bounds__(256) k_adj_asm(const AdjDesc *__restrict__ ad,
     }
 }
 
-// V_K -= sym(Ybar Lhat^T) on one 64 x 64 tile of the lower c x c triangle:
-// [Ybar, Lhat] [Lhat, Ybar]^T over k' < 2s, the diagonal counted once
+// V_K -= sym(Ybar Lhat^T) on one 32 x 32 tile of the lower c x c triangle
+// (four times the CTAs of 64 x 64 tiles for the few supernodes of the top
+// levels): [Ybar, Lhat] [Lhat, Ybar]^T over k' < 2s, the diagonal counted once
+constexpr int kVB = 32;
 __global__ void __launch_bounds__(256) k_adj_vupd(const AdjDesc *__restrict__ ad, const int4 *__restrict__ items,
                                                   int nitems) {
-    __shared__ SegSmem<double> sm;
+    __shared__ SegSmem<double, kVB> sm;
     const int w = blockIdx.x;
     if (w >= nitems) return;
     const AdjDesc &A = *ad;
@@ -154,8 +159,8 @@ __global__ void __launch_bounds__(256) k_adj_vupd(const AdjDesc *__restrict__ ad
     const double *Yb = A.YB + A.panel_off[K] + sK;   // Ybar(p, k) = Yb[k*ld + p]
     const double *Lh = A.LD + A.panel_off[K] + sK;   // Lhat(p, k)
     double *VK = A.V + A.v_off[K];
-    const int pa = ti * kSegB, st = tj * kSegB;
-    const int np = c - pa < kSegB ? c - pa : kSegB, nq = c - st < kSegB ? c - st : kSegB;
+    const int pa = ti * kVB, st = tj * kVB;
+    const int np = c - pa < kVB ? c - pa : kVB, nq = c - st < kVB ? c - st : kVB;
     auto x = [&](int pl, int k) {
         return k < sK ? Yb[(int64_t)k * ld + pa + pl] : Lh[(int64_t)(k - sK) * ld + pa + pl];
     };
@@ -166,7 +171,7 @@ __global__ void __launch_bounds__(256) k_adj_vupd(const AdjDesc *__restrict__ ad
         if (pa + pl == st + ql) v *= 0.5;
         VK[(int64_t)(st + ql) * c + pa + pl] -= v;
     };
-    seg_update<double>(pa, np, st, nq, 2 * sK, x, y, out, sm);
+    seg_update<double, decltype(x), decltype(y), decltype(out), kVB>(pa, np, st, nq, 2 * sK, x, y, out, sm);
 }
 
 // S (tile 0) and Ybar rows of one tile
@@ -877,7 +882,7 @@ void adjoint_release(void *p) {
     if (!a) return;
     auto fr = [](void *q) { if (q) cudaFree(q); };
     fr(a->d_items); fr(a->d_lhat); fr(a->d_linv);
-    fr(a->d_gitems); fr(a->d_citems); fr(a->d_js); fr(a->d_cz);
+    fr(a->d_gitems); fr(a->d_citems); fr(a->d_js); fr(a->d_cz); fr(a->d_vitems);
     fr(a->YB); fr(a->Zb); fr(a->Lbw); fr(a->Ab); fr(a->fin); fr(a->d_desc); fr(a->d_pdesc);
     fr(a->V);
     fr(a->d_sm); fr(a->d_wd); fr(a->d_row); fr(a->d_mbp); fr(a->d_dig); fr(a->d_tcdesc); fr(a->cy);
@@ -915,6 +920,7 @@ static int adj_build(selinv_plan_s *plan) {
         }
     }
     a->g_lptr.assign(1, 0); a->c_lptr.assign(1, 0); a->j_lptr.assign(1, 0); a->cz_lptr.assign(1, 0);
+    a->v_lptr.assign(1, 0);
     for (int l = p.nlevels - 1; l >= 0; l--) {      // deepest first, like every list here
         for (int64_t e = p.level_ptr[l]; e < p.level_ptr[l + 1]; e++) {
             const int32_t J = p.level_list[e];
@@ -925,8 +931,13 @@ static int adj_build(selinv_plan_s *plan) {
             for (int ch = 0; ch < nch; ch++) a->citems.push_back(make_int2(J, ch | (p.ntiles[J] << 16)));
             a->js.push_back(J);
             for (int jb = 0; jb < (s + 7) / 8; jb++) a->cz_work.push_back(make_int2(J, jb));
+            const int64_t cJ = p.rowptr[J + 1] - p.rowptr[J] - s;
+            const int nvt = (int)((cJ + kVB - 1) / kVB);
+            for (int ti = 0; ti < nvt; ti++)
+                for (int tj = 0; tj <= ti; tj++) a->vitems.push_back(make_int4(J, ti, tj, 0));
         }
         a->cz_lptr.push_back((int64_t)a->cz_work.size());
+        a->v_lptr.push_back((int64_t)a->vitems.size());
         a->g_lptr.push_back((int64_t)a->gitems.size());
         a->c_lptr.push_back((int64_t)a->citems.size());
         a->j_lptr.push_back((int64_t)a->js.size());
@@ -949,7 +960,7 @@ static int adj_build(selinv_plan_s *plan) {
     if ((rc = upl(&a->d_items, a->items)) || (rc = upl(&a->d_lhat, a->lhat_items)) ||
         (rc = upl(&a->d_linv, a->linv_work)) ||
         (rc = upl(&a->d_gitems, a->gitems)) || (rc = upl(&a->d_citems, a->citems)) || (rc = upl(&a->d_js, a->js)) ||
-        (rc = upl(&a->d_cz, a->cz_work))) {
+        (rc = upl(&a->d_cz, a->cz_work)) || (rc = upl(&a->d_vitems, a->vitems))) {
         adjoint_release(a);
         return rc;
     }
@@ -1168,8 +1179,8 @@ extern "C" int selinv_adjoint(selinv_plan plan, selinv_dtype dtype, const void *
         const int r0 = (int)a->row_lptr[li], r1 = (int)a->row_lptr[li + 1];
         const int m0 = (int)a->mbp_lptr[li], m1 = (int)a->mbp_lptr[li + 1];
         if (r1 > r0) { k_adj_rowprod<RP_YBAR><<<r1 - r0, kThreads, 0, st>>>(a->d_desc, a->d_row + r0, r1 - r0); note_launch(); }
-        const int64_t v0 = f->u_lptr[li], v1 = f->u_lptr[li + 1];
-        if (v1 > v0) { k_adj_vupd<<<(int)(v1 - v0), 256, 0, st>>>(a->d_desc, f->d_uitems + v0, (int)(v1 - v0)); note_launch(); }
+        const int64_t v0 = a->v_lptr[li], v1 = a->v_lptr[li + 1];
+        if (v1 > v0) { k_adj_vupd<<<(int)(v1 - v0), 256, 0, st>>>(a->d_desc, a->d_vitems + v0, (int)(v1 - v0)); note_launch(); }
         const int d0 = (int)a->dig_lptr[li], d1 = (int)a->dig_lptr[li + 1];
         if (d1 > d0) {
             launch_lhat_digits(a->d_tcdesc, a->d_dig + d0, d1 - d0, st);
