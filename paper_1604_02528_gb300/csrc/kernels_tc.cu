@@ -87,6 +87,31 @@ __device__ __forceinline__ void store_plane(uint16_t *dst, const uint32_t (&lo)[
     *reinterpret_cast<uint4 *>(dst) = q;
 }
 
+// The digit products of one k16 step, A digit planes i (128 rows) against B
+// digit planes j (TN rows each), summed into group i + j at tensor-memory
+// columns (i + j) TN.  The 7 B planes lie one after the other with the
+// row-group stride of the operand layout, so planes j0 .. j0 + m - 1 form one
+// operand of m TN rows: one MMA of N = m TN (at most 256) at columns
+// (i + j0) TN computes A_i B_j0 .. A_i B_{j0+m-1} into groups i + j0 ..
+// i + j0 + m - 1.  Per step 10 MMAs for TN = 64, 7 for TN <= 32 (against 28
+// of N = TN).  A group starts from zero at the first step of a chunk, with
+// the products of A plane 0.
+template <int TN, int A_PLANE, int B_PLANE>
+__device__ __forceinline__ void digit_products(uint32_t tmem, uint64_t ad0, uint64_t bd0, bool first) {
+    constexpr int kPer = 256 / TN;   // B planes per MMA (N <= 256)
+#pragma unroll
+    for (int i = 0; i < kTcDig; i++) {
+        const uint64_t ad = ad0 + (uint64_t)(i * A_PLANE * 2 / 16);
+#pragma unroll
+        for (int j0 = 0; j0 < kTcDig - i; j0 += kPer) {
+            const int m = kTcDig - i - j0 < kPer ? kTcDig - i - j0 : kPer;
+            const uint64_t bd = bd0 + (uint64_t)(j0 * B_PLANE * 2 / 16);
+            umma::mma_f16kind(tmem + (uint32_t)((i + j0) * TN), ad, bd, umma::idesc_f16_f32(kTcM, m * TN),
+                              (first && i == 0) ? 0u : 1u);
+        }
+    }
+}
+
 // Address of entry (p, q) of A^{-1}_{C,C} in the ancestors' panels (stored at
 // (max, min) by symmetry) in two parts: a base known at once and the relative
 // row, which comes from memory -- so that its load can stay in flight; base
@@ -272,7 +297,6 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_selinv_tc(const ProbDesc *__r
         // ---- one thread copies the Lhat digit planes (bulk, tcgen05 layout:
         // one contiguous block per plane and step) and issues the products
         if (lane == 0) {
-            const uint32_t idesc = umma::idesc_f16_f32(kTcM, TN);
             const int64_t s64 = (s + 63) / 64 * 64;
             const uint16_t *Bu = P.lhsu + P.lhsu_off[K] + (int64_t)(n0 / 8) * 128;
             constexpr uint32_t kBBytes = TN * 16 * 2;
@@ -297,16 +321,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_selinv_tc(const ProbDesc *__r
                 // plane i's descriptor = plane 0's + the plane offset in the start-address field
                 const uint64_t ad0 = umma::smem_desc(umma::smem_u32(As + stage * Cfg::A_STAGE), 128, 256);
                 const uint64_t bd0 = umma::smem_desc(umma::smem_u32(Bs + stage * Cfg::B_STAGE), 128, 256);
-#pragma unroll
-                for (int i = 0; i < kTcDig; i++) {
-                    const uint64_t ad = ad0 + (uint64_t)(i * Cfg::A_PLANE * 2 / 16);
-#pragma unroll
-                    for (int j = 0; i + j < kTcDig; j++) {
-                        const uint64_t bd = bd0 + (uint64_t)(j * Cfg::B_PLANE * 2 / 16);
-                        // group i + j starts from zero at its first product of a chunk (i == 0)
-                        umma::mma_f16kind(tmem + (uint32_t)((i + j) * TN), ad, bd, idesc, (first && i == 0) ? 0u : 1u);
-                    }
-                }
+                digit_products<TN, Cfg::A_PLANE, Cfg::B_PLANE>(tmem, ad0, bd0, first);
                 umma::commit(&empty[stage]);
                 if (i_ % kTcFlush == kTcFlush - 1 || i_ == n - 1) umma::commit(&acc_full);
                 // B of the next step into the other stage once the products of
@@ -610,7 +625,6 @@ __global__ void __launch_bounds__(kDtThreads, 1) k_diag_tc(const ProbDesc *__res
     } else if (warp == kDtMmaWarp) {
         // ---- one thread copies the Lhat digit planes and issues the products
         if (lane == 0) {
-            const uint32_t idesc = umma::idesc_f16_f32(kTcM, TN);
             const uint16_t *Au = P.lhsu + P.lhsu_off[K];
             const uint32_t aBytes = (uint32_t)(s64 * 16 * 2);
             auto load_a = [&](int i_) {
@@ -633,15 +647,7 @@ __global__ void __launch_bounds__(kDtThreads, 1) k_diag_tc(const ProbDesc *__res
                 umma::fence_after_sync();
                 const uint64_t ad0 = umma::smem_desc(umma::smem_u32(As + stage * Cfg::A_STAGE), 128, 256);
                 const uint64_t bd0 = umma::smem_desc(umma::smem_u32(Bs + stage * Cfg::B_STAGE), 128, 256);
-#pragma unroll
-                for (int i = 0; i < kTcDig; i++) {
-                    const uint64_t ad = ad0 + (uint64_t)(i * Cfg::A_PLANE * 2 / 16);
-#pragma unroll
-                    for (int j = 0; i + j < kTcDig; j++) {
-                        const uint64_t bd = bd0 + (uint64_t)(j * Cfg::B_PLANE * 2 / 16);
-                        umma::mma_f16kind(tmem + (uint32_t)((i + j) * TN), ad, bd, idesc, (first && i == 0) ? 0u : 1u);
-                    }
-                }
+                digit_products<TN, Cfg::A_PLANE, Cfg::B_PLANE>(tmem, ad0, bd0, first);
                 umma::commit(&empty[stage]);
                 if (i_ % kTcFlush == kTcFlush - 1 || i_ == n - 1) umma::commit(&acc_full);
                 if (i_ + 1 < n) {
