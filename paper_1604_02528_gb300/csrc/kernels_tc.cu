@@ -27,7 +27,7 @@ namespace selinv {
 
 constexpr int kTcM = 128;          // rows of C per item (tensor-memory lanes)
 constexpr int kTcProd = 8;         // producer warps: gather + digits of A, copies of B
-constexpr int kTcEpi = 4;          // epilogue warps: one per tensor-memory lane quarter
+constexpr int kTcEpi = 8;          // epilogue warps: two per tensor-memory lane quarter (half the columns each)
 constexpr int kTcMmaWarp = kTcProd + kTcEpi;
 constexpr int kTcThreads = 32 * (kTcProd + kTcEpi + 1);
 constexpr int kTcDig = 7;
@@ -339,7 +339,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_selinv_tc(const ProbDesc *__r
         __syncwarp();
     } else {
         // ---- epilogue: every chunk's exact fp32 group sums -> int64 (hi, lo)
-        const int lb = 32 * (warp % 4), row = lb + lane;
+        const int lb = 32 * (warp % 4), row = lb + lane, half = (warp / 4) & 1;
         for (int f = 0; f < nflush; f++) {
             if (!umma::mbar_wait(&acc_full, (uint32_t)(f & 1), wait_limit)) {
                 s_abort = 1;
@@ -347,7 +347,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_selinv_tc(const ProbDesc *__r
             }
             umma::fence_after_sync();
 #pragma unroll 1
-            for (int cb = 0; cb < TN / 8; cb++) {
+            for (int cb = half; cb < TN / 8; cb += 2) {
                 uint32_t acc[kTcDig][8];
 #pragma unroll
                 for (int gq = 0; gq < kTcDig; gq++)
@@ -494,7 +494,7 @@ cudaError_t launch_tc_reduce(int tn, const ProbDesc *d, const Item *items, const
 // grid 2^(F - 1029 - 8i) of Lhat's columns, the B digits on 2^(E - 1028 - 8j).
 // ---------------------------------------------------------------------------
 constexpr int kDtProd = 4;                       // producer warps (digit planes of Y)
-constexpr int kDtEpi = 4;                        // epilogue warps (tensor memory -> int64)
+constexpr int kDtEpi = 8;                        // epilogue warps (tensor memory -> int64), two per lane quarter
 constexpr int kDtMmaWarp = kDtProd + kDtEpi;
 constexpr int kDtThreads = 32 * (kDtProd + kDtEpi + 1);
 
@@ -663,7 +663,7 @@ __global__ void __launch_bounds__(kDtThreads, 1) k_diag_tc(const ProbDesc *__res
         __syncwarp();
     } else {
         // ---- epilogue: every chunk's exact fp32 group sums -> int64 (hi, lo)
-        const int lb = 32 * (warp % 4), row = lb + lane;
+        const int lb = 32 * (warp % 4), row = lb + lane, half = (warp / 4) & 1;
         for (int f = 0; f < nflush; f++) {
             if (!umma::mbar_wait(&acc_full, (uint32_t)(f & 1), wait_limit)) {
                 s_abort = 1;
@@ -671,7 +671,7 @@ __global__ void __launch_bounds__(kDtThreads, 1) k_diag_tc(const ProbDesc *__res
             }
             umma::fence_after_sync();
 #pragma unroll 1
-            for (int cb = 0; cb < TN / 8; cb++) {
+            for (int cb = half; cb < TN / 8; cb += 2) {
                 uint32_t acc[kTcDig][8];
 #pragma unroll
                 for (int gq = 0; gq < kTcDig; gq++)
