@@ -7,11 +7,15 @@
 //     live in tensor memory (7 TN columns), written by tcgen05.mma issued from
 //     one thread, completion signalled through mbarriers;
 //   * operands in shared memory in the K-major layout without swizzle, two
-//     stages: while the tensor cores work on step k, all 8 warps gather the
-//     A^{-1}(C,C) entries of step k + 1, cut them into digits (integer
-//     operations only) and copy the Lhat digit planes of step k + 1;
-//   * every 128 k the group sums are read from tensor memory and added as
-//     int64 into per-element (hi, lo) words in shared memory.
+//     stages: while the tensor cores work on step k, 16 producer warps gather
+//     the A^{-1}(C,C) entries of step k + 1 and cut them into digits (integer
+//     operations only, 4 values per thread), and bulk copies bring the Lhat
+//     digit planes of step k + 1;
+//   * one MMA per A digit plane against up to 256 / TN B planes at once
+//     (digit_products: 10 MMAs per step for TN = 64);
+//   * every 128 k the group sums are read from tensor memory by 8 epilogue
+//     warps and added as int64 into per-element (hi, lo) words in shared
+//     memory.
 // Split-k items store their int64 words in a per-CTA slab slot; k_tc_reduce,
 // launched next, sums the slots of each row tile (exact) and writes A^{-1}_{C,K}.
 #include <cuda_runtime.h>
@@ -26,7 +30,7 @@
 namespace selinv {
 
 constexpr int kTcM = 128;          // rows of C per item (tensor-memory lanes)
-constexpr int kTcProd = 8;         // producer warps: gather + digits of A, copies of B
+constexpr int kTcProd = 16;        // producer warps: gather + digits of A (4 values per thread and step)
 constexpr int kTcEpi = 8;          // epilogue warps: two per tensor-memory lane quarter (half the columns each)
 constexpr int kTcMmaWarp = kTcProd + kTcEpi;
 constexpr int kTcThreads = 32 * (kTcProd + kTcEpi + 1);
@@ -73,20 +77,6 @@ __device__ __forceinline__ uint32_t digit_pair(uint32_t w0, uint32_t w1) {
     return r;
 }
 
-// Digit plane PL (weight 256^(6 - PL)) of the 8 values whose biased fixed-
-// point words are (lo[u], hi[u]): one 16-byte core-matrix row of fp16.
-template <int PL>
-__device__ __forceinline__ void store_plane(uint16_t *dst, const uint32_t (&lo)[8], const uint32_t (&hi)[8]) {
-    constexpr int T = 6 - PL;
-    const uint32_t(&w)[8] = T >= 4 ? hi : lo;
-    uint4 q;
-    q.x = digit_pair<T>(w[0], w[1]);
-    q.y = digit_pair<T>(w[2], w[3]);
-    q.z = digit_pair<T>(w[4], w[5]);
-    q.w = digit_pair<T>(w[6], w[7]);
-    *reinterpret_cast<uint4 *>(dst) = q;
-}
-
 // The digit products of one k16 step, A digit planes i (128 rows) against B
 // digit planes j (TN rows each), summed into group i + j at tensor-memory
 // columns (i + j) TN.  The 7 B planes lie one after the other with the
@@ -110,6 +100,18 @@ __device__ __forceinline__ void digit_products(uint32_t tmem, uint64_t ad0, uint
                               (first && i == 0) ? 0u : 1u);
         }
     }
+}
+
+// Digit plane PL (weight 256^(6 - PL)) of the 4 values whose biased fixed-
+// point words are (lo[u], hi[u]): half a 16-byte core-matrix row of fp16.
+template <int PL>
+__device__ __forceinline__ void store_plane4(uint16_t *dst, const uint32_t (&lo)[4], const uint32_t (&hi)[4]) {
+    constexpr int T = 6 - PL;
+    const uint32_t(&w)[4] = T >= 4 ? hi : lo;
+    uint2 q;
+    q.x = digit_pair<T>(w[0], w[1]);
+    q.y = digit_pair<T>(w[2], w[3]);
+    *reinterpret_cast<uint2 *>(dst) = q;
 }
 
 // Address of entry (p, q) of A^{-1}_{C,C} in the ancestors' panels (stored at
@@ -236,23 +238,26 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_selinv_tc(const ProbDesc *__r
     const uint32_t tmem = s_tmem;
 
     if (warp < kTcProd) {
-        // ---- producers: A digits, gathered with a two-deep load pipeline
+        // ---- producers: A digits, gathered with a two-deep load pipeline.
+        // Thread (row r, quarter kq) slices the k-values 4 kq .. 4 kq + 3 of
+        // each 16-k step; a warp holds 16 rows x 2 quarters, so that its
+        // stores of a plane fill two 128-byte core matrices
         const TcGather g{P.colbase + pos0, P.relbase + pos0, P.relidx, tile_cb, tile_rb, p0, c};
         const double *Zg = static_cast<const double *>(P.Z);
-        const int r = tid % kTcM, kh = tid / kTcM;        // row r, k-values kh*8 .. kh*8+7
+        const int r = (warp % 8) * 16 + (lane >> 1), kq = (warp / 8) * 2 + (lane & 1);
         const int E = rowE[r];
-        double v[8];
-        int64_t ab[8];
-        int32_t ar[8];
+        double v[4];
+        int64_t ab[4];
+        int32_t ar[4];
         if (n > 0) {
 #pragma unroll
-            for (int u = 0; u < 8; u++) {
-                g.parts(r, st0 * 16 + kh * 8 + u, ab[u], ar[u]);
+            for (int u = 0; u < 4; u++) {
+                g.parts(r, st0 * 16 + kq * 4 + u, ab[u], ar[u]);
                 v[u] = ab[u] >= 0 ? Zg[ab[u] + ar[u]] : 0.0;
             }
 #pragma unroll
-            for (int u = 0; u < 8; u++) {
-                if (n > 1) g.parts(r, (st0 + 1) * 16 + kh * 8 + u, ab[u], ar[u]);
+            for (int u = 0; u < 4; u++) {
+                if (n > 1) g.parts(r, (st0 + 1) * 16 + kq * 4 + u, ab[u], ar[u]);
                 else ab[u] = -1;
             }
         }
@@ -264,28 +269,28 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_selinv_tc(const ProbDesc *__r
                 break;
             }
             {
-                uint32_t lo[8], hi[8];
+                uint32_t lo[4], hi[4];
 #pragma unroll
-                for (int u = 0; u < 8; u++) {
+                for (int u = 0; u < 4; u++) {
                     const unsigned long long wv = (unsigned long long)(fixed54(v[u], E) + 0x80808080808080ll);
                     lo[u] = (uint32_t)wv;
                     hi[u] = (uint32_t)(wv >> 32);
                 }
-                uint16_t *dst = Ab + (r / 8) * 128 + kh * 64 + (r % 8) * 8;
-                store_plane<0>(dst + 0 * Cfg::A_PLANE, lo, hi);
-                store_plane<1>(dst + 1 * Cfg::A_PLANE, lo, hi);
-                store_plane<2>(dst + 2 * Cfg::A_PLANE, lo, hi);
-                store_plane<3>(dst + 3 * Cfg::A_PLANE, lo, hi);
-                store_plane<4>(dst + 4 * Cfg::A_PLANE, lo, hi);
-                store_plane<5>(dst + 5 * Cfg::A_PLANE, lo, hi);
-                store_plane<6>(dst + 6 * Cfg::A_PLANE, lo, hi);
+                uint16_t *dst = Ab + (r / 8) * 128 + (kq / 2) * 64 + (r % 8) * 8 + (kq % 2) * 4;
+                store_plane4<0>(dst + 0 * Cfg::A_PLANE, lo, hi);
+                store_plane4<1>(dst + 1 * Cfg::A_PLANE, lo, hi);
+                store_plane4<2>(dst + 2 * Cfg::A_PLANE, lo, hi);
+                store_plane4<3>(dst + 3 * Cfg::A_PLANE, lo, hi);
+                store_plane4<4>(dst + 4 * Cfg::A_PLANE, lo, hi);
+                store_plane4<5>(dst + 5 * Cfg::A_PLANE, lo, hi);
+                store_plane4<6>(dst + 6 * Cfg::A_PLANE, lo, hi);
             }
             // loads of the next step's values, address lookups of the one after
 #pragma unroll
-            for (int u = 0; u < 8; u++) v[u] = ab[u] >= 0 ? Zg[ab[u] + ar[u]] : 0.0;
+            for (int u = 0; u < 4; u++) v[u] = ab[u] >= 0 ? Zg[ab[u] + ar[u]] : 0.0;
 #pragma unroll
-            for (int u = 0; u < 8; u++) {
-                if (i_ + 2 < n) g.parts(r, k0 + 32 + kh * 8 + u, ab[u], ar[u]);
+            for (int u = 0; u < 4; u++) {
+                if (i_ + 2 < n) g.parts(r, k0 + 32 + kq * 4 + u, ab[u], ar[u]);
                 else ab[u] = -1;
             }
             umma::fence_proxy_async();
@@ -347,20 +352,20 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_selinv_tc(const ProbDesc *__r
             }
             umma::fence_after_sync();
 #pragma unroll 1
-            for (int cb = half; cb < TN / 8; cb += 2) {
-                uint32_t acc[kTcDig][8];
+            for (int cb = half; cb < TN / 4; cb += 2) {
+                uint32_t acc[kTcDig][4];
 #pragma unroll
                 for (int gq = 0; gq < kTcDig; gq++)
-                    umma::tmem_ld8(tmem + ((uint32_t)lb << 16) + (uint32_t)(gq * TN + cb * 8), acc[gq]);
+                    umma::tmem_ld4(tmem + ((uint32_t)lb << 16) + (uint32_t)(gq * TN + cb * 4), acc[gq]);
                 umma::tmem_wait_ld();
 #pragma unroll
-                for (int jj = 0; jj < 8; jj++) {
+                for (int jj = 0; jj < 4; jj++) {
                     long long gv[kTcDig];
 #pragma unroll
                     for (int gq = 0; gq < kTcDig; gq++) gv[gq] = (long long)__float2int_rn(__uint_as_float(acc[gq][jj]));
                     const long long h = (gv[0] << 16) + (gv[1] << 8) + gv[2];
                     const long long l = (gv[3] << 24) + (gv[4] << 16) + (gv[5] << 8) + gv[6];
-                    long long *ph = Hi + (cb * 8 + jj) * kTcM + row, *pl = Lo + (cb * 8 + jj) * kTcM + row;
+                    long long *ph = Hi + (cb * 4 + jj) * kTcM + row, *pl = Lo + (cb * 4 + jj) * kTcM + row;
                     if (f == 0) {   // the first chunk writes, the later ones add
                         *ph = h;
                         *pl = l;
@@ -493,7 +498,7 @@ cudaError_t launch_tc_reduce(int tn, const ProbDesc *d, const Item *items, const
 // folded into int64 every 128 k, as in k_selinv_tc.  The A digits sit on the
 // grid 2^(F - 1029 - 8i) of Lhat's columns, the B digits on 2^(E - 1028 - 8j).
 // ---------------------------------------------------------------------------
-constexpr int kDtProd = 4;                       // producer warps (digit planes of Y)
+constexpr int kDtProd = 8;                       // producer warps (digit planes of Y, 4 values per thread and step)
 constexpr int kDtEpi = 8;                        // epilogue warps (tensor memory -> int64), two per lane quarter
 constexpr int kDtMmaWarp = kDtProd + kDtEpi;
 constexpr int kDtThreads = 32 * (kDtProd + kDtEpi + 1);
@@ -507,7 +512,7 @@ template <int TN> struct DtCfg {
     static constexpr size_t SMEM =
         sizeof(uint16_t) * 2 * (size_t)(A_STAGE + B_STAGE) + sizeof(long long) * 2 * (size_t)kTcM * TN;
 };
-static_assert(2 * 64 <= 32 * kDtProd, "a producer thread per (column, 8-row half) of a 64-column tile");
+static_assert(4 * 64 <= 32 * kDtProd, "a producer thread per (column, 4-row quarter) of a 64-column tile");
 
 // items: tile = chunk * ncol + column tile, ntiles = number of chunks
 template <int TN>
@@ -572,24 +577,24 @@ __global__ void __launch_bounds__(kDtThreads, 1) k_diag_tc(const ProbDesc *__res
     const uint32_t tmem = s_tmem;
 
     if (warp < kDtProd) {
-        // ---- producers: column r of the tile, rows kh*8 .. kh*8+7 of each 16-row step
-        const int r = tid % TN, kh = tid / TN;
-        const bool act = kh < 2;
+        // ---- producers: thread (column r, quarter kq) slices rows 4 kq .. 4 kq + 3
+        // of each 16-row step; a warp holds 16 columns x 2 quarters, so that its
+        // stores of a plane fill two 128-byte core matrices.  The values of the
+        // next step are loaded while this one is sliced.
+        const int r = (warp % 4) * 16 + (lane >> 1), kq = (warp / 4) * 2 + (lane & 1);
+        const bool act = r < TN;
         const double *Yc = static_cast<const double *>(P.Z) + P.panel_off[K] + (int64_t)(n0 + r) * ld + s;
         const bool colok = act && n0 + r < s;
         const int E = colok ? colE[r] : 0;
-        double v[8], v2[8];      // the values of this step and of the next one
-        auto fetch = [&](double (&x)[8], int step) {
+        double v[4];
+        auto fetch = [&](int step) {
 #pragma unroll
-            for (int u = 0; u < 8; u++) {
-                const int q = step * 16 + kh * 8 + u;
-                x[u] = (colok && step < st1 && q < c) ? Yc[q] : 0.0;
+            for (int u = 0; u < 4; u++) {
+                const int q = step * 16 + kq * 4 + u;
+                v[u] = (colok && step < st1 && q < c) ? Yc[q] : 0.0;
             }
         };
-        if (n > 0) {
-            fetch(v, st0);
-            fetch(v2, st0 + 1);
-        }
+        if (n > 0) fetch(st0);
         for (int i_ = 0; i_ < n; i_++) {
             const int stage = i_ & 1, use = i_ >> 1;
             uint16_t *Bb = Bs + stage * Cfg::B_STAGE;
@@ -598,25 +603,23 @@ __global__ void __launch_bounds__(kDtThreads, 1) k_diag_tc(const ProbDesc *__res
                 break;
             }
             if (act) {
-                uint32_t lo[8], hi[8];
+                uint32_t lo[4], hi[4];
 #pragma unroll
-                for (int u = 0; u < 8; u++) {
+                for (int u = 0; u < 4; u++) {
                     const unsigned long long wv = (unsigned long long)(fixed54(v[u], E) + 0x80808080808080ll);
                     lo[u] = (uint32_t)wv;
                     hi[u] = (uint32_t)(wv >> 32);
                 }
-                uint16_t *dst = Bb + (r / 8) * 128 + kh * 64 + (r % 8) * 8;
-                store_plane<0>(dst + 0 * Cfg::B_PLANE, lo, hi);
-                store_plane<1>(dst + 1 * Cfg::B_PLANE, lo, hi);
-                store_plane<2>(dst + 2 * Cfg::B_PLANE, lo, hi);
-                store_plane<3>(dst + 3 * Cfg::B_PLANE, lo, hi);
-                store_plane<4>(dst + 4 * Cfg::B_PLANE, lo, hi);
-                store_plane<5>(dst + 5 * Cfg::B_PLANE, lo, hi);
-                store_plane<6>(dst + 6 * Cfg::B_PLANE, lo, hi);
+                uint16_t *dst = Bb + (r / 8) * 128 + (kq / 2) * 64 + (r % 8) * 8 + (kq % 2) * 4;
+                store_plane4<0>(dst + 0 * Cfg::B_PLANE, lo, hi);
+                store_plane4<1>(dst + 1 * Cfg::B_PLANE, lo, hi);
+                store_plane4<2>(dst + 2 * Cfg::B_PLANE, lo, hi);
+                store_plane4<3>(dst + 3 * Cfg::B_PLANE, lo, hi);
+                store_plane4<4>(dst + 4 * Cfg::B_PLANE, lo, hi);
+                store_plane4<5>(dst + 5 * Cfg::B_PLANE, lo, hi);
+                store_plane4<6>(dst + 6 * Cfg::B_PLANE, lo, hi);
             }
-#pragma unroll
-            for (int u = 0; u < 8; u++) v[u] = v2[u];
-            if (i_ + 2 < n) fetch(v2, st0 + i_ + 2);
+            if (i_ + 1 < n) fetch(st0 + i_ + 1);
             umma::fence_proxy_async();
             __syncwarp();
             if (lane == 0) umma::mbar_arrive(&full[stage]);
