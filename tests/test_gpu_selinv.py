@@ -142,6 +142,34 @@ def test_tensor_core_and_dfma_paths_match_oracle(native, cuda_device, name, make
         assert oracle.block_errors(sym, G, outs[2]).max() <= TOL
 
 
+def test_tensor_core_result_is_independent_of_the_k_split(native, cuda_device):
+    """The tcgen05 contraction's split-k partial sums are exact int64 words,
+    added exactly by k_tc_reduce, and every k-range works on the same row and
+    column exponent grids: the result is bitwise the same for any k-split
+    (one CTA per output tile, or up to several k-ranges of >= 8 steps)."""
+    import torch
+    p = synth.laplacian_3d(26, seed=4)          # c up to 880 rows: up to 6 k-ranges of >= 8 steps
+    sym = oracle.symbolic_for(p)
+    L, D = oracle.ldlt(p, sym)
+    plan = native.selinv_symbolic(sym.n, sym.nsuper, sym.super_ptr, sym.sparent, sym.rowptr, sym.rows)
+    Lt, Dt = torch.from_numpy(L).cuda(), torch.from_numpy(D).cuda()
+    outs = []
+    for target, min_steps in ((1, 64), (2, 8), (8, 8), (4, 16)):
+        o = native.selinv_default_opts()
+        o.fast_contraction = 1
+        o.split_target = target
+        o.split_min_steps = min_steps
+        native.selinv_plan_set_opts(plan, o)
+        Zt = torch.full_like(Lt, float("nan"))
+        native.selinv_numeric(plan, native.SELINV_F64, Lt, Dt, Zt, torch.cuda.current_stream())
+        torch.cuda.synchronize()
+        assert native.selinv_status(plan) == 0
+        outs.append(Zt.cpu().numpy())
+    for G in outs[1:]:
+        assert np.array_equal(G, outs[0])
+    assert oracle.block_errors(sym, outs[0], oracle.selinv(sym, L, D)).max() <= TOL
+
+
 def test_autotuned_plan_matches_oracle(native, cuda_device):
     """The first call tunes (engine, k-split, narrowest tensor-core supernode)
     on the caller's data; the tuned options stay valid and every result meets
