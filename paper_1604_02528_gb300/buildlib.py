@@ -17,7 +17,7 @@ OBJ = os.path.join(HERE, "_build")
 TARGET = os.path.join(HERE, "libselinv.so")
 NVCC = os.environ.get("NVCC", "nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
+FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2", "-Xcompiler", "-pthread",
          "-I" + os.path.join(ROOT, "include"), "-I" + CSRC]
 
 
@@ -58,7 +58,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     if (force or not os.path.exists(TARGET)
             or os.path.getmtime(TARGET) < max(os.path.getmtime(o) for o in objs)):
         tmp = TARGET + f".tmp{os.getpid()}"
-        cmd = [NVCC] + ARCH + ["-shared", "-o", tmp] + objs + ["-lcudart"]
+        cmd = [NVCC] + ARCH + ["-shared", "-o", tmp] + objs + ["-lcudart", "-lpthread"]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")

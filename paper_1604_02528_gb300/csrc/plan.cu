@@ -11,6 +11,7 @@
 #include <cstring>
 #include <memory>
 #include <new>
+#include <thread>
 #include <vector>
 
 #include "common.cuh"
@@ -24,8 +25,8 @@ void note_launch(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
 size_t elem_size(int dtype) { return dtype == SELINV_F64 ? 8 : 16; }
 
-template <typename X>
-static int upload(X **dptr, const std::vector<X> &h) {
+template <typename X, typename A>
+static int upload(X **dptr, const std::vector<X, A> &h) {
     *dptr = nullptr;
     size_t bytes = sizeof(X) * (h.empty() ? 1 : h.size());
     if (cudaMalloc((void **)dptr, bytes) != cudaSuccess) return SELINV_ERR_OOM;
@@ -169,47 +170,97 @@ static int build_plan(PlanData &p, int32_t n, int32_t ns, const int32_t *super_p
         std::vector<int64_t> f(p.level_ptr.begin(), p.level_ptr.end() - 1);
         for (int32_t K = 0; K < ns; K++) p.level_list[f[p.level[K]]++] = K;
     }
-    // owner segments of every C, relative indices (merge walk in the owner's rows)
-    p.seg_ptr.assign(ns + 1, 0);
-    p.seg_owner.clear(); p.seg_start.clear(); p.seg_coloff.clear();
-    p.rel_ptr.assign(1, 0);
-    p.relidx.clear();
-    p.colbase.assign(nrows > 0 ? nrows : 1, 0);
-    p.relbase.assign(nrows > 0 ? nrows : 1, 0);
+    // owner segments of every C, relative indices (merge walk in the owner's
+    // rows).  Pass 1 counts each supernode's segments and relative indices
+    // (serial, O(sum c)); pass 2 fills them with the supernodes spread over
+    // host threads, each supernode into its own ranges, so that the plan does
+    // not depend on the threads.
+    std::vector<int64_t> nseg(ns + 1, 0), nrel(ns + 1, 0);
     for (int32_t K = 0; K < ns; K++) {
         const int32_t s = super_ptr[K + 1] - super_ptr[K];
         const int64_t c = rowptr[K + 1] - rowptr[K] - s;
         const int32_t *C = rowind + rowptr[K] + s;
-        p.seg_ptr[K] = (int64_t)p.seg_owner.size();
-        int64_t q = 0;
+        int64_t q = 0, segs = 0, rels = 0;
         while (q < c) {
             const int32_t J = col2s[C[q]];
             if (J <= K) return SELINV_ERR_BAD_PATTERN;
             int64_t qe = q;
             while (qe < c && col2s[C[qe]] == J) qe++;
-            const int32_t fcJ = super_ptr[J];
-            const int64_t mJ = rowptr[J + 1] - rowptr[J];
-            const int32_t *RJ = rowind + rowptr[J];
-            p.seg_owner.push_back(J);
-            p.seg_start.push_back((int32_t)q);
-            p.seg_coloff.push_back(C[q] - fcJ);
-            const int64_t rbase = (int64_t)p.relidx.size();
-            int64_t t = C[q] - fcJ;  // C[q] is a column of J, at that position of rows(J)
-            for (int64_t r = q; r < c; r++) {
-                while (t < mJ && RJ[t] < C[r]) t++;
-                if (t >= mJ || RJ[t] != C[r]) return SELINV_ERR_BAD_PATTERN;  // not closed
-                p.relidx.push_back((int32_t)t);
-            }
-            p.rel_ptr.push_back((int64_t)p.relidx.size());
-            for (int64_t r = q; r < qe; r++) {
-                const int64_t pos = rowptr[K] + s + r;
-                p.colbase[pos] = p.panel_off[J] + (int64_t)(C[r] - fcJ) * mJ;
-                p.relbase[pos] = rbase - q;
-            }
+            segs++;
+            rels += c - q;
             q = qe;
         }
+        nseg[K + 1] = nseg[K] + segs;
+        nrel[K + 1] = nrel[K] + rels;
     }
-    p.seg_ptr[ns] = (int64_t)p.seg_owner.size();
+    const int64_t tseg = nseg[ns], trel = nrel[ns];
+    p.seg_ptr.assign(nseg.begin(), nseg.end());
+    p.seg_owner.assign(tseg, 0);
+    p.seg_start.assign(tseg, 0);
+    p.seg_coloff.assign(tseg, 0);
+    p.rel_ptr.assign(tseg + 1, 0);
+    p.rel_ptr[tseg] = trel;
+    // written in full by the fill below (colbase / relbase: C positions there,
+    // the diagonal-block positions zeroed there)
+    p.relidx.resize(trel);
+    p.colbase.resize(nrows > 0 ? nrows : 1);
+    p.relbase.resize(nrows > 0 ? nrows : 1);
+    if (nrows == 0) p.colbase[0] = p.relbase[0] = 0;
+    std::atomic<int> bad{0};
+    std::atomic<int32_t> next{0};
+    constexpr int32_t kBlock = 64;   // supernodes per claim
+    auto fill = [&]() {
+        for (;;) {
+            const int32_t K0 = next.fetch_add(kBlock);
+            if (K0 >= ns || bad.load(std::memory_order_relaxed)) return;
+            for (int32_t K = K0; K < std::min(ns, K0 + kBlock); K++) {
+                const int32_t s = super_ptr[K + 1] - super_ptr[K];
+                const int64_t c = rowptr[K + 1] - rowptr[K] - s;
+                const int32_t *C = rowind + rowptr[K] + s;
+                int64_t g = nseg[K], rb = nrel[K], q = 0;
+                for (int64_t r = 0; r < s; r++) p.colbase[rowptr[K] + r] = p.relbase[rowptr[K] + r] = 0;
+                while (q < c) {
+                    const int32_t J = col2s[C[q]];
+                    int64_t qe = q;
+                    while (qe < c && col2s[C[qe]] == J) qe++;
+                    const int32_t fcJ = super_ptr[J];
+                    const int64_t mJ = rowptr[J + 1] - rowptr[J];
+                    const int32_t *RJ = rowind + rowptr[J];
+                    p.seg_owner[g] = J;
+                    p.seg_start[g] = (int32_t)q;
+                    p.seg_coloff[g] = C[q] - fcJ;
+                    p.rel_ptr[g] = rb;
+                    int64_t t = C[q] - fcJ;  // C[q] is a column of J, at that position of rows(J)
+                    for (int64_t r = q; r < c; r++) {
+                        while (t < mJ && RJ[t] < C[r]) t++;
+                        if (t >= mJ || RJ[t] != C[r]) {   // not closed
+                            bad.store(1);
+                            return;
+                        }
+                        p.relidx[rb + (r - q)] = (int32_t)t;
+                    }
+                    for (int64_t r = q; r < qe; r++) {
+                        const int64_t pos = rowptr[K] + s + r;
+                        p.colbase[pos] = p.panel_off[J] + (int64_t)(C[r] - fcJ) * mJ;
+                        p.relbase[pos] = rb - q;
+                    }
+                    rb += c - q;
+                    g++;
+                    q = qe;
+                }
+            }
+        }
+    };
+    {
+        const int64_t work = trel + nrows;
+        const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
+        const int nthr = work < (1 << 18) ? 1 : (int)std::min<unsigned>(hw, 16u);
+        std::vector<std::thread> pool;
+        for (int i = 1; i < nthr; i++) pool.emplace_back(fill);
+        fill();
+        for (auto &th : pool) th.join();
+    }
+    if (bad.load()) return SELINV_ERR_BAD_PATTERN;
     // L_KK^{-1} offsets; split-partial offsets inside each level
     p.linv_off.assign(ns + 1, 0);
     p.part_off.assign(ns > 0 ? ns : 1, 0);

@@ -5,11 +5,27 @@
 
 #include <cstdint>
 #include <algorithm>
+#include <memory>
+#include <utility>
 #include <vector>
 
 #include "common.cuh"
 
 namespace selinv {
+
+// Host allocator that leaves new elements default-initialized (no zeroing):
+// for large index arrays that are filled completely right after allocation,
+// so that their pages are first touched by the threads that fill them.
+template <typename T> struct UninitAlloc : std::allocator<T> {
+    template <typename U> struct rebind { using other = UninitAlloc<U>; };
+    UninitAlloc() = default;
+    template <typename U> UninitAlloc(const UninitAlloc<U> &) noexcept {}
+    template <typename U> void construct(U *ptr) noexcept { ::new (static_cast<void *>(ptr)) U; }
+    template <typename U, typename... A> void construct(U *ptr, A &&...a) {
+        ::new (static_cast<void *>(ptr)) U(std::forward<A>(a)...);
+    }
+};
+template <typename T> using fill_vector = std::vector<T, UninitAlloc<T>>;
 
 struct PlanData {
     int32_t n = 0, ns = 0;
@@ -17,10 +33,11 @@ struct PlanData {
     bool tuned[3] = {false, false, false};   // autotuning done, per selinv_dtype
     // host arrays (kept for inspection and schedule building)
     std::vector<int32_t> super_ptr, sparent, rows, level, level_list;
-    std::vector<int32_t> seg_owner, seg_start, seg_coloff, relidx, ntiles;
+    std::vector<int32_t> seg_owner, seg_start, seg_coloff, ntiles;
+    fill_vector<int32_t> relidx;
     std::vector<int64_t> rowptr, panel_off, seg_ptr, rel_ptr, level_ptr, linv_off, part_off;
     std::vector<int64_t> part_off_all;  // split-partial offsets disjoint over all levels (persistent schedule)
-    std::vector<int64_t> colbase, relbase;  // per row-list position
+    fill_vector<int64_t> colbase, relbase;  // per row-list position
     std::vector<int64_t> lhs_off;           // digit-plane offsets (tensor-core path)
     std::vector<int64_t> lhsu_off;          // the same in the tcgen05 operand layout
     std::vector<int64_t> tile_base;         // prefix sums of the 64-row tiles of each supernode
