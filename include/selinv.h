@@ -366,6 +366,15 @@ const char *selinv_error_string(int code);
 /* Number of kernel launches the library issued since load (for accounting). */
 int64_t selinv_launch_count(void);
 
+/* Frees the device buffers that destroyed plans (and workspaces replaced by a
+ * wider element type) left in the library's cache for reuse.  The cache
+ * keeps released workspace buffers, keyed by exact size, up to 8 GB, so that
+ * re-planning one pattern allocates and frees nothing; it is emptied by
+ * itself when a device allocation fails.  Returns SELINV_OK; no device work
+ * may be in flight on buffers of destroyed plans (destroying a plan already
+ * synchronizes the device). */
+int selinv_release_cached_memory(void);
+
 #ifdef __cplusplus
 }
 #endif

@@ -84,6 +84,7 @@ def _load() -> ct.CDLL:
         "selinv_status": (I, [P]),
         "selinv_error_string": (ct.c_char_p, [I]),
         "selinv_launch_count": (I64, []),
+        "selinv_release_cached_memory": (I, []),
         "selinv_dinv_noalloc": (I, [I32, P, I64, P, P, I64, P]),
         "selinv_plan_select": (I, [P, I64, P, P, P]),
         "selinv_numeric_lu": (I, [P, I, P, P, P, P, P]),
@@ -109,7 +110,7 @@ REQUIRED_SYMBOLS = ("selinv_default_opts", "selinv_analyse", "selinv_analysis_ge
                     "selinv_adjoint", "selinv_factor_adjoint", "selinv_status",
                     "selinv_error_string", "selinv_launch_count", "selinv_dinv_noalloc",
                     "selinv_plan_select", "selinv_plan_selected", "selinv_gather", "selinv_pole_sum",
-                    "selinv_numeric_lu")
+                    "selinv_numeric_lu", "selinv_release_cached_memory")
 
 
 def error_string(code: int) -> str:
@@ -392,3 +393,9 @@ def selinv_status(plan: Plan) -> int:
 
 def selinv_launch_count() -> int:
     return int(LIB.selinv_launch_count())
+
+
+def selinv_release_cached_memory():
+    """Frees the device buffers that destroyed plans left in the library's
+    reuse cache."""
+    _check(LIB.selinv_release_cached_memory(), "selinv_release_cached_memory")

@@ -40,54 +40,66 @@ static void dfree(void *p) {
 }
 
 void Workspace::release() {
-    dfree(LDu); dfree(Vt);
+    if (!owned.empty()) {
+        cudaDeviceSynchronize();   // no kernel may still use a buffer that goes into the cache
+        for (auto &o : owned) dev_release(o.first, o.second);
+        owned.clear();
+    }
     LDu = Vt = nullptr;
-    dfree(LD); dfree(Linv); dfree(partial); dfree(counter); dfree(done); dfree(work); dfree(ticket);
-    dfree(partial_all);
     ticket = nullptr;
     partial_all = nullptr;
-    dfree(lhs); dfree(lhsu); dfree(colexp); dfree(colexpY); dfree(dacc); dfree(colexpZ); dfree(yacc); dfree(tcount);
     colexpZ = tcount = nullptr;
     yacc = nullptr;
     lhs = nullptr;
     lhsu = nullptr;
     colexp = colexpY = nullptr;
     dacc = nullptr;
+    linvd = nullptr;
+    linvexp = nullptr;
     LD = Linv = partial = nullptr;
     counter = done = nullptr;
     work = nullptr;
     bytes_elem = 0;
 }
 
+// a workspace buffer of `bytes`, recorded for release
+template <typename X> static bool wget(Workspace &w, X **ptr, size_t bytes) {
+    void *v = nullptr;
+    if (dev_alloc(&v, bytes) != cudaSuccess) return false;
+    w.owned.emplace_back(v, bytes);
+    *ptr = static_cast<X *>(v);
+    return true;
+}
+
 int Workspace::ensure(const PlanData &p, int dtype) {
     const size_t es = elem_size(dtype);
     if (LD && bytes_elem >= es) return SELINV_OK;
     release();
-    if (cudaMalloc(&LD, es * (size_t)std::max<int64_t>(p.nnz, 1)) != cudaSuccess) return SELINV_ERR_OOM;
-    if (cudaMalloc(&Linv, es * (size_t)std::max<int64_t>(p.linv_total, 1)) != cudaSuccess) return SELINV_ERR_OOM;
-    if (cudaMalloc(&partial, es * (size_t)std::max<int64_t>(p.part_max, 1)) != cudaSuccess) return SELINV_ERR_OOM;
-    if (cudaMalloc((void **)&counter, sizeof(int) * (size_t)std::max(p.ns, 1)) != cudaSuccess) return SELINV_ERR_OOM;
+    if (!wget(*this, &LD, es * (size_t)std::max<int64_t>(p.nnz, 1))) return SELINV_ERR_OOM;
+    if (!wget(*this, &Linv, es * (size_t)std::max<int64_t>(p.linv_total, 1))) return SELINV_ERR_OOM;
+    if (!wget(*this, &partial, es * (size_t)std::max<int64_t>(p.part_max, 1))) return SELINV_ERR_OOM;
+    if (!wget(*this, &counter, sizeof(int) * (size_t)std::max(p.ns, 1))) return SELINV_ERR_OOM;
     // one extra flag (index ns) that nothing ever sets: the target of the timeout test
-    if (cudaMalloc((void **)&done, sizeof(int) * (size_t)(p.ns + 1)) != cudaSuccess) return SELINV_ERR_OOM;
-    if (cudaMalloc((void **)&ticket, sizeof(int)) != cudaSuccess) return SELINV_ERR_OOM;
-    if (cudaMalloc(&work, es * (size_t)std::max<int64_t>(p.nnz, 1)) != cudaSuccess) return SELINV_ERR_OOM;
-    if (cudaMalloc((void **)&lhs, sizeof(uint16_t) * (size_t)std::max<int64_t>(p.lhs_total, 8)) != cudaSuccess)
+    if (!wget(*this, &done, sizeof(int) * (size_t)(p.ns + 1))) return SELINV_ERR_OOM;
+    if (!wget(*this, &ticket, sizeof(int))) return SELINV_ERR_OOM;
+    if (!wget(*this, &work, es * (size_t)std::max<int64_t>(p.nnz, 1))) return SELINV_ERR_OOM;
+    if (!wget(*this, &lhs, sizeof(uint16_t) * (size_t)std::max<int64_t>(p.lhs_total, 8)))
         return SELINV_ERR_OOM;
-    if (cudaMalloc((void **)&lhsu, sizeof(uint16_t) * (size_t)std::max<int64_t>(p.lhsu_total, 8)) != cudaSuccess)
+    if (!wget(*this, &lhsu, sizeof(uint16_t) * (size_t)std::max<int64_t>(p.lhsu_total, 8)))
         return SELINV_ERR_OOM;
     cudaMemset(lhsu, 0, sizeof(uint16_t) * (size_t)std::max<int64_t>(p.lhsu_total, 8));   // padding stays zero
-    if (cudaMalloc((void **)&colexp, sizeof(int) * (size_t)std::max(p.n, 1)) != cudaSuccess) return SELINV_ERR_OOM;
-    if (cudaMalloc((void **)&colexpY, sizeof(int) * (size_t)std::max(p.n, 1)) != cudaSuccess) return SELINV_ERR_OOM;
-    if (cudaMalloc((void **)&dacc, sizeof(long long) * 2 * (size_t)std::max<int64_t>(p.linv_total, 1)) != cudaSuccess)
+    if (!wget(*this, &colexp, sizeof(int) * (size_t)std::max(p.n, 1))) return SELINV_ERR_OOM;
+    if (!wget(*this, &colexpY, sizeof(int) * (size_t)std::max(p.n, 1))) return SELINV_ERR_OOM;
+    if (!wget(*this, &dacc, sizeof(long long) * 2 * (size_t)std::max<int64_t>(p.linv_total, 1)))
         return SELINV_ERR_OOM;
-    if (cudaMalloc((void **)&colexpZ, sizeof(int) * (size_t)std::max(p.n, 1)) != cudaSuccess) return SELINV_ERR_OOM;
-    if (cudaMalloc((void **)&linvexp, sizeof(int) * (size_t)std::max(p.n, 1)) != cudaSuccess) return SELINV_ERR_OOM;
-    if (cudaMalloc((void **)&linvd, sizeof(uint16_t) * (size_t)std::max<int64_t>(p.linvd_total, 8)) != cudaSuccess)
+    if (!wget(*this, &colexpZ, sizeof(int) * (size_t)std::max(p.n, 1))) return SELINV_ERR_OOM;
+    if (!wget(*this, &linvexp, sizeof(int) * (size_t)std::max(p.n, 1))) return SELINV_ERR_OOM;
+    if (!wget(*this, &linvd, sizeof(uint16_t) * (size_t)std::max<int64_t>(p.linvd_total, 8)))
         return SELINV_ERR_OOM;
     cudaMemset(colexpZ, 0, sizeof(int) * (size_t)std::max(p.n, 1));
     const size_t ny = (dtype == SELINV_F64 && p.lhs_total > 0) ? 2 * (size_t)p.nnz : 2;
-    if (cudaMalloc((void **)&yacc, sizeof(long long) * ny) != cudaSuccess) return SELINV_ERR_OOM;
-    if (cudaMalloc((void **)&tcount, sizeof(int) * (size_t)std::max<int64_t>(p.tile_total, 1)) != cudaSuccess)
+    if (!wget(*this, &yacc, sizeof(long long) * ny)) return SELINV_ERR_OOM;
+    if (!wget(*this, &tcount, sizeof(int) * (size_t)std::max<int64_t>(p.tile_total, 1)))
         return SELINV_ERR_OOM;
     cudaMemset(yacc, 0, sizeof(long long) * ny);
     cudaMemset(tcount, 0, sizeof(int) * (size_t)std::max<int64_t>(p.tile_total, 1));
@@ -103,14 +115,14 @@ int Workspace::ensure(const PlanData &p, int dtype) {
 // the LU form's extra scratch (element size of the current workspace)
 int Workspace::ensure_lu(const PlanData &p) {
     if (LDu) return SELINV_OK;
-    if (cudaMalloc(&LDu, bytes_elem * (size_t)std::max<int64_t>(p.nnz, 1)) != cudaSuccess) return SELINV_ERR_OOM;
-    if (cudaMalloc(&Vt, bytes_elem * (size_t)std::max<int64_t>(p.linv_total, 1)) != cudaSuccess) return SELINV_ERR_OOM;
+    if (!wget(*this, &LDu, bytes_elem * (size_t)std::max<int64_t>(p.nnz, 1))) return SELINV_ERR_OOM;
+    if (!wget(*this, &Vt, bytes_elem * (size_t)std::max<int64_t>(p.linv_total, 1))) return SELINV_ERR_OOM;
     return SELINV_OK;
 }
 
 int Workspace::ensure_persistent(const PlanData &p) {
     if (partial_all) return SELINV_OK;
-    if (cudaMalloc(&partial_all, bytes_elem * (size_t)std::max<int64_t>(p.part_all, 1)) != cudaSuccess)
+    if (!wget(*this, &partial_all, bytes_elem * (size_t)std::max<int64_t>(p.part_all, 1)))
         return SELINV_ERR_OOM;
     return SELINV_OK;
 }

@@ -82,11 +82,18 @@ struct Workspace {
     void *LDu = nullptr;       // LU form: Uhat^T panels
     void *Vt = nullptr;        // LU form: (U_KK^T)^{-1} blocks
     size_t bytes_elem = 0;
+    std::vector<std::pair<void *, size_t>> owned;   // every buffer above, with its size
     int ensure(const PlanData &p, int dtype);
     int ensure_lu(const PlanData &p);
     int ensure_persistent(const PlanData &p);
     void release();
 };
+
+// Device buffers through the cache of released workspaces (devmem.cu):
+// dev_alloc hands out a cached buffer of exactly `bytes` or allocates one;
+// dev_release caches the buffer (the caller has synchronized the device).
+cudaError_t dev_alloc(void **ptr, size_t bytes);
+void dev_release(void *ptr, size_t bytes);
 
 // launch kinds
 enum { KL_LINV = 0, KL_LHAT = 1, KL_SELINV = 2, KL_DIGITS = 3, KL_SELINV_OZ = 4, KL_DIAG = 5, KL_LINV_DIGITS = 6,

@@ -170,6 +170,23 @@ def test_tensor_core_result_is_independent_of_the_k_split(native, cuda_device):
     assert oracle.block_errors(sym, outs[0], oracle.selinv(sym, L, D)).max() <= TOL
 
 
+def test_replanning_reuses_cached_workspaces(native, cuda_device):
+    """Plans destroyed and re-created (one pattern, then another) run on
+    workspace buffers from the reuse cache, whose old contents must not leak
+    into the result; the cache is then emptied."""
+    import gc
+    cases = [CASES[7], CASES[3], CASES[7]]
+    for name, make in cases:
+        p = make()
+        sym, L, D, Z = oracle_run(p)
+        for _ in range(2):
+            G, plan = gpu_selinv(native, sym, L, D)
+            assert oracle.block_errors(sym, G, Z).max() <= TOL, name
+            del plan
+            gc.collect()
+    native.selinv_release_cached_memory()
+
+
 def test_autotuned_plan_matches_oracle(native, cuda_device):
     """The first call tunes (engine, k-split, narrowest tensor-core supernode)
     on the caller's data; the tuned options stay valid and every result meets

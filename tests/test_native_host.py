@@ -73,6 +73,12 @@ def test_analysis_matches_oracle_on_full_workloads(native, cfg):
         assert np.array_equal(a[k], getattr(o, k)), k
 
 
+def test_release_cached_memory_without_device_buffers(native):
+    """An empty reuse cache is emptied without touching the device."""
+    native.selinv_release_cached_memory()
+    native.selinv_release_cached_memory()
+
+
 def make_plan(native, sym):
     return native.selinv_symbolic(sym.n, sym.nsuper, sym.super_ptr, sym.sparent, sym.rowptr, sym.rows)
 
