@@ -21,6 +21,7 @@ import argparse
 import hashlib
 import json
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -169,13 +170,22 @@ def measured_peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "source": "of fallback (1.9 PFLOP/s)"}
 
 
+def code_text(src: str) -> str:
+    """C++/CUDA source without its comments and with whitespace collapsed:
+    what the compiler sees of it (string literals here hold no comment
+    markers)."""
+    src = re.sub(r"/\*.*?\*/", " ", src, flags=re.S)
+    src = re.sub(r"//[^\n]*", " ", src)
+    return " ".join(src.split())
+
+
 def kernel_source_hash(kernel: str) -> str:
-    """Hash of the sources that define `kernel` (a traffic figure taken on
-    other sources no longer applies)."""
+    """Hash of the code (comments and whitespace aside) of the sources that
+    define `kernel`: a traffic figure taken on other code no longer applies."""
     h = hashlib.sha256()
     for f in KERNEL_SOURCES.get(kernel, DEFAULT_SOURCES):
-        with open(os.path.join(ROOT, "paper_1604_02528_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(ROOT, "paper_1604_02528_gb300", "csrc", f), encoding="utf-8") as fh:
+            h.update(code_text(fh.read()).encode())
     return h.hexdigest()[:16]
 
 

@@ -11,8 +11,8 @@
 //     the A^{-1}(C,C) entries of step k + 1 and cut them into digits (integer
 //     operations only, 4 values per thread), and bulk copies bring the Lhat
 //     digit planes of step k + 1;
-//   * one MMA per A digit plane against up to 256 / TN B planes at once
-//     (digit_products: 10 MMAs per step for TN = 64);
+//   * each MMA takes one A digit plane against up to 256 / TN B planes
+//     (digit_products: 10 MMAs per step for TN = 64, 7 for TN <= 32);
 //   * every 128 k the group sums are read from tensor memory by 8 epilogue
 //     warps and added as int64 into per-element (hi, lo) words in shared
 //     memory.
@@ -491,7 +491,7 @@ cudaError_t launch_tc_reduce(int tn, const ProbDesc *d, const Item *items, const
 //       of C -- the digit planes of Lhat are already stored in this operand
 //       layout (they are the gather-GEMM's B), so one bulk copy per plane and
 //       16-row step brings them in;
-//   B = Y columns n0 .. n0 + TN - 1, k = q: 4 producer warps slice A^{-1}_{C,K}
+//   B = Y columns n0 .. n0 + TN - 1, k = q: 8 producer warps slice A^{-1}_{C,K}
 //       (written by the gather-GEMM of this level) into digit planes on the
 //       column exponents colexpY, integer operations only.
 // Digit products grouped by i + j into exact fp32 sums in tensor memory,
