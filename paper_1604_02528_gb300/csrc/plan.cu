@@ -108,6 +108,10 @@ int Workspace::ensure(const PlanData &p, int dtype) {
     cudaMemset(counter, 0, sizeof(int) * (size_t)std::max(p.ns, 1));
     cudaMemset(done, 0, sizeof(int) * (size_t)(p.ns + 1));
     cudaMemset(ticket, 0, sizeof(int));
+    // the zeroing above runs on the legacy default stream, which a caller's
+    // non-blocking stream does not wait for: finish it before any kernel can
+    // see the buffers (reused ones hold a previous plan's data)
+    if (cudaDeviceSynchronize() != cudaSuccess) return SELINV_ERR_CUDA;
     bytes_elem = es;
     return SELINV_OK;
 }
