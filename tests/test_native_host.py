@@ -79,6 +79,35 @@ def test_release_cached_memory_without_device_buffers(native):
     native.selinv_release_cached_memory()
 
 
+def test_rejects_unclosed_structure_on_the_threaded_path(native):
+    """A row list that is not closed under the tree is rejected also when the
+    relative indices are filled by several host threads (large plans)."""
+    p = synth.laplacian_3d(26, seed=2)
+    sym, (sp, par, rp, rows) = _sym_arrays(p)
+    ns = sym.nsuper
+    # relative indices + row-list positions above the library's single-thread threshold (2^18)
+    assert oracle.plan(sym)["relidx"].size + rp[-1] > (1 << 18)
+    col2s = np.repeat(np.arange(ns), np.diff(sp))
+    for K in range(ns - 1, -1, -1):                # a supernode near the root: late in the fill
+        s = sp[K + 1] - sp[K]
+        C = rows[rp[K] + s:rp[K + 1]]
+        if C.size < 2:
+            continue
+        J = col2s[C[0]]
+        below = [x for x in C[1:] if x >= sp[J + 1]]
+        if below:
+            break
+    RJ = rows[rp[J]:rp[J + 1]]
+    drop = rp[J] + int(np.searchsorted(RJ, below[0]))
+    rows2 = np.delete(rows, drop)
+    rp2 = rp.copy()
+    rp2[J + 1:] -= 1
+    with pytest.raises(native.SelinvError) as e:
+        native.selinv_symbolic(sym.n, ns, sp, par, rp2, rows2)
+    assert e.value.code in (-3, -2)
+    native.selinv_symbolic(sym.n, ns, sp, par, rp, rows)   # the intact structure still plans
+
+
 def make_plan(native, sym):
     return native.selinv_symbolic(sym.n, sym.nsuper, sym.super_ptr, sym.sparent, sym.rowptr, sym.rows)
 
