@@ -224,12 +224,14 @@ static int build_plan(PlanData &p, int32_t n, int32_t ns, const int32_t *super_p
     if (nrows == 0) p.colbase[0] = p.relbase[0] = 0;
     std::atomic<int> bad{0};
     std::atomic<int32_t> next{0};
-    constexpr int32_t kBlock = 64;   // supernodes per claim
+    constexpr int32_t kBlock = 16;   // supernodes per claim
+    // blocks are claimed from the root end: the supernodes near the root
+    // carry the longest row lists, so they start first
     auto fill = [&]() {
         for (;;) {
-            const int32_t K0 = next.fetch_add(kBlock);
-            if (K0 >= ns || bad.load(std::memory_order_relaxed)) return;
-            for (int32_t K = K0; K < std::min(ns, K0 + kBlock); K++) {
+            const int32_t K1 = ns - next.fetch_add(kBlock);
+            if (K1 <= 0 || bad.load(std::memory_order_relaxed)) return;
+            for (int32_t K = std::max(0, K1 - kBlock); K < K1; K++) {
                 const int32_t s = super_ptr[K + 1] - super_ptr[K];
                 const int64_t c = rowptr[K + 1] - rowptr[K] - s;
                 const int32_t *C = rowind + rowptr[K] + s;
