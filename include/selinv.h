@@ -176,6 +176,11 @@ int selinv_plan_stats(selinv_plan plan, selinv_dtype dtype, double *flops, doubl
  *   9 panel_off[nsuper+1] int64
  *  10 active[nsuper] int32: 1 if the supernode runs under the current
  *     subset selection (selinv_plan_select), else 0
+ *  11 colbase[rowptr[nsuper]] int64, 12 relbase[rowptr[nsuper]] int64: per
+ *     row-list position rowptr[K]+s+q (q-th row of C_K), the panel element of
+ *     column C_K[q] in its owner J's panel and the offset into relidx such
+ *     that relidx[relbase + p] is the row of C_K[p] in rows(J), p >= q; zero
+ *     at the positions of K's own columns
  * Returns the element count, or <0 on a bad field.  dst may be NULL. */
 int64_t selinv_plan_get(selinv_plan plan, int field, void *dst);
 /* The plan's current options (after autotuning: the chosen ones). */

@@ -237,7 +237,8 @@ def selinv_plan_stats(plan: Plan, dtype: int) -> Tuple[float, float]:
 _PLAN_FIELDS = {"level": (0, np.int32), "seg_ptr": (1, np.int64), "seg_owner": (2, np.int32),
                 "seg_start": (3, np.int32), "seg_coloff": (4, np.int32), "rel_ptr": (5, np.int64),
                 "relidx": (6, np.int32), "level_ptr": (7, np.int64), "level_list": (8, np.int32),
-                "panel_off": (9, np.int64), "active": (10, np.int32)}
+                "panel_off": (9, np.int64), "active": (10, np.int32), "colbase": (11, np.int64),
+                "relbase": (12, np.int64)}
 
 
 def selinv_plan_get(plan: Plan, name: str) -> np.ndarray:

@@ -1108,6 +1108,8 @@ extern "C" int64_t selinv_plan_get(selinv_plan plan, int field, void *dst) {
     case 7: src = p.level_ptr.data(); cnt = (int64_t)p.level_ptr.size(); es = 8; break;
     case 8: src = p.level_list.data(); cnt = p.ns; break;
     case 9: src = p.panel_off.data(); cnt = p.ns + 1; es = 8; break;
+    case 11: src = p.colbase.data(); cnt = p.rowptr[p.ns]; es = 8; break;
+    case 12: src = p.relbase.data(); cnt = p.rowptr[p.ns]; es = 8; break;
     case 10: {   // supernodes that run under the current selection (1 = runs)
         if (dst)
             for (int32_t K = 0; K < p.ns; K++)

@@ -132,6 +132,36 @@ def test_plan_matches_oracle_bit_exact(native, make):
         assert native.selinv_plan_panel_offset(plan, K) == sym.panel_offsets()[K]
 
 
+@pytest.mark.parametrize("make", PROBLEMS[:3] + [lambda: synth.laplacian_3d(26, seed=2)])
+def test_gather_addresses_follow_the_definition(native, make):
+    """The per-position gather bases: entry (C[p], C[q]), p >= q, of A^{-1}
+    sits in the panel of the owner J of column C[q] (Sec. II-B), column
+    C[q] - first column of J, at the row of C[p] in rows(J).  Checked from the
+    row lists alone for every q and a spread of p (26^3 fills on several
+    host threads)."""
+    p = make()
+    sym = oracle.symbolic_for(p)
+    plan = make_plan(native, sym)
+    cb = native.selinv_plan_get(plan, "colbase")
+    rb = native.selinv_plan_get(plan, "relbase")
+    rel = native.selinv_plan_get(plan, "relidx")
+    sp, rp, rows = sym.super_ptr, sym.rowptr, sym.rows
+    off = sym.panel_offsets()
+    col2s = np.repeat(np.arange(sym.nsuper), np.diff(sp))
+    assert cb.size == rp[-1] and rb.size == rp[-1]
+    for K in range(sym.nsuper):
+        s = sp[K + 1] - sp[K]
+        C = rows[rp[K] + s:rp[K + 1]]
+        assert not cb[rp[K]:rp[K] + s].any() and not rb[rp[K]:rp[K] + s].any()
+        for q in range(C.size):
+            J = col2s[C[q]]
+            RJ = rows[rp[J]:rp[J + 1]]
+            pos = rp[K] + s + q
+            assert cb[pos] == off[J] + (C[q] - sp[J]) * RJ.size
+            ps = np.unique(np.r_[q, C.size - 1, np.linspace(q, C.size - 1, 5).astype(int)])
+            assert np.array_equal(RJ[rel[rb[pos] + ps]], C[ps])
+
+
 def test_plan_stats_formula(native):
     p = synth.make_config(1)
     sym = oracle.symbolic_for(p)
