@@ -1,11 +1,11 @@
-// Device buffers of released workspaces, kept for reuse.
+// Device buffers of released workspaces, kept for reuse (per device).
 //
 // A plan's numeric workspace is a dozen buffers of up to a few hundred MB
 // (panel-sized scratch, digit planes, exact sums).  Creating and destroying
 // plans of one pattern again and again (the end-to-end path re-plans from
 // host arrays every call) would pay a cudaMalloc and a synchronizing
 // cudaFree for each of them every time.  Released buffers go into a cache
-// keyed by their exact size instead, up to kCacheCap bytes; the owner
+// keyed by their device and exact size instead, up to kCacheCap bytes; the owner
 // synchronizes the device once before releasing, so that no kernel can still
 // be using a cached buffer when it is handed out again.  A failed cudaMalloc
 // empties the cache and retries; selinv_release_cached_memory empties it on
@@ -15,6 +15,7 @@
 #include <cstddef>
 #include <map>
 #include <mutex>
+#include <utility>
 
 #include "selinv.h"
 #include "plan.h"
@@ -24,20 +25,42 @@ namespace selinv {
 namespace {
 constexpr size_t kCacheCap = size_t(8) << 30;   // bytes kept at most
 std::mutex g_mu;
-std::multimap<size_t, void *> g_cache;
+std::multimap<std::pair<int, size_t>, void *> g_cache;   // (device, bytes) -> buffer
 size_t g_cached = 0;
 
+// frees every cached buffer on its own device (the current device is kept)
 void trim_locked() {
-    for (auto &e : g_cache) cudaFree(e.second);
+    if (g_cache.empty()) return;   // nothing to free: no device call
+    int cur = 0;
+    const bool have = cudaGetDevice(&cur) == cudaSuccess;
+    for (auto &e : g_cache) {
+        cudaSetDevice(e.first.first);
+        cudaFree(e.second);
+    }
+    if (have) cudaSetDevice(cur);
     g_cache.clear();
     g_cached = 0;
+}
+
+int current_device() {
+    int d = 0;
+    return cudaGetDevice(&d) == cudaSuccess ? d : 0;
+}
+
+// the device a buffer was allocated on
+int device_of(const void *ptr) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, ptr) == cudaSuccess) return a.device;
+    cudaGetLastError();
+    return current_device();
 }
 }  // namespace
 
 cudaError_t dev_alloc(void **ptr, size_t bytes) {
+    const int dev = current_device();
     {
         std::lock_guard<std::mutex> lk(g_mu);
-        auto it = g_cache.find(bytes);
+        auto it = g_cache.find(std::make_pair(dev, bytes));
         if (it != g_cache.end()) {
             *ptr = it->second;
             g_cache.erase(it);
@@ -60,9 +83,10 @@ cudaError_t dev_alloc(void **ptr, size_t bytes) {
 
 void dev_release(void *ptr, size_t bytes) {
     if (!ptr) return;
+    const int dev = device_of(ptr);
     std::lock_guard<std::mutex> lk(g_mu);
     if (g_cached + bytes <= kCacheCap) {
-        g_cache.emplace(bytes, ptr);
+        g_cache.emplace(std::make_pair(dev, bytes), ptr);
         g_cached += bytes;
     } else {
         cudaFree(ptr);
