@@ -13,7 +13,10 @@ Each check is independent of the recursion it pins:
     the pattern);
   * Alg. 1 (pull) against Alg. 2 (push), two summation orders;
   * LDL^T residual;
-  * adjoints against the dense gradient -(Z Wbar Z) and central differences.
+  * adjoints against the dense gradient -(Z Wbar Z) and central differences,
+    real and complex symmetric (plain transposes: the loss is bilinear in Z,
+    so the gradient is the holomorphic derivative and central differences
+    along the real and the imaginary axis must give the same value).
 """
 import numpy as np
 import pytest
@@ -213,14 +216,15 @@ def loss_and_grad_dense(p, sym, W):
     it, with M = Z Wbar Z and Wbar = W scattered to the lower triangle."""
     Zd = np.linalg.inv(p.dense())
     r, c, low = oracle.panel_entries(sym)
-    Wb = np.zeros((p.n, p.n))
+    Wb = np.zeros((p.n, p.n), dtype=Zd.dtype)
     Wb[r[low], c[low]] = W[low]
     M = Zd @ Wb @ Zd
     G = -(M + M.T)
     G[np.diag_indices(p.n)] = -np.diag(M)
-    grad = np.zeros(r.size)
+    grad = np.zeros(r.size, dtype=Zd.dtype)
     grad[low] = G[r[low], c[low]]
-    loss = float((W[low] * oracle.dense_to_panels(sym, Zd)[low]).sum())
+    loss = (W[low] * oracle.dense_to_panels(sym, Zd)[low]).sum()
+    loss = complex(loss) if np.iscomplexobj(loss) else float(loss)
     return loss, grad
 
 
@@ -305,3 +309,96 @@ def test_solve_matches_dense_solve(make):
     x = oracle.solve(sym, L, D, b)
     ref = np.linalg.solve(p.dense(), b)
     assert np.abs(x - ref).max() <= 1e-12 * np.abs(ref).max()
+
+
+# ------------------------------------------------- complex symmetric adjoints
+#
+# A = A^T with complex values: Z = A^{-1} is a holomorphic function of the
+# stored entries and the loss l = sum W_ij Z_ij is bilinear, so dl/da is the
+# complex derivative, dZ = -Z dA Z with plain transposes (Sec. II-C), and the
+# dense gradient is the same expression as in the real case.
+
+CPLX_ADJ = [
+    ("rand-fund", lambda: synth.random_sparse_spd(60, 0.08, 61, complex_values=True)),
+    ("rand-relaxed", lambda: synth.random_sparse_spd(70, 0.06, 62, complex_values=True,
+                                                     supernodes=synth.problems.RELAXED_128)),
+    ("dft-small", lambda: synth.dft_sheet(side=4, nbasis=4, seed=63)),
+]
+
+
+def complex_weights(low, seed):
+    rng = np.random.default_rng(seed)
+    w = rng.standard_normal(low.size) + 1j * rng.standard_normal(low.size)
+    return np.where(low, w, 0.0)
+
+
+@pytest.mark.parametrize("name,make", CPLX_ADJ)
+def test_complex_adjoint_chain_matches_dense_gradient(name, make):
+    p = make()
+    assert np.iscomplexobj(p.values)
+    sym, L, D, Z = run(p)
+    low = oracle.lower_mask(sym)
+    W = complex_weights(low, 64)
+    Lb, Db = oracle.selinv_adjoint(sym, L, D, Z, W)
+    Ab = oracle.ldlt_adjoint(sym, L, D, Lb, Db)
+    loss, grad = loss_and_grad_dense(p, sym, W)
+    assert abs(loss - (W * Z)[low].sum()) <= 1e-10 * abs(loss)
+    assert np.abs(Ab - grad)[low].max() <= 1e-10 * np.abs(grad).max(), name
+    assert np.all(Ab[~low] == 0)
+    # a conjugating (Hermitian-style) chain would be a different, wrong answer here
+    assert np.abs(Ab.conj() - grad)[low].max() > 1e-3 * np.abs(grad).max()
+
+
+def test_complex_selinv_adjoint_central_differences_on_L_and_D():
+    """Central differences of the complex loss along the real and the
+    imaginary direction of single entries of L and D: for a holomorphic
+    function both quotients equal the derivative."""
+    p = synth.random_sparse_spd(40, 0.12, 65, complex_values=True)
+    sym, L, D, Z = run(p)
+    low = oracle.lower_mask(sym)
+    W = complex_weights(low, 66)
+    Lb, Db = oracle.selinv_adjoint(sym, L, D, Z, W)
+    r, c, _ = oracle.panel_entries(sym)
+    strict = np.nonzero(r > c)[0]
+    rng = np.random.default_rng(67)
+    h = 1e-6
+    f = lambda LL, DD: complex((W * oracle.selinv(sym, LL, DD))[low].sum())
+    for e in rng.choice(strict, size=8, replace=False):
+        for step in (h, 1j * h):
+            Lp = L.copy(); Lp[e] += step
+            Lm = L.copy(); Lm[e] -= step
+            fd = (f(Lp, D) - f(Lm, D)) / (2 * step)
+            assert abs(fd - Lb[e]) <= 1e-6 * max(1.0, abs(Lb[e]))
+    for k in rng.choice(p.n, size=5, replace=False):
+        for step in (h, 1j * h):
+            Dp = D.copy(); Dp[k] += step
+            Dm = D.copy(); Dm[k] -= step
+            fd = (f(L, Dp) - f(L, Dm)) / (2 * step)
+            assert abs(fd - Db[k]) <= 1e-6 * max(1.0, abs(Db[k]))
+
+
+def test_complex_ldlt_adjoint_central_differences_on_A():
+    """dl/da for single stored entries of a complex symmetric A, through the
+    factorization and Alg. 1, by central differences of the whole chain."""
+    p = synth.random_sparse_spd(36, 0.15, 68, complex_values=True)
+    sym, L, D, Z = run(p)
+    low = oracle.lower_mask(sym)
+    W = complex_weights(low, 69)
+    Lb, Db = oracle.selinv_adjoint(sym, L, D, Z, W)
+    Ab = oracle.ldlt_adjoint(sym, L, D, Lb, Db)
+    pos = a_positions(sym, p)
+
+    def loss(vals):
+        q = synth.problems.Problem(p.name, p.n, p.colptr, p.rowind, vals, p.perm, p.supernodes, p.meta)
+        Lq, Dq = oracle.ldlt(q, sym)
+        return complex((W * oracle.selinv(sym, Lq, Dq))[low].sum())
+
+    rng = np.random.default_rng(70)
+    h = 1e-6
+    for k in rng.choice(p.values.size, size=10, replace=False):
+        for step in (h, 1j * h):
+            vp = p.values.copy(); vp[k] += step
+            vm = p.values.copy(); vm[k] -= step
+            fd = (loss(vp) - loss(vm)) / (2 * step)
+            g = Ab[pos[k]]
+            assert abs(fd - g) <= 1e-6 * max(1.0, abs(g))
