@@ -59,7 +59,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-variants", action="store_true",
                     help="skip the plain / batched / adjoint comparison runs")
-    ap.add_argument("--batch-poles", type=int, default=8)
+    ap.add_argument("--batch-poles", type=int, default=40)
     ap.add_argument("--schedule", type=int, default=1, help="0 plain, 1 level, 2 persistent")
     ap.add_argument("--autotune", type=int, default=1,
                     help="1: the library's autotuner picks its options on the first (untimed) call")
@@ -268,11 +268,11 @@ def variant_batched(dev, stream, flush, N, npoles, lap_scale):
         flops += c.stats(dts[-1])[0]
     torch.cuda.synchronize()
     plans = [c.plan for c in ctxs]
-    t_batched = time_calls(lambda: N.selinv_numeric_batched(plans, dts, Ls, Ds, Zs, stream), stream, 1, 2, flush)
+    t_batched = time_calls(lambda: N.selinv_numeric_batched(plans, dts, Ls, Ds, Zs, stream), stream, 1, 5, flush)
     def each():
         for c, d, L, D, Z in zip(ctxs, dts, Ls, Ds, Zs):
             N.selinv_numeric(c.plan, d, L, D, Z, stream)
-    t_each = time_calls(each, stream, 1, 2, flush)
+    t_each = time_calls(each, stream, 1, 5, flush)
     # pole-expansion sum over the diagonal of the pole shifts (after the timings: the
     # selection restricts the shared plan, which then needs every supernode anyway)
     poles = [i for i, c in enumerate(ctxs) if c is base_ctx]
@@ -283,10 +283,48 @@ def variant_batched(dev, stream, flush, N, npoles, lap_scale):
     t_pole = time_calls(lambda: N.selinv_pole_sum([dts[i] for i in poles], [Zs[i] for i in poles], w, pos, out,
                                                   stream), stream, 3, 10, flush)
     N.selinv_plan_select(base_ctx.plan, [], [])
+    flops_c = sum(c.stats(d)[0] for c, d in zip(ctxs, dts) if d != N.SELINV_F64)
     return {"problems": f"{npoles} complex pole shifts of the 40^3 pattern + 8 Laplacians (side x {lap_scale})",
+            "timed_calls": 5, "flops_per_call": flops, "complex_flops_per_call": flops_c,
             "batched_ms": round(t_batched, 3), "one_call_per_problem_ms": round(t_each, 3),
             "speedup": round(t_each / t_batched, 3), "gflops": round(flops / t_batched / 1e6, 2),
             "pole_sum_diag_ms": round(t_pole, 4)}
+
+
+def variant_config(dev, stream, flush, N, cfg, steps_level, steps_plain):
+    """Another configuration on its own: the level schedule (autotuned on the
+    first, untimed call) against the plain per-supernode traversal, both
+    timed with L2 flushed between calls."""
+    import torch
+    import synth
+    from paper_1604_02528_gb300.api import SelInvContext
+    p = synth.make_config(cfg)
+    ctx = SelInvContext.from_problem(p)
+    dt = N.SELINV_C128 if p.values.dtype.kind == "c" else N.SELINV_F64
+    L, D = ctx.factor(torch.from_numpy(p.values).to(dev))
+    Z = torch.empty_like(L)
+    ctx.set_options(autotune=1)
+    N.selinv_numeric(ctx.plan, dt, L, D, Z, stream)
+    stream.synchronize()
+    if ctx.status() != 0:
+        raise RuntimeError(f"configuration {cfg} reported a device error")
+    topts = N.selinv_plan_get_opts(ctx.plan)
+    topts.autotune = 0
+    N.selinv_plan_set_opts(ctx.plan, topts)
+    t_level = time_calls(lambda: N.selinv_numeric(ctx.plan, dt, L, D, Z, stream), stream, 3, steps_level, flush)
+    o = N.selinv_default_opts()
+    o.schedule = N.SELINV_SCHED_PLAIN
+    N.selinv_plan_set_opts(ctx.plan, o)
+    t_plain = time_calls(lambda: N.selinv_numeric(ctx.plan, dt, L, D, Z, stream), stream, 1, steps_plain, flush)
+    F, B = ctx.stats(dt)
+    return {"workload": workload_name(cfg), "dtype": "c128" if dt != N.SELINV_F64 else "f64",
+            "n": p.n, "nsuper": ctx.nsuper, "flops_per_step": F, "bytes_per_step": B,
+            "level_ms": round(t_level, 4), "level_steps": steps_level,
+            "plain_ms": round(t_plain, 4), "plain_steps": steps_plain,
+            "level_over_plain_speedup": round(t_plain / t_level, 3),
+            "gflops": round(F / t_level / 1e6, 2),
+            "contraction": {0: "FP64 DFMA", 1: "tcgen05", 2: "mma.sync"}[topts.fast_contraction],
+            "oz_min_s": topts.oz_min_s}
 
 
 def variant_selection(ctx, dt, L, D, Z, stream, flush, N):
@@ -346,11 +384,37 @@ def oracle_sample_setup(problem):
     return sym, L, D
 
 
-def oracle_sample_run(sym, L, D, kmin):
+def oracle_sample_run(sym, L, D, kmin, threads=1):
+    """Wall time of the oracle's Alg. 1 over the supernodes K >= kmin; with
+    threads > 1 the supernodes of one tree level run on that many host
+    threads at a time (the same per-supernode steps, bit for bit)."""
     import oracle
     t = time.perf_counter()
-    oracle.selinv_top(sym, L, D, kmin)
+    if threads > 1:
+        oracle.selinv_levels(sym, L, D, threads, kmin=kmin)
+    else:
+        oracle.selinv_top(sym, L, D, kmin)
     return time.perf_counter() - t
+
+
+def host_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def host_cpu_model() -> str:
+    try:
+        with open("/proc/cpuinfo") as fh:
+            for line in fh:
+                k = line.split(":")[0].strip().lower()
+                if k in ("model name", "cpu part"):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
 
 
 def run_reference(args):
@@ -362,19 +426,21 @@ def run_reference(args):
     p = synth.make_config(args.config)
     sym, L, D = oracle_sample_setup(p)
     kmin, fs = sample_kmin(sym, 3.0e9)
+    cores = host_cores()
     for _ in range(args.warmup):
-        oracle_sample_run(sym, L, D, kmin)
-    times = [oracle_sample_run(sym, L, D, kmin) for _ in range(args.steps)]
+        oracle_sample_run(sym, L, D, kmin, cores)
+    times = [oracle_sample_run(sym, L, D, kmin, cores) for _ in range(args.steps)]
     tot = sum(times)
     value = fs * len(times) / tot / 1e9
     sample = (f"supernodes {kmin}..{sym.nsuper - 1} of {sym.nsuper} (root side of the tree), "
-              f"{fs:.3e} of {sample_kmin(sym, 1e30)[1]:.3e} flops per step")
+              f"{fs:.3e} of {sample_kmin(sym, 1e30)[1]:.3e} flops per step, each tree level on "
+              f"{cores} host threads ({host_cpu_model()})")
     line = {"impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": "GFLOP/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": round(1e3 * tot / len(times), 3), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": workload_name(args.config), "sample": sample},
-            "cpu_baseline": {"value": round(value, 4), "unit": "GFLOP/s", "cores": 1,
+            "cpu_baseline": {"value": round(value, 4), "unit": "GFLOP/s", "cores": cores,
                              "kind": "oracle", "sample": sample},
             "e2e": {"value": round(value, 4), "unit": "GFLOP/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
@@ -541,15 +607,24 @@ def main():
         variants["selection"] = variant_selection(ctx, dt, L, D, Z, stream, flush, N)
         variants["batched"] = variant_batched(dev, stream, flush, N, args.batch_poles, 1.0)
         variants["adjoint"] = variant_adjoint(dev, stream, flush, N)
+        variants["config1"] = variant_config(dev, stream, flush, N, 1, 50, 20)
+        variants["config3"] = variant_config(dev, stream, flush, N, 3, 10, 3)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        # the oracle as it stands: (i) the whole selected inversion with each
+        # tree level on all host cores; (ii) one core on a root-side sample
         sym, Lo, Do = oracle_sample_setup(p)
+        cores = host_cores()
+        secs_all = oracle_sample_run(sym, Lo, Do, 0, cores)
         kmin, fs = sample_kmin(sym, 1.2e10)
         secs = oracle_sample_run(sym, Lo, Do, kmin)
-        cpu = {"value": round(fs / secs / 1e9, 4), "unit": "GFLOP/s", "cores": 1, "kind": "oracle",
-               "sample": f"root-side supernodes {kmin}..{sym.nsuper - 1} of {sym.nsuper}, "
-                         f"{fs:.3e} of {F:.3e} flops, {secs:.1f} s"}
+        cpu = {"value": round(F / secs_all / 1e9, 4), "unit": "GFLOP/s", "cores": cores, "kind": "oracle",
+               "sample": f"the whole selected inversion ({F:.3e} flops, {secs_all:.1f} s), the supernodes of "
+                         f"each tree level on {cores} host threads ({host_cpu_model()})",
+               "single_core": {"value": round(fs / secs / 1e9, 4), "unit": "GFLOP/s", "cores": 1,
+                               "sample": f"root-side supernodes {kmin}..{sym.nsuper - 1} of {sym.nsuper}, "
+                                         f"{fs:.3e} of {F:.3e} flops, {secs:.1f} s"}}
 
     clocks = clk.summary()
     if rank == 0:

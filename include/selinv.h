@@ -230,8 +230,11 @@ int selinv_factor(selinv_plan plan, selinv_dtype dtype, const void *A_vals_dev, 
  * Reverse mode (no counterpart in the paper; the chain rule through the
  * steps of Alg. 1 taken leaves-to-root, recomputing the gathers of
  * A^{-1}_{C,C}).  F64 only.
- *   selinv_adjoint: given the cotangent Ainv_bar of every stored lower entry of
- *     A^{-1} (panels; the strictly upper part of diagonal blocks is ignored),
+ *   selinv_adjoint: given the cotangent Ainv_bar of every panel slot that
+ *     selinv_numeric writes (panels: the lower entries and the strictly upper
+ *     part of the diagonal blocks, which holds the mirrored lower entries; a
+ *     cotangent on an upper slot counts for its lower mirror, so a caller
+ *     that differentiates only the lower entries passes zeros there),
  *     returns L_bar (panels, strictly lower entries) and D_bar [n].  Uses the
  *     forward outputs L, D, Ainv.  Ainv_bar is not modified (the plan keeps a
  *     working copy).
@@ -355,7 +358,10 @@ int selinv_status(selinv_plan plan);
  * SELINV_NOALLOC_MAX_S^2 doubles (128 KB) that every GPU loading the library
  * holds until the process exits.  Its device address is looked up on the
  * first call on each device (with that device current), so make the first
- * call on a device before any stream capture.  All calls share the array:
+ * call on a device before any stream capture.  The looked-up address is
+ * kept for the life of the process; cudaDeviceReset invalidates it, so do
+ * not call this entry point on a device after resetting that device.  All
+ * calls share the array:
  * calls that overlap on the GPU (different streams, no ordering between
  * them) race on it.  Nothing in it needs clearing between calls.
  * Asynchronous on cuda_stream; no cudaMalloc, cudaFree or allocating library

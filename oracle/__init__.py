@@ -11,6 +11,8 @@ the paper's definitions and algorithms with plain loops:
 * ``ldlt``      -- LDL^T without pivoting on the supernodal pattern (Sec. IV)
 * ``selinv``    -- Alg. 1 (pull), diagonal blocks symmetrized (Sec. II-C);
                    ``hermitian=True``: conjugate transposes, A = A^H
+* ``selinv_levels`` -- the same per-supernode steps, one tree level at a time
+                   on several host threads (bit for bit ``selinv``)
 * ``selinv_push`` -- Alg. 2 (left-looking push), a different summation order
 * ``lu``, ``selinv_lu`` -- nonsymmetric values: LU without pivoting (U kept
                    transposed in the panel layout) and Alg. 1 in its LU form
@@ -72,6 +74,10 @@ def _load():
             f = getattr(lib, "orc_ldlt_adjoint" + sfx)
             f.restype = ct.c_int
             f.argtypes = [ct.c_int32, P, P, P, P, P, P, P, P, P]
+        for sfx in ("_d", "_z", "_h"):
+            f = getattr(lib, "orc_selinv_levels" + sfx)
+            f.restype = ct.c_int
+            f.argtypes = [ct.c_int32, P, P, P, P, P, P, P, ct.c_int, ct.c_int32, ct.c_int]
         # complex Hermitian: the factorization and Alg. 1 only
         lib.orc_ldlt_h.restype = ct.c_int
         lib.orc_ldlt_h.argtypes = [ct.c_int32, P, P, P, ct.c_int32, P, P, P, P, P, P]
@@ -247,6 +253,23 @@ def selinv_top(sym: Sym, L: np.ndarray, D: np.ndarray, kmin: int, Z: np.ndarray 
     rc = getattr(lib, "orc_selinv_top" + _sfx(L.dtype))(*_sym_args(sym), _p(L), _p(D), _p(Z),
                                                        int(symmetrize), int(kmin))
     _check(rc, "selinv_top")
+    return Z
+
+
+def selinv_levels(sym: Sym, L: np.ndarray, D: np.ndarray, nthreads: int, kmin: int = 0,
+                  Z: np.ndarray = None, symmetrize: bool = True, hermitian: bool = False) -> np.ndarray:
+    """Alg. 1 with the supernodes of one tree level on ``nthreads`` host
+    threads at a time (root level first); supernodes K >= kmin.  Bit for bit
+    the result of ``selinv`` / ``selinv_top``."""
+    lib = _load()
+    L = np.ascontiguousarray(L); D = np.ascontiguousarray(D, dtype=L.dtype)
+    if Z is None:
+        Z = np.zeros_like(L)
+    if hermitian and L.dtype.kind != "c":
+        raise ValueError("the Hermitian form takes complex values")
+    fn = getattr(lib, "orc_selinv_levels" + ("_h" if hermitian else _sfx(L.dtype)))
+    rc = fn(*_sym_args(sym), _p(L), _p(D), _p(Z), int(symmetrize), int(kmin), int(nthreads))
+    _check(rc, "selinv_levels")
     return Z
 
 

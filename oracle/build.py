@@ -20,7 +20,7 @@ def build(force: bool = False) -> str:
             and os.path.getmtime(TARGET) >= max(os.path.getmtime(d) for d in deps)):
         return TARGET
     tmp = TARGET + f".tmp{os.getpid()}"
-    cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-o", tmp] + srcs + ["-lm"]
+    cmd = ["gcc", "-O2", "-std=gnu11", "-pthread", "-fPIC", "-shared", "-o", tmp] + srcs + ["-lm"]
     subprocess.run(cmd, check=True, cwd=HERE)
     os.replace(tmp, TARGET)
     return TARGET

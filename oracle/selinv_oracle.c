@@ -15,10 +15,13 @@
  *   orc_symbolic / orc_sym_get / orc_sym_free / orc_plan  (oracle_symbolic.c)
  *   orc_ldlt_*          supernodal-pattern LDL^T, no pivoting (Sec. IV prerequisite)
  *   orc_selinv_*        Alg. 1 (pull), symmetrized diagonal blocks (Sec. II-C)
+ *   orc_selinv_levels_* the same steps, the supernodes of one tree level on
+ *                       host threads at a time (bit for bit orc_selinv)
  *   orc_selinv_push_*   Alg. 2 (left-looking push: outer/inner products)
  *   orc_selinv_adjoint_*, orc_ldlt_adjoint_*   reverse mode of the two above
  */
 #include <complex.h>
+#include <pthread.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>

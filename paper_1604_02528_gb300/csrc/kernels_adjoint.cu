@@ -174,6 +174,28 @@ __global__ void __launch_bounds__(256) k_adj_vupd(const AdjDesc *__restrict__ ad
     seg_update<double, decltype(x), decltype(y), decltype(out), kVB>(pa, np, st, nq, 2 * sK, x, y, out, sm);
 }
 
+// The forward writes whole diagonal blocks (the strictly upper part holds
+// copies of the lower entries), so a cotangent may arrive on an upper slot:
+// add it to the lower mirror and clear it, one CTA per supernode.  Every
+// later step reads only the lower triangle of a diagonal block.
+__global__ void __launch_bounds__(256) k_adj_fold(const AdjDesc *__restrict__ ad, int ns) {
+    const int K = blockIdx.x;
+    if (K >= ns) return;
+    const AdjDesc &A = *ad;
+    const int s = A.super_ptr[K + 1] - A.super_ptr[K];
+    const int64_t ld = A.rowptr[K + 1] - A.rowptr[K];
+    double *Zb = A.Zb + A.panel_off[K];
+    for (int e = threadIdx.x; e < s * s; e += blockDim.x) {
+        const int i = e % s, j = e / s;
+        if (i <= j) continue;
+        const double up = Zb[(int64_t)i * ld + j];
+        if (up != 0.0) {
+            Zb[(int64_t)j * ld + i] += up;
+            Zb[(int64_t)i * ld + j] = 0.0;
+        }
+    }
+}
+
 // S (tile 0) and Ybar rows of one tile
 __global__ void __launch_bounds__(256) k_adj_ybar(const AdjDesc *__restrict__ ad,
                                                   const Item *__restrict__ items, int nitems) {
@@ -1152,6 +1174,8 @@ extern "C" int selinv_adjoint(selinv_plan plan, selinv_dtype dtype, const void *
                            static_cast<const double *>(Z), static_cast<double *>(Lbar),
                            static_cast<double *>(Dbar));
     cudaMemcpyAsync(a->d_desc, &h, sizeof(h), cudaMemcpyHostToDevice, st);
+    k_adj_fold<<<p.ns, 256, 0, st>>>(a->d_desc, p.ns);
+    note_launch();
     FactorData *f = plan->factor;
     cudaMemsetAsync(a->V, 0, 8 * (size_t)std::max<int64_t>(f->u_off[p.ns], 1), st);
     Workspace &w = plan->ws[0];

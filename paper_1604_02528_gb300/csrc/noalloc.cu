@@ -27,7 +27,10 @@ constexpr int kMaxDevices = 64;
 static __device__ __align__(256) double g_linv_scratch[kMaxS * kMaxS];
 
 // Device address of g_linv_scratch per device ordinal, looked up once per
-// device (in host code the symbol is only a host-side stand-in).
+// device (in host code the symbol is only a host-side stand-in).  The
+// address belongs to the device's primary context: after cudaDeviceReset
+// the module is loaded again and the cached address is stale, so a process
+// that resets a device must not call this entry point on it afterwards.
 std::mutex g_lock;
 double *g_addr[kMaxDevices] = {nullptr};
 

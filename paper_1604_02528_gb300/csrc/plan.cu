@@ -41,6 +41,9 @@ static void dfree(void *p) {
 
 void Workspace::release() {
     if (!owned.empty()) {
+        // the buffers' own device: its kernels must be done with them, and
+        // the reuse cache files them under that device
+        DeviceGuard g(device);
         cudaDeviceSynchronize();   // no kernel may still use a buffer that goes into the cache
         for (auto &o : owned) dev_release(o.first, o.second);
         owned.clear();
@@ -75,6 +78,8 @@ int Workspace::ensure(const PlanData &p, int dtype) {
     const size_t es = elem_size(dtype);
     if (LD && bytes_elem >= es) return SELINV_OK;
     release();
+    DeviceGuard g(p.device);
+    device = p.device;
     if (!wget(*this, &LD, es * (size_t)std::max<int64_t>(p.nnz, 1))) return SELINV_ERR_OOM;
     if (!wget(*this, &Linv, es * (size_t)std::max<int64_t>(p.linv_total, 1))) return SELINV_ERR_OOM;
     if (!wget(*this, &partial, es * (size_t)std::max<int64_t>(p.part_max, 1))) return SELINV_ERR_OOM;
@@ -119,6 +124,7 @@ int Workspace::ensure(const PlanData &p, int dtype) {
 // the LU form's extra scratch (element size of the current workspace)
 int Workspace::ensure_lu(const PlanData &p) {
     if (LDu) return SELINV_OK;
+    DeviceGuard g(device);
     if (!wget(*this, &LDu, bytes_elem * (size_t)std::max<int64_t>(p.nnz, 1))) return SELINV_ERR_OOM;
     if (!wget(*this, &Vt, bytes_elem * (size_t)std::max<int64_t>(p.linv_total, 1))) return SELINV_ERR_OOM;
     return SELINV_OK;
@@ -126,6 +132,7 @@ int Workspace::ensure_lu(const PlanData &p) {
 
 int Workspace::ensure_persistent(const PlanData &p) {
     if (partial_all) return SELINV_OK;
+    DeviceGuard g(device);
     if (!wget(*this, &partial_all, bytes_elem * (size_t)std::max<int64_t>(p.part_all, 1)))
         return SELINV_ERR_OOM;
     return SELINV_OK;
@@ -342,6 +349,7 @@ static int build_plan(PlanData &p, int32_t n, int32_t ns, const int32_t *super_p
 // and inspected on a host without a GPU).
 int ensure_device(PlanData &p) {
     if (p.d_status) return SELINV_OK;
+    if (cudaGetDevice(&p.device) != cudaSuccess) return SELINV_ERR_CUDA;
     static bool configured = false;
     if (!configured) {
         if (configure_selinv_kernels() != cudaSuccess) return SELINV_ERR_CUDA;
@@ -1057,6 +1065,7 @@ extern "C" int selinv_symbolic(int32_t n, int32_t nsuper, const int32_t *super_p
 }
 
 selinv_plan_s::~selinv_plan_s() {
+    DeviceGuard g(data.device);   // free on the plan's device, whichever is current
     single.release();
     lu.release();
     for (auto &b : batch_cache) b.sched.release();

@@ -29,6 +29,7 @@ template <typename T> using fill_vector = std::vector<T, UninitAlloc<T>>;
 
 struct PlanData {
     int32_t n = 0, ns = 0;
+    int device = -1;   // CUDA device of the plan's device arrays (set by ensure_device)
     selinv_opts opts{};
     bool tuned[3] = {false, false, false};   // autotuning done, per selinv_dtype
     // host arrays (kept for inspection and schedule building)
@@ -64,7 +65,24 @@ struct PlanData {
 // Numeric scratch of one problem: Dinv/Lhat panels, L_KK^{-1} blocks, split
 // partials of the diagonal blocks, per-supernode tile counters and
 // completion flags, and one more panel-sized buffer (adjoint working copy).
+// Makes `dev` the current device for a scope and restores the caller's
+// device afterwards (dev < 0: nothing to do).
+struct DeviceGuard {
+    int prev = -1;
+    bool switched = false;
+    explicit DeviceGuard(int dev) {
+        if (dev >= 0 && cudaGetDevice(&prev) == cudaSuccess && prev != dev)
+            switched = cudaSetDevice(dev) == cudaSuccess;
+    }
+    ~DeviceGuard() {
+        if (switched) cudaSetDevice(prev);
+    }
+    DeviceGuard(const DeviceGuard &) = delete;
+    DeviceGuard &operator=(const DeviceGuard &) = delete;
+};
+
 struct Workspace {
+    int device = -1;           // device the buffers below live on
     void *LD = nullptr, *Linv = nullptr, *partial = nullptr, *work = nullptr;
     void *partial_all = nullptr;  // persistent schedule: supernodes of every level in flight at once
     int *counter = nullptr, *done = nullptr;

@@ -18,6 +18,7 @@ from .problems import (  # noqa: F401
     random_sparse_hpd,
     magnetic_laplacian_3d,
     random_sparse_nonsym,
+    symmetric_scaling,
     tridiagonal,
     make_config,
     lower_pattern_weights,

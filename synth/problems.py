@@ -22,7 +22,7 @@ __all__ = [
     "Problem", "grid_nd_order", "laplacian_2d", "laplacian_3d", "dft_sheet",
     "diffusion_3d", "pole_shifts", "batch_laplacians", "random_sparse_spd",
     "tridiagonal", "make_config", "lower_pattern_weights", "random_sparse_hpd",
-    "magnetic_laplacian_3d", "random_sparse_nonsym",
+    "magnetic_laplacian_3d", "random_sparse_nonsym", "symmetric_scaling",
 ]
 
 FUNDAMENTAL_64 = {"kind": "fundamental", "cap": 64, "fill": 0.0}
@@ -208,17 +208,18 @@ def laplacian_2d(nx: int, ny: Optional[int] = None, shift: float = 0.1,
 
 
 def laplacian_3d(nx: int, seed: int, name: Optional[str] = None,
-                 supernodes: Optional[Dict[str, object]] = None) -> Problem:
-    """3D 7-point Laplacian, diagonal 6 + U(0,1) (seeded, by original node id)."""
+                 supernodes: Optional[Dict[str, object]] = None, shift: float = 0.0) -> Problem:
+    """3D 7-point Laplacian, diagonal 6 + shift + U(0,1) (seeded, by original
+    node id).  A large shift makes A^{-1} decay fast away from the diagonal."""
     dims = (nx, nx, nx)
     n = nx ** 3
     rng = np.random.default_rng(seed)
-    diag = 6.0 + rng.uniform(0.0, 1.0, n)
+    diag = 6.0 + shift + rng.uniform(0.0, 1.0, n)
     perm = grid_nd_order(dims)
     ei, ej = _grid_edges(dims)
     colptr, rowind, vals, _ = _lower_csc(n, perm, diag, ei, ej, np.full(ei.size, -1.0))
     return Problem(name or f"lap3d_{nx}", n, colptr, rowind, vals.astype(np.float64), perm,
-                   dict(supernodes or RELAXED_128), {"dims": dims, "seed": seed})
+                   dict(supernodes or RELAXED_128), {"dims": dims, "seed": seed, "shift": shift})
 
 
 # ---------------------------------------------------------------------------
@@ -475,6 +476,22 @@ def _hermitian_lower(n: int, perm: np.ndarray, diag: np.ndarray, ei: np.ndarray,
     iperm[perm] = np.arange(n, dtype=np.int64)
     ev = np.where(iperm[ei] > iperm[ej], ev, np.conj(ev))
     return _lower_csc(n, perm, diag, ei, ej, ev)
+
+
+def symmetric_scaling(p: Problem, decades: float, seed: int) -> Problem:
+    """S A S with S = diag(10^u), u ~ U(-decades/4, decades/4) per original
+    node: still symmetric (positive definite if A is), its diagonal spread
+    over about `decades` orders of magnitude, and the entries of A^{-1}
+    (= S^{-1} A^{-1} S^{-1}) spread over as many within each row."""
+    rng = np.random.default_rng(seed)
+    u = 10.0 ** rng.uniform(-decades / 4.0, decades / 4.0, p.n)
+    sc = u[p.perm]                                  # by permuted index
+    cols = np.repeat(np.arange(p.n), np.diff(p.colptr))
+    vals = p.values * sc[p.rowind] * sc[cols]
+    meta = dict(p.meta)
+    meta["scaling_decades"] = decades
+    return Problem(p.name + f"_scaled{decades:g}", p.n, p.colptr, p.rowind, vals, p.perm,
+                   dict(p.supernodes), meta)
 
 
 def random_sparse_hpd(n: int, density: float, seed: int,

@@ -123,3 +123,60 @@ def test_autograd_diffusion_gradient(native, cuda_device):
             vals.append(float((W * oracle.selinv(sym, Lq, Dq)).sum()))
         fd = (vals[0] - vals[1]) / (2 * h)
         assert abs(fd - g[e]) <= 1e-6 * max(1.0, abs(g[e]))
+
+
+def test_autograd_unmasked_loss_reads_whole_diagonal_blocks(native, cuda_device):
+    """The forward returns whole diagonal blocks (upper part = mirrored lower
+    entries).  A loss over every returned slot (Z.sum() and an unmasked W)
+    must give the gradient of that loss: on the oracle side the upper slots'
+    weights are added to their lower mirrors (same value of Z)."""
+    import torch
+    from paper_1604_02528_gb300.api import SelInvContext
+    from paper_1604_02528_gb300.autograd import SelInv
+    p = synth.random_sparse_spd(120, 0.05, 91, supernodes=synth.problems.RELAXED_128)
+    sym = oracle.symbolic_for(p)
+    low = oracle.lower_mask(sym)
+    r, c, _ = oracle.panel_entries(sym)
+    rng = np.random.default_rng(92)
+    ctx = SelInvContext.from_problem(p)
+    L0, D0 = oracle.ldlt(p, sym)
+    Z0 = oracle.selinv(sym, L0, D0)
+    pos = a_positions(sym, p)
+    # mirror slot of each upper diagonal-block slot (same supernode, same panel)
+    off = sym.panel_offsets()
+    sp = sym.super_ptr
+    col2s = np.repeat(np.arange(sym.nsuper), np.diff(sp))
+    mirror = np.arange(low.size)
+    up = np.nonzero(~low)[0]
+    for e in up:
+        i, j = int(r[e]), int(c[e])          # row i < column j, both columns of one supernode
+        K = col2s[j]
+        ld = sym.rowptr[K + 1] - sym.rowptr[K]
+        mirror[e] = off[K] + (i - sp[K]) * ld + (j - sp[K])
+    for kind in ("sum", "unmasked"):
+        W = np.ones(low.size) if kind == "sum" else rng.standard_normal(low.size)
+        A = torch.from_numpy(p.values).cuda().requires_grad_(True)
+        Z = SelInv.apply(ctx, A)
+        loss = (torch.from_numpy(W).cuda() * Z).sum()
+        loss.backward()
+        g = A.grad.cpu().numpy()
+        Wf = np.where(low, W, 0.0)
+        np.add.at(Wf, mirror[up], W[up])
+        Lb0, Db0 = oracle.selinv_adjoint(sym, L0, D0, Z0, Wf)
+        Ab0 = oracle.ldlt_adjoint(sym, L0, D0, Lb0, Db0)
+        assert rel(g, Ab0[pos]) <= 1e-10, kind
+        assert abs(loss.item() - float((W * Z0).sum())) <= 1e-10 * abs(float((W * Z0).sum()))
+
+
+def test_autograd_raises_on_zero_pivot(native, cuda_device):
+    """A zero pivot in the forward factorization is reported, not returned."""
+    import torch
+    from paper_1604_02528_gb300.api import SelInvContext
+    from paper_1604_02528_gb300.autograd import SelInv
+    # [[0, 1], [1, 0]]: the first pivot is exactly zero
+    colptr = np.array([0, 2, 3], np.int64)
+    rowind = np.array([0, 1, 1], np.int32)
+    ctx = SelInvContext(2, colptr, rowind)
+    A = torch.tensor([0.0, 1.0, 0.0], dtype=torch.float64, device="cuda").requires_grad_(True)
+    with pytest.raises(native.SelinvError):
+        SelInv.apply(ctx, A)

@@ -402,3 +402,27 @@ def test_complex_ldlt_adjoint_central_differences_on_A():
             fd = (loss(vp) - loss(vm)) / (2 * step)
             g = Ab[pos[k]]
             assert abs(fd - g) <= 1e-6 * max(1.0, abs(g))
+
+
+# ------------------------------------------------- level-parallel oracle
+
+@pytest.mark.parametrize("name,make,herm", [
+    ("lap3d-9", lambda: synth.laplacian_3d(9, seed=71), False),
+    ("rand-cplx-relaxed", lambda: synth.random_sparse_spd(150, 0.04, 72, complex_values=True,
+                                                          supernodes=synth.problems.RELAXED_128), False),
+    ("hpd", lambda: synth.random_sparse_hpd(120, 0.05, 73), True),
+])
+def test_level_parallel_oracle_is_bitwise_serial(name, make, herm):
+    """Supernodes of one tree level share no output and read only earlier
+    levels: the threaded traversal reproduces the serial one bit for bit,
+    for any thread count, and also on a root-side subset."""
+    p = make()
+    sym = oracle.symbolic_for(p)
+    L, D = oracle.ldlt(p, sym)     # the Hermitian factorization for a Hermitian problem
+    Z = oracle.selinv(sym, L, D, hermitian=herm)
+    for nt in (1, 3, 8):
+        Zp = oracle.selinv_levels(sym, L, D, nt, hermitian=herm)
+        assert np.array_equal(Zp, Z), (name, nt)
+    if not herm:
+        kmin = sym.nsuper // 2
+        assert np.array_equal(oracle.selinv_levels(sym, L, D, 4, kmin=kmin), oracle.selinv_top(sym, L, D, kmin))
