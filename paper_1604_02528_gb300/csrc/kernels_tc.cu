@@ -24,18 +24,16 @@
 #include "common.cuh"
 #include "fixedpoint.cuh"
 #include "launch.h"
+#include "tc_digits.cuh"
 #include "tile_gemm.cuh"
 #include "umma.cuh"
 
 namespace selinv {
 
-constexpr int kTcM = 128;          // rows of C per item (tensor-memory lanes)
 constexpr int kTcProd = 16;        // producer warps: gather + digits of A (4 values per thread and step)
 constexpr int kTcEpi = 8;          // epilogue warps: two per tensor-memory lane quarter (half the columns each)
 constexpr int kTcMmaWarp = kTcProd + kTcEpi;
 constexpr int kTcThreads = 32 * (kTcProd + kTcEpi + 1);
-constexpr int kTcDig = 7;
-constexpr int kTcFlush = 8;        // k16 steps per exact fp32 chunk (128 k)
 // slab slot of a split-k item: (hi, lo) words [64 columns][128 rows] each, then the rows' exponents
 constexpr int64_t kTcSlot = kTcSlotWords;
 static_assert(kTcSlotWords == 2 * kTcM * 64 + kTcM / 2, "slot layout");
@@ -52,92 +50,6 @@ template <int TN> struct TcCfg {
         sizeof(int) * kTcM;
 };
 
-// x = M * 2^(E - 1076) with |M| < 2^54 (E >= the biased exponent of x),
-// truncated toward zero; integer operations only.
-__device__ __forceinline__ long long fixed54(double x, int E) {
-    const long long b = __double_as_longlong(x);
-    const int ex = (int)((b >> 52) & 0x7FF);
-    const long long mant = ex ? ((b & 0xFFFFFFFFFFFFFll) | (1ll << 52)) : 0ll;
-    const int sh = E - ex - 1;
-    const long long M = sh < 0 ? (mant << 1) : (sh < 63 ? (mant >> sh) : 0ll);
-    return b < 0 ? -M : M;
-}
-
-// With u = M + 0x80808080808080 (M as above), byte t of u minus 128 is the
-// balanced base-256 digit of weight 256^t, in [-128, 127].  The digits of
-// byte t of two values as an fp16 pair (w0's in the low half): the bytes are
-// placed in the mantissas of 1024 + byte (fp16 bits 0x6400 | byte) and 1152
-// is subtracted -- exact, three instructions per pair.
-template <int T>
-__device__ __forceinline__ uint32_t digit_pair(uint32_t w0, uint32_t w1) {
-    const uint32_t b = __byte_perm(w0, w1, (T & 3) | (((T & 3) + 4) << 8) | (((T & 3) + 4) << 16)) & 0x00FF00FFu;
-    const uint32_t h = b | 0x64006400u;
-    uint32_t r;
-    asm("add.rn.f16x2 %0, %1, %2;\n" : "=r"(r) : "r"(h), "r"(0xE480E480u));   // + (-1152, -1152)
-    return r;
-}
-
-// The digit products of one k16 step, A digit planes i (128 rows) against B
-// digit planes j (TN rows each), summed into group i + j at tensor-memory
-// columns (i + j) TN.  The 7 B planes lie one after the other with the
-// row-group stride of the operand layout, so planes j0 .. j0 + m - 1 form one
-// operand of m TN rows: one MMA of N = m TN (at most 256) at columns
-// (i + j0) TN computes A_i B_j0 .. A_i B_{j0+m-1} into groups i + j0 ..
-// i + j0 + m - 1.  Per step 10 MMAs for TN = 64, 7 for TN <= 32 (against 28
-// of N = TN).  A group starts from zero at the first step of a chunk, with
-// the products of A plane 0.
-template <int TN, int A_PLANE, int B_PLANE>
-__device__ __forceinline__ void digit_products(uint32_t tmem, uint64_t ad0, uint64_t bd0, bool first) {
-    constexpr int kPer = 256 / TN;   // B planes per MMA (N <= 256)
-#pragma unroll
-    for (int i = 0; i < kTcDig; i++) {
-        const uint64_t ad = ad0 + (uint64_t)(i * A_PLANE * 2 / 16);
-#pragma unroll
-        for (int j0 = 0; j0 < kTcDig - i; j0 += kPer) {
-            const int m = kTcDig - i - j0 < kPer ? kTcDig - i - j0 : kPer;
-            const uint64_t bd = bd0 + (uint64_t)(j0 * B_PLANE * 2 / 16);
-            umma::mma_f16kind(tmem + (uint32_t)((i + j0) * TN), ad, bd, umma::idesc_f16_f32(kTcM, m * TN),
-                              (first && i == 0) ? 0u : 1u);
-        }
-    }
-}
-
-// Digit plane PL (weight 256^(6 - PL)) of the 4 values whose biased fixed-
-// point words are (lo[u], hi[u]): half a 16-byte core-matrix row of fp16.
-template <int PL>
-__device__ __forceinline__ void store_plane4(uint16_t *dst, const uint32_t (&lo)[4], const uint32_t (&hi)[4]) {
-    constexpr int T = 6 - PL;
-    const uint32_t(&w)[4] = T >= 4 ? hi : lo;
-    uint2 q;
-    q.x = digit_pair<T>(w[0], w[1]);
-    q.y = digit_pair<T>(w[2], w[3]);
-    *reinterpret_cast<uint2 *>(dst) = q;
-}
-
-// Address of entry (p, q) of A^{-1}_{C,C} in the ancestors' panels (stored at
-// (max, min) by symmetry) in two parts: a base known at once and the relative
-// row, which comes from memory -- so that its load can stay in flight; base
-// -1 outside C x C.  pl = p - p0.
-struct TcGather {
-    const int64_t *pcb, *prb;
-    const int32_t *relidx;
-    const int64_t *tile_cb, *tile_rb;
-    int p0, c;
-    __device__ __forceinline__ void parts(int pl, int q, int64_t &base, int32_t &rel) const {
-        const int p = p0 + pl;
-        if (p >= c || q >= c) {
-            base = -1;
-            rel = 0;
-        } else if (p >= q) {
-            base = pcb[q];
-            rel = relidx[prb[q] + p];
-        } else {
-            base = tile_cb[pl];
-            rel = relidx[tile_rb[pl] + q];
-        }
-    }
-};
-
 template <int TN>
 __global__ void __launch_bounds__(kTcThreads, 1) k_selinv_tc(const ProbDesc *__restrict__ descs,
                                                              const Item *__restrict__ items, int nitems,
@@ -150,11 +62,12 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_selinv_tc(const ProbDesc *__r
     long long *Lo = Hi + kTcM * TN;                                        // [TN][128]
     int *rowE = reinterpret_cast<int *>(Lo + kTcM * TN);                   // [128]
     __shared__ int64_t tile_cb[kTcM], tile_rb[kTcM];
-    // full[s]: the producer warps wrote A and the bulk copies of B landed in
-    // stage s; empty[s]: the products that read stage s are done; acc_full: a
-    // chunk's group sums are complete in tensor memory; tmem_free: the
-    // epilogue warps have read them
-    __shared__ __align__(8) uint64_t full[2], empty[2], acc_full, tmem_free;
+    // full[s]: the producer warps wrote A in stage s; bfull[s]: the bulk
+    // copies of B landed there; empty[s]: the products that read stage s are
+    // done; acc_full: a chunk's group sums are complete in tensor memory;
+    // tmem_free: the epilogue warps have read them; drain: every product
+    // issued before an abort is done
+    __shared__ __align__(8) uint64_t full[2], bfull[2], empty[2], acc_full, tmem_free, drain;
     __shared__ uint32_t s_tmem;
     __shared__ int s_pre;
     __shared__ volatile int s_abort;
@@ -162,6 +75,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_selinv_tc(const ProbDesc *__r
 
     const int w = blockIdx.x;
     if (w >= nitems) return;
+    const long long mlim = wait_limit > kMbarMinPolls ? wait_limit : kMbarMinPolls;
     const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
     const Item it = items[w];
     const ProbDesc &P = descs[it.prob];
@@ -207,11 +121,13 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_selinv_tc(const ProbDesc *__r
     for (int e = tid; e < 128; e += kTcThreads) ymax[e] = 0;
     if (tid == 0) {
         for (int st = 0; st < 2; st++) {
-            umma::mbar_init(&full[st], kTcProd + 1);   // + the arrival that expects B's bytes
+            umma::mbar_init(&full[st], kTcProd);
+            umma::mbar_init(&bfull[st], 1);     // the arrival that expects B's bytes
             umma::mbar_init(&empty[st], 1);
         }
         umma::mbar_init(&acc_full, 1);
         umma::mbar_init(&tmem_free, kTcEpi);
+        umma::mbar_init(&drain, 1);
         umma::mbar_init_fence();
     }
     if (warp == kTcMmaWarp) {
@@ -236,6 +152,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_selinv_tc(const ProbDesc *__r
     }
     __syncthreads();
     const uint32_t tmem = s_tmem;
+    int b_issued = -1;   // last step whose B copies the MMA thread issued
 
     if (warp < kTcProd) {
         // ---- producers: A digits, gathered with a two-deep load pipeline.
@@ -264,7 +181,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_selinv_tc(const ProbDesc *__r
         for (int i_ = 0; i_ < n; i_++) {
             const int step = st0 + i_, stage = i_ & 1, use = i_ >> 1, k0 = step * 16;
             uint16_t *Ab = As + stage * Cfg::A_STAGE;
-            if (i_ >= 2 && !umma::mbar_wait(&empty[stage], (uint32_t)((use - 1) & 1), wait_limit)) {
+            if (i_ >= 2 && !umma::mbar_wait(&empty[stage], (uint32_t)((use - 1) & 1), mlim)) {
                 s_abort = 1;
                 break;
             }
@@ -307,18 +224,20 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_selinv_tc(const ProbDesc *__r
             constexpr uint32_t kBBytes = TN * 16 * 2;
             auto load_b = [&](int i_) {
                 const int st = i_ & 1;
-                umma::mbar_arrive_expect_tx(&full[st], kTcDig * kBBytes);
+                umma::mbar_arrive_expect_tx(&bfull[st], kTcDig * kBBytes);
 #pragma unroll
                 for (int pl = 0; pl < kTcDig; pl++)
                     umma::bulk_g2s(Bs + st * Cfg::B_STAGE + pl * Cfg::B_PLANE,
-                                   Bu + ((int64_t)pl * nsteps + st0 + i_) * s64 * 16, kBBytes, &full[st]);
+                                   Bu + ((int64_t)pl * nsteps + st0 + i_) * s64 * 16, kBBytes, &bfull[st]);
+                b_issued = i_;
             };
             if (n > 0) load_b(0);
             for (int i_ = 0; i_ < n; i_++) {
                 const int stage = i_ & 1, use = i_ >> 1, ch = i_ / kTcFlush;
                 const bool first = i_ % kTcFlush == 0;
-                if (!umma::mbar_wait(&full[stage], (uint32_t)(use & 1), wait_limit) ||
-                    (first && ch > 0 && !umma::mbar_wait(&tmem_free, (uint32_t)((ch - 1) & 1), wait_limit))) {
+                if (!umma::mbar_wait(&bfull[stage], (uint32_t)(use & 1), mlim) ||
+                    !umma::mbar_wait(&full[stage], (uint32_t)(use & 1), mlim) ||
+                    (first && ch > 0 && !umma::mbar_wait(&tmem_free, (uint32_t)((ch - 1) & 1), mlim))) {
                     s_abort = 1;
                     break;
                 }
@@ -332,7 +251,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_selinv_tc(const ProbDesc *__r
                 // B of the next step into the other stage once the products of
                 // the step before this one have finished reading it
                 if (i_ + 1 < n) {
-                    if (i_ >= 1 && !umma::mbar_wait(&empty[(i_ + 1) & 1], (uint32_t)((((i_ + 1) >> 1) - 1) & 1), wait_limit)) {
+                    if (i_ >= 1 && !umma::mbar_wait(&empty[(i_ + 1) & 1], (uint32_t)((((i_ + 1) >> 1) - 1) & 1), mlim)) {
                         s_abort = 1;
                         break;
                     }
@@ -346,7 +265,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_selinv_tc(const ProbDesc *__r
         // ---- epilogue: every chunk's exact fp32 group sums -> int64 (hi, lo)
         const int lb = 32 * (warp % 4), row = lb + lane, half = (warp / 4) & 1;
         for (int f = 0; f < nflush; f++) {
-            if (!umma::mbar_wait(&acc_full, (uint32_t)(f & 1), wait_limit)) {
+            if (!umma::mbar_wait(&acc_full, (uint32_t)(f & 1), mlim)) {
                 s_abort = 1;
                 break;
             }
@@ -384,14 +303,22 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_selinv_tc(const ProbDesc *__r
     umma::fence_before_sync();
     __syncthreads();
     if (s_abort) {
-        // a wait ran out: report, let in-flight products drain (bounded),
-        // release the tensor memory and leave
+        // a wait ran out: report, wait (bounded) for the products this CTA
+        // issued (a commit after the last of them) and for its last bulk
+        // copies, release the tensor memory and leave
         if (tid == 0) atomicCAS(P.status, 0, SELINV_ERR_TIMEOUT);
-        if (warp == kTcMmaWarp && n > 0) umma::mbar_wait(&acc_full, (uint32_t)((nflush - 1) & 1), wait_limit);
+        if (warp == kTcMmaWarp && lane == 0) {
+            umma::commit(&drain);
+            umma::mbar_wait(&drain, 0u, mlim);
+            if (b_issued >= 0) umma::mbar_wait(&bfull[b_issued & 1], (uint32_t)((b_issued >> 1) & 1), mlim);
+        }
+        umma::fence_before_sync();
         __syncthreads();
+        umma::fence_after_sync();
         if (warp == kTcMmaWarp) umma::tmem_dealloc(tmem, Cfg::TCOLS);
         return;
     }
+    umma::fence_after_sync();
     if (warp == kTcMmaWarp) umma::tmem_dealloc(tmem, Cfg::TCOLS);
 
     double *Zk = static_cast<double *>(P.Yout) + P.panel_off[K];
@@ -525,13 +452,16 @@ __global__ void __launch_bounds__(kDtThreads, 1) k_diag_tc(const ProbDesc *__res
     uint16_t *Bs = As + 2 * Cfg::A_STAGE;                                  // [2][7][B_PLANE]
     long long *Hi = reinterpret_cast<long long *>(Bs + 2 * Cfg::B_STAGE);  // [TN][128]
     long long *Lo = Hi + kTcM * TN;
-    __shared__ __align__(8) uint64_t full[2], empty[2], acc_full, tmem_free;
+    // full / afull: the producers' B and the bulk copies of A in a stage;
+    // drain: every product issued before an abort is done
+    __shared__ __align__(8) uint64_t full[2], afull[2], empty[2], acc_full, tmem_free, drain;
     __shared__ uint32_t s_tmem;
     __shared__ volatile int s_abort;
     __shared__ int colE[TN];
 
     const int w = blockIdx.x;
     if (w >= nitems) return;
+    const long long mlim = wait_limit > kMbarMinPolls ? wait_limit : kMbarMinPolls;
     const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
     const Item it = items[w];
     const ProbDesc &P = descs[it.prob];
@@ -559,11 +489,13 @@ __global__ void __launch_bounds__(kDtThreads, 1) k_diag_tc(const ProbDesc *__res
     for (int j = tid; j < TN; j += kDtThreads) colE[j] = n0 + j < s ? P.colexpY[fc + n0 + j] : 0;
     if (tid == 0) {
         for (int st = 0; st < 2; st++) {
-            umma::mbar_init(&full[st], kDtProd + 1);   // + the arrival that expects A's bytes
+            umma::mbar_init(&full[st], kDtProd);
+            umma::mbar_init(&afull[st], 1);     // the arrival that expects A's bytes
             umma::mbar_init(&empty[st], 1);
         }
         umma::mbar_init(&acc_full, 1);
         umma::mbar_init(&tmem_free, kDtEpi);
+        umma::mbar_init(&drain, 1);
         umma::mbar_init_fence();
     }
     if (warp == kDtMmaWarp) {
@@ -575,6 +507,7 @@ __global__ void __launch_bounds__(kDtThreads, 1) k_diag_tc(const ProbDesc *__res
     __syncthreads();
     umma::fence_after_sync();
     const uint32_t tmem = s_tmem;
+    int a_issued = -1;   // last step whose A copies the MMA thread issued
 
     if (warp < kDtProd) {
         // ---- producers: thread (column r, quarter kq) slices rows 4 kq .. 4 kq + 3
@@ -598,7 +531,7 @@ __global__ void __launch_bounds__(kDtThreads, 1) k_diag_tc(const ProbDesc *__res
         for (int i_ = 0; i_ < n; i_++) {
             const int stage = i_ & 1, use = i_ >> 1;
             uint16_t *Bb = Bs + stage * Cfg::B_STAGE;
-            if (i_ >= 2 && !umma::mbar_wait(&empty[stage], (uint32_t)((use - 1) & 1), wait_limit)) {
+            if (i_ >= 2 && !umma::mbar_wait(&empty[stage], (uint32_t)((use - 1) & 1), mlim)) {
                 s_abort = 1;
                 break;
             }
@@ -632,18 +565,20 @@ __global__ void __launch_bounds__(kDtThreads, 1) k_diag_tc(const ProbDesc *__res
             const uint32_t aBytes = (uint32_t)(s64 * 16 * 2);
             auto load_a = [&](int i_) {
                 const int st = i_ & 1;
-                umma::mbar_arrive_expect_tx(&full[st], kTcDig * aBytes);
+                umma::mbar_arrive_expect_tx(&afull[st], kTcDig * aBytes);
 #pragma unroll
                 for (int pl = 0; pl < kTcDig; pl++)
                     umma::bulk_g2s(As + st * Cfg::A_STAGE + pl * Cfg::A_PLANE,
-                                   Au + ((int64_t)pl * nsteps + st0 + i_) * s64 * 16, aBytes, &full[st]);
+                                   Au + ((int64_t)pl * nsteps + st0 + i_) * s64 * 16, aBytes, &afull[st]);
+                a_issued = i_;
             };
             if (n > 0) load_a(0);
             for (int i_ = 0; i_ < n; i_++) {
                 const int stage = i_ & 1, use = i_ >> 1, chk = i_ / kTcFlush;
                 const bool first = i_ % kTcFlush == 0;
-                if (!umma::mbar_wait(&full[stage], (uint32_t)(use & 1), wait_limit) ||
-                    (first && chk > 0 && !umma::mbar_wait(&tmem_free, (uint32_t)((chk - 1) & 1), wait_limit))) {
+                if (!umma::mbar_wait(&afull[stage], (uint32_t)(use & 1), mlim) ||
+                    !umma::mbar_wait(&full[stage], (uint32_t)(use & 1), mlim) ||
+                    (first && chk > 0 && !umma::mbar_wait(&tmem_free, (uint32_t)((chk - 1) & 1), mlim))) {
                     s_abort = 1;
                     break;
                 }
@@ -654,7 +589,7 @@ __global__ void __launch_bounds__(kDtThreads, 1) k_diag_tc(const ProbDesc *__res
                 umma::commit(&empty[stage]);
                 if (i_ % kTcFlush == kTcFlush - 1 || i_ == n - 1) umma::commit(&acc_full);
                 if (i_ + 1 < n) {
-                    if (i_ >= 1 && !umma::mbar_wait(&empty[(i_ + 1) & 1], (uint32_t)((((i_ + 1) >> 1) - 1) & 1), wait_limit)) {
+                    if (i_ >= 1 && !umma::mbar_wait(&empty[(i_ + 1) & 1], (uint32_t)((((i_ + 1) >> 1) - 1) & 1), mlim)) {
                         s_abort = 1;
                         break;
                     }
@@ -668,7 +603,7 @@ __global__ void __launch_bounds__(kDtThreads, 1) k_diag_tc(const ProbDesc *__res
         // ---- epilogue: every chunk's exact fp32 group sums -> int64 (hi, lo)
         const int lb = 32 * (warp % 4), row = lb + lane, half = (warp / 4) & 1;
         for (int f = 0; f < nflush; f++) {
-            if (!umma::mbar_wait(&acc_full, (uint32_t)(f & 1), wait_limit)) {
+            if (!umma::mbar_wait(&acc_full, (uint32_t)(f & 1), mlim)) {
                 s_abort = 1;
                 break;
             }
@@ -706,12 +641,20 @@ __global__ void __launch_bounds__(kDtThreads, 1) k_diag_tc(const ProbDesc *__res
     umma::fence_before_sync();
     __syncthreads();
     if (s_abort) {
+        // as in k_selinv_tc: drain this CTA's products and last bulk copies (bounded)
         if (tid == 0) atomicCAS(P.status, 0, SELINV_ERR_TIMEOUT);
-        if (warp == kDtMmaWarp && n > 0) umma::mbar_wait(&acc_full, (uint32_t)((nflush - 1) & 1), wait_limit);
+        if (warp == kDtMmaWarp && lane == 0) {
+            umma::commit(&drain);
+            umma::mbar_wait(&drain, 0u, mlim);
+            if (a_issued >= 0) umma::mbar_wait(&afull[a_issued & 1], (uint32_t)((a_issued >> 1) & 1), mlim);
+        }
+        umma::fence_before_sync();
         __syncthreads();
+        umma::fence_after_sync();
         if (warp == kDtMmaWarp) umma::tmem_dealloc(tmem, Cfg::TCOLS);
         return;
     }
+    umma::fence_after_sync();
     if (warp == kDtMmaWarp) umma::tmem_dealloc(tmem, Cfg::TCOLS);
     if (n == 0) return;
     // the chunk's exact sums into K's (cleared at the start of every call):

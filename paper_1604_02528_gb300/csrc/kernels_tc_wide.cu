@@ -1,0 +1,470 @@
+// A^{-1}_{C,K} = -A^{-1}_{C,C} Lhat_{C,K} (Alg. 1, the product after the
+// gather) on tcgen05 for supernodes wider than 64 columns, in the transposed
+// orientation: the MMA's 128 rows (tensor-memory lanes) are the columns of
+// K and its N dimension runs over 64 rows of C, so that every gathered
+// entry of A^{-1}_{C,C} is cut into digits once for all of K's columns
+// (the row-tile orientation of k_selinv_tc covers at most 64 columns per
+// CTA and would gather and slice each entry once per 64 columns).
+//
+//   A = Lhat^T digit planes: rows = the s columns of K (zero past s), k = the
+//       rows q of C; already stored in this operand layout (one contiguous
+//       block of roundup(s, 64) x 16 per plane and 16-q step), brought in by
+//       bulk copies;
+//   B = A^{-1}_{C,C} digit planes: rows = 64 rows p of C, k = q; 8 producer
+//       warps gather the entries and slice them with integer operations;
+//   D (tensor memory) = 7 group accumulators of 128 x 64, group g holding
+//       the exact fp32 sum of the digit products with i + j = g;
+//   every 128 k the groups are read back (tcgen05.ld) by 8 epilogue warps
+//   and added as int64 (hi, lo) words into shared memory.
+// Same digit scheme, exponent grids and exact sums as k_selinv_tc, so the
+// result does not depend on which of the two kernels forms it.
+//
+// Complex symmetric values (template CPLX) run the same contraction on the
+// real 2c-long k dimension k' = 2q + part: B(p, 2q) = Re A^{-1}(p, q),
+// B(p, 2q + 1) = Im A^{-1}(p, q), and the 2s rows of A are
+// [Re Lhat, -Im Lhat] (rows j: the real part of column j of the product)
+// and [Im Lhat, Re Lhat] (rows s + j: its imaginary part), so one real
+// contraction holds the four real products of the complex one.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "common.cuh"
+#include "fixedpoint.cuh"
+#include "launch.h"
+#include "tc_digits.cuh"
+#include "tile_gemm.cuh"
+#include "umma.cuh"
+
+namespace selinv {
+
+constexpr int kTwN = 64;           // rows of C per item: N of one digit plane
+constexpr int kTwProd = 8;         // producer warps: 64 rows x 4 quarters of a 16-k step, 4 values per thread
+constexpr int kTwEpi = 8;          // epilogue warps: two per tensor-memory lane quarter (32 rows of C each)
+constexpr int kTwMmaWarp = kTwProd + kTwEpi;
+constexpr int kTwThreads = 32 * (kTwProd + kTwEpi + 1);
+constexpr int kTwHS = kTcM + 1;    // words per row of C in the int64 sums [p][m]: conflict-free both ways
+static_assert(2 * kTcM * kTwN + kTwN / 2 <= kTcSlotWords, "a split-k slot holds the (hi, lo) words and rowE");
+
+struct TwCfg {
+    static constexpr int A_PLANE = kTcM * 16;    // fp16 elements of one Lhat^T digit plane per k16 step
+    static constexpr int B_PLANE = kTwN * 16;    // ... of one gathered digit plane
+    static constexpr int A_STAGE = kTcDig * A_PLANE;
+    static constexpr int B_STAGE = kTcDig * B_PLANE;
+    static constexpr uint32_t TCOLS = 512;       // 7 groups x 64 columns
+    static constexpr size_t SMEM = sizeof(uint16_t) * 2 * (size_t)(A_STAGE + B_STAGE) +
+                                   sizeof(long long) * 2 * (size_t)kTwN * kTwHS + sizeof(int) * kTwN;
+};
+static_assert(kTcDig * kTwN <= (int)TwCfg::TCOLS, "the group accumulators fit the tensor memory");
+
+// items: tile = (row tile * nmt + m tile) * nsplit + k-range, ntiles = nsplit;
+// nmt = ceil(rows of A / 128) (1 for real supernodes of <= 128 columns)
+template <bool CPLX>
+__global__ void __launch_bounds__(kTwThreads, 1) k_selinv_tcw(const ProbDesc *__restrict__ descs,
+                                                              const Item *__restrict__ items, int nitems,
+                                                              long long *__restrict__ slab, long long wait_limit) {
+    using Cfg = TwCfg;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    uint16_t *As = reinterpret_cast<uint16_t *>(smem_raw);                // [2][7][A_PLANE] Lhat^T digits
+    uint16_t *Bs = As + 2 * Cfg::A_STAGE;                                  // [2][7][B_PLANE] gathered digits
+    long long *Hi = reinterpret_cast<long long *>(Bs + 2 * Cfg::B_STAGE);  // [64 p][kTwHS]
+    long long *Lo = Hi + kTwN * kTwHS;
+    int *rowE = reinterpret_cast<int *>(Lo + kTwN * kTwHS);                // [64]
+    __shared__ int64_t tile_cb[kTwN], tile_rb[kTwN];
+    // full[s]: the producers wrote B of stage s; afull[s]: the bulk copies of
+    // A landed in stage s; empty[s]: the products that read stage s are done;
+    // acc_full: a chunk's group sums are complete; tmem_free: the epilogue
+    // read them; drain: every product issued before an abort is done
+    __shared__ __align__(8) uint64_t full[2], afull[2], empty[2], acc_full, tmem_free, drain;
+    __shared__ uint32_t s_tmem;
+    __shared__ int s_pre;
+    __shared__ volatile int s_abort;
+    __shared__ int ymax[kTcM];
+
+    const int w = blockIdx.x;
+    if (w >= nitems) return;
+    const long long mlim = wait_limit > kMbarMinPolls ? wait_limit : kMbarMinPolls;
+    const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
+    const Item it = items[w];
+    const ProbDesc &P = descs[it.prob];
+    const int K = it.K;
+    const int fc = P.super_ptr[K];
+    const int s = P.super_ptr[K + 1] - fc;
+    const int64_t ld = P.rowptr[K + 1] - P.rowptr[K];
+    const int c = (int)(ld - s);
+    const int kw = CPLX ? 2 * c : c;                     // k extent
+    const int mrows = CPLX ? 2 * s : s;                  // rows of A (output rows)
+    const int s64 = (mrows + 63) / 64 * 64;              // operand rows of a stored digit block
+    const int nmt = (mrows + kTcM - 1) / kTcM;
+    const int nsplit = it.ntiles;
+    const int ksp = it.tile % nsplit;
+    const int mt = (it.tile / nsplit) % nmt;
+    const int tile = it.tile / nsplit / nmt;
+    const int p0 = tile * kTwN, m0 = mt * kTcM;
+    const int64_t pos0 = P.rowptr[K] + s;
+    const int nsteps = (kw + 15) / 16;
+    const int chunk = ((nsteps + nsplit - 1) / nsplit + kTcFlush - 1) / kTcFlush * kTcFlush;
+    const int st0 = ksp * chunk;
+    const int st1 = st0 + chunk < nsteps ? st0 + chunk : nsteps;
+    const int n = st1 > st0 ? st1 - st0 : 0;             // k16 steps of this item
+    const int nflush = (n + kTcFlush - 1) / kTcFlush;
+    const int arows = s64 - m0 < kTcM ? s64 - m0 : kTcM; // rows of A in the stored blocks
+
+    // row exponents of the gathered block: row p is bounded by the largest
+    // whole-column exponent of A^{-1} over C[0..p] (entry (p, q) sits in
+    // the ancestor column C[min(p, q)])
+    if (tid == 0) { s_pre = 0; s_abort = 0; }
+    // rows of A past the stored blocks stay zero in both stages
+    if (arows < kTcM)
+        for (int e = tid; e < 2 * Cfg::A_STAGE / 8; e += kTwThreads)
+            reinterpret_cast<uint4 *>(As)[e] = make_uint4(0, 0, 0, 0);
+    __syncthreads();
+    {
+        int e = 0;
+        for (int q = tid; q < p0 && q < c; q += kTwThreads) e = max(e, P.colexpZ[P.rows[pos0 + q]]);
+        if (e) atomicMax(&s_pre, e);
+    }
+    for (int e = tid; e < kTwN; e += kTwThreads) {
+        const int p = p0 + e;
+        tile_cb[e] = p < c ? P.colbase[pos0 + p] : 0;
+        tile_rb[e] = p < c ? P.relbase[pos0 + p] : 0;
+        rowE[e] = p < c ? P.colexpZ[P.rows[pos0 + p]] : 0;
+    }
+    // Hi and Lo are written by the first flush; an item without steps leaves zeros
+    if (n == 0)
+        for (int e = tid; e < 2 * kTwN * kTwHS; e += kTwThreads) Hi[e] = 0;
+    for (int e = tid; e < kTcM; e += kTwThreads) ymax[e] = 0;
+    if (tid == 0) {
+        for (int st = 0; st < 2; st++) {
+            umma::mbar_init(&full[st], kTwProd);
+            umma::mbar_init(&afull[st], 1);      // the arrival that expects A's bytes
+            umma::mbar_init(&empty[st], 1);
+        }
+        umma::mbar_init(&acc_full, 1);
+        umma::mbar_init(&tmem_free, kTwEpi);
+        umma::mbar_init(&drain, 1);
+        umma::mbar_init_fence();
+    }
+    if (warp == kTwMmaWarp) {
+        umma::tmem_alloc(&s_tmem, Cfg::TCOLS);
+        umma::tmem_relinquish();
+    }
+    umma::fence_proxy_async();   // zeroed A rows are seen by the tensor cores
+    umma::fence_before_sync();
+    __syncthreads();
+    umma::fence_after_sync();
+    if (warp == 0) {             // prefix max over the 64 rows
+        int carry = s_pre;
+        for (int b = 0; b < kTwN; b += 32) {
+            int v = max(rowE[b + lane], carry);
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int u = __shfl_up_sync(0xffffffffu, v, o);
+                if (lane >= o) v = max(v, u);
+            }
+            rowE[b + lane] = v;
+            carry = __shfl_sync(0xffffffffu, v, 31);
+        }
+    }
+    __syncthreads();
+    const uint32_t tmem = s_tmem;
+    int a_issued = -1;   // last step whose A copies the MMA thread issued
+
+    if (warp < kTwProd) {
+        // ---- producers: thread (row r, quarter kq) slices the k-values
+        // 4 kq .. 4 kq + 3 of each 16-k step, gathered with a two-deep load
+        // pipeline; a warp holds 16 rows x 2 quarters, so that its stores of
+        // a plane fill two 128-byte core matrices.  Complex: the 4 k-values
+        // are (Re, Im) of the entries q = 8 step + 2 kq and + 1.
+        const TcGather g{P.colbase + pos0, P.relbase + pos0, P.relidx, tile_cb, tile_rb, p0, c};
+        const int r = (warp % 4) * 16 + (lane >> 1), kq = (warp / 4) * 2 + (lane & 1);
+        const int E = rowE[r];
+        constexpr int NV = CPLX ? 2 : 4;        // entries of A^{-1}_{C,C} per thread and step
+        constexpr int QS = CPLX ? 8 : 16;       // entries per step
+        double v[4];
+        int64_t ab[NV];
+        int32_t ar[NV];
+        auto load = [&]() {
+            if (CPLX) {
+                const double2 *Zc = static_cast<const double2 *>(P.Z);
+#pragma unroll
+                for (int u = 0; u < NV; u++) {
+                    const double2 z = ab[u] >= 0 ? Zc[ab[u] + ar[u]] : make_double2(0.0, 0.0);
+                    v[2 * u] = z.x;
+                    v[2 * u + 1] = z.y;
+                }
+            } else {
+                const double *Zg = static_cast<const double *>(P.Z);
+#pragma unroll
+                for (int u = 0; u < NV; u++) v[u] = ab[u] >= 0 ? Zg[ab[u] + ar[u]] : 0.0;
+            }
+        };
+        auto lookup = [&](int step) {
+#pragma unroll
+            for (int u = 0; u < NV; u++) g.parts(r, step * QS + kq * NV + u, ab[u], ar[u]);
+        };
+        if (n > 0) {
+            lookup(st0);
+            load();
+            if (n > 1) lookup(st0 + 1);
+            else
+#pragma unroll
+                for (int u = 0; u < NV; u++) ab[u] = -1;
+        }
+        for (int i_ = 0; i_ < n; i_++) {
+            const int stage = i_ & 1, use = i_ >> 1;
+            uint16_t *Bb = Bs + stage * Cfg::B_STAGE;
+            if (i_ >= 2 && !umma::mbar_wait(&empty[stage], (uint32_t)((use - 1) & 1), mlim)) {
+                s_abort = 1;
+                break;
+            }
+            {
+                uint32_t lo[4], hi[4];
+#pragma unroll
+                for (int u = 0; u < 4; u++) {
+                    const unsigned long long wv = (unsigned long long)(fixed54(v[u], E) + 0x80808080808080ll);
+                    lo[u] = (uint32_t)wv;
+                    hi[u] = (uint32_t)(wv >> 32);
+                }
+                uint16_t *dst = Bb + (r / 8) * 128 + (kq / 2) * 64 + (r % 8) * 8 + (kq % 2) * 4;
+                store_plane4<0>(dst + 0 * Cfg::B_PLANE, lo, hi);
+                store_plane4<1>(dst + 1 * Cfg::B_PLANE, lo, hi);
+                store_plane4<2>(dst + 2 * Cfg::B_PLANE, lo, hi);
+                store_plane4<3>(dst + 3 * Cfg::B_PLANE, lo, hi);
+                store_plane4<4>(dst + 4 * Cfg::B_PLANE, lo, hi);
+                store_plane4<5>(dst + 5 * Cfg::B_PLANE, lo, hi);
+                store_plane4<6>(dst + 6 * Cfg::B_PLANE, lo, hi);
+            }
+            // loads of the next step's values, address lookups of the one after
+            load();
+            if (i_ + 2 < n) lookup(st0 + i_ + 2);
+            else
+#pragma unroll
+                for (int u = 0; u < NV; u++) ab[u] = -1;
+            umma::fence_proxy_async();
+            __syncwarp();
+            if (lane == 0) umma::mbar_arrive(&full[stage]);
+            if (s_abort) break;
+        }
+    } else if (warp == kTwMmaWarp) {
+        // ---- one thread copies the Lhat^T digit planes (rows m0 .. m0 + 127
+        // of each stored block) and issues the products
+        if (lane == 0) {
+            const uint16_t *Au = P.lhsu + P.lhsu_off[K] + (int64_t)(m0 / 8) * 128;
+            const uint32_t aBytes = (uint32_t)(arows * 16 * 2);
+            auto load_a = [&](int i_) {
+                const int st = i_ & 1;
+                umma::mbar_arrive_expect_tx(&afull[st], kTcDig * aBytes);
+#pragma unroll
+                for (int pl = 0; pl < kTcDig; pl++)
+                    umma::bulk_g2s(As + st * Cfg::A_STAGE + pl * Cfg::A_PLANE,
+                                   Au + ((int64_t)pl * nsteps + st0 + i_) * s64 * 16, aBytes, &afull[st]);
+                a_issued = i_;
+            };
+            if (n > 0) load_a(0);
+            for (int i_ = 0; i_ < n; i_++) {
+                const int stage = i_ & 1, use = i_ >> 1, ch = i_ / kTcFlush;
+                const bool first = i_ % kTcFlush == 0;
+                if (!umma::mbar_wait(&afull[stage], (uint32_t)(use & 1), mlim) ||
+                    !umma::mbar_wait(&full[stage], (uint32_t)(use & 1), mlim) ||
+                    (first && ch > 0 && !umma::mbar_wait(&tmem_free, (uint32_t)((ch - 1) & 1), mlim))) {
+                    s_abort = 1;
+                    break;
+                }
+                umma::fence_after_sync();
+                const uint64_t ad0 = umma::smem_desc(umma::smem_u32(As + stage * Cfg::A_STAGE), 128, 256);
+                const uint64_t bd0 = umma::smem_desc(umma::smem_u32(Bs + stage * Cfg::B_STAGE), 128, 256);
+                digit_products<kTwN, Cfg::A_PLANE, Cfg::B_PLANE>(tmem, ad0, bd0, first);
+                umma::commit(&empty[stage]);
+                if (i_ % kTcFlush == kTcFlush - 1 || i_ == n - 1) umma::commit(&acc_full);
+                // A of the next step into the other stage once the products of
+                // the step before this one have finished reading it
+                if (i_ + 1 < n) {
+                    if (i_ >= 1 && !umma::mbar_wait(&empty[(i_ + 1) & 1], (uint32_t)((((i_ + 1) >> 1) - 1) & 1), mlim)) {
+                        s_abort = 1;
+                        break;
+                    }
+                    load_a(i_ + 1);
+                }
+                if (s_abort) break;
+            }
+        }
+        __syncwarp();
+    } else {
+        // ---- epilogue: every chunk's exact fp32 group sums -> int64 (hi, lo);
+        // warp (lane quarter, half) reads output rows 32 (warp % 4) .. + 31
+        // and rows of C 32 half .. + 31
+        const int lb = 32 * (warp % 4), m = lb + lane, half = (warp / 4) & 1;
+        for (int f = 0; f < nflush; f++) {
+            if (!umma::mbar_wait(&acc_full, (uint32_t)(f & 1), mlim)) {
+                s_abort = 1;
+                break;
+            }
+            umma::fence_after_sync();
+#pragma unroll 1
+            for (int cb = 0; cb < 4; cb++) {
+                uint32_t acc[kTcDig][8];
+#pragma unroll
+                for (int gq = 0; gq < kTcDig; gq++)
+                    umma::tmem_ld8(tmem + ((uint32_t)lb << 16) + (uint32_t)(gq * kTwN + half * 32 + cb * 8), acc[gq]);
+                umma::tmem_wait_ld();
+#pragma unroll
+                for (int jj = 0; jj < 8; jj++) {
+                    long long gv[kTcDig];
+#pragma unroll
+                    for (int gq = 0; gq < kTcDig; gq++) gv[gq] = (long long)__float2int_rn(__uint_as_float(acc[gq][jj]));
+                    const long long h = (gv[0] << 16) + (gv[1] << 8) + gv[2];
+                    const long long l = (gv[3] << 24) + (gv[4] << 16) + (gv[5] << 8) + gv[6];
+                    const int p = half * 32 + cb * 8 + jj;
+                    long long *ph = Hi + p * kTwHS + m, *pl = Lo + p * kTwHS + m;
+                    if (f == 0) {   // the first chunk writes, the later ones add
+                        *ph = h;
+                        *pl = l;
+                    } else {
+                        *ph += h;
+                        *pl += l;
+                    }
+                }
+            }
+            umma::fence_before_sync();
+            __syncwarp();
+            if (lane == 0) umma::mbar_arrive(&tmem_free);
+            if (s_abort) break;
+        }
+    }
+    umma::fence_before_sync();
+    __syncthreads();
+    if (s_abort) {
+        // a wait ran out: report, wait (bounded) for the products this CTA
+        // issued (a commit after the last of them) and for its last bulk
+        // copies, release the tensor memory and leave
+        if (tid == 0) atomicCAS(P.status, 0, SELINV_ERR_TIMEOUT);
+        if (warp == kTwMmaWarp && lane == 0) {
+            umma::commit(&drain);
+            umma::mbar_wait(&drain, 0u, mlim);
+            if (a_issued >= 0) umma::mbar_wait(&afull[a_issued & 1], (uint32_t)((a_issued >> 1) & 1), mlim);
+        }
+        umma::fence_before_sync();
+        __syncthreads();
+        umma::fence_after_sync();
+        if (warp == kTwMmaWarp) umma::tmem_dealloc(tmem, Cfg::TCOLS);
+        return;
+    }
+    umma::fence_after_sync();
+    if (warp == kTwMmaWarp) umma::tmem_dealloc(tmem, Cfg::TCOLS);
+
+    // Y = -(A^{-1}_{C,C} Lhat): B digits on 2^(E - 1028 - 8i) of the row of
+    // C, A digits on 2^(F - 1029 - 8j) of the column of K, so the value is
+    // (hi 2^-16 + lo 2^-48) 2^(E + F - 2057)
+    if (nsplit == 1) {
+        double *Zk = static_cast<double *>(P.Yout) + (CPLX ? 2 : 1) * P.panel_off[K];
+        for (int e = tid; e < kTwN * kTcM; e += kTwThreads) {
+            const int p = e % kTwN, mm = e / kTwN, jr = m0 + mm;   // a warp shares mm
+            if (p0 + p >= c || jr >= mrows) continue;
+            const int j = CPLX && jr >= s ? jr - s : jr;
+            const int sc = (rowE[p] - 1022) + (P.colexp[fc + j] - 1022) - 13;
+            const double y = fixed_to_double(Hi[p * kTwHS + mm], Lo[p * kTwHS + mm], sc);
+            const int64_t at = (int64_t)j * ld + s + p0 + p;
+            if (CPLX) Zk[2 * at + (jr >= s ? 1 : 0)] = -y;
+            else Zk[at] = -y;
+            warp_uniform_atomic_max(&ymax[mm], bexp(y));
+        }
+    } else {
+        // split k: the partial tile and the rows' exponents go to this CTA's
+        // slab slot, [output row][row of C]; k_tcw_reduce sums the slots
+        long long *mine = slab + (int64_t)blockIdx.x * kTcSlotWords;
+        for (int e = tid; e < kTwN * kTcM; e += kTwThreads) {
+            const int p = e % kTwN, mm = e / kTwN;
+            mine[e] = Hi[p * kTwHS + mm];
+            mine[kTwN * kTcM + e] = Lo[p * kTwHS + mm];
+        }
+        int *re = reinterpret_cast<int *>(mine + 2 * kTwN * kTcM);
+        for (int e = tid; e < kTwN; e += kTwThreads) re[e] = rowE[e];
+        return;
+    }
+    __syncthreads();
+    // column exponents of A^{-1}_{C,K} over all row tiles (used by the diagonal block)
+    for (int mm = tid; mm < kTcM; mm += kTwThreads) {
+        const int jr = m0 + mm;
+        if (jr < mrows && ymax[mm] > 0) atomicMax(&P.colexpY[fc + (CPLX && jr >= s ? jr - s : jr)], ymax[mm]);
+    }
+}
+
+// Split-k reduction of k_selinv_tcw: one CTA per (row tile of 64, 8 output
+// rows); each element sums the int64 words of the group's k-range slots in
+// k order (exact) and forms A^{-1}_{C,K} = -(sum).
+// red[w] = {index of the group's first item, its slab slot, block of 8 output rows}.
+template <bool CPLX>
+__global__ void __launch_bounds__(256) k_tcw_reduce(const ProbDesc *__restrict__ descs,
+                                                    const Item *__restrict__ items, const int4 *__restrict__ red,
+                                                    int nred, const long long *__restrict__ slab) {
+    __shared__ int ymax[8];
+    const int w = blockIdx.x;
+    if (w >= nred) return;
+    const int4 rr = red[w];
+    const Item it = items[rr.x];
+    const ProbDesc &P = descs[it.prob];
+    const int K = it.K;
+    const int fc = P.super_ptr[K];
+    const int s = P.super_ptr[K + 1] - fc;
+    const int64_t ld = P.rowptr[K + 1] - P.rowptr[K];
+    const int c = (int)(ld - s);
+    const int mrows = CPLX ? 2 * s : s;
+    const int nmt = (mrows + kTcM - 1) / kTcM;
+    const int nsplit = it.ntiles;
+    const int mt = (it.tile / nsplit) % nmt;
+    const int p0 = (it.tile / nsplit / nmt) * kTwN, m0 = mt * kTcM;
+    const int *rowE = reinterpret_cast<const int *>(slab + (int64_t)rr.y * kTcSlotWords + 2 * kTwN * kTcM);
+    if (threadIdx.x < 8) ymax[threadIdx.x] = 0;
+    __syncthreads();
+    double *Zk = static_cast<double *>(P.Yout) + (CPLX ? 2 : 1) * P.panel_off[K];
+    const int p = threadIdx.x % kTwN;
+    for (int r8 = threadIdx.x / kTwN; r8 < 8; r8 += 256 / kTwN) {   // a warp shares r8
+        const int mm = rr.z * 8 + r8, jr = m0 + mm;
+        if (jr >= mrows || p0 + p >= c) continue;
+        long long hi = 0, lo = 0;
+        for (int k2 = 0; k2 < nsplit; k2++) {
+            const long long *sl = slab + ((int64_t)rr.y + k2) * kTcSlotWords;
+            hi += sl[mm * kTwN + p];
+            lo += sl[kTwN * kTcM + mm * kTwN + p];
+        }
+        const int j = CPLX && jr >= s ? jr - s : jr;
+        const int sc = (rowE[p] - 1022) + (P.colexp[fc + j] - 1022) - 13;
+        const double y = fixed_to_double(hi, lo, sc);
+        const int64_t at = (int64_t)j * ld + s + p0 + p;
+        if (CPLX) Zk[2 * at + (jr >= s ? 1 : 0)] = -y;
+        else Zk[at] = -y;
+        warp_uniform_atomic_max(&ymax[r8], bexp(y));
+    }
+    __syncthreads();
+    if (threadIdx.x < 8) {
+        const int jr = m0 + rr.z * 8 + (int)threadIdx.x;
+        if (jr < mrows && ymax[threadIdx.x] > 0)
+            atomicMax(&P.colexpY[fc + (CPLX && jr >= s ? jr - s : jr)], ymax[threadIdx.x]);
+    }
+}
+
+cudaError_t configure_tcw_kernels() {
+    cudaError_t e = cudaFuncSetAttribute(k_selinv_tcw<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)TwCfg::SMEM);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_selinv_tcw<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TwCfg::SMEM);
+    return e;
+}
+
+cudaError_t launch_selinv_tcw(int cplx, const ProbDesc *d, const Item *items, int n, long long *slab,
+                              long long wait_limit, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    if (cplx) k_selinv_tcw<true><<<n, kTwThreads, TwCfg::SMEM, st>>>(d, items, n, slab, wait_limit);
+    else k_selinv_tcw<false><<<n, kTwThreads, TwCfg::SMEM, st>>>(d, items, n, slab, wait_limit);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tcw_reduce(int cplx, const ProbDesc *d, const Item *items, const int4 *red, int n,
+                              const long long *slab, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    if (cplx) k_tcw_reduce<true><<<n, 256, 0, st>>>(d, items, red, n, slab);
+    else k_tcw_reduce<false><<<n, 256, 0, st>>>(d, items, red, n, slab);
+    return cudaGetLastError();
+}
+
+}  // namespace selinv

@@ -355,6 +355,7 @@ int ensure_device(PlanData &p) {
         if (configure_selinv_kernels() != cudaSuccess) return SELINV_ERR_CUDA;
         if (configure_ozaki_kernels() != cudaSuccess) return SELINV_ERR_CUDA;
         if (configure_tc_kernels() != cudaSuccess) return SELINV_ERR_CUDA;
+        if (configure_tcw_kernels() != cudaSuccess) return SELINV_ERR_CUDA;
         configured = true;
     }
     int rc;
@@ -580,7 +581,7 @@ int build_schedule(Schedule &S, const std::vector<const PlanData *> &plans,
             const Item &it = S.h_items[e];
             const PlanData &p = *plans[it.prob];
             const int s = p.super_ptr[it.K + 1] - p.super_ptr[it.K];
-            const int ncol = (s + tl.bucket - 1) / tl.bucket;
+            const int ncol = tl.bucket == kTcWide ? 1 : (s + tl.bucket - 1) / tl.bucket;
             if (it.ntiles < 2 || it.tile % (it.ntiles * ncol) != 0) continue;   // not a group's first item
             for (int cb = 0; cb < (s + 7) / 8; cb++) S.h_red.push_back(make_int4((int)e, (int)(e - tl.off), cb, 0));
         }
@@ -627,15 +628,22 @@ int build_schedule(Schedule &S, const std::vector<const PlanData *> &plans,
     // tensor-core items: (row tile, column tile of width tn, k-range) triples,
     // ntiles field = number of k-ranges; c == 0 has none
     auto oz_tn = [](int s) { return s <= 16 ? 16 : (s <= 32 ? 32 : 64); };
-    // row tiles of the contraction: 64 rows on mma.sync, 128 on tcgen05
     auto use_tc = [&](int i) { return plans[i]->opts.fast_contraction == 1; };
+    // supernodes wider than 64 columns on tcgen05 run the transposed kernel
+    // (k_selinv_tcw: all columns of K per CTA, 64 rows of C), launch bucket 128
+    auto tc_wide = [&](int i, int s) { return use_tc(i) && s > 64; };
+    auto tn_of = [&](int i, int s) { return tc_wide(i, s) ? kTcWide : oz_tn(s); };
+    // row tiles of the contraction: 64 rows on mma.sync and on the transposed
+    // tcgen05 kernel, 128 on the row-tile tcgen05 kernel
     // the diagonal block of a supernode on the tcgen05 engine runs on tcgen05
     // when it is wider than 32 columns, else on the mma.sync kernel (cheaper per item)
     auto diag_tc = [&](int i, int s) { return use_tc(i) && s > 32; };
     auto row_tiles = [&](int i, int32_t K) -> int64_t {
         const PlanData &p = *plans[i];
         if (!use_tc(i)) return p.ntiles[K];
-        const int64_t c = p.rowptr[K + 1] - p.rowptr[K] - (p.super_ptr[K + 1] - p.super_ptr[K]);
+        const int s = p.super_ptr[K + 1] - p.super_ptr[K];
+        const int64_t c = p.rowptr[K + 1] - p.rowptr[K] - s;
+        if (tc_wide(i, s)) return (c + kTcWideRows - 1) / kTcWideRows;
         return (c + kTcRows - 1) / kTcRows;
     };
     auto push_oz = [&](int i, int32_t K, int tn, int nsplit) {
@@ -643,7 +651,7 @@ int build_schedule(Schedule &S, const std::vector<const PlanData *> &plans,
         const int s = p.super_ptr[K + 1] - p.super_ptr[K];
         const int64_t c = p.rowptr[K + 1] - p.rowptr[K] - s;
         if (c == 0) return;
-        const int ncol = (s + tn - 1) / tn;
+        const int ncol = tn == kTcWide ? 1 : (s + tn - 1) / tn;   // the transposed kernel covers all columns
         const int64_t nt = row_tiles(i, K);
         for (int t = 0; t < nt; t++)
             for (int ct = 0; ct < ncol; ct++)
@@ -666,7 +674,7 @@ int build_schedule(Schedule &S, const std::vector<const PlanData *> &plans,
         const int s = p.super_ptr[K + 1] - p.super_ptr[K];
         const int64_t c = p.rowptr[K + 1] - p.rowptr[K] - s;
         if (c == 0) return 0;
-        return row_tiles(i, K) * ((s + oz_tn(s) - 1) / oz_tn(s));
+        return row_tiles(i, K) * (tc_wide(i, s) ? 1 : (s + oz_tn(s) - 1) / oz_tn(s));
     };
 
     if (mode == SELINV_SCHED_PERSISTENT) {
@@ -759,7 +767,7 @@ int build_schedule(Schedule &S, const std::vector<const PlanData *> &plans,
                 if (!act(i, K)) continue;
                 const int s = p.super_ptr[K + 1] - p.super_ptr[K];
                 if (ozok(i, s)) {
-                    const int tn = oz_tn(s);
+                    const int tn = tn_of(i, s);
                     const int64_t off = (int64_t)S.h_items.size();
                     push_oz(i, K, tn, oz_split(i, K, oz_ctas(i, K)));
                     if (S.h_items.size() > (size_t)off) {
@@ -806,12 +814,12 @@ int build_schedule(Schedule &S, const std::vector<const PlanData *> &plans,
             int64_t level_ctas = 0;
             for (auto &ik : oz) level_ctas += oz_ctas(ik.first, ik.second);
             for (int tc = 1; tc >= 0; tc--)
-                for (int tn : {64, 32, 16}) {
+                for (int tn : {kTcWide, 64, 32, 16}) {
                     const int64_t off = (int64_t)S.h_items.size();
                     for (auto &ik : oz) {
                         const PlanData &p = *plans[ik.first];
                         const int s = p.super_ptr[ik.second + 1] - p.super_ptr[ik.second];
-                        if (oz_tn(s) == tn && use_tc(ik.first) == (tc == 1))
+                        if (tn_of(ik.first, s) == tn && use_tc(ik.first) == (tc == 1))
                             push_oz(ik.first, ik.second, tn, oz_split(ik.first, ik.second, level_ctas));
                     }
                     const int cnt = (int)(S.h_items.size() - off);
@@ -937,8 +945,12 @@ cudaError_t launch_with(const Schedule &S, const Launch &L, const ProbDesc *d, c
     case KL_LINV_DIGITS: return launch_linv_digits(d, S.d_work + L.off, L.count, st);
     case KL_LHAT_OZ: return launch_lhat_oz(L.bucket, d, S.d_items + L.off, L.count, st);
     case KL_SELINV_TC:
+        if (L.bucket == kTcWide)
+            return launch_selinv_tcw(L.dtype != SELINV_F64, d, S.d_items + L.off, L.count, S.tcslab, S.spin_limit, st);
         return launch_selinv_tc(L.bucket, d, S.d_items + L.off, L.count, S.tcslab, S.spin_limit, st);
     case KL_TC_REDUCE:
+        if (L.bucket == kTcWide)
+            return launch_tcw_reduce(L.dtype != SELINV_F64, d, S.d_items, S.d_red + L.off, L.count, S.tcslab, st);
         return launch_tc_reduce(L.bucket, d, S.d_items, S.d_red + L.off, L.count, S.tcslab, st);
     case KL_DIAG_FIN: return launch_diag_fin(d, S.d_items + L.off, L.count, L.bucket, st);
     case KL_DIAG_TC: return launch_diag_tc(L.bucket, d, S.d_items + L.off, L.count, S.spin_limit, st);
