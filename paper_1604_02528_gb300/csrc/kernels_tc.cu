@@ -155,31 +155,47 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_selinv_tc(const ProbDesc *__r
     int b_issued = -1;   // last step whose B copies the MMA thread issued
 
     if (warp < kTcProd) {
-        // ---- producers: A digits, gathered with a two-deep load pipeline.
-        // Thread (row r, quarter kq) slices the k-values 4 kq .. 4 kq + 3 of
-        // each 16-k step; a warp holds 16 rows x 2 quarters, so that its
-        // stores of a plane fill two 128-byte core matrices
+        // ---- producers: A digits.  Thread (row r, quarter kq) slices the
+        // k-values 4 kq .. 4 kq + 3 of each 16-k step; a warp holds 16 rows x
+        // 2 quarters, so that its stores of a plane fill two 128-byte core
+        // matrices.  The gather runs three steps ahead in registers, every
+        // load a whole step before its use: column data (step i + 3),
+        // relative rows (i + 2), values (i + 1).
         const TcGather g{P.colbase + pos0, P.relbase + pos0, P.relidx, tile_cb, tile_rb, p0, c};
         const double *Zg = static_cast<const double *>(P.Z);
         const int r = (warp % 8) * 16 + (lane >> 1), kq = (warp / 8) * 2 + (lane & 1);
         const int E = rowE[r];
         double v[4];
-        int64_t ab[4];
+        int64_t ab[4], cb[4], rb[4];
         int32_t ar[4];
+        auto cols = [&](int i_) {
+#pragma unroll
+            for (int u = 0; u < 4; u++) {
+                if (i_ < n) g.cols((st0 + i_) * 16 + kq * 4 + u, cb[u], rb[u]);
+                else { cb[u] = -1; rb[u] = 0; }
+            }
+        };
+        auto parts = [&](int i_) {
+#pragma unroll
+            for (int u = 0; u < 4; u++) {
+                if (i_ < n) g.parts(r, (st0 + i_) * 16 + kq * 4 + u, cb[u], rb[u], ab[u], ar[u]);
+                else { ab[u] = -1; ar[u] = 0; }
+            }
+        };
+        auto load = [&]() {
+#pragma unroll
+            for (int u = 0; u < 4; u++) v[u] = ab[u] >= 0 ? Zg[ab[u] + ar[u]] : 0.0;
+        };
         if (n > 0) {
-#pragma unroll
-            for (int u = 0; u < 4; u++) {
-                g.parts(r, st0 * 16 + kq * 4 + u, ab[u], ar[u]);
-                v[u] = ab[u] >= 0 ? Zg[ab[u] + ar[u]] : 0.0;
-            }
-#pragma unroll
-            for (int u = 0; u < 4; u++) {
-                if (n > 1) g.parts(r, (st0 + 1) * 16 + kq * 4 + u, ab[u], ar[u]);
-                else ab[u] = -1;
-            }
+            cols(0);
+            parts(0);
+            load();
+            cols(1);
+            parts(1);
+            cols(2);
         }
         for (int i_ = 0; i_ < n; i_++) {
-            const int step = st0 + i_, stage = i_ & 1, use = i_ >> 1, k0 = step * 16;
+            const int stage = i_ & 1, use = i_ >> 1;
             uint16_t *Ab = As + stage * Cfg::A_STAGE;
             if (i_ >= 2 && !umma::mbar_wait(&empty[stage], (uint32_t)((use - 1) & 1), mlim)) {
                 s_abort = 1;
@@ -202,14 +218,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_selinv_tc(const ProbDesc *__r
                 store_plane4<5>(dst + 5 * Cfg::A_PLANE, lo, hi);
                 store_plane4<6>(dst + 6 * Cfg::A_PLANE, lo, hi);
             }
-            // loads of the next step's values, address lookups of the one after
-#pragma unroll
-            for (int u = 0; u < 4; u++) v[u] = ab[u] >= 0 ? Zg[ab[u] + ar[u]] : 0.0;
-#pragma unroll
-            for (int u = 0; u < 4; u++) {
-                if (i_ + 2 < n) g.parts(r, k0 + 32 + kq * 4 + u, ab[u], ar[u]);
-                else ab[u] = -1;
-            }
+            load();            // values of step i + 1
+            parts(i_ + 2);     // relative rows of step i + 2
+            cols(i_ + 3);      // column data of step i + 3
             umma::fence_proxy_async();
             __syncwarp();
             if (lane == 0) umma::mbar_arrive(&full[stage]);

@@ -171,17 +171,19 @@ __global__ void __launch_bounds__(kTwThreads, 1) k_selinv_tcw(const ProbDesc *__
 
     if (warp < kTwProd) {
         // ---- producers: thread (row r, quarter kq) slices the k-values
-        // 4 kq .. 4 kq + 3 of each 16-k step, gathered with a two-deep load
-        // pipeline; a warp holds 16 rows x 2 quarters, so that its stores of
-        // a plane fill two 128-byte core matrices.  Complex: the 4 k-values
-        // are (Re, Im) of the entries q = 8 step + 2 kq and + 1.
+        // 4 kq .. 4 kq + 3 of each 16-k step; a warp holds 16 rows x 2
+        // quarters, so that its stores of a plane fill two 128-byte core
+        // matrices.  Complex: the 4 k-values are (Re, Im) of the entries
+        // q = 8 step + 2 kq and + 1.  The gather runs three steps ahead in
+        // registers, every load a whole step before its use: column data
+        // (step i + 3), relative rows (i + 2), values (i + 1).
         const TcGather g{P.colbase + pos0, P.relbase + pos0, P.relidx, tile_cb, tile_rb, p0, c};
         const int r = (warp % 4) * 16 + (lane >> 1), kq = (warp / 4) * 2 + (lane & 1);
         const int E = rowE[r];
         constexpr int NV = CPLX ? 2 : 4;        // entries of A^{-1}_{C,C} per thread and step
         constexpr int QS = CPLX ? 8 : 16;       // entries per step
         double v[4];
-        int64_t ab[NV];
+        int64_t ab[NV], cb[NV], rb[NV];
         int32_t ar[NV];
         auto load = [&]() {
             if (CPLX) {
@@ -198,17 +200,28 @@ __global__ void __launch_bounds__(kTwThreads, 1) k_selinv_tcw(const ProbDesc *__
                 for (int u = 0; u < NV; u++) v[u] = ab[u] >= 0 ? Zg[ab[u] + ar[u]] : 0.0;
             }
         };
-        auto lookup = [&](int step) {
+        // column data of step i_ (of this item), none past the last step
+        auto cols = [&](int i_) {
 #pragma unroll
-            for (int u = 0; u < NV; u++) g.parts(r, step * QS + kq * NV + u, ab[u], ar[u]);
+            for (int u = 0; u < NV; u++) {
+                if (i_ < n) g.cols((st0 + i_) * QS + kq * NV + u, cb[u], rb[u]);
+                else { cb[u] = -1; rb[u] = 0; }
+            }
+        };
+        auto parts = [&](int i_) {
+#pragma unroll
+            for (int u = 0; u < NV; u++) {
+                if (i_ < n) g.parts(r, (st0 + i_) * QS + kq * NV + u, cb[u], rb[u], ab[u], ar[u]);
+                else { ab[u] = -1; ar[u] = 0; }
+            }
         };
         if (n > 0) {
-            lookup(st0);
+            cols(0);
+            parts(0);
             load();
-            if (n > 1) lookup(st0 + 1);
-            else
-#pragma unroll
-                for (int u = 0; u < NV; u++) ab[u] = -1;
+            cols(1);
+            parts(1);
+            cols(2);
         }
         for (int i_ = 0; i_ < n; i_++) {
             const int stage = i_ & 1, use = i_ >> 1;
@@ -234,12 +247,9 @@ __global__ void __launch_bounds__(kTwThreads, 1) k_selinv_tcw(const ProbDesc *__
                 store_plane4<5>(dst + 5 * Cfg::B_PLANE, lo, hi);
                 store_plane4<6>(dst + 6 * Cfg::B_PLANE, lo, hi);
             }
-            // loads of the next step's values, address lookups of the one after
-            load();
-            if (i_ + 2 < n) lookup(st0 + i_ + 2);
-            else
-#pragma unroll
-                for (int u = 0; u < NV; u++) ab[u] = -1;
+            load();            // values of step i + 1
+            parts(i_ + 2);     // relative rows of step i + 2
+            cols(i_ + 3);      // column data of step i + 3
             umma::fence_proxy_async();
             __syncwarp();
             if (lane == 0) umma::mbar_arrive(&full[stage]);

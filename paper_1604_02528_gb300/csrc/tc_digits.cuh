@@ -81,22 +81,33 @@ __device__ __forceinline__ void store_plane4(uint16_t *dst, const uint32_t (&lo)
 }
 
 // Address of entry (p, q) of A^{-1}_{C,C} in the ancestors' panels (stored at
-// (max, min) by symmetry) in two parts: a base known at once and the relative
-// row, which comes from memory -- so that its load can stay in flight; base
-// -1 outside C x C.  pl = p - p0.
+// (max, min) by symmetry), in three dependent parts so that a producer can
+// keep each load a whole step ahead of its use: the column data of q (panel
+// address of column C[q] in its owner and the start of its relative rows),
+// then the base and the relative row (a load), then the value; base -1
+// outside C x C.  pl = p - p0; the tile's own rows come from shared memory.
 struct TcGather {
     const int64_t *pcb, *prb;
     const int32_t *relidx;
     const int64_t *tile_cb, *tile_rb;
     int p0, c;
-    __device__ __forceinline__ void parts(int pl, int q, int64_t &base, int32_t &rel) const {
+    __device__ __forceinline__ void cols(int q, int64_t &cb, int64_t &rb) const {
+        if (q < c) {
+            cb = pcb[q];
+            rb = prb[q];
+        } else {
+            cb = -1;
+            rb = 0;
+        }
+    }
+    __device__ __forceinline__ void parts(int pl, int q, int64_t cb, int64_t rb, int64_t &base, int32_t &rel) const {
         const int p = p0 + pl;
         if (p >= c || q >= c) {
             base = -1;
             rel = 0;
         } else if (p >= q) {
-            base = pcb[q];
-            rel = relidx[prb[q] + p];
+            base = cb;
+            rel = relidx[rb + p];
         } else {
             base = tile_cb[pl];
             rel = relidx[tile_rb[pl] + q];
