@@ -14,10 +14,15 @@
 //       warps gather the entries and slice them with integer operations;
 //   D (tensor memory) = 7 group accumulators of 128 x 64, group g holding
 //       the exact fp32 sum of the digit products with i + j = g;
-//   every 128 k the groups are read back (tcgen05.ld) by 8 epilogue warps
-//   and added as int64 (hi, lo) words into shared memory.
-// Same digit scheme, exponent grids and exact sums as k_selinv_tc, so the
-// result does not depend on which of the two kernels forms it.
+//   every 128 k the groups are read back (tcgen05.ld) by 8 epilogue warps:
+//   their exact sum, floored to a multiple of 2^16 units of the digit grid
+//   (the size of the digit pairs that the scheme drops anyway), is added
+//   into one int64 word per entry in shared memory.
+// Operand rings: 4 stages for the Lhat^T copies (issued three steps ahead,
+// which is what their latency needs), 3 for the gathered digits.
+// The same digit scheme and exponent grids as k_selinv_tc; the chunk
+// boundaries sit at fixed multiples of 128 k, so the result does not depend
+// on the k-split.
 //
 // Complex symmetric values (template CPLX) run the same contraction on the
 // real 2c-long k dimension k' = 2q + part: B(p, 2q) = Re A^{-1}(p, q),
@@ -43,7 +48,9 @@ constexpr int kTwEpi = 8;          // epilogue warps: two per tensor-memory lane
 constexpr int kTwMmaWarp = kTwProd + kTwEpi;
 constexpr int kTwThreads = 32 * (kTwProd + kTwEpi + 1);
 constexpr int kTwHS = kTcM + 1;    // words per row of C in the int64 sums [p][m]: conflict-free both ways
-static_assert(2 * kTcM * kTwN + kTwN / 2 <= kTcSlotWords, "a split-k slot holds the (hi, lo) words and rowE");
+constexpr int kTwAS = 4;           // stages of the Lhat^T ring
+constexpr int kTwBS = 3;           // stages of the gathered-digit ring
+static_assert(kTcM * kTwN + kTwN / 2 <= kTcSlotWords, "a split-k slot holds the int64 words and rowE");
 
 struct TwCfg {
     static constexpr int A_PLANE = kTcM * 16;    // fp16 elements of one Lhat^T digit plane per k16 step
@@ -51,9 +58,24 @@ struct TwCfg {
     static constexpr int A_STAGE = kTcDig * A_PLANE;
     static constexpr int B_STAGE = kTcDig * B_PLANE;
     static constexpr uint32_t TCOLS = 512;       // 7 groups x 64 columns
-    static constexpr size_t SMEM = sizeof(uint16_t) * 2 * (size_t)(A_STAGE + B_STAGE) +
-                                   sizeof(long long) * 2 * (size_t)kTwN * kTwHS + sizeof(int) * kTwN;
+    static constexpr size_t SMEM = sizeof(uint16_t) * (size_t)(kTwAS * A_STAGE + kTwBS * B_STAGE) +
+                                   sizeof(long long) * (size_t)kTwN * kTwHS + sizeof(int) * kTwN;
 };
+static_assert(TwCfg::SMEM + 2048 <= 232448, "dynamic + static shared memory within the opt-in limit");
+
+// The exact value of one chunk's group sums (g weighted 256^(6 - g)) in
+// units of 2^16, floored: h 2^16 + floor(l 2^-16) for the value h 2^32 + l,
+// h = g0 2^16 + g1 2^8 + g2, l = g3 2^24 + g4 2^16 + g5 2^8 + g6.  Group g
+// holds at most g + 1 digit pairs, |g_g| <= (g + 1) 2^21, so the result stays
+// below 2^54 per chunk: int64 sums hold hundreds of chunks.
+__device__ __forceinline__ long long chunk_value16(const uint32_t (&acc)[kTcDig][8], int jj) {
+    long long gv[kTcDig];
+#pragma unroll
+    for (int gq = 0; gq < kTcDig; gq++) gv[gq] = (long long)__float2int_rn(__uint_as_float(acc[gq][jj]));
+    const long long h = (gv[0] << 16) + (gv[1] << 8) + gv[2];
+    const long long l = (gv[3] << 24) + (gv[4] << 16) + (gv[5] << 8) + gv[6];
+    return (h << 16) + (l >> 16);
+}
 static_assert(kTcDig * kTwN <= (int)TwCfg::TCOLS, "the group accumulators fit the tensor memory");
 
 // items: tile = (row tile * nmt + m tile) * nsplit + k-range, ntiles = nsplit;
@@ -64,17 +86,18 @@ __global__ void __launch_bounds__(kTwThreads, 1) k_selinv_tcw(const ProbDesc *__
                                                               long long *__restrict__ slab, long long wait_limit) {
     using Cfg = TwCfg;
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    uint16_t *As = reinterpret_cast<uint16_t *>(smem_raw);                // [2][7][A_PLANE] Lhat^T digits
-    uint16_t *Bs = As + 2 * Cfg::A_STAGE;                                  // [2][7][B_PLANE] gathered digits
-    long long *Hi = reinterpret_cast<long long *>(Bs + 2 * Cfg::B_STAGE);  // [64 p][kTwHS]
-    long long *Lo = Hi + kTwN * kTwHS;
-    int *rowE = reinterpret_cast<int *>(Lo + kTwN * kTwHS);                // [64]
+    uint16_t *As = reinterpret_cast<uint16_t *>(smem_raw);                    // [kTwAS][7][A_PLANE] Lhat^T digits
+    uint16_t *Bs = As + kTwAS * Cfg::A_STAGE;                                  // [kTwBS][7][B_PLANE] gathered digits
+    long long *Acc = reinterpret_cast<long long *>(Bs + kTwBS * Cfg::B_STAGE); // [64 p][kTwHS] sums, 2^16 units
+    int *rowE = reinterpret_cast<int *>(Acc + kTwN * kTwHS);                  // [64]
     __shared__ int64_t tile_cb[kTwN], tile_rb[kTwN];
-    // full[s]: the producers wrote B of stage s; afull[s]: the bulk copies of
-    // A landed in stage s; empty[s]: the products that read stage s are done;
-    // acc_full: a chunk's group sums are complete; tmem_free: the epilogue
-    // read them; drain: every product issued before an abort is done
-    __shared__ __align__(8) uint64_t full[2], afull[2], empty[2], acc_full, tmem_free, drain;
+    // full[s] / bempty[s]: the producers wrote B of stage s / the products
+    // that read it are done; afull[s] / aempty[s]: the bulk copies of A landed
+    // in stage s / the products that read it are done; acc_full: a chunk's
+    // group sums are complete; tmem_free: the epilogue read them; drain:
+    // every product issued before an abort is done
+    __shared__ __align__(8) uint64_t full[kTwBS], bempty[kTwBS], afull[kTwAS], aempty[kTwAS], acc_full, tmem_free,
+        drain;
     __shared__ uint32_t s_tmem;
     __shared__ int s_pre;
     __shared__ volatile int s_abort;
@@ -113,9 +136,9 @@ __global__ void __launch_bounds__(kTwThreads, 1) k_selinv_tcw(const ProbDesc *__
     // whole-column exponent of A^{-1} over C[0..p] (entry (p, q) sits in
     // the ancestor column C[min(p, q)])
     if (tid == 0) { s_pre = 0; s_abort = 0; }
-    // rows of A past the stored blocks stay zero in both stages
+    // rows of A past the stored blocks stay zero in every stage
     if (arows < kTcM)
-        for (int e = tid; e < 2 * Cfg::A_STAGE / 8; e += kTwThreads)
+        for (int e = tid; e < kTwAS * Cfg::A_STAGE / 8; e += kTwThreads)
             reinterpret_cast<uint4 *>(As)[e] = make_uint4(0, 0, 0, 0);
     __syncthreads();
     {
@@ -129,15 +152,18 @@ __global__ void __launch_bounds__(kTwThreads, 1) k_selinv_tcw(const ProbDesc *__
         tile_rb[e] = p < c ? P.relbase[pos0 + p] : 0;
         rowE[e] = p < c ? P.colexpZ[P.rows[pos0 + p]] : 0;
     }
-    // Hi and Lo are written by the first flush; an item without steps leaves zeros
+    // the sums are written by the first flush; an item without steps leaves zeros
     if (n == 0)
-        for (int e = tid; e < 2 * kTwN * kTwHS; e += kTwThreads) Hi[e] = 0;
+        for (int e = tid; e < kTwN * kTwHS; e += kTwThreads) Acc[e] = 0;
     for (int e = tid; e < kTcM; e += kTwThreads) ymax[e] = 0;
     if (tid == 0) {
-        for (int st = 0; st < 2; st++) {
+        for (int st = 0; st < kTwBS; st++) {
             umma::mbar_init(&full[st], kTwProd);
+            umma::mbar_init(&bempty[st], 1);
+        }
+        for (int st = 0; st < kTwAS; st++) {
             umma::mbar_init(&afull[st], 1);      // the arrival that expects A's bytes
-            umma::mbar_init(&empty[st], 1);
+            umma::mbar_init(&aempty[st], 1);
         }
         umma::mbar_init(&acc_full, 1);
         umma::mbar_init(&tmem_free, kTwEpi);
@@ -224,9 +250,9 @@ __global__ void __launch_bounds__(kTwThreads, 1) k_selinv_tcw(const ProbDesc *__
             cols(2);
         }
         for (int i_ = 0; i_ < n; i_++) {
-            const int stage = i_ & 1, use = i_ >> 1;
+            const int stage = i_ % kTwBS, use = i_ / kTwBS;
             uint16_t *Bb = Bs + stage * Cfg::B_STAGE;
-            if (i_ >= 2 && !umma::mbar_wait(&empty[stage], (uint32_t)((use - 1) & 1), mlim)) {
+            if (i_ >= kTwBS && !umma::mbar_wait(&bempty[stage], (uint32_t)((use - 1) & 1), mlim)) {
                 s_abort = 1;
                 break;
             }
@@ -262,7 +288,7 @@ __global__ void __launch_bounds__(kTwThreads, 1) k_selinv_tcw(const ProbDesc *__
             const uint16_t *Au = P.lhsu + P.lhsu_off[K] + (int64_t)(m0 / 8) * 128;
             const uint32_t aBytes = (uint32_t)(arows * 16 * 2);
             auto load_a = [&](int i_) {
-                const int st = i_ & 1;
+                const int st = i_ % kTwAS;
                 umma::mbar_arrive_expect_tx(&afull[st], kTcDig * aBytes);
 #pragma unroll
                 for (int pl = 0; pl < kTcDig; pl++)
@@ -270,37 +296,39 @@ __global__ void __launch_bounds__(kTwThreads, 1) k_selinv_tcw(const ProbDesc *__
                                    Au + ((int64_t)pl * nsteps + st0 + i_) * s64 * 16, aBytes, &afull[st]);
                 a_issued = i_;
             };
-            if (n > 0) load_a(0);
+            for (int i_ = 0; i_ < kTwAS - 1 && i_ < n; i_++) load_a(i_);
             for (int i_ = 0; i_ < n; i_++) {
-                const int stage = i_ & 1, use = i_ >> 1, ch = i_ / kTcFlush;
+                const int sa = i_ % kTwAS, sb = i_ % kTwBS, ch = i_ / kTcFlush;
                 const bool first = i_ % kTcFlush == 0;
-                if (!umma::mbar_wait(&afull[stage], (uint32_t)(use & 1), mlim) ||
-                    !umma::mbar_wait(&full[stage], (uint32_t)(use & 1), mlim) ||
+                if (!umma::mbar_wait(&afull[sa], (uint32_t)((i_ / kTwAS) & 1), mlim) ||
+                    !umma::mbar_wait(&full[sb], (uint32_t)((i_ / kTwBS) & 1), mlim) ||
                     (first && ch > 0 && !umma::mbar_wait(&tmem_free, (uint32_t)((ch - 1) & 1), mlim))) {
                     s_abort = 1;
                     break;
                 }
                 umma::fence_after_sync();
-                const uint64_t ad0 = umma::smem_desc(umma::smem_u32(As + stage * Cfg::A_STAGE), 128, 256);
-                const uint64_t bd0 = umma::smem_desc(umma::smem_u32(Bs + stage * Cfg::B_STAGE), 128, 256);
+                const uint64_t ad0 = umma::smem_desc(umma::smem_u32(As + sa * Cfg::A_STAGE), 128, 256);
+                const uint64_t bd0 = umma::smem_desc(umma::smem_u32(Bs + sb * Cfg::B_STAGE), 128, 256);
                 digit_products<kTwN, Cfg::A_PLANE, Cfg::B_PLANE>(tmem, ad0, bd0, first);
-                umma::commit(&empty[stage]);
+                umma::commit(&aempty[sa]);
+                umma::commit(&bempty[sb]);
                 if (i_ % kTcFlush == kTcFlush - 1 || i_ == n - 1) umma::commit(&acc_full);
-                // A of the next step into the other stage once the products of
-                // the step before this one have finished reading it
-                if (i_ + 1 < n) {
-                    if (i_ >= 1 && !umma::mbar_wait(&empty[(i_ + 1) & 1], (uint32_t)((((i_ + 1) >> 1) - 1) & 1), mlim)) {
+                // A of step i + 3 into the stage of step i - 1 once the
+                // products of step i - 1 have finished reading it
+                const int nx = i_ + kTwAS - 1;
+                if (nx < n) {
+                    if (i_ >= 1 && !umma::mbar_wait(&aempty[(i_ - 1) % kTwAS], (uint32_t)(((i_ - 1) / kTwAS) & 1), mlim)) {
                         s_abort = 1;
                         break;
                     }
-                    load_a(i_ + 1);
+                    load_a(nx);
                 }
                 if (s_abort) break;
             }
         }
         __syncwarp();
     } else {
-        // ---- epilogue: every chunk's exact fp32 group sums -> int64 (hi, lo);
+        // ---- epilogue: every chunk's exact fp32 group sums -> one int64 word;
         // warp (lane quarter, half) reads output rows 32 (warp % 4) .. + 31
         // and rows of C 32 half .. + 31
         const int lb = 32 * (warp % 4), m = lb + lane, half = (warp / 4) & 1;
@@ -319,20 +347,9 @@ __global__ void __launch_bounds__(kTwThreads, 1) k_selinv_tcw(const ProbDesc *__
                 umma::tmem_wait_ld();
 #pragma unroll
                 for (int jj = 0; jj < 8; jj++) {
-                    long long gv[kTcDig];
-#pragma unroll
-                    for (int gq = 0; gq < kTcDig; gq++) gv[gq] = (long long)__float2int_rn(__uint_as_float(acc[gq][jj]));
-                    const long long h = (gv[0] << 16) + (gv[1] << 8) + gv[2];
-                    const long long l = (gv[3] << 24) + (gv[4] << 16) + (gv[5] << 8) + gv[6];
-                    const int p = half * 32 + cb * 8 + jj;
-                    long long *ph = Hi + p * kTwHS + m, *pl = Lo + p * kTwHS + m;
-                    if (f == 0) {   // the first chunk writes, the later ones add
-                        *ph = h;
-                        *pl = l;
-                    } else {
-                        *ph += h;
-                        *pl += l;
-                    }
+                    const long long v = chunk_value16(acc, jj);
+                    long long *pa = Acc + (half * 32 + cb * 8 + jj) * kTwHS + m;
+                    *pa = f == 0 ? v : *pa + v;   // the first chunk writes, the later ones add
                 }
             }
             umma::fence_before_sync();
@@ -351,7 +368,9 @@ __global__ void __launch_bounds__(kTwThreads, 1) k_selinv_tcw(const ProbDesc *__
         if (warp == kTwMmaWarp && lane == 0) {
             umma::commit(&drain);
             umma::mbar_wait(&drain, 0u, mlim);
-            if (a_issued >= 0) umma::mbar_wait(&afull[a_issued & 1], (uint32_t)((a_issued >> 1) & 1), mlim);
+            // copies issued after the last step that waited for its own
+            for (int j = a_issued - (kTwAS - 2) > 0 ? a_issued - (kTwAS - 2) : 0; j <= a_issued; j++)
+                umma::mbar_wait(&afull[j % kTwAS], (uint32_t)((j / kTwAS) & 1), mlim);
         }
         umma::fence_before_sync();
         __syncthreads();
@@ -364,7 +383,7 @@ __global__ void __launch_bounds__(kTwThreads, 1) k_selinv_tcw(const ProbDesc *__
 
     // Y = -(A^{-1}_{C,C} Lhat): B digits on 2^(E - 1028 - 8i) of the row of
     // C, A digits on 2^(F - 1029 - 8j) of the column of K, so the value is
-    // (hi 2^-16 + lo 2^-48) 2^(E + F - 2057)
+    // (sum 2^-32) 2^(E + F - 2057) for the sum in 2^16 units
     if (nsplit == 1) {
         double *Zk = static_cast<double *>(P.Yout) + (CPLX ? 2 : 1) * P.panel_off[K];
         for (int e = tid; e < kTwN * kTcM; e += kTwThreads) {
@@ -372,7 +391,7 @@ __global__ void __launch_bounds__(kTwThreads, 1) k_selinv_tcw(const ProbDesc *__
             if (p0 + p >= c || jr >= mrows) continue;
             const int j = CPLX && jr >= s ? jr - s : jr;
             const int sc = (rowE[p] - 1022) + (P.colexp[fc + j] - 1022) - 13;
-            const double y = fixed_to_double(Hi[p * kTwHS + mm], Lo[p * kTwHS + mm], sc);
+            const double y = int64_to_double_scaled(Acc[p * kTwHS + mm], sc - 32);
             const int64_t at = (int64_t)j * ld + s + p0 + p;
             if (CPLX) Zk[2 * at + (jr >= s ? 1 : 0)] = -y;
             else Zk[at] = -y;
@@ -384,10 +403,9 @@ __global__ void __launch_bounds__(kTwThreads, 1) k_selinv_tcw(const ProbDesc *__
         long long *mine = slab + (int64_t)blockIdx.x * kTcSlotWords;
         for (int e = tid; e < kTwN * kTcM; e += kTwThreads) {
             const int p = e % kTwN, mm = e / kTwN;
-            mine[e] = Hi[p * kTwHS + mm];
-            mine[kTwN * kTcM + e] = Lo[p * kTwHS + mm];
+            mine[e] = Acc[p * kTwHS + mm];
         }
-        int *re = reinterpret_cast<int *>(mine + 2 * kTwN * kTcM);
+        int *re = reinterpret_cast<int *>(mine + kTwN * kTcM);
         for (int e = tid; e < kTwN; e += kTwThreads) re[e] = rowE[e];
         return;
     }
@@ -400,8 +418,8 @@ __global__ void __launch_bounds__(kTwThreads, 1) k_selinv_tcw(const ProbDesc *__
 }
 
 // Split-k reduction of k_selinv_tcw: one CTA per (row tile of 64, 8 output
-// rows); each element sums the int64 words of the group's k-range slots in
-// k order (exact) and forms A^{-1}_{C,K} = -(sum).
+// rows); each element adds the int64 words of the group's k-range slots
+// (exact integer sums) and forms A^{-1}_{C,K} = -(sum).
 // red[w] = {index of the group's first item, its slab slot, block of 8 output rows}.
 template <bool CPLX>
 __global__ void __launch_bounds__(256) k_tcw_reduce(const ProbDesc *__restrict__ descs,
@@ -423,7 +441,7 @@ __global__ void __launch_bounds__(256) k_tcw_reduce(const ProbDesc *__restrict__
     const int nsplit = it.ntiles;
     const int mt = (it.tile / nsplit) % nmt;
     const int p0 = (it.tile / nsplit / nmt) * kTwN, m0 = mt * kTcM;
-    const int *rowE = reinterpret_cast<const int *>(slab + (int64_t)rr.y * kTcSlotWords + 2 * kTwN * kTcM);
+    const int *rowE = reinterpret_cast<const int *>(slab + (int64_t)rr.y * kTcSlotWords + kTwN * kTcM);
     if (threadIdx.x < 8) ymax[threadIdx.x] = 0;
     __syncthreads();
     double *Zk = static_cast<double *>(P.Yout) + (CPLX ? 2 : 1) * P.panel_off[K];
@@ -431,15 +449,11 @@ __global__ void __launch_bounds__(256) k_tcw_reduce(const ProbDesc *__restrict__
     for (int r8 = threadIdx.x / kTwN; r8 < 8; r8 += 256 / kTwN) {   // a warp shares r8
         const int mm = rr.z * 8 + r8, jr = m0 + mm;
         if (jr >= mrows || p0 + p >= c) continue;
-        long long hi = 0, lo = 0;
-        for (int k2 = 0; k2 < nsplit; k2++) {
-            const long long *sl = slab + ((int64_t)rr.y + k2) * kTcSlotWords;
-            hi += sl[mm * kTwN + p];
-            lo += sl[kTwN * kTcM + mm * kTwN + p];
-        }
+        long long sum = 0;
+        for (int k2 = 0; k2 < nsplit; k2++) sum += slab[((int64_t)rr.y + k2) * kTcSlotWords + mm * kTwN + p];
         const int j = CPLX && jr >= s ? jr - s : jr;
         const int sc = (rowE[p] - 1022) + (P.colexp[fc + j] - 1022) - 13;
-        const double y = fixed_to_double(hi, lo, sc);
+        const double y = int64_to_double_scaled(sum, sc - 32);
         const int64_t at = (int64_t)j * ld + s + p0 + p;
         if (CPLX) Zk[2 * at + (jr >= s ? 1 : 0)] = -y;
         else Zk[at] = -y;
