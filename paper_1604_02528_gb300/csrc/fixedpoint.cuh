@@ -36,31 +36,4 @@ __device__ __forceinline__ double fixed_to_double(long long hi, long long lo, in
     return __longlong_as_double((long long)(sgn | ((unsigned long long)be << 52) | (q & 0xFFFFFFFFFFFFFull)));
 }
 
-// v * 2^e2 as a double, rounded once to nearest even, integer operations
-// only.
-__device__ __forceinline__ double int64_to_double_scaled(long long v, int e2) {
-    if (v == 0) return 0.0;
-    const unsigned long long sgn = v < 0 ? 0x8000000000000000ull : 0ull;
-    const unsigned long long m = v < 0 ? 0ull - (unsigned long long)v : (unsigned long long)v;
-    const int nb = 64 - __clzll((long long)m);          // bit length
-    unsigned long long q;
-    if (nb <= 53) {
-        q = m << (53 - nb);
-        e2 -= 53 - nb;
-    } else {
-        const int r = nb - 53;
-        q = m >> r;
-        const unsigned long long rem = m & ((1ull << r) - 1), half = 1ull << (r - 1);
-        if (rem > half || (rem == half && (q & 1ull))) q++;
-        e2 += r;
-        if (q >> 53) { q >>= 1; e2++; }
-    }
-    const int be = e2 + 52 + 1023;                      // q in [2^52, 2^53)
-    if (be <= 0 || be >= 2047) {                        // outside the normal range
-        const double x = ldexp((double)q, e2);
-        return sgn ? -x : x;
-    }
-    return __longlong_as_double((long long)(sgn | ((unsigned long long)be << 52) | (q & 0xFFFFFFFFFFFFFull)));
-}
-
 }  // namespace selinv

@@ -14,12 +14,12 @@
 //       warps gather the entries and slice them with integer operations;
 //   D (tensor memory) = 7 group accumulators of 128 x 64, group g holding
 //       the exact fp32 sum of the digit products with i + j = g;
-//   every 128 k the groups are read back (tcgen05.ld) by 8 epilogue warps:
-//   their exact sum, floored to a multiple of 2^16 units of the digit grid
-//   (the size of the digit pairs that the scheme drops anyway), is added
-//   into one int64 word per entry in shared memory.
-// Operand rings: 4 stages for the Lhat^T copies (issued three steps ahead,
-// which is what their latency needs), 3 for the gathered digits.
+//   every 128 k the groups are read back (tcgen05.ld) by 8 epilogue warps
+//   and their exact sum is added into a 96-bit word per entry in shared
+//   memory (an int64 high part and a 32-bit low part, carried after every
+//   chunk).
+// Operand rings: 3 stages for the Lhat^T copies (issued two steps ahead,
+// to cover their latency), 3 for the gathered digits.
 // The same digit scheme and exponent grids as k_selinv_tc; the chunk
 // boundaries sit at fixed multiples of 128 k, so the result does not depend
 // on the k-split.
@@ -48,9 +48,9 @@ constexpr int kTwEpi = 8;          // epilogue warps: two per tensor-memory lane
 constexpr int kTwMmaWarp = kTwProd + kTwEpi;
 constexpr int kTwThreads = 32 * (kTwProd + kTwEpi + 1);
 constexpr int kTwHS = kTcM + 1;    // words per row of C in the int64 sums [p][m]: conflict-free both ways
-constexpr int kTwAS = 4;           // stages of the Lhat^T ring
+constexpr int kTwAS = 3;           // stages of the Lhat^T ring
 constexpr int kTwBS = 3;           // stages of the gathered-digit ring
-static_assert(kTcM * kTwN + kTwN / 2 <= kTcSlotWords, "a split-k slot holds the int64 words and rowE");
+static_assert(2 * kTcM * kTwN + kTwN / 2 <= kTcSlotWords, "a split-k slot holds the (hi, lo) words and rowE");
 
 struct TwCfg {
     static constexpr int A_PLANE = kTcM * 16;    // fp16 elements of one Lhat^T digit plane per k16 step
@@ -59,24 +59,25 @@ struct TwCfg {
     static constexpr int B_STAGE = kTcDig * B_PLANE;
     static constexpr uint32_t TCOLS = 512;       // 7 groups x 64 columns
     static constexpr size_t SMEM = sizeof(uint16_t) * (size_t)(kTwAS * A_STAGE + kTwBS * B_STAGE) +
-                                   sizeof(long long) * (size_t)kTwN * kTwHS + sizeof(int) * kTwN;
+                                   (sizeof(long long) + sizeof(uint32_t)) * (size_t)kTwN * kTwHS + sizeof(int) * kTwN;
 };
 static_assert(TwCfg::SMEM + 2048 <= 232448, "dynamic + static shared memory within the opt-in limit");
 
-// The exact value of one chunk's group sums (g weighted 256^(6 - g)) in
-// units of 2^16, floored: h 2^16 + floor(l 2^-16) for the value h 2^32 + l,
-// h = g0 2^16 + g1 2^8 + g2, l = g3 2^24 + g4 2^16 + g5 2^8 + g6.  Group g
-// holds at most g + 1 digit pairs, |g_g| <= (g + 1) 2^21, so the result stays
-// below 2^54 per chunk: int64 sums hold hundreds of chunks.
-__device__ __forceinline__ long long chunk_value16(const uint32_t (&acc)[kTcDig][8], int jj) {
+// One chunk's group sums (g weighted 256^(6 - g)), exact, added into the
+// entry's 96-bit sum hi 2^32 + lo (0 <= lo < 2^32): the chunk's value is
+// h 2^32 + l with h = g0 2^16 + g1 2^8 + g2 and l = g3 2^24 + g4 2^16 +
+// g5 2^8 + g6 (|l| < 2^48), and what lo cannot hold is carried into hi.
+__device__ __forceinline__ void add_chunk(const uint32_t (&acc)[kTcDig][8], int jj, bool first, long long &hi,
+                                          uint32_t &lo) {
     long long gv[kTcDig];
 #pragma unroll
     for (int gq = 0; gq < kTcDig; gq++) gv[gq] = (long long)__float2int_rn(__uint_as_float(acc[gq][jj]));
     const long long h = (gv[0] << 16) + (gv[1] << 8) + gv[2];
     const long long l = (gv[3] << 24) + (gv[4] << 16) + (gv[5] << 8) + gv[6];
-    return (h << 16) + (l >> 16);
+    const long long t = (first ? 0ll : (long long)lo) + l;
+    hi = (first ? 0ll : hi) + h + (t >> 32);
+    lo = (uint32_t)t;
 }
-static_assert(kTcDig * kTwN <= (int)TwCfg::TCOLS, "the group accumulators fit the tensor memory");
 
 // items: tile = (row tile * nmt + m tile) * nsplit + k-range, ntiles = nsplit;
 // nmt = ceil(rows of A / 128) (1 for real supernodes of <= 128 columns)
@@ -88,8 +89,9 @@ __global__ void __launch_bounds__(kTwThreads, 1) k_selinv_tcw(const ProbDesc *__
     extern __shared__ __align__(128) unsigned char smem_raw[];
     uint16_t *As = reinterpret_cast<uint16_t *>(smem_raw);                    // [kTwAS][7][A_PLANE] Lhat^T digits
     uint16_t *Bs = As + kTwAS * Cfg::A_STAGE;                                  // [kTwBS][7][B_PLANE] gathered digits
-    long long *Acc = reinterpret_cast<long long *>(Bs + kTwBS * Cfg::B_STAGE); // [64 p][kTwHS] sums, 2^16 units
-    int *rowE = reinterpret_cast<int *>(Acc + kTwN * kTwHS);                  // [64]
+    long long *Hi = reinterpret_cast<long long *>(Bs + kTwBS * Cfg::B_STAGE);  // [64 p][kTwHS] high words of the sums
+    uint32_t *Lo = reinterpret_cast<uint32_t *>(Hi + kTwN * kTwHS);          // [64 p][kTwHS] low 32 bits
+    int *rowE = reinterpret_cast<int *>(Lo + kTwN * kTwHS);                   // [64]
     __shared__ int64_t tile_cb[kTwN], tile_rb[kTwN];
     // full[s] / bempty[s]: the producers wrote B of stage s / the products
     // that read it are done; afull[s] / aempty[s]: the bulk copies of A landed
@@ -154,7 +156,10 @@ __global__ void __launch_bounds__(kTwThreads, 1) k_selinv_tcw(const ProbDesc *__
     }
     // the sums are written by the first flush; an item without steps leaves zeros
     if (n == 0)
-        for (int e = tid; e < kTwN * kTwHS; e += kTwThreads) Acc[e] = 0;
+        for (int e = tid; e < kTwN * kTwHS; e += kTwThreads) {
+            Hi[e] = 0;
+            Lo[e] = 0;
+        }
     for (int e = tid; e < kTcM; e += kTwThreads) ymax[e] = 0;
     if (tid == 0) {
         for (int st = 0; st < kTwBS; st++) {
@@ -328,7 +333,7 @@ __global__ void __launch_bounds__(kTwThreads, 1) k_selinv_tcw(const ProbDesc *__
         }
         __syncwarp();
     } else {
-        // ---- epilogue: every chunk's exact fp32 group sums -> one int64 word;
+        // ---- epilogue: every chunk's exact fp32 group sums -> the 96-bit sums;
         // warp (lane quarter, half) reads output rows 32 (warp % 4) .. + 31
         // and rows of C 32 half .. + 31
         const int lb = 32 * (warp % 4), m = lb + lane, half = (warp / 4) & 1;
@@ -346,10 +351,9 @@ __global__ void __launch_bounds__(kTwThreads, 1) k_selinv_tcw(const ProbDesc *__
                     umma::tmem_ld8(tmem + ((uint32_t)lb << 16) + (uint32_t)(gq * kTwN + half * 32 + cb * 8), acc[gq]);
                 umma::tmem_wait_ld();
 #pragma unroll
-                for (int jj = 0; jj < 8; jj++) {
-                    const long long v = chunk_value16(acc, jj);
-                    long long *pa = Acc + (half * 32 + cb * 8 + jj) * kTwHS + m;
-                    *pa = f == 0 ? v : *pa + v;   // the first chunk writes, the later ones add
+                for (int jj = 0; jj < 8; jj++) {   // the first chunk writes, the later ones add
+                    const int e = (half * 32 + cb * 8 + jj) * kTwHS + m;
+                    add_chunk(acc, jj, f == 0, Hi[e], Lo[e]);
                 }
             }
             umma::fence_before_sync();
@@ -383,7 +387,7 @@ __global__ void __launch_bounds__(kTwThreads, 1) k_selinv_tcw(const ProbDesc *__
 
     // Y = -(A^{-1}_{C,C} Lhat): B digits on 2^(E - 1028 - 8i) of the row of
     // C, A digits on 2^(F - 1029 - 8j) of the column of K, so the value is
-    // (sum 2^-32) 2^(E + F - 2057) for the sum in 2^16 units
+    // (hi 2^-16 + lo 2^-48) 2^(E + F - 2057)
     if (nsplit == 1) {
         double *Zk = static_cast<double *>(P.Yout) + (CPLX ? 2 : 1) * P.panel_off[K];
         for (int e = tid; e < kTwN * kTcM; e += kTwThreads) {
@@ -391,7 +395,7 @@ __global__ void __launch_bounds__(kTwThreads, 1) k_selinv_tcw(const ProbDesc *__
             if (p0 + p >= c || jr >= mrows) continue;
             const int j = CPLX && jr >= s ? jr - s : jr;
             const int sc = (rowE[p] - 1022) + (P.colexp[fc + j] - 1022) - 13;
-            const double y = int64_to_double_scaled(Acc[p * kTwHS + mm], sc - 32);
+            const double y = fixed_to_double(Hi[p * kTwHS + mm], (long long)Lo[p * kTwHS + mm], sc);
             const int64_t at = (int64_t)j * ld + s + p0 + p;
             if (CPLX) Zk[2 * at + (jr >= s ? 1 : 0)] = -y;
             else Zk[at] = -y;
@@ -403,9 +407,10 @@ __global__ void __launch_bounds__(kTwThreads, 1) k_selinv_tcw(const ProbDesc *__
         long long *mine = slab + (int64_t)blockIdx.x * kTcSlotWords;
         for (int e = tid; e < kTwN * kTcM; e += kTwThreads) {
             const int p = e % kTwN, mm = e / kTwN;
-            mine[e] = Acc[p * kTwHS + mm];
+            mine[e] = Hi[p * kTwHS + mm];
+            mine[kTwN * kTcM + e] = (long long)Lo[p * kTwHS + mm];
         }
-        int *re = reinterpret_cast<int *>(mine + kTwN * kTcM);
+        int *re = reinterpret_cast<int *>(mine + 2 * kTwN * kTcM);
         for (int e = tid; e < kTwN; e += kTwThreads) re[e] = rowE[e];
         return;
     }
@@ -418,7 +423,7 @@ __global__ void __launch_bounds__(kTwThreads, 1) k_selinv_tcw(const ProbDesc *__
 }
 
 // Split-k reduction of k_selinv_tcw: one CTA per (row tile of 64, 8 output
-// rows); each element adds the int64 words of the group's k-range slots
+// rows); each element adds the (hi, lo) words of the group's k-range slots
 // (exact integer sums) and forms A^{-1}_{C,K} = -(sum).
 // red[w] = {index of the group's first item, its slab slot, block of 8 output rows}.
 template <bool CPLX>
@@ -441,7 +446,7 @@ __global__ void __launch_bounds__(256) k_tcw_reduce(const ProbDesc *__restrict__
     const int nsplit = it.ntiles;
     const int mt = (it.tile / nsplit) % nmt;
     const int p0 = (it.tile / nsplit / nmt) * kTwN, m0 = mt * kTcM;
-    const int *rowE = reinterpret_cast<const int *>(slab + (int64_t)rr.y * kTcSlotWords + kTwN * kTcM);
+    const int *rowE = reinterpret_cast<const int *>(slab + (int64_t)rr.y * kTcSlotWords + 2 * kTwN * kTcM);
     if (threadIdx.x < 8) ymax[threadIdx.x] = 0;
     __syncthreads();
     double *Zk = static_cast<double *>(P.Yout) + (CPLX ? 2 : 1) * P.panel_off[K];
@@ -449,11 +454,15 @@ __global__ void __launch_bounds__(256) k_tcw_reduce(const ProbDesc *__restrict__
     for (int r8 = threadIdx.x / kTwN; r8 < 8; r8 += 256 / kTwN) {   // a warp shares r8
         const int mm = rr.z * 8 + r8, jr = m0 + mm;
         if (jr >= mrows || p0 + p >= c) continue;
-        long long sum = 0;
-        for (int k2 = 0; k2 < nsplit; k2++) sum += slab[((int64_t)rr.y + k2) * kTcSlotWords + mm * kTwN + p];
+        long long hi = 0, lo = 0;
+        for (int k2 = 0; k2 < nsplit; k2++) {
+            const long long *sl = slab + ((int64_t)rr.y + k2) * kTcSlotWords;
+            hi += sl[mm * kTwN + p];
+            lo += sl[kTwN * kTcM + mm * kTwN + p];
+        }
         const int j = CPLX && jr >= s ? jr - s : jr;
         const int sc = (rowE[p] - 1022) + (P.colexp[fc + j] - 1022) - 13;
-        const double y = int64_to_double_scaled(sum, sc - 32);
+        const double y = fixed_to_double(hi, lo, sc);
         const int64_t at = (int64_t)j * ld + s + p0 + p;
         if (CPLX) Zk[2 * at + (jr >= s ? 1 : 0)] = -y;
         else Zk[at] = -y;
