@@ -101,9 +101,10 @@ struct ProbDesc {
     int *status;                // latched error code
     uint16_t *lhs;              // fp16 digit planes of Lhat, [plane][column][q] (mma.sync kernels)
     const int64_t *lhs_off;     // [ns+1] offsets into lhs (elements)
-    uint16_t *lhsu;             // the same digits in the tcgen05 operand layout: per plane and
-                                // 16-row step a block of roundup(s, 64) columns x 16 q, K-major
-                                // 8 x 8 core matrices (column groups 256 bytes apart); zero padding
+    uint16_t *lhsu;             // the same digits in the tcgen05 operand layout: per 16-row step
+                                // and plane (the 7 planes of a step one after the other) a block
+                                // of roundup(s, 64) columns x 16 q, K-major 8 x 8 core matrices
+                                // (column groups 256 bytes apart); zero padding
     const int64_t *lhsu_off;    // [ns+1] offsets into lhsu (elements)
     int *colexp;                // [n] biased exponent of each column of Lhat
     int *colexpY;               // [n] biased exponent of each column of A^{-1}_{C,K} (atomic max)

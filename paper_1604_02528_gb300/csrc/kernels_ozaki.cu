@@ -90,10 +90,11 @@ __global__ void __launch_bounds__(256) k_lhat_digits(const ProbDesc *__restrict_
     if (lane == 0) P.colexp[fc + j] = E;
     uint16_t *pl = P.lhs + P.lhs_off[K];
     const int64_t plane = (int64_t)s * c16;
-    // tcgen05 layout: block (plane, step) of s64 x 16, column group j/8 at 128
-    // elements, k group (q % 16) / 8 at 64, row j % 8 at 8, q % 8
+    // tcgen05 layout: block (step, plane) of s64 x 16 (the 7 planes of a step
+    // one after the other), column group j/8 at 128 elements, k group
+    // (q % 16) / 8 at 64, row j % 8 at 8, q % 8
     uint16_t *pu = P.lhsu + P.lhsu_off[K];
-    const int64_t s64 = (s + 63) / 64 * 64, nst = c16 / 16;
+    const int64_t s64 = (s + 63) / 64 * 64;
     for (int q = lane; q < c16; q += 32) {
         int d[kDig];
         if (q < c) digits7(Lh[q], E, d);
@@ -101,12 +102,12 @@ __global__ void __launch_bounds__(256) k_lhat_digits(const ProbDesc *__restrict_
 #pragma unroll
             for (int i = 0; i < kDig; i++) d[i] = 0;
         }
-        const int64_t ub = (int64_t)(q / 16) * s64 * 16 + (j / 8) * 128 + ((q % 16) / 8) * 64 + (j % 8) * 8 + q % 8;
+        const int64_t ub = (int64_t)(q / 16) * kDig * s64 * 16 + (j / 8) * 128 + ((q % 16) / 8) * 64 + (j % 8) * 8 + q % 8;
 #pragma unroll
         for (int i = 0; i < kDig; i++) {
             const uint16_t h = (uint16_t)f16_of_int(d[i]);
             pl[i * plane + (int64_t)j * c16 + q] = h;
-            pu[i * nst * s64 * 16 + ub] = h;
+            pu[i * s64 * 16 + ub] = h;
         }
     }
 }

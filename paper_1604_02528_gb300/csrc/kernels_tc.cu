@@ -239,7 +239,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_selinv_tc(const ProbDesc *__r
 #pragma unroll
                 for (int pl = 0; pl < kTcDig; pl++)
                     umma::bulk_g2s(Bs + st * Cfg::B_STAGE + pl * Cfg::B_PLANE,
-                                   Bu + ((int64_t)pl * nsteps + st0 + i_) * s64 * 16, kBBytes, &bfull[st]);
+                                   Bu + ((int64_t)(st0 + i_) * kTcDig + pl) * s64 * 16, kBBytes, &bfull[st]);
                 b_issued = i_;
             };
             if (n > 0) load_b(0);
@@ -580,7 +580,7 @@ __global__ void __launch_bounds__(kDtThreads, 1) k_diag_tc(const ProbDesc *__res
 #pragma unroll
                 for (int pl = 0; pl < kTcDig; pl++)
                     umma::bulk_g2s(As + st * Cfg::A_STAGE + pl * Cfg::A_PLANE,
-                                   Au + ((int64_t)pl * nsteps + st0 + i_) * s64 * 16, aBytes, &afull[st]);
+                                   Au + ((int64_t)(st0 + i_) * kTcDig + pl) * s64 * 16, aBytes, &afull[st]);
                 a_issued = i_;
             };
             if (n > 0) load_a(0);

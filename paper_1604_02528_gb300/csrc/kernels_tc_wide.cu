@@ -134,15 +134,58 @@ __global__ void __launch_bounds__(kTwThreads, 1) k_selinv_tcw(const ProbDesc *__
     const int nflush = (n + kTcFlush - 1) / kTcFlush;
     const int arows = s64 - m0 < kTcM ? s64 - m0 : kTcM; // rows of A in the stored blocks
 
+    int a_issued = -1;   // last step whose A copies the MMA thread issued
+    // copies of the Lhat^T digit planes of step i_ (rows m0 .. m0 + 127 of
+    // each stored block); the 7 planes of a step lie one after the other, so
+    // a block of exactly 128 rows comes in one copy
+    const uint16_t *Au = P.lhsu + P.lhsu_off[K] + (int64_t)(m0 / 8) * 128;
+    const uint32_t aBytes = (uint32_t)(arows * 16 * 2);
+    const bool whole = m0 == 0 && s64 == kTcM;
+    auto load_a = [&](int i_) {
+        const int st = i_ % kTwAS;
+        const uint16_t *src = Au + (int64_t)(st0 + i_) * kTcDig * s64 * 16;
+        umma::mbar_arrive_expect_tx(&afull[st], kTcDig * aBytes);
+        if (whole) {
+            umma::bulk_g2s(As + st * Cfg::A_STAGE, src, kTcDig * aBytes, &afull[st]);
+        } else {
+#pragma unroll
+            for (int pl = 0; pl < kTcDig; pl++)
+                umma::bulk_g2s(As + st * Cfg::A_STAGE + pl * Cfg::A_PLANE, src + (int64_t)pl * s64 * 16, aBytes,
+                               &afull[st]);
+        }
+        a_issued = i_;
+    };
+    if (tid == 0) {
+        s_pre = 0;
+        s_abort = 0;
+        for (int st = 0; st < kTwBS; st++) {
+            umma::mbar_init(&full[st], kTwProd);
+            umma::mbar_init(&bempty[st], 1);
+        }
+        for (int st = 0; st < kTwAS; st++) {
+            umma::mbar_init(&afull[st], 1);      // the arrival that expects A's bytes
+            umma::mbar_init(&aempty[st], 1);
+        }
+        umma::mbar_init(&acc_full, 1);
+        umma::mbar_init(&tmem_free, kTwEpi);
+        umma::mbar_init(&drain, 1);
+        umma::mbar_init_fence();
+    }
+    // rows of A past the stored blocks stay zero in every stage (the copies
+    // write only the rows before them)
+    if (arows < kTcM)
+        for (int st = 0; st < kTwAS; st++)
+            for (int pl = 0; pl < kTcDig; pl++)
+                for (int e = arows * 16 + tid * 8; e < Cfg::A_PLANE; e += kTwThreads * 8)
+                    *reinterpret_cast<uint4 *>(As + st * Cfg::A_STAGE + pl * Cfg::A_PLANE + e) = make_uint4(0, 0, 0, 0);
+    umma::fence_proxy_async();   // zeroed A rows are seen by the tensor cores
+    __syncthreads();
+    // the first copies go out before the rest of the set-up
+    if (warp == kTwMmaWarp && lane == 0)
+        for (int i_ = 0; i_ < kTwAS - 1 && i_ < n; i_++) load_a(i_);
     // row exponents of the gathered block: row p is bounded by the largest
     // whole-column exponent of A^{-1} over C[0..p] (entry (p, q) sits in
     // the ancestor column C[min(p, q)])
-    if (tid == 0) { s_pre = 0; s_abort = 0; }
-    // rows of A past the stored blocks stay zero in every stage
-    if (arows < kTcM)
-        for (int e = tid; e < kTwAS * Cfg::A_STAGE / 8; e += kTwThreads)
-            reinterpret_cast<uint4 *>(As)[e] = make_uint4(0, 0, 0, 0);
-    __syncthreads();
     {
         int e = 0;
         for (int q = tid; q < p0 && q < c; q += kTwThreads) e = max(e, P.colexpZ[P.rows[pos0 + q]]);
@@ -161,25 +204,10 @@ __global__ void __launch_bounds__(kTwThreads, 1) k_selinv_tcw(const ProbDesc *__
             Lo[e] = 0;
         }
     for (int e = tid; e < kTcM; e += kTwThreads) ymax[e] = 0;
-    if (tid == 0) {
-        for (int st = 0; st < kTwBS; st++) {
-            umma::mbar_init(&full[st], kTwProd);
-            umma::mbar_init(&bempty[st], 1);
-        }
-        for (int st = 0; st < kTwAS; st++) {
-            umma::mbar_init(&afull[st], 1);      // the arrival that expects A's bytes
-            umma::mbar_init(&aempty[st], 1);
-        }
-        umma::mbar_init(&acc_full, 1);
-        umma::mbar_init(&tmem_free, kTwEpi);
-        umma::mbar_init(&drain, 1);
-        umma::mbar_init_fence();
-    }
     if (warp == kTwMmaWarp) {
         umma::tmem_alloc(&s_tmem, Cfg::TCOLS);
         umma::tmem_relinquish();
     }
-    umma::fence_proxy_async();   // zeroed A rows are seen by the tensor cores
     umma::fence_before_sync();
     __syncthreads();
     umma::fence_after_sync();
@@ -198,7 +226,6 @@ __global__ void __launch_bounds__(kTwThreads, 1) k_selinv_tcw(const ProbDesc *__
     }
     __syncthreads();
     const uint32_t tmem = s_tmem;
-    int a_issued = -1;   // last step whose A copies the MMA thread issued
 
     if (warp < kTwProd) {
         // ---- producers: thread (row r, quarter kq) slices the k-values
@@ -287,21 +314,9 @@ __global__ void __launch_bounds__(kTwThreads, 1) k_selinv_tcw(const ProbDesc *__
             if (s_abort) break;
         }
     } else if (warp == kTwMmaWarp) {
-        // ---- one thread copies the Lhat^T digit planes (rows m0 .. m0 + 127
-        // of each stored block) and issues the products
+        // ---- one thread copies the Lhat^T digit planes (the first ones went
+        // out during the set-up) and issues the products
         if (lane == 0) {
-            const uint16_t *Au = P.lhsu + P.lhsu_off[K] + (int64_t)(m0 / 8) * 128;
-            const uint32_t aBytes = (uint32_t)(arows * 16 * 2);
-            auto load_a = [&](int i_) {
-                const int st = i_ % kTwAS;
-                umma::mbar_arrive_expect_tx(&afull[st], kTcDig * aBytes);
-#pragma unroll
-                for (int pl = 0; pl < kTcDig; pl++)
-                    umma::bulk_g2s(As + st * Cfg::A_STAGE + pl * Cfg::A_PLANE,
-                                   Au + ((int64_t)pl * nsteps + st0 + i_) * s64 * 16, aBytes, &afull[st]);
-                a_issued = i_;
-            };
-            for (int i_ = 0; i_ < kTwAS - 1 && i_ < n; i_++) load_a(i_);
             for (int i_ = 0; i_ < n; i_++) {
                 const int sa = i_ % kTwAS, sb = i_ % kTwBS, ch = i_ / kTcFlush;
                 const bool first = i_ % kTcFlush == 0;
