@@ -50,6 +50,7 @@ constexpr int kTwThreads = 32 * (kTwProd + kTwEpi + 1);
 constexpr int kTwHS = kTcM + 1;    // words per row of C in the int64 sums [p][m]: conflict-free both ways
 constexpr int kTwAS = 3;           // stages of the Lhat^T ring
 constexpr int kTwBS = 3;           // stages of the gathered-digit ring
+constexpr int kTwPrefetch = 8;     // steps ahead at which the Lhat^T blocks are asked into L2
 static_assert(2 * kTcM * kTwN + kTwN / 2 <= kTcSlotWords, "a split-k slot holds the (hi, lo) words and rowE");
 
 struct TwCfg {
@@ -180,9 +181,14 @@ __global__ void __launch_bounds__(kTwThreads, 1) k_selinv_tcw(const ProbDesc *__
                     *reinterpret_cast<uint4 *>(As + st * Cfg::A_STAGE + pl * Cfg::A_PLANE + e) = make_uint4(0, 0, 0, 0);
     umma::fence_proxy_async();   // zeroed A rows are seen by the tensor cores
     __syncthreads();
-    // the first copies go out before the rest of the set-up
-    if (warp == kTwMmaWarp && lane == 0)
+    // the first copies go out before the rest of the set-up; the blocks of
+    // the steps after them are asked into L2 (the CTAs of one supernode run
+    // in step, so each block would otherwise come from DRAM for all of them)
+    if (warp == kTwMmaWarp && lane == 0) {
         for (int i_ = 0; i_ < kTwAS - 1 && i_ < n; i_++) load_a(i_);
+        for (int i_ = kTwAS - 1; i_ < kTwPrefetch && i_ < n; i_++)
+            umma::bulk_prefetch_l2(Au + (int64_t)(st0 + i_) * kTcDig * s64 * 16, kTcDig * aBytes);
+    }
     // row exponents of the gathered block: row p is bounded by the largest
     // whole-column exponent of A^{-1} over C[0..p] (entry (p, q) sits in
     // the ancestor column C[min(p, q)])
@@ -336,6 +342,8 @@ __global__ void __launch_bounds__(kTwThreads, 1) k_selinv_tcw(const ProbDesc *__
                 // A of step i + 3 into the stage of step i - 1 once the
                 // products of step i - 1 have finished reading it
                 const int nx = i_ + kTwAS - 1;
+                if (i_ + kTwPrefetch < n)
+                    umma::bulk_prefetch_l2(Au + (int64_t)(st0 + i_ + kTwPrefetch) * kTcDig * s64 * 16, kTcDig * aBytes);
                 if (nx < n) {
                     if (i_ >= 1 && !umma::mbar_wait(&aempty[(i_ - 1) % kTwAS], (uint32_t)(((i_ - 1) / kTwAS) & 1), mlim)) {
                         s_abort = 1;

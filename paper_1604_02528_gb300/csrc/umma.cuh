@@ -93,6 +93,12 @@ __device__ __forceinline__ void bulk_g2s(void *smem, const void *gmem, uint32_t 
                  : "memory");
 }
 
+// Asks L2 to fetch `bytes` at `gmem` (16-byte aligned, a multiple of 16) in
+// the background; nothing is written to shared memory.
+__device__ __forceinline__ void bulk_prefetch_l2(const void *gmem, uint32_t bytes) {
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;\n" ::"l"(gmem), "r"(bytes) : "memory");
+}
+
 // Waits for the completion of the phase with the given parity; gives up after
 // `limit` polls and returns false.
 __device__ __forceinline__ bool mbar_wait(uint64_t *mbar, uint32_t parity, long long limit) {
