@@ -27,40 +27,10 @@
 
 namespace selinv {
 
-constexpr int kDig = 7;          // digits per operand
 constexpr int kOzK = 16;         // k per mma step
 constexpr int kFlushSteps = 8;   // 128 k per exact fp32 chunk
 constexpr int kApad = 24;        // smem row stride (fp16) of a 16-wide k slab: conflict-free
 constexpr int kOzThreads = 256;
-
-// fp16 bit pattern of a small integer v (|v| <= 128): exact via an fp32
-// round trip through the magic constant 1.5 * 2^23, then an exact narrowing.
-__device__ __forceinline__ uint32_t f16_of_int(int v) {
-    const float f = __int_as_float(0x4B400000 + v) - 12582912.0f;
-    return (uint32_t)__half_as_ushort(__float2half_rn(f));
-}
-
-// 7 balanced base-256 digits (most significant first) of x on the grid of
-// biased exponent E (E >= exponent of x): x ~= sum_i d_i 2^(E-1022-7-8i).
-__device__ __forceinline__ void digits7(double x, int E, int d[kDig]) {
-    const long long b = __double_as_longlong(x);
-    const int ex = (int)((b >> 52) & 0x7FF);
-    unsigned long long mant = ex ? ((b & 0xFFFFFFFFFFFFFull) | (1ull << 52)) : 0ull;
-    const int sh = E - ex - 2;                       // M = mant * 2^(2 - (E - ex)) < 2^55
-    unsigned long long M = sh < 0 ? (mant << (-sh)) : (sh < 64 ? (mant >> sh) : 0ull);
-#pragma unroll
-    for (int i = kDig - 1; i >= 1; i--) {
-        int v = (int)(M & 0xFFull);
-        M >>= 8;
-        if (v >= 128) { v -= 256; M += 1; }
-        d[i] = v;
-    }
-    d[0] = (int)M;                                   // <= 128
-    if (b < 0) {
-#pragma unroll
-        for (int i = 0; i < kDig; i++) d[i] = -d[i];
-    }
-}
 
 // ---------------------------------------------------------------------------
 // k_lhat_digits: digit planes of Lhat_{C,K} (per column j: exponent over all

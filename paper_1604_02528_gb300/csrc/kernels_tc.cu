@@ -452,8 +452,13 @@ template <int TN> struct DtCfg {
 };
 static_assert(4 * 64 <= 32 * kDtProd, "a producer thread per (column, 4-row quarter) of a 64-column tile");
 
-// items: tile = chunk * ncol + column tile, ntiles = number of chunks
-template <int TN>
+// items: tile = (chunk * ncol + column tile) * nmt + m tile, ntiles = number
+// of chunks; nmt = 1 for real supernodes.  CPLX: complex symmetric values,
+// the real contraction over k' = 2q + part with the 2s rows of the complex
+// Lhat operand (rows j: real part of row j of Lhat^T Y, rows s + j: its
+// imaginary part; two m tiles when 2s > 128) and Y's (Re, Im) along k'; the
+// sums go to (Re hi, Re lo, Im hi, Im lo) words per entry.
+template <int TN, bool CPLX>
 __global__ void __launch_bounds__(kDtThreads, 1) k_diag_tc(const ProbDesc *__restrict__ descs,
                                                            const Item *__restrict__ items, int nitems,
                                                            long long wait_limit) {
@@ -481,20 +486,25 @@ __global__ void __launch_bounds__(kDtThreads, 1) k_diag_tc(const ProbDesc *__res
     const int s = P.super_ptr[K + 1] - fc;
     const int64_t ld = P.rowptr[K + 1] - P.rowptr[K];
     const int c = (int)(ld - s);
-    const int nsteps = ((c + 15) & ~15) / 16;
+    const int kw = CPLX ? 2 * c : c;                    // k extent
+    const int mrows = CPLX ? 2 * s : s;                 // rows of A (output rows)
+    const int nsteps = (kw + 15) / 16;
     const int ncol = (s + TN - 1) / TN;
+    const int nmt = (mrows + kTcM - 1) / kTcM;
     const int nch = it.ntiles;
-    const int ct = it.tile % ncol, ch = it.tile / ncol;
-    const int n0 = ct * TN;
+    const int mt = it.tile % nmt;
+    const int ct = (it.tile / nmt) % ncol, ch = it.tile / nmt / ncol;
+    const int n0 = ct * TN, m0 = mt * kTcM;
     const int chunk = ((nsteps + nch - 1) / nch + kTcFlush - 1) / kTcFlush * kTcFlush;
     const int st0 = ch * chunk;
     const int st1 = st0 + chunk < nsteps ? st0 + chunk : nsteps;
     const int n = st1 > st0 ? st1 - st0 : 0;
     const int nflush = (n + kTcFlush - 1) / kTcFlush;
-    const int64_t s64 = (s + 63) / 64 * 64;
+    const int64_t s64 = (mrows + 63) / 64 * 64;         // operand rows of a stored digit block
+    const int arows = s64 - m0 < kTcM ? (int)(s64 - m0) : kTcM;
 
     if (tid == 0) s_abort = 0;
-    // both A stages start at zero: the bulk copies fill rows < s64 only
+    // both A stages start at zero: the bulk copies fill rows < arows only
     for (int e = tid; e < 2 * Cfg::A_STAGE / 8; e += kDtThreads) reinterpret_cast<uint4 *>(As)[e] = make_uint4(0, 0, 0, 0);
 
     for (int j = tid; j < TN; j += kDtThreads) colE[j] = n0 + j < s ? P.colexpY[fc + n0 + j] : 0;
@@ -525,17 +535,30 @@ __global__ void __launch_bounds__(kDtThreads, 1) k_diag_tc(const ProbDesc *__res
         // of each 16-row step; a warp holds 16 columns x 2 quarters, so that its
         // stores of a plane fill two 128-byte core matrices.  The values of the
         // next step are loaded while this one is sliced.
+        // Complex: the 4 k-values are (Re, Im) of rows q = 8 step + 2 kq and + 1.
         const int r = (warp % 4) * 16 + (lane >> 1), kq = (warp / 4) * 2 + (lane & 1);
         const bool act = r < TN;
-        const double *Yc = static_cast<const double *>(P.Z) + P.panel_off[K] + (int64_t)(n0 + r) * ld + s;
+        const int64_t ycol = P.panel_off[K] + (int64_t)(n0 + r) * ld + s;
         const bool colok = act && n0 + r < s;
         const int E = colok ? colE[r] : 0;
         double v[4];
         auto fetch = [&](int step) {
+            if (CPLX) {
+                const double2 *Yz = static_cast<const double2 *>(P.Z) + ycol;
 #pragma unroll
-            for (int u = 0; u < 4; u++) {
-                const int q = step * 16 + kq * 4 + u;
-                v[u] = (colok && step < st1 && q < c) ? Yc[q] : 0.0;
+                for (int u = 0; u < 2; u++) {
+                    const int q = step * 8 + kq * 2 + u;
+                    const double2 y = (colok && step < st1 && q < c) ? Yz[q] : make_double2(0.0, 0.0);
+                    v[2 * u] = y.x;
+                    v[2 * u + 1] = y.y;
+                }
+            } else {
+                const double *Yc = static_cast<const double *>(P.Z) + ycol;
+#pragma unroll
+                for (int u = 0; u < 4; u++) {
+                    const int q = step * 16 + kq * 4 + u;
+                    v[u] = (colok && step < st1 && q < c) ? Yc[q] : 0.0;
+                }
             }
         };
         if (n > 0) fetch(st0);
@@ -572,8 +595,8 @@ __global__ void __launch_bounds__(kDtThreads, 1) k_diag_tc(const ProbDesc *__res
     } else if (warp == kDtMmaWarp) {
         // ---- one thread copies the Lhat digit planes and issues the products
         if (lane == 0) {
-            const uint16_t *Au = P.lhsu + P.lhsu_off[K];
-            const uint32_t aBytes = (uint32_t)(s64 * 16 * 2);
+            const uint16_t *Au = P.lhsu + P.lhsu_off[K] + (int64_t)(m0 / 8) * 128;
+            const uint32_t aBytes = (uint32_t)(arows * 16 * 2);
             auto load_a = [&](int i_) {
                 const int st = i_ & 1;
                 umma::mbar_arrive_expect_tx(&afull[st], kTcDig * aBytes);
@@ -670,22 +693,29 @@ __global__ void __launch_bounds__(kDtThreads, 1) k_diag_tc(const ProbDesc *__res
     if (n == 0) return;
     // the chunk's exact sums into K's (cleared at the start of every call):
     // integer additions, so the order of chunks and column tiles does not matter
-    long long *acc64 = P.dacc + 2 * P.linv_off[K];
+    long long *acc64 = P.dacc + (CPLX ? 4 : 2) * P.linv_off[K];
     for (int e = tid; e < kTcM * TN; e += kDtThreads) {
-        const int i = e % kTcM, col = e / kTcM, j = n0 + col;
-        if (i >= s || j >= s) continue;
-        const long long hi = Hi[col * kTcM + i], lo = Lo[col * kTcM + i];
-        unsigned long long *dst = reinterpret_cast<unsigned long long *>(acc64 + 2 * ((int64_t)j * s + i));
+        const int ir = e % kTcM, col = e / kTcM, j = n0 + col, i = m0 + ir;
+        if (i >= mrows || j >= s) continue;
+        const long long hi = Hi[col * kTcM + ir], lo = Lo[col * kTcM + ir];
+        unsigned long long *dst =
+            CPLX ? reinterpret_cast<unsigned long long *>(acc64 + 4 * ((int64_t)j * s + (i < s ? i : i - s)) + (i < s ? 0 : 2))
+                 : reinterpret_cast<unsigned long long *>(acc64 + 2 * ((int64_t)j * s + i));
         if (hi) atomicAdd(dst, (unsigned long long)hi);
         if (lo) atomicAdd(dst + 1, (unsigned long long)lo);
     }
 }
 
-cudaError_t launch_diag_tc(int tn, const ProbDesc *d, const Item *items, int n, long long wait_limit,
+cudaError_t launch_diag_tc(int tn, int cplx, const ProbDesc *d, const Item *items, int n, long long wait_limit,
                            cudaStream_t st) {
     if (n <= 0) return cudaSuccess;
-    if (tn == 32) k_diag_tc<32><<<n, kDtThreads, DtCfg<32>::SMEM, st>>>(d, items, n, wait_limit);
-    else k_diag_tc<64><<<n, kDtThreads, DtCfg<64>::SMEM, st>>>(d, items, n, wait_limit);
+    if (cplx) {
+        if (tn == 32) k_diag_tc<32, true><<<n, kDtThreads, DtCfg<32>::SMEM, st>>>(d, items, n, wait_limit);
+        else k_diag_tc<64, true><<<n, kDtThreads, DtCfg<64>::SMEM, st>>>(d, items, n, wait_limit);
+    } else {
+        if (tn == 32) k_diag_tc<32, false><<<n, kDtThreads, DtCfg<32>::SMEM, st>>>(d, items, n, wait_limit);
+        else k_diag_tc<64, false><<<n, kDtThreads, DtCfg<64>::SMEM, st>>>(d, items, n, wait_limit);
+    }
     return cudaGetLastError();
 }
 
@@ -693,8 +723,10 @@ cudaError_t configure_tc_kernels() {
     cudaError_t e = cudaFuncSetAttribute(k_selinv_tc<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TcCfg<16>::SMEM);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_selinv_tc<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TcCfg<32>::SMEM);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_selinv_tc<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TcCfg<64>::SMEM);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_diag_tc<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)DtCfg<32>::SMEM);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_diag_tc<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)DtCfg<64>::SMEM);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_diag_tc<32, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)DtCfg<32>::SMEM);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_diag_tc<64, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)DtCfg<64>::SMEM);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_diag_tc<32, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)DtCfg<32>::SMEM);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_diag_tc<64, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)DtCfg<64>::SMEM);
     return e;
 }
 

@@ -31,8 +31,10 @@ cudaError_t launch_selinv_tcw(int cplx, const ProbDesc *d, const Item *items, in
 cudaError_t launch_tcw_reduce(int cplx, const ProbDesc *d, const Item *items, const int4 *red, int n,
                               const long long *slab, cudaStream_t st);
 cudaError_t launch_diag_fin(const ProbDesc *d, const Item *items, int n, int bshift, cudaStream_t st);
-cudaError_t launch_diag_tc(int tn, const ProbDesc *d, const Item *items, int n, long long wait_limit,
+cudaError_t launch_diag_tc(int tn, int cplx, const ProbDesc *d, const Item *items, int n, long long wait_limit,
                            cudaStream_t st);
+cudaError_t launch_lhat_digits_z(const ProbDesc *d, const int2 *work, int nwork, cudaStream_t st);
+cudaError_t launch_diag_fin_z(const ProbDesc *d, const Item *items, int n, cudaStream_t st);
 cudaError_t launch_check_finite(const void *x, int64_t n_doubles, int *status, cudaStream_t st);
 cudaError_t launch_selinv_persist(int dtype, const ProbDesc *d, const Item *items, const int8_t *buckets,
                                   int n, int *ticket, long long spin_limit, int wait_on_unset,

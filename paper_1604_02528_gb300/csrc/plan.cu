@@ -90,13 +90,14 @@ int Workspace::ensure(const PlanData &p, int dtype) {
     if (!wget(*this, &work, es * (size_t)std::max<int64_t>(p.nnz, 1))) return SELINV_ERR_OOM;
     if (!wget(*this, &lhs, sizeof(uint16_t) * (size_t)std::max<int64_t>(p.lhs_total, 8)))
         return SELINV_ERR_OOM;
-    if (!wget(*this, &lhsu, sizeof(uint16_t) * (size_t)std::max<int64_t>(p.lhsu_total, 8)))
-        return SELINV_ERR_OOM;
-    cudaMemset(lhsu, 0, sizeof(uint16_t) * (size_t)std::max<int64_t>(p.lhsu_total, 8));   // padding stays zero
+    // tcgen05 operand layout of the Lhat digits: real, or the complex operand
+    const int64_t nlhsu = std::max<int64_t>(dtype == SELINV_F64 ? p.lhsu_total : std::max(p.lhsu_total, p.lhsuz_total), 8);
+    if (!wget(*this, &lhsu, sizeof(uint16_t) * (size_t)nlhsu)) return SELINV_ERR_OOM;
+    cudaMemset(lhsu, 0, sizeof(uint16_t) * (size_t)nlhsu);   // padding stays zero
     if (!wget(*this, &colexp, sizeof(int) * (size_t)std::max(p.n, 1))) return SELINV_ERR_OOM;
     if (!wget(*this, &colexpY, sizeof(int) * (size_t)std::max(p.n, 1))) return SELINV_ERR_OOM;
-    if (!wget(*this, &dacc, sizeof(long long) * 2 * (size_t)std::max<int64_t>(p.linv_total, 1)))
-        return SELINV_ERR_OOM;
+    const size_t dwords = (dtype == SELINV_F64 ? 2 : 4) * (size_t)std::max<int64_t>(p.linv_total, 1);
+    if (!wget(*this, &dacc, sizeof(long long) * dwords)) return SELINV_ERR_OOM;
     if (!wget(*this, &colexpZ, sizeof(int) * (size_t)std::max(p.n, 1))) return SELINV_ERR_OOM;
     if (!wget(*this, &linvexp, sizeof(int) * (size_t)std::max(p.n, 1))) return SELINV_ERR_OOM;
     if (!wget(*this, &linvd, sizeof(uint16_t) * (size_t)std::max<int64_t>(p.linvd_total, 8)))
@@ -109,7 +110,7 @@ int Workspace::ensure(const PlanData &p, int dtype) {
     cudaMemset(yacc, 0, sizeof(long long) * ny);
     cudaMemset(tcount, 0, sizeof(int) * (size_t)std::max<int64_t>(p.tile_total, 1));
     cudaMemset(colexpY, 0, sizeof(int) * (size_t)std::max(p.n, 1));
-    cudaMemset(dacc, 0, sizeof(long long) * 2 * (size_t)std::max<int64_t>(p.linv_total, 1));
+    cudaMemset(dacc, 0, sizeof(long long) * dwords);
     cudaMemset(counter, 0, sizeof(int) * (size_t)std::max(p.ns, 1));
     cudaMemset(done, 0, sizeof(int) * (size_t)(p.ns + 1));
     cudaMemset(ticket, 0, sizeof(int));
@@ -314,6 +315,15 @@ static int build_plan(PlanData &p, int32_t n, int32_t ns, const int32_t *super_p
         p.lhsu_off[K + 1] = p.lhsu_off[K] + (s >= kOzMinS ? 7 * s64 * c16 : 0);
     }
     p.lhsu_total = p.lhsu_off[ns];
+    // complex symmetric: the operand of 2s rows over k' = 2q + part (2c long)
+    p.lhsuz_off.assign(ns + 1, 0);
+    for (int32_t K = 0; K < ns; K++) {
+        const int64_t s = super_ptr[K + 1] - super_ptr[K];
+        const int64_t c = rowptr[K + 1] - rowptr[K] - s;
+        const int64_t k16 = (2 * c + 15) / 16 * 16, s64 = (2 * s + 63) / 64 * 64;
+        p.lhsuz_off[K + 1] = p.lhsuz_off[K] + (s >= kOzMinS ? 7 * s64 * k16 : 0);
+    }
+    p.lhsuz_total = p.lhsuz_off[ns];
     p.linvd_off.assign(ns + 1, 0);
     for (int32_t K = 0; K < ns; K++) {
         const int64_t s = super_ptr[K + 1] - super_ptr[K];
@@ -372,6 +382,7 @@ int ensure_device(PlanData &p) {
     if ((rc = upload(&p.d_part_off_all, p.part_off_all))) return rc;
     if ((rc = upload(&p.d_lhs_off, p.lhs_off))) return rc;
     if ((rc = upload(&p.d_lhsu_off, p.lhsu_off))) return rc;
+    if ((rc = upload(&p.d_lhsuz_off, p.lhsuz_off))) return rc;
     if ((rc = upload(&p.d_tile_base, p.tile_base))) return rc;
     if ((rc = upload(&p.d_linvd_off, p.linvd_off))) return rc;
     if ((rc = upload(&p.d_seg_ptr, p.seg_ptr))) return rc;
@@ -386,9 +397,9 @@ int ensure_device(PlanData &p) {
 void PlanData::release_device() {
     dfree(d_super_ptr); dfree(d_sparent); dfree(d_rowptr); dfree(d_rows); dfree(d_panel_off);
     dfree(d_colbase); dfree(d_relbase); dfree(d_relidx); dfree(d_linv_off); dfree(d_part_off); dfree(d_part_off_all);
-    dfree(d_lhs_off); dfree(d_lhsu_off); dfree(d_tile_base); dfree(d_linvd_off); dfree(d_status); dfree(d_sel_pos);
+    dfree(d_lhs_off); dfree(d_lhsu_off); dfree(d_lhsuz_off); dfree(d_tile_base); dfree(d_linvd_off); dfree(d_status); dfree(d_sel_pos);
     dfree(d_seg_ptr); dfree(d_seg_start);
-    d_lhs_off = d_lhsu_off = d_tile_base = d_linvd_off = d_sel_pos = d_seg_ptr = nullptr;
+    d_lhs_off = d_lhsu_off = d_lhsuz_off = d_tile_base = d_linvd_off = d_sel_pos = d_seg_ptr = nullptr;
     d_seg_start = nullptr;
     d_super_ptr = d_sparent = d_rows = d_relidx = nullptr;
     d_rowptr = d_panel_off = d_colbase = d_relbase = d_linv_off = d_part_off = d_part_off_all = nullptr;
@@ -424,7 +435,7 @@ ProbDesc make_desc(const PlanData &p, Workspace &w, int dtype, const void *L, co
     d.lhs = w.lhs;
     d.lhs_off = p.d_lhs_off;
     d.lhsu = w.lhsu;
-    d.lhsu_off = p.d_lhsu_off;
+    d.lhsu_off = dtype == SELINV_F64 ? p.d_lhsu_off : p.d_lhsuz_off;
     d.colexp = w.colexp;
     d.colexpY = w.colexpY;
     d.dacc = w.dacc;
@@ -468,12 +479,20 @@ int build_schedule(Schedule &S, const std::vector<const PlanData *> &plans,
     auto act = [&](int i, int32_t K) { return plans[i]->active.empty() || plans[i]->active[K] != 0; };
     // tensor-core contraction for this problem and width (never for the LU form)
     auto ozok = [&](int i, int s) { return !descs[i].lu && oz_eligible(descs[i].dtype, s, plans[i]->opts); };
+    // complex symmetric supernodes on tcgen05 (the transposed gather-GEMM and
+    // the diagonal block over the real 2c-long contraction; level and plain
+    // schedules, not the Hermitian or LU forms; their Lhat stays on the FP64 pipe)
+    auto zok = [&](int i, int s) {
+        const selinv_opts &o = plans[i]->opts;
+        return !descs[i].lu && !descs[i].herm && descs[i].dtype == SELINV_C128 && o.fast_contraction == 1 &&
+               s >= std::max(kOzMinS, o.oz_min_s) && (mode == SELINV_SCHED_LEVEL || mode == SELINV_SCHED_PLAIN);
+    };
     // DFMA supernodes small enough for a warp each (k_selinv_tiny; not the LU form)
     auto tiny = [&](int i, int32_t K) {
         const PlanData &p = *plans[i];
         const int s = p.super_ptr[K + 1] - p.super_ptr[K];
         const int64_t c = p.rowptr[K + 1] - p.rowptr[K] - s;
-        return !descs[i].lu && s <= 8 && c <= 64 && !ozok(i, s);
+        return !descs[i].lu && s <= 8 && c <= 64 && !ozok(i, s) && !zok(i, s);
     };
     // 1) L_KK^{-1}, Dinv for every supernode (one launch per dtype and size class)
     for (int dt = 0; dt < 2; dt++)
@@ -568,6 +587,19 @@ int build_schedule(Schedule &S, const std::vector<const PlanData *> &plans,
         }
         const int cnt = (int)(S.h_work.size() - off);
         if (cnt) S.launches.push_back({KL_DIGITS, SELINV_F64, 0, off, cnt, -1});
+        // the complex operand (after the FP64 Lhat of step 2)
+        const int64_t offz = (int64_t)S.h_work.size();
+        for (int i = 0; i < np; i++) {
+            const PlanData &p = *plans[i];
+            for (int32_t K = 0; K < p.ns; K++) {
+                const int s = p.super_ptr[K + 1] - p.super_ptr[K];
+                const int64_t c = p.rowptr[K + 1] - p.rowptr[K] - s;
+                if (c == 0 || !act(i, K) || !zok(i, s)) continue;
+                for (int jb = 0; jb < (s + 7) / 8; jb++) S.h_work.push_back(make_int2(i, (K << 8) | jb));
+            }
+        }
+        const int cntz = (int)(S.h_work.size() - offz);
+        if (cntz) S.launches.push_back({KL_DIGITS, SELINV_C128, 0, offz, cntz, -1});
     }
     // 3) the traversal, root to leaves
     auto push_items = [&](int i, int32_t K) {
@@ -583,7 +615,14 @@ int build_schedule(Schedule &S, const std::vector<const PlanData *> &plans,
             const int s = p.super_ptr[it.K + 1] - p.super_ptr[it.K];
             const int ncol = tl.bucket == kTcWide ? 1 : (s + tl.bucket - 1) / tl.bucket;
             if (it.ntiles < 2 || it.tile % (it.ntiles * ncol) != 0) continue;   // not a group's first item
-            for (int cb = 0; cb < (s + 7) / 8; cb++) S.h_red.push_back(make_int4((int)e, (int)(e - tl.off), cb, 0));
+            // output rows of the item: s columns, or the 2s (part, column)
+            // rows of a complex one in 128-row m tiles
+            int rows = s;
+            if (tl.bucket == kTcWide && tl.dtype != SELINV_F64) {
+                const int nmt = (2 * s + kTcRows - 1) / kTcRows, mt = (it.tile / it.ntiles) % nmt;
+                rows = std::min(kTcRows, 2 * s - mt * kTcRows);
+            }
+            for (int cb = 0; cb < (rows + 7) / 8; cb++) S.h_red.push_back(make_int4((int)e, (int)(e - tl.off), cb, 0));
         }
         const int cnt = (int)((int64_t)S.h_red.size() - off);
         if (cnt) S.launches.push_back({KL_TC_REDUCE, SELINV_F64, tl.bucket, off, cnt, tl.level});
@@ -599,7 +638,7 @@ int build_schedule(Schedule &S, const std::vector<const PlanData *> &plans,
             for (int cb = 0; cb < (s + 7) / 8; cb++) S.h_items.push_back({it.prob, it.K, cb, 0});
         }
         const int cnt = (int)((int64_t)S.h_items.size() - off);
-        if (cnt) S.launches.push_back({KL_DIAG_FIN, SELINV_F64, bshift, off, cnt, dl.level});
+        if (cnt) S.launches.push_back({KL_DIAG_FIN, dl.dtype, bshift, off, cnt, dl.level});
     };
     // tensor-core diagonal block: (64-row tile, 32-column pass) items
     auto push_diag = [&](int i, int32_t K) {
@@ -624,6 +663,82 @@ int build_schedule(Schedule &S, const std::vector<const PlanData *> &plans,
         const int nch = (int)std::max<int64_t>(1, std::min(want, (nsteps + 7) / 8));
         for (int ch = 0; ch < nch; ch++)
             for (int ct = 0; ct < ncol; ct++) S.h_items.push_back({i, K, ch * ncol + ct, nch});
+    };
+    // complex tcgen05 items: the transposed gather-GEMM over (64-row tile, m
+    // tile of the 2s output rows, k-range), ntiles = number of k-ranges; the
+    // diagonal block over (chunk, column tile, m tile), ntiles = number of chunks
+    auto z_nmt = [&](int s) { return (2 * s + kTcRows - 1) / kTcRows; };
+    auto z_ctas = [&](int i, int32_t K) -> int64_t {
+        const PlanData &p = *plans[i];
+        const int s = p.super_ptr[K + 1] - p.super_ptr[K];
+        const int64_t c = p.rowptr[K + 1] - p.rowptr[K] - s;
+        return c == 0 ? 0 : (c + kTcWideRows - 1) / kTcWideRows * z_nmt(s);
+    };
+    auto z_split = [&](int i, int32_t K, int64_t level_ctas) {
+        const PlanData &p = *plans[i];
+        const int s = p.super_ptr[K + 1] - p.super_ptr[K];
+        const int64_t c = p.rowptr[K + 1] - p.rowptr[K] - s;
+        const selinv_opts &o = p.opts;
+        const int64_t target = (int64_t)o.split_target * 152;
+        const int64_t want = (target + level_ctas - 1) / std::max<int64_t>(level_ctas, 1);
+        const int64_t maxsplit = std::max<int64_t>(1, ((2 * c + 15) / 16) / o.split_min_steps);
+        return (int)std::max<int64_t>(1, std::min(want, maxsplit));
+    };
+    auto push_z = [&](int i, int32_t K, int nsplit) {
+        const PlanData &p = *plans[i];
+        const int s = p.super_ptr[K + 1] - p.super_ptr[K];
+        const int64_t c = p.rowptr[K + 1] - p.rowptr[K] - s;
+        if (c == 0) return;
+        const int nmt = z_nmt(s);
+        const int64_t nt = (c + kTcWideRows - 1) / kTcWideRows;
+        for (int64_t t = 0; t < nt; t++)
+            for (int mt = 0; mt < nmt; mt++)
+                for (int ks = 0; ks < nsplit; ks++) S.h_items.push_back({i, K, (int)((t * nmt + mt) * nsplit + ks), nsplit});
+    };
+    auto push_zdiag = [&](int i, int32_t K, int64_t diag_units) {
+        const PlanData &p = *plans[i];
+        const int s = p.super_ptr[K + 1] - p.super_ptr[K];
+        const int64_t c = p.rowptr[K + 1] - p.rowptr[K] - s;
+        const int tn = s <= 32 ? 32 : 64, ncol = (s + tn - 1) / tn, nmt = z_nmt(s);
+        const int64_t nsteps = (2 * c + 15) / 16;
+        const int64_t want = (152 + diag_units - 1) / std::max<int64_t>(diag_units, 1);
+        const int nch = (int)std::max<int64_t>(1, std::min(want, (nsteps + 7) / 8));
+        for (int ch = 0; ch < nch; ch++)
+            for (int ct = 0; ct < ncol; ct++)
+                for (int mt = 0; mt < nmt; mt++) S.h_items.push_back({i, K, (ch * ncol + ct) * nmt + mt, nch});
+    };
+    // the launches of the complex tcgen05 supernodes zs (one level, or one
+    // supernode in the plain schedule): contraction, its split-k sums, the
+    // diagonal block per column-tile width and its finisher
+    auto launch_z = [&](const std::vector<std::pair<int, int32_t>> &zs, int level, int64_t other_ctas) {
+        if (zs.empty()) return;
+        int64_t ctas = other_ctas;
+        for (auto &ik : zs) ctas += z_ctas(ik.first, ik.second);
+        const int64_t off = (int64_t)S.h_items.size();
+        for (auto &ik : zs) push_z(ik.first, ik.second, z_split(ik.first, ik.second, ctas));
+        const int cnt = (int)(S.h_items.size() - off);
+        if (cnt) {
+            S.launches.push_back({KL_SELINV_TC, SELINV_C128, kTcWide, off, cnt, level});
+            add_tc_reduce(S.launches.back());
+        }
+        int64_t units = 0;
+        for (auto &ik : zs) {
+            const int s = plans[ik.first]->super_ptr[ik.second + 1] - plans[ik.first]->super_ptr[ik.second];
+            const int tn = s <= 32 ? 32 : 64;
+            units += (int64_t)((s + tn - 1) / tn) * z_nmt(s);
+        }
+        for (int tn : {64, 32}) {
+            const int64_t off2 = (int64_t)S.h_items.size();
+            for (auto &ik : zs) {
+                const int s = plans[ik.first]->super_ptr[ik.second + 1] - plans[ik.first]->super_ptr[ik.second];
+                if ((s <= 32 ? 32 : 64) == tn) push_zdiag(ik.first, ik.second, units);
+            }
+            const int cnt2 = (int)(S.h_items.size() - off2);
+            if (cnt2) {
+                S.launches.push_back({KL_DIAG_TC, SELINV_C128, tn, off2, cnt2, level});
+                add_diag_fin(S.launches.back(), 1);
+            }
+        }
     };
     // tensor-core items: (row tile, column tile of width tn, k-range) triples,
     // ntiles field = number of k-ranges; c == 0 has none
@@ -766,6 +881,10 @@ int build_schedule(Schedule &S, const std::vector<const PlanData *> &plans,
             for (int32_t K = p.ns - 1; K >= 0; K--) {
                 if (!act(i, K)) continue;
                 const int s = p.super_ptr[K + 1] - p.super_ptr[K];
+                if (zok(i, s)) {
+                    launch_z({{i, K}}, p.level[K], 0);
+                    continue;
+                }
                 if (ozok(i, s)) {
                     const int tn = tn_of(i, s);
                     const int64_t off = (int64_t)S.h_items.size();
@@ -811,8 +930,18 @@ int build_schedule(Schedule &S, const std::vector<const PlanData *> &plans,
                         oz.push_back({i, K});
                 }
             }
+            std::vector<std::pair<int, int32_t>> zs;   // complex tcgen05 supernodes of the level
+            for (int i = 0; i < np; i++) {
+                const PlanData &p = *plans[i];
+                if (l >= p.nlevels) continue;
+                for (int64_t e = p.level_ptr[l]; e < p.level_ptr[l + 1]; e++) {
+                    const int32_t K = p.level_list[e];
+                    if (act(i, K) && zok(i, p.super_ptr[K + 1] - p.super_ptr[K])) zs.push_back({i, K});
+                }
+            }
             int64_t level_ctas = 0;
             for (auto &ik : oz) level_ctas += oz_ctas(ik.first, ik.second);
+            launch_z(zs, l, level_ctas);
             for (int tc = 1; tc >= 0; tc--)
                 for (int tn : {kTcWide, 64, 32, 16}) {
                     const int64_t off = (int64_t)S.h_items.size();
@@ -884,7 +1013,8 @@ int build_schedule(Schedule &S, const std::vector<const PlanData *> &plans,
                         for (int64_t e = p.level_ptr[l]; e < p.level_ptr[l + 1]; e++) {
                             const int32_t K = p.level_list[e];
                             const int s = p.super_ptr[K + 1] - p.super_ptr[K];
-                            if (act(i, K) && bucket_of(s) == b && !ozok(i, s) && !tiny(i, K)) push_items(i, K);
+                            if (act(i, K) && bucket_of(s) == b && !ozok(i, s) && !zok(i, s) && !tiny(i, K))
+                                push_items(i, K);
                         }
                     }
                     const int cnt = (int)(S.h_items.size() - off);
@@ -908,7 +1038,8 @@ int build_schedule(Schedule &S, const std::vector<const PlanData *> &plans,
         for (int i = 0; i < np; i++) {
             if (!has[i]) continue;
             S.pre_ptr.push_back(descs[i].dacc);
-            S.pre_bytes.push_back(sizeof(long long) * 2 * (size_t)std::max<int64_t>(plans[i]->linv_total, 1));
+            S.pre_bytes.push_back(sizeof(long long) * (descs[i].dtype == SELINV_F64 ? 2 : 4) *
+                                  (size_t)std::max<int64_t>(plans[i]->linv_total, 1));
             S.pre_ptr.push_back(descs[i].colexpY);
             S.pre_bytes.push_back(sizeof(int) * (size_t)std::max(plans[i]->n, 1));
         }
@@ -939,7 +1070,9 @@ cudaError_t launch_with(const Schedule &S, const Launch &L, const ProbDesc *d, c
     case KL_DINV: return launch_dinv(L.dtype, d, S.d_work + L.off, L.count, st);
     case KL_LHAT: return launch_lhat(L.dtype, L.bucket, d, S.d_items + L.off, L.count, st);
     case KL_SELINV: return launch_selinv(L.dtype, L.bucket, d, S.d_items + L.off, L.count, st);
-    case KL_DIGITS: return launch_lhat_digits(d, S.d_work + L.off, L.count, st);
+    case KL_DIGITS:
+        if (L.dtype != SELINV_F64) return launch_lhat_digits_z(d, S.d_work + L.off, L.count, st);
+        return launch_lhat_digits(d, S.d_work + L.off, L.count, st);
     case KL_SELINV_OZ: return launch_selinv_oz(L.bucket, d, S.d_items + L.off, L.count, st);
     case KL_DIAG: return launch_diag_oz(d, S.d_items + L.off, L.count, st);
     case KL_LINV_DIGITS: return launch_linv_digits(d, S.d_work + L.off, L.count, st);
@@ -952,8 +1085,11 @@ cudaError_t launch_with(const Schedule &S, const Launch &L, const ProbDesc *d, c
         if (L.bucket == kTcWide)
             return launch_tcw_reduce(L.dtype != SELINV_F64, d, S.d_items, S.d_red + L.off, L.count, S.tcslab, st);
         return launch_tc_reduce(L.bucket, d, S.d_items, S.d_red + L.off, L.count, S.tcslab, st);
-    case KL_DIAG_FIN: return launch_diag_fin(d, S.d_items + L.off, L.count, L.bucket, st);
-    case KL_DIAG_TC: return launch_diag_tc(L.bucket, d, S.d_items + L.off, L.count, S.spin_limit, st);
+    case KL_DIAG_FIN:
+        if (L.dtype != SELINV_F64) return launch_diag_fin_z(d, S.d_items + L.off, L.count, st);
+        return launch_diag_fin(d, S.d_items + L.off, L.count, L.bucket, st);
+    case KL_DIAG_TC:
+        return launch_diag_tc(L.bucket, L.dtype != SELINV_F64, d, S.d_items + L.off, L.count, S.spin_limit, st);
     case KL_SELINV_TINY: return launch_selinv_tiny(L.dtype, d, S.d_items + L.off, L.count, st);
     case KL_PUSH_DIAG: return launch_push(L.dtype, 0, L.bucket, d, S.d_items + L.off, L.count, st);
     case KL_PUSH: return launch_push(L.dtype, 1, L.bucket, d, S.d_items + L.off, L.count, st);

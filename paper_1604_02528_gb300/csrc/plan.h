@@ -41,6 +41,7 @@ struct PlanData {
     fill_vector<int64_t> colbase, relbase;  // per row-list position
     std::vector<int64_t> lhs_off;           // digit-plane offsets (tensor-core path)
     std::vector<int64_t> lhsu_off;          // the same in the tcgen05 operand layout
+    std::vector<int64_t> lhsuz_off;         // complex Lhat operand (2s rows, 2c k) in that layout
     std::vector<int64_t> tile_base;         // prefix sums of the 64-row tiles of each supernode
     std::vector<int64_t> linvd_off;         // digit planes of L_KK^{-1} (tensor-core path)
     // subset selection: the supernodes that run (empty: all) and the panel
@@ -50,11 +51,13 @@ struct PlanData {
     int64_t sel_version = 0;
     int64_t *d_sel_pos = nullptr;
     int nlevels = 0;
-    int64_t nnz = 0, linv_total = 0, part_max = 1, part_all = 1, lhs_total = 0, lhsu_total = 0, tile_total = 0, linvd_total = 0;
+    int64_t nnz = 0, linv_total = 0, part_max = 1, part_all = 1, lhs_total = 0, lhsu_total = 0, tile_total = 0, linvd_total = 0,
+            lhsuz_total = 0;
     // device copies
     int32_t *d_super_ptr = nullptr, *d_sparent = nullptr, *d_rows = nullptr, *d_relidx = nullptr;
     int64_t *d_rowptr = nullptr, *d_panel_off = nullptr, *d_colbase = nullptr, *d_relbase = nullptr;
-    int64_t *d_linv_off = nullptr, *d_part_off = nullptr, *d_part_off_all = nullptr, *d_lhs_off = nullptr, *d_lhsu_off = nullptr, *d_tile_base = nullptr;
+    int64_t *d_linv_off = nullptr, *d_part_off = nullptr, *d_part_off_all = nullptr, *d_lhs_off = nullptr, *d_lhsu_off = nullptr, *d_tile_base = nullptr,
+            *d_lhsuz_off = nullptr;
     int64_t *d_linvd_off = nullptr;
     int64_t *d_seg_ptr = nullptr;      // owner segments (push schedule)
     int32_t *d_seg_start = nullptr;
@@ -90,7 +93,7 @@ struct Workspace {
     uint16_t *lhsu = nullptr;  // the same in the tcgen05 operand layout (zero padding)
     int *colexp = nullptr;     // [n]
     int *colexpY = nullptr;    // [n], zero between calls
-    long long *dacc = nullptr; // [2 * linv_total], zero between calls
+    long long *dacc = nullptr; // [2 * linv_total] (complex: 4 *), zero between calls
     int *colexpZ = nullptr;    // [n], rewritten for every column in every call
     int *ticket = nullptr;     // work-item ticket of the persistent schedule
     uint16_t *linvd = nullptr; // digit planes of L_KK^{-1}

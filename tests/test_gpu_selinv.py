@@ -208,3 +208,45 @@ def test_autotuned_plan_matches_oracle(native, cuda_device):
     t = native.selinv_plan_get_opts(plan)
     assert t.fast_contraction in (0, 1, 2)
     assert t.split_target in (1, 2, 4) and t.split_min_steps in (8, 16, 32) and t.oz_min_s in (1, 8, 16, 32, 64)
+
+
+@pytest.mark.parametrize("name,make", [CASES[2], CASES[4], CASES[8],
+                                       ("dft-6x6-nb32", lambda: synth.dft_sheet(side=6, nbasis=32, seed=13)),
+                                       ("rand300-c128-relaxed", lambda: synth.random_sparse_spd(
+                                           300, 0.02, 14, complex_values=True, supernodes=synth.problems.RELAXED_128))])
+def test_complex_tensor_core_path_matches_oracle(native, cuda_device, name, make):
+    """Complex symmetric supernodes on tcgen05 (the real contraction over
+    k' = 2q + part with the 2s-row complex Lhat operand), every supernode
+    (oz_min_s 1) and the default threshold, with and without k-splits: each
+    block within 1e-10 of the oracle, the k-split bitwise irrelevant, and the
+    FP64-pipe result within the same tolerance."""
+    import torch
+    p = make()
+    sym, L, D, Z = oracle_run(p)
+    plan = native.selinv_symbolic(sym.n, sym.nsuper, sym.super_ptr, sym.sparent, sym.rowptr, sym.rows)
+    Lt = torch.from_numpy(L).cuda(); Dt = torch.from_numpy(D).cuda()
+    outs = {}
+    for fast, ozm, target, mins in ((1, 1, 1, 64), (1, 1, 8, 8), (1, 16, 2, 8), (0, 16, 2, 16)):
+        o = native.selinv_default_opts()
+        o.fast_contraction = fast
+        o.oz_min_s = ozm
+        o.split_target = target
+        o.split_min_steps = mins
+        native.selinv_plan_set_opts(plan, o)
+        Zt = torch.full_like(Lt, float("nan"))
+        native.selinv_numeric(plan, native.SELINV_C128, Lt, Dt, Zt, torch.cuda.current_stream())
+        torch.cuda.synchronize()
+        assert native.selinv_status(plan) == 0
+        G = Zt.cpu().numpy()
+        assert np.all(np.isfinite(G[oracle.lower_mask(sym)]))
+        err = oracle.block_errors(sym, G, Z)
+        assert err.max() <= TOL, (name, fast, ozm, target, float(err.max()))
+        outs[(fast, ozm, target)] = G
+    assert np.array_equal(outs[(1, 1, 1)], outs[(1, 1, 8)])
+    # the full diagonal block is written, symmetric (plain transpose)
+    G = outs[(1, 1, 1)]
+    off = sym.panel_offsets()
+    s, c = sym.sizes()
+    for K in range(0, sym.nsuper, max(1, sym.nsuper // 40)):
+        blk = G[off[K]:off[K + 1]].reshape(s[K], s[K] + c[K]).T[: s[K], :]
+        assert np.array_equal(blk, blk.T)
