@@ -625,7 +625,7 @@ int build_schedule(Schedule &S, const std::vector<const PlanData *> &plans,
             for (int cb = 0; cb < (rows + 7) / 8; cb++) S.h_red.push_back(make_int4((int)e, (int)(e - tl.off), cb, 0));
         }
         const int cnt = (int)((int64_t)S.h_red.size() - off);
-        if (cnt) S.launches.push_back({KL_TC_REDUCE, SELINV_F64, tl.bucket, off, cnt, tl.level});
+        if (cnt) S.launches.push_back({KL_TC_REDUCE, tl.dtype, tl.bucket, off, cnt, tl.level});
     };
     // after a tensor-core diagonal-block launch: its finisher, (K, 8 columns) items
     auto add_diag_fin = [&](const Launch dl, int bshift) {
