@@ -168,6 +168,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_selinv_tc(const ProbDesc *__r
         double v[4];
         int64_t ab[4], cb[4], rb[4];
         int32_t ar[4];
+        bool up[4];
         auto cols = [&](int i_) {
 #pragma unroll
             for (int u = 0; u < 4; u++) {
@@ -178,7 +179,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_selinv_tc(const ProbDesc *__r
         auto parts = [&](int i_) {
 #pragma unroll
             for (int u = 0; u < 4; u++) {
-                if (i_ < n) g.parts(r, (st0 + i_) * 16 + kq * 4 + u, cb[u], rb[u], ab[u], ar[u]);
+                if (i_ < n) g.parts(r, (st0 + i_) * 16 + kq * 4 + u, cb[u], rb[u], ab[u], ar[u], up[u]);
                 else { ab[u] = -1; ar[u] = 0; }
             }
         };
@@ -542,6 +543,9 @@ __global__ void __launch_bounds__(kDtThreads, 1) k_diag_tc(const ProbDesc *__res
         const bool colok = act && n0 + r < s;
         const int E = colok ? colE[r] : 0;
         double v[4];
+        // Hermitian: Lhat^H Y = conj(Lhat^T conj(Y)), so the digits are those
+        // of conj(Y) and the finisher conjugates the sums
+        const bool cj = CPLX && P.herm;
         auto fetch = [&](int step) {
             if (CPLX) {
                 const double2 *Yz = static_cast<const double2 *>(P.Z) + ycol;
@@ -550,7 +554,7 @@ __global__ void __launch_bounds__(kDtThreads, 1) k_diag_tc(const ProbDesc *__res
                     const int q = step * 8 + kq * 2 + u;
                     const double2 y = (colok && step < st1 && q < c) ? Yz[q] : make_double2(0.0, 0.0);
                     v[2 * u] = y.x;
-                    v[2 * u + 1] = y.y;
+                    v[2 * u + 1] = cj ? -y.y : y.y;
                 }
             } else {
                 const double *Yc = static_cast<const double *>(P.Z) + ycol;

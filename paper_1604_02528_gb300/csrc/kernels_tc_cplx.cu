@@ -80,7 +80,9 @@ __global__ void __launch_bounds__(256) k_lhat_digits_z(const ProbDesc *__restric
 
 // ---------------------------------------------------------------------------
 // k_diag_fin_z: A^{-1}_KK = Dinv_K - Lhat^T A^{-1}_{C,K} (complex) from the
-// exact sums of k_diag_tc, symmetrized with the plain transpose (Sec. II-C).
+// exact sums of k_diag_tc, symmetrized with the plain transpose (Sec. II-C);
+// Hermitian: Dinv_K - Lhat^H A^{-1}_{C,K} (the sums are those of
+// Lhat^T conj(A^{-1}_{C,K}), conjugated here), symmetrized as (X + X^H) / 2.
 // Same structure as k_diag_fin: one CTA per 8 columns j, a warp per column,
 // lanes over rows i; entry (i, j) and its mirror come from the same sums in
 // the same order, so the block is exactly symmetric.  The sums hold
@@ -102,12 +104,14 @@ __global__ void __launch_bounds__(256) k_diag_fin_z(const ProbDesc *__restrict__
     const double2 *LDk = static_cast<const double2 *>(P.LD) + P.panel_off[K];
     double2 *Zk = static_cast<double2 *>(P.Z) + P.panel_off[K];
     const long long *acc64 = P.dacc + 4 * P.linv_off[K];
-    auto prod = [&](int a, int b) -> double2 {   // (Lhat^T Y)(a, b)
+    const bool herm = P.herm;
+    auto prod = [&](int a, int b) -> double2 {   // (Lhat^T Y)(a, b), Hermitian: (Lhat^H Y)(a, b)
         const long long *q = acc64 + 4 * ((int64_t)b * s + a);
         const int ey = P.colexpY[fc + b];
         if (ey == 0) return make_double2(0.0, 0.0);
         const int sc = (P.colexp[fc + a] - 1022) + (ey - 1022) - 14 + 1;
-        return make_double2(fixed_to_double(q[0], q[1], sc), fixed_to_double(q[2], q[3], sc));
+        const double im = fixed_to_double(q[2], q[3], sc);
+        return make_double2(fixed_to_double(q[0], q[1], sc), herm ? -im : im);
     };
     int mj = 0;
     for (int i = lane; i < s; i += 32) {
@@ -115,7 +119,8 @@ __global__ void __launch_bounds__(256) k_diag_fin_z(const ProbDesc *__restrict__
         double2 x = make_double2(d1.x - p1.x, d1.y - p1.y);
         if (P.symmetrize) {
             const double2 d2 = LDk[(int64_t)i * ld + j], p2 = prod(j, i);
-            x = make_double2(0.5 * (x.x + (d2.x - p2.x)), 0.5 * (x.y + (d2.y - p2.y)));
+            const double2 y = make_double2(d2.x - p2.x, herm ? -(d2.y - p2.y) : d2.y - p2.y);
+            x = make_double2(0.5 * (x.x + y.x), 0.5 * (x.y + y.y));
         }
         Zk[(int64_t)j * ld + i] = x;
         mj = max(mj, max(bexp(x.x), bexp(x.y)));

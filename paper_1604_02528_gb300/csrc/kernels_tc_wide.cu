@@ -249,6 +249,9 @@ __global__ void __launch_bounds__(kTwThreads, 1) k_selinv_tcw(const ProbDesc *__
         double v[4];
         int64_t ab[NV], cb[NV], rb[NV];
         int32_t ar[NV];
+        bool up[NV];
+        // Hermitian: an entry above the diagonal is the conjugate of the stored one
+        const bool herm = CPLX && P.herm;
         auto load = [&]() {
             if (CPLX) {
                 const double2 *Zc = static_cast<const double2 *>(P.Z);
@@ -256,7 +259,7 @@ __global__ void __launch_bounds__(kTwThreads, 1) k_selinv_tcw(const ProbDesc *__
                 for (int u = 0; u < NV; u++) {
                     const double2 z = ab[u] >= 0 ? Zc[ab[u] + ar[u]] : make_double2(0.0, 0.0);
                     v[2 * u] = z.x;
-                    v[2 * u + 1] = z.y;
+                    v[2 * u + 1] = herm && up[u] ? -z.y : z.y;
                 }
             } else {
                 const double *Zg = static_cast<const double *>(P.Z);
@@ -275,7 +278,7 @@ __global__ void __launch_bounds__(kTwThreads, 1) k_selinv_tcw(const ProbDesc *__
         auto parts = [&](int i_) {
 #pragma unroll
             for (int u = 0; u < NV; u++) {
-                if (i_ < n) g.parts(r, (st0 + i_) * QS + kq * NV + u, cb[u], rb[u], ab[u], ar[u]);
+                if (i_ < n) g.parts(r, (st0 + i_) * QS + kq * NV + u, cb[u], rb[u], ab[u], ar[u], up[u]);
                 else { ab[u] = -1; ar[u] = 0; }
             }
         };

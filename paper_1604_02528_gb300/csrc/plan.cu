@@ -479,12 +479,12 @@ int build_schedule(Schedule &S, const std::vector<const PlanData *> &plans,
     auto act = [&](int i, int32_t K) { return plans[i]->active.empty() || plans[i]->active[K] != 0; };
     // tensor-core contraction for this problem and width (never for the LU form)
     auto ozok = [&](int i, int s) { return !descs[i].lu && oz_eligible(descs[i].dtype, s, plans[i]->opts); };
-    // complex symmetric supernodes on tcgen05 (the transposed gather-GEMM and
-    // the diagonal block over the real 2c-long contraction; level and plain
-    // schedules, not the Hermitian or LU forms; their Lhat stays on the FP64 pipe)
+    // complex supernodes (symmetric or Hermitian) on tcgen05 (the transposed
+    // gather-GEMM and the diagonal block over the real 2c-long contraction;
+    // level and plain schedules, not the LU form; their Lhat stays on the FP64 pipe)
     auto zok = [&](int i, int s) {
         const selinv_opts &o = plans[i]->opts;
-        return !descs[i].lu && !descs[i].herm && descs[i].dtype == SELINV_C128 && o.fast_contraction == 1 &&
+        return !descs[i].lu && descs[i].dtype == SELINV_C128 && o.fast_contraction == 1 &&
                s >= std::max(kOzMinS, o.oz_min_s) && (mode == SELINV_SCHED_LEVEL || mode == SELINV_SCHED_PLAIN);
     };
     // DFMA supernodes small enough for a warp each (k_selinv_tiny; not the LU form)

@@ -86,6 +86,8 @@ __device__ __forceinline__ void store_plane4(uint16_t *dst, const uint32_t (&lo)
 // address of column C[q] in its owner and the start of its relative rows),
 // then the base and the relative row (a load), then the value; base -1
 // outside C x C.  pl = p - p0; the tile's own rows come from shared memory.
+// parts() also reports whether (p, q) lies above the diagonal (stored as its
+// mirror: a Hermitian matrix stores the conjugate there).
 struct TcGather {
     const int64_t *pcb, *prb;
     const int32_t *relidx;
@@ -100,8 +102,10 @@ struct TcGather {
             rb = 0;
         }
     }
-    __device__ __forceinline__ void parts(int pl, int q, int64_t cb, int64_t rb, int64_t &base, int32_t &rel) const {
+    __device__ __forceinline__ void parts(int pl, int q, int64_t cb, int64_t rb, int64_t &base, int32_t &rel,
+                                          bool &upper) const {
         const int p = p0 + pl;
+        upper = p < q;
         if (p >= c || q >= c) {
             base = -1;
             rel = 0;

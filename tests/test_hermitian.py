@@ -157,3 +157,33 @@ def test_gpu_hermitian_factor_and_end_to_end(native, cuda_device, name, make):
     Ainv = np.linalg.inv(p.dense())
     m = pattern_mask(sym)
     assert np.abs((G - Ainv)[m]).max() <= TOL * np.abs(Ainv).max()
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("name,make", HERM_CASES)
+def test_gpu_hermitian_tensor_core_path(native, cuda_device, name, make):
+    """Hermitian supernodes on tcgen05 (entries above the diagonal of
+    A^{-1}_{C,C} conjugated in the gather, Lhat^H in the diagonal block),
+    every supernode (oz_min_s 1), with and without k-splits: within 1e-10 of
+    the oracle, the k-split bitwise irrelevant, and the diagonal blocks
+    exactly Hermitian with a real diagonal."""
+    p = make()
+    sym = oracle.symbolic_for(p)
+    L, D = oracle.ldlt(p, sym)
+    Z = oracle.selinv(sym, L, D, hermitian=True)
+    plan = native.selinv_symbolic(sym.n, sym.nsuper, sym.super_ptr, sym.sparent, sym.rowptr, sym.rows)
+    outs = []
+    for target, mins in ((1, 64), (8, 8)):
+        G, st = run(native, plan, L, D, native.SELINV_C128H, fast_contraction=1, oz_min_s=1,
+                    split_target=target, split_min_steps=mins)
+        assert st == 0
+        assert oracle.block_errors(sym, G, Z).max() <= TOL, (name, target)
+        outs.append(G)
+    assert np.array_equal(outs[0], outs[1])
+    G = outs[0]
+    off = sym.panel_offsets()
+    s, c = sym.sizes()
+    for K in range(0, sym.nsuper, max(1, sym.nsuper // 40)):
+        blk = G[off[K]:off[K + 1]].reshape(s[K], s[K] + c[K]).T[: s[K], :]
+        assert np.array_equal(blk, blk.conj().T)
+        assert np.all(blk.diagonal().imag == 0)
