@@ -18,8 +18,10 @@
 //   and their exact sum is added into a 96-bit word per entry in shared
 //   memory (an int64 high part and a 32-bit low part, carried after every
 //   chunk).
-// Operand rings: 3 stages for the Lhat^T copies (issued two steps ahead,
-// to cover their latency), 3 for the gathered digits.
+// Operand rings: 3 stages for the Lhat^T copies, 3 for the gathered digits.
+// The copies are issued by a thread of their own, so that the thread issuing
+// the products never waits for products to finish: it waits only for its
+// operands, and the tensor cores always have the next step queued.
 // The same digit scheme and exponent grids as k_selinv_tc; the chunk
 // boundaries sit at fixed multiples of 128 k, so the result does not depend
 // on the k-split.
@@ -45,8 +47,9 @@ namespace selinv {
 constexpr int kTwN = 64;           // rows of C per item: N of one digit plane
 constexpr int kTwProd = 8;         // producer warps: 64 rows x 4 quarters of a 16-k step, 4 values per thread
 constexpr int kTwEpi = 8;          // epilogue warps: two per tensor-memory lane quarter (32 rows of C each)
-constexpr int kTwMmaWarp = kTwProd + kTwEpi;
-constexpr int kTwThreads = 32 * (kTwProd + kTwEpi + 1);
+constexpr int kTwMmaWarp = kTwProd + kTwEpi;   // one thread issues the products
+constexpr int kTwCopyWarp = kTwMmaWarp + 1;     // one thread issues the Lhat^T copies
+constexpr int kTwThreads = 32 * (kTwProd + kTwEpi + 2);
 constexpr int kTwHS = kTcM + 1;    // words per row of C in the int64 sums [p][m]: conflict-free both ways
 constexpr int kTwAS = 3;           // stages of the Lhat^T ring
 constexpr int kTwBS = 3;           // stages of the gathered-digit ring
@@ -181,12 +184,13 @@ __global__ void __launch_bounds__(kTwThreads, 1) k_selinv_tcw(const ProbDesc *__
                     *reinterpret_cast<uint4 *>(As + st * Cfg::A_STAGE + pl * Cfg::A_PLANE + e) = make_uint4(0, 0, 0, 0);
     umma::fence_proxy_async();   // zeroed A rows are seen by the tensor cores
     __syncthreads();
-    // the first copies go out before the rest of the set-up; the blocks of
-    // the steps after them are asked into L2 (the CTAs of one supernode run
-    // in step, so each block would otherwise come from DRAM for all of them)
-    if (warp == kTwMmaWarp && lane == 0) {
-        for (int i_ = 0; i_ < kTwAS - 1 && i_ < n; i_++) load_a(i_);
-        for (int i_ = kTwAS - 1; i_ < kTwPrefetch && i_ < n; i_++)
+    // the first copies (one per stage) go out before the rest of the set-up;
+    // the blocks of the steps after them are asked into L2 (the CTAs of one
+    // supernode run in step, so each block would otherwise come from DRAM for
+    // all of them)
+    if (warp == kTwCopyWarp && lane == 0) {
+        for (int i_ = 0; i_ < kTwAS && i_ < n; i_++) load_a(i_);
+        for (int i_ = kTwAS; i_ < kTwPrefetch && i_ < n; i_++)
             umma::bulk_prefetch_l2(Au + (int64_t)(st0 + i_) * kTcDig * s64 * 16, kTcDig * aBytes);
     }
     // row exponents of the gathered block: row p is bounded by the largest
@@ -323,8 +327,9 @@ __global__ void __launch_bounds__(kTwThreads, 1) k_selinv_tcw(const ProbDesc *__
             if (s_abort) break;
         }
     } else if (warp == kTwMmaWarp) {
-        // ---- one thread copies the Lhat^T digit planes (the first ones went
-        // out during the set-up) and issues the products
+        // ---- one thread issues the products once both operands of a step
+        // have landed (and, at the start of a chunk, the epilogue has read the
+        // group sums of the previous one)
         if (lane == 0) {
             for (int i_ = 0; i_ < n; i_++) {
                 const int sa = i_ % kTwAS, sb = i_ % kTwBS, ch = i_ / kTcFlush;
@@ -342,18 +347,24 @@ __global__ void __launch_bounds__(kTwThreads, 1) k_selinv_tcw(const ProbDesc *__
                 umma::commit(&aempty[sa]);
                 umma::commit(&bempty[sb]);
                 if (i_ % kTcFlush == kTcFlush - 1 || i_ == n - 1) umma::commit(&acc_full);
-                // A of step i + 3 into the stage of step i - 1 once the
-                // products of step i - 1 have finished reading it
-                const int nx = i_ + kTwAS - 1;
-                if (i_ + kTwPrefetch < n)
-                    umma::bulk_prefetch_l2(Au + (int64_t)(st0 + i_ + kTwPrefetch) * kTcDig * s64 * 16, kTcDig * aBytes);
-                if (nx < n) {
-                    if (i_ >= 1 && !umma::mbar_wait(&aempty[(i_ - 1) % kTwAS], (uint32_t)(((i_ - 1) / kTwAS) & 1), mlim)) {
-                        s_abort = 1;
-                        break;
-                    }
-                    load_a(nx);
+                if (s_abort) break;
+            }
+        }
+        __syncwarp();
+    } else if (warp == kTwCopyWarp) {
+        // ---- one thread copies the Lhat^T digit planes of step i into the
+        // stage of step i - 3 once the products of that step are done (the
+        // first three went out during the set-up)
+        if (lane == 0) {
+            for (int i_ = kTwAS; i_ < n; i_++) {
+                if (!umma::mbar_wait(&aempty[i_ % kTwAS], (uint32_t)((i_ / kTwAS - 1) & 1), mlim)) {
+                    s_abort = 1;
+                    break;
                 }
+                load_a(i_);
+                if (i_ + kTwPrefetch - kTwAS < n)
+                    umma::bulk_prefetch_l2(Au + (int64_t)(st0 + i_ + kTwPrefetch - kTwAS) * kTcDig * s64 * 16,
+                                           kTcDig * aBytes);
                 if (s_abort) break;
             }
         }
@@ -398,10 +409,10 @@ __global__ void __launch_bounds__(kTwThreads, 1) k_selinv_tcw(const ProbDesc *__
         if (warp == kTwMmaWarp && lane == 0) {
             umma::commit(&drain);
             umma::mbar_wait(&drain, 0u, mlim);
-            // copies issued after the last step that waited for its own
-            for (int j = a_issued - (kTwAS - 2) > 0 ? a_issued - (kTwAS - 2) : 0; j <= a_issued; j++)
-                umma::mbar_wait(&afull[j % kTwAS], (uint32_t)((j / kTwAS) & 1), mlim);
         }
+        if (warp == kTwCopyWarp && lane == 0)   // the copies that may still be in flight
+            for (int j = a_issued - (kTwAS - 1) > 0 ? a_issued - (kTwAS - 1) : 0; j <= a_issued; j++)
+                umma::mbar_wait(&afull[j % kTwAS], (uint32_t)((j / kTwAS) & 1), mlim);
         umma::fence_before_sync();
         __syncthreads();
         umma::fence_after_sync();
