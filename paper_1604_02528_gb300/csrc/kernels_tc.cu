@@ -32,8 +32,9 @@ namespace selinv {
 
 constexpr int kTcProd = 16;        // producer warps: gather + digits of A (4 values per thread and step)
 constexpr int kTcEpi = 8;          // epilogue warps: two per tensor-memory lane quarter (half the columns each)
-constexpr int kTcMmaWarp = kTcProd + kTcEpi;
-constexpr int kTcThreads = 32 * (kTcProd + kTcEpi + 1);
+constexpr int kTcMmaWarp = kTcProd + kTcEpi;   // one thread issues the products
+constexpr int kTcCopyWarp = kTcMmaWarp + 1;     // one thread issues the Lhat digit copies
+constexpr int kTcThreads = 32 * (kTcProd + kTcEpi + 2);
 // slab slot of a split-k item: (hi, lo) words [64 columns][128 rows] each, then the rows' exponents
 constexpr int64_t kTcSlot = kTcSlotWords;
 static_assert(kTcSlotWords == 2 * kTcM * 64 + kTcM / 2, "slot layout");
@@ -152,7 +153,21 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_selinv_tc(const ProbDesc *__r
     }
     __syncthreads();
     const uint32_t tmem = s_tmem;
-    int b_issued = -1;   // last step whose B copies the MMA thread issued
+    int b_issued = -1;   // last step whose B copies the copy thread issued
+    // copies of the Lhat digit planes of step i_ (bulk, tcgen05 layout: one
+    // contiguous block per plane and step) into stage i_ % 2
+    const int64_t s64 = (s + 63) / 64 * 64;
+    const uint16_t *Bu = P.lhsu + P.lhsu_off[K] + (int64_t)(n0 / 8) * 128;
+    constexpr uint32_t kBBytes = TN * 16 * 2;
+    auto load_b = [&](int i_) {
+        const int st = i_ & 1;
+        umma::mbar_arrive_expect_tx(&bfull[st], kTcDig * kBBytes);
+#pragma unroll
+        for (int pl = 0; pl < kTcDig; pl++)
+            umma::bulk_g2s(Bs + st * Cfg::B_STAGE + pl * Cfg::B_PLANE,
+                           Bu + ((int64_t)(st0 + i_) * kTcDig + pl) * s64 * 16, kBBytes, &bfull[st]);
+        b_issued = i_;
+    };
 
     if (warp < kTcProd) {
         // ---- producers: A digits.  Thread (row r, quarter kq) slices the
@@ -228,22 +243,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_selinv_tc(const ProbDesc *__r
             if (s_abort) break;
         }
     } else if (warp == kTcMmaWarp) {
-        // ---- one thread copies the Lhat digit planes (bulk, tcgen05 layout:
-        // one contiguous block per plane and step) and issues the products
+        // ---- one thread issues the products once both operands of a step
+        // are in place (and, at the start of a chunk, the epilogue has read
+        // the previous one's group sums); it never waits for products
         if (lane == 0) {
-            const int64_t s64 = (s + 63) / 64 * 64;
-            const uint16_t *Bu = P.lhsu + P.lhsu_off[K] + (int64_t)(n0 / 8) * 128;
-            constexpr uint32_t kBBytes = TN * 16 * 2;
-            auto load_b = [&](int i_) {
-                const int st = i_ & 1;
-                umma::mbar_arrive_expect_tx(&bfull[st], kTcDig * kBBytes);
-#pragma unroll
-                for (int pl = 0; pl < kTcDig; pl++)
-                    umma::bulk_g2s(Bs + st * Cfg::B_STAGE + pl * Cfg::B_PLANE,
-                                   Bu + ((int64_t)(st0 + i_) * kTcDig + pl) * s64 * 16, kBBytes, &bfull[st]);
-                b_issued = i_;
-            };
-            if (n > 0) load_b(0);
             for (int i_ = 0; i_ < n; i_++) {
                 const int stage = i_ & 1, use = i_ >> 1, ch = i_ / kTcFlush;
                 const bool first = i_ % kTcFlush == 0;
@@ -260,15 +263,20 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_selinv_tc(const ProbDesc *__r
                 digit_products<TN, Cfg::A_PLANE, Cfg::B_PLANE>(tmem, ad0, bd0, first);
                 umma::commit(&empty[stage]);
                 if (i_ % kTcFlush == kTcFlush - 1 || i_ == n - 1) umma::commit(&acc_full);
-                // B of the next step into the other stage once the products of
-                // the step before this one have finished reading it
-                if (i_ + 1 < n) {
-                    if (i_ >= 1 && !umma::mbar_wait(&empty[(i_ + 1) & 1], (uint32_t)((((i_ + 1) >> 1) - 1) & 1), mlim)) {
-                        s_abort = 1;
-                        break;
-                    }
-                    load_b(i_ + 1);
+                if (s_abort) break;
+            }
+        }
+        __syncwarp();
+    } else if (warp == kTcCopyWarp) {
+        // ---- one thread copies the Lhat digit planes of step i into the
+        // stage of step i - 2 once the products of that step are done
+        if (lane == 0) {
+            for (int i_ = 0; i_ < n; i_++) {
+                if (i_ >= 2 && !umma::mbar_wait(&empty[i_ & 1], (uint32_t)(((i_ >> 1) - 1) & 1), mlim)) {
+                    s_abort = 1;
+                    break;
                 }
+                load_b(i_);
                 if (s_abort) break;
             }
         }
@@ -322,8 +330,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_selinv_tc(const ProbDesc *__r
         if (warp == kTcMmaWarp && lane == 0) {
             umma::commit(&drain);
             umma::mbar_wait(&drain, 0u, mlim);
-            if (b_issued >= 0) umma::mbar_wait(&bfull[b_issued & 1], (uint32_t)((b_issued >> 1) & 1), mlim);
         }
+        if (warp == kTcCopyWarp && lane == 0)   // the copies that may still be in flight
+            for (int j = b_issued - 1 > 0 ? b_issued - 1 : 0; j <= b_issued; j++)
+                umma::mbar_wait(&bfull[j & 1], (uint32_t)((j >> 1) & 1), mlim);
         umma::fence_before_sync();
         __syncthreads();
         umma::fence_after_sync();
@@ -439,8 +449,9 @@ cudaError_t launch_tc_reduce(int tn, const ProbDesc *d, const Item *items, const
 // ---------------------------------------------------------------------------
 constexpr int kDtProd = 8;                       // producer warps (digit planes of Y, 4 values per thread and step)
 constexpr int kDtEpi = 8;                        // epilogue warps (tensor memory -> int64), two per lane quarter
-constexpr int kDtMmaWarp = kDtProd + kDtEpi;
-constexpr int kDtThreads = 32 * (kDtProd + kDtEpi + 1);
+constexpr int kDtMmaWarp = kDtProd + kDtEpi;     // one thread issues the products
+constexpr int kDtCopyWarp = kDtMmaWarp + 1;       // one thread issues the Lhat digit copies
+constexpr int kDtThreads = 32 * (kDtProd + kDtEpi + 2);
 
 template <int TN> struct DtCfg {
     static constexpr int A_PLANE = kTcM * 16;
@@ -529,7 +540,7 @@ __global__ void __launch_bounds__(kDtThreads, 1) k_diag_tc(const ProbDesc *__res
     __syncthreads();
     umma::fence_after_sync();
     const uint32_t tmem = s_tmem;
-    int a_issued = -1;   // last step whose A copies the MMA thread issued
+    int a_issued = -1;   // last step whose A copies the copy thread issued
 
     if (warp < kDtProd) {
         // ---- producers: thread (column r, quarter kq) slices rows 4 kq .. 4 kq + 3
@@ -597,20 +608,8 @@ __global__ void __launch_bounds__(kDtThreads, 1) k_diag_tc(const ProbDesc *__res
             if (s_abort) break;
         }
     } else if (warp == kDtMmaWarp) {
-        // ---- one thread copies the Lhat digit planes and issues the products
+        // ---- one thread issues the products once both operands are in place
         if (lane == 0) {
-            const uint16_t *Au = P.lhsu + P.lhsu_off[K] + (int64_t)(m0 / 8) * 128;
-            const uint32_t aBytes = (uint32_t)(arows * 16 * 2);
-            auto load_a = [&](int i_) {
-                const int st = i_ & 1;
-                umma::mbar_arrive_expect_tx(&afull[st], kTcDig * aBytes);
-#pragma unroll
-                for (int pl = 0; pl < kTcDig; pl++)
-                    umma::bulk_g2s(As + st * Cfg::A_STAGE + pl * Cfg::A_PLANE,
-                                   Au + ((int64_t)(st0 + i_) * kTcDig + pl) * s64 * 16, aBytes, &afull[st]);
-                a_issued = i_;
-            };
-            if (n > 0) load_a(0);
             for (int i_ = 0; i_ < n; i_++) {
                 const int stage = i_ & 1, use = i_ >> 1, chk = i_ / kTcFlush;
                 const bool first = i_ % kTcFlush == 0;
@@ -626,13 +625,28 @@ __global__ void __launch_bounds__(kDtThreads, 1) k_diag_tc(const ProbDesc *__res
                 digit_products<TN, Cfg::A_PLANE, Cfg::B_PLANE>(tmem, ad0, bd0, first);
                 umma::commit(&empty[stage]);
                 if (i_ % kTcFlush == kTcFlush - 1 || i_ == n - 1) umma::commit(&acc_full);
-                if (i_ + 1 < n) {
-                    if (i_ >= 1 && !umma::mbar_wait(&empty[(i_ + 1) & 1], (uint32_t)((((i_ + 1) >> 1) - 1) & 1), mlim)) {
-                        s_abort = 1;
-                        break;
-                    }
-                    load_a(i_ + 1);
+                if (s_abort) break;
+            }
+        }
+        __syncwarp();
+    } else if (warp == kDtCopyWarp) {
+        // ---- one thread copies the Lhat digit planes of step i into the
+        // stage of step i - 2 once the products of that step are done
+        if (lane == 0) {
+            const uint16_t *Au = P.lhsu + P.lhsu_off[K] + (int64_t)(m0 / 8) * 128;
+            const uint32_t aBytes = (uint32_t)(arows * 16 * 2);
+            for (int i_ = 0; i_ < n; i_++) {
+                if (i_ >= 2 && !umma::mbar_wait(&empty[i_ & 1], (uint32_t)(((i_ >> 1) - 1) & 1), mlim)) {
+                    s_abort = 1;
+                    break;
                 }
+                const int st = i_ & 1;
+                umma::mbar_arrive_expect_tx(&afull[st], kTcDig * aBytes);
+#pragma unroll
+                for (int pl = 0; pl < kTcDig; pl++)
+                    umma::bulk_g2s(As + st * Cfg::A_STAGE + pl * Cfg::A_PLANE,
+                                   Au + ((int64_t)(st0 + i_) * kTcDig + pl) * s64 * 16, aBytes, &afull[st]);
+                a_issued = i_;
                 if (s_abort) break;
             }
         }
@@ -684,8 +698,10 @@ __global__ void __launch_bounds__(kDtThreads, 1) k_diag_tc(const ProbDesc *__res
         if (warp == kDtMmaWarp && lane == 0) {
             umma::commit(&drain);
             umma::mbar_wait(&drain, 0u, mlim);
-            if (a_issued >= 0) umma::mbar_wait(&afull[a_issued & 1], (uint32_t)((a_issued >> 1) & 1), mlim);
         }
+        if (warp == kDtCopyWarp && lane == 0)   // the copies that may still be in flight
+            for (int j = a_issued - 1 > 0 ? a_issued - 1 : 0; j <= a_issued; j++)
+                umma::mbar_wait(&afull[j & 1], (uint32_t)((j >> 1) & 1), mlim);
         umma::fence_before_sync();
         __syncthreads();
         umma::fence_after_sync();

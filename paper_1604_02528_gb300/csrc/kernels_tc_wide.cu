@@ -71,11 +71,17 @@ static_assert(TwCfg::SMEM + 2048 <= 232448, "dynamic + static shared memory with
 // entry's 96-bit sum hi 2^32 + lo (0 <= lo < 2^32): the chunk's value is
 // h 2^32 + l with h = g0 2^16 + g1 2^8 + g2 and l = g3 2^24 + g4 2^16 +
 // g5 2^8 + g6 (|l| < 2^48), and what lo cannot hold is carried into hi.
+// Groups 0 and 1 (one and two digit pairs: |g| <= 2^22) are converted by the
+// exact magic-number addition on the FP32 pipe, the others by F2I, whose
+// unit is the epilogue's bottleneck.
 __device__ __forceinline__ void add_chunk(const uint32_t (&acc)[kTcDig][8], int jj, bool first, long long &hi,
                                           uint32_t &lo) {
     long long gv[kTcDig];
 #pragma unroll
-    for (int gq = 0; gq < kTcDig; gq++) gv[gq] = (long long)__float2int_rn(__uint_as_float(acc[gq][jj]));
+    for (int gq = 0; gq < 2; gq++)
+        gv[gq] = (long long)(__float_as_int(__fadd_rn(__uint_as_float(acc[gq][jj]), 12582912.0f)) - 0x4B400000);
+#pragma unroll
+    for (int gq = 2; gq < kTcDig; gq++) gv[gq] = (long long)__float2int_rn(__uint_as_float(acc[gq][jj]));
     const long long h = (gv[0] << 16) + (gv[1] << 8) + gv[2];
     const long long l = (gv[3] << 24) + (gv[4] << 16) + (gv[5] << 8) + gv[6];
     const long long t = (first ? 0ll : (long long)lo) + l;
