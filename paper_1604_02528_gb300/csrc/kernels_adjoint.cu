@@ -32,6 +32,7 @@
 
 #include "common.cuh"
 #include "launch.h"
+#include "nvtx.h"
 #include "plan.h"
 #include "tile_gemm.cuh"
 #include "seg_update.cuh"
@@ -1152,6 +1153,7 @@ using namespace selinv;
 
 extern "C" int selinv_adjoint(selinv_plan plan, selinv_dtype dtype, const void *L, const void *D,
                               const void *Z, const void *Zbar, void *Lbar, void *Dbar, void *stream) {
+    NvtxRange nvtx_range("selinv_adjoint");
     if (!plan) return SELINV_ERR_INVALID_ARG;
     if (dtype != SELINV_F64) return SELINV_ERR_UNSUPPORTED;
     if (plan->data.ns == 0) return SELINV_OK;
@@ -1238,6 +1240,7 @@ extern "C" int selinv_adjoint(selinv_plan plan, selinv_dtype dtype, const void *
 
 extern "C" int selinv_factor_adjoint(selinv_plan plan, selinv_dtype dtype, const void *L, const void *D,
                                      const void *Lbar, const void *Dbar, void *Abar_vals, void *stream) {
+    NvtxRange nvtx_range("selinv_factor_adjoint");
     if (!plan || !plan->factor) return SELINV_ERR_INVALID_ARG;
     if (dtype != SELINV_F64) return SELINV_ERR_UNSUPPORTED;
     if (plan->data.ns == 0) return SELINV_OK;

@@ -19,6 +19,7 @@
 
 #include "common.cuh"
 #include "launch.h"
+#include "nvtx.h"
 #include "plan.h"
 #include "seg_update.cuh"
 
@@ -360,6 +361,7 @@ extern "C" int selinv_plan_set_matrix(selinv_plan plan, int32_t n, const int64_t
 
 extern "C" int selinv_factor(selinv_plan plan, selinv_dtype dtype, const void *A, void *L, void *D,
                              void *stream) {
+    NvtxRange nvtx_range("selinv_factor");
     if (!plan || !plan->factor || (dtype != SELINV_F64 && dtype != SELINV_C128 && dtype != SELINV_C128H))
         return SELINV_ERR_INVALID_ARG;
     if (plan->data.ns == 0) return SELINV_OK;

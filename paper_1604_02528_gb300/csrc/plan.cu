@@ -16,6 +16,7 @@
 
 #include "common.cuh"
 #include "launch.h"
+#include "nvtx.h"
 #include "plan.h"
 
 namespace selinv {
@@ -1115,11 +1116,21 @@ static cudaError_t issue_pre(const Schedule &S, cudaStream_t st) {
     return cudaSuccess;
 }
 
+const char *launch_kind_name(int kind) {
+    static const char *names[KL_NKINDS] = {"linv", "lhat", "selinv", "lhat_digits", "selinv_oz", "diag",
+                                           "linv_digits", "lhat_oz", "persist", "selinv_tc", "tc_reduce",
+                                           "diag_fin", "push_diag", "push", "dinv", "diag_tc", "selinv_tiny"};
+    return kind >= 0 && kind < KL_NKINDS ? names[kind] : "?";
+}
+
 static cudaError_t issue(const Schedule &S, cudaStream_t st, bool count) {
     if (count) note_launch((int)S.launches.size());
     cudaError_t e0 = issue_pre(S, st);
     if (e0 != cudaSuccess) return e0;
     for (const Launch &L : S.launches) {
+        char name[48];
+        std::snprintf(name, sizeof(name), "L%d %s", L.level, launch_kind_name(L.kind));
+        NvtxRange r(name);
         cudaError_t e = launch_one(S, L, st);
         if (e != cudaSuccess) return e;
     }
@@ -1182,6 +1193,7 @@ extern "C" void selinv_default_opts(selinv_opts *o) {
 extern "C" int selinv_symbolic(int32_t n, int32_t nsuper, const int32_t *super_ptr,
                                const int32_t *sparent, const int64_t *rowptr, const int32_t *rowind,
                                const selinv_opts *opts, selinv_plan *out_plan) {
+    NvtxRange nvtx_range("selinv_symbolic");
     if (!out_plan) return SELINV_ERR_INVALID_ARG;
     *out_plan = nullptr;
     if (n < 0 || nsuper < 0 || (nsuper == 0) != (n == 0) || !super_ptr || !rowptr ||
@@ -1372,6 +1384,7 @@ static int autotune(selinv_plan plan, selinv_dtype dtype, const void *L, const v
 
 extern "C" int selinv_numeric(selinv_plan plan, selinv_dtype dtype, const void *L, const void *D,
                               void *Z, void *stream) {
+    NvtxRange nvtx_range("selinv_numeric");
     if (!plan || (dtype != SELINV_F64 && dtype != SELINV_C128 && dtype != SELINV_C128H)) return SELINV_ERR_INVALID_ARG;
     PlanData &p = plan->data;
     if (p.ns == 0) return SELINV_OK;
@@ -1428,6 +1441,7 @@ static int numeric_run(selinv_plan plan, selinv_dtype dtype, const void *L, cons
 // LU fields set; level schedule unless the plan asks for the plain one.
 extern "C" int selinv_numeric_lu(selinv_plan plan, selinv_dtype dtype, const void *L, const void *Ut, void *Zl,
                                  void *Zu, void *stream) {
+    NvtxRange nvtx_range("selinv_numeric_lu");
     if (!plan || (dtype != SELINV_F64 && dtype != SELINV_C128)) return SELINV_ERR_INVALID_ARG;
     PlanData &p = plan->data;
     if (p.ns == 0) return SELINV_OK;
@@ -1465,6 +1479,7 @@ extern "C" int selinv_numeric_lu(selinv_plan plan, selinv_dtype dtype, const voi
 extern "C" int selinv_numeric_profile(selinv_plan plan, selinv_dtype dtype, const void *L,
                                       const void *D, void *Z, void *stream, double *kernel_ms,
                                       int64_t *kernel_launches) {
+    NvtxRange nvtx_range("selinv_numeric_profile");
     if (!kernel_ms || !kernel_launches) return SELINV_ERR_INVALID_ARG;
     // build (or reuse) the schedule through the normal path, without a graph
     if (!plan) return SELINV_ERR_INVALID_ARG;
@@ -1503,6 +1518,7 @@ extern "C" int selinv_numeric_profile(selinv_plan plan, selinv_dtype dtype, cons
 extern "C" int selinv_numeric_batched(int nitems, const selinv_plan *plans, const selinv_dtype *dtypes,
                                       const void *const *L, const void *const *D, void *const *Z,
                                       void *stream) {
+    NvtxRange nvtx_range("selinv_numeric_batched");
     if (nitems <= 0 || !plans || !dtypes || !L || !D || !Z) return SELINV_ERR_INVALID_ARG;
     selinv_plan owner = plans[0];
     if (!owner) return SELINV_ERR_INVALID_ARG;

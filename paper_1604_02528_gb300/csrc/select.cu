@@ -19,6 +19,7 @@
 
 #include "common.cuh"
 #include "launch.h"
+#include "nvtx.h"
 #include "plan.h"
 
 namespace selinv {
@@ -114,6 +115,7 @@ extern "C" int64_t selinv_plan_selected(selinv_plan plan, int64_t *pos_out) {
 }
 
 extern "C" int selinv_gather(selinv_plan plan, selinv_dtype dtype, const void *Ainv, void *out, void *stream) {
+    NvtxRange nvtx_range("selinv_gather");
     if (!plan || (dtype != SELINV_F64 && dtype != SELINV_C128 && dtype != SELINV_C128H)) return SELINV_ERR_INVALID_ARG;
     PlanData &p = plan->data;
     const int64_t n = (int64_t)p.sel_pos.size();
@@ -140,6 +142,7 @@ extern "C" int selinv_gather(selinv_plan plan, selinv_dtype dtype, const void *A
 
 extern "C" int selinv_pole_sum(int nitems, const selinv_dtype *dtypes, const void *const *Ainv,
                                const double *weights, int64_t npos, const int64_t *pos, void *out, void *stream) {
+    NvtxRange nvtx_range("selinv_pole_sum");
     if (nitems <= 0 || !dtypes || !Ainv || !weights || npos < 0) return SELINV_ERR_INVALID_ARG;
     if (npos == 0) return SELINV_OK;
     if (!pos || !out) return SELINV_ERR_INVALID_ARG;
