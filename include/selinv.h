@@ -64,6 +64,7 @@ extern "C" {
 #define SELINV_ERR_CUDA (-7)
 #define SELINV_ERR_TIMEOUT (-8)      /* a bounded device wait ran out              */
 #define SELINV_ERR_UNSUPPORTED (-9)
+#define SELINV_ERR_BAD_INDEX (-10)   /* a gather address fell outside the panels (debug_checks bit 2) */
 
 typedef struct selinv_plan_s *selinv_plan;          /* opaque, owned by the library */
 typedef struct selinv_analysis_s *selinv_analysis;  /* opaque, owned by the library */
@@ -92,7 +93,11 @@ typedef struct {
                               default 0                                                 */
     int debug_checks;      /* bit 0: scan inputs for non-finite values; bit 1: the
                               persistent schedule waits on a flag that is never set,
-                              so every wait runs out (tests the timeout path); default 0 */
+                              so every wait runs out (tests the timeout path); bit 2:
+                              every address of the gather of A^{-1}_{C,C} is checked
+                              against the panel array before the load: one outside it
+                              is read as zero and latches SELINV_ERR_BAD_INDEX (no trap,
+                              the results are then invalid); default 0                 */
     long long spin_limit;  /* polls (about 256 ns each) of every device spin-wait before
                               it gives up and latches SELINV_ERR_TIMEOUT; default 1<<22 */
     int use_graph;         /* 1: capture the level schedule in a CUDA graph; default 1  */

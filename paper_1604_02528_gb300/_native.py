@@ -34,6 +34,8 @@ SELINV_ERR_OOM = -6
 SELINV_ERR_CUDA = -7
 SELINV_ERR_TIMEOUT = -8
 SELINV_ERR_UNSUPPORTED = -9
+SELINV_ERR_BAD_INDEX = -10
+DEBUG_CHECK_FINITE, DEBUG_TIMEOUT_TEST, DEBUG_CHECK_GATHER = 1, 2, 4   # selinv_opts.debug_checks bits
 
 # kernel kinds reported by selinv_numeric_profile
 PROFILE_KINDS = ("k_linv", "k_lhat", "k_selinv", "k_lhat_digits", "k_selinv_oz", "k_diag",

@@ -117,6 +117,8 @@ struct ProbDesc {
     int *tcount;                // [sum ntiles] arrivals per (K, row tile), zero between calls
     const int64_t *tile_base;   // [ns+1] prefix sums of the row tiles of each supernode
     int32_t ns, n;
+    int64_t nnz;                // panel entries (every gather address lies in [0, nnz))
+    int32_t check_gather;       // 1: bounds-check gather addresses (debug_checks bit 2)
     int32_t dtype;              // element type: SELINV_F64 or SELINV_C128
     int32_t symmetrize;
     int32_t herm;               // complex Hermitian (SELINV_C128H): conjugate transposes
@@ -143,6 +145,26 @@ constexpr int kDiagCols = 32;   // columns j per work item of the tensor-core di
 constexpr long long kTcSlotWords = 2 * 128 * 64 + 64;
 
 #ifdef __CUDACC__
+// Optional bounds check of gather addresses (debug_checks bit 2): an address
+// outside the panel array latches SELINV_ERR_BAD_INDEX and is not read.
+struct GatherCheck {
+    int64_t nnz = 0;
+    int *status = nullptr;
+    int on = 0;
+    __device__ __forceinline__ bool ok(int64_t addr) const {
+        if (!on || (addr >= 0 && addr < nnz)) return true;
+        atomicCAS(status, 0, SELINV_ERR_BAD_INDEX);
+        return false;
+    }
+};
+__device__ __forceinline__ GatherCheck gather_check(const ProbDesc &P) {
+    GatherCheck g;
+    g.nnz = P.nnz;
+    g.status = P.status;
+    g.on = P.check_gather;
+    return g;
+}
+
 // atomicMax on a shared slot that every active lane of the warp targets: one
 // atomic per warp instead of one per lane (the lanes would serialize on it)
 __device__ __forceinline__ void warp_uniform_atomic_max(int *slot, int v) {

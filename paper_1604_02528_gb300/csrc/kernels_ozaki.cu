@@ -107,11 +107,12 @@ struct Gather {
     const int32_t *relidx;
     const int64_t *tile_cb, *tile_rb; // the tile's rows (shared memory)
     int p0, c;
+    GatherCheck chk;
     __device__ __forceinline__ double operator()(int pl, int q) const {
         const int p = p0 + pl;
         if (p >= c || q >= c) return 0.0;
         const int64_t addr = p >= q ? pcb[q] + relidx[prb[q] + p] : tile_cb[pl] + relidx[tile_rb[pl] + q];
-        return Z[addr];
+        return chk.ok(addr) ? Z[addr] : 0.0;
     }
 };
 
@@ -205,7 +206,7 @@ __global__ void __launch_bounds__(kOzThreads, 1) k_selinv_oz(const ProbDesc *__r
     }
     __syncthreads();
     const Gather g{static_cast<const double *>(P.Z), P.colbase + pos0, P.relbase + pos0, P.relidx,
-                   tile_cb, tile_rb, p0, c};
+                   tile_cb, tile_rb, p0, c, gather_check(P)};
 
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
     const int mt = warp % 4;                  // m-tile: rows mt*16 .. +15

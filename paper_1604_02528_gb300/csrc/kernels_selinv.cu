@@ -330,7 +330,7 @@ __device__ void selinv_item(const ProbDesc &P, const Item &it, unsigned char *sm
     if (pm > 0) {
         // LU form: entries above the diagonal from the transposed upper panels
         LoadGather<T, TN> la{Zc, P.colbase + pos0, P.relbase + pos0, P.relidx, tile_cb, tile_rb, p0, c,
-                             P.herm != 0, P.lu ? static_cast<const T *>(P.Zu) : nullptr};
+                             P.herm != 0, P.lu ? static_cast<const T *>(P.Zu) : nullptr, gather_check(P)};
         LoadColMajor<T, TN> lb{LDk + s, ld, c, s};  // Lhat(q, j) = LD[j*ld + s + q]
         tile_gemm<T, TN>(c, la, lb, acc, As, Bs);
     }
@@ -362,7 +362,8 @@ __device__ void selinv_item(const ProbDesc &P, const Item &it, unsigned char *sm
         for (int i = 0; i < S::MI; i++)
 #pragma unroll
             for (int j = 0; j < S::NJ; j++) acc[i][j] = Sc<T>::zero();
-        LoadGather<T, TN> lu{Zu, P.colbase + pos0, P.relbase + pos0, P.relidx, tile_cb, tile_rb, p0, c, false, Zc};
+        LoadGather<T, TN> lu{Zu, P.colbase + pos0, P.relbase + pos0, P.relidx, tile_cb, tile_rb, p0, c, false, Zc,
+                             gather_check(P)};
         LoadColMajor<T, TN> lb{LDu + s, ld, c, s};
         tile_gemm<T, TN>(c, lu, lb, acc, As, Bs);
         T *Zuk = Zu + P.panel_off[K];
@@ -433,6 +434,7 @@ template <typename T> struct LoadPush {
     const int32_t *relidx;
     int p0, pm, q0, kd;
     bool herm;
+    GatherCheck chk;
     __device__ void operator()(int k0, T *As) const {
         for (int e = threadIdx.x; e < kTK * kTM; e += kThreads) {
             const int pl = e % kTM, kk = e / kTM;
@@ -440,7 +442,8 @@ template <typename T> struct LoadPush {
             if (pl < pm && k0 + kk < kd) {
                 const int p = p0 + pl, q = q0 + k0 + kk;
                 const int m = p < q ? p : q, M = p < q ? q : p;
-                v = Z[pcb[m] + relidx[prb[m] + M]];
+                const int64_t addr = pcb[m] + relidx[prb[m] + M];
+                if (chk.ok(addr)) v = Z[addr];
                 if (p < q) v = cjif(v, herm);
             }
             As[kk * kTM + pl] = v;
@@ -482,7 +485,7 @@ __global__ void __launch_bounds__(kThreads) k_push(const ProbDesc *__restrict__ 
     for (int i = 0; i < S::MI; i++)
 #pragma unroll
         for (int j = 0; j < S::NJ; j++) acc[i][j] = Sc<T>::zero();
-    LoadPush<T> la{Z, P.colbase + pos0, P.relbase + pos0, P.relidx, p0, pm, q0, kd, P.herm != 0};
+    LoadPush<T> la{Z, P.colbase + pos0, P.relbase + pos0, P.relidx, p0, pm, q0, kd, P.herm != 0, gather_check(P)};
     LoadColMajor<T, TN> lb{LDi + s + q0, ld, kd, s};   // Lhat(q0 + k, j)
     tile_gemm<T, TN>(kd, la, lb, acc, As, Bs);
     const int tx = threadIdx.x % S::TX, ty = threadIdx.x / S::TX;
@@ -545,6 +548,7 @@ __global__ void __launch_bounds__(256) k_selinv_tiny(const ProbDesc *__restrict_
 #pragma unroll
         for (int j = 0; j < kTinyS; j++) acc[r][j] = Sc<T>::zero();
     // four q at a time: their gathers are in flight together
+    const GatherCheck chk = gather_check(P);
     for (int q0 = 0; q0 < c; q0 += 4) {
         T v[2][4];
 #pragma unroll
@@ -556,7 +560,7 @@ __global__ void __launch_bounds__(256) k_selinv_tiny(const ProbDesc *__restrict_
                 if (p >= c || q >= c) continue;
                 // entry (p, q) of A^{-1}_{C,C}: stored at (max, min)
                 const int64_t addr = p >= q ? pcb[q] + P.relidx[prb[q] + p] : pcb[p] + P.relidx[prb[p] + q];
-                v[r][u] = Zc[addr];
+                if (chk.ok(addr)) v[r][u] = Zc[addr];
                 if (p < q) v[r][u] = cjif(v[r][u], h);
             }
 #pragma unroll

@@ -176,7 +176,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_selinv_tc(const ProbDesc *__r
         // matrices.  The gather runs three steps ahead in registers, every
         // load a whole step before its use: column data (step i + 3),
         // relative rows (i + 2), values (i + 1).
-        const TcGather g{P.colbase + pos0, P.relbase + pos0, P.relidx, tile_cb, tile_rb, p0, c};
+        const TcGather g{P.colbase + pos0, P.relbase + pos0, P.relidx, tile_cb, tile_rb, p0, c, gather_check(P)};
         const double *Zg = static_cast<const double *>(P.Z);
         const int r = (warp % 8) * 16 + (lane >> 1), kq = (warp / 8) * 2 + (lane & 1);
         const int E = rowE[r];
@@ -200,7 +200,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_selinv_tc(const ProbDesc *__r
         };
         auto load = [&]() {
 #pragma unroll
-            for (int u = 0; u < 4; u++) v[u] = ab[u] >= 0 ? Zg[ab[u] + ar[u]] : 0.0;
+            for (int u = 0; u < 4; u++) v[u] = ab[u] >= 0 && g.chk.ok(ab[u] + ar[u]) ? Zg[ab[u] + ar[u]] : 0.0;
         };
         if (n > 0) {
             cols(0);

@@ -251,7 +251,7 @@ __global__ void __launch_bounds__(kTwThreads, 1) k_selinv_tcw(const ProbDesc *__
         // q = 8 step + 2 kq and + 1.  The gather runs three steps ahead in
         // registers, every load a whole step before its use: column data
         // (step i + 3), relative rows (i + 2), values (i + 1).
-        const TcGather g{P.colbase + pos0, P.relbase + pos0, P.relidx, tile_cb, tile_rb, p0, c};
+        const TcGather g{P.colbase + pos0, P.relbase + pos0, P.relidx, tile_cb, tile_rb, p0, c, gather_check(P)};
         const int r = (warp % 4) * 16 + (lane >> 1), kq = (warp / 4) * 2 + (lane & 1);
         const int E = rowE[r];
         constexpr int NV = CPLX ? 2 : 4;        // entries of A^{-1}_{C,C} per thread and step
@@ -267,14 +267,14 @@ __global__ void __launch_bounds__(kTwThreads, 1) k_selinv_tcw(const ProbDesc *__
                 const double2 *Zc = static_cast<const double2 *>(P.Z);
 #pragma unroll
                 for (int u = 0; u < NV; u++) {
-                    const double2 z = ab[u] >= 0 ? Zc[ab[u] + ar[u]] : make_double2(0.0, 0.0);
+                    const double2 z = ab[u] >= 0 && g.chk.ok(ab[u] + ar[u]) ? Zc[ab[u] + ar[u]] : make_double2(0.0, 0.0);
                     v[2 * u] = z.x;
                     v[2 * u + 1] = herm && up[u] ? -z.y : z.y;
                 }
             } else {
                 const double *Zg = static_cast<const double *>(P.Z);
 #pragma unroll
-                for (int u = 0; u < NV; u++) v[u] = ab[u] >= 0 ? Zg[ab[u] + ar[u]] : 0.0;
+                for (int u = 0; u < NV; u++) v[u] = ab[u] >= 0 && g.chk.ok(ab[u] + ar[u]) ? Zg[ab[u] + ar[u]] : 0.0;
             }
         };
         // column data of step i_ (of this item), none past the last step

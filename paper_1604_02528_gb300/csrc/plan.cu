@@ -449,6 +449,8 @@ ProbDesc make_desc(const PlanData &p, Workspace &w, int dtype, const void *L, co
     d.tile_base = p.d_tile_base;
     d.ns = p.ns;
     d.n = p.n;
+    d.nnz = p.nnz;
+    d.check_gather = (p.opts.debug_checks & 4) ? 1 : 0;
     d.dtype = dtype == SELINV_C128H ? SELINV_C128 : dtype;   // element type of the kernels
     d.herm = dtype == SELINV_C128H;
     d.symmetrize = p.opts.symmetrize;
@@ -1173,7 +1175,7 @@ static bool opts_valid(const selinv_opts *o) {
     return o->schedule >= 0 && o->schedule <= 3 && o->fast_contraction >= 0 && o->fast_contraction <= 2 &&
            o->split_target >= 1 && o->split_target <= 8 && o->split_min_steps >= 8 &&
            o->split_min_steps <= 64 && o->split_min_steps % 8 == 0 && o->oz_min_s >= kOzMinS && o->oz_min_s <= 128 &&
-           o->spin_limit > 0;
+           o->spin_limit > 0 && o->debug_checks >= 0 && o->debug_checks <= 7;
 }
 
 extern "C" void selinv_default_opts(selinv_opts *o) {
@@ -1627,6 +1629,7 @@ extern "C" const char *selinv_error_string(int code) {
     case SELINV_ERR_CUDA: return "CUDA error";
     case SELINV_ERR_TIMEOUT: return "a bounded device wait timed out";
     case SELINV_ERR_UNSUPPORTED: return "unsupported";
+    case SELINV_ERR_BAD_INDEX: return "a gather address fell outside the panel array";
     default: return "unknown error";
     }
 }

@@ -7,6 +7,7 @@
 
 #include <stdint.h>
 
+#include "common.cuh"
 #include "umma.cuh"
 
 namespace selinv {
@@ -93,6 +94,7 @@ struct TcGather {
     const int32_t *relidx;
     const int64_t *tile_cb, *tile_rb;
     int p0, c;
+    GatherCheck chk;   // optional bounds check of the addresses (applied by the loads)
     __device__ __forceinline__ void cols(int q, int64_t &cb, int64_t &rb) const {
         if (q < c) {
             cb = pcb[q];

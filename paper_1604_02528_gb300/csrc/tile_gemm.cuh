@@ -92,6 +92,7 @@ template <typename T, int TN, bool kDoubleDiag = false> struct LoadGather {
     int p0, c;
     bool herm = false;    // Hermitian: an entry above the diagonal is the stored one's conjugate
     const T *Zup = nullptr;   // LU form: the entries above the diagonal come from this panel set
+    GatherCheck chk{};        // optional bounds check of the addresses
     __device__ void operator()(int k0, T *As) const {
         for (int e = threadIdx.x; e < kTK * kTM; e += kThreads) {
             const int pl = e % kTM, kk = e / kTM;
@@ -101,7 +102,7 @@ template <typename T, int TN, bool kDoubleDiag = false> struct LoadGather {
                 int64_t addr;
                 if (p >= q) addr = pcb[q] + relidx[prb[q] + p];
                 else addr = tile_cb[pl] + relidx[tile_rb[pl] + q];
-                v = ldcg((p < q && Zup ? Zup : Z) + addr);  // L2: written by other CTAs of a persistent launch
+                if (chk.ok(addr)) v = ldcg((p < q && Zup ? Zup : Z) + addr);  // L2: written by other CTAs of a persistent launch
                 if (p < q) v = cjif(v, herm);
                 if (kDoubleDiag && p == q) v = add(v, v);
             }

@@ -250,3 +250,32 @@ def test_complex_tensor_core_path_matches_oracle(native, cuda_device, name, make
     for K in range(0, sym.nsuper, max(1, sym.nsuper // 40)):
         blk = G[off[K]:off[K + 1]].reshape(s[K], s[K] + c[K]).T[: s[K], :]
         assert np.array_equal(blk, blk.T)
+
+
+@pytest.mark.parametrize("name,make", [CASES[1], CASES[4], CASES[7], CASES[8]])
+def test_bounds_checked_gathers_change_nothing(native, cuda_device, name, make):
+    """debug_checks bit 2 checks every gather address against the panel
+    array before the load; on a valid plan no address fails, the status
+    stays clear and every engine and schedule gives bit for bit the result
+    it gives without the check."""
+    import torch
+    p = make()
+    sym, L, D, Z = oracle_run(p)
+    plan = native.selinv_symbolic(sym.n, sym.nsuper, sym.super_ptr, sym.sparent, sym.rowptr, sym.rows)
+    dt = native.SELINV_C128 if L.dtype.kind == "c" else native.SELINV_F64
+    Lt = torch.from_numpy(L).cuda(); Dt = torch.from_numpy(D).cuda()
+    for fast, ozm, sched in ((1, 1, 1), (1, 16, 1), (2, 16, 1), (0, 16, 1), (0, 16, 3), (1, 16, 0)):
+        if fast == 2 and dt != native.SELINV_F64:
+            continue
+        outs = []
+        for checks in (0, native.DEBUG_CHECK_GATHER):
+            o = native.selinv_default_opts()
+            o.fast_contraction, o.oz_min_s, o.schedule, o.debug_checks = fast, ozm, sched, checks
+            native.selinv_plan_set_opts(plan, o)
+            Zt = torch.full_like(Lt, float("nan"))
+            native.selinv_numeric(plan, dt, Lt, Dt, Zt, torch.cuda.current_stream())
+            torch.cuda.synchronize()
+            assert native.selinv_status(plan) == 0, (name, fast, sched, checks)
+            outs.append(Zt.cpu().numpy())
+        assert np.array_equal(outs[0], outs[1]), (name, fast, sched)
+        assert oracle.block_errors(sym, outs[1], Z).max() <= TOL

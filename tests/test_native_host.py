@@ -266,7 +266,7 @@ def test_binding_constants_match_header(native):
     from pathlib import Path
     hdr = (Path(__file__).resolve().parents[1] / "include" / "selinv.h").read_text()
     codes = dict(re.findall(r"#define (SELINV_(?:OK|ERR_\w+))\s+\(?(-?\d+)\)?", hdr))
-    assert len(codes) == 10
+    assert len(codes) == 11
     for name, val in codes.items():
         assert getattr(native, name) == int(val), name
     kinds = int(re.search(r"#define SELINV_PROFILE_KINDS (\d+)", hdr).group(1))
@@ -283,9 +283,16 @@ def test_options_round_trip_and_validation(native):
     native.selinv_plan_set_opts(plan, o)
     g = native.selinv_plan_get_opts(plan)
     assert (g.fast_contraction, g.split_target, g.split_min_steps, g.oz_min_s) == (2, 4, 32, 64)
+    # the debug bits (non-finite scan, timeout test, bounds-checked gathers) round trip
+    for bits in (native.DEBUG_CHECK_FINITE, native.DEBUG_TIMEOUT_TEST, native.DEBUG_CHECK_GATHER, 7):
+        b = native.selinv_default_opts()
+        b.debug_checks = bits
+        native.selinv_plan_set_opts(plan, b)
+        assert native.selinv_plan_get_opts(plan).debug_checks == bits
+    assert "outside the panel" in native.error_string(native.SELINV_ERR_BAD_INDEX)
     for field, bad in (("split_target", 0), ("split_target", 9), ("split_min_steps", 12),
                        ("split_min_steps", 0), ("oz_min_s", 0), ("fast_contraction", 3), ("schedule", 4),
-                       ("spin_limit", 0)):
+                       ("spin_limit", 0), ("debug_checks", 8), ("debug_checks", -1)):
         b = native.selinv_default_opts()
         setattr(b, field, bad)
         with pytest.raises(native.SelinvError) as e:
