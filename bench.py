@@ -65,6 +65,10 @@ def parse():
                     help="1: the library's autotuner picks its options on the first (untimed) call")
     ap.add_argument("--fast", type=int, default=1,
                     help="FP64-exact tensor-core contraction for s >= 16 -- 1: tcgen05, 2: mma.sync; 0: DFMA only")
+    ap.add_argument("--oz-min-s", type=int, default=None,
+                    help="narrowest tensor-core supernode (with --autotune 0; the autotuner picks its own)")
+    ap.add_argument("--split-target", type=int, default=None, help="k-split: CTAs per SM on narrow levels")
+    ap.add_argument("--split-min-steps", type=int, default=None, help="k-split: smallest k-range in 16-row steps")
     return ap.parse_args()
 
 
@@ -150,9 +154,10 @@ class ClockSampler:
 
 KERNEL_SOURCES = {
     "k_selinv_oz": ("kernels_ozaki.cu", "common.cuh"),
-    "k_selinv_tc": ("kernels_tc.cu", "umma.cuh", "fixedpoint.cuh", "common.cuh"),
+    "k_selinv_tc": ("kernels_tc.cu", "kernels_tc_wide.cu", "tc_digits.cuh", "umma.cuh", "fixedpoint.cuh",
+                    "common.cuh"),
     "k_diag": ("kernels_ozaki.cu", "common.cuh"),
-    "k_diag_tc": ("kernels_tc.cu", "umma.cuh", "fixedpoint.cuh", "common.cuh"),
+    "k_diag_tc": ("kernels_tc.cu", "tc_digits.cuh", "umma.cuh", "fixedpoint.cuh", "common.cuh"),
 }
 DEFAULT_SOURCES = ("kernels_selinv.cu", "tile_gemm.cuh", "common.cuh")
 
@@ -473,6 +478,12 @@ def main():
     o.schedule = args.schedule
     o.fast_contraction = args.fast
     o.autotune = args.autotune
+    if args.oz_min_s is not None:
+        o.oz_min_s = args.oz_min_s
+    if args.split_target is not None:
+        o.split_target = args.split_target
+    if args.split_min_steps is not None:
+        o.split_min_steps = args.split_min_steps
     N.selinv_plan_set_opts(ctx.plan, o)
     dt = N.SELINV_C128 if p.values.dtype.kind == "c" else N.SELINV_F64
     A = torch.from_numpy(p.values).to(dev)
