@@ -197,10 +197,15 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_selinv_tc(const ProbDesc *__r
                 if (i_ < n) g.parts(r, (st0 + i_) * 16 + kq * 4 + u, cb[u], rb[u], ab[u], ar[u], up[u]);
                 else { ab[u] = -1; ar[u] = 0; }
             }
+            // bounds check (debug): an address outside the panels is dropped
+            if (g.chk.on)
+#pragma unroll
+                for (int u = 0; u < 4; u++)
+                    if (ab[u] >= 0 && !g.chk.ok(ab[u] + ar[u])) ab[u] = -1;
         };
         auto load = [&]() {
 #pragma unroll
-            for (int u = 0; u < 4; u++) v[u] = ab[u] >= 0 && g.chk.ok(ab[u] + ar[u]) ? Zg[ab[u] + ar[u]] : 0.0;
+            for (int u = 0; u < 4; u++) v[u] = ab[u] >= 0 ? Zg[ab[u] + ar[u]] : 0.0;
         };
         if (n > 0) {
             cols(0);

@@ -267,14 +267,14 @@ __global__ void __launch_bounds__(kTwThreads, 1) k_selinv_tcw(const ProbDesc *__
                 const double2 *Zc = static_cast<const double2 *>(P.Z);
 #pragma unroll
                 for (int u = 0; u < NV; u++) {
-                    const double2 z = ab[u] >= 0 && g.chk.ok(ab[u] + ar[u]) ? Zc[ab[u] + ar[u]] : make_double2(0.0, 0.0);
+                    const double2 z = ab[u] >= 0 ? Zc[ab[u] + ar[u]] : make_double2(0.0, 0.0);
                     v[2 * u] = z.x;
                     v[2 * u + 1] = herm && up[u] ? -z.y : z.y;
                 }
             } else {
                 const double *Zg = static_cast<const double *>(P.Z);
 #pragma unroll
-                for (int u = 0; u < NV; u++) v[u] = ab[u] >= 0 && g.chk.ok(ab[u] + ar[u]) ? Zg[ab[u] + ar[u]] : 0.0;
+                for (int u = 0; u < NV; u++) v[u] = ab[u] >= 0 ? Zg[ab[u] + ar[u]] : 0.0;
             }
         };
         // column data of step i_ (of this item), none past the last step
@@ -291,6 +291,11 @@ __global__ void __launch_bounds__(kTwThreads, 1) k_selinv_tcw(const ProbDesc *__
                 if (i_ < n) g.parts(r, (st0 + i_) * QS + kq * NV + u, cb[u], rb[u], ab[u], ar[u], up[u]);
                 else { ab[u] = -1; ar[u] = 0; }
             }
+            // bounds check (debug): an address outside the panels is dropped
+            if (g.chk.on)
+#pragma unroll
+                for (int u = 0; u < NV; u++)
+                    if (ab[u] >= 0 && !g.chk.ok(ab[u] + ar[u])) ab[u] = -1;
         };
         if (n > 0) {
             cols(0);
