@@ -101,10 +101,11 @@ typedef struct {
     long long spin_limit;  /* polls (about 256 ns each) of every device spin-wait before
                               it gives up and latches SELINV_ERR_TIMEOUT; default 1<<22 */
     int use_graph;         /* 1: capture the level schedule in a CUDA graph; default 1  */
-    int fast_contraction;  /* contraction of the large real supernodes (s >= 16): FP64-exact
-                              on bf16 tensor cores (error-free slicing, exact integer
-                              accumulation) -- 1: tcgen05 with tensor-memory accumulators
-                              (default), 2: mma.sync; 0: FP64 DFMA only                 */
+    int fast_contraction;  /* contraction of the supernodes with s >= oz_min_s: FP64-exact
+                              on fp16 tensor cores (error-free slicing into 8-bit digits,
+                              exact integer accumulation) -- 1: tcgen05 with tensor-memory
+                              accumulators (default; real, complex symmetric and Hermitian
+                              values), 2: mma.sync (real values only); 0: FP64 DFMA only */
     int split_target;      /* level schedule: k-splits of the contraction aim at this many
                               CTAs per SM on narrow levels (1..8); default 2           */
     int split_min_steps;   /* smallest k-range of a split item, in 16-row steps (8..64,
