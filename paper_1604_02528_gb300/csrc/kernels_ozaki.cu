@@ -24,6 +24,7 @@
 #include "launch.h"
 #include "tile_gemm.cuh"
 #include "fixedpoint.cuh"
+#include "diag_fin.cuh"
 
 namespace selinv {
 
@@ -34,8 +35,9 @@ constexpr int kOzThreads = 256;
 
 // ---------------------------------------------------------------------------
 // k_lhat_digits: digit planes of Lhat_{C,K} (per column j: exponent over all
-// q) in the layout plane[j][q] (q contiguous, padded to c16 with zeros).
-// One warp per column.
+// q) in the tcgen05 operand layout and, unless the work item says that only
+// that one is read, in the mma.sync layout plane[j][q] (q contiguous, padded
+// to c16 with zeros).  One warp per column.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) k_lhat_digits(const ProbDesc *__restrict__ descs,
                                                      const int2 *__restrict__ work, int nwork) {
@@ -43,8 +45,9 @@ __global__ void __launch_bounds__(256) k_lhat_digits(const ProbDesc *__restrict_
     const int w = blockIdx.x;
     if (w >= nwork) return;
     const ProbDesc &P = descs[work[w].x];
-    const int K = work[w].y >> 8;           // (K << 8) | column block of 8
-    const int jb = work[w].y & 0xFF;
+    const int K = work[w].y >> 8;           // (K << 8) | only_u << 7 | column block of 8
+    const int jb = work[w].y & 0x7F;
+    const bool both = !(work[w].y & 0x80);   // also the mma.sync layout
     const int fc = P.super_ptr[K];
     const int s = P.super_ptr[K + 1] - fc;
     const int64_t ld = P.rowptr[K + 1] - P.rowptr[K];
@@ -76,7 +79,7 @@ __global__ void __launch_bounds__(256) k_lhat_digits(const ProbDesc *__restrict_
 #pragma unroll
         for (int i = 0; i < kDig; i++) {
             const uint16_t h = (uint16_t)f16_of_int(d[i]);
-            pl[i * plane + (int64_t)j * c16 + q] = h;
+            if (both) pl[i * plane + (int64_t)j * c16 + q] = h;
             pu[i * s64 * 16 + ub] = h;
         }
     }
@@ -360,8 +363,9 @@ __global__ void __launch_bounds__(kOzThreads, 1) k_selinv_oz(const ProbDesc *__r
 
 // ---------------------------------------------------------------------------
 // k_linv_digits: fp16 digit planes of L_KK^{-1} for the tensor-core Lhat
-// product: per column j, exponent over k; layout plane[j][k], k padded to s16.
-// One warp per column.
+// product: per column j, exponent over k; layout plane[j][k], k padded to s16
+// (k_lhat_oz), or, when the work item says so, the tcgen05 operand layout of
+// the transposed product (rows j, k in 16-steps).  One warp per column.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) k_linv_digits(const ProbDesc *__restrict__ descs,
                                                      const int2 *__restrict__ work, int nwork) {
@@ -370,7 +374,8 @@ __global__ void __launch_bounds__(256) k_linv_digits(const ProbDesc *__restrict_
     if (w >= nwork) return;
     const ProbDesc &P = descs[work[w].x];
     const int K = work[w].y >> 8;
-    const int jb = work[w].y & 0xFF;
+    const int jb = work[w].y & 0x7F;
+    const bool tcl = work[w].y & 0x80;      // the tcgen05 operand layout
     const int fc = P.super_ptr[K];
     const int s = P.super_ptr[K + 1] - fc;
     const int s16 = (s + 15) & ~15;
@@ -391,8 +396,17 @@ __global__ void __launch_bounds__(256) k_linv_digits(const ProbDesc *__restrict_
 #pragma unroll
             for (int i = 0; i < kDig; i++) d[i] = 0;
         }
+        if (tcl) {
+            // rows j, k in 16-steps: per step the 7 planes of s64 x 16 one
+            // after the other, K-major 8 x 8 core matrices
+            const int64_t s64 = (s + 63) / 64 * 64;
+            const int64_t ub = (int64_t)(k / 16) * kDig * s64 * 16 + (j / 8) * 128 + ((k % 16) / 8) * 64 + (j % 8) * 8 + k % 8;
 #pragma unroll
-        for (int i = 0; i < kDig; i++) pl[i * plane + (int64_t)j * s16 + k] = (uint16_t)f16_of_int(d[i]);
+            for (int i = 0; i < kDig; i++) pl[i * s64 * 16 + ub] = (uint16_t)f16_of_int(d[i]);
+        } else {
+#pragma unroll
+            for (int i = 0; i < kDig; i++) pl[i * plane + (int64_t)j * s16 + k] = (uint16_t)f16_of_int(d[i]);
+        }
     }
 }
 
@@ -654,49 +668,19 @@ __global__ void __launch_bounds__(kOzThreads, 1) k_diag_oz(const ProbDesc *__res
 }
 
 // ---------------------------------------------------------------------------
-// k_diag_fin: A^{-1}_KK = Dinv_K - Lhat^T Y from the exact tile sums of
-// k_diag_oz, symmetrized (Sec. II-C).  One CTA per 8 columns j of the block,
-// a warp per column, lanes over all rows i.  Entry (i, j) and its mirror are
-// formed from the same sums in the same order by the CTAs of columns j and i,
-// so the block is exactly symmetric; each CTA writes only its own columns and
-// their whole-column exponents (for the row bounds of later gathers).  The
-// sums are cleared before every call.
+// k_diag_fin: A^{-1}_KK = Dinv_K - Lhat^T Y from the exact sums of k_diag_oz
+// (bshift 0) or k_diag_tc (bshift 1), symmetrized: one CTA per (K, 8 columns),
+// a warp per column (diag_fin_column).  items: (K, column block) per supernode.
 // ---------------------------------------------------------------------------
-// bshift: 1 when the sums come from k_diag_tc (its Y digits sit on a grid
-// twice as coarse as k_diag_oz's)
 __global__ void __launch_bounds__(256) k_diag_fin(const ProbDesc *__restrict__ descs,
                                                   const Item *__restrict__ items, int nitems, int bshift) {
     const int w = blockIdx.x;
     if (w >= nitems) return;
     const Item it = items[w];
     const ProbDesc &P = descs[it.prob];
-    const int K = it.K;
-    const int fc = P.super_ptr[K];
-    const int s = P.super_ptr[K + 1] - fc;
-    const int64_t ld = P.rowptr[K + 1] - P.rowptr[K];
-    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-    const int j = it.tile * 8 + warp;
-    if (j >= s) return;                       // the whole warp
-    const double *LDk = static_cast<const double *>(P.LD) + P.panel_off[K];
-    double *Zk = static_cast<double *>(P.Z) + P.panel_off[K];
-    const long long *acc64 = P.dacc + 2 * P.linv_off[K];
-    auto prod = [&](int a, int b) -> double {   // (Lhat^T Y)(a, b)
-        const long long *q = acc64 + 2 * ((int64_t)b * s + a);
-        const long long hi = q[0], lo = q[1];
-        const int ey = P.colexpY[fc + b];
-        if (ey == 0 || (hi == 0 && lo == 0)) return 0.0;
-        const int sc = (P.colexp[fc + a] - 1022) + (ey - 1022) - 14 + bshift;
-        return fixed_to_double(hi, lo, sc);
-    };
-    int mj = 0;
-    for (int i = lane; i < s; i += 32) {
-        double x = LDk[(int64_t)j * ld + i] - prod(i, j);
-        if (P.symmetrize) x = 0.5 * (x + (LDk[(int64_t)i * ld + j] - prod(j, i)));
-        Zk[(int64_t)j * ld + i] = x;
-        mj = max(mj, bexp(x));
-    }
-    mj = __reduce_max_sync(0xffffffffu, mj);
-    if (lane == 0) P.colexpZ[fc + j] = max(mj, P.colexpY[fc + j]);
+    const int s = P.super_ptr[it.K + 1] - P.super_ptr[it.K];
+    const int j = it.tile * 8 + threadIdx.x / 32;
+    if (j < s) diag_fin_column<false>(P, it.K, j, bshift, threadIdx.x % 32);
 }
 
 constexpr size_t diag_oz_smem() {

@@ -73,8 +73,76 @@ __device__ void linv_lu(const ProbDesc &P, int K, int s, int64_t ld, const T *L,
     }
 }
 
-// with_dinv = 0: only L_KK^{-1} (k_dinv forms Dinv_K afterwards, spread over tiles)
-template <typename T>
+// X = L_KK^{-1} (unit lower, s > 32) in shared memory by 32 x 32 blocks, in
+// ceil(s/32) dependent phases instead of s - 1: with L_ij the blocks of L_KK
+// and X_ij those of X,
+//   X_ii = L_ii^{-1}                                   (all i at once)
+//   X_ij = -X_ii sum_{k = j..i-1} L_ik X_kj,  j < i     (block row i after rows < i)
+// A diagonal block is inverted by one warp, lane c owning column c in
+// registers (column-oriented substitution: no synchronization); an
+// off-diagonal block row is a product with the finished rows above it, then
+// a product with X_ii.  Rows and columns past s act as the identity.  X must
+// hold the identity on entry.
+__device__ void linv_blocked(const double *__restrict__ L, int64_t ld, double *X, int lx, int s) {
+    const int nb = (s + 31) / 32;
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    for (int b = warp; b < nb; b += kLinvThreads / 32) {
+        const int o = 32 * b, n = min(32, s - o);
+        const double *Lb = L + (int64_t)o * ld + o;   // L_bb(i, k) = Lb[k * ld + i]
+        double x[32];
+#pragma unroll
+        for (int i = 0; i < 32; i++) x[i] = i == lane ? 1.0 : 0.0;
+#pragma unroll
+        for (int k = 0; k < 31; k++) {
+            if (k + 1 < n) {
+#pragma unroll
+                for (int i = k + 1; i < 32; i++)
+                    if (i < n) x[i] = fma(-Lb[(int64_t)k * ld + i], x[k], x[i]);
+            }
+        }
+        if (lane < n) {
+#pragma unroll
+            for (int i = 0; i < 32; i++)
+                if (i < n) X[(o + lane) * lx + o + i] = x[i];
+        }
+    }
+    __syncthreads();
+    for (int bi = 1; bi < nb; bi++) {
+        const int oi = 32 * bi, ni = min(32, s - oi);
+        // T = sum_k L_ik X_kj for every column j < oi, into X's block row i
+        for (int e = threadIdx.x; e < oi * 32; e += kLinvThreads) {
+            const int r = e % 32, col = e / 32;
+            if (r < ni) {
+                double acc = 0.0;
+                for (int t = col; t < oi; t++) acc = fma(L[(int64_t)t * ld + oi + r], X[col * lx + t], acc);
+                X[col * lx + oi + r] = acc;
+            }
+        }
+        __syncthreads();
+        // X_ij = -X_ii T, a column of T per thread
+        for (int col = threadIdx.x; col < oi; col += kLinvThreads) {
+            double tv[32];
+#pragma unroll
+            for (int r = 0; r < 32; r++) tv[r] = r < ni ? X[col * lx + oi + r] : 0.0;
+#pragma unroll
+            for (int r = 0; r < 32; r++) {
+                if (r < ni) {
+                    double acc = 0.0;
+#pragma unroll
+                    for (int t = 0; t <= r; t++) acc = fma(X[(oi + t) * lx + oi + r], tv[t], acc);
+                    X[col * lx + oi + r] = -acc;
+                }
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// with_dinv = 0: only L_KK^{-1} (k_dinv forms Dinv_K afterwards, spread over tiles).
+// WIDE: the launch for s > 32, which takes the blocked inversion for real
+// values (a kernel of its own: the blocked path's registers would cut the
+// occupancy of the launch of narrow supernodes)
+template <typename T, bool WIDE>
 __global__ void __launch_bounds__(kLinvThreads) k_linv(const ProbDesc *__restrict__ descs,
                                                        const int2 *__restrict__ work, int nwork,
                                                        size_t smem_cap, int with_dinv) {
@@ -108,7 +176,14 @@ __global__ void __launch_bounds__(kLinvThreads) k_linv(const ProbDesc *__restric
         if (in_smem) rD[j] = recip(D[j]);
     }
     __syncthreads();
-    for (int k = 0; k + 1 < s; k++) {
+    bool blocked = false;
+    if constexpr (WIDE && sizeof(T) == sizeof(double)) {
+        if (in_smem && s > 32) {
+            linv_blocked(reinterpret_cast<const double *>(L), ld, reinterpret_cast<double *>(X), lx, s);
+            blocked = true;
+        }
+    }
+    for (int k = 0; !blocked && k + 1 < s; k++) {
         const int m = s - 1 - k;                 // rows i = k+1 .. s-1
         for (int e = threadIdx.x; e < m * (k + 1); e += kLinvThreads) {
             const int i = k + 1 + e % m, j = e / m;
@@ -713,7 +788,8 @@ static cudaError_t launch_linv_t(const ProbDesc *d, const int2 *work, int nwork,
     if (nwork <= 0) return cudaSuccess;
     // small blocks (s <= 32) need at most 17 KB; large ones get room for s = 128 (real)
     const size_t cap = large ? kLinvSmemMax : (32 * 33 + 32) * sizeof(T);
-    k_linv<T><<<nwork, kLinvThreads, cap, st>>>(d, work, nwork, cap, with_dinv);
+    if (large) k_linv<T, true><<<nwork, kLinvThreads, cap, st>>>(d, work, nwork, cap, with_dinv);
+    else k_linv<T, false><<<nwork, kLinvThreads, cap, st>>>(d, work, nwork, cap, with_dinv);
     return cudaGetLastError();
 }
 
@@ -787,9 +863,9 @@ cudaError_t launch_selinv_persist(int dtype, const ProbDesc *d, const Item *item
 
 // opt every kernel in to its dynamic shared memory (outside any graph capture)
 cudaError_t configure_selinv_kernels() {
-    cudaError_t e = cudaFuncSetAttribute(k_linv<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kLinvSmemMax);
+    cudaError_t e = cudaFuncSetAttribute(k_linv<double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kLinvSmemMax);
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_linv<zd>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kLinvSmemMax);
+        e = cudaFuncSetAttribute(k_linv<zd, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kLinvSmemMax);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_selinv_persist<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)persist_smem<double>());
     if (e == cudaSuccess)

@@ -17,6 +17,7 @@
 #include "common.cuh"
 #include "fixedpoint.cuh"
 #include "launch.h"
+#include "diag_fin.cuh"
 #include "tile_gemm.cuh"
 
 namespace selinv {
@@ -81,12 +82,8 @@ __global__ void __launch_bounds__(256) k_lhat_digits_z(const ProbDesc *__restric
 // ---------------------------------------------------------------------------
 // k_diag_fin_z: A^{-1}_KK = Dinv_K - Lhat^T A^{-1}_{C,K} (complex) from the
 // exact sums of k_diag_tc, symmetrized with the plain transpose (Sec. II-C);
-// Hermitian: Dinv_K - Lhat^H A^{-1}_{C,K} (the sums are those of
-// Lhat^T conj(A^{-1}_{C,K}), conjugated here), symmetrized as (X + X^H) / 2.
-// Same structure as k_diag_fin: one CTA per 8 columns j, a warp per column,
-// lanes over rows i; entry (i, j) and its mirror come from the same sums in
-// the same order, so the block is exactly symmetric.  The sums hold
-// (Re hi, Re lo, Im hi, Im lo) per entry.
+// Hermitian: Dinv_K - Lhat^H A^{-1}_{C,K}, symmetrized as (X + X^H) / 2
+// (diag_fin_column).  One CTA per (K, 8 columns), a warp per column.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) k_diag_fin_z(const ProbDesc *__restrict__ descs,
                                                     const Item *__restrict__ items, int nitems) {
@@ -94,39 +91,9 @@ __global__ void __launch_bounds__(256) k_diag_fin_z(const ProbDesc *__restrict__
     if (w >= nitems) return;
     const Item it = items[w];
     const ProbDesc &P = descs[it.prob];
-    const int K = it.K;
-    const int fc = P.super_ptr[K];
-    const int s = P.super_ptr[K + 1] - fc;
-    const int64_t ld = P.rowptr[K + 1] - P.rowptr[K];
-    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-    const int j = it.tile * 8 + warp;
-    if (j >= s) return;
-    const double2 *LDk = static_cast<const double2 *>(P.LD) + P.panel_off[K];
-    double2 *Zk = static_cast<double2 *>(P.Z) + P.panel_off[K];
-    const long long *acc64 = P.dacc + 4 * P.linv_off[K];
-    const bool herm = P.herm;
-    auto prod = [&](int a, int b) -> double2 {   // (Lhat^T Y)(a, b), Hermitian: (Lhat^H Y)(a, b)
-        const long long *q = acc64 + 4 * ((int64_t)b * s + a);
-        const int ey = P.colexpY[fc + b];
-        if (ey == 0) return make_double2(0.0, 0.0);
-        const int sc = (P.colexp[fc + a] - 1022) + (ey - 1022) - 14 + 1;
-        const double im = fixed_to_double(q[2], q[3], sc);
-        return make_double2(fixed_to_double(q[0], q[1], sc), herm ? -im : im);
-    };
-    int mj = 0;
-    for (int i = lane; i < s; i += 32) {
-        const double2 d1 = LDk[(int64_t)j * ld + i], p1 = prod(i, j);
-        double2 x = make_double2(d1.x - p1.x, d1.y - p1.y);
-        if (P.symmetrize) {
-            const double2 d2 = LDk[(int64_t)i * ld + j], p2 = prod(j, i);
-            const double2 y = make_double2(d2.x - p2.x, herm ? -(d2.y - p2.y) : d2.y - p2.y);
-            x = make_double2(0.5 * (x.x + y.x), 0.5 * (x.y + y.y));
-        }
-        Zk[(int64_t)j * ld + i] = x;
-        mj = max(mj, max(bexp(x.x), bexp(x.y)));
-    }
-    mj = __reduce_max_sync(0xffffffffu, mj);
-    if (lane == 0) P.colexpZ[fc + j] = max(mj, P.colexpY[fc + j]);
+    const int s = P.super_ptr[it.K + 1] - P.super_ptr[it.K];
+    const int j = it.tile * 8 + threadIdx.x / 32;
+    if (j < s) diag_fin_column<true>(P, it.K, j, 1, threadIdx.x % 32);
 }
 
 cudaError_t launch_lhat_digits_z(const ProbDesc *d, const int2 *work, int nwork, cudaStream_t st) {

@@ -90,8 +90,15 @@ __device__ __forceinline__ void add_chunk(const uint32_t (&acc)[kTcDig][8], int 
 }
 
 // items: tile = (row tile * nmt + m tile) * nsplit + k-range, ntiles = nsplit;
-// nmt = ceil(rows of A / 128) (1 for real supernodes of <= 128 columns)
-template <bool CPLX>
+// nmt = ceil(rows of A / 128) (1 for real supernodes of <= 128 columns).
+//
+// LHAT: the same machinery forms Lhat_{C,K} = L_{C,K} L_KK^{-1} (Alg. 1,
+// first loop) for real supernodes wider than 64 columns: A = digit planes of
+// L_KK^{-1} transposed (rows = the columns j of K, k = the s columns of L_KK,
+// written by k_linv_digits in this operand layout), B = 64 rows of the dense
+// L_{C,K} (row exponent over the row's s entries), k = s: a single chunk, no
+// k-split.  The result goes to Lhat's slots of the LD panel.
+template <bool CPLX, bool LHAT = false>
 __global__ void __launch_bounds__(kTwThreads, 1) k_selinv_tcw(const ProbDesc *__restrict__ descs,
                                                               const Item *__restrict__ items, int nitems,
                                                               long long *__restrict__ slab, long long wait_limit) {
@@ -126,7 +133,7 @@ __global__ void __launch_bounds__(kTwThreads, 1) k_selinv_tcw(const ProbDesc *__
     const int s = P.super_ptr[K + 1] - fc;
     const int64_t ld = P.rowptr[K + 1] - P.rowptr[K];
     const int c = (int)(ld - s);
-    const int kw = CPLX ? 2 * c : c;                     // k extent
+    const int kw = LHAT ? s : (CPLX ? 2 * c : c);        // k extent
     const int mrows = CPLX ? 2 * s : s;                  // rows of A (output rows)
     const int s64 = (mrows + 63) / 64 * 64;              // operand rows of a stored digit block
     const int nmt = (mrows + kTcM - 1) / kTcM;
@@ -148,7 +155,7 @@ __global__ void __launch_bounds__(kTwThreads, 1) k_selinv_tcw(const ProbDesc *__
     // copies of the Lhat^T digit planes of step i_ (rows m0 .. m0 + 127 of
     // each stored block); the 7 planes of a step lie one after the other, so
     // a block of exactly 128 rows comes in one copy
-    const uint16_t *Au = P.lhsu + P.lhsu_off[K] + (int64_t)(m0 / 8) * 128;
+    const uint16_t *Au = (LHAT ? P.linvd + P.linvd_off[K] : P.lhsu + P.lhsu_off[K]) + (int64_t)(m0 / 8) * 128;
     const uint32_t aBytes = (uint32_t)(arows * 16 * 2);
     const bool whole = m0 == 0 && s64 == kTcM;
     auto load_a = [&](int i_) {
@@ -188,6 +195,8 @@ __global__ void __launch_bounds__(kTwThreads, 1) k_selinv_tcw(const ProbDesc *__
             for (int pl = 0; pl < kTcDig; pl++)
                 for (int e = arows * 16 + tid * 8; e < Cfg::A_PLANE; e += kTwThreads * 8)
                     *reinterpret_cast<uint4 *>(As + st * Cfg::A_STAGE + pl * Cfg::A_PLANE + e) = make_uint4(0, 0, 0, 0);
+    if (LHAT)
+        for (int e = tid; e < kTwN; e += kTwThreads) rowE[e] = 0;
     umma::fence_proxy_async();   // zeroed A rows are seen by the tensor cores
     __syncthreads();
     // the first copies (one per stage) go out before the rest of the set-up;
@@ -199,19 +208,27 @@ __global__ void __launch_bounds__(kTwThreads, 1) k_selinv_tcw(const ProbDesc *__
         for (int i_ = kTwAS; i_ < kTwPrefetch && i_ < n; i_++)
             umma::bulk_prefetch_l2(Au + (int64_t)(st0 + i_) * kTcDig * s64 * 16, kTcDig * aBytes);
     }
-    // row exponents of the gathered block: row p is bounded by the largest
-    // whole-column exponent of A^{-1} over C[0..p] (entry (p, q) sits in
-    // the ancestor column C[min(p, q)])
-    {
+    if constexpr (LHAT) {
+        // row exponents of L_{C,K}: row p over its s entries
+        const int r = tid % kTwN;
+        int e = 0;
+        if (p0 + r < c)
+            for (int k = tid / kTwN; k < s; k += kTwThreads / kTwN)
+                e = max(e, bexp(static_cast<const double *>(P.L)[P.panel_off[K] + (int64_t)k * ld + s + p0 + r]));
+        if (e) atomicMax(&rowE[r], e);
+    } else {
+        // row exponents of the gathered block: row p is bounded by the largest
+        // whole-column exponent of A^{-1} over C[0..p] (entry (p, q) sits in
+        // the ancestor column C[min(p, q)])
         int e = 0;
         for (int q = tid; q < p0 && q < c; q += kTwThreads) e = max(e, P.colexpZ[P.rows[pos0 + q]]);
         if (e) atomicMax(&s_pre, e);
-    }
-    for (int e = tid; e < kTwN; e += kTwThreads) {
-        const int p = p0 + e;
-        tile_cb[e] = p < c ? P.colbase[pos0 + p] : 0;
-        tile_rb[e] = p < c ? P.relbase[pos0 + p] : 0;
-        rowE[e] = p < c ? P.colexpZ[P.rows[pos0 + p]] : 0;
+        for (int i = tid; i < kTwN; i += kTwThreads) {
+            const int p = p0 + i;
+            tile_cb[i] = p < c ? P.colbase[pos0 + p] : 0;
+            tile_rb[i] = p < c ? P.relbase[pos0 + p] : 0;
+            rowE[i] = p < c ? P.colexpZ[P.rows[pos0 + p]] : 0;
+        }
     }
     // the sums are written by the first flush; an item without steps leaves zeros
     if (n == 0)
@@ -227,7 +244,7 @@ __global__ void __launch_bounds__(kTwThreads, 1) k_selinv_tcw(const ProbDesc *__
     umma::fence_before_sync();
     __syncthreads();
     umma::fence_after_sync();
-    if (warp == 0) {             // prefix max over the 64 rows
+    if (!LHAT && warp == 0) {    // prefix max over the 64 rows
         int carry = s_pre;
         for (int b = 0; b < kTwN; b += 32) {
             int v = max(rowE[b + lane], carry);
@@ -285,6 +302,16 @@ __global__ void __launch_bounds__(kTwThreads, 1) k_selinv_tcw(const ProbDesc *__
                 else { cb[u] = -1; rb[u] = 0; }
             }
         };
+        // LHAT: the 4 values of step i_ straight from the dense panel
+        const double *Lc = static_cast<const double *>(P.L) + P.panel_off[K] + s + p0 + r;   // L_C(p0 + r, k) = Lc[k ld]
+        const bool rok = p0 + r < c;
+        auto load_dense = [&](int i_) {
+#pragma unroll
+            for (int u = 0; u < 4; u++) {
+                const int k = (st0 + i_) * 16 + kq * 4 + u;
+                v[u] = (rok && i_ < n && k < s) ? Lc[(int64_t)k * ld] : 0.0;
+            }
+        };
         auto parts = [&](int i_) {
 #pragma unroll
             for (int u = 0; u < NV; u++) {
@@ -297,7 +324,9 @@ __global__ void __launch_bounds__(kTwThreads, 1) k_selinv_tcw(const ProbDesc *__
                 for (int u = 0; u < NV; u++)
                     if (ab[u] >= 0 && !g.chk.ok(ab[u] + ar[u])) ab[u] = -1;
         };
-        if (n > 0) {
+        if (LHAT) {
+            if (n > 0) load_dense(0);
+        } else if (n > 0) {
             cols(0);
             parts(0);
             load();
@@ -329,9 +358,13 @@ __global__ void __launch_bounds__(kTwThreads, 1) k_selinv_tcw(const ProbDesc *__
                 store_plane4<5>(dst + 5 * Cfg::B_PLANE, lo, hi);
                 store_plane4<6>(dst + 6 * Cfg::B_PLANE, lo, hi);
             }
-            load();            // values of step i + 1
-            parts(i_ + 2);     // relative rows of step i + 2
-            cols(i_ + 3);      // column data of step i + 3
+            if (LHAT) {
+                load_dense(i_ + 1);
+            } else {
+                load();            // values of step i + 1
+                parts(i_ + 2);     // relative rows of step i + 2
+                cols(i_ + 3);      // column data of step i + 3
+            }
             umma::fence_proxy_async();
             __syncwarp();
             if (lane == 0) umma::mbar_arrive(&full[stage]);
@@ -435,7 +468,18 @@ __global__ void __launch_bounds__(kTwThreads, 1) k_selinv_tcw(const ProbDesc *__
 
     // Y = -(A^{-1}_{C,C} Lhat): B digits on 2^(E - 1028 - 8i) of the row of
     // C, A digits on 2^(F - 1029 - 8j) of the column of K, so the value is
-    // (hi 2^-16 + lo 2^-48) 2^(E + F - 2057)
+    // (hi 2^-16 + lo 2^-48) 2^(E + F - 2057); LHAT: Lhat = L_{C,K} L_KK^{-1}
+    // on the same grids (F: the column exponent of L_KK^{-1})
+    if constexpr (LHAT) {
+        double *Lh = static_cast<double *>(P.LD) + P.panel_off[K];
+        for (int e = tid; e < kTwN * kTcM; e += kTwThreads) {
+            const int p = e % kTwN, j = e / kTwN;
+            if (p0 + p >= c || j >= s) continue;
+            const int sc = (rowE[p] - 1022) + (P.linvexp[fc + j] - 1022) - 13;
+            Lh[(int64_t)j * ld + s + p0 + p] = fixed_to_double(Hi[p * kTwHS + j], (long long)Lo[p * kTwHS + j], sc);
+        }
+        return;
+    }
     if (nsplit == 1) {
         double *Zk = static_cast<double *>(P.Yout) + (CPLX ? 2 : 1) * P.panel_off[K];
         for (int e = tid; e < kTwN * kTcM; e += kTwThreads) {
@@ -529,6 +573,9 @@ cudaError_t configure_tcw_kernels() {
                                          (int)TwCfg::SMEM);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_selinv_tcw<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TwCfg::SMEM);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_selinv_tcw<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)TwCfg::SMEM);
     return e;
 }
 
@@ -537,6 +584,12 @@ cudaError_t launch_selinv_tcw(int cplx, const ProbDesc *d, const Item *items, in
     if (n <= 0) return cudaSuccess;
     if (cplx) k_selinv_tcw<true><<<n, kTwThreads, TwCfg::SMEM, st>>>(d, items, n, slab, wait_limit);
     else k_selinv_tcw<false><<<n, kTwThreads, TwCfg::SMEM, st>>>(d, items, n, slab, wait_limit);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_lhat_tcw(const ProbDesc *d, const Item *items, int n, long long wait_limit, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    k_selinv_tcw<false, true><<<n, kTwThreads, TwCfg::SMEM, st>>>(d, items, n, nullptr, wait_limit);
     return cudaGetLastError();
 }
 

@@ -103,6 +103,7 @@ int Workspace::ensure(const PlanData &p, int dtype) {
     if (!wget(*this, &linvexp, sizeof(int) * (size_t)std::max(p.n, 1))) return SELINV_ERR_OOM;
     if (!wget(*this, &linvd, sizeof(uint16_t) * (size_t)std::max<int64_t>(p.linvd_total, 8)))
         return SELINV_ERR_OOM;
+    cudaMemset(linvd, 0, sizeof(uint16_t) * (size_t)std::max<int64_t>(p.linvd_total, 8));   // padding rows stay zero
     cudaMemset(colexpZ, 0, sizeof(int) * (size_t)std::max(p.n, 1));
     const size_t ny = (dtype == SELINV_F64 && p.lhs_total > 0) ? 2 * (size_t)p.nnz : 2;
     if (!wget(*this, &yacc, sizeof(long long) * ny)) return SELINV_ERR_OOM;
@@ -328,7 +329,10 @@ static int build_plan(PlanData &p, int32_t n, int32_t ns, const int32_t *super_p
     p.linvd_off.assign(ns + 1, 0);
     for (int32_t K = 0; K < ns; K++) {
         const int64_t s = super_ptr[K + 1] - super_ptr[K];
-        p.linvd_off[K + 1] = p.linvd_off[K] + (s >= kOzMinS ? 7 * s * ((s + 15) / 16 * 16) : 0);
+        // supernodes wider than 64 columns may hold the tcgen05 operand layout
+        // (rows padded to 128) for the transposed Lhat product
+        const int64_t rows = s > 64 ? (s + 63) / 64 * 64 : s;
+        p.linvd_off[K + 1] = p.linvd_off[K] + (s >= kOzMinS ? 7 * rows * ((s + 15) / 16 * 16) : 0);
     }
     p.linvd_total = p.linvd_off[ns];
     p.tile_base.assign(ns + 1, 0);
@@ -482,6 +486,8 @@ int build_schedule(Schedule &S, const std::vector<const PlanData *> &plans,
     auto act = [&](int i, int32_t K) { return plans[i]->active.empty() || plans[i]->active[K] != 0; };
     // tensor-core contraction for this problem and width (never for the LU form)
     auto ozok = [&](int i, int s) { return !descs[i].lu && oz_eligible(descs[i].dtype, s, plans[i]->opts); };
+    // Lhat of a tensor-core supernode wider than 64 columns: the transposed tcgen05 kernel
+    auto lhat_tc = [&](int i, int s) { return plans[i]->opts.fast_contraction == 1 && s > 64; };
     // complex supernodes (symmetric or Hermitian) on tcgen05 (the transposed
     // gather-GEMM and the diagonal block over the real 2c-long contraction;
     // level and plain schedules, not the LU form; their Lhat stays on the FP64 pipe)
@@ -534,11 +540,28 @@ int build_schedule(Schedule &S, const std::vector<const PlanData *> &plans,
                 const int s = p.super_ptr[K + 1] - p.super_ptr[K];
                 const int64_t c = p.rowptr[K + 1] - p.rowptr[K] - s;
                 if (c == 0 || !act(i, K) || !ozok(i, s)) continue;
-                for (int jb = 0; jb < (s + 7) / 8; jb++) S.h_work.push_back(make_int2(i, (K << 8) | jb));
+                // bit 7: the tcgen05 operand layout, for the transposed Lhat product
+                const int tcl = lhat_tc(i, s) ? 0x80 : 0;
+                for (int jb = 0; jb < (s + 7) / 8; jb++) S.h_work.push_back(make_int2(i, (K << 8) | tcl | jb));
             }
         }
         const int cnt = (int)(S.h_work.size() - off);
         if (cnt) S.launches.push_back({KL_LINV_DIGITS, SELINV_F64, 0, off, cnt, -1});
+    }
+    {
+        // Lhat of the supernodes wider than 64 columns on tcgen05: (K, 64-row tile) items
+        const int64_t off = (int64_t)S.h_items.size();
+        for (int i = 0; i < np; i++) {
+            const PlanData &p = *plans[i];
+            for (int32_t K = 0; K < p.ns; K++) {
+                const int s = p.super_ptr[K + 1] - p.super_ptr[K];
+                const int64_t c = p.rowptr[K + 1] - p.rowptr[K] - s;
+                if (c == 0 || !act(i, K) || !ozok(i, s) || !lhat_tc(i, s)) continue;
+                for (int64_t t = 0; t < (c + kTcWideRows - 1) / kTcWideRows; t++) S.h_items.push_back({i, K, (int)t, 1});
+            }
+        }
+        const int cnt = (int)(S.h_items.size() - off);
+        if (cnt) S.launches.push_back({KL_LHAT_OZ, SELINV_F64, kTcWide, off, cnt, -1});
     }
     for (int tn : {64, 32, 16}) {
         const int64_t off = (int64_t)S.h_items.size();
@@ -547,7 +570,7 @@ int build_schedule(Schedule &S, const std::vector<const PlanData *> &plans,
             for (int32_t K = 0; K < p.ns; K++) {
                 const int s = p.super_ptr[K + 1] - p.super_ptr[K];
                 const int64_t c = p.rowptr[K + 1] - p.rowptr[K] - s;
-                if (c == 0 || !act(i, K) || !ozok(i, s)) continue;
+                if (c == 0 || !act(i, K) || !ozok(i, s) || lhat_tc(i, s)) continue;
                 const int ktn = s <= 16 ? 16 : 32;   // 32-column tiles: two CTAs per SM
                 if (ktn != tn) continue;
                 const int ncol = (s + tn - 1) / tn;
@@ -585,7 +608,10 @@ int build_schedule(Schedule &S, const std::vector<const PlanData *> &plans,
                 if (c == 0 || !act(i, K) || mode == SELINV_SCHED_PERSISTENT || mode == SELINV_SCHED_PUSH ||
                     !ozok(i, s))
                     continue;
-                for (int jb = 0; jb < (s + 7) / 8; jb++) S.h_work.push_back(make_int2(i, (K << 8) | jb));
+                // bit 7: only the tcgen05 layout is read (tcgen05 gather-GEMM and
+                // diagonal block); the mma.sync kernels read the other one
+                const int only_u = p.opts.fast_contraction == 1 && s > 32 ? 0x80 : 0;
+                for (int jb = 0; jb < (s + 7) / 8; jb++) S.h_work.push_back(make_int2(i, (K << 8) | only_u | jb));
             }
         }
         const int cnt = (int)(S.h_work.size() - off);
@@ -1079,7 +1105,9 @@ cudaError_t launch_with(const Schedule &S, const Launch &L, const ProbDesc *d, c
     case KL_SELINV_OZ: return launch_selinv_oz(L.bucket, d, S.d_items + L.off, L.count, st);
     case KL_DIAG: return launch_diag_oz(d, S.d_items + L.off, L.count, st);
     case KL_LINV_DIGITS: return launch_linv_digits(d, S.d_work + L.off, L.count, st);
-    case KL_LHAT_OZ: return launch_lhat_oz(L.bucket, d, S.d_items + L.off, L.count, st);
+    case KL_LHAT_OZ:
+        if (L.bucket == kTcWide) return launch_lhat_tcw(d, S.d_items + L.off, L.count, S.spin_limit, st);
+        return launch_lhat_oz(L.bucket, d, S.d_items + L.off, L.count, st);
     case KL_SELINV_TC:
         if (L.bucket == kTcWide)
             return launch_selinv_tcw(L.dtype != SELINV_F64, d, S.d_items + L.off, L.count, S.tcslab, S.spin_limit, st);
