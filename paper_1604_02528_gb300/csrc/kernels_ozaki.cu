@@ -37,10 +37,13 @@ constexpr int kOzThreads = 256;
 // k_lhat_digits: digit planes of Lhat_{C,K} (per column j: exponent over all
 // q) in the tcgen05 operand layout and, unless the work item says that only
 // that one is read, in the mma.sync layout plane[j][q] (q contiguous, padded
-// to c16 with zeros).  One warp per column.
+// to c16 with zeros).  One CTA per 8 columns: a warp per column finds its
+// exponent, then each thread cuts 8 consecutive q of one column, whose digits
+// of a plane are one 16-byte store in both layouts.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) k_lhat_digits(const ProbDesc *__restrict__ descs,
                                                      const int2 *__restrict__ work, int nwork) {
+    __shared__ int colE[8];
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
     const int w = blockIdx.x;
     if (w >= nwork) return;
@@ -53,14 +56,20 @@ __global__ void __launch_bounds__(256) k_lhat_digits(const ProbDesc *__restrict_
     const int64_t ld = P.rowptr[K + 1] - P.rowptr[K];
     const int c = (int)(ld - s);
     const int c16 = (c + 15) & ~15;
-    const int j = jb * 8 + warp;
-    if (j >= s) return;
-    const double *Lh = static_cast<const double *>(P.LD) + P.panel_off[K] + (int64_t)j * ld + s;
-    int E = 0;
-    for (int q = lane; q < c; q += 32) E = max(E, bexp(Lh[q]));
+    const int j0 = jb * 8, nj = s - j0 < 8 ? s - j0 : 8;
+    const double *LDk = static_cast<const double *>(P.LD) + P.panel_off[K] + s;   // Lhat(q, j) = LDk[j*ld + q]
+    if (warp < nj) {
+        const double *Lh = LDk + (int64_t)(j0 + warp) * ld;
+        int E = 0;
+        for (int q = lane; q < c; q += 32) E = max(E, bexp(Lh[q]));
 #pragma unroll
-    for (int o = 16; o; o >>= 1) E = max(E, __shfl_xor_sync(0xffffffffu, E, o));
-    if (lane == 0) P.colexp[fc + j] = E;
+        for (int o = 16; o; o >>= 1) E = max(E, __shfl_xor_sync(0xffffffffu, E, o));
+        if (lane == 0) {
+            colE[warp] = E;
+            P.colexp[fc + j0 + warp] = E;
+        }
+    }
+    __syncthreads();
     uint16_t *pl = P.lhs + P.lhs_off[K];
     const int64_t plane = (int64_t)s * c16;
     // tcgen05 layout: block (step, plane) of s64 x 16 (the 7 planes of a step
@@ -68,19 +77,25 @@ __global__ void __launch_bounds__(256) k_lhat_digits(const ProbDesc *__restrict_
     // (q % 16) / 8 at 64, row j % 8 at 8, q % 8
     uint16_t *pu = P.lhsu + P.lhsu_off[K];
     const int64_t s64 = (s + 63) / 64 * 64;
-    for (int q = lane; q < c16; q += 32) {
-        int d[kDig];
-        if (q < c) digits7(Lh[q], E, d);
-        else {
+    for (int e = threadIdx.x; e < 8 * (c16 / 8); e += 256) {
+        const int jl = e % 8, q0 = (e / 8) * 8, j = j0 + jl;
+        if (jl >= nj) continue;
+        const double *Lh = LDk + (int64_t)j * ld;
+        uint32_t h[kDig][4];
 #pragma unroll
-            for (int i = 0; i < kDig; i++) d[i] = 0;
+        for (int t = 0; t < 8; t += 2) {
+            int d0[kDig], d1[kDig];
+            digits7(q0 + t < c ? Lh[q0 + t] : 0.0, colE[jl], d0);
+            digits7(q0 + t + 1 < c ? Lh[q0 + t + 1] : 0.0, colE[jl], d1);
+#pragma unroll
+            for (int i = 0; i < kDig; i++) h[i][t / 2] = f16_of_int(d0[i]) | (f16_of_int(d1[i]) << 16);
         }
-        const int64_t ub = (int64_t)(q / 16) * kDig * s64 * 16 + (j / 8) * 128 + ((q % 16) / 8) * 64 + (j % 8) * 8 + q % 8;
+        const int64_t ub = (int64_t)(q0 / 16) * kDig * s64 * 16 + (j / 8) * 128 + ((q0 % 16) / 8) * 64 + (j % 8) * 8;
 #pragma unroll
         for (int i = 0; i < kDig; i++) {
-            const uint16_t h = (uint16_t)f16_of_int(d[i]);
-            if (both) pl[i * plane + (int64_t)j * c16 + q] = h;
-            pu[i * s64 * 16 + ub] = h;
+            const uint4 v = make_uint4(h[i][0], h[i][1], h[i][2], h[i][3]);
+            *reinterpret_cast<uint4 *>(pu + i * s64 * 16 + ub) = v;
+            if (both) *reinterpret_cast<uint4 *>(pl + i * plane + (int64_t)j * c16 + q0) = v;
         }
     }
 }
@@ -670,17 +685,17 @@ __global__ void __launch_bounds__(kOzThreads, 1) k_diag_oz(const ProbDesc *__res
 // ---------------------------------------------------------------------------
 // k_diag_fin: A^{-1}_KK = Dinv_K - Lhat^T Y from the exact sums of k_diag_oz
 // (bshift 0) or k_diag_tc (bshift 1), symmetrized: one CTA per (K, 8 columns),
-// a warp per column (diag_fin_column).  items: (K, column block) per supernode.
+// a warp per column (diag_fin_column).  items: (K, column block, bshift).
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) k_diag_fin(const ProbDesc *__restrict__ descs,
-                                                  const Item *__restrict__ items, int nitems, int bshift) {
+                                                  const Item *__restrict__ items, int nitems) {
     const int w = blockIdx.x;
     if (w >= nitems) return;
     const Item it = items[w];
     const ProbDesc &P = descs[it.prob];
     const int s = P.super_ptr[it.K + 1] - P.super_ptr[it.K];
     const int j = it.tile * 8 + threadIdx.x / 32;
-    if (j < s) diag_fin_column<false>(P, it.K, j, bshift, threadIdx.x % 32);
+    if (j < s) diag_fin_column<false>(P, it.K, j, it.ntiles, threadIdx.x % 32);
 }
 
 constexpr size_t diag_oz_smem() {
@@ -693,9 +708,9 @@ cudaError_t launch_diag_oz(const ProbDesc *d, const Item *items, int n, cudaStre
     return cudaGetLastError();
 }
 
-cudaError_t launch_diag_fin(const ProbDesc *d, const Item *items, int n, int bshift, cudaStream_t st) {
+cudaError_t launch_diag_fin(const ProbDesc *d, const Item *items, int n, cudaStream_t st) {
     if (n <= 0) return cudaSuccess;
-    k_diag_fin<<<n, 256, 0, st>>>(d, items, n, bshift);
+    k_diag_fin<<<n, 256, 0, st>>>(d, items, n);
     return cudaGetLastError();
 }
 

@@ -73,76 +73,8 @@ __device__ void linv_lu(const ProbDesc &P, int K, int s, int64_t ld, const T *L,
     }
 }
 
-// X = L_KK^{-1} (unit lower, s > 32) in shared memory by 32 x 32 blocks, in
-// ceil(s/32) dependent phases instead of s - 1: with L_ij the blocks of L_KK
-// and X_ij those of X,
-//   X_ii = L_ii^{-1}                                   (all i at once)
-//   X_ij = -X_ii sum_{k = j..i-1} L_ik X_kj,  j < i     (block row i after rows < i)
-// A diagonal block is inverted by one warp, lane c owning column c in
-// registers (column-oriented substitution: no synchronization); an
-// off-diagonal block row is a product with the finished rows above it, then
-// a product with X_ii.  Rows and columns past s act as the identity.  X must
-// hold the identity on entry.
-__device__ void linv_blocked(const double *__restrict__ L, int64_t ld, double *X, int lx, int s) {
-    const int nb = (s + 31) / 32;
-    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-    for (int b = warp; b < nb; b += kLinvThreads / 32) {
-        const int o = 32 * b, n = min(32, s - o);
-        const double *Lb = L + (int64_t)o * ld + o;   // L_bb(i, k) = Lb[k * ld + i]
-        double x[32];
-#pragma unroll
-        for (int i = 0; i < 32; i++) x[i] = i == lane ? 1.0 : 0.0;
-#pragma unroll
-        for (int k = 0; k < 31; k++) {
-            if (k + 1 < n) {
-#pragma unroll
-                for (int i = k + 1; i < 32; i++)
-                    if (i < n) x[i] = fma(-Lb[(int64_t)k * ld + i], x[k], x[i]);
-            }
-        }
-        if (lane < n) {
-#pragma unroll
-            for (int i = 0; i < 32; i++)
-                if (i < n) X[(o + lane) * lx + o + i] = x[i];
-        }
-    }
-    __syncthreads();
-    for (int bi = 1; bi < nb; bi++) {
-        const int oi = 32 * bi, ni = min(32, s - oi);
-        // T = sum_k L_ik X_kj for every column j < oi, into X's block row i
-        for (int e = threadIdx.x; e < oi * 32; e += kLinvThreads) {
-            const int r = e % 32, col = e / 32;
-            if (r < ni) {
-                double acc = 0.0;
-                for (int t = col; t < oi; t++) acc = fma(L[(int64_t)t * ld + oi + r], X[col * lx + t], acc);
-                X[col * lx + oi + r] = acc;
-            }
-        }
-        __syncthreads();
-        // X_ij = -X_ii T, a column of T per thread
-        for (int col = threadIdx.x; col < oi; col += kLinvThreads) {
-            double tv[32];
-#pragma unroll
-            for (int r = 0; r < 32; r++) tv[r] = r < ni ? X[col * lx + oi + r] : 0.0;
-#pragma unroll
-            for (int r = 0; r < 32; r++) {
-                if (r < ni) {
-                    double acc = 0.0;
-#pragma unroll
-                    for (int t = 0; t <= r; t++) acc = fma(X[(oi + t) * lx + oi + r], tv[t], acc);
-                    X[col * lx + oi + r] = -acc;
-                }
-            }
-        }
-        __syncthreads();
-    }
-}
-
-// with_dinv = 0: only L_KK^{-1} (k_dinv forms Dinv_K afterwards, spread over tiles).
-// WIDE: the launch for s > 32, which takes the blocked inversion for real
-// values (a kernel of its own: the blocked path's registers would cut the
-// occupancy of the launch of narrow supernodes)
-template <typename T, bool WIDE>
+// with_dinv = 0: only L_KK^{-1} (k_dinv forms Dinv_K afterwards, spread over tiles)
+template <typename T>
 __global__ void __launch_bounds__(kLinvThreads) k_linv(const ProbDesc *__restrict__ descs,
                                                        const int2 *__restrict__ work, int nwork,
                                                        size_t smem_cap, int with_dinv) {
@@ -176,14 +108,7 @@ __global__ void __launch_bounds__(kLinvThreads) k_linv(const ProbDesc *__restric
         if (in_smem) rD[j] = recip(D[j]);
     }
     __syncthreads();
-    bool blocked = false;
-    if constexpr (WIDE && sizeof(T) == sizeof(double)) {
-        if (in_smem && s > 32) {
-            linv_blocked(reinterpret_cast<const double *>(L), ld, reinterpret_cast<double *>(X), lx, s);
-            blocked = true;
-        }
-    }
-    for (int k = 0; !blocked && k + 1 < s; k++) {
+    for (int k = 0; k + 1 < s; k++) {
         const int m = s - 1 - k;                 // rows i = k+1 .. s-1
         for (int e = threadIdx.x; e < m * (k + 1); e += kLinvThreads) {
             const int i = k + 1 + e % m, j = e / m;
@@ -582,8 +507,10 @@ __global__ void __launch_bounds__(kThreads) k_push(const ProbDesc *__restrict__ 
 // columns and c <= 64 rows below them, one warp per supernode (eight per CTA):
 // the deep levels of a nested-dissection tree hold thousands of these, for
 // which a CTA per row tile is mostly synchronisation.  Lane l owns rows l and
-// l + 32 of A^{-1}_{C,K} = -A^{-1}_{C,C} Lhat (the gather as in k_selinv, four
-// entries in flight, Lhat rows broadcast); each entry of the s x s diagonal
+// l + 32 of A^{-1}_{C,K} = -A^{-1}_{C,C} Lhat (the gather as in k_selinv,
+// 16 columns of C at a time with all their loads in flight -- the kernel is
+// bound by the latency of the gathers' dependent loads --, Lhat rows
+// broadcast); each entry of the s x s diagonal
 // block Dinv - Lhat^T A^{-1}_{C,K} is a warp sum over the lanes' own rows,
 // symmetrized through shared memory.  Writes the whole-column exponents for
 // the row bounds of later tensor-core gathers.
@@ -597,70 +524,93 @@ __device__ __forceinline__ double warp_sum(double v) {
 }
 __device__ __forceinline__ zd warp_sum(zd v) { return make_zd(warp_sum(v.x), warp_sum(v.y)); }
 
-template <typename T>
-__global__ void __launch_bounds__(256) k_selinv_tiny(const ProbDesc *__restrict__ descs,
-                                                     const Item *__restrict__ items, int nitems) {
-    __shared__ T Xs[8][kTinyS * kTinyS];   // per warp: the unsymmetrized diagonal block
-    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-    const int w = blockIdx.x * 8 + warp;
-    if (w >= nitems) return;               // the whole warp
-    const Item it = items[w];
-    const ProbDesc &P = descs[it.prob];
-    const int K = it.K;
+// The supernode's work with its width S known at compile time, and nr = 1
+// or 2 row groups of 32 (c <= 32 or c <= 64): no product term is spent on
+// columns past s or rows past c (the kernel is bound by the FP64 pipe).
+template <typename T, int S>
+__device__ __forceinline__ void tiny_one(const ProbDesc &P, const int K, const int lane, T *Xw) {
     const int fc = P.super_ptr[K];
-    const int s = P.super_ptr[K + 1] - fc;
+    const int s = S;
     const int64_t ld = P.rowptr[K + 1] - P.rowptr[K];
     const int c = (int)(ld - s);
+    const int nr = c > 32 ? 2 : 1;
     const int64_t pos0 = P.rowptr[K] + s;
     const bool h = P.herm != 0;
     const T *Zc = static_cast<const T *>(P.Z);
     T *Zk = static_cast<T *>(P.Z) + P.panel_off[K];
     const T *LDk = static_cast<const T *>(P.LD) + P.panel_off[K];
     const int64_t *pcb = P.colbase + pos0, *prb = P.relbase + pos0;
-    T acc[2][kTinyS];
+    T acc[2][S];
 #pragma unroll
     for (int r = 0; r < 2; r++)
 #pragma unroll
-        for (int j = 0; j < kTinyS; j++) acc[r][j] = Sc<T>::zero();
-    // four q at a time: their gathers are in flight together
+        for (int j = 0; j < S; j++) acc[r][j] = Sc<T>::zero();
+    // the column data of C, lane l holding positions l and l + 32 (the lanes'
+    // own rows p use theirs for the entries above the diagonal); then QB
+    // columns q at a time: all their relative rows in flight together, then
+    // all their values
     const GatherCheck chk = gather_check(P);
-    for (int q0 = 0; q0 < c; q0 += 4) {
-        T v[2][4];
+    int64_t cbq[2] = {0, 0}, rbq[2] = {0, 0};
 #pragma unroll
-        for (int u = 0; u < 4; u++)
+    for (int r = 0; r < 2; r++)
+        if (lane + 32 * r < c) {
+            cbq[r] = pcb[lane + 32 * r];
+            rbq[r] = prb[lane + 32 * r];
+        }
+    constexpr int QB = sizeof(T) == sizeof(double) ? 16 : 4;
+    for (int q0 = 0; q0 < c; q0 += QB) {
+        int32_t rel[2][QB];
+#pragma unroll
+        for (int u = 0; u < QB; u++) {
+            const int q = q0 + u;   // the same in every lane
+            const int64_t rq = __shfl_sync(0xffffffffu, q < 32 ? rbq[0] : rbq[1], q & 31);
 #pragma unroll
             for (int r = 0; r < 2; r++) {
-                const int p = lane + 32 * r, q = q0 + u;
+                const int p = lane + 32 * r;
+                // entry (p, q) of A^{-1}_{C,C}: stored at (max, min)
+                rel[r][u] = (p < c && q < c) ? P.relidx[p >= q ? rq + p : rbq[r] + q] : 0;
+            }
+        }
+        T v[2][QB];
+#pragma unroll
+        for (int u = 0; u < QB; u++) {
+            const int q = q0 + u;
+            const int64_t cq = __shfl_sync(0xffffffffu, q < 32 ? cbq[0] : cbq[1], q & 31);
+#pragma unroll
+            for (int r = 0; r < 2; r++) {
+                const int p = lane + 32 * r;
                 v[r][u] = Sc<T>::zero();
                 if (p >= c || q >= c) continue;
-                // entry (p, q) of A^{-1}_{C,C}: stored at (max, min)
-                const int64_t addr = p >= q ? pcb[q] + P.relidx[prb[q] + p] : pcb[p] + P.relidx[prb[p] + q];
+                const int64_t addr = (p >= q ? cq : cbq[r]) + rel[r][u];
                 if (chk.ok(addr)) v[r][u] = Zc[addr];
                 if (p < q) v[r][u] = cjif(v[r][u], h);
             }
+        }
 #pragma unroll
-        for (int u = 0; u < 4; u++) {
+        for (int u = 0; u < QB; u++) {
             const int q = q0 + u;
             if (q >= c) break;
-            T lh[kTinyS];
+            T lh[S];
 #pragma unroll
-            for (int j = 0; j < kTinyS; j++) lh[j] = j < s ? LDk[(int64_t)j * ld + s + q] : Sc<T>::zero();
+            for (int j = 0; j < S; j++) lh[j] = LDk[(int64_t)j * ld + s + q];
 #pragma unroll
-            for (int r = 0; r < 2; r++)
+            for (int r = 0; r < 2; r++) {
+                if (r >= nr) break;
 #pragma unroll
-                for (int j = 0; j < kTinyS; j++) madd(acc[r][j], v[r][u], lh[j]);
+                for (int j = 0; j < S; j++) madd(acc[r][j], v[r][u], lh[j]);
+            }
         }
     }
     // A^{-1}_{C,K} = -acc, written; the lanes' own Lhat rows for the diagonal block
-    T own[2][kTinyS];
-    int ye[kTinyS];
+    T own[2][S];
+    int ye[S];
 #pragma unroll
-    for (int j = 0; j < kTinyS; j++) {
+    for (int j = 0; j < S; j++) {
         int e = 0;
 #pragma unroll
         for (int r = 0; r < 2; r++) {
             const int p = lane + 32 * r;
-            const bool ok = p < c && j < s;
+            const bool ok = p < c;
             acc[r][j] = ok ? neg(acc[r][j]) : Sc<T>::zero();
             own[r][j] = ok ? cjif(LDk[(int64_t)j * ld + s + p], h) : Sc<T>::zero();
             if (ok) {
@@ -672,22 +622,24 @@ __global__ void __launch_bounds__(256) k_selinv_tiny(const ProbDesc *__restrict_
     }
     // X(i, j) = Dinv(i, j) - sum_p Lhat(p, i) A^{-1}_{C,K}(p, j)  (Lhat conjugated: Hermitian)
 #pragma unroll
-    for (int i = 0; i < kTinyS; i++)
+    for (int i = 0; i < S; i++)
 #pragma unroll
-        for (int j = 0; j < kTinyS; j++) {
-            if (i >= s || j >= s) continue;
+        for (int j = 0; j < S; j++) {
             T part = Sc<T>::zero();
 #pragma unroll
-            for (int r = 0; r < 2; r++) madd(part, own[r][i], acc[r][j]);
+            for (int r = 0; r < 2; r++) {
+                if (r >= nr) break;
+                madd(part, own[r][i], acc[r][j]);
+            }
             part = warp_sum(part);
-            if (lane == 0) Xs[warp][j * kTinyS + i] = sub(LDk[(int64_t)j * ld + i], part);
+            if (lane == 0) Xw[j * kTinyS + i] = sub(LDk[(int64_t)j * ld + i], part);
         }
     __syncwarp();
     int ze = 0;
     for (int e = lane; e < s * s; e += 32) {
         const int i = e % s, j = e / s;
-        T x = Xs[warp][j * kTinyS + i];
-        if (P.symmetrize) x = half(add(x, cjif(Xs[warp][i * kTinyS + j], h)));
+        T x = Xw[j * kTinyS + i];
+        if (P.symmetrize) x = half(add(x, cjif(Xw[i * kTinyS + j], h)));
         Zk[(int64_t)j * ld + i] = x;
         ze = max(ze, bexp(x));
     }
@@ -697,9 +649,31 @@ __global__ void __launch_bounds__(256) k_selinv_tiny(const ProbDesc *__restrict_
     if (lane < s) {
         int y = 0;
 #pragma unroll
-        for (int j = 0; j < kTinyS; j++)
+        for (int j = 0; j < S; j++)
             if (j == lane) y = ye[j];
         P.colexpZ[fc + lane] = max(ze, y);
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_selinv_tiny(const ProbDesc *__restrict__ descs,
+                                                     const Item *__restrict__ items, int nitems) {
+    __shared__ T Xs[8][kTinyS * kTinyS];   // per warp: the unsymmetrized diagonal block
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    const int w = blockIdx.x * 8 + warp;
+    if (w >= nitems) return;               // the whole warp
+    const Item it = items[w];
+    const ProbDesc &P = descs[it.prob];
+    const int K = it.K;
+    switch (P.super_ptr[K + 1] - P.super_ptr[K]) {
+    case 1: tiny_one<T, 1>(P, K, lane, Xs[warp]); break;
+    case 2: tiny_one<T, 2>(P, K, lane, Xs[warp]); break;
+    case 3: tiny_one<T, 3>(P, K, lane, Xs[warp]); break;
+    case 4: tiny_one<T, 4>(P, K, lane, Xs[warp]); break;
+    case 5: tiny_one<T, 5>(P, K, lane, Xs[warp]); break;
+    case 6: tiny_one<T, 6>(P, K, lane, Xs[warp]); break;
+    case 7: tiny_one<T, 7>(P, K, lane, Xs[warp]); break;
+    default: tiny_one<T, 8>(P, K, lane, Xs[warp]); break;
     }
 }
 
@@ -788,8 +762,7 @@ static cudaError_t launch_linv_t(const ProbDesc *d, const int2 *work, int nwork,
     if (nwork <= 0) return cudaSuccess;
     // small blocks (s <= 32) need at most 17 KB; large ones get room for s = 128 (real)
     const size_t cap = large ? kLinvSmemMax : (32 * 33 + 32) * sizeof(T);
-    if (large) k_linv<T, true><<<nwork, kLinvThreads, cap, st>>>(d, work, nwork, cap, with_dinv);
-    else k_linv<T, false><<<nwork, kLinvThreads, cap, st>>>(d, work, nwork, cap, with_dinv);
+    k_linv<T><<<nwork, kLinvThreads, cap, st>>>(d, work, nwork, cap, with_dinv);
     return cudaGetLastError();
 }
 
@@ -863,9 +836,9 @@ cudaError_t launch_selinv_persist(int dtype, const ProbDesc *d, const Item *item
 
 // opt every kernel in to its dynamic shared memory (outside any graph capture)
 cudaError_t configure_selinv_kernels() {
-    cudaError_t e = cudaFuncSetAttribute(k_linv<double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kLinvSmemMax);
+    cudaError_t e = cudaFuncSetAttribute(k_linv<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kLinvSmemMax);
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_linv<zd, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kLinvSmemMax);
+        e = cudaFuncSetAttribute(k_linv<zd>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kLinvSmemMax);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_selinv_persist<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)persist_smem<double>());
     if (e == cudaSuccess)

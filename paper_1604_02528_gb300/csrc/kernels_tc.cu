@@ -239,12 +239,14 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_selinv_tc(const ProbDesc *__r
                 store_plane4<5>(dst + 5 * Cfg::A_PLANE, lo, hi);
                 store_plane4<6>(dst + 6 * Cfg::A_PLANE, lo, hi);
             }
-            load();            // values of step i + 1
-            parts(i_ + 2);     // relative rows of step i + 2
-            cols(i_ + 3);      // column data of step i + 3
+            // release the step's operand first: the loads of later steps are
+            // issued after the arrival, not between the stores and the fence
             umma::fence_proxy_async();
             __syncwarp();
             if (lane == 0) umma::mbar_arrive(&full[stage]);
+            load();            // values of step i + 1
+            parts(i_ + 2);     // relative rows of step i + 2
+            cols(i_ + 3);      // column data of step i + 3
             if (s_abort) break;
         }
     } else if (warp == kTcMmaWarp) {
@@ -606,10 +608,10 @@ __global__ void __launch_bounds__(kDtThreads, 1) k_diag_tc(const ProbDesc *__res
                 store_plane4<5>(dst + 5 * Cfg::B_PLANE, lo, hi);
                 store_plane4<6>(dst + 6 * Cfg::B_PLANE, lo, hi);
             }
-            if (i_ + 1 < n) fetch(st0 + i_ + 1);
             umma::fence_proxy_async();
             __syncwarp();
             if (lane == 0) umma::mbar_arrive(&full[stage]);
+            if (i_ + 1 < n) fetch(st0 + i_ + 1);   // after the arrival (see k_selinv_tc)
             if (s_abort) break;
         }
     } else if (warp == kDtMmaWarp) {

@@ -358,6 +358,11 @@ __global__ void __launch_bounds__(kTwThreads, 1) k_selinv_tcw(const ProbDesc *__
                 store_plane4<5>(dst + 5 * Cfg::B_PLANE, lo, hi);
                 store_plane4<6>(dst + 6 * Cfg::B_PLANE, lo, hi);
             }
+            // release the step's operand first: the loads of later steps are
+            // issued after the arrival, not between the stores and the fence
+            umma::fence_proxy_async();
+            __syncwarp();
+            if (lane == 0) umma::mbar_arrive(&full[stage]);
             if (LHAT) {
                 load_dense(i_ + 1);
             } else {
@@ -365,9 +370,6 @@ __global__ void __launch_bounds__(kTwThreads, 1) k_selinv_tcw(const ProbDesc *__
                 parts(i_ + 2);     // relative rows of step i + 2
                 cols(i_ + 3);      // column data of step i + 3
             }
-            umma::fence_proxy_async();
-            __syncwarp();
-            if (lane == 0) umma::mbar_arrive(&full[stage]);
             if (s_abort) break;
         }
     } else if (warp == kTwMmaWarp) {

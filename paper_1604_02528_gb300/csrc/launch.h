@@ -31,7 +31,7 @@ cudaError_t launch_selinv_tcw(int cplx, const ProbDesc *d, const Item *items, in
 cudaError_t launch_lhat_tcw(const ProbDesc *d, const Item *items, int n, long long wait_limit, cudaStream_t st);
 cudaError_t launch_tcw_reduce(int cplx, const ProbDesc *d, const Item *items, const int4 *red, int n,
                               const long long *slab, cudaStream_t st);
-cudaError_t launch_diag_fin(const ProbDesc *d, const Item *items, int n, int bshift, cudaStream_t st);
+cudaError_t launch_diag_fin(const ProbDesc *d, const Item *items, int n, cudaStream_t st);
 cudaError_t launch_diag_tc(int tn, int cplx, const ProbDesc *d, const Item *items, int n, long long wait_limit,
                            cudaStream_t st);
 cudaError_t launch_lhat_digits_z(const ProbDesc *d, const int2 *work, int nwork, cudaStream_t st);

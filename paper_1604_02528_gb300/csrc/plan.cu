@@ -657,17 +657,22 @@ int build_schedule(Schedule &S, const std::vector<const PlanData *> &plans,
         if (cnt) S.launches.push_back({KL_TC_REDUCE, tl.dtype, tl.bucket, off, cnt, tl.level});
     };
     // after a tensor-core diagonal-block launch: its finisher, (K, 8 columns) items
-    auto add_diag_fin = [&](const Launch dl, int bshift) {
+    // (K, 8 columns) items, the digit grid's shift (1: tcgen05 sums, 0:
+    // mma.sync sums) in the ntiles field; one launch for the diagonal-block
+    // launches of a level
+    auto add_diag_fin = [&](const std::vector<std::pair<Launch, int>> &dls) {
+        if (dls.empty()) return;
         const int64_t off = (int64_t)S.h_items.size();
-        for (int64_t e = dl.off; e < dl.off + dl.count; e++) {
-            const Item it = S.h_items[e];
-            if (it.tile != 0) continue;                      // one entry per supernode
-            const PlanData &p = *plans[it.prob];
-            const int s = p.super_ptr[it.K + 1] - p.super_ptr[it.K];
-            for (int cb = 0; cb < (s + 7) / 8; cb++) S.h_items.push_back({it.prob, it.K, cb, 0});
-        }
+        for (const auto &db : dls)
+            for (int64_t e = db.first.off; e < db.first.off + db.first.count; e++) {
+                const Item it = S.h_items[e];
+                if (it.tile != 0) continue;                      // one entry per supernode
+                const PlanData &p = *plans[it.prob];
+                const int s = p.super_ptr[it.K + 1] - p.super_ptr[it.K];
+                for (int cb = 0; cb < (s + 7) / 8; cb++) S.h_items.push_back({it.prob, it.K, cb, db.second});
+            }
         const int cnt = (int)((int64_t)S.h_items.size() - off);
-        if (cnt) S.launches.push_back({KL_DIAG_FIN, dl.dtype, bshift, off, cnt, dl.level});
+        if (cnt) S.launches.push_back({KL_DIAG_FIN, dls[0].first.dtype, 0, off, cnt, dls[0].first.level});
     };
     // tensor-core diagonal block: (64-row tile, 32-column pass) items
     auto push_diag = [&](int i, int32_t K) {
@@ -765,7 +770,7 @@ int build_schedule(Schedule &S, const std::vector<const PlanData *> &plans,
             const int cnt2 = (int)(S.h_items.size() - off2);
             if (cnt2) {
                 S.launches.push_back({KL_DIAG_TC, SELINV_C128, tn, off2, cnt2, level});
-                add_diag_fin(S.launches.back(), 1);
+                add_diag_fin({{S.launches.back(), 1}});
             }
         }
     };
@@ -928,12 +933,12 @@ int build_schedule(Schedule &S, const std::vector<const PlanData *> &plans,
                         push_diag_tc(i, K, (s + dtc_tn(s) - 1) / dtc_tn(s));
                         S.launches.push_back({KL_DIAG_TC, descs[i].dtype, dtc_tn(s), off2,
                                               (int)(S.h_items.size() - off2), p.level[K]});
-                        add_diag_fin(S.launches.back(), 1);
+                        add_diag_fin({{S.launches.back(), 1}});
                     } else {
                         push_diag(i, K);
                         S.launches.push_back({KL_DIAG, descs[i].dtype, bucket_of(s), off2,
                                               (int)(S.h_items.size() - off2), p.level[K]});
-                        add_diag_fin(S.launches.back(), 0);
+                        add_diag_fin({{S.launches.back(), 0}});
                     }
                     continue;
                 }
@@ -993,6 +998,7 @@ int build_schedule(Schedule &S, const std::vector<const PlanData *> &plans,
                     const int s = plans[ik.first]->super_ptr[ik.second + 1] - plans[ik.first]->super_ptr[ik.second];
                     if (diag_tc(ik.first, s)) diag_units += (s + dtc_tn(s) - 1) / dtc_tn(s);
                 }
+                std::vector<std::pair<Launch, int>> fins;
                 for (int tn : {64, 32}) {
                     const int64_t off = (int64_t)S.h_items.size();
                     for (auto &ik : oz) {
@@ -1002,7 +1008,7 @@ int build_schedule(Schedule &S, const std::vector<const PlanData *> &plans,
                     const int cnt = (int)(S.h_items.size() - off);
                     if (cnt) {
                         S.launches.push_back({KL_DIAG_TC, SELINV_F64, tn, off, cnt, l});
-                        add_diag_fin(S.launches.back(), 1);
+                        fins.push_back({S.launches.back(), 1});
                     }
                 }
                 const int64_t off = (int64_t)S.h_items.size();
@@ -1013,8 +1019,9 @@ int build_schedule(Schedule &S, const std::vector<const PlanData *> &plans,
                 const int cnt = (int)(S.h_items.size() - off);
                 if (cnt) {
                     S.launches.push_back({KL_DIAG, SELINV_F64, 0, off, cnt, l});
-                    add_diag_fin(S.launches.back(), 0);
+                    fins.push_back({S.launches.back(), 0});
                 }
+                add_diag_fin(fins);
             }
             // fused DFMA kernel for everything else: a warp per tiny supernode,
             // a CTA per row tile for the rest
@@ -1118,7 +1125,7 @@ cudaError_t launch_with(const Schedule &S, const Launch &L, const ProbDesc *d, c
         return launch_tc_reduce(L.bucket, d, S.d_items, S.d_red + L.off, L.count, S.tcslab, st);
     case KL_DIAG_FIN:
         if (L.dtype != SELINV_F64) return launch_diag_fin_z(d, S.d_items + L.off, L.count, st);
-        return launch_diag_fin(d, S.d_items + L.off, L.count, L.bucket, st);
+        return launch_diag_fin(d, S.d_items + L.off, L.count, st);
     case KL_DIAG_TC:
         return launch_diag_tc(L.bucket, L.dtype != SELINV_F64, d, S.d_items + L.off, L.count, S.spin_limit, st);
     case KL_SELINV_TINY: return launch_selinv_tiny(L.dtype, d, S.d_items + L.off, L.count, st);
