@@ -808,15 +808,23 @@ int build_schedule(Schedule &S, const std::vector<const PlanData *> &plans,
     };
     // k-split of the contraction: enough CTAs for two per SM on narrow levels,
     // each k-range at least 256 long
-    auto oz_split = [&](int i, int32_t K, int64_t level_ctas) {
+    auto oz_split = [&](int i, int32_t K, int64_t level_ctas, int cap = 1 << 30) {
         const PlanData &p = *plans[i];
         const int s = p.super_ptr[K + 1] - p.super_ptr[K];
         const int64_t c = p.rowptr[K + 1] - p.rowptr[K] - s;
         const selinv_opts &o = p.opts;
         const int64_t target = (int64_t)o.split_target * 152;
-        const int64_t want = (target + level_ctas - 1) / std::max<int64_t>(level_ctas, 1);
+        const int64_t want = std::min<int64_t>(cap, (target + level_ctas - 1) / std::max<int64_t>(level_ctas, 1));
         const int64_t maxsplit = std::max<int64_t>(1, ((c + 15) / 16) / o.split_min_steps);
         return (int)std::max<int64_t>(1, std::min(want, maxsplit));
+    };
+    // steps of the first k-range of K's items under split ns (ranges are
+    // whole 128-k chunks; the last one takes the rest)
+    auto oz_chunk = [&](int i, int32_t K, int ns) -> int64_t {
+        const PlanData &p = *plans[i];
+        const int64_t c = p.rowptr[K + 1] - p.rowptr[K] - (p.super_ptr[K + 1] - p.super_ptr[K]);
+        const int64_t steps = (c + 15) / 16;
+        return ((steps + ns - 1) / ns + kTcChunkSteps - 1) / kTcChunkSteps * kTcChunkSteps;
     };
     auto oz_ctas = [&](int i, int32_t K) -> int64_t {
         const PlanData &p = *plans[i];
@@ -824,6 +832,50 @@ int build_schedule(Schedule &S, const std::vector<const PlanData *> &plans,
         const int64_t c = p.rowptr[K + 1] - p.rowptr[K] - s;
         if (c == 0) return 0;
         return row_tiles(i, K) * (tc_wide(i, s) ? 1 : (s + oz_tn(s) - 1) / oz_tn(s));
+    };
+    // k-split cap of a level: the split rule's value or a smaller one when an
+    // estimate of the level's makespan prefers it.  The estimate assigns the
+    // CTAs, longest first, to the SM that frees first (one CTA per SM), each
+    // costing its k16 steps plus a fixed cost, and charges a split level the
+    // reduction of its partial sums.
+    auto level_split = [&](const std::vector<std::pair<int, int32_t>> &oz, int64_t level_ctas) -> int {
+        if (oz.empty() || level_ctas <= 0) return 1;
+        constexpr int64_t kCtaCost = 8, kReduceCost = 6;   // in k16 steps
+        int smax = 1;
+        for (auto &ik : oz) smax = std::max(smax, oz_split(ik.first, ik.second, level_ctas));
+        int best = smax;
+        int64_t best_t = -1;
+        std::vector<std::pair<int64_t, int64_t>> lens;   // (cost, CTAs)
+        for (int sg = 1; sg <= smax; sg++) {
+            lens.clear();
+            bool split = false;
+            for (auto &ik : oz) {
+                const int ns = oz_split(ik.first, ik.second, level_ctas, sg);
+                const PlanData &p = *plans[ik.first];
+                const int64_t c = p.rowptr[ik.second + 1] - p.rowptr[ik.second] -
+                                  (p.super_ptr[ik.second + 1] - p.super_ptr[ik.second]);
+                const int64_t steps = (c + 15) / 16, ch = oz_chunk(ik.first, ik.second, ns);
+                const int64_t tiles = oz_ctas(ik.first, ik.second);
+                split = split || ns > 1;
+                for (int x = 0; x < ns; x++)
+                    lens.push_back({std::max<int64_t>(0, std::min(ch, steps - x * ch)) + kCtaCost, tiles});
+            }
+            std::sort(lens.begin(), lens.end(), [](const std::pair<int64_t, int64_t> &a,
+                                                   const std::pair<int64_t, int64_t> &b) { return a.first > b.first; });
+            std::vector<int64_t> heap(152, 0);   // min-heap of the SMs' finish times
+            for (auto &lc : lens)
+                for (int64_t m = 0; m < lc.second; m++) {
+                    std::pop_heap(heap.begin(), heap.end(), std::greater<int64_t>());
+                    heap.back() += lc.first;
+                    std::push_heap(heap.begin(), heap.end(), std::greater<int64_t>());
+                }
+            const int64_t t = *std::max_element(heap.begin(), heap.end()) + (split ? kReduceCost : 0);
+            if (best_t < 0 || t < best_t) {
+                best_t = t;
+                best = sg;
+            }
+        }
+        return best;
     };
 
     if (mode == SELINV_SCHED_PERSISTENT) {
@@ -976,6 +1028,13 @@ int build_schedule(Schedule &S, const std::vector<const PlanData *> &plans,
             int64_t level_ctas = 0;
             for (auto &ik : oz) level_ctas += oz_ctas(ik.first, ik.second);
             launch_z(zs, l, level_ctas);
+            // the level's split, and its supernodes in the order of their items'
+            // length, longest first (the CTAs that start last are short ones)
+            const int sig = level_split(oz, level_ctas);
+            std::stable_sort(oz.begin(), oz.end(), [&](const std::pair<int, int32_t> &a, const std::pair<int, int32_t> &b) {
+                return oz_chunk(a.first, a.second, oz_split(a.first, a.second, level_ctas, sig)) >
+                       oz_chunk(b.first, b.second, oz_split(b.first, b.second, level_ctas, sig));
+            });
             for (int tc = 1; tc >= 0; tc--)
                 for (int tn : {kTcWide, 64, 32, 16}) {
                     const int64_t off = (int64_t)S.h_items.size();
@@ -983,7 +1042,7 @@ int build_schedule(Schedule &S, const std::vector<const PlanData *> &plans,
                         const PlanData &p = *plans[ik.first];
                         const int s = p.super_ptr[ik.second + 1] - p.super_ptr[ik.second];
                         if (tn_of(ik.first, s) == tn && use_tc(ik.first) == (tc == 1))
-                            push_oz(ik.first, ik.second, tn, oz_split(ik.first, ik.second, level_ctas));
+                            push_oz(ik.first, ik.second, tn, oz_split(ik.first, ik.second, level_ctas, sig));
                     }
                     const int cnt = (int)(S.h_items.size() - off);
                     if (cnt) {

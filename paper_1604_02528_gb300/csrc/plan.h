@@ -128,6 +128,7 @@ inline bool oz_eligible(int dtype, int s, const selinv_opts &o) {
     return o.fast_contraction && dtype == SELINV_F64 && s >= std::max(kOzMinS, o.oz_min_s);
 }
 constexpr int kTcRows = 128;   // rows of C per tcgen05 item
+constexpr int kTcChunkSteps = 8;   // k16 steps per exact fp32 chunk of the tensor-core kernels (k-ranges are whole chunks)
 constexpr int kTcWide = 128;   // launch bucket of the transposed tcgen05 kernel (supernodes wider than 64)
 constexpr int kTcWideRows = 64;   // rows of C per item of that kernel
 

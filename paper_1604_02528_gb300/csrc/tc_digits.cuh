@@ -15,6 +15,7 @@ namespace selinv {
 constexpr int kTcM = 128;          // tensor-memory lanes (M of every MMA)
 constexpr int kTcDig = 7;          // digits per FP64 operand
 constexpr int kTcFlush = 8;        // k16 steps per exact fp32 chunk (128 k)
+static_assert(kTcFlush == 8, "the planner sizes k-ranges in whole chunks of 8 steps");
 // Bounded mbarrier waits inside one CTA get at least this many polls
 // (about a second), whatever the caller's bound on waits between CTAs.
 constexpr long long kMbarMinPolls = 1ll << 22;
