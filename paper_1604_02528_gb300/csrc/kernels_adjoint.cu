@@ -108,6 +108,13 @@ struct AdjData {
     int2 *d_dig = nullptr;
     ProbDesc *d_tcdesc = nullptr;
     int *cy = nullptr;                        // column maxima the tcgen05 launches record (unused here)
+    // the per-level loops of the two passes as CUDA graphs (captured on first
+    // use, rebuilt when the lists or the workspace change)
+    int gen = 0;                              // bumped whenever the lists are rebuilt
+    cudaGraphExec_t g_sel = nullptr, g_fac = nullptr;
+    int g_sel_n = 0, g_fac_n = 0;             // launches in each graph
+    long long g_sel_key = -1, g_fac_key = -1;
+    const void *g_sel_ws = nullptr, *g_fac_ws = nullptr;
 };
 
 // ---------------------------------------------------------------------------
@@ -909,6 +916,8 @@ void adjoint_release(void *p) {
     fr(a->YB); fr(a->Zb); fr(a->Lbw); fr(a->Ab); fr(a->fin); fr(a->d_desc); fr(a->d_pdesc);
     fr(a->V);
     fr(a->d_sm); fr(a->d_wd); fr(a->d_row); fr(a->d_mbp); fr(a->d_dig); fr(a->d_tcdesc); fr(a->cy);
+    if (a->g_sel) cudaGraphExecDestroy(a->g_sel);
+    if (a->g_fac) cudaGraphExecDestroy(a->g_fac);
     a->tcs.release();
     delete a;
 }
@@ -1129,6 +1138,7 @@ static int adj_split(selinv_plan_s *plan) {
     if (!a->cy && cudaMalloc((void **)&a->cy, sizeof(int) * (size_t)std::max(p.n, 1)) != cudaSuccess)
         return SELINV_ERR_OOM;
     a->split_key = key;
+    a->gen++;
     return SELINV_OK;
 }
 
@@ -1150,6 +1160,49 @@ static int adj_prepare(selinv_plan_s *plan) {
 }  // namespace selinv
 
 using namespace selinv;
+
+// Issues body(st) through a CUDA graph captured on the first call and replayed
+// afterwards.  The per-level launches of the reverse passes take only the
+// plan's own device buffers as arguments (the caller's pointers reach them
+// through descriptors uploaded before the graph runs), so one capture serves
+// every call until the lists (key) or the workspace (ws) change.  A stream
+// that cannot be captured -- the legacy default stream, or one the caller is
+// capturing already -- runs body(st) directly.
+template <class F>
+static int run_captured(cudaGraphExec_t &exec, int &nlaunch, long long &key, const void *&ws, long long want_key,
+                        const void *want_ws, cudaStream_t st, F body) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (st == nullptr || st == cudaStreamLegacy || cudaStreamIsCapturing(st, &cs) != cudaSuccess ||
+        cs != cudaStreamCaptureStatusNone) {
+        body(st);
+        return cudaGetLastError() == cudaSuccess ? SELINV_OK : SELINV_ERR_CUDA;
+    }
+    if (!exec || key != want_key || ws != want_ws) {
+        if (exec) cudaGraphExecDestroy(exec);
+        exec = nullptr;
+        const int64_t n0 = selinv_launch_count();
+        cudaGraph_t g = nullptr;
+        if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return SELINV_ERR_CUDA;
+        body(st);
+        cudaError_t e = cudaStreamEndCapture(st, &g);
+        nlaunch = (int)(selinv_launch_count() - n0);
+        note_launch(-nlaunch);   // captured, not yet issued
+        if (e != cudaSuccess || !g) {
+            if (g) cudaGraphDestroy(g);
+            return SELINV_ERR_CUDA;
+        }
+        e = cudaGraphInstantiate(&exec, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) {
+            exec = nullptr;
+            return SELINV_ERR_CUDA;
+        }
+        key = want_key;
+        ws = want_ws;
+    }
+    note_launch(nlaunch);
+    return cudaGraphLaunch(exec, st) == cudaSuccess ? SELINV_OK : SELINV_ERR_CUDA;
+}
 
 extern "C" int selinv_adjoint(selinv_plan plan, selinv_dtype dtype, const void *L, const void *D,
                               const void *Z, const void *Zbar, void *Lbar, void *Dbar, void *stream) {
@@ -1194,48 +1247,50 @@ extern "C" int selinv_adjoint(selinv_plan plan, selinv_dtype dtype, const void *
         note_launch();
     }
     const int nl = p.nlevels;
-    for (int li = 0; li < nl; li++) {  // deepest level first
-        // the children's update matrices complete Zbar on K's panel and start V_K
-        for (int r = 0; r < f->npass; r++) {
-            const int64_t x0 = f->asm_lptr[li * f->npass + r], x1 = f->asm_lptr[li * f->npass + r + 1];
-            if (x1 > x0) { k_adj_asm<<<(int)(x1 - x0), 256, 0, st>>>(a->d_desc, f->d_asm + x0, (int)(x1 - x0)); note_launch(); }
-        }
-        const int i0 = a->sm_bptr[li * kNumBuckets], i1 = a->sm_bptr[(li + 1) * kNumBuckets];
-        if (i1 > i0) { k_adj_ybar<<<i1 - i0, 256, 0, st>>>(a->d_desc, a->d_sm + i0, i1 - i0); note_launch(); }
-        const int r0 = (int)a->row_lptr[li], r1 = (int)a->row_lptr[li + 1];
-        const int m0 = (int)a->mbp_lptr[li], m1 = (int)a->mbp_lptr[li + 1];
-        if (r1 > r0) { k_adj_rowprod<RP_YBAR><<<r1 - r0, kThreads, 0, st>>>(a->d_desc, a->d_row + r0, r1 - r0); note_launch(); }
-        const int64_t v0 = a->v_lptr[li], v1 = a->v_lptr[li + 1];
-        if (v1 > v0) { k_adj_vupd<<<(int)(v1 - v0), 256, 0, st>>>(a->d_desc, a->d_vitems + v0, (int)(v1 - v0)); note_launch(); }
-        const int d0 = (int)a->dig_lptr[li], d1 = (int)a->dig_lptr[li + 1];
-        if (d1 > d0) {
-            launch_lhat_digits(a->d_tcdesc, a->d_dig + d0, d1 - d0, st);
-            note_launch();
-            for (int e : a->tc_launch[li]) {
-                launch_with(a->tcs, a->tcs.launches[e], a->d_tcdesc, st);
-                note_launch();
+    auto levels = [&](cudaStream_t st) {
+        for (int li = 0; li < nl; li++) {  // deepest level first
+            // the children's update matrices complete Zbar on K's panel and start V_K
+            for (int r = 0; r < f->npass; r++) {
+                const int64_t x0 = f->asm_lptr[li * f->npass + r], x1 = f->asm_lptr[li * f->npass + r + 1];
+                if (x1 > x0) { k_adj_asm<<<(int)(x1 - x0), 256, 0, st>>>(a->d_desc, f->d_asm + x0, (int)(x1 - x0)); note_launch(); }
             }
+            const int i0 = a->sm_bptr[li * kNumBuckets], i1 = a->sm_bptr[(li + 1) * kNumBuckets];
+            if (i1 > i0) { k_adj_ybar<<<i1 - i0, 256, 0, st>>>(a->d_desc, a->d_sm + i0, i1 - i0); note_launch(); }
+            const int r0 = (int)a->row_lptr[li], r1 = (int)a->row_lptr[li + 1];
+            const int m0 = (int)a->mbp_lptr[li], m1 = (int)a->mbp_lptr[li + 1];
+            if (r1 > r0) { k_adj_rowprod<RP_YBAR><<<r1 - r0, kThreads, 0, st>>>(a->d_desc, a->d_row + r0, r1 - r0); note_launch(); }
+            const int64_t v0 = a->v_lptr[li], v1 = a->v_lptr[li + 1];
+            if (v1 > v0) { k_adj_vupd<<<(int)(v1 - v0), 256, 0, st>>>(a->d_desc, a->d_vitems + v0, (int)(v1 - v0)); note_launch(); }
+            const int d0 = (int)a->dig_lptr[li], d1 = (int)a->dig_lptr[li + 1];
+            if (d1 > d0) {
+                launch_lhat_digits(a->d_tcdesc, a->d_dig + d0, d1 - d0, st);
+                note_launch();
+                for (int e : a->tc_launch[li]) {
+                    launch_with(a->tcs, a->tcs.launches[e], a->d_tcdesc, st);
+                    note_launch();
+                }
+            }
+            for (int b = 0; b < kNumBuckets; b++) {
+                const int b0 = a->sm_bptr[li * kNumBuckets + b], b1 = a->sm_bptr[li * kNumBuckets + b + 1];
+                launch_bucket(0, b, a->d_desc, a->d_sm + b0, b1 - b0, st);
+            }
+            if (r1 > r0) {
+                k_adj_rowprod<RP_LHB><<<r1 - r0, kThreads, 0, st>>>(a->d_desc, a->d_row + r0, r1 - r0);
+                k_adj_rowprod<RP_MBP><<<m1 - m0, kThreads, 0, st>>>(a->d_desc, a->d_mbp + m0, m1 - m0);
+                k_adj_rowprod<RP_LBC><<<r1 - r0, kThreads, 0, st>>>(a->d_desc, a->d_row + r0, r1 - r0);
+                note_launch(3);
+            }
+            // per-supernode s x s steps, batched over the level
+            const int64_t c0 = a->c_lptr[li], c1 = a->c_lptr[li + 1];
+            const int64_t j0 = a->j_lptr[li], j1 = a->j_lptr[li + 1];
+            launch_level_gemm(a, OP_SEL_T1, li, st);
+            if (c1 > c0) { k_adj_sel_mbar<<<(int)(c1 - c0), 256, 0, st>>>(a->d_desc, a->d_citems + c0, (int)(c1 - c0)); note_launch(); }
+            launch_level_gemm(a, OP_SEL_W, li, st);
+            launch_level_gemm(a, OP_SEL_LB, li, st);
+            if (j1 > j0) { k_adj_sel_dbar<<<(int)(j1 - j0), 128, 0, st>>>(a->d_desc, a->d_js + j0, (int)(j1 - j0)); note_launch(); }
         }
-        for (int b = 0; b < kNumBuckets; b++) {
-            const int b0 = a->sm_bptr[li * kNumBuckets + b], b1 = a->sm_bptr[li * kNumBuckets + b + 1];
-            launch_bucket(0, b, a->d_desc, a->d_sm + b0, b1 - b0, st);
-        }
-        if (r1 > r0) {
-            k_adj_rowprod<RP_LHB><<<r1 - r0, kThreads, 0, st>>>(a->d_desc, a->d_row + r0, r1 - r0);
-            k_adj_rowprod<RP_MBP><<<m1 - m0, kThreads, 0, st>>>(a->d_desc, a->d_mbp + m0, m1 - m0);
-            k_adj_rowprod<RP_LBC><<<r1 - r0, kThreads, 0, st>>>(a->d_desc, a->d_row + r0, r1 - r0);
-            note_launch(3);
-        }
-        // per-supernode s x s steps, batched over the level
-        const int64_t c0 = a->c_lptr[li], c1 = a->c_lptr[li + 1];
-        const int64_t j0 = a->j_lptr[li], j1 = a->j_lptr[li + 1];
-        launch_level_gemm(a, OP_SEL_T1, li, st);
-        if (c1 > c0) { k_adj_sel_mbar<<<(int)(c1 - c0), 256, 0, st>>>(a->d_desc, a->d_citems + c0, (int)(c1 - c0)); note_launch(); }
-        launch_level_gemm(a, OP_SEL_W, li, st);
-        launch_level_gemm(a, OP_SEL_LB, li, st);
-        if (j1 > j0) { k_adj_sel_dbar<<<(int)(j1 - j0), 128, 0, st>>>(a->d_desc, a->d_js + j0, (int)(j1 - j0)); note_launch(); }
-    }
-    return cudaGetLastError() == cudaSuccess ? SELINV_OK : SELINV_ERR_CUDA;
+    };
+    return run_captured(a->g_sel, a->g_sel_n, a->g_sel_key, a->g_sel_ws, a->gen, w.colexpZ, st, levels);
 }
 
 extern "C" int selinv_factor_adjoint(selinv_plan plan, selinv_dtype dtype, const void *L, const void *D,
@@ -1278,53 +1333,56 @@ extern "C" int selinv_factor_adjoint(selinv_plan plan, selinv_dtype dtype, const
         note_launch();
     }
     const int nl = p.nlevels;
-    for (int li = nl - 1; li >= 0; li--) {  // root level first
-        const int d0 = (int)a->dig_lptr[li], d1 = (int)a->dig_lptr[li + 1];
-        if (d1 > d0)
-            for (int e : a->tc_launch[li]) {
-                launch_with(a->tcs, a->tcs.launches[e], a->d_tcdesc, st);
+    auto levels = [&](cudaStream_t st) {
+        for (int li = nl - 1; li >= 0; li--) {  // root level first
+            const int d0 = (int)a->dig_lptr[li], d1 = (int)a->dig_lptr[li + 1];
+            if (d1 > d0)
+                for (int e : a->tc_launch[li]) {
+                    launch_with(a->tcs, a->tcs.launches[e], a->d_tcdesc, st);
+                    note_launch();
+                }
+            for (int b = 0; b < kNumBuckets; b++) {
+                const int b0 = a->sm_bptr[li * kNumBuckets + b], b1 = a->sm_bptr[li * kNumBuckets + b + 1];
+                launch_bucket(1, b, a->d_desc, a->d_sm + b0, b1 - b0, st);
+            }
+            const int w0 = (int)a->wd_lptr[li], w1 = (int)a->wd_lptr[li + 1];
+            if (w1 > w0) { k_fadj_pull_tc<<<w1 - w0, 256, 0, st>>>(a->d_desc, a->d_wd + w0, w1 - w0); note_launch(); }
+            for (int b = 0; b < kNumBuckets; b++) {
+                const int b0 = a->sm_bptr[li * kNumBuckets + b], b1 = a->sm_bptr[li * kNumBuckets + b + 1];
+                launch_bucket(2, b, a->d_desc, a->d_sm + b0, b1 - b0, st);
+            }
+            const int r0 = (int)a->row_lptr[li], r1 = (int)a->row_lptr[li + 1];
+            const int m0 = (int)a->mbp_lptr[li], m1 = (int)a->mbp_lptr[li + 1];
+            if (r1 > r0) {
+                k_adj_rowprod<RP_FAC><<<r1 - r0, kThreads, 0, st>>>(a->d_desc, a->d_row + r0, r1 - r0);
+                k_adj_rowprod<RP_FNBP><<<m1 - m0, kThreads, 0, st>>>(a->d_desc, a->d_mbp + m0, m1 - m0);
+                k_adj_rowprod<RP_FABAR><<<r1 - r0, kThreads, 0, st>>>(a->d_desc, a->d_row + r0, r1 - r0);
+                note_launch(3);
+            }
+            const int64_t c0 = a->c_lptr[li], c1 = a->c_lptr[li + 1];
+            const int64_t j0 = a->j_lptr[li], j1 = a->j_lptr[li + 1];
+            if (c1 > c0) { k_fadj_nbar<<<(int)(c1 - c0), 256, 0, st>>>(a->d_desc, a->d_citems + c0, (int)(c1 - c0)); note_launch(); }
+            launch_level_gemm(a, OP_FAC_T2, li, st);
+            launch_level_gemm(a, OP_FAC_U, li, st);
+            if (j1 > j0) {
+                k_fadj_ubar<<<(int)(j1 - j0), 256, 0, st>>>(a->d_desc, a->d_js + j0, (int)(j1 - j0));
                 note_launch();
             }
-        for (int b = 0; b < kNumBuckets; b++) {
-            const int b0 = a->sm_bptr[li * kNumBuckets + b], b1 = a->sm_bptr[li * kNumBuckets + b + 1];
-            launch_bucket(1, b, a->d_desc, a->d_sm + b0, b1 - b0, st);
-        }
-        const int w0 = (int)a->wd_lptr[li], w1 = (int)a->wd_lptr[li + 1];
-        if (w1 > w0) { k_fadj_pull_tc<<<w1 - w0, 256, 0, st>>>(a->d_desc, a->d_wd + w0, w1 - w0); note_launch(); }
-        for (int b = 0; b < kNumBuckets; b++) {
-            const int b0 = a->sm_bptr[li * kNumBuckets + b], b1 = a->sm_bptr[li * kNumBuckets + b + 1];
-            launch_bucket(2, b, a->d_desc, a->d_sm + b0, b1 - b0, st);
-        }
-        const int r0 = (int)a->row_lptr[li], r1 = (int)a->row_lptr[li + 1];
-        const int m0 = (int)a->mbp_lptr[li], m1 = (int)a->mbp_lptr[li + 1];
-        if (r1 > r0) {
-            k_adj_rowprod<RP_FAC><<<r1 - r0, kThreads, 0, st>>>(a->d_desc, a->d_row + r0, r1 - r0);
-            k_adj_rowprod<RP_FNBP><<<m1 - m0, kThreads, 0, st>>>(a->d_desc, a->d_mbp + m0, m1 - m0);
-            k_adj_rowprod<RP_FABAR><<<r1 - r0, kThreads, 0, st>>>(a->d_desc, a->d_row + r0, r1 - r0);
-            note_launch(3);
-        }
-        const int64_t c0 = a->c_lptr[li], c1 = a->c_lptr[li + 1];
-        const int64_t j0 = a->j_lptr[li], j1 = a->j_lptr[li + 1];
-        if (c1 > c0) { k_fadj_nbar<<<(int)(c1 - c0), 256, 0, st>>>(a->d_desc, a->d_citems + c0, (int)(c1 - c0)); note_launch(); }
-        launch_level_gemm(a, OP_FAC_T2, li, st);
-        launch_level_gemm(a, OP_FAC_U, li, st);
-        if (j1 > j0) {
-            k_fadj_ubar<<<(int)(j1 - j0), 256, 0, st>>>(a->d_desc, a->d_js + j0, (int)(j1 - j0));
-            note_launch();
-        }
-        launch_level_gemm(a, OP_FAC_T3, li, st);
-        launch_level_gemm(a, OP_FAC_G1, li, st);
-        launch_level_gemm(a, OP_FAC_G2, li, st);
-        if (j1 > j0) {
-            k_fadj_fold<<<(int)(j1 - j0), 256, 0, st>>>(a->d_desc, a->d_js + j0, (int)(j1 - j0));
-            note_launch();
-            const int z0 = (int)a->cz_lptr[li], z1 = (int)a->cz_lptr[li + 1];
-            if (tc && li > 0 && z1 > z0) {
-                k_adj_colexpz<<<z1 - z0, 256, 0, st>>>(a->d_desc, a->Ab, w.colexpZ, a->d_cz + z0, z1 - z0);
+            launch_level_gemm(a, OP_FAC_T3, li, st);
+            launch_level_gemm(a, OP_FAC_G1, li, st);
+            launch_level_gemm(a, OP_FAC_G2, li, st);
+            if (j1 > j0) {
+                k_fadj_fold<<<(int)(j1 - j0), 256, 0, st>>>(a->d_desc, a->d_js + j0, (int)(j1 - j0));
                 note_launch();
+                const int z0 = (int)a->cz_lptr[li], z1 = (int)a->cz_lptr[li + 1];
+                if (tc && li > 0 && z1 > z0) {
+                    k_adj_colexpz<<<z1 - z0, 256, 0, st>>>(a->d_desc, a->Ab, w.colexpZ, a->d_cz + z0, z1 - z0);
+                    note_launch();
+                }
             }
         }
-    }
+    };
+    if ((rc = run_captured(a->g_fac, a->g_fac_n, a->g_fac_key, a->g_fac_ws, a->gen, w.colexpZ, st, levels))) return rc;
     if (f->nnzA > 0) {
         const int blocks = (int)std::min<int64_t>((f->nnzA + 255) / 256, 152 * 8);
         k_gather_vals<<<blocks, 256, 0, st>>>(f->d_a_pos, a->Ab, f->nnzA, static_cast<double *>(Abar_vals));
