@@ -120,6 +120,8 @@ struct ProbDesc {
     int64_t nnz;                // panel entries (every gather address lies in [0, nnz))
     int32_t check_gather;       // 1: bounds-check gather addresses (debug_checks bit 2)
     int32_t dtype;              // element type: SELINV_F64 or SELINV_C128
+    int32_t prod_op;            // product mode of the transposed tcgen05 kernel (out = LD):
+                                // 0: out = acc, 1: out -= acc, 2: out = Yout - acc
     int32_t symmetrize;
     int32_t herm;               // complex Hermitian (SELINV_C128H): conjugate transposes
     // nonsymmetric values (LU form): U transposed in the panel layout, the

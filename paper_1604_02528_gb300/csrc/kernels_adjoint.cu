@@ -34,6 +34,7 @@
 #include "launch.h"
 #include "nvtx.h"
 #include "plan.h"
+#include "fixedpoint.cuh"
 #include "tile_gemm.cuh"
 #include "seg_update.cuh"
 
@@ -115,6 +116,20 @@ struct AdjData {
     int g_sel_n = 0, g_fac_n = 0;             // launches in each graph
     long long g_sel_key = -1, g_fac_key = -1;
     const void *g_sel_ws = nullptr, *g_fac_ws = nullptr;
+    // row products of the wide supernodes on the transposed tcgen05 kernel:
+    // (K, 64-row tile) items and (K, 8-column block) digit work per level, the
+    // digit planes of the s x s factor (7 x roundup(s, 64) x roundup(s, 16) per
+    // supernode) and its column exponents, one descriptor per product
+    std::vector<Item> pr_items;
+    std::vector<int64_t> pr_lptr;
+    std::vector<int2> sd_work;
+    std::vector<int64_t> sd_lptr;
+    Item *d_pr = nullptr;
+    int2 *d_sdw = nullptr;
+    uint16_t *sd = nullptr;
+    int64_t *d_sd_off = nullptr;
+    int *sdexp = nullptr;
+    ProbDesc *d_pdp = nullptr;               // [5]: YBAR, LHB, LBC, FAC, FABAR
 };
 
 // ---------------------------------------------------------------------------
@@ -354,6 +369,60 @@ enum { RP_YBAR = 0, RP_LHB, RP_LBC, RP_MBP, RP_FAC, RP_FABAR, RP_FNBP };
 //   RP_FNBP  partial of tile t: N_t(i, j) = sum_{p in t} A_C(p, i) Lbar_C(p, j)
 // items (K, t, 32-column chunk of s, half): t is the 32-row block of C, or
 // for the partials the 64-row tile of C whose slot they fill.
+// Digit planes of the s x s factor B of a row product X B of supernode K, in
+// the operand layout of the transposed tcgen05 product (rows = the columns j
+// of B, k in 16-steps, the 7 planes of a step one after the other, K-major
+// 8 x 8 core matrices), with one exponent per column j.  B by product:
+//   RP_YBAR  S, the symmetric cotangent of the diagonal block (also stored
+//            in YB's diagonal block, as the product RP_LHB reads it)
+//   RP_LHB   S from YB's diagonal block
+//   RP_LBC   M^T, M = L_KK^{-1}
+//   RP_FAC   D L_KK^T
+//   RP_FABAR D^{-1} M
+// One CTA per 8 columns, a warp per column; work: (0, K << 8 | column block).
+template <int OP>
+__global__ void __launch_bounds__(256) k_small_digits(const AdjDesc *__restrict__ ad, const int2 *__restrict__ work,
+                                                      int nwork, uint16_t *__restrict__ sd,
+                                                      const int64_t *__restrict__ sd_off, int *__restrict__ sdexp) {
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    const int w = blockIdx.x;
+    if (w >= nwork) return;
+    const AdjDesc &A = *ad;
+    const int K = work[w].y >> 8, j = (work[w].y & 0xFF) * 8 + warp;
+    const int fc = A.super_ptr[K];
+    const int s = A.super_ptr[K + 1] - fc;
+    if (j >= s) return;
+    const int64_t ld = A.rowptr[K + 1] - A.rowptr[K];
+    const int64_t off = A.panel_off[K];
+    const int s16 = (s + 15) & ~15;
+    const int64_t s64 = (s + 63) / 64 * 64;
+    auto val = [&](int k) -> double {
+        if (OP == RP_YBAR) {
+            if (k == j) return A.Zb[off + (int64_t)j * ld + j];
+            return 0.5 * (k > j ? A.Zb[off + (int64_t)j * ld + k] : A.Zb[off + (int64_t)k * ld + j]);
+        }
+        if (OP == RP_LHB) return A.YB[off + (int64_t)j * ld + k];
+        if (OP == RP_LBC) return A.Linv[A.linv_off[K] + (int64_t)k * s + j];
+        if (OP == RP_FAC) return k == j ? A.D[fc + k] : (k < j ? A.D[fc + k] * A.L[off + (int64_t)k * ld + j] : 0.0);
+        return k >= j ? A.Linv[A.linv_off[K] + (int64_t)j * s + k] / A.D[fc + k] : 0.0;
+    };
+    int E = 0;
+    for (int k = lane; k < s; k += 32) E = max(E, bexp(val(k)));
+#pragma unroll
+    for (int o = 16; o; o >>= 1) E = max(E, __shfl_xor_sync(0xffffffffu, E, o));
+    if (lane == 0) sdexp[fc + j] = E;
+    uint16_t *pu = sd + sd_off[K];
+    for (int k = lane; k < s16; k += 32) {
+        const double x = k < s ? val(k) : 0.0;
+        if (OP == RP_YBAR && k < s) A.YB[off + (int64_t)j * ld + k] = x;
+        int d[kDig];
+        digits7(x, E, d);
+        const int64_t ub = (int64_t)(k / 16) * kDig * s64 * 16 + (j / 8) * 128 + ((k % 16) / 8) * 64 + (j % 8) * 8 + k % 8;
+#pragma unroll
+        for (int i = 0; i < kDig; i++) pu[i * s64 * 16 + ub] = (uint16_t)f16_of_int(d[i]);
+    }
+}
+
 template <int OP>
 __global__ void __launch_bounds__(kThreads) k_adj_rowprod(const AdjDesc *__restrict__ ad,
                                                           const int4 *__restrict__ items, int nitems) {
@@ -916,6 +985,7 @@ void adjoint_release(void *p) {
     fr(a->YB); fr(a->Zb); fr(a->Lbw); fr(a->Ab); fr(a->fin); fr(a->d_desc); fr(a->d_pdesc);
     fr(a->V);
     fr(a->d_sm); fr(a->d_wd); fr(a->d_row); fr(a->d_mbp); fr(a->d_dig); fr(a->d_tcdesc); fr(a->cy);
+    fr(a->d_pr); fr(a->d_sdw); fr(a->sd); fr(a->d_sd_off); fr(a->sdexp); fr(a->d_pdp);
     if (a->g_sel) cudaGraphExecDestroy(a->g_sel);
     if (a->g_fac) cudaGraphExecDestroy(a->g_fac);
     a->tcs.release();
@@ -1074,11 +1144,16 @@ static int adj_split(selinv_plan_s *plan) {
     if (key == a->split_key) return SELINV_OK;
     auto fr = [](void *q) { if (q) cudaFree(q); };
     fr(a->d_sm); fr(a->d_wd); fr(a->d_row); fr(a->d_mbp); fr(a->d_dig);
+    fr(a->d_pr); fr(a->d_sdw); fr(a->sd); fr(a->d_sd_off);
     a->d_sm = a->d_wd = nullptr; a->d_row = a->d_mbp = nullptr; a->d_dig = nullptr;
+    a->d_pr = nullptr; a->d_sdw = nullptr; a->sd = nullptr; a->d_sd_off = nullptr;
     a->tcs.release();
     a->tcs.launches.clear();
     a->sm_items.clear(); a->wd_items.clear(); a->row_items.clear(); a->mbp_items.clear(); a->dig_work.clear();
+    a->pr_items.clear(); a->sd_work.clear();
     a->sm_bptr.assign(1, 0); a->wd_lptr.assign(1, 0); a->row_lptr.assign(1, 0); a->mbp_lptr.assign(1, 0); a->dig_lptr.assign(1, 0);
+    a->pr_lptr.assign(1, 0); a->sd_lptr.assign(1, 0);
+    std::vector<int64_t> sd_off(p.ns + 1, 0);
     a->tc_launch.assign(p.nlevels, {});
     auto wide = [&](int s) { return key > 0 && s >= key; };
     for (int l = p.nlevels - 1; l >= 0; l--) {
@@ -1105,16 +1180,30 @@ static int adj_split(selinv_plan_s *plan) {
                     for (int h = 0; h < (s + 63) / 64; h++) a->mbp_items.push_back(make_int4(J, t, ch, h));
             if (c > 0)
                 for (int jb = 0; jb < (s + 7) / 8; jb++) a->dig_work.push_back(make_int2(0, (J << 8) | jb));
+            for (int64_t t = 0; t < (c + kTcWideRows - 1) / kTcWideRows; t++) a->pr_items.push_back({0, J, (int)t, 1});
+            for (int jb = 0; jb < (s + 7) / 8; jb++) a->sd_work.push_back(make_int2(0, (J << 8) | jb));
         }
         a->wd_lptr.push_back((int64_t)a->wd_items.size());
         a->row_lptr.push_back((int64_t)a->row_items.size());
         a->mbp_lptr.push_back((int64_t)a->mbp_items.size());
         a->dig_lptr.push_back((int64_t)a->dig_work.size());
+        a->pr_lptr.push_back((int64_t)a->pr_items.size());
+        a->sd_lptr.push_back((int64_t)a->sd_work.size());
+    }
+    for (int32_t J = 0; J < p.ns; J++) {
+        const int64_t s = p.super_ptr[J + 1] - p.super_ptr[J];
+        sd_off[J + 1] = sd_off[J] + (wide((int)s) ? 7 * ((s + 63) / 64 * 64) * ((s + 15) / 16 * 16) : 0);
     }
     int rc;
     if ((rc = upl(&a->d_sm, a->sm_items)) || (rc = upl(&a->d_wd, a->wd_items)) || (rc = upl(&a->d_row, a->row_items)) ||
-        (rc = upl(&a->d_mbp, a->mbp_items)) || (rc = upl(&a->d_dig, a->dig_work)))
+        (rc = upl(&a->d_mbp, a->mbp_items)) || (rc = upl(&a->d_dig, a->dig_work)) ||
+        (rc = upl(&a->d_pr, a->pr_items)) || (rc = upl(&a->d_sdw, a->sd_work)) || (rc = upl(&a->d_sd_off, sd_off)))
         return rc;
+    if (sd_off[p.ns] > 0 && cudaMalloc((void **)&a->sd, sizeof(uint16_t) * (size_t)sd_off[p.ns]) != cudaSuccess)
+        return SELINV_ERR_OOM;
+    if (!a->sdexp && cudaMalloc((void **)&a->sdexp, sizeof(int) * (size_t)std::max(p.n, 1)) != cudaSuccess)
+        return SELINV_ERR_OOM;
+    if (!a->d_pdp && cudaMalloc((void **)&a->d_pdp, 5 * sizeof(ProbDesc)) != cudaSuccess) return SELINV_ERR_OOM;
     if (!a->dig_work.empty()) {
         // the forward's level schedule supplies the tcgen05 items of every
         // level (row tiles, column tiles, k-splits) and their reductions
@@ -1160,6 +1249,23 @@ static int adj_prepare(selinv_plan_s *plan) {
 }  // namespace selinv
 
 using namespace selinv;
+
+// One row product X B of the level's wide supernodes on the transposed
+// tcgen05 kernel: the digit planes of B, then the product (descriptor pd of
+// d_pdp: the panel X, the output and its mode).
+template <int OP>
+static void row_product(AdjData *a, int pd, int li, cudaStream_t st) {
+    const int q0 = (int)a->sd_lptr[li], q1 = (int)a->sd_lptr[li + 1];
+    if (q1 > q0) {
+        k_small_digits<OP><<<q1 - q0, 256, 0, st>>>(a->d_desc, a->d_sdw + q0, q1 - q0, a->sd, a->d_sd_off, a->sdexp);
+        note_launch();
+    }
+    const int t0 = (int)a->pr_lptr[li], t1 = (int)a->pr_lptr[li + 1];
+    if (t1 > t0) {
+        launch_lhat_tcw(a->d_pdp + pd, a->d_pr + t0, t1 - t0, a->tcs.spin_limit, st);
+        note_launch();
+    }
+}
 
 // Issues body(st) through a CUDA graph captured on the first call and replayed
 // afterwards.  The per-level launches of the reverse passes take only the
@@ -1242,6 +1348,17 @@ extern "C" int selinv_adjoint(selinv_plan plan, selinv_dtype dtype, const void *
         pd.Yout = w.work;
         pd.colexpY = a->cy;
         cudaMemcpyAsync(a->d_tcdesc, &pd, sizeof(pd), cudaMemcpyHostToDevice, st);
+        // the row products: Ybar = Zbar_{C,K} - Lhat S, G -= Y S (G becomes
+        // Lhat_bar), Lbar_{C,K} = Lhat_bar M^T
+        ProbDesc base = make_desc(p, w, SELINV_F64, L, D, const_cast<void *>(Z), false);
+        base.linvd = a->sd;
+        base.linvd_off = a->d_sd_off;
+        base.linvexp = a->sdexp;
+        ProbDesc pdp[3] = {base, base, base};
+        pdp[0].L = w.LD; pdp[0].LD = a->YB; pdp[0].Yout = a->Zb; pdp[0].prod_op = 2;
+        pdp[1].L = Z; pdp[1].LD = w.work; pdp[1].prod_op = 1;
+        pdp[2].L = w.work; pdp[2].LD = Lbar; pdp[2].prod_op = 0;
+        cudaMemcpyAsync(a->d_pdp, pdp, sizeof(pdp), cudaMemcpyHostToDevice, st);
         const int ncz = (int)a->cz_work.size();
         k_adj_colexpz<<<ncz, 256, 0, st>>>(a->d_desc, static_cast<const double *>(Z), w.colexpZ, a->d_cz, ncz);
         note_launch();
@@ -1258,7 +1375,7 @@ extern "C" int selinv_adjoint(selinv_plan plan, selinv_dtype dtype, const void *
             if (i1 > i0) { k_adj_ybar<<<i1 - i0, 256, 0, st>>>(a->d_desc, a->d_sm + i0, i1 - i0); note_launch(); }
             const int r0 = (int)a->row_lptr[li], r1 = (int)a->row_lptr[li + 1];
             const int m0 = (int)a->mbp_lptr[li], m1 = (int)a->mbp_lptr[li + 1];
-            if (r1 > r0) { k_adj_rowprod<RP_YBAR><<<r1 - r0, kThreads, 0, st>>>(a->d_desc, a->d_row + r0, r1 - r0); note_launch(); }
+            if (r1 > r0) row_product<RP_YBAR>(a, 0, li, st);
             const int64_t v0 = a->v_lptr[li], v1 = a->v_lptr[li + 1];
             if (v1 > v0) { k_adj_vupd<<<(int)(v1 - v0), 256, 0, st>>>(a->d_desc, a->d_vitems + v0, (int)(v1 - v0)); note_launch(); }
             const int d0 = (int)a->dig_lptr[li], d1 = (int)a->dig_lptr[li + 1];
@@ -1275,10 +1392,10 @@ extern "C" int selinv_adjoint(selinv_plan plan, selinv_dtype dtype, const void *
                 launch_bucket(0, b, a->d_desc, a->d_sm + b0, b1 - b0, st);
             }
             if (r1 > r0) {
-                k_adj_rowprod<RP_LHB><<<r1 - r0, kThreads, 0, st>>>(a->d_desc, a->d_row + r0, r1 - r0);
+                row_product<RP_LHB>(a, 1, li, st);
                 k_adj_rowprod<RP_MBP><<<m1 - m0, kThreads, 0, st>>>(a->d_desc, a->d_mbp + m0, m1 - m0);
-                k_adj_rowprod<RP_LBC><<<r1 - r0, kThreads, 0, st>>>(a->d_desc, a->d_row + r0, r1 - r0);
-                note_launch(3);
+                note_launch();
+                row_product<RP_LBC>(a, 2, li, st);
             }
             // per-supernode s x s steps, batched over the level
             const int64_t c0 = a->c_lptr[li], c1 = a->c_lptr[li + 1];
@@ -1329,6 +1446,15 @@ extern "C" int selinv_factor_adjoint(selinv_plan plan, selinv_dtype dtype, const
         pd.Yout = w.work;
         pd.colexpY = a->cy;
         cudaMemcpyAsync(a->d_tcdesc, &pd, sizeof(pd), cudaMemcpyHostToDevice, st);
+        // the row products: G = A_C = L_C D L_KK^T, Abar_C = Lbar_C D^{-1} M
+        ProbDesc base = make_desc(p, w, SELINV_F64, L, D, a->Ab, false);
+        base.linvd = a->sd;
+        base.linvd_off = a->d_sd_off;
+        base.linvexp = a->sdexp;
+        ProbDesc pdp[2] = {base, base};
+        pdp[0].L = L; pdp[0].LD = w.work; pdp[0].prod_op = 0;
+        pdp[1].L = a->Lbw; pdp[1].LD = a->Ab; pdp[1].prod_op = 0;
+        cudaMemcpyAsync(a->d_pdp + 3, pdp, sizeof(pdp), cudaMemcpyHostToDevice, st);
         launch_lhat_digits(a->d_tcdesc, a->d_dig, (int)a->dig_work.size(), st);
         note_launch();
     }
@@ -1354,10 +1480,10 @@ extern "C" int selinv_factor_adjoint(selinv_plan plan, selinv_dtype dtype, const
             const int r0 = (int)a->row_lptr[li], r1 = (int)a->row_lptr[li + 1];
             const int m0 = (int)a->mbp_lptr[li], m1 = (int)a->mbp_lptr[li + 1];
             if (r1 > r0) {
-                k_adj_rowprod<RP_FAC><<<r1 - r0, kThreads, 0, st>>>(a->d_desc, a->d_row + r0, r1 - r0);
+                row_product<RP_FAC>(a, 3, li, st);
                 k_adj_rowprod<RP_FNBP><<<m1 - m0, kThreads, 0, st>>>(a->d_desc, a->d_mbp + m0, m1 - m0);
-                k_adj_rowprod<RP_FABAR><<<r1 - r0, kThreads, 0, st>>>(a->d_desc, a->d_row + r0, r1 - r0);
-                note_launch(3);
+                note_launch();
+                row_product<RP_FABAR>(a, 4, li, st);
             }
             const int64_t c0 = a->c_lptr[li], c1 = a->c_lptr[li + 1];
             const int64_t j0 = a->j_lptr[li], j1 = a->j_lptr[li + 1];

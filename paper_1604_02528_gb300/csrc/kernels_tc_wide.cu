@@ -92,12 +92,14 @@ __device__ __forceinline__ void add_chunk(const uint32_t (&acc)[kTcDig][8], int 
 // items: tile = (row tile * nmt + m tile) * nsplit + k-range, ntiles = nsplit;
 // nmt = ceil(rows of A / 128) (1 for real supernodes of <= 128 columns).
 //
-// LHAT: the same machinery forms Lhat_{C,K} = L_{C,K} L_KK^{-1} (Alg. 1,
-// first loop) for real supernodes wider than 64 columns: A = digit planes of
-// L_KK^{-1} transposed (rows = the columns j of K, k = the s columns of L_KK,
-// written by k_linv_digits in this operand layout), B = 64 rows of the dense
-// L_{C,K} (row exponent over the row's s entries), k = s: a single chunk, no
-// k-split.  The result goes to Lhat's slots of the LD panel.
+// LHAT: the same machinery forms products of a panel's rows with an s x s
+// matrix, out(p, j) = sum_k X(p, k) B(k, j) for the rows p of C: A = digit
+// planes of B transposed (rows = the columns j, k = the s columns of the
+// panel, in this operand layout, with an exponent per column j), B = 64
+// rows of the dense panel X (row exponent over the row's s entries), k = s:
+// a single chunk, no k-split.  The forward's Lhat_{C,K} = L_{C,K} L_KK^{-1}
+// (Alg. 1, first loop; digits by k_linv_digits) goes to Lhat's slots of the
+// LD panel; the reverse passes' row products use the other prod_op modes.
 template <bool CPLX, bool LHAT = false>
 __global__ void __launch_bounds__(kTwThreads, 1) k_selinv_tcw(const ProbDesc *__restrict__ descs,
                                                               const Item *__restrict__ items, int nitems,
@@ -474,11 +476,17 @@ __global__ void __launch_bounds__(kTwThreads, 1) k_selinv_tcw(const ProbDesc *__
     // on the same grids (F: the column exponent of L_KK^{-1})
     if constexpr (LHAT) {
         double *Lh = static_cast<double *>(P.LD) + P.panel_off[K];
+        const double *Ad = static_cast<const double *>(P.Yout) + P.panel_off[K];
+        const int op = P.prod_op;
         for (int e = tid; e < kTwN * kTcM; e += kTwThreads) {
             const int p = e % kTwN, j = e / kTwN;
             if (p0 + p >= c || j >= s) continue;
             const int sc = (rowE[p] - 1022) + (P.linvexp[fc + j] - 1022) - 13;
-            Lh[(int64_t)j * ld + s + p0 + p] = fixed_to_double(Hi[p * kTwHS + j], (long long)Lo[p * kTwHS + j], sc);
+            const double y = fixed_to_double(Hi[p * kTwHS + j], (long long)Lo[p * kTwHS + j], sc);
+            const int64_t at = (int64_t)j * ld + s + p0 + p;
+            if (op == 0) Lh[at] = y;
+            else if (op == 1) Lh[at] -= y;
+            else Lh[at] = Ad[at] - y;
         }
         return;
     }
