@@ -130,6 +130,24 @@ struct AdjData {
     int64_t *d_sd_off = nullptr;
     int *sdexp = nullptr;
     ProbDesc *d_pdp = nullptr;               // [5]: YBAR, LHB, LBC, FAC, FABAR
+    // the update V_K -= sym(Ybar Lhat^T) of the wide supernodes on the
+    // transposed tcgen05 kernel (SYRK mode): digit work (K, 32-row block) and
+    // items (K, 128 x 64 tile) per level, the digit planes of [Ybar, Lhat]
+    // (offsets restart at every level) and their row exponents; the narrow
+    // supernodes keep k_adj_vupd (vn: their items)
+    std::vector<int2> sy_work;
+    std::vector<int64_t> sy_wlptr;
+    std::vector<Item> sy_items;
+    std::vector<int64_t> sy_lptr;
+    std::vector<int4> vn_items;
+    std::vector<int64_t> vn_lptr;
+    int2 *d_syw = nullptr;
+    Item *d_sy = nullptr;
+    int4 *d_vn = nullptr;
+    uint16_t *sy = nullptr;
+    int64_t *d_sy_off = nullptr;
+    int *syexp = nullptr;
+    ProbDesc *d_sydesc = nullptr;
 };
 
 // ---------------------------------------------------------------------------
@@ -420,6 +438,64 @@ __global__ void __launch_bounds__(256) k_small_digits(const AdjDesc *__restrict_
         const int64_t ub = (int64_t)(k / 16) * kDig * s64 * 16 + (j / 8) * 128 + ((k % 16) / 8) * 64 + (j % 8) * 8 + k % 8;
 #pragma unroll
         for (int i = 0; i < kDig; i++) pu[i * s64 * 16 + ub] = (uint16_t)f16_of_int(d[i]);
+    }
+}
+
+// Digit planes of [Ybar, Lhat] (rows p of C, the 2s columns k) for the SYRK
+// update of the transposed tcgen05 kernel: per block of 128 rows, per
+// 16-step of k the 7 planes of 128 x 16 one after the other (K-major 8 x 8
+// core matrices), one exponent per row (at its row position in syexp).  One
+// CTA per 32 rows: a warp per 4 rows finds their exponents, then each thread
+// cuts 8 consecutive k of one row, a 16-byte store per plane.
+// work: (K, 32-row block).
+__global__ void __launch_bounds__(256) k_syrk_digits(const AdjDesc *__restrict__ ad, const int2 *__restrict__ work,
+                                                     int nwork, uint16_t *__restrict__ sy,
+                                                     const int64_t *__restrict__ sy_off, int *__restrict__ syexp) {
+    __shared__ int rowE[32];
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    const int w = blockIdx.x;
+    if (w >= nwork) return;
+    const AdjDesc &A = *ad;
+    const int K = work[w].x, b = work[w].y;
+    const int s = A.super_ptr[K + 1] - A.super_ptr[K];
+    const int64_t ld = A.rowptr[K + 1] - A.rowptr[K];
+    const int c = (int)(ld - s);
+    const int64_t off = A.panel_off[K];
+    const int kw = 2 * s, k16 = (kw + 15) / 16 * 16, nst = k16 / 16;
+    auto x = [&](int p, int k) -> double {   // [Ybar, Lhat](p, k)
+        return k < s ? A.YB[off + (int64_t)k * ld + s + p] : A.LD[off + (int64_t)(k - s) * ld + s + p];
+    };
+    for (int rr = 0; rr < 4; rr++) {
+        const int r = warp * 4 + rr, p = b * 32 + r;
+        int E = 0;
+        if (p < c)
+            for (int k = lane; k < kw; k += 32) E = max(E, bexp(x(p, k)));
+#pragma unroll
+        for (int o = 16; o; o >>= 1) E = max(E, __shfl_xor_sync(0xffffffffu, E, o));
+        if (lane == 0) {
+            rowE[r] = E;
+            if (p < c) syexp[A.rowptr[K] + s + p] = E;
+        }
+    }
+    __syncthreads();
+    uint16_t *base = sy + sy_off[K];
+    for (int e = threadIdx.x; e < 32 * (k16 / 8); e += 256) {
+        const int r = e % 32, k0 = (e / 32) * 8, p = b * 32 + r;
+        if (p >= c) continue;
+        uint32_t h[kDig][4];
+#pragma unroll
+        for (int t = 0; t < 8; t += 2) {
+            int d0[kDig], d1[kDig];
+            digits7(k0 + t < kw ? x(p, k0 + t) : 0.0, rowE[r], d0);
+            digits7(k0 + t + 1 < kw ? x(p, k0 + t + 1) : 0.0, rowE[r], d1);
+#pragma unroll
+            for (int i = 0; i < kDig; i++) h[i][t / 2] = f16_of_int(d0[i]) | (f16_of_int(d1[i]) << 16);
+        }
+        const int t1 = p / 128, r128 = p % 128, st = k0 / 16;
+        const int64_t ub = ((int64_t)(t1 * nst + st) * kDig) * 128 * 16 + (r128 / 8) * 128 + ((k0 % 16) / 8) * 64 + (r128 % 8) * 8;
+#pragma unroll
+        for (int i = 0; i < kDig; i++)
+            *reinterpret_cast<uint4 *>(base + ub + (int64_t)i * 128 * 16) = make_uint4(h[i][0], h[i][1], h[i][2], h[i][3]);
     }
 }
 
@@ -986,6 +1062,7 @@ void adjoint_release(void *p) {
     fr(a->V);
     fr(a->d_sm); fr(a->d_wd); fr(a->d_row); fr(a->d_mbp); fr(a->d_dig); fr(a->d_tcdesc); fr(a->cy);
     fr(a->d_pr); fr(a->d_sdw); fr(a->sd); fr(a->d_sd_off); fr(a->sdexp); fr(a->d_pdp);
+    fr(a->d_syw); fr(a->d_sy); fr(a->d_vn); fr(a->sy); fr(a->d_sy_off); fr(a->syexp); fr(a->d_sydesc);
     if (a->g_sel) cudaGraphExecDestroy(a->g_sel);
     if (a->g_fac) cudaGraphExecDestroy(a->g_fac);
     a->tcs.release();
@@ -1145,8 +1222,14 @@ static int adj_split(selinv_plan_s *plan) {
     auto fr = [](void *q) { if (q) cudaFree(q); };
     fr(a->d_sm); fr(a->d_wd); fr(a->d_row); fr(a->d_mbp); fr(a->d_dig);
     fr(a->d_pr); fr(a->d_sdw); fr(a->sd); fr(a->d_sd_off);
+    fr(a->d_syw); fr(a->d_sy); fr(a->d_vn); fr(a->sy); fr(a->d_sy_off);
     a->d_sm = a->d_wd = nullptr; a->d_row = a->d_mbp = nullptr; a->d_dig = nullptr;
     a->d_pr = nullptr; a->d_sdw = nullptr; a->sd = nullptr; a->d_sd_off = nullptr;
+    a->d_syw = nullptr; a->d_sy = nullptr; a->d_vn = nullptr; a->sy = nullptr; a->d_sy_off = nullptr;
+    a->sy_work.clear(); a->sy_items.clear(); a->vn_items.clear();
+    a->sy_wlptr.assign(1, 0); a->sy_lptr.assign(1, 0); a->vn_lptr.assign(1, 0);
+    std::vector<int64_t> sy_off(p.ns + 1, 0);
+    int64_t sy_max = 0;
     a->tcs.release();
     a->tcs.launches.clear();
     a->sm_items.clear(); a->wd_items.clear(); a->row_items.clear(); a->mbp_items.clear(); a->dig_work.clear();
@@ -1189,6 +1272,33 @@ static int adj_split(selinv_plan_s *plan) {
         a->dig_lptr.push_back((int64_t)a->dig_work.size());
         a->pr_lptr.push_back((int64_t)a->pr_items.size());
         a->sd_lptr.push_back((int64_t)a->sd_work.size());
+        // the update matrices: SYRK items for the wide supernodes, k_adj_vupd
+        // tiles for the rest; digit offsets restart at every level
+        int64_t lev_off = 0;
+        for (int64_t e = p.level_ptr[l]; e < p.level_ptr[l + 1]; e++) {
+            const int32_t J = p.level_list[e];
+            const int s = p.super_ptr[J + 1] - p.super_ptr[J];
+            const int64_t c = p.rowptr[J + 1] - p.rowptr[J] - s;
+            if (c == 0) continue;
+            if (!wide(s)) {
+                const int nvt = (int)((c + kVB - 1) / kVB);
+                for (int ti = 0; ti < nvt; ti++)
+                    for (int tj = 0; tj <= ti; tj++) a->vn_items.push_back(make_int4(J, ti, tj, 0));
+                continue;
+            }
+            const int64_t n1 = (c + 127) / 128, n2 = (c + kTcWideRows - 1) / kTcWideRows;
+            const int64_t k16 = (2 * (int64_t)s + 15) / 16 * 16;
+            sy_off[J] = lev_off;
+            lev_off += n1 * 128 * k16 * 7;
+            for (int64_t t1 = 0; t1 < n1; t1++)
+                for (int64_t t2 = 0; t2 < n2 && t2 * kTcWideRows <= t1 * 128 + 127; t2++)
+                    a->sy_items.push_back({0, J, (int)(t1 * n2 + t2), 1});
+            for (int64_t b = 0; b < (c + 31) / 32; b++) a->sy_work.push_back(make_int2(J, (int)b));
+        }
+        sy_max = std::max(sy_max, lev_off);
+        a->sy_wlptr.push_back((int64_t)a->sy_work.size());
+        a->sy_lptr.push_back((int64_t)a->sy_items.size());
+        a->vn_lptr.push_back((int64_t)a->vn_items.size());
     }
     for (int32_t J = 0; J < p.ns; J++) {
         const int64_t s = p.super_ptr[J + 1] - p.super_ptr[J];
@@ -1197,8 +1307,15 @@ static int adj_split(selinv_plan_s *plan) {
     int rc;
     if ((rc = upl(&a->d_sm, a->sm_items)) || (rc = upl(&a->d_wd, a->wd_items)) || (rc = upl(&a->d_row, a->row_items)) ||
         (rc = upl(&a->d_mbp, a->mbp_items)) || (rc = upl(&a->d_dig, a->dig_work)) ||
-        (rc = upl(&a->d_pr, a->pr_items)) || (rc = upl(&a->d_sdw, a->sd_work)) || (rc = upl(&a->d_sd_off, sd_off)))
+        (rc = upl(&a->d_pr, a->pr_items)) || (rc = upl(&a->d_sdw, a->sd_work)) || (rc = upl(&a->d_sd_off, sd_off)) ||
+        (rc = upl(&a->d_syw, a->sy_work)) || (rc = upl(&a->d_sy, a->sy_items)) || (rc = upl(&a->d_vn, a->vn_items)) ||
+        (rc = upl(&a->d_sy_off, sy_off)))
         return rc;
+    if (sy_max > 0 && cudaMalloc((void **)&a->sy, sizeof(uint16_t) * (size_t)sy_max) != cudaSuccess)
+        return SELINV_ERR_OOM;
+    if (!a->syexp && cudaMalloc((void **)&a->syexp, sizeof(int) * (size_t)std::max<int64_t>(p.rowptr[p.ns], 1)) != cudaSuccess)
+        return SELINV_ERR_OOM;
+    if (!a->d_sydesc && cudaMalloc((void **)&a->d_sydesc, sizeof(ProbDesc)) != cudaSuccess) return SELINV_ERR_OOM;
     if (sd_off[p.ns] > 0 && cudaMalloc((void **)&a->sd, sizeof(uint16_t) * (size_t)sd_off[p.ns]) != cudaSuccess)
         return SELINV_ERR_OOM;
     if (!a->sdexp && cudaMalloc((void **)&a->sdexp, sizeof(int) * (size_t)std::max(p.n, 1)) != cudaSuccess)
@@ -1359,6 +1476,17 @@ extern "C" int selinv_adjoint(selinv_plan plan, selinv_dtype dtype, const void *
         pdp[1].L = Z; pdp[1].LD = w.work; pdp[1].prod_op = 1;
         pdp[2].L = w.work; pdp[2].LD = Lbar; pdp[2].prod_op = 0;
         cudaMemcpyAsync(a->d_pdp, pdp, sizeof(pdp), cudaMemcpyHostToDevice, st);
+        // the update V_K -= sym(Ybar Lhat^T): B = [Lhat, Ybar] from the panels
+        // LD and YB, A = the digit planes of [Ybar, Lhat], out V (offsets u_off)
+        ProbDesc sy = base;
+        sy.L = w.LD;
+        sy.Z = a->YB;
+        sy.Yout = a->V;
+        sy.part_off = f->d_uoff;
+        sy.linvd = a->sy;
+        sy.linvd_off = a->d_sy_off;
+        sy.linvexp = a->syexp;
+        cudaMemcpyAsync(a->d_sydesc, &sy, sizeof(sy), cudaMemcpyHostToDevice, st);
         const int ncz = (int)a->cz_work.size();
         k_adj_colexpz<<<ncz, 256, 0, st>>>(a->d_desc, static_cast<const double *>(Z), w.colexpZ, a->d_cz, ncz);
         note_launch();
@@ -1376,8 +1504,18 @@ extern "C" int selinv_adjoint(selinv_plan plan, selinv_dtype dtype, const void *
             const int r0 = (int)a->row_lptr[li], r1 = (int)a->row_lptr[li + 1];
             const int m0 = (int)a->mbp_lptr[li], m1 = (int)a->mbp_lptr[li + 1];
             if (r1 > r0) row_product<RP_YBAR>(a, 0, li, st);
-            const int64_t v0 = a->v_lptr[li], v1 = a->v_lptr[li + 1];
-            if (v1 > v0) { k_adj_vupd<<<(int)(v1 - v0), 256, 0, st>>>(a->d_desc, a->d_vitems + v0, (int)(v1 - v0)); note_launch(); }
+            const int64_t v0 = a->vn_lptr[li], v1 = a->vn_lptr[li + 1];
+            if (v1 > v0) { k_adj_vupd<<<(int)(v1 - v0), 256, 0, st>>>(a->d_desc, a->d_vn + v0, (int)(v1 - v0)); note_launch(); }
+            const int64_t y0 = a->sy_wlptr[li], y1 = a->sy_wlptr[li + 1];
+            if (y1 > y0) {
+                k_syrk_digits<<<(int)(y1 - y0), 256, 0, st>>>(a->d_desc, a->d_syw + y0, (int)(y1 - y0), a->sy, a->d_sy_off, a->syexp);
+                note_launch();
+            }
+            const int64_t z0 = a->sy_lptr[li], z1 = a->sy_lptr[li + 1];
+            if (z1 > z0) {
+                launch_syrk_tcw(a->d_sydesc, a->d_sy + z0, (int)(z1 - z0), a->tcs.spin_limit, st);
+                note_launch();
+            }
             const int d0 = (int)a->dig_lptr[li], d1 = (int)a->dig_lptr[li + 1];
             if (d1 > d0) {
                 launch_lhat_digits(a->d_tcdesc, a->d_dig + d0, d1 - d0, st);

@@ -92,6 +92,13 @@ __device__ __forceinline__ void add_chunk(const uint32_t (&acc)[kTcDig][8], int 
 // items: tile = (row tile * nmt + m tile) * nsplit + k-range, ntiles = nsplit;
 // nmt = ceil(rows of A / 128) (1 for real supernodes of <= 128 columns).
 //
+// SYRK: the update that the reverse pass of the gather hands to the
+// ancestors, V_K -= [Ybar, Lhat] [Lhat, Ybar]^T over the 2s columns (lower
+// triangle of the c x c update matrix, its diagonal halved): A = digit
+// planes of [Ybar, Lhat] for 128 rows of C (k_syrk_digits, one exponent per
+// row), B = 64 rows of [Lhat, Ybar] sliced here; items (K, 128-row block *
+// number of 64-row blocks + 64-row block) on or below the diagonal.
+//
 // LHAT: the same machinery forms products of a panel's rows with an s x s
 // matrix, out(p, j) = sum_k X(p, k) B(k, j) for the rows p of C: A = digit
 // planes of B transposed (rows = the columns j, k = the s columns of the
@@ -100,7 +107,7 @@ __device__ __forceinline__ void add_chunk(const uint32_t (&acc)[kTcDig][8], int 
 // a single chunk, no k-split.  The forward's Lhat_{C,K} = L_{C,K} L_KK^{-1}
 // (Alg. 1, first loop; digits by k_linv_digits) goes to Lhat's slots of the
 // LD panel; the reverse passes' row products use the other prod_op modes.
-template <bool CPLX, bool LHAT = false>
+template <bool CPLX, bool LHAT = false, bool SYRK = false>
 __global__ void __launch_bounds__(kTwThreads, 1) k_selinv_tcw(const ProbDesc *__restrict__ descs,
                                                               const Item *__restrict__ items, int nitems,
                                                               long long *__restrict__ slab, long long wait_limit) {
@@ -135,15 +142,18 @@ __global__ void __launch_bounds__(kTwThreads, 1) k_selinv_tcw(const ProbDesc *__
     const int s = P.super_ptr[K + 1] - fc;
     const int64_t ld = P.rowptr[K + 1] - P.rowptr[K];
     const int c = (int)(ld - s);
-    const int kw = LHAT ? s : (CPLX ? 2 * c : c);        // k extent
-    const int mrows = CPLX ? 2 * s : s;                  // rows of A (output rows)
-    const int s64 = (mrows + 63) / 64 * 64;              // operand rows of a stored digit block
-    const int nmt = (mrows + kTcM - 1) / kTcM;
+    constexpr bool DENSE = LHAT || SYRK;                 // B from dense panels
+    const int kw = SYRK ? 2 * s : (LHAT ? s : (CPLX ? 2 * c : c));   // k extent
+    const int mrows = SYRK ? c : (CPLX ? 2 * s : s);     // rows of A (output rows)
+    // operand rows of a stored digit block (SYRK: blocks of exactly 128 rows)
+    const int s64 = SYRK ? kTcM : (mrows + 63) / 64 * 64;
+    const int nmt = SYRK ? 1 : (mrows + kTcM - 1) / kTcM;
     const int nsplit = it.ntiles;
     const int ksp = it.tile % nsplit;
-    const int mt = (it.tile / nsplit) % nmt;
-    const int tile = it.tile / nsplit / nmt;
-    const int p0 = tile * kTwN, m0 = mt * kTcM;
+    const int n2 = (c + kTwN - 1) / kTwN;                // SYRK: 64-row blocks of C
+    const int mt = SYRK ? 0 : (it.tile / nsplit) % nmt;
+    const int tile = SYRK ? it.tile % n2 : it.tile / nsplit / nmt;
+    const int p0 = tile * kTwN, m0 = SYRK ? (it.tile / n2) * kTcM : mt * kTcM;
     const int64_t pos0 = P.rowptr[K] + s;
     const int nsteps = (kw + 15) / 16;
     const int chunk = ((nsteps + nsplit - 1) / nsplit + kTcFlush - 1) / kTcFlush * kTcFlush;
@@ -151,15 +161,16 @@ __global__ void __launch_bounds__(kTwThreads, 1) k_selinv_tcw(const ProbDesc *__
     const int st1 = st0 + chunk < nsteps ? st0 + chunk : nsteps;
     const int n = st1 > st0 ? st1 - st0 : 0;             // k16 steps of this item
     const int nflush = (n + kTcFlush - 1) / kTcFlush;
-    const int arows = s64 - m0 < kTcM ? s64 - m0 : kTcM; // rows of A in the stored blocks
+    const int arows = SYRK ? kTcM : (s64 - m0 < kTcM ? s64 - m0 : kTcM);   // rows of A in the stored blocks
 
     int a_issued = -1;   // last step whose A copies the MMA thread issued
     // copies of the Lhat^T digit planes of step i_ (rows m0 .. m0 + 127 of
     // each stored block); the 7 planes of a step lie one after the other, so
     // a block of exactly 128 rows comes in one copy
-    const uint16_t *Au = (LHAT ? P.linvd + P.linvd_off[K] : P.lhsu + P.lhsu_off[K]) + (int64_t)(m0 / 8) * 128;
+    const uint16_t *Au = SYRK ? P.linvd + P.linvd_off[K] + (int64_t)(m0 / kTcM) * nsteps * kTcDig * kTcM * 16
+                              : (LHAT ? P.linvd + P.linvd_off[K] : P.lhsu + P.lhsu_off[K]) + (int64_t)(m0 / 8) * 128;
     const uint32_t aBytes = (uint32_t)(arows * 16 * 2);
-    const bool whole = m0 == 0 && s64 == kTcM;
+    const bool whole = SYRK || (m0 == 0 && s64 == kTcM);
     auto load_a = [&](int i_) {
         const int st = i_ % kTwAS;
         const uint16_t *src = Au + (int64_t)(st0 + i_) * kTcDig * s64 * 16;
@@ -197,7 +208,7 @@ __global__ void __launch_bounds__(kTwThreads, 1) k_selinv_tcw(const ProbDesc *__
             for (int pl = 0; pl < kTcDig; pl++)
                 for (int e = arows * 16 + tid * 8; e < Cfg::A_PLANE; e += kTwThreads * 8)
                     *reinterpret_cast<uint4 *>(As + st * Cfg::A_STAGE + pl * Cfg::A_PLANE + e) = make_uint4(0, 0, 0, 0);
-    if (LHAT)
+    if (DENSE)
         for (int e = tid; e < kTwN; e += kTwThreads) rowE[e] = 0;
     umma::fence_proxy_async();   // zeroed A rows are seen by the tensor cores
     __syncthreads();
@@ -210,13 +221,16 @@ __global__ void __launch_bounds__(kTwThreads, 1) k_selinv_tcw(const ProbDesc *__
         for (int i_ = kTwAS; i_ < kTwPrefetch && i_ < n; i_++)
             umma::bulk_prefetch_l2(Au + (int64_t)(st0 + i_) * kTcDig * s64 * 16, kTcDig * aBytes);
     }
-    if constexpr (LHAT) {
-        // row exponents of L_{C,K}: row p over its s entries
+    if constexpr (DENSE) {
+        // row exponents of the dense B rows: row p over its kw entries (LHAT:
+        // the panel L; SYRK: [Lhat, Ybar] from the panels L and Z)
         const int r = tid % kTwN;
         int e = 0;
         if (p0 + r < c)
-            for (int k = tid / kTwN; k < s; k += kTwThreads / kTwN)
-                e = max(e, bexp(static_cast<const double *>(P.L)[P.panel_off[K] + (int64_t)k * ld + s + p0 + r]));
+            for (int k = tid / kTwN; k < kw; k += kTwThreads / kTwN) {
+                const double *src = static_cast<const double *>(SYRK && k >= s ? P.Z : P.L);
+                e = max(e, bexp(src[P.panel_off[K] + (int64_t)(SYRK && k >= s ? k - s : k) * ld + s + p0 + r]));
+            }
         if (e) atomicMax(&rowE[r], e);
     } else {
         // row exponents of the gathered block: row p is bounded by the largest
@@ -246,7 +260,7 @@ __global__ void __launch_bounds__(kTwThreads, 1) k_selinv_tcw(const ProbDesc *__
     umma::fence_before_sync();
     __syncthreads();
     umma::fence_after_sync();
-    if (!LHAT && warp == 0) {    // prefix max over the 64 rows
+    if (!DENSE && warp == 0) {   // prefix max over the 64 rows
         int carry = s_pre;
         for (int b = 0; b < kTwN; b += 32) {
             int v = max(rowE[b + lane], carry);
@@ -304,14 +318,15 @@ __global__ void __launch_bounds__(kTwThreads, 1) k_selinv_tcw(const ProbDesc *__
                 else { cb[u] = -1; rb[u] = 0; }
             }
         };
-        // LHAT: the 4 values of step i_ straight from the dense panel
-        const double *Lc = static_cast<const double *>(P.L) + P.panel_off[K] + s + p0 + r;   // L_C(p0 + r, k) = Lc[k ld]
+        // DENSE: the 4 values of step i_ straight from the dense panel(s)
+        const double *Lc = static_cast<const double *>(P.L) + P.panel_off[K] + s + p0 + r;   // X(p0 + r, k) = Lc[k ld]
+        const double *Zc2 = static_cast<const double *>(P.Z) + P.panel_off[K] + s + p0 + r;  // SYRK: k >= s
         const bool rok = p0 + r < c;
         auto load_dense = [&](int i_) {
 #pragma unroll
             for (int u = 0; u < 4; u++) {
                 const int k = (st0 + i_) * 16 + kq * 4 + u;
-                v[u] = (rok && i_ < n && k < s) ? Lc[(int64_t)k * ld] : 0.0;
+                v[u] = (rok && i_ < n && k < kw) ? (SYRK && k >= s ? Zc2[(int64_t)(k - s) * ld] : Lc[(int64_t)k * ld]) : 0.0;
             }
         };
         auto parts = [&](int i_) {
@@ -326,7 +341,7 @@ __global__ void __launch_bounds__(kTwThreads, 1) k_selinv_tcw(const ProbDesc *__
                 for (int u = 0; u < NV; u++)
                     if (ab[u] >= 0 && !g.chk.ok(ab[u] + ar[u])) ab[u] = -1;
         };
-        if (LHAT) {
+        if (DENSE) {
             if (n > 0) load_dense(0);
         } else if (n > 0) {
             cols(0);
@@ -365,7 +380,7 @@ __global__ void __launch_bounds__(kTwThreads, 1) k_selinv_tcw(const ProbDesc *__
             umma::fence_proxy_async();
             __syncwarp();
             if (lane == 0) umma::mbar_arrive(&full[stage]);
-            if (LHAT) {
+            if (DENSE) {
                 load_dense(i_ + 1);
             } else {
                 load();            // values of step i + 1
@@ -474,6 +489,18 @@ __global__ void __launch_bounds__(kTwThreads, 1) k_selinv_tcw(const ProbDesc *__
     // C, A digits on 2^(F - 1029 - 8j) of the column of K, so the value is
     // (hi 2^-16 + lo 2^-48) 2^(E + F - 2057); LHAT: Lhat = L_{C,K} L_KK^{-1}
     // on the same grids (F: the column exponent of L_KK^{-1})
+    if constexpr (SYRK) {
+        // V_K(p1, p2) -= the product, p1 >= p2, the diagonal halved (exactly:
+        // one less in the scale); A's rows carry their own exponents
+        double *V = static_cast<double *>(P.Yout) + P.part_off[K];
+        for (int e = tid; e < kTwN * kTcM; e += kTwThreads) {
+            const int p = e % kTwN, mm = e / kTwN, p1 = m0 + mm, p2 = p0 + p;
+            if (p1 >= c || p2 >= c || p1 < p2) continue;
+            const int sc = (rowE[p] - 1022) + (P.linvexp[pos0 + p1] - 1022) - 13 - (p1 == p2 ? 1 : 0);
+            V[(int64_t)p2 * c + p1] -= fixed_to_double(Hi[p * kTwHS + mm], (long long)Lo[p * kTwHS + mm], sc);
+        }
+        return;
+    }
     if constexpr (LHAT) {
         double *Lh = static_cast<double *>(P.LD) + P.panel_off[K];
         const double *Ad = static_cast<const double *>(P.Yout) + P.panel_off[K];
@@ -586,6 +613,9 @@ cudaError_t configure_tcw_kernels() {
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_selinv_tcw<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)TwCfg::SMEM);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_selinv_tcw<false, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)TwCfg::SMEM);
     return e;
 }
 
@@ -600,6 +630,12 @@ cudaError_t launch_selinv_tcw(int cplx, const ProbDesc *d, const Item *items, in
 cudaError_t launch_lhat_tcw(const ProbDesc *d, const Item *items, int n, long long wait_limit, cudaStream_t st) {
     if (n <= 0) return cudaSuccess;
     k_selinv_tcw<false, true><<<n, kTwThreads, TwCfg::SMEM, st>>>(d, items, n, nullptr, wait_limit);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_syrk_tcw(const ProbDesc *d, const Item *items, int n, long long wait_limit, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    k_selinv_tcw<false, false, true><<<n, kTwThreads, TwCfg::SMEM, st>>>(d, items, n, nullptr, wait_limit);
     return cudaGetLastError();
 }
 

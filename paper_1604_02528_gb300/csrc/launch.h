@@ -29,6 +29,7 @@ cudaError_t configure_tcw_kernels();
 cudaError_t launch_selinv_tcw(int cplx, const ProbDesc *d, const Item *items, int n, long long *slab,
                               long long wait_limit, cudaStream_t st);
 cudaError_t launch_lhat_tcw(const ProbDesc *d, const Item *items, int n, long long wait_limit, cudaStream_t st);
+cudaError_t launch_syrk_tcw(const ProbDesc *d, const Item *items, int n, long long wait_limit, cudaStream_t st);
 cudaError_t launch_tcw_reduce(int cplx, const ProbDesc *d, const Item *items, const int4 *red, int n,
                               const long long *slab, cudaStream_t st);
 cudaError_t launch_diag_fin(const ProbDesc *d, const Item *items, int n, cudaStream_t st);
