@@ -19,9 +19,11 @@
 
 namespace selinv {
 
-// Column j of A^{-1}_KK: one warp, lanes over the rows i.
+// Rows i = i0, i0 + 32, ... (i < i1) of column j of A^{-1}_KK: one warp,
+// lanes over the rows; returns the largest exponent of the warp's entries
+// (the same in every lane).
 template <bool CPLX>
-__device__ __forceinline__ void diag_fin_column(const ProbDesc &P, int K, int j, int bshift, int lane) {
+__device__ __forceinline__ int diag_fin_rows(const ProbDesc &P, int K, int j, int bshift, int i0, int i1) {
     const int fc = P.super_ptr[K];
     const int s = P.super_ptr[K + 1] - fc;
     const int64_t ld = P.rowptr[K + 1] - P.rowptr[K];
@@ -38,7 +40,7 @@ __device__ __forceinline__ void diag_fin_column(const ProbDesc &P, int K, int j,
             const int sc = (P.colexp[fc + a] - 1022) + (ey - 1022) - 14 + bshift;
             return fixed_to_double(hi, lo, sc);
         };
-        for (int i = lane; i < s; i += 32) {
+        for (int i = i0; i < i1 && i < s; i += 32) {
             double x = LDk[(int64_t)j * ld + i] - prod(i, j);
             if (P.symmetrize) x = 0.5 * (x + (LDk[(int64_t)i * ld + j] - prod(j, i)));
             Zk[(int64_t)j * ld + i] = x;
@@ -59,7 +61,7 @@ __device__ __forceinline__ void diag_fin_column(const ProbDesc &P, int K, int j,
             const double im = fixed_to_double(q[2], q[3], sc);
             return make_double2(fixed_to_double(q[0], q[1], sc), herm ? -im : im);
         };
-        for (int i = lane; i < s; i += 32) {
+        for (int i = i0; i < i1 && i < s; i += 32) {
             const double2 d1 = LDk[(int64_t)j * ld + i], p1 = prod(i, j);
             double2 x = make_double2(d1.x - p1.x, d1.y - p1.y);
             if (P.symmetrize) {
@@ -71,8 +73,32 @@ __device__ __forceinline__ void diag_fin_column(const ProbDesc &P, int K, int j,
             mj = max(mj, max(bexp(x.x), bexp(x.y)));
         }
     }
-    mj = __reduce_max_sync(0xffffffffu, mj);
-    if (lane == 0) P.colexpZ[fc + j] = max(mj, P.colexpY[fc + j]);
+    return __reduce_max_sync(0xffffffffu, mj);
+}
+
+// The finisher's CTA (256 threads) for two columns j0, j0 + 1 of K: four
+// warps per column, a quarter of its rows each (short chains of dependent
+// loads and conversions: the finisher is latency-bound); the column's
+// exponent (whole column of K's panel: the block and the rows below) is
+// reduced through shared memory.
+template <bool CPLX>
+__device__ __forceinline__ void diag_fin_pair(const ProbDesc &P, int K, int j0, int bshift) {
+    __shared__ int wmax[8];
+    const int fc = P.super_ptr[K];
+    const int s = P.super_ptr[K + 1] - fc;
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    const int j = j0 + warp / 4, q = warp % 4;
+    const int rows = (s + 3) / 4;   // rows per warp, a multiple of 32 or the rest
+    const int r0 = ((rows + 31) / 32) * 32 * q;
+    int mj = 0;
+    if (j < s) mj = diag_fin_rows<CPLX>(P, K, j, bshift, r0 + lane, r0 + ((rows + 31) / 32) * 32);
+    if (lane == 0) wmax[warp] = mj;
+    __syncthreads();
+    if (threadIdx.x < 2 && j0 + (int)threadIdx.x < s) {
+        const int t = threadIdx.x;
+        const int m = max(max(wmax[4 * t], wmax[4 * t + 1]), max(wmax[4 * t + 2], wmax[4 * t + 3]));
+        P.colexpZ[fc + j0 + t] = max(m, P.colexpY[fc + j0 + t]);
+    }
 }
 
 }  // namespace selinv

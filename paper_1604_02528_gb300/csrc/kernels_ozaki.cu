@@ -684,18 +684,15 @@ __global__ void __launch_bounds__(kOzThreads, 1) k_diag_oz(const ProbDesc *__res
 
 // ---------------------------------------------------------------------------
 // k_diag_fin: A^{-1}_KK = Dinv_K - Lhat^T Y from the exact sums of k_diag_oz
-// (bshift 0) or k_diag_tc (bshift 1), symmetrized: one CTA per (K, 8 columns),
-// a warp per column (diag_fin_column).  items: (K, column block, bshift).
+// (bshift 0) or k_diag_tc (bshift 1), symmetrized: one CTA per (K, 2 columns)
+// (diag_fin_pair).  items: (K, column pair, bshift).
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) k_diag_fin(const ProbDesc *__restrict__ descs,
                                                   const Item *__restrict__ items, int nitems) {
     const int w = blockIdx.x;
     if (w >= nitems) return;
     const Item it = items[w];
-    const ProbDesc &P = descs[it.prob];
-    const int s = P.super_ptr[it.K + 1] - P.super_ptr[it.K];
-    const int j = it.tile * 8 + threadIdx.x / 32;
-    if (j < s) diag_fin_column<false>(P, it.K, j, it.ntiles, threadIdx.x % 32);
+    diag_fin_pair<false>(descs[it.prob], it.K, 2 * it.tile, it.ntiles);
 }
 
 constexpr size_t diag_oz_smem() {

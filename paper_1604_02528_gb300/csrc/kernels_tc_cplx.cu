@@ -83,17 +83,14 @@ __global__ void __launch_bounds__(256) k_lhat_digits_z(const ProbDesc *__restric
 // k_diag_fin_z: A^{-1}_KK = Dinv_K - Lhat^T A^{-1}_{C,K} (complex) from the
 // exact sums of k_diag_tc, symmetrized with the plain transpose (Sec. II-C);
 // Hermitian: Dinv_K - Lhat^H A^{-1}_{C,K}, symmetrized as (X + X^H) / 2
-// (diag_fin_column).  One CTA per (K, 8 columns), a warp per column.
+// (diag_fin_pair).  One CTA per (K, 2 columns).
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) k_diag_fin_z(const ProbDesc *__restrict__ descs,
                                                     const Item *__restrict__ items, int nitems) {
     const int w = blockIdx.x;
     if (w >= nitems) return;
     const Item it = items[w];
-    const ProbDesc &P = descs[it.prob];
-    const int s = P.super_ptr[it.K + 1] - P.super_ptr[it.K];
-    const int j = it.tile * 8 + threadIdx.x / 32;
-    if (j < s) diag_fin_column<true>(P, it.K, j, 1, threadIdx.x % 32);
+    diag_fin_pair<true>(descs[it.prob], it.K, 2 * it.tile, 1);
 }
 
 cudaError_t launch_lhat_digits_z(const ProbDesc *d, const int2 *work, int nwork, cudaStream_t st) {

@@ -657,7 +657,7 @@ int build_schedule(Schedule &S, const std::vector<const PlanData *> &plans,
         if (cnt) S.launches.push_back({KL_TC_REDUCE, tl.dtype, tl.bucket, off, cnt, tl.level});
     };
     // after a tensor-core diagonal-block launch: its finisher, (K, 8 columns) items
-    // (K, 8 columns) items, the digit grid's shift (1: tcgen05 sums, 0:
+    // (K, 2 columns) items, the digit grid's shift (1: tcgen05 sums, 0:
     // mma.sync sums) in the ntiles field; one launch for the diagonal-block
     // launches of a level
     auto add_diag_fin = [&](const std::vector<std::pair<Launch, int>> &dls) {
@@ -669,7 +669,7 @@ int build_schedule(Schedule &S, const std::vector<const PlanData *> &plans,
                 if (it.tile != 0) continue;                      // one entry per supernode
                 const PlanData &p = *plans[it.prob];
                 const int s = p.super_ptr[it.K + 1] - p.super_ptr[it.K];
-                for (int cb = 0; cb < (s + 7) / 8; cb++) S.h_items.push_back({it.prob, it.K, cb, db.second});
+                for (int cb = 0; cb < (s + 1) / 2; cb++) S.h_items.push_back({it.prob, it.K, cb, db.second});
             }
         const int cnt = (int)((int64_t)S.h_items.size() - off);
         if (cnt) S.launches.push_back({KL_DIAG_FIN, dls[0].first.dtype, 0, off, cnt, dls[0].first.level});
