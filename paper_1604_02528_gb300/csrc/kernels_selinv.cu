@@ -29,12 +29,24 @@ __device__ inline void latch_status(int *status, int code) {
 // substitution on all columns at once: row k of X is final after step k-1,
 // and step k updates every X(i, j), i > k, j <= k, in parallel.  X stays in
 // shared memory when it fits (odd stride: row and column walks hit distinct
-// banks), else in the global scratch.  Then the symmetric
-// Dinv(i, j) = sum_{k >= max(i, j)} X(k, i) X(k, j) / D_k, lower half
-// computed and mirrored.
+// banks), else in the global scratch.  When there is room, the columns of
+// L_KK arrive in shared memory 32 at a time, the next block copied
+// (cp.async) while the current one is used, so that no step waits on a
+// global load: the s - 1 dependent steps are then bound by the FP64 pipe.
+// Then the symmetric Dinv(i, j) = sum_{k >= max(i, j)} X(k, i) X(k, j) / D_k,
+// lower half computed and mirrored.
 // ---------------------------------------------------------------------------
 constexpr int kLinvThreads = 256;
-constexpr size_t kLinvSmemMax = (128 * 129 + 128) * sizeof(double);
+constexpr size_t kLinvSmemMax = (128 * 129 + 128 + 64 * 128) * sizeof(double);
+
+template <typename T>
+__device__ __forceinline__ void cp_async_elem(T *smem, const T *g) {
+    const uint32_t sa = (uint32_t)__cvta_generic_to_shared(smem);
+    if constexpr (sizeof(T) == 8) asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(g));
+    else asm volatile("cp.async.ca.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(g));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+template <int N> __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
 
 // LU form of the normalisation (Alg. 1 first loop with U kept separately):
 // X = L_KK^{-1} and V = (U_KK^T)^{-1} (U_KK^T is the lower diagonal block of
@@ -107,12 +119,40 @@ __global__ void __launch_bounds__(kLinvThreads) k_linv(const ProbDesc *__restric
         if (is_zero(D[j]) || !finite_val(D[j])) latch_status(P.status, SELINV_ERR_ZERO_PIVOT);
         if (in_smem) rD[j] = recip(D[j]);
     }
+    // two blocks of 32 columns of L_KK in shared memory, [column][row]
+    const bool stage = in_smem && sizeof(T) * ((size_t)s * sp + s + 64 * (size_t)s) <= smem_cap;
+    T *Lb = stage ? rD + s : nullptr;
+    const int nb = (s + 31) / 32;
+    auto fetch = [&](int b) {   // columns 32 b .. 32 b + 31 (rows below the diagonal) into buffer b & 1
+        T *dst = Lb + (size_t)(b & 1) * 32 * s;
+        for (int e = threadIdx.x; e < 32 * s; e += kLinvThreads) {
+            const int kk = e / s, i = e % s, k = 32 * b + kk;
+            if (k < s && i > k) cp_async_elem(dst + e, L + (int64_t)k * ld + i);
+        }
+        cp_async_commit();
+    };
+    if (stage) fetch(0);
     __syncthreads();
     for (int k = 0; k + 1 < s; k++) {
+        const T *Lk = L + (int64_t)k * ld;       // L(i, k) = Lk[i]
+        if (stage) {
+            if (k % 32 == 0) {
+                // the next block goes out now (its buffer was last read before
+                // the previous step's barrier); then this block must be in
+                if (k / 32 + 1 < nb) {
+                    fetch(k / 32 + 1);
+                    cp_async_wait<1>();
+                } else {
+                    cp_async_wait<0>();
+                }
+                __syncthreads();
+            }
+            Lk = Lb + (size_t)((k / 32) & 1) * 32 * s + (size_t)(k % 32) * s;
+        }
         const int m = s - 1 - k;                 // rows i = k+1 .. s-1
         for (int e = threadIdx.x; e < m * (k + 1); e += kLinvThreads) {
             const int i = k + 1 + e % m, j = e / m;
-            msub(X[j * lx + i], L[(int64_t)k * ld + i], X[j * lx + k]);
+            msub(X[j * lx + i], Lk[i], X[j * lx + k]);
         }
         __syncthreads();
     }
@@ -760,8 +800,9 @@ template <typename T>
 static cudaError_t launch_linv_t(const ProbDesc *d, const int2 *work, int nwork, int large, int with_dinv,
                                  cudaStream_t st) {
     if (nwork <= 0) return cudaSuccess;
-    // small blocks (s <= 32) need at most 17 KB; large ones get room for s = 128 (real)
-    const size_t cap = large ? kLinvSmemMax : (32 * 33 + 32) * sizeof(T);
+    // small blocks (s <= 32) need at most 33 KB (X and a staged block of L);
+    // large ones get room for s = 128 (real)
+    const size_t cap = large ? kLinvSmemMax : (32 * 33 + 32 + 64 * 32) * sizeof(T);
     k_linv<T><<<nwork, kLinvThreads, cap, st>>>(d, work, nwork, cap, with_dinv);
     return cudaGetLastError();
 }
