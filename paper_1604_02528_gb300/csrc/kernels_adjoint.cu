@@ -40,6 +40,10 @@
 
 namespace selinv {
 
+constexpr int kNumSMs = 152;   // GB300
+constexpr int kFinY = 4;   // CTAs per supernode (grid y) of the per-supernode s x s steps
+constexpr int kAdjWideC = 256;   // rows of C from which any supernode takes the split (wide) path
+
 struct AdjDesc {
     const int32_t *super_ptr;
     const int64_t *rowptr;
@@ -91,19 +95,20 @@ struct AdjData {
     // Both adjoints, split by supernode width (rebuilt when the
     // options change).  Wide supernodes (s >= the tensor-core threshold) run
     // the gather-GEMM on the tcgen05 kernel and their c x s by s x s products
-    // as (K, 32-row block, 32-column chunk) and (K, 64-row tile, chunk, 64-row half of s) items; narrow
+    // as (K, 32-row block, 32-column chunk) and (K, 64-row tile, chunk, 32-row block of s) items; narrow
     // ones keep the fused one-CTA-per-tile kernels.  Lists per level, deepest first.
     int split_key = -1;
     std::vector<Item> sm_items;               // narrow: (K, tile) per level x bucket
     std::vector<int> sm_bptr;
     std::vector<Item> wd_items;               // wide: (K, tile) per level
     std::vector<int64_t> wd_lptr;
-    std::vector<int4> row_items, mbp_items;   // wide: (K, tile, chunk, 0) / (K, tile, chunk, half)
+    std::vector<int4> row_items, mbp_items;   // wide: (K, tile, chunk, 0) / (K, tile, chunk, row block)
     std::vector<int64_t> row_lptr, mbp_lptr;
     std::vector<int2> dig_work;               // wide with c > 0: (0, K << 8 | 8-column block)
     std::vector<int64_t> dig_lptr;
     std::vector<std::vector<int>> tc_launch;  // per level: tcgen05 and reduction launches of `tcs`
     Schedule tcs;                             // their items, split-k reductions and slab
+    Schedule tcn;                             // the forward's normalization (L_KK^{-1}, Dinv, Lhat) of every supernode
     Item *d_sm = nullptr, *d_wd = nullptr;
     int4 *d_row = nullptr, *d_mbp = nullptr;
     int2 *d_dig = nullptr;
@@ -173,7 +178,7 @@ __global__ void __launch_bounds__(256) k_adj_asm(const AdjDesc *__restrict__ ad,
     double *VK = A.V + A.v_off[K];
     double *ZbK = A.Zb + A.panel_off[K];
     const int64_t cc = (int64_t)cch * cch;
-    for (int64_t e = (int64_t)chunk * 4096 + threadIdx.x; e < cc && e < (int64_t)(chunk + 1) * 4096; e += 256) {
+    for (int64_t e = (int64_t)chunk * kAsmChunk + threadIdx.x; e < cc && e < (int64_t)(chunk + 1) * kAsmChunk; e += 256) {
         const int a = (int)(e % cch), b = (int)(e / cch);
         if (a < b) continue;
         const double v = Vc[e];
@@ -218,7 +223,8 @@ __global__ void __launch_bounds__(256) k_adj_vupd(const AdjDesc *__restrict__ ad
 // The forward writes whole diagonal blocks (the strictly upper part holds
 // copies of the lower entries), so a cotangent may arrive on an upper slot:
 // add it to the lower mirror and clear it, one CTA per supernode.  Every
-// later step reads only the lower triangle of a diagonal block.
+// later step reads only the lower triangle of a diagonal block.  Grid
+// (supernodes, kFinY).
 __global__ void __launch_bounds__(256) k_adj_fold(const AdjDesc *__restrict__ ad, int ns) {
     const int K = blockIdx.x;
     if (K >= ns) return;
@@ -226,7 +232,7 @@ __global__ void __launch_bounds__(256) k_adj_fold(const AdjDesc *__restrict__ ad
     const int s = A.super_ptr[K + 1] - A.super_ptr[K];
     const int64_t ld = A.rowptr[K + 1] - A.rowptr[K];
     double *Zb = A.Zb + A.panel_off[K];
-    for (int e = threadIdx.x; e < s * s; e += blockDim.x) {
+    for (int e = blockIdx.y * blockDim.x + threadIdx.x; e < s * s; e += gridDim.y * blockDim.x) {
         const int i = e % s, j = e / s;
         if (i <= j) continue;
         const double up = Zb[(int64_t)i * ld + j];
@@ -350,7 +356,7 @@ __global__ void __launch_bounds__(kThreads) k_adj_lhbar(const AdjDesc *__restric
 // runs on the tcgen05 kernel (its row exponents: colexpZ, the largest biased
 // exponent of each column of A^{-1} on and below the diagonal, where every
 // gathered entry is stored); the s-inner products run as separate launches
-// of 32 x 32 (and 64 x 32) output blocks so that a level's few tiles still fill the SMs.
+// of 32 x 32 output blocks so that a level's few tiles still fill the SMs.
 // ---------------------------------------------------------------------------
 // work (K, 8-column block): a warp per column
 __global__ void __launch_bounds__(256) k_adj_colexpz(const AdjDesc *__restrict__ ad, const double *__restrict__ src,
@@ -375,18 +381,19 @@ __global__ void __launch_bounds__(256) k_adj_colexpz(const AdjDesc *__restrict__
 
 enum { RP_YBAR = 0, RP_LHB, RP_LBC, RP_MBP, RP_FAC, RP_FABAR, RP_FNBP };
 
-// One 32 x 32 block (64 x 32 for the partials) of
+// One 32 x 32 block of
 //   RP_YBAR  Ybar = Zbar_{C,K} - Lhat S          (block 0 also stores S)
 //   RP_LHB   G   -= Y S                          (G becomes Lhat_bar)
 //   RP_LBC   Lbar_{C,K} = Lhat_bar M^T
 //   RP_MBP   partial of tile t: P_t(i, j) = sum_{p in t} L_C(p, i) Lhat_bar(p, j),
-//            rows i of the item's 64-row half of s
+//            rows i of the item's 32-row block of s
 // and of the factorization adjoint (Lb = the working Lbar)
 //   RP_FAC   G = A_C = L_C D L_KK^T
 //   RP_FABAR Abar_C = Lbar_C D^{-1} M,  M = L_KK^{-1}
 //   RP_FNBP  partial of tile t: N_t(i, j) = sum_{p in t} A_C(p, i) Lbar_C(p, j)
-// items (K, t, 32-column chunk of s, half): t is the 32-row block of C, or
-// for the partials the 64-row tile of C whose slot they fill.
+// items (K, t, 32-column chunk of s, b): t is the 32-row block of C, or
+// for the partials the 64-row tile of C whose slot they fill; b is the
+// partials' 32-row block of s.
 // Digit planes of the s x s factor B of a row product X B of supernode K, in
 // the operand layout of the transposed tcgen05 product (rows = the columns j
 // of B, k in 16-steps, the 7 planes of a step one after the other, K-major
@@ -499,18 +506,36 @@ __global__ void __launch_bounds__(256) k_syrk_digits(const AdjDesc *__restrict__
     }
 }
 
+// The k16 stage of a row-product block: thread (tx, ty) adds rows ty + 16 i
+// (i < NI) and columns tx (+ 16 when TWO) of the BM x 32 block.
+template <int NI, bool TWO, int BM>
+__device__ __forceinline__ void rowprod_stage(const double *As, const double *Bs, int tx, int ty,
+                                              double (&acc)[BM / 16][2]) {
+#pragma unroll 4
+    for (int kk = 0; kk < kTK; kk++) {
+        const double b0 = Bs[kk * 32 + tx];
+        const double b1 = TWO ? Bs[kk * 32 + tx + 16] : 0.0;
+#pragma unroll
+        for (int i = 0; i < NI; i++) {
+            const double a = As[kk * BM + ty + 16 * i];
+            acc[i][0] = fma(a, b0, acc[i][0]);
+            if (TWO) acc[i][1] = fma(a, b1, acc[i][1]);
+        }
+    }
+}
+
 template <int OP>
 __global__ void __launch_bounds__(kThreads) k_adj_rowprod(const AdjDesc *__restrict__ ad,
                                                           const int4 *__restrict__ items, int nitems) {
     constexpr bool kPart = OP == RP_MBP || OP == RP_FNBP;
-    constexpr int BM = kPart ? 64 : 32;     // rows of the output block
+    constexpr int BM = 32;                  // rows of the output block
     constexpr int MI = BM / 16;
     __shared__ double As[kTK * BM], Bs[kTK * 32];
     const int w = blockIdx.x;
     if (w >= nitems) return;
     const AdjDesc &A = *ad;
     const int4 it = items[w];
-    const int K = it.x, t = it.y, j0 = it.z * 32, i0 = it.w * 64;
+    const int K = it.x, t = it.y, j0 = it.z * 32, i0 = it.w * 32;
     const int s = A.super_ptr[K + 1] - A.super_ptr[K];
     const int64_t ld = A.rowptr[K + 1] - A.rowptr[K];
     const int c = (int)(ld - s);
@@ -519,7 +544,7 @@ __global__ void __launch_bounds__(kThreads) k_adj_rowprod(const AdjDesc *__restr
     const int p0 = t * rb;
     const int pm = c - p0 < rb ? (c - p0 > 0 ? c - p0 : 0) : rb;
     const int nj = s - j0 < 32 ? s - j0 : 32;
-    const int mrows = kPart ? (s - i0 < 64 ? s - i0 : 64) : pm;
+    const int mrows = kPart ? (s - i0 < 32 ? s - i0 : 32) : pm;
     const int kdim = kPart ? pm : s;
     const int fc = A.super_ptr[K];
     const double *Zb = A.Zb + off;
@@ -547,8 +572,14 @@ __global__ void __launch_bounds__(kThreads) k_adj_rowprod(const AdjDesc *__restr
         if (OP == RP_FABAR) return k >= j ? A.Linv[A.linv_off[K] + (int64_t)j * s + k] / A.D[fc + k] : 0.0;
         return A.Lb[off + (int64_t)j * ld + s + p0 + k];
     };
-    // thread (tx, ty) owns rows ty + 16 i and columns tx + 16 j of the block
+    // thread (tx, ty) owns rows ty + 16 i and columns tx + 16 j of the block.
+    // A warp holds rows 2 warp, 2 warp + 1 (+ 16 i): the row blocks with no
+    // row of the item, and the second column half when nj <= 16, are skipped
+    // (warp-uniform), which for the narrow supernodes is most of the block.
     const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+    const int wrow = 2 * (threadIdx.x / 32);
+    const int ni = mrows > wrow ? min((mrows - wrow + 15) / 16, MI) : 0;
+    const int sel = ni * 2 + (nj > 16 ? 1 : 0);
     double acc[MI][2];
 #pragma unroll
     for (int i = 0; i < MI; i++) acc[i][0] = acc[i][1] = 0.0;
@@ -563,15 +594,16 @@ __global__ void __launch_bounds__(kThreads) k_adj_rowprod(const AdjDesc *__restr
             Bs[kk * 32 + jl] = (k < kdim && jl < nj) ? b_at(k, jl) : 0.0;
         }
         __syncthreads();
-#pragma unroll 4
-        for (int kk = 0; kk < kTK; kk++) {
-            const double b0 = Bs[kk * 32 + tx], b1 = Bs[kk * 32 + tx + 16];
-#pragma unroll
-            for (int i = 0; i < MI; i++) {
-                const double a = As[kk * BM + ty + 16 * i];
-                acc[i][0] = fma(a, b0, acc[i][0]);
-                acc[i][1] = fma(a, b1, acc[i][1]);
-            }
+        switch (sel) {
+        case 2: rowprod_stage<1, false, BM>(As, Bs, tx, ty, acc); break;
+        case 3: rowprod_stage<1, true, BM>(As, Bs, tx, ty, acc); break;
+        case 4: rowprod_stage<2, false, BM>(As, Bs, tx, ty, acc); break;
+        case 5: rowprod_stage<2, true, BM>(As, Bs, tx, ty, acc); break;
+        case 6: if constexpr (MI >= 3) rowprod_stage<3, false, BM>(As, Bs, tx, ty, acc); break;
+        case 7: if constexpr (MI >= 3) rowprod_stage<3, true, BM>(As, Bs, tx, ty, acc); break;
+        case 8: if constexpr (MI >= 4) rowprod_stage<4, false, BM>(As, Bs, tx, ty, acc); break;
+        case 9: if constexpr (MI >= 4) rowprod_stage<4, true, BM>(As, Bs, tx, ty, acc); break;
+        default: break;
         }
     }
 #pragma unroll
@@ -803,21 +835,30 @@ __global__ void k_gather_vals(const int64_t *__restrict__ pos, const double *__r
 // 4 * linv_off[J] (selinv: Mbar, W, T1; factorization: Nbar, T2, N, U).
 // ---------------------------------------------------------------------------
 enum { OP_SEL_T1 = 0, OP_SEL_W, OP_SEL_LB, OP_FAC_T2, OP_FAC_U, OP_FAC_T3, OP_FAC_G1, OP_FAC_G2 };
+constexpr int kFinChunk = 1024;   // entries of an s x s block per item of the partial sums
 
 // C (16 x 16 tile) of an s x s product; items (J, tile), tiles row-major over
 // ceil(s/16)^2 (16 CTAs per 64 columns: the top levels hold one or two
-// supernodes).  256 threads, one output each, k staged 32 at a time.
+// supernodes).  Q = 1: a CTA of 256 threads per tile, one output each; Q = 4
+// (levels with fewer tiles than SMs): four CTAs of 64 threads per tile, an
+// 8 x 8 quarter each, so that the FP64 work spreads over four times the SMs.
+// k staged 32 at a time.
 constexpr int kGT = 16;
+template <int Q>
 __global__ void __launch_bounds__(256) k_adj_gemm(const AdjDesc *__restrict__ ad, int op,
                                                   const int2 *__restrict__ items, int nitems) {
-    __shared__ double As[kGT][33], Bs[32][kGT + 1];
-    const int w = blockIdx.x;
+    constexpr int GT = Q == 1 ? kGT : kGT / 2;   // output tile side of the CTA
+    constexpr int NT = GT * GT;                  // threads
+    __shared__ double As[GT][33], Bs[32][GT + 1];
+    const int w = blockIdx.x / Q, qd = blockIdx.x % Q;
     if (w >= nitems) return;
     const AdjDesc &A = *ad;
     const int J = items[w].x;
     const int s = A.super_ptr[J + 1] - A.super_ptr[J];
     const int nt = (s + kGT - 1) / kGT;
-    const int i0 = (items[w].y / nt) * kGT, j0 = (items[w].y % nt) * kGT;
+    const int i0 = (items[w].y / nt) * kGT + (Q == 1 ? 0 : (qd / 2) * GT);
+    const int j0 = (items[w].y % nt) * kGT + (Q == 1 ? 0 : (qd % 2) * GT);
+    if (i0 >= s || j0 >= s) return;
     const int64_t ss = (int64_t)s * s;
     const int64_t ld = A.rowptr[J + 1] - A.rowptr[J];
     const double *M = A.Linv + A.linv_off[J];             // M(i, k) = M[k*s + i]
@@ -849,18 +890,27 @@ __global__ void __launch_bounds__(256) k_adj_gemm(const AdjDesc *__restrict__ ad
         default: return F[ss + (int64_t)j * s + k];                   // P M
         }
     };
-    const int tx = threadIdx.x % kGT, ty = threadIdx.x / kGT;
+    const int tx = threadIdx.x % GT, ty = threadIdx.x / GT;
+    // a warp holds 32 / GT rows of the tile: warps past s skip the products,
+    // and the last k stage stops at s
+    const bool wact = i0 + (32 / GT) * (int)(threadIdx.x / 32) < s;
     double acc = 0.0;
     for (int k0 = 0; k0 < s; k0 += 32) {
         __syncthreads();
-        for (int e = threadIdx.x; e < kGT * 32; e += 256) {
-            const int r = e % kGT, q = e / kGT;
+        for (int e = threadIdx.x; e < GT * 32; e += NT) {
+            const int r = e % GT, q = e / GT;
             As[r][q] = (i0 + r < s && k0 + q < s) ? a_at(i0 + r, k0 + q) : 0.0;
             Bs[q][r] = (k0 + q < s && j0 + r < s) ? b_at(k0 + q, j0 + r) : 0.0;
         }
         __syncthreads();
+        if (wact) {
+            if (s - k0 >= 32) {
 #pragma unroll 8
-        for (int q = 0; q < 32; q++) acc = fma(As[ty][q], Bs[q][tx], acc);
+                for (int q = 0; q < 32; q++) acc = fma(As[ty][q], Bs[q][tx], acc);
+            } else {
+                for (int q = 0; q < s - k0; q++) acc = fma(As[ty][q], Bs[q][tx], acc);
+            }
+        }
     }
     double *Lb = A.Lb + A.panel_off[J];
     const int i = i0 + ty, j = j0 + tx;
@@ -880,21 +930,21 @@ __global__ void __launch_bounds__(256) k_adj_gemm(const AdjDesc *__restrict__ ad
     }
 }
 
-// selinv adjoint: Mbar = sum of the tile partials + 2 D^{-1} T1 (T1 = M S)
+// selinv adjoint: Mbar = sum of the tile partials + 2 D^{-1} T1 (T1 = M S);
+// items (J, chunk of kFinChunk entries | ntiles << 16)
 __global__ void __launch_bounds__(256) k_adj_sel_mbar(const AdjDesc *__restrict__ ad,
                                                       const int2 *__restrict__ items, int nitems) {
     const int w = blockIdx.x;
     if (w >= nitems) return;
     const AdjDesc &A = *ad;
-    const int J = items[w].x, chunk = items[w].y;
+    const int J = items[w].x, chunk = items[w].y & 0xFFFF, ntiles = items[w].y >> 16;
     const int fc = A.super_ptr[J];
     const int s = A.super_ptr[J + 1] - fc;
-    const int ntiles = items[w].y >> 16;
     const int64_t ss = (int64_t)s * s;
-    double *F = A.fin + 4 * A.linv_off[J];
-    const double *part = A.partial + A.part_off[J];
-    for (int64_t e = (int64_t)(chunk & 0xFFFF) * 4096 + threadIdx.x; e < ss && e < (int64_t)((chunk & 0xFFFF) + 1) * 4096;
-         e += blockDim.x) {
+    double *__restrict__ F = A.fin + 4 * A.linv_off[J];
+    const double *__restrict__ part = A.partial + A.part_off[J];
+    const int64_t e1 = (int64_t)(chunk + 1) * kFinChunk < ss ? (int64_t)(chunk + 1) * kFinChunk : ss;
+    for (int64_t e = (int64_t)chunk * kFinChunk + threadIdx.x; e < e1; e += blockDim.x) {
         const int i = (int)(e % s);
         double v = 0.0;
         for (int t = 0; t < ntiles; t++) v += part[t * ss + e];
@@ -902,9 +952,12 @@ __global__ void __launch_bounds__(256) k_adj_sel_mbar(const AdjDesc *__restrict_
     }
 }
 
-// selinv adjoint: Dbar_k = -(M S M^T)_kk / D_k^2 = -sum_a T1(k, a) M(k, a) / D_k^2
-__global__ void __launch_bounds__(128) k_adj_sel_dbar(const AdjDesc *__restrict__ ad,
+// selinv adjoint: Dbar_k = -(M S M^T)_kk / D_k^2 = -sum_a T1(k, a) M(k, a) / D_k^2;
+// grid (supernodes, kFinY): 32 values of k per pass, the eight warps take
+// every eighth a, their sums added in a fixed order
+__global__ void __launch_bounds__(256) k_adj_sel_dbar(const AdjDesc *__restrict__ ad,
                                                       const int *__restrict__ js, int nj) {
+    __shared__ double red[8][33];
     const int w = blockIdx.x;
     if (w >= nj) return;
     const AdjDesc &A = *ad;
@@ -912,16 +965,28 @@ __global__ void __launch_bounds__(128) k_adj_sel_dbar(const AdjDesc *__restrict_
     const int fc = A.super_ptr[J];
     const int s = A.super_ptr[J + 1] - fc;
     const int64_t ss = (int64_t)s * s;
-    const double *M = A.Linv + A.linv_off[J];
-    const double *T1 = A.fin + 4 * A.linv_off[J] + 2 * ss;
-    for (int k = threadIdx.x; k < s; k += blockDim.x) {
+    const double *__restrict__ M = A.Linv + A.linv_off[J];
+    const double *__restrict__ T1 = A.fin + 4 * A.linv_off[J] + 2 * ss;
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    for (int kb = blockIdx.y; kb * 32 < s; kb += gridDim.y) {
+        const int k = kb * 32 + lane;
         double v = 0.0;
-        for (int a = 0; a < s; a++) v = fma(T1[(int64_t)a * s + k], M[(int64_t)a * s + k], v);
-        A.Db[fc + k] = -v / (A.D[fc + k] * A.D[fc + k]);
+        if (k < s)
+            for (int a = warp; a < s; a += 8) v = fma(T1[(int64_t)a * s + k], M[(int64_t)a * s + k], v);
+        red[warp][lane] = v;
+        __syncthreads();
+        if (warp == 0 && k < s) {
+            double t = 0.0;
+#pragma unroll
+            for (int q = 0; q < 8; q++) t += red[q][lane];
+            A.Db[fc + k] = -t / (A.D[fc + k] * A.D[fc + k]);
+        }
+        __syncthreads();
     }
 }
 
-// factorization adjoint: Nbar = sum of the tile partials; N = M^T D^{-1}
+// factorization adjoint: Nbar = sum of the tile partials; N = M^T D^{-1};
+// items as in k_adj_sel_mbar
 __global__ void __launch_bounds__(256) k_fadj_nbar(const AdjDesc *__restrict__ ad,
                                                    const int2 *__restrict__ items, int nitems) {
     const int w = blockIdx.x;
@@ -931,10 +996,11 @@ __global__ void __launch_bounds__(256) k_fadj_nbar(const AdjDesc *__restrict__ a
     const int fc = A.super_ptr[J];
     const int s = A.super_ptr[J + 1] - fc;
     const int64_t ss = (int64_t)s * s;
-    double *F = A.fin + 4 * A.linv_off[J];
-    const double *M = A.Linv + A.linv_off[J];
-    const double *part = A.partial + A.part_off[J];
-    for (int64_t e = (int64_t)chunk * 4096 + threadIdx.x; e < ss && e < (int64_t)(chunk + 1) * 4096; e += blockDim.x) {
+    double *__restrict__ F = A.fin + 4 * A.linv_off[J];
+    const double *__restrict__ M = A.Linv + A.linv_off[J];
+    const double *__restrict__ part = A.partial + A.part_off[J];
+    const int64_t e1 = (int64_t)(chunk + 1) * kFinChunk < ss ? (int64_t)(chunk + 1) * kFinChunk : ss;
+    for (int64_t e = (int64_t)chunk * kFinChunk + threadIdx.x; e < e1; e += blockDim.x) {
         const int i = (int)(e % s), j = (int)(e / s);
         double v = 0.0;
         for (int t = 0; t < ntiles; t++) v += part[t * ss + e];
@@ -944,9 +1010,11 @@ __global__ void __launch_bounds__(256) k_fadj_nbar(const AdjDesc *__restrict__ a
 }
 
 // factorization adjoint: U = D L^T gives Dbar_i += sum_{j>=i} Ubar(i,j) L(j,i),
-// Lbar(j,i) += Ubar(i,j) D_i (j > i)
+// Lbar(j,i) += Ubar(i,j) D_i (j > i); grid (supernodes, kFinY), the sums as
+// in k_adj_sel_dbar
 __global__ void __launch_bounds__(256) k_fadj_ubar(const AdjDesc *__restrict__ ad,
                                                    const int *__restrict__ js, int nj) {
+    __shared__ double red[8][33];
     const int w = blockIdx.x;
     if (w >= nj) return;
     const AdjDesc &A = *ad;
@@ -955,16 +1023,27 @@ __global__ void __launch_bounds__(256) k_fadj_ubar(const AdjDesc *__restrict__ a
     const int s = A.super_ptr[J + 1] - fc;
     const int64_t ss = (int64_t)s * s;
     const int64_t ld = A.rowptr[J + 1] - A.rowptr[J];
-    const double *U = A.fin + 4 * A.linv_off[J] + 3 * ss;
-    const double *L = A.L + A.panel_off[J];
-    double *Lb = A.Lb + A.panel_off[J];
-    for (int i = threadIdx.x; i < s; i += blockDim.x) {
-        double v = U[(int64_t)i * s + i];
-        for (int j = i + 1; j < s; j++) v = fma(U[(int64_t)j * s + i], L[(int64_t)i * ld + j], v);
-        A.Db[fc + i] += v;
+    const double *__restrict__ U = A.fin + 4 * A.linv_off[J] + 3 * ss;
+    const double *__restrict__ L = A.L + A.panel_off[J];
+    double *__restrict__ Lb = A.Lb + A.panel_off[J];
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    for (int ib = blockIdx.y; ib * 32 < s; ib += gridDim.y) {
+        const int i = ib * 32 + lane;
+        double v = 0.0;
+        if (i < s)
+            for (int j = i + 1 + warp; j < s; j += 8) v = fma(U[(int64_t)j * s + i], L[(int64_t)i * ld + j], v);
+        red[warp][lane] = v;
+        __syncthreads();
+        if (warp == 0 && i < s) {
+            double t = U[(int64_t)i * s + i];
+#pragma unroll
+            for (int q = 0; q < 8; q++) t += red[q][lane];
+            A.Db[fc + i] += t;
+        }
+        __syncthreads();
     }
-    for (int e = threadIdx.x; e < s * s; e += blockDim.x) {
-        const int j = e % s, i = e / s;
+    for (int64_t e = (int64_t)blockIdx.y * blockDim.x + threadIdx.x; e < ss; e += (int64_t)gridDim.y * blockDim.x) {
+        const int j = (int)(e % s), i = (int)(e / s);
         if (j > i) Lb[(int64_t)i * ld + j] += U[(int64_t)j * s + i] * A.D[fc + i];
     }
 }
@@ -976,6 +1055,7 @@ __global__ void __launch_bounds__(256) k_fadj_ubar(const AdjDesc *__restrict__ a
 // and the full-matrix gradient is G = L^{-T} P L^{-1} = M^T P M (M = L_JJ^{-1};
 // three s x s products in k_adj_gemm).  The stored lower entries of the
 // symmetric block get G(i,j) + G(j,i) below the diagonal, G(i,i) on it.
+// Grid (supernodes, kFinY).
 __global__ void __launch_bounds__(256) k_fadj_fold(const AdjDesc *__restrict__ ad,
                                                    const int *__restrict__ js, int nj) {
     const int w = blockIdx.x;
@@ -985,10 +1065,10 @@ __global__ void __launch_bounds__(256) k_fadj_fold(const AdjDesc *__restrict__ a
     const int s = A.super_ptr[J + 1] - A.super_ptr[J];
     const int64_t ld = A.rowptr[J + 1] - A.rowptr[J];
     const int64_t ss = (int64_t)s * s;
-    const double *G = A.fin + 4 * A.linv_off[J] + 2 * ss;
-    double *Ab = A.Ab + A.panel_off[J];
-    for (int e = threadIdx.x; e < s * s; e += blockDim.x) {
-        const int i = e % s, k = e / s;
+    const double *__restrict__ G = A.fin + 4 * A.linv_off[J] + 2 * ss;
+    double *__restrict__ Ab = A.Ab + A.panel_off[J];
+    for (int64_t e = (int64_t)blockIdx.y * blockDim.x + threadIdx.x; e < ss; e += (int64_t)gridDim.y * blockDim.x) {
+        const int i = (int)(e % s), k = (int)(e / s);
         Ab[(int64_t)k * ld + i] = i > k ? G[(int64_t)k * s + i] + G[(int64_t)i * s + k]
                                         : (i == k ? G[(int64_t)k * s + i] : 0.0);
     }
@@ -1022,10 +1102,11 @@ template <template <int> class KF> struct Dummy {};
 
 static void launch_level_gemm(AdjData *a, int op, int li, cudaStream_t st) {
     const int64_t g0 = a->g_lptr[li], g1 = a->g_lptr[li + 1];
-    if (g1 > g0) {
-        k_adj_gemm<<<(int)(g1 - g0), 256, 0, st>>>(a->d_desc, op, a->d_gitems + g0, (int)(g1 - g0));
-        note_launch();
-    }
+    const int n = (int)(g1 - g0);
+    if (n <= 0) return;
+    if (n < kNumSMs) k_adj_gemm<4><<<4 * n, kGT * kGT / 4, 0, st>>>(a->d_desc, op, a->d_gitems + g0, n);
+    else k_adj_gemm<1><<<n, kGT * kGT, 0, st>>>(a->d_desc, op, a->d_gitems + g0, n);
+    note_launch();
 }
 
 static void launch_bucket(int kind, int b, const AdjDesc *d, const Item *items, int n, cudaStream_t st) {
@@ -1066,6 +1147,7 @@ void adjoint_release(void *p) {
     if (a->g_sel) cudaGraphExecDestroy(a->g_sel);
     if (a->g_fac) cudaGraphExecDestroy(a->g_fac);
     a->tcs.release();
+    a->tcn.release();
     delete a;
 }
 
@@ -1106,7 +1188,7 @@ static int adj_build(selinv_plan_s *plan) {
             const int s = p.super_ptr[J + 1] - p.super_ptr[J];
             const int nt = (s + kGT - 1) / kGT;
             for (int t = 0; t < nt * nt; t++) a->gitems.push_back(make_int2(J, t));
-            const int nch = (int)(((int64_t)s * s + 4095) / 4096);
+            const int nch = (int)(((int64_t)s * s + kFinChunk - 1) / kFinChunk);
             for (int ch = 0; ch < nch; ch++) a->citems.push_back(make_int2(J, ch | (p.ntiles[J] << 16)));
             a->js.push_back(J);
             for (int jb = 0; jb < (s + 7) / 8; jb++) a->cz_work.push_back(make_int2(J, jb));
@@ -1185,12 +1267,12 @@ static int adj_normalize(selinv_plan_s *plan, const void *L, const void *D, cuda
     AdjData *a = static_cast<AdjData *>(plan->factor->adj);
     ProbDesc pd = make_desc(plan->data, plan->ws[0], SELINV_F64, L, D, nullptr, false);
     cudaMemcpyAsync(a->d_pdesc, &pd, sizeof(pd), cudaMemcpyHostToDevice, st);
-    if (!a->tcs.launches.empty()) {
+    if (!a->tcn.launches.empty()) {
         // the forward's own normalization launches (Lhat of the wide supernodes on the tensor cores)
-        for (const Launch &Ln : a->tcs.launches)
+        for (const Launch &Ln : a->tcn.launches)
             if (Ln.kind == KL_LINV || Ln.kind == KL_DINV || Ln.kind == KL_LINV_DIGITS || Ln.kind == KL_LHAT_OZ ||
                 Ln.kind == KL_LHAT) {
-                launch_with(a->tcs, Ln, a->d_pdesc, st);
+                launch_with(a->tcn, Ln, a->d_pdesc, st);
                 note_launch();
             }
         return cudaGetLastError() == cudaSuccess ? SELINV_OK : SELINV_ERR_CUDA;
@@ -1214,9 +1296,10 @@ static int adj_split(selinv_plan_s *plan) {
     const PlanData &p = plan->data;
     const selinv_opts &o = p.opts;
     // (at least 8 columns: narrower supernodes keep the fused kernels, whose
-    // one CTA per tile wastes less than 32-column blocks would).  Any tensor
-    // engine of the forward means tcgen05 here: the reverse passes have no
-    // mma.sync variant.
+    // one CTA per tile wastes less than 32-column blocks would, unless C has
+    // kAdjWideC rows or more: there one fused CTA per tile would run the whole
+    // gather over C alone).  Any tensor engine of the forward means tcgen05
+    // here: the reverse passes have no mma.sync variant.
     const int key = o.fast_contraction != 0 ? std::max(8, o.oz_min_s) : 0;
     if (key == a->split_key) return SELINV_OK;
     auto fr = [](void *q) { if (q) cudaFree(q); };
@@ -1232,19 +1315,25 @@ static int adj_split(selinv_plan_s *plan) {
     int64_t sy_max = 0;
     a->tcs.release();
     a->tcs.launches.clear();
+    a->tcn.release();
+    a->tcn.launches.clear();
     a->sm_items.clear(); a->wd_items.clear(); a->row_items.clear(); a->mbp_items.clear(); a->dig_work.clear();
     a->pr_items.clear(); a->sd_work.clear();
     a->sm_bptr.assign(1, 0); a->wd_lptr.assign(1, 0); a->row_lptr.assign(1, 0); a->mbp_lptr.assign(1, 0); a->dig_lptr.assign(1, 0);
     a->pr_lptr.assign(1, 0); a->sd_lptr.assign(1, 0);
     std::vector<int64_t> sd_off(p.ns + 1, 0);
     a->tc_launch.assign(p.nlevels, {});
-    auto wide = [&](int s) { return key > 0 && s >= key; };
+    auto wide = [&](int s, int64_t c) { return key > 0 && (s >= key || c >= kAdjWideC); };
+    auto wideK = [&](int32_t J) {
+        const int s = p.super_ptr[J + 1] - p.super_ptr[J];
+        return wide(s, p.rowptr[J + 1] - p.rowptr[J] - s);
+    };
     for (int l = p.nlevels - 1; l >= 0; l--) {
         for (int b = 0; b < kNumBuckets; b++) {
             for (int64_t e = p.level_ptr[l]; e < p.level_ptr[l + 1]; e++) {
                 const int32_t J = p.level_list[e];
                 const int s = p.super_ptr[J + 1] - p.super_ptr[J];
-                if (wide(s) || bucket_of(s) != b) continue;
+                if (wideK(J) || bucket_of(s) != b) continue;
                 for (int t = 0; t < p.ntiles[J]; t++) a->sm_items.push_back({0, J, t, p.ntiles[J]});
             }
             a->sm_bptr.push_back((int)a->sm_items.size());
@@ -1252,7 +1341,7 @@ static int adj_split(selinv_plan_s *plan) {
         for (int64_t e = p.level_ptr[l]; e < p.level_ptr[l + 1]; e++) {
             const int32_t J = p.level_list[e];
             const int s = p.super_ptr[J + 1] - p.super_ptr[J];
-            if (!wide(s)) continue;
+            if (!wideK(J)) continue;
             const int64_t c = p.rowptr[J + 1] - p.rowptr[J] - s;
             const int nch = (s + 31) / 32;
             for (int t = 0; t < p.ntiles[J]; t++) a->wd_items.push_back({0, J, t, p.ntiles[J]});
@@ -1260,7 +1349,7 @@ static int adj_split(selinv_plan_s *plan) {
                 for (int ch = 0; ch < nch; ch++) a->row_items.push_back(make_int4(J, b, ch, 0));
             for (int t = 0; t < p.ntiles[J]; t++)
                 for (int ch = 0; ch < nch; ch++)
-                    for (int h = 0; h < (s + 63) / 64; h++) a->mbp_items.push_back(make_int4(J, t, ch, h));
+                    for (int h = 0; h < (s + 31) / 32; h++) a->mbp_items.push_back(make_int4(J, t, ch, h));
             if (c > 0)
                 for (int jb = 0; jb < (s + 7) / 8; jb++) a->dig_work.push_back(make_int2(0, (J << 8) | jb));
             for (int64_t t = 0; t < (c + kTcWideRows - 1) / kTcWideRows; t++) a->pr_items.push_back({0, J, (int)t, 1});
@@ -1280,7 +1369,7 @@ static int adj_split(selinv_plan_s *plan) {
             const int s = p.super_ptr[J + 1] - p.super_ptr[J];
             const int64_t c = p.rowptr[J + 1] - p.rowptr[J] - s;
             if (c == 0) continue;
-            if (!wide(s)) {
+            if (!wide(s, c)) {
                 const int nvt = (int)((c + kVB - 1) / kVB);
                 for (int ti = 0; ti < nvt; ti++)
                     for (int tj = 0; tj <= ti; tj++) a->vn_items.push_back(make_int4(J, ti, tj, 0));
@@ -1302,7 +1391,7 @@ static int adj_split(selinv_plan_s *plan) {
     }
     for (int32_t J = 0; J < p.ns; J++) {
         const int64_t s = p.super_ptr[J + 1] - p.super_ptr[J];
-        sd_off[J + 1] = sd_off[J] + (wide((int)s) ? 7 * ((s + 63) / 64 * 64) * ((s + 15) / 16 * 16) : 0);
+        sd_off[J + 1] = sd_off[J] + (wideK(J) ? 7 * ((s + 63) / 64 * 64) * ((s + 15) / 16 * 16) : 0);
     }
     int rc;
     if ((rc = upl(&a->d_sm, a->sm_items)) || (rc = upl(&a->d_wd, a->wd_items)) || (rc = upl(&a->d_row, a->row_items)) ||
@@ -1323,16 +1412,25 @@ static int adj_split(selinv_plan_s *plan) {
     if (!a->d_pdp && cudaMalloc((void **)&a->d_pdp, 5 * sizeof(ProbDesc)) != cudaSuccess) return SELINV_ERR_OOM;
     if (!a->dig_work.empty()) {
         // the forward's level schedule supplies the tcgen05 items of every
-        // level (row tiles, column tiles, k-splits) and their reductions
-        // (every supernode: a subset selection of the forward does not apply here)
+        // level (row tiles, column tiles, k-splits) and their reductions, built
+        // for exactly the wide supernodes (as the selection, whatever width;
+        // a subset selection of the forward does not apply here)
         const ProbDesc pd = make_desc(p, plan->ws[0], SELINV_F64, nullptr, nullptr, nullptr, false);
-        std::vector<uint8_t> sel;
+        std::vector<uint8_t> sel(p.ns, 0);
+        for (int32_t J = 0; J < p.ns; J++) sel[J] = wideK(J) ? 1 : 0;
         sel.swap(plan->data.active);
-        const int fcon = plan->data.opts.fast_contraction;
+        const int fcon = plan->data.opts.fast_contraction, ozm = plan->data.opts.oz_min_s;
         plan->data.opts.fast_contraction = 1;
+        plan->data.opts.oz_min_s = kOzMinS;
         rc = build_schedule(a->tcs, {&p}, {pd}, SELINV_SCHED_LEVEL);
-        plan->data.opts.fast_contraction = fcon;
+        plan->data.opts.oz_min_s = ozm;
         sel.swap(plan->data.active);
+        // and the normalization of every supernode, as the forward runs it
+        sel.clear();
+        sel.swap(plan->data.active);
+        if (!rc) rc = build_schedule(a->tcn, {&p}, {pd}, SELINV_SCHED_LEVEL);
+        sel.swap(plan->data.active);
+        plan->data.opts.fast_contraction = fcon;
         if (rc) return rc;
         for (int e = 0; e < (int)a->tcs.launches.size(); e++) {
             const Launch &L = a->tcs.launches[e];
@@ -1352,6 +1450,7 @@ static int adj_split(selinv_plan_s *plan) {
 static void adj_refresh(selinv_plan_s *plan) {
     AdjData *a = static_cast<AdjData *>(plan->factor->adj);
     a->tcs.spin_limit = plan->data.opts.spin_limit;
+    a->tcn.spin_limit = plan->data.opts.spin_limit;
 }
 
 static int adj_prepare(selinv_plan_s *plan) {
@@ -1452,7 +1551,7 @@ extern "C" int selinv_adjoint(selinv_plan plan, selinv_dtype dtype, const void *
                            static_cast<const double *>(Z), static_cast<double *>(Lbar),
                            static_cast<double *>(Dbar));
     cudaMemcpyAsync(a->d_desc, &h, sizeof(h), cudaMemcpyHostToDevice, st);
-    k_adj_fold<<<p.ns, 256, 0, st>>>(a->d_desc, p.ns);
+    k_adj_fold<<<dim3(p.ns, kFinY), 256, 0, st>>>(a->d_desc, p.ns);
     note_launch();
     FactorData *f = plan->factor;
     cudaMemsetAsync(a->V, 0, 8 * (size_t)std::max<int64_t>(f->u_off[p.ns], 1), st);
@@ -1542,7 +1641,7 @@ extern "C" int selinv_adjoint(selinv_plan plan, selinv_dtype dtype, const void *
             if (c1 > c0) { k_adj_sel_mbar<<<(int)(c1 - c0), 256, 0, st>>>(a->d_desc, a->d_citems + c0, (int)(c1 - c0)); note_launch(); }
             launch_level_gemm(a, OP_SEL_W, li, st);
             launch_level_gemm(a, OP_SEL_LB, li, st);
-            if (j1 > j0) { k_adj_sel_dbar<<<(int)(j1 - j0), 128, 0, st>>>(a->d_desc, a->d_js + j0, (int)(j1 - j0)); note_launch(); }
+            if (j1 > j0) { k_adj_sel_dbar<<<dim3((int)(j1 - j0), kFinY), 256, 0, st>>>(a->d_desc, a->d_js + j0, (int)(j1 - j0)); note_launch(); }
         }
     };
     return run_captured(a->g_sel, a->g_sel_n, a->g_sel_key, a->g_sel_ws, a->gen, w.colexpZ, st, levels);
@@ -1629,14 +1728,14 @@ extern "C" int selinv_factor_adjoint(selinv_plan plan, selinv_dtype dtype, const
             launch_level_gemm(a, OP_FAC_T2, li, st);
             launch_level_gemm(a, OP_FAC_U, li, st);
             if (j1 > j0) {
-                k_fadj_ubar<<<(int)(j1 - j0), 256, 0, st>>>(a->d_desc, a->d_js + j0, (int)(j1 - j0));
+                k_fadj_ubar<<<dim3((int)(j1 - j0), kFinY), 256, 0, st>>>(a->d_desc, a->d_js + j0, (int)(j1 - j0));
                 note_launch();
             }
             launch_level_gemm(a, OP_FAC_T3, li, st);
             launch_level_gemm(a, OP_FAC_G1, li, st);
             launch_level_gemm(a, OP_FAC_G2, li, st);
             if (j1 > j0) {
-                k_fadj_fold<<<(int)(j1 - j0), 256, 0, st>>>(a->d_desc, a->d_js + j0, (int)(j1 - j0));
+                k_fadj_fold<<<dim3((int)(j1 - j0), kFinY), 256, 0, st>>>(a->d_desc, a->d_js + j0, (int)(j1 - j0));
                 note_launch();
                 const int z0 = (int)a->cz_lptr[li], z1 = (int)a->cz_lptr[li + 1];
                 if (tc && li > 0 && z1 > z0) {

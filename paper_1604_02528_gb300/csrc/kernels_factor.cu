@@ -57,7 +57,7 @@ __global__ void __launch_bounds__(256) k_fasm(const FactorDesc *__restrict__ fd,
     T *UJ = static_cast<T *>(F.U) + F.u_off[J];
     T *PJ = static_cast<T *>(F.L) + F.panel_off[J];
     const int64_t cc = (int64_t)cch * cch;
-    for (int64_t e = (int64_t)chunk * 4096 + threadIdx.x; e < cc && e < (int64_t)(chunk + 1) * 4096; e += 256) {
+    for (int64_t e = (int64_t)chunk * kAsmChunk + threadIdx.x; e < cc && e < (int64_t)(chunk + 1) * kAsmChunk; e += 256) {
         const int a = (int)(e % cch), b = (int)(e / cch);
         if (a < b) continue;
         const T v = Uc[e];
@@ -241,7 +241,7 @@ int factor_tables(selinv_plan_s *plan) {
                 if (r >= nchild[K]) continue;
                 const int32_t ch = kids[kid_ptr[K] + r];
                 const int64_t cc = f->u_off[ch + 1] - f->u_off[ch];
-                for (int64_t ck = 0; ck < (cc + 4095) / 4096; ck++) f->asm_items.push_back(make_int2(ch, (int)ck));
+                for (int64_t ck = 0; ck < (cc + kAsmChunk - 1) / kAsmChunk; ck++) f->asm_items.push_back(make_int2(ch, (int)ck));
             }
             f->asm_lptr.push_back((int64_t)f->asm_items.size());
         }

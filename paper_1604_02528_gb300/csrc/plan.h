@@ -131,6 +131,7 @@ constexpr int kTcRows = 128;   // rows of C per tcgen05 item
 constexpr int kTcChunkSteps = 8;   // k16 steps per exact fp32 chunk of the tensor-core kernels (k-ranges are whole chunks)
 constexpr int kTcWide = 128;   // launch bucket of the transposed tcgen05 kernel (supernodes wider than 64)
 constexpr int kTcWideRows = 64;   // rows of C per item of that kernel
+constexpr int kAsmChunk = 1024;   // entries of an update matrix per extend-add item
 
 struct Launch {
     int kind;    // KL_*
@@ -219,7 +220,7 @@ struct FactorData {
     // with the selected-inversion adjoint)
     std::vector<int64_t> u_off;
     std::vector<int32_t> chpos;
-    std::vector<int2> asm_items;      // (child, 4096-entry chunk) per level and child rank
+    std::vector<int2> asm_items;      // (child, kAsmChunk-entry chunk) per level and child rank
     std::vector<int64_t> asm_lptr;    // [level * npass + rank]
     int npass = 1;
     std::vector<int4> uitems;         // (K, row tile, column tile) of the lower c x c, per level

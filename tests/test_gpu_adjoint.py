@@ -15,6 +15,8 @@ CASES = [
     ("diffusion-8", lambda: synth.diffusion_3d(8)),
     ("lap3d-12", lambda: synth.laplacian_3d(12, seed=44)),
     ("diffusion-16", lambda: synth.diffusion_3d(16)),
+    # narrow supernodes with 256 or more rows below: the split path whatever their width
+    ("rand400-long-c", lambda: synth.random_sparse_spd(400, 0.03, 46)),
 ]
 
 
