@@ -8,6 +8,15 @@
 
 namespace selinv {
 
+// Programmatic dependent launch: in the captured level loops every
+// kernel-to-kernel edge lets the next grid be scheduled once the previous one
+// has started all its blocks, so its launch overlaps the previous grid's
+// run; each kernel waits here, before it reads anything, until its
+// predecessor has completed and its memory operations are visible.  A grid
+// launched without such an edge passes at once.
+__device__ __forceinline__ void grid_dep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+
 // complex128 as two doubles.  Transposes are plain for complex symmetric
 // problems (A = A^T); a Hermitian problem (ProbDesc::herm) conjugates every
 // transposed factor (cjif below).

@@ -163,6 +163,7 @@ struct AdjData {
 // never run together: no conflicts, a fixed order.
 __global__ void __launch_bounds__(256) k_adj_asm(const AdjDesc *__restrict__ ad, const int2 *__restrict__ items,
                                                  int nitems) {
+    grid_dep_wait();
     const int w = blockIdx.x;
     if (w >= nitems) return;
     const AdjDesc &A = *ad;
@@ -194,6 +195,7 @@ __global__ void __launch_bounds__(256) k_adj_asm(const AdjDesc *__restrict__ ad,
 constexpr int kVB = 32;
 __global__ void __launch_bounds__(256) k_adj_vupd(const AdjDesc *__restrict__ ad, const int4 *__restrict__ items,
                                                   int nitems) {
+    grid_dep_wait();
     __shared__ SegSmem<double, kVB> sm;
     const int w = blockIdx.x;
     if (w >= nitems) return;
@@ -226,6 +228,7 @@ __global__ void __launch_bounds__(256) k_adj_vupd(const AdjDesc *__restrict__ ad
 // later step reads only the lower triangle of a diagonal block.  Grid
 // (supernodes, kFinY).
 __global__ void __launch_bounds__(256) k_adj_fold(const AdjDesc *__restrict__ ad, int ns) {
+    grid_dep_wait();
     const int K = blockIdx.x;
     if (K >= ns) return;
     const AdjDesc &A = *ad;
@@ -246,6 +249,7 @@ __global__ void __launch_bounds__(256) k_adj_fold(const AdjDesc *__restrict__ ad
 // S (tile 0) and Ybar rows of one tile
 __global__ void __launch_bounds__(256) k_adj_ybar(const AdjDesc *__restrict__ ad,
                                                   const Item *__restrict__ items, int nitems) {
+    grid_dep_wait();
     const int w = blockIdx.x;
     if (w >= nitems) return;
     const AdjDesc &A = *ad;
@@ -278,6 +282,7 @@ __global__ void __launch_bounds__(256) k_adj_ybar(const AdjDesc *__restrict__ ad
 template <int TN>
 __global__ void __launch_bounds__(kThreads) k_adj_lhbar(const AdjDesc *__restrict__ ad,
                                                         const Item *__restrict__ items, int nitems) {
+    grid_dep_wait();
     using Sh = Shape<TN>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     double *As = reinterpret_cast<double *>(smem_raw);
@@ -362,6 +367,7 @@ __global__ void __launch_bounds__(kThreads) k_adj_lhbar(const AdjDesc *__restric
 __global__ void __launch_bounds__(256) k_adj_colexpz(const AdjDesc *__restrict__ ad, const double *__restrict__ src,
                                                      int *__restrict__ colexpZ, const int2 *__restrict__ work,
                                                      int nwork) {
+    grid_dep_wait();
     const int w = blockIdx.x;
     if (w >= nwork) return;
     const AdjDesc &A = *ad;
@@ -409,6 +415,7 @@ template <int OP>
 __global__ void __launch_bounds__(256) k_small_digits(const AdjDesc *__restrict__ ad, const int2 *__restrict__ work,
                                                       int nwork, uint16_t *__restrict__ sd,
                                                       const int64_t *__restrict__ sd_off, int *__restrict__ sdexp) {
+    grid_dep_wait();
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
     const int w = blockIdx.x;
     if (w >= nwork) return;
@@ -458,6 +465,7 @@ __global__ void __launch_bounds__(256) k_small_digits(const AdjDesc *__restrict_
 __global__ void __launch_bounds__(256) k_syrk_digits(const AdjDesc *__restrict__ ad, const int2 *__restrict__ work,
                                                      int nwork, uint16_t *__restrict__ sy,
                                                      const int64_t *__restrict__ sy_off, int *__restrict__ syexp) {
+    grid_dep_wait();
     __shared__ int rowE[32];
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
     const int w = blockIdx.x;
@@ -527,6 +535,7 @@ __device__ __forceinline__ void rowprod_stage(const double *As, const double *Bs
 template <int OP>
 __global__ void __launch_bounds__(kThreads) k_adj_rowprod(const AdjDesc *__restrict__ ad,
                                                           const int4 *__restrict__ items, int nitems) {
+    grid_dep_wait();
     constexpr bool kPart = OP == RP_MBP || OP == RP_FNBP;
     constexpr int BM = 32;                  // rows of the output block
     constexpr int MI = BM / 16;
@@ -637,6 +646,7 @@ __global__ void __launch_bounds__(kThreads) k_adj_rowprod(const AdjDesc *__restr
 template <int TN>
 __global__ void __launch_bounds__(kThreads) k_fadj_pull(const AdjDesc *__restrict__ ad,
                                                         const Item *__restrict__ items, int nitems) {
+    grid_dep_wait();
     using Sh = Shape<TN>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     double *As = reinterpret_cast<double *>(smem_raw);
@@ -712,6 +722,7 @@ __global__ void __launch_bounds__(kThreads) k_fadj_pull(const AdjDesc *__restric
 // doubled diagonal adds Abar(C[p], C[p]) L_C(p, :) here.  A warp per column.
 __global__ void __launch_bounds__(256) k_fadj_pull_tc(const AdjDesc *__restrict__ ad,
                                                       const Item *__restrict__ items, int nitems) {
+    grid_dep_wait();
     __shared__ double dg[kTM];
     __shared__ int s_last;
     const int w = blockIdx.x;
@@ -769,6 +780,7 @@ __global__ void __launch_bounds__(256) k_fadj_pull_tc(const AdjDesc *__restrict_
 template <int TN>
 __global__ void __launch_bounds__(kThreads) k_fadj_trsm(const AdjDesc *__restrict__ ad,
                                                         const Item *__restrict__ items, int nitems) {
+    grid_dep_wait();
     extern __shared__ __align__(16) unsigned char smem_raw[];
     double *Ar = reinterpret_cast<double *>(smem_raw);    // [TM][TN] A_C rows
     double *Br = Ar + kTM * TN;                            // [TM][TN] Lbar_C rows
@@ -824,6 +836,7 @@ __global__ void __launch_bounds__(kThreads) k_fadj_trsm(const AdjDesc *__restric
 
 __global__ void k_gather_vals(const int64_t *__restrict__ pos, const double *__restrict__ src,
                               int64_t n, double *__restrict__ dst) {
+    grid_dep_wait();
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
         dst[e] = src[pos[e]];
 }
@@ -842,14 +855,16 @@ constexpr int kFinChunk = 1024;   // entries of an s x s block per item of the p
 // supernodes).  Q = 1: a CTA of 256 threads per tile, one output each; Q = 4
 // (levels with fewer tiles than SMs): four CTAs of 64 threads per tile, an
 // 8 x 8 quarter each, so that the FP64 work spreads over four times the SMs.
-// k staged 32 at a time.
+// k staged kGK at a time (one stage up to s = 128: one round of load latency).
 constexpr int kGT = 16;
+constexpr int kGK = 128;
 template <int Q>
 __global__ void __launch_bounds__(256) k_adj_gemm(const AdjDesc *__restrict__ ad, int op,
                                                   const int2 *__restrict__ items, int nitems) {
+    grid_dep_wait();
     constexpr int GT = Q == 1 ? kGT : kGT / 2;   // output tile side of the CTA
     constexpr int NT = GT * GT;                  // threads
-    __shared__ double As[GT][33], Bs[32][GT + 1];
+    __shared__ double As[GT][kGK + 1], Bs[kGK][GT + 1];
     const int w = blockIdx.x / Q, qd = blockIdx.x % Q;
     if (w >= nitems) return;
     const AdjDesc &A = *ad;
@@ -895,21 +910,25 @@ __global__ void __launch_bounds__(256) k_adj_gemm(const AdjDesc *__restrict__ ad
     // and the last k stage stops at s
     const bool wact = i0 + (32 / GT) * (int)(threadIdx.x / 32) < s;
     double acc = 0.0;
-    for (int k0 = 0; k0 < s; k0 += 32) {
+    for (int k0 = 0; k0 < s; k0 += kGK) {
+        const int kn = s - k0 < kGK ? s - k0 : kGK;
         __syncthreads();
-        for (int e = threadIdx.x; e < GT * 32; e += NT) {
+        for (int e = threadIdx.x; e < GT * kn; e += NT) {
             const int r = e % GT, q = e / GT;
-            As[r][q] = (i0 + r < s && k0 + q < s) ? a_at(i0 + r, k0 + q) : 0.0;
-            Bs[q][r] = (k0 + q < s && j0 + r < s) ? b_at(k0 + q, j0 + r) : 0.0;
+            As[r][q] = i0 + r < s ? a_at(i0 + r, k0 + q) : 0.0;
+            Bs[q][r] = j0 + r < s ? b_at(k0 + q, j0 + r) : 0.0;
         }
         __syncthreads();
         if (wact) {
-            if (s - k0 >= 32) {
-#pragma unroll 8
-                for (int q = 0; q < 32; q++) acc = fma(As[ty][q], Bs[q][tx], acc);
-            } else {
-                for (int q = 0; q < s - k0; q++) acc = fma(As[ty][q], Bs[q][tx], acc);
+            double a2 = 0.0;   // two chains: half the FMA latency per k
+            int q = 0;
+#pragma unroll 4
+            for (; q + 1 < kn; q += 2) {
+                acc = fma(As[ty][q], Bs[q][tx], acc);
+                a2 = fma(As[ty][q + 1], Bs[q + 1][tx], a2);
             }
+            if (q < kn) acc = fma(As[ty][q], Bs[q][tx], acc);
+            acc += a2;
         }
     }
     double *Lb = A.Lb + A.panel_off[J];
@@ -934,6 +953,7 @@ __global__ void __launch_bounds__(256) k_adj_gemm(const AdjDesc *__restrict__ ad
 // items (J, chunk of kFinChunk entries | ntiles << 16)
 __global__ void __launch_bounds__(256) k_adj_sel_mbar(const AdjDesc *__restrict__ ad,
                                                       const int2 *__restrict__ items, int nitems) {
+    grid_dep_wait();
     const int w = blockIdx.x;
     if (w >= nitems) return;
     const AdjDesc &A = *ad;
@@ -957,6 +977,7 @@ __global__ void __launch_bounds__(256) k_adj_sel_mbar(const AdjDesc *__restrict_
 // every eighth a, their sums added in a fixed order
 __global__ void __launch_bounds__(256) k_adj_sel_dbar(const AdjDesc *__restrict__ ad,
                                                       const int *__restrict__ js, int nj) {
+    grid_dep_wait();
     __shared__ double red[8][33];
     const int w = blockIdx.x;
     if (w >= nj) return;
@@ -989,6 +1010,7 @@ __global__ void __launch_bounds__(256) k_adj_sel_dbar(const AdjDesc *__restrict_
 // items as in k_adj_sel_mbar
 __global__ void __launch_bounds__(256) k_fadj_nbar(const AdjDesc *__restrict__ ad,
                                                    const int2 *__restrict__ items, int nitems) {
+    grid_dep_wait();
     const int w = blockIdx.x;
     if (w >= nitems) return;
     const AdjDesc &A = *ad;
@@ -1014,6 +1036,7 @@ __global__ void __launch_bounds__(256) k_fadj_nbar(const AdjDesc *__restrict__ a
 // in k_adj_sel_dbar
 __global__ void __launch_bounds__(256) k_fadj_ubar(const AdjDesc *__restrict__ ad,
                                                    const int *__restrict__ js, int nj) {
+    grid_dep_wait();
     __shared__ double red[8][33];
     const int w = blockIdx.x;
     if (w >= nj) return;
@@ -1058,6 +1081,7 @@ __global__ void __launch_bounds__(256) k_fadj_ubar(const AdjDesc *__restrict__ a
 // Grid (supernodes, kFinY).
 __global__ void __launch_bounds__(256) k_fadj_fold(const AdjDesc *__restrict__ ad,
                                                    const int *__restrict__ js, int nj) {
+    grid_dep_wait();
     const int w = blockIdx.x;
     if (w >= nj) return;
     const AdjDesc &A = *ad;
@@ -1511,6 +1535,10 @@ static int run_captured(cudaGraphExec_t &exec, int &nlaunch, long long &key, con
         note_launch(-nlaunch);   // captured, not yet issued
         if (e != cudaSuccess || !g) {
             if (g) cudaGraphDestroy(g);
+            return SELINV_ERR_CUDA;
+        }
+        if (programmatic_edges(g) != cudaSuccess) {
+            cudaGraphDestroy(g);
             return SELINV_ERR_CUDA;
         }
         e = cudaGraphInstantiate(&exec, g, 0);

@@ -30,6 +30,7 @@ constexpr int kFT = 64;  // rows per factor tile
 template <typename T>
 __global__ void k_assemble(const int64_t *__restrict__ pos, const T *__restrict__ vals, int64_t nnz,
                            T *__restrict__ L) {
+    grid_dep_wait();
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nnz;
          e += (int64_t)gridDim.x * blockDim.x)
         L[pos[e]] = vals[e];
@@ -42,6 +43,7 @@ __global__ void k_assemble(const int64_t *__restrict__ pos, const T *__restrict_
 template <typename T>
 __global__ void __launch_bounds__(256) k_fasm(const FactorDesc *__restrict__ fd, const int2 *__restrict__ items,
                                               int nitems) {
+    grid_dep_wait();
     const int w = blockIdx.x;
     if (w >= nitems) return;
     const FactorDesc &F = *fd;
@@ -71,6 +73,7 @@ __global__ void __launch_bounds__(256) k_fasm(const FactorDesc *__restrict__ fd,
 template <typename T>
 __global__ void __launch_bounds__(256) k_fupd(const FactorDesc *__restrict__ fd, const int4 *__restrict__ items,
                                               int nitems) {
+    grid_dep_wait();
     __shared__ SegSmem<T> sm;
     const int w = blockIdx.x;
     if (w >= nitems) return;
@@ -96,6 +99,7 @@ __global__ void __launch_bounds__(256) k_fupd(const FactorDesc *__restrict__ fd,
 template <typename T>
 __global__ void __launch_bounds__(256) k_fdiag(const FactorDesc *__restrict__ fd,
                                                const int *__restrict__ js, int nj) {
+    grid_dep_wait();
     const int w = blockIdx.x;
     if (w >= nj) return;
     const FactorDesc &F = *fd;
@@ -138,6 +142,7 @@ __global__ void __launch_bounds__(256) k_fdiag(const FactorDesc *__restrict__ fd
 template <typename T>
 __global__ void __launch_bounds__(64) k_ftrsm(const FactorDesc *__restrict__ fd,
                                               const int2 *__restrict__ tiles, int ntiles) {
+    grid_dep_wait();
     const int w = blockIdx.x;
     if (w >= ntiles) return;
     const FactorDesc &F = *fd;

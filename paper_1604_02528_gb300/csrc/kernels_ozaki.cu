@@ -43,6 +43,7 @@ constexpr int kOzThreads = 256;
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) k_lhat_digits(const ProbDesc *__restrict__ descs,
                                                      const int2 *__restrict__ work, int nwork) {
+    grid_dep_wait();
     __shared__ int colE[8];
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
     const int w = blockIdx.x;
@@ -151,6 +152,7 @@ template <int TN> struct OzShape {
 template <int TN>
 __global__ void __launch_bounds__(kOzThreads, 1) k_selinv_oz(const ProbDesc *__restrict__ descs,
                                                              const Item *__restrict__ items, int nitems) {
+    grid_dep_wait();
     constexpr int NT = OzShape<TN>::NT;
     constexpr int ABUF = kDig * kTM * kApad, BBUF = kDig * TN * kApad;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -384,6 +386,7 @@ __global__ void __launch_bounds__(kOzThreads, 1) k_selinv_oz(const ProbDesc *__r
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) k_linv_digits(const ProbDesc *__restrict__ descs,
                                                      const int2 *__restrict__ work, int nwork) {
+    grid_dep_wait();
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
     const int w = blockIdx.x;
     if (w >= nwork) return;
@@ -434,6 +437,7 @@ __global__ void __launch_bounds__(256) k_linv_digits(const ProbDesc *__restrict_
 template <int TN>
 __global__ void __launch_bounds__(kOzThreads, TN <= 32 ? 2 : 1) k_lhat_oz(const ProbDesc *__restrict__ descs,
                                                            const Item *__restrict__ items, int nitems) {
+    grid_dep_wait();
     constexpr int NT = TN / 16;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     uint16_t *As = reinterpret_cast<uint16_t *>(smem_raw);     // [7][64][kApad]
@@ -562,6 +566,7 @@ constexpr int kDJ = kDiagCols;   // columns j per item
 
 __global__ void __launch_bounds__(kOzThreads, 1) k_diag_oz(const ProbDesc *__restrict__ descs,
                                                            const Item *__restrict__ items, int nitems) {
+    grid_dep_wait();
     extern __shared__ __align__(16) unsigned char smem_raw[];
     uint16_t *As = reinterpret_cast<uint16_t *>(smem_raw);          // [7][128][kDpad]
     uint16_t *Bs = As + kDig * 128 * kDpad;                         // [7][kDJ][kDpad]
@@ -689,6 +694,7 @@ __global__ void __launch_bounds__(kOzThreads, 1) k_diag_oz(const ProbDesc *__res
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) k_diag_fin(const ProbDesc *__restrict__ descs,
                                                   const Item *__restrict__ items, int nitems) {
+    grid_dep_wait();
     const int w = blockIdx.x;
     if (w >= nitems) return;
     const Item it = items[w];

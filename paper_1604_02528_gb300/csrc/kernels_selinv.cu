@@ -90,6 +90,7 @@ template <typename T>
 __global__ void __launch_bounds__(kLinvThreads) k_linv(const ProbDesc *__restrict__ descs,
                                                        const int2 *__restrict__ work, int nwork,
                                                        size_t smem_cap, int with_dinv) {
+    grid_dep_wait();
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int w = blockIdx.x;
     if (w >= nwork) return;
@@ -180,6 +181,7 @@ __global__ void __launch_bounds__(kLinvThreads) k_linv(const ProbDesc *__restric
 template <typename T>
 __global__ void __launch_bounds__(256) k_dinv(const ProbDesc *__restrict__ descs, const int2 *__restrict__ work,
                                               int nwork) {
+    grid_dep_wait();
     __shared__ T As[32][33], Bs[32][33];
     __shared__ T rD[128];
     const int w = blockIdx.x;
@@ -251,6 +253,7 @@ template <typename T, int TN> __host__ __device__ constexpr size_t smem_bytes() 
 template <typename T, int TN>
 __global__ void __launch_bounds__(kThreads) k_lhat(const ProbDesc *__restrict__ descs,
                                                    const Item *__restrict__ items, int nitems) {
+    grid_dep_wait();
     using S = Shape<TN>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *As = reinterpret_cast<T *>(smem_raw);
@@ -421,6 +424,7 @@ __device__ void selinv_item(const ProbDesc &P, const Item &it, unsigned char *sm
 template <typename T, int TN>
 __global__ void __launch_bounds__(kThreads) k_selinv(const ProbDesc *__restrict__ descs,
                                                      const Item *__restrict__ items, int nitems) {
+    grid_dep_wait();
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int w = blockIdx.x;
     if (w >= nitems) return;
@@ -448,6 +452,7 @@ __global__ void __launch_bounds__(kThreads) k_selinv(const ProbDesc *__restrict_
 template <typename T, int TN>
 __global__ void __launch_bounds__(kThreads) k_push_diag(const ProbDesc *__restrict__ descs,
                                                         const Item *__restrict__ items, int nitems) {
+    grid_dep_wait();
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int w = blockIdx.x;
     if (w >= nitems) return;
@@ -495,6 +500,7 @@ template <typename T> struct LoadPush {
 template <typename T, int TN>
 __global__ void __launch_bounds__(kThreads) k_push(const ProbDesc *__restrict__ descs,
                                                    const Item *__restrict__ items, int nitems) {
+    grid_dep_wait();
     using S = Shape<TN>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *As = reinterpret_cast<T *>(smem_raw);
@@ -698,6 +704,7 @@ __device__ __forceinline__ void tiny_one(const ProbDesc &P, const int K, const i
 template <typename T>
 __global__ void __launch_bounds__(256) k_selinv_tiny(const ProbDesc *__restrict__ descs,
                                                      const Item *__restrict__ items, int nitems) {
+    grid_dep_wait();
     __shared__ T Xs[8][kTinyS * kTinyS];   // per warp: the unsymmetrized diagonal block
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
     const int w = blockIdx.x * 8 + warp;
@@ -743,6 +750,7 @@ __global__ void __launch_bounds__(kThreads) k_selinv_persist(const ProbDesc *__r
                                                              const int8_t *__restrict__ buckets, int nitems,
                                                              int *ticket, long long spin_limit,
                                                              int wait_on_unset) {
+    grid_dep_wait();
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ int s_task;
     for (;;) {
@@ -780,6 +788,7 @@ __global__ void __launch_bounds__(kThreads) k_selinv_persist(const ProbDesc *__r
 // debug check of the inputs: latches SELINV_ERR_NONFINITE when any of the n
 // doubles is a NaN or an infinity (complex data: both parts)
 __global__ void __launch_bounds__(256) k_check_finite(const double *__restrict__ x, int64_t n, int *status) {
+    grid_dep_wait();
     int bad = 0;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
         bad |= !isfinite(x[e]);

@@ -55,6 +55,7 @@ template <int TN>
 __global__ void __launch_bounds__(kTcThreads, 1) k_selinv_tc(const ProbDesc *__restrict__ descs,
                                                              const Item *__restrict__ items, int nitems,
                                                              long long *__restrict__ slab, long long wait_limit) {
+    grid_dep_wait();
     using Cfg = TcCfg<TN>;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     uint16_t *As = reinterpret_cast<uint16_t *>(smem_raw);                // [2][7][A_PLANE]
@@ -390,6 +391,7 @@ template <int TN>
 __global__ void __launch_bounds__(256) k_tc_reduce(const ProbDesc *__restrict__ descs,
                                                    const Item *__restrict__ items, const int4 *__restrict__ red,
                                                    int nred, const long long *__restrict__ slab) {
+    grid_dep_wait();
     __shared__ int ymax[8];
     const int w = blockIdx.x;
     if (w >= nred) return;
@@ -481,6 +483,7 @@ template <int TN, bool CPLX>
 __global__ void __launch_bounds__(kDtThreads, 1) k_diag_tc(const ProbDesc *__restrict__ descs,
                                                            const Item *__restrict__ items, int nitems,
                                                            long long wait_limit) {
+    grid_dep_wait();
     using Cfg = DtCfg<TN>;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     uint16_t *As = reinterpret_cast<uint16_t *>(smem_raw);                // [2][7][A_PLANE]

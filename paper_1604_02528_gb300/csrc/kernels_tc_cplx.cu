@@ -33,6 +33,7 @@ namespace selinv {
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) k_lhat_digits_z(const ProbDesc *__restrict__ descs,
                                                        const int2 *__restrict__ work, int nwork) {
+    grid_dep_wait();
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
     const int w = blockIdx.x;
     if (w >= nwork) return;
@@ -87,6 +88,7 @@ __global__ void __launch_bounds__(256) k_lhat_digits_z(const ProbDesc *__restric
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) k_diag_fin_z(const ProbDesc *__restrict__ descs,
                                                     const Item *__restrict__ items, int nitems) {
+    grid_dep_wait();
     const int w = blockIdx.x;
     if (w >= nitems) return;
     const Item it = items[w];

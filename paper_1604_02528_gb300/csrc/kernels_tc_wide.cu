@@ -111,6 +111,7 @@ template <bool CPLX, bool LHAT = false, bool SYRK = false>
 __global__ void __launch_bounds__(kTwThreads, 1) k_selinv_tcw(const ProbDesc *__restrict__ descs,
                                                               const Item *__restrict__ items, int nitems,
                                                               long long *__restrict__ slab, long long wait_limit) {
+    grid_dep_wait();
     using Cfg = TwCfg;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     uint16_t *As = reinterpret_cast<uint16_t *>(smem_raw);                    // [kTwAS][7][A_PLANE] Lhat^T digits
@@ -559,6 +560,7 @@ template <bool CPLX>
 __global__ void __launch_bounds__(256) k_tcw_reduce(const ProbDesc *__restrict__ descs,
                                                     const Item *__restrict__ items, const int4 *__restrict__ red,
                                                     int nred, const long long *__restrict__ slab) {
+    grid_dep_wait();
     __shared__ int ymax[8];
     const int w = blockIdx.x;
     if (w >= nred) return;

@@ -1233,6 +1233,48 @@ static cudaError_t issue(const Schedule &S, cudaStream_t st, bool count) {
     return cudaSuccess;
 }
 
+// The kernel-to-kernel edges of a captured level loop become programmatic
+// ones on the launch-completion port: the next grid is scheduled once every
+// block of the previous one has started, and each kernel waits in
+// grid_dep_wait() for its predecessor to complete.  Edges into or out of
+// other nodes (copies, memsets) stay full dependencies.  An edge that cannot
+// be converted stays as it was; the result is an error only when an edge
+// could be neither converted nor restored (the graph must then be dropped).
+cudaError_t programmatic_edges(cudaGraph_t g) {
+    size_t n = 0;
+    if (cudaGraphGetEdges(g, nullptr, nullptr, nullptr, &n) != cudaSuccess || n == 0) {
+        cudaGetLastError();
+        return cudaSuccess;
+    }
+    std::vector<cudaGraphNode_t> from(n), to(n);
+    std::vector<cudaGraphEdgeData> ed(n);
+    if (cudaGraphGetEdges(g, from.data(), to.data(), ed.data(), &n) != cudaSuccess) {
+        cudaGetLastError();
+        return cudaSuccess;
+    }
+    for (size_t i = 0; i < n; i++) {
+        cudaGraphNodeType ta, tb;
+        if (cudaGraphNodeGetType(from[i], &ta) != cudaSuccess || cudaGraphNodeGetType(to[i], &tb) != cudaSuccess ||
+            ta != cudaGraphNodeTypeKernel || tb != cudaGraphNodeTypeKernel || ed[i].type != cudaGraphDependencyTypeDefault)
+            continue;
+        cudaGraphEdgeData pe;
+        std::memset(&pe, 0, sizeof(pe));
+        pe.from_port = cudaGraphKernelNodePortProgrammatic;
+        pe.type = cudaGraphDependencyTypeProgrammatic;
+        if (cudaGraphRemoveDependencies(g, &from[i], &to[i], &ed[i], 1) != cudaSuccess) {
+            cudaGetLastError();
+            continue;
+        }
+        if (cudaGraphAddDependencies(g, &from[i], &to[i], &pe, 1) != cudaSuccess) {
+            cudaGetLastError();
+            const cudaError_t e = cudaGraphAddDependencies(g, &from[i], &to[i], &ed[i], 1);
+            if (e != cudaSuccess) return e;
+        }
+    }
+    cudaGetLastError();
+    return cudaSuccess;
+}
+
 int run_schedule(Schedule &S, cudaStream_t st, bool use_graph) {
     // graphs need a capturable stream (not the legacy default stream)
     if (use_graph && st != nullptr && st != cudaStreamLegacy) {
@@ -1243,6 +1285,10 @@ int run_schedule(Schedule &S, cudaStream_t st, bool use_graph) {
             cudaError_t e2 = cudaStreamEndCapture(st, &g);
             if (e != cudaSuccess || e2 != cudaSuccess) {
                 if (g) cudaGraphDestroy(g);
+                return SELINV_ERR_CUDA;
+            }
+            if (programmatic_edges(g) != cudaSuccess) {
+                cudaGraphDestroy(g);
                 return SELINV_ERR_CUDA;
             }
             e = cudaGraphInstantiate(&S.graph, g, 0);

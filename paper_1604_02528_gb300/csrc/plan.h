@@ -187,6 +187,8 @@ ProbDesc make_desc(const PlanData &p, Workspace &w, int dtype, const void *L, co
 int build_schedule(Schedule &S, const std::vector<const PlanData *> &plans,
                    const std::vector<ProbDesc> &descs, int mode);
 int run_schedule(Schedule &S, cudaStream_t st, bool use_graph);
+// kernel-to-kernel edges of a captured graph -> programmatic (see plan.cu)
+cudaError_t programmatic_edges(cudaGraph_t g);
 cudaError_t launch_with(const Schedule &S, const Launch &L, const ProbDesc *d, cudaStream_t st);
 
 // factorization / adjoint state

@@ -27,6 +27,7 @@ namespace selinv {
 template <typename T>
 __global__ void k_gather_sel(const T *__restrict__ src, const int64_t *__restrict__ pos, int64_t n,
                              T *__restrict__ dst) {
+    grid_dep_wait();
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
         dst[e] = src[pos[e]];
 }
@@ -42,6 +43,7 @@ struct PoleTerms {
 
 // out[e] (+)= sum_l w_l Z_l[pos[e]] in complex arithmetic, terms in order l
 __global__ void k_pole_sum(const PoleTerms t, const int64_t *__restrict__ pos, int64_t n, double2 *__restrict__ out) {
+    grid_dep_wait();
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
         const int64_t q = pos[e];
         double2 acc = t.accumulate ? out[e] : make_double2(0.0, 0.0);
