@@ -9,11 +9,11 @@
 namespace selinv {
 
 // Programmatic dependent launch: in the captured level loops every
-// kernel-to-kernel edge lets the next grid be scheduled once the previous one
-// has started all its blocks, so its launch overlaps the previous grid's
-// run; each kernel waits here, before it reads anything, until its
-// predecessor has completed and its memory operations are visible.  A grid
-// launched without such an edge passes at once.
+// kernel-to-kernel edge is a programmatic one, so the next grid is scheduled
+// as the previous one drains instead of after a full serialization; each
+// kernel waits here, before it reads anything, until its predecessors have
+// completed and their memory operations are visible.  A grid launched
+// without such an edge passes at once.
 __device__ __forceinline__ void grid_dep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 
 

@@ -1446,13 +1446,13 @@ static int adj_split(selinv_plan_s *plan) {
         const int fcon = plan->data.opts.fast_contraction, ozm = plan->data.opts.oz_min_s;
         plan->data.opts.fast_contraction = 1;
         plan->data.opts.oz_min_s = kOzMinS;
-        rc = build_schedule(a->tcs, {&p}, {pd}, SELINV_SCHED_LEVEL);
+        rc = build_schedule(a->tcs, {&p}, {pd}, SELINV_SCHED_LEVEL, false);
         plan->data.opts.oz_min_s = ozm;
         sel.swap(plan->data.active);
         // and the normalization of every supernode, as the forward runs it
         sel.clear();
         sel.swap(plan->data.active);
-        if (!rc) rc = build_schedule(a->tcn, {&p}, {pd}, SELINV_SCHED_LEVEL);
+        if (!rc) rc = build_schedule(a->tcn, {&p}, {pd}, SELINV_SCHED_LEVEL, false);
         sel.swap(plan->data.active);
         plan->data.opts.fast_contraction = fcon;
         if (rc) return rc;

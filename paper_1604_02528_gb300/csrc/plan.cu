@@ -467,12 +467,18 @@ ProbDesc make_desc(const PlanData &p, Workspace &w, int dtype, const void *L, co
 void Schedule::release() {
     if (graph) cudaGraphExecDestroy(graph);
     graph = nullptr;
+    if (side) cudaStreamDestroy(side);
+    if (ev_fork) cudaEventDestroy(ev_fork);
+    if (ev_join) cudaEventDestroy(ev_join);
+    side = nullptr;
+    ev_fork = ev_join = nullptr;
+    join_at = -1;
     dfree(d_descs); dfree(d_items); dfree(d_work); dfree(d_buckets); dfree(tcslab); dfree(d_red);
     d_descs = nullptr; d_items = nullptr; d_work = nullptr; d_buckets = nullptr; tcslab = nullptr; d_red = nullptr;
 }
 
 int build_schedule(Schedule &S, const std::vector<const PlanData *> &plans,
-                   const std::vector<ProbDesc> &descs, int mode) {
+                   const std::vector<ProbDesc> &descs, int mode, bool split_norm) {
     S.release();
     S.launches.clear();
     S.h_items.clear();
@@ -503,132 +509,161 @@ int build_schedule(Schedule &S, const std::vector<const PlanData *> &plans,
         const int64_t c = p.rowptr[K + 1] - p.rowptr[K] - s;
         return !descs[i].lu && s <= 8 && c <= 64 && !ozok(i, s) && !zok(i, s);
     };
-    // 1) L_KK^{-1}, Dinv for every supernode (one launch per dtype and size class)
-    for (int dt = 0; dt < 2; dt++)
-        for (int large = 1; large >= 0; large--) {
+    // Level schedule: the normalization (steps 1, 2, 2b) runs in two phases.
+    // The supernodes of the first `ltop` levels -- the top of the tree, a few
+    // large supernodes per level whose launches leave most SMs idle -- are
+    // normalized first on the main stream; the rest on a side stream, while
+    // the main stream traverses those levels (the traversal of a level reads
+    // the normalization of its own supernodes only); the main stream waits for
+    // the side stream before level ltop.
+    int ltop = 0;
+    if (mode == SELINV_SCHED_LEVEL && split_norm) {
+        int nlev = 0;
+        for (int i = 0; i < np; i++) nlev = std::max(nlev, plans[i]->nlevels);
+        int64_t seen = 0;
+        for (int l = 0; l < nlev; l++) {
+            for (int i = 0; i < np; i++)
+                if (l < plans[i]->nlevels) seen += plans[i]->level_ptr[l + 1] - plans[i]->level_ptr[l];
+            if (seen > kTopSupernodes) break;
+            ltop = l + 1;
+        }
+        if (ltop >= nlev) ltop = 0;   // the whole tree is "top": nothing to overlap
+    }
+    const int nph = ltop > 0 ? 2 : 1;
+    for (int ph = 0; ph < nph; ph++) {
+        const size_t ph_first = S.launches.size();
+        // supernodes of this phase (both when there is one phase)
+        auto actn = [&](int i, int32_t K) {
+            return act(i, K) && (nph == 1 || (plans[i]->level[K] < ltop) == (ph == 0));
+        };
+        // 1) L_KK^{-1}, Dinv for every supernode (one launch per dtype and size class)
+        for (int dt = 0; dt < 2; dt++)
+            for (int large = 1; large >= 0; large--) {
+                const int64_t off = (int64_t)S.h_work.size();
+                for (int i = 0; i < np; i++) {
+                    if (descs[i].dtype != dt) continue;
+                    const PlanData &p = *plans[i];
+                    for (int32_t K = 0; K < p.ns; K++)
+                        if (actn(i, K) && (p.super_ptr[K + 1] - p.super_ptr[K] > 32) == (large == 1))
+                            S.h_work.push_back(make_int2(i, K));
+                }
+                const int cnt = (int)(S.h_work.size() - off);
+                if (cnt) S.launches.push_back({0, dt, large, off, cnt, -1});
+                if (!cnt || !large) continue;
+                // Dinv_K of the wide ones, a CTA per 32 x 32 tile of its lower triangle
+                // (the LU form's own Dinv comes from k_linv)
+                const int64_t off2 = (int64_t)S.h_work.size();
+                for (int64_t e = off; e < off + cnt; e++) {
+                    const int2 wk = S.h_work[e];
+                    if (descs[wk.x].lu) continue;
+                    const int s = plans[wk.x]->super_ptr[wk.y + 1] - plans[wk.x]->super_ptr[wk.y];
+                    const int nt = (s + 31) / 32;
+                    for (int t = 0; t < nt * (nt + 1) / 2; t++) S.h_work.push_back(make_int2(wk.x, (wk.y << 8) | t));
+                }
+                const int cnt2 = (int)(S.h_work.size() - off2);
+                if (cnt2) S.launches.push_back({KL_DINV, dt, 0, off2, cnt2, -1});
+            }
+        // 2) Lhat for every row tile: the tensor-core product for eligible
+        //    supernodes (after the digit planes of L_KK^{-1}), FP64 for the rest
+        {
             const int64_t off = (int64_t)S.h_work.size();
             for (int i = 0; i < np; i++) {
-                if (descs[i].dtype != dt) continue;
-                const PlanData &p = *plans[i];
-                for (int32_t K = 0; K < p.ns; K++)
-                    if (act(i, K) && (p.super_ptr[K + 1] - p.super_ptr[K] > 32) == (large == 1))
-                        S.h_work.push_back(make_int2(i, K));
-            }
-            const int cnt = (int)(S.h_work.size() - off);
-            if (cnt) S.launches.push_back({0, dt, large, off, cnt, -1});
-            if (!cnt || !large) continue;
-            // Dinv_K of the wide ones, a CTA per 32 x 32 tile of its lower triangle
-            // (the LU form's own Dinv comes from k_linv)
-            const int64_t off2 = (int64_t)S.h_work.size();
-            for (int64_t e = off; e < off + cnt; e++) {
-                const int2 wk = S.h_work[e];
-                if (descs[wk.x].lu) continue;
-                const int s = plans[wk.x]->super_ptr[wk.y + 1] - plans[wk.x]->super_ptr[wk.y];
-                const int nt = (s + 31) / 32;
-                for (int t = 0; t < nt * (nt + 1) / 2; t++) S.h_work.push_back(make_int2(wk.x, (wk.y << 8) | t));
-            }
-            const int cnt2 = (int)(S.h_work.size() - off2);
-            if (cnt2) S.launches.push_back({KL_DINV, dt, 0, off2, cnt2, -1});
-        }
-    // 2) Lhat for every row tile: the tensor-core product for eligible
-    //    supernodes (after the digit planes of L_KK^{-1}), FP64 for the rest
-    {
-        const int64_t off = (int64_t)S.h_work.size();
-        for (int i = 0; i < np; i++) {
-            const PlanData &p = *plans[i];
-            for (int32_t K = 0; K < p.ns; K++) {
-                const int s = p.super_ptr[K + 1] - p.super_ptr[K];
-                const int64_t c = p.rowptr[K + 1] - p.rowptr[K] - s;
-                if (c == 0 || !act(i, K) || !ozok(i, s)) continue;
-                // bit 7: the tcgen05 operand layout, for the transposed Lhat product
-                const int tcl = lhat_tc(i, s) ? 0x80 : 0;
-                for (int jb = 0; jb < (s + 7) / 8; jb++) S.h_work.push_back(make_int2(i, (K << 8) | tcl | jb));
-            }
-        }
-        const int cnt = (int)(S.h_work.size() - off);
-        if (cnt) S.launches.push_back({KL_LINV_DIGITS, SELINV_F64, 0, off, cnt, -1});
-    }
-    {
-        // Lhat of the supernodes wider than 64 columns on tcgen05: (K, 64-row tile) items
-        const int64_t off = (int64_t)S.h_items.size();
-        for (int i = 0; i < np; i++) {
-            const PlanData &p = *plans[i];
-            for (int32_t K = 0; K < p.ns; K++) {
-                const int s = p.super_ptr[K + 1] - p.super_ptr[K];
-                const int64_t c = p.rowptr[K + 1] - p.rowptr[K] - s;
-                if (c == 0 || !act(i, K) || !ozok(i, s) || !lhat_tc(i, s)) continue;
-                for (int64_t t = 0; t < (c + kTcWideRows - 1) / kTcWideRows; t++) S.h_items.push_back({i, K, (int)t, 1});
-            }
-        }
-        const int cnt = (int)(S.h_items.size() - off);
-        if (cnt) S.launches.push_back({KL_LHAT_OZ, SELINV_F64, kTcWide, off, cnt, -1});
-    }
-    for (int tn : {64, 32, 16}) {
-        const int64_t off = (int64_t)S.h_items.size();
-        for (int i = 0; i < np; i++) {
-            const PlanData &p = *plans[i];
-            for (int32_t K = 0; K < p.ns; K++) {
-                const int s = p.super_ptr[K + 1] - p.super_ptr[K];
-                const int64_t c = p.rowptr[K + 1] - p.rowptr[K] - s;
-                if (c == 0 || !act(i, K) || !ozok(i, s) || lhat_tc(i, s)) continue;
-                const int ktn = s <= 16 ? 16 : 32;   // 32-column tiles: two CTAs per SM
-                if (ktn != tn) continue;
-                const int ncol = (s + tn - 1) / tn;
-                for (int t = 0; t < p.ntiles[K]; t++)
-                    for (int ct = 0; ct < ncol; ct++) S.h_items.push_back({i, K, t * ncol + ct, p.ntiles[K]});
-            }
-        }
-        const int cnt = (int)(S.h_items.size() - off);
-        if (cnt) S.launches.push_back({KL_LHAT_OZ, SELINV_F64, tn, off, cnt, -1});
-    }
-    for (int dt = 0; dt < 2; dt++)
-        for (int b = 0; b < kNumBuckets; b++) {
-            const int64_t off = (int64_t)S.h_items.size();
-            for (int i = 0; i < np; i++) {
-                if (descs[i].dtype != dt) continue;
                 const PlanData &p = *plans[i];
                 for (int32_t K = 0; K < p.ns; K++) {
                     const int s = p.super_ptr[K + 1] - p.super_ptr[K];
                     const int64_t c = p.rowptr[K + 1] - p.rowptr[K] - s;
-                    if (c == 0 || !act(i, K) || bucket_of(s) != b || ozok(i, s)) continue;
-                    for (int t = 0; t < p.ntiles[K]; t++) S.h_items.push_back({i, K, t, p.ntiles[K]});
+                    if (c == 0 || !actn(i, K) || !ozok(i, s)) continue;
+                    // bit 7: the tcgen05 operand layout, for the transposed Lhat product
+                    const int tcl = lhat_tc(i, s) ? 0x80 : 0;
+                    for (int jb = 0; jb < (s + 7) / 8; jb++) S.h_work.push_back(make_int2(i, (K << 8) | tcl | jb));
+                }
+            }
+            const int cnt = (int)(S.h_work.size() - off);
+            if (cnt) S.launches.push_back({KL_LINV_DIGITS, SELINV_F64, 0, off, cnt, -1});
+        }
+        {
+            // Lhat of the supernodes wider than 64 columns on tcgen05: (K, 64-row tile) items
+            const int64_t off = (int64_t)S.h_items.size();
+            for (int i = 0; i < np; i++) {
+                const PlanData &p = *plans[i];
+                for (int32_t K = 0; K < p.ns; K++) {
+                    const int s = p.super_ptr[K + 1] - p.super_ptr[K];
+                    const int64_t c = p.rowptr[K + 1] - p.rowptr[K] - s;
+                    if (c == 0 || !actn(i, K) || !ozok(i, s) || !lhat_tc(i, s)) continue;
+                    for (int64_t t = 0; t < (c + kTcWideRows - 1) / kTcWideRows; t++) S.h_items.push_back({i, K, (int)t, 1});
                 }
             }
             const int cnt = (int)(S.h_items.size() - off);
-            if (cnt) S.launches.push_back({1, dt, b, off, cnt, -1});
+            if (cnt) S.launches.push_back({KL_LHAT_OZ, SELINV_F64, kTcWide, off, cnt, -1});
         }
-    // 2b) bf16 digit planes of Lhat for the tensor-core contraction
-    {
-        const int64_t off = (int64_t)S.h_work.size();
-        for (int i = 0; i < np; i++) {
-            const PlanData &p = *plans[i];
-            for (int32_t K = 0; K < p.ns; K++) {
-                const int s = p.super_ptr[K + 1] - p.super_ptr[K];
-                const int64_t c = p.rowptr[K + 1] - p.rowptr[K] - s;
-                if (c == 0 || !act(i, K) || mode == SELINV_SCHED_PERSISTENT || mode == SELINV_SCHED_PUSH ||
-                    !ozok(i, s))
-                    continue;
-                // bit 7: only the tcgen05 layout is read (tcgen05 gather-GEMM and
-                // diagonal block); the mma.sync kernels read the other one
-                const int only_u = p.opts.fast_contraction == 1 && s > 32 ? 0x80 : 0;
-                for (int jb = 0; jb < (s + 7) / 8; jb++) S.h_work.push_back(make_int2(i, (K << 8) | only_u | jb));
+        for (int tn : {64, 32, 16}) {
+            const int64_t off = (int64_t)S.h_items.size();
+            for (int i = 0; i < np; i++) {
+                const PlanData &p = *plans[i];
+                for (int32_t K = 0; K < p.ns; K++) {
+                    const int s = p.super_ptr[K + 1] - p.super_ptr[K];
+                    const int64_t c = p.rowptr[K + 1] - p.rowptr[K] - s;
+                    if (c == 0 || !actn(i, K) || !ozok(i, s) || lhat_tc(i, s)) continue;
+                    const int ktn = s <= 16 ? 16 : 32;   // 32-column tiles: two CTAs per SM
+                    if (ktn != tn) continue;
+                    const int ncol = (s + tn - 1) / tn;
+                    for (int t = 0; t < p.ntiles[K]; t++)
+                        for (int ct = 0; ct < ncol; ct++) S.h_items.push_back({i, K, t * ncol + ct, p.ntiles[K]});
+                }
             }
+            const int cnt = (int)(S.h_items.size() - off);
+            if (cnt) S.launches.push_back({KL_LHAT_OZ, SELINV_F64, tn, off, cnt, -1});
         }
-        const int cnt = (int)(S.h_work.size() - off);
-        if (cnt) S.launches.push_back({KL_DIGITS, SELINV_F64, 0, off, cnt, -1});
-        // the complex operand (after the FP64 Lhat of step 2)
-        const int64_t offz = (int64_t)S.h_work.size();
-        for (int i = 0; i < np; i++) {
-            const PlanData &p = *plans[i];
-            for (int32_t K = 0; K < p.ns; K++) {
-                const int s = p.super_ptr[K + 1] - p.super_ptr[K];
-                const int64_t c = p.rowptr[K + 1] - p.rowptr[K] - s;
-                if (c == 0 || !act(i, K) || !zok(i, s)) continue;
-                for (int jb = 0; jb < (s + 7) / 8; jb++) S.h_work.push_back(make_int2(i, (K << 8) | jb));
+        for (int dt = 0; dt < 2; dt++)
+            for (int b = 0; b < kNumBuckets; b++) {
+                const int64_t off = (int64_t)S.h_items.size();
+                for (int i = 0; i < np; i++) {
+                    if (descs[i].dtype != dt) continue;
+                    const PlanData &p = *plans[i];
+                    for (int32_t K = 0; K < p.ns; K++) {
+                        const int s = p.super_ptr[K + 1] - p.super_ptr[K];
+                        const int64_t c = p.rowptr[K + 1] - p.rowptr[K] - s;
+                        if (c == 0 || !actn(i, K) || bucket_of(s) != b || ozok(i, s)) continue;
+                        for (int t = 0; t < p.ntiles[K]; t++) S.h_items.push_back({i, K, t, p.ntiles[K]});
+                    }
+                }
+                const int cnt = (int)(S.h_items.size() - off);
+                if (cnt) S.launches.push_back({1, dt, b, off, cnt, -1});
             }
+        // 2b) bf16 digit planes of Lhat for the tensor-core contraction
+        {
+            const int64_t off = (int64_t)S.h_work.size();
+            for (int i = 0; i < np; i++) {
+                const PlanData &p = *plans[i];
+                for (int32_t K = 0; K < p.ns; K++) {
+                    const int s = p.super_ptr[K + 1] - p.super_ptr[K];
+                    const int64_t c = p.rowptr[K + 1] - p.rowptr[K] - s;
+                    if (c == 0 || !actn(i, K) || mode == SELINV_SCHED_PERSISTENT || mode == SELINV_SCHED_PUSH ||
+                        !ozok(i, s))
+                        continue;
+                    // bit 7: only the tcgen05 layout is read (tcgen05 gather-GEMM and
+                    // diagonal block); the mma.sync kernels read the other one
+                    const int only_u = p.opts.fast_contraction == 1 && s > 32 ? 0x80 : 0;
+                    for (int jb = 0; jb < (s + 7) / 8; jb++) S.h_work.push_back(make_int2(i, (K << 8) | only_u | jb));
+                }
+            }
+            const int cnt = (int)(S.h_work.size() - off);
+            if (cnt) S.launches.push_back({KL_DIGITS, SELINV_F64, 0, off, cnt, -1});
+            // the complex operand (after the FP64 Lhat of step 2)
+            const int64_t offz = (int64_t)S.h_work.size();
+            for (int i = 0; i < np; i++) {
+                const PlanData &p = *plans[i];
+                for (int32_t K = 0; K < p.ns; K++) {
+                    const int s = p.super_ptr[K + 1] - p.super_ptr[K];
+                    const int64_t c = p.rowptr[K + 1] - p.rowptr[K] - s;
+                    if (c == 0 || !actn(i, K) || !zok(i, s)) continue;
+                    for (int jb = 0; jb < (s + 7) / 8; jb++) S.h_work.push_back(make_int2(i, (K << 8) | jb));
+                }
+            }
+            const int cntz = (int)(S.h_work.size() - offz);
+            if (cntz) S.launches.push_back({KL_DIGITS, SELINV_C128, 0, offz, cntz, -1});
         }
-        const int cntz = (int)(S.h_work.size() - offz);
-        if (cntz) S.launches.push_back({KL_DIGITS, SELINV_C128, 0, offz, cntz, -1});
+        for (size_t q = ph_first; q < S.launches.size(); q++) S.launches[q].side = ph;
     }
     // 3) the traversal, root to leaves
     auto push_items = [&](int i, int32_t K) {
@@ -1004,6 +1039,7 @@ int build_schedule(Schedule &S, const std::vector<const PlanData *> &plans,
         int nlev = 0;
         for (int i = 0; i < np; i++) nlev = std::max(nlev, plans[i]->nlevels);
         for (int l = 0; l < nlev; l++) {
+            if (nph == 2 && l == ltop) S.join_at = (int)S.launches.size();
             // tensor-core contraction of every eligible supernode of the level
             // (one launch per column-tile width), then their diagonal blocks
             std::vector<std::pair<int, int32_t>> oz;  // (problem, K)
@@ -1219,24 +1255,48 @@ const char *launch_kind_name(int kind) {
     return kind >= 0 && kind < KL_NKINDS ? names[kind] : "?";
 }
 
-static cudaError_t issue(const Schedule &S, cudaStream_t st, bool count) {
+// The launches in order on `st`, those marked `side` on the schedule's side
+// stream: it forks from `st` at its first launch and joins back before launch
+// join_at (or at the end).
+static cudaError_t issue(Schedule &S, cudaStream_t st, bool count) {
     if (count) note_launch((int)S.launches.size());
     cudaError_t e0 = issue_pre(S, st);
     if (e0 != cudaSuccess) return e0;
-    for (const Launch &L : S.launches) {
+    bool forked = false;
+    auto join = [&]() -> cudaError_t {
+        forked = false;
+        cudaError_t e = cudaEventRecord(S.ev_join, S.side);
+        return e == cudaSuccess ? cudaStreamWaitEvent(st, S.ev_join, 0) : e;
+    };
+    for (size_t i = 0; i < S.launches.size(); i++) {
+        const Launch &L = S.launches[i];
+        cudaError_t e = cudaSuccess;
+        if (forked && (int)i == S.join_at && (e = join()) != cudaSuccess) return e;
+        cudaStream_t ls = st;
+        if (L.side) {
+            if (!forked) {
+                if (!S.side && (e = cudaStreamCreateWithFlags(&S.side, cudaStreamNonBlocking)) != cudaSuccess) return e;
+                if (!S.ev_fork && (e = cudaEventCreateWithFlags(&S.ev_fork, cudaEventDisableTiming)) != cudaSuccess) return e;
+                if (!S.ev_join && (e = cudaEventCreateWithFlags(&S.ev_join, cudaEventDisableTiming)) != cudaSuccess) return e;
+                if ((e = cudaEventRecord(S.ev_fork, st)) != cudaSuccess) return e;
+                if ((e = cudaStreamWaitEvent(S.side, S.ev_fork, 0)) != cudaSuccess) return e;
+                forked = true;
+            }
+            ls = S.side;
+        }
         char name[48];
         std::snprintf(name, sizeof(name), "L%d %s", L.level, launch_kind_name(L.kind));
         NvtxRange r(name);
-        cudaError_t e = launch_one(S, L, st);
-        if (e != cudaSuccess) return e;
+        if ((e = launch_one(S, L, ls)) != cudaSuccess) return e;
     }
-    return cudaSuccess;
+    return forked ? join() : cudaSuccess;
 }
 
 // The kernel-to-kernel edges of a captured level loop become programmatic
-// ones on the launch-completion port: the next grid is scheduled once every
-// block of the previous one has started, and each kernel waits in
-// grid_dep_wait() for its predecessor to complete.  Edges into or out of
+// ones on the programmatic port: the next grid is scheduled as the blocks of
+// the previous one finish (none triggers earlier), without the full
+// serialization of an ordinary edge, and each kernel waits in
+// grid_dep_wait() for its predecessors to complete.  Edges into or out of
 // other nodes (copies, memsets) stay full dependencies.  An edge that cannot
 // be converted stays as it was; the result is an error only when an edge
 // could be neither converted nor restored (the graph must then be dropped).

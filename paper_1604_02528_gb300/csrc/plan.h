@@ -132,6 +132,7 @@ constexpr int kTcChunkSteps = 8;   // k16 steps per exact fp32 chunk of the tens
 constexpr int kTcWide = 128;   // launch bucket of the transposed tcgen05 kernel (supernodes wider than 64)
 constexpr int kTcWideRows = 64;   // rows of C per item of that kernel
 constexpr int kAsmChunk = 1024;   // entries of an update matrix per extend-add item
+constexpr int kTopSupernodes = 16;   // level schedule: the top levels (up to this many supernodes) normalized first
 
 struct Launch {
     int kind;    // KL_*
@@ -140,6 +141,7 @@ struct Launch {
     int64_t off;
     int count;
     int level;
+    int side = 0;   // 1: issued on the schedule's side stream (normalization of the lower levels)
 };
 
 struct Schedule {
@@ -167,6 +169,12 @@ struct Schedule {
     long long spin_limit = 0;   // bound of every device wait of the schedule's kernels
     int wait_on_unset = 0;
     cudaGraphExec_t graph = nullptr;
+    // level schedule: the side stream that normalizes the lower levels'
+    // supernodes while the main stream traverses the top levels, and the
+    // launch before which the main stream waits for it (-1: none)
+    int join_at = -1;
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     void release();
 };
 
@@ -184,8 +192,10 @@ size_t elem_size(int dtype);
 int ensure_device(PlanData &p);
 ProbDesc make_desc(const PlanData &p, Workspace &w, int dtype, const void *L, const void *D, void *Z,
                    bool persistent);
+// split_norm: in the level schedule, normalize the lower levels on the side
+// stream (see plan.cu); false keeps every launch on one stream
 int build_schedule(Schedule &S, const std::vector<const PlanData *> &plans,
-                   const std::vector<ProbDesc> &descs, int mode);
+                   const std::vector<ProbDesc> &descs, int mode, bool split_norm = true);
 int run_schedule(Schedule &S, cudaStream_t st, bool use_graph);
 // kernel-to-kernel edges of a captured graph -> programmatic (see plan.cu)
 cudaError_t programmatic_edges(cudaGraph_t g);
