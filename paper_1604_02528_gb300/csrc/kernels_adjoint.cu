@@ -43,6 +43,7 @@ namespace selinv {
 constexpr int kNumSMs = 152;   // GB300
 constexpr int kFinY = 4;   // CTAs per supernode (grid y) of the per-supernode s x s steps
 constexpr int kAdjWideC = 256;   // rows of C from which any supernode takes the split (wide) path
+constexpr int kRowSimtS = 32;    // levels whose wide supernodes are this narrow: row products on the FP64 kernel
 
 struct AdjDesc {
     const int32_t *super_ptr;
@@ -102,7 +103,11 @@ struct AdjData {
     std::vector<int> sm_bptr;
     std::vector<Item> wd_items;               // wide: (K, tile) per level
     std::vector<int64_t> wd_lptr;
-    std::vector<int4> row_items, mbp_items;   // wide: (K, tile, chunk, 0) / (K, tile, chunk, row block)
+    // row_items: (K, 32-row block, chunk, 0) of the row products of the wide
+    // supernodes of levels whose widest is kRowSimtS columns or less (FP64
+    // kernel; other levels: pr_items on tcgen05); mbp_items: (K, tile, chunk,
+    // row block) of the split partials
+    std::vector<int4> row_items, mbp_items;
     std::vector<int64_t> row_lptr, mbp_lptr;
     std::vector<int2> dig_work;               // wide with c > 0: (0, K << 8 | 8-column block)
     std::vector<int64_t> dig_lptr;
@@ -1362,6 +1367,15 @@ static int adj_split(selinv_plan_s *plan) {
             }
             a->sm_bptr.push_back((int)a->sm_items.size());
         }
+        // the level's row products on the FP64 kernel when none of its wide
+        // supernodes is wider than kRowSimtS columns, else all on tcgen05 (one
+        // launch per product: a second, narrower launch would add its latency)
+        int wmax = 0;
+        for (int64_t e = p.level_ptr[l]; e < p.level_ptr[l + 1]; e++) {
+            const int32_t J = p.level_list[e];
+            if (wideK(J)) wmax = std::max(wmax, p.super_ptr[J + 1] - p.super_ptr[J]);
+        }
+        const bool simt = wmax <= kRowSimtS;
         for (int64_t e = p.level_ptr[l]; e < p.level_ptr[l + 1]; e++) {
             const int32_t J = p.level_list[e];
             const int s = p.super_ptr[J + 1] - p.super_ptr[J];
@@ -1369,15 +1383,18 @@ static int adj_split(selinv_plan_s *plan) {
             const int64_t c = p.rowptr[J + 1] - p.rowptr[J] - s;
             const int nch = (s + 31) / 32;
             for (int t = 0; t < p.ntiles[J]; t++) a->wd_items.push_back({0, J, t, p.ntiles[J]});
-            for (int b = 0; b < std::max<int64_t>(1, (c + 31) / 32); b++)
-                for (int ch = 0; ch < nch; ch++) a->row_items.push_back(make_int4(J, b, ch, 0));
+            if (simt)   // (one block even without C: block 0 of RP_YBAR also stores S)
+                for (int b = 0; b < std::max<int64_t>(1, (c + 31) / 32); b++)
+                    for (int ch = 0; ch < nch; ch++) a->row_items.push_back(make_int4(J, b, ch, 0));
             for (int t = 0; t < p.ntiles[J]; t++)
                 for (int ch = 0; ch < nch; ch++)
                     for (int h = 0; h < (s + 31) / 32; h++) a->mbp_items.push_back(make_int4(J, t, ch, h));
             if (c > 0)
                 for (int jb = 0; jb < (s + 7) / 8; jb++) a->dig_work.push_back(make_int2(0, (J << 8) | jb));
-            for (int64_t t = 0; t < (c + kTcWideRows - 1) / kTcWideRows; t++) a->pr_items.push_back({0, J, (int)t, 1});
-            for (int jb = 0; jb < (s + 7) / 8; jb++) a->sd_work.push_back(make_int2(0, (J << 8) | jb));
+            if (!simt) {
+                for (int64_t t = 0; t < (c + kTcWideRows - 1) / kTcWideRows; t++) a->pr_items.push_back({0, J, (int)t, 1});
+                for (int jb = 0; jb < (s + 7) / 8; jb++) a->sd_work.push_back(make_int2(0, (J << 8) | jb));
+            }
         }
         a->wd_lptr.push_back((int64_t)a->wd_items.size());
         a->row_lptr.push_back((int64_t)a->row_items.size());
@@ -1495,6 +1512,11 @@ using namespace selinv;
 // d_pdp: the panel X, the output and its mode).
 template <int OP>
 static void row_product(AdjData *a, int pd, int li, cudaStream_t st) {
+    const int r0 = (int)a->row_lptr[li], r1 = (int)a->row_lptr[li + 1];
+    if (r1 > r0) {   // the narrower wide supernodes: 32 x 32 blocks on the FP64 kernel
+        k_adj_rowprod<OP><<<r1 - r0, kThreads, 0, st>>>(a->d_desc, a->d_row + r0, r1 - r0);
+        note_launch();
+    }
     const int q0 = (int)a->sd_lptr[li], q1 = (int)a->sd_lptr[li + 1];
     if (q1 > q0) {
         k_small_digits<OP><<<q1 - q0, 256, 0, st>>>(a->d_desc, a->d_sdw + q0, q1 - q0, a->sd, a->d_sd_off, a->sdexp);
@@ -1628,9 +1650,8 @@ extern "C" int selinv_adjoint(selinv_plan plan, selinv_dtype dtype, const void *
             }
             const int i0 = a->sm_bptr[li * kNumBuckets], i1 = a->sm_bptr[(li + 1) * kNumBuckets];
             if (i1 > i0) { k_adj_ybar<<<i1 - i0, 256, 0, st>>>(a->d_desc, a->d_sm + i0, i1 - i0); note_launch(); }
-            const int r0 = (int)a->row_lptr[li], r1 = (int)a->row_lptr[li + 1];
             const int m0 = (int)a->mbp_lptr[li], m1 = (int)a->mbp_lptr[li + 1];
-            if (r1 > r0) row_product<RP_YBAR>(a, 0, li, st);
+            row_product<RP_YBAR>(a, 0, li, st);
             const int64_t v0 = a->vn_lptr[li], v1 = a->vn_lptr[li + 1];
             if (v1 > v0) { k_adj_vupd<<<(int)(v1 - v0), 256, 0, st>>>(a->d_desc, a->d_vn + v0, (int)(v1 - v0)); note_launch(); }
             const int64_t y0 = a->sy_wlptr[li], y1 = a->sy_wlptr[li + 1];
@@ -1656,12 +1677,12 @@ extern "C" int selinv_adjoint(selinv_plan plan, selinv_dtype dtype, const void *
                 const int b0 = a->sm_bptr[li * kNumBuckets + b], b1 = a->sm_bptr[li * kNumBuckets + b + 1];
                 launch_bucket(0, b, a->d_desc, a->d_sm + b0, b1 - b0, st);
             }
-            if (r1 > r0) {
-                row_product<RP_LHB>(a, 1, li, st);
+            row_product<RP_LHB>(a, 1, li, st);
+            if (m1 > m0) {
                 k_adj_rowprod<RP_MBP><<<m1 - m0, kThreads, 0, st>>>(a->d_desc, a->d_mbp + m0, m1 - m0);
                 note_launch();
-                row_product<RP_LBC>(a, 2, li, st);
             }
+            row_product<RP_LBC>(a, 2, li, st);
             // per-supernode s x s steps, batched over the level
             const int64_t c0 = a->c_lptr[li], c1 = a->c_lptr[li + 1];
             const int64_t j0 = a->j_lptr[li], j1 = a->j_lptr[li + 1];
@@ -1742,14 +1763,13 @@ extern "C" int selinv_factor_adjoint(selinv_plan plan, selinv_dtype dtype, const
                 const int b0 = a->sm_bptr[li * kNumBuckets + b], b1 = a->sm_bptr[li * kNumBuckets + b + 1];
                 launch_bucket(2, b, a->d_desc, a->d_sm + b0, b1 - b0, st);
             }
-            const int r0 = (int)a->row_lptr[li], r1 = (int)a->row_lptr[li + 1];
             const int m0 = (int)a->mbp_lptr[li], m1 = (int)a->mbp_lptr[li + 1];
-            if (r1 > r0) {
-                row_product<RP_FAC>(a, 3, li, st);
+            row_product<RP_FAC>(a, 3, li, st);
+            if (m1 > m0) {
                 k_adj_rowprod<RP_FNBP><<<m1 - m0, kThreads, 0, st>>>(a->d_desc, a->d_mbp + m0, m1 - m0);
                 note_launch();
-                row_product<RP_FABAR>(a, 4, li, st);
             }
+            row_product<RP_FABAR>(a, 4, li, st);
             const int64_t c0 = a->c_lptr[li], c1 = a->c_lptr[li + 1];
             const int64_t j0 = a->j_lptr[li], j1 = a->j_lptr[li + 1];
             if (c1 > c0) { k_fadj_nbar<<<(int)(c1 - c0), 256, 0, st>>>(a->d_desc, a->d_citems + c0, (int)(c1 - c0)); note_launch(); }
