@@ -863,9 +863,9 @@ constexpr int kFinChunk = 1024;   // entries of an s x s block per item of the p
 // k staged kGK at a time (one stage up to s = 128: one round of load latency).
 constexpr int kGT = 16;
 constexpr int kGK = 128;
-template <int Q>
-__global__ void __launch_bounds__(256) k_adj_gemm(const AdjDesc *__restrict__ ad, int op,
-                                                  const int2 *__restrict__ items, int nitems) {
+template <int Q, int op>
+__global__ void __launch_bounds__(256) k_adj_gemm(const AdjDesc *__restrict__ ad, const int2 *__restrict__ items,
+                                                  int nitems) {
     grid_dep_wait();
     constexpr int GT = Q == 1 ? kGT : kGT / 2;   // output tile side of the CTA
     constexpr int NT = GT * GT;                  // threads
@@ -914,10 +914,25 @@ __global__ void __launch_bounds__(256) k_adj_gemm(const AdjDesc *__restrict__ ad
     // a warp holds 32 / GT rows of the tile: warps past s skip the products,
     // and the last k stage stops at s
     const bool wact = i0 + (32 / GT) * (int)(threadIdx.x / 32) < s;
+    // every product has a triangular factor (M = L_JJ^{-1} and L_JJ are lower
+    // triangular): the k-range of the tile stops at its last row or column, or
+    // starts at its first -- half the FP64 work on average
+    int klo = 0, khi = s;
+    switch (op) {
+    case OP_SEL_T1: khi = min(s, i0 + GT); break;   // M(i, k): k <= i
+    case OP_SEL_W: khi = min(s, j0 + GT); break;    // M(j, k): k <= j
+    case OP_SEL_LB: klo = i0; break;                // M(k, i): k >= i
+    case OP_FAC_T2: klo = j0; break;                // N(j, k) = M(k, j) / D_k: k >= j
+    case OP_FAC_U: khi = min(s, i0 + GT); break;    // N(k, i) = M(i, k) / D_i: k <= i
+    case OP_FAC_T3: klo = i0; break;                // L_JJ(k, i): k >= i
+    case OP_FAC_G1: klo = j0; break;                // M(k, j): k >= j
+    default: klo = i0; break;                       // M(k, i): k >= i
+    }
     double acc = 0.0;
-    for (int k0 = 0; k0 < s; k0 += kGK) {
-        const int kn = s - k0 < kGK ? s - k0 : kGK;
+    for (int k0 = klo; k0 < khi; k0 += kGK) {
+        const int kn = khi - k0 < kGK ? khi - k0 : kGK;
         __syncthreads();
+#pragma unroll 4
         for (int e = threadIdx.x; e < GT * kn; e += NT) {
             const int r = e % GT, q = e / GT;
             As[r][q] = i0 + r < s ? a_at(i0 + r, k0 + q) : 0.0;
@@ -1129,12 +1144,26 @@ static cudaError_t configure_adjoint() {
 
 template <template <int> class KF> struct Dummy {};
 
+template <int OP>
+static void launch_gemm_op(AdjData *a, int64_t g0, int n, cudaStream_t st) {
+    if (n < kNumSMs) k_adj_gemm<4, OP><<<4 * n, kGT * kGT / 4, 0, st>>>(a->d_desc, a->d_gitems + g0, n);
+    else k_adj_gemm<1, OP><<<n, kGT * kGT, 0, st>>>(a->d_desc, a->d_gitems + g0, n);
+}
+
 static void launch_level_gemm(AdjData *a, int op, int li, cudaStream_t st) {
     const int64_t g0 = a->g_lptr[li], g1 = a->g_lptr[li + 1];
     const int n = (int)(g1 - g0);
     if (n <= 0) return;
-    if (n < kNumSMs) k_adj_gemm<4><<<4 * n, kGT * kGT / 4, 0, st>>>(a->d_desc, op, a->d_gitems + g0, n);
-    else k_adj_gemm<1><<<n, kGT * kGT, 0, st>>>(a->d_desc, op, a->d_gitems + g0, n);
+    switch (op) {
+    case OP_SEL_T1: launch_gemm_op<OP_SEL_T1>(a, g0, n, st); break;
+    case OP_SEL_W: launch_gemm_op<OP_SEL_W>(a, g0, n, st); break;
+    case OP_SEL_LB: launch_gemm_op<OP_SEL_LB>(a, g0, n, st); break;
+    case OP_FAC_T2: launch_gemm_op<OP_FAC_T2>(a, g0, n, st); break;
+    case OP_FAC_U: launch_gemm_op<OP_FAC_U>(a, g0, n, st); break;
+    case OP_FAC_T3: launch_gemm_op<OP_FAC_T3>(a, g0, n, st); break;
+    case OP_FAC_G1: launch_gemm_op<OP_FAC_G1>(a, g0, n, st); break;
+    default: launch_gemm_op<OP_FAC_G2>(a, g0, n, st); break;
+    }
     note_launch();
 }
 
