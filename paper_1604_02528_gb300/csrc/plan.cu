@@ -1609,6 +1609,20 @@ static int numeric_run(selinv_plan plan, selinv_dtype dtype, const void *L, cons
     if (rc) return rc;
     Schedule &S = plan->single;
     const int mode = p.opts.schedule;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    const bool capturing = st != nullptr && st != cudaStreamLegacy &&
+                           (cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone);
+    cudaGetLastError();
+    if (S.valid && S.key_dtype == dtype && S.mode == mode && !capturing &&
+        (S.key_L != L || S.key_D != D || S.key_Z != Z)) {
+        // only the caller's buffers changed: every kernel of the schedule
+        // reads them through the device descriptors, so those are rewritten
+        // in stream order and the schedule (and its graph) stays
+        S.h_descs.assign(1, make_desc(p, plan->ws[0], dtype, L, D, Z, mode == SELINV_SCHED_PERSISTENT));
+        if (cudaMemcpyAsync(S.d_descs, S.h_descs.data(), sizeof(ProbDesc), cudaMemcpyHostToDevice, st) != cudaSuccess)
+            return SELINV_ERR_CUDA;
+        S.key_L = L; S.key_D = D; S.key_Z = Z;
+    }
     if (!S.valid || S.key_L != L || S.key_D != D || S.key_Z != Z || S.key_dtype != dtype ||
         S.mode != mode) {
         std::vector<const PlanData *> plans{&p};

@@ -187,6 +187,34 @@ def test_replanning_reuses_cached_workspaces(native, cuda_device):
     native.selinv_release_cached_memory()
 
 
+def test_other_buffers_on_one_plan_are_read(native, cuda_device):
+    """Calls on one plan with other device buffers (another matrix of the same
+    pattern) keep its schedule and graph; the kernels must read the new
+    buffers (the descriptors are rewritten in stream order)."""
+    import torch
+    p = CASES[7][1]()
+    sym, L, D, Z = oracle_run(p)
+    v = p.values.copy()
+    v[p.diag_positions()] += 1.5
+    L2, D2 = oracle.ldlt(p.with_values(v), sym)
+    Z2 = oracle.selinv(sym, L2, D2)
+    plan = native.selinv_symbolic(sym.n, sym.nsuper, sym.super_ptr, sym.sparent, sym.rowptr, sym.rows)
+    bufs = []
+    for (Lh, Dh) in ((L, D), (L2, D2), (L, D)):
+        Lt = torch.from_numpy(Lh).cuda()
+        Dt = torch.from_numpy(np.ascontiguousarray(Dh)).cuda()
+        bufs.append((Lt, Dt, torch.full_like(Lt, float("nan"))))   # all alive: distinct addresses
+    s = torch.cuda.Stream()
+    for Lt, Dt, Zt in bufs:
+        native.selinv_numeric(plan, native.SELINV_F64, Lt, Dt, Zt, s)
+    s.synchronize()
+    assert native.selinv_status(plan) == 0
+    G = [b[2].cpu().numpy() for b in bufs]
+    assert oracle.block_errors(sym, G[0], Z).max() <= TOL
+    assert oracle.block_errors(sym, G[1], Z2).max() <= TOL
+    assert np.array_equal(G[0], G[2])
+
+
 def test_autotuned_plan_matches_oracle(native, cuda_device):
     """The first call tunes (engine, k-split, narrowest tensor-core supernode)
     on the caller's data; the tuned options stay valid and every result meets
