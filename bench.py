@@ -194,16 +194,23 @@ def kernel_source_hash(kernel: str) -> str:
     return h.hexdigest()[:16]
 
 
-def ncu_traffic(kernel: str):
+def options_tag(o) -> str:
+    """The options that decide a schedule's launch set (which supernodes run on
+    the tensor cores and how their k-ranges split)."""
+    return f"oz{o.oz_min_s}-st{o.split_target}-sm{o.split_min_steps}"
+
+
+def ncu_traffic(kernel: str, tag: str):
     """DRAM bytes per launch of `kernel` from the committed ncu summary, if it
-    was taken on the current kernel sources (else None)."""
+    was taken on the current kernel sources with the same launch set (the
+    options tag); else None."""
     path = os.path.join(ROOT, "profiles", "ncu_traffic.txt")
     if not os.path.exists(path):
         return None
     want = kernel_source_hash(kernel)
     for line in open(path):
         parts = line.split()
-        if len(parts) >= 3 and parts[0] == kernel and parts[1] == want:
+        if len(parts) >= 4 and parts[0] == kernel and parts[1] == want and parts[3] == tag:
             return float(parts[2])
     return None
 
@@ -558,7 +565,7 @@ def main():
             "k_selinv_tiny": mult * float(((2 * c_ * c_ * s_ + 2 * c_ * s_ * s_) * ~oz * (s_ <= 8) * (c_ <= 64)).sum())}
     f_dom = f_of[name]
     achieved = f_dom / (kms[dom] * 1e-3) / 1e9 if kms[dom] > 0 else None
-    traffic = ncu_traffic(name)
+    traffic = ncu_traffic(name, options_tag(topts))
     if name in ("k_selinv_oz", "k_selinv_tc", "k_diag", "k_diag_tc", "k_lhat_oz"):
         # FP64-exact products on bf16 tensor cores: 28 digit-pair products per FP64 product
         peak, unit, bound = peaks["bf16_tflops"], "TFLOP/s", "tensor"
@@ -569,7 +576,8 @@ def main():
         peak, unit, bound, ach = FP64_PEAK_GFLOPS, "GFLOP/s", "alu", achieved
         note = "FP64 FMA pipe: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (measured DFMA loop 1204)"
     roof = {"bound": bound, "achieved": round(ach, 3) if ach else None, "peak": peak, "unit": unit,
-            "frac": round(ach / peak, 4) if ach else None, "traffic": traffic, "kernel": name,
+            "frac": round(ach / peak, 4) if ach else None, "traffic": traffic,
+            "traffic_options": options_tag(topts), "kernel": name,
             "kernel_ms_per_step": round(kms[dom], 3), "launches_per_step": int(kcnt[dom]),
             "fp64_equiv_gflops": round(achieved, 2) if achieved else None,
             "kernel_ms_all": {k: round(v, 3) for k, v in zip(N.PROFILE_KINDS, kms)},
