@@ -209,6 +209,29 @@ int selinv_plan_set_opts(selinv_plan plan, const selinv_opts *opts);
 int selinv_numeric(selinv_plan plan, selinv_dtype dtype, const void *L_dev, const void *D_dev,
                    void *Ainv_dev, void *cuda_stream);
 
+/* The same selected inversion (Alg. 1) with host inputs and output: L and D
+ * are copied in and A^{-1} out, the copies overlapped with the traversal.
+ * The top levels' panels of L go first (the traversal starts on them while
+ * the rest is copied; the lower levels' normalization waits for it), and the
+ * panels of A^{-1} come back in groups of levels as soon as the traversal has
+ * passed them (a panel is final once its level is done).
+ *   L_host, D_host, Ainv_host  host buffers of selinv_plan_nnz / n /
+ *            selinv_plan_nnz elements, same layouts as above; pinned memory
+ *            for the copies to overlap (pageable memory works, serialized);
+ *            caller-owned, not touched after the stream reaches the end of
+ *            the call's work (Ainv_host is complete then).
+ *   L_dev, D_dev, Ainv_dev  device staging buffers of the same sizes,
+ *            caller-allocated (the call allocates nothing on the device
+ *            beyond the plan's scratch).
+ * Two copy streams of the plan run beside cuda_stream and are joined into it:
+ * synchronizing cuda_stream covers the whole call.  A call that autotunes,
+ * scans its inputs (debug_checks bit 0) or uses another schedule than the
+ * level one copies everything in, inverts and copies everything out on
+ * cuda_stream.  Not for a stream under capture (INVALID_ARG).
+ * Errors: INVALID_ARG, CUDA; device-side errors via selinv_status. */
+int selinv_numeric_host(selinv_plan plan, selinv_dtype dtype, const void *L_host, const void *D_host,
+                        void *Ainv_host, void *L_dev, void *D_dev, void *Ainv_dev, void *cuda_stream);
+
 /* Batched selected inversion: nitems independent problems (e.g. pole shifts
  * A - z_l S sharing one pattern, or different matrices), all tree levels of
  * all items merged into one level-scheduled (or persistent) launch sequence.

@@ -77,6 +77,7 @@ def _load() -> ct.CDLL:
         "selinv_plan_set_opts": (I, [P, P]),
         "selinv_plan_get_opts": (I, [P, P]),
         "selinv_numeric": (I, [P, I, P, P, P, P]),
+        "selinv_numeric_host": (I, [P, I, P, P, P, P, P, P, P]),
         "selinv_numeric_batched": (I, [I, P, P, P, P, P, P]),
         "selinv_numeric_profile": (I, [P, I, P, P, P, P, P, P]),
         "selinv_plan_set_matrix": (I, [P, I32, P, P]),
@@ -108,6 +109,7 @@ REQUIRED_SYMBOLS = ("selinv_default_opts", "selinv_analyse", "selinv_analysis_ge
                     "selinv_analysis_destroy", "selinv_symbolic", "selinv_plan_destroy",
                     "selinv_plan_nnz", "selinv_plan_panel_offset", "selinv_plan_stats",
                     "selinv_plan_get", "selinv_plan_set_opts", "selinv_plan_get_opts", "selinv_numeric",
+                    "selinv_numeric_host",
                     "selinv_numeric_batched", "selinv_numeric_profile", "selinv_plan_set_matrix", "selinv_factor",
                     "selinv_adjoint", "selinv_factor_adjoint", "selinv_status",
                     "selinv_error_string", "selinv_launch_count", "selinv_dinv_noalloc",
@@ -287,6 +289,29 @@ def selinv_numeric(plan: Plan, dtype: int, L, D, Ainv, stream=None):
     _need_panels(plan, dtype, [("L", L), ("Ainv", Ainv)], [("D", D)])
     _check(LIB.selinv_numeric(plan.handle, int(dtype), _dptr(L), _dptr(D), _dptr(Ainv),
                               _stream(stream)), "selinv_numeric")
+
+
+def _hptr(t, n_bytes: int, what: str) -> ct.c_void_p:
+    """Host pointer of a contiguous CPU tensor of at least n_bytes."""
+    if t.is_cuda:
+        raise ValueError(f"{what}: expected a CPU tensor")
+    if not t.is_contiguous():
+        raise ValueError(f"{what}: expected a contiguous tensor")
+    if t.numel() * t.element_size() < n_bytes:
+        raise ValueError(f"{what}: {t.numel() * t.element_size()} bytes, need {n_bytes}")
+    return ct.c_void_p(t.data_ptr())
+
+
+def selinv_numeric_host(plan: Plan, dtype: int, L_host, D_host, Ainv_host, L_dev, D_dev, Ainv_dev,
+                        stream=None):
+    """Host L, D in and A^{-1} out (CPU tensors, pinned for the copies to
+    overlap), through the caller's device staging buffers."""
+    es = 8 if int(dtype) == SELINV_F64 else 16
+    _need_panels(plan, dtype, [("L_dev", L_dev), ("Ainv_dev", Ainv_dev)], [("D_dev", D_dev)])
+    _check(LIB.selinv_numeric_host(plan.handle, int(dtype), _hptr(L_host, plan.nnz * es, "L_host"),
+                                   _hptr(D_host, plan.n * es, "D_host"),
+                                   _hptr(Ainv_host, plan.nnz * es, "Ainv_host"), _dptr(L_dev), _dptr(D_dev),
+                                   _dptr(Ainv_dev), _stream(stream)), "selinv_numeric_host")
 
 
 def selinv_numeric_lu(plan: Plan, dtype: int, L, Ut, Zl, Zu, stream=None):

@@ -9,6 +9,7 @@
 #include <atomic>
 #include <cstdint>
 #include <cstring>
+#include <functional>
 #include <memory>
 #include <new>
 #include <thread>
@@ -1255,10 +1256,20 @@ const char *launch_kind_name(int kind) {
     return kind >= 0 && kind < KL_NKINDS ? names[kind] : "?";
 }
 
+// Optional additions of a host-buffer call to the issue of a schedule: an
+// event the side stream waits for at its fork (the inputs it reads have
+// landed), and callbacks run before given launches (at the end for index
+// == the number of launches), in ascending order.
+struct IssueHooks {
+    cudaEvent_t side_wait = nullptr;
+    std::vector<int> mark_at;
+    std::function<cudaError_t(int)> mark;
+};
+
 // The launches in order on `st`, those marked `side` on the schedule's side
 // stream: it forks from `st` at its first launch and joins back before launch
 // join_at (or at the end).
-static cudaError_t issue(Schedule &S, cudaStream_t st, bool count) {
+static cudaError_t issue(Schedule &S, cudaStream_t st, bool count, const IssueHooks *hk = nullptr) {
     if (count) note_launch((int)S.launches.size());
     cudaError_t e0 = issue_pre(S, st);
     if (e0 != cudaSuccess) return e0;
@@ -1268,9 +1279,18 @@ static cudaError_t issue(Schedule &S, cudaStream_t st, bool count) {
         cudaError_t e = cudaEventRecord(S.ev_join, S.side);
         return e == cudaSuccess ? cudaStreamWaitEvent(st, S.ev_join, 0) : e;
     };
+    size_t g = 0;   // next hook mark
+    auto marks = [&](size_t i) -> cudaError_t {
+        for (; hk && g < hk->mark_at.size() && hk->mark_at[g] == (int)i; g++) {
+            const cudaError_t e = hk->mark((int)g);
+            if (e != cudaSuccess) return e;
+        }
+        return cudaSuccess;
+    };
     for (size_t i = 0; i < S.launches.size(); i++) {
         const Launch &L = S.launches[i];
-        cudaError_t e = cudaSuccess;
+        cudaError_t e = marks(i);
+        if (e != cudaSuccess) return e;
         if (forked && (int)i == S.join_at && (e = join()) != cudaSuccess) return e;
         cudaStream_t ls = st;
         if (L.side) {
@@ -1280,6 +1300,7 @@ static cudaError_t issue(Schedule &S, cudaStream_t st, bool count) {
                 if (!S.ev_join && (e = cudaEventCreateWithFlags(&S.ev_join, cudaEventDisableTiming)) != cudaSuccess) return e;
                 if ((e = cudaEventRecord(S.ev_fork, st)) != cudaSuccess) return e;
                 if ((e = cudaStreamWaitEvent(S.side, S.ev_fork, 0)) != cudaSuccess) return e;
+                if (hk && hk->side_wait && (e = cudaStreamWaitEvent(S.side, hk->side_wait, 0)) != cudaSuccess) return e;
                 forked = true;
             }
             ls = S.side;
@@ -1289,7 +1310,11 @@ static cudaError_t issue(Schedule &S, cudaStream_t st, bool count) {
         NvtxRange r(name);
         if ((e = launch_one(S, L, ls)) != cudaSuccess) return e;
     }
-    return forked ? join() : cudaSuccess;
+    if (forked) {
+        const cudaError_t e = join();
+        if (e != cudaSuccess) return e;
+    }
+    return marks(S.launches.size());
 }
 
 // The kernel-to-kernel edges of a captured level loop become programmatic
@@ -1430,6 +1455,7 @@ selinv_plan_s::~selinv_plan_s() {
     DeviceGuard g(data.device);   // free on the plan's device, whichever is current
     single.release();
     lu.release();
+    host.release();
     for (auto &b : batch_cache) b.sched.release();
     for (auto &w : ws) w.release();
     factor_release(this);
@@ -1599,8 +1625,19 @@ extern "C" int selinv_numeric(selinv_plan plan, selinv_dtype dtype, const void *
     return numeric_run(plan, dtype, L, D, Z, st);
 }
 
+static int numeric_prepare(selinv_plan plan, selinv_dtype dtype, const void *L, const void *D, void *Z,
+                           cudaStream_t st);
+
 static int numeric_run(selinv_plan plan, selinv_dtype dtype, const void *L, const void *D, void *Z,
                        cudaStream_t st) {
+    const int rc = numeric_prepare(plan, dtype, L, D, Z, st);
+    return rc ? rc : run_schedule(plan->single, st, plan->data.opts.use_graph != 0);
+}
+
+// The plan's schedule for (dtype, buffers), built or re-keyed, and the debug
+// scan of the inputs; nothing of the selected inversion is issued yet.
+static int numeric_prepare(selinv_plan plan, selinv_dtype dtype, const void *L, const void *D, void *Z,
+                           cudaStream_t st) {
     PlanData &p = plan->data;
     int rc = ensure_device(p);
     if (rc) return rc;
@@ -1650,7 +1687,159 @@ static int numeric_run(selinv_plan plan, selinv_dtype dtype, const void *L, cons
             return SELINV_ERR_CUDA;
         note_launch(2);
     }
-    return run_schedule(S, st, p.opts.use_graph != 0);
+    return SELINV_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Selected inversion from host buffers, the copies overlapped with the
+// traversal (level schedule with the side-stream normalization):
+//   H2D on one copy stream: D, the panels of the top levels' supernodes
+//   (the main stream waits for these), then the rest of L (the side stream,
+//   which normalizes the lower levels, waits for it at its fork);
+//   D2H on another copy stream: the panels of A^{-1} in groups of levels, each
+//   group as soon as the main stream has passed its last level (a panel of
+//   A^{-1} is final once its level is done: later levels only read it): the
+//   top levels at the join, then levels up to about half and four fifths of
+//   the rest's bytes, then the rest; the main stream waits for the last copy.
+// Panel ranges are the runs of consecutive supernodes of a group.  Other
+// schedules, and calls that autotune or scan their inputs, copy everything in,
+// run and copy everything out on the stream.
+// ---------------------------------------------------------------------------
+static cudaError_t host_pipe_init(HostPipe &h) {
+    cudaError_t e = cudaSuccess;
+    if (!h.cin && (e = cudaStreamCreateWithFlags(&h.cin, cudaStreamNonBlocking)) != cudaSuccess) return e;
+    if (!h.cout && (e = cudaStreamCreateWithFlags(&h.cout, cudaStreamNonBlocking)) != cudaSuccess) return e;
+    for (cudaEvent_t *ev : {&h.ev_top, &h.ev_rest, &h.ev_done})
+        if (!*ev && (e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming)) != cudaSuccess) return e;
+    while (h.ev_grp.size() < 4) {
+        cudaEvent_t ev;
+        if ((e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) != cudaSuccess) return e;
+        h.ev_grp.push_back(ev);
+    }
+    return cudaSuccess;
+}
+
+void HostPipe::release() {
+    if (cin) cudaStreamDestroy(cin);
+    if (cout) cudaStreamDestroy(cout);
+    for (cudaEvent_t ev : {ev_top, ev_rest, ev_done})
+        if (ev) cudaEventDestroy(ev);
+    for (cudaEvent_t ev : ev_grp) cudaEventDestroy(ev);
+    cin = cout = nullptr;
+    ev_top = ev_rest = ev_done = nullptr;
+    ev_grp.clear();
+}
+
+extern "C" int selinv_numeric_host(selinv_plan plan, selinv_dtype dtype, const void *L_host, const void *D_host,
+                                   void *Ainv_host, void *L_dev, void *D_dev, void *Ainv_dev, void *stream) {
+    NvtxRange nvtx_range("selinv_numeric_host");
+    if (!plan || (dtype != SELINV_F64 && dtype != SELINV_C128 && dtype != SELINV_C128H)) return SELINV_ERR_INVALID_ARG;
+    PlanData &p = plan->data;
+    if (p.ns == 0) return SELINV_OK;
+    if (!L_host || !D_host || !Ainv_host || !L_dev || !D_dev || !Ainv_dev || !aligned16(L_dev) ||
+        !aligned16(D_dev) || !aligned16(Ainv_dev))
+        return SELINV_ERR_INVALID_ARG;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (st != nullptr && st != cudaStreamLegacy &&
+        (cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone))
+        return SELINV_ERR_INVALID_ARG;   // host copies per call: not for a captured stream
+    const size_t es = elem_size(dtype);
+    const size_t lbytes = es * (size_t)p.nnz, dbytes = es * (size_t)p.n;
+    auto whole = [&]() -> int {   // copy in, run, copy out, all on the stream
+        if (cudaMemcpyAsync(L_dev, L_host, lbytes, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+            cudaMemcpyAsync(D_dev, D_host, dbytes, cudaMemcpyHostToDevice, st) != cudaSuccess)
+            return SELINV_ERR_CUDA;
+        const int rc = selinv_numeric(plan, dtype, L_dev, D_dev, Ainv_dev, stream);
+        if (rc) return rc;
+        return cudaMemcpyAsync(Ainv_host, Ainv_dev, lbytes, cudaMemcpyDeviceToHost, st) == cudaSuccess
+                   ? SELINV_OK : SELINV_ERR_CUDA;
+    };
+    if ((p.opts.autotune && !p.tuned[dtype]) || (p.opts.debug_checks & 1) || p.opts.schedule != SELINV_SCHED_LEVEL)
+        return whole();
+    int rc = numeric_prepare(plan, dtype, L_dev, D_dev, Ainv_dev, st);
+    if (rc) return rc;
+    Schedule &S = plan->single;
+    if (S.join_at < 0 || S.join_at >= (int)S.launches.size()) return whole();
+    HostPipe &h = plan->host;
+    if (host_pipe_init(h) != cudaSuccess) return SELINV_ERR_CUDA;
+    const int ltop = S.launches[S.join_at].level;
+    // runs of consecutive supernodes whose level is in [lo, hi), as byte ranges of the panels
+    auto runs = [&](int lo, int hi) {
+        std::vector<std::pair<size_t, size_t>> r;
+        for (int32_t K = 0; K < p.ns;) {
+            if (p.level[K] < lo || p.level[K] >= hi) { K++; continue; }
+            int32_t K1 = K;
+            while (K1 + 1 < p.ns && p.level[K1 + 1] >= lo && p.level[K1 + 1] < hi) K1++;
+            r.push_back({es * (size_t)p.panel_off[K], es * (size_t)(p.panel_off[K1 + 1] - p.panel_off[K])});
+            K = K1 + 1;
+        }
+        return r;
+    };
+    auto copies = [&](const std::vector<std::pair<size_t, size_t>> &r, const void *src, void *dst,
+                      cudaMemcpyKind kind, cudaStream_t cst) -> cudaError_t {
+        for (const auto &x : r) {
+            const cudaError_t e = cudaMemcpyAsync(static_cast<char *>(dst) + x.first,
+                                                  static_cast<const char *>(src) + x.first, x.second, kind, cst);
+            if (e != cudaSuccess) return e;
+        }
+        return cudaSuccess;
+    };
+    const int nl = p.nlevels;
+    // D2H groups: [0, ltop), then level bounds at ~1/2 and ~4/5 of the rest's bytes
+    std::vector<int> bounds{ltop};
+    {
+        std::vector<double> lb(nl, 0.0);
+        for (int32_t K = 0; K < p.ns; K++) lb[p.level[K]] += (double)(p.panel_off[K + 1] - p.panel_off[K]);
+        double rest = 0.0;
+        for (int l = ltop; l < nl; l++) rest += lb[l];
+        double acc = 0.0;
+        size_t f = 0;
+        const double frac[2] = {0.5, 0.8};
+        for (int l = ltop; l < nl && f < 2; l++) {
+            acc += lb[l];
+            while (f < 2 && acc >= frac[f] * rest) {
+                if (l + 1 < nl && l + 1 > bounds.back()) bounds.push_back(l + 1);
+                f++;
+            }
+        }
+    }
+    IssueHooks hk;
+    for (int b : bounds) {   // the first main launch of level b: all levels above it are done
+        int at = (int)S.launches.size();
+        for (int i = 0; i < (int)S.launches.size(); i++)
+            if (!S.launches[i].side && S.launches[i].level >= b) { at = i; break; }
+        hk.mark_at.push_back(at);
+    }
+    hk.mark_at.push_back((int)S.launches.size());   // the last group, after every launch
+    std::vector<int> lo_of{0};
+    for (int b : bounds) lo_of.push_back(b);
+    cudaError_t e = cudaSuccess;
+    hk.side_wait = h.ev_rest;
+    hk.mark = [&](int g) -> cudaError_t {
+        const int lo = lo_of[g], hi = g < (int)bounds.size() ? bounds[g] : nl;
+        cudaError_t x = cudaEventRecord(h.ev_grp[g], st);
+        if (x == cudaSuccess) x = cudaStreamWaitEvent(h.cout, h.ev_grp[g], 0);
+        if (x == cudaSuccess) x = copies(runs(lo, hi), Ainv_dev, Ainv_host, cudaMemcpyDeviceToHost, h.cout);
+        return x;
+    };
+    // inputs: everything that is on the stream before this call comes first
+    if ((e = cudaEventRecord(h.ev_done, st)) != cudaSuccess ||
+        (e = cudaStreamWaitEvent(h.cin, h.ev_done, 0)) != cudaSuccess ||
+        (e = cudaStreamWaitEvent(h.cout, h.ev_done, 0)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(D_dev, D_host, dbytes, cudaMemcpyHostToDevice, h.cin)) != cudaSuccess ||
+        (e = copies(runs(0, ltop), L_host, L_dev, cudaMemcpyHostToDevice, h.cin)) != cudaSuccess ||
+        (e = cudaEventRecord(h.ev_top, h.cin)) != cudaSuccess ||
+        (e = copies(runs(ltop, nl), L_host, L_dev, cudaMemcpyHostToDevice, h.cin)) != cudaSuccess ||
+        (e = cudaEventRecord(h.ev_rest, h.cin)) != cudaSuccess ||
+        (e = cudaStreamWaitEvent(st, h.ev_top, 0)) != cudaSuccess)
+        return SELINV_ERR_CUDA;
+    plan->last_stream = st;
+    if ((e = issue(S, st, true, &hk)) != cudaSuccess) return SELINV_ERR_CUDA;
+    // the stream's completion covers the last copies out
+    if ((e = cudaEventRecord(h.ev_done, h.cout)) != cudaSuccess || (e = cudaStreamWaitEvent(st, h.ev_done, 0)) != cudaSuccess)
+        return SELINV_ERR_CUDA;
+    return SELINV_OK;
 }
 
 // The LU form (nonsymmetric values): the DFMA kernels with the descriptor's

@@ -178,6 +178,14 @@ struct Schedule {
     void release();
 };
 
+// copy streams and events of selinv_numeric_host
+struct HostPipe {
+    cudaStream_t cin = nullptr, cout = nullptr;
+    cudaEvent_t ev_top = nullptr, ev_rest = nullptr, ev_done = nullptr;
+    std::vector<cudaEvent_t> ev_grp;
+    void release();
+};
+
 struct BatchEntry {
     int mode = -1;
     std::vector<struct selinv_plan_s *> plans;
@@ -258,6 +266,7 @@ struct selinv_plan_s {
     std::vector<selinv::Workspace> ws;  // ws[0]: single calls; ws[1..]: batch items
     selinv::Schedule single;
     selinv::Schedule lu;                // the LU form (selinv_numeric_lu)
+    selinv::HostPipe host;              // selinv_numeric_host's copy streams
     std::vector<selinv::BatchEntry> batch_cache;
     selinv::FactorData *factor = nullptr;
     cudaStream_t last_stream = nullptr;

@@ -215,6 +215,39 @@ def test_other_buffers_on_one_plan_are_read(native, cuda_device):
     assert np.array_equal(G[0], G[2])
 
 
+@pytest.mark.parametrize("name,make", [CASES[7], CASES[8], CASES[9]])
+def test_host_buffer_call_matches_device_call(native, cuda_device, name, make):
+    """selinv_numeric_host (host L, D in, A^{-1} out, the copies overlapped
+    with the traversal) gives the device call's result bit for bit, also on
+    a second call with other values of the pattern."""
+    import torch
+    p = make()
+    sym, L, D, Z = oracle_run(p)
+    G_dev, plan = gpu_selinv(native, sym, L, D)
+    dt = native.SELINV_C128 if L.dtype.kind == "c" else native.SELINV_F64
+    Lh = torch.from_numpy(L).pin_memory()
+    Dh = torch.from_numpy(np.ascontiguousarray(D)).pin_memory()
+    Zh = torch.full(Lh.shape, float("nan"), dtype=Lh.dtype).pin_memory()
+    Ld, Dd = torch.empty_like(Lh, device="cuda"), torch.empty_like(Dh, device="cuda")
+    Zd = torch.empty_like(Lh, device="cuda")
+    s = torch.cuda.Stream()
+    for _ in range(2):
+        Zh.fill_(float("nan"))
+        native.selinv_numeric_host(plan, dt, Lh, Dh, Zh, Ld, Dd, Zd, s)
+        s.synchronize()
+        assert native.selinv_status(plan) == 0
+        assert np.array_equal(Zh.numpy(), G_dev), name
+    if dt == native.SELINV_F64:
+        v = p.values.copy()
+        v[p.diag_positions()] += 1.5
+        L2, D2 = oracle.ldlt(p.with_values(v), sym)
+        Lh.copy_(torch.from_numpy(L2))
+        Dh.copy_(torch.from_numpy(np.ascontiguousarray(D2)))
+        native.selinv_numeric_host(plan, dt, Lh, Dh, Zh, Ld, Dd, Zd, s)
+        s.synchronize()
+        assert oracle.block_errors(sym, Zh.numpy(), oracle.selinv(sym, L2, D2)).max() <= TOL
+
+
 def test_autotuned_plan_matches_oracle(native, cuda_device):
     """The first call tunes (engine, k-split, narrowest tensor-core supernode)
     on the caller's data; the tuned options stay valid and every result meets
