@@ -6,6 +6,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <array>
 #include <atomic>
 #include <cstdint>
 #include <cstring>
@@ -468,12 +469,16 @@ ProbDesc make_desc(const PlanData &p, Workspace &w, int dtype, const void *L, co
 void Schedule::release() {
     if (graph) cudaGraphExecDestroy(graph);
     graph = nullptr;
+    if (graph_host) cudaGraphExecDestroy(graph_host);
+    graph_host = nullptr;
+    host_key.fill(nullptr);
     if (side) cudaStreamDestroy(side);
     if (ev_fork) cudaEventDestroy(ev_fork);
     if (ev_join) cudaEventDestroy(ev_join);
+    if (ev_mid) cudaEventDestroy(ev_mid);
     side = nullptr;
-    ev_fork = ev_join = nullptr;
-    join_at = -1;
+    ev_fork = ev_join = ev_mid = nullptr;
+    join_at = join_at2 = -1;
     dfree(d_descs); dfree(d_items); dfree(d_work); dfree(d_buckets); dfree(tcslab); dfree(d_red);
     d_descs = nullptr; d_items = nullptr; d_work = nullptr; d_buckets = nullptr; tcslab = nullptr; d_red = nullptr;
 }
@@ -510,33 +515,38 @@ int build_schedule(Schedule &S, const std::vector<const PlanData *> &plans,
         const int64_t c = p.rowptr[K + 1] - p.rowptr[K] - s;
         return !descs[i].lu && s <= 8 && c <= 64 && !ozok(i, s) && !zok(i, s);
     };
-    // Level schedule: the normalization (steps 1, 2, 2b) runs in two phases.
-    // The supernodes of the first `ltop` levels -- the top of the tree, a few
-    // large supernodes per level whose launches leave most SMs idle -- are
-    // normalized first on the main stream; the rest on a side stream, while
-    // the main stream traverses those levels (the traversal of a level reads
-    // the normalization of its own supernodes only); the main stream waits for
-    // the side stream before level ltop.
-    int ltop = 0;
+    // Level schedule: the normalization (steps 1, 2, 2b) runs in up to three
+    // phases.  The supernodes of the first `ltop` levels -- the top of the
+    // tree, a few large supernodes per level whose launches leave most SMs
+    // idle -- are normalized first on the main stream; those of the levels
+    // [ltop, lmid), then the rest, on a side stream, while the main stream
+    // traverses the levels above them (the traversal of a level reads the
+    // normalization of its own supernodes only).  The main stream waits for
+    // the side stream's first phase before level ltop and for the second
+    // before level lmid (two phases: lmid = the number of levels).
+    int ltop = 0, lmid = 0;
+    int nlev_all = 0;
+    for (int i = 0; i < np; i++) nlev_all = std::max(nlev_all, plans[i]->nlevels);
     if (mode == SELINV_SCHED_LEVEL && split_norm) {
-        int nlev = 0;
-        for (int i = 0; i < np; i++) nlev = std::max(nlev, plans[i]->nlevels);
         int64_t seen = 0;
-        for (int l = 0; l < nlev; l++) {
+        for (int l = 0; l < nlev_all; l++) {
             for (int i = 0; i < np; i++)
                 if (l < plans[i]->nlevels) seen += plans[i]->level_ptr[l + 1] - plans[i]->level_ptr[l];
-            if (seen > kTopSupernodes) break;
-            ltop = l + 1;
+            if (seen <= kTopSupernodes) ltop = l + 1;
+            if (seen <= kMidSupernodes) lmid = l + 1;
         }
-        if (ltop >= nlev) ltop = 0;   // the whole tree is "top": nothing to overlap
+        if (ltop >= nlev_all) ltop = 0;   // the whole tree is "top": nothing to overlap
+        if (ltop == 0 || lmid <= ltop || lmid >= nlev_all) lmid = nlev_all;
     }
-    const int nph = ltop > 0 ? 2 : 1;
+    const int nph = ltop == 0 ? 1 : (lmid < nlev_all ? 3 : 2);
+    auto phase_of = [&](int i, int32_t K) {
+        const int l = plans[i]->level[K];
+        return l < ltop ? 0 : (l < lmid ? 1 : 2);
+    };
     for (int ph = 0; ph < nph; ph++) {
         const size_t ph_first = S.launches.size();
-        // supernodes of this phase (both when there is one phase)
-        auto actn = [&](int i, int32_t K) {
-            return act(i, K) && (nph == 1 || (plans[i]->level[K] < ltop) == (ph == 0));
-        };
+        // supernodes of this phase (all when there is one phase)
+        auto actn = [&](int i, int32_t K) { return act(i, K) && (nph == 1 || phase_of(i, K) == ph); };
         // 1) L_KK^{-1}, Dinv for every supernode (one launch per dtype and size class)
         for (int dt = 0; dt < 2; dt++)
             for (int large = 1; large >= 0; large--) {
@@ -1040,7 +1050,8 @@ int build_schedule(Schedule &S, const std::vector<const PlanData *> &plans,
         int nlev = 0;
         for (int i = 0; i < np; i++) nlev = std::max(nlev, plans[i]->nlevels);
         for (int l = 0; l < nlev; l++) {
-            if (nph == 2 && l == ltop) S.join_at = (int)S.launches.size();
+            if (nph >= 2 && l == ltop) S.join_at = (int)S.launches.size();
+            if (nph == 3 && l == lmid) S.join_at2 = (int)S.launches.size();
             // tensor-core contraction of every eligible supernode of the level
             // (one launch per column-tile width), then their diagonal blocks
             std::vector<std::pair<int, int32_t>> oz;  // (problem, K)
@@ -1261,7 +1272,7 @@ const char *launch_kind_name(int kind) {
 // landed), and callbacks run before given launches (at the end for index
 // == the number of launches), in ascending order.
 struct IssueHooks {
-    cudaEvent_t side_wait = nullptr;
+    cudaEvent_t side_wait[2] = {nullptr, nullptr};   // before the side stream's first / second phase
     std::vector<int> mark_at;
     std::function<cudaError_t(int)> mark;
 };
@@ -1287,21 +1298,32 @@ static cudaError_t issue(Schedule &S, cudaStream_t st, bool count, const IssueHo
         }
         return cudaSuccess;
     };
+    int side_phase = 0;   // phase of the side stream's last launch
     for (size_t i = 0; i < S.launches.size(); i++) {
         const Launch &L = S.launches[i];
         cudaError_t e = marks(i);
         if (e != cudaSuccess) return e;
-        if (forked && (int)i == S.join_at && (e = join()) != cudaSuccess) return e;
+        if (forked && (int)i == S.join_at) {
+            if (S.join_at2 < 0) e = join();   // (two phases: the side stream's whole work)
+            else e = cudaStreamWaitEvent(st, S.ev_mid, 0);
+            if (e != cudaSuccess) return e;
+        }
+        if (forked && (int)i == S.join_at2 && (e = join()) != cudaSuccess) return e;
         cudaStream_t ls = st;
         if (L.side) {
             if (!forked) {
                 if (!S.side && (e = cudaStreamCreateWithFlags(&S.side, cudaStreamNonBlocking)) != cudaSuccess) return e;
-                if (!S.ev_fork && (e = cudaEventCreateWithFlags(&S.ev_fork, cudaEventDisableTiming)) != cudaSuccess) return e;
-                if (!S.ev_join && (e = cudaEventCreateWithFlags(&S.ev_join, cudaEventDisableTiming)) != cudaSuccess) return e;
+                for (cudaEvent_t *ev : {&S.ev_fork, &S.ev_join, &S.ev_mid})
+                    if (!*ev && (e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming)) != cudaSuccess) return e;
                 if ((e = cudaEventRecord(S.ev_fork, st)) != cudaSuccess) return e;
                 if ((e = cudaStreamWaitEvent(S.side, S.ev_fork, 0)) != cudaSuccess) return e;
-                if (hk && hk->side_wait && (e = cudaStreamWaitEvent(S.side, hk->side_wait, 0)) != cudaSuccess) return e;
                 forked = true;
+            }
+            if (L.side != side_phase) {   // the side stream enters a phase
+                if (side_phase == 1 && (e = cudaEventRecord(S.ev_mid, S.side)) != cudaSuccess) return e;
+                cudaEvent_t w = hk && L.side <= 2 ? hk->side_wait[L.side - 1] : nullptr;
+                if (w && (e = cudaStreamWaitEvent(S.side, w, 0)) != cudaSuccess) return e;
+                side_phase = L.side;
             }
             ls = S.side;
         }
@@ -1694,22 +1716,24 @@ static int numeric_prepare(selinv_plan plan, selinv_dtype dtype, const void *L, 
 // Selected inversion from host buffers, the copies overlapped with the
 // traversal (level schedule with the side-stream normalization):
 //   H2D on one copy stream: D, the panels of the top levels' supernodes
-//   (the main stream waits for these), then the rest of L (the side stream,
-//   which normalizes the lower levels, waits for it at its fork);
+//   (the main stream waits for these), then those of the side stream's
+//   first and second normalization phases (each phase waits for its own);
 //   D2H on another copy stream: the panels of A^{-1} in groups of levels, each
 //   group as soon as the main stream has passed its last level (a panel of
 //   A^{-1} is final once its level is done: later levels only read it): the
 //   top levels at the join, then levels up to about half and four fifths of
 //   the rest's bytes, then the rest; the main stream waits for the last copy.
-// Panel ranges are the runs of consecutive supernodes of a group.  Other
-// schedules, and calls that autotune or scan their inputs, copy everything in,
-// run and copy everything out on the stream.
+// Panel ranges are the runs of consecutive supernodes of a group.  With
+// pinned host buffers the call is captured once per set of buffers into a
+// graph (its copy nodes included) and replayed.  Other schedules, and calls
+// that autotune or scan their inputs, copy everything in, run and copy
+// everything out on the stream.
 // ---------------------------------------------------------------------------
 static cudaError_t host_pipe_init(HostPipe &h) {
     cudaError_t e = cudaSuccess;
     if (!h.cin && (e = cudaStreamCreateWithFlags(&h.cin, cudaStreamNonBlocking)) != cudaSuccess) return e;
     if (!h.cout && (e = cudaStreamCreateWithFlags(&h.cout, cudaStreamNonBlocking)) != cudaSuccess) return e;
-    for (cudaEvent_t *ev : {&h.ev_top, &h.ev_rest, &h.ev_done})
+    for (cudaEvent_t *ev : {&h.ev_top, &h.ev_mid, &h.ev_rest, &h.ev_done, &h.ev_in_done})
         if (!*ev && (e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming)) != cudaSuccess) return e;
     while (h.ev_grp.size() < 4) {
         cudaEvent_t ev;
@@ -1722,11 +1746,11 @@ static cudaError_t host_pipe_init(HostPipe &h) {
 void HostPipe::release() {
     if (cin) cudaStreamDestroy(cin);
     if (cout) cudaStreamDestroy(cout);
-    for (cudaEvent_t ev : {ev_top, ev_rest, ev_done})
+    for (cudaEvent_t ev : {ev_top, ev_mid, ev_rest, ev_done, ev_in_done})
         if (ev) cudaEventDestroy(ev);
     for (cudaEvent_t ev : ev_grp) cudaEventDestroy(ev);
     cin = cout = nullptr;
-    ev_top = ev_rest = ev_done = nullptr;
+    ev_top = ev_mid = ev_rest = ev_done = ev_in_done = nullptr;
     ev_grp.clear();
 }
 
@@ -1764,6 +1788,7 @@ extern "C" int selinv_numeric_host(selinv_plan plan, selinv_dtype dtype, const v
     HostPipe &h = plan->host;
     if (host_pipe_init(h) != cudaSuccess) return SELINV_ERR_CUDA;
     const int ltop = S.launches[S.join_at].level;
+    const int lmid = S.join_at2 >= 0 && S.join_at2 < (int)S.launches.size() ? S.launches[S.join_at2].level : p.nlevels;
     // runs of consecutive supernodes whose level is in [lo, hi), as byte ranges of the panels
     auto runs = [&](int lo, int hi) {
         std::vector<std::pair<size_t, size_t>> r;
@@ -1815,7 +1840,8 @@ extern "C" int selinv_numeric_host(selinv_plan plan, selinv_dtype dtype, const v
     std::vector<int> lo_of{0};
     for (int b : bounds) lo_of.push_back(b);
     cudaError_t e = cudaSuccess;
-    hk.side_wait = h.ev_rest;
+    hk.side_wait[0] = h.ev_mid;    // the side stream's phases wait for their panels of L
+    hk.side_wait[1] = h.ev_rest;
     hk.mark = [&](int g) -> cudaError_t {
         const int lo = lo_of[g], hi = g < (int)bounds.size() ? bounds[g] : nl;
         cudaError_t x = cudaEventRecord(h.ev_grp[g], st);
@@ -1823,23 +1849,68 @@ extern "C" int selinv_numeric_host(selinv_plan plan, selinv_dtype dtype, const v
         if (x == cudaSuccess) x = copies(runs(lo, hi), Ainv_dev, Ainv_host, cudaMemcpyDeviceToHost, h.cout);
         return x;
     };
-    // inputs: everything that is on the stream before this call comes first
-    if ((e = cudaEventRecord(h.ev_done, st)) != cudaSuccess ||
-        (e = cudaStreamWaitEvent(h.cin, h.ev_done, 0)) != cudaSuccess ||
-        (e = cudaStreamWaitEvent(h.cout, h.ev_done, 0)) != cudaSuccess ||
-        (e = cudaMemcpyAsync(D_dev, D_host, dbytes, cudaMemcpyHostToDevice, h.cin)) != cudaSuccess ||
-        (e = copies(runs(0, ltop), L_host, L_dev, cudaMemcpyHostToDevice, h.cin)) != cudaSuccess ||
-        (e = cudaEventRecord(h.ev_top, h.cin)) != cudaSuccess ||
-        (e = copies(runs(ltop, nl), L_host, L_dev, cudaMemcpyHostToDevice, h.cin)) != cudaSuccess ||
-        (e = cudaEventRecord(h.ev_rest, h.cin)) != cudaSuccess ||
-        (e = cudaStreamWaitEvent(st, h.ev_top, 0)) != cudaSuccess)
-        return SELINV_ERR_CUDA;
+    auto body = [&]() -> cudaError_t {
+        cudaError_t x;
+        // inputs: everything that is on the stream before this call comes first
+        if ((x = cudaEventRecord(h.ev_done, st)) != cudaSuccess ||
+            (x = cudaStreamWaitEvent(h.cin, h.ev_done, 0)) != cudaSuccess ||
+            (x = cudaStreamWaitEvent(h.cout, h.ev_done, 0)) != cudaSuccess ||
+            (x = cudaMemcpyAsync(D_dev, D_host, dbytes, cudaMemcpyHostToDevice, h.cin)) != cudaSuccess ||
+            (x = copies(runs(0, ltop), L_host, L_dev, cudaMemcpyHostToDevice, h.cin)) != cudaSuccess ||
+            (x = cudaEventRecord(h.ev_top, h.cin)) != cudaSuccess ||
+            (x = copies(runs(ltop, lmid), L_host, L_dev, cudaMemcpyHostToDevice, h.cin)) != cudaSuccess ||
+            (x = cudaEventRecord(h.ev_mid, h.cin)) != cudaSuccess ||
+            (x = copies(runs(lmid, nl), L_host, L_dev, cudaMemcpyHostToDevice, h.cin)) != cudaSuccess ||
+            (x = cudaEventRecord(h.ev_rest, h.cin)) != cudaSuccess ||
+            (x = cudaStreamWaitEvent(st, h.ev_top, 0)) != cudaSuccess)
+            return x;
+        if ((x = issue(S, st, false, &hk)) != cudaSuccess) return x;
+        // the stream's completion covers both copy streams
+        if ((x = cudaEventRecord(h.ev_in_done, h.cin)) != cudaSuccess ||
+            (x = cudaStreamWaitEvent(st, h.ev_in_done, 0)) != cudaSuccess ||
+            (x = cudaEventRecord(h.ev_done, h.cout)) != cudaSuccess)
+            return x;
+        return cudaStreamWaitEvent(st, h.ev_done, 0);
+    };
     plan->last_stream = st;
-    if ((e = issue(S, st, true, &hk)) != cudaSuccess) return SELINV_ERR_CUDA;
-    // the stream's completion covers the last copies out
-    if ((e = cudaEventRecord(h.ev_done, h.cout)) != cudaSuccess || (e = cudaStreamWaitEvent(st, h.ev_done, 0)) != cudaSuccess)
-        return SELINV_ERR_CUDA;
-    return SELINV_OK;
+    note_launch((int)S.launches.size());
+    // with pinned host buffers the whole call (copies, kernels, the streams'
+    // forks and joins) is captured once per set of buffers and replayed
+    auto pinned = [](const void *q) {
+        cudaPointerAttributes a;
+        const bool ok = cudaPointerGetAttributes(&a, q) == cudaSuccess && a.type == cudaMemoryTypeHost;
+        cudaGetLastError();
+        return ok;
+    };
+    if (p.opts.use_graph && st != nullptr && st != cudaStreamLegacy && pinned(L_host) && pinned(D_host) &&
+        pinned(Ainv_host)) {
+        const std::array<const void *, 6> key{L_host, D_host, Ainv_host, L_dev, D_dev, Ainv_dev};
+        if (!S.graph_host || S.host_key != key) {
+            if (S.graph_host) cudaGraphExecDestroy(S.graph_host);
+            S.graph_host = nullptr;
+            cudaGraph_t g = nullptr;
+            if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return SELINV_ERR_CUDA;
+            e = body();
+            const cudaError_t e2 = cudaStreamEndCapture(st, &g);
+            if (e != cudaSuccess || e2 != cudaSuccess || !g) {
+                if (g) cudaGraphDestroy(g);
+                return SELINV_ERR_CUDA;
+            }
+            if (programmatic_edges(g) != cudaSuccess) {
+                cudaGraphDestroy(g);
+                return SELINV_ERR_CUDA;
+            }
+            e = cudaGraphInstantiate(&S.graph_host, g, 0);
+            cudaGraphDestroy(g);
+            if (e != cudaSuccess) {
+                S.graph_host = nullptr;
+                return SELINV_ERR_CUDA;
+            }
+            S.host_key = key;
+        }
+        return cudaGraphLaunch(S.graph_host, st) == cudaSuccess ? SELINV_OK : SELINV_ERR_CUDA;
+    }
+    return body() == cudaSuccess ? SELINV_OK : SELINV_ERR_CUDA;
 }
 
 // The LU form (nonsymmetric values): the DFMA kernels with the descriptor's

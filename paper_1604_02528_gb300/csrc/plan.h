@@ -5,6 +5,7 @@
 
 #include <cstdint>
 #include <algorithm>
+#include <array>
 #include <memory>
 #include <utility>
 #include <vector>
@@ -133,6 +134,7 @@ constexpr int kTcWide = 128;   // launch bucket of the transposed tcgen05 kernel
 constexpr int kTcWideRows = 64;   // rows of C per item of that kernel
 constexpr int kAsmChunk = 1024;   // entries of an update matrix per extend-add item
 constexpr int kTopSupernodes = 16;   // level schedule: the top levels (up to this many supernodes) normalized first
+constexpr int kMidSupernodes = 256;  // ... and the levels up to this many normalized in the side stream's first phase
 
 struct Launch {
     int kind;    // KL_*
@@ -141,7 +143,7 @@ struct Launch {
     int64_t off;
     int count;
     int level;
-    int side = 0;   // 1: issued on the schedule's side stream (normalization of the lower levels)
+    int side = 0;   // 1, 2: issued on the schedule's side stream (normalization phases of the lower levels)
 };
 
 struct Schedule {
@@ -169,19 +171,22 @@ struct Schedule {
     long long spin_limit = 0;   // bound of every device wait of the schedule's kernels
     int wait_on_unset = 0;
     cudaGraphExec_t graph = nullptr;
+    // selinv_numeric_host's captured call and the buffers it was captured for
+    cudaGraphExec_t graph_host = nullptr;
+    std::array<const void *, 6> host_key{};
     // level schedule: the side stream that normalizes the lower levels'
     // supernodes while the main stream traverses the top levels, and the
     // launch before which the main stream waits for it (-1: none)
-    int join_at = -1;
+    int join_at = -1, join_at2 = -1;   // the second join: three phases
     cudaStream_t side = nullptr;
-    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_mid = nullptr;
     void release();
 };
 
 // copy streams and events of selinv_numeric_host
 struct HostPipe {
     cudaStream_t cin = nullptr, cout = nullptr;
-    cudaEvent_t ev_top = nullptr, ev_rest = nullptr, ev_done = nullptr;
+    cudaEvent_t ev_top = nullptr, ev_mid = nullptr, ev_rest = nullptr, ev_done = nullptr, ev_in_done = nullptr;
     std::vector<cudaEvent_t> ev_grp;
     void release();
 };
