@@ -626,29 +626,32 @@ def main():
     ev_in = [torch.cuda.Event() for _ in range(2)]     # inputs of a buffer landed
     ev_done = [torch.cuda.Event() for _ in range(2)]   # the inversion of a buffer finished
     ev_out = [torch.cuda.Event() for _ in range(2)]    # the result of a buffer was read back
+    def pipe_run(steps):
+        for i in range(steps + 1):
+            if i < steps:
+                b = i % 2
+                Lb_, Db_, Zb_, Zhb = bufs[b]
+                with torch.cuda.stream(cs_in):
+                    if i >= 2:
+                        cs_in.wait_event(ev_done[b])   # the buffer's previous inversion read its inputs
+                    Lb_.copy_(Lh, non_blocking=True)
+                    Db_.copy_(Dh, non_blocking=True)
+                    ev_in[b].record(cs_in)
+                stream.wait_event(ev_in[b])
+                if i >= 2:
+                    stream.wait_event(ev_out[b])       # its previous result was read back
+                N.selinv_numeric(plan, dt, Lb_, Db_, Zb_, stream)
+                ev_done[b].record(stream)
+            if i >= 1:
+                q = (i - 1) % 2
+                with torch.cuda.stream(cs_out):
+                    cs_out.wait_event(ev_done[q])
+                    bufs[q][3].copy_(bufs[q][2], non_blocking=True)
+                    ev_out[q].record(cs_out)
+    pipe_run(2)   # untimed: the first calls with the second buffer set build what they need
     torch.cuda.synchronize()
     t1 = time.perf_counter()
-    for i in range(e2e_steps + 1):
-        if i < e2e_steps:
-            b = i % 2
-            Lb_, Db_, Zb_, Zhb = bufs[b]
-            with torch.cuda.stream(cs_in):
-                if i >= 2:
-                    cs_in.wait_event(ev_done[b])   # the buffer's previous inversion read its inputs
-                Lb_.copy_(Lh, non_blocking=True)
-                Db_.copy_(Dh, non_blocking=True)
-                ev_in[b].record(cs_in)
-            stream.wait_event(ev_in[b])
-            if i >= 2:
-                stream.wait_event(ev_out[b])       # its previous result was read back
-            N.selinv_numeric(plan, dt, Lb_, Db_, Zb_, stream)
-            ev_done[b].record(stream)
-        if i >= 1:
-            q = (i - 1) % 2
-            with torch.cuda.stream(cs_out):
-                cs_out.wait_event(ev_done[q])
-                bufs[q][3].copy_(bufs[q][2], non_blocking=True)
-                ev_out[q].record(cs_out)
+    pipe_run(e2e_steps)
     torch.cuda.synchronize()
     pipe_s = (time.perf_counter() - t1) / e2e_steps
     del plan
