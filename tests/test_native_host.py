@@ -315,3 +315,6 @@ def test_binding_refuses_undersized_buffers(native):
             native.selinv_numeric(plan, dt, real, d, real)
     with pytest.raises(ValueError, match="need"):
         native.selinv_numeric(plan, native.SELINV_F64, real, real[:3], real)
+    # the host-buffer call checks its host buffers too (no device needed to refuse)
+    with pytest.raises(ValueError, match="need"):
+        native.selinv_numeric_host(plan, native.SELINV_F64, real[:5], real, real, real, real, real)
