@@ -44,6 +44,10 @@ constexpr int kNumSMs = 152;   // GB300
 constexpr int kFinY = 4;   // CTAs per supernode (grid y) of the per-supernode s x s steps
 constexpr int kAdjWideC = 256;   // rows of C from which any supernode takes the split (wide) path
 constexpr int kRowSimtS = 32;    // levels whose wide supernodes are this narrow: row products on the FP64 kernel
+// levels whose row products have fewer multiply-adds run them as 16 x 16 FP64
+// tiles: measured at the top of the 24^3 tree, 1.8e6 of them take 11-14 us
+// there against ~30 us (+ a digit pass) on tcgen05, 6e6 take 40-59 us
+constexpr double kSmallProdFma = 2.5e6;
 
 struct AdjDesc {
     const int32_t *super_ptr;
@@ -109,6 +113,11 @@ struct AdjData {
     // row block) of the split partials
     std::vector<int4> row_items, mbp_items;
     std::vector<int64_t> row_lptr, mbp_lptr;
+    // rg_items: (K, 16 x 16 tile) of the row products on levels of fewer than
+    // kSmallProdFma multiply-adds per product
+    std::vector<int2> rg_items;
+    std::vector<int64_t> rg_lptr;
+    int2 *d_rg = nullptr;
     std::vector<int2> dig_work;               // wide with c > 0: (0, K << 8 | 8-column block)
     std::vector<int64_t> dig_lptr;
     std::vector<std::vector<int>> tc_launch;  // per level: tcgen05 and reduction launches of `tcs`
@@ -969,6 +978,100 @@ __global__ void __launch_bounds__(256) k_adj_gemm(const AdjDesc *__restrict__ ad
     }
 }
 
+// A row product X B (c x s by s x s) of a wide supernode as 16 x 16 output
+// tiles (Q = 1, 256 threads) or their 8 x 8 quarters (Q = 4, 64 threads),
+// for the levels whose tcgen05 product launch would run only a few CTAs (the
+// top of the tree): the FP64 work spreads over every SM.  OP as in
+// k_adj_rowprod (YBAR, LHB, LBC, FAC, FABAR); items (K, tile), tiles
+// row-major over ceil(max(c, 1) / 16) x ceil(s / 16); the tiles of row 0 of
+// RP_YBAR also store S.
+template <int Q, int OP>
+__global__ void __launch_bounds__(256) k_adj_rowgemm(const AdjDesc *__restrict__ ad, const int2 *__restrict__ items,
+                                                     int nitems) {
+    grid_dep_wait();
+    constexpr int GT = Q == 1 ? kGT : kGT / 2;
+    constexpr int NT = GT * GT;
+    __shared__ double As[GT][kGK + 1], Bs[kGK][GT + 1];
+    const int w = blockIdx.x / Q, qd = blockIdx.x % Q;
+    if (w >= nitems) return;
+    const AdjDesc &A = *ad;
+    const int K = items[w].x;
+    const int fc = A.super_ptr[K];
+    const int s = A.super_ptr[K + 1] - fc;
+    const int64_t ld = A.rowptr[K + 1] - A.rowptr[K];
+    const int c = (int)(ld - s);
+    const int64_t off = A.panel_off[K];
+    const int ntj = (s + kGT - 1) / kGT;
+    const int ti = items[w].y / ntj;
+    const int i0 = ti * kGT + (Q == 1 ? 0 : (qd / 2) * GT);
+    const int j0 = (items[w].y % ntj) * kGT + (Q == 1 ? 0 : (qd % 2) * GT);
+    if (j0 >= s) return;
+    const double *Zb = A.Zb + off;
+    auto sym = [&](int k, int j) -> double {   // S from the cotangent's lower diagonal block
+        if (k == j) return Zb[(int64_t)j * ld + j];
+        return 0.5 * (k > j ? Zb[(int64_t)j * ld + k] : Zb[(int64_t)k * ld + j]);
+    };
+    if (OP == RP_YBAR && ti == 0 && qd < 2)   // S into YB's diagonal block, this tile's columns
+        for (int e = threadIdx.x; e < s * GT; e += NT) {
+            const int k = e % s, j = j0 + e / s;
+            if (j < s) A.YB[off + (int64_t)j * ld + k] = sym(k, j);
+        }
+    if (i0 >= c) return;
+    auto a_at = [&](int i, int k) -> double {   // X(i, k), i a row of C
+        const int64_t e = off + (int64_t)k * ld + s + i;
+        if (OP == RP_YBAR) return A.LD[e];
+        if (OP == RP_LHB) return A.Z[e];
+        if (OP == RP_LBC) return A.G[e];
+        if (OP == RP_FAC) return A.L[e] * A.D[fc + k];
+        return A.Lb[e];
+    };
+    auto b_at = [&](int k, int j) -> double {   // B(k, j)
+        if (OP == RP_YBAR) return sym(k, j);
+        if (OP == RP_LHB) return A.YB[off + (int64_t)j * ld + k];
+        if (OP == RP_LBC) return A.Linv[A.linv_off[K] + (int64_t)k * s + j];
+        if (OP == RP_FAC) return k == j ? 1.0 : (k < j ? A.L[off + (int64_t)k * ld + j] : 0.0);   // L_KK(j, k)
+        return k >= j ? A.Linv[A.linv_off[K] + (int64_t)j * s + k] / A.D[fc + k] : 0.0;
+    };
+    // triangular factors: M^T (LBC) and L_KK^T (FAC) vanish for k > j,
+    // D^{-1} M (FABAR) for k < j
+    int klo = 0, khi = s;
+    if (OP == RP_LBC || OP == RP_FAC) khi = min(s, j0 + GT);
+    if (OP == RP_FABAR) klo = j0;
+    const int tx = threadIdx.x % GT, ty = threadIdx.x / GT;
+    const bool wact = i0 + (32 / GT) * (int)(threadIdx.x / 32) < c;
+    double acc = 0.0;
+    for (int k0 = klo; k0 < khi; k0 += kGK) {
+        const int kn = khi - k0 < kGK ? khi - k0 : kGK;
+        __syncthreads();
+#pragma unroll 4
+        for (int e = threadIdx.x; e < GT * kn; e += NT) {
+            const int r = e % GT, q = e / GT;
+            As[r][q] = i0 + r < c ? a_at(i0 + r, k0 + q) : 0.0;
+            Bs[q][r] = j0 + r < s ? b_at(k0 + q, j0 + r) : 0.0;
+        }
+        __syncthreads();
+        if (wact) {
+            double a2 = 0.0;
+            int q = 0;
+#pragma unroll 4
+            for (; q + 1 < kn; q += 2) {
+                acc = fma(As[ty][q], Bs[q][tx], acc);
+                a2 = fma(As[ty][q + 1], Bs[q + 1][tx], a2);
+            }
+            if (q < kn) acc = fma(As[ty][q], Bs[q][tx], acc);
+            acc += a2;
+        }
+    }
+    const int i = i0 + ty, j = j0 + tx;
+    if (i >= c || j >= s) return;
+    const int64_t e = off + (int64_t)j * ld + s + i;
+    if (OP == RP_YBAR) A.YB[e] = A.Zb[e] - acc;
+    else if (OP == RP_LHB) A.G[e] -= acc;
+    else if (OP == RP_LBC) A.Lb[e] = acc;
+    else if (OP == RP_FAC) A.G[e] = acc;
+    else A.Ab[e] = acc;
+}
+
 // selinv adjoint: Mbar = sum of the tile partials + 2 D^{-1} T1 (T1 = M S);
 // items (J, chunk of kFinChunk entries | ntiles << 16)
 __global__ void __launch_bounds__(256) k_adj_sel_mbar(const AdjDesc *__restrict__ ad,
@@ -1199,7 +1302,7 @@ void adjoint_release(void *p) {
     fr(a->d_gitems); fr(a->d_citems); fr(a->d_js); fr(a->d_cz); fr(a->d_vitems);
     fr(a->YB); fr(a->Zb); fr(a->Lbw); fr(a->Ab); fr(a->fin); fr(a->d_desc); fr(a->d_pdesc);
     fr(a->V);
-    fr(a->d_sm); fr(a->d_wd); fr(a->d_row); fr(a->d_mbp); fr(a->d_dig); fr(a->d_tcdesc); fr(a->cy);
+    fr(a->d_sm); fr(a->d_wd); fr(a->d_row); fr(a->d_rg); fr(a->d_mbp); fr(a->d_dig); fr(a->d_tcdesc); fr(a->cy);
     fr(a->d_pr); fr(a->d_sdw); fr(a->sd); fr(a->d_sd_off); fr(a->sdexp); fr(a->d_pdp);
     fr(a->d_syw); fr(a->d_sy); fr(a->d_vn); fr(a->sy); fr(a->d_sy_off); fr(a->syexp); fr(a->d_sydesc);
     if (a->g_sel) cudaGraphExecDestroy(a->g_sel);
@@ -1361,10 +1464,10 @@ static int adj_split(selinv_plan_s *plan) {
     const int key = o.fast_contraction != 0 ? std::max(8, o.oz_min_s) : 0;
     if (key == a->split_key) return SELINV_OK;
     auto fr = [](void *q) { if (q) cudaFree(q); };
-    fr(a->d_sm); fr(a->d_wd); fr(a->d_row); fr(a->d_mbp); fr(a->d_dig);
+    fr(a->d_sm); fr(a->d_wd); fr(a->d_row); fr(a->d_rg); fr(a->d_mbp); fr(a->d_dig);
     fr(a->d_pr); fr(a->d_sdw); fr(a->sd); fr(a->d_sd_off);
     fr(a->d_syw); fr(a->d_sy); fr(a->d_vn); fr(a->sy); fr(a->d_sy_off);
-    a->d_sm = a->d_wd = nullptr; a->d_row = a->d_mbp = nullptr; a->d_dig = nullptr;
+    a->d_sm = a->d_wd = nullptr; a->d_row = a->d_mbp = nullptr; a->d_dig = nullptr; a->d_rg = nullptr;
     a->d_pr = nullptr; a->d_sdw = nullptr; a->sd = nullptr; a->d_sd_off = nullptr;
     a->d_syw = nullptr; a->d_sy = nullptr; a->d_vn = nullptr; a->sy = nullptr; a->d_sy_off = nullptr;
     a->sy_work.clear(); a->sy_items.clear(); a->vn_items.clear();
@@ -1376,6 +1479,7 @@ static int adj_split(selinv_plan_s *plan) {
     a->tcn.release();
     a->tcn.launches.clear();
     a->sm_items.clear(); a->wd_items.clear(); a->row_items.clear(); a->mbp_items.clear(); a->dig_work.clear();
+    a->rg_items.clear(); a->rg_lptr.assign(1, 0);
     a->pr_items.clear(); a->sd_work.clear();
     a->sm_bptr.assign(1, 0); a->wd_lptr.assign(1, 0); a->row_lptr.assign(1, 0); a->mbp_lptr.assign(1, 0); a->dig_lptr.assign(1, 0);
     a->pr_lptr.assign(1, 0); a->sd_lptr.assign(1, 0);
@@ -1405,6 +1509,14 @@ static int adj_split(selinv_plan_s *plan) {
             if (wideK(J)) wmax = std::max(wmax, p.super_ptr[J + 1] - p.super_ptr[J]);
         }
         const bool simt = wmax <= kRowSimtS;
+        double fma = 0.0;   // multiply-adds of one of the level's row products
+        for (int64_t e = p.level_ptr[l]; e < p.level_ptr[l + 1]; e++) {
+            const int32_t J = p.level_list[e];
+            if (!wideK(J)) continue;
+            const double sj = p.super_ptr[J + 1] - p.super_ptr[J];
+            fma += (double)(p.rowptr[J + 1] - p.rowptr[J] - (int64_t)sj) * sj * sj;
+        }
+        const bool small = !simt && fma < kSmallProdFma;
         for (int64_t e = p.level_ptr[l]; e < p.level_ptr[l + 1]; e++) {
             const int32_t J = p.level_list[e];
             const int s = p.super_ptr[J + 1] - p.super_ptr[J];
@@ -1420,13 +1532,17 @@ static int adj_split(selinv_plan_s *plan) {
                     for (int h = 0; h < (s + 31) / 32; h++) a->mbp_items.push_back(make_int4(J, t, ch, h));
             if (c > 0)
                 for (int jb = 0; jb < (s + 7) / 8; jb++) a->dig_work.push_back(make_int2(0, (J << 8) | jb));
-            if (!simt) {
+            if (small) {
+                const int ntj = (s + kGT - 1) / kGT, nti = (int)std::max<int64_t>(1, (c + kGT - 1) / kGT);
+                for (int t = 0; t < nti * ntj; t++) a->rg_items.push_back(make_int2(J, t));
+            } else if (!simt) {
                 for (int64_t t = 0; t < (c + kTcWideRows - 1) / kTcWideRows; t++) a->pr_items.push_back({0, J, (int)t, 1});
                 for (int jb = 0; jb < (s + 7) / 8; jb++) a->sd_work.push_back(make_int2(0, (J << 8) | jb));
             }
         }
         a->wd_lptr.push_back((int64_t)a->wd_items.size());
         a->row_lptr.push_back((int64_t)a->row_items.size());
+        a->rg_lptr.push_back((int64_t)a->rg_items.size());
         a->mbp_lptr.push_back((int64_t)a->mbp_items.size());
         a->dig_lptr.push_back((int64_t)a->dig_work.size());
         a->pr_lptr.push_back((int64_t)a->pr_items.size());
@@ -1465,6 +1581,7 @@ static int adj_split(selinv_plan_s *plan) {
     }
     int rc;
     if ((rc = upl(&a->d_sm, a->sm_items)) || (rc = upl(&a->d_wd, a->wd_items)) || (rc = upl(&a->d_row, a->row_items)) ||
+        (rc = upl(&a->d_rg, a->rg_items)) ||
         (rc = upl(&a->d_mbp, a->mbp_items)) || (rc = upl(&a->d_dig, a->dig_work)) ||
         (rc = upl(&a->d_pr, a->pr_items)) || (rc = upl(&a->d_sdw, a->sd_work)) || (rc = upl(&a->d_sd_off, sd_off)) ||
         (rc = upl(&a->d_syw, a->sy_work)) || (rc = upl(&a->d_sy, a->sy_items)) || (rc = upl(&a->d_vn, a->vn_items)) ||
@@ -1544,6 +1661,14 @@ static void row_product(AdjData *a, int pd, int li, cudaStream_t st) {
     const int r0 = (int)a->row_lptr[li], r1 = (int)a->row_lptr[li + 1];
     if (r1 > r0) {   // the narrower wide supernodes: 32 x 32 blocks on the FP64 kernel
         k_adj_rowprod<OP><<<r1 - r0, kThreads, 0, st>>>(a->d_desc, a->d_row + r0, r1 - r0);
+        note_launch();
+    }
+    const int g0 = (int)a->rg_lptr[li], g1 = (int)a->rg_lptr[li + 1];
+    if (g1 > g0) {   // the top levels: 16 x 16 tiles (8 x 8 quarters) on the FP64 kernel
+        if (g1 - g0 < kNumSMs)
+            k_adj_rowgemm<4, OP><<<4 * (g1 - g0), kGT * kGT / 4, 0, st>>>(a->d_desc, a->d_rg + g0, g1 - g0);
+        else
+            k_adj_rowgemm<1, OP><<<g1 - g0, kGT * kGT, 0, st>>>(a->d_desc, a->d_rg + g0, g1 - g0);
         note_launch();
     }
     const int q0 = (int)a->sd_lptr[li], q1 = (int)a->sd_lptr[li + 1];
