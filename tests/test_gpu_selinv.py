@@ -237,6 +237,11 @@ def test_host_buffer_call_matches_device_call(native, cuda_device, name, make):
         s.synchronize()
         assert native.selinv_status(plan) == 0
         assert np.array_equal(Zh.numpy(), G_dev), name
+    # pageable host buffers: the same result (the copies then serialize)
+    Zp = torch.full(Lh.shape, float("nan"), dtype=Lh.dtype)
+    native.selinv_numeric_host(plan, dt, Lh.clone(), Dh.clone(), Zp, Ld, Dd, Zd, s)
+    s.synchronize()
+    assert np.array_equal(Zp.numpy(), G_dev), name
     if dt == native.SELINV_F64:
         v = p.values.copy()
         v[p.diag_positions()] += 1.5
