@@ -239,7 +239,8 @@ def test_host_buffer_call_matches_device_call(native, cuda_device, name, make):
         assert np.array_equal(Zh.numpy(), G_dev), name
     # pageable host buffers: the same result (the copies then serialize)
     Zp = torch.full(Lh.shape, float("nan"), dtype=Lh.dtype)
-    native.selinv_numeric_host(plan, dt, Lh.clone(), Dh.clone(), Zp, Ld, Dd, Zd, s)
+    native.selinv_numeric_host(plan, dt, torch.from_numpy(L), torch.from_numpy(np.ascontiguousarray(D)), Zp,
+                               Ld, Dd, Zd, s)
     s.synchronize()
     assert np.array_equal(Zp.numpy(), G_dev), name
     if dt == native.SELINV_F64:
