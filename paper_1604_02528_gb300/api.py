@@ -96,6 +96,27 @@ class SelInvContext:
         N.selinv_numeric(self.plan, dt, L, D, out, stream)
         return out
 
+    def selinv_host(self, L_host, D_host, out=None, stream=None):
+        """Selected inverse of host panels (CPU tensors; pinned for the copies
+        to overlap the traversal), returned in a host tensor (pinned when it
+        is allocated here).  The device staging buffers are kept on the
+        context and reused; synchronizes the stream before returning."""
+        import torch
+        dt = selinv_dtype_of(L_host, self.hermitian)
+        if out is None:
+            out = torch.empty(self.nnz, dtype=torch_dtype(dt)).pin_memory()
+        st = getattr(self, "_host_staging", None)
+        if st is None or st[0].dtype != L_host.dtype:
+            st = (torch.empty(self.nnz, dtype=L_host.dtype, device="cuda"),
+                  torch.empty(self.n, dtype=D_host.dtype, device="cuda"),
+                  torch.empty(self.nnz, dtype=L_host.dtype, device="cuda"))
+            self._host_staging = st
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        N.selinv_numeric_host(self.plan, dt, L_host, D_host, out, st[0], st[1], st[2], stream)
+        stream.synchronize()
+        return out
+
     def select(self, rows, cols) -> np.ndarray:
         """Restrict later selected inversions to the entries (rows[e], cols[e])
         (and the supernodes they need); returns their panel positions.  Empty

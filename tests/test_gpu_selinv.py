@@ -254,6 +254,18 @@ def test_host_buffer_call_matches_device_call(native, cuda_device, name, make):
         assert oracle.block_errors(sym, Zh.numpy(), oracle.selinv(sym, L2, D2)).max() <= TOL
 
 
+def test_context_host_call_matches_oracle(native, cuda_device):
+    """SelInvContext.selinv_host: host panels in, host A^{-1} out."""
+    import torch
+    from paper_1604_02528_gb300.api import SelInvContext
+    p = synth.laplacian_3d(12, seed=8)
+    sym, L, D, Z = oracle_run(p)
+    ctx = SelInvContext.from_problem(p)
+    G = ctx.selinv_host(torch.from_numpy(L).pin_memory(), torch.from_numpy(np.ascontiguousarray(D)).pin_memory())
+    assert ctx.status() == 0
+    assert oracle.block_errors(sym, G.numpy(), Z).max() <= TOL
+
+
 def test_autotuned_plan_matches_oracle(native, cuda_device):
     """The first call tunes (engine, k-split, narrowest tensor-core supernode)
     on the caller's data; the tuned options stay valid and every result meets
